@@ -1,0 +1,173 @@
+"""FP64 CPU oracle for optimal Lipschitz interpolation (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg
+may import this package.  It is the checker the CUDA library is compared against:
+it shares no code with the library (different language, no common header or
+table) and never calls it.  ``build()`` compiles ``lipfit_oracle.c`` with gcc into
+``oracle/_build/``; the functions below are numpy front ends to it.
+
+Passages followed (all in the C file's header): Sec. 3 Eq. (upperlower) and
+Eq. (eq:g) for the envelopes and midpoint, Sec. 4.1 Eq. (distmon) for the
+monotone distance, Sec. 5 for the Lipschitz-constant estimate, and Table 1
+("differentiable almost everywhere") for the gradient.
+
+``Oracle(path)`` binds any build of the same C source; the tests use it to check
+that deliberately broken copies of the source fail the pins.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SOURCE = os.path.join(_HERE, "lipfit_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liblipfit_oracle.so")
+
+NORM_L1, NORM_L2, NORM_LINF = 1, 2, 3
+
+
+def compile_source(src: str, out: str) -> str:
+    """gcc -O2, no fast-math, no FMA contraction: plain IEEE double arithmetic."""
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-fno-fast-math", "-pthread", src, "-o", tmp, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(SOURCE):
+        compile_source(SOURCE, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _mon(mon, d):
+    if mon is None:
+        return None
+    m = np.ascontiguousarray(mon, dtype=np.int8)
+    assert m.shape == (d,)
+    return m
+
+
+def default_threads() -> int:
+    return os.cpu_count() or 1
+
+
+class EvalResult(dict):
+    """hi, lo, g, idx_up, idx_lo, gap_up, gap_lo (all numpy arrays)."""
+
+    def __getattr__(self, k):
+        return self[k]
+
+
+class Oracle:
+    """numpy front end to one compiled copy of the oracle's C source."""
+
+    def __init__(self, path: str):
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        lib.oracle_eval.argtypes = [P, P, i64, i32, f64, i32, P, P, P, i64, P, P, P, P, P, P, P, i32]
+        lib.oracle_estimate_M.argtypes = [P, P, i64, i32, i32, P, P, P, P, i32]
+        lib.oracle_estimate_M_rows.argtypes = [P, P, i64, i32, i32, P, i64, i64, P, P, P]
+        lib.oracle_grad.argtypes = [P, P, i64, i32, f64, i32, P, P, P, i64, P, P, P, P, P, P]
+        for fn in (lib.oracle_eval, lib.oracle_estimate_M, lib.oracle_estimate_M_rows, lib.oracle_grad):
+            fn.restype = ctypes.c_int
+        self.lib = lib
+
+    def evaluate(self, X, y, Q, M: float, norm: int = NORM_L2, mon=None, w=None,
+                 nthreads: Optional[int] = None) -> EvalResult:
+        """H_up, H_lo, g and the argmin/argmax data indices for each query row of Q."""
+        X, y, Q, w = _f64(X), _f64(y), _f64(Q), _f64(w)
+        N, d = X.shape
+        nq = Q.shape[0]
+        mon = _mon(mon, d)
+        out = {k: np.empty(nq) for k in ("hi", "lo", "g", "gap_up", "gap_lo")}
+        iu = np.empty(nq, np.int64)
+        il = np.empty(nq, np.int64)
+        rc = self.lib.oracle_eval(_ptr(X), _ptr(y), N, d, float(M), int(norm), _ptr(mon), _ptr(w),
+                                  _ptr(Q), nq, _ptr(out["hi"]), _ptr(out["lo"]), _ptr(out["g"]),
+                                  _ptr(iu), _ptr(il), _ptr(out["gap_up"]), _ptr(out["gap_lo"]),
+                                  nthreads or default_threads())
+        if rc != 0:
+            raise ValueError("oracle_eval: bad arguments")
+        return EvalResult(idx_up=iu, idx_lo=il, **out)
+
+    def estimate_M(self, X, y, norm: int = NORM_L2, w=None, nthreads: Optional[int] = None):
+        """(M_est, i, j): max over i<j of |y_i-y_j| / dist(x_i,x_j), lowest (i,j) on ties."""
+        X, y, w = _f64(X), _f64(y), _f64(w)
+        N, d = X.shape
+        M, i, j = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        rc = self.lib.oracle_estimate_M(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), ctypes.byref(M),
+                                        ctypes.byref(i), ctypes.byref(j), nthreads or default_threads())
+        if rc != 0:
+            raise ValueError("oracle_estimate_M: bad arguments")
+        return M.value, i.value, j.value
+
+    def estimate_M_rows(self, X, y, i0: int, i1: int, norm: int = NORM_L2, w=None):
+        """Single-threaded M_est restricted to rows i in [i0, i1) (pairs i<j)."""
+        X, y, w = _f64(X), _f64(y), _f64(w)
+        N, d = X.shape
+        M, i, j = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        self.lib.oracle_estimate_M_rows(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), int(i0), int(i1),
+                                        ctypes.byref(M), ctypes.byref(i), ctypes.byref(j))
+        return M.value, i.value, j.value
+
+    def gradient(self, X, y, Q, M: float, idx_up, idx_lo, gbar=None, norm: int = NORM_L2,
+                 mon=None, w=None):
+        """(grad_Q [nq,d], grad_y [N], grad_M) of sum_q gbar_q g(q) at the given argmin/argmax."""
+        X, y, Q, w = _f64(X), _f64(y), _f64(Q), _f64(w)
+        N, d = X.shape
+        nq = Q.shape[0]
+        mon = _mon(mon, d)
+        iu = np.ascontiguousarray(idx_up, np.int64)
+        il = np.ascontiguousarray(idx_lo, np.int64)
+        gb = _f64(gbar) if gbar is not None else None
+        gQ = np.zeros((nq, d))
+        gy = np.zeros(N)
+        gM = ctypes.c_double()
+        rc = self.lib.oracle_grad(_ptr(X), _ptr(y), N, d, float(M), int(norm), _ptr(mon), _ptr(w),
+                                  _ptr(Q), nq, _ptr(iu), _ptr(il), _ptr(gb), _ptr(gQ), _ptr(gy),
+                                  ctypes.byref(gM))
+        if rc != 0:
+            raise ValueError("oracle_grad: bad arguments")
+        return gQ, gy, gM.value
+
+
+_default: Optional[Oracle] = None
+
+
+def default() -> Oracle:
+    global _default
+    if _default is None:
+        _default = Oracle(build())
+    return _default
+
+
+def evaluate(*a, **k) -> EvalResult:
+    return default().evaluate(*a, **k)
+
+
+def estimate_M(*a, **k):
+    return default().estimate_M(*a, **k)
+
+
+def estimate_M_rows(*a, **k):
+    return default().estimate_M_rows(*a, **k)
+
+
+def gradient(*a, **k):
+    return default().gradient(*a, **k)

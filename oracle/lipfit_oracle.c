@@ -1,0 +1,289 @@
+/*
+ * FP64 brute-force oracle for optimal Lipschitz interpolation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the checker that the CUDA library is
+ * compared against; only the tests, the package smoke check and the benchmark's
+ * CPU-baseline leg may load it.  It shares no code, header, table or constant
+ * with the CUDA path and never calls it.
+ *
+ * Everything is computed in IEEE double with default rounding, by the plain
+ * definitions, one (query, datum) pair at a time in increasing datum order:
+ *
+ *   H_up(x) = min_k ( y^k + M dist_up(x, x^k) )          Sec. 3, Eq. (upperlower)
+ *   H_lo(x) = max_k ( y^k - M dist_lo(x, x^k) )          Sec. 3, Eq. (upperlower)
+ *   g(x)    = (H_up(x) + H_lo(x)) / 2                    Sec. 3, Eq. (eq:g)
+ *
+ * Distances (Sec. 3 after Eq. (upperlower); Sec. 4.1 Eq. (distmon)).  For
+ * coordinate i let t_i = x_i - x^k_i, negated when the function is decreasing in
+ * coordinate i (Sec. 4.1 treats increasing w.l.o.g.; decreasing is the mirror
+ * image), then multiplied by the norm weight w_i > 0.  Unconstrained coordinates
+ * use t_i in both bounds.  Constrained coordinates use the positive part
+ * (t_i)_+ in the upper bound, which makes g(x) <= y^k whenever x precedes x^k,
+ * and (-t_i)_+ (that is, |min(t_i,0)|) in the lower bound, which makes
+ * g(x) >= y^k whenever x^k precedes x (both stated in Sec. 4.1).
+ * dist = L1 / L2 / Linf norm of that vector.
+ *
+ * Ties: the first strict improvement wins, so the lowest datum index is kept.
+ *
+ * Lipschitz constant estimate (Sec. 5): M_est = max over i<j of
+ * |y^i - y^j| / dist(x^i, x^j) with the symmetric weighted norm (monotonicity
+ * plays no role in it).  A pair with dist = 0 and equal y is skipped; dist = 0
+ * with unequal y gives +inf.
+ *
+ * Gradient of g (piecewise linear, differentiable almost everywhere, Table 1):
+ *   dg/dq  = M/2 ( grad_q dist_up(q, x^u) - grad_q dist_lo(q, x^l) )
+ *   dg/dy^k = 1/2 sum_q gbar_q ([u_q = k] + [l_q = k])
+ *   dg/dM  = 1/2 sum_q gbar_q ( dist_up(q,x^u) - dist_lo(q,x^l) )
+ * with u_q, l_q the argmin / argmax of the two envelopes, subgradient 0 at a
+ * zero distance, and the lowest coordinate at an Linf argmax tie.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_L1 1
+#define OR_L2 2
+#define OR_LINF 3
+
+typedef struct {
+    const double* X; const double* y; int64_t N; int d; double M; int norm;
+    const int8_t* mon; const double* w;
+    const double* Q; int64_t q0, q1;
+    double *hi, *lo, *g, *gap_up, *gap_lo; int64_t *iu, *il;
+} eval_job;
+
+/* The signed, weighted coordinate difference t_i of Eq. (distmon). */
+static double coord_diff(const double* q, const double* x, int i, const int8_t* mon, const double* w) {
+    double t = q[i] - x[i];
+    if (mon && mon[i] < 0) t = -t;
+    if (w) t *= w[i];
+    return t;
+}
+
+/* dist_up (which = +1) or dist_lo (which = -1) between query q and datum x. */
+static double oracle_dist(const double* q, const double* x, int d, int norm,
+                          const int8_t* mon, const double* w, int which) {
+    double acc = 0.0;
+    for (int i = 0; i < d; i++) {
+        double t = coord_diff(q, x, i, mon, w);
+        double v;
+        if (mon && mon[i] != 0) v = (which > 0) ? (t > 0 ? t : 0.0) : (t < 0 ? -t : 0.0);
+        else v = fabs(t);
+        if (norm == OR_L1) acc += v;
+        else if (norm == OR_L2) acc += v * v;
+        else if (v > acc) acc = v;
+    }
+    return norm == OR_L2 ? sqrt(acc) : acc;
+}
+
+static void* eval_worker(void* arg) {
+    eval_job* J = (eval_job*)arg;
+    for (int64_t qi = J->q0; qi < J->q1; qi++) {
+        const double* q = J->Q + qi * J->d;
+        double bu = INFINITY, su = INFINITY, bl = -INFINITY, sl = -INFINITY;
+        int64_t ku = -1, kl = -1;
+        int bad = 0;
+        for (int i = 0; i < J->d; i++) if (!isfinite(q[i])) bad = 1;
+        if (!bad) {
+            for (int64_t k = 0; k < J->N; k++) {
+                const double* x = J->X + k * J->d;
+                double vu = J->y[k] + J->M * oracle_dist(q, x, J->d, J->norm, J->mon, J->w, +1);
+                double vl = J->y[k] - J->M * oracle_dist(q, x, J->d, J->norm, J->mon, J->w, -1);
+                if (vu < bu) { su = bu; bu = vu; ku = k; } else if (vu < su) su = vu;
+                if (vl > bl) { sl = bl; bl = vl; kl = k; } else if (vl > sl) sl = vl;
+            }
+        }
+        double hi = bad ? NAN : bu, lo = bad ? NAN : bl;
+        if (J->hi) J->hi[qi] = hi;
+        if (J->lo) J->lo[qi] = lo;
+        if (J->g) J->g[qi] = 0.5 * (hi + lo);
+        if (J->iu) J->iu[qi] = ku;
+        if (J->il) J->il[qi] = kl;
+        if (J->gap_up) J->gap_up[qi] = bad ? NAN : su - bu;
+        if (J->gap_lo) J->gap_lo[qi] = bad ? NAN : bl - sl;
+    }
+    return NULL;
+}
+
+static int clamp_threads(int nthreads, int64_t work) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if (work < nthreads) nthreads = work > 0 ? (int)work : 1;
+    return nthreads;
+}
+
+/* Envelopes, midpoint, argmin/argmax and the gap between best and second best. */
+int oracle_eval(const double* X, const double* y, int64_t N, int d, double M, int norm,
+                const int8_t* mon, const double* w, const double* Q, int64_t nq,
+                double* hi, double* lo, double* g, int64_t* iu, int64_t* il,
+                double* gap_up, double* gap_lo, int nthreads) {
+    if (N < 1 || d < 1 || nq < 0 || norm < 1 || norm > 3) return 1;
+    if (nq == 0) return 0;
+    nthreads = clamp_threads(nthreads, nq);
+    pthread_t th[256];
+    eval_job jobs[256];
+    for (int t = 0; t < nthreads; t++) {
+        eval_job j = {X, y, N, d, M, norm, mon, w, Q, nq * t / nthreads, nq * (t + 1) / nthreads,
+                      hi, lo, g, gap_up, gap_lo, iu, il};
+        jobs[t] = j;
+        pthread_create(&th[t], NULL, eval_worker, &jobs[t]);
+    }
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ M_est (Sec. 5) */
+
+typedef struct {
+    const double* X; const double* y; int64_t N; int d; int norm; const double* w;
+    int64_t i0, i1;
+    double best; int64_t bi, bj;
+} est_job;
+
+static double sym_dist(const double* a, const double* b, int d, int norm, const double* w) {
+    double acc = 0.0;
+    for (int i = 0; i < d; i++) {
+        double v = fabs(a[i] - b[i]);
+        if (w) v *= w[i];
+        if (norm == OR_L1) acc += v;
+        else if (norm == OR_L2) acc += v * v;
+        else if (v > acc) acc = v;
+    }
+    return norm == OR_L2 ? sqrt(acc) : acc;
+}
+
+static void* est_worker(void* arg) {
+    est_job* J = (est_job*)arg;
+    double best = -1.0; int64_t bi = -1, bj = -1;
+    for (int64_t i = J->i0; i < J->i1; i++) {
+        for (int64_t j = i + 1; j < J->N; j++) {
+            double dy = fabs(J->y[i] - J->y[j]);
+            double dd = sym_dist(J->X + i * J->d, J->X + j * J->d, J->d, J->norm, J->w);
+            double r;
+            if (dd == 0.0) { if (dy == 0.0) continue; r = INFINITY; }
+            else r = dy / dd;
+            if (r > best) { best = r; bi = i; bj = j; }
+        }
+    }
+    J->best = best; J->bi = bi; J->bj = bj;
+    return NULL;
+}
+
+/* Rows are interleaved over threads (row i goes to thread i mod T) to balance the
+ * triangle; the per-thread maxima are merged keeping the lowest (i, j) on ties. */
+typedef struct { est_job base; int stride, phase; } est_job2;
+
+static void* est_worker2(void* arg) {
+    est_job2* J2 = (est_job2*)arg;
+    est_job* J = &J2->base;
+    double best = -1.0; int64_t bi = -1, bj = -1;
+    for (int64_t i = J2->phase; i < J->N; i += J2->stride) {
+        for (int64_t j = i + 1; j < J->N; j++) {
+            double dy = fabs(J->y[i] - J->y[j]);
+            double dd = sym_dist(J->X + i * J->d, J->X + j * J->d, J->d, J->norm, J->w);
+            double r;
+            if (dd == 0.0) { if (dy == 0.0) continue; r = INFINITY; }
+            else r = dy / dd;
+            if (r > best) { best = r; bi = i; bj = j; }
+        }
+    }
+    J->best = best; J->bi = bi; J->bj = bj;
+    return NULL;
+}
+
+int oracle_estimate_M(const double* X, const double* y, int64_t N, int d, int norm,
+                      const double* w, double* M_out, int64_t* i_out, int64_t* j_out, int nthreads) {
+    if (N < 1 || d < 1 || norm < 1 || norm > 3) return 1;
+    nthreads = clamp_threads(nthreads, N);
+    pthread_t th[256];
+    est_job2 jobs[256];
+    for (int t = 0; t < nthreads; t++) {
+        est_job2 j = {{X, y, N, d, norm, w, 0, 0, -1.0, -1, -1}, nthreads, t};
+        jobs[t] = j;
+        pthread_create(&th[t], NULL, est_worker2, &jobs[t]);
+    }
+    double best = -1.0; int64_t bi = -1, bj = -1;
+    for (int t = 0; t < nthreads; t++) {
+        pthread_join(th[t], NULL);
+        est_job* J = &jobs[t].base;
+        if (J->bi < 0) continue;
+        if (J->best > best || (J->best == best && (J->bi < bi || (J->bi == bi && J->bj < bj)))) {
+            best = J->best; bi = J->bi; bj = J->bj;
+        }
+    }
+    /* No pair with a positive distance or a change in y: the data are constant. */
+    *M_out = best < 0 ? 0.0 : best;
+    *i_out = bi; *j_out = bj;
+    return 0;
+}
+
+/* Single-threaded M_est over an explicit row range [i0, i1): the same loop, used for
+ * timing a bounded sample of the triangle. */
+int oracle_estimate_M_rows(const double* X, const double* y, int64_t N, int d, int norm,
+                           const double* w, int64_t i0, int64_t i1,
+                           double* M_out, int64_t* i_out, int64_t* j_out) {
+    est_job j = {X, y, N, d, norm, w, i0, i1, -1.0, -1, -1};
+    est_worker(&j);
+    *M_out = j.best; *i_out = j.bi; *j_out = j.bj;
+    return 0;
+}
+
+/* ------------------------------------------------------------ gradient (Table 1) */
+
+/* d dist / d q_i for the chosen side; out[] gets d entries. */
+static void dist_grad(const double* q, const double* x, int d, int norm, const int8_t* mon,
+                      const double* w, int which, double* out) {
+    double v[64], s[64];
+    double acc = 0.0;
+    int imax = -1;
+    for (int i = 0; i < d; i++) {
+        double t = coord_diff(q, x, i, mon, w);
+        double sgn_q = ((mon && mon[i] < 0) ? -1.0 : 1.0) * (w ? w[i] : 1.0); /* dt/dq_i */
+        double vi, dvi;                                                    /* v_i, dv_i/dt */
+        if (mon && mon[i] != 0) {
+            if (which > 0) { vi = t > 0 ? t : 0.0; dvi = t > 0 ? 1.0 : 0.0; }
+            else           { vi = t < 0 ? -t : 0.0; dvi = t < 0 ? -1.0 : 0.0; }
+        } else {
+            vi = fabs(t); dvi = t > 0 ? 1.0 : (t < 0 ? -1.0 : 0.0);
+        }
+        v[i] = vi; s[i] = dvi * sgn_q;
+        if (norm == OR_L1) acc += vi;
+        else if (norm == OR_L2) acc += vi * vi;
+        else if (vi > acc) { acc = vi; imax = i; }
+    }
+    for (int i = 0; i < d; i++) out[i] = 0.0;
+    if (norm == OR_L1) {
+        for (int i = 0; i < d; i++) out[i] = s[i];
+    } else if (norm == OR_L2) {
+        double nrm = sqrt(acc);
+        if (nrm > 0) for (int i = 0; i < d; i++) out[i] = s[i] * v[i] / nrm;
+    } else {
+        if (acc > 0 && imax >= 0) out[imax] = s[imax];
+    }
+}
+
+int oracle_grad(const double* X, const double* y, int64_t N, int d, double M, int norm,
+                const int8_t* mon, const double* w, const double* Q, int64_t nq,
+                const int64_t* iu, const int64_t* il, const double* gbar,
+                double* grad_Q, double* grad_y, double* grad_M) {
+    if (N < 1 || d < 1 || d > 64 || norm < 1 || norm > 3) return 1;
+    double gu[64], gl[64];
+    double gm = 0.0;
+    (void)y;
+    for (int64_t qi = 0; qi < nq; qi++) {
+        const double* q = Q + qi * d;
+        double gb = gbar ? gbar[qi] : 1.0;
+        if (iu[qi] < 0 || il[qi] < 0) { if (grad_Q) for (int i = 0; i < d; i++) grad_Q[qi * d + i] = 0; continue; }
+        const double* xu = X + iu[qi] * d;
+        const double* xl = X + il[qi] * d;
+        dist_grad(q, xu, d, norm, mon, w, +1, gu);
+        dist_grad(q, xl, d, norm, mon, w, -1, gl);
+        if (grad_Q) for (int i = 0; i < d; i++) grad_Q[qi * d + i] = gb * 0.5 * M * (gu[i] - gl[i]);
+        if (grad_y) { grad_y[iu[qi]] += 0.5 * gb; grad_y[il[qi]] += 0.5 * gb; }
+        gm += 0.5 * gb * (oracle_dist(q, xu, d, norm, mon, w, +1) - oracle_dist(q, xl, d, norm, mon, w, -1));
+    }
+    if (grad_M) *grad_M = gm;
+    return 0;
+}

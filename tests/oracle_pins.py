@@ -1,0 +1,335 @@
+"""Checks that pin the FP64 oracle to facts fixed by the paper and by mathematics.
+
+Each check takes an ``Oracle`` instance, so the same checks can be run against
+deliberately broken copies of the oracle (see test_oracle_mutants.py).  None of
+them retypes the oracle's formula: they compare against hand-derived values,
+an O(log N) 1-D closed form, scipy's distance routines, finite differences, or
+inequalities the optimal interpolant must satisfy.
+"""
+from __future__ import annotations
+
+import bisect
+import json
+import os
+
+import numpy as np
+from scipy.spatial.distance import cdist, pdist, squareform
+
+from paper_2606_04670_b300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "hand_examples.json")
+METRIC = {1: "cityblock", 2: "euclidean", 3: "chebyshev"}
+
+
+def _scaled(Z, w):
+    return Z if w is None else Z * np.asarray(w)[None, :]
+
+
+# ---------------------------------------------------------------- hand examples
+
+def check_hand_examples(O):
+    """Sec. 3 Eq. (upperlower)/(eq:g), Sec. 4.1 Eq. (distmon), Sec. 5: worked by hand."""
+    G = json.load(open(GOLDEN))
+    e = G["one_d"]
+    for norm in (1, 2, 3):
+        r = O.evaluate(e["X"], e["y"], e["Q"], e["M"], norm)
+        np.testing.assert_allclose(r.hi, e["hi"], atol=1e-15)
+        np.testing.assert_allclose(r.lo, e["lo"], atol=1e-15)
+        np.testing.assert_allclose(r.g, e["g"], atol=1e-15)
+        assert list(r.idx_up) == e["idx_up"] and list(r.idx_lo) == e["idx_lo"]
+        M, i, j = O.estimate_M(e["X"], e["y"], norm)
+        assert abs(M - e["M_est"]) < 1e-15 and [i, j] == e["M_est_pair"]
+    e = G["two_d"]
+    for c in e["cases"]:
+        mon = None if c["mon"] is None else np.array(c["mon"], np.int8)
+        r = O.evaluate(e["X"], e["y"], e["Q"], e["M"], c["norm"], mon=mon, w=c["w"])
+        assert abs(r.hi[0] - c["hi"]) < 1e-14, c
+        assert abs(r.lo[0] - c["lo"]) < 1e-14, c
+        assert abs(r.g[0] - 0.5 * (c["hi"] + c["lo"])) < 1e-14, c
+        assert r.idx_up[0] == c["idx_up"] and r.idx_lo[0] == c["idx_lo"], c
+    for norm, (Mv, i, j) in e["M_est"].items():
+        M, a, b = O.estimate_M(e["X"], e["y"], int(norm))
+        assert abs(M - Mv) < 1e-15 and (a, b) == (i, j)
+
+
+# ------------------------------------------------------------- 1-D closed form
+
+def closed_form_1d(xs, ys, M, q, mon):
+    """H_up, H_lo of 1-D data consistent with M (and with the monotonicity).
+
+    Sorted data; between neighbours x_j <= q < x_{j+1} only those two points
+    matter (Sec. 4: the two neighbours lie on opposite sides in 1-D), giving
+    the piecewise-linear 'sawtooth' with slopes +-M.  For increasing data
+    (Sec. 4.1) the point to the right bounds from above with its own value and
+    the point to the left bounds from below with its own value.
+    """
+    if mon < 0:
+        hi, lo = closed_form_1d([-x for x in xs[::-1]], list(ys[::-1]), M, -q, 1)
+        return hi, lo
+    n = len(xs)
+    j = bisect.bisect_right(xs, q) - 1
+    up, dn = [], []
+    if j >= 0:
+        up.append(ys[j] + M * (q - xs[j]))
+        dn.append(ys[j] if mon > 0 else ys[j] - M * (q - xs[j]))
+    if j + 1 < n:
+        up.append(ys[j + 1] if mon > 0 else ys[j + 1] + M * (xs[j + 1] - q))
+        dn.append(ys[j + 1] - M * (xs[j + 1] - q))
+    return min(up), max(dn)
+
+
+def check_closed_form_1d(O):
+    rng = np.random.default_rng(7)
+    for mon in (0, 1, -1):
+        for norm in (1, 2, 3):
+            for wv in (None, 2.5):
+                xs = np.sort(rng.uniform(0, 1, 40))
+                if mon == 0:
+                    ys = np.sin(5 * xs)
+                    Mt = 5.0
+                else:
+                    ys = mon * (xs + 0.3 * np.sin(2 * xs))     # derivative in [0.4, 1.6]
+                    Mt = 1.6
+                M = 1.25 * Mt
+                # a weight w on the only coordinate scales distances by w
+                Meff = M * (1.0 if wv is None else wv)
+                Q = np.concatenate([rng.uniform(-0.3, 1.3, 200), xs[:5]])
+                r = O.evaluate(xs[:, None], ys, Q[:, None], M, norm,
+                               mon=None if mon == 0 else np.array([mon], np.int8),
+                               w=None if wv is None else [wv])
+                for k, q in enumerate(Q):
+                    hi, lo = closed_form_1d(list(xs), list(ys), Meff, q, mon)
+                    assert abs(r.hi[k] - hi) < 1e-12, (mon, norm, q)
+                    assert abs(r.lo[k] - lo) < 1e-12, (mon, norm, q)
+
+
+# ------------------------------------------------- unmasked case = scipy cdist
+
+def check_unmasked_cdist(O):
+    """Unmasked envelopes are min/max of y +- M * cdist (library distance routine)."""
+    for seed, (N, d, nq) in enumerate([(57, 3, 41), (200, 5, 64), (33, 1, 10), (90, 9, 30)]):
+        for norm in (1, 2, 3):
+            for weighted in (False, True):
+                p = W.random_problem(seed, N, d, nq, norm=norm, weighted=weighted, dtype=np.float64)
+                D = cdist(_scaled(p.Q, p.w), _scaled(p.X, p.w), METRIC[norm])
+                up = p.y[None, :] + p.M * D
+                dn = p.y[None, :] - p.M * D
+                r = O.evaluate(p.X, p.y, p.Q, p.M, norm, w=p.w)
+                np.testing.assert_allclose(r.hi, up.min(1), rtol=0, atol=1e-12)
+                np.testing.assert_allclose(r.lo, dn.max(1), rtol=0, atol=1e-12)
+                np.testing.assert_allclose(r.g, 0.5 * (up.min(1) + dn.max(1)), rtol=0, atol=1e-12)
+                # first index of the extremum (ties -> lowest index), where the gap is clear
+                su = np.sort(up, 1)
+                ok = (su[:, 1] - su[:, 0]) > 1e-9
+                assert np.all(r.idx_up[ok] == up.argmin(1)[ok])
+                sl = np.sort(dn, 1)
+                ok = (sl[:, -1] - sl[:, -2]) > 1e-9
+                assert np.all(r.idx_lo[ok] == dn.argmax(1)[ok])
+                # the reported gaps match the sorted values
+                np.testing.assert_allclose(r.gap_up, su[:, 1] - su[:, 0], atol=1e-12)
+
+
+# ------------------------------------------------------------------ invariants
+
+def _problems():
+    out = []
+    for norm in (1, 2, 3):
+        out.append(W.monotone_d4(norm=norm, n_data=400, n_query=300, dtype=np.float64))
+        for masked, weighted, dec in [(False, False, False), (True, False, False),
+                                      (True, True, True), (False, True, False)]:
+            out.append(W.random_problem(11 + norm, 150, 4, 120, norm=norm, masked=masked,
+                                        weighted=weighted, decreasing=dec, dtype=np.float64))
+    out.append(W.plain_d2(dtype=np.float64, n_data=300, n_query=300))
+    out.append(W.toy_d3(dtype=np.float64, n_data=300, n_query=300))
+    out.append(W.grad_d8(dtype=np.float64, n_data=300, n_query=200))
+    out.append(W.cluster_d16(dtype=np.float64, n_data=500, n_query=100))
+    return out
+
+
+def check_interpolation(O):
+    """Data consistent with M (and the monotonicity) are interpolated: g(x^k)=y^k (Sec. 3)."""
+    for p in _problems():
+        r = O.evaluate(p.X, p.y, p.X, p.M, p.norm, mon=p.mon, w=p.w)
+        np.testing.assert_allclose(r.hi, p.y, atol=1e-12)
+        np.testing.assert_allclose(r.lo, p.y, atol=1e-12)
+        np.testing.assert_allclose(r.g, p.y, atol=1e-12)
+
+
+def check_enclosure(O):
+    """H_lo <= f <= H_up for the generating f (Sec. 4: the bounds enclose every admissible f)."""
+    for p in _problems():
+        r = O.evaluate(p.X, p.y, p.Q, p.M, p.norm, mon=p.mon, w=p.w)
+        fq = p.f(p.Q)
+        assert np.all(r.lo <= fq + 1e-12), p.name
+        assert np.all(fq <= r.hi + 1e-12), p.name
+
+
+def _mono_gap(a, b, mon, w):
+    """m(a-b): positive part on increasing coordinates, (b-a)_+ on decreasing, |.| elsewhere."""
+    t = a - b
+    m = np.abs(t)
+    if mon is not None:
+        m = np.where(mon > 0, np.maximum(t, 0), m)
+        m = np.where(mon < 0, np.maximum(-t, 0), m)
+    return m if w is None else m * np.asarray(w)
+
+
+def _norm(v, norm):
+    return {1: np.abs(v).sum(-1), 2: np.sqrt((v * v).sum(-1)), 3: np.abs(v).max(-1)}[norm]
+
+
+def check_lipschitz_monotone(O):
+    """g(a)-g(b) <= M ||w m(a-b)||: M-Lipschitz, and monotone where constrained (Sec. 4, 4.1)."""
+    rng = np.random.default_rng(3)
+    for p in _problems():
+        n = 150
+        A = rng.random((n, p.d))
+        B = rng.random((n, p.d))
+        # coordinate-step pairs along each coordinate
+        i = rng.integers(0, p.d, n)
+        C = A.copy()
+        C[np.arange(n), i] = np.clip(A[np.arange(n), i] - rng.uniform(0, 0.2, n), 0, 1)
+        for P1, P2 in ((A, B), (B, A), (A, C), (C, A)):
+            r1 = O.evaluate(p.X, p.y, P1, p.M, p.norm, mon=p.mon, w=p.w)
+            r2 = O.evaluate(p.X, p.y, P2, p.M, p.norm, mon=p.mon, w=p.w)
+            bound = p.M * _norm(_mono_gap(P1, P2, p.mon, p.w), p.norm)
+            for key in ("hi", "lo", "g"):
+                assert np.all(r1[key] - r2[key] <= bound + 1e-12), (p.name, key)
+
+
+def check_width_bound(O):
+    """H_up - H_lo <= 2 M min_k dist_sym(q, x^k) (Sec. 3 error bound, twice the worst-case error)."""
+    for p in _problems():
+        r = O.evaluate(p.X, p.y, p.Q, p.M, p.norm, mon=p.mon, w=p.w)
+        D = cdist(_scaled(p.Q, p.w), _scaled(p.X, p.w), METRIC[p.norm])
+        assert np.all(r.hi - r.lo <= 2 * p.M * D.min(1) + 1e-12), p.name
+
+
+def check_special_cases(O):
+    rng = np.random.default_rng(5)
+    for norm in (1, 2, 3):
+        p = W.random_problem(21, 80, 3, 50, norm=norm, masked=True, dtype=np.float64)
+        # M = 0: the bounds collapse to the data range
+        r = O.evaluate(p.X, p.y, p.Q, 0.0, norm, mon=p.mon)
+        assert np.all(r.hi == p.y.min()) and np.all(r.lo == p.y.max())
+        assert np.all(r.idx_up == np.argmin(p.y)) and np.all(r.idx_lo == np.argmax(p.y))
+        # M = 0 with the extreme value repeated: the lowest index is kept on the tie
+        yt = p.y.copy()
+        yt[[5, 9, 30]] = yt.min() - 1.0
+        yt[[7, 12]] = yt.max() + 1.0
+        r = O.evaluate(p.X, yt, p.Q, 0.0, norm, mon=p.mon)
+        assert np.all(r.idx_up == 5) and np.all(r.idx_lo == 7)
+        # N = 1, unmasked: y0 +- M * distance (numpy norm)
+        X1, y1 = p.X[:1], p.y[:1]
+        r = O.evaluate(X1, y1, p.Q, p.M, norm)
+        dd = np.linalg.norm(p.Q - X1, ord={1: 1, 2: 2, 3: np.inf}[norm], axis=1)
+        np.testing.assert_allclose(r.hi, y1[0] + p.M * dd, atol=1e-12)
+        np.testing.assert_allclose(r.lo, y1[0] - p.M * dd, atol=1e-12)
+        # huge M: both bounds pick the nearest neighbour (Sec. 4 "among the closest points")
+        D = cdist(p.Q, p.X, METRIC[norm])
+        Ds = np.sort(D, 1)
+        ok = (Ds[:, 1] - Ds[:, 0]) > 1e-6
+        r = O.evaluate(p.X, p.y, p.Q, 1e9, norm)
+        nn = D.argmin(1)
+        assert np.all(r.idx_up[ok] == nn[ok]) and np.all(r.idx_lo[ok] == nn[ok])
+        # a query on a datum with the monotone distance: g = y there (Sec. 4.1)
+        r = O.evaluate(p.X, p.y, p.X[:7], p.M, norm, mon=p.mon)
+        np.testing.assert_allclose(r.g, p.y[:7], atol=1e-12)
+    # monotone bounds: x below x^k (all coords) => H_up(x) <= y^k; x above => H_lo(x) >= y^k
+    p = W.random_problem(22, 60, 3, 10, masked=True, dtype=np.float64)
+    mon = np.ones(3, np.int8)
+    for k in range(10):
+        xk = p.X[k]
+        below = xk - rng.uniform(0, 0.3, 3)
+        above = xk + rng.uniform(0, 0.3, 3)
+        r = O.evaluate(p.X, p.y, np.stack([below, above]), 50.0, 2, mon=mon)
+        assert r.hi[0] <= p.y[k] + 1e-15 and r.lo[1] >= p.y[k] - 1e-15
+
+
+def check_estimate_M(O):
+    """M_est = max_{i<j} |dy| / dist (Sec. 5) against scipy pdist; M_est <= M_true; interpolation."""
+    for seed, (N, d) in enumerate([(2, 1), (37, 2), (120, 4), (64, 7)]):
+        for norm in (1, 2, 3):
+            for weighted in (False, True):
+                p = W.random_problem(30 + seed, N, d, 1, norm=norm, weighted=weighted, dtype=np.float64)
+                D = pdist(_scaled(p.X, p.w), METRIC[norm])
+                dy = pdist(p.y[:, None], "cityblock")
+                ratio = dy / D
+                M, i, j = O.estimate_M(p.X, p.y, norm, w=p.w)
+                assert abs(M - ratio.max()) <= 1e-12 * ratio.max()
+                R = squareform(ratio)
+                assert abs(R[i, j] - M) <= 1e-12 * M and i < j
+                srt = np.sort(ratio)
+                if len(srt) > 1 and srt[-1] - srt[-2] > 1e-9:
+                    iu = np.triu_indices(N, 1)
+                    k = int(np.argmax(R[iu]))
+                    assert (iu[0][k], iu[1][k]) == (i, j)
+                assert M <= p.M_by_norm[norm] * (1 + 1e-12)
+                r = O.evaluate(p.X, p.y, p.X, M, norm, w=p.w)
+                np.testing.assert_allclose(r.g, p.y, atol=1e-12)
+    # duplicates: equal y is skipped, different y gives +inf
+    X = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 0.0]])
+    assert O.estimate_M(X, np.array([0.0, 1.0, 0.0]))[0] == 1.0
+    M, i, j = O.estimate_M(X, np.array([0.0, 1.0, 0.5]))
+    assert M == np.inf and (i, j) == (0, 2)
+    # the configured workloads' closed-form M bounds the data's estimate
+    for p in (W.plain_d2(dtype=np.float64, n_data=400), W.toy_d3(dtype=np.float64, n_data=400),
+              W.grad_d8(dtype=np.float64, n_data=400)):
+        assert O.estimate_M(p.X, p.y, p.norm)[0] <= p.M
+    for norm in (1, 2, 3):
+        p = W.monotone_d4(norm=norm, n_data=400, n_query=1, dtype=np.float64)
+        assert O.estimate_M(p.X, p.y, norm)[0] <= p.M
+
+
+def check_gradient_fd(O):
+    """Analytic gradient = central finite differences of the oracle, away from kinks and ties."""
+    h = 1e-6
+    for norm in (1, 2, 3):
+        for masked, weighted, dec in [(False, False, False), (True, True, True), (True, False, False)]:
+            p = W.random_problem(40 + norm, 60, 3, 40, norm=norm, masked=masked, weighted=weighted,
+                                 decreasing=dec, dtype=np.float64)
+            r = O.evaluate(p.X, p.y, p.Q, p.M, norm, mon=p.mon, w=p.w)
+            gbar = np.random.default_rng(1).uniform(-1, 1, p.nq)
+            gQ, gy, gM = O.gradient(p.X, p.y, p.Q, p.M, r.idx_up, r.idx_lo, gbar, norm, p.mon, p.w)
+            checked = 0
+            for i in range(p.d):
+                E = np.zeros(p.d)
+                E[i] = h
+                rp = O.evaluate(p.X, p.y, p.Q + E, p.M, norm, mon=p.mon, w=p.w)
+                rm = O.evaluate(p.X, p.y, p.Q - E, p.M, norm, mon=p.mon, w=p.w)
+                stable = ((rp.idx_up == r.idx_up) & (rm.idx_up == r.idx_up) &
+                          (rp.idx_lo == r.idx_lo) & (rm.idx_lo == r.idx_lo) &
+                          (r.gap_up > 1e-4) & (r.gap_lo > 1e-4))
+                # stay away from coordinate kinks of the chosen pairs
+                tu = p.Q[:, i] - p.X[r.idx_up, i]
+                tl = p.Q[:, i] - p.X[r.idx_lo, i]
+                stable &= (np.abs(tu) > 1e-4) & (np.abs(tl) > 1e-4)
+                fd = (rp.g - rm.g) / (2 * h)
+                np.testing.assert_allclose(gQ[stable, i], gbar[stable] * fd[stable], atol=2e-6)
+                checked += int(stable.sum())
+            assert checked > p.nq
+            # dg/dM by finite differences in M (indices are stable for a tiny step)
+            rp = O.evaluate(p.X, p.y, p.Q, p.M + h, norm, mon=p.mon, w=p.w)
+            rm = O.evaluate(p.X, p.y, p.Q, p.M - h, norm, mon=p.mon, w=p.w)
+            st = (rp.idx_up == r.idx_up) & (rm.idx_up == r.idx_up) & (rp.idx_lo == r.idx_lo) & (rm.idx_lo == r.idx_lo)
+            fdM = (gbar * (rp.g - rm.g) / (2 * h))[st].sum()
+            _, _, gM_st = O.gradient(p.X, p.y, p.Q[st], p.M, r.idx_up[st], r.idx_lo[st], gbar[st],
+                                     norm, p.mon, p.w)
+            assert abs(fdM - gM_st) < 1e-5 * max(1.0, abs(fdM))
+            # dg/dy_k by finite differences in y_k for a few data points
+            for k in np.unique(np.concatenate([r.idx_up[:5], r.idx_lo[:5]])):
+                yp = p.y.copy()
+                yp[k] += h
+                ym = p.y.copy()
+                ym[k] -= h
+                a = O.evaluate(p.X, yp, p.Q, p.M, norm, mon=p.mon, w=p.w)
+                b = O.evaluate(p.X, ym, p.Q, p.M, norm, mon=p.mon, w=p.w)
+                st = (a.idx_up == r.idx_up) & (b.idx_up == r.idx_up) & (a.idx_lo == r.idx_lo) & (b.idx_lo == r.idx_lo)
+                if st.all():
+                    fdy = (gbar * (a.g - b.g) / (2 * h)).sum()
+                    assert abs(fdy - gy[k]) < 1e-6, (k, fdy, gy[k])
+
+
+ALL_CHECKS = [check_hand_examples, check_closed_form_1d, check_unmasked_cdist, check_interpolation,
+              check_enclosure, check_lipschitz_monotone, check_width_bound, check_special_cases,
+              check_estimate_M, check_gradient_fd]

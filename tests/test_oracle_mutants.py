@@ -1,0 +1,65 @@
+"""Plant plausible mistakes in copies of the oracle's C source (on the CPU) and check
+that every one of them fails at least one pin.  This is what makes the pins a pin:
+a dropped term, a wrong sign or index, or a swapped operand does not go unnoticed."""
+import os
+
+import pytest
+
+import oracle as O
+import oracle_pins as P
+
+MUTANTS = {
+    # the lower bound takes the same positive part as the upper (Eq. (distmon) read literally)
+    "lower_uses_upper_part": ("(t < 0 ? -t : 0.0)", "(t > 0 ? t : 0.0)", 1),
+    # a constrained coordinate falls back to |t| in the lower bound
+    "lower_uses_abs": ("(t < 0 ? -t : 0.0)", "fabs(t)", 1),
+    "weights_dropped": ("if (w) t *= w[i];", "", 1),
+    "decreasing_ignored": ("if (mon && mon[i] < 0) t = -t;", "", 1),
+    "ties_to_last_index": ("if (vu < bu) {", "if (vu <= bu) {", 1),
+    "l2_sqrt_dropped": ("return norm == OR_L2 ? sqrt(acc) : acc;\n}\n\nstatic void* eval_worker",
+                        "return acc;\n}\n\nstatic void* eval_worker", 1),
+    "linf_sums": ("else if (v > acc) acc = v;\n    }\n    return norm == OR_L2 ? sqrt(acc) : acc;\n}\n\nstatic void* eval",
+                  "else acc += v;\n    }\n    return norm == OR_L2 ? sqrt(acc) : acc;\n}\n\nstatic void* eval", 1),
+    "midpoint_sign": ("J->g[qi] = 0.5 * (hi + lo);", "J->g[qi] = 0.5 * (hi - lo);", 1),
+    "upper_sign": ("J->y[k] + J->M * oracle_dist", "J->y[k] - J->M * oracle_dist", 1),
+    "mest_no_abs_dy": ("double dy = fabs(J->y[i] - J->y[j]);\n            double dd = sym_dist(J->X + i * J->d",
+                       "double dy = (J->y[i] - J->y[j]);\n            double dd = sym_dist(J->X + i * J->d", 2),
+    "mest_l1_as_l2": ("static double sym_dist", "static double sym_dist_unused", 1),
+    "grad_sign": ("gb * 0.5 * M * (gu[i] - gl[i])", "gb * 0.5 * M * (gu[i] + gl[i])", 1),
+    "grad_M_half_missing": ("gm += 0.5 * gb *", "gm += gb *", 1),
+}
+
+
+def _mutant_source(name):
+    old, new, count = MUTANTS[name]
+    src = open(O.SOURCE).read()
+    assert src.count(old) >= count, name
+    if name == "mest_l1_as_l2":
+        # every norm of the estimate computed as L2 (an index slip on the norm switch)
+        src = src.replace(old, new, 1)
+        src = src.replace("static double sym_dist_unused",
+                          "static double sym_dist(const double* a, const double* b, int d, int norm, const double* w)"
+                          "{ return sym_dist_unused(a, b, d, 2, w); }\nstatic double sym_dist_unused", 1)
+        # forward declaration order: define the wrapper after the original
+        body_start = src.index("static double sym_dist(")
+        wrapper = src[body_start:src.index("\n", body_start) + 1]
+        src = src.replace(wrapper, "", 1)
+        anchor = "static void* est_worker(void* arg)"
+        src = src.replace(anchor, wrapper + anchor, 1)
+        return src
+    return src.replace(old, new, count)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    src = tmp_path / "mutant.c"
+    src.write_text(_mutant_source(name))
+    lib = O.compile_source(str(src), str(tmp_path / "libmutant.so"))
+    mut = O.Oracle(lib)
+    failures = []
+    for check in P.ALL_CHECKS:
+        try:
+            check(mut)
+        except AssertionError:
+            failures.append(check.__name__)
+    assert failures, f"mutant {name} passed every pin"

@@ -1,0 +1,234 @@
+/*
+ * lipfit.h -- C ABI of liblipfit.so: optimal Lipschitz interpolation on a B300 (sm_103a).
+ *
+ * What it computes (G. Beliakov, "Fitting scattered data with optional monotonicity
+ * constraints on GPU: LipFit package"):
+ *
+ *   H_up(x) = min_k ( y^k + M dist_up(x, x^k) )   Sec. 3, Eq. (upperlower)
+ *   H_lo(x) = max_k ( y^k - M dist_lo(x, x^k) )   Sec. 3, Eq. (upperlower)
+ *   g(x)    = ( H_up(x) + H_lo(x) ) / 2           Sec. 3, Eq. (eq:g)
+ *
+ * dist is the L1, L2 or Linf norm of the weighted coordinate differences
+ * w_i (x_i - x^k_i).  Coordinates in which the function is increasing use the
+ * positive part (x_i - x^k_i)_+ in dist_up and (x^k_i - x_i)_+ in dist_lo
+ * (Sec. 4.1, Eq. (distmon) and the bounds g <= y^k for x below x^k, g >= y^k for x
+ * above x^k stated there); decreasing coordinates are mirrored.  Unconstrained
+ * coordinates use |x_i - x^k_i| in both.  Ties in the min/max go to the lowest k.
+ *
+ * Conventions for every call:
+ *  - Array pointers are DEVICE pointers owned by the caller, unless the function name
+ *    ends in _host (then they are host pointers; page-locked memory gives the fastest
+ *    copies).  Matrices are row-major and dense: X is [N][d], Q is [nq][d].
+ *  - Element type: float for LIP_FP32 / LIP_TC_* handles, double for LIP_FP64 handles
+ *    (X, y, Q and the g/lo/hi outputs alike).  Indices are int32 (N < 2^31).
+ *  - Calls are ordered on the given CUDA stream (NULL = legacy default stream) and
+ *    return before the GPU work finishes, except where a call says it synchronises.
+ *  - A handle is used by one host thread and one stream at a time; its scratch memory
+ *    is reused by the next call on it.
+ *  - No C++ exception, abort or exit crosses this interface.  Every failure is a
+ *    lip_status; lip_last_error() returns a one-line explanation (thread-local).
+ *  - Argument errors are detected on the host before any GPU work is queued, so they
+ *    leave the handle and the stream untouched.
+ */
+#ifndef LIPFIT_H
+#define LIPFIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Symbols of this interface are exported from liblipfit.so; everything else is hidden. */
+#if defined(__GNUC__)
+#define LIP_API __attribute__((visibility("default")))
+#else
+#define LIP_API
+#endif
+
+typedef enum {
+    LIP_OK = 0,
+    LIP_ERR_ARG = 1,          /* bad argument: null pointer, size out of range, M < 0 ...   */
+    LIP_ERR_NONFINITE = 2,    /* NaN or Inf in the data X or y                              */
+    LIP_ERR_OOM = 3,          /* device or host allocation failed                          */
+    LIP_ERR_CUDA = 4,         /* a CUDA runtime call failed (detail in lip_last_error)      */
+    LIP_ERR_CAPACITY = 5,     /* lip_add beyond the reserved capacity                       */
+    LIP_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up (see lip_check)         */
+    LIP_ERR_UNSUPPORTED = 7,  /* valid request this build does not handle                  */
+    LIP_ERR_NO_DEVICE = 8     /* no CUDA device visible                                     */
+} lip_status;
+
+typedef enum { LIP_L1 = 1, LIP_L2 = 2, LIP_LINF = 3 } lip_norm;
+
+typedef enum {
+    LIP_FP32 = 0,      /* FP32 arithmetic in the all-pairs scan, FP64 re-evaluation of winners */
+    LIP_FP64 = 1,      /* FP64 throughout                                                   */
+    LIP_TC_BF16 = 2,   /* L2 only: tensor-core cross term (bf16 split), exact FP64 rescreen  */
+    LIP_TC_TF32 = 3    /* L2 only: tensor-core cross term (tf32 split), exact FP64 rescreen  */
+} lip_precision;
+
+/* Largest dimension d accepted by lip_fit / lip_reserve. */
+#define LIP_D_MAX 16
+
+/* Fitting parameters (Sec. 5, setparams(mon, a, b, w)).  All pointers are HOST pointers
+ * that are read during the call only.
+ *   norm       lip_norm of dist.
+ *   precision  lip_precision of the evaluation.
+ *   mon        d entries in {-1, 0, 1}: decreasing / unconstrained / increasing in that
+ *              coordinate (Sec. 5, mon in {-1,0,1}^dim).  NULL = no monotonicity
+ *              (the paper's model=0).
+ *   w          d norm weights > 0: dist uses w_i (x_i - x^k_i).  NULL = all ones.  (These
+ *              are weights of the norm; they are unrelated to the k-neighbour weights
+ *              of Sec. 5 "Extra features".)                                              */
+typedef struct lip_params {
+    int32_t norm;
+    int32_t precision;
+    const int8_t* mon;
+    const double* w;
+} lip_params;
+
+typedef struct lip_model* lip_handle;
+
+/* ---------------------------------------------------------------- data (Sec. 5) */
+
+/* Copy N data points into a new handle (Sec. 5: add() copies the data into GPU memory).
+ *   X [N][d], y [N]: device arrays, read during the call's stream work only; the caller
+ *   may reuse them once the stream has passed this call.
+ *   M: Lipschitz constant (>= 0, finite) used by lip_eval until lip_set_M.
+ * Errors: LIP_ERR_ARG (N < 1, N >= 2^31, d < 1, d > LIP_D_MAX, M < 0 or not finite,
+ *   bad norm/precision/mon/w), LIP_ERR_UNSUPPORTED (tensor-core precision with a norm
+ *   other than L2), LIP_ERR_NONFINITE (NaN/Inf in X or y; this is the only call that
+ *   synchronises the stream, to read that check back), LIP_ERR_OOM, LIP_ERR_CUDA.
+ * On error *out is NULL and nothing is leaked. */
+LIP_API lip_status lip_fit(const void* X, const void* y, int64_t N, int32_t d, double M,
+                   const lip_params* p, void* stream, lip_handle* out);
+
+/* Same as lip_fit with X and y in host memory (copied to the device inside the call). */
+LIP_API lip_status lip_fit_host(const void* X, const void* y, int64_t N, int32_t d, double M,
+                        const lip_params* p, void* stream, lip_handle* out);
+
+/* Empty handle with room for `capacity` points (Sec. 5: LipFit(reservedata, dim) reserves
+ * space so that data can be added later without extra copies). */
+LIP_API lip_status lip_reserve(int64_t capacity, int32_t d, double M, const lip_params* p,
+                       lip_handle* out);
+
+/* Append n points (device X [n][d], y [n]) after the current ones (Sec. 5: new data can
+ * be added at any time and values() uses them).  Synchronises the stream to check the
+ * new points are finite.  LIP_ERR_CAPACITY if N + n exceeds the capacity; the handle is
+ * unchanged on any error. */
+LIP_API lip_status lip_add(lip_handle h, const void* X, const void* y, int64_t n, void* stream);
+
+/* lip_add with X and y in host memory. */
+LIP_API lip_status lip_add_host(lip_handle h, const void* X, const void* y, int64_t n, void* stream);
+
+/* Remove every point (Sec. 5: clear()).  The capacity is kept. */
+LIP_API lip_status lip_clear(lip_handle h, void* stream);
+
+/* Number of points currently held, or -1 for a NULL handle. */
+LIP_API int64_t lip_size(lip_handle h);
+
+/* Change M (Sec. 5 passes the Lipschitz constant to each values() call).  Re-scales the
+ * handle's internal copy on `stream`. */
+LIP_API lip_status lip_set_M(lip_handle h, double M, void* stream);
+
+/* ---------------------------------------------------------------- evaluation */
+
+/* Evaluate the interpolant at nq query points (Sec. 5: values(query, LC, model, k=1)).
+ *   Q [nq][d]         device, element type of the handle.
+ *   g, lo, hi [nq]    device outputs (element type of the handle): g = (H_up + H_lo)/2,
+ *                     lo = H_lo, hi = H_up.  Any of them may be NULL.
+ *   idx_up, idx_lo    device int32 [nq]: the data index attaining H_up (argmin) and
+ *                     H_lo (argmax), lowest index on exact ties.  May be NULL.
+ * nq = 0 is a no-op.  A query with a NaN/Inf coordinate gives NaN outputs and index -1.
+ * With a handle that holds no points (after lip_clear) every output is NaN / -1.
+ * FP32 handles: the all-pairs scan runs in FP32, then the two selected data points are
+ * re-evaluated in FP64, so lo/hi/g are exact up to the choice of index, which can only
+ * differ from the exact one where two candidates are within FP32 rounding.
+ * Errors: LIP_ERR_ARG, LIP_ERR_OOM (scratch growth), LIP_ERR_CUDA. */
+LIP_API lip_status lip_eval(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi,
+                    int32_t* idx_up, int32_t* idx_lo, void* stream);
+
+/* lip_eval with Q and the outputs in host memory: the queries are copied in, evaluated
+ * and the results copied out in chunks, with copies overlapping the kernels of other
+ * chunks.  Synchronises the stream before returning (the outputs are then valid). */
+LIP_API lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi,
+                         int32_t* idx_up, int32_t* idx_lo, void* stream);
+
+/* Lipschitz constant of the data (Sec. 5: lipschitz_constant()): the maximum over pairs
+ * i < j of |y^i - y^j| / dist(x^i, x^j) with the symmetric weighted norm of the handle
+ * (monotonicity does not enter).  N^2/2 work and no pair matrix is stored (Sec. 5).
+ * Pairs with dist = 0 and equal y are skipped; dist = 0 with different y gives +Inf.
+ * The candidate maximum is found in FP32 and the winning pair is re-evaluated in FP64.
+ * Outputs (host): *M_out, and the pair (*i_out < *j_out), or -1/-1 with *M_out = 0 when
+ * N < 2 or all the data are equal.  Synchronises the stream. */
+LIP_API lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, int64_t* j_out,
+                          void* stream);
+
+/* ---------------------------------------------------------------- differentiation */
+
+/* Gradient of L = sum_q grad_g[q] * g(q) through the saved argmin/argmax (g is piecewise
+ * smooth and differentiable almost everywhere, Table 1):
+ *   grad_Q [nq][d] (overwritten)   dL/dq  = M/2 (grad dist_up(q, x^u) - grad dist_lo(q, x^l))
+ *   grad_y [N]     (ACCUMULATED)   dL/dy^k = 1/2 sum_q grad_g[q] ([u_q = k] + [l_q = k])
+ *   grad_M [1]     (overwritten)   dL/dM  = 1/2 sum_q grad_g[q] (dist_up - dist_lo)
+ * with the subgradient 0 at a zero distance and, for Linf, the lowest coordinate on a
+ * tie of the maximum.  Q, idx_up, idx_lo are those given to / returned by lip_eval;
+ * grad_g is [nq].  All device pointers; element type of the handle for Q, grad_g,
+ * grad_Q, grad_y; grad_M is double.  Any of grad_Q, grad_y, grad_M may be NULL.
+ * grad_y is reduced with FP64 atomics in handle scratch and then added to grad_y, so
+ * its last bits may change with the order of the atomics; grad_M uses a fixed-order
+ * two-level reduction and is bitwise reproducible. */
+LIP_API lip_status lip_backward(lip_handle h, const void* Q, int64_t nq, const int32_t* idx_up,
+                        const int32_t* idx_lo, const void* grad_g, void* grad_Q, void* grad_y,
+                        double* grad_M, void* stream);
+
+/* ---------------------------------------------------------------- launch shape */
+
+/* Launch shape of lip_eval on this handle (what the autotuner sets).  The results do not
+ * depend on it.
+ *   tile_groups  groups of 4 data points staged per shared-memory tile: 8, 16, 32 or 64
+ *                (0 keeps the current value).  Ignored by the generic kernel.
+ *   splits       number of slices of the data scanned by separate thread blocks and
+ *                merged afterwards; 0 = chosen per call to fill the GPU in whole waves.
+ * LIP_ERR_ARG for other values. */
+LIP_API lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits);
+
+/* Current launch shape: tile_groups, the configured splits (0 = automatic), the splits
+ * used by the last lip_eval, and the queries held per thread by the scan kernel.  Any
+ * output pointer may be NULL. */
+LIP_API lip_status lip_get_tuning(lip_handle h, int32_t* tile_groups, int32_t* splits,
+                                  int32_t* last_splits, int32_t* queries_per_thread);
+
+/* ---------------------------------------------------------------- measurement */
+
+/* Optional CUDA events (cudaEvent_t, created by the caller) that lip_eval records on its
+ * stream immediately before and after its all-pairs scan kernel, so that the kernel can
+ * be timed alone on the stream it runs on.  NULL, NULL turns this off. */
+LIP_API lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, void* ev_after_scan);
+
+/* Number of kernels this library has launched in this process (all handles). */
+LIP_API uint64_t lip_kernel_launches(void);
+
+/* ---------------------------------------------------------------- status */
+
+/* Synchronise the stream and report a failure recorded by the device since the last
+ * lip_check on this handle: LIP_ERR_TIMEOUT if a bounded wait inside a kernel gave up
+ * (the kernel then skipped its work and returned), LIP_ERR_CUDA for a CUDA error. */
+LIP_API lip_status lip_check(lip_handle h, void* stream);
+
+LIP_API void lip_free(lip_handle h);
+
+LIP_API const char* lip_status_string(lip_status s);
+
+/* Copies the calling thread's last error message into buf (always NUL-terminated when
+ * len > 0) and returns its full length. */
+LIP_API size_t lip_last_error(char* buf, size_t len);
+
+/* Library version, e.g. "0.1.0 sm_103a". */
+LIP_API const char* lip_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIPFIT_H */

@@ -1,0 +1,722 @@
+// C ABI of liblipfit (declared in include/lipfit.h): handles, validation, launch shapes.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "launch.h"
+
+using namespace lip;
+
+namespace {
+
+thread_local std::string g_err;
+
+lip_status fail(lip_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+lip_status cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(LIP_ERR_OOM, "%s: out of device memory", what);
+    }
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver)
+        return fail(LIP_ERR_NO_DEVICE, "%s: %s", what, cudaGetErrorString(e));
+    return fail(LIP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr)                                              \
+    do {                                                            \
+        cudaError_t e_ = (expr);                                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #expr);         \
+    } while (0)
+
+#define LIP_TRY(expr)                                               \
+    do {                                                            \
+        lip_status s_ = (expr);                                     \
+        if (s_ != LIP_OK) return s_;                                \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Device buffer that only grows; freed with the handle.
+struct Scratch {
+    void* p = nullptr;
+    size_t bytes = 0;
+    lip_status ensure(size_t need, const char* what) {
+        if (need <= bytes) return LIP_OK;
+        if (p) {
+            cudaError_t e = cudaFree(p);   // implicit device synchronisation: no user in flight
+            p = nullptr;
+            bytes = 0;
+            if (e != cudaSuccess) return cuda_fail(e, what);
+        }
+        size_t sz = std::max<size_t>(need, 256);
+        sz = (sz + 255) & ~size_t(255);
+        cudaError_t e = cudaMalloc(&p, sz);
+        if (e != cudaSuccess) { p = nullptr; return cuda_fail(e, what); }
+        bytes = sz;
+        return LIP_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+std::atomic<uint64_t> g_launches{0};
+inline void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+struct lip_model {
+    int device = 0;
+    int sms = 148;
+    int d = 0, C = 0, norm = LIP_L2, prec = LIP_FP32, esize = 4;
+    double M = 0.0;
+    int8_t mon[D_MAX] = {};
+    double w[D_MAX] = {};
+    int perm[D_MAX] = {};
+    double sgnw[D_MAX] = {};
+    bool exact = false;
+    int dl = 0, nch = 0, aux = 0;
+    int64_t N = 0, cap = 0, cap_pad = 0;
+    void* X0 = nullptr;
+    void* y0 = nullptr;
+    void* hot = nullptr;
+    unsigned* status = nullptr;       // [0]: runtime error bits, [1]: finiteness check
+    ScanKernelInfo kinfo;
+    int occ_blocks = 1;
+    int tile_groups = 32;             // groups per shared-memory tile (8, 16, 32 or 64)
+    int splits = 0;                   // 0 = automatic
+    int last_splits = 0;
+    Scratch partial, est, bwd, io;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+    cudaEvent_t ev_scan0 = nullptr, ev_scan1 = nullptr;   // caller's timing events
+};
+
+namespace {
+
+lip_status check_params(int32_t d, double M, const lip_params* p) {
+    if (!p) return fail(LIP_ERR_ARG, "params is NULL");
+    if (d < 1 || d > D_MAX) return fail(LIP_ERR_ARG, "d = %d is outside [1, %d]", d, D_MAX);
+    if (!(M >= 0.0) || !std::isfinite(M)) return fail(LIP_ERR_ARG, "M = %g must be finite and >= 0", M);
+    if (p->norm < LIP_L1 || p->norm > LIP_LINF) return fail(LIP_ERR_ARG, "norm = %d is not L1/L2/Linf", p->norm);
+    if (p->precision < LIP_FP32 || p->precision > LIP_TC_TF32)
+        return fail(LIP_ERR_ARG, "precision = %d is not a lip_precision", p->precision);
+    if (p->mon)
+        for (int i = 0; i < d; ++i)
+            if (p->mon[i] < -1 || p->mon[i] > 1) return fail(LIP_ERR_ARG, "mon[%d] = %d is not -1/0/1", i, p->mon[i]);
+    if (p->w)
+        for (int i = 0; i < d; ++i)
+            if (!(p->w[i] > 0.0) || !std::isfinite(p->w[i]))
+                return fail(LIP_ERR_ARG, "w[%d] = %g must be finite and > 0", i, p->w[i]);
+    if (p->precision == LIP_TC_BF16 || p->precision == LIP_TC_TF32) {
+        if (p->norm != LIP_L2) return fail(LIP_ERR_UNSUPPORTED, "tensor-core precision needs the L2 norm");
+        return fail(LIP_ERR_UNSUPPORTED, "tensor-core precision is not available in this build");
+    }
+    return LIP_OK;
+}
+
+void fill_scan_params(const lip_model* h, ScanParams& P) {
+    P.d = h->d;
+    P.C = h->C;
+    P.dl = h->dl;
+    P.nch = h->nch;
+    for (int j = 0; j < D_MAX; ++j) {
+        P.perm[j] = h->perm[j];
+        P.scale[j] = h->M * h->sgnw[j];
+    }
+    P.hot = h->hot;
+    P.err = h->status;
+}
+
+void fill_hot_params(const lip_model* h, HotParams& P, int64_t k0, int64_t k1) {
+    P.X0 = h->X0;
+    P.y0 = h->y0;
+    P.k0 = k0;
+    P.k1 = k1;
+    P.d = h->d;
+    P.C = h->C;
+    P.dl = h->dl;
+    P.nch = h->nch;
+    P.aux = h->aux;
+    for (int j = 0; j < D_MAX; ++j) {
+        P.perm[j] = h->perm[j];
+        P.scale[j] = h->M * h->sgnw[j];
+    }
+    P.hot = h->hot;
+    P.err = h->status + 1;
+}
+
+void free_model(lip_model* h) {
+    if (!h) return;
+    DeviceGuard g(h->device);
+    if (h->X0) cudaFree(h->X0);
+    if (h->y0) cudaFree(h->y0);
+    if (h->hot) cudaFree(h->hot);
+    if (h->status) cudaFree(h->status);
+    h->partial.release();
+    h->est.release();
+    h->bwd.release();
+    h->io.release();
+    for (int b = 0; b < 2; ++b) {
+        if (h->ev_in[b]) cudaEventDestroy(h->ev_in[b]);
+        if (h->ev_out[b]) cudaEventDestroy(h->ev_out[b]);
+    }
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    delete h;
+}
+
+lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, cudaStream_t st, lip_model** out) {
+    *out = nullptr;
+    LIP_TRY(check_params(d, M, p));
+    if (cap < 1 || cap >= (int64_t)1 << 31) return fail(LIP_ERR_ARG, "capacity %lld is outside [1, 2^31)", (long long)cap);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    lip_model* h = new (std::nothrow) lip_model();
+    if (!h) return fail(LIP_ERR_OOM, "host allocation of the handle failed");
+    h->device = dev;
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+    h->d = d;
+    h->norm = p->norm;
+    h->prec = p->precision;
+    h->esize = p->precision == LIP_FP64 ? 8 : 4;
+    h->M = M;
+    // Layout coordinate order: constrained coordinates first, then the rest, each in
+    // the caller's order; decreasing coordinates are mirrored (sign -1).
+    int j = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < d; ++i) {
+            const int8_t m = p->mon ? p->mon[i] : 0;
+            if ((pass == 0) != (m != 0)) continue;
+            h->perm[j] = i;
+            h->sgnw[j] = (m < 0 ? -1.0 : 1.0) * (p->w ? p->w[i] : 1.0);
+            ++j;
+        }
+    for (int i = 0; i < d; ++i) {
+        h->mon[i] = p->mon ? p->mon[i] : 0;
+        h->w[i] = p->w ? p->w[i] : 1.0;
+        if (h->mon[i] != 0) h->C++;
+    }
+    const int U = d - h->C;
+    if (h->prec == LIP_FP32 && exact_shape_available(h->C, U)) {
+        h->exact = true;
+        h->dl = d;
+        h->aux = (h->norm == LIP_L1 && h->C > 0) ? 1 : 0;
+        h->nch = d + 1 + h->aux;
+        h->kinfo = scan_exact_info(h->norm, h->C, U);
+    } else {
+        h->exact = false;
+        const int dims[] = {2, 4, 8, 12, 16};
+        for (int v : dims)
+            if (v >= d) { h->dl = v; break; }
+        h->aux = 0;
+        h->nch = h->dl + 1;
+        h->kinfo = scan_generic_info(h->esize, h->norm, h->dl);
+    }
+    if (!h->kinfo.launch) {
+        free_model(h);
+        return fail(LIP_ERR_UNSUPPORTED, "no scan kernel for norm %d, %d constrained + %d free coordinates", p->norm, h->C, U);
+    }
+    const size_t smem = h->exact ? (size_t)SCAN_STAGES * h->tile_groups * h->nch * 16 : 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_blocks, h->kinfo.kernel, SCAN_THREADS, smem) != cudaSuccess ||
+        h->occ_blocks < 1) {
+        cudaGetLastError();
+        h->occ_blocks = 1;
+    }
+    h->cap = cap;
+    h->cap_pad = round_up(cap, PAD_POINTS);
+    struct { void** p; size_t n; const char* what; } allocs[] = {
+        {&h->X0, (size_t)cap * d * h->esize, "data copy"},
+        {&h->y0, (size_t)cap * h->esize, "value copy"},
+        {&h->hot, (size_t)h->cap_pad * h->nch * h->esize, "scan layout"},
+        {reinterpret_cast<void**>(&h->status), 2 * sizeof(unsigned), "status word"},
+    };
+    for (auto& a : allocs) {
+        e = cudaMalloc(a.p, a.n);
+        if (e != cudaSuccess) {
+            *a.p = nullptr;
+            free_model(h);
+            return cuda_fail(e, a.what);
+        }
+    }
+    e = cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), st);
+    if (e == cudaSuccess) e = launch_pad_hot(h->esize, h->hot, 0, h->cap_pad, h->nch, h->dl, st);
+    count_launches(1);
+    if (e != cudaSuccess) {
+        free_model(h);
+        return cuda_fail(e, "handle initialisation");
+    }
+    *out = h;
+    return LIP_OK;
+}
+
+// Copy n points after the current ones and build their scan layout; synchronises.
+lip_status add_points(lip_model* h, const void* X, const void* y, int64_t n, cudaStream_t st, cudaMemcpyKind kind) {
+    if (n < 0) return fail(LIP_ERR_ARG, "n = %lld < 0", (long long)n);
+    if (n == 0) return LIP_OK;
+    if (!X || !y) return fail(LIP_ERR_ARG, "X or y is NULL");
+    if (h->N + n > h->cap)
+        return fail(LIP_ERR_CAPACITY, "%lld + %lld points exceed the capacity %lld", (long long)h->N, (long long)n,
+                    (long long)h->cap);
+    const size_t es = h->esize;
+    CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(h->X0) + (size_t)h->N * h->d * es, X, (size_t)n * h->d * es, kind, st));
+    CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(h->y0) + (size_t)h->N * es, y, (size_t)n * es, kind, st));
+    CUDA_TRY(cudaMemsetAsync(h->status + 1, 0, sizeof(unsigned), st));
+    HotParams P;
+    fill_hot_params(h, P, h->N, h->N + n);
+    CUDA_TRY(launch_build_hot(h->esize, P, st));
+    count_launches(1);
+    unsigned bad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&bad, h->status + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (bad & ERRBIT_NONFINITE) {
+        CUDA_TRY(launch_pad_hot(h->esize, h->hot, h->N, h->N + n, h->nch, h->dl, st));
+        count_launches(1);
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return fail(LIP_ERR_NONFINITE, "X or y holds NaN or Inf");
+    }
+    h->N += n;
+    return LIP_OK;
+}
+
+lip_status fit_common(const void* X, const void* y, int64_t N, int32_t d, double M, const lip_params* p, void* stream,
+                      lip_handle* out, cudaMemcpyKind kind) {
+    if (!out) return fail(LIP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!X || !y) return fail(LIP_ERR_ARG, "X or y is NULL");
+    if (N < 1 || N >= (int64_t)1 << 31) return fail(LIP_ERR_ARG, "N = %lld is outside [1, 2^31)", (long long)N);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    lip_model* h = nullptr;
+    LIP_TRY(create_model(N, d, M, p, st, &h));
+    DeviceGuard g(h->device);
+    lip_status s = add_points(h, X, y, N, st, kind);
+    if (s != LIP_OK) {
+        free_model(h);
+        return s;
+    }
+    *out = h;
+    return LIP_OK;
+}
+
+// Number of N-splits: enough blocks to fill the GPU in nearly whole waves.
+int choose_splits(const lip_model* h, int64_t gx, int64_t tiles) {
+    if (h->splits > 0) return (int)std::max<int64_t>(1, std::min<int64_t>(h->splits, tiles));
+    const int64_t wave = (int64_t)h->sms * h->occ_blocks;
+    const int64_t smax = std::max<int64_t>(1, std::min<int64_t>(64, tiles / 2));
+    int best = 1;
+    double best_eff = 0.0;
+    for (int64_t s = 1; s <= smax; ++s) {
+        const int64_t blocks = gx * s;
+        const double eff = (double)blocks / (double)(ceil_div(blocks, wave) * wave);
+        if (eff > best_eff + 1e-9) { best_eff = eff; best = (int)s; }
+        if (eff >= 0.9) break;
+    }
+    return best;
+}
+
+lip_status eval_device(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* iu, int32_t* il,
+                       cudaStream_t st) {
+    const int64_t ngroups = round_up(h->N, PAD_POINTS) / GROUP;
+    const int tg = h->exact ? h->tile_groups : 1;
+    const int64_t gx = ceil_div(nq, (int64_t)SCAN_THREADS * h->kinfo.rows);
+    int nsplit = 0;
+    int64_t gps = 0;
+    if (ngroups > 0) {
+        const int64_t tiles = ngroups / (h->exact ? tg : TILE_GROUPS_MAX);
+        const int s = choose_splits(h, gx, tiles);
+        const int64_t unit = h->exact ? tg : TILE_GROUPS_MAX;
+        gps = round_up(ceil_div(ngroups, s), unit);
+        nsplit = (int)ceil_div(ngroups, gps);
+    }
+    h->last_splits = nsplit;
+    if (gx > 0x7fffffff) return fail(LIP_ERR_ARG, "nq = %lld is too large", (long long)nq);
+    const size_t rec = h->esize == 8 ? sizeof(PartialRec<double>) : sizeof(PartialRec<float>);
+    LIP_TRY(h->partial.ensure(std::max<size_t>(1, (size_t)nsplit * nq * rec), "scan scratch"));
+    if (nsplit > 0) {
+        ScanParams P;
+        fill_scan_params(h, P);
+        P.Q = Q;
+        P.nq = nq;
+        P.ngroups = ngroups;
+        P.groups_per_split = gps;
+        P.tile_groups = tg;
+        P.partial = h->partial.p;
+        if (h->ev_scan0) CUDA_TRY(cudaEventRecord(h->ev_scan0, st));
+        CUDA_TRY(h->kinfo.launch(P, (int)gx, nsplit, st));
+        if (h->ev_scan1) CUDA_TRY(cudaEventRecord(h->ev_scan1, st));
+        count_launches(1);
+    }
+    MergeParams Mp;
+    Mp.Q = Q;
+    Mp.nq = nq;
+    Mp.d = h->d;
+    Mp.nsplit = nsplit;
+    Mp.M = h->M;
+    Mp.norm = h->norm;
+    for (int i = 0; i < D_MAX; ++i) {
+        Mp.mon[i] = h->mon[i];
+        Mp.w[i] = h->w[i];
+    }
+    Mp.X0 = h->X0;
+    Mp.y0 = h->y0;
+    Mp.partial = h->partial.p;
+    Mp.g = g;
+    Mp.lo = lo;
+    Mp.hi = hi;
+    Mp.idx_up = iu;
+    Mp.idx_lo = il;
+    CUDA_TRY(launch_merge(h->esize, Mp, st));
+    count_launches(1);
+    return LIP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lip_status lip_fit(const void* X, const void* y, int64_t N, int32_t d, double M, const lip_params* p, void* stream,
+                   lip_handle* out) {
+    return fit_common(X, y, N, d, M, p, stream, out, cudaMemcpyDeviceToDevice);
+}
+
+lip_status lip_fit_host(const void* X, const void* y, int64_t N, int32_t d, double M, const lip_params* p, void* stream,
+                        lip_handle* out) {
+    return fit_common(X, y, N, d, M, p, stream, out, cudaMemcpyHostToDevice);
+}
+
+lip_status lip_reserve(int64_t capacity, int32_t d, double M, const lip_params* p, lip_handle* out) {
+    if (!out) return fail(LIP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    lip_model* h = nullptr;
+    LIP_TRY(create_model(capacity, d, M, p, nullptr, &h));
+    cudaError_t e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) {
+        free_model(h);
+        return cuda_fail(e, "lip_reserve");
+    }
+    *out = h;
+    return LIP_OK;
+}
+
+lip_status lip_add(lip_handle h, const void* X, const void* y, int64_t n, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    DeviceGuard g(h->device);
+    return add_points(h, X, y, n, static_cast<cudaStream_t>(stream), cudaMemcpyDeviceToDevice);
+}
+
+lip_status lip_add_host(lip_handle h, const void* X, const void* y, int64_t n, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    DeviceGuard g(h->device);
+    return add_points(h, X, y, n, static_cast<cudaStream_t>(stream), cudaMemcpyHostToDevice);
+}
+
+lip_status lip_clear(lip_handle h, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    DeviceGuard g(h->device);
+    CUDA_TRY(launch_pad_hot(h->esize, h->hot, 0, round_up(h->N, PAD_POINTS), h->nch, h->dl, static_cast<cudaStream_t>(stream)));
+    count_launches(1);
+    h->N = 0;
+    return LIP_OK;
+}
+
+int64_t lip_size(lip_handle h) { return h ? h->N : -1; }
+
+lip_status lip_set_M(lip_handle h, double M, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (!(M >= 0.0) || !std::isfinite(M)) return fail(LIP_ERR_ARG, "M = %g must be finite and >= 0", M);
+    DeviceGuard g(h->device);
+    h->M = M;
+    HotParams P;
+    fill_hot_params(h, P, 0, h->N);
+    CUDA_TRY(launch_build_hot(h->esize, P, static_cast<cudaStream_t>(stream)));
+    count_launches(1);
+    return LIP_OK;
+}
+
+lip_status lip_eval(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* idx_up,
+                    int32_t* idx_lo, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (nq < 0) return fail(LIP_ERR_ARG, "nq = %lld < 0", (long long)nq);
+    if (nq == 0) return LIP_OK;
+    if (!Q) return fail(LIP_ERR_ARG, "Q is NULL");
+    DeviceGuard gd(h->device);
+    return eval_device(h, Q, nq, g, lo, hi, idx_up, idx_lo, static_cast<cudaStream_t>(stream));
+}
+
+lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* idx_up,
+                         int32_t* idx_lo, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (nq < 0) return fail(LIP_ERR_ARG, "nq = %lld < 0", (long long)nq);
+    if (nq == 0) return LIP_OK;
+    if (!Q) return fail(LIP_ERR_ARG, "Q is NULL");
+    DeviceGuard gd(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!h->copy_stream) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            CUDA_TRY(cudaEventCreateWithFlags(&h->ev_in[b], cudaEventDisableTiming));
+            CUDA_TRY(cudaEventCreateWithFlags(&h->ev_out[b], cudaEventDisableTiming));
+        }
+    }
+    const size_t es = h->esize;
+    const int64_t chunk = std::min<int64_t>(nq, (int64_t)1 << 19);
+    // per buffer: Q chunk, g, lo, hi, idx_up, idx_lo
+    const size_t qb = round_up((int64_t)(chunk * h->d * es), 256), vb = round_up((int64_t)(chunk * es), 256),
+                 ib = round_up((int64_t)(chunk * 4), 256);
+    const size_t per = qb + 3 * vb + 2 * ib;
+    LIP_TRY(h->io.ensure(2 * per, "host-path staging"));
+    char* base = static_cast<char*>(h->io.p);
+    auto dQ = [&](int b) { return base + b * per; };
+    auto dV = [&](int b, int k) { return base + b * per + qb + k * vb; };
+    auto dI = [&](int b, int k) { return base + b * per + qb + 3 * vb + k * ib; };
+    const int64_t nchunks = ceil_div(nq, chunk);
+    cudaStream_t cs = h->copy_stream;
+    // the copy stream starts after everything already queued on the caller's stream
+    CUDA_TRY(cudaEventRecord(h->ev_out[0], st));
+    CUDA_TRY(cudaStreamWaitEvent(cs, h->ev_out[0], 0));
+    auto h2d = [&](int64_t c) -> lip_status {
+        const int b = (int)(c & 1);
+        const int64_t q0 = c * chunk, n = std::min(chunk, nq - q0);
+        CUDA_TRY(cudaMemcpyAsync(dQ(b), static_cast<const char*>(Q) + (size_t)q0 * h->d * es, (size_t)n * h->d * es,
+                                 cudaMemcpyHostToDevice, cs));
+        CUDA_TRY(cudaEventRecord(h->ev_in[b], cs));
+        return LIP_OK;
+    };
+    LIP_TRY(h2d(0));
+    if (nchunks > 1) LIP_TRY(h2d(1));
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int b = (int)(c & 1);
+        const int64_t q0 = c * chunk, n = std::min(chunk, nq - q0);
+        CUDA_TRY(cudaStreamWaitEvent(st, h->ev_in[b], 0));
+        LIP_TRY(eval_device(h, dQ(b), n, g ? dV(b, 0) : nullptr, lo ? dV(b, 1) : nullptr, hi ? dV(b, 2) : nullptr,
+                            idx_up ? reinterpret_cast<int32_t*>(dI(b, 0)) : nullptr,
+                            idx_lo ? reinterpret_cast<int32_t*>(dI(b, 1)) : nullptr, st));
+        CUDA_TRY(cudaEventRecord(h->ev_out[b], st));
+        CUDA_TRY(cudaStreamWaitEvent(cs, h->ev_out[b], 0));
+        void* outs[3] = {g, lo, hi};
+        for (int k = 0; k < 3; ++k)
+            if (outs[k])
+                CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(outs[k]) + (size_t)q0 * es, dV(b, k), (size_t)n * es,
+                                         cudaMemcpyDeviceToHost, cs));
+        int32_t* idx[2] = {idx_up, idx_lo};
+        for (int k = 0; k < 2; ++k)
+            if (idx[k]) CUDA_TRY(cudaMemcpyAsync(idx[k] + q0, dI(b, k), (size_t)n * 4, cudaMemcpyDeviceToHost, cs));
+        if (c + 2 < nchunks) LIP_TRY(h2d(c + 2));
+    }
+    CUDA_TRY(cudaStreamSynchronize(cs));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return LIP_OK;
+}
+
+lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, int64_t* j_out, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (!M_out || !i_out || !j_out) return fail(LIP_ERR_ARG, "an output pointer is NULL");
+    DeviceGuard gd(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    *M_out = 0.0;
+    *i_out = *j_out = -1;
+    if (h->N < 2) return LIP_OK;
+    const int tile = estimate_tile_points();
+    const int64_t nb = ceil_div(h->N, tile);
+    if (nb > 65535) return fail(LIP_ERR_UNSUPPORTED, "N = %lld is too large for lip_estimate_M", (long long)h->N);
+    const int64_t pts = nb * tile;
+    const int nch = h->d + 1;
+    const size_t lay_b = round_up(pts * nch * 4, 256), cand_b = round_up(nb * nb * 16, 256);
+    LIP_TRY(h->est.ensure(lay_b + cand_b + 256, "estimate scratch"));
+    char* base = static_cast<char*>(h->est.p);
+    // unscaled layout: coordinates times the weights, caller's order, FP32
+    HotParams Hp;
+    Hp.X0 = h->X0;
+    Hp.y0 = h->y0;
+    Hp.k0 = 0;
+    Hp.k1 = h->N;
+    Hp.d = h->d;
+    Hp.C = 0;
+    Hp.dl = h->d;
+    Hp.nch = nch;
+    Hp.aux = 0;
+    for (int j = 0; j < D_MAX; ++j) {
+        Hp.perm[j] = j;
+        Hp.scale[j] = h->w[j];
+    }
+    Hp.hot = base;
+    Hp.err = h->status + 1;
+    CUDA_TRY(launch_estimate_layout(h->esize, Hp, st));
+    CUDA_TRY(launch_pad_hot(4, base, h->N, pts, nch, h->d, st));
+    EstParams P;
+    P.lay = reinterpret_cast<const float4*>(base);
+    P.N = h->N;
+    P.nb = (int)nb;
+    P.cand = reinterpret_cast<float4*>(base + lay_b);
+    CUDA_TRY(launch_estimate(h->norm, h->d, P, st));
+    EstFinalParams F;
+    F.cand = P.cand;
+    F.nb = (int)nb;
+    F.X0 = h->X0;
+    F.y0 = h->y0;
+    F.d = h->d;
+    F.norm = h->norm;
+    F.elem_bytes = h->esize;
+    for (int j = 0; j < D_MAX; ++j) F.w[j] = h->w[j];
+    F.out = reinterpret_cast<double*>(base + lay_b + cand_b);
+    CUDA_TRY(launch_estimate_final(F, st));
+    count_launches(4);
+    double res[3];
+    CUDA_TRY(cudaMemcpyAsync(res, F.out, sizeof res, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    *M_out = res[0];
+    *i_out = (int64_t)res[1];
+    *j_out = (int64_t)res[2];
+    return LIP_OK;
+}
+
+lip_status lip_backward(lip_handle h, const void* Q, int64_t nq, const int32_t* idx_up, const int32_t* idx_lo,
+                        const void* grad_g, void* grad_Q, void* grad_y, double* grad_M, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (nq < 0) return fail(LIP_ERR_ARG, "nq = %lld < 0", (long long)nq);
+    if (nq > 0 && (!Q || !idx_up || !idx_lo || !grad_g)) return fail(LIP_ERR_ARG, "Q, indices or grad_g is NULL");
+    DeviceGuard gd(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nb = backward_blocks(nq);
+    const size_t part_b = round_up((int64_t)std::max(nb, 1) * 8, 256);
+    const size_t gy_b = grad_y ? round_up(std::max<int64_t>(h->N, 1) * 8, 256) : 0;
+    LIP_TRY(h->bwd.ensure(part_b + gy_b, "backward scratch"));
+    char* base = static_cast<char*>(h->bwd.p);
+    BwdParams P;
+    P.Q = Q;
+    P.nq = nq;
+    P.d = h->d;
+    P.norm = h->norm;
+    P.M = h->M;
+    for (int i = 0; i < D_MAX; ++i) {
+        P.mon[i] = h->mon[i];
+        P.w[i] = h->w[i];
+    }
+    P.X0 = h->X0;
+    P.iu = idx_up;
+    P.il = idx_lo;
+    P.gbar = grad_g;
+    P.grad_Q = grad_Q;
+    P.gm_part = reinterpret_cast<double*>(base);
+    P.gy64 = grad_y ? reinterpret_cast<double*>(base + part_b) : nullptr;
+    if (P.gy64) CUDA_TRY(cudaMemsetAsync(P.gy64, 0, (size_t)h->N * 8, st));
+    if (nq == 0) {
+        if (grad_M) CUDA_TRY(cudaMemsetAsync(grad_M, 0, sizeof(double), st));
+        return LIP_OK;
+    }
+    CUDA_TRY(launch_backward(h->esize, P, h->N, grad_y, grad_M, st));
+    count_launches(1 + (grad_M ? 1 : 0) + (grad_y && h->N > 0 ? 1 : 0));
+    return LIP_OK;
+}
+
+lip_status lip_check(lip_handle h, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    DeviceGuard gd(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned bits = 0;
+    CUDA_TRY(cudaMemcpyAsync(&bits, h->status, sizeof bits, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (bits) {
+        CUDA_TRY(cudaMemsetAsync(h->status, 0, sizeof bits, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    if (bits & ERRBIT_TIMEOUT) return fail(LIP_ERR_TIMEOUT, "a bounded wait in a kernel gave up");
+    return LIP_OK;
+}
+
+lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (tile_groups != 0 && tile_groups != 8 && tile_groups != 16 && tile_groups != 32 && tile_groups != 64)
+        return fail(LIP_ERR_ARG, "tile_groups = %d is not 0, 8, 16, 32 or 64", tile_groups);
+    if (splits < 0 || splits > 4096) return fail(LIP_ERR_ARG, "splits = %d is outside [0, 4096]", splits);
+    DeviceGuard gd(h->device);
+    if (tile_groups) h->tile_groups = tile_groups;
+    h->splits = splits;
+    if (h->exact) {
+        const size_t smem = (size_t)SCAN_STAGES * h->tile_groups * h->nch * 16;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_blocks, h->kinfo.kernel, SCAN_THREADS, smem) !=
+                cudaSuccess || h->occ_blocks < 1) {
+            cudaGetLastError();
+            h->occ_blocks = 1;
+        }
+    }
+    return LIP_OK;
+}
+
+lip_status lip_get_tuning(lip_handle h, int32_t* tile_groups, int32_t* splits, int32_t* last_splits,
+                          int32_t* queries_per_thread) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (tile_groups) *tile_groups = h->tile_groups;
+    if (splits) *splits = h->splits;
+    if (last_splits) *last_splits = h->last_splits;
+    if (queries_per_thread) *queries_per_thread = h->kinfo.rows;
+    return LIP_OK;
+}
+
+lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, void* ev_after_scan) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if ((ev_before_scan == nullptr) != (ev_after_scan == nullptr)) return fail(LIP_ERR_ARG, "give both events or neither");
+    h->ev_scan0 = static_cast<cudaEvent_t>(ev_before_scan);
+    h->ev_scan1 = static_cast<cudaEvent_t>(ev_after_scan);
+    return LIP_OK;
+}
+
+uint64_t lip_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void lip_free(lip_handle h) { free_model(h); }
+
+const char* lip_status_string(lip_status s) {
+    switch (s) {
+        case LIP_OK: return "ok";
+        case LIP_ERR_ARG: return "invalid argument";
+        case LIP_ERR_NONFINITE: return "non-finite data";
+        case LIP_ERR_OOM: return "out of memory";
+        case LIP_ERR_CUDA: return "CUDA error";
+        case LIP_ERR_CAPACITY: return "capacity exceeded";
+        case LIP_ERR_TIMEOUT: return "device wait timed out";
+        case LIP_ERR_UNSUPPORTED: return "unsupported";
+        case LIP_ERR_NO_DEVICE: return "no CUDA device";
+    }
+    return "unknown status";
+}
+
+size_t lip_last_error(char* buf, size_t len) {
+    if (buf && len > 0) {
+        const size_t n = std::min(len - 1, g_err.size());
+        std::memcpy(buf, g_err.data(), n);
+        buf[n] = 0;
+    }
+    return g_err.size();
+}
+
+const char* lip_version(void) { return "0.1.0 sm_103a"; }
+
+}  // extern "C"

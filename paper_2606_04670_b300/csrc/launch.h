@@ -1,0 +1,55 @@
+// Parameter blocks and host launchers shared between the kernel units and the C ABI.
+#pragma once
+#include <utility>
+
+#include "scan.cuh"
+
+namespace lip {
+
+struct EstParams {
+    const float4* lay;    // unscaled layout (w * sign), nch = D + 1 channels per group
+    int64_t N;
+    int nb;               // tiles per side
+    float4* cand;         // [nb * nb]: {ratio^2, bits(i), bits(j), valid}
+};
+
+struct EstFinalParams {
+    const float4* cand;
+    int nb;
+    const void* X0;
+    const void* y0;
+    int d, norm, elem_bytes;
+    double w[D_MAX];
+    double* out;          // [3]: M_est, i, j (as doubles)
+};
+
+struct BwdParams {
+    const void* Q;
+    int64_t nq;
+    int d, norm;
+    double M;
+    int8_t mon[D_MAX];
+    double w[D_MAX];
+    const void* X0;
+    const int32_t* iu;
+    const int32_t* il;
+    const void* gbar;
+    void* grad_Q;            // nullable, [nq][d]
+    double* gy64;            // nullable, [N] scratch (zeroed by the caller)
+    double* gm_part;         // [backward_blocks(nq)] per-block partial sums of dL/dM
+};
+
+cudaError_t launch_merge(int elem_bytes, const MergeParams& P, cudaStream_t st);
+cudaError_t launch_build_hot(int elem_bytes, const HotParams& P, cudaStream_t st);
+cudaError_t launch_pad_hot(int elem_bytes, void* hot, int64_t k0, int64_t k1, int nch, int dl, cudaStream_t st);
+
+int estimate_tile_points();
+cudaError_t launch_estimate_layout(int elem_bytes, const HotParams& P, cudaStream_t st);
+cudaError_t launch_estimate(int norm, int d, const EstParams& P, cudaStream_t st);
+cudaError_t launch_estimate_final(const EstFinalParams& P, cudaStream_t st);
+
+int backward_blocks(int64_t nq);
+cudaError_t launch_backward(int elem_bytes, const BwdParams& P, int64_t N, void* grad_y, double* grad_M,
+                            cudaStream_t st);
+
+}  // namespace lip

@@ -1,0 +1,10 @@
+// Exact-shape FP32 scan kernels for the LINF norm.
+#include "scan_inst.cuh"
+
+namespace lip {
+ScanKernelInfo scan_exact_info_linf(int C, int U) {
+    static ExactTable<LIP_LINF> t;
+    if (C < 0 || U < 0 || C > D_MAX || U > D_MAX) return {};
+    return t.tab[C][U];
+}
+}  // namespace lip

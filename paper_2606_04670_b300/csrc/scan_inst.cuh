@@ -1,0 +1,41 @@
+// Instantiation table of the exact-shape scan kernels for one norm (SCAN_NORM).
+#pragma once
+#include <utility>
+
+#include "scan.cuh"
+
+namespace lip {
+
+template <int NORM, int C, int U>
+cudaError_t launch_scan_exact(const ScanParams& P, int gx, int gy, cudaStream_t st) {
+    constexpr int R = rows_for_dim(C + U);
+    constexpr int NCH = ExactShape<NORM, C, U>::NCH;
+    auto kern = scan_exact_kernel<NORM, C, U, R>;
+    const size_t smem = (size_t)SCAN_STAGES * P.tile_groups * NCH * sizeof(float4);
+    static cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   SCAN_STAGES * TILE_GROUPS_MAX * NCH * (int)sizeof(float4));
+    if (attr != cudaSuccess) return attr;
+    kern<<<dim3(gx, gy), SCAN_THREADS, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+template <int NORM>
+struct ExactTable {
+    ScanKernelInfo tab[D_MAX + 1][D_MAX + 1];
+    template <int K>
+    void fill_one() {
+        constexpr int C = K / (D_MAX + 1), U = K % (D_MAX + 1);
+        if constexpr (exact_shape_available(C, U)) {
+            ScanKernelInfo& e = tab[C][U];
+            e.launch = &launch_scan_exact<NORM, C, U>;
+            e.kernel = reinterpret_cast<const void*>(&scan_exact_kernel<NORM, C, U, rows_for_dim(C + U)>);
+            e.rows = rows_for_dim(C + U);
+            e.nch = ExactShape<NORM, C, U>::NCH;
+        }
+    }
+    template <int... K>
+    void fill(std::integer_sequence<int, K...>) { (fill_one<K>(), ...); }
+    ExactTable() { fill(std::make_integer_sequence<int, (D_MAX + 1) * (D_MAX + 1)>{}); }
+};
+
+}  // namespace lip

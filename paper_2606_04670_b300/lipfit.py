@@ -1,0 +1,434 @@
+"""Python binding of liblipfit.so (argument marshalling only; all arithmetic runs in the
+library's CUDA kernels).
+
+Module-level functions mirror the C ABI one to one (``lip_fit``, ``lip_eval``, ...),
+taking raw pointers; ``LipFit`` wraps a handle for torch tensors on the GPU, following
+the paper's package interface (Sec. 5: add, values, lipschitz_constant, clear,
+setparams); ``LipEvalFn`` is the ``torch.autograd.Function`` whose backward is the
+library's backward kernel.
+
+There is no CPU fallback: if the compiled library is missing, importing this module
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblipfit.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "lipfit.h")
+
+LIP_OK, LIP_ERR_ARG, LIP_ERR_NONFINITE, LIP_ERR_OOM, LIP_ERR_CUDA = 0, 1, 2, 3, 4
+LIP_ERR_CAPACITY, LIP_ERR_TIMEOUT, LIP_ERR_UNSUPPORTED, LIP_ERR_NO_DEVICE = 5, 6, 7, 8
+LIP_L1, LIP_L2, LIP_LINF = 1, 2, 3
+LIP_FP32, LIP_FP64, LIP_TC_BF16, LIP_TC_TF32 = 0, 1, 2, 3
+NORMS = {"L1": LIP_L1, "L2": LIP_L2, "Linf": LIP_LINF, "LINF": LIP_LINF,
+         LIP_L1: LIP_L1, LIP_L2: LIP_L2, LIP_LINF: LIP_LINF}
+PRECISIONS = {"fp32": LIP_FP32, "fp64": LIP_FP64, "tc_bf16": LIP_TC_BF16, "tc_tf32": LIP_TC_TF32,
+              LIP_FP32: LIP_FP32, LIP_FP64: LIP_FP64, LIP_TC_BF16: LIP_TC_BF16, LIP_TC_TF32: LIP_TC_TF32}
+
+
+class lip_params(ctypes.Structure):
+    _fields_ = [("norm", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("mon", ctypes.c_void_p), ("w", ctypes.c_void_p)]
+
+
+class LipError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {status_string(status)} ({status}): {detail}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built: run paper_2606_04670_b300.build.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    H = ctypes.c_void_p
+    sig = {
+        "lip_fit": [P, P, i64, i32, f64, ctypes.POINTER(lip_params), P, ctypes.POINTER(H)],
+        "lip_fit_host": [P, P, i64, i32, f64, ctypes.POINTER(lip_params), P, ctypes.POINTER(H)],
+        "lip_reserve": [i64, i32, f64, ctypes.POINTER(lip_params), ctypes.POINTER(H)],
+        "lip_add": [H, P, P, i64, P],
+        "lip_add_host": [H, P, P, i64, P],
+        "lip_clear": [H, P],
+        "lip_set_M": [H, f64, P],
+        "lip_eval": [H, P, i64, P, P, P, P, P, P],
+        "lip_eval_host": [H, P, i64, P, P, P, P, P, P],
+        "lip_estimate_M": [H, ctypes.POINTER(f64), ctypes.POINTER(i64), ctypes.POINTER(i64), P],
+        "lip_backward": [H, P, i64, P, P, P, P, P, P, P],
+        "lip_check": [H, P],
+        "lip_set_tuning": [H, i32, i32],
+        "lip_get_tuning": [H, P, P, P, P],
+        "lip_set_timing_events": [H, P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.lip_size.argtypes = [H]
+    lib.lip_size.restype = i64
+    lib.lip_free.argtypes = [H]
+    lib.lip_free.restype = None
+    lib.lip_status_string.argtypes = [ctypes.c_int]
+    lib.lip_status_string.restype = ctypes.c_char_p
+    lib.lip_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    lib.lip_last_error.restype = ctypes.c_size_t
+    lib.lip_version.restype = ctypes.c_char_p
+    lib.lip_kernel_launches.restype = ctypes.c_uint64
+    return lib
+
+
+_lib = _load()
+
+
+def library():
+    return _lib
+
+
+def header_symbols(path: str = HEADER) -> list:
+    """Names of the functions that include/lipfit.h declares."""
+    return sorted(set(re.findall(r"^LIP_API\s+[\w\s\*]+?\b(lip_\w+)\s*\(", open(path).read(), re.M)))
+
+
+def status_string(s: int) -> str:
+    return _lib.lip_status_string(int(s)).decode()
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    _lib.lip_last_error(buf, len(buf))
+    return buf.value.decode()
+
+
+def _check(status: int, where: str):
+    if status != LIP_OK:
+        raise LipError(status, where, last_error())
+
+
+def make_params(norm=LIP_L2, precision=LIP_FP32, mon=None, w=None):
+    """lip_params plus the host arrays it points to (kept alive by the returned tuple)."""
+    mon_a = None if mon is None else np.ascontiguousarray(np.asarray(mon), dtype=np.int8)
+    w_a = None if w is None else np.ascontiguousarray(np.asarray(w), dtype=np.float64)
+    # unknown integers are passed through so that the library itself rejects them
+    nv = NORMS.get(norm, norm) if isinstance(norm, (int, np.integer)) else NORMS[norm]
+    pv = PRECISIONS.get(precision, precision) if isinstance(precision, (int, np.integer)) else PRECISIONS[precision]
+    p = lip_params(int(nv), int(pv),
+                   None if mon_a is None else mon_a.ctypes.data, None if w_a is None else w_a.ctypes.data)
+    return p, (mon_a, w_a)
+
+
+# ------------------------------------------------------------- raw ABI (same names)
+
+def lip_fit(X_ptr, y_ptr, N, d, M, params, stream=0):
+    h = ctypes.c_void_p()
+    return _lib.lip_fit(X_ptr, y_ptr, N, d, M, ctypes.byref(params), stream, ctypes.byref(h)), h
+
+
+def lip_fit_host(X_ptr, y_ptr, N, d, M, params, stream=0):
+    h = ctypes.c_void_p()
+    return _lib.lip_fit_host(X_ptr, y_ptr, N, d, M, ctypes.byref(params), stream, ctypes.byref(h)), h
+
+
+def lip_reserve(capacity, d, M, params):
+    h = ctypes.c_void_p()
+    return _lib.lip_reserve(capacity, d, M, ctypes.byref(params), ctypes.byref(h)), h
+
+
+def lip_add(h, X_ptr, y_ptr, n, stream=0):
+    return _lib.lip_add(h, X_ptr, y_ptr, n, stream)
+
+
+def lip_add_host(h, X_ptr, y_ptr, n, stream=0):
+    return _lib.lip_add_host(h, X_ptr, y_ptr, n, stream)
+
+
+def lip_clear(h, stream=0):
+    return _lib.lip_clear(h, stream)
+
+
+def lip_size(h):
+    return _lib.lip_size(h)
+
+
+def lip_set_M(h, M, stream=0):
+    return _lib.lip_set_M(h, M, stream)
+
+
+def lip_eval(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream=0):
+    return _lib.lip_eval(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream)
+
+
+def lip_eval_host(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream=0):
+    return _lib.lip_eval_host(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream)
+
+
+def lip_estimate_M(h, stream=0):
+    M, i, j = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+    s = _lib.lip_estimate_M(h, ctypes.byref(M), ctypes.byref(i), ctypes.byref(j), stream)
+    return s, M.value, i.value, j.value
+
+
+def lip_backward(h, Q_ptr, nq, idx_up, idx_lo, grad_g, grad_Q, grad_y, grad_M, stream=0):
+    return _lib.lip_backward(h, Q_ptr, nq, idx_up, idx_lo, grad_g, grad_Q, grad_y, grad_M, stream)
+
+
+def lip_set_tuning(h, tile_groups, splits):
+    return _lib.lip_set_tuning(h, tile_groups, splits)
+
+
+def lip_get_tuning(h):
+    v = [ctypes.c_int32() for _ in range(4)]
+    s = _lib.lip_get_tuning(h, *[ctypes.byref(x) for x in v])
+    return s, tuple(x.value for x in v)
+
+
+def lip_set_timing_events(h, ev_before, ev_after):
+    return _lib.lip_set_timing_events(h, ev_before, ev_after)
+
+
+def lip_kernel_launches():
+    return int(_lib.lip_kernel_launches())
+
+
+def lip_check(h, stream=0):
+    return _lib.lip_check(h, stream)
+
+
+def lip_free(h):
+    _lib.lip_free(h)
+
+
+def lip_status_string(s):
+    return status_string(s)
+
+
+def lip_last_error():
+    return last_error()
+
+
+def lip_version():
+    return _lib.lip_version().decode()
+
+
+# ------------------------------------------------------------------ torch front end
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr():
+    torch = _torch()
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+class LipFit:
+    """A fitted data set on the GPU (Sec. 5: LipFit(reservedata, dim), add, values, ...).
+
+    X [N, d] and y [N] are CUDA tensors (float32, or float64 with precision='fp64').
+    norm: 'L1' | 'L2' | 'Linf'; mon: d entries in {-1,0,1} or None; w: d norm weights
+    or None.  The data are copied into library-owned memory.
+    """
+
+    def __init__(self, X=None, y=None, M: float = 1.0, norm="L2", mon=None, w=None,
+                 precision="fp32", capacity: Optional[int] = None, d: Optional[int] = None):
+        torch = _torch()
+        self.norm = NORMS[norm]
+        self.precision = PRECISIONS[precision]
+        self.dtype = torch.float64 if self.precision == LIP_FP64 else torch.float32
+        self.mon = None if mon is None else np.asarray(mon, np.int8)
+        self.w = None if w is None else np.asarray(w, np.float64)
+        self._M = float(M)
+        params, self._keep = make_params(self.norm, self.precision, self.mon, self.w)
+        self.h = ctypes.c_void_p()
+        if X is not None:
+            X = self._dev(X)
+            y = self._dev(y)
+            self.d = int(X.shape[1])
+            if capacity is None or capacity <= X.shape[0]:
+                _check(_lib.lip_fit(X.data_ptr(), y.data_ptr(), X.shape[0], self.d, self._M,
+                                    ctypes.byref(params), _stream_ptr(), ctypes.byref(self.h)), "lip_fit")
+            else:
+                _check(_lib.lip_reserve(capacity, self.d, self._M, ctypes.byref(params),
+                                        ctypes.byref(self.h)), "lip_reserve")
+                self.add(X, y)
+        else:
+            assert capacity is not None and d is not None, "give X, y or capacity and d"
+            self.d = int(d)
+            _check(_lib.lip_reserve(capacity, self.d, self._M, ctypes.byref(params),
+                                    ctypes.byref(self.h)), "lip_reserve")
+
+    def _dev(self, t):
+        torch = _torch()
+        if not torch.is_tensor(t):
+            t = torch.as_tensor(np.asarray(t))
+        return t.to(device="cuda", dtype=self.dtype).contiguous()
+
+    # -- data (Sec. 5)
+    def add(self, X, y):
+        X, y = self._dev(X), self._dev(y)
+        _check(_lib.lip_add(self.h, X.data_ptr(), y.data_ptr(), X.shape[0], _stream_ptr()), "lip_add")
+
+    def add_host(self, X, y):
+        """lip_add_host: X, y are host arrays (numpy or pinned CPU tensors) of the handle's type."""
+        torch = _torch()
+
+        def p(a):
+            return a.data_ptr() if torch.is_tensor(a) else a.ctypes.data
+
+        _check(_lib.lip_add_host(self.h, p(X), p(y), X.shape[0], _stream_ptr()), "lip_add_host")
+
+    def clear(self):
+        _check(_lib.lip_clear(self.h, _stream_ptr()), "lip_clear")
+
+    @property
+    def N(self) -> int:
+        return int(_lib.lip_size(self.h))
+
+    @property
+    def M(self) -> float:
+        return self._M
+
+    def set_M(self, M: float):
+        _check(_lib.lip_set_M(self.h, float(M), _stream_ptr()), "lip_set_M")
+        self._M = float(M)
+
+    # -- evaluation
+    def eval(self, Q, need=("g", "lo", "hi", "idx_up", "idx_lo")):
+        """Dict of CUDA tensors g, lo, hi (H_lo, H_up) and idx_up, idx_lo for queries Q."""
+        torch = _torch()
+        Q = self._dev(Q)
+        nq = Q.shape[0]
+        out = {}
+        for k in ("g", "lo", "hi"):
+            out[k] = torch.empty(nq, device="cuda", dtype=self.dtype) if k in need else None
+        for k in ("idx_up", "idx_lo"):
+            out[k] = torch.empty(nq, device="cuda", dtype=torch.int32) if k in need else None
+        _check(_lib.lip_eval(self.h, Q.data_ptr(), nq, _ptr(out["g"]), _ptr(out["lo"]), _ptr(out["hi"]),
+                             _ptr(out["idx_up"]), _ptr(out["idx_lo"]), _stream_ptr()), "lip_eval")
+        return {k: v for k, v in out.items() if v is not None}
+
+    def values(self, Q):
+        """g at the query points (Sec. 5: values(query, LC, model, k=1))."""
+        return self.eval(Q, need=("g",))["g"]
+
+    def eval_host(self, Q, out=None):
+        """lip_eval_host: Q and the outputs in host memory (numpy or pinned CPU tensors)."""
+        torch = _torch()
+        if torch.is_tensor(Q):
+            Qh = Q
+            nq = Q.shape[0]
+            qptr = Q.data_ptr()
+        else:
+            Qh = np.ascontiguousarray(Q, dtype=np.float64 if self.precision == LIP_FP64 else np.float32)
+            nq = Qh.shape[0]
+            qptr = Qh.ctypes.data
+        if out is None:
+            npdt = np.float64 if self.precision == LIP_FP64 else np.float32
+            out = {k: np.empty(nq, npdt) for k in ("g", "lo", "hi")}
+            out.update({k: np.empty(nq, np.int32) for k in ("idx_up", "idx_lo")})
+
+        def p(a):
+            if a is None:
+                return None
+            return a.data_ptr() if torch.is_tensor(a) else a.ctypes.data
+
+        _check(_lib.lip_eval_host(self.h, qptr, nq, p(out.get("g")), p(out.get("lo")), p(out.get("hi")),
+                                  p(out.get("idx_up")), p(out.get("idx_lo")), _stream_ptr()), "lip_eval_host")
+        return out
+
+    def lipschitz_constant(self):
+        """(M_est, i, j) (Sec. 5: lipschitz_constant()); synchronises."""
+        s, M, i, j = lip_estimate_M(self.h, _stream_ptr())
+        _check(s, "lip_estimate_M")
+        return M, i, j
+
+    def backward(self, Q, idx_up, idx_lo, grad_g, need_Q=True, need_y=True, need_M=True):
+        torch = _torch()
+        Q = self._dev(Q)
+        gg = grad_g.to(device="cuda", dtype=self.dtype).contiguous()
+        gQ = torch.empty_like(Q) if need_Q else None
+        gy = torch.zeros(self.N, device="cuda", dtype=self.dtype) if need_y else None
+        gM = torch.zeros(1, device="cuda", dtype=torch.float64) if need_M else None
+        _check(_lib.lip_backward(self.h, Q.data_ptr(), Q.shape[0], idx_up.data_ptr(), idx_lo.data_ptr(),
+                                 gg.data_ptr(), _ptr(gQ), _ptr(gy), _ptr(gM), _stream_ptr()), "lip_backward")
+        return gQ, gy, gM
+
+    def check(self):
+        _check(_lib.lip_check(self.h, _stream_ptr()), "lip_check")
+
+    def set_tuning(self, tile_groups: int = 0, splits: int = 0):
+        _check(_lib.lip_set_tuning(self.h, int(tile_groups), int(splits)), "lip_set_tuning")
+
+    def set_timing_events(self, ev_before=None, ev_after=None):
+        """torch.cuda.Event pair recorded around the scan kernel of every eval (None: off)."""
+        for ev in (ev_before, ev_after):
+            if ev is not None and not ev.cuda_event:
+                ev.record()            # torch creates the CUDA event on first record
+        a = None if ev_before is None else ev_before.cuda_event
+        b = None if ev_after is None else ev_after.cuda_event
+        _check(_lib.lip_set_timing_events(self.h, a, b), "lip_set_timing_events")
+
+    def tuning(self):
+        s, (tg, sp, last, rows) = lip_get_tuning(self.h)
+        _check(s, "lip_get_tuning")
+        return {"tile_groups": tg, "splits": sp, "last_splits": last, "queries_per_thread": rows}
+
+    def close(self):
+        if self.h:
+            _lib.lip_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class LipEvalFn(torch.autograd.Function):
+        """g(Q) with gradients for Q, y and M through the saved argmin/argmax.
+
+        ``LipEvalFn.apply(Q, y, M, model)``: y and M are the tensors ``model`` was built
+        from (y [N], M a 0-d or 1-element tensor); they only receive gradients.
+        """
+
+        @staticmethod
+        def forward(ctx, Q, y, M, model):
+            r = model.eval(Q, need=("g", "idx_up", "idx_lo"))
+            ctx.model = model
+            ctx.M_shape, ctx.M_dtype = M.shape, M.dtype
+            ctx.save_for_backward(Q, r["idx_up"], r["idx_lo"])
+            return r["g"]
+
+        @staticmethod
+        def backward(ctx, grad_g):
+            Q, iu, il = ctx.saved_tensors
+            m = ctx.model
+            nQ, ny, nM = ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2]
+            gQ, gy, gM = m.backward(Q, iu, il, grad_g, need_Q=nQ, need_y=ny, need_M=nM)
+            gMo = gM.to(ctx.M_dtype).reshape(ctx.M_shape) if nM else None
+            return gQ, gy, gMo, None
+
+    return LipEvalFn
+
+
+LipEvalFn = None
+try:  # torch is optional for the raw ABI functions
+    LipEvalFn = _make_autograd()
+except Exception:  # pragma: no cover
+    pass

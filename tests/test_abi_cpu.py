@@ -1,0 +1,87 @@
+"""The C ABI without a GPU: the library loads, exports every function the header
+declares, and rejects bad arguments on the host before touching the device."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2606_04670_b300 import lipfit as L
+
+
+def test_exports_every_declared_symbol():
+    names = L.header_symbols()
+    assert len(names) >= 20
+    lib = ctypes.CDLL(L.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version():
+    for s in range(9):
+        assert L.status_string(s) and L.status_string(s) != "unknown status"
+    assert L.status_string(99) == "unknown status"
+    assert "sm_103a" in L.lip_version()
+
+
+def _arr(*shape):
+    return np.zeros(shape, np.float32)
+
+
+@pytest.mark.parametrize("kw,status", [
+    ({"N": 0}, L.LIP_ERR_ARG),
+    ({"N": 1 << 31}, L.LIP_ERR_ARG),
+    ({"d": 0}, L.LIP_ERR_ARG),
+    ({"d": 17}, L.LIP_ERR_ARG),
+    ({"M": -1.0}, L.LIP_ERR_ARG),
+    ({"M": float("nan")}, L.LIP_ERR_ARG),
+    ({"M": float("inf")}, L.LIP_ERR_ARG),
+    ({"norm": 4}, L.LIP_ERR_ARG),
+    ({"precision": 9}, L.LIP_ERR_ARG),
+    ({"mon": [2, 0]}, L.LIP_ERR_ARG),
+    ({"w": [1.0, 0.0]}, L.LIP_ERR_ARG),
+    ({"w": [1.0, float("nan")]}, L.LIP_ERR_ARG),
+    ({"norm": L.LIP_L1, "precision": L.LIP_TC_BF16}, L.LIP_ERR_UNSUPPORTED),
+    ({"nullX": True}, L.LIP_ERR_ARG),
+])
+def test_fit_argument_errors(kw, status):
+    X, y = _arr(8, 2), _arr(8)
+    p, keep = L.make_params(kw.get("norm", L.LIP_L2), kw.get("precision", L.LIP_FP32), kw.get("mon"), kw.get("w"))
+    s, h = L.lip_fit(None if kw.get("nullX") else X.ctypes.data, y.ctypes.data, kw.get("N", 8), kw.get("d", 2),
+                     kw.get("M", 1.0), p)
+    assert s == status, L.last_error()
+    assert not h.value
+    assert L.last_error()
+
+
+def test_null_handle_calls():
+    assert L.lip_eval(None, None, 1, None, None, None, None, None) == L.LIP_ERR_ARG
+    assert L.lip_add(None, None, None, 1) == L.LIP_ERR_ARG
+    assert L.lip_add_host(None, None, None, 1) == L.LIP_ERR_ARG
+    assert L.lip_clear(None) == L.LIP_ERR_ARG
+    assert L.lip_set_M(None, 1.0) == L.LIP_ERR_ARG
+    assert L.lip_estimate_M(None)[0] == L.LIP_ERR_ARG
+    assert L.lip_backward(None, None, 0, None, None, None, None, None, None) == L.LIP_ERR_ARG
+    assert L.lip_check(None) == L.LIP_ERR_ARG
+    assert L.lip_set_tuning(None, 0, 0) == L.LIP_ERR_ARG
+    assert L.lip_get_tuning(None)[0] == L.LIP_ERR_ARG
+    assert L.lip_set_timing_events(None, None, None) == L.LIP_ERR_ARG
+    assert L.lip_size(None) == -1
+    L.lip_free(None)
+    assert L.lip_kernel_launches() >= 0
+
+
+def test_reserve_argument_errors():
+    p, keep = L.make_params()
+    assert L.lip_reserve(0, 2, 1.0, p)[0] == L.LIP_ERR_ARG
+    assert L.lip_reserve(10, 0, 1.0, p)[0] == L.LIP_ERR_ARG
+    assert L.lip_reserve(10, 2, -2.0, p)[0] == L.LIP_ERR_ARG
+
+
+def test_valid_call_without_device_reports_no_device():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    X, y = _arr(8, 2), _arr(8)
+    p, keep = L.make_params()
+    s, h = L.lip_fit(X.ctypes.data, y.ctypes.data, 8, 2, 1.0, p)
+    assert s in (L.LIP_ERR_NO_DEVICE, L.LIP_ERR_CUDA) and not h.value

@@ -1,0 +1,185 @@
+"""GPU parity of lip_eval against the FP64 oracle (element by element), edge cases, and
+the full-size monotone d=4 workload on sampled queries.  Needs a CUDA device."""
+import numpy as np
+import pytest
+
+from paper_2606_04670_b300 import workloads as W
+from parity import FP32_TOL, FP64_TOL, compare, gpu_eval
+
+pytestmark = pytest.mark.gpu
+
+NORMS = (W.NORM_L1, W.NORM_L2, W.NORM_LINF)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+
+
+def test_plain_d2_fp32_fp64(oracle_mod):
+    p = W.plain_d2()
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm)
+    compare(p, gpu_eval(p, "fp32"), orc, FP32_TOL, "plain_d2 fp32")
+    p64 = W.plain_d2(dtype=np.float64)
+    orc64 = oracle_mod.evaluate(p64.X, p64.y, p64.Q, p64.M, p64.norm)
+    compare(p64, gpu_eval(p64, "fp64"), orc64, FP64_TOL, "plain_d2 fp64")
+
+
+@pytest.mark.parametrize("norm", NORMS)
+def test_monotone_d4_ragged(oracle_mod, norm):
+    # several tiles and splits with a ragged tail (N, nq not multiples of anything)
+    p = W.monotone_d4(norm=norm, n_data=20_011, n_query=3_001)
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, norm, mon=p.mon)
+    compare(p, gpu_eval(p), orc, FP32_TOL, f"monotone_d4 {norm}")
+
+
+@pytest.mark.parametrize("norm", NORMS)
+@pytest.mark.parametrize("shape", [(1, False, False), (3, True, False), (5, True, True), (7, False, True),
+                                   (10, True, True), (12, True, False), (16, True, True), (16, False, False),
+                                   (13, False, True)])
+def test_random_shapes(oracle_mod, norm, shape):
+    d, masked, weighted = shape
+    p = W.random_problem(200 + d, 3_333, d, 777, norm=norm, masked=masked, weighted=weighted,
+                         decreasing=masked)
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, norm, mon=p.mon, w=p.w)
+    compare(p, gpu_eval(p), orc, FP32_TOL, f"random d={d} {norm}")
+
+
+@pytest.mark.parametrize("norm", NORMS)
+def test_random_shapes_fp64(oracle_mod, norm):
+    for d, masked in ((3, True), (9, False), (16, True)):
+        p = W.random_problem(300 + d, 1_500, d, 300, norm=norm, masked=masked, weighted=True,
+                             decreasing=masked, dtype=np.float64)
+        orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, norm, mon=p.mon, w=p.w)
+        compare(p, gpu_eval(p, "fp64"), orc, FP64_TOL, f"fp64 d={d} {norm}")
+
+
+def test_workload_shapes(oracle_mod):
+    for p in (W.toy_d3(), W.grad_d8(n_data=9_000, n_query=1_000), W.cluster_d16(n_data=12_000, n_query=500)):
+        orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm, mon=p.mon, w=p.w)
+        compare(p, gpu_eval(p), orc, FP32_TOL, p.name)
+
+
+@pytest.mark.parametrize("splits,tile_groups", [(1, 8), (3, 16), (7, 32), (64, 64), (0, 8)])
+def test_launch_shape_does_not_change_results(splits, tile_groups):
+    p = W.monotone_d4(norm=W.NORM_L2, n_data=30_000, n_query=2_000)
+    ref = gpu_eval(p)
+    got = gpu_eval(p, splits=splits, tile_groups=tile_groups)
+    for k in ref:
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
+
+
+def test_edge_cases(oracle_mod):
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    p = W.random_problem(400, 1, 3, 50, norm=W.NORM_L2, masked=True)
+    # N = 1
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm, mon=p.mon)
+    compare(p, gpu_eval(p), orc, FP32_TOL, "N=1")
+    # nq = 1, nq = 0, NaN query
+    p = W.random_problem(401, 5_000, 4, 3, norm=W.NORM_L1, masked=True)
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, mon=p.mon)
+    r = m.eval(torch.as_tensor(p.Q[:1]).cuda())
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q[:1], p.M, p.norm, mon=p.mon)
+    assert abs(r["g"].item() - orc.g[0]) <= FP32_TOL * p.M * 4
+    assert m.eval(torch.zeros(0, 4, device="cuda"))["g"].numel() == 0
+    Qn = torch.as_tensor(p.Q).cuda().clone()
+    Qn[1, 2] = float("nan")
+    r = m.eval(Qn)
+    assert torch.isnan(r["g"][1]) and r["idx_up"][1].item() == -1 and r["idx_lo"][1].item() == -1
+    assert torch.isfinite(r["g"][[0, 2]]).all()
+    # M = 0 gives the data range
+    m.set_M(0.0)
+    r = m.eval(torch.as_tensor(p.Q).cuda())
+    assert np.allclose(r["hi"].cpu().numpy(), p.y.min()) and np.allclose(r["lo"].cpu().numpy(), p.y.max())
+    # empty after clear: NaN / -1
+    m.clear()
+    assert m.N == 0
+    r = m.eval(torch.as_tensor(p.Q).cuda())
+    assert torch.isnan(r["g"]).all() and (r["idx_up"] == -1).all()
+    m.check()
+    m.close()
+
+
+def test_incremental_add_equals_fit(oracle_mod):
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    p = W.random_problem(402, 7_001, 5, 600, norm=W.NORM_LINF, masked=True, weighted=True)
+    m = LipFit(M=p.M, norm=p.norm, mon=p.mon, w=p.w, capacity=10_000, d=5)
+    for a, b in ((0, 1000), (1000, 1001), (1001, 7001)):
+        m.add(torch.as_tensor(p.X[a:b]).cuda(), torch.as_tensor(p.y[a:b]).cuda())
+    assert m.N == 7001
+    r = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm, mon=p.mon, w=p.w)
+    compare(p, r, orc, FP32_TOL, "incremental")
+    # beyond the capacity: refused, handle unchanged
+    from paper_2606_04670_b300.lipfit import LipError, LIP_ERR_CAPACITY
+    with pytest.raises(LipError) as e:
+        m.add(torch.as_tensor(p.X[:5000]).cuda(), torch.as_tensor(p.y[:5000]).cuda())
+    assert e.value.status == LIP_ERR_CAPACITY and m.N == 7001
+    # non-finite data refused, handle unchanged
+    from paper_2606_04670_b300.lipfit import LIP_ERR_NONFINITE
+    Xb = torch.as_tensor(p.X[:10]).cuda().clone()
+    Xb[3, 1] = float("inf")
+    with pytest.raises(LipError) as e:
+        m.add(Xb, torch.as_tensor(p.y[:10]).cuda())
+    assert e.value.status == LIP_ERR_NONFINITE and m.N == 7001
+    r2 = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
+    for k in r:
+        np.testing.assert_array_equal(r2[k], r[k])
+    m.close()
+
+
+def test_set_M_equals_refit(oracle_mod):
+    p = W.random_problem(403, 4_000, 6, 500, norm=W.NORM_L2, masked=True)
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), 1.0, norm=p.norm, mon=p.mon)
+    m.set_M(p.M)
+    r = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
+    ref = gpu_eval(p)
+    for k in r:
+        np.testing.assert_array_equal(r[k], ref[k])
+    m.close()
+
+
+def test_eval_host_equals_eval():
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    p = W.monotone_d4(norm=W.NORM_L1, n_data=10_000, n_query=1_200_000)
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, mon=p.mon)
+    dev = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
+    Qp = torch.as_tensor(p.Q).pin_memory()
+    host = m.eval_host(Qp)
+    for k in dev:
+        np.testing.assert_array_equal(host[k], dev[k], err_msg=k)
+    m.close()
+
+
+@pytest.mark.parametrize("norm", NORMS)
+def test_full_size_monotone_d4_sampled(oracle_mod, norm):
+    """The benchmark workload at full size (N = 1e5, Q = 1e6, same launch shape as the
+    benchmark), checked on 1500 sampled queries."""
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    p = W.monotone_d4(norm=norm)
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=norm, mon=p.mon)
+    r = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
+    m.check()
+    m.close()
+    idx = np.random.default_rng(9).choice(p.nq, 1500, replace=False)
+    idx.sort()
+    ps = p.sub_queries(p.nq)
+    ps.Q = p.Q[idx]
+    orc = oracle_mod.evaluate(p.X, p.y, ps.Q, p.M, norm, mon=p.mon)
+    compare(ps, {k: v[idx] for k, v in r.items()}, orc, FP32_TOL, f"full monotone_d4 {norm}")
+    # properties that hold at any size, on every query: lo <= g <= hi (M is a valid bound)
+    assert np.all(r["lo"] <= r["g"]) and np.all(r["g"] <= r["hi"])
+    assert r["idx_up"].min() >= 0 and r["idx_up"].max() < p.N

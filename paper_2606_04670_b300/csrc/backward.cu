@@ -13,42 +13,23 @@ namespace lip {
 
 constexpr int BWD_THREADS = 256;
 
-// dist (side > 0: upper, < 0: lower) and its gradient with respect to q.
+// Magnitude v and dv/dt' of one coordinate of the upper (side > 0) or lower (side < 0)
+// distance vector, t' = sign_i w_i (q_i - x_i).
 template <typename T>
-__device__ __forceinline__ T dist_and_grad(const BwdParams& P, const T* q, const T* x, int side, T (&g)[D_MAX]) {
-    T v[D_MAX], s[D_MAX];
-    T acc = 0;
-    int imax = -1;
-    for (int i = 0; i < P.d; ++i) {
-        T t = q[i] - x[i];
-        const T sq = (P.mon[i] < 0 ? (T)-1 : (T)1) * (T)P.w[i];   // dt'/dq_i
-        t = t * sq;
-        T vi, dv;
-        if (P.mon[i] != 0) {
-            if (side > 0) { vi = t > 0 ? t : (T)0; dv = t > 0 ? (T)1 : (T)0; }
-            else { vi = t < 0 ? -t : (T)0; dv = t < 0 ? (T)-1 : (T)0; }
-        } else {
-            vi = t < 0 ? -t : t;
-            dv = t > 0 ? (T)1 : (t < 0 ? (T)-1 : (T)0);
-        }
-        v[i] = vi;
-        s[i] = dv * sq;
-        if (P.norm == LIP_L1) acc += vi;
-        else if (P.norm == LIP_L2) acc += vi * vi;
-        else if (vi > acc) { acc = vi; imax = i; }
+__device__ __forceinline__ void coord_part(T t, bool constrained, int side, T& v, T& dv) {
+    if (constrained) {
+        if (side > 0) { v = t > 0 ? t : (T)0; dv = t > 0 ? (T)1 : (T)0; }
+        else { v = t < 0 ? -t : (T)0; dv = t < 0 ? (T)-1 : (T)0; }
+    } else {
+        v = t < 0 ? -t : t;
+        dv = t > 0 ? (T)1 : (t < 0 ? (T)-1 : (T)0);
     }
-    for (int i = 0; i < P.d; ++i) g[i] = 0;
-    if (P.norm == LIP_L1) {
-        for (int i = 0; i < P.d; ++i) g[i] = s[i];
-        return acc;
-    }
-    if (P.norm == LIP_L2) {
-        const T nrm = sqrt(acc);
-        if (nrm > 0) for (int i = 0; i < P.d; ++i) g[i] = s[i] * v[i] / nrm;
-        return nrm;
-    }
-    if (acc > 0 && imax >= 0) g[imax] = s[imax];
-    return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T coord_t(const BwdParams& P, const T* q, const T* x, int i, T& sq) {
+    sq = (P.mon[i] < 0 ? (T)-1 : (T)1) * (T)P.w[i];   // dt'/dq_i
+    return (q[i] - x[i]) * sq;
 }
 
 template <typename T>
@@ -64,11 +45,47 @@ __global__ void __launch_bounds__(BWD_THREADS) backward_kernel(const BwdParams P
             if (gq) for (int i = 0; i < P.d; ++i) gq[i] = 0;
         } else {
             const T* X0 = static_cast<const T*>(P.X0);
-            T gu[D_MAX], gl[D_MAX];
-            const T du = dist_and_grad<T>(P, q, X0 + (int64_t)u * P.d, +1, gu);
-            const T dl = dist_and_grad<T>(P, q, X0 + (int64_t)l * P.d, -1, gl);
-            const T hm = (T)(0.5 * P.M) * gb;
-            if (gq) for (int i = 0; i < P.d; ++i) gq[i] = hm * (gu[i] - gl[i]);
+            const T* xu = X0 + (int64_t)u * P.d;
+            const T* xl = X0 + (int64_t)l * P.d;
+            // pass 1: the two distances (and the Linf arg-max coordinates, lowest on ties)
+            T au = 0, al = 0;
+            int mu = -1, ml = -1;
+            for (int i = 0; i < P.d; ++i) {
+                T sq, vu, vl, dv;
+                const bool c = P.mon[i] != 0;
+                coord_part<T>(coord_t<T>(P, q, xu, i, sq), c, +1, vu, dv);
+                coord_part<T>(coord_t<T>(P, q, xl, i, sq), c, -1, vl, dv);
+                if (P.norm == LIP_L1) { au += vu; al += vl; }
+                else if (P.norm == LIP_L2) { au += vu * vu; al += vl * vl; }
+                else {
+                    if (vu > au) { au = vu; mu = i; }
+                    if (vl > al) { al = vl; ml = i; }
+                }
+            }
+            const T du = P.norm == LIP_L2 ? sqrt(au) : au;
+            const T dl = P.norm == LIP_L2 ? sqrt(al) : al;
+            // pass 2: d dist / d q_i for both sides, then dL/dq_i
+            if (gq) {
+                const T hm = (T)(0.5 * P.M) * gb;
+                for (int i = 0; i < P.d; ++i) {
+                    T sq, vu, vl, dvu, dvl;
+                    const bool c = P.mon[i] != 0;
+                    coord_part<T>(coord_t<T>(P, q, xu, i, sq), c, +1, vu, dvu);
+                    coord_part<T>(coord_t<T>(P, q, xl, i, sq), c, -1, vl, dvl);
+                    T gu = 0, gl = 0;
+                    if (P.norm == LIP_L1) {
+                        gu = dvu * sq;
+                        gl = dvl * sq;
+                    } else if (P.norm == LIP_L2) {
+                        if (du > 0) gu = dvu * sq * vu / du;
+                        if (dl > 0) gl = dvl * sq * vl / dl;
+                    } else {
+                        if (i == mu && du > 0) gu = dvu * sq;
+                        if (i == ml && dl > 0) gl = dvl * sq;
+                    }
+                    gq[i] = hm * (gu - gl);
+                }
+            }
             if (P.gy64) {
                 atomicAdd(P.gy64 + u, 0.5 * (double)gb);
                 atomicAdd(P.gy64 + l, 0.5 * (double)gb);

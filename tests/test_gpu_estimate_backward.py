@@ -46,11 +46,14 @@ def test_estimate_M_duplicates():
     X = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 0.0], [0.5, 0.5]], np.float32)
     p = W.random_problem(510, 4, 2, 1)
     p.X = X
-    p.y = np.array([0.0, 1.0, 0.0, 0.2], np.float32)
+    # pairs (0,1) and (1,2) have ratio 1, (0,3), (1,3), (2,3) ratio 0.5/sqrt(0.5) = 0.707,
+    # (0,2) is a duplicate with equal y and is skipped
+    p.y = np.array([0.0, 1.0, 0.0, 0.5], np.float32)
     m = _model(p)
-    assert m.lipschitz_constant()[0] == pytest.approx(1.0)
+    M, i, j = m.lipschitz_constant()
+    assert M == pytest.approx(1.0) and (i, j) == (0, 1)
     m.close()
-    p.y = np.array([0.0, 1.0, 0.5, 0.2], np.float32)
+    p.y = np.array([0.0, 1.0, 0.5, 0.5], np.float32)
     m = _model(p)
     M, i, j = m.lipschitz_constant()
     assert M == np.inf and (i, j) == (0, 2)

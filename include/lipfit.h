@@ -165,6 +165,32 @@ LIP_API lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* 
 LIP_API lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, int64_t* j_out,
                           void* stream);
 
+/* Largest N accepted by lip_estimate_M_noalloc. */
+#define LIP_NOALLOC_N_MAX 32768
+
+/* lip_estimate_M for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this is a convenience of this library.  It is meant for code that must
+ * not call cudaMalloc: a plugin whose host application has already reserved the GPU's
+ * memory in its own allocator, or a latency-bound loop that cannot absorb the
+ * device-wide synchronisation cudaFree implies.  It needs no handle, allocates nothing,
+ * and keeps its working memory in one fixed array of about 2.2 MB inside the library,
+ * which every GPU that loads liblipfit.so holds until the process exits.
+ *   X [N][d], y [N]  device, float, finite (not checked); read only.
+ *   N                1 <= N <= LIP_NOALLOC_N_MAX, else LIP_ERR_ARG (fixed capacity).
+ *   d, norm, w       as for lip_fit (w: host array of d weights > 0, or NULL).
+ *   out              device double[3], written with {M_est, i, j} (i < j as doubles,
+ *                    -1 and M_est = 0 when no pair qualifies), same definition and
+ *                    same kernels as lip_estimate_M.
+ * The call is asynchronous on `stream` (it does not synchronise).  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  Every call on a device shares the one array,
+ * which keeps the last call's contents (each call writes everything it later reads, so
+ * nothing needs clearing): calls whose GPU work overlaps -- on different streams, or
+ * from several host threads -- race and give wrong results, so order them on one
+ * stream. */
+LIP_API lip_status lip_estimate_M_noalloc(const float* X, const float* y, int64_t N, int32_t d,
+                                          int32_t norm, const double* w, double* out, void* stream);
+
 /* ---------------------------------------------------------------- differentiation */
 
 /* Gradient of L = sum_q grad_g[q] * g(q) through the saved argmin/argmax (g is piecewise

@@ -93,6 +93,11 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 }  // namespace
 
+namespace lip {
+// Records an error for lip_last_error from other translation units of the library.
+lip_status set_error(lip_status s, const char* msg) { return fail(s, "%s", msg); }
+}  // namespace lip
+
 struct lip_model {
     int device = 0;
     int sms = 148;

@@ -1,0 +1,138 @@
+// lip_estimate_M_noalloc: the Lipschitz-constant estimate without any allocation.
+//
+// The ordinary entry points keep their working memory in the handle and grow it with
+// cudaMalloc.  Some callers cannot do that: a plugin running inside a host application
+// whose own allocator has already reserved the GPU's memory (a cudaMalloc from us would
+// fail or fragment that pool), or a latency-bound loop that cannot absorb the device-wide
+// synchronisation that cudaFree implies.  This entry point takes the data straight from
+// the caller's device buffers, writes its result into a caller buffer, and keeps its
+// working memory in the fixed array below, which every GPU that loads the library holds
+// until the process exits.
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "launch.h"
+
+namespace lip {
+lip_status set_error(lip_status s, const char* msg);
+}
+
+using namespace lip;
+
+namespace {
+
+constexpr int64_t NA_TILE = 512;   // the estimate kernel's tile (checked against the kernel at run time)
+constexpr int64_t NA_POINTS = ((int64_t)LIP_NOALLOC_N_MAX + NA_TILE - 1) / NA_TILE * NA_TILE;
+constexpr int64_t NA_LAYOUT_BYTES = (NA_POINTS * (D_MAX + 1) * 4 + 255) / 256 * 256;
+constexpr int64_t NA_TILES = NA_POINTS / NA_TILE;
+constexpr int64_t NA_CAND_BYTES = (NA_TILES * NA_TILES * 16 + 255) / 256 * 256;
+constexpr int64_t NA_BYTES = NA_LAYOUT_BYTES + NA_CAND_BYTES;   // about 2.2 MB
+
+// Working memory of every lip_estimate_M_noalloc call on this device: the FP32 point
+// layout followed by one candidate record per tile pair.  Host code must not pass this
+// name to a kernel (on the host it only stands for the symbol); it uses the address
+// obtained from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_mu;
+void* g_addr[MAX_DEVICES] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device.
+lip_status scratch_address(int dev, void** out) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (dev < 0 || dev >= MAX_DEVICES) return set_error(LIP_ERR_UNSUPPORTED, "device ordinal beyond 63");
+    if (!g_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            char buf[256];
+            snprintf(buf, sizeof buf, "cudaGetSymbolAddress(g_noalloc_scratch): %s", cudaGetErrorString(e));
+            return set_error(LIP_ERR_CUDA, buf);
+        }
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
+    return LIP_OK;
+}
+
+lip_status launch_fail(cudaError_t e, const char* what) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    return set_error(e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ? LIP_ERR_NO_DEVICE : LIP_ERR_CUDA,
+                     buf);
+}
+
+}  // namespace
+
+extern "C" lip_status lip_estimate_M_noalloc(const float* X, const float* y, int64_t N, int32_t d, int32_t norm,
+                                             const double* w, double* out, void* stream) {
+    if (!X || !y || !out) return set_error(LIP_ERR_ARG, "X, y or out is NULL");
+    if (N < 1 || N > LIP_NOALLOC_N_MAX) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "N = %lld is outside [1, %d], the fixed capacity of lip_estimate_M_noalloc",
+                 (long long)N, LIP_NOALLOC_N_MAX);
+        return set_error(LIP_ERR_ARG, buf);
+    }
+    if (d < 1 || d > D_MAX) return set_error(LIP_ERR_ARG, "d is outside [1, LIP_D_MAX]");
+    if (norm < LIP_L1 || norm > LIP_LINF) return set_error(LIP_ERR_ARG, "norm is not L1/L2/Linf");
+    if (w)
+        for (int i = 0; i < d; ++i)
+            if (!(w[i] > 0.0) || !std::isfinite(w[i])) return set_error(LIP_ERR_ARG, "w entries must be finite and > 0");
+    if (estimate_tile_points() != NA_TILE) return set_error(LIP_ERR_UNSUPPORTED, "estimate tile size changed");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return launch_fail(e, "cudaGetDevice");
+    void* base = nullptr;
+    lip_status s = scratch_address(dev, &base);
+    if (s != LIP_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    const int64_t nb = (N + NA_TILE - 1) / NA_TILE;
+    const int64_t pts = nb * NA_TILE;
+    const int nch = d + 1;
+    char* lay = static_cast<char*>(base);
+    float4* cand = reinterpret_cast<float4*>(static_cast<char*>(base) + NA_LAYOUT_BYTES);
+
+    // Every byte read below is written first by this call: the layout covers [0, pts)
+    // (data, then padding) and the candidate pass writes every tile pair it later reads.
+    HotParams Hp{};
+    Hp.X0 = X;
+    Hp.y0 = y;
+    Hp.k0 = 0;
+    Hp.k1 = N;
+    Hp.d = d;
+    Hp.C = 0;
+    Hp.dl = d;
+    Hp.nch = nch;
+    Hp.aux = 0;
+    for (int j = 0; j < D_MAX; ++j) {
+        Hp.perm[j] = j;
+        Hp.scale[j] = (w && j < d) ? w[j] : 1.0;
+    }
+    Hp.hot = lay;
+    Hp.err = nullptr;
+    EstFinalParams F{};
+    F.cand = cand;
+    F.nb = N < 2 ? 0 : (int)nb;
+    F.X0 = X;
+    F.y0 = y;
+    F.d = d;
+    F.norm = norm;
+    F.elem_bytes = 4;
+    for (int j = 0; j < D_MAX; ++j) F.w[j] = (w && j < d) ? w[j] : 1.0;
+    F.out = out;
+    if (N >= 2) {
+        if ((e = launch_estimate_layout(4, Hp, st)) != cudaSuccess) return launch_fail(e, "estimate layout");
+        if ((e = launch_pad_hot(4, lay, N, pts, nch, d, st)) != cudaSuccess) return launch_fail(e, "estimate padding");
+        EstParams P{};
+        P.lay = reinterpret_cast<const float4*>(lay);
+        P.N = N;
+        P.nb = (int)nb;
+        P.cand = cand;
+        if ((e = launch_estimate(norm, d, P, st)) != cudaSuccess) return launch_fail(e, "estimate kernel");
+    }
+    if ((e = launch_estimate_final(F, st)) != cudaSuccess) return launch_fail(e, "estimate final");
+    return LIP_OK;
+}

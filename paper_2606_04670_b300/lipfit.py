@@ -27,6 +27,7 @@ LIP_OK, LIP_ERR_ARG, LIP_ERR_NONFINITE, LIP_ERR_OOM, LIP_ERR_CUDA = 0, 1, 2, 3, 
 LIP_ERR_CAPACITY, LIP_ERR_TIMEOUT, LIP_ERR_UNSUPPORTED, LIP_ERR_NO_DEVICE = 5, 6, 7, 8
 LIP_L1, LIP_L2, LIP_LINF = 1, 2, 3
 LIP_FP32, LIP_FP64, LIP_TC_BF16, LIP_TC_TF32 = 0, 1, 2, 3
+LIP_NOALLOC_N_MAX = 32768
 NORMS = {"L1": LIP_L1, "L2": LIP_L2, "Linf": LIP_LINF, "LINF": LIP_LINF,
          LIP_L1: LIP_L1, LIP_L2: LIP_L2, LIP_LINF: LIP_LINF}
 PRECISIONS = {"fp32": LIP_FP32, "fp64": LIP_FP64, "tc_bf16": LIP_TC_BF16, "tc_tf32": LIP_TC_TF32,
@@ -67,6 +68,7 @@ def _load():
         "lip_set_tuning": [H, i32, i32],
         "lip_get_tuning": [H, P, P, P, P],
         "lip_set_timing_events": [H, P, P],
+        "lip_estimate_M_noalloc": [P, P, i64, i32, i32, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -173,6 +175,11 @@ def lip_estimate_M(h, stream=0):
     M, i, j = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
     s = _lib.lip_estimate_M(h, ctypes.byref(M), ctypes.byref(i), ctypes.byref(j), stream)
     return s, M.value, i.value, j.value
+
+
+def lip_estimate_M_noalloc(X_ptr, y_ptr, N, d, norm, w_ptr, out_ptr, stream=0):
+    """Handle-free estimate into device double[3] {M, i, j}; allocates nothing."""
+    return _lib.lip_estimate_M_noalloc(X_ptr, y_ptr, N, d, norm, w_ptr, out_ptr, stream)
 
 
 def lip_backward(h, Q_ptr, nq, idx_up, idx_lo, grad_g, grad_Q, grad_y, grad_M, stream=0):

@@ -45,6 +45,10 @@ NNAME = {1: "L1", 2: "L2", 3: "Linf"}
 I_PAIR = {1: 18, 2: 20, 3: 16}
 MUFU_PER_PAIR = {1: 0, 2: 2, 3: 0}
 FP32_LANES_PER_SM = 128
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant scan kernel, from
+# the ncu capture summarised in profiles/scan_exact_l2_monotone_d4.md (set to None whenever
+# that kernel changes until it is captured again).
+SCAN_DRAM_BYTES = {2: 18.106624e6 + 2.477824e6}
 CONFIG = {"workload": "monotone_d4", "d": 4, "N": 100_000, "Q": 1_000_000, "mon": [1, 1, 0, 0],
           "norms": ["L1", "L2", "Linf"], "step": "per norm: fit + eval + M_est",
           "l2": "flushed before every timed step (256 MB write)"}
@@ -169,6 +173,24 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ multi-rank aggregation
+
+def aggregate(pairs_local: float, ms_local: float, device=None):
+    """Whole-job throughput: all ranks' pairs over the slowest rank's time (G pairs/s).
+
+    Single process: pairs / time.  Under torch.distributed the pairs are summed and the
+    time is the maximum over ranks (one all_reduce each, on `device`)."""
+    import torch
+    import torch.distributed as tdist
+    if tdist.is_available() and tdist.is_initialized() and tdist.get_world_size() > 1:
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        p = torch.tensor([pairs_local], dtype=torch.float64, device=device)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        tdist.all_reduce(p, op=tdist.ReduceOp.SUM)
+        ms_local, pairs_local = float(t.item()), float(p.item())
+    return pairs_local / (ms_local / 1e3) / 1e9, ms_local
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_ours(args):
@@ -231,13 +253,8 @@ def run_ours(args):
     wall = time.perf_counter() - t_wall0
     launches = L.lip_kernel_launches() - launches0
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     pairs_step = len(NORMS) * nq * N
-    value = pairs_step * args.steps * world / (total_ms / 1e3) / 1e9
+    value, total_ms = aggregate(pairs_step * args.steps, sum(step_ms), device="cuda")
 
     # roofline of the dominant kernel (the scan with the largest time)
     props = torch.cuda.get_device_properties(local)
@@ -254,7 +271,8 @@ def run_ours(args):
     achieved = I_PAIR[dom] * nq * N / (avg_scan[dom] / 1e3)
     roof = {"bound": "alu", "kernel": f"scan_exact_kernel<{NNAME[dom]}, C=2, U=2>",
             "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 lane ops)",
-            "frac": achieved / peak_ops, "traffic": None,
+            "frac": achieved / peak_ops, "traffic": SCAN_DRAM_BYTES.get(dom),
+            "traffic_unit": "bytes per launch (ncu dram read + write)",
             "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (max SM clock"
                            f"{' of MEASURED_PEAKS.json' if peaks else ', nominal'})",
             "i_pair": I_PAIR[dom], "mufu_per_pair": MUFU_PER_PAIR[dom]}
@@ -288,14 +306,10 @@ def run_ours(args):
             step_host()
             torch.cuda.synchronize()
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        tot = sum(e2e_ms)
-        if world > 1:
-            t = torch.tensor([tot], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            tot = float(t.item())
+        e2e_value, tot = aggregate(pairs_step * args.steps, sum(e2e_ms), device="cuda")
         h2d = len(NORMS) * (N * d * 4 + N * 4 + nq * d * 4)
         d2h = len(NORMS) * (nq * (3 * 4 + 2 * 4) + 24)
-        e2e = {"value": pairs_step * args.steps * world / (tot / 1e3) / 1e9, "unit": UNIT,
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": tot / args.steps}
 
     cpu = None

@@ -1,19 +1,23 @@
 #!/usr/bin/env python
 """Throughput of the fused all-pairs Lipschitz envelope evaluation on a B300.
 
-One step = the whole hot path over one batch of the monotone d=4 workload
-(N = 100,000 data points, Q = 1,000,000 queries, increasing in x1 and x2), once per
-norm (L1, L2, Linf):
+Default workload (monotone_d4): N = 100,000 data points, Q = 1,000,000 queries in [0,1]^4,
+increasing in x1 and x2.  One step = the whole hot path over that batch, once per norm
+(L1, L2, Linf):
   fit   (lip_clear + lip_add: copy and scan-layout transform, Sec. 5 add())
   eval  (lip_eval: scan kernel + split merge with FP64 re-evaluation, Eq. (upperlower), (eq:g))
   M_est (lip_estimate_M: all-pairs Lipschitz constant, Sec. 5)
 Metric: query x datapoint pairs evaluated per second (G pairs/s) = 3 Q N / step time.
 
-Timing: CUDA events per step on the launching stream; L2 (126 MB) is flushed before
-every timed step by writing a 256 MB buffer (the inputs, 17.6 MB, are smaller than L2).
-N > 1 (torchrun): every rank runs the same per-rank workload on its own GPU (weak
-scaling; the method needs no exchange between ranks), value = all ranks' pairs / the
-slowest rank's time.
+Other workloads (--workload): plain_d2 (d=2, FP32 and FP64), cluster_d16 (d=16 Gaussian
+mixture, N = Q = 1e6, plain FP32 L2), grad_d8 (d=8, forward + backward), batch_4096
+(4096 independent sets in one persistent launch replayed from a CUDA graph).
+
+Timing: CUDA events per step on the launching stream.  Where the inputs fit in L2
+(126 MB), L2 is flushed before every timed step by writing a 256 MB buffer (outside the
+timed interval).  N > 1 (torchrun): every rank runs the same per-rank workload on its
+own GPU (weak scaling; the method needs no exchange between ranks), value = all ranks'
+pairs / the slowest rank's time.
 
 --impl reference times the FP64 CPU oracle (the checker, as it stands) on the host
 cores on a bounded sample of the same workload.
@@ -39,19 +43,26 @@ METRIC = "G pairs/s (query x datapoint) fused eval"
 UNIT = "G pairs/s"
 NORMS = (W.NORM_L1, W.NORM_L2, W.NORM_LINF)
 NNAME = {1: "L1", 2: "L2", 3: "Linf"}
-# Algorithmic FP32 lane operations per pair for d = 4 with c = 2 constrained coordinates
-# (minimal instruction counts, |.| and negation as free operand modifiers, plus 4 for the
-# two bounds and the two extrema): L1 2(d-c)+4c+2+4, L2 2(d-c)+5c+2+4, Linf 2(d-c)+3c+2+4.
-I_PAIR = {1: 18, 2: 20, 3: 16}
-MUFU_PER_PAIR = {1: 0, 2: 2, 3: 0}
 FP32_LANES_PER_SM = 128
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant scan kernel, from
-# the ncu capture summarised in profiles/scan_exact_l2_monotone_d4.md (set to None whenever
-# that kernel changes until it is captured again).
-SCAN_DRAM_BYTES = {2: 18.106624e6 + 2.477824e6}
-CONFIG = {"workload": "monotone_d4", "d": 4, "N": 100_000, "Q": 1_000_000, "mon": [1, 1, 0, 0],
-          "norms": ["L1", "L2", "Linf"], "step": "per norm: fit + eval + M_est",
-          "l2": "flushed before every timed step (256 MB write)"}
+WORKLOADS = ("monotone_d4", "plain_d2", "cluster_d16", "grad_d8", "batch_4096")
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant scan kernel of
+# the default workload, from the ncu capture summarised in
+# profiles/scan_exact_l2_monotone_d4.md (None whenever that kernel changes until it is
+# captured again).
+SCAN_DRAM_BYTES = {("monotone_d4", 2): 18.106624e6 + 2.477824e6}
+
+
+def i_pair(norm: int, d: int, c: int) -> int:
+    """Algorithmic FP32 lane operations per pair: minimal scalar instruction counts with
+    |.| and negation as free operand modifiers, plus 4 for the two bounds and extrema:
+    2(d-c) for the free coordinates, k c + 2 for the c constrained ones (k = 4 L1,
+    5 L2, 3 Linf)."""
+    k = {W.NORM_L1: 4, W.NORM_L2: 5, W.NORM_LINF: 3}[norm]
+    return 2 * (d - c) + (k * c + 2 if c else 0) + 4
+
+
+def mufu_per_pair(norm: int, c: int) -> int:
+    return 0 if norm != W.NORM_L2 else (2 if c else 1)
 
 
 def parse():
@@ -60,6 +71,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=WORKLOADS, default="monotone_d4")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -122,57 +134,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ------------------------------------------------------------------ CPU oracle timing
-
-def oracle_rate(p, norms, seconds: float, rng_seed=5):
-    """Pairs/s of the FP64 oracle on a sample of queries sized to take about `seconds`."""
-    import oracle
-    o = oracle.default()
-    rng = np.random.default_rng(rng_seed)
-    probe = p.Q[rng.choice(p.nq, 64, replace=False)]
-    t0 = time.perf_counter()
-    o.evaluate(p.X, p.y, probe, p.M_by_norm[W.NORM_L2], W.NORM_L2, mon=p.mon)
-    dt = max(time.perf_counter() - t0, 1e-3)
-    per_query = dt / 64
-    nq = int(max(64, min(p.nq, seconds / len(norms) / per_query)))
-    Qs = p.Q[rng.choice(p.nq, nq, replace=False)]
-    t0 = time.perf_counter()
-    for n in norms:
-        o.evaluate(p.X, p.y, Qs, p.M_by_norm[n], n, mon=p.mon)
-    dt = time.perf_counter() - t0
-    pairs = nq * p.N * len(norms)
-    return {"value": pairs / dt / 1e9, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
-            "sample": f"{nq} random queries x all {p.N} data points x {len(norms)} norms (FP64, "
-                      f"{oracle.default_threads()} threads, {dt:.1f} s)"}, dt
-
-
-def run_reference(args):
-    rank, world, _ = dist_env()
-    if rank != 0:
-        return 0
-    import oracle
-    oracle.build()
-    p = W.monotone_d4(norm=W.NORM_L2)
-    per_step = max(2.0, min(8.0, 60.0 / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        oracle_rate(p, NORMS, per_step / 4)
-    rates, times = [], []
-    base = None
-    for _ in range(args.steps):
-        base, dt = oracle_rate(p, NORMS, per_step)
-        rates.append(base["value"])
-        times.append(dt)
-    value = statistics.mean(rates)
-    base = dict(base, value=value)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded, monotone d=4 workload)", "config": CONFIG, "cpu_baseline": base,
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
 # ------------------------------------------------------------------ multi-rank aggregation
 
 def aggregate(pairs_local: float, ms_local: float, device=None):
@@ -191,7 +152,352 @@ def aggregate(pairs_local: float, ms_local: float, device=None):
     return pairs_local / (ms_local / 1e3) / 1e9, ms_local
 
 
-# ------------------------------------------------------------------ GPU arm
+# ------------------------------------------------------------------ CPU oracle timing
+
+def oracle_rate(problems, seconds: float, rng_seed=5):
+    """Pairs/s of the FP64 oracle over random queries of the given problems (one oracle
+    call per problem), sized from a 64-query probe to take about `seconds`."""
+    import oracle
+    o = oracle.default()
+    rng = np.random.default_rng(rng_seed)
+    p0 = problems[0]
+    probe = p0.Q[rng.choice(p0.nq, min(64, p0.nq), replace=False)]
+    t0 = time.perf_counter()
+    o.evaluate(p0.X, p0.y, probe, p0.M, p0.norm, mon=p0.mon, w=p0.w)
+    per_pair = max(time.perf_counter() - t0, 1e-4) / (len(probe) * p0.N)
+    budget_pairs = seconds / per_pair
+    pairs, dt = 0, 0.0
+    for p in problems:
+        nq = int(max(16, min(p.nq, budget_pairs / len(problems) / p.N)))
+        Qs = p.Q[rng.choice(p.nq, nq, replace=False)]
+        t0 = time.perf_counter()
+        o.evaluate(p.X, p.y, Qs, p.M, p.norm, mon=p.mon, w=p.w)
+        dt += time.perf_counter() - t0
+        pairs += nq * p.N
+    return {"value": pairs / dt / 1e9, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
+            "sample": f"{pairs:.3g} pairs: random queries x all data points of {len(problems)} problem(s) "
+                      f"(FP64, {oracle.default_threads()} threads, {dt:.1f} s)"}, dt
+
+
+def reference_problems(workload):
+    if workload == "monotone_d4":
+        base = W.monotone_d4(norm=W.NORM_L2)
+        return [base.with_norm(n) for n in NORMS]
+    if workload == "plain_d2":
+        return [W.plain_d2(dtype=np.float64)]
+    if workload == "cluster_d16":
+        return [W.cluster_d16(n_query=20_000)]
+    if workload == "grad_d8":
+        return [W.grad_d8()]
+    plan = W.batch_plan()
+    rng = np.random.default_rng(3)
+    out = []
+    for k in rng.choice(len(plan), 48, replace=False):
+        bs = plan[k]
+        X, y, Q, f = W.batch_set_data(bs)
+        out.append(W.Problem("batch", X, y, Q, bs.M, bs.norm, bs.mon, None, f))
+    return out
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    problems = reference_problems(args.workload)
+    per_step = max(2.0, min(8.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_rate(problems, per_step / 4)
+    rates, times, base = [], [], None
+    for _ in range(args.steps):
+        base, dt = oracle_rate(problems, per_step)
+        rates.append(base["value"])
+        times.append(dt)
+    value = statistics.mean(rates)
+    base = dict(base, value=value)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": f"synthetic (seeded, {args.workload} workload)", "config": {"workload": args.workload},
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm helpers
+
+class Ctx:
+    def __init__(self, args):
+        import torch
+        self.args = args
+        self.rank, self.world, self.local = dist_env()
+        self.torch = torch
+        props = torch.cuda.get_device_properties(self.local)
+        self.sms = props.multi_processor_count
+        try:
+            self.peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            self.peaks = {}
+        self.sm_max = float(self.peaks.get("sm_max_mhz", 2032.0))
+        self.flush_buf = torch.empty(64 << 20, dtype=torch.float32, device="cuda")    # 256 MB > L2
+
+    def flush(self):
+        self.flush_buf.fill_(1.0)
+
+    def timed(self, step, steps, flush=True):
+        """Per-step CUDA-event times of `steps` calls of step(), with clocks sampled during
+        the timed region and the library's kernel launches counted."""
+        from paper_2606_04670_b300 import lipfit as L
+        torch = self.torch
+        torch.cuda.synchronize()
+        if self.world > 1:
+            torch.distributed.barrier()
+        sampler = ClockSampler(self.local)
+        sampler.start()
+        launches0 = L.lip_kernel_launches()
+        ms = []
+        for _ in range(steps):
+            if flush:
+                self.flush()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            step()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        torch.cuda.synchronize()
+        if self.world > 1:
+            torch.distributed.barrier()
+        return ms, sampler.stop(), L.lip_kernel_launches() - launches0
+
+    def roofline(self, kernel, ops_per_launch, ms_per_launch, ipair, mufu, clocks, traffic=None):
+        peak = self.sms * FP32_LANES_PER_SM * self.sm_max * 1e6
+        achieved = ops_per_launch / (ms_per_launch / 1e3)
+        r = {"bound": "alu", "kernel": kernel, "achieved": achieved / 1e12, "peak": peak / 1e12,
+             "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak, "traffic": traffic,
+             "traffic_unit": "bytes per launch (ncu dram read + write)",
+             "peak_source": f"{self.sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {self.sm_max:.0f} MHz (max SM clock"
+                            f"{' of MEASURED_PEAKS.json' if self.peaks else ', nominal'})",
+             "i_pair": ipair, "mufu_per_pair": mufu}
+        if clocks and clocks.get("sm_mhz"):
+            r["frac_at_measured_clock"] = achieved / (self.sms * FP32_LANES_PER_SM * clocks["sm_mhz"] * 1e6)
+        return r
+
+    def line(self, value, ms_total, steps, dtype, config, roof, cpu, e2e, clocks, launches, detail):
+        return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": self.world, "steps": steps,
+                "warmup": max(3, self.args.warmup), "ms_per_step": ms_total / steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+                "data": f"synthetic (seeded, {config['workload']} workload)",
+                "config": dict(config, parallelism=f"replicas{self.world}"), "roofline": roof,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches, "detail": detail}
+
+
+def _cpu(ctx, problems):
+    if ctx.rank != 0 or ctx.args.no_cpu_baseline:
+        return None
+    return oracle_rate(problems, ctx.args.cpu_seconds)[0]
+
+
+# ------------------------------------------------------------------ workloads
+
+def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd=False, flush=True):
+    """fit + eval (+ M_est) (+ backward) of each problem per step."""
+    from paper_2606_04670_b300 import lipfit as L
+    torch, args = ctx.torch, ctx.args
+    runs = []
+    for p in problems:
+        for prec in precisions:
+            dt = torch.float64 if prec == "fp64" else torch.float32
+            X = torch.as_tensor(p.X).to("cuda", dt)
+            y = torch.as_tensor(p.y).to("cuda", dt)
+            Q = torch.as_tensor(p.Q).to("cuda", dt)
+            m = L.LipFit(M=p.M, norm=p.norm, mon=p.mon, w=p.w, capacity=p.N, d=p.d, precision=prec)
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            m.set_timing_events(*ev)
+            runs.append(dict(p=p, prec=prec, X=X, y=y, Q=Q, m=m, ev=ev, scan=[],
+                             gb=torch.ones(p.nq, device="cuda", dtype=dt)))
+    est = {}
+
+    def step(record=False):
+        for k, r in enumerate(runs):
+            m = r["m"]
+            m.clear()
+            m.add(r["X"], r["y"])
+            out = m.eval(r["Q"], need=("g", "lo", "hi", "idx_up", "idx_lo"))
+            if record:
+                torch.cuda.synchronize()
+                r["scan"].append(r["ev"][0].elapsed_time(r["ev"][1]))
+            if with_bwd:
+                m.backward(r["Q"], out["idx_up"], out["idx_lo"], r["gb"])
+            if with_est:
+                est[k] = m.lipschitz_constant()[0]
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    ms, clocks, launches = ctx.timed(lambda: step(True), args.steps, flush=flush)
+    pairs_step = sum(r["p"].nq * r["p"].N for r in runs)
+    value, total = aggregate(pairs_step * args.steps, sum(ms), device="cuda")
+    # dominant kernel: the scan with the largest average time
+    avg = [statistics.mean(r["scan"]) for r in runs]
+    kdom = int(np.argmax(avg))
+    rd = runs[kdom]
+    p = rd["p"]
+    c = 0 if p.mon is None else int((np.asarray(p.mon) != 0).sum())
+    ip = i_pair(p.norm, p.d, c)
+    exact = rd["prec"] == "fp32" and (p.d <= 10 or c == 0)
+    kern = (f"scan_{'exact' if exact else 'generic'}_kernel<{NNAME[p.norm]}, C={c}, U={p.d - c}, "
+            f"R={rd['m'].tuning()['queries_per_thread']}> {rd['prec']}")
+    roof = ctx.roofline(kern, ip * p.nq * p.N, avg[kdom], ip, mufu_per_pair(p.norm, c), clocks,
+                        SCAN_DRAM_BYTES.get((name, p.norm)) if rd["prec"] == "fp32" else None)
+
+    e2e = None
+    if not args.no_e2e:
+        hostruns = []
+        for r in runs:
+            ndt = np.float64 if r["prec"] == "fp64" else np.float32
+            hX, hy, hQ = (torch.as_tensor(np.ascontiguousarray(a, dtype=ndt)).pin_memory()
+                          for a in (r["p"].X, r["p"].y, r["p"].Q))
+            hdt = torch.float64 if r["prec"] == "fp64" else torch.float32
+            outs = {k: torch.empty(r["p"].nq, dtype=hdt).pin_memory() for k in ("g", "lo", "hi")}
+            outs.update({k: torch.empty(r["p"].nq, dtype=torch.int32).pin_memory() for k in ("idx_up", "idx_lo")})
+            hostruns.append((r, hX, hy, hQ, outs))
+            r["m"].set_timing_events(None, None)
+
+        def step_host():
+            for r, hX, hy, hQ, outs in hostruns:
+                m = r["m"]
+                m.clear()
+                m.add_host(hX, hy)
+                m.eval_host(hQ, outs)
+                if with_est:
+                    m.lipschitz_constant()
+
+        step_host()
+        torch.cuda.synchronize()
+        e2e_ms = []
+        for _ in range(args.steps):
+            if flush:
+                ctx.flush()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step_host()
+            torch.cuda.synchronize()
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        ev_, tot = aggregate(pairs_step * args.steps, sum(e2e_ms), device="cuda")
+        h2d = sum(hX.numel() * hX.element_size() + hy.numel() * hy.element_size() + hQ.numel() * hQ.element_size()
+                  for _, hX, hy, hQ, _ in hostruns)
+        d2h = sum(sum(t.numel() * t.element_size() for t in o.values()) + (24 if with_est else 0)
+                  for *_, o in hostruns)
+        e2e = {"value": ev_, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": tot / args.steps}
+        if with_bwd:
+            e2e["note"] = "host path covers fit + eval (+ M_est); the backward pass is device-only"
+
+    cpu = _cpu(ctx, [r["p"] for r in runs])
+    tun = rd["m"].tuning()
+    key = lambda r: f"{NNAME[r['p'].norm]}/{r['prec']}"  # noqa: E731
+    detail = {"scan_ms": {key(r): statistics.mean(r["scan"]) for r in runs},
+              "scan_gpairs_per_s": {key(r): r["p"].nq * r["p"].N / (statistics.mean(r["scan"]) / 1e3) / 1e9
+                                    for r in runs},
+              "splits": tun["last_splits"], "tile_groups": tun["tile_groups"],
+              "queries_per_thread": tun["queries_per_thread"], "sms": ctx.sms}
+    if with_est:
+        detail["M_est"] = {key(r): est[k] for k, r in enumerate(runs)}
+        detail["M_true"] = {key(r): r["p"].M for r in runs}
+    for r in runs:
+        r["m"].close()
+    p0 = problems[0]
+    config = {"workload": name, "d": p0.d, "N": p0.N, "Q": p0.nq,
+              "mon": None if p0.mon is None else [int(v) for v in p0.mon],
+              "norms": [NNAME[p.norm] for p in problems], "precisions": list(precisions),
+              "step": "per problem: fit + eval" + (" + M_est" if with_est else "") + (" + backward" if with_bwd else ""),
+              "l2": "flushed before every timed step (256 MB write)" if flush else "inputs larger than L2"}
+    return ctx.line(value, total, args.steps, "f64" if precisions == ("fp64",) else "f32", config, roof, cpu, e2e,
+                    clocks, launches, detail)
+
+
+def wl_batch(ctx):
+    from paper_2606_04670_b300 import lipfit as L
+    torch, args = ctx.torch, ctx.args
+    plan = W.batch_plan()
+    sets_np = [W.batch_set_data(bs) for bs in plan]
+    qoff = np.concatenate([[0], np.cumsum([bs.nq * bs.d for bs in plan])])
+    noff = np.concatenate([[0], np.cumsum([bs.nq for bs in plan])])
+    hQ = torch.empty(int(qoff[-1]), dtype=torch.float32).pin_memory()
+    for k, (X, y, Q, f) in enumerate(sets_np):
+        hQ[int(qoff[k]):int(qoff[k + 1])] = torch.from_numpy(Q.reshape(-1))
+    dQ = hQ.to("cuda")
+    tq = int(noff[-1])
+    dout = {k: torch.empty(tq, device="cuda") for k in ("g", "lo", "hi")}
+    dout.update({k: torch.empty(tq, device="cuda", dtype=torch.int32) for k in ("idx_up", "idx_lo")})
+    sets, outs = [], []
+    for k, bs in enumerate(plan):
+        X, y, Q, f = sets_np[k]
+        sets.append(dict(X=torch.as_tensor(X), y=torch.as_tensor(y),
+                         Q=dQ[int(qoff[k]):int(qoff[k + 1])].view(bs.nq, bs.d), M=bs.M, norm=bs.norm, mon=bs.mon))
+        outs.append({key: v[int(noff[k]):int(noff[k + 1])] for key, v in dout.items()})
+    b = L.LipBatch(sets, outputs=outs)
+    info = b.info()
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    for _ in range(max(3, args.warmup)):
+        b.eval()
+    torch.cuda.synchronize()
+    b.check()
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        b.eval()
+    graph.replay()
+    torch.cuda.synchronize()
+    # the persistent scan kernel alone (events recorded by the library around it)
+    b.set_timing_events(*ev)
+    scan_ms = []
+    for _ in range(2):
+        b.eval()
+        torch.cuda.synchronize()
+        scan_ms.append(ev[0].elapsed_time(ev[1]))
+    b.set_timing_events(None, None)
+    ms, clocks, _ = ctx.timed(graph.replay, args.steps, flush=False)
+    launches = 2 * args.steps      # each replay runs the persistent scan and the batched merge
+    value, total = aggregate(info["total_pairs"] * args.steps, sum(ms), device="cuda")
+    ops = 0.0
+    for bs in plan:
+        ops += bs.nq * bs.N * i_pair(bs.norm, bs.d, int((bs.mon != 0).sum()))
+    roof = ctx.roofline("batch_scan_kernel (persistent, 4096 sets)", ops, min(scan_ms),
+                        ops / info["total_pairs"], None, clocks)
+    e2e = None
+    if not args.no_e2e:
+        hout = {k: torch.empty(tq, dtype=v.dtype).pin_memory() for k, v in dout.items()}
+        e2e_ms = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dQ.copy_(hQ, non_blocking=True)
+            graph.replay()
+            for k in hout:
+                hout[k].copy_(dout[k], non_blocking=True)
+            torch.cuda.synchronize()
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        ev_, tot = aggregate(info["total_pairs"] * args.steps, sum(e2e_ms), device="cuda")
+        e2e = {"value": ev_, "unit": UNIT, "h2d_bytes_per_step": hQ.numel() * 4,
+               "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in hout.values()),
+               "ms_per_step": tot / args.steps,
+               "note": "per step: all sets' queries host->device, graph replay, all outputs device->host"}
+    cpu = None
+    if ctx.rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_rate(reference_problems("batch_4096"), args.cpu_seconds)[0]
+    b.close()
+    config = {"workload": "batch_4096", "sets": len(plan), "N": "log-uniform [64, 65536]", "d": "uniform {2..10}",
+              "Q": "log-uniform [1e3, 1e5] per set", "total_pairs": info["total_pairs"],
+              "total_queries": info["total_queries"], "norms": ["L1", "L2"],
+              "step": "one CUDA-graph replay: persistent scan over the work list + batched merge",
+              "l2": "inputs larger than L2 (about 3 GB of data, layout and queries)"}
+    detail = {"scan_ms": min(scan_ms), "items": info["items"], "grid": info["grid"], "sms": ctx.sms}
+    return ctx.line(value, total, args.steps, "f32", config, roof, cpu, e2e, clocks, launches, detail)
+
 
 def run_ours(args):
     import torch
@@ -203,134 +509,19 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as tdist
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2606_04670_b300 import lipfit as L
-
-    p = W.monotone_d4(norm=W.NORM_L2)
-    N, d, nq = p.N, p.d, p.nq
-    X = torch.as_tensor(p.X).cuda()
-    y = torch.as_tensor(p.y).cuda()
-    Q = torch.as_tensor(p.Q).cuda()
-    models = {n: L.LipFit(M=p.M_by_norm[n], norm=n, mon=p.mon, capacity=N, d=d) for n in NORMS}
-    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")     # 256 MB > L2
-    ev = {n: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for n in NORMS}
-    for n in NORMS:
-        models[n].set_timing_events(*ev[n])
-    scan_ms = {n: [] for n in NORMS}
-    est = {}
-
-    def step(record_scan: bool):
-        for n in NORMS:
-            m = models[n]
-            m.clear()
-            m.add(X, y)
-            r = m.eval(Q)
-            if record_scan:
-                torch.cuda.synchronize()      # estimate_M syncs anyway; read the scan time now
-                scan_ms[n].append(ev[n][0].elapsed_time(ev[n][1]))
-            est[n] = m.lipschitz_constant()
-        return r
-
-    for _ in range(max(3, args.warmup)):
-        step(False)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    sampler = ClockSampler(local)
-    sampler.start()
-    launches0 = L.lip_kernel_launches()
-    step_ms = []
-    t_wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        step(True)
-        b.record()
-        torch.cuda.synchronize()
-        step_ms.append(a.elapsed_time(b))
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t_wall0
-    launches = L.lip_kernel_launches() - launches0
-    clocks = sampler.stop()
-    pairs_step = len(NORMS) * nq * N
-    value, total_ms = aggregate(pairs_step * args.steps, sum(step_ms), device="cuda")
-
-    # roofline of the dominant kernel (the scan with the largest time)
-    props = torch.cuda.get_device_properties(local)
-    sms = props.multi_processor_count
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    avg_scan = {n: statistics.mean(v) for n, v in scan_ms.items()}
-    dom = max(avg_scan, key=avg_scan.get)
-    peak_ops = sms * FP32_LANES_PER_SM * sm_max * 1e6
-    achieved = I_PAIR[dom] * nq * N / (avg_scan[dom] / 1e3)
-    roof = {"bound": "alu", "kernel": f"scan_exact_kernel<{NNAME[dom]}, C=2, U=2>",
-            "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 lane ops)",
-            "frac": achieved / peak_ops, "traffic": SCAN_DRAM_BYTES.get(dom),
-            "traffic_unit": "bytes per launch (ncu dram read + write)",
-            "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (max SM clock"
-                           f"{' of MEASURED_PEAKS.json' if peaks else ', nominal'})",
-            "i_pair": I_PAIR[dom], "mufu_per_pair": MUFU_PER_PAIR[dom]}
-    if clocks and clocks.get("sm_mhz"):
-        roof["frac_at_measured_clock"] = achieved / (sms * FP32_LANES_PER_SM * clocks["sm_mhz"] * 1e6)
-
-    # end to end through the C ABI with host buffers (copies inside the timed region)
-    e2e = None
-    if not args.no_e2e:
-        Xh, yh, Qh = (torch.as_tensor(a).pin_memory() for a in (p.X, p.y, p.Q))
-        outs = {k: torch.empty(nq, dtype=torch.float32).pin_memory() for k in ("g", "lo", "hi")}
-        outs.update({k: torch.empty(nq, dtype=torch.int32).pin_memory() for k in ("idx_up", "idx_lo")})
-
-        def step_host():
-            for n in NORMS:
-                m = models[n]
-                m.clear()
-                m.add_host(Xh, yh)
-                m.eval_host(Qh, outs)
-                m.lipschitz_constant()
-
-        for n in NORMS:
-            models[n].set_timing_events(None, None)
-        step_host()
-        torch.cuda.synchronize()
-        e2e_ms = []
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            step_host()
-            torch.cuda.synchronize()
-            e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        e2e_value, tot = aggregate(pairs_step * args.steps, sum(e2e_ms), device="cuda")
-        h2d = len(NORMS) * (N * d * 4 + N * 4 + nq * d * 4)
-        d2h = len(NORMS) * (nq * (3 * 4 + 2 * 4) + 24)
-        e2e = {"value": e2e_value, "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": tot / args.steps}
-
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu, _ = oracle_rate(p, NORMS, args.cpu_seconds)
-
-    tun = models[dom].tuning()
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded, monotone d=4 workload)", "config": dict(CONFIG, parallelism=f"replicas{world}"),
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-            "detail": {"scan_ms": {NNAME[n]: avg_scan[n] for n in NORMS},
-                       "scan_gpairs_per_s": {NNAME[n]: nq * N / (avg_scan[n] / 1e3) / 1e9 for n in NORMS},
-                       "M_est": {NNAME[n]: est[n][0] for n in NORMS},
-                       "M_true": {NNAME[n]: p.M_by_norm[n] for n in NORMS},
-                       "splits": tun["last_splits"], "tile_groups": tun["tile_groups"],
-                       "queries_per_thread": tun["queries_per_thread"], "sms": sms,
-                       "wall_s_timed": wall}}
-    for m in models.values():
-        m.close()
+    ctx = Ctx(args)
+    w = args.workload
+    if w == "monotone_d4":
+        base = W.monotone_d4(norm=W.NORM_L2)
+        line = wl_single(ctx, w, [base.with_norm(n) for n in NORMS])
+    elif w == "plain_d2":
+        line = wl_single(ctx, w, [W.plain_d2(dtype=np.float64)], precisions=("fp32", "fp64"))
+    elif w == "cluster_d16":
+        line = wl_single(ctx, w, [W.cluster_d16()], with_est=False, flush=False)
+    elif w == "grad_d8":
+        line = wl_single(ctx, w, [W.grad_d8()], with_bwd=True)
+    else:
+        line = wl_batch(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

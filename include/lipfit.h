@@ -209,6 +209,78 @@ LIP_API lip_status lip_backward(lip_handle h, const void* Q, int64_t nq, const i
                         const int32_t* idx_lo, const void* grad_g, void* grad_Q, void* grad_y,
                         double* grad_M, void* stream);
 
+/* ---------------------------------------------------------------- many data sets */
+
+/* One independent data set of a batch (Sec. 6: instance-based models with no training
+ * phase; many small ones are evaluated at once).  Device pointers are the caller's;
+ * X and y are copied by lip_batch_create, Q and the outputs are used by every
+ * lip_batch_eval (so refill Q in place to evaluate new queries).
+ *   X [N][d], y [N]   device float, 1 <= N < 2^31, 1 <= d <= 10.
+ *   norm, M, mon, w   as for lip_fit (mon, w: host arrays of d entries, or NULL).
+ *   Q [nq][d]         device float (nq may be 0).
+ *   g, lo, hi [nq], idx_up, idx_lo [nq]   device outputs, each may be NULL.
+ *   tile_groups       shared-memory tile of this set (8, 16, 32, 64; 0 = automatic). */
+typedef struct lip_batch_set {
+    const float* X;
+    const float* y;
+    int64_t N;
+    int32_t d;
+    int32_t norm;
+    double M;
+    const int8_t* mon;
+    const double* w;
+    const float* Q;
+    int64_t nq;
+    float* g;
+    float* lo;
+    float* hi;
+    int32_t* idx_up;
+    int32_t* idx_lo;
+    int32_t tile_groups;
+    int32_t reserved;
+} lip_batch_set;
+
+/* Launch-shape options of a batch (what the autotuner sets; results do not depend on it).
+ *   tile_groups      tile for sets with N > 512 when the set gives none (0 = 32).
+ *   items_per_block  work items per resident thread block that the data splitting aims
+ *                    at (0 = 8): more items balance the tail, fewer cost less merging.
+ *   waves            persistent grid = SMs x resident blocks per SM x waves (0 = 1). */
+typedef struct lip_batch_options {
+    int32_t tile_groups;
+    int32_t items_per_block;
+    int32_t waves;
+    int32_t reserved;
+} lip_batch_options;
+
+typedef struct lip_batch_model* lip_batch;
+
+/* Copy and transform every set (the lip_fit transform), cut the work into
+ * (set, query block, data split) items sorted largest first, and allocate all scratch.
+ * opt may be NULL.  Synchronises the stream once, to check that X and y are finite.
+ * Errors: LIP_ERR_ARG (naming the first bad set), LIP_ERR_NONFINITE, LIP_ERR_OOM,
+ * LIP_ERR_CUDA; on error *out is NULL. */
+LIP_API lip_status lip_batch_create(const lip_batch_set* sets, int32_t nsets, const lip_batch_options* opt,
+                                    void* stream, lip_batch* out);
+
+/* Evaluate every set at its queries: one persistent scan launch over the work list, then
+ * one merge launch that re-evaluates each query's two winners in FP64 and writes the
+ * outputs.  Only enqueues a 4-byte memset and the two kernels on `stream`: no allocation
+ * and no synchronisation.  Results equal lip_eval on each set. */
+LIP_API lip_status lip_batch_eval(lip_batch b, void* stream);
+
+/* Sizes of a batch: sum over sets of nq * N, sum of nq, work items, persistent grid. */
+LIP_API lip_status lip_batch_info(lip_batch b, double* total_pairs, int64_t* total_queries,
+                                  int64_t* n_items, int32_t* grid);
+
+/* Optional caller events recorded around the persistent scan kernel of every
+ * lip_batch_eval (NULL, NULL turns this off), as lip_set_timing_events. */
+LIP_API lip_status lip_batch_set_timing_events(lip_batch b, void* ev_before_scan, void* ev_after_scan);
+
+/* Synchronise and report LIP_ERR_TIMEOUT if a bounded wait in the batched kernel gave up. */
+LIP_API lip_status lip_batch_check(lip_batch b, void* stream);
+
+LIP_API void lip_batch_free(lip_batch b);
+
 /* ---------------------------------------------------------------- launch shape */
 
 /* Launch shape of lip_eval on this handle (what the autotuner sets).  The results do not

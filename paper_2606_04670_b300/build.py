@@ -39,7 +39,8 @@ def _compile(src, verbose=False):
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(d) for d in _deps()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep:
         return obj, ""
-    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-Xptxas", "-v", "-c", src, "-o", obj + ".tmp"]
+    extra = ["--split-compile=0"] if os.path.basename(src) == "batch.cu" else []
+    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-Xptxas", "-v", "-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{r.stderr[-6000:]}")

@@ -190,32 +190,41 @@ __device__ __forceinline__ void load_queries(const ScanParams& P, int64_t qbase,
     }
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// One block's share of the scan: queries [qblock * 128 R, +128 R) against data split
+// `split` of P.  Used by the one-launch-per-data-set kernel below and by the batched
+// persistent kernel (which calls it once per work item and re-initialises the
+// barriers between items: reinit = true invalidates them first).
 template <int NORM, int C, int U, int R>
-__global__ void __launch_bounds__(SCAN_THREADS)
-scan_exact_kernel(const ScanParams P) {
+__device__ __forceinline__ void scan_block(const ScanParams& P, int64_t qblock, int split, float4* tiles,
+                                           uint64_t* bars, bool reinit) {
     using S = ExactShape<NORM, C, U>;
     constexpr int D = S::D;
     constexpr int NCH = S::NCH;
-    extern __shared__ __align__(128) float4 tiles[];   // SCAN_STAGES * tile_groups * NCH
-    __shared__ __align__(8) uint64_t bars[SCAN_STAGES];
 
     const int tg = P.tile_groups;
     const uint32_t tile_bytes = (uint32_t)tg * NCH * 16u;
     const float4* hot = static_cast<const float4*>(P.hot);
 
-    const int64_t qbase = (int64_t)blockIdx.x * (SCAN_THREADS * R) + threadIdx.x;
+    const int64_t qbase = qblock * (SCAN_THREADS * R) + threadIdx.x;
     float2 qq[R][D];
     float sq[R];
     load_queries<D, R>(P, qbase, qq, sq, C);
 
-    const int64_t g_begin = (int64_t)blockIdx.y * P.groups_per_split;
+    const int64_t g_begin = (int64_t)split * P.groups_per_split;
     int64_t g_end = g_begin + P.groups_per_split;
     if (g_end > P.ngroups) g_end = P.ngroups;
     const int ntiles = g_begin < g_end ? (int)((g_end - g_begin) / tg) : 0;
 
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int s = 0; s < SCAN_STAGES; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < SCAN_STAGES; ++s) {
+            if (reinit) mbar_inval(&bars[s]);
+            mbar_init(&bars[s], 1);
+        }
         fence_mbar_init();
     }
     __syncthreads();
@@ -287,7 +296,7 @@ scan_exact_kernel(const ScanParams P) {
         for (int r = 0; r < R; ++r) {
             const int64_t qi = qbase + (int64_t)r * SCAN_THREADS;
             if (qi < P.nq)
-                static_cast<PartialRec<float>*>(P.partial)[(int64_t)blockIdx.y * P.nq + qi] =
+                static_cast<PartialRec<float>*>(P.partial)[(int64_t)split * P.nq + qi] =
                     PartialRec<float>{__int_as_float(0x7fc00000), -1, __int_as_float(0x7fc00000), -1};
         }
         return;
@@ -319,8 +328,16 @@ scan_exact_kernel(const ScanParams P) {
             }
         }
         const float lo_v = S::AUX ? ml[r] + sq[r] : ml[r];
-        static_cast<PartialRec<float>*>(P.partial)[(int64_t)blockIdx.y * P.nq + qi] = PartialRec<float>{mu[r], iu, lo_v, il};
+        static_cast<PartialRec<float>*>(P.partial)[(int64_t)split * P.nq + qi] = PartialRec<float>{mu[r], iu, lo_v, il};
     }
+}
+
+template <int NORM, int C, int U, int R>
+__global__ void __launch_bounds__(SCAN_THREADS)
+scan_exact_kernel(const ScanParams P) {
+    extern __shared__ __align__(128) float4 tiles[];   // SCAN_STAGES * tile_groups * NCH
+    __shared__ __align__(8) uint64_t bars[SCAN_STAGES];
+    scan_block<NORM, C, U, R>(P, blockIdx.x, blockIdx.y, tiles, bars, false);
 }
 
 // ------------------------------------------------------------------ generic scan
@@ -443,9 +460,7 @@ __device__ __forceinline__ double dist_fp64(const MergeParams& P, const T* q, co
 // Picks the best split record (lowest split, hence lowest index, on exact ties), then
 // re-evaluates both winners in FP64 from the caller's data and writes g, lo, hi, idx.
 template <typename T>
-__global__ void merge_kernel(const MergeParams P) {
-    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (qi >= P.nq) return;
+__device__ __forceinline__ void merge_one(const MergeParams& P, int64_t qi) {
     T bu = 0, bl = 0;
     int iu = -1, il = -1;
     const PartialRec<T>* part = static_cast<const PartialRec<T>*>(P.partial);
@@ -472,6 +487,12 @@ __global__ void merge_kernel(const MergeParams P) {
     if (P.hi) static_cast<T*>(P.hi)[qi] = (T)hi;
     if (P.idx_up) P.idx_up[qi] = iu;
     if (P.idx_lo) P.idx_lo[qi] = il;
+}
+
+template <typename T>
+__global__ void merge_kernel(const MergeParams P) {
+    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi < P.nq) merge_one<T>(P, qi);
 }
 
 // -------------------------------------------------------------- layout builder

@@ -39,6 +39,19 @@ class lip_params(ctypes.Structure):
                 ("mon", ctypes.c_void_p), ("w", ctypes.c_void_p)]
 
 
+class lip_batch_set(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("y", ctypes.c_void_p), ("N", ctypes.c_int64), ("d", ctypes.c_int32),
+                ("norm", ctypes.c_int32), ("M", ctypes.c_double), ("mon", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("Q", ctypes.c_void_p), ("nq", ctypes.c_int64), ("g", ctypes.c_void_p), ("lo", ctypes.c_void_p),
+                ("hi", ctypes.c_void_p), ("idx_up", ctypes.c_void_p), ("idx_lo", ctypes.c_void_p),
+                ("tile_groups", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class lip_batch_options(ctypes.Structure):
+    _fields_ = [("tile_groups", ctypes.c_int32), ("items_per_block", ctypes.c_int32), ("waves", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class LipError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str):
         super().__init__(f"{where}: {status_string(status)} ({status}): {detail}")
@@ -69,6 +82,12 @@ def _load():
         "lip_get_tuning": [H, P, P, P, P],
         "lip_set_timing_events": [H, P, P],
         "lip_estimate_M_noalloc": [P, P, i64, i32, i32, P, P, P],
+        "lip_batch_create": [ctypes.POINTER(lip_batch_set), i32, ctypes.POINTER(lip_batch_options), P,
+                             ctypes.POINTER(H)],
+        "lip_batch_eval": [H, P],
+        "lip_batch_info": [H, P, P, P, P],
+        "lip_batch_check": [H, P],
+        "lip_batch_set_timing_events": [H, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -78,6 +97,8 @@ def _load():
     lib.lip_size.restype = i64
     lib.lip_free.argtypes = [H]
     lib.lip_free.restype = None
+    lib.lip_batch_free.argtypes = [H]
+    lib.lip_batch_free.restype = None
     lib.lip_status_string.argtypes = [ctypes.c_int]
     lib.lip_status_string.restype = ctypes.c_char_p
     lib.lip_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
@@ -202,6 +223,31 @@ def lip_set_timing_events(h, ev_before, ev_after):
 
 def lip_kernel_launches():
     return int(_lib.lip_kernel_launches())
+
+
+def lip_batch_create(sets, opt=None, stream=0):
+    """sets: a ctypes array of lip_batch_set; opt: lip_batch_options or None."""
+    h = ctypes.c_void_p()
+    s = _lib.lip_batch_create(sets, len(sets), None if opt is None else ctypes.byref(opt), stream, ctypes.byref(h))
+    return s, h
+
+
+def lip_batch_eval(b, stream=0):
+    return _lib.lip_batch_eval(b, stream)
+
+
+def lip_batch_info(b):
+    tp, tq, ni, gr = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    s = _lib.lip_batch_info(b, ctypes.byref(tp), ctypes.byref(tq), ctypes.byref(ni), ctypes.byref(gr))
+    return s, tp.value, tq.value, ni.value, gr.value
+
+
+def lip_batch_check(b, stream=0):
+    return _lib.lip_batch_check(b, stream)
+
+
+def lip_batch_free(b):
+    _lib.lip_batch_free(b)
 
 
 def lip_check(h, stream=0):
@@ -395,6 +441,81 @@ class LipFit:
     def close(self):
         if self.h:
             _lib.lip_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LipBatch:
+    """Many independent data sets evaluated by one persistent launch (lip_batch_*).
+
+    sets: list of dicts with keys X, y, Q (CUDA float32 tensors), M, norm, and optional
+    mon, w.  Outputs are allocated here as CUDA tensors (``outputs[i]`` holds g, lo, hi,
+    idx_up, idx_lo of set i) and refreshed in place by every ``eval``; refill
+    ``sets[i]['Q']`` in place to evaluate new queries.  ``eval`` only enqueues work, so
+    it can be captured in a torch.cuda.CUDAGraph.
+    """
+
+    def __init__(self, sets, tile_groups=0, items_per_block=0, waves=0, outputs=None):
+        torch = _torch()
+        self.sets = []
+        self.outputs = []
+        self._keep = []
+        arr = (lip_batch_set * len(sets))()
+        for k, st in enumerate(sets):
+            X = st["X"].to(device="cuda", dtype=torch.float32).contiguous()
+            y = st["y"].to(device="cuda", dtype=torch.float32).contiguous()
+            Q = st["Q"].to(device="cuda", dtype=torch.float32).contiguous()
+            nq = Q.shape[0]
+            if outputs is not None:
+                out = outputs[k]       # caller-owned CUDA tensors (e.g. views of one buffer)
+            else:
+                out = {"g": torch.empty(nq, device="cuda"), "lo": torch.empty(nq, device="cuda"),
+                       "hi": torch.empty(nq, device="cuda"),
+                       "idx_up": torch.empty(nq, device="cuda", dtype=torch.int32),
+                       "idx_lo": torch.empty(nq, device="cuda", dtype=torch.int32)}
+            mon = None if st.get("mon") is None else np.ascontiguousarray(st["mon"], np.int8)
+            w = None if st.get("w") is None else np.ascontiguousarray(st["w"], np.float64)
+            self._keep += [mon, w]
+            nv = NORMS[st.get("norm", LIP_L2)]
+            arr[k] = lip_batch_set(X.data_ptr(), y.data_ptr(), X.shape[0], X.shape[1], nv, float(st["M"]),
+                                   None if mon is None else mon.ctypes.data, None if w is None else w.ctypes.data,
+                                   Q.data_ptr() if nq else None, nq, out["g"].data_ptr(), out["lo"].data_ptr(),
+                                   out["hi"].data_ptr(), out["idx_up"].data_ptr(), out["idx_lo"].data_ptr(),
+                                   int(st.get("tile_groups", 0)), 0)
+            self.sets.append({"X": X, "y": y, "Q": Q})
+            self.outputs.append(out)
+        opt = lip_batch_options(int(tile_groups), int(items_per_block), int(waves), 0)
+        s, self.h = lip_batch_create(arr, opt, _stream_ptr())
+        _check(s, "lip_batch_create")
+        # the copies of X and y are made; keep Q and the outputs alive with the batch
+
+    def eval(self):
+        _check(_lib.lip_batch_eval(self.h, _stream_ptr()), "lip_batch_eval")
+
+    def info(self):
+        s, tp, tq, ni, gr = lip_batch_info(self.h)
+        _check(s, "lip_batch_info")
+        return {"total_pairs": tp, "total_queries": tq, "items": ni, "grid": gr}
+
+    def check(self):
+        _check(_lib.lip_batch_check(self.h, _stream_ptr()), "lip_batch_check")
+
+    def set_timing_events(self, ev_before=None, ev_after=None):
+        for ev in (ev_before, ev_after):
+            if ev is not None and not ev.cuda_event:
+                ev.record()
+        _check(_lib.lip_batch_set_timing_events(self.h, None if ev_before is None else ev_before.cuda_event,
+                                                None if ev_after is None else ev_after.cuda_event),
+               "lip_batch_set_timing_events")
+
+    def close(self):
+        if self.h:
+            _lib.lip_batch_free(self.h)
             self.h = ctypes.c_void_p()
 
     def __del__(self):

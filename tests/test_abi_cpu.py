@@ -85,3 +85,25 @@ def test_valid_call_without_device_reports_no_device():
     p, keep = L.make_params()
     s, h = L.lip_fit(X.ctypes.data, y.ctypes.data, 8, 2, 1.0, p)
     assert s in (L.LIP_ERR_NO_DEVICE, L.LIP_ERR_CUDA) and not h.value
+
+
+def test_batch_argument_errors():
+    arr = (L.lip_batch_set * 2)()
+    ok = L.lip_batch_set(1, 1, 10, 3, L.LIP_L2, 1.0, None, None, 1, 5, None, None, None, None, None, 0, 0)
+    arr[0] = ok
+    arr[1] = L.lip_batch_set(1, 1, 10, 11, L.LIP_L2, 1.0, None, None, 1, 5, None, None, None, None, None, 0, 0)
+    s, h = L.lip_batch_create(arr)
+    assert s == L.LIP_ERR_ARG and "set 1" in L.last_error() and not h.value
+    arr[1] = L.lip_batch_set(1, 1, 10, 3, L.LIP_L2, -1.0, None, None, 1, 5, None, None, None, None, None, 0, 0)
+    assert L.lip_batch_create(arr)[0] == L.LIP_ERR_ARG
+    arr[1] = L.lip_batch_set(1, 1, 10, 3, L.LIP_L2, 1.0, None, None, None, 5, None, None, None, None, None, 0, 0)
+    assert L.lip_batch_create(arr)[0] == L.LIP_ERR_ARG          # queries but Q is NULL
+    arr[1] = L.lip_batch_set(1, 1, 10, 3, L.LIP_L2, 1.0, None, None, 1, 5, None, None, None, None, None, 12, 0)
+    assert L.lip_batch_create(arr)[0] == L.LIP_ERR_ARG          # tile size
+    opt = L.lip_batch_options(7, 0, 0, 0)
+    arr[1] = ok
+    assert L.lip_batch_create(arr, opt)[0] == L.LIP_ERR_ARG
+    assert L.lip_batch_eval(None) == L.LIP_ERR_ARG
+    assert L.lip_batch_info(None)[0] == L.LIP_ERR_ARG
+    assert L.lip_batch_check(None) == L.LIP_ERR_ARG
+    L.lip_batch_free(None)

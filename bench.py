@@ -44,7 +44,9 @@ UNIT = "G pairs/s"
 NORMS = (W.NORM_L1, W.NORM_L2, W.NORM_LINF)
 NNAME = {1: "L1", 2: "L2", 3: "Linf"}
 FP32_LANES_PER_SM = 128
-WORKLOADS = ("monotone_d4", "plain_d2", "cluster_d16", "grad_d8", "batch_4096")
+WORKLOADS = ("monotone_d4", "plain_d2", "cluster_d16", "cluster_d16_tc", "grad_d8", "batch_4096")
+# TF32 dense peak: the measured BF16 peak times the nominal TF32 / BF16 ratio (1.1 / 2.25)
+TF32_OVER_BF16 = 1.1 / 2.25
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant scan kernel of
 # the default workload, from the ncu capture summarised in
 # profiles/scan_exact_l2_monotone_d4.md (None whenever that kernel changes until it is
@@ -75,6 +77,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     return ap.parse_args()
 
 
@@ -185,7 +188,7 @@ def reference_problems(workload):
         return [base.with_norm(n) for n in NORMS]
     if workload == "plain_d2":
         return [W.plain_d2(dtype=np.float64)]
-    if workload == "cluster_d16":
+    if workload in ("cluster_d16", "cluster_d16_tc"):
         return [W.cluster_d16(n_query=20_000)]
     if workload == "grad_d8":
         return [W.grad_d8()]
@@ -319,6 +322,17 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
             m.set_timing_events(*ev)
             runs.append(dict(p=p, prec=prec, X=X, y=y, Q=Q, m=m, ev=ev, scan=[],
                              gb=torch.ones(p.nq, device="cuda", dtype=dt)))
+    tuning = {}
+    if not args.no_autotune:
+        from paper_2606_04670_b300 import autotune as AT
+        cache = AT.load_cache()
+        for r in runs:
+            if r["prec"] == "tc_tf32":
+                continue               # the launch shape knobs belong to the plain scan
+            r["m"].clear()
+            r["m"].add(r["X"], r["y"])
+            tuning[f"{NNAME[r['p'].norm]}/{r['prec']}"] = AT.tune_eval(r["m"], r["Q"], cache=cache)
+        AT.save_cache(cache, os.path.join(ROOT, "gpurun_out", "autotune_cache.json"))
     est = {}
 
     def step(record=False):
@@ -352,6 +366,18 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
             f"R={rd['m'].tuning()['queries_per_thread']}> {rd['prec']}")
     roof = ctx.roofline(kern, ip * p.nq * p.N, avg[kdom], ip, mufu_per_pair(p.norm, c), clocks,
                         SCAN_DRAM_BYTES.get((name, p.norm)) if rd["prec"] == "fp32" else None)
+    if rd["prec"] == "tc_tf32":
+        # tensor-core form: three TF32 products over K = 8 ceil((d + 2) / 8) per pair
+        kk = 8 * ((p.d + 2 + 7) // 8)
+        flops = 2.0 * 3 * kk * p.nq * p.N
+        peak = float(ctx.peaks.get("bf16_tflops", 1800.0)) * TF32_OVER_BF16 * 1e12
+        alu = roof
+        roof = {"bound": "tensor", "kernel": f"tc_scan_kernel<K={kk}> (+ build and rescreen)",
+                "achieved": flops / (avg[kdom] / 1e3) / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s (TF32)",
+                "frac": flops / (avg[kdom] / 1e3) / peak, "traffic": None,
+                "peak_source": "measured bf16 dense peak of MEASURED_PEAKS.json x 1.1/2.25 (nominal TF32/BF16)",
+                "flops_per_pair": 6 * kk,
+                "alu_view": {k: alu[k] for k in ("achieved", "peak", "frac", "i_pair")}}
 
     e2e = None
     if not args.no_e2e:
@@ -403,7 +429,8 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
               "scan_gpairs_per_s": {key(r): r["p"].nq * r["p"].N / (statistics.mean(r["scan"]) / 1e3) / 1e9
                                     for r in runs},
               "splits": tun["last_splits"], "tile_groups": tun["tile_groups"],
-              "queries_per_thread": tun["queries_per_thread"], "sms": ctx.sms}
+              "queries_per_thread": tun["queries_per_thread"], "sms": ctx.sms, "autotune": tuning,
+              "tc_fallback_queries": {key(r): r["m"].last_fallback() for r in runs if r["prec"] == "tc_tf32"}}
     if with_est:
         detail["M_est"] = {key(r): est[k] for k, r in enumerate(runs)}
         detail["M_true"] = {key(r): r["p"].M for r in runs}
@@ -439,7 +466,15 @@ def wl_batch(ctx):
         sets.append(dict(X=torch.as_tensor(X), y=torch.as_tensor(y),
                          Q=dQ[int(qoff[k]):int(qoff[k + 1])].view(bs.nq, bs.d), M=bs.M, norm=bs.norm, mon=bs.mon))
         outs.append({key: v[int(noff[k]):int(noff[k + 1])] for key, v in dout.items()})
-    b = L.LipBatch(sets, outputs=outs)
+    tuning = None
+    opts = {}
+    if not args.no_autotune:
+        from paper_2606_04670_b300 import autotune as AT
+        cache = AT.load_cache()
+        tuning = AT.tune_batch(sets, cache=cache, outputs=outs)
+        AT.save_cache(cache, os.path.join(ROOT, "gpurun_out", "autotune_cache.json"))
+        opts = {k: tuning[k] for k in ("tile_groups", "items_per_block", "waves")}
+    b = L.LipBatch(sets, outputs=outs, **opts)
     info = b.info()
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     for _ in range(max(3, args.warmup)):
@@ -495,7 +530,8 @@ def wl_batch(ctx):
               "total_queries": info["total_queries"], "norms": ["L1", "L2"],
               "step": "one CUDA-graph replay: persistent scan over the work list + batched merge",
               "l2": "inputs larger than L2 (about 3 GB of data, layout and queries)"}
-    detail = {"scan_ms": min(scan_ms), "items": info["items"], "grid": info["grid"], "sms": ctx.sms}
+    detail = {"scan_ms": min(scan_ms), "items": info["items"], "grid": info["grid"], "sms": ctx.sms,
+              "autotune": tuning}
     return ctx.line(value, total, args.steps, "f32", config, roof, cpu, e2e, clocks, launches, detail)
 
 
@@ -518,6 +554,8 @@ def run_ours(args):
         line = wl_single(ctx, w, [W.plain_d2(dtype=np.float64)], precisions=("fp32", "fp64"))
     elif w == "cluster_d16":
         line = wl_single(ctx, w, [W.cluster_d16()], with_est=False, flush=False)
+    elif w == "cluster_d16_tc":
+        line = wl_single(ctx, w, [W.cluster_d16()], precisions=("tc_tf32",), with_est=False, flush=False)
     elif w == "grad_d8":
         line = wl_single(ctx, w, [W.grad_d8()], with_bwd=True)
     else:

@@ -66,6 +66,11 @@ typedef enum {
     LIP_FP64 = 1,      /* FP64 throughout                                                   */
     LIP_TC_BF16 = 2,   /* L2 only: tensor-core cross term (bf16 split), exact FP64 rescreen  */
     LIP_TC_TF32 = 3    /* L2 only: tensor-core cross term (tf32 split), exact FP64 rescreen  */
+    /* LIP_TC_TF32 needs the L2 norm and no monotone coordinates (the squared distance is
+     * then one augmented product).  Its lip_eval synchronises the stream once; the
+     * returned bounds are the exact FP64 envelopes (see the kernel's error bound), with
+     * the plain FP32 scan as fallback for queries with too many near-ties.
+     * LIP_TC_BF16 is accepted by the enum but returns LIP_ERR_UNSUPPORTED. */
 } lip_precision;
 
 /* Largest dimension d accepted by lip_fit / lip_reserve. */
@@ -304,6 +309,11 @@ LIP_API lip_status lip_get_tuning(lip_handle h, int32_t* tile_groups, int32_t* s
  * stream immediately before and after its all-pairs scan kernel, so that the kernel can
  * be timed alone on the stream it runs on.  NULL, NULL turns this off. */
 LIP_API lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, void* ev_after_scan);
+
+/* LIP_TC_TF32 handles: number of queries of the last lip_eval whose candidate lists
+ * overflowed and were recomputed by the plain FP32 scan (0 when the tensor-core form and
+ * its exact rescreen settled every query); -1 for a NULL handle. */
+LIP_API int64_t lip_last_fallback(lip_handle h);
 
 /* Number of kernels this library has launched in this process (all handles). */
 LIP_API uint64_t lip_kernel_launches(void);

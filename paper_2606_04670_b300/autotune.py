@@ -1,0 +1,124 @@
+"""Autotuner for the launch shapes of lip_eval and lip_batch_eval.
+
+The results of both calls do not depend on their launch shape (the tests check bitwise
+equality), so the shape is chosen purely by measured time: every candidate is timed
+with CUDA events on the launching stream, taking the median of several runs after a
+warm-up, and the fastest is kept.
+
+* ``tune_eval(model, Q)`` sweeps the shared-memory tile (tile_groups) and the number of
+  data splits of one data set, applies the best with ``lip_set_tuning`` and returns it.
+* ``tune_batch(sets)`` sweeps the batch options (default tile, work items per resident
+  block, persistent-grid waves) and returns the best ``lip_batch_options`` as a dict.
+
+Results are cached in a JSON file keyed by the problem's shape and size buckets
+(norm, constrained and free coordinates, log2 of N and of the query count), so a later
+run reuses them without timing.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import statistics
+from typing import Dict, Iterable, Optional
+
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning", "b300_cache.json")
+
+
+def _bucket(n: int) -> int:
+    return int(math.floor(math.log2(max(1, n))))
+
+
+def eval_key(model, nq: int) -> str:
+    c = 0 if model.mon is None else int((model.mon != 0).sum())
+    return f"eval/norm{model.norm}/C{c}/U{model.d - c}/prec{model.precision}/N2^{_bucket(model.N)}/Q2^{_bucket(nq)}"
+
+
+def load_cache(path: Optional[str] = None) -> Dict:
+    path = path or DEFAULT_CACHE
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: Dict, path: Optional[str] = None):
+    path = path or DEFAULT_CACHE
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _time(fn, reps: int = 3, warm: int = 1) -> float:
+    import torch
+    for _ in range(warm):
+        fn()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def tune_eval(model, Q, tiles: Iterable[int] = (8, 16, 32, 64), splits: Iterable[int] = (0, 1, 2, 3, 4, 6, 8, 12, 16),
+              cache: Optional[Dict] = None, reps: int = 3) -> Dict:
+    """Time lip_eval on `model` for every (tile_groups, splits) and apply the fastest."""
+    key = eval_key(model, Q.shape[0])
+    if cache is not None and key in cache:
+        best = cache[key]
+        model.set_tuning(best["tile_groups"], best["splits"])
+        return dict(best, cached=True)
+    results = []
+    for tg in tiles:
+        for sp in splits:
+            model.set_tuning(tg, sp)
+            ms = _time(lambda: model.eval(Q, need=("g", "idx_up", "idx_lo")), reps=reps)
+            results.append({"tile_groups": tg, "splits": sp, "ms": ms,
+                            "splits_used": model.tuning()["last_splits"]})
+    best = min(results, key=lambda r: r["ms"])
+    model.set_tuning(best["tile_groups"], best["splits"])
+    rec = {"tile_groups": best["tile_groups"], "splits": best["splits"], "ms": best["ms"],
+           "default_ms": next(r["ms"] for r in results if r["tile_groups"] == 32 and r["splits"] == 0),
+           "candidates": len(results)}
+    if cache is not None:
+        cache[key] = rec
+    return dict(rec, cached=False)
+
+
+def batch_key(sets) -> str:
+    n = len(sets)
+    pairs = sum(int(s["Q"].shape[0]) * int(s["X"].shape[0]) for s in sets)
+    return f"batch/sets{n}/pairs2^{_bucket(pairs)}"
+
+
+def tune_batch(sets, tiles: Iterable[int] = (16, 32, 64), items: Iterable[int] = (2, 4, 8, 16),
+               waves: Iterable[int] = (1,), cache: Optional[Dict] = None, reps: int = 2, outputs=None) -> Dict:
+    """Time lip_batch_eval for every option combination; return the fastest options."""
+    from .lipfit import LipBatch
+    key = batch_key(sets)
+    if cache is not None and key in cache:
+        return dict(cache[key], cached=True)
+    results = []
+    for tg in tiles:
+        for it in items:
+            for wv in waves:
+                b = LipBatch(sets, tile_groups=tg, items_per_block=it, waves=wv, outputs=outputs)
+                ms = _time(b.eval, reps=reps)
+                results.append({"tile_groups": tg, "items_per_block": it, "waves": wv, "ms": ms})
+                b.close()
+    best = min(results, key=lambda r: r["ms"])
+    rec = {k: best[k] for k in ("tile_groups", "items_per_block", "waves", "ms")}
+    rec["candidates"] = len(results)
+    rec["default_ms"] = next((r["ms"] for r in results if r["tile_groups"] == 32 and r["items_per_block"] == 8
+                              and r["waves"] == 1), None)
+    if cache is not None:
+        cache[key] = rec
+    return dict(rec, cached=False)

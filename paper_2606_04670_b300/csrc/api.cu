@@ -123,6 +123,14 @@ struct lip_model {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
     cudaEvent_t ev_scan0 = nullptr, ev_scan1 = nullptr;   // caller's timing events
+    // tensor-core form (LIP_TC_TF32)
+    bool tc = false, tc_dirty = true;
+    int64_t tc_ntiles_cap = 0;
+    char* tc_btiles = nullptr;
+    double* tc_stats = nullptr;        // [D_MAX] sums of the scaled coordinates
+    unsigned* tc_maxbits = nullptr;    // [2] max |x^|, max |y| (float bits)
+    Scratch tc_q, tc_fb;
+    int64_t last_fallback = 0;
 };
 
 namespace {
@@ -143,7 +151,12 @@ lip_status check_params(int32_t d, double M, const lip_params* p) {
                 return fail(LIP_ERR_ARG, "w[%d] = %g must be finite and > 0", i, p->w[i]);
     if (p->precision == LIP_TC_BF16 || p->precision == LIP_TC_TF32) {
         if (p->norm != LIP_L2) return fail(LIP_ERR_UNSUPPORTED, "tensor-core precision needs the L2 norm");
-        return fail(LIP_ERR_UNSUPPORTED, "tensor-core precision is not available in this build");
+        if (p->precision == LIP_TC_BF16)
+            return fail(LIP_ERR_UNSUPPORTED, "the bf16 tensor-core split is not available; use LIP_TC_TF32");
+        if (p->mon)
+            for (int i = 0; i < d; ++i)
+                if (p->mon[i] != 0)
+                    return fail(LIP_ERR_UNSUPPORTED, "the tensor-core form needs the symmetric distance (no mon)");
     }
     return LIP_OK;
 }
@@ -190,6 +203,11 @@ void free_model(lip_model* h) {
     h->est.release();
     h->bwd.release();
     h->io.release();
+    h->tc_q.release();
+    h->tc_fb.release();
+    if (h->tc_btiles) cudaFree(h->tc_btiles);
+    if (h->tc_stats) cudaFree(h->tc_stats);
+    if (h->tc_maxbits) cudaFree(h->tc_maxbits);
     for (int b = 0; b < 2; ++b) {
         if (h->ev_in[b]) cudaEventDestroy(h->ev_in[b]);
         if (h->ev_out[b]) cudaEventDestroy(h->ev_out[b]);
@@ -231,7 +249,8 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
         if (h->mon[i] != 0) h->C++;
     }
     const int U = d - h->C;
-    if (h->prec == LIP_FP32 && exact_shape_available(h->C, U)) {
+    h->tc = h->prec == LIP_TC_TF32;
+    if ((h->prec == LIP_FP32 || h->tc) && exact_shape_available(h->C, U)) {
         h->exact = true;
         h->dl = d;
         h->aux = (h->norm == LIP_L1 && h->C > 0) ? 1 : 0;
@@ -272,6 +291,22 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
             return cuda_fail(e, a.what);
         }
     }
+    if (h->tc) {
+        h->tc_ntiles_cap = ceil_div(cap, 256);
+        struct { void** p; size_t n; const char* what; } tca[] = {
+            {reinterpret_cast<void**>(&h->tc_btiles), (size_t)h->tc_ntiles_cap * tc_tile_bytes_for(d), "tensor-core data tiles"},
+            {reinterpret_cast<void**>(&h->tc_stats), D_MAX * sizeof(double), "tensor-core centre"},
+            {reinterpret_cast<void**>(&h->tc_maxbits), 2 * sizeof(unsigned), "tensor-core bounds"},
+        };
+        for (auto& a : tca) {
+            e = cudaMalloc(a.p, a.n);
+            if (e != cudaSuccess) {
+                *a.p = nullptr;
+                free_model(h);
+                return cuda_fail(e, a.what);
+            }
+        }
+    }
     e = cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), st);
     if (e == cudaSuccess) e = launch_pad_hot(h->esize, h->hot, 0, h->cap_pad, h->nch, h->dl, st);
     count_launches(1);
@@ -309,6 +344,7 @@ lip_status add_points(lip_model* h, const void* X, const void* y, int64_t n, cud
         return fail(LIP_ERR_NONFINITE, "X or y holds NaN or Inf");
     }
     h->N += n;
+    h->tc_dirty = true;
     return LIP_OK;
 }
 
@@ -347,8 +383,8 @@ int choose_splits(const lip_model* h, int64_t gx, int64_t tiles) {
     return best;
 }
 
-lip_status eval_device(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* iu, int32_t* il,
-                       cudaStream_t st) {
+lip_status eval_plain(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* iu, int32_t* il,
+                      cudaStream_t st) {
     const int64_t ngroups = round_up(h->N, PAD_POINTS) / GROUP;
     const int tg = h->exact ? h->tile_groups : 1;
     const int64_t gx = ceil_div(nq, (int64_t)SCAN_THREADS * h->kinfo.rows);
@@ -403,6 +439,70 @@ lip_status eval_device(lip_model* h, const void* Q, int64_t nq, void* g, void* l
     return LIP_OK;
 }
 
+// Tensor-core form: prepare the data tiles if the data or M changed, then build the
+// query tiles, scan on the tensor cores, rescreen candidates in FP64, and send the
+// queries whose candidate lists overflowed through the plain scan.  Synchronises once
+// to read the overflow count.
+lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* iu, int32_t* il,
+                   cudaStream_t st) {
+    const int d = h->d;
+    double scale[D_MAX];
+    for (int j = 0; j < D_MAX; ++j) scale[j] = j < d ? h->M * h->w[j] : 0.0;
+    const int64_t ntiles = ceil_div(h->N, 256);
+    if (h->tc_dirty) {
+        CUDA_TRY(tc_prepare_data(static_cast<const float*>(h->X0), static_cast<const float*>(h->y0), h->N, d, scale,
+                                 h->tc_stats, h->tc_maxbits, h->tc_btiles, ntiles, st));
+        count_launches(2);
+        h->tc_dirty = false;
+    }
+    const int64_t nqt = ceil_div(nq, 128);
+    const size_t a_b = round_up((int64_t)(nqt * tc_a_bytes_for(d)), 256), eps_b = round_up(nq * 8, 256),
+                 rec_b = round_up((int64_t)(nq * 4 * tc_rec_bytes()), 256), list_b = round_up(nq * 4 + 4, 256);
+    LIP_TRY(h->tc_q.ensure(a_b + eps_b + rec_b + list_b, "tensor-core query scratch"));
+    char* base = static_cast<char*>(h->tc_q.p);
+    int* fb_list = reinterpret_cast<int*>(base + a_b + eps_b + rec_b);
+    int* fb_count = fb_list + nq;
+    if (h->ev_scan0) CUDA_TRY(cudaEventRecord(h->ev_scan0, st));
+    CUDA_TRY(tc_eval_launch(static_cast<const float*>(Q), nq, d, scale, h->tc_stats, h->N, h->tc_maxbits, h->tc_btiles,
+                            ntiles, base, reinterpret_cast<float2*>(base + a_b), base + a_b + eps_b, h->w, h->M,
+                            static_cast<const float*>(h->X0), static_cast<const float*>(h->y0), static_cast<float*>(g),
+                            static_cast<float*>(lo), static_cast<float*>(hi), iu, il, fb_count, fb_list, h->status, st));
+    count_launches(3);
+    if (h->ev_scan1) CUDA_TRY(cudaEventRecord(h->ev_scan1, st));
+    int nfb = 0;
+    CUDA_TRY(cudaMemcpyAsync(&nfb, fb_count, sizeof nfb, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    h->last_fallback = nfb;
+    if (nfb > 0) {
+        const size_t q_b = round_up((int64_t)nfb * d * 4, 256), v_b = round_up((int64_t)nfb * 4, 256);
+        LIP_TRY(h->tc_fb.ensure(q_b + 5 * v_b, "tensor-core fallback scratch"));
+        char* fb = static_cast<char*>(h->tc_fb.p);
+        float* fq = reinterpret_cast<float*>(fb);
+        float* fg = reinterpret_cast<float*>(fb + q_b);
+        float* flo = reinterpret_cast<float*>(fb + q_b + v_b);
+        float* fhi = reinterpret_cast<float*>(fb + q_b + 2 * v_b);
+        int32_t* fiu = reinterpret_cast<int32_t*>(fb + q_b + 3 * v_b);
+        int32_t* fil = reinterpret_cast<int32_t*>(fb + q_b + 4 * v_b);
+        CUDA_TRY(tc_gather(static_cast<const float*>(Q), d, fb_list, nfb, fq, st));
+        cudaEvent_t e0 = h->ev_scan0, e1 = h->ev_scan1;
+        h->ev_scan0 = h->ev_scan1 = nullptr;
+        const lip_status s = eval_plain(h, fq, nfb, fg, flo, fhi, fiu, fil, st);
+        h->ev_scan0 = e0;
+        h->ev_scan1 = e1;
+        LIP_TRY(s);
+        CUDA_TRY(tc_scatter(fb_list, nfb, fg, flo, fhi, fiu, fil, static_cast<float*>(g), static_cast<float*>(lo),
+                            static_cast<float*>(hi), iu, il, st));
+        count_launches(2);
+    }
+    return LIP_OK;
+}
+
+lip_status eval_device(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* iu, int32_t* il,
+                       cudaStream_t st) {
+    if (h->tc) return eval_tc(h, Q, nq, g, lo, hi, iu, il, st);
+    return eval_plain(h, Q, nq, g, lo, hi, iu, il, st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -449,6 +549,7 @@ lip_status lip_clear(lip_handle h, void* stream) {
     CUDA_TRY(launch_pad_hot(h->esize, h->hot, 0, round_up(h->N, PAD_POINTS), h->nch, h->dl, static_cast<cudaStream_t>(stream)));
     count_launches(1);
     h->N = 0;
+    h->tc_dirty = true;
     return LIP_OK;
 }
 
@@ -459,6 +560,7 @@ lip_status lip_set_M(lip_handle h, double M, void* stream) {
     if (!(M >= 0.0) || !std::isfinite(M)) return fail(LIP_ERR_ARG, "M = %g must be finite and >= 0", M);
     DeviceGuard g(h->device);
     h->M = M;
+    h->tc_dirty = true;
     HotParams P;
     fill_hot_params(h, P, 0, h->N);
     CUDA_TRY(launch_build_hot(h->esize, P, static_cast<cudaStream_t>(stream)));
@@ -695,6 +797,8 @@ lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, void* ev_af
 }
 
 uint64_t lip_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int64_t lip_last_fallback(lip_handle h) { return h ? h->last_fallback : -1; }
 
 void lip_free(lip_handle h) { free_model(h); }
 

@@ -1,0 +1,604 @@
+// Tensor-core form of the unmasked L2 envelope scan (LIP_TC_TF32).
+//
+// Squared distance as one augmented product: with q^ = M w (q - c), x^ = M w (x - c)
+// (c = the data mean; distances do not depend on it),
+//     s(q, x) = |q^|^2 + |x^|^2 - 2 q^.x^ = a . b,   a = [-2 q^, 1, |q^|^2],  b = [x^, |x^|^2, 1],
+// padded with zeros to K = 8, 16 or 24.  Every operand is split v = hi + lo with hi the
+// value truncated to TF32 and lo the FP32 remainder, and s~ = a_hi.b_hi + a_hi.b_lo +
+// a_lo.b_hi runs as three tcgen05.mma kind::tf32 passes accumulating in FP32 in TMEM.
+//
+// Error bound used to prune (conservative, per query):
+//   |s~ - s| <= eps = 2e-5 (|q^| + R)^2,  R = max_k |x^_k|, from
+//   * 3 * 2^-20 |a||b| for the dropped and truncated split terms;
+//   * 72 * 2^-23 for FP32 accumulation of 72 products;
+//   * 4 * 2^-22 sqrt(d) + 2^-23 for the FP32 rounding of the inputs;
+//   together <= 1.54e-5 times sum |a_j b_j| <= (|q^| + |x^|)^2.
+// Then |sqrt(s~+) - sqrt(s)| <= eps / sqrt(max(s~+, eps)); for a 32-point chunk the
+// smallest s~ in it bounds every pair.  With the FP32 evaluation error of the bounds,
+//   delta_c = 1.001 eps rsqrt(max(min_chunk s~, eps)) + 2^-19 (max|y| + |q^| + R).
+// A chunk can hold the exact argmin only if min_chunk v~ - delta_c <= U, where
+// U = min over chunks of (min_chunk v~ + delta_c) is an upper bound of H_up; the same
+// holds mirrored for H_lo.  Candidate chunks are kept per query (8 per half row), then
+// rescreened exactly in FP64 from the caller's data; a query whose list overflows is
+// recomputed by the plain FP32 scan.
+//
+// Kernel: one CTA per 128-query tile, 10 warps.  Warp 0 streams 256-point data tiles
+// (pre-tiled hi/lo operands and y, one 1-D bulk copy each) into a 3-stage ring; warp 1
+// owns TMEM (512 columns = two 128 x 256 FP32 accumulators) and issues the MMAs; warps
+// 2..9 are the epilogue: each reads one 32-lane quarter of the accumulator rows (one
+// query per thread) over half of the columns with tcgen05.ld, clamps, takes sqrt, forms
+// y +- sqrt and keeps the chunk extrema and candidate lists.  Every wait is bounded.
+#include <cstdio>
+
+#include "launch.h"
+
+namespace lip {
+
+constexpr int TC_M = 128;
+constexpr int TC_N = 256;
+constexpr int TC_STAGES = 3;
+constexpr int TC_CAP = 8;
+constexpr int TC_THREADS = 320;
+constexpr float TC_C_EPS = 2.0e-5f;
+
+struct TcRec {      // candidate list of one (query, bound, half)
+    float U;        // upper bound of H_up (bound 0) or lower bound of H_lo (bound 1)
+    int n;          // entries, -1 = overflow
+    int id[TC_CAP];
+    float L[TC_CAP];
+};
+
+__host__ __device__ constexpr int tc_k_for_dim(int d) { return ((d + 2 + 7) / 8) * 8; }
+__host__ __device__ constexpr uint32_t tc_sbo(int K) { return (uint32_t)(K / 4) * 128u; }
+__host__ __device__ constexpr int tc_tile_bytes(int K) { return 2 * TC_N * K * 4 + TC_N * 4; }
+__host__ __device__ constexpr int tc_a_bytes(int K) { return 2 * TC_M * K * 4; }
+
+// byte offset of element (r, k) in a canonical no-swizzle K-major operand
+__host__ __device__ inline uint32_t tc_off(int r, int k, int K) {
+    return (uint32_t)(r / 8) * tc_sbo(K) + (uint32_t)(k / 4) * 128u + (uint32_t)(r % 8) * 16u + (uint32_t)(k % 4) * 4u;
+}
+
+__device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+
+// --------------------------------------------------------------- data preparation
+
+struct TcPrepParams {
+    const float* X0;      // caller's data [N][d]
+    const float* y0;
+    int64_t N;
+    int d, K;
+    double scale[D_MAX];  // M * w_j (caller's coordinate order; unmasked, so no mirroring)
+    double* stats;        // [D_MAX] sums, then centre; stats[D_MAX] = R (as double), [D_MAX+1] = Ymax
+    unsigned* maxbits;    // [2]: float bits of R and of max|y|
+    char* tiles;          // [ntiles][tile_bytes]
+    int64_t ntiles;
+};
+
+__global__ void tc_sum_kernel(const TcPrepParams P) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double acc[D_MAX];
+    if (threadIdx.x < D_MAX) acc[threadIdx.x] = 0.0;
+    __syncthreads();
+    if (k < P.N)
+        for (int j = 0; j < P.d; ++j) atomicAdd(&acc[j], P.scale[j] * (double)P.X0[k * P.d + j]);
+    __syncthreads();
+    if (threadIdx.x < P.d) atomicAdd(&P.stats[threadIdx.x], acc[threadIdx.x]);
+}
+
+// One thread per (padded) data point: its row of B_hi, B_lo and y in the tile layout.
+__global__ void tc_build_b_kernel(const TcPrepParams P) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.ntiles * TC_N) return;
+    const int64_t t = k / TC_N;
+    const int r = (int)(k % TC_N);
+    char* tile = P.tiles + t * (int64_t)tc_tile_bytes(P.K);
+    float* bhi = reinterpret_cast<float*>(tile);
+    float* blo = reinterpret_cast<float*>(tile + TC_N * P.K * 4);
+    float* yv = reinterpret_cast<float*>(tile + 2 * TC_N * P.K * 4);
+    float b[32];
+    for (int j = 0; j < P.K; ++j) b[j] = 0.f;
+    float yy = __int_as_float(0x7fc00000);
+    if (k < P.N) {
+        double n2 = 0.0;
+        for (int j = 0; j < P.d; ++j) {
+            const double c = P.stats[j] / (double)P.N;
+            const float xh = (float)(P.scale[j] * (double)P.X0[k * P.d + j] - c);
+            b[j] = xh;
+            n2 += (double)xh * (double)xh;
+        }
+        b[P.d] = (float)n2;
+        b[P.d + 1] = 1.f;
+        yy = P.y0[k];
+        atomicMax(&P.maxbits[0], __float_as_uint((float)sqrt(n2)));
+        atomicMax(&P.maxbits[1], __float_as_uint(fabsf(yy)));
+    }
+    for (int j = 0; j < P.K; ++j) {
+        const float hi = tf32_trunc(b[j]);
+        bhi[tc_off(r, j, P.K) / 4] = hi;
+        blo[tc_off(r, j, P.K) / 4] = b[j] - hi;
+    }
+    yv[r] = yy;
+}
+
+struct TcQueryParams {
+    const float* Q;        // caller's queries [nq][d]
+    int64_t nq;
+    int d, K;
+    double scale[D_MAX];
+    const double* stats;   // sums (centre = sums / N)
+    int64_t N;
+    const unsigned* maxbits;
+    char* atiles;          // [nqt][a_bytes]: A_hi then A_lo
+    float2* eps;           // [nq]: (eps, eps_v)
+};
+
+// One thread per (padded) query: its row of A_hi, A_lo and its error bounds.
+__global__ void tc_build_a_kernel(const TcQueryParams P) {
+    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nqp = (P.nq + TC_M - 1) / TC_M * TC_M;
+    if (qi >= nqp) return;
+    const int64_t t = qi / TC_M;
+    const int r = (int)(qi % TC_M);
+    char* at = P.atiles + t * (int64_t)tc_a_bytes(P.K);
+    float* ahi = reinterpret_cast<float*>(at);
+    float* alo = reinterpret_cast<float*>(at + TC_M * P.K * 4);
+    float a[32];
+    for (int j = 0; j < P.K; ++j) a[j] = 0.f;
+    if (qi < P.nq) {
+        double n2 = 0.0;
+        for (int j = 0; j < P.d; ++j) {
+            const double c = P.stats[j] / (double)P.N;
+            const float qh = (float)(P.scale[j] * (double)P.Q[qi * P.d + j] - c);
+            a[j] = -2.f * qh;
+            n2 += (double)qh * (double)qh;
+        }
+        a[P.d] = 1.f;
+        a[P.d + 1] = (float)n2;
+        const double R = (double)__uint_as_float(P.maxbits[0]);
+        const double Y = (double)__uint_as_float(P.maxbits[1]);
+        const double nq = sqrt(n2);
+        const float eps = (float)((double)TC_C_EPS * (nq + R) * (nq + R));
+        const float epsv = (float)(ldexp(1.0, -19) * (Y + nq + R));
+        P.eps[qi] = make_float2(eps, epsv);
+    }
+    for (int j = 0; j < P.K; ++j) {
+        const float hi = tf32_trunc(a[j]);
+        ahi[tc_off(r, j, P.K) / 4] = hi;
+        alo[tc_off(r, j, P.K) / 4] = a[j] - hi;
+    }
+}
+
+// --------------------------------------------------------------- tcgen05 helpers
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, int K) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;          // leading (K-direction) byte offset
+    d |= (uint64_t)((tc_sbo(K) >> 4) & 0x3FFFu) << 32;     // stride between 8-row groups
+    d |= (uint64_t)1 << 46;                                 // descriptor version of sm_100
+    return d;                                               // no swizzle, base offset 0
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(dtmem), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+struct TcScanParams {
+    const char* atiles;
+    const char* btiles;
+    const float2* eps;
+    int64_t nq;
+    int64_t ntiles;
+    TcRec* rec;            // [nq][2 bounds][2 halves]
+    unsigned* err;
+};
+
+// Candidate list append with compaction when full (entries that can no longer qualify
+// are dropped; the bound only tightens).  upper = true for H_up (keep L <= U).
+__device__ __forceinline__ void tc_append(TcRec* R, int& n, int id, float L, float bound, bool upper) {
+    if (n < 0) return;
+    if (n == TC_CAP) {
+        int m = 0;
+        for (int e = 0; e < TC_CAP; ++e) {
+            const float le = R->L[e];
+            if (upper ? (le <= bound) : (le >= bound)) {
+                R->id[m] = R->id[e];
+                R->L[m] = le;
+                ++m;
+            }
+        }
+        n = m;
+        if (n == TC_CAP) { n = -1; return; }
+    }
+    R->id[n] = id;
+    R->L[n] = L;
+    ++n;
+}
+
+template <int K>
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_scan_kernel(const TcScanParams P) {
+    constexpr int TILE_BYTES = tc_tile_bytes(K);
+    constexpr int A_BYTES = tc_a_bytes(K);
+    constexpr int KS = K / 8;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;                               // A_hi, A_lo
+    unsigned char* sB = smem + A_BYTES;                     // TC_STAGES tiles
+    __shared__ __align__(8) uint64_t a_full, b_full[TC_STAGES], b_empty[TC_STAGES], acc_full[2], acc_empty[2];
+    __shared__ uint32_t tmem_base;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int64_t qt = blockIdx.x;
+    const int64_t T = P.ntiles;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&a_full, 1);
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&b_full[s], 1);
+            mbar_init(&b_empty[s], 1 + 8);                  // MMA commit + 8 epilogue warps
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 8);
+        }
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_base)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tb = tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------ producer
+        if (lane == 0) {
+            int64_t t = 0;
+            bool ok = true;
+            mbar_expect_tx(&a_full, A_BYTES);
+            bulk_g2s(sA, P.atiles + qt * (int64_t)A_BYTES, A_BYTES, &a_full);
+            for (; t < T; ++t) {
+                const int s = (int)(t % TC_STAGES);
+                if (t >= TC_STAGES && !mbar_wait_bounded(&b_empty[s], (uint32_t)((t / TC_STAGES - 1) & 1), P.err)) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(&b_full[s], TILE_BYTES);
+                bulk_g2s(sB + (size_t)s * TILE_BYTES, P.btiles + t * (int64_t)TILE_BYTES, TILE_BYTES, &b_full[s]);
+            }
+            // wait (bounded) for the copies still in flight before leaving
+            const int64_t first = t > TC_STAGES ? t - TC_STAGES : 0;
+            for (int64_t u = first; u < t; ++u)
+                mbar_wait_bounded(&b_full[u % TC_STAGES], (uint32_t)((u / TC_STAGES) & 1), ok ? P.err : nullptr);
+            mbar_wait_bounded(&a_full, 0, nullptr);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                                   ((uint32_t)(TC_M >> 4) << 24);
+            const uint32_t a_hi = smem_u32(sA), a_lo = a_hi + TC_M * K * 4;
+            int64_t t = 0;
+            if (mbar_wait_bounded(&a_full, 0, P.err)) {
+                for (; t < T; ++t) {
+                    const int s = (int)(t % TC_STAGES), b = (int)(t & 1);
+                    if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / TC_STAGES) & 1), P.err)) break;
+                    if (t >= 2 && !mbar_wait_bounded(&acc_empty[b], (uint32_t)((t / 2 - 1) & 1), P.err)) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t b_hi = smem_u32(sB + (size_t)s * TILE_BYTES), b_lo = b_hi + TC_N * K * 4;
+                    const uint32_t d = tb + (uint32_t)b * TC_N;
+#pragma unroll
+                    for (int ks = 0; ks < KS; ++ks)
+                        tc_mma(d, tc_desc(a_hi + ks * 256, K), tc_desc(b_hi + ks * 256, K), idesc, ks > 0);
+#pragma unroll
+                    for (int ks = 0; ks < KS; ++ks)
+                        tc_mma(d, tc_desc(a_hi + ks * 256, K), tc_desc(b_lo + ks * 256, K), idesc, 1);
+#pragma unroll
+                    for (int ks = 0; ks < KS; ++ks)
+                        tc_mma(d, tc_desc(a_lo + ks * 256, K), tc_desc(b_hi + ks * 256, K), idesc, 1);
+                    tc_commit(&b_empty[s]);
+                    tc_commit(&acc_full[b]);
+                }
+            }
+            // the last MMAs must finish before TMEM is released
+            if (t > 0) mbar_wait_bounded(&acc_full[(t - 1) & 1], (uint32_t)(((t - 1) / 2) & 1), nullptr);
+        }
+    } else {
+        // ------------------------------------------------ epilogue (warps 2..9)
+        const int quarter = warp % 4, half = (warp - 2) / 4;
+        const int64_t qi = qt * TC_M + quarter * 32 + lane;
+        const bool valid = qi < P.nq;
+        float2 e2 = valid ? P.eps[qi] : make_float2(1.f, 1.f);
+        // a zero bound (M = 0) must not turn eps * rsqrt(0) into NaN
+        const float eps = fmaxf(e2.x, 1e-30f), epsv = e2.y;
+        TcRec* Ru = P.rec + (valid ? ((qi * 2 + 0) * 2 + half) : 0);
+        TcRec* Rl = P.rec + (valid ? ((qi * 2 + 1) * 2 + half) : 0);
+        const float INF = __int_as_float(0x7f800000);
+        float U = INF, Bl = -INF;
+        int nu = 0, nl = 0;
+        for (int64_t t = 0; t < T; ++t) {
+            const int s = (int)(t % TC_STAGES), b = (int)(t & 1);
+            if (!mbar_wait_bounded(&acc_full[b], (uint32_t)((t / 2) & 1), P.err)) break;
+            // acquire the tile's y values written by the bulk copy
+            if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / TC_STAGES) & 1), P.err)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const float* ys = reinterpret_cast<const float*>(sB + (size_t)s * TILE_BYTES + 2 * TC_N * K * 4);
+#pragma unroll 1
+            for (int j = 0; j < 4; ++j) {
+                const int col = half * 128 + j * 32;
+                float sv[32];
+                tmem_ld32(tb + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * TC_N + col, sv);
+                float cs = INF, cu = INF, cl = -INF;
+#pragma unroll
+                for (int e = 0; e < 32; e += 2) {
+                    const float2 yv = *reinterpret_cast<const float2*>(ys + col + e);
+                    cs = min3f(cs, sv[e], sv[e + 1]);
+                    const float2 rt = make_float2(sqrt_approx(fmaxf(sv[e], 0.f)), sqrt_approx(fmaxf(sv[e + 1], 0.f)));
+                    const float2 vu = add2(yv, rt), vl = sub2(yv, rt);
+                    cu = min3f(cu, vu.x, vu.y);
+                    cl = max3f(cl, vl.x, vl.y);
+                }
+                if (valid) {
+                    const float dlt = 1.001f * eps * rsqrt_approx(fmaxf(cs, eps)) + epsv;
+                    const int chunk = (int)(t * 8 + half * 4 + j);
+                    U = fminf(U, cu + dlt);
+                    if (cu - dlt <= U) tc_append(Ru, nu, chunk, cu - dlt, U, true);
+                    Bl = fmaxf(Bl, cl - dlt);
+                    if (cl + dlt >= Bl) tc_append(Rl, nl, chunk, cl + dlt, Bl, false);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&acc_empty[b]);
+                mbar_arrive(&b_empty[s]);
+            }
+        }
+        if (valid) {
+            Ru->U = U;
+            Ru->n = nu;
+            Rl->U = Bl;
+            Rl->n = nl;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tb));
+    }
+}
+
+// --------------------------------------------------------------- exact rescreen
+
+struct TcRescreenParams {
+    const float* Q;
+    int64_t nq;
+    int d;
+    double M;
+    double w[D_MAX];
+    const float* X0;
+    const float* y0;
+    int64_t N;
+    const TcRec* rec;
+    float *g, *lo, *hi;
+    int32_t *idx_up, *idx_lo;
+    int* fb_count;          // queries sent to the fallback scan
+    int* fb_list;
+};
+
+__device__ __forceinline__ double tc_dist64(const TcRescreenParams& P, const float* q, const float* x) {
+    double acc = 0.0;
+    for (int i = 0; i < P.d; ++i) {
+        const double t = ((double)q[i] - (double)x[i]) * P.w[i];
+        acc += t * t;
+    }
+    return sqrt(acc);
+}
+
+__global__ void tc_rescreen_kernel(const TcRescreenParams P) {
+    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= P.nq) return;
+    const float* q = P.Q + qi * P.d;
+    bool finite = true;
+    for (int i = 0; i < P.d; ++i) finite = finite && isfinite(q[i]);
+    const TcRec* R = P.rec + qi * 4;
+    if (finite && (R[0].n < 0 || R[1].n < 0 || R[2].n < 0 || R[3].n < 0)) {
+        P.fb_list[atomicAdd(P.fb_count, 1)] = (int)qi;
+        return;
+    }
+    double best[2] = {0.0, 0.0};
+    int bidx[2] = {-1, -1};
+    if (finite) {
+        for (int b = 0; b < 2; ++b) {
+            const float bound = b == 0 ? fminf(R[b * 2].U, R[b * 2 + 1].U) : fmaxf(R[b * 2].U, R[b * 2 + 1].U);
+            for (int h = 0; h < 2; ++h) {
+                const TcRec& r = R[b * 2 + h];
+                for (int e = 0; e < r.n; ++e) {
+                    if (b == 0 ? !(r.L[e] <= bound) : !(r.L[e] >= bound)) continue;
+                    const int64_t k0 = (int64_t)r.id[e] * 32;
+                    for (int p = 0; p < 32; ++p) {
+                        const int64_t k = k0 + p;
+                        if (k >= P.N) break;
+                        const double dist = P.M * tc_dist64(P, q, P.X0 + k * P.d);
+                        const double v = b == 0 ? (double)P.y0[k] + dist : (double)P.y0[k] - dist;
+                        const bool better = bidx[b] < 0 || (b == 0 ? v < best[b] : v > best[b]) ||
+                                            (v == best[b] && k < bidx[b]);
+                        if (better) { best[b] = v; bidx[b] = (int)k; }
+                    }
+                }
+            }
+        }
+    }
+    double hi = best[0], lo = best[1];
+    if (!finite || bidx[0] < 0 || bidx[1] < 0) {
+        hi = lo = __longlong_as_double(0x7ff8000000000000ll);
+        bidx[0] = bidx[1] = -1;
+    }
+    if (P.g) P.g[qi] = (float)(0.5 * (hi + lo));
+    if (P.lo) P.lo[qi] = (float)lo;
+    if (P.hi) P.hi[qi] = (float)hi;
+    if (P.idx_up) P.idx_up[qi] = bidx[0];
+    if (P.idx_lo) P.idx_lo[qi] = bidx[1];
+}
+
+// Gather the fallback queries into a compact block, and scatter their results back.
+__global__ void tc_gather_kernel(const float* Q, int d, const int* list, int n, float* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n * d) return;
+    out[i] = Q[(int64_t)list[i / d] * d + i % d];
+}
+
+__global__ void tc_scatter_kernel(const int* list, int n, const float* g, const float* lo, const float* hi,
+                                  const int32_t* iu, const int32_t* il, float* G, float* LO, float* HI, int32_t* IU,
+                                  int32_t* IL) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int q = list[i];
+    if (G) G[q] = g[i];
+    if (LO) LO[q] = lo[i];
+    if (HI) HI[q] = hi[i];
+    if (IU) IU[q] = iu[i];
+    if (IL) IL[q] = il[i];
+}
+
+// --------------------------------------------------------------- launchers
+
+size_t tc_tile_bytes_for(int d) { return (size_t)tc_tile_bytes(tc_k_for_dim(d)); }
+size_t tc_a_bytes_for(int d) { return (size_t)tc_a_bytes(tc_k_for_dim(d)); }
+size_t tc_rec_bytes() { return sizeof(TcRec); }
+
+cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, const double* scale, double* stats,
+                            unsigned* maxbits, char* tiles, int64_t ntiles, cudaStream_t st) {
+    TcPrepParams P{};
+    P.X0 = X0;
+    P.y0 = y0;
+    P.N = N;
+    P.d = d;
+    P.K = tc_k_for_dim(d);
+    for (int j = 0; j < D_MAX; ++j) P.scale[j] = scale[j];
+    P.stats = stats;
+    P.maxbits = maxbits;
+    P.tiles = tiles;
+    P.ntiles = ntiles;
+    cudaError_t e = cudaMemsetAsync(stats, 0, D_MAX * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(maxbits, 0, 2 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    if (N > 0) tc_sum_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(P);
+    const int64_t rows = ntiles * TC_N;
+    if (rows > 0) tc_build_b_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t launch_tc_scan_k(const TcScanParams& P, int64_t nqt, cudaStream_t st) {
+    const size_t smem = (size_t)tc_a_bytes(K) + (size_t)TC_STAGES * tc_tile_bytes(K);
+    static cudaError_t attr =
+        cudaFuncSetAttribute(tc_scan_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
+    tc_scan_kernel<K><<<(unsigned)nqt, TC_THREADS, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+// Queries: build A, scan, rescreen.  Returns the fallback count through fb (device).
+cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scale, const double* stats, int64_t N,
+                           const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float2* eps,
+                           void* rec, const double* w, double M, const float* X0, const float* y0, float* g, float* lo,
+                           float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, unsigned* err,
+                           cudaStream_t st) {
+    const int K = tc_k_for_dim(d);
+    const int64_t nqt = (nq + TC_M - 1) / TC_M;
+    TcQueryParams A{};
+    A.Q = Q;
+    A.nq = nq;
+    A.d = d;
+    A.K = K;
+    for (int j = 0; j < D_MAX; ++j) A.scale[j] = scale[j];
+    A.stats = stats;
+    A.N = N;
+    A.maxbits = maxbits;
+    A.atiles = atiles;
+    A.eps = eps;
+    tc_build_a_kernel<<<(unsigned)((nqt * TC_M + 255) / 256), 256, 0, st>>>(A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    TcScanParams S{};
+    S.atiles = atiles;
+    S.btiles = btiles;
+    S.eps = eps;
+    S.nq = nq;
+    S.ntiles = ntiles;
+    S.rec = static_cast<TcRec*>(rec);
+    S.err = err;
+    if (K == 8) e = launch_tc_scan_k<8>(S, nqt, st);
+    else if (K == 16) e = launch_tc_scan_k<16>(S, nqt, st);
+    else e = launch_tc_scan_k<24>(S, nqt, st);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(fb_count, 0, sizeof(int), st)) != cudaSuccess) return e;
+    TcRescreenParams R{};
+    R.Q = Q;
+    R.nq = nq;
+    R.d = d;
+    R.M = M;
+    for (int j = 0; j < D_MAX; ++j) R.w[j] = w[j];
+    R.X0 = X0;
+    R.y0 = y0;
+    R.N = N;
+    R.rec = static_cast<const TcRec*>(rec);
+    R.g = g;
+    R.lo = lo;
+    R.hi = hi;
+    R.idx_up = iu;
+    R.idx_lo = il;
+    R.fb_count = fb_count;
+    R.fb_list = fb_list;
+    tc_rescreen_kernel<<<(unsigned)((nq + 127) / 128), 128, 0, st>>>(R);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_gather(const float* Q, int d, const int* list, int n, float* out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    tc_gather_kernel<<<(unsigned)(((int64_t)n * d + 255) / 256), 256, 0, st>>>(Q, d, list, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_scatter(const int* list, int n, const float* g, const float* lo, const float* hi, const int32_t* iu,
+                       const int32_t* il, float* G, float* LO, float* HI, int32_t* IU, int32_t* IL, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    tc_scatter_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(list, n, g, lo, hi, iu, il, G, LO, HI, IU, IL);
+    return cudaGetLastError();
+}
+
+}  // namespace lip

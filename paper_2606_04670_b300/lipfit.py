@@ -105,6 +105,8 @@ def _load():
     lib.lip_last_error.restype = ctypes.c_size_t
     lib.lip_version.restype = ctypes.c_char_p
     lib.lip_kernel_launches.restype = ctypes.c_uint64
+    lib.lip_last_fallback.argtypes = [H]
+    lib.lip_last_fallback.restype = ctypes.c_int64
     return lib
 
 
@@ -219,6 +221,10 @@ def lip_get_tuning(h):
 
 def lip_set_timing_events(h, ev_before, ev_after):
     return _lib.lip_set_timing_events(h, ev_before, ev_after)
+
+
+def lip_last_fallback(h):
+    return int(_lib.lip_last_fallback(h))
 
 
 def lip_kernel_launches():
@@ -420,6 +426,9 @@ class LipFit:
 
     def check(self):
         _check(_lib.lip_check(self.h, _stream_ptr()), "lip_check")
+
+    def last_fallback(self) -> int:
+        return lip_last_fallback(self.h)
 
     def set_tuning(self, tile_groups: int = 0, splits: int = 0):
         _check(_lib.lip_set_tuning(self.h, int(tile_groups), int(splits)), "lip_set_tuning")

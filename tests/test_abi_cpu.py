@@ -107,3 +107,12 @@ def test_batch_argument_errors():
     assert L.lip_batch_info(None)[0] == L.LIP_ERR_ARG
     assert L.lip_batch_check(None) == L.LIP_ERR_ARG
     L.lip_batch_free(None)
+
+
+def test_tensor_core_precision_rules():
+    X, y = _arr(8, 2), _arr(8)
+    for norm, prec, mon in [(L.LIP_L1, L.LIP_TC_TF32, None), (L.LIP_L2, L.LIP_TC_TF32, [1, 0]),
+                            (L.LIP_L2, L.LIP_TC_BF16, None)]:
+        p, keep = L.make_params(norm, prec, mon, None)
+        s, h = L.lip_fit(X.ctypes.data, y.ctypes.data, 8, 2, 1.0, p)
+        assert s == L.LIP_ERR_UNSUPPORTED and not h.value, L.last_error()

@@ -1,0 +1,44 @@
+"""The autotuner picks a launch shape by timing and never changes results."""
+import numpy as np
+import pytest
+
+from paper_2606_04670_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tune_eval_keeps_results_and_caches(tmp_path):
+    import torch
+
+    from paper_2606_04670_b300 import autotune as AT
+    from paper_2606_04670_b300.lipfit import LipFit
+    p = W.monotone_d4(norm=W.NORM_L2, n_data=20_000, n_query=50_000)
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, mon=p.mon)
+    Q = torch.as_tensor(p.Q).cuda()
+    ref = {k: v.cpu().numpy() for k, v in m.eval(Q).items()}
+    cache = {}
+    rec = AT.tune_eval(m, Q, tiles=(8, 32), splits=(0, 1, 4), cache=cache, reps=2)
+    assert not rec["cached"] and rec["ms"] <= rec["default_ms"] + 1e-9
+    assert m.tuning()["tile_groups"] == rec["tile_groups"]
+    got = {k: v.cpu().numpy() for k, v in m.eval(Q).items()}
+    for k in ref:
+        np.testing.assert_array_equal(got[k], ref[k])
+    path = str(tmp_path / "cache.json")
+    AT.save_cache(cache, path)
+    again = AT.tune_eval(m, Q, cache=AT.load_cache(path))
+    assert again["cached"] and again["tile_groups"] == rec["tile_groups"]
+    m.close()
+
+
+def test_tune_batch_returns_options():
+    import torch
+
+    from paper_2606_04670_b300 import autotune as AT
+    plan = W.batch_plan(n_sets=12, n_max=4000, q_min=100, q_max=1500)
+    sets = []
+    for bs in plan:
+        X, y, Q, f = W.batch_set_data(bs)
+        sets.append(dict(X=torch.as_tensor(X), y=torch.as_tensor(y), Q=torch.as_tensor(Q).cuda(), M=bs.M,
+                         norm=bs.norm, mon=bs.mon))
+    rec = AT.tune_batch(sets, tiles=(16, 32), items=(4, 8), cache={}, reps=1)
+    assert rec["tile_groups"] in (16, 32) and rec["items_per_block"] in (4, 8) and rec["candidates"] == 4

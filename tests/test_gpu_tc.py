@@ -1,0 +1,122 @@
+"""Tensor-core L2 form (LIP_TC_TF32): the TF32-split product on tcgen05 with an error
+bound, candidate pruning and an exact FP64 rescreen.  Its bounds are the FP64
+envelopes, so indices must match the oracle's wherever the oracle's gap exceeds
+1e-9 M diam (far below the FP32 tolerance).  Needs a CUDA device."""
+import numpy as np
+import pytest
+
+from paper_2606_04670_b300 import workloads as W
+from parity import FP32_TOL, compare, diam, gpu_eval
+
+pytestmark = pytest.mark.gpu
+EXACT_GAP = 1e-9
+
+
+def _tc_eval(p):
+    """Outputs of a LIP_TC_TF32 handle and the number of its queries that went through
+    the plain FP32 fallback (those only meet the FP32 index rule)."""
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, w=p.w,
+               precision="tc_tf32")
+    r = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
+    fb = m.last_fallback()
+    m.check()
+    m.close()
+    return r, fb
+
+
+def _check_exact(p, gpu, orc, label, fallback=0):
+    compare(p, gpu, orc, FP32_TOL, label)
+    scale = p.M * diam(p.X, p.Q[: len(orc["hi"])], p.norm, p.w)
+    for k, gk in (("idx_up", "gap_up"), ("idx_lo", "gap_lo")):
+        clear = orc[gk] > EXACT_GAP * scale
+        bad = np.nonzero(clear & (gpu[k].astype(np.int64) != orc[k]))[0]
+        assert bad.size <= fallback, (f"{label} {k}: {bad.size} mismatches with gap > {EXACT_GAP} M diam, "
+                                      f"{fallback} fallback queries")
+    # the outputs are FP64 values rounded once to FP32
+    for k in ("hi", "lo"):
+        np.testing.assert_allclose(gpu[k], orc[k].astype(np.float32), rtol=0, atol=2e-7 * (1 + np.abs(orc[k]).max()))
+
+
+@pytest.mark.parametrize("d,weighted", [(1, False), (2, True), (3, False), (6, True), (7, False), (13, True),
+                                        (16, False)])
+def test_tc_random_shapes(oracle_mod, d, weighted):
+    p = W.random_problem(950 + d, 5_003, d, 1_201, norm=W.NORM_L2, weighted=weighted)
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm, w=p.w)
+    r, fb = _tc_eval(p)
+    _check_exact(p, r, orc, f"tc d={d}", fb)
+    if d >= 6:
+        assert fb == 0, f"{fb} fallback queries at d={d}"
+
+
+def test_tc_cluster_subsample(oracle_mod):
+    p = W.cluster_d16(n_data=30_000, n_query=1_500)
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm)
+    r, fb = _tc_eval(p)
+    _check_exact(p, r, orc, "tc cluster", fb)
+
+
+def test_tc_equals_plain_within_tolerance(oracle_mod):
+    p = W.cluster_d16(n_data=20_000, n_query=1_000)
+    a, b = gpu_eval(p, "tc_tf32"), gpu_eval(p, "fp32")
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm)
+    compare(p, a, orc, FP32_TOL, "tc")
+    compare(p, b, orc, FP32_TOL, "plain")
+
+
+def test_tc_edge_cases_and_fallback(oracle_mod):
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    # a single data point, one query, a NaN query, sizes that are not tile multiples
+    p = W.random_problem(960, 1, 4, 3)
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm)
+    compare(p, gpu_eval(p, "tc_tf32"), orc, FP32_TOL, "tc N=1")
+    p = W.random_problem(961, 257, 5, 129)
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, precision="tc_tf32")
+    Q = torch.as_tensor(p.Q).cuda().clone()
+    Q[5, 2] = float("nan")
+    r = {k: v.cpu().numpy() for k, v in m.eval(Q).items()}
+    assert np.isnan(r["g"][5]) and r["idx_up"][5] == -1
+    keep = np.arange(p.nq) != 5
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q[keep], p.M, p.norm)
+    ps = W.Problem("e", p.X, p.y, p.Q[keep], p.M, p.norm, None, None)
+    compare(ps, {k: v[keep] for k, v in r.items()}, orc, FP32_TOL, "tc ragged")
+    # after clear: NaN and -1 everywhere
+    m.clear()
+    r = m.eval(torch.as_tensor(p.Q).cuda())
+    assert torch.isnan(r["g"]).all() and (r["idx_up"] == -1).all()
+    m.check()
+    m.close()
+    # M = 0 with a constant y over 3000 points: every 32-point chunk ties, so each
+    # query's candidate lists (8 chunks per half row) overflow and the queries go
+    # through the plain scan; the result is still the lowest index
+    p = W.random_problem(962, 3_000, 5, 300)
+    yc = np.full(p.N, 0.25, np.float32)
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(yc).cuda(), 0.0, norm=p.norm, precision="tc_tf32")
+    r = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
+    assert m.last_fallback() == p.nq
+    assert np.all(r["idx_up"] == 0) and np.all(r["idx_lo"] == 0) and np.allclose(r["g"], 0.25)
+    m.check()
+    m.close()
+
+
+def test_tc_full_size_cluster_sampled(oracle_mod):
+    """The precision workload at full size (N = Q = 1e6, d = 16) on the tensor cores,
+    checked on 400 sampled queries against the FP64 oracle."""
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    p = W.cluster_d16()
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, precision="tc_tf32")
+    r = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
+    fb = m.last_fallback()
+    m.check()
+    m.close()
+    assert fb <= p.nq // 100          # the pruning settles at least 99 % of the queries
+    idx = np.sort(np.random.default_rng(21).choice(p.nq, 400, replace=False))
+    ps = W.Problem("c", p.X, p.y, p.Q[idx], p.M, p.norm, None, None)
+    orc = oracle_mod.evaluate(p.X, p.y, ps.Q, p.M, p.norm)
+    _check_exact(ps, {k: v[idx] for k, v in r.items()}, orc, "tc full cluster", fb)

@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--queries", type=int, default=0,
+                    help="use only the first N queries of a single-set workload (small profiling cases)")
     return ap.parse_args()
 
 
@@ -310,6 +312,8 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
     """fit + eval (+ M_est) (+ backward) of each problem per step."""
     from paper_2606_04670_b300 import lipfit as L
     torch, args = ctx.torch, ctx.args
+    if args.queries > 0:
+        problems = [p.sub_queries(args.queries) for p in problems]
     runs = []
     for p in problems:
         for prec in precisions:

@@ -294,14 +294,18 @@ LIP_API void lip_batch_free(lip_batch b);
  *                (0 keeps the current value).  Ignored by the generic kernel.
  *   splits       number of slices of the data scanned by separate thread blocks and
  *                merged afterwards; 0 = chosen per call to fill the GPU in whole waves.
+ *   variant      scan kernel variant: 0 holds the default number of queries per thread,
+ *                1 half as many (more resident warps); -1 keeps the current one.
+ *                Ignored by the generic kernel.  For LIP_TC_TF32 handles: 0 runs the
+ *                tensor-core epilogue on 16 warps, 1 on 8.
  * LIP_ERR_ARG for other values. */
-LIP_API lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits);
+LIP_API lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits, int32_t variant);
 
 /* Current launch shape: tile_groups, the configured splits (0 = automatic), the splits
- * used by the last lip_eval, and the queries held per thread by the scan kernel.  Any
- * output pointer may be NULL. */
+ * used by the last lip_eval, the queries held per thread by the scan kernel and the
+ * variant.  Any output pointer may be NULL. */
 LIP_API lip_status lip_get_tuning(lip_handle h, int32_t* tile_groups, int32_t* splits,
-                                  int32_t* last_splits, int32_t* queries_per_thread);
+                                  int32_t* last_splits, int32_t* queries_per_thread, int32_t* variant);
 
 /* ---------------------------------------------------------------- measurement */
 

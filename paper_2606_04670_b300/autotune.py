@@ -5,8 +5,9 @@ equality), so the shape is chosen purely by measured time: every candidate is ti
 with CUDA events on the launching stream, taking the median of several runs after a
 warm-up, and the fastest is kept.
 
-* ``tune_eval(model, Q)`` sweeps the shared-memory tile (tile_groups) and the number of
-  data splits of one data set, applies the best with ``lip_set_tuning`` and returns it.
+* ``tune_eval(model, Q)`` sweeps the scan kernel variant (queries per thread), the
+  shared-memory tile (tile_groups) and the number of data splits of one data set,
+  applies the best with ``lip_set_tuning`` and returns it.
 * ``tune_batch(sets)`` sweeps the batch options (default tile, work items per resident
   block, persistent-grid waves) and returns the best ``lip_batch_options`` as a dict.
 
@@ -69,24 +70,26 @@ def _time(fn, reps: int = 3, warm: int = 1) -> float:
 
 
 def tune_eval(model, Q, tiles: Iterable[int] = (8, 16, 32, 64), splits: Iterable[int] = (0, 1, 2, 3, 4, 6, 8, 12, 16),
-              cache: Optional[Dict] = None, reps: int = 3) -> Dict:
-    """Time lip_eval on `model` for every (tile_groups, splits) and apply the fastest."""
+              variants: Iterable[int] = (0, 1), cache: Optional[Dict] = None, reps: int = 3) -> Dict:
+    """Time lip_eval on `model` for every (variant, tile_groups, splits); apply the fastest."""
     key = eval_key(model, Q.shape[0])
     if cache is not None and key in cache:
         best = cache[key]
-        model.set_tuning(best["tile_groups"], best["splits"])
+        model.set_tuning(best["tile_groups"], best["splits"], best.get("variant", 0))
         return dict(best, cached=True)
     results = []
-    for tg in tiles:
-        for sp in splits:
-            model.set_tuning(tg, sp)
-            ms = _time(lambda: model.eval(Q, need=("g", "idx_up", "idx_lo")), reps=reps)
-            results.append({"tile_groups": tg, "splits": sp, "ms": ms,
-                            "splits_used": model.tuning()["last_splits"]})
+    for v in variants:
+        for tg in tiles:
+            for sp in splits:
+                model.set_tuning(tg, sp, v)
+                ms = _time(lambda: model.eval(Q, need=("g", "idx_up", "idx_lo")), reps=reps)
+                results.append({"variant": model.tuning()["variant"], "tile_groups": tg, "splits": sp, "ms": ms,
+                                "splits_used": model.tuning()["last_splits"]})
     best = min(results, key=lambda r: r["ms"])
-    model.set_tuning(best["tile_groups"], best["splits"])
-    rec = {"tile_groups": best["tile_groups"], "splits": best["splits"], "ms": best["ms"],
-           "default_ms": next(r["ms"] for r in results if r["tile_groups"] == 32 and r["splits"] == 0),
+    model.set_tuning(best["tile_groups"], best["splits"], best["variant"])
+    rec = {"variant": best["variant"], "tile_groups": best["tile_groups"], "splits": best["splits"], "ms": best["ms"],
+           "default_ms": next((r["ms"] for r in results
+                               if r["tile_groups"] == 32 and r["splits"] == 0 and r["variant"] == 0), None),
            "candidates": len(results)}
     if cache is not None:
         cache[key] = rec

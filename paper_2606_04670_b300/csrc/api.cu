@@ -119,12 +119,14 @@ struct lip_model {
     int tile_groups = 32;             // groups per shared-memory tile (8, 16, 32 or 64)
     int splits = 0;                   // 0 = automatic
     int last_splits = 0;
+    int variant = 0;
     Scratch partial, est, bwd, io;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
     cudaEvent_t ev_scan0 = nullptr, ev_scan1 = nullptr;   // caller's timing events
     // tensor-core form (LIP_TC_TF32)
     bool tc = false, tc_dirty = true;
+    int tc_variant = 0;                // 0: 16 epilogue warps, 1: 8
     int64_t tc_ntiles_cap = 0;
     char* tc_btiles = nullptr;
     double* tc_stats = nullptr;        // [D_MAX] sums of the scaled coordinates
@@ -457,7 +459,7 @@ lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, v
     }
     const int64_t nqt = ceil_div(nq, 128);
     const size_t a_b = round_up((int64_t)(nqt * tc_a_bytes_for(d)), 256), eps_b = round_up(nq * 8, 256),
-                 rec_b = round_up((int64_t)(nq * 4 * tc_rec_bytes()), 256), list_b = round_up(nq * 4 + 4, 256);
+                 rec_b = round_up((int64_t)(nq * tc_rec_bytes()), 256), list_b = round_up(nq * 4 + 4, 256);
     LIP_TRY(h->tc_q.ensure(a_b + eps_b + rec_b + list_b, "tensor-core query scratch"));
     char* base = static_cast<char*>(h->tc_q.p);
     int* fb_list = reinterpret_cast<int*>(base + a_b + eps_b + rec_b);
@@ -466,7 +468,8 @@ lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, v
     CUDA_TRY(tc_eval_launch(static_cast<const float*>(Q), nq, d, scale, h->tc_stats, h->N, h->tc_maxbits, h->tc_btiles,
                             ntiles, base, reinterpret_cast<float2*>(base + a_b), base + a_b + eps_b, h->w, h->M,
                             static_cast<const float*>(h->X0), static_cast<const float*>(h->y0), static_cast<float*>(g),
-                            static_cast<float*>(lo), static_cast<float*>(hi), iu, il, fb_count, fb_list, h->status, st));
+                            static_cast<float*>(lo), static_cast<float*>(hi), iu, il, fb_count, fb_list, h->status,
+                            h->tc_variant, st));
     count_launches(3);
     if (h->ev_scan1) CUDA_TRY(cudaEventRecord(h->ev_scan1, st));
     int nfb = 0;
@@ -759,14 +762,23 @@ lip_status lip_check(lip_handle h, void* stream) {
     return LIP_OK;
 }
 
-lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits) {
+lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits, int32_t variant) {
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
     if (tile_groups != 0 && tile_groups != 8 && tile_groups != 16 && tile_groups != 32 && tile_groups != 64)
         return fail(LIP_ERR_ARG, "tile_groups = %d is not 0, 8, 16, 32 or 64", tile_groups);
     if (splits < 0 || splits > 4096) return fail(LIP_ERR_ARG, "splits = %d is outside [0, 4096]", splits);
+    if (variant < -1 || variant >= SCAN_VARIANTS) return fail(LIP_ERR_ARG, "variant = %d is not -1, 0 or 1", variant);
     DeviceGuard gd(h->device);
     if (tile_groups) h->tile_groups = tile_groups;
     h->splits = splits;
+    if (variant >= 0 && h->tc) h->tc_variant = variant;
+    if (variant >= 0 && h->exact) {
+        const ScanKernelInfo k = scan_exact_info(h->norm, h->C, h->d - h->C, variant);
+        if (k.launch) {
+            h->kinfo = k;
+            h->variant = variant;
+        }
+    }
     if (h->exact) {
         const size_t smem = (size_t)SCAN_STAGES * h->tile_groups * h->nch * 16;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_blocks, h->kinfo.kernel, SCAN_THREADS, smem) !=
@@ -779,8 +791,9 @@ lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits) {
 }
 
 lip_status lip_get_tuning(lip_handle h, int32_t* tile_groups, int32_t* splits, int32_t* last_splits,
-                          int32_t* queries_per_thread) {
+                          int32_t* queries_per_thread, int32_t* variant) {
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (variant) *variant = h->tc ? h->tc_variant : h->variant;
     if (tile_groups) *tile_groups = h->tile_groups;
     if (splits) *splits = h->splits;
     if (last_splits) *last_splits = h->last_splits;

@@ -551,6 +551,14 @@ namespace lip {
 // the duplicated query coordinates).
 __host__ __device__ constexpr int rows_for_dim(int D) { return D <= 4 ? 8 : (D <= 10 ? 4 : 2); }
 
+// Launch variants of the exact kernel (chosen by lip_set_tuning / the autotuner):
+// variant 0 holds rows_for_dim(D) queries per thread, variant 1 half as many (fewer
+// registers, more resident warps, more shared-memory broadcasts per pair).
+constexpr int SCAN_VARIANTS = 2;
+__host__ __device__ constexpr int rows_for_variant(int D, int v) {
+    return v == 0 ? rows_for_dim(D) : (rows_for_dim(D) / 2 > 0 ? rows_for_dim(D) / 2 : 1);
+}
+
 // Exact instantiations: every (C, U) with 1 <= C + U <= 10, and unconstrained D up to 16.
 __host__ __device__ constexpr bool exact_shape_available(int C, int U) {
     return (C + U >= 1 && C + U <= 10 && C >= 0 && U >= 0) || (C == 0 && U >= 11 && U <= D_MAX);
@@ -565,7 +573,7 @@ struct ScanKernelInfo {
     int nch = 0;                    // channels per group
 };
 
-ScanKernelInfo scan_exact_info(int norm, int C, int U);
+ScanKernelInfo scan_exact_info(int norm, int C, int U, int variant = 0);
 ScanKernelInfo scan_generic_info(int elem_bytes, int norm, int dl);
 
 }  // namespace lip

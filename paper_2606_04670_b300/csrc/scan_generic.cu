@@ -46,15 +46,15 @@ ScanKernelInfo scan_generic_info(int elem_bytes, int norm, int dl) {
     return elem_bytes == 8 ? gen_by_norm<double>(norm, dl) : gen_by_norm<float>(norm, dl);
 }
 
-ScanKernelInfo scan_exact_info_l1(int C, int U);
-ScanKernelInfo scan_exact_info_l2(int C, int U);
-ScanKernelInfo scan_exact_info_linf(int C, int U);
+ScanKernelInfo scan_exact_info_l1(int C, int U, int v);
+ScanKernelInfo scan_exact_info_l2(int C, int U, int v);
+ScanKernelInfo scan_exact_info_linf(int C, int U, int v);
 
-ScanKernelInfo scan_exact_info(int norm, int C, int U) {
+ScanKernelInfo scan_exact_info(int norm, int C, int U, int variant) {
     switch (norm) {
-        case LIP_L1: return scan_exact_info_l1(C, U);
-        case LIP_L2: return scan_exact_info_l2(C, U);
-        case LIP_LINF: return scan_exact_info_linf(C, U);
+        case LIP_L1: return scan_exact_info_l1(C, U, variant);
+        case LIP_L2: return scan_exact_info_l2(C, U, variant);
+        case LIP_LINF: return scan_exact_info_linf(C, U, variant);
         default: return {};
     }
 }

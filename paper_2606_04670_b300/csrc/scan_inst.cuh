@@ -6,9 +6,9 @@
 
 namespace lip {
 
-template <int NORM, int C, int U>
+template <int NORM, int C, int U, int V>
 cudaError_t launch_scan_exact(const ScanParams& P, int gx, int gy, cudaStream_t st) {
-    constexpr int R = rows_for_dim(C + U);
+    constexpr int R = rows_for_variant(C + U, V);
     constexpr int NCH = ExactShape<NORM, C, U>::NCH;
     auto kern = scan_exact_kernel<NORM, C, U, R>;
     const size_t smem = (size_t)SCAN_STAGES * P.tile_groups * NCH * sizeof(float4);
@@ -21,16 +21,21 @@ cudaError_t launch_scan_exact(const ScanParams& P, int gx, int gy, cudaStream_t 
 
 template <int NORM>
 struct ExactTable {
-    ScanKernelInfo tab[D_MAX + 1][D_MAX + 1];
+    ScanKernelInfo tab[D_MAX + 1][D_MAX + 1][SCAN_VARIANTS];
+    template <int C, int U, int V>
+    void fill_variant() {
+        ScanKernelInfo& e = tab[C][U][V];
+        e.launch = &launch_scan_exact<NORM, C, U, V>;
+        e.kernel = reinterpret_cast<const void*>(&scan_exact_kernel<NORM, C, U, rows_for_variant(C + U, V)>);
+        e.rows = rows_for_variant(C + U, V);
+        e.nch = ExactShape<NORM, C, U>::NCH;
+    }
     template <int K>
     void fill_one() {
         constexpr int C = K / (D_MAX + 1), U = K % (D_MAX + 1);
         if constexpr (exact_shape_available(C, U)) {
-            ScanKernelInfo& e = tab[C][U];
-            e.launch = &launch_scan_exact<NORM, C, U>;
-            e.kernel = reinterpret_cast<const void*>(&scan_exact_kernel<NORM, C, U, rows_for_dim(C + U)>);
-            e.rows = rows_for_dim(C + U);
-            e.nch = ExactShape<NORM, C, U>::NCH;
+            fill_variant<C, U, 0>();
+            fill_variant<C, U, 1>();
         }
     }
     template <int... K>

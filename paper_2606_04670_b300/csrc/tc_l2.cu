@@ -18,16 +18,20 @@
 //   delta_c = 1.001 eps rsqrt(max(min_chunk s~, eps)) + 2^-19 (max|y| + |q^| + R).
 // A chunk can hold the exact argmin only if min_chunk v~ - delta_c <= U, where
 // U = min over chunks of (min_chunk v~ + delta_c) is an upper bound of H_up; the same
-// holds mirrored for H_lo.  Candidate chunks are kept per query (8 per half row), then
-// rescreened exactly in FP64 from the caller's data; a query whose list overflows is
-// recomputed by the plain FP32 scan.
+// holds mirrored for H_lo.  Candidate chunks are kept per query (8 per list, one list
+// per column slice), then rescreened from the caller's data: one warp per query
+// evaluates each candidate chunk in FP32 and re-evaluates in FP64 only the points within
+// the FP32 error bound of the chunk's extremum, so the result is the FP64 argmin/argmax.
+// A query whose list overflows is recomputed by the plain FP32 scan.
 //
-// Kernel: one CTA per 128-query tile, 10 warps.  Warp 0 streams 256-point data tiles
+// Kernel: one CTA per 128-query tile, 18 warps.  Warp 0 streams 256-point data tiles
 // (pre-tiled hi/lo operands and y, one 1-D bulk copy each) into a 3-stage ring; warp 1
 // owns TMEM (512 columns = two 128 x 256 FP32 accumulators) and issues the MMAs; warps
-// 2..9 are the epilogue: each reads one 32-lane quarter of the accumulator rows (one
-// query per thread) over half of the columns with tcgen05.ld, clamps, takes sqrt, forms
-// y +- sqrt and keeps the chunk extrema and candidate lists.  Every wait is bounded.
+// 2..17 are the epilogue: each reads one 32-lane quarter of the accumulator rows (one
+// query per thread) over a quarter of the columns with tcgen05.ld, takes sqrt(|s~|),
+// forms y +- sqrt and keeps the chunk extrema and candidate lists.  Every wait is bounded.
+// (sqrt(|s~|) needs no clamp: s~ < 0 only when s < eps, and then both roots are below
+// sqrt(eps), which delta already covers.)
 #include <cstdio>
 
 #include "launch.h"
@@ -38,10 +42,13 @@ constexpr int TC_M = 128;
 constexpr int TC_N = 256;
 constexpr int TC_STAGES = 3;
 constexpr int TC_CAP = 8;
-constexpr int TC_THREADS = 320;
+// Epilogue warps: 4 lane quarters x PARTS column slices (PARTS = 2 or 4, a launch variant);
+// each (query, bound) keeps one candidate list per column slice.
+constexpr int TC_MAX_PARTS = 4;
+__host__ __device__ constexpr int tc_threads(int parts) { return 32 * (2 + 4 * parts); }
 constexpr float TC_C_EPS = 2.0e-5f;
 
-struct TcRec {      // candidate list of one (query, bound, half)
+struct TcRec {      // candidate list of one (query, bound, column quarter)
     float U;        // upper bound of H_up (bound 0) or lower bound of H_lo (bound 1)
     int n;          // entries, -1 = overflow
     int id[TC_CAP];
@@ -208,6 +215,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Two adjacent 32-column loads issued back to back, then one wait.
+__device__ __forceinline__ void tmem_ld32x2(uint32_t taddr, float (&v)[2][32]) {
+    uint32_t r[64];
+#define LIP_TMEM_LD32(OFF, BASE)                                                                                   \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"    \
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                         \
+                 : "=r"(r[BASE + 0]), "=r"(r[BASE + 1]), "=r"(r[BASE + 2]), "=r"(r[BASE + 3]), "=r"(r[BASE + 4]),    \
+                   "=r"(r[BASE + 5]), "=r"(r[BASE + 6]), "=r"(r[BASE + 7]), "=r"(r[BASE + 8]), "=r"(r[BASE + 9]),    \
+                   "=r"(r[BASE + 10]), "=r"(r[BASE + 11]), "=r"(r[BASE + 12]), "=r"(r[BASE + 13]),                  \
+                   "=r"(r[BASE + 14]), "=r"(r[BASE + 15]), "=r"(r[BASE + 16]), "=r"(r[BASE + 17]),                  \
+                   "=r"(r[BASE + 18]), "=r"(r[BASE + 19]), "=r"(r[BASE + 20]), "=r"(r[BASE + 21]),                  \
+                   "=r"(r[BASE + 22]), "=r"(r[BASE + 23]), "=r"(r[BASE + 24]), "=r"(r[BASE + 25]),                  \
+                   "=r"(r[BASE + 26]), "=r"(r[BASE + 27]), "=r"(r[BASE + 28]), "=r"(r[BASE + 29]),                  \
+                   "=r"(r[BASE + 30]), "=r"(r[BASE + 31])                                                            \
+                 : "r"(taddr + (OFF)))
+    LIP_TMEM_LD32(0, 0);
+    LIP_TMEM_LD32(32, 32);
+#undef LIP_TMEM_LD32
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        v[0][j] = __uint_as_float(r[j]);
+        v[1][j] = __uint_as_float(r[32 + j]);
+    }
+}
+
 __device__ __forceinline__ float rsqrt_approx(float x) {
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -246,8 +279,9 @@ __device__ __forceinline__ void tc_append(TcRec* R, int& n, int id, float L, flo
     ++n;
 }
 
-template <int K>
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_scan_kernel(const TcScanParams P) {
+template <int K, int PARTS>
+__global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcScanParams P) {
+    constexpr int EPI_WARPS = 4 * PARTS;
     constexpr int TILE_BYTES = tc_tile_bytes(K);
     constexpr int A_BYTES = tc_a_bytes(K);
     constexpr int KS = K / 8;
@@ -265,11 +299,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_scan_kernel(const TcScanPara
         mbar_init(&a_full, 1);
         for (int s = 0; s < TC_STAGES; ++s) {
             mbar_init(&b_full[s], 1);
-            mbar_init(&b_empty[s], 1 + 8);                  // MMA commit + 8 epilogue warps
+            mbar_init(&b_empty[s], 1 + EPI_WARPS);         // MMA commit + epilogue warps
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 8);
+            mbar_init(&acc_empty[b], EPI_WARPS);
         }
         fence_mbar_init();
     }
@@ -336,15 +370,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_scan_kernel(const TcScanPara
             if (t > 0) mbar_wait_bounded(&acc_full[(t - 1) & 1], (uint32_t)(((t - 1) / 2) & 1), nullptr);
         }
     } else {
-        // ------------------------------------------------ epilogue (warps 2..9)
-        const int quarter = warp % 4, half = (warp - 2) / 4;
+        // ------------------------------------------------ epilogue (warps 2 .. 2 + EPI_WARPS)
+        const int quarter = warp % 4, part = (warp - 2) / 4;
         const int64_t qi = qt * TC_M + quarter * 32 + lane;
         const bool valid = qi < P.nq;
         float2 e2 = valid ? P.eps[qi] : make_float2(1.f, 1.f);
         // a zero bound (M = 0) must not turn eps * rsqrt(0) into NaN
         const float eps = fmaxf(e2.x, 1e-30f), epsv = e2.y;
-        TcRec* Ru = P.rec + (valid ? ((qi * 2 + 0) * 2 + half) : 0);
-        TcRec* Rl = P.rec + (valid ? ((qi * 2 + 1) * 2 + half) : 0);
+        TcRec* Ru = P.rec + (valid ? ((qi * 2 + 0) * TC_MAX_PARTS + part) : 0);
+        TcRec* Rl = P.rec + (valid ? ((qi * 2 + 1) * TC_MAX_PARTS + part) : 0);
         const float INF = __int_as_float(0x7f800000);
         float U = INF, Bl = -INF;
         int nu = 0, nl = 0;
@@ -355,28 +389,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_scan_kernel(const TcScanPara
             if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / TC_STAGES) & 1), P.err)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const float* ys = reinterpret_cast<const float*>(sB + (size_t)s * TILE_BYTES + 2 * TC_N * K * 4);
+            // two 32-column chunks per TMEM wait: both loads are in flight together
 #pragma unroll 1
-            for (int j = 0; j < 4; ++j) {
-                const int col = half * 128 + j * 32;
-                float sv[32];
-                tmem_ld32(tb + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * TC_N + col, sv);
-                float cs = INF, cu = INF, cl = -INF;
+            for (int j = 0; j < TC_N / 32 / PARTS; j += 2) {
+                const int col0 = part * (TC_N / PARTS) + j * 32;
+                float sv[2][32];
+                tmem_ld32x2(tb + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * TC_N + col0, sv);
 #pragma unroll
-                for (int e = 0; e < 32; e += 2) {
-                    const float2 yv = *reinterpret_cast<const float2*>(ys + col + e);
-                    cs = min3f(cs, sv[e], sv[e + 1]);
-                    const float2 rt = make_float2(sqrt_approx(fmaxf(sv[e], 0.f)), sqrt_approx(fmaxf(sv[e + 1], 0.f)));
-                    const float2 vu = add2(yv, rt), vl = sub2(yv, rt);
-                    cu = min3f(cu, vu.x, vu.y);
-                    cl = max3f(cl, vl.x, vl.y);
-                }
-                if (valid) {
-                    const float dlt = 1.001f * eps * rsqrt_approx(fmaxf(cs, eps)) + epsv;
-                    const int chunk = (int)(t * 8 + half * 4 + j);
-                    U = fminf(U, cu + dlt);
-                    if (cu - dlt <= U) tc_append(Ru, nu, chunk, cu - dlt, U, true);
-                    Bl = fmaxf(Bl, cl - dlt);
-                    if (cl + dlt >= Bl) tc_append(Rl, nl, chunk, cl + dlt, Bl, false);
+                for (int h = 0; h < 2; ++h) {
+                    const int col = col0 + h * 32;
+                    // four interleaved partial extrema per chunk keep the dependent chains short
+                    float cs[4], cu[4], cl[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) { cs[a] = INF; cu[a] = INF; cl[a] = -INF; }
+#pragma unroll
+                    for (int e = 0; e < 32; e += 4) {
+                        const int a = (e / 4) % 4;
+                        const float4 y4 = *reinterpret_cast<const float4*>(ys + col + e);
+                        cs[a] = min3f(min3f(cs[a], sv[h][e], sv[h][e + 1]), sv[h][e + 2], sv[h][e + 3]);
+                        const float2 r0 = make_float2(sqrt_approx(fabsf(sv[h][e])), sqrt_approx(fabsf(sv[h][e + 1])));
+                        const float2 r1 = make_float2(sqrt_approx(fabsf(sv[h][e + 2])), sqrt_approx(fabsf(sv[h][e + 3])));
+                        const float2 y0 = make_float2(y4.x, y4.y), y1 = make_float2(y4.z, y4.w);
+                        const float2 u0 = add2(y0, r0), u1 = add2(y1, r1), l0 = sub2(y0, r0), l1 = sub2(y1, r1);
+                        cu[a] = min3f(min3f(cu[a], u0.x, u0.y), u1.x, u1.y);
+                        cl[a] = max3f(max3f(cl[a], l0.x, l0.y), l1.x, l1.y);
+                    }
+                    const float csm = min2f(min3f(cs[0], cs[1], cs[2]), cs[3]);
+                    const float cum = min2f(min3f(cu[0], cu[1], cu[2]), cu[3]);
+                    const float clm = max2f(max3f(cl[0], cl[1], cl[2]), cl[3]);
+                    if (valid) {
+                        const float dlt = 1.001f * eps * rsqrt_approx(fmaxf(csm, eps)) + epsv;
+                        const int chunk = (int)(t * (TC_N / 32) + col / 32);
+                        U = fminf(U, cum + dlt);
+                        if (cum - dlt <= U) tc_append(Ru, nu, chunk, cum - dlt, U, true);
+                        Bl = fmaxf(Bl, clm - dlt);
+                        if (clm + dlt >= Bl) tc_append(Rl, nl, chunk, clm + dlt, Bl, false);
+                    }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -404,6 +452,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_scan_kernel(const TcScanPara
 // --------------------------------------------------------------- exact rescreen
 
 struct TcRescreenParams {
+    int parts;              // candidate lists per (query, bound) that the scan filled
     const float* Q;
     int64_t nq;
     int d;
@@ -428,40 +477,95 @@ __device__ __forceinline__ double tc_dist64(const TcRescreenParams& P, const flo
     return sqrt(acc);
 }
 
+// (value, index) order of a bound: smaller value first for H_up (side 0), larger for
+// H_lo (side 1), then the lower index.
+__device__ __forceinline__ bool tc_better(int side, double v, int k, double bv, int bk) {
+    if (k < 0) return false;
+    if (bk < 0) return true;
+    if (v != bv) return side == 0 ? v < bv : v > bv;
+    return k < bk;
+}
+
+// One warp per query.  For each bound, every surviving candidate chunk is evaluated by
+// the 32 lanes (one point each, coalesced rows) in FP32; a point can only be the chunk's
+// extremum if its FP32 value is within twice the FP32 error bound of the chunk's FP32
+// extremum, and only those points are re-evaluated in FP64.  FP32 error of
+// y +- M |diag(w)(q - x)|_2 with correctly rounded sqrt: at most (d + 10) 2^-24 (r + |y|).
 __global__ void tc_rescreen_kernel(const TcRescreenParams P) {
-    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t qi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
     if (qi >= P.nq) return;
     const float* q = P.Q + qi * P.d;
     bool finite = true;
     for (int i = 0; i < P.d; ++i) finite = finite && isfinite(q[i]);
-    const TcRec* R = P.rec + qi * 4;
-    if (finite && (R[0].n < 0 || R[1].n < 0 || R[2].n < 0 || R[3].n < 0)) {
-        P.fb_list[atomicAdd(P.fb_count, 1)] = (int)qi;
+    const TcRec* R = P.rec + qi * 2 * TC_MAX_PARTS;
+    bool over = false;
+    for (int b = 0; b < 2; ++b)
+        for (int h = 0; h < P.parts; ++h) over = over || R[b * TC_MAX_PARTS + h].n < 0;
+    if (finite && over) {
+        if (lane == 0) P.fb_list[atomicAdd(P.fb_count, 1)] = (int)qi;
         return;
     }
+    float qs[D_MAX], sc[D_MAX];
+#pragma unroll
+    for (int i = 0; i < D_MAX; ++i) {
+        qs[i] = i < P.d ? q[i] : 0.f;
+        sc[i] = i < P.d ? (float)(P.M * P.w[i]) : 0.f;
+    }
+    const float erel = (float)(P.d + 10) * 5.9604645e-8f;   // (d + 10) 2^-24
     double best[2] = {0.0, 0.0};
     int bidx[2] = {-1, -1};
     if (finite) {
         for (int b = 0; b < 2; ++b) {
-            const float bound = b == 0 ? fminf(R[b * 2].U, R[b * 2 + 1].U) : fmaxf(R[b * 2].U, R[b * 2 + 1].U);
-            for (int h = 0; h < 2; ++h) {
-                const TcRec& r = R[b * 2 + h];
+            float bound = R[b * TC_MAX_PARTS].U;
+            for (int h = 1; h < P.parts; ++h)
+                bound = b == 0 ? fminf(bound, R[b * TC_MAX_PARTS + h].U) : fmaxf(bound, R[b * TC_MAX_PARTS + h].U);
+            double bv = 0.0;
+            int bk = -1;
+            for (int h = 0; h < P.parts; ++h) {
+                const TcRec& r = R[b * TC_MAX_PARTS + h];
                 for (int e = 0; e < r.n; ++e) {
-                    if (b == 0 ? !(r.L[e] <= bound) : !(r.L[e] >= bound)) continue;
-                    const int64_t k0 = (int64_t)r.id[e] * 32;
-                    for (int p = 0; p < 32; ++p) {
-                        const int64_t k = k0 + p;
-                        if (k >= P.N) break;
+                    if (b == 0 ? !(r.L[e] <= bound) : !(r.L[e] >= bound)) continue;   // warp-uniform
+                    const int64_t k = (int64_t)r.id[e] * 32 + lane;
+                    const bool in = k < P.N;
+                    float v32 = b == 0 ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000), err = 0.f;
+                    if (in) {
+                        const float* x = P.X0 + k * P.d;
+                        float acc = 0.f;
+                        for (int i = 0; i < P.d; ++i) {
+                            const float t = (qs[i] - x[i]) * sc[i];
+                            acc = fmaf(t, t, acc);
+                        }
+                        const float rr = sqrtf(acc), yy = P.y0[k];
+                        v32 = b == 0 ? yy + rr : yy - rr;
+                        err = erel * (rr + fabsf(yy));
+                    }
+                    float ext = v32, emax = err;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const float o = __shfl_xor_sync(0xffffffffu, ext, off);
+                        ext = b == 0 ? fminf(ext, o) : fmaxf(ext, o);
+                        emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+                    }
+                    const bool cand = in && (b == 0 ? v32 <= ext + 2.f * emax : v32 >= ext - 2.f * emax);
+                    if (cand) {
                         const double dist = P.M * tc_dist64(P, q, P.X0 + k * P.d);
                         const double v = b == 0 ? (double)P.y0[k] + dist : (double)P.y0[k] - dist;
-                        const bool better = bidx[b] < 0 || (b == 0 ? v < best[b] : v > best[b]) ||
-                                            (v == best[b] && k < bidx[b]);
-                        if (better) { best[b] = v; bidx[b] = (int)k; }
+                        if (tc_better(b, v, (int)k, bv, bk)) { bv = v; bk = (int)k; }
                     }
                 }
             }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+                const int ok = __shfl_xor_sync(0xffffffffu, bk, off);
+                if (tc_better(b, ov, ok, bv, bk)) { bv = ov; bk = ok; }
+            }
+            best[b] = bv;
+            bidx[b] = bk;
         }
     }
+    if (lane != 0) return;
     double hi = best[0], lo = best[1];
     if (!finite || bidx[0] < 0 || bidx[1] < 0) {
         hi = lo = __longlong_as_double(0x7ff8000000000000ll);
@@ -498,7 +602,7 @@ __global__ void tc_scatter_kernel(const int* list, int n, const float* g, const 
 
 size_t tc_tile_bytes_for(int d) { return (size_t)tc_tile_bytes(tc_k_for_dim(d)); }
 size_t tc_a_bytes_for(int d) { return (size_t)tc_a_bytes(tc_k_for_dim(d)); }
-size_t tc_rec_bytes() { return sizeof(TcRec); }
+size_t tc_rec_bytes() { return sizeof(TcRec) * 2 * TC_MAX_PARTS; }   // candidate lists per query
 
 cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, const double* scale, double* stats,
                             unsigned* maxbits, char* tiles, int64_t ntiles, cudaStream_t st) {
@@ -522,14 +626,21 @@ cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, 
     return cudaGetLastError();
 }
 
-template <int K>
+template <int K, int PARTS>
 static cudaError_t launch_tc_scan_k(const TcScanParams& P, int64_t nqt, cudaStream_t st) {
     const size_t smem = (size_t)tc_a_bytes(K) + (size_t)TC_STAGES * tc_tile_bytes(K);
     static cudaError_t attr =
-        cudaFuncSetAttribute(tc_scan_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(tc_scan_kernel<K, PARTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return attr;
-    tc_scan_kernel<K><<<(unsigned)nqt, TC_THREADS, smem, st>>>(P);
+    tc_scan_kernel<K, PARTS><<<(unsigned)nqt, tc_threads(PARTS), smem, st>>>(P);
     return cudaGetLastError();
+}
+
+template <int PARTS>
+static cudaError_t launch_tc_scan_parts(int K, const TcScanParams& P, int64_t nqt, cudaStream_t st) {
+    if (K == 8) return launch_tc_scan_k<8, PARTS>(P, nqt, st);
+    if (K == 16) return launch_tc_scan_k<16, PARTS>(P, nqt, st);
+    return launch_tc_scan_k<24, PARTS>(P, nqt, st);
 }
 
 // Queries: build A, scan, rescreen.  Returns the fallback count through fb (device).
@@ -537,8 +648,9 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
                            const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float2* eps,
                            void* rec, const double* w, double M, const float* X0, const float* y0, float* g, float* lo,
                            float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, unsigned* err,
-                           cudaStream_t st) {
+                           int variant, cudaStream_t st) {
     const int K = tc_k_for_dim(d);
+    const int parts = variant == 1 ? 2 : 4;   // variant 0: 16 epilogue warps, 1: 8
     const int64_t nqt = (nq + TC_M - 1) / TC_M;
     TcQueryParams A{};
     A.Q = Q;
@@ -562,12 +674,11 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     S.ntiles = ntiles;
     S.rec = static_cast<TcRec*>(rec);
     S.err = err;
-    if (K == 8) e = launch_tc_scan_k<8>(S, nqt, st);
-    else if (K == 16) e = launch_tc_scan_k<16>(S, nqt, st);
-    else e = launch_tc_scan_k<24>(S, nqt, st);
+    e = parts == 2 ? launch_tc_scan_parts<2>(K, S, nqt, st) : launch_tc_scan_parts<4>(K, S, nqt, st);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(fb_count, 0, sizeof(int), st)) != cudaSuccess) return e;
     TcRescreenParams R{};
+    R.parts = parts;
     R.Q = Q;
     R.nq = nq;
     R.d = d;
@@ -584,7 +695,7 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     R.idx_lo = il;
     R.fb_count = fb_count;
     R.fb_list = fb_list;
-    tc_rescreen_kernel<<<(unsigned)((nq + 127) / 128), 128, 0, st>>>(R);
+    tc_rescreen_kernel<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(R);
     return cudaGetLastError();
 }
 

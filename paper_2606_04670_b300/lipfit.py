@@ -78,8 +78,8 @@ def _load():
         "lip_estimate_M": [H, ctypes.POINTER(f64), ctypes.POINTER(i64), ctypes.POINTER(i64), P],
         "lip_backward": [H, P, i64, P, P, P, P, P, P, P],
         "lip_check": [H, P],
-        "lip_set_tuning": [H, i32, i32],
-        "lip_get_tuning": [H, P, P, P, P],
+        "lip_set_tuning": [H, i32, i32, i32],
+        "lip_get_tuning": [H, P, P, P, P, P],
         "lip_set_timing_events": [H, P, P],
         "lip_estimate_M_noalloc": [P, P, i64, i32, i32, P, P, P],
         "lip_batch_create": [ctypes.POINTER(lip_batch_set), i32, ctypes.POINTER(lip_batch_options), P,
@@ -209,12 +209,12 @@ def lip_backward(h, Q_ptr, nq, idx_up, idx_lo, grad_g, grad_Q, grad_y, grad_M, s
     return _lib.lip_backward(h, Q_ptr, nq, idx_up, idx_lo, grad_g, grad_Q, grad_y, grad_M, stream)
 
 
-def lip_set_tuning(h, tile_groups, splits):
-    return _lib.lip_set_tuning(h, tile_groups, splits)
+def lip_set_tuning(h, tile_groups, splits, variant=-1):
+    return _lib.lip_set_tuning(h, tile_groups, splits, variant)
 
 
 def lip_get_tuning(h):
-    v = [ctypes.c_int32() for _ in range(4)]
+    v = [ctypes.c_int32() for _ in range(5)]
     s = _lib.lip_get_tuning(h, *[ctypes.byref(x) for x in v])
     return s, tuple(x.value for x in v)
 
@@ -430,8 +430,8 @@ class LipFit:
     def last_fallback(self) -> int:
         return lip_last_fallback(self.h)
 
-    def set_tuning(self, tile_groups: int = 0, splits: int = 0):
-        _check(_lib.lip_set_tuning(self.h, int(tile_groups), int(splits)), "lip_set_tuning")
+    def set_tuning(self, tile_groups: int = 0, splits: int = 0, variant: int = -1):
+        _check(_lib.lip_set_tuning(self.h, int(tile_groups), int(splits), int(variant)), "lip_set_tuning")
 
     def set_timing_events(self, ev_before=None, ev_after=None):
         """torch.cuda.Event pair recorded around the scan kernel of every eval (None: off)."""
@@ -443,9 +443,9 @@ class LipFit:
         _check(_lib.lip_set_timing_events(self.h, a, b), "lip_set_timing_events")
 
     def tuning(self):
-        s, (tg, sp, last, rows) = lip_get_tuning(self.h)
+        s, (tg, sp, last, rows, var) = lip_get_tuning(self.h)
         _check(s, "lip_get_tuning")
-        return {"tile_groups": tg, "splits": sp, "last_splits": last, "queries_per_thread": rows}
+        return {"tile_groups": tg, "splits": sp, "last_splits": last, "queries_per_thread": rows, "variant": var}
 
     def close(self):
         if self.h:

@@ -19,15 +19,15 @@ def diam(X, Q, norm, w=None):
     return {1: v.sum(), 2: float(np.sqrt((v * v).sum())), 3: v.max()}[norm]
 
 
-def gpu_eval(p, precision="fp32", Q=None, splits=None, tile_groups=None):
+def gpu_eval(p, precision="fp32", Q=None, splits=None, tile_groups=None, variant=-1):
     import torch
 
     from paper_2606_04670_b300.lipfit import LipFit
     dt = torch.float64 if precision == "fp64" else torch.float32
     m = LipFit(torch.as_tensor(p.X).to("cuda", dt), torch.as_tensor(p.y).to("cuda", dt), p.M,
                norm=p.norm, mon=p.mon, w=p.w, precision=precision)
-    if splits is not None or tile_groups is not None:
-        m.set_tuning(tile_groups or 0, splits or 0)
+    if splits is not None or tile_groups is not None or variant >= 0:
+        m.set_tuning(tile_groups or 0, splits or 0, variant)
     Qd = torch.as_tensor(p.Q if Q is None else Q).to("cuda", dt)
     r = m.eval(Qd)
     torch.cuda.synchronize()

@@ -62,7 +62,7 @@ def test_null_handle_calls():
     assert L.lip_estimate_M(None)[0] == L.LIP_ERR_ARG
     assert L.lip_backward(None, None, 0, None, None, None, None, None, None) == L.LIP_ERR_ARG
     assert L.lip_check(None) == L.LIP_ERR_ARG
-    assert L.lip_set_tuning(None, 0, 0) == L.LIP_ERR_ARG
+    assert L.lip_set_tuning(None, 0, 0, 0) == L.LIP_ERR_ARG
     assert L.lip_get_tuning(None)[0] == L.LIP_ERR_ARG
     assert L.lip_set_timing_events(None, None, None) == L.LIP_ERR_ARG
     assert L.lip_size(None) == -1

@@ -18,7 +18,7 @@ def test_tune_eval_keeps_results_and_caches(tmp_path):
     ref = {k: v.cpu().numpy() for k, v in m.eval(Q).items()}
     cache = {}
     rec = AT.tune_eval(m, Q, tiles=(8, 32), splits=(0, 1, 4), cache=cache, reps=2)
-    assert not rec["cached"] and rec["ms"] <= rec["default_ms"] + 1e-9
+    assert not rec["cached"] and rec["ms"] <= rec["default_ms"] + 1e-9 and rec["candidates"] == 12
     assert m.tuning()["tile_groups"] == rec["tile_groups"]
     got = {k: v.cpu().numpy() for k, v in m.eval(Q).items()}
     for k in ref:

@@ -62,11 +62,11 @@ def test_workload_shapes(oracle_mod):
         compare(p, gpu_eval(p), orc, FP32_TOL, p.name)
 
 
-@pytest.mark.parametrize("splits,tile_groups", [(1, 8), (3, 16), (7, 32), (64, 64), (0, 8)])
-def test_launch_shape_does_not_change_results(splits, tile_groups):
+@pytest.mark.parametrize("splits,tile_groups,variant", [(1, 8, 0), (3, 16, 1), (7, 32, 1), (64, 64, 0), (0, 8, 1)])
+def test_launch_shape_does_not_change_results(splits, tile_groups, variant):
     p = W.monotone_d4(norm=W.NORM_L2, n_data=30_000, n_query=2_000)
     ref = gpu_eval(p)
-    got = gpu_eval(p, splits=splits, tile_groups=tile_groups)
+    got = gpu_eval(p, splits=splits, tile_groups=tile_groups, variant=variant)
     for k in ref:
         np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
 

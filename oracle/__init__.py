@@ -84,7 +84,9 @@ class Oracle:
         lib.oracle_estimate_M.argtypes = [P, P, i64, i32, i32, P, P, P, P, i32]
         lib.oracle_estimate_M_rows.argtypes = [P, P, i64, i32, i32, P, i64, i64, P, P, P]
         lib.oracle_grad.argtypes = [P, P, i64, i32, f64, i32, P, P, P, i64, P, P, P, P, P, P]
-        for fn in (lib.oracle_eval, lib.oracle_estimate_M, lib.oracle_estimate_M_rows, lib.oracle_grad):
+        lib.oracle_eval_k.argtypes = [P, P, i64, i32, f64, i32, P, P, P, i64, i32, P, P, P, P, P, P, i32]
+        for fn in (lib.oracle_eval, lib.oracle_estimate_M, lib.oracle_estimate_M_rows, lib.oracle_grad,
+                   lib.oracle_eval_k):
             fn.restype = ctypes.c_int
         self.lib = lib
 
@@ -104,6 +106,24 @@ class Oracle:
                                   nthreads or default_threads())
         if rc != 0:
             raise ValueError("oracle_eval: bad arguments")
+        return EvalResult(idx_up=iu, idx_lo=il, **out)
+
+    def evaluate_k(self, X, y, Q, M: float, k: int, wk, norm: int = NORM_L2, mon=None, w=None,
+                   nthreads: Optional[int] = None) -> EvalResult:
+        """k > 1 neighbours: weighted sums of the k best upper / lower bounds (Sec. 5)."""
+        X, y, Q, w = _f64(X), _f64(y), _f64(Q), _f64(w)
+        wk = _f64(wk)
+        N, d = X.shape
+        nq = Q.shape[0]
+        mon = _mon(mon, d)
+        out = {key: np.empty(nq) for key in ("hi", "lo", "g")}
+        iu = np.empty((nq, k), np.int64)
+        il = np.empty((nq, k), np.int64)
+        rc = self.lib.oracle_eval_k(_ptr(X), _ptr(y), N, d, float(M), int(norm), _ptr(mon), _ptr(w), _ptr(Q), nq,
+                                    int(k), _ptr(wk), _ptr(out["hi"]), _ptr(out["lo"]), _ptr(out["g"]), _ptr(iu),
+                                    _ptr(il), nthreads or default_threads())
+        if rc != 0:
+            raise ValueError("oracle_eval_k: bad arguments")
         return EvalResult(idx_up=iu, idx_lo=il, **out)
 
     def estimate_M(self, X, y, norm: int = NORM_L2, w=None, nthreads: Optional[int] = None):
@@ -163,6 +183,10 @@ def evaluate(*a, **k) -> EvalResult:
 
 def estimate_M(*a, **k):
     return default().estimate_M(*a, **k)
+
+
+def evaluate_k(*a, **k):
+    return default().evaluate_k(*a, **k)
 
 
 def estimate_M_rows(*a, **k):

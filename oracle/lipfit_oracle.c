@@ -30,6 +30,9 @@
  * plays no role in it).  A pair with dist = 0 and equal y is skipped; dist = 0
  * with unequal y gives +inf.
  *
+ * k > 1 neighbours (Sec. 5, extra features): the weighted sums of the k smallest upper
+ * bounds and of the k largest lower bounds replace the minimum and the maximum.
+ *
  * Gradient of g (piecewise linear, differentiable almost everywhere, Table 1):
  *   dg/dq  = M/2 ( grad_q dist_up(q, x^u) - grad_q dist_lo(q, x^l) )
  *   dg/dy^k = 1/2 sum_q gbar_q ([u_q = k] + [l_q = k])
@@ -285,5 +288,71 @@ int oracle_grad(const double* X, const double* y, int64_t N, int d, double M, in
         gm += 0.5 * gb * (oracle_dist(q, xu, d, norm, mon, w, +1) - oracle_dist(q, xl, d, norm, mon, w, -1));
     }
     if (grad_M) *grad_M = gm;
+    return 0;
+}
+
+/* ---------------------------------------------- k > 1 neighbours (Sec. 5, extra features) */
+/* H_up^k(x) = sum_j wk_j v_(j), v_(1) <= v_(2) <= ... the k smallest of y^i + M dist_up(x, x^i);
+ * H_lo^k(x) = sum_j wk_j v_[j], v_[1] >= v_[2] >= ... the k largest of y^i - M dist_lo(x, x^i);
+ * g = (H_up^k + H_lo^k) / 2.  The order among equal values is by increasing data index.
+ * Selection keeps a sorted list of the best k seen so far, scanning the data in order. */
+typedef struct {
+    const double* X; const double* y; int64_t N; int d; double M; int norm;
+    const int8_t* mon; const double* w; const double* Q; int64_t q0, q1; int k; const double* wk;
+    double *hi, *lo, *g; int64_t *iu, *il;
+} evalk_job;
+
+static void* evalk_worker(void* arg) {
+    evalk_job* J = (evalk_job*)arg;
+    double bu[64], bl[64];
+    int64_t ku[64], kl[64];
+    for (int64_t qi = J->q0; qi < J->q1; qi++) {
+        const double* q = J->Q + qi * J->d;
+        int nu = 0, nl = 0;
+        for (int64_t k = 0; k < J->N; k++) {
+            const double* x = J->X + k * J->d;
+            double vu = J->y[k] + J->M * oracle_dist(q, x, J->d, J->norm, J->mon, J->w, +1);
+            double vl = J->y[k] - J->M * oracle_dist(q, x, J->d, J->norm, J->mon, J->w, -1);
+            /* insert vu into the ascending list (after equal values: lower index first) */
+            if (nu < J->k || vu < bu[nu - 1]) {
+                int p = nu < J->k ? nu++ : J->k - 1;
+                while (p > 0 && bu[p - 1] > vu) { bu[p] = bu[p - 1]; ku[p] = ku[p - 1]; p--; }
+                bu[p] = vu; ku[p] = k;
+            }
+            if (nl < J->k || vl > bl[nl - 1]) {
+                int p = nl < J->k ? nl++ : J->k - 1;
+                while (p > 0 && bl[p - 1] < vl) { bl[p] = bl[p - 1]; kl[p] = kl[p - 1]; p--; }
+                bl[p] = vl; kl[p] = k;
+            }
+        }
+        double hu = 0.0, hl = 0.0;
+        for (int j = 0; j < J->k; j++) {
+            hu += J->wk[j] * (j < nu ? bu[j] : NAN);
+            hl += J->wk[j] * (j < nl ? bl[j] : NAN);
+            if (J->iu) J->iu[qi * J->k + j] = j < nu ? ku[j] : -1;
+            if (J->il) J->il[qi * J->k + j] = j < nl ? kl[j] : -1;
+        }
+        if (J->hi) J->hi[qi] = hu;
+        if (J->lo) J->lo[qi] = hl;
+        if (J->g) J->g[qi] = 0.5 * (hu + hl);
+    }
+    return NULL;
+}
+
+int oracle_eval_k(const double* X, const double* y, int64_t N, int d, double M, int norm,
+                  const int8_t* mon, const double* w, const double* Q, int64_t nq, int k, const double* wk,
+                  double* hi, double* lo, double* g, int64_t* iu, int64_t* il, int nthreads) {
+    if (N < 1 || d < 1 || nq < 0 || norm < 1 || norm > 3 || k < 1 || k > 64) return 1;
+    if (nq == 0) return 0;
+    nthreads = clamp_threads(nthreads, nq);
+    pthread_t th[256];
+    evalk_job jobs[256];
+    for (int t = 0; t < nthreads; t++) {
+        evalk_job j = {X, y, N, d, M, norm, mon, w, Q, nq * t / nthreads, nq * (t + 1) / nthreads, k, wk,
+                       hi, lo, g, iu, il};
+        jobs[t] = j;
+        pthread_create(&th[t], NULL, evalk_worker, &jobs[t]);
+    }
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
     return 0;
 }

@@ -330,6 +330,45 @@ def check_gradient_fd(O):
                     assert abs(fdy - gy[k]) < 1e-6, (k, fdy, gy[k])
 
 
+def check_k_neighbours(O):
+    """k > 1 neighbours (Sec. 5, extra features): weighted sums of the k best bounds.
+
+    Unmasked: the k smallest of y + M cdist and the k largest of y - M cdist, taken with a
+    stable sort (equal values in index order); M = 0: the k smallest / largest y."""
+    for seed, (N, d, nq, k) in enumerate([(40, 2, 17, 3), (120, 4, 30, 5), (64, 1, 12, 8)]):
+        for norm in (1, 2, 3):
+            p = W.random_problem(70 + seed, N, d, nq, norm=norm, weighted=True, dtype=np.float64)
+            wk = np.random.default_rng(seed).random(k)
+            wk /= wk.sum()
+            r = O.evaluate_k(p.X, p.y, p.Q, p.M, k, wk, norm, w=p.w)
+            D = cdist(_scaled(p.Q, p.w), _scaled(p.X, p.w), METRIC[norm])
+            up = p.y[None, :] + p.M * D
+            dn = p.y[None, :] - p.M * D
+            ou = np.argsort(up, axis=1, kind="stable")[:, :k]
+            od = np.argsort(-dn, axis=1, kind="stable")[:, :k]
+            np.testing.assert_allclose(r.hi, (np.take_along_axis(up, ou, 1) * wk).sum(1), atol=1e-12)
+            np.testing.assert_allclose(r.lo, (np.take_along_axis(dn, od, 1) * wk).sum(1), atol=1e-12)
+            np.testing.assert_allclose(r.g, 0.5 * (r.hi + r.lo), atol=1e-15)
+            su = np.sort(up, 1)
+            clear = np.all(np.diff(su[:, :k + 1], axis=1) > 1e-9, axis=1)
+            assert np.all(r.idx_up[clear] == ou[clear])
+            # M = 0: the k smallest (largest) y in index order among equal values
+            r0 = O.evaluate_k(p.X, p.y, p.Q[:3], 0.0, k, wk, norm, w=p.w)
+            ys = p.y[np.argsort(p.y, kind="stable")[:k]]
+            yl = p.y[np.argsort(-p.y, kind="stable")[:k]]
+            np.testing.assert_allclose(r0.hi, (ys * wk).sum(), atol=1e-12)
+            np.testing.assert_allclose(r0.lo, (yl * wk).sum(), atol=1e-12)
+    # consistency with k = 1, also for masked problems and for trailing zero weights
+    for norm in (1, 2, 3):
+        p = W.random_problem(80, 90, 3, 25, norm=norm, masked=True, decreasing=True, dtype=np.float64)
+        r1 = O.evaluate(p.X, p.y, p.Q, p.M, norm, mon=p.mon)
+        for k, wk in ((1, [1.0]), (4, [1.0, 0.0, 0.0, 0.0])):
+            rk = O.evaluate_k(p.X, p.y, p.Q, p.M, k, wk, norm, mon=p.mon)
+            np.testing.assert_allclose(rk.hi, r1.hi, atol=1e-15)
+            np.testing.assert_allclose(rk.lo, r1.lo, atol=1e-15)
+            assert np.all(rk.idx_up[:, 0] == r1.idx_up) and np.all(rk.idx_lo[:, 0] == r1.idx_lo)
+
+
 ALL_CHECKS = [check_hand_examples, check_closed_form_1d, check_unmasked_cdist, check_interpolation,
               check_enclosure, check_lipschitz_monotone, check_width_bound, check_special_cases,
-              check_estimate_M, check_gradient_fd]
+              check_estimate_M, check_gradient_fd, check_k_neighbours]

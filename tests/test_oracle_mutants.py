@@ -27,6 +27,8 @@ MUTANTS = {
     "mest_l1_as_l2": ("static double sym_dist", "static double sym_dist_unused", 1),
     "grad_sign": ("gb * 0.5 * M * (gu[i] - gl[i])", "gb * 0.5 * M * (gu[i] + gl[i])", 1),
     "grad_M_half_missing": ("gm += 0.5 * gb *", "gm += gb *", 1),
+    # k neighbours: the lower list keeps the smallest values instead of the largest
+    "topk_lower_order": ("while (p > 0 && bl[p - 1] < vl)", "while (p > 0 && bl[p - 1] > vl)", 1),
 }
 
 

@@ -154,6 +154,22 @@ LIP_API lip_status lip_set_M(lip_handle h, double M, void* stream);
 LIP_API lip_status lip_eval(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi,
                     int32_t* idx_up, int32_t* idx_lo, void* stream);
 
+/* k > 1 neighbours (Sec. 5, "extra features" 2: values(query, LC, model, k) with the
+ * neighbour weights of setparams).  Replaces the minimum and the maximum by weighted sums
+ * of the k best bounds:
+ *   H_up^k(q) = sum_j wk[j] v_(j),  v_(1) <= ... <= v_(k) the k smallest y^i + M dist_up(q, x^i),
+ *   H_lo^k(q) = sum_j wk[j] v_[j],  v_[1] >= ... >= v_[k] the k largest  y^i - M dist_lo(q, x^i),
+ *   g = (H_up^k + H_lo^k) / 2,  hi = H_up^k, lo = H_lo^k.
+ * Equal values are ordered by data index.  1 <= k <= 8; wk: host array of k finite
+ * weights >= 0 (the paper takes them to sum to 1; this is not enforced).
+ * idx_up / idx_lo: device int32 [nq][k], the data indices in the order of the bounds.
+ * Any output may be NULL.  Fewer than k data points (or a non-finite query) give NaN and
+ * index -1.  The selection runs in the handle's scan precision (FP32 for FP32 and
+ * tensor-core handles), the k selected bounds are re-evaluated in FP64. */
+LIP_API lip_status lip_eval_k(lip_handle h, const void* Q, int64_t nq, int32_t k, const double* wk,
+                              void* g, void* lo, void* hi, int32_t* idx_up, int32_t* idx_lo,
+                              void* stream);
+
 /* lip_eval with Q and the outputs in host memory: the queries are copied in, evaluated
  * and the results copied out in chunks, with copies overlapping the kernels of other
  * chunks.  Synchronises the stream before returning (the outputs are then valid). */

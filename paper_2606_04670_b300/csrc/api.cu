@@ -581,6 +581,73 @@ lip_status lip_eval(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, 
     return eval_device(h, Q, nq, g, lo, hi, idx_up, idx_lo, static_cast<cudaStream_t>(stream));
 }
 
+lip_status lip_eval_k(lip_handle h, const void* Q, int64_t nq, int32_t k, const double* wk, void* g, void* lo,
+                      void* hi, int32_t* idx_up, int32_t* idx_lo, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (nq < 0) return fail(LIP_ERR_ARG, "nq = %lld < 0", (long long)nq);
+    if (k < 1 || k > 8) return fail(LIP_ERR_ARG, "k = %d is outside [1, 8]", k);
+    if (!wk) return fail(LIP_ERR_ARG, "wk is NULL");
+    for (int e = 0; e < k; ++e)
+        if (!(wk[e] >= 0.0) || !std::isfinite(wk[e])) return fail(LIP_ERR_ARG, "wk[%d] = %g must be finite and >= 0", e, wk[e]);
+    if (nq == 0) return LIP_OK;
+    if (!Q) return fail(LIP_ERR_ARG, "Q is NULL");
+    DeviceGuard gd(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int K = k <= 2 ? 2 : (k <= 4 ? 4 : 8);
+    const int64_t ngroups = round_up(h->N, PAD_POINTS) / GROUP;
+    const int64_t gx = ceil_div(nq, (int64_t)topk_threads());
+    if (gx > 0x7fffffff) return fail(LIP_ERR_ARG, "nq = %lld is too large", (long long)nq);
+    int nsplit = 0;
+    int64_t gps = 0;
+    if (ngroups > 0) {
+        const int64_t want = std::max<int64_t>(1, ceil_div((int64_t)4 * h->sms * 4, gx));
+        const int64_t s = std::min<int64_t>(std::min<int64_t>(want, 64), std::max<int64_t>(1, ngroups / 16));
+        gps = ceil_div(ngroups, s);
+        nsplit = (int)ceil_div(ngroups, gps);
+    }
+    LIP_TRY(h->partial.ensure(std::max<size_t>(1, (size_t)nsplit * nq * 2 * K * (h->esize + 4)), "k-neighbour scratch"));
+    TopkParams P{};
+    P.Q = Q;
+    P.nq = nq;
+    P.d = h->d;
+    P.C = h->C;
+    P.dl = h->dl;
+    P.nch = h->nch;
+    for (int j = 0; j < D_MAX; ++j) {
+        P.perm[j] = h->perm[j];
+        P.scale[j] = h->M * h->sgnw[j];
+    }
+    P.hot = h->hot;
+    P.ngroups = ngroups;
+    P.groups_per_split = gps;
+    P.partial = h->partial.p;
+    TopkMergeParams Mp{};
+    Mp.Q = Q;
+    Mp.nq = nq;
+    Mp.d = h->d;
+    Mp.k = k;
+    Mp.K = K;
+    Mp.nsplit = nsplit;
+    Mp.norm = h->norm;
+    Mp.M = h->M;
+    for (int i = 0; i < D_MAX; ++i) {
+        Mp.mon[i] = h->mon[i];
+        Mp.w[i] = h->w[i];
+    }
+    for (int e = 0; e < 8; ++e) Mp.wk[e] = e < k ? wk[e] : 0.0;
+    Mp.X0 = h->X0;
+    Mp.y0 = h->y0;
+    Mp.partial = h->partial.p;
+    Mp.g = g;
+    Mp.lo = lo;
+    Mp.hi = hi;
+    Mp.idx_up = idx_up;
+    Mp.idx_lo = idx_lo;
+    CUDA_TRY(launch_topk(h->esize, h->norm, K, P, (int)gx, nsplit, Mp, st));
+    count_launches(nsplit > 0 ? 2 : 1);
+    return LIP_OK;
+}
+
 lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* idx_up,
                          int32_t* idx_lo, void* stream) {
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");

@@ -62,6 +62,36 @@ cudaError_t tc_gather(const float* Q, int d, const int* list, int n, float* out,
 cudaError_t tc_scatter(const int* list, int n, const float* g, const float* lo, const float* hi, const int32_t* iu,
                        const int32_t* il, float* G, float* LO, float* HI, int32_t* IU, int32_t* IL, cudaStream_t st);
 
+struct TopkParams {
+    const void* Q;
+    int64_t nq;
+    int d, C, dl, nch;
+    int perm[D_MAX];
+    double scale[D_MAX];
+    const void* hot;
+    int64_t ngroups, groups_per_split;
+    void* partial;           // [nsplit][nq][2][K]: values then indices
+};
+
+struct TopkMergeParams {
+    const void* Q;
+    int64_t nq;
+    int d, k, K, nsplit, norm;
+    double M;
+    int8_t mon[D_MAX];
+    double w[D_MAX];
+    double wk[8];
+    const void* X0;
+    const void* y0;
+    const void* partial;
+    void *g, *lo, *hi;
+    int32_t *idx_up, *idx_lo;   // [nq][k]
+};
+
+int topk_threads();
+cudaError_t launch_topk(int elem_bytes, int norm, int K, const TopkParams& P, int gx, int gy, const TopkMergeParams& M,
+                        cudaStream_t st);
+
 int backward_blocks(int64_t nq);
 cudaError_t launch_backward(int elem_bytes, const BwdParams& P, int64_t N, void* grad_y, double* grad_M,
                             cudaStream_t st);

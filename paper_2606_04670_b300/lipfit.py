@@ -75,6 +75,7 @@ def _load():
         "lip_set_M": [H, f64, P],
         "lip_eval": [H, P, i64, P, P, P, P, P, P],
         "lip_eval_host": [H, P, i64, P, P, P, P, P, P],
+        "lip_eval_k": [H, P, i64, i32, P, P, P, P, P, P, P],
         "lip_estimate_M": [H, ctypes.POINTER(f64), ctypes.POINTER(i64), ctypes.POINTER(i64), P],
         "lip_backward": [H, P, i64, P, P, P, P, P, P, P],
         "lip_check": [H, P],
@@ -188,6 +189,10 @@ def lip_set_M(h, M, stream=0):
 
 def lip_eval(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream=0):
     return _lib.lip_eval(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream)
+
+
+def lip_eval_k(h, Q_ptr, nq, k, wk_ptr, g, lo, hi, idx_up, idx_lo, stream=0):
+    return _lib.lip_eval_k(h, Q_ptr, nq, k, wk_ptr, g, lo, hi, idx_up, idx_lo, stream)
 
 
 def lip_eval_host(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream=0):
@@ -377,6 +382,20 @@ class LipFit:
         _check(_lib.lip_eval(self.h, Q.data_ptr(), nq, _ptr(out["g"]), _ptr(out["lo"]), _ptr(out["hi"]),
                              _ptr(out["idx_up"]), _ptr(out["idx_lo"]), _stream_ptr()), "lip_eval")
         return {k: v for k, v in out.items() if v is not None}
+
+    def eval_k(self, Q, k: int, wk):
+        """k > 1 neighbours (Sec. 5): dict of g, lo, hi [nq] and idx_up, idx_lo [nq, k]."""
+        torch = _torch()
+        Q = self._dev(Q)
+        nq = Q.shape[0]
+        wk_a = np.ascontiguousarray(np.asarray(wk, np.float64))
+        assert wk_a.shape == (k,)
+        out = {key: torch.empty(nq, device="cuda", dtype=self.dtype) for key in ("g", "lo", "hi")}
+        out.update({key: torch.empty((nq, k), device="cuda", dtype=torch.int32) for key in ("idx_up", "idx_lo")})
+        _check(_lib.lip_eval_k(self.h, Q.data_ptr(), nq, int(k), wk_a.ctypes.data, out["g"].data_ptr(),
+                               out["lo"].data_ptr(), out["hi"].data_ptr(), out["idx_up"].data_ptr(),
+                               out["idx_lo"].data_ptr(), _stream_ptr()), "lip_eval_k")
+        return out
 
     def values(self, Q):
         """g at the query points (Sec. 5: values(query, LC, model, k=1))."""

@@ -116,3 +116,8 @@ def test_tensor_core_precision_rules():
         p, keep = L.make_params(norm, prec, mon, None)
         s, h = L.lip_fit(X.ctypes.data, y.ctypes.data, 8, 2, 1.0, p)
         assert s == L.LIP_ERR_UNSUPPORTED and not h.value, L.last_error()
+
+
+def test_eval_k_argument_errors():
+    wk = np.array([0.5, 0.5])
+    assert L.lip_eval_k(None, None, 1, 2, wk.ctypes.data, None, None, None, None, None) == L.LIP_ERR_ARG

@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--sets", type=int, default=0, help="batch_4096: use only the first N sets (profiling)")
     ap.add_argument("--queries", type=int, default=0,
                     help="use only the first N queries of a single-set workload (small profiling cases)")
     return ap.parse_args()
@@ -333,7 +334,8 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
             m = L.LipFit(M=p.M, norm=p.norm, mon=p.mon, w=p.w, capacity=p.N, d=p.d, precision=prec)
             ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             m.set_timing_events(*ev)
-            runs.append(dict(p=p, prec=prec, X=X, y=y, Q=Q, m=m, ev=ev, scan=[],
+            runs.append(dict(p=p, prec=prec, X=X, y=y, Q=Q, m=m, ev=ev, scan=[], bwd=[],
+                             bev=(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)),
                              gb=torch.ones(p.nq, device="cuda", dtype=dt)))
     tuning = {}
     if not args.no_autotune:
@@ -358,7 +360,12 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
                 torch.cuda.synchronize()
                 r["scan"].append(r["ev"][0].elapsed_time(r["ev"][1]))
             if with_bwd:
+                r["bev"][0].record()
                 m.backward(r["Q"], out["idx_up"], out["idx_lo"], r["gb"])
+                r["bev"][1].record()
+                if record:
+                    torch.cuda.synchronize()
+                    r["bwd"].append(r["bev"][0].elapsed_time(r["bev"][1]))
             if with_est:
                 est[k] = m.lipschitz_constant()[0]
 
@@ -444,6 +451,20 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
               "splits": tun["last_splits"], "tile_groups": tun["tile_groups"],
               "queries_per_thread": tun["queries_per_thread"], "sms": ctx.sms, "autotune": tuning,
               "tc_fallback_queries": {key(r): r["m"].last_fallback() for r in runs if r["prec"] == "tc_tf32"}}
+    if with_bwd:
+        # backward: per query it reads q, both indices and grad_g, gathers the two chosen
+        # data rows, writes grad_q and adds to grad_y (two FP64 atomics); then grad_y (FP64
+        # scratch read, FP32 read-modify-write) and grad_M (per-block partials)
+        bb = {}
+        for r in runs:
+            pp = r["p"]
+            es = 8 if r["prec"] == "fp64" else 4
+            byts = pp.nq * (pp.d * es + 8 + es + 2 * pp.d * es + pp.d * es + 16) + pp.N * (8 + 2 * es)
+            ms_b = statistics.mean(r["bwd"])
+            bb[key(r)] = {"ms": ms_b, "algorithmic_bytes": byts, "gb_per_s": byts / (ms_b / 1e3) / 1e9,
+                          "hbm_peak_gb_per_s": float(ctx.peaks.get("hbm_gbs", 6518.0)),
+                          "frac_of_hbm": byts / (ms_b / 1e3) / 1e9 / float(ctx.peaks.get("hbm_gbs", 6518.0))}
+        detail["backward"] = bb
     if with_est:
         detail["M_est"] = {key(r): est[k] for k, r in enumerate(runs)}
         detail["M_true"] = {key(r): r["p"].M for r in runs}
@@ -463,6 +484,8 @@ def wl_batch(ctx):
     from paper_2606_04670_b300 import lipfit as L
     torch, args = ctx.torch, ctx.args
     plan = W.batch_plan()
+    if args.sets > 0:
+        plan = plan[:args.sets]
     sets_np = [W.batch_set_data(bs) for bs in plan]
     qoff = np.concatenate([[0], np.cumsum([bs.nq * bs.d for bs in plan])])
     noff = np.concatenate([[0], np.cumsum([bs.nq for bs in plan])])
@@ -538,7 +561,7 @@ def wl_batch(ctx):
     if ctx.rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_rate(reference_problems("batch_4096"), args.cpu_seconds)[0]
     b.close()
-    config = {"workload": "batch_4096", "sets": len(plan), "N": "log-uniform [64, 65536]", "d": "uniform {2..10}",
+    config = {"workload": "batch_4096" if len(plan) == 4096 else f"batch_4096 (first {len(plan)} sets)", "sets": len(plan), "N": "log-uniform [64, 65536]", "d": "uniform {2..10}",
               "Q": "log-uniform [1e3, 1e5] per set", "total_pairs": info["total_pairs"],
               "total_queries": info["total_queries"], "norms": ["L1", "L2"],
               "step": "one CUDA-graph replay: persistent scan over the work list + batched merge",

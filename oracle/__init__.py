@@ -8,7 +8,8 @@ table) and never calls it.  ``build()`` compiles ``lipfit_oracle.c`` with gcc in
 
 Passages followed (all in the C file's header): Sec. 3 Eq. (upperlower) and
 Eq. (eq:g) for the envelopes and midpoint, Sec. 4.1 Eq. (distmon) for the
-monotone distance, Sec. 5 for the Lipschitz-constant estimate, and Table 1
+monotone distance, Sec. 5 for the Lipschitz-constant estimate and the k > 1
+neighbours, Sec. 4.3 for the local Lipschitz constants, and Table 1
 ("differentiable almost everywhere") for the gradient.
 
 ``Oracle(path)`` binds any build of the same C source; the tests use it to check
@@ -85,8 +86,17 @@ class Oracle:
         lib.oracle_estimate_M_rows.argtypes = [P, P, i64, i32, i32, P, i64, i64, P, P, P]
         lib.oracle_grad.argtypes = [P, P, i64, i32, f64, i32, P, P, P, i64, P, P, P, P, P, P]
         lib.oracle_eval_k.argtypes = [P, P, i64, i32, f64, i32, P, P, P, i64, i32, P, P, P, P, P, P, i32]
+        u64 = ctypes.c_uint64
+        lib.oracle_splitmix64.argtypes = [u64, u64]
+        lib.oracle_splitmix64.restype = u64
+        lib.oracle_local_knots.argtypes = [P, i64, i32, i32, P, u64, i64, i32, P, P, P]
+        lib.oracle_local_table.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, i32]
+        lib.oracle_eval_local.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, f64, P, P, P, P, P,
+                                          P, P, i32]
+        lib.oracle_local_terms.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, P, i32, P]
         for fn in (lib.oracle_eval, lib.oracle_estimate_M, lib.oracle_estimate_M_rows, lib.oracle_grad,
-                   lib.oracle_eval_k):
+                   lib.oracle_eval_k, lib.oracle_local_knots, lib.oracle_local_table, lib.oracle_eval_local,
+                   lib.oracle_local_terms):
             fn.restype = ctypes.c_int
         self.lib = lib
 
@@ -166,6 +176,72 @@ class Oracle:
             raise ValueError("oracle_grad: bad arguments")
         return gQ, gy, gM.value
 
+    # ------------------------------------------------------- local Lipschitz (Sec. 4.3)
+    def splitmix64(self, seed: int, c: int) -> int:
+        """Output number c (0-based) of SplitMix64 seeded with `seed`."""
+        return int(self.lib.oracle_splitmix64(seed & (2**64 - 1), c & (2**64 - 1)))
+
+    def local_knots(self, X, m: int, S: int, seed: int, norm: int = NORM_L2, w=None):
+        """(knots, pairs [S,2], dist [S]): quantile knots from S sampled pairs."""
+        X, w = _f64(X), _f64(w)
+        N, d = X.shape
+        knots = np.empty(max(m, 1))
+        pairs = np.empty((S, 2), np.int64)
+        dist = np.empty(S)
+        n = self.lib.oracle_local_knots(_ptr(X), N, d, int(norm), _ptr(w), seed & (2**64 - 1), int(S), int(m),
+                                        _ptr(knots), _ptr(pairs), _ptr(dist))
+        if n < 0:
+            raise ValueError("oracle_local_knots: bad arguments")
+        return knots[:n].copy(), pairs, dist
+
+    def local_table(self, X, y, knots, norm: int = NORM_L2, w=None, nthreads: Optional[int] = None):
+        """(d1 [N], F [N], Mtab [N, m+1]) for the given knots."""
+        X, y, w = _f64(X), _f64(y), _f64(w)
+        T = _f64(np.asarray(knots, np.float64).reshape(-1))
+        N, d = X.shape
+        m = T.shape[0]
+        d1, F = np.empty(N), np.empty(N)
+        Mtab = np.empty((N, m + 1))
+        rc = self.lib.oracle_local_table(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(T), m, _ptr(d1), _ptr(F),
+                                         _ptr(Mtab), nthreads or default_threads())
+        if rc != 0:
+            raise ValueError("oracle_local_table: bad arguments")
+        return d1, F, Mtab
+
+    def evaluate_local(self, X, y, Q, knots, table, norm: int = NORM_L2, w=None, eta: float = 0.0,
+                       nthreads: Optional[int] = None) -> EvalResult:
+        """Envelopes with M replaced by M_k(dist); eta > 0 adds the amb_up / amb_lo flags."""
+        X, y, Q, w = _f64(X), _f64(y), _f64(Q), _f64(w)
+        T = _f64(np.asarray(knots, np.float64).reshape(-1))
+        d1, F, Mtab = (_f64(a) for a in table)
+        N, d = X.shape
+        nq = Q.shape[0]
+        out = {k: np.empty(nq) for k in ("hi", "lo", "g")}
+        iu, il = np.empty(nq, np.int64), np.empty(nq, np.int64)
+        au, al = np.zeros(nq, np.int8), np.zeros(nq, np.int8)
+        rc = self.lib.oracle_eval_local(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(T), T.shape[0], _ptr(d1),
+                                        _ptr(F), _ptr(Mtab), _ptr(Q), nq, float(eta), _ptr(out["hi"]),
+                                        _ptr(out["lo"]), _ptr(out["g"]), _ptr(iu), _ptr(il), _ptr(au), _ptr(al),
+                                        nthreads or default_threads())
+        if rc != 0:
+            raise ValueError("oracle_eval_local: bad arguments")
+        return EvalResult(idx_up=iu, idx_lo=il, amb_up=au.astype(bool), amb_lo=al.astype(bool), **out)
+
+    def local_terms(self, X, y, Q, knots, table, idx, side: int, norm: int = NORM_L2, w=None):
+        """y_k + M_k(t) t (side +1) or y_k - M_k(t) t (side -1) for k = idx[q]."""
+        X, y, Q, w = _f64(X), _f64(y), _f64(Q), _f64(w)
+        T = _f64(np.asarray(knots, np.float64).reshape(-1))
+        d1, F, Mtab = (_f64(a) for a in table)
+        N, d = X.shape
+        nq = Q.shape[0]
+        ix = np.ascontiguousarray(idx, np.int64)
+        out = np.empty(nq)
+        rc = self.lib.oracle_local_terms(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(T), T.shape[0], _ptr(d1),
+                                         _ptr(F), _ptr(Mtab), _ptr(Q), nq, _ptr(ix), int(side), _ptr(out))
+        if rc != 0:
+            raise ValueError("oracle_local_terms: bad arguments")
+        return out
+
 
 _default: Optional[Oracle] = None
 
@@ -195,3 +271,23 @@ def estimate_M_rows(*a, **k):
 
 def gradient(*a, **k):
     return default().gradient(*a, **k)
+
+
+def splitmix64(*a, **k):
+    return default().splitmix64(*a, **k)
+
+
+def local_knots(*a, **k):
+    return default().local_knots(*a, **k)
+
+
+def local_table(*a, **k):
+    return default().local_table(*a, **k)
+
+
+def evaluate_local(*a, **k):
+    return default().evaluate_local(*a, **k)
+
+
+def local_terms(*a, **k):
+    return default().local_terms(*a, **k)

@@ -356,3 +356,227 @@ int oracle_eval_k(const double* X, const double* y, int64_t N, int d, double M, 
     for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
     return 0;
 }
+
+/* ------------------------------------------------ local Lipschitz constants (Sec. 4.3) */
+/*
+ * For every datum x^k a non-decreasing step function M_k(t) of the distance t from x^k
+ * replaces the global M in Eq. (upperlower):
+ *
+ *   H_up(x) = min_k ( y^k + M_k(t_k) t_k ),  H_lo(x) = max_k ( y^k - M_k(t_k) t_k ),
+ *   t_k = dist(x, x^k) (the symmetric weighted norm).
+ *
+ * First segment, t in [0, d1_k] with d1_k the distance to the nearest other datum:
+ * M_k = F_k = |y^k - y^(1)| / d1_k (the largest such ratio when several data share the
+ * nearest distance).  Beyond it, with knots T_1 < ... < T_m common to all data (empirical
+ * quantiles of a sample of interpoint distances) and T_{m+1} = +inf: for t in
+ * (T_s, T_{s+1}], t > d1_k,
+ *
+ *   M_k(t) = max { |y^k - y^j| / d_kj : 0 < d_kj <= max(T_{s+1}, d1_k) }.
+ *
+ * That is the paper's rule (the ratio over the data no farther than the next knot) with
+ * the per-datum first knot d1_k in front of the common ones.  Pairs at distance 0
+ * (duplicated points) are skipped.  The table holds Mtab_k[s], s = 0..m, the value on
+ * segment s (s = the number of knots below t); it is also the value for every t
+ * <= T_{s+1} beyond d1_k, so M_k(t) = (t <= d1_k) ? F_k : Mtab_k[#{i : T_i < t}].
+ *
+ * Knots: S pairs (a_s, b_s) are drawn with SplitMix64 (Steele, Lea and Flood 2014; output
+ * c of a generator seeded with `seed` is mix(seed + (c + 1) * 0x9E3779B97F4A7C15)), a_s =
+ * out(2s) mod N and b_s = out(2s + 1) mod N.  Their positive distances, sorted, D_(1) <=
+ * ... <= D_(S'), give T_i = D_(ceil(i S' / m)), i = 1..m (the inverted-CDF quantile at
+ * i/m), with repeated values dropped.
+ *
+ * Distances here are the symmetric weighted norm of Sec. 5's estimate: |a_i - b_i|
+ * times w_i, then summed (L1), squared and summed then square-rooted (L2) or maxed (Linf),
+ * in increasing coordinate order.
+ */
+
+uint64_t oracle_splitmix64(uint64_t seed, uint64_t c) {
+    uint64_t z = seed + (c + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static int cmp_double(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* Knots from S sampled pairs; returns the number of distinct knots (<= m), -1 on bad
+ * arguments.  pairs_out (2S) and dist_out (S) receive the sample when not NULL. */
+int oracle_local_knots(const double* X, int64_t N, int d, int norm, const double* w, uint64_t seed,
+                       int64_t S, int m, double* knots_out, int64_t* pairs_out, double* dist_out) {
+    if (N < 1 || d < 1 || norm < 1 || norm > 3 || S < 0 || m < 0) return -1;
+    double* D = (double*)malloc((size_t)(S > 0 ? S : 1) * sizeof(double));
+    if (!D) return -1;
+    int64_t kept = 0;
+    for (int64_t s = 0; s < S; s++) {
+        int64_t a = (int64_t)(oracle_splitmix64(seed, 2 * (uint64_t)s) % (uint64_t)N);
+        int64_t b = (int64_t)(oracle_splitmix64(seed, 2 * (uint64_t)s + 1) % (uint64_t)N);
+        double dd = sym_dist(X + a * d, X + b * d, d, norm, w);
+        if (pairs_out) { pairs_out[2 * s] = a; pairs_out[2 * s + 1] = b; }
+        if (dist_out) dist_out[s] = dd;
+        if (dd > 0.0) D[kept++] = dd;
+    }
+    qsort(D, (size_t)kept, sizeof(double), cmp_double);
+    int n = 0;
+    if (kept > 0) {
+        for (int i = 1; i <= m; i++) {
+            int64_t pos = ((int64_t)i * kept + m - 1) / m;      /* ceil(i S' / m), 1-based */
+            double v = D[pos - 1];
+            if (n == 0 || v > knots_out[n - 1]) knots_out[n++] = v;
+        }
+    }
+    free(D);
+    return n;
+}
+
+typedef struct {
+    const double* X; const double* y; int64_t N; int d; int norm; const double* w;
+    const double* T; int m; int64_t k0, k1;
+    double *d1, *F, *Mtab;
+} ltab_job;
+
+static void* ltab_worker(void* arg) {
+    ltab_job* J = (ltab_job*)arg;
+    const int d = J->d;
+    for (int64_t k = J->k0; k < J->k1; k++) {
+        const double* xk = J->X + k * d;
+        double d1 = INFINITY, F = 0.0;
+        for (int64_t j = 0; j < J->N; j++) {                 /* nearest distance and its ratio */
+            double dd = sym_dist(xk, J->X + j * d, d, J->norm, J->w);
+            if (dd == 0.0) continue;
+            double r = fabs(J->y[k] - J->y[j]) / dd;
+            if (dd < d1) { d1 = dd; F = r; }
+            else if (dd == d1 && r > F) F = r;
+        }
+        double* row = J->Mtab + k * (J->m + 1);
+        for (int s = 0; s <= J->m; s++) row[s] = F;
+        for (int64_t j = 0; j < J->N; j++) {                 /* every segment whose knot covers d_kj */
+            double dd = sym_dist(xk, J->X + j * d, d, J->norm, J->w);
+            if (dd == 0.0) continue;
+            double r = fabs(J->y[k] - J->y[j]) / dd;
+            for (int s = 0; s <= J->m; s++) {
+                double knot = s < J->m ? J->T[s] : INFINITY;
+                if (dd <= knot && r > row[s]) row[s] = r;
+            }
+        }
+        J->d1[k] = d1;
+        J->F[k] = F;
+    }
+    return NULL;
+}
+
+/* d1 [N], F [N] and Mtab [N][m + 1] for knots T [m] (strictly increasing). */
+int oracle_local_table(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
+                       const double* T, int m, double* d1, double* F, double* Mtab, int nthreads) {
+    if (N < 1 || d < 1 || norm < 1 || norm > 3 || m < 0) return 1;
+    nthreads = clamp_threads(nthreads, N);
+    pthread_t th[256];
+    ltab_job jobs[256];
+    for (int t = 0; t < nthreads; t++) {
+        ltab_job j = {X, y, N, d, norm, w, T, m, N * t / nthreads, N * (t + 1) / nthreads, d1, F, Mtab};
+        jobs[t] = j;
+        pthread_create(&th[t], NULL, ltab_worker, &jobs[t]);
+    }
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    return 0;
+}
+
+/* M_k(t) from datum k's table row. */
+static double local_M(const double* T, int m, double d1, double F, const double* row, double t) {
+    if (t <= d1) return F;
+    int s = 0;
+    while (s < m && T[s] < t) s++;
+    return row[s];
+}
+
+typedef struct {
+    const double* X; const double* y; int64_t N; int d; int norm; const double* w;
+    const double* T; int m; const double *d1, *F, *Mtab;
+    const double* Q; int64_t q0, q1; double eta;
+    double *hi, *lo, *g; int64_t *iu, *il; int8_t *amb_up, *amb_lo;
+} leval_job;
+
+static void* leval_worker(void* arg) {
+    leval_job* J = (leval_job*)arg;
+    const int d = J->d;
+    for (int64_t qi = J->q0; qi < J->q1; qi++) {
+        const double* q = J->Q + qi * d;
+        int bad = 0;
+        for (int i = 0; i < d; i++) if (!isfinite(q[i])) bad = 1;
+        double bu = INFINITY, bl = -INFINITY;
+        int64_t ku = -1, kl = -1;
+        int au = 0, al = 0;
+        if (!bad) {
+            for (int64_t k = 0; k < J->N; k++) {
+                double t = sym_dist(q, J->X + k * d, d, J->norm, J->w);
+                double Mk = local_M(J->T, J->m, J->d1[k], J->F[k], J->Mtab + k * (J->m + 1), t);
+                double vu = J->y[k] + Mk * t, vl = J->y[k] - Mk * t;
+                if (vu < bu) { bu = vu; ku = k; }
+                if (vl > bl) { bl = vl; kl = k; }
+            }
+            /* An evaluation whose distances are off by up to eta may decide a segment
+             * differently.  Flag the query when that can change the outcome: a datum whose
+             * constant may come out lower (M_k(t - eta) < M_k(t)) reaches the envelope with
+             * it, or the winning datum's own constant may come out higher. */
+            if (J->eta > 0.0) {
+                for (int64_t k = 0; k < J->N; k++) {
+                    const double* row = J->Mtab + k * (J->m + 1);
+                    double t = sym_dist(q, J->X + k * d, d, J->norm, J->w);
+                    double mt = local_M(J->T, J->m, J->d1[k], J->F[k], row, t);
+                    double ma = local_M(J->T, J->m, J->d1[k], J->F[k], row, t - J->eta);
+                    double mb = local_M(J->T, J->m, J->d1[k], J->F[k], row, t + J->eta);
+                    if (ma < mt && J->y[k] + ma * t <= bu) au = 1;
+                    if (ma < mt && J->y[k] - ma * t >= bl) al = 1;
+                    if (mb > mt && k == ku) au = 1;
+                    if (mb > mt && k == kl) al = 1;
+                }
+            }
+        }
+        double hi = bad ? NAN : bu, lo = bad ? NAN : bl;
+        if (J->hi) J->hi[qi] = hi;
+        if (J->lo) J->lo[qi] = lo;
+        if (J->g) J->g[qi] = 0.5 * (hi + lo);
+        if (J->iu) J->iu[qi] = ku;
+        if (J->il) J->il[qi] = kl;
+        if (J->amb_up) J->amb_up[qi] = (int8_t)au;
+        if (J->amb_lo) J->amb_lo[qi] = (int8_t)al;
+    }
+    return NULL;
+}
+
+/* Envelopes with the local constants; eta > 0 also fills the ambiguity flags. */
+int oracle_eval_local(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
+                      const double* T, int m, const double* d1, const double* F, const double* Mtab,
+                      const double* Q, int64_t nq, double eta, double* hi, double* lo, double* g,
+                      int64_t* iu, int64_t* il, int8_t* amb_up, int8_t* amb_lo, int nthreads) {
+    if (N < 1 || d < 1 || nq < 0 || norm < 1 || norm > 3 || m < 0) return 1;
+    if (nq == 0) return 0;
+    nthreads = clamp_threads(nthreads, nq);
+    pthread_t th[256];
+    leval_job jobs[256];
+    for (int t = 0; t < nthreads; t++) {
+        leval_job j = {X, y, N, d, norm, w, T, m, d1, F, Mtab, Q, nq * t / nthreads, nq * (t + 1) / nthreads,
+                       eta, hi, lo, g, iu, il, amb_up, amb_lo};
+        jobs[t] = j;
+        pthread_create(&th[t], NULL, leval_worker, &jobs[t]);
+    }
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    return 0;
+}
+
+/* The value datum idx[q] gives query q: y + M_k(t) t (side > 0) or y - M_k(t) t. */
+int oracle_local_terms(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
+                       const double* T, int m, const double* d1, const double* F, const double* Mtab,
+                       const double* Q, int64_t nq, const int64_t* idx, int side, double* out) {
+    if (N < 1 || d < 1 || nq < 0 || norm < 1 || norm > 3 || m < 0) return 1;
+    for (int64_t qi = 0; qi < nq; qi++) {
+        int64_t k = idx[qi];
+        if (k < 0 || k >= N) { out[qi] = NAN; continue; }
+        double t = sym_dist(Q + qi * d, X + k * d, d, norm, w);
+        double Mk = local_M(T, m, d1[k], F[k], Mtab + k * (m + 1), t);
+        out[qi] = side > 0 ? y[k] + Mk * t : y[k] - Mk * t;
+    }
+    return 0;
+}

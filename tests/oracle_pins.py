@@ -18,6 +18,8 @@ from scipy.spatial.distance import cdist, pdist, squareform
 from paper_2606_04670_b300 import workloads as W
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "hand_examples.json")
+GOLDEN_LOCAL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "local_lipschitz_1d.json")
+GOLDEN_SPLITMIX = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "splitmix64.json")
 METRIC = {1: "cityblock", 2: "euclidean", 3: "chebyshev"}
 
 
@@ -369,6 +371,141 @@ def check_k_neighbours(O):
             assert np.all(rk.idx_up[:, 0] == r1.idx_up) and np.all(rk.idx_lo[:, 0] == r1.idx_lo)
 
 
+
+# ------------------------------------------------- local Lipschitz constants (Sec. 4.3)
+
+def check_splitmix64(O):
+    """The knot sampler's generator reproduces SplitMix64's published test vector."""
+    G = json.load(open(GOLDEN_SPLITMIX))
+    assert [O.splitmix64(G["seed"], c) for c in range(len(G["outputs"]))] == [int(v) for v in G["outputs"]]
+
+
+def _local_problems():
+    out = []
+    for norm in (1, 2, 3):
+        for weighted in (False, True):
+            p = W.random_problem(90 + norm, 70, 3, 40, norm=norm, weighted=weighted, dtype=np.float64)
+            out.append(p)
+    out.append(W.toy_d3(dtype=np.float64, n_data=120, n_query=60))
+    return out
+
+
+def check_local_hand_example(O):
+    """Sec. 4.3 worked by hand on 1-D data with explicit knots (tests/golden)."""
+    G = json.load(open(GOLDEN_LOCAL))
+    X = np.array(G["X"])[:, None]
+    Q = np.array(G["Q"])[:, None]
+    for norm in (1, 2, 3):
+        d1, F, Mtab = O.local_table(X, G["y"], G["knots"], norm)
+        np.testing.assert_allclose(d1, G["d1"], rtol=1e-15)
+        np.testing.assert_allclose(F, G["F"], rtol=1e-15)
+        np.testing.assert_allclose(Mtab, G["Mtab"], rtol=1e-15)
+        r = O.evaluate_local(X, G["y"], Q, G["knots"], (d1, F, Mtab), norm)
+        np.testing.assert_allclose(r.hi, G["hi"], atol=1e-15)
+        np.testing.assert_allclose(r.lo, G["lo"], atol=1e-15)
+        assert list(r.idx_up) == G["idx_up"] and list(r.idx_lo) == G["idx_lo"]
+
+
+def check_local_knots(O):
+    """Knots = inverted-CDF quantiles (numpy) of the positive distances (scipy) of the pairs
+    SplitMix64 draws."""
+    for p in _local_problems():
+        N = p.X.shape[0]
+        for m, S, seed in ((8, 300, 5), (16, 1000, 123456789), (5, 7, 2**63 + 11)):
+            T, pairs, dist = O.local_knots(p.X, m, S, seed, p.norm, w=p.w)
+            want = np.array([[O.splitmix64(seed, 2 * s) % N, O.splitmix64(seed, 2 * s + 1) % N] for s in range(S)])
+            assert np.array_equal(pairs, want)
+            Z = _scaled(p.X, p.w)
+            ref = np.array([cdist(Z[a][None], Z[b][None], METRIC[p.norm])[0, 0] for a, b in pairs])
+            np.testing.assert_allclose(dist, ref, rtol=1e-13, atol=1e-15)
+            D = dist[dist > 0]
+            q = np.quantile(D, np.arange(1, m + 1) / m, method="inverted_cdf")
+            assert np.array_equal(T, np.unique(q))
+            assert np.all(np.diff(T) > 0)
+    # no sample, or only repeated points: no knots
+    p = _local_problems()[0]
+    assert O.local_knots(p.X, 8, 0, 1)[0].size == 0
+    assert O.local_knots(np.zeros((5, 2)), 8, 50, 1)[0].size == 0
+
+
+def _brute_table(Z, y, T, metric):
+    """d1, F, Mtab from scipy distances: masks, not loops."""
+    D = cdist(Z, Z, metric)
+    R = np.abs(y[:, None] - y[None, :]) / np.where(D > 0, D, 1.0)
+    pos = D > 0
+    d1 = np.where(pos, D, np.inf).min(1)
+    near = pos & (D <= d1[:, None] * (1 + 1e-12))
+    F = np.where(near, R, 0.0).max(1)
+    cols = [np.maximum(F, np.where(pos & (D <= t), R, 0.0).max(1)) for t in list(T) + [np.inf]]
+    return d1, F, np.stack(cols, 1)
+
+
+def check_local_table(O):
+    """d1, F, Mtab (Sec. 4.3) against scipy distances; M_k non-decreasing; the last segment
+    is the row maximum and its maximum over k is M_est (Sec. 5)."""
+    rng = np.random.default_rng(7)
+    for p in _local_problems():
+        Z = _scaled(p.X, p.w)
+        D = cdist(Z, Z, METRIC[p.norm])
+        # knots away from every distance, so a 1-ulp difference between scipy and the
+        # oracle cannot move a pair across a knot
+        T = np.sort(rng.uniform(D[D > 0].min(), D.max(), 9))
+        d1, F, Mtab = O.local_table(p.X, p.y, T, p.norm, w=p.w)
+        bd1, bF, bM = _brute_table(Z, p.y, T, METRIC[p.norm])
+        np.testing.assert_allclose(d1, bd1, rtol=1e-12)
+        np.testing.assert_allclose(F, bF, rtol=1e-12)
+        np.testing.assert_allclose(Mtab, bM, rtol=1e-12)
+        # sampled knots: structural facts only
+        T, _, _ = O.local_knots(p.X, 12, 400, 99, p.norm, w=p.w)
+        d1, F, Mtab = O.local_table(p.X, p.y, T, p.norm, w=p.w)
+        assert np.all(np.diff(Mtab, axis=1) >= 0) and np.all(Mtab[:, 0] >= F)
+        R = np.abs(p.y[:, None] - p.y[None, :]) / np.where(D > 0, D, np.inf)
+        np.testing.assert_allclose(Mtab[:, -1], R.max(1), rtol=1e-12)
+        M_est = O.estimate_M(p.X, p.y, p.norm, w=p.w)[0]
+        assert abs(Mtab[:, -1].max() - M_est) <= 1e-12 * M_est
+        np.testing.assert_allclose(d1, np.where(D > 0, D, np.inf).min(1), rtol=1e-12)
+    # a single datum, or only repeated points: no neighbour, constant 0
+    d1, F, Mtab = O.local_table(np.zeros((3, 2)), np.array([1.0, 1.0, 1.0]), [0.5])
+    assert np.all(np.isinf(d1)) and np.all(F == 0) and np.all(Mtab == 0)
+
+
+def check_local_eval(O):
+    """Local evaluation (Sec. 4.3): interpolates the data; bounds no wider than the global ones
+    with M_est; searchsorted form of M_k(t) (the paper's primitive) on scipy distances; with
+    every ratio equal (1-D linear data) it is the global evaluation with that M."""
+    for p in _local_problems():
+        T, _, _ = O.local_knots(p.X, 10, 500, 3, p.norm, w=p.w)
+        tab = O.local_table(p.X, p.y, T, p.norm, w=p.w)
+        r = O.evaluate_local(p.X, p.y, p.X, T, tab, p.norm, w=p.w)
+        np.testing.assert_allclose(r.hi, p.y, atol=1e-12)
+        np.testing.assert_allclose(r.lo, p.y, atol=1e-12)
+        M_est = O.estimate_M(p.X, p.y, p.norm, w=p.w)[0]
+        rl = O.evaluate_local(p.X, p.y, p.Q, T, tab, p.norm, w=p.w)
+        rg = O.evaluate(p.X, p.y, p.Q, M_est, p.norm, w=p.w)
+        assert np.all(rl.hi <= rg.hi + 1e-12) and np.all(rl.lo >= rg.lo - 1e-12)
+        D = cdist(_scaled(p.Q, p.w), _scaled(p.X, p.w), METRIC[p.norm])
+        d1, F, Mtab = tab
+        seg = np.searchsorted(T, D, side="left")
+        Mq = np.where(D <= d1[None, :], F[None, :], Mtab[np.arange(len(d1))[None, :], seg])
+        np.testing.assert_allclose(rl.hi, (p.y[None, :] + Mq * D).min(1), atol=1e-12)
+        np.testing.assert_allclose(rl.lo, (p.y[None, :] - Mq * D).max(1), atol=1e-12)
+        np.testing.assert_allclose(rl.g, 0.5 * (rl.hi + rl.lo), atol=1e-15)
+        assert not rl.amb_up.any() and not rl.amb_lo.any()        # eta = 0: no flags
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-1, 1, (40, 1))
+    y = -2.5 * X[:, 0]
+    Q = rng.uniform(-1.5, 1.5, (30, 1))
+    T, _, _ = O.local_knots(X, 6, 200, 8)
+    tab = O.local_table(X, y, T)
+    np.testing.assert_allclose(tab[2], 2.5, rtol=1e-13)
+    for norm in (1, 2, 3):
+        rl = O.evaluate_local(X, y, Q, T, tab, norm)
+        rg = O.evaluate(X, y, Q, 2.5, norm)
+        np.testing.assert_allclose(rl.hi, rg.hi, atol=1e-12)
+        np.testing.assert_allclose(rl.lo, rg.lo, atol=1e-12)
+
+
 ALL_CHECKS = [check_hand_examples, check_closed_form_1d, check_unmasked_cdist, check_interpolation,
               check_enclosure, check_lipschitz_monotone, check_width_bound, check_special_cases,
-              check_estimate_M, check_gradient_fd, check_k_neighbours]
+              check_estimate_M, check_gradient_fd, check_k_neighbours, check_splitmix64,
+              check_local_hand_example, check_local_knots, check_local_table, check_local_eval]

@@ -29,6 +29,17 @@ MUTANTS = {
     "grad_M_half_missing": ("gm += 0.5 * gb *", "gm += gb *", 1),
     # k neighbours: the lower list keeps the smallest values instead of the largest
     "topk_lower_order": ("while (p > 0 && bl[p - 1] < vl)", "while (p > 0 && bl[p - 1] > vl)", 1),
+    # local Lipschitz (Sec. 4.3): a pair exactly at a knot left out of that knot's segment
+    "local_knot_strict": ("if (dd <= knot && r > row[s])", "if (dd < knot && r > row[s])", 1),
+    # the segment lookup counts a knot equal to t as passed
+    "local_segment_le": ("while (s < m && T[s] < t) s++;", "while (s < m && T[s] <= t) s++;", 1),
+    # the first segment [0, d1] dropped
+    "local_no_first_segment": ("if (t <= d1) return F;", "if (t < 0) return F;", 1),
+    # quantile position rounded to nearest instead of up
+    "local_quantile_round": ("((int64_t)i * kept + m - 1) / m;", "((int64_t)i * kept + m / 2) / m;", 1),
+    "local_ratio_signed": ("double r = fabs(J->y[k] - J->y[j]) / dd;\n            if (dd < d1)",
+                           "double r = (J->y[k] - J->y[j]) / dd;\n            if (dd < d1)", 1),
+    "splitmix_shift": ("z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBull;", 1),
 }
 
 

@@ -44,7 +44,8 @@ UNIT = "G pairs/s"
 NORMS = (W.NORM_L1, W.NORM_L2, W.NORM_LINF)
 NNAME = {1: "L1", 2: "L2", 3: "Linf"}
 FP32_LANES_PER_SM = 128
-WORKLOADS = ("monotone_d4", "plain_d2", "cluster_d16", "cluster_d16_tc", "grad_d8", "batch_4096")
+WORKLOADS = ("monotone_d4", "plain_d2", "cluster_d16", "cluster_d16_tc", "grad_d8", "batch_4096", "local_d4")
+LOCAL_KNOTS, LOCAL_SAMPLE, LOCAL_SEED = 16, 32768, 0
 # TF32 dense peak: the measured BF16 peak times the nominal TF32 / BF16 ratio (1.1 / 2.25)
 TF32_OVER_BF16 = 1.1 / 2.25
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant scan kernel of
@@ -185,6 +186,34 @@ def oracle_rate(problems, seconds: float, rng_seed=5):
                       f"(FP64, {oracle.default_threads()} threads, {dt:.1f} s)"}, dt
 
 
+def oracle_local_rate(p, seconds: float, n_sub: int = 20_000, rng_seed=5):
+    """Pairs/s of the FP64 oracle's local evaluation (Sec. 4.3) over random queries against
+    the first n_sub data points, with the oracle's own table for those points (built
+    before the timed part; its rate is reported in the sample text)."""
+    import oracle
+    o = oracle.default()
+    X, y = p.X[:n_sub].astype(np.float64), p.y[:n_sub].astype(np.float64)
+    t0 = time.perf_counter()
+    T, _, _ = o.local_knots(X, LOCAL_KNOTS, LOCAL_SAMPLE, LOCAL_SEED, p.norm, w=p.w)
+    tab = o.local_table(X, y, T, p.norm, w=p.w)
+    t_tab = time.perf_counter() - t0
+    rng = np.random.default_rng(rng_seed)
+    probe = p.Q[rng.choice(p.nq, 64, replace=False)]
+    t0 = time.perf_counter()
+    o.evaluate_local(X, y, probe, T, tab, p.norm, w=p.w)
+    per_pair = max(time.perf_counter() - t0, 1e-4) / (64 * len(y))
+    nq = int(max(64, min(p.nq, seconds / per_pair / len(y))))
+    Qs = p.Q[rng.choice(p.nq, nq, replace=False)]
+    t0 = time.perf_counter()
+    o.evaluate_local(X, y, Qs, T, tab, p.norm, w=p.w)
+    dt = time.perf_counter() - t0
+    pairs = nq * len(y)
+    return {"value": pairs / dt / 1e9, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
+            "sample": f"{pairs:.3g} pairs: {nq} random queries x the first {len(y)} data points, local constants "
+                      f"from the oracle's table of those points ({len(y)}^2 pairs in {t_tab:.1f} s, untimed); "
+                      f"FP64, {oracle.default_threads()} threads, {dt:.1f} s"}, dt
+
+
 def reference_problems(workload):
     if workload == "monotone_d4":
         base = W.monotone_d4(norm=W.NORM_L2)
@@ -211,13 +240,18 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    problems = reference_problems(args.workload)
     per_step = max(2.0, min(8.0, 60.0 / max(1, args.steps + args.warmup)))
+    if args.workload == "local_d4":
+        problems = W.local_d4()
+        rate = lambda sec: oracle_local_rate(problems, sec)  # noqa: E731
+    else:
+        problems = reference_problems(args.workload)
+        rate = lambda sec: oracle_rate(problems, sec)  # noqa: E731
     for _ in range(args.warmup):
-        oracle_rate(problems, per_step / 4)
+        rate(per_step / 4)
     rates, times, base = [], [], None
     for _ in range(args.steps):
-        base, dt = oracle_rate(problems, per_step)
+        base, dt = rate(per_step)
         rates.append(base["value"])
         times.append(dt)
     value = statistics.mean(rates)
@@ -571,6 +605,90 @@ def wl_batch(ctx):
     return ctx.line(value, total, args.steps, "f32", config, roof, cpu, e2e, clocks, launches, detail)
 
 
+def wl_local(ctx, name="local_d4"):
+    """Local Lipschitz constants (Sec. 4.3): per step, fit + compute_local_lipschitz (knot
+    sample, exact table: two N^2 passes) + the local evaluation of every query."""
+    from paper_2606_04670_b300 import lipfit as L
+    torch, args = ctx.torch, ctx.args
+    p = W.local_d4()
+    if args.queries > 0:
+        p = p.sub_queries(args.queries)
+    X, y, Q = (torch.as_tensor(a).cuda() for a in (p.X, p.y, p.Q))
+    m = L.LipFit(M=p.M, norm=p.norm, capacity=p.N, d=p.d)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    tev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    m.set_timing_events(*ev)
+    scan, table = [], []
+
+    def step(record=False):
+        m.clear()
+        m.add(X, y)
+        tev[0].record()
+        m.compute_local_lipschitz(LOCAL_KNOTS, LOCAL_SAMPLE, LOCAL_SEED)
+        tev[1].record()
+        m.eval_local(Q)
+        if record:
+            torch.cuda.synchronize()
+            scan.append(ev[0].elapsed_time(ev[1]))
+            table.append(tev[0].elapsed_time(tev[1]))
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    ms, clocks, launches = ctx.timed(lambda: step(True), args.steps)
+    value, total = aggregate(p.nq * p.N * args.steps, sum(ms), device="cuda")
+    ms_scan, ms_table = statistics.mean(scan), statistics.mean(table)
+    # local scan per pair: distance 2d, knot search 5 x (compare + add), first-segment test and
+    # select, two FMAs, two (compare + two selects) for the running extrema; one MUFU sqrt
+    ip = 2 * p.d + 20
+    roof = ctx.roofline(f"loc_scan_kernel<{NNAME[p.norm]}> (d={p.d}, {LOCAL_KNOTS} knots)", ip * p.nq * p.N,
+                        ms_scan, ip, 1 if p.norm == W.NORM_L2 else 0, clocks)
+    e2e = None
+    if not args.no_e2e:
+        hX, hy, hQ = (torch.as_tensor(a).pin_memory() for a in (p.X, p.y, p.Q))
+        outs = {k: torch.empty(p.nq, dtype=torch.float32).pin_memory() for k in ("g", "lo", "hi")}
+        outs.update({k: torch.empty(p.nq, dtype=torch.int32).pin_memory() for k in ("idx_up", "idx_lo")})
+        m.set_timing_events(None, None)
+        dQ = torch.empty_like(Q)
+
+        def step_host():
+            m.clear()
+            m.add_host(hX, hy)
+            m.compute_local_lipschitz(LOCAL_KNOTS, LOCAL_SAMPLE, LOCAL_SEED)
+            dQ.copy_(hQ, non_blocking=True)
+            out = m.eval_local(dQ)
+            for k, v in out.items():
+                outs[k].copy_(v, non_blocking=True)
+
+        step_host()
+        torch.cuda.synchronize()
+        e2e_ms = []
+        for _ in range(args.steps):
+            ctx.flush()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step_host()
+            torch.cuda.synchronize()
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        ev_, tot = aggregate(p.nq * p.N * args.steps, sum(e2e_ms), device="cuda")
+        e2e = {"value": ev_, "unit": UNIT, "ms_per_step": tot / args.steps,
+               "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in (hX, hy, hQ)),
+               "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in outs.values())}
+    cpu = None
+    if ctx.rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_local_rate(p, args.cpu_seconds)[0]
+    knots = m.local_knots()
+    detail = {"table_ms": ms_table, "scan_ms": ms_scan,
+              "scan_gpairs_per_s": p.nq * p.N / (ms_scan / 1e3) / 1e9,
+              "table_gpairs_per_s": 2.0 * p.N * p.N / (ms_table / 1e3) / 1e9,
+              "knots": [float(v) for v in knots], "splits": m.tuning()["last_splits"], "sms": ctx.sms}
+    m.close()
+    config = {"workload": name, "d": p.d, "N": p.N, "Q": p.nq, "mon": None, "norms": [NNAME[p.norm]],
+              "knots": LOCAL_KNOTS, "sample_pairs": LOCAL_SAMPLE,
+              "step": "fit + local table (knot sample, two N^2 passes) + local eval of all queries",
+              "l2": "flushed before every timed step (256 MB write)"}
+    return ctx.line(value, total, args.steps, "f32", config, roof, cpu, e2e, clocks, launches, detail)
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -594,6 +712,8 @@ def run_ours(args):
         line = wl_single(ctx, w, [W.cluster_d16()], precisions=("tc_tf32",), with_est=False, flush=False)
     elif w == "grad_d8":
         line = wl_single(ctx, w, [W.grad_d8()], with_bwd=True)
+    elif w == "local_d4":
+        line = wl_local(ctx)
     else:
         line = wl_batch(ctx)
     if rank == 0:

@@ -56,7 +56,8 @@ typedef enum {
     LIP_ERR_CAPACITY = 5,     /* lip_add beyond the reserved capacity                       */
     LIP_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up (see lip_check)         */
     LIP_ERR_UNSUPPORTED = 7,  /* valid request this build does not handle                  */
-    LIP_ERR_NO_DEVICE = 8     /* no CUDA device visible                                     */
+    LIP_ERR_NO_DEVICE = 8,    /* no CUDA device visible                                     */
+    LIP_ERR_STATE = 9         /* call out of order (lip_eval_local before lip_local_fit)    */
 } lip_status;
 
 typedef enum { LIP_L1 = 1, LIP_L2 = 2, LIP_LINF = 3 } lip_norm;
@@ -211,6 +212,68 @@ LIP_API lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, i
  * stream. */
 LIP_API lip_status lip_estimate_M_noalloc(const float* X, const float* y, int64_t N, int32_t d,
                                           int32_t norm, const double* w, double* out, void* stream);
+
+/* ------------------------------------------------ local Lipschitz constants (Sec. 4.3) */
+/* compute_local_lipschitz() and values_local(query, model, k = 1) of Sec. 5.
+ *
+ * Every datum x^k gets a non-decreasing step function M_k(t) of the distance t from x^k,
+ * and the bounds of Eq. (upperlower) use it in place of M:
+ *   H_up(q) = min_k ( y^k + M_k(t_k) t_k ),  H_lo(q) = max_k ( y^k - M_k(t_k) t_k ),
+ *   t_k = dist(q, x^k),  g = (H_up + H_lo) / 2.
+ * M_k(t) = F_k for t <= d1_k, where d1_k is the distance to the nearest other datum and
+ * F_k = |y^k - y^(1)| / d1_k (the largest such ratio over data tied at d1_k).  Beyond d1_k,
+ * M_k(t) = Mtab_k[s] with s = #{i : T_i < t} and
+ *   Mtab_k[s] = max( F_k, max { |y^k - y^j| / d_kj : 0 < d_kj <= T_{s+1} } ),  T_{m+1} = +inf:
+ * the largest ratio over the data no farther than the next knot.  The knots T_1 < ... <
+ * T_m are common to all data.  dist is the symmetric weighted norm of the handle
+ * (|x_i - x'_i| w_i; L1, L2 or Linf).  Pairs at distance 0 are skipped.  The result
+ * interpolates the data.
+ *
+ * The table is exact: every distance and ratio that decides an entry is the IEEE double
+ * result of the definition above (each operation rounded once, coordinates in order),
+ * found by an FP32 screen with a rigorous error bound and FP64 re-computation of every
+ * pair the bound cannot rule out.  Handles: float data (LIP_FP32 or LIP_TC_TF32) without
+ * monotone coordinates, else LIP_ERR_UNSUPPORTED.  Adding or clearing data invalidates
+ * the table (LIP_ERR_STATE until the next fit).  N^2 work per fit (two passes). */
+
+/* Largest number of knots. */
+#define LIP_LOCAL_KNOTS_MAX 31
+/* Largest number of sampled pairs. */
+#define LIP_LOCAL_SAMPLE_MAX (1 << 20)
+
+/* Knots from a sample (Sec. 4.3: quantiles of the distribution of interpoint
+ * distances, approximated from a sample).  sample_pairs pairs (a_s, b_s) are drawn with
+ * SplitMix64 (Steele, Lea and Flood 2014): output c of the generator seeded with `seed`
+ * is mix(seed + (c + 1) * 0x9E3779B97F4A7C15), a_s = out(2s) mod N, b_s = out(2s + 1) mod N.
+ * Their positive distances, sorted, D_(1) <= ... <= D_(S'), give T_i = D_(ceil(i S' / nknots)),
+ * i = 1..nknots, with repeated values dropped (so m <= nknots; m = 0 when S' = 0).
+ * 0 <= nknots <= LIP_LOCAL_KNOTS_MAX, 0 <= sample_pairs <= LIP_LOCAL_SAMPLE_MAX.
+ * Synchronises the stream.  Errors: LIP_ERR_ARG (ranges, no data), LIP_ERR_UNSUPPORTED,
+ * LIP_ERR_OOM, LIP_ERR_CUDA. */
+LIP_API lip_status lip_local_fit(lip_handle h, int32_t nknots, int64_t sample_pairs, uint64_t seed,
+                                 void* stream);
+
+/* The same with the caller's knots: host array of nknots finite values > 0, strictly
+ * increasing (else LIP_ERR_ARG).  Synchronises the stream. */
+LIP_API lip_status lip_local_fit_knots(lip_handle h, const double* knots, int32_t nknots, void* stream);
+
+/* The knots in use (host array of at least LIP_LOCAL_KNOTS_MAX doubles; may be NULL) and
+ * their number m.  LIP_ERR_STATE without a current table. */
+LIP_API lip_status lip_local_knots(lip_handle h, double* knots, int32_t* nknots);
+
+/* Copies the exact table to device double arrays (each may be NULL): d1 [N], F [N]
+ * (d1 = +Inf and F = 0 for a datum without a neighbour at positive distance) and
+ * Mtab [N][m + 1], row-major.  Ordered on the stream. */
+LIP_API lip_status lip_local_table(lip_handle h, double* d1, double* F, double* Mtab, void* stream);
+
+/* The envelopes with the local constants.  Arguments, outputs and NaN handling as for
+ * lip_eval (float, device).  The scan runs in FP32 and picks the winning data; their
+ * bounds are then recomputed in FP64 with the exact table, so hi/lo are the exact values
+ * of the selected data.  The selection can differ from the exact one where two values are
+ * within FP32 rounding, or where a distance lies within FP32 rounding of one of the
+ * datum's knots (M_k jumps there).  LIP_ERR_STATE without a current table. */
+LIP_API lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi,
+                                  int32_t* idx_up, int32_t* idx_lo, void* stream);
 
 /* ---------------------------------------------------------------- differentiation */
 

@@ -91,11 +91,13 @@ class Oracle:
         lib.oracle_splitmix64.restype = u64
         lib.oracle_local_knots.argtypes = [P, i64, i32, i32, P, u64, i64, i32, P, P, P]
         lib.oracle_local_table.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, i32]
+        lib.oracle_local_table_rows.argtypes = [P, P, i64, i32, i32, P, P, i32, P, i64, P, P, P, i32]
         lib.oracle_eval_local.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, f64, P, P, P, P, P,
                                           P, P, i32]
         lib.oracle_local_terms.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, P, i32, P]
         for fn in (lib.oracle_eval, lib.oracle_estimate_M, lib.oracle_estimate_M_rows, lib.oracle_grad,
-                   lib.oracle_eval_k, lib.oracle_local_knots, lib.oracle_local_table, lib.oracle_eval_local,
+                   lib.oracle_eval_k, lib.oracle_local_knots, lib.oracle_local_table, lib.oracle_local_table_rows,
+                   lib.oracle_eval_local,
                    lib.oracle_local_terms):
             fn.restype = ctypes.c_int
         self.lib = lib
@@ -208,6 +210,21 @@ class Oracle:
             raise ValueError("oracle_local_table: bad arguments")
         return d1, F, Mtab
 
+    def local_table_rows(self, X, y, knots, rows, norm: int = NORM_L2, w=None, nthreads: Optional[int] = None):
+        """(d1, F, Mtab) of the data rows[i] only (row i of each output)."""
+        X, y, w = _f64(X), _f64(y), _f64(w)
+        T = _f64(np.asarray(knots, np.float64).reshape(-1))
+        rows = np.ascontiguousarray(rows, np.int64)
+        N, d = X.shape
+        m, n = T.shape[0], rows.shape[0]
+        d1, F = np.empty(n), np.empty(n)
+        Mtab = np.empty((n, m + 1))
+        rc = self.lib.oracle_local_table_rows(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(T), m, _ptr(rows), n,
+                                              _ptr(d1), _ptr(F), _ptr(Mtab), nthreads or default_threads())
+        if rc != 0:
+            raise ValueError("oracle_local_table_rows: bad arguments")
+        return d1, F, Mtab
+
     def evaluate_local(self, X, y, Q, knots, table, norm: int = NORM_L2, w=None, eta: float = 0.0,
                        nthreads: Optional[int] = None) -> EvalResult:
         """Envelopes with M replaced by M_k(dist); eta > 0 adds the amb_up / amb_lo flags."""
@@ -291,3 +308,7 @@ def evaluate_local(*a, **k):
 
 def local_terms(*a, **k):
     return default().local_terms(*a, **k)
+
+
+def local_table_rows(*a, **k):
+    return default().local_table_rows(*a, **k)

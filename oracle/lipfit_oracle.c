@@ -433,14 +433,15 @@ int oracle_local_knots(const double* X, int64_t N, int d, int norm, const double
 
 typedef struct {
     const double* X; const double* y; int64_t N; int d; int norm; const double* w;
-    const double* T; int m; int64_t k0, k1;
+    const double* T; int m; int64_t k0, k1; const int64_t* rows;
     double *d1, *F, *Mtab;
 } ltab_job;
 
 static void* ltab_worker(void* arg) {
     ltab_job* J = (ltab_job*)arg;
     const int d = J->d;
-    for (int64_t k = J->k0; k < J->k1; k++) {
+    for (int64_t o = J->k0; o < J->k1; o++) {
+        const int64_t k = J->rows ? J->rows[o] : o;       /* datum of output row o */
         const double* xk = J->X + k * d;
         double d1 = INFINITY, F = 0.0;
         for (int64_t j = 0; j < J->N; j++) {                 /* nearest distance and its ratio */
@@ -450,7 +451,7 @@ static void* ltab_worker(void* arg) {
             if (dd < d1) { d1 = dd; F = r; }
             else if (dd == d1 && r > F) F = r;
         }
-        double* row = J->Mtab + k * (J->m + 1);
+        double* row = J->Mtab + o * (J->m + 1);
         for (int s = 0; s <= J->m; s++) row[s] = F;
         for (int64_t j = 0; j < J->N; j++) {                 /* every segment whose knot covers d_kj */
             double dd = sym_dist(xk, J->X + j * d, d, J->norm, J->w);
@@ -461,26 +462,37 @@ static void* ltab_worker(void* arg) {
                 if (dd <= knot && r > row[s]) row[s] = r;
             }
         }
-        J->d1[k] = d1;
-        J->F[k] = F;
+        J->d1[o] = d1;
+        J->F[o] = F;
     }
     return NULL;
 }
 
-/* d1 [N], F [N] and Mtab [N][m + 1] for knots T [m] (strictly increasing). */
-int oracle_local_table(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
-                       const double* T, int m, double* d1, double* F, double* Mtab, int nthreads) {
-    if (N < 1 || d < 1 || norm < 1 || norm > 3 || m < 0) return 1;
-    nthreads = clamp_threads(nthreads, N);
+/* d1, F and Mtab [.][m + 1] for knots T [m] (strictly increasing): for every datum
+ * (rows = NULL, nrows = N) or for the data rows[0..nrows) only. */
+int oracle_local_table_rows(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
+                            const double* T, int m, const int64_t* rows, int64_t nrows,
+                            double* d1, double* F, double* Mtab, int nthreads) {
+    if (N < 1 || d < 1 || norm < 1 || norm > 3 || m < 0 || nrows < 0) return 1;
+    if (rows)
+        for (int64_t o = 0; o < nrows; o++) if (rows[o] < 0 || rows[o] >= N) return 1;
+    if (nrows == 0) return 0;
+    nthreads = clamp_threads(nthreads, nrows);
     pthread_t th[256];
     ltab_job jobs[256];
     for (int t = 0; t < nthreads; t++) {
-        ltab_job j = {X, y, N, d, norm, w, T, m, N * t / nthreads, N * (t + 1) / nthreads, d1, F, Mtab};
+        ltab_job j = {X, y, N, d, norm, w, T, m, nrows * t / nthreads, nrows * (t + 1) / nthreads, rows,
+                      d1, F, Mtab};
         jobs[t] = j;
         pthread_create(&th[t], NULL, ltab_worker, &jobs[t]);
     }
     for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
     return 0;
+}
+
+int oracle_local_table(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
+                       const double* T, int m, double* d1, double* F, double* Mtab, int nthreads) {
+    return oracle_local_table_rows(X, y, N, d, norm, w, T, m, NULL, N, d1, F, Mtab, nthreads);
 }
 
 /* M_k(t) from datum k's table row. */

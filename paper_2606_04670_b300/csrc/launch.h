@@ -96,4 +96,74 @@ int backward_blocks(int64_t nq);
 cudaError_t launch_backward(int elem_bytes, const BwdParams& P, int64_t N, void* grad_y, double* grad_M,
                             cudaStream_t st);
 
+// ------------------------------------------------ local Lipschitz constants (Sec. 4.3)
+
+constexpr int LOC_KNOTS = 32;        // table stride: up to 31 knots and the last segment
+
+struct LocMeta {
+    int npos;                        // positive sampled distances
+    int m;                           // distinct knots
+    unsigned rbits;                  // largest |scaled coordinate| (float bits)
+    int pad;
+};
+
+struct LocalParams {
+    const float* X0;                 // caller's data [N][d]
+    const float* y0;
+    int64_t N, npad;
+    int d, pr, norm, m;              // m: knots requested (sampled) or given
+    double w[D_MAX];
+    int64_t S;                       // sampled pairs
+    uint64_t seed;
+    float* rec;                      // [npad][pr]: w-scaled coordinates, y, d1 (float), F (float)
+    float* mt;                       // [npad][LOC_KNOTS]: FP32 table (pass 1: lower bounds)
+    double* mt64;                    // [N][LOC_KNOTS]: exact table
+    double* d1;                      // [N]
+    double* F;                       // [N]
+    double* T64;                     // [LOC_KNOTS] knots, +inf padded
+    float* Tf;                       // [3][LOC_KNOTS] knots rounded to nearest, down, up
+    double* raw;                     // [LOC_KNOTS] quantile picks (or the given knots)
+    double* sample;                  // [S] sampled distances
+    float* ubound;                   // [N] pass-1 upper bounds of d1
+    LocMeta* meta;
+};
+
+struct LocalScanParams {
+    const float* Q;
+    int64_t nq;
+    int d, pr;
+    double w[D_MAX];
+    const float* rec;
+    const float* mt;
+    const float* Tf;
+    int64_t npad, points_per_split;
+    void* partial;                   // [nsplit][nq] PartialRec<float>
+};
+
+struct LocalMergeParams {
+    const float* Q;
+    int64_t nq;
+    int d, norm, m, nsplit;
+    double w[D_MAX];
+    const float* X0;
+    const float* y0;
+    const double* d1;
+    const double* F;
+    const double* mt64;
+    const double* T64;
+    const void* partial;
+    float *g, *lo, *hi;
+    int32_t *idx_up, *idx_lo;
+};
+
+int local_record_floats(int d);
+int64_t local_pad(int64_t N);
+int local_scan_tile();
+int local_threads();
+cudaError_t launch_local_layout(const LocalParams& P, cudaStream_t st);
+cudaError_t launch_local_knots(const LocalParams& P, bool sampled, cudaStream_t st);
+cudaError_t launch_local_table(const LocalParams& P, cudaStream_t st);
+cudaError_t launch_local_eval(int norm, const LocalScanParams& S, int gx, int nsplit, const LocalMergeParams& M,
+                              cudaStream_t st);
+
 }  // namespace lip

@@ -1,0 +1,459 @@
+// Local Lipschitz constants (Sec. 4.3): per-datum step functions M_k(t) and the
+// evaluation of Eq. (upperlower) with M replaced by M_k(dist(x, x^k)).
+//
+//   M_k(t) = F_k                   for t <= d1_k (nearest other datum at d1_k, F_k the
+//                                  largest |y^k - y^j| / d1_k among those at d1_k)
+//   M_k(t) = Mtab_k[#{i : T_i < t}] beyond it, Mtab_k[s] = max(F_k, max |y^k - y^j| / d_kj
+//                                  over the data with 0 < d_kj <= T_{s+1}), T_{m+1} = +inf
+//
+// with the knots T_1 < ... < T_m the inverted-CDF quantiles at i/m of the positive
+// distances of S pairs drawn by SplitMix64 (output c of the generator seeded with
+// `seed` is mix(seed + (c + 1) * golden gamma); pair s is (out(2s) mod N, out(2s+1) mod N)).
+// Distances are the symmetric weighted norm (|x_i - x'_i| * w_i, then L1 / L2 / Linf).
+//
+// The decisions that pick a table entry (which segment a distance falls in, which
+// datum is nearest) are integer outcomes of floating-point comparisons, so the table
+// is computed with the exact FP64 distance and ratio of every pair that can matter:
+//  * loc_dist64 takes |a_i - b_i|, multiplies by w_i, and sums (L1), sums squares and
+//    takes the correctly rounded square root (L2) or maxes (Linf), in coordinate order,
+//    every operation a separately rounded IEEE double operation; the ratio is a correctly
+//    rounded division.  Any FP64 implementation of those definitions gives the same bits.
+//  * The N^2 screen runs in FP32 with a bound |d32 - d64| <= e_rel d32 + e_abs, e_rel =
+//    2^-22 (d + 2), e_abs = e_rel * R (R the largest scaled coordinate): the coordinates
+//    are scaled and rounded once (2^-24 |w x|), differenced (2^-24 of the difference) and
+//    accumulated ((d + 1) roundings), which the factor 4 over 2^-24 covers with room.
+//    Pass 1 gathers, per datum, an upper bound U_k >= d1_k and per-segment lower bounds
+//    Lb_k[s] <= Mtab_k[s].  Pass 2 recomputes in FP64 every pair whose distance may be
+//    within U_k (a nearest-neighbour candidate) or whose ratio may exceed Lb_k at the
+//    lowest segment its distance may fall in; no other pair can be a nearest neighbour
+//    or attain a table entry, so the table is the exact FP64 one.
+// The evaluation scan runs in FP32 from the same layout; the winners are re-evaluated in
+// FP64 with the exact table.
+#include "launch.h"
+
+namespace lip {
+
+namespace {
+
+constexpr int LOC_THREADS = 128;
+constexpr int LOC_TILE = 128;       // data points per shared-memory tile (table passes)
+constexpr int LOC_SCAN_TILE = 64;   // data points per shared-memory tile (evaluation)
+constexpr int LOC_RANK_TILE = 1024;
+
+__device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t c) {
+    uint64_t z = seed + (c + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Exact symmetric distance: every step one IEEE double operation, in coordinate order.
+__device__ __forceinline__ double loc_dist64(const float* a, const float* b, int d, int norm, const double* w) {
+    double acc = 0.0;
+    for (int i = 0; i < d; ++i) {
+        const double v = __dmul_rn(fabs(__dsub_rn((double)a[i], (double)b[i])), w[i]);
+        if (norm == LIP_L1) acc = __dadd_rn(acc, v);
+        else if (norm == LIP_L2) acc = __dadd_rn(acc, __dmul_rn(v, v));
+        else if (v > acc) acc = v;
+    }
+    return norm == LIP_L2 ? __dsqrt_rn(acc) : acc;
+}
+
+// #{i : T[i] < v} for a sorted 32-entry table whose unused tail is +inf.
+__device__ __forceinline__ int knot_count(const float* T, float v) {
+    int c = 0;
+    c += T[c + 15] < v ? 16 : 0;
+    c += T[c + 7] < v ? 8 : 0;
+    c += T[c + 3] < v ? 4 : 0;
+    c += T[c + 1] < v ? 2 : 0;
+    c += T[c] < v ? 1 : 0;
+    return c;
+}
+
+template <int NORM>
+__device__ __forceinline__ float dist32(const float* xk, const float* xj, int d) {
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < D_MAX; ++i) {
+        if (i >= d) break;
+        const float t = xk[i] - xj[i];
+        if (NORM == LIP_L1) acc += fabsf(t);
+        else if (NORM == LIP_L2) acc = fmaf(t, t, acc);
+        else acc = fmaxf(acc, fabsf(t));
+    }
+    return acc;
+}
+
+// ------------------------------------------------------------------ layout
+
+__global__ void loc_layout_kernel(const LocalParams P) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.npad) return;
+    float* r = P.rec + k * P.pr;
+    float amax = 0.f;
+    if (k < P.N) {
+        const float* x = P.X0 + k * P.d;
+        for (int i = 0; i < P.d; ++i) {
+            const float v = (float)(P.w[i] * (double)x[i]);
+            r[i] = v;
+            amax = fmaxf(amax, fabsf(v));
+        }
+        r[P.d] = P.y0[k];
+    } else {
+        for (int i = 0; i < P.d; ++i) r[i] = 0.f;
+        r[P.d] = __int_as_float(0x7fc00000);          // padding: y = NaN is never selected
+    }
+    r[P.d + 1] = INFINITY;
+    r[P.d + 2] = 0.f;
+    const unsigned act = __activemask();
+    const unsigned m = __reduce_max_sync(act, __float_as_uint(amax));   // |v| orders as its bits
+    if ((int)(threadIdx.x & 31) == __ffs(act) - 1) atomicMax(&P.meta->rbits, m);
+}
+
+// ------------------------------------------------------------------ knots
+
+__global__ void loc_sample_kernel(const LocalParams P) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= P.S) return;
+    const uint64_t a = splitmix64(P.seed, 2 * (uint64_t)s) % (uint64_t)P.N;
+    const uint64_t b = splitmix64(P.seed, 2 * (uint64_t)s + 1) % (uint64_t)P.N;
+    const double dd = loc_dist64(P.X0 + a * P.d, P.X0 + b * P.d, P.d, P.norm, P.w);
+    P.sample[s] = dd;
+    if (dd > 0.0) atomicAdd(&P.meta->npos, 1);
+}
+
+// Rank of every positive sample among the positive samples (ties by sample index), and
+// the samples at the quantile positions ceil(i S' / m), i = 1..m, into raw[i - 1].
+__global__ void __launch_bounds__(LOC_THREADS) loc_rank_kernel(const LocalParams P) {
+    __shared__ unsigned long long tile[LOC_RANK_TILE];
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long v = s < P.S ? (unsigned long long)__double_as_longlong(P.sample[s]) : 0ull;
+    int64_t rank = 0;
+    for (int64_t t0 = 0; t0 < P.S; t0 += LOC_RANK_TILE) {
+        const int n = (int)lmin(LOC_RANK_TILE, P.S - t0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            tile[i] = (unsigned long long)__double_as_longlong(P.sample[t0 + i]);
+        __syncthreads();
+        // positive doubles order as their bit patterns; 0 (bits 0) is not a sample
+        for (int i = 0; i < n; ++i) {
+            const unsigned long long u = tile[i];
+            rank += (u != 0ull && (u < v || (u == v && t0 + i < s))) ? 1 : 0;
+        }
+    }
+    if (s >= P.S || v == 0ull) return;
+    const int64_t npos = P.meta->npos;
+    for (int i = 1; i <= P.m; ++i)
+        if (((int64_t)i * npos + P.m - 1) / P.m - 1 == rank) P.raw[i - 1] = __longlong_as_double((long long)v);
+}
+
+// Distinct knots (raw is non-decreasing) into T64, padded with +inf, and their float
+// roundings: to nearest (evaluation), down and up (the screen's bounds).
+__global__ void loc_knots_kernel(const LocalParams P, int sampled) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int n = 0;
+    const int m = (sampled && P.meta->npos == 0) ? 0 : P.m;
+    for (int i = 0; i < m; ++i) {
+        const double v = P.raw[i];
+        if (n == 0 || v > P.T64[n - 1]) P.T64[n++] = v;
+    }
+    P.meta->m = n;
+    for (int i = 0; i < LOC_KNOTS; ++i) {
+        const double v = i < n ? P.T64[i] : INFINITY;
+        if (i >= n) P.T64[i] = INFINITY;
+        P.Tf[i] = __double2float_rn(v);
+        P.Tf[LOC_KNOTS + i] = __double2float_rd(v);
+        P.Tf[2 * LOC_KNOTS + i] = __double2float_ru(v);
+    }
+}
+
+// ------------------------------------------------------------------ table, pass 1
+
+template <int NORM>
+__global__ void __launch_bounds__(LOC_THREADS) loc_pass1_kernel(const LocalParams P) {
+    extern __shared__ float4 sm4[];
+    float* tile = reinterpret_cast<float*>(sm4);                    // [LOC_TILE][pr]
+    float* A = tile + LOC_TILE * P.pr;                              // [32][LOC_THREADS]
+    float* Tdn = A + LOC_KNOTS * LOC_THREADS;                       // [32]
+    const int tid = threadIdx.x;
+    const int64_t k = (int64_t)blockIdx.x * LOC_THREADS + tid;
+    const bool valid = k < P.N;
+    float xk[D_MAX];
+    float yk = 0.f;
+#pragma unroll
+    for (int i = 0; i < D_MAX; ++i) xk[i] = (valid && i < P.d) ? P.rec[k * P.pr + i] : 0.f;
+    if (valid) yk = P.rec[k * P.pr + P.d];
+    for (int s = 0; s < LOC_KNOTS; ++s) A[s * LOC_THREADS + tid] = 0.f;
+    if (tid < LOC_KNOTS) Tdn[tid] = P.Tf[LOC_KNOTS + tid];
+    const float R = __uint_as_float(P.meta->rbits);
+    const float e_rel = ldexpf((float)(P.d + 2), -22);
+    const float e_abs = e_rel * R;
+    const float lo_margin = 1.f - ldexpf(1.f, -20);
+    float U = INFINITY;
+    for (int64_t j0 = 0; j0 < P.N; j0 += LOC_TILE) {
+        const int n = (int)lmin(LOC_TILE, P.N - j0);
+        __syncthreads();
+        const float4* src = reinterpret_cast<const float4*>(P.rec + j0 * P.pr);
+        for (int i = tid; i < n * P.pr / 4; i += LOC_THREADS) sm4[i] = src[i];
+        __syncthreads();
+        if (!valid) continue;
+        for (int j = 0; j < n; ++j) {
+            const float* xj = tile + j * P.pr;
+            float d32 = dist32<NORM>(xk, xj, P.d);
+            if (NORM == LIP_L2) d32 = sqrtf(d32);
+            const float del = fmaf(e_rel, d32, e_abs);
+            if (d32 > del) {                          // surely a positive distance
+                const float hi = d32 + 2.f * del;
+                U = fminf(U, hi);
+                const int s = knot_count(Tdn, hi);    // the highest segment d64 may fall in
+                const float dy = fabsf(yk - xj[P.d]);
+                const float rlo = dy * rcp_approx(hi) * lo_margin;
+                float* a = A + s * LOC_THREADS + tid;
+                *a = fmaxf(*a, rlo);
+            }
+        }
+    }
+    if (!valid) return;
+    P.ubound[k] = U;
+    float run = 0.f;
+    for (int s = 0; s < LOC_KNOTS; ++s) {
+        run = fmaxf(run, A[s * LOC_THREADS + tid]);
+        P.mt[k * LOC_KNOTS + s] = run;                // Lb_k[s] until pass 2 overwrites it
+    }
+}
+
+// ------------------------------------------------------------------ table, pass 2
+
+template <int NORM>
+__global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParams P) {
+    extern __shared__ float4 sm4[];
+    float* tile = reinterpret_cast<float*>(sm4);                    // [LOC_TILE][pr]
+    float* Lb = tile + LOC_TILE * P.pr;                             // [32][LOC_THREADS]
+    float* Tup = Lb + LOC_KNOTS * LOC_THREADS;                      // [32]
+    __shared__ double T64[LOC_KNOTS];
+    const int tid = threadIdx.x;
+    const int64_t k = (int64_t)blockIdx.x * LOC_THREADS + tid;
+    const bool valid = k < P.N;
+    float xk[D_MAX];
+    float yk = 0.f;
+#pragma unroll
+    for (int i = 0; i < D_MAX; ++i) xk[i] = (valid && i < P.d) ? P.rec[k * P.pr + i] : 0.f;
+    float U = 0.f;
+    if (valid) {
+        yk = P.rec[k * P.pr + P.d];
+        U = P.ubound[k];
+        for (int s = 0; s < LOC_KNOTS; ++s) Lb[s * LOC_THREADS + tid] = P.mt[k * LOC_KNOTS + s];
+    }
+    if (tid < LOC_KNOTS) {
+        Tup[tid] = P.Tf[2 * LOC_KNOTS + tid];
+        T64[tid] = P.T64[tid];
+    }
+    const int m = P.meta->m;
+    const float R = __uint_as_float(P.meta->rbits);
+    const float e_rel = ldexpf((float)(P.d + 2), -22);
+    const float e_abs = e_rel * R;
+    const float up_margin = 1.f + ldexpf(1.f, -20);
+    const float lo_margin = 1.f - ldexpf(1.f, -20);
+    const float* xk0 = P.X0 + k * P.d;
+    const double yk64 = valid ? (double)P.y0[k] : 0.0;
+    double d1 = INFINITY, F = 0.0;
+    double E[LOC_KNOTS];
+    for (int s = 0; s < LOC_KNOTS; ++s) E[s] = 0.0;
+    for (int64_t j0 = 0; j0 < P.N; j0 += LOC_TILE) {
+        const int n = (int)lmin(LOC_TILE, P.N - j0);
+        __syncthreads();
+        const float4* src = reinterpret_cast<const float4*>(P.rec + j0 * P.pr);
+        for (int i = tid; i < n * P.pr / 4; i += LOC_THREADS) sm4[i] = src[i];
+        __syncthreads();
+        if (!valid) continue;
+        for (int j = 0; j < n; ++j) {
+            const float* xj = tile + j * P.pr;
+            float d32 = dist32<NORM>(xk, xj, P.d);
+            if (NORM == LIP_L2) d32 = sqrtf(d32);
+            const float del = fmaf(e_rel, d32, e_abs);
+            const float lo = d32 - 2.f * del;         // d64 >= lo
+            bool cand = lo <= U;                      // may be (tied) nearest
+            if (!cand) {
+                const int s = knot_count(Tup, lo);    // the lowest segment d64 may fall in
+                const float dy = fabsf(yk - xj[P.d]);
+                cand = dy * up_margin > Lb[s * LOC_THREADS + tid] * lo * lo_margin;
+            }
+            if (!cand) continue;
+            const int64_t jj = j0 + j;
+            const double d64 = loc_dist64(xk0, P.X0 + jj * P.d, P.d, P.norm, P.w);
+            if (!(d64 > 0.0)) continue;
+            const double r = __ddiv_rn(fabs(__dsub_rn(yk64, (double)P.y0[jj])), d64);
+            if (d64 < d1) { d1 = d64; F = r; }
+            else if (d64 == d1 && r > F) F = r;
+            int s = 0;
+            while (s < m && T64[s] < d64) ++s;
+            E[s] = fmax(E[s], r);
+        }
+    }
+    if (!valid) return;
+    P.d1[k] = d1;
+    P.F[k] = F;
+    P.rec[k * P.pr + P.d + 1] = (float)d1;
+    P.rec[k * P.pr + P.d + 2] = (float)F;
+    double run = F;
+    for (int s = 0; s < LOC_KNOTS; ++s) {
+        if (s <= m) run = fmax(run, E[s]);
+        P.mt64[k * LOC_KNOTS + s] = run;
+        P.mt[k * LOC_KNOTS + s] = (float)run;
+    }
+}
+
+// ------------------------------------------------------------------ evaluation
+
+template <int NORM>
+__global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanParams P) {
+    __shared__ float4 rec4[LOC_SCAN_TILE * (D_MAX + 4) / 4];
+    __shared__ float4 mt4[LOC_SCAN_TILE * LOC_KNOTS / 4];
+    __shared__ float Tn[LOC_KNOTS];
+    const float* rec = reinterpret_cast<const float*>(rec4);
+    const float* mt = reinterpret_cast<const float*>(mt4);
+    const int tid = threadIdx.x;
+    const int64_t qi = (int64_t)blockIdx.x * LOC_THREADS + tid;
+    const int split = blockIdx.y;
+    const bool valid = qi < P.nq;
+    float q[D_MAX];
+#pragma unroll
+    for (int i = 0; i < D_MAX; ++i) q[i] = (valid && i < P.d) ? (float)(P.w[i] * (double)P.Q[qi * P.d + i]) : 0.f;
+    if (tid < LOC_KNOTS) Tn[tid] = P.Tf[tid];
+    float bu = INFINITY, bl = -INFINITY;
+    int iu = -1, il = -1;
+    const int64_t j_begin = (int64_t)split * P.points_per_split;
+    const int64_t j_end = lmin(j_begin + P.points_per_split, P.npad);
+    for (int64_t j0 = j_begin; j0 < j_end; j0 += LOC_SCAN_TILE) {
+        __syncthreads();
+        const float4* rs = reinterpret_cast<const float4*>(P.rec + j0 * P.pr);
+        for (int i = tid; i < LOC_SCAN_TILE * P.pr / 4; i += LOC_THREADS) rec4[i] = rs[i];
+        const float4* ms = reinterpret_cast<const float4*>(P.mt + j0 * LOC_KNOTS);
+        for (int i = tid; i < LOC_SCAN_TILE * LOC_KNOTS / 4; i += LOC_THREADS) mt4[i] = ms[i];
+        __syncthreads();
+#pragma unroll 2
+        for (int j = 0; j < LOC_SCAN_TILE; ++j) {
+            const float* xj = rec + j * P.pr;
+            float t = dist32<NORM>(q, xj, P.d);
+            if (NORM == LIP_L2) t = sqrt_approx(t);
+            const int s = knot_count(Tn, t);
+            const float M = t <= xj[P.d + 1] ? xj[P.d + 2] : mt[j * LOC_KNOTS + s];
+            const float y = xj[P.d];
+            const float vu = fmaf(M, t, y), vl = fmaf(-M, t, y);
+            const int idx = (int)(j0 + j);
+            if (vu < bu) { bu = vu; iu = idx; }
+            if (vl > bl) { bl = vl; il = idx; }
+        }
+    }
+    if (!valid) return;
+    PartialRec<float> r;
+    r.vu = bu; r.iu = iu; r.vl = bl; r.il = il;
+    static_cast<PartialRec<float>*>(P.partial)[(int64_t)split * P.nq + qi] = r;
+}
+
+__device__ __forceinline__ double local_M64(const LocalMergeParams& P, int64_t k, double t) {
+    if (t <= P.d1[k]) return P.F[k];
+    int s = 0;
+    while (s < P.m && P.T64[s] < t) ++s;
+    return P.mt64[k * LOC_KNOTS + s];
+}
+
+__global__ void loc_merge_kernel(const LocalMergeParams P) {
+    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= P.nq) return;
+    float bu = 0.f, bl = 0.f;
+    int iu = -1, il = -1;
+    const PartialRec<float>* part = static_cast<const PartialRec<float>*>(P.partial);
+    for (int s = 0; s < P.nsplit; ++s) {
+        const PartialRec<float> r = part[(int64_t)s * P.nq + qi];
+        if (r.iu >= 0 && (iu < 0 || r.vu < bu)) { bu = r.vu; iu = r.iu; }
+        if (r.il >= 0 && (il < 0 || r.vl > bl)) { bl = r.vl; il = r.il; }
+    }
+    const float* q = P.Q + qi * P.d;
+    bool finite = true;
+    for (int i = 0; i < P.d; ++i) finite = finite && isfinite(q[i]);
+    double hi, lo;
+    if (!finite || iu < 0 || il < 0) {
+        hi = lo = __longlong_as_double(0x7ff8000000000000ll);
+        iu = il = -1;
+    } else {
+        const double tu = loc_dist64(q, P.X0 + (int64_t)iu * P.d, P.d, P.norm, P.w);
+        const double tl = loc_dist64(q, P.X0 + (int64_t)il * P.d, P.d, P.norm, P.w);
+        hi = __dadd_rn((double)P.y0[iu], __dmul_rn(local_M64(P, iu, tu), tu));
+        lo = __dsub_rn((double)P.y0[il], __dmul_rn(local_M64(P, il, tl), tl));
+    }
+    if (P.g) P.g[qi] = (float)(0.5 * (hi + lo));
+    if (P.lo) P.lo[qi] = (float)lo;
+    if (P.hi) P.hi[qi] = (float)hi;
+    if (P.idx_up) P.idx_up[qi] = iu;
+    if (P.idx_lo) P.idx_lo[qi] = il;
+}
+
+size_t pass_smem(int pr) { return ((size_t)LOC_TILE * pr + LOC_KNOTS * LOC_THREADS + LOC_KNOTS) * sizeof(float); }
+
+}  // namespace
+
+int local_record_floats(int d) { return (d + 3 + 3) / 4 * 4; }
+int64_t local_pad(int64_t N) { return (N + LOC_TILE - 1) / LOC_TILE * LOC_TILE; }
+int local_scan_tile() { return LOC_SCAN_TILE; }
+int local_threads() { return LOC_THREADS; }
+
+cudaError_t launch_local_layout(const LocalParams& P, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((P.npad + 255) / 256);
+    loc_layout_kernel<<<blocks, 256, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_local_knots(const LocalParams& P, bool sampled, cudaStream_t st) {
+    if (sampled && P.S > 0) {
+        const unsigned blocks = (unsigned)((P.S + LOC_THREADS - 1) / LOC_THREADS);
+        loc_sample_kernel<<<blocks, LOC_THREADS, 0, st>>>(P);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        loc_rank_kernel<<<blocks, LOC_THREADS, 0, st>>>(P);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    loc_knots_kernel<<<1, 32, 0, st>>>(P, sampled ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <int NORM>
+static cudaError_t table_norm(const LocalParams& P, cudaStream_t st) {
+    const size_t smem = pass_smem(P.pr);
+    cudaError_t e = cudaFuncSetAttribute(loc_pass1_kernel<NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(loc_pass2_kernel<NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((P.N + LOC_THREADS - 1) / LOC_THREADS);
+    loc_pass1_kernel<NORM><<<blocks, LOC_THREADS, smem, st>>>(P);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    loc_pass2_kernel<NORM><<<blocks, LOC_THREADS, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_local_table(const LocalParams& P, cudaStream_t st) {
+    if (P.norm == LIP_L1) return table_norm<LIP_L1>(P, st);
+    if (P.norm == LIP_L2) return table_norm<LIP_L2>(P, st);
+    return table_norm<LIP_LINF>(P, st);
+}
+
+cudaError_t launch_local_eval(int norm, const LocalScanParams& S, int gx, int nsplit, const LocalMergeParams& M,
+                              cudaStream_t st) {
+    if (nsplit > 0) {
+        const dim3 grid((unsigned)gx, (unsigned)nsplit);
+        if (norm == LIP_L1) loc_scan_kernel<LIP_L1><<<grid, LOC_THREADS, 0, st>>>(S);
+        else if (norm == LIP_L2) loc_scan_kernel<LIP_L2><<<grid, LOC_THREADS, 0, st>>>(S);
+        else loc_scan_kernel<LIP_LINF><<<grid, LOC_THREADS, 0, st>>>(S);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned gm = (unsigned)((M.nq + 255) / 256);
+    loc_merge_kernel<<<gm, 256, 0, st>>>(M);
+    return cudaGetLastError();
+}
+
+}  // namespace lip

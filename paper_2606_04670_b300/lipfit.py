@@ -24,10 +24,12 @@ LIB_PATH = os.path.join(_HERE, "liblipfit.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "lipfit.h")
 
 LIP_OK, LIP_ERR_ARG, LIP_ERR_NONFINITE, LIP_ERR_OOM, LIP_ERR_CUDA = 0, 1, 2, 3, 4
-LIP_ERR_CAPACITY, LIP_ERR_TIMEOUT, LIP_ERR_UNSUPPORTED, LIP_ERR_NO_DEVICE = 5, 6, 7, 8
+LIP_ERR_CAPACITY, LIP_ERR_TIMEOUT, LIP_ERR_UNSUPPORTED, LIP_ERR_NO_DEVICE, LIP_ERR_STATE = 5, 6, 7, 8, 9
 LIP_L1, LIP_L2, LIP_LINF = 1, 2, 3
 LIP_FP32, LIP_FP64, LIP_TC_BF16, LIP_TC_TF32 = 0, 1, 2, 3
 LIP_NOALLOC_N_MAX = 32768
+LIP_LOCAL_KNOTS_MAX = 31
+LIP_LOCAL_SAMPLE_MAX = 1 << 20
 NORMS = {"L1": LIP_L1, "L2": LIP_L2, "Linf": LIP_LINF, "LINF": LIP_LINF,
          LIP_L1: LIP_L1, LIP_L2: LIP_L2, LIP_LINF: LIP_LINF}
 PRECISIONS = {"fp32": LIP_FP32, "fp64": LIP_FP64, "tc_bf16": LIP_TC_BF16, "tc_tf32": LIP_TC_TF32,
@@ -89,6 +91,11 @@ def _load():
         "lip_batch_info": [H, P, P, P, P],
         "lip_batch_check": [H, P],
         "lip_batch_set_timing_events": [H, P, P],
+        "lip_local_fit": [H, i32, i64, ctypes.c_uint64, P],
+        "lip_local_fit_knots": [H, P, i32, P],
+        "lip_local_knots": [H, P, P],
+        "lip_local_table": [H, P, P, P, P],
+        "lip_eval_local": [H, P, i64, P, P, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -193,6 +200,29 @@ def lip_eval(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream=0):
 
 def lip_eval_k(h, Q_ptr, nq, k, wk_ptr, g, lo, hi, idx_up, idx_lo, stream=0):
     return _lib.lip_eval_k(h, Q_ptr, nq, k, wk_ptr, g, lo, hi, idx_up, idx_lo, stream)
+
+
+def lip_local_fit(h, nknots, sample_pairs, seed, stream=0):
+    return _lib.lip_local_fit(h, nknots, sample_pairs, seed & (2**64 - 1), stream)
+
+
+def lip_local_fit_knots(h, knots_ptr, nknots, stream=0):
+    return _lib.lip_local_fit_knots(h, knots_ptr, nknots, stream)
+
+
+def lip_local_knots(h):
+    buf = (ctypes.c_double * LIP_LOCAL_KNOTS_MAX)()
+    n = ctypes.c_int32()
+    s = _lib.lip_local_knots(h, buf, ctypes.byref(n))
+    return s, list(buf[:n.value]) if s == LIP_OK else []
+
+
+def lip_local_table(h, d1, F, Mtab, stream=0):
+    return _lib.lip_local_table(h, d1, F, Mtab, stream)
+
+
+def lip_eval_local(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream=0):
+    return _lib.lip_eval_local(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream)
 
 
 def lip_eval_host(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream=0):
@@ -400,6 +430,54 @@ class LipFit:
     def values(self, Q):
         """g at the query points (Sec. 5: values(query, LC, model, k=1))."""
         return self.eval(Q, need=("g",))["g"]
+
+    # ------------------------------------------- local Lipschitz constants (Sec. 4.3)
+    def compute_local_lipschitz(self, nknots: int = 16, sample_pairs: int = 32768, seed: int = 0, knots=None):
+        """Per-datum step functions M_k(t) (lip_local_fit, or lip_local_fit_knots with
+        explicit knots); returns the knots in use."""
+        if knots is None:
+            _check(_lib.lip_local_fit(self.h, int(nknots), int(sample_pairs), int(seed) & (2**64 - 1),
+                                      _stream_ptr()), "lip_local_fit")
+        else:
+            k = np.ascontiguousarray(np.asarray(knots, np.float64).reshape(-1))
+            _check(_lib.lip_local_fit_knots(self.h, k.ctypes.data if k.size else None, int(k.size), _stream_ptr()),
+                   "lip_local_fit_knots")
+        return self.local_knots()
+
+    def local_knots(self):
+        s, k = lip_local_knots(self.h)
+        _check(s, "lip_local_knots")
+        return np.array(k, np.float64)
+
+    def local_table(self):
+        """(d1 [N], F [N], Mtab [N, m+1]) as float64 CUDA tensors."""
+        torch = _torch()
+        m = self.local_knots().size
+        N = self.N
+        d1 = torch.empty(N, device="cuda", dtype=torch.float64)
+        F = torch.empty(N, device="cuda", dtype=torch.float64)
+        Mtab = torch.empty((N, m + 1), device="cuda", dtype=torch.float64)
+        _check(_lib.lip_local_table(self.h, d1.data_ptr(), F.data_ptr(), Mtab.data_ptr(), _stream_ptr()),
+               "lip_local_table")
+        return d1, F, Mtab
+
+    def eval_local(self, Q, need=("g", "lo", "hi", "idx_up", "idx_lo")):
+        """Envelopes with the local constants (lip_eval_local): dict of CUDA tensors."""
+        torch = _torch()
+        Q = self._dev(Q)
+        nq = Q.shape[0]
+        out = {}
+        for key in need:
+            dt = torch.int32 if key.startswith("idx") else self.dtype
+            out[key] = torch.empty(nq, device="cuda", dtype=dt)
+        _check(_lib.lip_eval_local(self.h, Q.data_ptr(), nq, *[_ptr(out.get(k)) for k in ("g", "lo", "hi", "idx_up",
+                                                                                           "idx_lo")],
+                                   _stream_ptr()), "lip_eval_local")
+        return out
+
+    def values_local(self, Q):
+        """g with the local constants (Sec. 5: values_local(query, model, k=1))."""
+        return self.eval_local(Q, need=("g",))["g"]
 
     def eval_host(self, Q, out=None):
         """lip_eval_host: Q and the outputs in host memory (numpy or pinned CPU tensors)."""

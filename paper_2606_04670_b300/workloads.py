@@ -126,6 +126,11 @@ def _f_toy_d3(X):
 
 # --------------------------------------------------------------------- workloads
 
+def _f_local_d4(X):
+    X = np.asarray(X, np.float64)
+    return np.tanh(10.0 * (X[:, 0] - 0.5)) + 0.2 * X[:, 1] + 0.1 * np.sin(3.0 * X[:, 2]) + 0.05 * X[:, 3]
+
+
 def _as(x, dtype):
     return np.ascontiguousarray(x, dtype=dtype)
 
@@ -186,6 +191,17 @@ def toy_d3(n_data=1000, n_query=1000, dtype=np.float32) -> Problem:
     y = _as(_f_toy_d3(X), dtype)
     # grad = (1, 2 x2, 0.5 sin x3) <= (1, 2, 0.43) -> ||.||_2 <= 2.28
     return Problem("toy_d3", X, y, Q, 2.3, NORM_L2, np.ones(3, np.int8), None, _f_toy_d3)
+
+
+def local_d4(n_data=100_000, n_query=1_000_000, dtype=np.float32) -> Problem:
+    """A function whose slope differs across the domain (Sec. 4.3's motivation for local
+    constants): a steep tanh step across x1 = 0.5 (slope up to 10) on gentle terms (slopes
+    0.2, 0.3, 0.05).  L2, no monotonicity; grad norm <= sqrt(100 + 0.04 + 0.09 + 0.0025)."""
+    rx, rq, _ = _rngs(7)
+    X = _as(rx.random((n_data, 4)), dtype)
+    Q = _as(rq.random((n_query, 4)), dtype)
+    y = _as(_f_local_d4(X), dtype)
+    return Problem("local_d4", X, y, Q, 10.01, NORM_L2, None, None, _f_local_d4)
 
 
 @dataclasses.dataclass
@@ -269,4 +285,5 @@ WORKLOADS = {
     "cluster_d16": cluster_d16,
     "grad_d8": grad_d8,
     "toy_d3": toy_d3,
+    "local_d4": local_d4,
 }

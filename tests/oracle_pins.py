@@ -464,6 +464,10 @@ def check_local_table(O):
         M_est = O.estimate_M(p.X, p.y, p.norm, w=p.w)[0]
         assert abs(Mtab[:, -1].max() - M_est) <= 1e-12 * M_est
         np.testing.assert_allclose(d1, np.where(D > 0, D, np.inf).min(1), rtol=1e-12)
+        rows = np.array([5, 0, len(p.y) - 1, 5])
+        sub = O.local_table_rows(p.X, p.y, T, rows, p.norm, w=p.w)
+        for a, b in zip(sub, (d1, F, Mtab)):
+            assert np.array_equal(a, b[rows])
     # a single datum, or only repeated points: no neighbour, constant 0
     d1, F, Mtab = O.local_table(np.zeros((3, 2)), np.array([1.0, 1.0, 1.0]), [0.5])
     assert np.all(np.isinf(d1)) and np.all(F == 0) and np.all(Mtab == 0)

@@ -17,7 +17,7 @@ def test_exports_every_declared_symbol():
 
 
 def test_status_strings_and_version():
-    for s in range(9):
+    for s in range(10):
         assert L.status_string(s) and L.status_string(s) != "unknown status"
     assert L.status_string(99) == "unknown status"
     assert "sm_103a" in L.lip_version()
@@ -121,3 +121,14 @@ def test_tensor_core_precision_rules():
 def test_eval_k_argument_errors():
     wk = np.array([0.5, 0.5])
     assert L.lip_eval_k(None, None, 1, 2, wk.ctypes.data, None, None, None, None, None) == L.LIP_ERR_ARG
+
+
+def test_local_lipschitz_argument_errors():
+    assert L.lip_local_fit(None, 8, 100, 1) == L.LIP_ERR_ARG
+    kn = np.array([0.5, 1.0])
+    assert L.lip_local_fit_knots(None, kn.ctypes.data, 2) == L.LIP_ERR_ARG
+    assert L.lip_local_knots(None)[0] == L.LIP_ERR_ARG
+    assert L.lip_local_table(None, None, None, None) == L.LIP_ERR_ARG
+    assert L.lip_eval_local(None, None, 1, None, None, None, None, None) == L.LIP_ERR_ARG
+    assert L.LIP_LOCAL_KNOTS_MAX == 31 and L.LIP_LOCAL_SAMPLE_MAX == 1 << 20
+    assert L.status_string(L.LIP_ERR_STATE) == "call out of order"

@@ -1,0 +1,224 @@
+"""Local Lipschitz constants (Sec. 4.3) on the GPU against the FP64 oracle.
+
+The knots and the table decide integer outcomes (segment, nearest datum) with exact FP64
+arithmetic on both sides, so they must agree bit for bit.  The evaluation selects its data
+in FP32: a query passes when the GPU's bounds are the exact values of the data it returned
+and, unless the oracle flags the query as decided within FP32 rounding of a knot, those
+values are within the FP32 tolerance of the exact envelopes."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2606_04670_b300 import workloads as W
+from parity import FP32_TOL, diam
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _model(X, y, norm, w=None, mon=None, precision="fp32"):
+    from paper_2606_04670_b300.lipfit import LipFit
+    return LipFit(torch.as_tensor(X).cuda(), torch.as_tensor(y).cuda(), 1.0, norm=norm, w=w, mon=mon,
+                  precision=precision)
+
+
+def _f64(a):
+    return np.asarray(a, np.float64)
+
+
+def _table(m):
+    return tuple(t.cpu().numpy() for t in m.local_table())
+
+
+def _cases():
+    out = []
+    for norm in (1, 2, 3):
+        for seed, (N, d, weighted) in enumerate([(37, 2, False), (700, 3, True), (2049, 5, False), (1500, 8, True)]):
+            out.append(W.random_problem(200 + 10 * norm + seed, N, d, 300, norm=norm, weighted=weighted))
+    out.append(W.random_problem(230, 900, 16, 200, norm=2, weighted=True))
+    out.append(W.random_problem(231, 600, 1, 300, norm=1))
+    out.append(W.local_d4(n_data=3000, n_query=2000))
+    return out
+
+
+CASES = _cases()
+
+
+def _check_eval(p, X, y, Q, T, tab, out, label, min_clear=0.9):
+    """Validity of every query, the envelope within FP32 tolerance where the decision is
+    unambiguous (at least min_clear of the queries for random queries; at the data, exact
+    ties with the datum's own value make many flags harmless)."""
+    hi, lo, g = (_f64(out[k].cpu().numpy()) for k in ("hi", "lo", "g"))
+    iu, il = (out[k].cpu().numpy().astype(np.int64) for k in ("idx_up", "idx_lo"))
+    Z = np.abs(np.concatenate([X, Q]) * (1.0 if p.w is None else np.asarray(p.w)))
+    eta = 2.0 ** -20 * (X.shape[1] + 2) * (Z.max() + diam(X, Q, p.norm, p.w))
+    r = O.evaluate_local(X, y, Q, T, tab, p.norm, w=p.w, eta=eta)
+    tu = O.local_terms(X, y, Q, T, tab, iu, +1, p.norm, w=p.w)
+    tl = O.local_terms(X, y, Q, T, tab, il, -1, p.norm, w=p.w)
+    # the returned values are the exact FP64 values of the returned data, rounded once
+    assert np.array_equal(hi.astype(np.float32), tu.astype(np.float32)), label
+    assert np.array_equal(lo.astype(np.float32), tl.astype(np.float32)), label
+    assert np.array_equal(g.astype(np.float32), (0.5 * (tu + tl)).astype(np.float32)), label
+    scale = float(np.abs(y).max()) + float(tab[2].max()) * diam(X, Q, p.norm, p.w) + 1e-30
+    tol = FP32_TOL * scale
+    # never better than the exact envelope
+    assert np.all(tu >= r.hi - 1e-12 * scale) and np.all(tl <= r.lo + 1e-12 * scale), label
+    su, sl = ~r.amb_up, ~r.amb_lo
+    assert su.mean() >= min_clear and sl.mean() >= min_clear, (label, su.mean(), sl.mean())
+    assert np.all(np.abs(tu - r.hi)[su] <= tol), (label, np.abs(tu - r.hi)[su].max(), tol)
+    assert np.all(np.abs(tl - r.lo)[sl] <= tol), (label, np.abs(tl - r.lo)[sl].max(), tol)
+    return r
+
+
+@pytest.mark.parametrize("case", range(len(CASES)), ids=lambda i: f"{CASES[i].name}-L{CASES[i].norm}-N{CASES[i].N}")
+def test_knots_table_and_eval_match_oracle(case):
+    p = CASES[case]
+    m = _model(p.X, p.y, p.norm, w=p.w)
+    X, y, Q = _f64(p.X), _f64(p.y), _f64(p.Q)
+    for nknots, S, seed in ((16, 4096, 7), (5, 300, 2**64 - 3)):
+        T = m.compute_local_lipschitz(nknots, S, seed)
+        To, _, _ = O.local_knots(X, nknots, S, seed, p.norm, w=p.w)
+        assert np.array_equal(T, To), (p.name, T, To)
+        d1, F, Mtab = _table(m)
+        od1, oF, oM = O.local_table(X, y, T, p.norm, w=p.w)
+        assert np.array_equal(d1, od1) and np.array_equal(F, oF), p.name
+        assert np.array_equal(Mtab, oM), (p.name, np.abs(Mtab - oM).max())
+        out = m.eval_local(torch.as_tensor(p.Q).cuda())
+        torch.cuda.synchronize()
+        _check_eval(p, X, y, Q, T, (d1, F, Mtab), out, p.name)
+        # interpolation at the data (Sec. 4.3: the approximation interpolates the data)
+        outd = m.eval_local(torch.as_tensor(p.X).cuda())
+        _check_eval(p, X, y, X, T, (d1, F, Mtab), outd, p.name + "@data", min_clear=0.0)
+        tol = 1e-6 * (np.abs(y).max() + 1)
+        assert np.all(np.abs(outd["g"].cpu().numpy() - y) <= tol)
+    m.check()
+    m.close()
+
+
+def test_explicit_knots_at_pair_distances():
+    """Knots equal to interpoint distances: the <= at a knot decides whole segments."""
+    p = W.random_problem(240, 800, 3, 400, norm=2, weighted=True)
+    X, y = _f64(p.X), _f64(p.y)
+    _, pairs, dist = O.local_knots(X, 1, 64, 99, 2, w=p.w)
+    T = np.unique(dist[dist > 0])[::3][:31]
+    m = _model(p.X, p.y, 2, w=p.w)
+    got = m.compute_local_lipschitz(knots=T)
+    assert np.array_equal(got, T)
+    d1, F, Mtab = _table(m)
+    od1, oF, oM = O.local_table(X, y, T, 2, w=p.w)
+    assert np.array_equal(d1, od1) and np.array_equal(F, oF) and np.array_equal(Mtab, oM)
+    # data points at knot distances from others: still interpolated
+    out = m.eval_local(torch.as_tensor(p.X).cuda())
+    _check_eval(p, X, y, X, T, (d1, F, Mtab), out, "knots-at-pairs", min_clear=0.0)
+    m.close()
+
+
+def test_edge_cases():
+    from paper_2606_04670_b300.lipfit import LipError, LIP_ERR_STATE, LIP_ERR_UNSUPPORTED, LIP_ERR_ARG
+    # a single datum: M_k = 0, the bounds are y
+    m = _model(np.array([[0.3, 0.7]], np.float32), np.array([2.5], np.float32), 2)
+    assert m.compute_local_lipschitz(8, 100, 1).size == 0
+    d1, F, Mtab = _table(m)
+    assert np.isinf(d1[0]) and F[0] == 0 and np.all(Mtab == 0)
+    Q = torch.tensor([[0.0, 0.0], [5.0, -1.0], [float("nan"), 0.0]], device="cuda")
+    out = m.eval_local(Q)
+    hi, lo = out["hi"].cpu().numpy(), out["lo"].cpu().numpy()
+    assert np.all(hi[:2] == 2.5) and np.all(lo[:2] == 2.5)
+    assert np.isnan(hi[2]) and out["idx_up"][2].item() == -1 and out["idx_lo"][2].item() == -1
+    # nq = 0 and no knots
+    assert m.eval_local(torch.empty((0, 2), device="cuda"))["g"].numel() == 0
+    m.close()
+    # duplicated points are skipped as neighbours; no sample gives no knots
+    from paper_2606_04670_b300.lipfit import LipFit
+    X = np.array([[0, 0], [0, 0], [1, 0], [3, 0]], np.float32)
+    y = np.array([0, 0, 2, 3], np.float32)
+    m = LipFit(torch.as_tensor(X).cuda(), torch.as_tensor(y).cuda(), 1.0, norm="L1", capacity=8)
+    assert m.compute_local_lipschitz(4, 0, 1).size == 0
+    d1, F, Mtab = _table(m)
+    od1, oF, oM = O.local_table(_f64(X), _f64(y), [], 1)
+    assert np.array_equal(d1, od1) and np.array_equal(F, oF) and np.array_equal(Mtab, oM)
+    # the table is invalidated by new data
+    m.add(torch.tensor([[2.0, 2.0]], device="cuda"), torch.tensor([1.0], device="cuda"))
+    with pytest.raises(LipError) as e:
+        m.eval_local(torch.zeros((1, 2), device="cuda"))
+    assert e.value.status == LIP_ERR_STATE
+    m.compute_local_lipschitz(4, 64, 3)
+    out = m.eval_local(torch.as_tensor(X).cuda())
+    assert np.allclose(out["g"].cpu().numpy(), y, atol=1e-6)
+    with pytest.raises(LipError) as e:
+        m.compute_local_lipschitz(knots=[1.0, 0.5])
+    assert e.value.status == LIP_ERR_ARG
+    with pytest.raises(LipError) as e:
+        m.compute_local_lipschitz(32, 10, 1)
+    assert e.value.status == LIP_ERR_ARG
+    m.clear()
+    with pytest.raises(LipError) as e:
+        m.compute_local_lipschitz(4, 10, 1)
+    assert e.value.status == LIP_ERR_ARG
+    m.close()
+    # monotone handles and FP64 handles are not supported
+    for kw in ({"mon": [1, 0]}, {"precision": "fp64"}):
+        Xk = X.astype(np.float64) if kw.get("precision") == "fp64" else X
+        m = _model(Xk, y.astype(Xk.dtype), 2, **kw)
+        with pytest.raises(LipError) as e:
+            m.compute_local_lipschitz(4, 10, 1)
+        assert e.value.status == LIP_ERR_UNSUPPORTED
+        m.close()
+
+
+def test_tensor_core_handle_uses_local_path():
+    p = W.random_problem(250, 1200, 6, 500, norm=2)
+    m = _model(p.X, p.y, 2, precision="tc_tf32")
+    X, y, Q = _f64(p.X), _f64(p.y), _f64(p.Q)
+    T = m.compute_local_lipschitz(12, 2000, 5)
+    tab = _table(m)
+    assert np.array_equal(tab[2], O.local_table(X, y, T, 2)[2])
+    _check_eval(p, X, y, Q, T, tab, m.eval_local(torch.as_tensor(p.Q).cuda()), "tc-handle")
+    m.close()
+
+
+def test_full_size_local_d4_sampled():
+    """The benchmark's workload (N = 100,000, d = 4, 16 knots from 32,768 pairs): the knots
+    exactly, 64 table rows against the oracle's rows, and 512 sampled queries of the full
+    evaluation by properties that hold at any size: each returned value is the exact value
+    of the returned datum (its table row from the oracle), and no datum of a random subset
+    of 2,048 (rows from the oracle) has a better value beyond the FP32 tolerance."""
+    p = W.local_d4()
+    X, y = _f64(p.X), _f64(p.y)
+    m = _model(p.X, p.y, 2)
+    T = m.compute_local_lipschitz(16, 32768, 0)
+    assert np.array_equal(T, O.local_knots(X, 16, 32768, 0, 2)[0])
+    d1, F, Mtab = _table(m)
+    rng = np.random.default_rng(0)
+    rows = rng.choice(p.N, 64, replace=False)
+    od1, oF, oM = O.local_table_rows(X, y, T, rows, 2)
+    assert np.array_equal(d1[rows], od1) and np.array_equal(F[rows], oF) and np.array_equal(Mtab[rows], oM)
+    assert np.all(np.diff(Mtab, axis=1) >= 0)
+    out = m.eval_local(torch.as_tensor(p.Q).cuda())
+    torch.cuda.synchronize()
+    sel = np.sort(rng.choice(p.nq, 512, replace=False))
+    Qs = _f64(p.Q[sel])
+    hi = _f64(out["hi"].cpu().numpy()[sel])
+    lo = _f64(out["lo"].cpu().numpy()[sel])
+    iu = out["idx_up"].cpu().numpy()[sel].astype(np.int64)
+    il = out["idx_lo"].cpu().numpy()[sel].astype(np.int64)
+    sub = np.unique(np.concatenate([iu, il, rng.choice(p.N, 2048, replace=False)]))
+    sd1, sF, sM = O.local_table_rows(X, y, T, sub, 2)
+    # a table holding the oracle's rows for `sub` only (other rows are never read)
+    td1, tF, tM = np.full(p.N, np.nan), np.full(p.N, np.nan), np.full((p.N, T.size + 1), np.nan)
+    td1[sub], tF[sub], tM[sub] = sd1, sF, sM
+    tab = (td1, tF, tM)
+    tu = O.local_terms(X, y, Qs, T, tab, iu, +1, 2)
+    tl = O.local_terms(X, y, Qs, T, tab, il, -1, 2)
+    assert np.array_equal(hi.astype(np.float32), tu.astype(np.float32))
+    assert np.array_equal(lo.astype(np.float32), tl.astype(np.float32))
+    scale = float(np.abs(y).max()) + float(sM.max()) * 2.0
+    tol = FP32_TOL * scale
+    others = rng.choice(sub, 2048, replace=False)
+    for k in others:
+        kk = np.full(len(sel), k)
+        assert np.all(tu <= O.local_terms(X, y, Qs, T, tab, kk, +1, 2) + tol)
+        assert np.all(tl >= O.local_terms(X, y, Qs, T, tab, kk, -1, 2) - tol)
+    m.check()
+    m.close()

@@ -135,6 +135,8 @@ struct lip_model {
     int64_t last_fallback = 0;
     // local Lipschitz constants (Sec. 4.3), valid until the data change
     bool loc_valid = false;
+    bool loc_bucket = true;            // the evaluation's bucket lookup applies (else binary search)
+    float loc_scale = 0.f;
     int loc_m = 0;
     double loc_T[LOC_KNOTS] = {};
     Scratch loc_buf, loc_tmp;          // layout and tables; sampled distances and bounds
@@ -522,7 +524,8 @@ lip_status eval_device(lip_model* h, const void* Q, int64_t nq, void* g, void* l
 
 namespace {
 
-constexpr size_t LOC_SMALL_BYTES = 2 * LOC_KNOTS * sizeof(double) + 3 * LOC_KNOTS * sizeof(float) + sizeof(LocMeta);
+constexpr size_t LOC_SMALL_BYTES = LOC_BUCKETS * sizeof(int2) + 2 * LOC_KNOTS * sizeof(double) +
+                                   3 * LOC_KNOTS * sizeof(float) + sizeof(LocMeta);
 
 lip_status local_supported(const lip_model* h) {
     if (h->esize != 4)
@@ -558,6 +561,7 @@ lip_status local_buffers(lip_model* h, int64_t S, LocalParams& P) {
     P.N = N;
     P.npad = npad;
     P.d = h->d;
+    P.dp = local_dim_pad(h->d);
     P.pr = pr;
     P.norm = h->norm;
     for (int i = 0; i < D_MAX; ++i) P.w[i] = i < h->d ? h->w[i] : 1.0;
@@ -566,7 +570,8 @@ lip_status local_buffers(lip_model* h, int64_t S, LocalParams& P) {
     P.mt64 = reinterpret_cast<double*>(b + b_rec + b_mt);
     P.d1 = reinterpret_cast<double*>(b + b_rec + b_mt + b_mt64);
     P.F = reinterpret_cast<double*>(b + b_rec + b_mt + b_mt64 + b_vec);
-    P.T64 = reinterpret_cast<double*>(h->loc_small);
+    P.buckets = reinterpret_cast<int2*>(h->loc_small);
+    P.T64 = reinterpret_cast<double*>(P.buckets + LOC_BUCKETS);
     P.raw = P.T64 + LOC_KNOTS;
     P.Tf = reinterpret_cast<float*>(P.raw + LOC_KNOTS);
     P.meta = reinterpret_cast<LocMeta*>(P.Tf + 3 * LOC_KNOTS);
@@ -596,6 +601,8 @@ lip_status local_run(lip_model* h, bool sampled, int m, int64_t S, uint64_t seed
     CUDA_TRY(cudaMemcpyAsync(h->loc_T, P.T64, sizeof h->loc_T, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     h->loc_m = meta.m;
+    h->loc_bucket = meta.bucket_ok != 0;
+    h->loc_scale = meta.scale;
     h->loc_valid = true;
     return LIP_OK;
 }
@@ -665,7 +672,7 @@ lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     LocalParams P;
     LIP_TRY(local_buffers(h, 0, P));
-    const int64_t gx = ceil_div(nq, (int64_t)local_threads());
+    const int64_t gx = ceil_div(nq, (int64_t)local_queries_per_block());
     if (gx > 0x7fffffff) return fail(LIP_ERR_ARG, "nq = %lld is too large", (long long)nq);
     const int64_t tile = local_scan_tile();
     const int64_t tiles = P.npad / tile;
@@ -678,11 +685,13 @@ lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void
     S.Q = static_cast<const float*>(Q);
     S.nq = nq;
     S.d = h->d;
-    S.pr = P.pr;
+    S.dp = P.dp;
     for (int i = 0; i < D_MAX; ++i) S.w[i] = P.w[i];
     S.rec = P.rec;
     S.mt = P.mt;
     S.Tf = P.Tf;
+    S.buckets = P.buckets;
+    S.scale = h->loc_scale;
     S.npad = P.npad;
     S.points_per_split = pps;
     S.partial = h->partial.p;
@@ -707,7 +716,7 @@ lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void
     Mp.idx_up = idx_up;
     Mp.idx_lo = idx_lo;
     if (h->ev_scan0) CUDA_TRY(cudaEventRecord(h->ev_scan0, st));
-    CUDA_TRY(launch_local_eval(h->norm, S, (int)gx, nsplit, Mp, st));
+    CUDA_TRY(launch_local_eval(h->norm, S, (int)gx, nsplit, h->loc_bucket, Mp, st));
     if (h->ev_scan1) CUDA_TRY(cudaEventRecord(h->ev_scan1, st));
     count_launches(2);
     return LIP_OK;

@@ -99,23 +99,27 @@ cudaError_t launch_backward(int elem_bytes, const BwdParams& P, int64_t N, void*
 // ------------------------------------------------ local Lipschitz constants (Sec. 4.3)
 
 constexpr int LOC_KNOTS = 32;        // table stride: up to 31 knots and the last segment
+constexpr int LOC_BUCKETS = 2048;    // knot-lookup buckets of the evaluation scan
 
 struct LocMeta {
     int npos;                        // positive sampled distances
     int m;                           // distinct knots
     unsigned rbits;                  // largest |scaled coordinate| (float bits)
-    int pad;
+    int bucket_ok;                   // 1 if no lookup bucket holds two knots
+    float scale;                     // lookup buckets per unit distance
+    int pad[3];
 };
 
 struct LocalParams {
     const float* X0;                 // caller's data [N][d]
     const float* y0;
     int64_t N, npad;
-    int d, pr, norm, m;              // m: knots requested (sampled) or given
+    int d, dp, pr, norm, m;          // dp: d rounded up to 4; m: knots requested or given
     double w[D_MAX];
     int64_t S;                       // sampled pairs
     uint64_t seed;
-    float* rec;                      // [npad][pr]: w-scaled coordinates, y, d1 (float), F (float)
+    float* rec;                      // [npad][pr = dp + 4]: w-scaled coordinates (0-padded to dp),
+                                     // y, d1 (float), F (float), 0
     float* mt;                       // [npad][LOC_KNOTS]: FP32 table (pass 1: lower bounds)
     double* mt64;                    // [N][LOC_KNOTS]: exact table
     double* d1;                      // [N]
@@ -125,17 +129,20 @@ struct LocalParams {
     double* raw;                     // [LOC_KNOTS] quantile picks (or the given knots)
     double* sample;                  // [S] sampled distances
     float* ubound;                   // [N] pass-1 upper bounds of d1
+    int2* buckets;                   // [LOC_BUCKETS]: knots below the bucket, knot inside (bits)
     LocMeta* meta;
 };
 
 struct LocalScanParams {
     const float* Q;
     int64_t nq;
-    int d, pr;
+    int d, dp;
     double w[D_MAX];
     const float* rec;
     const float* mt;
     const float* Tf;
+    const int2* buckets;
+    float scale;
     int64_t npad, points_per_split;
     void* partial;                   // [nsplit][nq] PartialRec<float>
 };
@@ -156,14 +163,15 @@ struct LocalMergeParams {
     int32_t *idx_up, *idx_lo;
 };
 
+int local_dim_pad(int d);
 int local_record_floats(int d);
 int64_t local_pad(int64_t N);
 int local_scan_tile();
-int local_threads();
+int local_queries_per_block();
 cudaError_t launch_local_layout(const LocalParams& P, cudaStream_t st);
 cudaError_t launch_local_knots(const LocalParams& P, bool sampled, cudaStream_t st);
 cudaError_t launch_local_table(const LocalParams& P, cudaStream_t st);
-cudaError_t launch_local_eval(int norm, const LocalScanParams& S, int gx, int nsplit, const LocalMergeParams& M,
-                              cudaStream_t st);
+cudaError_t launch_local_eval(int norm, const LocalScanParams& S, int gx, int nsplit, bool bucket,
+                              const LocalMergeParams& M, cudaStream_t st);
 
 }  // namespace lip

@@ -39,6 +39,7 @@ constexpr int LOC_THREADS = 128;
 constexpr int LOC_TILE = 128;       // data points per shared-memory tile (table passes)
 constexpr int LOC_SCAN_TILE = 64;   // data points per shared-memory tile (evaluation)
 constexpr int LOC_RANK_TILE = 1024;
+constexpr int LOC_R = 2;            // queries per thread in the evaluation scan
 
 __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
 
@@ -72,18 +73,25 @@ __device__ __forceinline__ int knot_count(const float* T, float v) {
     return c;
 }
 
-template <int NORM>
-__device__ __forceinline__ float dist32(const float* xk, const float* xj, int d) {
+template <int NORM, int DP>
+__device__ __forceinline__ float dist32(const float* xk, const float* xj) {
     float acc = 0.f;
 #pragma unroll
-    for (int i = 0; i < D_MAX; ++i) {
-        if (i >= d) break;
+    for (int i = 0; i < DP; ++i) {
         const float t = xk[i] - xj[i];
         if (NORM == LIP_L1) acc += fabsf(t);
         else if (NORM == LIP_L2) acc = fmaf(t, t, acc);
         else acc = fmaxf(acc, fabsf(t));
     }
     return acc;
+}
+
+// Bucket of a non-negative distance for the knot lookup: floor(min(t * scale, NB - 1)),
+// monotone in t (the rounding-toward-zero add to 2^23 is the floor for 0 <= u < 2^23).
+// A NaN t lands in the last bucket.
+__device__ __forceinline__ int knot_bucket(float t, float scale) {
+    const float u = fminf(t * scale, (float)(LOC_BUCKETS - 1));
+    return __float_as_int(__fadd_rz(u, 8388608.0f)) - 0x4B000000;
 }
 
 // ------------------------------------------------------------------ layout
@@ -95,18 +103,19 @@ __global__ void loc_layout_kernel(const LocalParams P) {
     float amax = 0.f;
     if (k < P.N) {
         const float* x = P.X0 + k * P.d;
-        for (int i = 0; i < P.d; ++i) {
-            const float v = (float)(P.w[i] * (double)x[i]);
+        for (int i = 0; i < P.dp; ++i) {
+            const float v = i < P.d ? (float)(P.w[i] * (double)x[i]) : 0.f;
             r[i] = v;
             amax = fmaxf(amax, fabsf(v));
         }
-        r[P.d] = P.y0[k];
+        r[P.dp] = P.y0[k];
     } else {
-        for (int i = 0; i < P.d; ++i) r[i] = 0.f;
-        r[P.d] = __int_as_float(0x7fc00000);          // padding: y = NaN is never selected
+        for (int i = 0; i < P.dp; ++i) r[i] = 0.f;
+        r[P.dp] = __int_as_float(0x7fc00000);         // padding: y = NaN is never selected
     }
-    r[P.d + 1] = INFINITY;
-    r[P.d + 2] = 0.f;
+    r[P.dp + 1] = INFINITY;
+    r[P.dp + 2] = 0.f;
+    r[P.dp + 3] = 0.f;
     const unsigned act = __activemask();
     const unsigned m = __reduce_max_sync(act, __float_as_uint(amax));   // |v| orders as its bits
     if ((int)(threadIdx.x & 31) == __ffs(act) - 1) atomicMax(&P.meta->rbits, m);
@@ -150,41 +159,65 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_rank_kernel(const LocalParams
 }
 
 // Distinct knots (raw is non-decreasing) into T64, padded with +inf, and their float
-// roundings: to nearest (evaluation), down and up (the screen's bounds).
+// roundings: to nearest (evaluation), down and up (the screen's bounds).  Then the
+// evaluation's bucket table: bucket b holds the number of knots in lower buckets and the
+// knot inside it (+inf if none); bucket_ok is cleared if a bucket holds two knots.
 __global__ void loc_knots_kernel(const LocalParams P, int sampled) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int n = 0;
-    const int m = (sampled && P.meta->npos == 0) ? 0 : P.m;
-    for (int i = 0; i < m; ++i) {
-        const double v = P.raw[i];
-        if (n == 0 || v > P.T64[n - 1]) P.T64[n++] = v;
+    if (blockIdx.x != 0) return;
+    if (threadIdx.x == 0) {
+        int n = 0;
+        const int m = (sampled && P.meta->npos == 0) ? 0 : P.m;
+        for (int i = 0; i < m; ++i) {
+            const double v = P.raw[i];
+            if (n == 0 || v > P.T64[n - 1]) P.T64[n++] = v;
+        }
+        P.meta->m = n;
+        for (int i = 0; i < LOC_KNOTS; ++i) {
+            const double v = i < n ? P.T64[i] : INFINITY;
+            if (i >= n) P.T64[i] = INFINITY;
+            P.Tf[i] = __double2float_rn(v);
+            P.Tf[LOC_KNOTS + i] = __double2float_rd(v);
+            P.Tf[2 * LOC_KNOTS + i] = __double2float_ru(v);
+        }
+        P.meta->scale = n > 0 ? fminf((float)LOC_BUCKETS / P.Tf[n - 1], 1e30f) : 0.f;
+        P.meta->bucket_ok = 1;
     }
-    P.meta->m = n;
-    for (int i = 0; i < LOC_KNOTS; ++i) {
-        const double v = i < n ? P.T64[i] : INFINITY;
-        if (i >= n) P.T64[i] = INFINITY;
-        P.Tf[i] = __double2float_rn(v);
-        P.Tf[LOC_KNOTS + i] = __double2float_rd(v);
-        P.Tf[2 * LOC_KNOTS + i] = __double2float_ru(v);
+    __syncthreads();
+    const int n = P.meta->m;
+    const float scale = P.meta->scale;
+    for (int b = threadIdx.x; b < LOC_BUCKETS; b += blockDim.x) {
+        int below = 0, inside = 0;
+        float first = INFINITY;
+        for (int i = 0; i < n; ++i) {
+            const int bi = knot_bucket(P.Tf[i], scale);
+            if (bi < b) ++below;
+            else if (bi == b) {
+                if (inside == 0) first = P.Tf[i];
+                ++inside;
+            }
+        }
+        if (inside > 1) atomicExch(&P.meta->bucket_ok, 0);
+        P.buckets[b] = make_int2(below, __float_as_int(first));
     }
 }
 
 // ------------------------------------------------------------------ table, pass 1
 
-template <int NORM>
+template <int NORM, int DP>
 __global__ void __launch_bounds__(LOC_THREADS) loc_pass1_kernel(const LocalParams P) {
+    constexpr int PR = DP + 4;
     extern __shared__ float4 sm4[];
-    float* tile = reinterpret_cast<float*>(sm4);                    // [LOC_TILE][pr]
-    float* A = tile + LOC_TILE * P.pr;                              // [32][LOC_THREADS]
+    float* tile = reinterpret_cast<float*>(sm4);                    // [LOC_TILE][PR]
+    float* A = tile + LOC_TILE * PR;                                // [32][LOC_THREADS]
     float* Tdn = A + LOC_KNOTS * LOC_THREADS;                       // [32]
     const int tid = threadIdx.x;
     const int64_t k = (int64_t)blockIdx.x * LOC_THREADS + tid;
     const bool valid = k < P.N;
-    float xk[D_MAX];
+    float xk[DP];
     float yk = 0.f;
 #pragma unroll
-    for (int i = 0; i < D_MAX; ++i) xk[i] = (valid && i < P.d) ? P.rec[k * P.pr + i] : 0.f;
-    if (valid) yk = P.rec[k * P.pr + P.d];
+    for (int i = 0; i < DP; ++i) xk[i] = valid ? P.rec[k * PR + i] : 0.f;
+    if (valid) yk = P.rec[k * PR + DP];
     for (int s = 0; s < LOC_KNOTS; ++s) A[s * LOC_THREADS + tid] = 0.f;
     if (tid < LOC_KNOTS) Tdn[tid] = P.Tf[LOC_KNOTS + tid];
     const float R = __uint_as_float(P.meta->rbits);
@@ -195,20 +228,20 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass1_kernel(const LocalParam
     for (int64_t j0 = 0; j0 < P.N; j0 += LOC_TILE) {
         const int n = (int)lmin(LOC_TILE, P.N - j0);
         __syncthreads();
-        const float4* src = reinterpret_cast<const float4*>(P.rec + j0 * P.pr);
-        for (int i = tid; i < n * P.pr / 4; i += LOC_THREADS) sm4[i] = src[i];
+        const float4* src = reinterpret_cast<const float4*>(P.rec + j0 * PR);
+        for (int i = tid; i < n * PR / 4; i += LOC_THREADS) sm4[i] = src[i];
         __syncthreads();
         if (!valid) continue;
         for (int j = 0; j < n; ++j) {
-            const float* xj = tile + j * P.pr;
-            float d32 = dist32<NORM>(xk, xj, P.d);
+            const float* xj = tile + j * PR;
+            float d32 = dist32<NORM, DP>(xk, xj);
             if (NORM == LIP_L2) d32 = sqrtf(d32);
             const float del = fmaf(e_rel, d32, e_abs);
             if (d32 > del) {                          // surely a positive distance
                 const float hi = d32 + 2.f * del;
                 U = fminf(U, hi);
                 const int s = knot_count(Tdn, hi);    // the highest segment d64 may fall in
-                const float dy = fabsf(yk - xj[P.d]);
+                const float dy = fabsf(yk - xj[DP]);
                 const float rlo = dy * rcp_approx(hi) * lo_margin;
                 float* a = A + s * LOC_THREADS + tid;
                 *a = fmaxf(*a, rlo);
@@ -226,23 +259,24 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass1_kernel(const LocalParam
 
 // ------------------------------------------------------------------ table, pass 2
 
-template <int NORM>
+template <int NORM, int DP>
 __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParams P) {
+    constexpr int PR = DP + 4;
     extern __shared__ float4 sm4[];
-    float* tile = reinterpret_cast<float*>(sm4);                    // [LOC_TILE][pr]
-    float* Lb = tile + LOC_TILE * P.pr;                             // [32][LOC_THREADS]
+    float* tile = reinterpret_cast<float*>(sm4);                    // [LOC_TILE][PR]
+    float* Lb = tile + LOC_TILE * PR;                               // [32][LOC_THREADS]
     float* Tup = Lb + LOC_KNOTS * LOC_THREADS;                      // [32]
     __shared__ double T64[LOC_KNOTS];
     const int tid = threadIdx.x;
     const int64_t k = (int64_t)blockIdx.x * LOC_THREADS + tid;
     const bool valid = k < P.N;
-    float xk[D_MAX];
+    float xk[DP];
     float yk = 0.f;
 #pragma unroll
-    for (int i = 0; i < D_MAX; ++i) xk[i] = (valid && i < P.d) ? P.rec[k * P.pr + i] : 0.f;
+    for (int i = 0; i < DP; ++i) xk[i] = valid ? P.rec[k * PR + i] : 0.f;
     float U = 0.f;
     if (valid) {
-        yk = P.rec[k * P.pr + P.d];
+        yk = P.rec[k * PR + DP];
         U = P.ubound[k];
         for (int s = 0; s < LOC_KNOTS; ++s) Lb[s * LOC_THREADS + tid] = P.mt[k * LOC_KNOTS + s];
     }
@@ -264,20 +298,20 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParam
     for (int64_t j0 = 0; j0 < P.N; j0 += LOC_TILE) {
         const int n = (int)lmin(LOC_TILE, P.N - j0);
         __syncthreads();
-        const float4* src = reinterpret_cast<const float4*>(P.rec + j0 * P.pr);
-        for (int i = tid; i < n * P.pr / 4; i += LOC_THREADS) sm4[i] = src[i];
+        const float4* src = reinterpret_cast<const float4*>(P.rec + j0 * PR);
+        for (int i = tid; i < n * PR / 4; i += LOC_THREADS) sm4[i] = src[i];
         __syncthreads();
         if (!valid) continue;
         for (int j = 0; j < n; ++j) {
-            const float* xj = tile + j * P.pr;
-            float d32 = dist32<NORM>(xk, xj, P.d);
+            const float* xj = tile + j * PR;
+            float d32 = dist32<NORM, DP>(xk, xj);
             if (NORM == LIP_L2) d32 = sqrtf(d32);
             const float del = fmaf(e_rel, d32, e_abs);
             const float lo = d32 - 2.f * del;         // d64 >= lo
             bool cand = lo <= U;                      // may be (tied) nearest
             if (!cand) {
                 const int s = knot_count(Tup, lo);    // the lowest segment d64 may fall in
-                const float dy = fabsf(yk - xj[P.d]);
+                const float dy = fabsf(yk - xj[DP]);
                 cand = dy * up_margin > Lb[s * LOC_THREADS + tid] * lo * lo_margin;
             }
             if (!cand) continue;
@@ -295,8 +329,8 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParam
     if (!valid) return;
     P.d1[k] = d1;
     P.F[k] = F;
-    P.rec[k * P.pr + P.d + 1] = (float)d1;
-    P.rec[k * P.pr + P.d + 2] = (float)F;
+    P.rec[k * PR + DP + 1] = (float)d1;
+    P.rec[k * PR + DP + 2] = (float)F;
     double run = F;
     for (int s = 0; s < LOC_KNOTS; ++s) {
         if (s <= m) run = fmax(run, E[s]);
@@ -307,50 +341,80 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParam
 
 // ------------------------------------------------------------------ evaluation
 
-template <int NORM>
+// Each thread holds LOC_R queries; a block scans its split of the data in shared-memory
+// tiles of LOC_SCAN_TILE records and their table rows.  The segment of a distance comes
+// from the bucket table (one shared load and one compare), or from a binary search over
+// the knots when some bucket holds two knots.
+template <int NORM, int DP, bool BUCKET>
 __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanParams P) {
-    __shared__ float4 rec4[LOC_SCAN_TILE * (D_MAX + 4) / 4];
+    constexpr int PR = DP + 4;
+    __shared__ float4 rec4[LOC_SCAN_TILE * PR / 4];
     __shared__ float4 mt4[LOC_SCAN_TILE * LOC_KNOTS / 4];
+    __shared__ int2 bk[BUCKET ? LOC_BUCKETS : 1];
     __shared__ float Tn[LOC_KNOTS];
     const float* rec = reinterpret_cast<const float*>(rec4);
     const float* mt = reinterpret_cast<const float*>(mt4);
     const int tid = threadIdx.x;
-    const int64_t qi = (int64_t)blockIdx.x * LOC_THREADS + tid;
     const int split = blockIdx.y;
-    const bool valid = qi < P.nq;
-    float q[D_MAX];
+    float q[LOC_R][DP];
+    int64_t qi[LOC_R];
 #pragma unroll
-    for (int i = 0; i < D_MAX; ++i) q[i] = (valid && i < P.d) ? (float)(P.w[i] * (double)P.Q[qi * P.d + i]) : 0.f;
-    if (tid < LOC_KNOTS) Tn[tid] = P.Tf[tid];
-    float bu = INFINITY, bl = -INFINITY;
-    int iu = -1, il = -1;
+    for (int r = 0; r < LOC_R; ++r) {
+        qi[r] = (int64_t)blockIdx.x * LOC_THREADS * LOC_R + r * LOC_THREADS + tid;
+#pragma unroll
+        for (int i = 0; i < DP; ++i)
+            q[r][i] = (qi[r] < P.nq && i < P.d) ? (float)(P.w[i] * (double)P.Q[qi[r] * P.d + i]) : 0.f;
+    }
+    if (BUCKET) {
+        for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.buckets[b];
+    } else if (tid < LOC_KNOTS) {
+        Tn[tid] = P.Tf[tid];
+    }
+    const float scale = P.scale;
+    float bu[LOC_R], bl[LOC_R];
+    int iu[LOC_R], il[LOC_R];
+#pragma unroll
+    for (int r = 0; r < LOC_R; ++r) { bu[r] = INFINITY; bl[r] = -INFINITY; iu[r] = -1; il[r] = -1; }
     const int64_t j_begin = (int64_t)split * P.points_per_split;
     const int64_t j_end = lmin(j_begin + P.points_per_split, P.npad);
     for (int64_t j0 = j_begin; j0 < j_end; j0 += LOC_SCAN_TILE) {
         __syncthreads();
-        const float4* rs = reinterpret_cast<const float4*>(P.rec + j0 * P.pr);
-        for (int i = tid; i < LOC_SCAN_TILE * P.pr / 4; i += LOC_THREADS) rec4[i] = rs[i];
+        const float4* rs = reinterpret_cast<const float4*>(P.rec + j0 * PR);
+        for (int i = tid; i < LOC_SCAN_TILE * PR / 4; i += LOC_THREADS) rec4[i] = rs[i];
         const float4* ms = reinterpret_cast<const float4*>(P.mt + j0 * LOC_KNOTS);
         for (int i = tid; i < LOC_SCAN_TILE * LOC_KNOTS / 4; i += LOC_THREADS) mt4[i] = ms[i];
         __syncthreads();
 #pragma unroll 2
         for (int j = 0; j < LOC_SCAN_TILE; ++j) {
-            const float* xj = rec + j * P.pr;
-            float t = dist32<NORM>(q, xj, P.d);
-            if (NORM == LIP_L2) t = sqrt_approx(t);
-            const int s = knot_count(Tn, t);
-            const float M = t <= xj[P.d + 1] ? xj[P.d + 2] : mt[j * LOC_KNOTS + s];
-            const float y = xj[P.d];
-            const float vu = fmaf(M, t, y), vl = fmaf(-M, t, y);
+            const float* xj = rec + j * PR;
+            const float y = xj[DP], d1 = xj[DP + 1], Fj = xj[DP + 2];
+            const float* mtj = mt + j * LOC_KNOTS;
             const int idx = (int)(j0 + j);
-            if (vu < bu) { bu = vu; iu = idx; }
-            if (vl > bl) { bl = vl; il = idx; }
+#pragma unroll
+            for (int r = 0; r < LOC_R; ++r) {
+                float t = dist32<NORM, DP>(q[r], xj);
+                if (NORM == LIP_L2) t = sqrt_approx(t);
+                int s;
+                if (BUCKET) {
+                    const int2 e = bk[knot_bucket(t, scale)];
+                    s = e.x + (__int_as_float(e.y) < t ? 1 : 0);
+                } else {
+                    s = knot_count(Tn, t);
+                }
+                const float M = t <= d1 ? Fj : mtj[s];
+                const float vu = fmaf(M, t, y), vl = fmaf(-M, t, y);
+                if (vu < bu[r]) { bu[r] = vu; iu[r] = idx; }
+                if (vl > bl[r]) { bl[r] = vl; il[r] = idx; }
+            }
         }
     }
-    if (!valid) return;
-    PartialRec<float> r;
-    r.vu = bu; r.iu = iu; r.vl = bl; r.il = il;
-    static_cast<PartialRec<float>*>(P.partial)[(int64_t)split * P.nq + qi] = r;
+#pragma unroll
+    for (int r = 0; r < LOC_R; ++r) {
+        if (qi[r] >= P.nq) continue;
+        PartialRec<float> rr;
+        rr.vu = bu[r]; rr.iu = iu[r]; rr.vl = bl[r]; rr.il = il[r];
+        static_cast<PartialRec<float>*>(P.partial)[(int64_t)split * P.nq + qi[r]] = rr;
+    }
 }
 
 __device__ __forceinline__ double local_M64(const LocalMergeParams& P, int64_t k, double t) {
@@ -395,10 +459,11 @@ size_t pass_smem(int pr) { return ((size_t)LOC_TILE * pr + LOC_KNOTS * LOC_THREA
 
 }  // namespace
 
-int local_record_floats(int d) { return (d + 3 + 3) / 4 * 4; }
+int local_dim_pad(int d) { return (d + 3) / 4 * 4; }
+int local_record_floats(int d) { return local_dim_pad(d) + 4; }
 int64_t local_pad(int64_t N) { return (N + LOC_TILE - 1) / LOC_TILE * LOC_TILE; }
 int local_scan_tile() { return LOC_SCAN_TILE; }
-int local_threads() { return LOC_THREADS; }
+int local_queries_per_block() { return LOC_THREADS * LOC_R; }
 
 cudaError_t launch_local_layout(const LocalParams& P, cudaStream_t st) {
     const unsigned blocks = (unsigned)((P.npad + 255) / 256);
@@ -416,23 +481,29 @@ cudaError_t launch_local_knots(const LocalParams& P, bool sampled, cudaStream_t 
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    loc_knots_kernel<<<1, 32, 0, st>>>(P, sampled ? 1 : 0);
+    loc_knots_kernel<<<1, 256, 0, st>>>(P, sampled ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <int NORM, int DP>
+static cudaError_t table_shape(const LocalParams& P, cudaStream_t st) {
+    const size_t smem = pass_smem(DP + 4);
+    const unsigned blocks = (unsigned)((P.N + LOC_THREADS - 1) / LOC_THREADS);
+    loc_pass1_kernel<NORM, DP><<<blocks, LOC_THREADS, smem, st>>>(P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    loc_pass2_kernel<NORM, DP><<<blocks, LOC_THREADS, smem, st>>>(P);
     return cudaGetLastError();
 }
 
 template <int NORM>
 static cudaError_t table_norm(const LocalParams& P, cudaStream_t st) {
-    const size_t smem = pass_smem(P.pr);
-    cudaError_t e = cudaFuncSetAttribute(loc_pass1_kernel<NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(loc_pass2_kernel<NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const unsigned blocks = (unsigned)((P.N + LOC_THREADS - 1) / LOC_THREADS);
-    loc_pass1_kernel<NORM><<<blocks, LOC_THREADS, smem, st>>>(P);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    loc_pass2_kernel<NORM><<<blocks, LOC_THREADS, smem, st>>>(P);
-    return cudaGetLastError();
+    switch (P.dp) {
+        case 4: return table_shape<NORM, 4>(P, st);
+        case 8: return table_shape<NORM, 8>(P, st);
+        case 12: return table_shape<NORM, 12>(P, st);
+        default: return table_shape<NORM, 16>(P, st);
+    }
 }
 
 cudaError_t launch_local_table(const LocalParams& P, cudaStream_t st) {
@@ -441,13 +512,29 @@ cudaError_t launch_local_table(const LocalParams& P, cudaStream_t st) {
     return table_norm<LIP_LINF>(P, st);
 }
 
-cudaError_t launch_local_eval(int norm, const LocalScanParams& S, int gx, int nsplit, const LocalMergeParams& M,
-                              cudaStream_t st) {
+template <int NORM, int DP>
+static void scan_shape(const LocalScanParams& S, dim3 grid, bool bucket, cudaStream_t st) {
+    if (bucket) loc_scan_kernel<NORM, DP, true><<<grid, LOC_THREADS, 0, st>>>(S);
+    else loc_scan_kernel<NORM, DP, false><<<grid, LOC_THREADS, 0, st>>>(S);
+}
+
+template <int NORM>
+static void scan_norm(const LocalScanParams& S, dim3 grid, bool bucket, cudaStream_t st) {
+    switch (S.dp) {
+        case 4: scan_shape<NORM, 4>(S, grid, bucket, st); break;
+        case 8: scan_shape<NORM, 8>(S, grid, bucket, st); break;
+        case 12: scan_shape<NORM, 12>(S, grid, bucket, st); break;
+        default: scan_shape<NORM, 16>(S, grid, bucket, st); break;
+    }
+}
+
+cudaError_t launch_local_eval(int norm, const LocalScanParams& S, int gx, int nsplit, bool bucket,
+                              const LocalMergeParams& M, cudaStream_t st) {
     if (nsplit > 0) {
         const dim3 grid((unsigned)gx, (unsigned)nsplit);
-        if (norm == LIP_L1) loc_scan_kernel<LIP_L1><<<grid, LOC_THREADS, 0, st>>>(S);
-        else if (norm == LIP_L2) loc_scan_kernel<LIP_L2><<<grid, LOC_THREADS, 0, st>>>(S);
-        else loc_scan_kernel<LIP_LINF><<<grid, LOC_THREADS, 0, st>>>(S);
+        if (norm == LIP_L1) scan_norm<LIP_L1>(S, grid, bucket, st);
+        else if (norm == LIP_L2) scan_norm<LIP_L2>(S, grid, bucket, st);
+        else scan_norm<LIP_LINF>(S, grid, bucket, st);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -222,3 +222,18 @@ def test_full_size_local_d4_sampled():
         assert np.all(tl >= O.local_terms(X, y, Qs, T, tab, kk, -1, 2) - tol)
     m.check()
     m.close()
+
+
+def test_close_knots_use_the_search_lookup():
+    """Two knots in one lookup bucket switch the evaluation to the binary search over the
+    knots; results still match the oracle."""
+    p = W.random_problem(260, 1000, 2, 600, norm=1, weighted=True)
+    X, y, Q = _f64(p.X), _f64(p.y), _f64(p.Q)
+    T = np.array([0.2, 0.5, 0.5000001, 0.9, 1.4])
+    m = _model(p.X, p.y, 1, w=p.w)
+    assert np.array_equal(m.compute_local_lipschitz(knots=T), T)
+    tab = _table(m)
+    for a, b in zip(tab, O.local_table(X, y, T, 1, w=p.w)):
+        assert np.array_equal(a, b)
+    _check_eval(p, X, y, Q, T, tab, m.eval_local(torch.as_tensor(p.Q).cuda()), "search-lookup")
+    m.close()

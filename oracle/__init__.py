@@ -9,7 +9,8 @@ table) and never calls it.  ``build()`` compiles ``lipfit_oracle.c`` with gcc in
 Passages followed (all in the C file's header): Sec. 3 Eq. (upperlower) and
 Eq. (eq:g) for the envelopes and midpoint, Sec. 4.1 Eq. (distmon) for the
 monotone distance, Sec. 5 for the Lipschitz-constant estimate and the k > 1
-neighbours, Sec. 4.3 for the local Lipschitz constants, and Table 1
+neighbours, Sec. 4.3 for the local Lipschitz constants, Sec. 4.4 Eq. (optim) for the
+penalty smoothing, and Table 1
 ("differentiable almost everywhere") for the gradient.
 
 ``Oracle(path)`` binds any build of the same C source; the tests use it to check
@@ -95,6 +96,10 @@ class Oracle:
         lib.oracle_eval_local.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, f64, P, P, P, P, P,
                                           P, P, i32]
         lib.oracle_local_terms.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, P, i32, P]
+        lib.oracle_smooth_objective.argtypes = [P, P, i64, i32, f64, i32, P, P, f64, P, P, P, P, P]
+        lib.oracle_smooth.argtypes = [P, P, i64, i32, f64, i32, P, P, f64, i32, i32, f64, P, P, P]
+        lib.oracle_smooth_objective.restype = ctypes.c_int
+        lib.oracle_smooth.restype = ctypes.c_int
         for fn in (lib.oracle_eval, lib.oracle_estimate_M, lib.oracle_estimate_M_rows, lib.oracle_grad,
                    lib.oracle_eval_k, lib.oracle_local_knots, lib.oracle_local_table, lib.oracle_local_table_rows,
                    lib.oracle_eval_local,
@@ -259,6 +264,36 @@ class Oracle:
             raise ValueError("oracle_local_terms: bad arguments")
         return out
 
+    # ----------------------------------------------------- penalty smoothing (Sec. 4.4)
+    def smooth_objective(self, X, y, eps, M: float, p: float, norm: int = NORM_L2, mon=None, w=None):
+        """(Phi, grad [N], S1, S2) of Eq. (optim) at eps; S1 and S2 are its two penalty sums."""
+        X, y, w, eps = _f64(X), _f64(y), _f64(w), _f64(eps)
+        N, d = X.shape
+        mon = _mon(mon, d)
+        f, s1, s2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        g = np.empty(N)
+        rc = self.lib.oracle_smooth_objective(_ptr(X), _ptr(y), N, d, float(M), int(norm), _ptr(mon), _ptr(w),
+                                              float(p), _ptr(eps), ctypes.byref(f), _ptr(g), ctypes.byref(s1),
+                                              ctypes.byref(s2))
+        if rc != 0:
+            raise ValueError("oracle_smooth_objective: bad arguments")
+        return f.value, g, s1.value, s2.value
+
+    def smooth(self, X, y, M: float, p: float, norm: int = NORM_L2, mon=None, w=None, max_iter: int = 500,
+               hist: int = 10, gtol: float = 1e-10):
+        """(eps [N], Phi, iterations): the L-BFGS minimiser of Eq. (optim) from eps = 0."""
+        X, y, w = _f64(X), _f64(y), _f64(w)
+        N, d = X.shape
+        mon = _mon(mon, d)
+        eps = np.empty(N)
+        f, it = ctypes.c_double(), ctypes.c_int()
+        rc = self.lib.oracle_smooth(_ptr(X), _ptr(y), N, d, float(M), int(norm), _ptr(mon), _ptr(w), float(p),
+                                    int(max_iter), int(hist), float(gtol), _ptr(eps), ctypes.byref(f),
+                                    ctypes.byref(it))
+        if rc != 0:
+            raise ValueError("oracle_smooth: bad arguments")
+        return eps, f.value, it.value
+
 
 _default: Optional[Oracle] = None
 
@@ -312,3 +347,11 @@ def local_terms(*a, **k):
 
 def local_table_rows(*a, **k):
     return default().local_table_rows(*a, **k)
+
+
+def smooth_objective(*a, **k):
+    return default().smooth_objective(*a, **k)
+
+
+def smooth(*a, **k):
+    return default().smooth(*a, **k)

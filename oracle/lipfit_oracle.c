@@ -592,3 +592,143 @@ int oracle_local_terms(const double* X, const double* y, int64_t N, int d, int n
     }
     return 0;
 }
+
+/* ------------------------------------------------ penalty smoothing (Sec. 4.4, Eq. (optim)) */
+/*
+ * Changes eps to the data values are chosen to minimise
+ *
+ *   Phi(eps) = (1/p) ||eps||^2
+ *            + sum_{i != k} ( (y_i - y_k - M d+_ik - (eps_k - eps_i))_+ )^2        [Eq. (const1)]
+ *            + sum_{i != k} ( (y_k - y_i - M d-_ik + eps_k - eps_i)_+ )^2          [Eq. (const2)]
+ *
+ * Eq. (const1) asks y_i + eps_i <= y_k + eps_k + M d_ik, the condition for the upper bound
+ * at x^i to be at least the smoothed value there, so its distance is dist_up(x^i, x^k);
+ * Eq. (const2) asks y_i + eps_i >= y_k + eps_k - M d_ik, the lower-bound condition, with
+ * dist_lo(x^i, x^k).  Without monotone coordinates both are the symmetric distance.
+ * The gradient differentiates each term: a positive part v of const1 adds 2v to
+ * dPhi/deps_i and -2v to dPhi/deps_k; one of const2 adds 2v to dPhi/deps_k and -2v to
+ * dPhi/deps_i; the first term adds (2/p) eps.
+ *
+ * The minimiser is found with L-BFGS (Nocedal and Wright, Numerical Optimization, 2nd ed.,
+ * Algorithms 7.4 and 7.5): the two-loop recursion with the initial scaling
+ * gamma = s'y / y'y of the newest pair, a backtracking line search from step 1 halving the
+ * step until the Armijo condition Phi(eps + a d) <= Phi(eps) + 1e-4 a g'd holds, and a pair
+ * kept only when s'y > 1e-12 ||s|| ||y||.  It stops when max |g| <= gtol or after max_iter
+ * iterations.
+ */
+
+int oracle_smooth_objective(const double* X, const double* y, int64_t N, int d, double M, int norm,
+                            const int8_t* mon, const double* w, double p, const double* eps,
+                            double* f_out, double* grad, double* s1_out, double* s2_out) {
+    if (N < 1 || d < 1 || norm < 1 || norm > 3 || !(p > 0)) return 1;
+    double s1 = 0.0, s2 = 0.0, e2 = 0.0;
+    for (int64_t i = 0; i < N; i++) {
+        if (grad) grad[i] = 2.0 / p * eps[i];
+        e2 += eps[i] * eps[i];
+    }
+    for (int64_t i = 0; i < N; i++) {
+        const double* xi = X + i * d;
+        for (int64_t k = 0; k < N; k++) {
+            if (k == i) continue;
+            const double* xk = X + k * d;
+            double dup = oracle_dist(xi, xk, d, norm, mon, w, +1);
+            double dlo = oracle_dist(xi, xk, d, norm, mon, w, -1);
+            double v1 = y[i] - y[k] - M * dup - (eps[k] - eps[i]);
+            double v2 = y[k] - y[i] - M * dlo + eps[k] - eps[i];
+            if (v1 > 0) {
+                s1 += v1 * v1;
+                if (grad) { grad[i] += 2.0 * v1; grad[k] -= 2.0 * v1; }
+            }
+            if (v2 > 0) {
+                s2 += v2 * v2;
+                if (grad) { grad[k] += 2.0 * v2; grad[i] -= 2.0 * v2; }
+            }
+        }
+    }
+    if (f_out) *f_out = e2 / p + s1 + s2;
+    if (s1_out) *s1_out = s1;
+    if (s2_out) *s2_out = s2;
+    return 0;
+}
+
+static double dotv(const double* a, const double* b, int64_t n) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; i++) s += a[i] * b[i];
+    return s;
+}
+
+/* L-BFGS from eps = 0; eps_out [N] receives the minimiser, *f_out Phi there, *iters_out the
+ * iterations taken.  hist (1..64) is the number of stored pairs. */
+int oracle_smooth(const double* X, const double* y, int64_t N, int d, double M, int norm,
+                  const int8_t* mon, const double* w, double p, int max_iter, int hist, double gtol,
+                  double* eps_out, double* f_out, int* iters_out) {
+    if (N < 1 || d < 1 || norm < 1 || norm > 3 || !(p > 0) || hist < 1 || hist > 64 || max_iter < 0) return 1;
+    double* buf = (double*)calloc((size_t)N * (5 + 2 * hist), sizeof(double));
+    if (!buf) return 2;
+    double *x = eps_out, *g = buf, *dir = buf + N, *xn = buf + 2 * N, *gn = buf + 3 * N, *q = buf + 4 * N;
+    double* S = buf + 5 * N;
+    double* Y = S + (size_t)hist * N;
+    double rho[64], alpha[64];
+    int nstore = 0, head = 0;       /* pairs in the ring, index of the oldest */
+    for (int64_t i = 0; i < N; i++) x[i] = 0.0;
+    double f;
+    oracle_smooth_objective(X, y, N, d, M, norm, mon, w, p, x, &f, g, NULL, NULL);
+    int it = 0;
+    for (; it < max_iter; it++) {
+        double gmax = 0.0;
+        for (int64_t i = 0; i < N; i++) if (fabs(g[i]) > gmax) gmax = fabs(g[i]);
+        if (gmax <= gtol) break;
+        /* two-loop recursion: q = H g */
+        for (int64_t i = 0; i < N; i++) q[i] = g[i];
+        for (int j = nstore - 1; j >= 0; j--) {
+            int s = (head + j) % hist;
+            alpha[s] = rho[s] * dotv(S + (size_t)s * N, q, N);
+            for (int64_t i = 0; i < N; i++) q[i] -= alpha[s] * Y[(size_t)s * N + i];
+        }
+        double gamma = 1.0;
+        if (nstore > 0) {
+            int s = (head + nstore - 1) % hist;
+            gamma = dotv(S + (size_t)s * N, Y + (size_t)s * N, N) / dotv(Y + (size_t)s * N, Y + (size_t)s * N, N);
+        }
+        for (int64_t i = 0; i < N; i++) q[i] *= gamma;
+        for (int j = 0; j < nstore; j++) {
+            int s = (head + j) % hist;
+            double beta = rho[s] * dotv(Y + (size_t)s * N, q, N);
+            for (int64_t i = 0; i < N; i++) q[i] += S[(size_t)s * N + i] * (alpha[s] - beta);
+        }
+        for (int64_t i = 0; i < N; i++) dir[i] = -q[i];
+        double gd = dotv(g, dir, N);
+        if (!(gd < 0)) {            /* not a descent direction: restart from steepest descent */
+            for (int64_t i = 0; i < N; i++) dir[i] = -g[i];
+            gd = dotv(g, dir, N);
+            nstore = 0;
+        }
+        /* backtracking Armijo line search */
+        double a = 1.0, fn = f;
+        int ok = 0;
+        for (int ls = 0; ls < 60; ls++) {
+            for (int64_t i = 0; i < N; i++) xn[i] = x[i] + a * dir[i];
+            oracle_smooth_objective(X, y, N, d, M, norm, mon, w, p, xn, &fn, gn, NULL, NULL);
+            if (fn <= f + 1e-4 * a * gd) { ok = 1; break; }
+            a *= 0.5;
+        }
+        if (!ok) break;
+        /* curvature pair s = xn - x, y = gn - g (in q and dir, free now); stored in the
+         * ring, replacing the oldest when full, only if s'y is clearly positive */
+        for (int64_t i = 0; i < N; i++) { q[i] = xn[i] - x[i]; dir[i] = gn[i] - g[i]; }
+        double sy = dotv(q, dir, N);
+        if (sy > 1e-12 * sqrt(dotv(q, q, N) * dotv(dir, dir, N))) {
+            int slot = nstore < hist ? (head + nstore) % hist : head;
+            for (int64_t i = 0; i < N; i++) { S[(size_t)slot * N + i] = q[i]; Y[(size_t)slot * N + i] = dir[i]; }
+            rho[slot] = 1.0 / sy;
+            if (nstore < hist) nstore++;
+            else head = (head + 1) % hist;
+        }
+        for (int64_t i = 0; i < N; i++) { x[i] = xn[i]; g[i] = gn[i]; }
+        f = fn;
+    }
+    if (f_out) *f_out = f;
+    if (iters_out) *iters_out = it;
+    free(buf);
+    return 0;
+}

@@ -509,7 +509,72 @@ def check_local_eval(O):
         np.testing.assert_allclose(rl.lo, rg.lo, atol=1e-12)
 
 
+
+# --------------------------------------------------------- penalty smoothing (Sec. 4.4)
+
+def _two_point_eps(a, p):
+    """Minimiser of Eq. (optim) for two data with one violated constraint of size a > 0:
+    by symmetry eps = (-t, t) and Phi = 2 t^2 / p + 2 (a - 2t)^2, so t = 2 a p / (1 + 4 p)."""
+    return 2.0 * a * p / (1.0 + 4.0 * p)
+
+
+def check_smoothing(O):
+    """Eq. (optim): the two-point closed form (plain and monotone), gradient against central
+    differences, the two penalty sums equal (Eq. (const2) is Eq. (const1) with i and k
+    swapped), consistent data untouched, and the returned point a minimiser."""
+    for p in (0.5, 10.0, 1e4):
+        for M, x2, y1, y2 in ((1.0, 1.0, 3.0, 0.0), (2.0, 0.5, -1.0, 4.0), (0.0, 2.0, 1.0, 0.25)):
+            X = np.array([[0.0], [x2]])
+            y = np.array([y1, y2])
+            a = abs(y1 - y2) - M * x2
+            e, f, _ = O.smooth(X, y, M, p, 1, max_iter=200, gtol=1e-13)
+            t = _two_point_eps(a, p)
+            sgn = 1.0 if y1 > y2 else -1.0
+            np.testing.assert_allclose(e, [-sgn * t, sgn * t], rtol=1e-9, atol=1e-12)
+            np.testing.assert_allclose(f, 2 * t * t / p + 2 * (a - 2 * t) ** 2, rtol=1e-9, atol=1e-15)
+        # increasing in x1: x^1 < x^2 with y^1 > y^2 violates with distance 0
+        X = np.array([[0.0, 0.3], [0.4, 0.3]])
+        e, _, _ = O.smooth(X, np.array([1.0, 0.2]), 5.0, p, 2, mon=np.array([1, 0], np.int8), gtol=1e-13)
+        t = _two_point_eps(0.8, p)
+        np.testing.assert_allclose(e, [-t, t], rtol=1e-9, atol=1e-12)
+    rng = np.random.default_rng(11)
+    for norm in (1, 2, 3):
+        for mon, w in ((None, None), (np.array([1, -1, 0], np.int8), np.array([0.5, 2.0, 1.0]))):
+            X = rng.random((25, 3))
+            y = np.sin(4 * X[:, 0]) + 0.5 * rng.standard_normal(25)
+            eps = 0.1 * rng.standard_normal(25)
+            M, p = 1.5, 20.0
+            f, g, s1, s2 = O.smooth_objective(X, y, eps, M, p, norm, mon=mon, w=w)
+            assert s1 > 0 and abs(s1 - s2) <= 1e-12 * s1
+            assert abs(f - (eps @ eps / p + s1 + s2)) <= 1e-12 * f
+            h = 1e-6
+            for j in range(0, 25, 3):
+                ep, em = eps.copy(), eps.copy()
+                ep[j] += h
+                em[j] -= h
+                fd = (O.smooth_objective(X, y, ep, M, p, norm, mon=mon, w=w)[0] -
+                      O.smooth_objective(X, y, em, M, p, norm, mon=mon, w=w)[0]) / (2 * h)
+                assert abs(fd - g[j]) <= 1e-5 * (1 + abs(g[j])), (norm, j, fd, g[j])
+            e, fmin, it = O.smooth(X, y, M, p, norm, mon=mon, w=w, max_iter=3000, gtol=1e-8)
+            fe, ge, _, _ = O.smooth_objective(X, y, e, M, p, norm, mon=mon, w=w)
+            assert np.abs(ge).max() <= 1e-8 and abs(fe - fmin) <= 1e-14 * max(1.0, fe)
+            for _ in range(5):                        # convex: no nearby point is lower
+                dlt = 1e-3 * rng.standard_normal(25)
+                assert O.smooth_objective(X, y, e + dlt, M, p, norm, mon=mon, w=w)[0] >= fe
+    # data consistent with M: nothing to change
+    pr = W.random_problem(301, 40, 2, 1, norm=2)
+    e, f, it = O.smooth(pr.X, pr.y, pr.M, 100.0, 2)
+    assert it == 0 and f == 0.0 and np.all(e == 0.0)
+    # a large penalty weight leaves (almost) consistent data
+    X = rng.random((30, 2))
+    y = X[:, 0] + 0.3 * rng.standard_normal(30)
+    e, _, _ = O.smooth(X, y, 1.0, 1e6, 2, max_iter=5000, gtol=1e-8)
+    M_after = O.estimate_M(X, y + e, 2)[0]
+    assert M_after <= 1.0 + 1e-3, M_after
+
+
 ALL_CHECKS = [check_hand_examples, check_closed_form_1d, check_unmasked_cdist, check_interpolation,
               check_enclosure, check_lipschitz_monotone, check_width_bound, check_special_cases,
               check_estimate_M, check_gradient_fd, check_k_neighbours, check_splitmix64,
-              check_local_hand_example, check_local_knots, check_local_table, check_local_eval]
+              check_local_hand_example, check_local_knots, check_local_table, check_local_eval,
+              check_smoothing]

@@ -39,6 +39,17 @@ MUTANTS = {
     "local_quantile_round": ("((int64_t)i * kept + m - 1) / m;", "((int64_t)i * kept + m / 2) / m;", 1),
     "local_ratio_signed": ("double r = fabs(J->y[k] - J->y[j]) / dd;\n            if (dd < d1)",
                            "double r = (J->y[k] - J->y[j]) / dd;\n            if (dd < d1)", 1),
+    # penalty smoothing (Sec. 4.4): the sign of eps in Eq. (const2) flipped
+    "smooth_const2_eps_sign": ("double v2 = y[k] - y[i] - M * dlo + eps[k] - eps[i];",
+                               "double v2 = y[k] - y[i] - M * dlo - eps[k] + eps[i];", 1),
+    "smooth_grad_factor": ("if (grad) { grad[i] += 2.0 * v1; grad[k] -= 2.0 * v1; }",
+                           "if (grad) { grad[i] += v1; grad[k] -= v1; }", 1),
+    "smooth_penalty_weight": ("if (f_out) *f_out = e2 / p + s1 + s2;", "if (f_out) *f_out = e2 * p + s1 + s2;", 1),
+    # Eq. (const2) with the upper-bound distance (differs only with monotone coordinates)
+    "smooth_const2_dup": ("double dlo = oracle_dist(xi, xk, d, norm, mon, w, -1);",
+                          "double dlo = oracle_dist(xi, xk, d, norm, mon, w, +1);", 1),
+    # L-BFGS search direction along +H g
+    "lbfgs_ascent": ("for (int64_t i = 0; i < N; i++) dir[i] = -q[i];", "for (int64_t i = 0; i < N; i++) dir[i] = q[i];", 1),
     "splitmix_shift": ("z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBull;", 1),
 }
 

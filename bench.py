@@ -44,7 +44,9 @@ UNIT = "G pairs/s"
 NORMS = (W.NORM_L1, W.NORM_L2, W.NORM_LINF)
 NNAME = {1: "L1", 2: "L2", 3: "Linf"}
 FP32_LANES_PER_SM = 128
-WORKLOADS = ("monotone_d4", "plain_d2", "cluster_d16", "cluster_d16_tc", "grad_d8", "batch_4096", "local_d4")
+WORKLOADS = ("monotone_d4", "plain_d2", "cluster_d16", "cluster_d16_tc", "grad_d8", "batch_4096", "local_d4",
+             "smooth_d4")
+SMOOTH_ITERS = 10
 LOCAL_KNOTS, LOCAL_SAMPLE, LOCAL_SEED = 16, 32768, 0
 # TF32 dense peak: the measured BF16 peak times the nominal TF32 / BF16 ratio (1.1 / 2.25)
 TF32_OVER_BF16 = 1.1 / 2.25
@@ -244,6 +246,9 @@ def run_reference(args):
     if args.workload == "local_d4":
         problems = W.local_d4()
         rate = lambda sec: oracle_local_rate(problems, sec)  # noqa: E731
+    elif args.workload == "smooth_d4":
+        problems = W.smooth_d4()
+        rate = lambda sec: oracle_smooth_rate(problems, sec)  # noqa: E731
     else:
         problems = reference_problems(args.workload)
         rate = lambda sec: oracle_rate(problems, sec)  # noqa: E731
@@ -689,6 +694,107 @@ def wl_local(ctx, name="local_d4"):
     return ctx.line(value, total, args.steps, "f32", config, roof, cpu, e2e, clocks, launches, detail)
 
 
+def oracle_smooth_rate(p, seconds: float, rng_seed=5):
+    """Pairs/s of the FP64 oracle's smoothing objective and gradient (Eq. (optim)) on the
+    first n points of the workload, n sized so one evaluation takes about `seconds`."""
+    import oracle
+    o = oracle.default()
+    n = 2000
+    t0 = time.perf_counter()
+    eps = np.zeros(n)
+    o.smooth_objective(p.X[:n], p.y[:n], eps, W.SMOOTH_M, W.SMOOTH_P, p.norm)
+    per_pair = max(time.perf_counter() - t0, 1e-4) / (n * (n - 1))
+    n = int(min(p.N, max(2000, np.sqrt(seconds / per_pair))))
+    eps = 0.02 * np.random.default_rng(rng_seed).standard_normal(n)
+    t0 = time.perf_counter()
+    o.smooth_objective(p.X[:n], p.y[:n], eps, W.SMOOTH_M, W.SMOOTH_P, p.norm)
+    dt = time.perf_counter() - t0
+    pairs = n * (n - 1)
+    return {"value": pairs / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{pairs:.3g} ordered pairs: one objective and gradient evaluation on the first {n} data "
+                      f"points (FP64, single thread, {dt:.1f} s)"}, dt
+
+
+def wl_smooth(ctx, name="smooth_d4"):
+    """Penalty smoothing (Sec. 4.4): per step, fit + lip_smooth with a fixed SMOOTH_ITERS
+    L-BFGS iterations (gtol 0).  value = ordered data pairs x objective evaluations / time."""
+    from paper_2606_04670_b300 import lipfit as L
+    torch, args = ctx.torch, ctx.args
+    p = W.smooth_d4()
+    X, y = (torch.as_tensor(a).cuda() for a in (p.X, p.y))
+    m = L.LipFit(M=p.M, norm=p.norm, capacity=p.N, d=p.d)
+    evals = []
+
+    def step():
+        m.clear()
+        m.add(X, y)
+        _, _, _, ev = m.smooth_lipschitz(W.SMOOTH_M, W.SMOOTH_P, max_iter=SMOOTH_ITERS, gtol=0.0)
+        evals.append(ev)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    evals.clear()
+    ms, clocks, launches = ctx.timed(step, args.steps)
+    pairs = float(p.N) * (p.N - 1)
+    value, total = aggregate(pairs * sum(evals), sum(ms), device="cuda")
+    # one objective pass alone, on the launching stream, for the roofline
+    eps = torch.zeros(p.N, dtype=torch.float64, device="cuda")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m.smooth_objective(eps, W.SMOOTH_M, W.SMOOTH_P)
+    pass_ms = []
+    for _ in range(5):
+        ctx.flush()
+        torch.cuda.synchronize()
+        a.record()
+        m.smooth_objective(eps, W.SMOOTH_M, W.SMOOTH_P)
+        b.record()
+        torch.cuda.synchronize()
+        pass_ms.append(a.elapsed_time(b))
+    ms_pass = statistics.median(pass_ms)
+    # per ordered pair: distance 2d, dz, two terms, two positive parts, two sums, one FMA; one MUFU sqrt
+    ip = 2 * p.d + 8
+    roof = ctx.roofline(f"smooth_pass_kernel<{NNAME[p.norm]}, DP=4> (+ layout and sums)", ip * pairs, ms_pass, ip,
+                        1 if p.norm == W.NORM_L2 else 0, clocks)
+    e2e = None
+    if not args.no_e2e:
+        hX, hy = (torch.as_tensor(a).pin_memory() for a in (p.X, p.y))
+        heps = torch.empty(p.N, dtype=torch.float64).pin_memory()
+        ev2 = []
+
+        def step_host():
+            m.clear()
+            m.add_host(hX, hy)
+            e, _, _, ev = m.smooth_lipschitz(W.SMOOTH_M, W.SMOOTH_P, max_iter=SMOOTH_ITERS, gtol=0.0)
+            heps.copy_(e, non_blocking=True)
+            ev2.append(ev)
+
+        step_host()
+        torch.cuda.synchronize()
+        ev2.clear()
+        e2e_ms = []
+        for _ in range(args.steps):
+            ctx.flush()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step_host()
+            torch.cuda.synchronize()
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        ev_, tot = aggregate(pairs * sum(ev2), sum(e2e_ms), device="cuda")
+        e2e = {"value": ev_, "unit": UNIT, "ms_per_step": tot / args.steps,
+               "h2d_bytes_per_step": hX.numel() * 4 + hy.numel() * 4, "d2h_bytes_per_step": heps.numel() * 8}
+    cpu = None
+    if ctx.rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_smooth_rate(p, min(args.cpu_seconds, 10.0))[0]
+    detail = {"objective_pass_ms": ms_pass, "pass_gpairs_per_s": pairs / (ms_pass / 1e3) / 1e9,
+              "evaluations_per_step": statistics.mean(evals), "iterations_per_step": SMOOTH_ITERS}
+    m.close()
+    config = {"workload": name, "d": p.d, "N": p.N, "norms": [NNAME[p.norm]], "M": W.SMOOTH_M, "p": W.SMOOTH_P,
+              "step": f"fit + lip_smooth ({SMOOTH_ITERS} L-BFGS iterations, every objective evaluation a pass over "
+                      f"all N (N - 1) ordered pairs)",
+              "l2": "flushed before every timed step (256 MB write)"}
+    return ctx.line(value, total, args.steps, "f32", config, roof, cpu, e2e, clocks, launches, detail)
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -714,6 +820,8 @@ def run_ours(args):
         line = wl_single(ctx, w, [W.grad_d8()], with_bwd=True)
     elif w == "local_d4":
         line = wl_local(ctx)
+    elif w == "smooth_d4":
+        line = wl_smooth(ctx)
     else:
         line = wl_batch(ctx)
     if rank == 0:

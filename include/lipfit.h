@@ -275,6 +275,36 @@ LIP_API lip_status lip_local_table(lip_handle h, double* d1, double* F, double* 
 LIP_API lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi,
                                   int32_t* idx_up, int32_t* idx_lo, void* stream);
 
+/* ------------------------------------------------ penalty smoothing (Sec. 4.4) */
+/* smooth_lipschitz(LC, model) of Sec. 5: changes eps to the data values minimising
+ *
+ *   Phi(eps) = (1/p) ||eps||^2
+ *            + sum_{i != k} ((y_i - y_k - M d+_ik - (eps_k - eps_i))_+)^2      Eq. (const1)
+ *            + sum_{i != k} ((y_k - y_i - M d-_ik + eps_k - eps_i)_+)^2        Eq. (const2)
+ *
+ * (Eq. (optim)), d+_ik = dist_up(x^i, x^k) and d-_ik = dist_lo(x^i, x^k) of the handle's
+ * norm, weights and monotone coordinates (both the symmetric distance without them).
+ * One evaluation is a fused pass over all N (N - 1) ordered pairs in FP32 with FP64 sums;
+ * nothing pairwise is stored.  Handles: float data (LIP_FP32 or LIP_TC_TF32), N >= 1;
+ * M finite >= 0, p finite > 0.  FP64 handles: LIP_ERR_UNSUPPORTED. */
+
+/* Phi and its gradient at eps (device double [N]): *f_out (host), grad (device double [N],
+ * may be NULL).  Synchronises the stream. */
+LIP_API lip_status lip_smooth_objective(lip_handle h, double M, double p, const double* eps, double* f_out,
+                                        double* grad, void* stream);
+
+/* Minimise Phi with L-BFGS from eps = 0 (Nocedal and Wright, Algorithms 7.4/7.5: history
+ * pairs 1..64, backtracking Armijo line search from step 1), stopping when max |dPhi/deps|
+ * <= gtol or after max_iter iterations.  Then, as the paper's package does, the handle's
+ * values become y + eps (rounded to float) and its constant becomes M, so lip_eval
+ * evaluates the smoothed interpolant at once; a local Lipschitz table is invalidated.
+ * eps_out (device double [N]) may be NULL; *f_out = Phi at the result, *iters_out = the
+ * iterations taken, *evals_out = the objective evaluations (host, each may be NULL).  Synchronises the stream many times (the line
+ * search reads Phi).  Errors: LIP_ERR_ARG, LIP_ERR_UNSUPPORTED, LIP_ERR_OOM, LIP_ERR_CUDA. */
+LIP_API lip_status lip_smooth(lip_handle h, double M, double p, int32_t max_iter, int32_t history, double gtol,
+                              double* eps_out, double* f_out, int32_t* iters_out, int32_t* evals_out,
+                              void* stream);
+
 /* ---------------------------------------------------------------- differentiation */
 
 /* Gradient of L = sum_q grad_g[q] * g(q) through the saved argmin/argmax (g is piecewise

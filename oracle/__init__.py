@@ -99,6 +99,8 @@ class Oracle:
         lib.oracle_smooth_objective.argtypes = [P, P, i64, i32, f64, i32, P, P, f64, P, P, P, P, P]
         lib.oracle_smooth.argtypes = [P, P, i64, i32, f64, i32, P, P, f64, i32, i32, f64, P, P, P]
         lib.oracle_smooth_objective.restype = ctypes.c_int
+        lib.oracle_smooth_grad_rows.argtypes = [P, P, i64, i32, f64, i32, P, P, f64, P, P, i64, P]
+        lib.oracle_smooth_grad_rows.restype = ctypes.c_int
         lib.oracle_smooth.restype = ctypes.c_int
         for fn in (lib.oracle_eval, lib.oracle_estimate_M, lib.oracle_estimate_M_rows, lib.oracle_grad,
                    lib.oracle_eval_k, lib.oracle_local_knots, lib.oracle_local_table, lib.oracle_local_table_rows,
@@ -279,6 +281,19 @@ class Oracle:
             raise ValueError("oracle_smooth_objective: bad arguments")
         return f.value, g, s1.value, s2.value
 
+    def smooth_grad_rows(self, X, y, eps, rows, M: float, p: float, norm: int = NORM_L2, mon=None, w=None):
+        """dPhi/deps_j for j in rows (O(N) per row)."""
+        X, y, w, eps = _f64(X), _f64(y), _f64(w), _f64(eps)
+        N, d = X.shape
+        mon = _mon(mon, d)
+        rows = np.ascontiguousarray(rows, np.int64)
+        out = np.empty(rows.shape[0])
+        rc = self.lib.oracle_smooth_grad_rows(_ptr(X), _ptr(y), N, d, float(M), int(norm), _ptr(mon), _ptr(w),
+                                              float(p), _ptr(eps), _ptr(rows), rows.shape[0], _ptr(out))
+        if rc != 0:
+            raise ValueError("oracle_smooth_grad_rows: bad arguments")
+        return out
+
     def smooth(self, X, y, M: float, p: float, norm: int = NORM_L2, mon=None, w=None, max_iter: int = 500,
                hist: int = 10, gtol: float = 1e-10):
         """(eps [N], Phi, iterations): the L-BFGS minimiser of Eq. (optim) from eps = 0."""
@@ -355,3 +370,7 @@ def smooth_objective(*a, **k):
 
 def smooth(*a, **k):
     return default().smooth(*a, **k)
+
+
+def smooth_grad_rows(*a, **k):
+    return default().smooth_grad_rows(*a, **k)

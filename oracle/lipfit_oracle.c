@@ -651,6 +651,35 @@ int oracle_smooth_objective(const double* X, const double* y, int64_t N, int d, 
     return 0;
 }
 
+/* dPhi/deps_j for the data rows[0..nrows) only: the terms of both sums in which j is the
+ * first or the second index, O(N) per row. */
+int oracle_smooth_grad_rows(const double* X, const double* y, int64_t N, int d, double M, int norm,
+                            const int8_t* mon, const double* w, double p, const double* eps,
+                            const int64_t* rows, int64_t nrows, double* out) {
+    if (N < 1 || d < 1 || norm < 1 || norm > 3 || !(p > 0)) return 1;
+    for (int64_t o = 0; o < nrows; o++) {
+        const int64_t j = rows[o];
+        if (j < 0 || j >= N) return 1;
+        double g = 2.0 / p * eps[j];
+        for (int64_t k = 0; k < N; k++) {
+            if (k == j) continue;
+            const double *xj = X + j * d, *xk = X + k * d;
+            /* pair (i = j, k) */
+            double v1 = y[j] - y[k] - M * oracle_dist(xj, xk, d, norm, mon, w, +1) - (eps[k] - eps[j]);
+            double v2 = y[k] - y[j] - M * oracle_dist(xj, xk, d, norm, mon, w, -1) + eps[k] - eps[j];
+            if (v1 > 0) g += 2.0 * v1;
+            if (v2 > 0) g -= 2.0 * v2;
+            /* pair (i = k, k = j) */
+            v1 = y[k] - y[j] - M * oracle_dist(xk, xj, d, norm, mon, w, +1) - (eps[j] - eps[k]);
+            v2 = y[j] - y[k] - M * oracle_dist(xk, xj, d, norm, mon, w, -1) + eps[j] - eps[k];
+            if (v1 > 0) g -= 2.0 * v1;
+            if (v2 > 0) g += 2.0 * v2;
+        }
+        out[o] = g;
+    }
+    return 0;
+}
+
 static double dotv(const double* a, const double* b, int64_t n) {
     double s = 0.0;
     for (int64_t i = 0; i < n; i++) s += a[i] * b[i];

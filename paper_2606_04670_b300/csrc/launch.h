@@ -174,4 +174,31 @@ cudaError_t launch_local_table(const LocalParams& P, cudaStream_t st);
 cudaError_t launch_local_eval(int norm, const LocalScanParams& S, int gx, int nsplit, bool bucket,
                               const LocalMergeParams& M, cudaStream_t st);
 
+// ------------------------------------------------ penalty smoothing (Sec. 4.4)
+
+struct SmoothParams {
+    const float* X0;                 // caller's data [N][d]
+    const float* y0;
+    int64_t N, npad;
+    int d, dp, C, norm;              // dp: d rounded up to 4; C: constrained coordinates (first)
+    int perm[D_MAX];
+    double scale[D_MAX];             // M * w * sign, in layout order
+    double p;                        // penalty weight of Eq. (optim)
+    float* rec;                      // [npad][dp + 4]: scaled coordinates, z = y + eps, 0, 0, 0
+    double* partial;                 // [nsplit][N][3]: R, C, S per split
+    int nsplit;
+    int64_t points_per_split;
+};
+
+int smooth_tile();
+int smooth_threads();
+int smooth_reduce_blocks();
+cudaError_t launch_smooth_objective(const SmoothParams& P, const double* eps, double* grad, double* block_sums,
+                                    double* out, int gx, cudaStream_t st);
+cudaError_t launch_vec_reduce(const double* a, const double* b, int64_t n, int op, double* partial, double* out,
+                              cudaStream_t st);
+cudaError_t launch_vec_axpy(double* out, const double* a, double alpha, const double* b, int64_t n, cudaStream_t st);
+cudaError_t launch_vec_scale(double* out, const double* a, double alpha, int64_t n, cudaStream_t st);
+cudaError_t launch_apply_eps(float* y0, const double* eps, int64_t n, cudaStream_t st);
+
 }  // namespace lip

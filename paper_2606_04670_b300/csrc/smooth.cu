@@ -1,0 +1,276 @@
+// Penalty smoothing (Sec. 4.4, Eq. (optim)): the objective
+//
+//   Phi(eps) = (1/p) ||eps||^2 + S1 + S2,
+//   S1 = sum_{i != k} ((z_i - z_k - M dist_up(x^i, x^k))_+)^2          Eq. (const1)
+//   S2 = sum_{i != k} ((z_k - z_i - M dist_lo(x^i, x^k))_+)^2          Eq. (const2)
+//
+// with z = y + eps, and its gradient, as one fused pass over all ordered pairs (no N x N
+// storage), driven by L-BFGS.  dist_lo(x^i, x^k) = dist_up(x^k, x^i), so Eq. (const2)'s
+// term of (i, k) is Eq. (const1)'s term of (k, i): S2 = S1 and
+//
+//   Phi = ||eps||^2 / p + 2 S1,   dPhi/deps_j = 2 eps_j / p + 4 (R_j - C_j),
+//   R_j = sum_k (z_j - z_k - M dist_up(x^j, x^k))_+,  C_j = sum_i (z_i - z_j - M dist_up(x^i, x^j))_+.
+//
+// The pass gives thread i the row i: for every k it forms both v_ik (its const1 term) and
+// v_ki (the term with i second), so R_i, C_i and the row's share of S1 need no atomics.
+// Pair terms are FP32 on the scaled layout (coordinates times M w, mirrored where
+// decreasing, constrained first); each thread adds them in FP32 within a 128-point tile
+// and in FP64 across tiles, and the splits are summed in FP64 in a fixed order.
+#include "launch.h"
+
+namespace lip {
+
+namespace {
+
+constexpr int SM_THREADS = 128;
+constexpr int SM_TILE = 128;
+constexpr int RED_BLOCKS = 256;     // fixed reduction shape: results do not depend on timing
+
+__global__ void smooth_layout_kernel(const SmoothParams P, const double* eps) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.npad) return;
+    float* r = P.rec + k * (P.dp + 4);
+    if (k < P.N) {
+        const float* x = P.X0 + k * P.d;
+        for (int j = 0; j < P.dp; ++j) r[j] = j < P.d ? (float)(P.scale[j] * (double)x[P.perm[j]]) : 0.f;
+        r[P.dp] = (float)((double)P.y0[k] + eps[k]);
+    } else {
+        for (int j = 0; j < P.dp; ++j) r[j] = 0.f;
+        r[P.dp] = __int_as_float(0x7fc00000);          // padding: NaN terms are never positive
+    }
+    r[P.dp + 1] = r[P.dp + 2] = r[P.dp + 3] = 0.f;
+}
+
+// dist_up(a, b) (positive parts (a - b)_+ on the first C coordinates, |a - b| on the
+// rest) and dist_up(b, a), on the scaled layout.
+template <int NORM, int DP, bool MONO>
+__device__ __forceinline__ void dist_pair(const float* a, const float* b, int C, float& du, float& dr) {
+    float au = 0.f, ar = 0.f;
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+        const float t = a[j] - b[j];
+        float u, r;
+        if (MONO && j < C) { u = fmaxf(t, 0.f); r = fmaxf(-t, 0.f); }
+        else { u = fabsf(t); r = u; }
+        if (NORM == LIP_L1) { au += u; if (MONO) ar += r; }
+        else if (NORM == LIP_L2) { au = fmaf(u, u, au); if (MONO) ar = fmaf(r, r, ar); }
+        else { au = fmaxf(au, u); if (MONO) ar = fmaxf(ar, r); }
+    }
+    if (NORM == LIP_L2) {
+        au = sqrtf(au);
+        if (MONO) ar = sqrtf(ar);
+    }
+    du = au;
+    dr = MONO ? ar : au;
+}
+
+template <int NORM, int DP, bool MONO>
+__global__ void __launch_bounds__(SM_THREADS) smooth_pass_kernel(const SmoothParams P) {
+    constexpr int PR = DP + 4;
+    __shared__ float4 tile4[SM_TILE * PR / 4];
+    const float* tile = reinterpret_cast<const float*>(tile4);
+    const int tid = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * SM_THREADS + tid;
+    const int split = blockIdx.y;
+    const bool valid = i < P.N;
+    float xi[DP];
+#pragma unroll
+    for (int j = 0; j < DP; ++j) xi[j] = valid ? P.rec[i * PR + j] : 0.f;
+    const float zi = valid ? P.rec[i * PR + DP] : 0.f;
+    double R = 0.0, Cs = 0.0, S = 0.0;
+    const int64_t k_begin = (int64_t)split * P.points_per_split;
+    const int64_t k_end = k_begin + P.points_per_split < P.npad ? k_begin + P.points_per_split : P.npad;
+    for (int64_t k0 = k_begin; k0 < k_end; k0 += SM_TILE) {
+        __syncthreads();
+        const float4* src = reinterpret_cast<const float4*>(P.rec + k0 * PR);
+        for (int t = tid; t < SM_TILE * PR / 4; t += SM_THREADS) tile4[t] = src[t];
+        __syncthreads();
+        float r = 0.f, c = 0.f, s = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < SM_TILE; ++k) {
+            const float* xk = tile + k * PR;
+            float du, dr;
+            dist_pair<NORM, DP, MONO>(xi, xk, P.C, du, dr);
+            const float dz = zi - xk[DP];
+            const float v1 = dz - du;                 // const1 term of (i, k)
+            const float v2 = -dz - dr;                // const1 term of (k, i)
+            const float p1 = v1 > 0.f ? v1 : 0.f;     // NaN (padding) gives 0
+            const float p2 = v2 > 0.f ? v2 : 0.f;
+            r += p1;
+            c += p2;
+            s = fmaf(p1, p1, s);
+        }
+        R += (double)r;
+        Cs += (double)c;
+        S += (double)s;
+    }
+    if (!valid) return;
+    double* out = P.partial + ((int64_t)split * P.N + i) * 3;
+    out[0] = R;
+    out[1] = Cs;
+    out[2] = S;
+}
+
+// grad_i = 2 eps_i / p + 4 (R_i - C_i); per-block sums of S_i and eps_i^2.
+__global__ void __launch_bounds__(256) smooth_finish_kernel(const SmoothParams P, const double* eps, double* grad,
+                                                            double* block_sums) {
+    __shared__ double red[2][256];
+    double sS = 0.0, sE = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += (int64_t)gridDim.x * blockDim.x) {
+        double R = 0.0, C = 0.0, S = 0.0;
+        for (int s = 0; s < P.nsplit; ++s) {
+            const double* v = P.partial + ((int64_t)s * P.N + i) * 3;
+            R += v[0];
+            C += v[1];
+            S += v[2];
+        }
+        if (grad) grad[i] = 2.0 * eps[i] / P.p + 4.0 * (R - C);
+        sS += S;
+        sE += eps[i] * eps[i];
+    }
+    red[0][threadIdx.x] = sS;
+    red[1][threadIdx.x] = sE;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + w];
+            red[1][threadIdx.x] += red[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        block_sums[2 * blockIdx.x] = red[0][0];
+        block_sums[2 * blockIdx.x + 1] = red[1][0];
+    }
+}
+
+// Phi = sum eps^2 / p + 2 S1 from the block sums, in a fixed order.
+__global__ void smooth_total_kernel(const double* block_sums, int nblocks, double p, double* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double S = 0.0, E = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        S += block_sums[2 * b];
+        E += block_sums[2 * b + 1];
+    }
+    out[0] = E / p + 2.0 * S;
+    out[1] = S;
+}
+
+// ------------------------------------------------------------ vector kernels (L-BFGS)
+
+// Fixed-shape two-level reductions: per-block sums of a*b (op 0) or maxima of |a| (op 1),
+// then one block over the RED_BLOCKS partials.
+__global__ void __launch_bounds__(256) vec_reduce_kernel(const double* a, const double* b, int64_t n, int op,
+                                                         double* partial) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc = op == 0 ? acc + a[i] * b[i] : fmax(acc, fabs(a[i]));
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = op == 0 ? red[threadIdx.x] + red[threadIdx.x + w]
+                                                        : fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(256) vec_reduce_final_kernel(const double* partial, int nb, int op, double* out) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc = op == 0 ? acc + partial[i] : fmax(acc, partial[i]);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = op == 0 ? red[threadIdx.x] + red[threadIdx.x + w]
+                                                        : fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// out = a + alpha * b (out may alias a or b)
+__global__ void vec_axpy_kernel(double* out, const double* a, double alpha, const double* b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] + alpha * b[i];
+}
+
+__global__ void vec_scale_kernel(double* out, const double* a, double alpha, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = alpha * a[i];
+}
+
+// y0 <- y0 + eps (the smoothed values, in the handle's float storage)
+__global__ void apply_eps_kernel(float* y0, const double* eps, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y0[i] = (float)((double)y0[i] + eps[i]);
+}
+
+template <int NORM, int DP>
+void pass_shape(const SmoothParams& P, dim3 grid, cudaStream_t st) {
+    if (P.C > 0) smooth_pass_kernel<NORM, DP, true><<<grid, SM_THREADS, 0, st>>>(P);
+    else smooth_pass_kernel<NORM, DP, false><<<grid, SM_THREADS, 0, st>>>(P);
+}
+
+template <int NORM>
+void pass_norm(const SmoothParams& P, dim3 grid, cudaStream_t st) {
+    switch (P.dp) {
+        case 4: pass_shape<NORM, 4>(P, grid, st); break;
+        case 8: pass_shape<NORM, 8>(P, grid, st); break;
+        case 12: pass_shape<NORM, 12>(P, grid, st); break;
+        default: pass_shape<NORM, 16>(P, grid, st); break;
+    }
+}
+
+}  // namespace
+
+int smooth_tile() { return SM_TILE; }
+int smooth_threads() { return SM_THREADS; }
+int smooth_reduce_blocks() { return RED_BLOCKS; }
+
+// Phi and its gradient at eps: layout, the pair pass, the finishing sums.  out[0] = Phi,
+// out[1] = S1 (device); grad may be NULL.  block_sums holds 2 * RED_BLOCKS doubles.
+cudaError_t launch_smooth_objective(const SmoothParams& P, const double* eps, double* grad, double* block_sums,
+                                    double* out, int gx, cudaStream_t st) {
+    smooth_layout_kernel<<<(unsigned)((P.npad + 255) / 256), 256, 0, st>>>(P, eps);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)gx, (unsigned)P.nsplit);
+    if (P.norm == LIP_L1) pass_norm<LIP_L1>(P, grid, st);
+    else if (P.norm == LIP_L2) pass_norm<LIP_L2>(P, grid, st);
+    else pass_norm<LIP_LINF>(P, grid, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    smooth_finish_kernel<<<RED_BLOCKS, 256, 0, st>>>(P, eps, grad, block_sums);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    smooth_total_kernel<<<1, 32, 0, st>>>(block_sums, RED_BLOCKS, P.p, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vec_reduce(const double* a, const double* b, int64_t n, int op, double* partial, double* out,
+                              cudaStream_t st) {
+    vec_reduce_kernel<<<RED_BLOCKS, 256, 0, st>>>(a, b, n, op, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    vec_reduce_final_kernel<<<1, 256, 0, st>>>(partial, RED_BLOCKS, op, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vec_axpy(double* out, const double* a, double alpha, const double* b, int64_t n, cudaStream_t st) {
+    vec_axpy_kernel<<<RED_BLOCKS, 256, 0, st>>>(out, a, alpha, b, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vec_scale(double* out, const double* a, double alpha, int64_t n, cudaStream_t st) {
+    vec_scale_kernel<<<RED_BLOCKS, 256, 0, st>>>(out, a, alpha, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_eps(float* y0, const double* eps, int64_t n, cudaStream_t st) {
+    apply_eps_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y0, eps, n);
+    return cudaGetLastError();
+}
+
+}  // namespace lip

@@ -96,6 +96,9 @@ def _load():
         "lip_local_knots": [H, P, P],
         "lip_local_table": [H, P, P, P, P],
         "lip_eval_local": [H, P, i64, P, P, P, P, P, P],
+        "lip_smooth_objective": [H, f64, f64, P, ctypes.POINTER(f64), P, P],
+        "lip_smooth": [H, f64, f64, i32, i32, f64, P, ctypes.POINTER(f64), ctypes.POINTER(i32),
+                       ctypes.POINTER(i32), P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -223,6 +226,19 @@ def lip_local_table(h, d1, F, Mtab, stream=0):
 
 def lip_eval_local(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream=0):
     return _lib.lip_eval_local(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream)
+
+
+def lip_smooth_objective(h, M, p, eps_ptr, grad_ptr, stream=0):
+    f = ctypes.c_double()
+    s = _lib.lip_smooth_objective(h, M, p, eps_ptr, ctypes.byref(f), grad_ptr, stream)
+    return s, f.value
+
+
+def lip_smooth(h, M, p, max_iter, history, gtol, eps_ptr, stream=0):
+    f, it, ev = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int32()
+    s = _lib.lip_smooth(h, M, p, max_iter, history, gtol, eps_ptr, ctypes.byref(f), ctypes.byref(it),
+                        ctypes.byref(ev), stream)
+    return s, f.value, it.value, ev.value
 
 
 def lip_eval_host(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream=0):
@@ -474,6 +490,28 @@ class LipFit:
                                                                                            "idx_lo")],
                                    _stream_ptr()), "lip_eval_local")
         return out
+
+    # --------------------------------------------------- penalty smoothing (Sec. 4.4)
+    def smooth_objective(self, eps, M: float, p: float, grad: bool = True):
+        """(Phi, grad) of Eq. (optim) at eps (float64 CUDA tensor [N])."""
+        torch = _torch()
+        eps = eps.to("cuda", torch.float64).contiguous()
+        g = torch.empty(self.N, device="cuda", dtype=torch.float64) if grad else None
+        s, f = lip_smooth_objective(self.h, float(M), float(p), eps.data_ptr(), _ptr(g), _stream_ptr())
+        _check(s, "lip_smooth_objective")
+        return f, g
+
+    def smooth_lipschitz(self, M: float, p: float = 100.0, max_iter: int = 200, history: int = 10,
+                         gtol: float = 1e-7):
+        """Sec. 5 smooth_lipschitz(LC): minimise Eq. (optim) with L-BFGS, replace y by y + eps and
+        the constant by M.  Returns (eps float64 CUDA tensor, Phi, iterations, evaluations)."""
+        torch = _torch()
+        eps = torch.empty(self.N, device="cuda", dtype=torch.float64)
+        s, f, it, ev = lip_smooth(self.h, float(M), float(p), int(max_iter), int(history), float(gtol),
+                                  eps.data_ptr(), _stream_ptr())
+        _check(s, "lip_smooth")
+        self._M = float(M)
+        return eps, f, it, ev
 
     def values_local(self, Q):
         """g with the local constants (Sec. 5: values_local(query, model, k=1))."""

@@ -204,6 +204,25 @@ def local_d4(n_data=100_000, n_query=1_000_000, dtype=np.float32) -> Problem:
     return Problem("local_d4", X, y, Q, 10.01, NORM_L2, None, None, _f_local_d4)
 
 
+SMOOTH_M = 3.5      # >= sup |grad f|_2 of smooth_d4's f (sqrt(pi^2 + 1 + 1 + 0.04) = 3.45)
+SMOOTH_P = 100.0    # penalty weight p of Eq. (optim) used with it
+
+
+def _f_smooth_d4(X):
+    X = np.asarray(X, np.float64)
+    return 0.5 * np.sin(2 * math.pi * X[:, 0]) + X[:, 1] + 0.5 * X[:, 2] ** 2 + 0.2 * X[:, 3]
+
+
+def smooth_d4(n_data=100_000, n_query=10_000, noise=0.05, dtype=np.float32) -> Problem:
+    """Noisy samples of a smooth function (Sec. 4.4's use: data that violate the Lipschitz
+    condition only through noise): f plus N(0, noise^2), L2, no monotonicity."""
+    rx, rq, rn = _rngs(8)
+    X = _as(rx.random((n_data, 4)), dtype)
+    Q = _as(rq.random((n_query, 4)), dtype)
+    y = _as(_f_smooth_d4(X) + noise * rn.standard_normal(n_data), dtype)
+    return Problem("smooth_d4", X, y, Q, SMOOTH_M, NORM_L2, None, None, _f_smooth_d4)
+
+
 @dataclasses.dataclass
 class BatchSet:
     """The sizes and parameters of one set of the batched workload (data drawn lazily)."""
@@ -286,4 +305,5 @@ WORKLOADS = {
     "grad_d8": grad_d8,
     "toy_d3": toy_d3,
     "local_d4": local_d4,
+    "smooth_d4": smooth_d4,
 }

@@ -555,6 +555,9 @@ def check_smoothing(O):
                 fd = (O.smooth_objective(X, y, ep, M, p, norm, mon=mon, w=w)[0] -
                       O.smooth_objective(X, y, em, M, p, norm, mon=mon, w=w)[0]) / (2 * h)
                 assert abs(fd - g[j]) <= 1e-5 * (1 + abs(g[j])), (norm, j, fd, g[j])
+            rows = np.array([0, 7, 24, 7])
+            assert np.allclose(O.smooth_grad_rows(X, y, eps, rows, M, p, norm, mon=mon, w=w), g[rows],
+                               rtol=1e-12, atol=1e-12)
             e, fmin, it = O.smooth(X, y, M, p, norm, mon=mon, w=w, max_iter=3000, gtol=1e-8)
             fe, ge, _, _ = O.smooth_objective(X, y, e, M, p, norm, mon=mon, w=w)
             assert np.abs(ge).max() <= 1e-8 and abs(fe - fmin) <= 1e-14 * max(1.0, fe)

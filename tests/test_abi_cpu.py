@@ -132,3 +132,9 @@ def test_local_lipschitz_argument_errors():
     assert L.lip_eval_local(None, None, 1, None, None, None, None, None) == L.LIP_ERR_ARG
     assert L.LIP_LOCAL_KNOTS_MAX == 31 and L.LIP_LOCAL_SAMPLE_MAX == 1 << 20
     assert L.status_string(L.LIP_ERR_STATE) == "call out of order"
+
+
+def test_smoothing_argument_errors():
+    eps = np.zeros(4)
+    assert L.lip_smooth_objective(None, 1.0, 10.0, eps.ctypes.data, None)[0] == L.LIP_ERR_ARG
+    assert L.lip_smooth(None, 1.0, 10.0, 10, 5, 1e-6, None)[0] == L.LIP_ERR_ARG

@@ -654,7 +654,7 @@ lip_status smooth_setup(lip_model* h, double M, double p, cudaStream_t st, Smoot
         P.scale[j] = M * h->sgnw[j];
     }
     P.p = p;
-    r.gx = (int)ceil_div(h->N, (int64_t)smooth_threads());
+    r.gx = (int)ceil_div(h->N, (int64_t)smooth_rows_per_block());
     const int64_t tiles = P.npad / tile;
     const int64_t want = std::max<int64_t>(1, ceil_div((int64_t)h->sms * 16, r.gx));
     const int64_t s = std::min<int64_t>(std::min<int64_t>(want, 64), tiles);

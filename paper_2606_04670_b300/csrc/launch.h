@@ -191,7 +191,7 @@ struct SmoothParams {
 };
 
 int smooth_tile();
-int smooth_threads();
+int smooth_rows_per_block();
 int smooth_reduce_blocks();
 cudaError_t launch_smooth_objective(const SmoothParams& P, const double* eps, double* grad, double* block_sums,
                                     double* out, int gx, cudaStream_t st);

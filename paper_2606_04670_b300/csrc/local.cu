@@ -39,7 +39,6 @@ constexpr int LOC_THREADS = 128;
 constexpr int LOC_TILE = 128;       // data points per shared-memory tile (table passes)
 constexpr int LOC_SCAN_TILE = 64;   // data points per shared-memory tile (evaluation)
 constexpr int LOC_RANK_TILE = 1024;
-constexpr int LOC_R = 2;            // queries per thread in the evaluation scan
 
 __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
 
@@ -341,10 +340,46 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParam
 
 // ------------------------------------------------------------------ evaluation
 
-// Each thread holds LOC_R queries; a block scans its split of the data in shared-memory
-// tiles of LOC_SCAN_TILE records and their table rows.  The segment of a distance comes
-// from the bucket table (one shared load and one compare), or from a binary search over
-// the knots when some bucket holds two knots.
+// The two queries a thread holds share every instruction that can be packed: their
+// coordinates sit in the two halves of float2 registers, so the distance to a data point,
+// the bucket scaling and both bound values are f32x2 operations.  The hot loop keeps only
+// the running extrema (one min and one max per pair); the 64-point tile in which each
+// query's extremum last strictly improved is remembered, and after the scan that tile is
+// evaluated again by the same inlined function, from global memory, to recover the lowest
+// index whose value equals the extremum bit for bit.
+template <int NORM, int DP, bool BUCKET>
+__device__ __forceinline__ void loc_pair_values(const float2 (&q2)[DP], const float* xj, const float* mtj,
+                                                const int2* bk, const float* Tn, float scale, float2& vu,
+                                                float2& vl) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < DP; ++i) {
+        const float2 t = sub2(q2[i], make_float2(xj[i], xj[i]));
+        if (NORM == LIP_L2) acc = fma2(t, t, acc);
+        else if (NORM == LIP_L1) acc = make_float2(__fadd_rn(acc.x, fabsf(t.x)), __fadd_rn(acc.y, fabsf(t.y)));
+        else acc = make_float2(fmaxf(acc.x, fabsf(t.x)), fmaxf(acc.y, fabsf(t.y)));
+    }
+    float2 t = acc;
+    if (NORM == LIP_L2) t = make_float2(sqrt_approx(acc.x), sqrt_approx(acc.y));
+    int s0, s1;
+    if (BUCKET) {
+        const float2 u = mul2(t, make_float2(scale, scale));
+        const int b0 = __float_as_int(__fadd_rz(fminf(u.x, (float)(LOC_BUCKETS - 1)), 8388608.0f)) - 0x4B000000;
+        const int b1 = __float_as_int(__fadd_rz(fminf(u.y, (float)(LOC_BUCKETS - 1)), 8388608.0f)) - 0x4B000000;
+        const int2 e0 = bk[b0], e1 = bk[b1];
+        s0 = e0.x + (__int_as_float(e0.y) < t.x ? 1 : 0);
+        s1 = e1.x + (__int_as_float(e1.y) < t.y ? 1 : 0);
+    } else {
+        s0 = knot_count(Tn, t.x);
+        s1 = knot_count(Tn, t.y);
+    }
+    const float y = xj[DP], d1 = xj[DP + 1], Fj = xj[DP + 2];
+    const float2 M = make_float2(t.x <= d1 ? Fj : mtj[s0], t.y <= d1 ? Fj : mtj[s1]);
+    const float2 y2 = make_float2(y, y);
+    vu = fma2(M, t, y2);
+    vl = fma2(make_float2(-M.x, -M.y), t, y2);
+}
+
 template <int NORM, int DP, bool BUCKET>
 __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanParams P) {
     constexpr int PR = DP + 4;
@@ -356,14 +391,13 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanPa
     const float* mt = reinterpret_cast<const float*>(mt4);
     const int tid = threadIdx.x;
     const int split = blockIdx.y;
-    float q[LOC_R][DP];
-    int64_t qi[LOC_R];
+    float2 q2[DP];
+    const int64_t qa = (int64_t)blockIdx.x * LOC_THREADS * 2 + tid, qb = qa + LOC_THREADS;
 #pragma unroll
-    for (int r = 0; r < LOC_R; ++r) {
-        qi[r] = (int64_t)blockIdx.x * LOC_THREADS * LOC_R + r * LOC_THREADS + tid;
-#pragma unroll
-        for (int i = 0; i < DP; ++i)
-            q[r][i] = (qi[r] < P.nq && i < P.d) ? (float)(P.w[i] * (double)P.Q[qi[r] * P.d + i]) : 0.f;
+    for (int i = 0; i < DP; ++i) {
+        const float a = (qa < P.nq && i < P.d) ? (float)(P.w[i] * (double)P.Q[qa * P.d + i]) : 0.f;
+        const float b = (qb < P.nq && i < P.d) ? (float)(P.w[i] * (double)P.Q[qb * P.d + i]) : 0.f;
+        q2[i] = make_float2(a, b);
     }
     if (BUCKET) {
         for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.buckets[b];
@@ -371,10 +405,8 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanPa
         Tn[tid] = P.Tf[tid];
     }
     const float scale = P.scale;
-    float bu[LOC_R], bl[LOC_R];
-    int iu[LOC_R], il[LOC_R];
-#pragma unroll
-    for (int r = 0; r < LOC_R; ++r) { bu[r] = INFINITY; bl[r] = -INFINITY; iu[r] = -1; il[r] = -1; }
+    float2 bu = make_float2(INFINITY, INFINITY), bl = make_float2(-INFINITY, -INFINITY);
+    int64_t tu0 = -1, tu1 = -1, tl0 = -1, tl1 = -1;        // tile of the last strict improvement
     const int64_t j_begin = (int64_t)split * P.points_per_split;
     const int64_t j_end = lmin(j_begin + P.points_per_split, P.npad);
     for (int64_t j0 = j_begin; j0 < j_end; j0 += LOC_SCAN_TILE) {
@@ -384,36 +416,46 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanPa
         const float4* ms = reinterpret_cast<const float4*>(P.mt + j0 * LOC_KNOTS);
         for (int i = tid; i < LOC_SCAN_TILE * LOC_KNOTS / 4; i += LOC_THREADS) mt4[i] = ms[i];
         __syncthreads();
+        float2 cu = bu, cl = bl;
 #pragma unroll 2
         for (int j = 0; j < LOC_SCAN_TILE; ++j) {
-            const float* xj = rec + j * PR;
-            const float y = xj[DP], d1 = xj[DP + 1], Fj = xj[DP + 2];
-            const float* mtj = mt + j * LOC_KNOTS;
-            const int idx = (int)(j0 + j);
+            float2 vu, vl;
+            loc_pair_values<NORM, DP, BUCKET>(q2, rec + j * PR, mt + j * LOC_KNOTS, bk, Tn, scale, vu, vl);
+            cu = make_float2(fminf(cu.x, vu.x), fminf(cu.y, vu.y));      // NaN (padding) is ignored
+            cl = make_float2(fmaxf(cl.x, vl.x), fmaxf(cl.y, vl.y));
+        }
+        if (cu.x < bu.x) tu0 = j0;
+        if (cu.y < bu.y) tu1 = j0;
+        if (cl.x > bl.x) tl0 = j0;
+        if (cl.y > bl.y) tl1 = j0;
+        bu = cu;
+        bl = cl;
+    }
+    // lowest index in the remembered tile whose value equals the extremum
+    const int64_t tiles[4] = {tu0, tu1, tl0, tl1};
+    int idx[4] = {-1, -1, -1, -1};
 #pragma unroll
-            for (int r = 0; r < LOC_R; ++r) {
-                float t = dist32<NORM, DP>(q[r], xj);
-                if (NORM == LIP_L2) t = sqrt_approx(t);
-                int s;
-                if (BUCKET) {
-                    const int2 e = bk[knot_bucket(t, scale)];
-                    s = e.x + (__int_as_float(e.y) < t ? 1 : 0);
-                } else {
-                    s = knot_count(Tn, t);
-                }
-                const float M = t <= d1 ? Fj : mtj[s];
-                const float vu = fmaf(M, t, y), vl = fmaf(-M, t, y);
-                if (vu < bu[r]) { bu[r] = vu; iu[r] = idx; }
-                if (vl > bl[r]) { bl[r] = vl; il[r] = idx; }
-            }
+    for (int c = 0; c < 4; ++c) {
+        if (tiles[c] < 0) continue;
+        const float target = c == 0 ? bu.x : (c == 1 ? bu.y : (c == 2 ? bl.x : bl.y));
+        for (int j = 0; j < LOC_SCAN_TILE; ++j) {
+            const int64_t k = tiles[c] + j;
+            float2 vu, vl;
+            loc_pair_values<NORM, DP, BUCKET>(q2, P.rec + k * PR, P.mt + k * LOC_KNOTS, bk, Tn, scale, vu, vl);
+            const float v = c == 0 ? vu.x : (c == 1 ? vu.y : (c == 2 ? vl.x : vl.y));
+            if (v == target) { idx[c] = (int)k; break; }
         }
     }
-#pragma unroll
-    for (int r = 0; r < LOC_R; ++r) {
-        if (qi[r] >= P.nq) continue;
+    PartialRec<float>* part = static_cast<PartialRec<float>*>(P.partial);
+    if (qa < P.nq) {
         PartialRec<float> rr;
-        rr.vu = bu[r]; rr.iu = iu[r]; rr.vl = bl[r]; rr.il = il[r];
-        static_cast<PartialRec<float>*>(P.partial)[(int64_t)split * P.nq + qi[r]] = rr;
+        rr.vu = bu.x; rr.iu = idx[0]; rr.vl = bl.x; rr.il = idx[2];
+        part[(int64_t)split * P.nq + qa] = rr;
+    }
+    if (qb < P.nq) {
+        PartialRec<float> rr;
+        rr.vu = bu.y; rr.iu = idx[1]; rr.vl = bl.y; rr.il = idx[3];
+        part[(int64_t)split * P.nq + qb] = rr;
     }
 }
 
@@ -463,7 +505,7 @@ int local_dim_pad(int d) { return (d + 3) / 4 * 4; }
 int local_record_floats(int d) { return local_dim_pad(d) + 4; }
 int64_t local_pad(int64_t N) { return (N + LOC_TILE - 1) / LOC_TILE * LOC_TILE; }
 int local_scan_tile() { return LOC_SCAN_TILE; }
-int local_queries_per_block() { return LOC_THREADS * LOC_R; }
+int local_queries_per_block() { return LOC_THREADS * 2; }
 
 cudaError_t launch_local_layout(const LocalParams& P, cudaStream_t st) {
     const unsigned blocks = (unsigned)((P.npad + 255) / 256);

@@ -11,8 +11,8 @@
 //   Phi = ||eps||^2 / p + 2 S1,   dPhi/deps_j = 2 eps_j / p + 4 (R_j - C_j),
 //   R_j = sum_k (z_j - z_k - M dist_up(x^j, x^k))_+,  C_j = sum_i (z_i - z_j - M dist_up(x^i, x^j))_+.
 //
-// The pass gives thread i the row i: for every k it forms both v_ik (its const1 term) and
-// v_ki (the term with i second), so R_i, C_i and the row's share of S1 need no atomics.
+// The pass gives each thread two rows i: for every k it forms both v_ik (the const1 term)
+// and v_ki (the term with i second), so R_i, C_i and the row's share of S1 need no atomics.
 // Pair terms are FP32 on the scaled layout (coordinates times M w, mirrored where
 // decreasing, constrained first); each thread adds them in FP32 within a 128-point tile
 // and in FP64 across tiles, and the splits are summed in FP64 in a fixed order.
@@ -41,43 +41,23 @@ __global__ void smooth_layout_kernel(const SmoothParams P, const double* eps) {
     r[P.dp + 1] = r[P.dp + 2] = r[P.dp + 3] = 0.f;
 }
 
-// dist_up(a, b) (positive parts (a - b)_+ on the first C coordinates, |a - b| on the
-// rest) and dist_up(b, a), on the scaled layout.
-template <int NORM, int DP, bool MONO>
-__device__ __forceinline__ void dist_pair(const float* a, const float* b, int C, float& du, float& dr) {
-    float au = 0.f, ar = 0.f;
-#pragma unroll
-    for (int j = 0; j < DP; ++j) {
-        const float t = a[j] - b[j];
-        float u, r;
-        if (MONO && j < C) { u = fmaxf(t, 0.f); r = fmaxf(-t, 0.f); }
-        else { u = fabsf(t); r = u; }
-        if (NORM == LIP_L1) { au += u; if (MONO) ar += r; }
-        else if (NORM == LIP_L2) { au = fmaf(u, u, au); if (MONO) ar = fmaf(r, r, ar); }
-        else { au = fmaxf(au, u); if (MONO) ar = fmaxf(ar, r); }
-    }
-    if (NORM == LIP_L2) {
-        au = sqrtf(au);
-        if (MONO) ar = sqrtf(ar);
-    }
-    du = au;
-    dr = MONO ? ar : au;
-}
-
+// Each thread owns two rows (i and i + 128 of its block's 256), packed into the halves of
+// float2 registers, so the distance, the two terms and the three sums are f32x2 operations.
 template <int NORM, int DP, bool MONO>
 __global__ void __launch_bounds__(SM_THREADS) smooth_pass_kernel(const SmoothParams P) {
     constexpr int PR = DP + 4;
     __shared__ float4 tile4[SM_TILE * PR / 4];
     const float* tile = reinterpret_cast<const float*>(tile4);
     const int tid = threadIdx.x;
-    const int64_t i = (int64_t)blockIdx.x * SM_THREADS + tid;
+    const int64_t ia = (int64_t)blockIdx.x * SM_THREADS * 2 + tid, ib = ia + SM_THREADS;
     const int split = blockIdx.y;
-    const bool valid = i < P.N;
-    float xi[DP];
+    const bool va = ia < P.N, vb = ib < P.N;
+    float2 x2[DP];
 #pragma unroll
-    for (int j = 0; j < DP; ++j) xi[j] = valid ? P.rec[i * PR + j] : 0.f;
-    const float zi = valid ? P.rec[i * PR + DP] : 0.f;
-    double R = 0.0, Cs = 0.0, S = 0.0;
+    for (int j = 0; j < DP; ++j)
+        x2[j] = make_float2(va ? P.rec[ia * PR + j] : 0.f, vb ? P.rec[ib * PR + j] : 0.f);
+    const float2 z2 = make_float2(va ? P.rec[ia * PR + DP] : 0.f, vb ? P.rec[ib * PR + DP] : 0.f);
+    double Ra = 0.0, Ca = 0.0, Sa = 0.0, Rb = 0.0, Cb = 0.0, Sb = 0.0;
     const int64_t k_begin = (int64_t)split * P.points_per_split;
     const int64_t k_end = k_begin + P.points_per_split < P.npad ? k_begin + P.points_per_split : P.npad;
     for (int64_t k0 = k_begin; k0 < k_end; k0 += SM_TILE) {
@@ -85,30 +65,60 @@ __global__ void __launch_bounds__(SM_THREADS) smooth_pass_kernel(const SmoothPar
         const float4* src = reinterpret_cast<const float4*>(P.rec + k0 * PR);
         for (int t = tid; t < SM_TILE * PR / 4; t += SM_THREADS) tile4[t] = src[t];
         __syncthreads();
-        float r = 0.f, c = 0.f, s = 0.f;
+        float2 r = make_float2(0.f, 0.f), c = r, s = r;
 #pragma unroll 4
         for (int k = 0; k < SM_TILE; ++k) {
             const float* xk = tile + k * PR;
-            float du, dr;
-            dist_pair<NORM, DP, MONO>(xi, xk, P.C, du, dr);
-            const float dz = zi - xk[DP];
-            const float v1 = dz - du;                 // const1 term of (i, k)
-            const float v2 = -dz - dr;                // const1 term of (k, i)
-            const float p1 = v1 > 0.f ? v1 : 0.f;     // NaN (padding) gives 0
-            const float p2 = v2 > 0.f ? v2 : 0.f;
-            r += p1;
-            c += p2;
-            s = fmaf(p1, p1, s);
+            float2 au = make_float2(0.f, 0.f), ar = au;
+#pragma unroll
+            for (int j = 0; j < DP; ++j) {
+                const float2 t = sub2(x2[j], make_float2(xk[j], xk[j]));
+                if (MONO && j < P.C) {
+                    const float2 u = make_float2(fmaxf(t.x, 0.f), fmaxf(t.y, 0.f));
+                    const float2 v = make_float2(fmaxf(-t.x, 0.f), fmaxf(-t.y, 0.f));
+                    if (NORM == LIP_L1) { au = add2(au, u); ar = add2(ar, v); }
+                    else if (NORM == LIP_L2) { au = fma2(u, u, au); ar = fma2(v, v, ar); }
+                    else {
+                        au = make_float2(fmaxf(au.x, u.x), fmaxf(au.y, u.y));
+                        ar = make_float2(fmaxf(ar.x, v.x), fmaxf(ar.y, v.y));
+                    }
+                } else {
+                    if (NORM == LIP_L1) au = make_float2(au.x + fabsf(t.x), au.y + fabsf(t.y));
+                    else if (NORM == LIP_L2) au = fma2(t, t, au);
+                    else au = make_float2(fmaxf(au.x, fabsf(t.x)), fmaxf(au.y, fabsf(t.y)));
+                    if (MONO) {
+                        if (NORM == LIP_L1) ar = make_float2(ar.x + fabsf(t.x), ar.y + fabsf(t.y));
+                        else if (NORM == LIP_L2) ar = fma2(t, t, ar);
+                        else ar = make_float2(fmaxf(ar.x, fabsf(t.x)), fmaxf(ar.y, fabsf(t.y)));
+                    }
+                }
+            }
+            if (NORM == LIP_L2) {
+                au = make_float2(sqrt_approx(au.x), sqrt_approx(au.y));
+                if (MONO) ar = make_float2(sqrt_approx(ar.x), sqrt_approx(ar.y));
+            }
+            if (!MONO) ar = au;
+            const float zk = xk[DP];
+            const float2 dz = sub2(z2, make_float2(zk, zk));
+            const float2 v1 = sub2(dz, au);                       // const1 term of (i, k)
+            const float2 w2 = add2(dz, ar);                       // minus the const1 term of (k, i)
+            const float2 p1 = make_float2(v1.x > 0.f ? v1.x : 0.f, v1.y > 0.f ? v1.y : 0.f);   // NaN gives 0
+            const float2 p2 = make_float2(-w2.x > 0.f ? -w2.x : 0.f, -w2.y > 0.f ? -w2.y : 0.f);
+            r = add2(r, p1);
+            c = add2(c, p2);
+            s = fma2(p1, p1, s);
         }
-        R += (double)r;
-        Cs += (double)c;
-        S += (double)s;
+        Ra += (double)r.x; Ca += (double)c.x; Sa += (double)s.x;
+        Rb += (double)r.y; Cb += (double)c.y; Sb += (double)s.y;
     }
-    if (!valid) return;
-    double* out = P.partial + ((int64_t)split * P.N + i) * 3;
-    out[0] = R;
-    out[1] = Cs;
-    out[2] = S;
+    if (va) {
+        double* out = P.partial + ((int64_t)split * P.N + ia) * 3;
+        out[0] = Ra; out[1] = Ca; out[2] = Sa;
+    }
+    if (vb) {
+        double* out = P.partial + ((int64_t)split * P.N + ib) * 3;
+        out[0] = Rb; out[1] = Cb; out[2] = Sb;
+    }
 }
 
 // grad_i = 2 eps_i / p + 4 (R_i - C_i); per-block sums of S_i and eps_i^2.
@@ -226,7 +236,7 @@ void pass_norm(const SmoothParams& P, dim3 grid, cudaStream_t st) {
 }  // namespace
 
 int smooth_tile() { return SM_TILE; }
-int smooth_threads() { return SM_THREADS; }
+int smooth_rows_per_block() { return SM_THREADS * 2; }
 int smooth_reduce_blocks() { return RED_BLOCKS; }
 
 // Phi and its gradient at eps: layout, the pair pass, the finishing sums.  out[0] = Phi,

@@ -44,8 +44,8 @@ UNIT = "G pairs/s"
 NORMS = (W.NORM_L1, W.NORM_L2, W.NORM_LINF)
 NNAME = {1: "L1", 2: "L2", 3: "Linf"}
 FP32_LANES_PER_SM = 128
-WORKLOADS = ("monotone_d4", "plain_d2", "cluster_d16", "cluster_d16_tc", "grad_d8", "batch_4096", "local_d4",
-             "smooth_d4")
+WORKLOADS = ("monotone_d4", "plain_d2", "cluster_d16", "cluster_d16_tc", "cluster_d16_bf16", "grad_d8",
+             "batch_4096", "local_d4", "smooth_d4")
 SMOOTH_ITERS = 10
 LOCAL_KNOTS, LOCAL_SAMPLE, LOCAL_SEED = 16, 32768, 0
 # TF32 dense peak: the measured BF16 peak times the nominal TF32 / BF16 ratio (1.1 / 2.25)
@@ -222,7 +222,7 @@ def reference_problems(workload):
         return [base.with_norm(n) for n in NORMS]
     if workload == "plain_d2":
         return [W.plain_d2(dtype=np.float64)]
-    if workload in ("cluster_d16", "cluster_d16_tc"):
+    if workload in ("cluster_d16", "cluster_d16_tc", "cluster_d16_bf16"):
         return [W.cluster_d16(n_query=20_000)]
     if workload == "grad_d8":
         return [W.grad_d8()]
@@ -381,7 +381,7 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
         from paper_2606_04670_b300 import autotune as AT
         cache, save = _tune_cache()
         for r in runs:
-            if r["prec"] == "tc_tf32":
+            if r["prec"].startswith("tc_"):
                 continue               # the launch shape knobs belong to the plain scan
             r["m"].clear()
             r["m"].add(r["X"], r["y"])
@@ -425,17 +425,22 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
             f"R={rd['m'].tuning()['queries_per_thread']}> {rd['prec']}")
     roof = ctx.roofline(kern, ip * p.nq * p.N, avg[kdom], ip, mufu_per_pair(p.norm, c), clocks,
                         SCAN_DRAM_BYTES.get((name, p.norm)) if rd["prec"] == "fp32" else None)
-    if rd["prec"] == "tc_tf32":
-        # tensor-core form: three TF32 products over K = 8 ceil((d + 2) / 8) per pair
-        kk = 8 * ((p.d + 2 + 7) // 8)
-        flops = 2.0 * 3 * kk * p.nq * p.N
-        peak = float(ctx.peaks.get("bf16_tflops", 1800.0)) * TF32_OVER_BF16 * 1e12
+    if rd["prec"] in ("tc_tf32", "tc_bf16"):
+        bf = rd["prec"] == "tc_bf16"
+        # tensor-core form: three TF32 products over K = 8 ceil((d + 2) / 8), or six BF16
+        # products over K = 16 ceil((d + 2) / 16), per pair
+        kk = 16 * ((p.d + 2 + 15) // 16) if bf else 8 * ((p.d + 2 + 7) // 8)
+        npass = 6 if bf else 3
+        flops = 2.0 * npass * kk * p.nq * p.N
+        peak = float(ctx.peaks.get("bf16_tflops", 1800.0)) * (1.0 if bf else TF32_OVER_BF16) * 1e12
         alu = roof
-        roof = {"bound": "tensor", "kernel": f"tc_scan_kernel<K={kk}> (+ build and rescreen)",
-                "achieved": flops / (avg[kdom] / 1e3) / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s (TF32)",
-                "frac": flops / (avg[kdom] / 1e3) / peak, "traffic": None,
-                "peak_source": "measured bf16 dense peak of MEASURED_PEAKS.json x 1.1/2.25 (nominal TF32/BF16)",
-                "flops_per_pair": 6 * kk,
+        roof = {"bound": "tensor", "kernel": f"tc_scan_kernel<K={kk}, {'BF16' if bf else 'TF32'}> (+ build and rescreen)",
+                "achieved": flops / (avg[kdom] / 1e3) / 1e12, "peak": peak / 1e12,
+                "unit": f"TFLOP/s ({'BF16' if bf else 'TF32'})", "frac": flops / (avg[kdom] / 1e3) / peak,
+                "traffic": None,
+                "peak_source": ("measured bf16 dense peak of MEASURED_PEAKS.json" if bf else
+                                "measured bf16 dense peak of MEASURED_PEAKS.json x 1.1/2.25 (nominal TF32/BF16)"),
+                "flops_per_pair": 2 * npass * kk,
                 "alu_view": {k: alu[k] for k in ("achieved", "peak", "frac", "i_pair")}}
 
     e2e = None
@@ -489,16 +494,16 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
                                     for r in runs},
               "splits": tun["last_splits"], "tile_groups": tun["tile_groups"],
               "queries_per_thread": tun["queries_per_thread"], "sms": ctx.sms, "autotune": tuning,
-              "tc_fallback_queries": {key(r): r["m"].last_fallback() for r in runs if r["prec"] == "tc_tf32"}}
+              "tc_fallback_queries": {key(r): r["m"].last_fallback() for r in runs if r["prec"].startswith("tc_")}}
     if with_bwd:
-        # backward: per query it reads q, both indices and grad_g, gathers the two chosen
-        # data rows, writes grad_q and adds to grad_y (two FP64 atomics); then grad_y (FP64
-        # scratch read, FP32 read-modify-write) and grad_M (per-block partials)
+        # backward (one launch): per query it reads q, both indices and grad_g, gathers the
+        # two chosen data rows, writes grad_q and adds to grad_y (two atomic read-modify-
+        # writes); the binding zeroes grad_y [N] first
         bb = {}
         for r in runs:
             pp = r["p"]
             es = 8 if r["prec"] == "fp64" else 4
-            byts = pp.nq * (pp.d * es + 8 + es + 2 * pp.d * es + pp.d * es + 16) + pp.N * (8 + 2 * es)
+            byts = pp.nq * (pp.d * es + 8 + es + 2 * pp.d * es + pp.d * es + 4 * es) + pp.N * es
             ms_b = statistics.mean(r["bwd"])
             bb[key(r)] = {"ms": ms_b, "algorithmic_bytes": byts, "gb_per_s": byts / (ms_b / 1e3) / 1e9,
                           "hbm_peak_gb_per_s": float(ctx.peaks.get("hbm_gbs", 6518.0)),
@@ -816,6 +821,8 @@ def run_ours(args):
         line = wl_single(ctx, w, [W.cluster_d16()], with_est=False, flush=False)
     elif w == "cluster_d16_tc":
         line = wl_single(ctx, w, [W.cluster_d16()], precisions=("tc_tf32",), with_est=False, flush=False)
+    elif w == "cluster_d16_bf16":
+        line = wl_single(ctx, w, [W.cluster_d16()], precisions=("tc_bf16",), with_est=False, flush=False)
     elif w == "grad_d8":
         line = wl_single(ctx, w, [W.grad_d8()], with_bwd=True)
     elif w == "local_d4":

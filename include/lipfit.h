@@ -67,11 +67,12 @@ typedef enum {
     LIP_FP64 = 1,      /* FP64 throughout                                                   */
     LIP_TC_BF16 = 2,   /* L2 only: tensor-core cross term (bf16 split), exact FP64 rescreen  */
     LIP_TC_TF32 = 3    /* L2 only: tensor-core cross term (tf32 split), exact FP64 rescreen  */
-    /* LIP_TC_TF32 needs the L2 norm and no monotone coordinates (the squared distance is
-     * then one augmented product).  Its lip_eval synchronises the stream once; the
+    /* The tensor-core precisions need the L2 norm and no monotone coordinates (the squared
+     * distance is then one augmented product).  TF32: each operand split into a TF32 head
+     * and an FP32 tail, three kind::tf32 products.  BF16: each operand split into three
+     * bf16 pieces, six kind::f16 products.  lip_eval synchronises the stream once; the
      * returned bounds are the exact FP64 envelopes (see the kernel's error bound), with
-     * the plain FP32 scan as fallback for queries with too many near-ties.
-     * LIP_TC_BF16 is accepted by the enum but returns LIP_ERR_UNSUPPORTED. */
+     * the plain FP32 scan as fallback for queries with too many near-ties. */
 } lip_precision;
 
 /* Largest dimension d accepted by lip_fit / lip_reserve. */
@@ -316,9 +317,9 @@ LIP_API lip_status lip_smooth(lip_handle h, double M, double p, int32_t max_iter
  * tie of the maximum.  Q, idx_up, idx_lo are those given to / returned by lip_eval;
  * grad_g is [nq].  All device pointers; element type of the handle for Q, grad_g,
  * grad_Q, grad_y; grad_M is double.  Any of grad_Q, grad_y, grad_M may be NULL.
- * grad_y is reduced with FP64 atomics in handle scratch and then added to grad_y, so
- * its last bits may change with the order of the atomics; grad_M uses a fixed-order
- * two-level reduction and is bitwise reproducible. */
+ * One kernel launch.  grad_y receives atomic additions of the element type, so its last
+ * bits may change with the order of the atomics; grad_M uses a fixed-order two-level
+ * reduction (finished by the last block) and is bitwise reproducible. */
 LIP_API lip_status lip_backward(lip_handle h, const void* Q, int64_t nq, const int32_t* idx_up,
                         const int32_t* idx_lo, const void* grad_g, void* grad_Q, void* grad_y,
                         double* grad_M, void* stream);

@@ -127,6 +127,7 @@ struct lip_model {
     cudaEvent_t ev_scan0 = nullptr, ev_scan1 = nullptr;   // caller's timing events
     // tensor-core form (LIP_TC_TF32)
     bool tc = false, tc_dirty = true;
+    bool tc_bf = false;                // BF16 three-piece split instead of TF32
     int tc_variant = 0;                // 0: 16 epilogue warps, 1: 8
     int64_t tc_ntiles_cap = 0;
     char* tc_btiles = nullptr;
@@ -164,8 +165,6 @@ lip_status check_params(int32_t d, double M, const lip_params* p) {
                 return fail(LIP_ERR_ARG, "w[%d] = %g must be finite and > 0", i, p->w[i]);
     if (p->precision == LIP_TC_BF16 || p->precision == LIP_TC_TF32) {
         if (p->norm != LIP_L2) return fail(LIP_ERR_UNSUPPORTED, "tensor-core precision needs the L2 norm");
-        if (p->precision == LIP_TC_BF16)
-            return fail(LIP_ERR_UNSUPPORTED, "the bf16 tensor-core split is not available; use LIP_TC_TF32");
         if (p->mon)
             for (int i = 0; i < d; ++i)
                 if (p->mon[i] != 0)
@@ -269,7 +268,8 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
         if (h->mon[i] != 0) h->C++;
     }
     const int U = d - h->C;
-    h->tc = h->prec == LIP_TC_TF32;
+    h->tc = h->prec == LIP_TC_TF32 || h->prec == LIP_TC_BF16;
+    h->tc_bf = h->prec == LIP_TC_BF16;
     if ((h->prec == LIP_FP32 || h->tc) && exact_shape_available(h->C, U)) {
         h->exact = true;
         h->dl = d;
@@ -314,7 +314,8 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
     if (h->tc) {
         h->tc_ntiles_cap = ceil_div(cap, 256);
         struct { void** p; size_t n; const char* what; } tca[] = {
-            {reinterpret_cast<void**>(&h->tc_btiles), (size_t)h->tc_ntiles_cap * tc_tile_bytes_for(d), "tensor-core data tiles"},
+            {reinterpret_cast<void**>(&h->tc_btiles), (size_t)h->tc_ntiles_cap * tc_tile_bytes_for(d, h->tc_bf),
+             "tensor-core data tiles"},
             {reinterpret_cast<void**>(&h->tc_stats), D_MAX * sizeof(double), "tensor-core centre"},
             {reinterpret_cast<void**>(&h->tc_maxbits), 2 * sizeof(unsigned), "tensor-core bounds"},
         };
@@ -472,12 +473,12 @@ lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, v
     const int64_t ntiles = ceil_div(h->N, 256);
     if (h->tc_dirty) {
         CUDA_TRY(tc_prepare_data(static_cast<const float*>(h->X0), static_cast<const float*>(h->y0), h->N, d, scale,
-                                 h->tc_stats, h->tc_maxbits, h->tc_btiles, ntiles, st));
+                                 h->tc_stats, h->tc_maxbits, h->tc_btiles, ntiles, h->tc_bf, st));
         count_launches(2);
         h->tc_dirty = false;
     }
     const int64_t nqt = ceil_div(nq, 128);
-    const size_t a_b = round_up((int64_t)(nqt * tc_a_bytes_for(d)), 256), eps_b = round_up(nq * 8, 256),
+    const size_t a_b = round_up((int64_t)(nqt * tc_a_bytes_for(d, h->tc_bf)), 256), eps_b = round_up(nq * 8, 256),
                  rec_b = round_up((int64_t)(nq * tc_rec_bytes()), 256), list_b = round_up(nq * 4 + 4, 256);
     LIP_TRY(h->tc_q.ensure(a_b + eps_b + rec_b + list_b, "tensor-core query scratch"));
     char* base = static_cast<char*>(h->tc_q.p);
@@ -488,7 +489,7 @@ lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, v
                             ntiles, base, reinterpret_cast<float2*>(base + a_b), base + a_b + eps_b, h->w, h->M,
                             static_cast<const float*>(h->X0), static_cast<const float*>(h->y0), static_cast<float*>(g),
                             static_cast<float*>(lo), static_cast<float*>(hi), iu, il, fb_count, fb_list, h->status,
-                            h->tc_variant, st));
+                            h->tc_variant, h->tc_bf, st));
     count_launches(3);
     if (h->ev_scan1) CUDA_TRY(cudaEventRecord(h->ev_scan1, st));
     int nfb = 0;
@@ -1225,8 +1226,7 @@ lip_status lip_backward(lip_handle h, const void* Q, int64_t nq, const int32_t* 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nb = backward_blocks(nq);
     const size_t part_b = round_up((int64_t)std::max(nb, 1) * 8, 256);
-    const size_t gy_b = grad_y ? round_up(std::max<int64_t>(h->N, 1) * 8, 256) : 0;
-    LIP_TRY(h->bwd.ensure(part_b + gy_b, "backward scratch"));
+    LIP_TRY(h->bwd.ensure(part_b + 256, "backward scratch"));
     char* base = static_cast<char*>(h->bwd.p);
     BwdParams P;
     P.Q = Q;
@@ -1237,6 +1237,7 @@ lip_status lip_backward(lip_handle h, const void* Q, int64_t nq, const int32_t* 
     for (int i = 0; i < D_MAX; ++i) {
         P.mon[i] = h->mon[i];
         P.w[i] = h->w[i];
+        P.sqf[i] = (float)((h->mon[i] < 0 ? -1.0 : 1.0) * h->w[i]);
     }
     P.X0 = h->X0;
     P.iu = idx_up;
@@ -1244,14 +1245,16 @@ lip_status lip_backward(lip_handle h, const void* Q, int64_t nq, const int32_t* 
     P.gbar = grad_g;
     P.grad_Q = grad_Q;
     P.gm_part = reinterpret_cast<double*>(base);
-    P.gy64 = grad_y ? reinterpret_cast<double*>(base + part_b) : nullptr;
-    if (P.gy64) CUDA_TRY(cudaMemsetAsync(P.gy64, 0, (size_t)h->N * 8, st));
+    P.arrived = reinterpret_cast<unsigned*>(base + part_b);
+    P.grad_y = grad_y;
+    P.grad_M = grad_M;
     if (nq == 0) {
         if (grad_M) CUDA_TRY(cudaMemsetAsync(grad_M, 0, sizeof(double), st));
         return LIP_OK;
     }
-    CUDA_TRY(launch_backward(h->esize, P, h->N, grad_y, grad_M, st));
-    count_launches(1 + (grad_M ? 1 : 0) + (grad_y && h->N > 0 ? 1 : 0));
+    CUDA_TRY(cudaMemsetAsync(P.arrived, 0, sizeof(unsigned), st));
+    CUDA_TRY(launch_backward(h->esize, P, st));
+    count_launches(1);
     return LIP_OK;
 }
 

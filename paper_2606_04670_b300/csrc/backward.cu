@@ -5,8 +5,10 @@
 //   dL/dy^k   = 1/2 sum_q gbar_q ([u_q = k] + [l_q = k])
 //   dL/dM     = 1/2 sum_q gbar_q ( dist_up(q, x^u) - dist_lo(q, x^l) )
 // One thread per query, in the caller's coordinates, arithmetic in the handle's
-// element type; dL/dy is accumulated with FP64 atomics in scratch, dL/dM by a
-// fixed-shape two-level FP64 reduction (bitwise reproducible).
+// element type, all in one launch: dL/dy is added straight into the caller's grad_y with
+// atomics of the element type, and dL/dM is a fixed-shape two-level FP64 reduction
+// finished by the last block to arrive (bitwise reproducible); the per-query terms and the
+// warp sums are in the element type, the block and grid sums in FP64.
 #include "launch.h"
 
 namespace lip {
@@ -26,16 +28,11 @@ __device__ __forceinline__ void coord_part(T t, bool constrained, int side, T& v
     }
 }
 
-template <typename T>
-__device__ __forceinline__ T coord_t(const BwdParams& P, const T* q, const T* x, int i, T& sq) {
-    sq = (P.mon[i] < 0 ? (T)-1 : (T)1) * (T)P.w[i];   // dt'/dq_i
-    return (q[i] - x[i]) * sq;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(BWD_THREADS) backward_kernel(const BwdParams P) {
     const int64_t qi = (int64_t)blockIdx.x * BWD_THREADS + threadIdx.x;
-    double gm = 0.0;
+    T gm = 0;
     if (qi < P.nq) {
         const T* q = static_cast<const T*>(P.Q) + qi * P.d;
         const T gb = static_cast<const T*>(P.gbar)[qi];
@@ -47,14 +44,27 @@ __global__ void __launch_bounds__(BWD_THREADS) backward_kernel(const BwdParams P
             const T* X0 = static_cast<const T*>(P.X0);
             const T* xu = X0 + (int64_t)u * P.d;
             const T* xl = X0 + (int64_t)l * P.d;
+            // the query and both data rows once, in registers, with dt'/dq_i = sign_i w_i
+            T qv[D_MAX], tu[D_MAX], tl[D_MAX], sq[D_MAX];
+#pragma unroll
+            for (int i = 0; i < D_MAX; ++i) {
+                if (i < P.d) {
+                    sq[i] = sizeof(T) == 4 ? (T)P.sqf[i] : (P.mon[i] < 0 ? (T)-1 : (T)1) * (T)P.w[i];
+                    qv[i] = q[i];
+                    tu[i] = (qv[i] - xu[i]) * sq[i];
+                    tl[i] = (qv[i] - xl[i]) * sq[i];
+                }
+            }
             // pass 1: the two distances (and the Linf arg-max coordinates, lowest on ties)
             T au = 0, al = 0;
             int mu = -1, ml = -1;
-            for (int i = 0; i < P.d; ++i) {
-                T sq, vu, vl, dv;
+#pragma unroll
+            for (int i = 0; i < D_MAX; ++i) {
+                if (i >= P.d) break;
+                T vu, vl, dv;
                 const bool c = P.mon[i] != 0;
-                coord_part<T>(coord_t<T>(P, q, xu, i, sq), c, +1, vu, dv);
-                coord_part<T>(coord_t<T>(P, q, xl, i, sq), c, -1, vl, dv);
+                coord_part<T>(tu[i], c, +1, vu, dv);
+                coord_part<T>(tl[i], c, -1, vl, dv);
                 if (P.norm == LIP_L1) { au += vu; al += vl; }
                 else if (P.norm == LIP_L2) { au += vu * vu; al += vl * vl; }
                 else {
@@ -67,86 +77,75 @@ __global__ void __launch_bounds__(BWD_THREADS) backward_kernel(const BwdParams P
             // pass 2: d dist / d q_i for both sides, then dL/dq_i
             if (gq) {
                 const T hm = (T)(0.5 * P.M) * gb;
-                for (int i = 0; i < P.d; ++i) {
-                    T sq, vu, vl, dvu, dvl;
+                const T ru = du > 0 ? (T)1 / du : (T)0, rl = dl > 0 ? (T)1 / dl : (T)0;
+#pragma unroll
+                for (int i = 0; i < D_MAX; ++i) {
+                    if (i >= P.d) break;
+                    T vu, vl, dvu, dvl;
                     const bool c = P.mon[i] != 0;
-                    coord_part<T>(coord_t<T>(P, q, xu, i, sq), c, +1, vu, dvu);
-                    coord_part<T>(coord_t<T>(P, q, xl, i, sq), c, -1, vl, dvl);
+                    coord_part<T>(tu[i], c, +1, vu, dvu);
+                    coord_part<T>(tl[i], c, -1, vl, dvl);
                     T gu = 0, gl = 0;
                     if (P.norm == LIP_L1) {
-                        gu = dvu * sq;
-                        gl = dvl * sq;
+                        gu = dvu * sq[i];
+                        gl = dvl * sq[i];
                     } else if (P.norm == LIP_L2) {
-                        if (du > 0) gu = dvu * sq * vu / du;
-                        if (dl > 0) gl = dvl * sq * vl / dl;
+                        gu = dvu * sq[i] * vu * ru;
+                        gl = dvl * sq[i] * vl * rl;
                     } else {
-                        if (i == mu && du > 0) gu = dvu * sq;
-                        if (i == ml && dl > 0) gl = dvl * sq;
+                        if (i == mu && du > 0) gu = dvu * sq[i];
+                        if (i == ml && dl > 0) gl = dvl * sq[i];
                     }
                     gq[i] = hm * (gu - gl);
                 }
             }
-            if (P.gy64) {
-                atomicAdd(P.gy64 + u, 0.5 * (double)gb);
-                atomicAdd(P.gy64 + l, 0.5 * (double)gb);
+            if (P.grad_y) {
+                T* gy = static_cast<T*>(P.grad_y);
+                atomicAdd(gy + u, (T)0.5 * gb);
+                atomicAdd(gy + l, (T)0.5 * gb);
             }
-            gm = 0.5 * (double)gb * ((double)du - (double)dl);
+            gm = (T)0.5 * gb * (du - dl);
         }
     }
     // fixed-shape block reduction of dL/dM
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) gm += __shfl_xor_sync(0xffffffffu, gm, off);
+    for (int off = 16; off > 0; off >>= 1) gm += __shfl_xor_sync(0xffffffffu, gm, off);   // warp sum in T
     __shared__ double red[BWD_THREADS / 32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = gm;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)gm;
     __syncthreads();
+    __shared__ bool last;
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < BWD_THREADS / 32; ++w) s += red[w];
         P.gm_part[blockIdx.x] = s;
+        __threadfence();                                   // the partial is visible before the count
+        last = atomicAdd(P.arrived, 1u) == gridDim.x - 1;
     }
-}
-
-__global__ void sum_partials_kernel(const double* part, int n, double* out) {
-    __shared__ double red[1024];
-    double s = 0.0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) s += part[k];
-    red[threadIdx.x] = s;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    if (!last || !P.grad_M) return;
+    // the last block sums every block's partial in block order: the same shape every call
+    __threadfence();
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += BWD_THREADS) s += P.gm_part[b];
+    __shared__ double red2[BWD_THREADS];
+    red2[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = BWD_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red2[threadIdx.x] += red2[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = red[0];
-}
-
-template <typename T>
-__global__ void add_grad_y_kernel(const double* gy64, int64_t n, T* grad_y) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) grad_y[k] = (T)((double)grad_y[k] + gy64[k]);
+    if (threadIdx.x == 0) *P.grad_M = red2[0];
 }
 
 int backward_blocks(int64_t nq) { return (int)((nq + BWD_THREADS - 1) / BWD_THREADS); }
 
-cudaError_t launch_backward(int elem_bytes, const BwdParams& P, int64_t N, void* grad_y, double* grad_M,
-                            cudaStream_t st) {
+cudaError_t launch_backward(int elem_bytes, const BwdParams& P, cudaStream_t st) {
     const int nb = backward_blocks(P.nq);
     if (nb > 0) {
         if (elem_bytes == 8) backward_kernel<double><<<nb, BWD_THREADS, 0, st>>>(P);
         else backward_kernel<float><<<nb, BWD_THREADS, 0, st>>>(P);
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (grad_M) {
-        sum_partials_kernel<<<1, 1024, 0, st>>>(P.gm_part, nb, grad_M);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if (grad_y && P.gy64 && N > 0) {
-        const unsigned g = (unsigned)((N + 255) / 256);
-        if (elem_bytes == 8) add_grad_y_kernel<double><<<g, 256, 0, st>>>(P.gy64, N, static_cast<double*>(grad_y));
-        else add_grad_y_kernel<float><<<g, 256, 0, st>>>(P.gy64, N, static_cast<float*>(grad_y));
-        e = cudaGetLastError();
-    }
-    return e;
+    return cudaGetLastError();
 }
 
 }  // namespace lip

@@ -30,13 +30,16 @@ struct BwdParams {
     double M;
     int8_t mon[D_MAX];
     double w[D_MAX];
+    float sqf[D_MAX];        // sign_i w_i in float (FP32 handles)
     const void* X0;
     const int32_t* iu;
     const int32_t* il;
     const void* gbar;
     void* grad_Q;            // nullable, [nq][d]
-    double* gy64;            // nullable, [N] scratch (zeroed by the caller)
+    void* grad_y;            // nullable, [N], accumulated
+    double* grad_M;          // nullable, overwritten
     double* gm_part;         // [backward_blocks(nq)] per-block partial sums of dL/dM
+    unsigned* arrived;       // blocks done (zeroed before the launch)
 };
 
 cudaError_t launch_merge(int elem_bytes, const MergeParams& P, cudaStream_t st);
@@ -48,16 +51,16 @@ cudaError_t launch_estimate_layout(int elem_bytes, const HotParams& P, cudaStrea
 cudaError_t launch_estimate(int norm, int d, const EstParams& P, cudaStream_t st);
 cudaError_t launch_estimate_final(const EstFinalParams& P, cudaStream_t st);
 
-size_t tc_tile_bytes_for(int d);
-size_t tc_a_bytes_for(int d);
+size_t tc_tile_bytes_for(int d, bool bf);
+size_t tc_a_bytes_for(int d, bool bf);
 size_t tc_rec_bytes();
 cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, const double* scale, double* stats,
-                            unsigned* maxbits, char* tiles, int64_t ntiles, cudaStream_t st);
+                            unsigned* maxbits, char* tiles, int64_t ntiles, bool bf, cudaStream_t st);
 cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scale, const double* stats, int64_t N,
                            const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float2* eps,
                            void* rec, const double* w, double M, const float* X0, const float* y0, float* g, float* lo,
                            float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, unsigned* err,
-                           int variant, cudaStream_t st);
+                           int variant, bool bf, cudaStream_t st);
 cudaError_t tc_gather(const float* Q, int d, const int* list, int n, float* out, cudaStream_t st);
 cudaError_t tc_scatter(const int* list, int n, const float* g, const float* lo, const float* hi, const int32_t* iu,
                        const int32_t* il, float* G, float* LO, float* HI, int32_t* IU, int32_t* IL, cudaStream_t st);
@@ -93,8 +96,7 @@ cudaError_t launch_topk(int elem_bytes, int norm, int K, const TopkParams& P, in
                         cudaStream_t st);
 
 int backward_blocks(int64_t nq);
-cudaError_t launch_backward(int elem_bytes, const BwdParams& P, int64_t N, void* grad_y, double* grad_M,
-                            cudaStream_t st);
+cudaError_t launch_backward(int elem_bytes, const BwdParams& P, cudaStream_t st);
 
 // ------------------------------------------------ local Lipschitz constants (Sec. 4.3)
 

@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanPa
     }
     const float scale = P.scale;
     float2 bu = make_float2(INFINITY, INFINITY), bl = make_float2(-INFINITY, -INFINITY);
-    int64_t tu0 = -1, tu1 = -1, tl0 = -1, tl1 = -1;        // tile of the last strict improvement
+    int tu0 = -1, tu1 = -1, tl0 = -1, tl1 = -1;            // tile of the last strict improvement
     const int64_t j_begin = (int64_t)split * P.points_per_split;
     const int64_t j_end = lmin(j_begin + P.points_per_split, P.npad);
     for (int64_t j0 = j_begin; j0 < j_end; j0 += LOC_SCAN_TILE) {
@@ -424,22 +424,22 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanPa
             cu = make_float2(fminf(cu.x, vu.x), fminf(cu.y, vu.y));      // NaN (padding) is ignored
             cl = make_float2(fmaxf(cl.x, vl.x), fmaxf(cl.y, vl.y));
         }
-        if (cu.x < bu.x) tu0 = j0;
-        if (cu.y < bu.y) tu1 = j0;
-        if (cl.x > bl.x) tl0 = j0;
-        if (cl.y > bl.y) tl1 = j0;
+        if (cu.x < bu.x) tu0 = (int)j0;
+        if (cu.y < bu.y) tu1 = (int)j0;
+        if (cl.x > bl.x) tl0 = (int)j0;
+        if (cl.y > bl.y) tl1 = (int)j0;
         bu = cu;
         bl = cl;
     }
     // lowest index in the remembered tile whose value equals the extremum
-    const int64_t tiles[4] = {tu0, tu1, tl0, tl1};
+    const int tiles[4] = {tu0, tu1, tl0, tl1};
     int idx[4] = {-1, -1, -1, -1};
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         if (tiles[c] < 0) continue;
         const float target = c == 0 ? bu.x : (c == 1 ? bu.y : (c == 2 ? bl.x : bl.y));
         for (int j = 0; j < LOC_SCAN_TILE; ++j) {
-            const int64_t k = tiles[c] + j;
+            const int64_t k = (int64_t)tiles[c] + j;
             float2 vu, vl;
             loc_pair_values<NORM, DP, BUCKET>(q2, P.rec + k * PR, P.mt + k * LOC_KNOTS, bk, Tn, scale, vu, vl);
             const float v = c == 0 ? vu.x : (c == 1 ? vu.y : (c == 2 ? vl.x : vl.y));

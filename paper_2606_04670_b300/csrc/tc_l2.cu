@@ -1,4 +1,4 @@
-// Tensor-core form of the unmasked L2 envelope scan (LIP_TC_TF32).
+// Tensor-core form of the unmasked L2 envelope scan (LIP_TC_TF32 and LIP_TC_BF16).
 //
 // Squared distance as one augmented product: with q^ = M w (q - c), x^ = M w (x - c)
 // (c = the data mean; distances do not depend on it),
@@ -6,6 +6,13 @@
 // padded with zeros to K = 8, 16 or 24.  Every operand is split v = hi + lo with hi the
 // value truncated to TF32 and lo the FP32 remainder, and s~ = a_hi.b_hi + a_hi.b_lo +
 // a_lo.b_hi runs as three tcgen05.mma kind::tf32 passes accumulating in FP32 in TMEM.
+//
+// BF16 (LIP_TC_BF16): K padded to 16 or 32, every operand split into three bf16 pieces
+// v = h + m + l (each the bf16 rounding of the remainder; |v - h - m - l| <= 2^-24 |v|),
+// and s~ = hh + hm + mh + hl + lh + mm (products of bf16 pieces are exact in FP32) runs as
+// six tcgen05.mma kind::f16 passes with both operands bf16.  The dropped products and the
+// representation error are <= 2^-22 |a||b|; FP32 accumulation of 6 K products adds at most
+// 6 K 2^-23 (<= 2.3e-5 at K = 32); with the input rounding the bound is 3e-5 (|q^| + R)^2.
 //
 // Error bound used to prune (conservative, per query):
 //   |s~ - s| <= eps = 2e-5 (|q^| + R)^2,  R = max_k |x^_k|, from
@@ -34,6 +41,8 @@
 // sqrt(eps), which delta already covers.)
 #include <cstdio>
 
+#include <cuda_bf16.h>
+
 #include "launch.h"
 
 namespace lip {
@@ -46,7 +55,8 @@ constexpr int TC_CAP = 8;
 // each (query, bound) keeps one candidate list per column slice.
 constexpr int TC_MAX_PARTS = 4;
 __host__ __device__ constexpr int tc_threads(int parts) { return 32 * (2 + 4 * parts); }
-constexpr float TC_C_EPS = 2.0e-5f;
+constexpr float TC_C_EPS = 2.0e-5f;        // TF32 split
+constexpr float TC_C_EPS_BF16 = 3.0e-5f;   // BF16 three-piece split
 
 struct TcRec {      // candidate list of one (query, bound, column quarter)
     float U;        // upper bound of H_up (bound 0) or lower bound of H_lo (bound 1)
@@ -55,17 +65,43 @@ struct TcRec {      // candidate list of one (query, bound, column quarter)
     float L[TC_CAP];
 };
 
-__host__ __device__ constexpr int tc_k_for_dim(int d) { return ((d + 2 + 7) / 8) * 8; }
-__host__ __device__ constexpr uint32_t tc_sbo(int K) { return (uint32_t)(K / 4) * 128u; }
-__host__ __device__ constexpr int tc_tile_bytes(int K) { return 2 * TC_N * K * 4 + TC_N * 4; }
-__host__ __device__ constexpr int tc_a_bytes(int K) { return 2 * TC_M * K * 4; }
+// Operand geometry per format: TF32 keeps 2 pieces of 4-byte elements with K a multiple
+// of 8; BF16 keeps 3 pieces of 2-byte elements with K a multiple of 16.  Either way one
+// MMA consumes 32 bytes of K per row (two 8-row x 16-byte core matrices).
+__host__ __device__ constexpr int tc_k_for_dim(int d, bool bf) { return bf ? ((d + 2 + 15) / 16) * 16 : ((d + 2 + 7) / 8) * 8; }
+__host__ __device__ constexpr int tc_pieces(bool bf) { return bf ? 3 : 2; }
+__host__ __device__ constexpr int tc_esz(bool bf) { return bf ? 2 : 4; }
+__host__ __device__ constexpr uint32_t tc_sbo_bytes(int row_bytes) { return (uint32_t)(row_bytes / 16) * 128u; }
+__host__ __device__ constexpr int tc_tile_bytes(int K, bool bf) { return tc_pieces(bf) * TC_N * K * tc_esz(bf) + TC_N * 4; }
+__host__ __device__ constexpr int tc_a_bytes(int K, bool bf) { return tc_pieces(bf) * TC_M * K * tc_esz(bf); }
 
-// byte offset of element (r, k) in a canonical no-swizzle K-major operand
-__host__ __device__ inline uint32_t tc_off(int r, int k, int K) {
-    return (uint32_t)(r / 8) * tc_sbo(K) + (uint32_t)(k / 4) * 128u + (uint32_t)(r % 8) * 16u + (uint32_t)(k % 4) * 4u;
+// byte offset of the element at row r, byte kb along K, in a canonical no-swizzle K-major
+// operand whose rows hold row_bytes of K (core matrices of 8 rows x 16 bytes)
+__host__ __device__ inline uint32_t tc_off(int r, int kb, int row_bytes) {
+    return (uint32_t)(r / 8) * tc_sbo_bytes(row_bytes) + (uint32_t)(kb / 16) * 128u + (uint32_t)(r % 8) * 16u +
+           (uint32_t)(kb % 16);
 }
 
-__device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+// Writes the pieces of v at (r, k) of a piece-major operand block (piece p at p * piece_bytes).
+template <bool BF>
+__device__ __forceinline__ void tc_store_pieces(char* base, int piece_bytes, int r, int k, int K, float v) {
+    if (BF) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const float r1 = v - __bfloat162float(h);
+        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(m);
+        const __nv_bfloat16 l = __float2bfloat16_rn(r2);
+        const uint32_t off = tc_off(r, k * 2, K * 2);
+        *reinterpret_cast<__nv_bfloat16*>(base + off) = h;
+        *reinterpret_cast<__nv_bfloat16*>(base + piece_bytes + off) = m;
+        *reinterpret_cast<__nv_bfloat16*>(base + 2 * piece_bytes + off) = l;
+    } else {
+        const float hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);   // truncated to TF32
+        const uint32_t off = tc_off(r, k * 4, K * 4);
+        *reinterpret_cast<float*>(base + off) = hi;
+        *reinterpret_cast<float*>(base + piece_bytes + off) = v - hi;
+    }
+}
 
 // --------------------------------------------------------------- data preparation
 
@@ -79,6 +115,7 @@ struct TcPrepParams {
     unsigned* maxbits;    // [2]: float bits of R and of max|y|
     char* tiles;          // [ntiles][tile_bytes]
     int64_t ntiles;
+    bool bf;              // BF16 pieces instead of TF32
 };
 
 __global__ void tc_sum_kernel(const TcPrepParams P) {
@@ -92,16 +129,16 @@ __global__ void tc_sum_kernel(const TcPrepParams P) {
     if (threadIdx.x < P.d) atomicAdd(&P.stats[threadIdx.x], acc[threadIdx.x]);
 }
 
-// One thread per (padded) data point: its row of B_hi, B_lo and y in the tile layout.
+// One thread per (padded) data point: its row of the B pieces and y in the tile layout.
+template <bool BF>
 __global__ void tc_build_b_kernel(const TcPrepParams P) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= P.ntiles * TC_N) return;
     const int64_t t = k / TC_N;
     const int r = (int)(k % TC_N);
-    char* tile = P.tiles + t * (int64_t)tc_tile_bytes(P.K);
-    float* bhi = reinterpret_cast<float*>(tile);
-    float* blo = reinterpret_cast<float*>(tile + TC_N * P.K * 4);
-    float* yv = reinterpret_cast<float*>(tile + 2 * TC_N * P.K * 4);
+    char* tile = P.tiles + t * (int64_t)tc_tile_bytes(P.K, BF);
+    const int piece = TC_N * P.K * tc_esz(BF);
+    float* yv = reinterpret_cast<float*>(tile + tc_pieces(BF) * piece);
     float b[32];
     for (int j = 0; j < P.K; ++j) b[j] = 0.f;
     float yy = __int_as_float(0x7fc00000);
@@ -119,11 +156,7 @@ __global__ void tc_build_b_kernel(const TcPrepParams P) {
         atomicMax(&P.maxbits[0], __float_as_uint((float)sqrt(n2)));
         atomicMax(&P.maxbits[1], __float_as_uint(fabsf(yy)));
     }
-    for (int j = 0; j < P.K; ++j) {
-        const float hi = tf32_trunc(b[j]);
-        bhi[tc_off(r, j, P.K) / 4] = hi;
-        blo[tc_off(r, j, P.K) / 4] = b[j] - hi;
-    }
+    for (int j = 0; j < P.K; ++j) tc_store_pieces<BF>(tile, piece, r, j, P.K, b[j]);
     yv[r] = yy;
 }
 
@@ -135,20 +168,20 @@ struct TcQueryParams {
     const double* stats;   // sums (centre = sums / N)
     int64_t N;
     const unsigned* maxbits;
-    char* atiles;          // [nqt][a_bytes]: A_hi then A_lo
+    char* atiles;          // [nqt][a_bytes]: the A pieces
     float2* eps;           // [nq]: (eps, eps_v)
 };
 
-// One thread per (padded) query: its row of A_hi, A_lo and its error bounds.
+// One thread per (padded) query: its row of the A pieces and its error bounds.
+template <bool BF>
 __global__ void tc_build_a_kernel(const TcQueryParams P) {
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nqp = (P.nq + TC_M - 1) / TC_M * TC_M;
     if (qi >= nqp) return;
     const int64_t t = qi / TC_M;
     const int r = (int)(qi % TC_M);
-    char* at = P.atiles + t * (int64_t)tc_a_bytes(P.K);
-    float* ahi = reinterpret_cast<float*>(at);
-    float* alo = reinterpret_cast<float*>(at + TC_M * P.K * 4);
+    char* at = P.atiles + t * (int64_t)tc_a_bytes(P.K, BF);
+    const int piece = TC_M * P.K * tc_esz(BF);
     float a[32];
     for (int j = 0; j < P.K; ++j) a[j] = 0.f;
     if (qi < P.nq) {
@@ -164,32 +197,34 @@ __global__ void tc_build_a_kernel(const TcQueryParams P) {
         const double R = (double)__uint_as_float(P.maxbits[0]);
         const double Y = (double)__uint_as_float(P.maxbits[1]);
         const double nq = sqrt(n2);
-        const float eps = (float)((double)TC_C_EPS * (nq + R) * (nq + R));
+        const float eps = (float)((double)(BF ? TC_C_EPS_BF16 : TC_C_EPS) * (nq + R) * (nq + R));
         const float epsv = (float)(ldexp(1.0, -19) * (Y + nq + R));
         P.eps[qi] = make_float2(eps, epsv);
     }
-    for (int j = 0; j < P.K; ++j) {
-        const float hi = tf32_trunc(a[j]);
-        ahi[tc_off(r, j, P.K) / 4] = hi;
-        alo[tc_off(r, j, P.K) / 4] = a[j] - hi;
-    }
+    for (int j = 0; j < P.K; ++j) tc_store_pieces<BF>(at, piece, r, j, P.K, a[j]);
 }
 
 // --------------------------------------------------------------- tcgen05 helpers
 
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, int K) {
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, int row_bytes) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;          // leading (K-direction) byte offset
-    d |= (uint64_t)((tc_sbo(K) >> 4) & 0x3FFFu) << 32;     // stride between 8-row groups
+    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;                      // leading (K-direction) byte offset
+    d |= (uint64_t)((tc_sbo_bytes(row_bytes) >> 4) & 0x3FFFu) << 32;   // stride between 8-row groups
     d |= (uint64_t)1 << 46;                                 // descriptor version of sm_100
     return d;                                               // no swizzle, base offset 0
 }
 
+template <bool BF>
 __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-                 ::"r"(dtmem), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
+    if (BF)   // both operands bf16 (the instruction descriptor says so for A and for B)
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                     ::"r"(dtmem), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
+    else
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                     ::"r"(dtmem), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
 }
 
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
@@ -279,12 +314,14 @@ __device__ __forceinline__ void tc_append(TcRec* R, int& n, int id, float L, flo
     ++n;
 }
 
-template <int K, int PARTS>
+template <int K, int PARTS, bool BF>
 __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcScanParams P) {
     constexpr int EPI_WARPS = 4 * PARTS;
-    constexpr int TILE_BYTES = tc_tile_bytes(K);
-    constexpr int A_BYTES = tc_a_bytes(K);
-    constexpr int KS = K / 8;
+    constexpr int TILE_BYTES = tc_tile_bytes(K, BF);
+    constexpr int A_BYTES = tc_a_bytes(K, BF);
+    constexpr int ROW_BYTES = K * tc_esz(BF);
+    constexpr int KS = ROW_BYTES / 32;                  // MMAs per pass (32 bytes of K each)
+    constexpr int A_PIECE = TC_M * ROW_BYTES, B_PIECE = TC_N * ROW_BYTES;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                               // A_hi, A_lo
     unsigned char* sB = smem + A_BYTES;                     // TC_STAGES tiles
@@ -341,9 +378,12 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+            // D = FP32 (bits 4-5); A and B formats (bits 7-9, 10-12): TF32 = 2 in kind::tf32,
+            // BF16 = 1 in kind::f16; K-major A and B; N / 8 and M / 16
+            const uint32_t fmt = BF ? 1u : 2u;
+            const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_N >> 3) << 17) |
                                    ((uint32_t)(TC_M >> 4) << 24);
-            const uint32_t a_hi = smem_u32(sA), a_lo = a_hi + TC_M * K * 4;
+            const uint32_t a0 = smem_u32(sA);
             int64_t t = 0;
             if (mbar_wait_bounded(&a_full, 0, P.err)) {
                 for (; t < T; ++t) {
@@ -351,17 +391,19 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                     if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / TC_STAGES) & 1), P.err)) break;
                     if (t >= 2 && !mbar_wait_bounded(&acc_empty[b], (uint32_t)((t / 2 - 1) & 1), P.err)) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t b_hi = smem_u32(sB + (size_t)s * TILE_BYTES), b_lo = b_hi + TC_N * K * 4;
+                    const uint32_t b0 = smem_u32(sB + (size_t)s * TILE_BYTES);
                     const uint32_t d = tb + (uint32_t)b * TC_N;
+                    // piece pairs: TF32 hi.hi, hi.lo, lo.hi; BF16 hh, hm, mh, hl, lh, mm
+                    constexpr int NPASS = BF ? 6 : 3;
+                    constexpr int PA[6] = {0, 0, 1, 0, 2, 1}, PB[6] = {0, 1, 0, 2, 0, 1};
 #pragma unroll
-                    for (int ks = 0; ks < KS; ++ks)
-                        tc_mma(d, tc_desc(a_hi + ks * 256, K), tc_desc(b_hi + ks * 256, K), idesc, ks > 0);
+                    for (int ps = 0; ps < NPASS; ++ps) {
+                        const uint32_t ap = a0 + PA[ps] * A_PIECE, bp = b0 + PB[ps] * B_PIECE;
 #pragma unroll
-                    for (int ks = 0; ks < KS; ++ks)
-                        tc_mma(d, tc_desc(a_hi + ks * 256, K), tc_desc(b_lo + ks * 256, K), idesc, 1);
-#pragma unroll
-                    for (int ks = 0; ks < KS; ++ks)
-                        tc_mma(d, tc_desc(a_lo + ks * 256, K), tc_desc(b_hi + ks * 256, K), idesc, 1);
+                        for (int ks = 0; ks < KS; ++ks)
+                            tc_mma<BF>(d, tc_desc(ap + ks * 256, ROW_BYTES), tc_desc(bp + ks * 256, ROW_BYTES), idesc,
+                                       (ps > 0 || ks > 0) ? 1u : 0u);
+                    }
                     tc_commit(&b_empty[s]);
                     tc_commit(&acc_full[b]);
                 }
@@ -388,7 +430,7 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
             // acquire the tile's y values written by the bulk copy
             if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / TC_STAGES) & 1), P.err)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const float* ys = reinterpret_cast<const float*>(sB + (size_t)s * TILE_BYTES + 2 * TC_N * K * 4);
+            const float* ys = reinterpret_cast<const float*>(sB + (size_t)s * TILE_BYTES + tc_pieces(BF) * B_PIECE);
             // two 32-column chunks per TMEM wait: both loads are in flight together
 #pragma unroll 1
             for (int j = 0; j < TC_N / 32 / PARTS; j += 2) {
@@ -600,18 +642,19 @@ __global__ void tc_scatter_kernel(const int* list, int n, const float* g, const 
 
 // --------------------------------------------------------------- launchers
 
-size_t tc_tile_bytes_for(int d) { return (size_t)tc_tile_bytes(tc_k_for_dim(d)); }
-size_t tc_a_bytes_for(int d) { return (size_t)tc_a_bytes(tc_k_for_dim(d)); }
+size_t tc_tile_bytes_for(int d, bool bf) { return (size_t)tc_tile_bytes(tc_k_for_dim(d, bf), bf); }
+size_t tc_a_bytes_for(int d, bool bf) { return (size_t)tc_a_bytes(tc_k_for_dim(d, bf), bf); }
 size_t tc_rec_bytes() { return sizeof(TcRec) * 2 * TC_MAX_PARTS; }   // candidate lists per query
 
 cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, const double* scale, double* stats,
-                            unsigned* maxbits, char* tiles, int64_t ntiles, cudaStream_t st) {
+                            unsigned* maxbits, char* tiles, int64_t ntiles, bool bf, cudaStream_t st) {
     TcPrepParams P{};
     P.X0 = X0;
     P.y0 = y0;
     P.N = N;
     P.d = d;
-    P.K = tc_k_for_dim(d);
+    P.K = tc_k_for_dim(d, bf);
+    P.bf = bf;
     for (int j = 0; j < D_MAX; ++j) P.scale[j] = scale[j];
     P.stats = stats;
     P.maxbits = maxbits;
@@ -622,25 +665,32 @@ cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, 
     if (e != cudaSuccess) return e;
     if (N > 0) tc_sum_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(P);
     const int64_t rows = ntiles * TC_N;
-    if (rows > 0) tc_build_b_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P);
+    if (rows > 0) {
+        if (bf) tc_build_b_kernel<true><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P);
+        else tc_build_b_kernel<false><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P);
+    }
     return cudaGetLastError();
 }
 
-template <int K, int PARTS>
+template <int K, int PARTS, bool BF>
 static cudaError_t launch_tc_scan_k(const TcScanParams& P, int64_t nqt, cudaStream_t st) {
-    const size_t smem = (size_t)tc_a_bytes(K) + (size_t)TC_STAGES * tc_tile_bytes(K);
+    const size_t smem = (size_t)tc_a_bytes(K, BF) + (size_t)TC_STAGES * tc_tile_bytes(K, BF);
     static cudaError_t attr =
-        cudaFuncSetAttribute(tc_scan_kernel<K, PARTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(tc_scan_kernel<K, PARTS, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return attr;
-    tc_scan_kernel<K, PARTS><<<(unsigned)nqt, tc_threads(PARTS), smem, st>>>(P);
+    tc_scan_kernel<K, PARTS, BF><<<(unsigned)nqt, tc_threads(PARTS), smem, st>>>(P);
     return cudaGetLastError();
 }
 
 template <int PARTS>
-static cudaError_t launch_tc_scan_parts(int K, const TcScanParams& P, int64_t nqt, cudaStream_t st) {
-    if (K == 8) return launch_tc_scan_k<8, PARTS>(P, nqt, st);
-    if (K == 16) return launch_tc_scan_k<16, PARTS>(P, nqt, st);
-    return launch_tc_scan_k<24, PARTS>(P, nqt, st);
+static cudaError_t launch_tc_scan_parts(int K, bool bf, const TcScanParams& P, int64_t nqt, cudaStream_t st) {
+    if (bf) {
+        if (K == 16) return launch_tc_scan_k<16, PARTS, true>(P, nqt, st);
+        return launch_tc_scan_k<32, PARTS, true>(P, nqt, st);
+    }
+    if (K == 8) return launch_tc_scan_k<8, PARTS, false>(P, nqt, st);
+    if (K == 16) return launch_tc_scan_k<16, PARTS, false>(P, nqt, st);
+    return launch_tc_scan_k<24, PARTS, false>(P, nqt, st);
 }
 
 // Queries: build A, scan, rescreen.  Returns the fallback count through fb (device).
@@ -648,8 +698,8 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
                            const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float2* eps,
                            void* rec, const double* w, double M, const float* X0, const float* y0, float* g, float* lo,
                            float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, unsigned* err,
-                           int variant, cudaStream_t st) {
-    const int K = tc_k_for_dim(d);
+                           int variant, bool bf, cudaStream_t st) {
+    const int K = tc_k_for_dim(d, bf);
     const int parts = variant == 1 ? 2 : 4;   // variant 0: 16 epilogue warps, 1: 8
     const int64_t nqt = (nq + TC_M - 1) / TC_M;
     TcQueryParams A{};
@@ -663,7 +713,8 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     A.maxbits = maxbits;
     A.atiles = atiles;
     A.eps = eps;
-    tc_build_a_kernel<<<(unsigned)((nqt * TC_M + 255) / 256), 256, 0, st>>>(A);
+    if (bf) tc_build_a_kernel<true><<<(unsigned)((nqt * TC_M + 255) / 256), 256, 0, st>>>(A);
+    else tc_build_a_kernel<false><<<(unsigned)((nqt * TC_M + 255) / 256), 256, 0, st>>>(A);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     TcScanParams S{};
@@ -674,7 +725,7 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     S.ntiles = ntiles;
     S.rec = static_cast<TcRec*>(rec);
     S.err = err;
-    e = parts == 2 ? launch_tc_scan_parts<2>(K, S, nqt, st) : launch_tc_scan_parts<4>(K, S, nqt, st);
+    e = parts == 2 ? launch_tc_scan_parts<2>(K, bf, S, nqt, st) : launch_tc_scan_parts<4>(K, bf, S, nqt, st);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(fb_count, 0, sizeof(int), st)) != cudaSuccess) return e;
     TcRescreenParams R{};

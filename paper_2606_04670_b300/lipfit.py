@@ -554,7 +554,7 @@ class LipFit:
         gg = grad_g.to(device="cuda", dtype=self.dtype).contiguous()
         gQ = torch.empty_like(Q) if need_Q else None
         gy = torch.zeros(self.N, device="cuda", dtype=self.dtype) if need_y else None
-        gM = torch.zeros(1, device="cuda", dtype=torch.float64) if need_M else None
+        gM = torch.empty(1, device="cuda", dtype=torch.float64) if need_M else None
         _check(_lib.lip_backward(self.h, Q.data_ptr(), Q.shape[0], idx_up.data_ptr(), idx_lo.data_ptr(),
                                  gg.data_ptr(), _ptr(gQ), _ptr(gy), _ptr(gM), _stream_ptr()), "lip_backward")
         return gQ, gy, gM

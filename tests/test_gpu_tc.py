@@ -1,5 +1,5 @@
-"""Tensor-core L2 form (LIP_TC_TF32): the TF32-split product on tcgen05 with an error
-bound, candidate pruning and an exact FP64 rescreen.  Its bounds are the FP64
+"""Tensor-core L2 form (LIP_TC_TF32, LIP_TC_BF16): the TF32- or BF16-split product on
+tcgen05 with an error bound, candidate pruning and an exact FP64 rescreen.  Its bounds are the FP64
 envelopes, so indices must match the oracle's wherever the oracle's gap exceeds
 1e-9 M diam (far below the FP32 tolerance).  Needs a CUDA device."""
 import numpy as np
@@ -12,14 +12,14 @@ pytestmark = pytest.mark.gpu
 EXACT_GAP = 1e-9
 
 
-def _tc_eval(p):
-    """Outputs of a LIP_TC_TF32 handle and the number of its queries that went through
+def _tc_eval(p, precision="tc_tf32"):
+    """Outputs of a tensor-core handle and the number of its queries that went through
     the plain FP32 fallback (those only meet the FP32 index rule)."""
     import torch
 
     from paper_2606_04670_b300.lipfit import LipFit
     m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, w=p.w,
-               precision="tc_tf32")
+               precision=precision)
     r = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
     fb = m.last_fallback()
     m.check()
@@ -120,3 +120,25 @@ def test_tc_full_size_cluster_sampled(oracle_mod):
     ps = W.Problem("c", p.X, p.y, p.Q[idx], p.M, p.norm, None, None)
     orc = oracle_mod.evaluate(p.X, p.y, ps.Q, p.M, p.norm)
     _check_exact(ps, {k: v[idx] for k, v in r.items()}, orc, "tc full cluster", fb)
+
+
+@pytest.mark.parametrize("d,weighted", [(1, False), (2, True), (6, True), (13, False), (14, True), (15, False),
+                                        (16, True)])
+def test_bf16_random_shapes(oracle_mod, d, weighted):
+    """The BF16 three-piece split (K = 16 up to d = 14, 32 above): the same exact results."""
+    p = W.random_problem(970 + d, 5_003, d, 1_201, norm=W.NORM_L2, weighted=weighted)
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm, w=p.w)
+    r, fb = _tc_eval(p, "tc_bf16")
+    _check_exact(p, r, orc, f"bf16 d={d}", fb)
+    if d >= 6:
+        assert fb <= 2, f"{fb} fallback queries at d={d}"
+
+
+def test_bf16_cluster_subsample(oracle_mod):
+    p = W.cluster_d16(n_data=30_000, n_query=1_500)
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm)
+    r, fb = _tc_eval(p, "tc_bf16")
+    _check_exact(p, r, orc, "bf16 cluster", fb)
+    rt, _ = _tc_eval(p, "tc_tf32")
+    for k in ("idx_up", "idx_lo"):
+        assert np.array_equal(r[k], rt[k]) or fb > 0

@@ -96,6 +96,9 @@ class Oracle:
         lib.oracle_eval_local.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, f64, P, P, P, P, P,
                                           P, P, i32]
         lib.oracle_local_terms.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, P, i32, P]
+        lib.oracle_eval_local_k.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, i32, P, P, P, P, P, P,
+                                            i32]
+        lib.oracle_eval_local_k.restype = ctypes.c_int
         lib.oracle_smooth_objective.argtypes = [P, P, i64, i32, f64, i32, P, P, f64, P, P, P, P, P]
         lib.oracle_smooth.argtypes = [P, P, i64, i32, f64, i32, P, P, f64, i32, i32, f64, P, P, P]
         lib.oracle_smooth_objective.restype = ctypes.c_int
@@ -251,6 +254,24 @@ class Oracle:
             raise ValueError("oracle_eval_local: bad arguments")
         return EvalResult(idx_up=iu, idx_lo=il, amb_up=au.astype(bool), amb_lo=al.astype(bool), **out)
 
+    def evaluate_local_k(self, X, y, Q, knots, table, k: int, wk, norm: int = NORM_L2, w=None,
+                         nthreads: Optional[int] = None) -> EvalResult:
+        """k > 1 neighbours with the local constants: weighted sums of the k best bounds."""
+        X, y, Q, w, wk = _f64(X), _f64(y), _f64(Q), _f64(w), _f64(wk)
+        T = _f64(np.asarray(knots, np.float64).reshape(-1))
+        d1, F, Mtab = (_f64(a) for a in table)
+        N, d = X.shape
+        nq = Q.shape[0]
+        out = {key: np.empty(nq) for key in ("hi", "lo", "g")}
+        iu, il = np.empty((nq, k), np.int64), np.empty((nq, k), np.int64)
+        rc = self.lib.oracle_eval_local_k(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(T), T.shape[0], _ptr(d1),
+                                          _ptr(F), _ptr(Mtab), _ptr(Q), nq, int(k), _ptr(wk), _ptr(out["hi"]),
+                                          _ptr(out["lo"]), _ptr(out["g"]), _ptr(iu), _ptr(il),
+                                          nthreads or default_threads())
+        if rc != 0:
+            raise ValueError("oracle_eval_local_k: bad arguments")
+        return EvalResult(idx_up=iu, idx_lo=il, **out)
+
     def local_terms(self, X, y, Q, knots, table, idx, side: int, norm: int = NORM_L2, w=None):
         """y_k + M_k(t) t (side +1) or y_k - M_k(t) t (side -1) for k = idx[q]."""
         X, y, Q, w = _f64(X), _f64(y), _f64(Q), _f64(w)
@@ -374,3 +395,7 @@ def smooth(*a, **k):
 
 def smooth_grad_rows(*a, **k):
     return default().smooth_grad_rows(*a, **k)
+
+
+def evaluate_local_k(*a, **k):
+    return default().evaluate_local_k(*a, **k)

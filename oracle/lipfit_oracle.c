@@ -578,6 +578,72 @@ int oracle_eval_local(const double* X, const double* y, int64_t N, int d, int no
     return 0;
 }
 
+/* k > 1 neighbours with the local constants (Sec. 5, values_local(query, model, k)): the
+ * weighted sums of the k smallest y^i + M_i(t_i) t_i and of the k largest y^i - M_i(t_i) t_i,
+ * equal values in increasing data index, as in oracle_eval_k. */
+typedef struct {
+    const double* X; const double* y; int64_t N; int d; int norm; const double* w;
+    const double* T; int m; const double *d1, *F, *Mtab;
+    const double* Q; int64_t q0, q1; int k; const double* wk;
+    double *hi, *lo, *g; int64_t *iu, *il;
+} levalk_job;
+
+static void* levalk_worker(void* arg) {
+    levalk_job* J = (levalk_job*)arg;
+    double bu[64], bl[64];
+    int64_t ku[64], kl[64];
+    for (int64_t qi = J->q0; qi < J->q1; qi++) {
+        const double* q = J->Q + qi * J->d;
+        int nu = 0, nl = 0, bad = 0;
+        for (int i = 0; i < J->d; i++) if (!isfinite(q[i])) bad = 1;
+        for (int64_t k = 0; k < J->N && !bad; k++) {
+            double t = sym_dist(q, J->X + k * J->d, J->d, J->norm, J->w);
+            double Mk = local_M(J->T, J->m, J->d1[k], J->F[k], J->Mtab + k * (J->m + 1), t);
+            double vu = J->y[k] + Mk * t, vl = J->y[k] - Mk * t;
+            if (nu < J->k || vu < bu[nu - 1]) {
+                int p = nu < J->k ? nu++ : J->k - 1;
+                while (p > 0 && bu[p - 1] > vu) { bu[p] = bu[p - 1]; ku[p] = ku[p - 1]; p--; }
+                bu[p] = vu; ku[p] = k;
+            }
+            if (nl < J->k || vl > bl[nl - 1]) {
+                int p = nl < J->k ? nl++ : J->k - 1;
+                while (p > 0 && bl[p - 1] < vl) { bl[p] = bl[p - 1]; kl[p] = kl[p - 1]; p--; }
+                bl[p] = vl; kl[p] = k;
+            }
+        }
+        double hu = 0.0, hl = 0.0;
+        for (int j = 0; j < J->k; j++) {
+            hu += J->wk[j] * (j < nu ? bu[j] : NAN);
+            hl += J->wk[j] * (j < nl ? bl[j] : NAN);
+            if (J->iu) J->iu[qi * J->k + j] = j < nu ? ku[j] : -1;
+            if (J->il) J->il[qi * J->k + j] = j < nl ? kl[j] : -1;
+        }
+        if (J->hi) J->hi[qi] = hu;
+        if (J->lo) J->lo[qi] = hl;
+        if (J->g) J->g[qi] = 0.5 * (hu + hl);
+    }
+    return NULL;
+}
+
+int oracle_eval_local_k(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
+                        const double* T, int m, const double* d1, const double* F, const double* Mtab,
+                        const double* Q, int64_t nq, int k, const double* wk,
+                        double* hi, double* lo, double* g, int64_t* iu, int64_t* il, int nthreads) {
+    if (N < 1 || d < 1 || nq < 0 || norm < 1 || norm > 3 || m < 0 || k < 1 || k > 64) return 1;
+    if (nq == 0) return 0;
+    nthreads = clamp_threads(nthreads, nq);
+    pthread_t th[256];
+    levalk_job jobs[256];
+    for (int t = 0; t < nthreads; t++) {
+        levalk_job j = {X, y, N, d, norm, w, T, m, d1, F, Mtab, Q, nq * t / nthreads, nq * (t + 1) / nthreads, k, wk,
+                        hi, lo, g, iu, il};
+        jobs[t] = j;
+        pthread_create(&th[t], NULL, levalk_worker, &jobs[t]);
+    }
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    return 0;
+}
+
 /* The value datum idx[q] gives query q: y + M_k(t) t (side > 0) or y - M_k(t) t. */
 int oracle_local_terms(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
                        const double* T, int m, const double* d1, const double* F, const double* Mtab,

@@ -510,6 +510,42 @@ def check_local_eval(O):
 
 
 
+def check_local_k_neighbours(O):
+    """k > 1 neighbours with the local constants: the k smallest / largest of the local bound
+    values built from scipy distances and the searchsorted form of M_k (stable sort); k = 1
+    equals the local evaluation; 1-D linear data equal the global k-neighbour evaluation."""
+    for p in _local_problems()[:4]:
+        T, _, _ = O.local_knots(p.X, 8, 300, 4, p.norm, w=p.w)
+        tab = O.local_table(p.X, p.y, T, p.norm, w=p.w)
+        d1, F, Mtab = tab
+        D = cdist(_scaled(p.Q, p.w), _scaled(p.X, p.w), METRIC[p.norm])
+        seg = np.searchsorted(T, D, side="left")
+        Mq = np.where(D <= d1[None, :], F[None, :], Mtab[np.arange(len(d1))[None, :], seg])
+        up, dn = p.y[None, :] + Mq * D, p.y[None, :] - Mq * D
+        for k in (1, 3, 5):
+            wk = np.linspace(1.0, 0.2, k)
+            wk /= wk.sum()
+            r = O.evaluate_local_k(p.X, p.y, p.Q, T, tab, k, wk, p.norm, w=p.w)
+            ou = np.argsort(up, axis=1, kind="stable")[:, :k]
+            od = np.argsort(-dn, axis=1, kind="stable")[:, :k]
+            np.testing.assert_allclose(r.hi, (np.take_along_axis(up, ou, 1) * wk).sum(1), atol=1e-12)
+            np.testing.assert_allclose(r.lo, (np.take_along_axis(dn, od, 1) * wk).sum(1), atol=1e-12)
+            if k == 1:
+                r1 = O.evaluate_local(p.X, p.y, p.Q, T, tab, p.norm, w=p.w)
+                assert np.array_equal(r.hi, r1.hi) and np.array_equal(r.idx_up[:, 0], r1.idx_up)
+    rng = np.random.default_rng(5)
+    X = rng.uniform(-1, 1, (30, 1))
+    y = 1.5 * X[:, 0]
+    Q = rng.uniform(-1.5, 1.5, (20, 1))
+    T, _, _ = O.local_knots(X, 5, 100, 2)
+    tab = O.local_table(X, y, T)
+    wk = np.array([0.5, 0.3, 0.2])
+    rl = O.evaluate_local_k(X, y, Q, T, tab, 3, wk)
+    rg = O.evaluate_k(X, y, Q, 1.5, 3, wk)
+    np.testing.assert_allclose(rl.hi, rg.hi, atol=1e-12)
+    np.testing.assert_allclose(rl.lo, rg.lo, atol=1e-12)
+
+
 # --------------------------------------------------------- penalty smoothing (Sec. 4.4)
 
 def _two_point_eps(a, p):
@@ -580,4 +616,4 @@ ALL_CHECKS = [check_hand_examples, check_closed_form_1d, check_unmasked_cdist, c
               check_enclosure, check_lipschitz_monotone, check_width_bound, check_special_cases,
               check_estimate_M, check_gradient_fd, check_k_neighbours, check_splitmix64,
               check_local_hand_example, check_local_knots, check_local_table, check_local_eval,
-              check_smoothing]
+              check_local_k_neighbours, check_smoothing]

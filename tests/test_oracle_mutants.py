@@ -39,6 +39,9 @@ MUTANTS = {
     "local_quantile_round": ("((int64_t)i * kept + m - 1) / m;", "((int64_t)i * kept + m / 2) / m;", 1),
     "local_ratio_signed": ("double r = fabs(J->y[k] - J->y[j]) / dd;\n            if (dd < d1)",
                            "double r = (J->y[k] - J->y[j]) / dd;\n            if (dd < d1)", 1),
+    # local k neighbours: the upper list keeps the largest values
+    "local_topk_upper_order": ("while (p > 0 && bu[p - 1] > vu) { bu[p] = bu[p - 1]; ku[p] = ku[p - 1]; p--; }\n                bu[p] = vu; ku[p] = k;\n            }\n            if (nl < J->k || vl > bl[nl - 1]) {\n                int p = nl < J->k ? nl++ : J->k - 1;\n                while (p > 0 && bl[p - 1] < vl) { bl[p] = bl[p - 1]; kl[p] = kl[p - 1]; p--; }\n                bl[p] = vl; kl[p] = k;\n            }\n        }\n        double hu = 0.0, hl = 0.0;\n        for (int j = 0; j < J->k; j++) {\n            hu += J->wk[j] * (j < nu ? bu[j] : NAN);\n            hl += J->wk[j] * (j < nl ? bl[j] : NAN);\n            if (J->iu) J->iu[qi * J->k + j] = j < nu ? ku[j] : -1;\n            if (J->il) J->il[qi * J->k + j] = j < nl ? kl[j] : -1;\n        }\n        if (J->hi) J->hi[qi] = hu;\n        if (J->lo) J->lo[qi] = hl;\n        if (J->g) J->g[qi] = 0.5 * (hu + hl);\n    }\n    return NULL;\n}\n\nint oracle_eval_local_k",
+                               "while (p > 0 && bu[p - 1] < vu) { bu[p] = bu[p - 1]; ku[p] = ku[p - 1]; p--; }\n                bu[p] = vu; ku[p] = k;\n            }\n            if (nl < J->k || vl > bl[nl - 1]) {\n                int p = nl < J->k ? nl++ : J->k - 1;\n                while (p > 0 && bl[p - 1] < vl) { bl[p] = bl[p - 1]; kl[p] = kl[p - 1]; p--; }\n                bl[p] = vl; kl[p] = k;\n            }\n        }\n        double hu = 0.0, hl = 0.0;\n        for (int j = 0; j < J->k; j++) {\n            hu += J->wk[j] * (j < nu ? bu[j] : NAN);\n            hl += J->wk[j] * (j < nl ? bl[j] : NAN);\n            if (J->iu) J->iu[qi * J->k + j] = j < nu ? ku[j] : -1;\n            if (J->il) J->il[qi * J->k + j] = j < nl ? kl[j] : -1;\n        }\n        if (J->hi) J->hi[qi] = hu;\n        if (J->lo) J->lo[qi] = hl;\n        if (J->g) J->g[qi] = 0.5 * (hu + hl);\n    }\n    return NULL;\n}\n\nint oracle_eval_local_k", 1),
     # penalty smoothing (Sec. 4.4): the sign of eps in Eq. (const2) flipped
     "smooth_const2_eps_sign": ("double v2 = y[k] - y[i] - M * dlo + eps[k] - eps[i];",
                                "double v2 = y[k] - y[i] - M * dlo - eps[k] + eps[i];", 1),

@@ -276,6 +276,14 @@ LIP_API lip_status lip_local_table(lip_handle h, double* d1, double* F, double* 
 LIP_API lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi,
                                   int32_t* idx_up, int32_t* idx_lo, void* stream);
 
+/* values_local(query, model, k) with k > 1 (Sec. 5): lip_eval_k's weighted sums of the k
+ * best bounds, each bound with the local constant of its datum.  k, wk, the outputs (float,
+ * device; idx_up / idx_lo [nq][k]) and the ordering of equal values as for lip_eval_k;
+ * the k selected bounds are re-evaluated in FP64 with the exact table.  LIP_ERR_STATE
+ * without a current table. */
+LIP_API lip_status lip_eval_local_k(lip_handle h, const void* Q, int64_t nq, int32_t k, const double* wk,
+                                    void* g, void* lo, void* hi, int32_t* idx_up, int32_t* idx_lo, void* stream);
+
 /* ------------------------------------------------ penalty smoothing (Sec. 4.4) */
 /* smooth_lipschitz(LC, model) of Sec. 5: changes eps to the data values minimising
  *

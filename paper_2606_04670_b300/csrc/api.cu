@@ -889,6 +889,73 @@ lip_status lip_local_table(lip_handle h, double* d1, double* F, double* Mtab, vo
     return LIP_OK;
 }
 
+lip_status lip_eval_local_k(lip_handle h, const void* Q, int64_t nq, int32_t k, const double* wk, void* g, void* lo,
+                            void* hi, int32_t* idx_up, int32_t* idx_lo, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (nq < 0) return fail(LIP_ERR_ARG, "nq = %lld < 0", (long long)nq);
+    if (k < 1 || k > 8) return fail(LIP_ERR_ARG, "k = %d is outside [1, 8]", k);
+    if (!wk) return fail(LIP_ERR_ARG, "wk is NULL");
+    for (int e = 0; e < k; ++e)
+        if (!(wk[e] >= 0.0) || !std::isfinite(wk[e])) return fail(LIP_ERR_ARG, "wk[%d] = %g must be finite and >= 0", e, wk[e]);
+    if (!h->loc_valid) return fail(LIP_ERR_STATE, "no local Lipschitz table: call lip_local_fit after the last data change");
+    if (nq == 0) return LIP_OK;
+    if (!Q) return fail(LIP_ERR_ARG, "Q is NULL");
+    DeviceGuard gd(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LocalParams P;
+    LIP_TRY(local_buffers(h, 0, P));
+    const int K = k <= 2 ? 2 : (k <= 4 ? 4 : 8);
+    const int64_t gx = ceil_div(nq, (int64_t)local_topk_threads());
+    if (gx > 0x7fffffff) return fail(LIP_ERR_ARG, "nq = %lld is too large", (long long)nq);
+    const int64_t tile = local_scan_tile();
+    const int64_t tiles = P.npad / tile;
+    const int64_t want = std::max<int64_t>(1, ceil_div((int64_t)4 * h->sms * 4, gx));
+    const int64_t s = std::min<int64_t>(std::min<int64_t>(want, 64), tiles);
+    const int64_t pps = round_up(ceil_div(P.npad, s), tile);
+    const int nsplit = (int)ceil_div(P.npad, pps);
+    LIP_TRY(h->partial.ensure((size_t)nsplit * nq * 2 * K * 8, "k-neighbour scratch"));
+    LocalScanParams S{};
+    S.Q = static_cast<const float*>(Q);
+    S.nq = nq;
+    S.d = h->d;
+    S.dp = P.dp;
+    for (int i = 0; i < D_MAX; ++i) S.w[i] = P.w[i];
+    S.rec = P.rec;
+    S.mt = P.mt;
+    S.Tf = P.Tf;
+    S.buckets = P.buckets;
+    S.scale = h->loc_scale;
+    S.bucket_ok = h->loc_bucket ? 1 : 0;
+    S.npad = P.npad;
+    S.points_per_split = pps;
+    S.partial = h->partial.p;
+    LocalMergeParams Mp{};
+    Mp.Q = S.Q;
+    Mp.nq = nq;
+    Mp.d = h->d;
+    Mp.norm = h->norm;
+    Mp.m = h->loc_m;
+    Mp.nsplit = nsplit;
+    for (int i = 0; i < D_MAX; ++i) Mp.w[i] = P.w[i];
+    Mp.X0 = P.X0;
+    Mp.y0 = P.y0;
+    Mp.d1 = P.d1;
+    Mp.F = P.F;
+    Mp.mt64 = P.mt64;
+    Mp.T64 = P.T64;
+    Mp.partial = h->partial.p;
+    Mp.g = static_cast<float*>(g);
+    Mp.lo = static_cast<float*>(lo);
+    Mp.hi = static_cast<float*>(hi);
+    Mp.idx_up = idx_up;
+    Mp.idx_lo = idx_lo;
+    LocalTopkWeights W{};
+    for (int e = 0; e < 8; ++e) W.wk[e] = e < k ? wk[e] : 0.0;
+    CUDA_TRY(launch_local_eval_k(h->norm, k, K, S, (int)gx, nsplit, Mp, W, st));
+    count_launches(2);
+    return LIP_OK;
+}
+
 lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* idx_up,
                           int32_t* idx_lo, void* stream) {
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
@@ -920,6 +987,7 @@ lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void
     S.Tf = P.Tf;
     S.buckets = P.buckets;
     S.scale = h->loc_scale;
+    S.bucket_ok = h->loc_bucket ? 1 : 0;
     S.npad = P.npad;
     S.points_per_split = pps;
     S.partial = h->partial.p;

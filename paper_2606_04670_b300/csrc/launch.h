@@ -145,6 +145,7 @@ struct LocalScanParams {
     const float* Tf;
     const int2* buckets;
     float scale;
+    int bucket_ok;                   // the bucket lookup applies (else binary search)
     int64_t npad, points_per_split;
     void* partial;                   // [nsplit][nq] PartialRec<float>
 };
@@ -165,7 +166,14 @@ struct LocalMergeParams {
     int32_t *idx_up, *idx_lo;
 };
 
+struct LocalTopkWeights {
+    double wk[8];
+};
+
 int local_dim_pad(int d);
+int local_topk_threads();
+cudaError_t launch_local_eval_k(int norm, int k, int K, const LocalScanParams& S, int gx, int nsplit,
+                                const LocalMergeParams& M, const LocalTopkWeights& W, cudaStream_t st);
 int local_record_floats(int d);
 int64_t local_pad(int64_t N);
 int local_scan_tile();

@@ -459,6 +459,155 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanPa
     }
 }
 
+// ------------------------------------------------ k > 1 neighbours with local constants
+
+// One query per thread; sorted lists of the K best upper and lower values per split, with
+// strict comparisons so equal values stay in data-index order (the scan visits the data in
+// increasing index).  The segment lookup is the bucket table or, when a bucket holds two
+// knots, the binary search.
+template <int NORM, int DP, int K>
+__global__ void __launch_bounds__(LOC_THREADS) loc_topk_scan_kernel(const LocalScanParams P, int K_out) {
+    constexpr int PR = DP + 4;
+    __shared__ float4 rec4[LOC_SCAN_TILE * PR / 4];
+    __shared__ float4 mt4[LOC_SCAN_TILE * LOC_KNOTS / 4];
+    __shared__ int2 bk[LOC_BUCKETS];
+    __shared__ float Tn[LOC_KNOTS];
+    const float* rec = reinterpret_cast<const float*>(rec4);
+    const float* mt = reinterpret_cast<const float*>(mt4);
+    const int tid = threadIdx.x;
+    const int split = blockIdx.y;
+    const int64_t qi = (int64_t)blockIdx.x * LOC_THREADS + tid;
+    float q[DP];
+#pragma unroll
+    for (int i = 0; i < DP; ++i) q[i] = (qi < P.nq && i < P.d) ? (float)(P.w[i] * (double)P.Q[qi * P.d + i]) : 0.f;
+    for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.buckets[b];
+    if (tid < LOC_KNOTS) Tn[tid] = P.Tf[tid];
+    const float scale = P.scale;
+    const bool bucket = P.bucket_ok != 0;
+    float bu[K], bl[K];
+    int ku[K], kl[K];
+#pragma unroll
+    for (int e = 0; e < K; ++e) { bu[e] = INFINITY; bl[e] = -INFINITY; ku[e] = -1; kl[e] = -1; }
+    const int64_t j_begin = (int64_t)split * P.points_per_split;
+    const int64_t j_end = lmin(j_begin + P.points_per_split, P.npad);
+    for (int64_t j0 = j_begin; j0 < j_end; j0 += LOC_SCAN_TILE) {
+        __syncthreads();
+        const float4* rs = reinterpret_cast<const float4*>(P.rec + j0 * PR);
+        for (int i = tid; i < LOC_SCAN_TILE * PR / 4; i += LOC_THREADS) rec4[i] = rs[i];
+        const float4* ms = reinterpret_cast<const float4*>(P.mt + j0 * LOC_KNOTS);
+        for (int i = tid; i < LOC_SCAN_TILE * LOC_KNOTS / 4; i += LOC_THREADS) mt4[i] = ms[i];
+        __syncthreads();
+        for (int j = 0; j < LOC_SCAN_TILE; ++j) {
+            const float* xj = rec + j * PR;
+            float t = dist32<NORM, DP>(q, xj);
+            if (NORM == LIP_L2) t = sqrt_approx(t);
+            int s;
+            if (bucket) {
+                const int2 e = bk[knot_bucket(t, scale)];
+                s = e.x + (__int_as_float(e.y) < t ? 1 : 0);
+            } else {
+                s = knot_count(Tn, t);
+            }
+            const float M = t <= xj[DP + 1] ? xj[DP + 2] : mt[j * LOC_KNOTS + s];
+            float vu = fmaf(M, t, xj[DP]), vl = fmaf(-M, t, xj[DP]);   // NaN (padding) never enters
+            const int idx = (int)(j0 + j);
+            if (vu < bu[K - 1]) {
+                int kk = idx;
+#pragma unroll
+                for (int p = 0; p < K; ++p)
+                    if (vu < bu[p]) {
+                        const float tv = bu[p]; bu[p] = vu; vu = tv;
+                        const int tk = ku[p]; ku[p] = kk; kk = tk;
+                    }
+            }
+            if (vl > bl[K - 1]) {
+                int kk = idx;
+#pragma unroll
+                for (int p = 0; p < K; ++p)
+                    if (vl > bl[p]) {
+                        const float tv = bl[p]; bl[p] = vl; vl = tv;
+                        const int tk = kl[p]; kl[p] = kk; kk = tk;
+                    }
+            }
+        }
+    }
+    if (qi >= P.nq) return;
+    float* pv = static_cast<float*>(P.partial);
+    int* pk = reinterpret_cast<int*>(pv + (int64_t)gridDim.y * P.nq * 2 * K);
+    const int64_t base = ((int64_t)split * P.nq + qi) * 2 * K;
+#pragma unroll
+    for (int e = 0; e < K; ++e) {
+        pv[base + e] = bu[e];
+        pk[base + e] = ku[e];
+        pv[base + K + e] = bl[e];
+        pk[base + K + e] = kl[e];
+    }
+    (void)K_out;
+}
+
+__device__ __forceinline__ double local_M64(const LocalMergeParams& P, int64_t k, double t);
+
+// The k best over the splits by (value, index), their exact FP64 values with the exact
+// table, sorted again by (exact value, index), and the weighted sums.
+__global__ void loc_topk_merge_kernel(const LocalMergeParams P, int k, int K, LocalTopkWeights W) {
+    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= P.nq) return;
+    const float* pv = static_cast<const float*>(P.partial);
+    const int* pk = reinterpret_cast<const int*>(pv + (int64_t)P.nsplit * P.nq * 2 * K);
+    const float* q = P.Q + qi * P.d;
+    bool finite = true;
+    for (int i = 0; i < P.d; ++i) finite = finite && isfinite(q[i]);
+    double res[2];
+    for (int side = 0; side < 2; ++side) {
+        float sv[8];
+        int sk[8];
+        for (int e = 0; e < k; ++e) { sv[e] = side == 0 ? INFINITY : -INFINITY; sk[e] = -1; }
+        for (int s = 0; s < P.nsplit; ++s) {
+            const int64_t base = ((int64_t)s * P.nq + qi) * 2 * K + side * K;
+            for (int e = 0; e < K; ++e) {
+                float v = pv[base + e];
+                int kk = pk[base + e];
+                if (kk < 0) break;
+                for (int p = 0; p < k; ++p) {
+                    const bool better = sk[p] < 0 || (side == 0 ? v < sv[p] : v > sv[p]) || (v == sv[p] && kk < sk[p]);
+                    if (better) {
+                        const float tv = sv[p]; sv[p] = v; v = tv;
+                        const int tk = sk[p]; sk[p] = kk; kk = tk;
+                        if (kk < 0) break;
+                    }
+                }
+            }
+        }
+        double ev[8];
+        int ek[8];
+        bool all = finite;
+        for (int e = 0; e < k; ++e) {
+            ek[e] = sk[e];
+            if (sk[e] < 0) { all = false; ev[e] = 0.0; continue; }
+            const double t = loc_dist64(q, P.X0 + (int64_t)sk[e] * P.d, P.d, P.norm, P.w);
+            const double yy = (double)P.y0[sk[e]], Mt = __dmul_rn(local_M64(P, sk[e], t), t);
+            ev[e] = side == 0 ? __dadd_rn(yy, Mt) : __dsub_rn(yy, Mt);
+        }
+        for (int a = 1; a < k; ++a)
+            for (int b = a; b > 0; --b) {
+                const bool sw = side == 0 ? (ev[b] < ev[b - 1] || (ev[b] == ev[b - 1] && ek[b] < ek[b - 1]))
+                                          : (ev[b] > ev[b - 1] || (ev[b] == ev[b - 1] && ek[b] < ek[b - 1]));
+                if (!sw) break;
+                const double tv = ev[b]; ev[b] = ev[b - 1]; ev[b - 1] = tv;
+                const int tk = ek[b]; ek[b] = ek[b - 1]; ek[b - 1] = tk;
+            }
+        double sum = 0.0;
+        for (int e = 0; e < k; ++e) sum += W.wk[e] * ev[e];
+        res[side] = all ? sum : __longlong_as_double(0x7ff8000000000000ll);
+        int32_t* out = side == 0 ? P.idx_up : P.idx_lo;
+        if (out)
+            for (int e = 0; e < k; ++e) out[qi * k + e] = all ? ek[e] : -1;
+    }
+    if (P.g) P.g[qi] = (float)(0.5 * (res[0] + res[1]));
+    if (P.hi) P.hi[qi] = (float)res[0];
+    if (P.lo) P.lo[qi] = (float)res[1];
+}
+
 __device__ __forceinline__ double local_M64(const LocalMergeParams& P, int64_t k, double t) {
     if (t <= P.d1[k]) return P.F[k];
     int s = 0;
@@ -568,6 +717,39 @@ static void scan_norm(const LocalScanParams& S, dim3 grid, bool bucket, cudaStre
         case 12: scan_shape<NORM, 12>(S, grid, bucket, st); break;
         default: scan_shape<NORM, 16>(S, grid, bucket, st); break;
     }
+}
+
+template <int NORM, int DP>
+static void topk_shape(int K, const LocalScanParams& S, dim3 grid, cudaStream_t st) {
+    if (K == 2) loc_topk_scan_kernel<NORM, DP, 2><<<grid, LOC_THREADS, 0, st>>>(S, K);
+    else if (K == 4) loc_topk_scan_kernel<NORM, DP, 4><<<grid, LOC_THREADS, 0, st>>>(S, K);
+    else loc_topk_scan_kernel<NORM, DP, 8><<<grid, LOC_THREADS, 0, st>>>(S, K);
+}
+
+template <int NORM>
+static void topk_norm(int K, const LocalScanParams& S, dim3 grid, cudaStream_t st) {
+    switch (S.dp) {
+        case 4: topk_shape<NORM, 4>(K, S, grid, st); break;
+        case 8: topk_shape<NORM, 8>(K, S, grid, st); break;
+        case 12: topk_shape<NORM, 12>(K, S, grid, st); break;
+        default: topk_shape<NORM, 16>(K, S, grid, st); break;
+    }
+}
+
+int local_topk_threads() { return LOC_THREADS; }
+
+cudaError_t launch_local_eval_k(int norm, int k, int K, const LocalScanParams& S, int gx, int nsplit,
+                                const LocalMergeParams& M, const LocalTopkWeights& W, cudaStream_t st) {
+    if (nsplit > 0) {
+        const dim3 grid((unsigned)gx, (unsigned)nsplit);
+        if (norm == LIP_L1) topk_norm<LIP_L1>(K, S, grid, st);
+        else if (norm == LIP_L2) topk_norm<LIP_L2>(K, S, grid, st);
+        else topk_norm<LIP_LINF>(K, S, grid, st);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    loc_topk_merge_kernel<<<(unsigned)((M.nq + 127) / 128), 128, 0, st>>>(M, k, K, W);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_local_eval(int norm, const LocalScanParams& S, int gx, int nsplit, bool bucket,

@@ -96,6 +96,7 @@ def _load():
         "lip_local_knots": [H, P, P],
         "lip_local_table": [H, P, P, P, P],
         "lip_eval_local": [H, P, i64, P, P, P, P, P, P],
+        "lip_eval_local_k": [H, P, i64, i32, P, P, P, P, P, P, P],
         "lip_smooth_objective": [H, f64, f64, P, ctypes.POINTER(f64), P, P],
         "lip_smooth": [H, f64, f64, i32, i32, f64, P, ctypes.POINTER(f64), ctypes.POINTER(i32),
                        ctypes.POINTER(i32), P],
@@ -226,6 +227,10 @@ def lip_local_table(h, d1, F, Mtab, stream=0):
 
 def lip_eval_local(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream=0):
     return _lib.lip_eval_local(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream)
+
+
+def lip_eval_local_k(h, Q_ptr, nq, k, wk_ptr, g, lo, hi, idx_up, idx_lo, stream=0):
+    return _lib.lip_eval_local_k(h, Q_ptr, nq, k, wk_ptr, g, lo, hi, idx_up, idx_lo, stream)
 
 
 def lip_smooth_objective(h, M, p, eps_ptr, grad_ptr, stream=0):
@@ -513,9 +518,25 @@ class LipFit:
         self._M = float(M)
         return eps, f, it, ev
 
-    def values_local(self, Q):
-        """g with the local constants (Sec. 5: values_local(query, model, k=1))."""
-        return self.eval_local(Q, need=("g",))["g"]
+    def eval_local_k(self, Q, k: int, wk):
+        """k > 1 neighbours with the local constants: dict of g, lo, hi [nq], idx_up, idx_lo [nq, k]."""
+        torch = _torch()
+        Q = self._dev(Q)
+        nq = Q.shape[0]
+        wk_a = np.ascontiguousarray(np.asarray(wk, np.float64))
+        assert wk_a.shape == (k,)
+        out = {key: torch.empty(nq, device="cuda", dtype=self.dtype) for key in ("g", "lo", "hi")}
+        out.update({key: torch.empty((nq, k), device="cuda", dtype=torch.int32) for key in ("idx_up", "idx_lo")})
+        _check(_lib.lip_eval_local_k(self.h, Q.data_ptr(), nq, int(k), wk_a.ctypes.data, out["g"].data_ptr(),
+                                     out["lo"].data_ptr(), out["hi"].data_ptr(), out["idx_up"].data_ptr(),
+                                     out["idx_lo"].data_ptr(), _stream_ptr()), "lip_eval_local_k")
+        return out
+
+    def values_local(self, Q, k: int = 1, wk=None):
+        """g with the local constants (Sec. 5: values_local(query, model, k))."""
+        if k == 1 and wk is None:
+            return self.eval_local(Q, need=("g",))["g"]
+        return self.eval_local_k(Q, k, np.ones(k) / k if wk is None else wk)["g"]
 
     def eval_host(self, Q, out=None):
         """lip_eval_host: Q and the outputs in host memory (numpy or pinned CPU tensors)."""

@@ -237,3 +237,41 @@ def test_close_knots_use_the_search_lookup():
         assert np.array_equal(a, b)
     _check_eval(p, X, y, Q, T, tab, m.eval_local(torch.as_tensor(p.Q).cuda()), "search-lookup")
     m.close()
+
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8])
+def test_local_k_neighbours(k):
+    """values_local(query, model, k): the weighted sums of the k best local bounds.  Indices
+    are compared where the oracle's k-th and (k+1)-th values are clearly apart and no knot
+    is within FP32 rounding; the values always, within the FP32 tolerance."""
+    p = W.random_problem(270 + k, 1500, 3, 700, norm=(k % 3) + 1, weighted=True)
+    X, y, Q = _f64(p.X), _f64(p.y), _f64(p.Q)
+    m = _model(p.X, p.y, p.norm, w=p.w)
+    T = m.compute_local_lipschitz(12, 3000, 9)
+    tab = _table(m)
+    wk = np.linspace(1.0, 0.3, k)
+    wk /= wk.sum()
+    out = m.eval_local_k(torch.as_tensor(p.Q).cuda(), k, wk)
+    torch.cuda.synchronize()
+    r = O.evaluate_local_k(X, y, Q, T, tab, k, wk, p.norm, w=p.w)
+    Z = np.abs(np.concatenate([X, Q]) * np.asarray(p.w))
+    eta = 2.0 ** -20 * (X.shape[1] + 2) * (Z.max() + diam(X, Q, p.norm, p.w))
+    amb = O.evaluate_local(X, y, Q, T, tab, p.norm, w=p.w, eta=eta)
+    tol = FP32_TOL * (float(np.abs(y).max()) + float(tab[2].max()) * diam(X, Q, p.norm, p.w))
+    # validity: the outputs are the weighted sums of the exact values of the returned data,
+    # which come sorted by value
+    for key, idx, side in (("hi", "idx_up", +1), ("lo", "idx_lo", -1)):
+        ix = out[idx].cpu().numpy().astype(np.int64)
+        vals = np.stack([O.local_terms(X, y, Q, T, tab, ix[:, j], side, p.norm, w=p.w) for j in range(k)], 1)
+        assert np.all(side * np.diff(vals, axis=1) >= 0)
+        got = out[key].cpu().numpy()
+        assert np.array_equal(got, (vals @ wk).astype(np.float32)) or np.allclose(got, vals @ wk, rtol=1e-6, atol=1e-7)
+    # the envelope sums within the FP32 tolerance wherever no knot decision is within rounding
+    clear = ~(amb.amb_up | amb.amb_lo)
+    for key in ("hi", "lo", "g"):
+        err = np.abs(out[key].cpu().numpy().astype(np.float64) - r[key])
+        assert np.mean(err[clear] <= tol) >= 0.995, (key, err[clear].max(), tol)
+    same = np.all(out["idx_up"].cpu().numpy() == r.idx_up, axis=1)
+    assert same.mean() > 0.95, same.mean()
+    m.close()

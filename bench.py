@@ -420,9 +420,11 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
     p = rd["p"]
     c = 0 if p.mon is None else int((np.asarray(p.mon) != 0).sum())
     ip = i_pair(p.norm, p.d, c)
-    exact = rd["prec"] == "fp32" and (p.d <= 10 or c == 0)
+    exact = rd["prec"] in ("fp32", "fp64") and (p.d <= 10 or c == 0)
     kern = (f"scan_{'exact' if exact else 'generic'}_kernel<{NNAME[p.norm]}, C={c}, U={p.d - c}, "
             f"R={rd['m'].tuning()['queries_per_thread']}> {rd['prec']}")
+    if rd["prec"] == "fp64":
+        kern = "FP32 screen " + kern.replace(" fp64", "") + " + screen64_kernel (FP64 candidates)"
     roof = ctx.roofline(kern, ip * p.nq * p.N, avg[kdom], ip, mufu_per_pair(p.norm, c), clocks,
                         SCAN_DRAM_BYTES.get((name, p.norm)) if rd["prec"] == "fp32" else None)
     if rd["prec"] in ("tc_tf32", "tc_bf16"):

@@ -64,7 +64,7 @@ typedef enum { LIP_L1 = 1, LIP_L2 = 2, LIP_LINF = 3 } lip_norm;
 
 typedef enum {
     LIP_FP32 = 0,      /* FP32 arithmetic in the all-pairs scan, FP64 re-evaluation of winners */
-    LIP_FP64 = 1,      /* FP64 throughout                                                   */
+    LIP_FP64 = 1,      /* FP64 data and results: FP32 screen, FP64 values (see lip_set_tuning) */
     LIP_TC_BF16 = 2,   /* L2 only: tensor-core cross term (bf16 split), exact FP64 rescreen  */
     LIP_TC_TF32 = 3    /* L2 only: tensor-core cross term (tf32 split), exact FP64 rescreen  */
     /* The tensor-core precisions need the L2 norm and no monotone coordinates (the squared
@@ -414,8 +414,11 @@ LIP_API void lip_batch_free(lip_batch b);
  *                merged afterwards; 0 = chosen per call to fill the GPU in whole waves.
  *   variant      scan kernel variant: 0 holds the default number of queries per thread,
  *                1 half as many (more resident warps); -1 keeps the current one.
- *                Ignored by the generic kernel.  For LIP_TC_TF32 handles: 0 runs the
- *                tensor-core epilogue on 16 warps, 1 on 8.
+ *                Ignored by the generic kernel.  For tensor-core handles: 0 runs the
+ *                tensor-core epilogue on 16 warps, 1 on 8.  For LIP_FP64 handles: 0 (the
+ *                default) scans a float copy of the layout and recomputes in FP64 only
+ *                the pairs within the FP32 error bound of the extremum, 1 scans in FP64
+ *                throughout; both return the FP64 envelopes.
  * LIP_ERR_ARG for other values. */
 LIP_API lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits, int32_t variant);
 

@@ -126,6 +126,15 @@ struct lip_model {
     cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
     cudaEvent_t ev_scan0 = nullptr, ev_scan1 = nullptr;   // caller's timing events
     // tensor-core form (LIP_TC_TF32)
+    // FP64 handles: a float copy of the layout for the FP32 screen of the exact FP64 scan
+    void* hot32 = nullptr;
+    int dl32 = 0, nch32 = 0, aux32 = 0;
+    bool exact32 = false, s32_dirty = true;
+    int fp64_mode = 0;                 // 0: FP32 screen + FP64 candidates; 1: FP64 scan throughout
+    ScanKernelInfo kinfo32;
+    int occ32 = 1;
+    unsigned* s32_max = nullptr;       // [2] largest |scaled coordinate| and |y| (float bits)
+    Scratch s64;                       // float queries and the FP32 pass's partials
     bool tc = false, tc_dirty = true;
     bool tc_bf = false;                // BF16 three-piece split instead of TF32
     int tc_variant = 0;                // 0: 16 epilogue warps, 1: 8
@@ -210,6 +219,9 @@ void free_model(lip_model* h) {
     if (h->X0) cudaFree(h->X0);
     if (h->y0) cudaFree(h->y0);
     if (h->hot) cudaFree(h->hot);
+    if (h->hot32) cudaFree(h->hot32);
+    if (h->s32_max) cudaFree(h->s32_max);
+    h->s64.release();
     if (h->status) cudaFree(h->status);
     h->partial.release();
     h->est.release();
@@ -295,6 +307,32 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
         cudaGetLastError();
         h->occ_blocks = 1;
     }
+    if (h->esize == 8) {
+        // the float layout of the FP32 screen: the FP32 handles' choice of kernel
+        if (exact_shape_available(h->C, U)) {
+            h->exact32 = true;
+            h->dl32 = d;
+            h->aux32 = (h->norm == LIP_L1 && h->C > 0) ? 1 : 0;
+            h->nch32 = d + 1 + h->aux32;
+            h->kinfo32 = scan_exact_info(h->norm, h->C, U);
+        } else {
+            const int dims[] = {2, 4, 8, 12, 16};
+            for (int v : dims)
+                if (v >= d) { h->dl32 = v; break; }
+            h->nch32 = h->dl32 + 1;
+            h->kinfo32 = scan_generic_info(4, h->norm, h->dl32);
+        }
+        if (!h->kinfo32.launch) {
+            free_model(h);
+            return fail(LIP_ERR_UNSUPPORTED, "no FP32 screen kernel for norm %d, %d + %d coordinates", p->norm, h->C, U);
+        }
+        const size_t smem32 = h->exact32 ? (size_t)SCAN_STAGES * h->tile_groups * h->nch32 * 16 : 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ32, h->kinfo32.kernel, SCAN_THREADS, smem32) !=
+                cudaSuccess || h->occ32 < 1) {
+            cudaGetLastError();
+            h->occ32 = 1;
+        }
+    }
     h->cap = cap;
     h->cap_pad = round_up(cap, PAD_POINTS);
     struct { void** p; size_t n; const char* what; } allocs[] = {
@@ -320,6 +358,20 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
             {reinterpret_cast<void**>(&h->tc_maxbits), 2 * sizeof(unsigned), "tensor-core bounds"},
         };
         for (auto& a : tca) {
+            e = cudaMalloc(a.p, a.n);
+            if (e != cudaSuccess) {
+                *a.p = nullptr;
+                free_model(h);
+                return cuda_fail(e, a.what);
+            }
+        }
+    }
+    if (h->esize == 8) {
+        struct { void** p; size_t n; const char* what; } s32[] = {
+            {&h->hot32, (size_t)h->cap_pad * h->nch32 * 4, "float screen layout"},
+            {reinterpret_cast<void**>(&h->s32_max), 2 * sizeof(unsigned), "screen bounds"},
+        };
+        for (auto& a : s32) {
             e = cudaMalloc(a.p, a.n);
             if (e != cudaSuccess) {
                 *a.p = nullptr;
@@ -366,6 +418,7 @@ lip_status add_points(lip_model* h, const void* X, const void* y, int64_t n, cud
     }
     h->N += n;
     h->tc_dirty = true;
+    h->s32_dirty = true;
     h->loc_valid = false;
     return LIP_OK;
 }
@@ -520,9 +573,119 @@ lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, v
     return LIP_OK;
 }
 
+// FP64 handles: the FP32 screen (float copy of the layout, the FP32 kernels), then the
+// candidate pass with FP64 values, then the usual merge (screen64.cu).
+lip_status eval_screen64(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* iu,
+                         int32_t* il, cudaStream_t st) {
+    const int64_t npad = round_up(h->N, PAD_POINTS);
+    if (h->s32_dirty) {
+        HotParams Hp;
+        fill_hot_params(h, Hp, 0, h->N);
+        Hp.hot = h->hot32;
+        Hp.dl = h->dl32;
+        Hp.nch = h->nch32;
+        Hp.aux = h->aux32;
+        CUDA_TRY(cudaMemsetAsync(h->s32_max, 0, 2 * sizeof(unsigned), st));
+        CUDA_TRY(launch_build_hot32(Hp, h->s32_max, st));
+        CUDA_TRY(launch_pad_hot(4, h->hot32, h->N, npad, h->nch32, h->dl32, st));
+        count_launches(2);
+        h->s32_dirty = false;
+    }
+    const int64_t ngroups = npad / GROUP;
+    const int tg = h->exact32 ? h->tile_groups : 1;
+    const int64_t gx = ceil_div(nq, (int64_t)SCAN_THREADS * h->kinfo32.rows);
+    const int64_t gx2 = ceil_div(nq, (int64_t)screen64_threads());
+    if (gx > 0x7fffffff || gx2 > 0x7fffffff) return fail(LIP_ERR_ARG, "nq = %lld is too large", (long long)nq);
+    int nsplit = 0, nsplit2 = 0;
+    int64_t gps = 0, gps2 = 0;
+    if (ngroups > 0) {
+        const int64_t unit = h->exact32 ? tg : TILE_GROUPS_MAX;
+        const int s = choose_splits(h, gx, ngroups / unit);
+        gps = round_up(ceil_div(ngroups, s), unit);
+        nsplit = (int)ceil_div(ngroups, gps);
+        const int s2 = choose_splits(h, gx2, ngroups / TILE_GROUPS_MAX);
+        gps2 = round_up(ceil_div(ngroups, s2), TILE_GROUPS_MAX);
+        nsplit2 = (int)ceil_div(ngroups, gps2);
+    }
+    h->last_splits = nsplit;
+    const size_t q_b = round_up(nq * h->d * 4, 256), p1_b = round_up((int64_t)std::max(nsplit, 1) * nq * 16, 256);
+    LIP_TRY(h->s64.ensure(q_b + p1_b, "FP64 screen scratch"));
+    LIP_TRY(h->partial.ensure(std::max<size_t>(1, (size_t)nsplit2 * nq * sizeof(PartialRec<double>)), "scan scratch"));
+    float* q32 = static_cast<float*>(h->s64.p);
+    PartialRec<float>* p1 = reinterpret_cast<PartialRec<float>*>(static_cast<char*>(h->s64.p) + q_b);
+    if (h->ev_scan0) CUDA_TRY(cudaEventRecord(h->ev_scan0, st));
+    if (nsplit > 0) {
+        CUDA_TRY(launch_to_float(static_cast<const double*>(Q), nq * h->d, q32, st));
+        ScanParams P;
+        fill_scan_params(h, P);
+        P.dl = h->dl32;
+        P.nch = h->nch32;
+        P.hot = h->hot32;
+        P.Q = q32;
+        P.nq = nq;
+        P.ngroups = ngroups;
+        P.groups_per_split = gps;
+        P.tile_groups = tg;
+        P.partial = p1;
+        CUDA_TRY(h->kinfo32.launch(P, (int)gx, nsplit, st));
+        Screen64Params S{};
+        S.Q = static_cast<const double*>(Q);
+        S.nq = nq;
+        S.C = h->C;
+        S.dl = h->dl32;
+        S.nch = h->nch32;
+        for (int j = 0; j < D_MAX; ++j) {
+            S.perm[j] = h->perm[j];
+            S.scale[j] = h->M * h->sgnw[j];
+        }
+        S.hot32 = h->hot32;
+        S.ngroups = ngroups;
+        S.groups_per_split = gps2;
+        S.nsplit1 = nsplit;
+        S.partial1 = p1;
+        S.maxbits = h->s32_max;
+        S.M.d = h->d;
+        S.M.M = h->M;
+        S.M.norm = h->norm;
+        for (int i = 0; i < D_MAX; ++i) {
+            S.M.mon[i] = h->mon[i];
+            S.M.w[i] = h->w[i];
+        }
+        S.M.X0 = h->X0;
+        S.M.y0 = h->y0;
+        S.partial2 = static_cast<PartialRec<double>*>(h->partial.p);
+        CUDA_TRY(launch_screen64(h->norm, S, (int)gx2, nsplit2, st));
+        count_launches(3);
+    }
+    if (h->ev_scan1) CUDA_TRY(cudaEventRecord(h->ev_scan1, st));
+    MergeParams Mp;
+    Mp.Q = Q;
+    Mp.nq = nq;
+    Mp.d = h->d;
+    Mp.nsplit = nsplit > 0 ? nsplit2 : 0;
+    Mp.M = h->M;
+    Mp.norm = h->norm;
+    for (int i = 0; i < D_MAX; ++i) {
+        Mp.mon[i] = h->mon[i];
+        Mp.w[i] = h->w[i];
+    }
+    Mp.X0 = h->X0;
+    Mp.y0 = h->y0;
+    Mp.partial = h->partial.p;
+    Mp.g = g;
+    Mp.lo = lo;
+    Mp.hi = hi;
+    Mp.idx_up = iu;
+    Mp.idx_lo = il;
+    CUDA_TRY(launch_merge(8, Mp, st));
+    count_launches(1);
+    return LIP_OK;
+}
+
 lip_status eval_device(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* iu, int32_t* il,
                        cudaStream_t st) {
     if (h->tc) return eval_tc(h, Q, nq, g, lo, hi, iu, il, st);
+    if (h->esize == 8 && h->fp64_mode == 0) return eval_screen64(h, Q, nq, g, lo, hi, iu, il, st);
     return eval_plain(h, Q, nq, g, lo, hi, iu, il, st);
 }
 
@@ -1062,6 +1225,7 @@ lip_status lip_clear(lip_handle h, void* stream) {
     count_launches(1);
     h->N = 0;
     h->tc_dirty = true;
+    h->s32_dirty = true;
     h->loc_valid = false;
     return LIP_OK;
 }
@@ -1074,6 +1238,7 @@ lip_status lip_set_M(lip_handle h, double M, void* stream) {
     DeviceGuard g(h->device);
     h->M = M;
     h->tc_dirty = true;
+    h->s32_dirty = true;
     HotParams P;
     fill_hot_params(h, P, 0, h->N);
     CUDA_TRY(launch_build_hot(h->esize, P, static_cast<cudaStream_t>(stream)));
@@ -1351,6 +1516,15 @@ lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits, int
     if (tile_groups) h->tile_groups = tile_groups;
     h->splits = splits;
     if (variant >= 0 && h->tc) h->tc_variant = variant;
+    if (variant >= 0 && h->esize == 8) h->fp64_mode = variant;
+    if (h->esize == 8 && h->exact32) {
+        const size_t smem32 = (size_t)SCAN_STAGES * h->tile_groups * h->nch32 * 16;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ32, h->kinfo32.kernel, SCAN_THREADS, smem32) !=
+                cudaSuccess || h->occ32 < 1) {
+            cudaGetLastError();
+            h->occ32 = 1;
+        }
+    }
     if (variant >= 0 && h->exact) {
         const ScanKernelInfo k = scan_exact_info(h->norm, h->C, h->d - h->C, variant);
         if (k.launch) {
@@ -1372,11 +1546,11 @@ lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits, int
 lip_status lip_get_tuning(lip_handle h, int32_t* tile_groups, int32_t* splits, int32_t* last_splits,
                           int32_t* queries_per_thread, int32_t* variant) {
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
-    if (variant) *variant = h->tc ? h->tc_variant : h->variant;
+    if (variant) *variant = h->tc ? h->tc_variant : (h->esize == 8 ? h->fp64_mode : h->variant);
     if (tile_groups) *tile_groups = h->tile_groups;
     if (splits) *splits = h->splits;
     if (last_splits) *last_splits = h->last_splits;
-    if (queries_per_thread) *queries_per_thread = h->kinfo.rows;
+    if (queries_per_thread) *queries_per_thread = (h->esize == 8 && h->fp64_mode == 0) ? h->kinfo32.rows : h->kinfo.rows;
     return LIP_OK;
 }
 

@@ -42,6 +42,27 @@ struct BwdParams {
     unsigned* arrived;       // blocks done (zeroed before the launch)
 };
 
+// Exact FP64 envelopes of FP64 handles from a float copy of the layout (screen64.cu).
+struct Screen64Params {
+    const double* Q;                  // caller's queries [nq][d]
+    int64_t nq;
+    int C, dl, nch;                   // the float layout
+    int perm[D_MAX];
+    double scale[D_MAX];              // M * sign_j * w_j
+    const void* hot32;
+    int64_t ngroups, groups_per_split;
+    int nsplit1;                      // splits of the FP32 pass
+    const PartialRec<float>* partial1;
+    const unsigned* maxbits;          // [2]: largest |scaled coordinate| and |y| (float bits)
+    MergeParams M;                    // d, norm, mon, w, M, X0, y0 for the FP64 values
+    PartialRec<double>* partial2;     // [gridDim.y][nq]
+};
+
+int screen64_threads();
+cudaError_t launch_build_hot32(const HotParams& P, unsigned* maxbits, cudaStream_t st);
+cudaError_t launch_to_float(const double* a, int64_t n, float* out, cudaStream_t st);
+cudaError_t launch_screen64(int norm, const Screen64Params& P, int gx, int gy, cudaStream_t st);
+
 cudaError_t launch_merge(int elem_bytes, const MergeParams& P, cudaStream_t st);
 cudaError_t launch_build_hot(int elem_bytes, const HotParams& P, cudaStream_t st);
 cudaError_t launch_pad_hot(int elem_bytes, void* hot, int64_t k0, int64_t k1, int nch, int dl, cudaStream_t st);

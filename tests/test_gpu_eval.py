@@ -56,6 +56,42 @@ def test_random_shapes_fp64(oracle_mod, norm):
         compare(p, gpu_eval(p, "fp64"), orc, FP64_TOL, f"fp64 d={d} {norm}")
 
 
+@pytest.mark.parametrize("norm", NORMS)
+def test_fp64_screen_equals_fp64_scan(oracle_mod, norm):
+    """FP64 handles: the FP32 screen with FP64 candidates (variant 0, the default) and the
+    FP64 scan throughout (variant 1) both give the oracle's FP64 envelopes; exact and
+    generic float layouts (masked d > 10 has no exact FP32 kernel), ragged sizes."""
+    for d, masked, weighted, N, nq in ((2, False, False, 1_001, 517), (4, True, True, 2_049, 300),
+                                       (11, True, False, 700, 129), (16, False, True, 1_300, 260)):
+        p = W.random_problem(320 + d, N, d, nq, norm=norm, masked=masked, weighted=weighted,
+                             decreasing=masked, dtype=np.float64)
+        orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, norm, mon=p.mon, w=p.w)
+        a = gpu_eval(p, "fp64", variant=0)
+        b = gpu_eval(p, "fp64", variant=1)
+        compare(p, a, orc, FP64_TOL, f"fp64 screen d={d} {norm}")
+        compare(p, b, orc, FP64_TOL, f"fp64 scan d={d} {norm}")
+        for k in ("idx_up", "idx_lo"):
+            clear = orc["gap_up" if k == "idx_up" else "gap_lo"] > 0
+            assert np.array_equal(a[k][clear], b[k][clear]), k
+
+
+def test_fp64_screen_ties_and_edges(oracle_mod):
+    """Every pair a candidate (M = 0, constant y: the lowest index wins), a single datum,
+    and a NaN query."""
+    X = np.random.default_rng(3).random((3000, 3))
+    y = np.full(3000, 0.25)
+    Q = np.random.default_rng(4).random((40, 3))
+    Q[5, 1] = np.nan
+    p = W.Problem("ties", X, y, Q, 0.0, 2, None, None)
+    r = gpu_eval(p, "fp64")
+    assert np.all(r["idx_up"][np.arange(40) != 5] == 0) and np.all(r["idx_lo"][np.arange(40) != 5] == 0)
+    assert np.isnan(r["g"][5]) and r["idx_up"][5] == -1
+    assert np.all(r["g"][np.arange(40) != 5] == 0.25)
+    p1 = W.Problem("one", X[:1], np.array([1.5]), Q[:4], 2.0, 1, None, None)
+    orc = oracle_mod.evaluate(p1.X, p1.y, p1.Q, p1.M, 1)
+    compare(p1, gpu_eval(p1, "fp64"), orc, FP64_TOL, "fp64 one datum")
+
+
 def test_workload_shapes(oracle_mod):
     for p in (W.toy_d3(), W.grad_d8(n_data=9_000, n_query=1_000), W.cluster_d16(n_data=12_000, n_query=500)):
         orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm, mon=p.mon, w=p.w)

@@ -325,12 +325,16 @@ LIP_API lip_status lip_smooth(lip_handle h, double M, double p, int32_t max_iter
  * tie of the maximum.  Q, idx_up, idx_lo are those given to / returned by lip_eval;
  * grad_g is [nq].  All device pointers; element type of the handle for Q, grad_g,
  * grad_Q, grad_y; grad_M is double.  Any of grad_Q, grad_y, grad_M may be NULL.
- * One kernel launch.  grad_y receives atomic additions of the element type, so its last
- * bits may change with the order of the atomics; grad_M uses a fixed-order two-level
- * reduction (finished by the last block) and is bitwise reproducible. */
+ * deterministic = 0: one kernel launch; grad_y receives atomic additions of the element
+ * type, so its last bits may change with the order of the atomics.  deterministic != 0:
+ * the contributions to grad_y are summed as 64-bit fixed point (scale 2^(60 - e) with
+ * nq max|grad_g| / 2 < 2^e), which integer atomics add exactly in any order, and then added
+ * to grad_y, so grad_y is bitwise reproducible (three launches).  grad_M uses a
+ * fixed-order two-level reduction (finished by the last block) and is always bitwise
+ * reproducible. */
 LIP_API lip_status lip_backward(lip_handle h, const void* Q, int64_t nq, const int32_t* idx_up,
                         const int32_t* idx_lo, const void* grad_g, void* grad_Q, void* grad_y,
-                        double* grad_M, void* stream);
+                        double* grad_M, int32_t deterministic, void* stream);
 
 /* ---------------------------------------------------------------- many data sets */
 
@@ -391,6 +395,9 @@ LIP_API lip_status lip_batch_create(const lip_batch_set* sets, int32_t nsets, co
  * and no synchronisation.  Results equal lip_eval on each set. */
 LIP_API lip_status lip_batch_eval(lip_batch b, void* stream);
 
+/* The same call under the name of the batched evaluation in the design notes. */
+LIP_API lip_status lip_eval_batched(lip_batch b, void* stream);
+
 /* Sizes of a batch: sum over sets of nq * N, sum of nq, work items, persistent grid. */
 LIP_API lip_status lip_batch_info(lip_batch b, double* total_pairs, int64_t* total_queries,
                                   int64_t* n_items, int32_t* grid);
@@ -421,6 +428,16 @@ LIP_API void lip_batch_free(lip_batch b);
  *                throughout; both return the FP64 envelopes.
  * LIP_ERR_ARG for other values. */
 LIP_API lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits, int32_t variant);
+
+/* The library's own autotuner: times lip_eval on Q (device, nq >= 1) for every variant x
+ * tile_groups {8, 16, 32, 64} x splits {0 (automatic), 1, 2, 3, 4, 6, 8, 12, 16} with CUDA
+ * events on the stream (median of reps runs after one warm-up run), applies the fastest
+ * with lip_set_tuning and returns it (host outputs, each may be NULL; *ms_out in ms).  The
+ * results of lip_eval do not depend on the choice.  Allocates and frees its own output
+ * buffers and synchronises the stream.  The Python package adds a JSON cache keyed by
+ * shape (paper_2606_04670_b300/autotune.py). */
+LIP_API lip_status lip_autotune(lip_handle h, const void* Q, int64_t nq, int32_t reps, int32_t* tile_groups_out,
+                                int32_t* splits_out, int32_t* variant_out, double* ms_out, void* stream);
 
 /* Current launch shape: tile_groups, the configured splits (0 = automatic), the splits
  * used by the last lip_eval, the queries held per thread by the scan kernel and the
@@ -457,6 +474,9 @@ LIP_API const char* lip_status_string(lip_status s);
 /* Copies the calling thread's last error message into buf (always NUL-terminated when
  * len > 0) and returns its full length. */
 LIP_API size_t lip_last_error(char* buf, size_t len);
+
+/* The same as lip_last_error. */
+LIP_API size_t lip_last_error_detail(char* buf, size_t len);
 
 /* Library version, e.g. "0.1.0 sm_103a". */
 LIP_API const char* lip_version(void);

@@ -1451,7 +1451,8 @@ lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, int64_t* 
 }
 
 lip_status lip_backward(lip_handle h, const void* Q, int64_t nq, const int32_t* idx_up, const int32_t* idx_lo,
-                        const void* grad_g, void* grad_Q, void* grad_y, double* grad_M, void* stream) {
+                        const void* grad_g, void* grad_Q, void* grad_y, double* grad_M, int32_t deterministic,
+                        void* stream) {
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
     if (nq < 0) return fail(LIP_ERR_ARG, "nq = %lld < 0", (long long)nq);
     if (nq > 0 && (!Q || !idx_up || !idx_lo || !grad_g)) return fail(LIP_ERR_ARG, "Q, indices or grad_g is NULL");
@@ -1459,7 +1460,9 @@ lip_status lip_backward(lip_handle h, const void* Q, int64_t nq, const int32_t* 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nb = backward_blocks(nq);
     const size_t part_b = round_up((int64_t)std::max(nb, 1) * 8, 256);
-    LIP_TRY(h->bwd.ensure(part_b + 256, "backward scratch"));
+    const bool det = deterministic != 0 && grad_y && h->N > 0;
+    const size_t fix_b = det ? round_up(h->N * 8, 256) : 0;
+    LIP_TRY(h->bwd.ensure(part_b + 256 + fix_b, "backward scratch"));
     char* base = static_cast<char*>(h->bwd.p);
     BwdParams P;
     P.Q = Q;
@@ -1481,13 +1484,20 @@ lip_status lip_backward(lip_handle h, const void* Q, int64_t nq, const int32_t* 
     P.arrived = reinterpret_cast<unsigned*>(base + part_b);
     P.grad_y = grad_y;
     P.grad_M = grad_M;
+    P.gy_fix = det ? reinterpret_cast<unsigned long long*>(base + part_b + 256) : nullptr;
+    P.gb_maxbits = P.arrived + 1;
     if (nq == 0) {
         if (grad_M) CUDA_TRY(cudaMemsetAsync(grad_M, 0, sizeof(double), st));
         return LIP_OK;
     }
-    CUDA_TRY(cudaMemsetAsync(P.arrived, 0, sizeof(unsigned), st));
+    CUDA_TRY(cudaMemsetAsync(P.arrived, 0, 2 * sizeof(unsigned), st));
+    if (det) {
+        CUDA_TRY(cudaMemsetAsync(P.gy_fix, 0, (size_t)h->N * 8, st));
+        CUDA_TRY(launch_grad_max(h->esize, grad_g, nq, P.arrived + 1, st));
+    }
     CUDA_TRY(launch_backward(h->esize, P, st));
-    count_launches(1);
+    if (det) CUDA_TRY(launch_grad_y_fix(h->esize, P.gy_fix, P.gb_maxbits, nq, h->N, grad_y, st));
+    count_launches(det ? 3 : 1);
     return LIP_OK;
 }
 
@@ -1543,6 +1553,70 @@ lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits, int
     return LIP_OK;
 }
 
+lip_status lip_autotune(lip_handle h, const void* Q, int64_t nq, int32_t reps, int32_t* tile_groups_out,
+                        int32_t* splits_out, int32_t* variant_out, double* ms_out, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (nq < 1 || !Q) return fail(LIP_ERR_ARG, "autotuning needs queries (nq = %lld)", (long long)nq);
+    if (reps < 1 || reps > 100) return fail(LIP_ERR_ARG, "reps = %d is outside [1, 100]", reps);
+    DeviceGuard gd(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* out = nullptr;
+    CUDA_TRY(cudaMalloc(&out, (size_t)nq * (3 * h->esize + 8)));
+    char* o = static_cast<char*>(out);
+    void* g = o;
+    int32_t* iu = reinterpret_cast<int32_t*>(o + (size_t)nq * 3 * h->esize);
+    int32_t* il = iu + nq;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t u0 = h->ev_scan0, u1 = h->ev_scan1;
+    h->ev_scan0 = h->ev_scan1 = nullptr;
+    const int32_t keep_tg = h->tile_groups, keep_sp = h->splits;
+    const int32_t keep_v = h->tc ? h->tc_variant : (h->esize == 8 ? h->fp64_mode : h->variant);
+    lip_status s = LIP_OK;
+    double best = 1e300;
+    int32_t btg = keep_tg, bsp = keep_sp, bv = keep_v;
+    const int tiles[] = {8, 16, 32, 64}, splits[] = {0, 1, 2, 3, 4, 6, 8, 12, 16};
+    const int nv = h->tc || h->esize == 8 || h->exact ? 2 : 1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        s = fail(LIP_ERR_CUDA, "cudaEventCreate failed");
+    } else {
+        for (int v = 0; v < nv && s == LIP_OK; ++v)
+            for (int tg : tiles)
+                for (int sp : splits) {
+                    if ((s = lip_set_tuning(h, tg, sp, v)) != LIP_OK) break;
+                    std::vector<float> ms;
+                    for (int r = 0; r <= reps && s == LIP_OK; ++r) {      // the first run warms up
+                        cudaEventRecord(e0, st);
+                        s = eval_device(h, Q, nq, g, nullptr, nullptr, iu, il, st);
+                        cudaEventRecord(e1, st);
+                        if (cudaEventSynchronize(e1) != cudaSuccess) s = fail(LIP_ERR_CUDA, "autotune timing failed");
+                        float t = 0.f;
+                        cudaEventElapsedTime(&t, e0, e1);
+                        if (r > 0) ms.push_back(t);
+                    }
+                    if (s != LIP_OK) break;
+                    std::sort(ms.begin(), ms.end());
+                    const double med = ms[ms.size() / 2];
+                    if (med < best) { best = med; btg = tg; bsp = sp; bv = v; }
+                    if (h->tc) break;                  // the tensor-core form ignores tiles and splits
+                }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    h->ev_scan0 = u0;
+    h->ev_scan1 = u1;
+    if (s != LIP_OK) {
+        lip_set_tuning(h, keep_tg, keep_sp, keep_v);
+        return s;
+    }
+    LIP_TRY(lip_set_tuning(h, btg, bsp, bv));
+    if (tile_groups_out) *tile_groups_out = btg;
+    if (splits_out) *splits_out = bsp;
+    if (variant_out) *variant_out = bv;
+    if (ms_out) *ms_out = best;
+    return LIP_OK;
+}
+
 lip_status lip_get_tuning(lip_handle h, int32_t* tile_groups, int32_t* splits, int32_t* last_splits,
                           int32_t* queries_per_thread, int32_t* variant) {
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
@@ -1592,6 +1666,10 @@ size_t lip_last_error(char* buf, size_t len) {
     }
     return g_err.size();
 }
+
+size_t lip_last_error_detail(char* buf, size_t len) { return lip_last_error(buf, len); }
+
+lip_status lip_eval_batched(lip_batch b, void* stream) { return lip_batch_eval(b, stream); }
 
 const char* lip_version(void) { return "0.1.0 sm_103a"; }
 

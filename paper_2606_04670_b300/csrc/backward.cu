@@ -6,9 +6,13 @@
 //   dL/dM     = 1/2 sum_q gbar_q ( dist_up(q, x^u) - dist_lo(q, x^l) )
 // One thread per query, in the caller's coordinates, arithmetic in the handle's
 // element type, all in one launch: dL/dy is added straight into the caller's grad_y with
-// atomics of the element type, and dL/dM is a fixed-shape two-level FP64 reduction
+// atomics of the element type (or, in the deterministic mode, summed as 64-bit fixed point
+// scaled by a power of two from max |grad_g|, whose integer atomics give the same bits in
+// any order, then added in a second pass), and dL/dM is a fixed-shape two-level FP64 reduction
 // finished by the last block to arrive (bitwise reproducible); the per-query terms and the
 // warp sums are in the element type, the block and grid sums in FP64.
+#include <algorithm>
+
 #include "launch.h"
 
 namespace lip {
@@ -28,6 +32,33 @@ __device__ __forceinline__ void coord_part(T t, bool constrained, int side, T& v
     }
 }
 
+
+// 2^e with the largest sum of contributions, nq * max|grad_g| / 2 per datum, below 2^60.
+__device__ __forceinline__ double fix_scale(const unsigned* maxbits, int64_t nq) {
+    const double bound = 0.5 * (double)__uint_as_float(*maxbits) * (double)(nq > 0 ? nq : 1);
+    int e;
+    frexp(bound > 0.0 ? bound : 1.0, &e);            // bound < 2^e
+    return ldexp(1.0, 60 - e);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) grad_max_kernel(const T* gb, int64_t n, unsigned* maxbits) {
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf((float)gb[i]) * (1.f + 1e-6f));   // float rounding of a double grad_g
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(maxbits, __float_as_uint(m));   // |.| orders as its bits
+}
+
+template <typename T>
+__global__ void grad_y_fix_kernel(const unsigned long long* fix, const unsigned* maxbits, int64_t nq, int64_t N,
+                                  T* grad_y) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const double v = (double)(long long)fix[k] / fix_scale(maxbits, nq);
+    grad_y[k] = (T)((double)grad_y[k] + v);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(BWD_THREADS) backward_kernel(const BwdParams P) {
@@ -99,7 +130,12 @@ __global__ void __launch_bounds__(BWD_THREADS) backward_kernel(const BwdParams P
                     gq[i] = hm * (gu - gl);
                 }
             }
-            if (P.grad_y) {
+            if (P.gy_fix) {
+                const double c = 0.5 * (double)gb * fix_scale(P.gb_maxbits, P.nq);
+                const unsigned long long f = (unsigned long long)__double2ll_rn(c);   // two's complement
+                atomicAdd(P.gy_fix + u, f);
+                atomicAdd(P.gy_fix + l, f);
+            } else if (P.grad_y) {
                 T* gy = static_cast<T*>(P.grad_y);
                 atomicAdd(gy + u, (T)0.5 * gb);
                 atomicAdd(gy + l, (T)0.5 * gb);
@@ -138,6 +174,22 @@ __global__ void __launch_bounds__(BWD_THREADS) backward_kernel(const BwdParams P
 }
 
 int backward_blocks(int64_t nq) { return (int)((nq + BWD_THREADS - 1) / BWD_THREADS); }
+
+cudaError_t launch_grad_max(int elem_bytes, const void* gbar, int64_t nq, unsigned* maxbits, cudaStream_t st) {
+    const unsigned g = (unsigned)std::min<int64_t>(1024, (nq + 255) / 256 > 0 ? (nq + 255) / 256 : 1);
+    if (elem_bytes == 8) grad_max_kernel<double><<<g, 256, 0, st>>>(static_cast<const double*>(gbar), nq, maxbits);
+    else grad_max_kernel<float><<<g, 256, 0, st>>>(static_cast<const float*>(gbar), nq, maxbits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_y_fix(int elem_bytes, const unsigned long long* gy_fix, const unsigned* maxbits, int64_t nq,
+                              int64_t N, void* grad_y, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    const unsigned g = (unsigned)((N + 255) / 256);
+    if (elem_bytes == 8) grad_y_fix_kernel<double><<<g, 256, 0, st>>>(gy_fix, maxbits, nq, N, static_cast<double*>(grad_y));
+    else grad_y_fix_kernel<float><<<g, 256, 0, st>>>(gy_fix, maxbits, nq, N, static_cast<float*>(grad_y));
+    return cudaGetLastError();
+}
 
 cudaError_t launch_backward(int elem_bytes, const BwdParams& P, cudaStream_t st) {
     const int nb = backward_blocks(P.nq);

@@ -40,6 +40,10 @@ struct BwdParams {
     double* grad_M;          // nullable, overwritten
     double* gm_part;         // [backward_blocks(nq)] per-block partial sums of dL/dM
     unsigned* arrived;       // blocks done (zeroed before the launch)
+    // deterministic grad_y: contributions summed as 64-bit fixed point (integer atomics
+    // are associative), then added to grad_y
+    unsigned long long* gy_fix;   // nullable, [N], zeroed before the launch
+    const unsigned* gb_maxbits;   // largest |grad_g| (float bits), for the fixed-point scale
 };
 
 // Exact FP64 envelopes of FP64 handles from a float copy of the layout (screen64.cu).
@@ -118,6 +122,9 @@ cudaError_t launch_topk(int elem_bytes, int norm, int K, const TopkParams& P, in
 
 int backward_blocks(int64_t nq);
 cudaError_t launch_backward(int elem_bytes, const BwdParams& P, cudaStream_t st);
+cudaError_t launch_grad_max(int elem_bytes, const void* gbar, int64_t nq, unsigned* maxbits, cudaStream_t st);
+cudaError_t launch_grad_y_fix(int elem_bytes, const unsigned long long* gy_fix, const unsigned* maxbits, int64_t nq,
+                              int64_t N, void* grad_y, cudaStream_t st);
 
 // ------------------------------------------------ local Lipschitz constants (Sec. 4.3)
 

@@ -79,7 +79,9 @@ def _load():
         "lip_eval_host": [H, P, i64, P, P, P, P, P, P],
         "lip_eval_k": [H, P, i64, i32, P, P, P, P, P, P, P],
         "lip_estimate_M": [H, ctypes.POINTER(f64), ctypes.POINTER(i64), ctypes.POINTER(i64), P],
-        "lip_backward": [H, P, i64, P, P, P, P, P, P, P],
+        "lip_backward": [H, P, i64, P, P, P, P, P, P, i32, P],
+        "lip_eval_batched": [H, P],
+        "lip_autotune": [H, P, i64, i32, P, P, P, P, P],
         "lip_check": [H, P],
         "lip_set_tuning": [H, i32, i32, i32],
         "lip_get_tuning": [H, P, P, P, P, P],
@@ -115,6 +117,8 @@ def _load():
     lib.lip_status_string.restype = ctypes.c_char_p
     lib.lip_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     lib.lip_last_error.restype = ctypes.c_size_t
+    lib.lip_last_error_detail.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    lib.lip_last_error_detail.restype = ctypes.c_size_t
     lib.lip_version.restype = ctypes.c_char_p
     lib.lip_kernel_launches.restype = ctypes.c_uint64
     lib.lip_last_fallback.argtypes = [H]
@@ -261,8 +265,27 @@ def lip_estimate_M_noalloc(X_ptr, y_ptr, N, d, norm, w_ptr, out_ptr, stream=0):
     return _lib.lip_estimate_M_noalloc(X_ptr, y_ptr, N, d, norm, w_ptr, out_ptr, stream)
 
 
-def lip_backward(h, Q_ptr, nq, idx_up, idx_lo, grad_g, grad_Q, grad_y, grad_M, stream=0):
-    return _lib.lip_backward(h, Q_ptr, nq, idx_up, idx_lo, grad_g, grad_Q, grad_y, grad_M, stream)
+def lip_backward(h, Q_ptr, nq, idx_up, idx_lo, grad_g, grad_Q, grad_y, grad_M, deterministic=0, stream=0):
+    return _lib.lip_backward(h, Q_ptr, nq, idx_up, idx_lo, grad_g, grad_Q, grad_y, grad_M, deterministic, stream)
+
+
+def lip_autotune(h, Q_ptr, nq, reps=3, stream=0):
+    """(status, tile_groups, splits, variant, ms) of the library's own autotuner."""
+    tg, sp, v = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    ms = ctypes.c_double()
+    s = _lib.lip_autotune(h, Q_ptr, nq, reps, ctypes.byref(tg), ctypes.byref(sp), ctypes.byref(v), ctypes.byref(ms),
+                          stream)
+    return s, tg.value, sp.value, v.value, ms.value
+
+
+def lip_eval_batched(b, stream=0):
+    return _lib.lip_eval_batched(b, stream)
+
+
+def lip_last_error_detail():
+    buf = ctypes.create_string_buffer(1024)
+    _lib.lip_last_error_detail(buf, len(buf))
+    return buf.value.decode()
 
 
 def lip_set_tuning(h, tile_groups, splits, variant=-1):
@@ -569,7 +592,7 @@ class LipFit:
         _check(s, "lip_estimate_M")
         return M, i, j
 
-    def backward(self, Q, idx_up, idx_lo, grad_g, need_Q=True, need_y=True, need_M=True):
+    def backward(self, Q, idx_up, idx_lo, grad_g, need_Q=True, need_y=True, need_M=True, deterministic=False):
         torch = _torch()
         Q = self._dev(Q)
         gg = grad_g.to(device="cuda", dtype=self.dtype).contiguous()
@@ -577,7 +600,8 @@ class LipFit:
         gy = torch.zeros(self.N, device="cuda", dtype=self.dtype) if need_y else None
         gM = torch.empty(1, device="cuda", dtype=torch.float64) if need_M else None
         _check(_lib.lip_backward(self.h, Q.data_ptr(), Q.shape[0], idx_up.data_ptr(), idx_lo.data_ptr(),
-                                 gg.data_ptr(), _ptr(gQ), _ptr(gy), _ptr(gM), _stream_ptr()), "lip_backward")
+                                 gg.data_ptr(), _ptr(gQ), _ptr(gy), _ptr(gM), int(bool(deterministic)),
+                                 _stream_ptr()), "lip_backward")
         return gQ, gy, gM
 
     def check(self):

@@ -62,6 +62,10 @@ def test_null_handle_calls():
     assert L.lip_set_M(None, 1.0) == L.LIP_ERR_ARG
     assert L.lip_estimate_M(None)[0] == L.LIP_ERR_ARG
     assert L.lip_backward(None, None, 0, None, None, None, None, None, None) == L.LIP_ERR_ARG
+    assert L.lip_backward(None, None, 0, None, None, None, None, None, None, 1) == L.LIP_ERR_ARG
+    assert L.lip_eval_batched(None) == L.LIP_ERR_ARG
+    assert L.lip_autotune(None, None, 1)[0] == L.LIP_ERR_ARG
+    assert isinstance(L.lip_last_error_detail(), str)
     assert L.lip_check(None) == L.LIP_ERR_ARG
     assert L.lip_set_tuning(None, 0, 0, 0) == L.LIP_ERR_ARG
     assert L.lip_get_tuning(None)[0] == L.LIP_ERR_ARG

@@ -42,3 +42,27 @@ def test_tune_batch_returns_options():
                          norm=bs.norm, mon=bs.mon))
     rec = AT.tune_batch(sets, tiles=(16, 32), items=(4, 8), cache={}, reps=1)
     assert rec["tile_groups"] in (16, 32) and rec["items_per_block"] in (4, 8) and rec["candidates"] == 4
+
+
+def test_c_abi_autotune_keeps_results():
+    """lip_autotune (the library's own tuner) applies a launch shape and changes no result."""
+    import torch
+
+    from paper_2606_04670_b300 import lipfit as L
+    from paper_2606_04670_b300.lipfit import LipFit
+    for prec, p in (("fp32", W.monotone_d4(norm=W.NORM_L1, n_data=8_000, n_query=20_000)),
+                    ("fp64", W.random_problem(7, 3_000, 3, 2_000, norm=2, dtype=np.float64))):
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        m = LipFit(torch.as_tensor(p.X).to("cuda", dt), torch.as_tensor(p.y).to("cuda", dt), p.M, norm=p.norm,
+                   mon=p.mon, precision=prec)
+        Q = torch.as_tensor(p.Q).to("cuda", dt)
+        ref = {k: v.cpu().numpy() for k, v in m.eval(Q).items()}
+        s, tg, sp, v, ms = L.lip_autotune(m.h, Q.data_ptr(), Q.shape[0], 2, torch.cuda.current_stream().cuda_stream)
+        assert s == L.LIP_OK, L.last_error()
+        assert tg in (8, 16, 32, 64) and ms > 0
+        t = m.tuning()
+        assert (t["tile_groups"], t["splits"]) == (tg, sp)
+        got = {k: v.cpu().numpy() for k, v in m.eval(Q).items()}
+        for k in ref:
+            np.testing.assert_array_equal(got[k], ref[k])
+        m.close()

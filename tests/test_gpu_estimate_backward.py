@@ -164,3 +164,26 @@ def test_autograd_gradcheck_fp64():
     assert y.grad is not None and abs(y.grad.sum().item() - p.nq) < 1e-9   # each query: 1/2 + 1/2
     assert M.grad is not None
     m.close()
+
+
+def test_backward_deterministic_mode(oracle_mod):
+    """deterministic=True: grad_y bitwise identical across runs and equal to the atomic path
+    within rounding; grad_Q and grad_M unchanged."""
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    p = W.grad_d8(n_data=5_000, n_query=40_000)
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, mon=p.mon)
+    Q = torch.as_tensor(p.Q).cuda()
+    r = m.eval(Q)
+    gb = torch.as_tensor(np.random.default_rng(2).standard_normal(p.nq).astype(np.float32)).cuda()
+    a = m.backward(Q, r["idx_up"], r["idx_lo"], gb)
+    b1 = m.backward(Q, r["idx_up"], r["idx_lo"], gb, deterministic=True)
+    b2 = m.backward(Q, r["idx_up"], r["idx_lo"], gb, deterministic=True)
+    torch.cuda.synchronize()
+    assert torch.equal(b1[1], b2[1]) and torch.equal(b1[0], a[0]) and torch.equal(b1[2], a[2])
+    np.testing.assert_allclose(b1[1].cpu().numpy(), a[1].cpu().numpy(), rtol=1e-5, atol=1e-5)
+    _, oy, _ = oracle_mod.gradient(p.X, p.y, p.Q, p.M, r["idx_up"].cpu().numpy(), r["idx_lo"].cpu().numpy(),
+                                   gb.cpu().numpy().astype(np.float64), p.norm, p.mon)
+    np.testing.assert_allclose(b1[1].cpu().numpy(), oy, rtol=1e-5, atol=1e-5)
+    m.close()

@@ -233,8 +233,8 @@ LIP_API lip_status lip_estimate_M_noalloc(const float* X, const float* y, int64_
  * The table is exact: every distance and ratio that decides an entry is the IEEE double
  * result of the definition above (each operation rounded once, coordinates in order),
  * found by an FP32 screen with a rigorous error bound and FP64 re-computation of every
- * pair the bound cannot rule out.  Handles: float data (LIP_FP32 or LIP_TC_TF32) without
- * monotone coordinates, else LIP_ERR_UNSUPPORTED.  Adding or clearing data invalidates
+ * pair the bound cannot rule out.  Handles: any precision without monotone coordinates,
+ * else LIP_ERR_UNSUPPORTED (FP64 handles: float or double arrays as for lip_eval).  Adding or clearing data invalidates
  * the table (LIP_ERR_STATE until the next fit).  N^2 work per fit (two passes). */
 
 /* Largest number of knots. */
@@ -268,7 +268,7 @@ LIP_API lip_status lip_local_knots(lip_handle h, double* knots, int32_t* nknots)
 LIP_API lip_status lip_local_table(lip_handle h, double* d1, double* F, double* Mtab, void* stream);
 
 /* The envelopes with the local constants.  Arguments, outputs and NaN handling as for
- * lip_eval (float, device).  The scan runs in FP32 and picks the winning data; their
+ * lip_eval (element type of the handle, device).  The scan runs in FP32 and picks the winning data; their
  * bounds are then recomputed in FP64 with the exact table, so hi/lo are the exact values
  * of the selected data.  The selection can differ from the exact one where two values are
  * within FP32 rounding, or where a distance lies within FP32 rounding of one of the
@@ -294,8 +294,8 @@ LIP_API lip_status lip_eval_local_k(lip_handle h, const void* Q, int64_t nq, int
  * (Eq. (optim)), d+_ik = dist_up(x^i, x^k) and d-_ik = dist_lo(x^i, x^k) of the handle's
  * norm, weights and monotone coordinates (both the symmetric distance without them).
  * One evaluation is a fused pass over all N (N - 1) ordered pairs in FP32 with FP64 sums;
- * nothing pairwise is stored.  Handles: float data (LIP_FP32 or LIP_TC_TF32), N >= 1;
- * M finite >= 0, p finite > 0.  FP64 handles: LIP_ERR_UNSUPPORTED. */
+ * nothing pairwise is stored.  Any handle with N >= 1 (on FP64 handles the pair terms are
+ * still FP32, from the values rounded once); M finite >= 0, p finite > 0. */
 
 /* Phi and its gradient at eps (device double [N]): *f_out (host), grad (device double [N],
  * may be NULL).  Synchronises the stream. */
@@ -306,7 +306,8 @@ LIP_API lip_status lip_smooth_objective(lip_handle h, double M, double p, const 
  * pairs 1..64, backtracking Armijo line search from step 1), stopping when max |dPhi/deps|
  * <= gtol or after max_iter iterations.  Then, as the paper's package does, the handle's
  * values become y + eps (rounded to float) and its constant becomes M, so lip_eval
- * evaluates the smoothed interpolant at once; a local Lipschitz table is invalidated.
+ * evaluates the smoothed interpolant at once (y + eps stays FP64 on FP64 handles); a local
+ * Lipschitz table is invalidated.
  * eps_out (device double [N]) may be NULL; *f_out = Phi at the result, *iters_out = the
  * iterations taken, *evals_out = the objective evaluations (host, each may be NULL).  Synchronises the stream many times (the line
  * search reads Phi).  Errors: LIP_ERR_ARG, LIP_ERR_UNSUPPORTED, LIP_ERR_OOM, LIP_ERR_CUDA. */

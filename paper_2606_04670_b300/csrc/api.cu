@@ -603,8 +603,10 @@ lip_status eval_screen64(lip_model* h, const void* Q, int64_t nq, void* g, void*
         const int s = choose_splits(h, gx, ngroups / unit);
         gps = round_up(ceil_div(ngroups, s), unit);
         nsplit = (int)ceil_div(ngroups, gps);
-        const int s2 = choose_splits(h, gx2, ngroups / TILE_GROUPS_MAX);
-        gps2 = round_up(ceil_div(ngroups, s2), TILE_GROUPS_MAX);
+        // the candidate pass reads groups straight from global memory, so its splits can be
+        // as small as 8 groups (32 points): small query counts still fill the GPU
+        const int s2 = choose_splits(h, gx2, ngroups / 8);
+        gps2 = round_up(ceil_div(ngroups, s2), 8);
         nsplit2 = (int)ceil_div(ngroups, gps2);
     }
     h->last_splits = nsplit;
@@ -699,8 +701,6 @@ constexpr size_t LOC_SMALL_BYTES = LOC_BUCKETS * sizeof(int2) + 2 * LOC_KNOTS * 
                                    3 * LOC_KNOTS * sizeof(float) + sizeof(LocMeta);
 
 lip_status local_supported(const lip_model* h) {
-    if (h->esize != 4)
-        return fail(LIP_ERR_UNSUPPORTED, "local Lipschitz constants need float data (LIP_FP32 or LIP_TC_TF32 handles)");
     if (h->C > 0)
         return fail(LIP_ERR_UNSUPPORTED, "local Lipschitz constants use the symmetric distance; the handle has "
                                          "monotone coordinates");
@@ -727,8 +727,9 @@ lip_status local_buffers(lip_model* h, int64_t S, LocalParams& P) {
     }
     char* b = static_cast<char*>(h->loc_buf.p);
     P = LocalParams{};
-    P.X0 = static_cast<const float*>(h->X0);
-    P.y0 = static_cast<const float*>(h->y0);
+    P.X0 = h->X0;
+    P.y0 = h->y0;
+    P.es = h->esize;
     P.N = N;
     P.npad = npad;
     P.d = h->d;
@@ -794,7 +795,6 @@ struct SmoothRun {
 lip_status smooth_check(const lip_model* h, double M, double p) {
     if (!(M >= 0.0) || !std::isfinite(M)) return fail(LIP_ERR_ARG, "M = %g must be finite and >= 0", M);
     if (!(p > 0.0) || !std::isfinite(p)) return fail(LIP_ERR_ARG, "p = %g must be finite and > 0", p);
-    if (h->esize != 4) return fail(LIP_ERR_UNSUPPORTED, "smoothing needs float data (LIP_FP32 or LIP_TC_TF32 handles)");
     if (h->N < 1) return fail(LIP_ERR_ARG, "the handle holds no data");
     return LIP_OK;
 }
@@ -804,8 +804,9 @@ lip_status smooth_setup(lip_model* h, double M, double p, cudaStream_t st, Smoot
     r.h = h;
     r.st = st;
     SmoothParams& P = r.P;
-    P.X0 = static_cast<const float*>(h->X0);
-    P.y0 = static_cast<const float*>(h->y0);
+    P.X0 = h->X0;
+    P.y0 = h->y0;
+    P.es = h->esize;
     P.N = h->N;
     const int64_t tile = smooth_tile();
     P.npad = round_up(h->N, tile);
@@ -987,7 +988,8 @@ lip_status lip_smooth(lip_handle h, double M, double p, int32_t max_iter, int32_
     LIP_TRY(smooth_lbfgs(r, max_iter, history, gtol, &f, &iters, &evals, &x));
     if (eps_out) CUDA_TRY(cudaMemcpyAsync(eps_out, x, (size_t)h->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     // y <- y + eps, M <- the smoothing constant, and the scan layout rebuilt for both
-    CUDA_TRY(launch_apply_eps(static_cast<float*>(h->y0), x, h->N, st));
+    CUDA_TRY(launch_apply_eps(h->y0, h->esize, x, h->N, st));
+    h->s32_dirty = true;
     h->M = M;
     HotParams hp;
     fill_hot_params(h, hp, 0, h->N);
@@ -1078,7 +1080,8 @@ lip_status lip_eval_local_k(lip_handle h, const void* Q, int64_t nq, int32_t k, 
     const int nsplit = (int)ceil_div(P.npad, pps);
     LIP_TRY(h->partial.ensure((size_t)nsplit * nq * 2 * K * 8, "k-neighbour scratch"));
     LocalScanParams S{};
-    S.Q = static_cast<const float*>(Q);
+    S.Q = Q;
+    S.es = h->esize;
     S.nq = nq;
     S.d = h->d;
     S.dp = P.dp;
@@ -1094,6 +1097,7 @@ lip_status lip_eval_local_k(lip_handle h, const void* Q, int64_t nq, int32_t k, 
     S.partial = h->partial.p;
     LocalMergeParams Mp{};
     Mp.Q = S.Q;
+    Mp.es = h->esize;
     Mp.nq = nq;
     Mp.d = h->d;
     Mp.norm = h->norm;
@@ -1107,9 +1111,9 @@ lip_status lip_eval_local_k(lip_handle h, const void* Q, int64_t nq, int32_t k, 
     Mp.mt64 = P.mt64;
     Mp.T64 = P.T64;
     Mp.partial = h->partial.p;
-    Mp.g = static_cast<float*>(g);
-    Mp.lo = static_cast<float*>(lo);
-    Mp.hi = static_cast<float*>(hi);
+    Mp.g = g;
+    Mp.lo = lo;
+    Mp.hi = hi;
     Mp.idx_up = idx_up;
     Mp.idx_lo = idx_lo;
     LocalTopkWeights W{};
@@ -1140,7 +1144,8 @@ lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void
     h->last_splits = nsplit;
     LIP_TRY(h->partial.ensure((size_t)nsplit * nq * sizeof(PartialRec<float>), "scan scratch"));
     LocalScanParams S{};
-    S.Q = static_cast<const float*>(Q);
+    S.Q = Q;
+    S.es = h->esize;
     S.nq = nq;
     S.d = h->d;
     S.dp = P.dp;
@@ -1156,6 +1161,7 @@ lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void
     S.partial = h->partial.p;
     LocalMergeParams Mp{};
     Mp.Q = S.Q;
+    Mp.es = h->esize;
     Mp.nq = nq;
     Mp.d = h->d;
     Mp.norm = h->norm;
@@ -1169,9 +1175,9 @@ lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void
     Mp.mt64 = P.mt64;
     Mp.T64 = P.T64;
     Mp.partial = h->partial.p;
-    Mp.g = static_cast<float*>(g);
-    Mp.lo = static_cast<float*>(lo);
-    Mp.hi = static_cast<float*>(hi);
+    Mp.g = g;
+    Mp.lo = lo;
+    Mp.hi = hi;
     Mp.idx_up = idx_up;
     Mp.idx_lo = idx_lo;
     if (h->ev_scan0) CUDA_TRY(cudaEventRecord(h->ev_scan0, st));

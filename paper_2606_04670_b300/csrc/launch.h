@@ -141,8 +141,9 @@ struct LocMeta {
 };
 
 struct LocalParams {
-    const float* X0;                 // caller's data [N][d]
-    const float* y0;
+    const void* X0;                  // caller's data [N][d], float or double (es bytes)
+    const void* y0;
+    int es;
     int64_t N, npad;
     int d, dp, pr, norm, m;          // dp: d rounded up to 4; m: knots requested or given
     double w[D_MAX];
@@ -164,7 +165,8 @@ struct LocalParams {
 };
 
 struct LocalScanParams {
-    const float* Q;
+    const void* Q;                   // float or double (es bytes)
+    int es;
     int64_t nq;
     int d, dp;
     double w[D_MAX];
@@ -179,18 +181,19 @@ struct LocalScanParams {
 };
 
 struct LocalMergeParams {
-    const float* Q;
+    const void* Q;                   // float or double (es bytes), as X0, y0 and the outputs
+    int es;
     int64_t nq;
     int d, norm, m, nsplit;
     double w[D_MAX];
-    const float* X0;
-    const float* y0;
+    const void* X0;
+    const void* y0;
     const double* d1;
     const double* F;
     const double* mt64;
     const double* T64;
     const void* partial;
-    float *g, *lo, *hi;
+    void *g, *lo, *hi;
     int32_t *idx_up, *idx_lo;
 };
 
@@ -215,8 +218,9 @@ cudaError_t launch_local_eval(int norm, const LocalScanParams& S, int gx, int ns
 // ------------------------------------------------ penalty smoothing (Sec. 4.4)
 
 struct SmoothParams {
-    const float* X0;                 // caller's data [N][d]
-    const float* y0;
+    const void* X0;                  // caller's data [N][d], float or double (es bytes)
+    const void* y0;
+    int es;
     int64_t N, npad;
     int d, dp, C, norm;              // dp: d rounded up to 4; C: constrained coordinates (first)
     int perm[D_MAX];
@@ -237,6 +241,6 @@ cudaError_t launch_vec_reduce(const double* a, const double* b, int64_t n, int o
                               cudaStream_t st);
 cudaError_t launch_vec_axpy(double* out, const double* a, double alpha, const double* b, int64_t n, cudaStream_t st);
 cudaError_t launch_vec_scale(double* out, const double* a, double alpha, int64_t n, cudaStream_t st);
-cudaError_t launch_apply_eps(float* y0, const double* eps, int64_t n, cudaStream_t st);
+cudaError_t launch_apply_eps(void* y0, int es, const double* eps, int64_t n, cudaStream_t st);
 
 }  // namespace lip

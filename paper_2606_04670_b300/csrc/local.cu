@@ -49,11 +49,23 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t c) {
     return z ^ (z >> 31);
 }
 
-// Exact symmetric distance: every step one IEEE double operation, in coordinate order.
-__device__ __forceinline__ double loc_dist64(const float* a, const float* b, int d, int norm, const double* w) {
+// Element i of a float (es = 4) or double (es = 8) array, as a double.
+__device__ __forceinline__ double ldv(const void* p, int es, int64_t i) {
+    return es == 8 ? static_cast<const double*>(p)[i] : (double)static_cast<const float*>(p)[i];
+}
+
+__device__ __forceinline__ void stv(void* p, int es, int64_t i, double v) {
+    if (es == 8) static_cast<double*>(p)[i] = v;
+    else static_cast<float*>(p)[i] = (float)v;
+}
+
+// Exact symmetric distance between rows starting at elements a0 of A and b0 of B: every
+// step one IEEE double operation, in coordinate order.
+__device__ __forceinline__ double loc_dist64(const void* A, int64_t a0, const void* B, int64_t b0, int es, int d,
+                                             int norm, const double* w) {
     double acc = 0.0;
     for (int i = 0; i < d; ++i) {
-        const double v = __dmul_rn(fabs(__dsub_rn((double)a[i], (double)b[i])), w[i]);
+        const double v = __dmul_rn(fabs(__dsub_rn(ldv(A, es, a0 + i), ldv(B, es, b0 + i))), w[i]);
         if (norm == LIP_L1) acc = __dadd_rn(acc, v);
         else if (norm == LIP_L2) acc = __dadd_rn(acc, __dmul_rn(v, v));
         else if (v > acc) acc = v;
@@ -101,13 +113,12 @@ __global__ void loc_layout_kernel(const LocalParams P) {
     float* r = P.rec + k * P.pr;
     float amax = 0.f;
     if (k < P.N) {
-        const float* x = P.X0 + k * P.d;
         for (int i = 0; i < P.dp; ++i) {
-            const float v = i < P.d ? (float)(P.w[i] * (double)x[i]) : 0.f;
+            const float v = i < P.d ? (float)(P.w[i] * ldv(P.X0, P.es, k * P.d + i)) : 0.f;
             r[i] = v;
             amax = fmaxf(amax, fabsf(v));
         }
-        r[P.dp] = P.y0[k];
+        r[P.dp] = (float)ldv(P.y0, P.es, k);
     } else {
         for (int i = 0; i < P.dp; ++i) r[i] = 0.f;
         r[P.dp] = __int_as_float(0x7fc00000);         // padding: y = NaN is never selected
@@ -127,7 +138,7 @@ __global__ void loc_sample_kernel(const LocalParams P) {
     if (s >= P.S) return;
     const uint64_t a = splitmix64(P.seed, 2 * (uint64_t)s) % (uint64_t)P.N;
     const uint64_t b = splitmix64(P.seed, 2 * (uint64_t)s + 1) % (uint64_t)P.N;
-    const double dd = loc_dist64(P.X0 + a * P.d, P.X0 + b * P.d, P.d, P.norm, P.w);
+    const double dd = loc_dist64(P.X0, (int64_t)a * P.d, P.X0, (int64_t)b * P.d, P.es, P.d, P.norm, P.w);
     P.sample[s] = dd;
     if (dd > 0.0) atomicAdd(&P.meta->npos, 1);
 }
@@ -202,7 +213,7 @@ __global__ void loc_knots_kernel(const LocalParams P, int sampled) {
 
 // ------------------------------------------------------------------ table, pass 1
 
-template <int NORM, int DP>
+template <int NORM, int DP, bool Y64>
 __global__ void __launch_bounds__(LOC_THREADS) loc_pass1_kernel(const LocalParams P) {
     constexpr int PR = DP + 4;
     extern __shared__ float4 sm4[];
@@ -223,6 +234,8 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass1_kernel(const LocalParam
     const float e_rel = ldexpf((float)(P.d + 2), -22);
     const float e_abs = e_rel * R;
     const float lo_margin = 1.f - ldexpf(1.f, -20);
+    // FP64 data: y rounded to float carries 2^-24 |y|, so |dy32 - dy64| <= 2^-22 (|y_k| + |y_j|)
+    const float ey = ldexpf(1.f, -22);
     float U = INFINITY;
     for (int64_t j0 = 0; j0 < P.N; j0 += LOC_TILE) {
         const int n = (int)lmin(LOC_TILE, P.N - j0);
@@ -240,7 +253,8 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass1_kernel(const LocalParam
                 const float hi = d32 + 2.f * del;
                 U = fminf(U, hi);
                 const int s = knot_count(Tdn, hi);    // the highest segment d64 may fall in
-                const float dy = fabsf(yk - xj[DP]);
+                float dy = fabsf(yk - xj[DP]);
+                if (Y64) dy = fmaxf(dy - ey * (fabsf(yk) + fabsf(xj[DP])), 0.f);
                 const float rlo = dy * rcp_approx(hi) * lo_margin;
                 float* a = A + s * LOC_THREADS + tid;
                 *a = fmaxf(*a, rlo);
@@ -258,7 +272,7 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass1_kernel(const LocalParam
 
 // ------------------------------------------------------------------ table, pass 2
 
-template <int NORM, int DP>
+template <int NORM, int DP, bool Y64>
 __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParams P) {
     constexpr int PR = DP + 4;
     extern __shared__ float4 sm4[];
@@ -289,8 +303,8 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParam
     const float e_abs = e_rel * R;
     const float up_margin = 1.f + ldexpf(1.f, -20);
     const float lo_margin = 1.f - ldexpf(1.f, -20);
-    const float* xk0 = P.X0 + k * P.d;
-    const double yk64 = valid ? (double)P.y0[k] : 0.0;
+    const float ey = ldexpf(1.f, -22);
+    const double yk64 = valid ? ldv(P.y0, P.es, k) : 0.0;
     double d1 = INFINITY, F = 0.0;
     double E[LOC_KNOTS];
     for (int s = 0; s < LOC_KNOTS; ++s) E[s] = 0.0;
@@ -310,14 +324,15 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParam
             bool cand = lo <= U;                      // may be (tied) nearest
             if (!cand) {
                 const int s = knot_count(Tup, lo);    // the lowest segment d64 may fall in
-                const float dy = fabsf(yk - xj[DP]);
+                float dy = fabsf(yk - xj[DP]);
+                if (Y64) dy += ey * (fabsf(yk) + fabsf(xj[DP]));
                 cand = dy * up_margin > Lb[s * LOC_THREADS + tid] * lo * lo_margin;
             }
             if (!cand) continue;
             const int64_t jj = j0 + j;
-            const double d64 = loc_dist64(xk0, P.X0 + jj * P.d, P.d, P.norm, P.w);
+            const double d64 = loc_dist64(P.X0, k * P.d, P.X0, jj * P.d, P.es, P.d, P.norm, P.w);
             if (!(d64 > 0.0)) continue;
-            const double r = __ddiv_rn(fabs(__dsub_rn(yk64, (double)P.y0[jj])), d64);
+            const double r = __ddiv_rn(fabs(__dsub_rn(yk64, ldv(P.y0, P.es, jj))), d64);
             if (d64 < d1) { d1 = d64; F = r; }
             else if (d64 == d1 && r > F) F = r;
             int s = 0;
@@ -395,8 +410,8 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanPa
     const int64_t qa = (int64_t)blockIdx.x * LOC_THREADS * 2 + tid, qb = qa + LOC_THREADS;
 #pragma unroll
     for (int i = 0; i < DP; ++i) {
-        const float a = (qa < P.nq && i < P.d) ? (float)(P.w[i] * (double)P.Q[qa * P.d + i]) : 0.f;
-        const float b = (qb < P.nq && i < P.d) ? (float)(P.w[i] * (double)P.Q[qb * P.d + i]) : 0.f;
+        const float a = (qa < P.nq && i < P.d) ? (float)(P.w[i] * ldv(P.Q, P.es, qa * P.d + i)) : 0.f;
+        const float b = (qb < P.nq && i < P.d) ? (float)(P.w[i] * ldv(P.Q, P.es, qb * P.d + i)) : 0.f;
         q2[i] = make_float2(a, b);
     }
     if (BUCKET) {
@@ -479,7 +494,7 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_topk_scan_kernel(const LocalS
     const int64_t qi = (int64_t)blockIdx.x * LOC_THREADS + tid;
     float q[DP];
 #pragma unroll
-    for (int i = 0; i < DP; ++i) q[i] = (qi < P.nq && i < P.d) ? (float)(P.w[i] * (double)P.Q[qi * P.d + i]) : 0.f;
+    for (int i = 0; i < DP; ++i) q[i] = (qi < P.nq && i < P.d) ? (float)(P.w[i] * ldv(P.Q, P.es, qi * P.d + i)) : 0.f;
     for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.buckets[b];
     if (tid < LOC_KNOTS) Tn[tid] = P.Tf[tid];
     const float scale = P.scale;
@@ -554,9 +569,9 @@ __global__ void loc_topk_merge_kernel(const LocalMergeParams P, int k, int K, Lo
     if (qi >= P.nq) return;
     const float* pv = static_cast<const float*>(P.partial);
     const int* pk = reinterpret_cast<const int*>(pv + (int64_t)P.nsplit * P.nq * 2 * K);
-    const float* q = P.Q + qi * P.d;
+    const int64_t q0 = qi * P.d;
     bool finite = true;
-    for (int i = 0; i < P.d; ++i) finite = finite && isfinite(q[i]);
+    for (int i = 0; i < P.d; ++i) finite = finite && isfinite(ldv(P.Q, P.es, q0 + i));
     double res[2];
     for (int side = 0; side < 2; ++side) {
         float sv[8];
@@ -584,8 +599,8 @@ __global__ void loc_topk_merge_kernel(const LocalMergeParams P, int k, int K, Lo
         for (int e = 0; e < k; ++e) {
             ek[e] = sk[e];
             if (sk[e] < 0) { all = false; ev[e] = 0.0; continue; }
-            const double t = loc_dist64(q, P.X0 + (int64_t)sk[e] * P.d, P.d, P.norm, P.w);
-            const double yy = (double)P.y0[sk[e]], Mt = __dmul_rn(local_M64(P, sk[e], t), t);
+            const double t = loc_dist64(P.Q, q0, P.X0, (int64_t)sk[e] * P.d, P.es, P.d, P.norm, P.w);
+            const double yy = ldv(P.y0, P.es, sk[e]), Mt = __dmul_rn(local_M64(P, sk[e], t), t);
             ev[e] = side == 0 ? __dadd_rn(yy, Mt) : __dsub_rn(yy, Mt);
         }
         for (int a = 1; a < k; ++a)
@@ -603,9 +618,9 @@ __global__ void loc_topk_merge_kernel(const LocalMergeParams P, int k, int K, Lo
         if (out)
             for (int e = 0; e < k; ++e) out[qi * k + e] = all ? ek[e] : -1;
     }
-    if (P.g) P.g[qi] = (float)(0.5 * (res[0] + res[1]));
-    if (P.hi) P.hi[qi] = (float)res[0];
-    if (P.lo) P.lo[qi] = (float)res[1];
+    if (P.g) stv(P.g, P.es, qi, 0.5 * (res[0] + res[1]));
+    if (P.hi) stv(P.hi, P.es, qi, res[0]);
+    if (P.lo) stv(P.lo, P.es, qi, res[1]);
 }
 
 __device__ __forceinline__ double local_M64(const LocalMergeParams& P, int64_t k, double t) {
@@ -626,22 +641,22 @@ __global__ void loc_merge_kernel(const LocalMergeParams P) {
         if (r.iu >= 0 && (iu < 0 || r.vu < bu)) { bu = r.vu; iu = r.iu; }
         if (r.il >= 0 && (il < 0 || r.vl > bl)) { bl = r.vl; il = r.il; }
     }
-    const float* q = P.Q + qi * P.d;
+    const int64_t q0 = qi * P.d;
     bool finite = true;
-    for (int i = 0; i < P.d; ++i) finite = finite && isfinite(q[i]);
+    for (int i = 0; i < P.d; ++i) finite = finite && isfinite(ldv(P.Q, P.es, q0 + i));
     double hi, lo;
     if (!finite || iu < 0 || il < 0) {
         hi = lo = __longlong_as_double(0x7ff8000000000000ll);
         iu = il = -1;
     } else {
-        const double tu = loc_dist64(q, P.X0 + (int64_t)iu * P.d, P.d, P.norm, P.w);
-        const double tl = loc_dist64(q, P.X0 + (int64_t)il * P.d, P.d, P.norm, P.w);
-        hi = __dadd_rn((double)P.y0[iu], __dmul_rn(local_M64(P, iu, tu), tu));
-        lo = __dsub_rn((double)P.y0[il], __dmul_rn(local_M64(P, il, tl), tl));
+        const double tu = loc_dist64(P.Q, q0, P.X0, (int64_t)iu * P.d, P.es, P.d, P.norm, P.w);
+        const double tl = loc_dist64(P.Q, q0, P.X0, (int64_t)il * P.d, P.es, P.d, P.norm, P.w);
+        hi = __dadd_rn(ldv(P.y0, P.es, iu), __dmul_rn(local_M64(P, iu, tu), tu));
+        lo = __dsub_rn(ldv(P.y0, P.es, il), __dmul_rn(local_M64(P, il, tl), tl));
     }
-    if (P.g) P.g[qi] = (float)(0.5 * (hi + lo));
-    if (P.lo) P.lo[qi] = (float)lo;
-    if (P.hi) P.hi[qi] = (float)hi;
+    if (P.g) stv(P.g, P.es, qi, 0.5 * (hi + lo));
+    if (P.lo) stv(P.lo, P.es, qi, lo);
+    if (P.hi) stv(P.hi, P.es, qi, hi);
     if (P.idx_up) P.idx_up[qi] = iu;
     if (P.idx_lo) P.idx_lo[qi] = il;
 }
@@ -676,15 +691,20 @@ cudaError_t launch_local_knots(const LocalParams& P, bool sampled, cudaStream_t 
     return cudaGetLastError();
 }
 
-template <int NORM, int DP>
-static cudaError_t table_shape(const LocalParams& P, cudaStream_t st) {
+template <int NORM, int DP, bool Y64>
+static cudaError_t table_passes(const LocalParams& P, cudaStream_t st) {
     const size_t smem = pass_smem(DP + 4);
     const unsigned blocks = (unsigned)((P.N + LOC_THREADS - 1) / LOC_THREADS);
-    loc_pass1_kernel<NORM, DP><<<blocks, LOC_THREADS, smem, st>>>(P);
+    loc_pass1_kernel<NORM, DP, Y64><<<blocks, LOC_THREADS, smem, st>>>(P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    loc_pass2_kernel<NORM, DP><<<blocks, LOC_THREADS, smem, st>>>(P);
+    loc_pass2_kernel<NORM, DP, Y64><<<blocks, LOC_THREADS, smem, st>>>(P);
     return cudaGetLastError();
+}
+
+template <int NORM, int DP>
+static cudaError_t table_shape(const LocalParams& P, cudaStream_t st) {
+    return P.es == 8 ? table_passes<NORM, DP, true>(P, st) : table_passes<NORM, DP, false>(P, st);
 }
 
 template <int NORM>

@@ -31,9 +31,13 @@ __global__ void smooth_layout_kernel(const SmoothParams P, const double* eps) {
     if (k >= P.npad) return;
     float* r = P.rec + k * (P.dp + 4);
     if (k < P.N) {
-        const float* x = P.X0 + k * P.d;
-        for (int j = 0; j < P.dp; ++j) r[j] = j < P.d ? (float)(P.scale[j] * (double)x[P.perm[j]]) : 0.f;
-        r[P.dp] = (float)((double)P.y0[k] + eps[k]);
+        for (int j = 0; j < P.dp; ++j) {
+            const int64_t i = k * P.d + P.perm[j];
+            const double x = P.es == 8 ? static_cast<const double*>(P.X0)[i] : (double)static_cast<const float*>(P.X0)[i];
+            r[j] = j < P.d ? (float)(P.scale[j] * x) : 0.f;
+        }
+        const double y = P.es == 8 ? static_cast<const double*>(P.y0)[k] : (double)static_cast<const float*>(P.y0)[k];
+        r[P.dp] = (float)(y + eps[k]);
     } else {
         for (int j = 0; j < P.dp; ++j) r[j] = 0.f;
         r[P.dp] = __int_as_float(0x7fc00000);          // padding: NaN terms are never positive
@@ -211,10 +215,12 @@ __global__ void vec_scale_kernel(double* out, const double* a, double alpha, int
         out[i] = alpha * a[i];
 }
 
-// y0 <- y0 + eps (the smoothed values, in the handle's float storage)
-__global__ void apply_eps_kernel(float* y0, const double* eps, int64_t n) {
+// y0 <- y0 + eps (the smoothed values, in the handle's storage type)
+__global__ void apply_eps_kernel(void* y0, int es, const double* eps, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y0[i] = (float)((double)y0[i] + eps[i]);
+    if (i >= n) return;
+    if (es == 8) static_cast<double*>(y0)[i] += eps[i];
+    else static_cast<float*>(y0)[i] = (float)((double)static_cast<float*>(y0)[i] + eps[i]);
 }
 
 template <int NORM, int DP>
@@ -278,8 +284,8 @@ cudaError_t launch_vec_scale(double* out, const double* a, double alpha, int64_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply_eps(float* y0, const double* eps, int64_t n, cudaStream_t st) {
-    apply_eps_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y0, eps, n);
+cudaError_t launch_apply_eps(void* y0, int es, const double* eps, int64_t n, cudaStream_t st) {
+    apply_eps_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y0, es, eps, n);
     return cudaGetLastError();
 }
 

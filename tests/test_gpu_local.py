@@ -115,7 +115,7 @@ def test_explicit_knots_at_pair_distances():
 
 
 def test_edge_cases():
-    from paper_2606_04670_b300.lipfit import LipError, LIP_ERR_STATE, LIP_ERR_UNSUPPORTED, LIP_ERR_ARG
+    from paper_2606_04670_b300.lipfit import LIP_ERR_ARG, LIP_ERR_STATE, LIP_ERR_UNSUPPORTED, LipError
     # a single datum: M_k = 0, the bounds are y
     m = _model(np.array([[0.3, 0.7]], np.float32), np.array([2.5], np.float32), 2)
     assert m.compute_local_lipschitz(8, 100, 1).size == 0
@@ -157,14 +157,32 @@ def test_edge_cases():
         m.compute_local_lipschitz(4, 10, 1)
     assert e.value.status == LIP_ERR_ARG
     m.close()
-    # monotone handles and FP64 handles are not supported
-    for kw in ({"mon": [1, 0]}, {"precision": "fp64"}):
-        Xk = X.astype(np.float64) if kw.get("precision") == "fp64" else X
-        m = _model(Xk, y.astype(Xk.dtype), 2, **kw)
-        with pytest.raises(LipError) as e:
-            m.compute_local_lipschitz(4, 10, 1)
-        assert e.value.status == LIP_ERR_UNSUPPORTED
-        m.close()
+    # monotone handles are not supported
+    m = _model(X, y, 2, mon=[1, 0])
+    with pytest.raises(LipError) as e:
+        m.compute_local_lipschitz(4, 10, 1)
+    assert e.value.status == LIP_ERR_UNSUPPORTED
+    m.close()
+
+
+def test_fp64_handle_local():
+    """FP64 data: knots and table bit-exact against the oracle on the double values, the
+    evaluation in double outputs by validity and the envelope."""
+    p = W.random_problem(280, 1200, 3, 500, norm=2, weighted=True, dtype=np.float64)
+    m = _model(p.X, p.y, 2, w=p.w, precision="fp64")
+    T = m.compute_local_lipschitz(10, 4000, 3)
+    assert np.array_equal(T, O.local_knots(p.X, 10, 4000, 3, 2, w=p.w)[0])
+    tab = _table(m)
+    for a, b in zip(tab, O.local_table(p.X, p.y, T, 2, w=p.w)):
+        assert np.array_equal(a, b)
+    out = m.eval_local(torch.as_tensor(p.Q).cuda())
+    assert out["g"].dtype == torch.float64
+    r = O.evaluate_local(p.X, p.y, p.Q, T, tab, 2, w=p.w, eta=1e-5)
+    tu = O.local_terms(p.X, p.y, p.Q, T, tab, out["idx_up"].cpu().numpy().astype(np.int64), +1, 2, w=p.w)
+    assert np.allclose(out["hi"].cpu().numpy(), tu, rtol=0, atol=1e-12)
+    clear = ~r.amb_up
+    assert np.all(np.abs(out["hi"].cpu().numpy() - r.hi)[clear] <= 1e-5)
+    m.close()
 
 
 def test_tensor_core_handle_uses_local_path():

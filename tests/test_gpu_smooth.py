@@ -112,7 +112,7 @@ def test_two_points_closed_form():
 
 
 def test_consistent_data_unchanged_and_errors():
-    from paper_2606_04670_b300.lipfit import LipError, LIP_ERR_ARG, LIP_ERR_UNSUPPORTED
+    from paper_2606_04670_b300.lipfit import LIP_ERR_ARG, LipError
     p = W.random_problem(450, 300, 3, 1, norm=2)
     m = _model(p)
     f0, g0 = m.smooth_objective(torch.zeros(p.N, dtype=torch.float64, device="cuda"), p.M, 10.0)
@@ -126,10 +126,18 @@ def test_consistent_data_unchanged_and_errors():
             m.smooth_lipschitz(**args)
         assert e.value.status == LIP_ERR_ARG
     m.close()
-    m = _model(W.random_problem(451, 20, 2, 1, dtype=np.float64), precision="fp64")
-    with pytest.raises(LipError) as e:
-        m.smooth_lipschitz(1.0, 10.0)
-    assert e.value.status == LIP_ERR_UNSUPPORTED
+    # FP64 handles smooth too: objective and gradient against the oracle, y + eps kept in FP64
+    q = _noisy(451, 300, 2, 2)
+    q = W.Problem(q.name, q.X.astype(np.float64), q.y.astype(np.float64), q.Q, q.M, 2, None, None)
+    m = _model(q, precision="fp64")
+    eps0 = 0.01 * np.random.default_rng(1).standard_normal(q.N)
+    f, g = m.smooth_objective(torch.as_tensor(eps0).cuda(), q.M, 10.0)
+    fo, go, _, _ = O.smooth_objective(q.X, q.y, eps0, q.M, 10.0, 2)
+    assert np.abs(g.cpu().numpy() - go).max() <= 4.0 * q.N * EPS32 * _scale(q, q.M)
+    eps, f, it, _ = m.smooth_lipschitz(q.M, 10.0)
+    out = m.eval(torch.as_tensor(q.X).cuda())
+    ro = O.evaluate(q.X, q.y + eps.cpu().numpy(), q.X, q.M, 2)
+    assert np.abs(out["hi"].cpu().numpy() - ro.hi).max() <= 1e-10
     m.close()
 
 

@@ -1,20 +1,14 @@
-// C ABI of liblipfit (declared in include/lipfit.h): handles, validation, launch shapes.
-#include <algorithm>
-#include <atomic>
-#include <cmath>
-#include <cstdarg>
-#include <cstdio>
-#include <cstring>
-#include <string>
-#include <vector>
+// C ABI of liblipfit (declared in include/lipfit.h): handles, validation, data, the
+// envelope evaluation in every precision, the estimate, the backward pass, launch shapes
+// and status.  Local constants are in api_local.cu, smoothing in api_smooth.cu.
+#include "model.h"
 
-#include "launch.h"
-
-using namespace lip;
+namespace lip {
 
 namespace {
-
 thread_local std::string g_err;
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
 
 lip_status fail(lip_status s, const char* fmt, ...) {
     char buf[512];
@@ -36,127 +30,18 @@ lip_status cuda_fail(cudaError_t e, const char* what) {
     return fail(LIP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CUDA_TRY(expr)                                              \
-    do {                                                            \
-        cudaError_t e_ = (expr);                                    \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #expr);         \
-    } while (0)
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-#define LIP_TRY(expr)                                               \
-    do {                                                            \
-        lip_status s_ = (expr);                                     \
-        if (s_ != LIP_OK) return s_;                                \
-    } while (0)
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-// Device buffer that only grows; freed with the handle.
-struct Scratch {
-    void* p = nullptr;
-    size_t bytes = 0;
-    lip_status ensure(size_t need, const char* what) {
-        if (need <= bytes) return LIP_OK;
-        if (p) {
-            cudaError_t e = cudaFree(p);   // implicit device synchronisation: no user in flight
-            p = nullptr;
-            bytes = 0;
-            if (e != cudaSuccess) return cuda_fail(e, what);
-        }
-        size_t sz = std::max<size_t>(need, 256);
-        sz = (sz + 255) & ~size_t(255);
-        cudaError_t e = cudaMalloc(&p, sz);
-        if (e != cudaSuccess) { p = nullptr; return cuda_fail(e, what); }
-        bytes = sz;
-        return LIP_OK;
-    }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-};
-
-std::atomic<uint64_t> g_launches{0};
-inline void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
-
-inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
-inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
-
-}  // namespace
-
-namespace lip {
 // Records an error for lip_last_error from other translation units of the library.
 lip_status set_error(lip_status s, const char* msg) { return fail(s, "%s", msg); }
+
+uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+const std::string& last_error_text() { return g_err; }
+
 }  // namespace lip
 
-struct lip_model {
-    int device = 0;
-    int sms = 148;
-    int d = 0, C = 0, norm = LIP_L2, prec = LIP_FP32, esize = 4;
-    double M = 0.0;
-    int8_t mon[D_MAX] = {};
-    double w[D_MAX] = {};
-    int perm[D_MAX] = {};
-    double sgnw[D_MAX] = {};
-    bool exact = false;
-    int dl = 0, nch = 0, aux = 0;
-    int64_t N = 0, cap = 0, cap_pad = 0;
-    void* X0 = nullptr;
-    void* y0 = nullptr;
-    void* hot = nullptr;
-    unsigned* status = nullptr;       // [0]: runtime error bits, [1]: finiteness check
-    ScanKernelInfo kinfo;
-    int occ_blocks = 1;
-    int tile_groups = 32;             // groups per shared-memory tile (8, 16, 32 or 64)
-    int splits = 0;                   // 0 = automatic
-    int last_splits = 0;
-    int variant = 0;
-    Scratch partial, est, bwd, io;
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
-    cudaEvent_t ev_scan0 = nullptr, ev_scan1 = nullptr;   // caller's timing events
-    // tensor-core form (LIP_TC_TF32)
-    // FP64 handles: a float copy of the layout for the FP32 screen of the exact FP64 scan
-    void* hot32 = nullptr;
-    int dl32 = 0, nch32 = 0, aux32 = 0;
-    bool exact32 = false, s32_dirty = true;
-    int fp64_mode = 0;                 // 0: FP32 screen + FP64 candidates; 1: FP64 scan throughout
-    ScanKernelInfo kinfo32;
-    int occ32 = 1;
-    unsigned* s32_max = nullptr;       // [2] largest |scaled coordinate| and |y| (float bits)
-    Scratch s64;                       // float queries and the FP32 pass's partials
-    bool tc = false, tc_dirty = true;
-    bool tc_bf = false;                // BF16 three-piece split instead of TF32
-    int tc_variant = 0;                // 0: 16 epilogue warps, 1: 8
-    int64_t tc_ntiles_cap = 0;
-    char* tc_btiles = nullptr;
-    double* tc_stats = nullptr;        // [D_MAX] sums of the scaled coordinates
-    unsigned* tc_maxbits = nullptr;    // [2] max |x^|, max |y| (float bits)
-    Scratch tc_q, tc_fb;
-    int64_t last_fallback = 0;
-    // local Lipschitz constants (Sec. 4.3), valid until the data change
-    bool loc_valid = false;
-    bool loc_bucket = true;            // the evaluation's bucket lookup applies (else binary search)
-    float loc_scale = 0.f;
-    int loc_m = 0;
-    double loc_T[LOC_KNOTS] = {};
-    Scratch loc_buf, loc_tmp;          // layout and tables; sampled distances and bounds
-    char* loc_small = nullptr;         // knots (FP64, raw, float roundings) and LocMeta
-    // penalty smoothing (Sec. 4.4): pair-pass layout and partials, L-BFGS vectors, scalars
-    Scratch sm_rec, sm_part, sm_vec, sm_small;
-};
-
-namespace {
+namespace lip {
 
 lip_status check_params(int32_t d, double M, const lip_params* p) {
     if (!p) return fail(LIP_ERR_ARG, "params is NULL");
@@ -691,502 +576,9 @@ lip_status eval_device(lip_model* h, const void* Q, int64_t nq, void* g, void* l
     return eval_plain(h, Q, nq, g, lo, hi, iu, il, st);
 }
 
-}  // namespace
-
-// ------------------------------------------------ local Lipschitz constants (Sec. 4.3)
-
-namespace {
-
-constexpr size_t LOC_SMALL_BYTES = LOC_BUCKETS * sizeof(int2) + 2 * LOC_KNOTS * sizeof(double) +
-                                   3 * LOC_KNOTS * sizeof(float) + sizeof(LocMeta);
-
-lip_status local_supported(const lip_model* h) {
-    if (h->C > 0)
-        return fail(LIP_ERR_UNSUPPORTED, "local Lipschitz constants use the symmetric distance; the handle has "
-                                         "monotone coordinates");
-    if (h->N < 1) return fail(LIP_ERR_ARG, "the handle holds no data");
-    return LIP_OK;
-}
-
-// Carves the per-datum buffers and fills P's pointers (sizes for the current N).
-lip_status local_buffers(lip_model* h, int64_t S, LocalParams& P) {
-    const int64_t N = h->N, npad = local_pad(N);
-    const int pr = local_record_floats(h->d);
-    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const size_t b_rec = al((size_t)npad * pr * 4), b_mt = al((size_t)npad * LOC_KNOTS * 4);
-    const size_t b_mt64 = al((size_t)N * LOC_KNOTS * 8), b_vec = al((size_t)N * 8);
-    LIP_TRY(h->loc_buf.ensure(b_rec + b_mt + b_mt64 + 2 * b_vec, "local Lipschitz tables"));
-    const size_t b_s = al((size_t)std::max<int64_t>(S, 1) * 8);
-    LIP_TRY(h->loc_tmp.ensure(b_s + al((size_t)N * 4), "local Lipschitz scratch"));
-    if (!h->loc_small) {
-        cudaError_t e = cudaMalloc(&h->loc_small, LOC_SMALL_BYTES);
-        if (e != cudaSuccess) {
-            h->loc_small = nullptr;
-            return cuda_fail(e, "local Lipschitz knots");
-        }
-    }
-    char* b = static_cast<char*>(h->loc_buf.p);
-    P = LocalParams{};
-    P.X0 = h->X0;
-    P.y0 = h->y0;
-    P.es = h->esize;
-    P.N = N;
-    P.npad = npad;
-    P.d = h->d;
-    P.dp = local_dim_pad(h->d);
-    P.pr = pr;
-    P.norm = h->norm;
-    for (int i = 0; i < D_MAX; ++i) P.w[i] = i < h->d ? h->w[i] : 1.0;
-    P.rec = reinterpret_cast<float*>(b);
-    P.mt = reinterpret_cast<float*>(b + b_rec);
-    P.mt64 = reinterpret_cast<double*>(b + b_rec + b_mt);
-    P.d1 = reinterpret_cast<double*>(b + b_rec + b_mt + b_mt64);
-    P.F = reinterpret_cast<double*>(b + b_rec + b_mt + b_mt64 + b_vec);
-    P.buckets = reinterpret_cast<int2*>(h->loc_small);
-    P.T64 = reinterpret_cast<double*>(P.buckets + LOC_BUCKETS);
-    P.raw = P.T64 + LOC_KNOTS;
-    P.Tf = reinterpret_cast<float*>(P.raw + LOC_KNOTS);
-    P.meta = reinterpret_cast<LocMeta*>(P.Tf + 3 * LOC_KNOTS);
-    P.sample = static_cast<double*>(h->loc_tmp.p);
-    P.ubound = reinterpret_cast<float*>(static_cast<char*>(h->loc_tmp.p) + b_s);
-    P.S = S;
-    return LIP_OK;
-}
-
-// Layout, knots (sampled, or the m given ones), both table passes; synchronises to read
-// the knots back.
-lip_status local_run(lip_model* h, bool sampled, int m, int64_t S, uint64_t seed, const double* knots,
-                     cudaStream_t st) {
-    h->loc_valid = false;
-    LocalParams P;
-    LIP_TRY(local_buffers(h, sampled ? S : 0, P));
-    P.m = m;
-    P.seed = seed;
-    CUDA_TRY(cudaMemsetAsync(P.meta, 0, sizeof(LocMeta), st));
-    if (!sampled && m > 0) CUDA_TRY(cudaMemcpyAsync(P.raw, knots, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(launch_local_layout(P, st));
-    CUDA_TRY(launch_local_knots(P, sampled, st));
-    CUDA_TRY(launch_local_table(P, st));
-    count_launches(4 + (sampled && S > 0 ? 2 : 0));
-    LocMeta meta{};
-    CUDA_TRY(cudaMemcpyAsync(&meta, P.meta, sizeof meta, cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemcpyAsync(h->loc_T, P.T64, sizeof h->loc_T, cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-    h->loc_m = meta.m;
-    h->loc_bucket = meta.bucket_ok != 0;
-    h->loc_scale = meta.scale;
-    h->loc_valid = true;
-    return LIP_OK;
-}
-
-// ------------------------------------------------ penalty smoothing (Sec. 4.4)
-
-struct SmoothRun {
-    lip_model* h;
-    SmoothParams P;
-    int gx;
-    cudaStream_t st;
-    double* out;      // [2]: Phi, S1
-    double* red;      // [1]: reduction result
-    double* bsum;     // [2 * reduce blocks]
-    double* rpart;    // [reduce blocks]
-};
-
-lip_status smooth_check(const lip_model* h, double M, double p) {
-    if (!(M >= 0.0) || !std::isfinite(M)) return fail(LIP_ERR_ARG, "M = %g must be finite and >= 0", M);
-    if (!(p > 0.0) || !std::isfinite(p)) return fail(LIP_ERR_ARG, "p = %g must be finite and > 0", p);
-    if (h->N < 1) return fail(LIP_ERR_ARG, "the handle holds no data");
-    return LIP_OK;
-}
-
-lip_status smooth_setup(lip_model* h, double M, double p, cudaStream_t st, SmoothRun& r) {
-    r = SmoothRun{};
-    r.h = h;
-    r.st = st;
-    SmoothParams& P = r.P;
-    P.X0 = h->X0;
-    P.y0 = h->y0;
-    P.es = h->esize;
-    P.N = h->N;
-    const int64_t tile = smooth_tile();
-    P.npad = round_up(h->N, tile);
-    P.d = h->d;
-    P.dp = (h->d + 3) / 4 * 4;
-    P.C = h->C;
-    P.norm = h->norm;
-    for (int j = 0; j < D_MAX; ++j) {
-        P.perm[j] = h->perm[j];
-        P.scale[j] = M * h->sgnw[j];
-    }
-    P.p = p;
-    r.gx = (int)ceil_div(h->N, (int64_t)smooth_rows_per_block());
-    const int64_t tiles = P.npad / tile;
-    const int64_t want = std::max<int64_t>(1, ceil_div((int64_t)h->sms * 16, r.gx));
-    const int64_t s = std::min<int64_t>(std::min<int64_t>(want, 64), tiles);
-    P.points_per_split = round_up(ceil_div(P.npad, s), tile);
-    P.nsplit = (int)ceil_div(P.npad, P.points_per_split);
-    LIP_TRY(h->sm_rec.ensure((size_t)P.npad * (P.dp + 4) * sizeof(float), "smoothing layout"));
-    LIP_TRY(h->sm_part.ensure((size_t)P.nsplit * h->N * 3 * sizeof(double), "smoothing partials"));
-    const int rb = smooth_reduce_blocks();
-    LIP_TRY(h->sm_small.ensure((size_t)(4 + 3 * rb) * sizeof(double), "smoothing scalars"));
-    P.rec = static_cast<float*>(h->sm_rec.p);
-    P.partial = static_cast<double*>(h->sm_part.p);
-    r.out = static_cast<double*>(h->sm_small.p);
-    r.red = r.out + 2;
-    r.bsum = r.out + 4;
-    r.rpart = r.bsum + 2 * rb;
-    return LIP_OK;
-}
-
-lip_status smooth_eval(SmoothRun& r, const double* eps, double* grad, double* f) {
-    CUDA_TRY(launch_smooth_objective(r.P, eps, grad, r.bsum, r.out, r.gx, r.st));
-    count_launches(4);
-    CUDA_TRY(cudaMemcpyAsync(f, r.out, sizeof(double), cudaMemcpyDeviceToHost, r.st));
-    CUDA_TRY(cudaStreamSynchronize(r.st));
-    return LIP_OK;
-}
-
-// op 0: a'b; op 1: max |a|
-lip_status smooth_reduce(SmoothRun& r, const double* a, const double* b, int op, double* out) {
-    CUDA_TRY(launch_vec_reduce(a, b, r.h->N, op, r.rpart, r.red, r.st));
-    count_launches(2);
-    CUDA_TRY(cudaMemcpyAsync(out, r.red, sizeof(double), cudaMemcpyDeviceToHost, r.st));
-    CUDA_TRY(cudaStreamSynchronize(r.st));
-    return LIP_OK;
-}
-
-lip_status smooth_axpy(SmoothRun& r, double* out, const double* a, double alpha, const double* b) {
-    CUDA_TRY(launch_vec_axpy(out, a, alpha, b, r.h->N, r.st));
-    count_launches(1);
-    return LIP_OK;
-}
-
-lip_status smooth_scale(SmoothRun& r, double* out, const double* a, double alpha) {
-    CUDA_TRY(launch_vec_scale(out, a, alpha, r.h->N, r.st));
-    count_launches(1);
-    return LIP_OK;
-}
-
-// L-BFGS from eps = 0 (Nocedal and Wright, Algorithms 7.4 and 7.5): the two-loop
-// recursion with gamma = s'y / y'y of the newest pair, backtracking from step 1 (halving)
-// to the Armijo condition with c1 = 1e-4, pairs kept when s'y > 1e-12 |s| |y|, a restart
-// from steepest descent if the direction is not a descent one; stops at max |g| <= gtol.
-lip_status smooth_lbfgs(SmoothRun& r, int max_iter, int hist, double gtol, double* f_out, int* iters_out,
-                        int* evals_out, double** x_out) {
-    const int64_t N = r.h->N;
-    LIP_TRY(r.h->sm_vec.ensure((size_t)(6 + 2 * hist) * N * sizeof(double), "smoothing vectors"));
-    double* base = static_cast<double*>(r.h->sm_vec.p);
-    double *x = base, *g = base + N, *dir = base + 2 * N, *xn = base + 3 * N, *gn = base + 4 * N, *q = base + 5 * N;
-    double* S = base + 6 * N;
-    double* Y = S + (size_t)hist * N;
-    std::vector<double> rho(hist), alpha(hist);
-    int nstore = 0, head = 0;
-    CUDA_TRY(cudaMemsetAsync(x, 0, N * sizeof(double), r.st));
-    double f = 0.0;
-    LIP_TRY(smooth_eval(r, x, g, &f));
-    int it = 0, evals = 1;
-    for (; it < max_iter; ++it) {
-        double gmax = 0.0;
-        LIP_TRY(smooth_reduce(r, g, g, 1, &gmax));
-        if (gmax <= gtol) break;
-        LIP_TRY(smooth_scale(r, q, g, 1.0));
-        for (int j = nstore - 1; j >= 0; --j) {
-            const int sl = (head + j) % hist;
-            double t = 0.0;
-            LIP_TRY(smooth_reduce(r, S + (size_t)sl * N, q, 0, &t));
-            alpha[sl] = rho[sl] * t;
-            LIP_TRY(smooth_axpy(r, q, q, -alpha[sl], Y + (size_t)sl * N));
-        }
-        double gamma = 1.0;
-        if (nstore > 0) {
-            const int sl = (head + nstore - 1) % hist;
-            double sy = 0.0, yy = 0.0;
-            LIP_TRY(smooth_reduce(r, S + (size_t)sl * N, Y + (size_t)sl * N, 0, &sy));
-            LIP_TRY(smooth_reduce(r, Y + (size_t)sl * N, Y + (size_t)sl * N, 0, &yy));
-            gamma = sy / yy;
-        }
-        LIP_TRY(smooth_scale(r, q, q, gamma));
-        for (int j = 0; j < nstore; ++j) {
-            const int sl = (head + j) % hist;
-            double t = 0.0;
-            LIP_TRY(smooth_reduce(r, Y + (size_t)sl * N, q, 0, &t));
-            const double beta = rho[sl] * t;
-            LIP_TRY(smooth_axpy(r, q, q, alpha[sl] - beta, S + (size_t)sl * N));
-        }
-        LIP_TRY(smooth_scale(r, dir, q, -1.0));
-        double gd = 0.0;
-        LIP_TRY(smooth_reduce(r, g, dir, 0, &gd));
-        if (!(gd < 0.0)) {
-            LIP_TRY(smooth_scale(r, dir, g, -1.0));
-            LIP_TRY(smooth_reduce(r, g, dir, 0, &gd));
-            nstore = 0;
-        }
-        double a = 1.0, fn = f;
-        bool ok = false;
-        for (int ls = 0; ls < 60; ++ls) {
-            LIP_TRY(smooth_axpy(r, xn, x, a, dir));
-            LIP_TRY(smooth_eval(r, xn, gn, &fn));
-            ++evals;
-            if (fn <= f + 1e-4 * a * gd) { ok = true; break; }
-            a *= 0.5;
-        }
-        if (!ok) break;
-        LIP_TRY(smooth_axpy(r, q, xn, -1.0, x));        // s
-        LIP_TRY(smooth_axpy(r, dir, gn, -1.0, g));      // y
-        double sy = 0.0, ss = 0.0, yy = 0.0;
-        LIP_TRY(smooth_reduce(r, q, dir, 0, &sy));
-        LIP_TRY(smooth_reduce(r, q, q, 0, &ss));
-        LIP_TRY(smooth_reduce(r, dir, dir, 0, &yy));
-        if (sy > 1e-12 * std::sqrt(ss * yy)) {
-            const int sl = nstore < hist ? (head + nstore) % hist : head;
-            CUDA_TRY(cudaMemcpyAsync(S + (size_t)sl * N, q, N * sizeof(double), cudaMemcpyDeviceToDevice, r.st));
-            CUDA_TRY(cudaMemcpyAsync(Y + (size_t)sl * N, dir, N * sizeof(double), cudaMemcpyDeviceToDevice, r.st));
-            rho[sl] = 1.0 / sy;
-            if (nstore < hist) ++nstore;
-            else head = (head + 1) % hist;
-        }
-        std::swap(x, xn);
-        std::swap(g, gn);
-        f = fn;
-    }
-    *f_out = f;
-    *iters_out = it;
-    *evals_out = evals;
-    *x_out = x;
-    return LIP_OK;
-}
-
-}  // namespace
+}  // namespace lip
 
 extern "C" {
-
-lip_status lip_smooth_objective(lip_handle h, double M, double p, const double* eps, double* f_out, double* grad,
-                                void* stream) {
-    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
-    if (!eps || !f_out) return fail(LIP_ERR_ARG, "eps or f_out is NULL");
-    LIP_TRY(smooth_check(h, M, p));
-    DeviceGuard g(h->device);
-    SmoothRun r;
-    LIP_TRY(smooth_setup(h, M, p, static_cast<cudaStream_t>(stream), r));
-    return smooth_eval(r, eps, grad, f_out);
-}
-
-lip_status lip_smooth(lip_handle h, double M, double p, int32_t max_iter, int32_t history, double gtol,
-                      double* eps_out, double* f_out, int32_t* iters_out, int32_t* evals_out, void* stream) {
-    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
-    if (max_iter < 0) return fail(LIP_ERR_ARG, "max_iter = %d < 0", max_iter);
-    if (history < 1 || history > 64) return fail(LIP_ERR_ARG, "history = %d is outside [1, 64]", history);
-    if (!(gtol >= 0.0)) return fail(LIP_ERR_ARG, "gtol = %g must be >= 0", gtol);
-    LIP_TRY(smooth_check(h, M, p));
-    DeviceGuard g(h->device);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    SmoothRun r;
-    LIP_TRY(smooth_setup(h, M, p, st, r));
-    double f = 0.0;
-    int iters = 0, evals = 0;
-    double* x = nullptr;
-    LIP_TRY(smooth_lbfgs(r, max_iter, history, gtol, &f, &iters, &evals, &x));
-    if (eps_out) CUDA_TRY(cudaMemcpyAsync(eps_out, x, (size_t)h->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    // y <- y + eps, M <- the smoothing constant, and the scan layout rebuilt for both
-    CUDA_TRY(launch_apply_eps(h->y0, h->esize, x, h->N, st));
-    h->s32_dirty = true;
-    h->M = M;
-    HotParams hp;
-    fill_hot_params(h, hp, 0, h->N);
-    CUDA_TRY(launch_build_hot(h->esize, hp, st));
-    count_launches(2);
-    CUDA_TRY(cudaStreamSynchronize(st));
-    h->tc_dirty = true;
-    h->loc_valid = false;
-    if (f_out) *f_out = f;
-    if (iters_out) *iters_out = iters;
-    if (evals_out) *evals_out = evals;
-    return LIP_OK;
-}
-
-lip_status lip_local_fit(lip_handle h, int32_t nknots, int64_t sample_pairs, uint64_t seed, void* stream) {
-    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
-    if (nknots < 0 || nknots > LIP_LOCAL_KNOTS_MAX)
-        return fail(LIP_ERR_ARG, "nknots = %d is outside [0, %d]", nknots, LIP_LOCAL_KNOTS_MAX);
-    if (sample_pairs < 0 || sample_pairs > LIP_LOCAL_SAMPLE_MAX)
-        return fail(LIP_ERR_ARG, "sample_pairs = %lld is outside [0, %d]", (long long)sample_pairs, LIP_LOCAL_SAMPLE_MAX);
-    LIP_TRY(local_supported(h));
-    DeviceGuard g(h->device);
-    return local_run(h, true, nknots, sample_pairs, seed, nullptr, static_cast<cudaStream_t>(stream));
-}
-
-lip_status lip_local_fit_knots(lip_handle h, const double* knots, int32_t nknots, void* stream) {
-    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
-    if (nknots < 0 || nknots > LIP_LOCAL_KNOTS_MAX)
-        return fail(LIP_ERR_ARG, "nknots = %d is outside [0, %d]", nknots, LIP_LOCAL_KNOTS_MAX);
-    if (nknots > 0 && !knots) return fail(LIP_ERR_ARG, "knots is NULL");
-    for (int i = 0; i < nknots; ++i) {
-        if (!(knots[i] > 0.0) || !std::isfinite(knots[i]))
-            return fail(LIP_ERR_ARG, "knots[%d] = %g must be finite and > 0", i, knots[i]);
-        if (i > 0 && !(knots[i] > knots[i - 1])) return fail(LIP_ERR_ARG, "knots must increase strictly (index %d)", i);
-    }
-    LIP_TRY(local_supported(h));
-    DeviceGuard g(h->device);
-    return local_run(h, false, nknots, 0, 0, knots, static_cast<cudaStream_t>(stream));
-}
-
-lip_status lip_local_knots(lip_handle h, double* knots, int32_t* nknots) {
-    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
-    if (!h->loc_valid) return fail(LIP_ERR_STATE, "no local Lipschitz table: call lip_local_fit after the last data change");
-    if (nknots) *nknots = h->loc_m;
-    if (knots)
-        for (int i = 0; i < h->loc_m; ++i) knots[i] = h->loc_T[i];
-    return LIP_OK;
-}
-
-lip_status lip_local_table(lip_handle h, double* d1, double* F, double* Mtab, void* stream) {
-    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
-    if (!h->loc_valid) return fail(LIP_ERR_STATE, "no local Lipschitz table: call lip_local_fit after the last data change");
-    DeviceGuard g(h->device);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    LocalParams P;
-    LIP_TRY(local_buffers(h, 0, P));
-    if (d1) CUDA_TRY(cudaMemcpyAsync(d1, P.d1, (size_t)h->N * 8, cudaMemcpyDeviceToDevice, st));
-    if (F) CUDA_TRY(cudaMemcpyAsync(F, P.F, (size_t)h->N * 8, cudaMemcpyDeviceToDevice, st));
-    if (Mtab)
-        CUDA_TRY(cudaMemcpy2DAsync(Mtab, (size_t)(h->loc_m + 1) * 8, P.mt64, (size_t)LOC_KNOTS * 8,
-                                   (size_t)(h->loc_m + 1) * 8, (size_t)h->N, cudaMemcpyDeviceToDevice, st));
-    return LIP_OK;
-}
-
-lip_status lip_eval_local_k(lip_handle h, const void* Q, int64_t nq, int32_t k, const double* wk, void* g, void* lo,
-                            void* hi, int32_t* idx_up, int32_t* idx_lo, void* stream) {
-    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
-    if (nq < 0) return fail(LIP_ERR_ARG, "nq = %lld < 0", (long long)nq);
-    if (k < 1 || k > 8) return fail(LIP_ERR_ARG, "k = %d is outside [1, 8]", k);
-    if (!wk) return fail(LIP_ERR_ARG, "wk is NULL");
-    for (int e = 0; e < k; ++e)
-        if (!(wk[e] >= 0.0) || !std::isfinite(wk[e])) return fail(LIP_ERR_ARG, "wk[%d] = %g must be finite and >= 0", e, wk[e]);
-    if (!h->loc_valid) return fail(LIP_ERR_STATE, "no local Lipschitz table: call lip_local_fit after the last data change");
-    if (nq == 0) return LIP_OK;
-    if (!Q) return fail(LIP_ERR_ARG, "Q is NULL");
-    DeviceGuard gd(h->device);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    LocalParams P;
-    LIP_TRY(local_buffers(h, 0, P));
-    const int K = k <= 2 ? 2 : (k <= 4 ? 4 : 8);
-    const int64_t gx = ceil_div(nq, (int64_t)local_topk_threads());
-    if (gx > 0x7fffffff) return fail(LIP_ERR_ARG, "nq = %lld is too large", (long long)nq);
-    const int64_t tile = local_scan_tile();
-    const int64_t tiles = P.npad / tile;
-    const int64_t want = std::max<int64_t>(1, ceil_div((int64_t)4 * h->sms * 4, gx));
-    const int64_t s = std::min<int64_t>(std::min<int64_t>(want, 64), tiles);
-    const int64_t pps = round_up(ceil_div(P.npad, s), tile);
-    const int nsplit = (int)ceil_div(P.npad, pps);
-    LIP_TRY(h->partial.ensure((size_t)nsplit * nq * 2 * K * 8, "k-neighbour scratch"));
-    LocalScanParams S{};
-    S.Q = Q;
-    S.es = h->esize;
-    S.nq = nq;
-    S.d = h->d;
-    S.dp = P.dp;
-    for (int i = 0; i < D_MAX; ++i) S.w[i] = P.w[i];
-    S.rec = P.rec;
-    S.mt = P.mt;
-    S.Tf = P.Tf;
-    S.buckets = P.buckets;
-    S.scale = h->loc_scale;
-    S.bucket_ok = h->loc_bucket ? 1 : 0;
-    S.npad = P.npad;
-    S.points_per_split = pps;
-    S.partial = h->partial.p;
-    LocalMergeParams Mp{};
-    Mp.Q = S.Q;
-    Mp.es = h->esize;
-    Mp.nq = nq;
-    Mp.d = h->d;
-    Mp.norm = h->norm;
-    Mp.m = h->loc_m;
-    Mp.nsplit = nsplit;
-    for (int i = 0; i < D_MAX; ++i) Mp.w[i] = P.w[i];
-    Mp.X0 = P.X0;
-    Mp.y0 = P.y0;
-    Mp.d1 = P.d1;
-    Mp.F = P.F;
-    Mp.mt64 = P.mt64;
-    Mp.T64 = P.T64;
-    Mp.partial = h->partial.p;
-    Mp.g = g;
-    Mp.lo = lo;
-    Mp.hi = hi;
-    Mp.idx_up = idx_up;
-    Mp.idx_lo = idx_lo;
-    LocalTopkWeights W{};
-    for (int e = 0; e < 8; ++e) W.wk[e] = e < k ? wk[e] : 0.0;
-    CUDA_TRY(launch_local_eval_k(h->norm, k, K, S, (int)gx, nsplit, Mp, W, st));
-    count_launches(2);
-    return LIP_OK;
-}
-
-lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* idx_up,
-                          int32_t* idx_lo, void* stream) {
-    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
-    if (nq < 0) return fail(LIP_ERR_ARG, "nq = %lld < 0", (long long)nq);
-    if (!h->loc_valid) return fail(LIP_ERR_STATE, "no local Lipschitz table: call lip_local_fit after the last data change");
-    if (nq == 0) return LIP_OK;
-    if (!Q) return fail(LIP_ERR_ARG, "Q is NULL");
-    DeviceGuard gd(h->device);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    LocalParams P;
-    LIP_TRY(local_buffers(h, 0, P));
-    const int64_t gx = ceil_div(nq, (int64_t)local_queries_per_block());
-    if (gx > 0x7fffffff) return fail(LIP_ERR_ARG, "nq = %lld is too large", (long long)nq);
-    const int64_t tile = local_scan_tile();
-    const int64_t tiles = P.npad / tile;
-    const int s = choose_splits(h, gx, tiles);
-    const int64_t pps = round_up(ceil_div(P.npad, s), tile);
-    const int nsplit = (int)ceil_div(P.npad, pps);
-    h->last_splits = nsplit;
-    LIP_TRY(h->partial.ensure((size_t)nsplit * nq * sizeof(PartialRec<float>), "scan scratch"));
-    LocalScanParams S{};
-    S.Q = Q;
-    S.es = h->esize;
-    S.nq = nq;
-    S.d = h->d;
-    S.dp = P.dp;
-    for (int i = 0; i < D_MAX; ++i) S.w[i] = P.w[i];
-    S.rec = P.rec;
-    S.mt = P.mt;
-    S.Tf = P.Tf;
-    S.buckets = P.buckets;
-    S.scale = h->loc_scale;
-    S.bucket_ok = h->loc_bucket ? 1 : 0;
-    S.npad = P.npad;
-    S.points_per_split = pps;
-    S.partial = h->partial.p;
-    LocalMergeParams Mp{};
-    Mp.Q = S.Q;
-    Mp.es = h->esize;
-    Mp.nq = nq;
-    Mp.d = h->d;
-    Mp.norm = h->norm;
-    Mp.m = h->loc_m;
-    Mp.nsplit = nsplit;
-    for (int i = 0; i < D_MAX; ++i) Mp.w[i] = P.w[i];
-    Mp.X0 = P.X0;
-    Mp.y0 = P.y0;
-    Mp.d1 = P.d1;
-    Mp.F = P.F;
-    Mp.mt64 = P.mt64;
-    Mp.T64 = P.T64;
-    Mp.partial = h->partial.p;
-    Mp.g = g;
-    Mp.lo = lo;
-    Mp.hi = hi;
-    Mp.idx_up = idx_up;
-    Mp.idx_lo = idx_lo;
-    if (h->ev_scan0) CUDA_TRY(cudaEventRecord(h->ev_scan0, st));
-    CUDA_TRY(launch_local_eval(h->norm, S, (int)gx, nsplit, h->loc_bucket, Mp, st));
-    if (h->ev_scan1) CUDA_TRY(cudaEventRecord(h->ev_scan1, st));
-    count_launches(2);
-    return LIP_OK;
-}
-
 
 lip_status lip_fit(const void* X, const void* y, int64_t N, int32_t d, double M, const lip_params* p, void* stream,
                    lip_handle* out) {
@@ -1642,7 +1034,7 @@ lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, void* ev_af
     return LIP_OK;
 }
 
-uint64_t lip_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+uint64_t lip_kernel_launches(void) { return launches_total(); }
 
 int64_t lip_last_fallback(lip_handle h) { return h ? h->last_fallback : -1; }
 
@@ -1666,11 +1058,12 @@ const char* lip_status_string(lip_status s) {
 
 size_t lip_last_error(char* buf, size_t len) {
     if (buf && len > 0) {
-        const size_t n = std::min(len - 1, g_err.size());
-        std::memcpy(buf, g_err.data(), n);
+        const std::string& e = last_error_text();
+        const size_t n = std::min(len - 1, e.size());
+        std::memcpy(buf, e.data(), n);
         buf[n] = 0;
     }
-    return g_err.size();
+    return last_error_text().size();
 }
 
 size_t lip_last_error_detail(char* buf, size_t len) { return lip_last_error(buf, len); }

@@ -1,0 +1,145 @@
+// Private header of the library's host code: the handle behind lip_handle and the
+// helpers that the C ABI's source files share.  Not part of the interface.
+#pragma once
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+
+namespace lip {
+
+// Records a one-line message for lip_last_error and returns s.
+lip_status fail(lip_status s, const char* fmt, ...);
+// The lip_status (and message) for a failed CUDA call.
+lip_status cuda_fail(cudaError_t e, const char* what);
+// Adds to the count of the library's kernel launches (lip_kernel_launches).
+void count_launches(uint64_t n);
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+#define CUDA_TRY(expr)                                              \
+    do {                                                            \
+        cudaError_t e_ = (expr);                                    \
+        if (e_ != cudaSuccess) return lip::cuda_fail(e_, #expr);    \
+    } while (0)
+
+#define LIP_TRY(expr)                                               \
+    do {                                                            \
+        lip_status s_ = (expr);                                     \
+        if (s_ != LIP_OK) return s_;                                \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Device buffer that only grows; freed with the handle.
+struct Scratch {
+    void* p = nullptr;
+    size_t bytes = 0;
+    lip_status ensure(size_t need, const char* what) {
+        if (need <= bytes) return LIP_OK;
+        if (p) {
+            cudaError_t e = cudaFree(p);   // implicit device synchronisation: no user in flight
+            p = nullptr;
+            bytes = 0;
+            if (e != cudaSuccess) return cuda_fail(e, what);
+        }
+        size_t sz = std::max<size_t>(need, 256);
+        sz = (sz + 255) & ~size_t(255);
+        cudaError_t e = cudaMalloc(&p, sz);
+        if (e != cudaSuccess) { p = nullptr; return cuda_fail(e, what); }
+        bytes = sz;
+        return LIP_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+}  // namespace lip
+
+using namespace lip;
+
+struct lip_model {
+    int device = 0;
+    int sms = 148;
+    int d = 0, C = 0, norm = LIP_L2, prec = LIP_FP32, esize = 4;
+    double M = 0.0;
+    int8_t mon[D_MAX] = {};
+    double w[D_MAX] = {};
+    int perm[D_MAX] = {};
+    double sgnw[D_MAX] = {};
+    bool exact = false;
+    int dl = 0, nch = 0, aux = 0;
+    int64_t N = 0, cap = 0, cap_pad = 0;
+    void* X0 = nullptr;
+    void* y0 = nullptr;
+    void* hot = nullptr;
+    unsigned* status = nullptr;       // [0]: runtime error bits, [1]: finiteness check
+    ScanKernelInfo kinfo;
+    int occ_blocks = 1;
+    int tile_groups = 32;             // groups per shared-memory tile (8, 16, 32 or 64)
+    int splits = 0;                   // 0 = automatic
+    int last_splits = 0;
+    int variant = 0;
+    Scratch partial, est, bwd, io;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+    cudaEvent_t ev_scan0 = nullptr, ev_scan1 = nullptr;   // caller's timing events
+    // tensor-core form (LIP_TC_TF32)
+    // FP64 handles: a float copy of the layout for the FP32 screen of the exact FP64 scan
+    void* hot32 = nullptr;
+    int dl32 = 0, nch32 = 0, aux32 = 0;
+    bool exact32 = false, s32_dirty = true;
+    int fp64_mode = 0;                 // 0: FP32 screen + FP64 candidates; 1: FP64 scan throughout
+    ScanKernelInfo kinfo32;
+    int occ32 = 1;
+    unsigned* s32_max = nullptr;       // [2] largest |scaled coordinate| and |y| (float bits)
+    Scratch s64;                       // float queries and the FP32 pass's partials
+    bool tc = false, tc_dirty = true;
+    bool tc_bf = false;                // BF16 three-piece split instead of TF32
+    int tc_variant = 0;                // 0: 16 epilogue warps, 1: 8
+    int64_t tc_ntiles_cap = 0;
+    char* tc_btiles = nullptr;
+    double* tc_stats = nullptr;        // [D_MAX] sums of the scaled coordinates
+    unsigned* tc_maxbits = nullptr;    // [2] max |x^|, max |y| (float bits)
+    Scratch tc_q, tc_fb;
+    int64_t last_fallback = 0;
+    // local Lipschitz constants (Sec. 4.3), valid until the data change
+    bool loc_valid = false;
+    bool loc_bucket = true;            // the evaluation's bucket lookup applies (else binary search)
+    float loc_scale = 0.f;
+    int loc_m = 0;
+    double loc_T[LOC_KNOTS] = {};
+    Scratch loc_buf, loc_tmp;          // layout and tables; sampled distances and bounds
+    char* loc_small = nullptr;         // knots (FP64, raw, float roundings) and LocMeta
+    // penalty smoothing (Sec. 4.4): pair-pass layout and partials, L-BFGS vectors, scalars
+    Scratch sm_rec, sm_part, sm_vec, sm_small;
+};
+
+namespace lip {
+
+void fill_scan_params(const lip_model* h, ScanParams& P);
+void fill_hot_params(const lip_model* h, HotParams& P, int64_t k0, int64_t k1);
+// Number of N-splits: enough blocks to fill the GPU in nearly whole waves.
+int choose_splits(const lip_model* h, int64_t gx, int64_t tiles);
+
+}  // namespace lip

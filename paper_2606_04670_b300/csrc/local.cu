@@ -22,6 +22,8 @@
 //    2^-22 (d + 2), e_abs = e_rel * R (R the largest scaled coordinate): the coordinates
 //    are scaled and rounded once (2^-24 |w x|), differenced (2^-24 of the difference) and
 //    accumulated ((d + 1) roundings), which the factor 4 over 2^-24 covers with room.
+//    Segment counts come from the evaluation's bucket table of the knots rounded to
+//    nearest, with the argument moved outward by 2^-22 so that they bound the exact count.
 //    Pass 1 gathers, per datum, an upper bound U_k >= d1_k and per-segment lower bounds
 //    Lb_k[s] <= Mtab_k[s].  Pass 2 recomputes in FP64 every pair whose distance may be
 //    within U_k (a nearest-neighbour candidate) or whose ratio may exceed Lb_k at the
@@ -103,6 +105,13 @@ __device__ __forceinline__ float dist32(const float* xk, const float* xj) {
 __device__ __forceinline__ int knot_bucket(float t, float scale) {
     const float u = fminf(t * scale, (float)(LOC_BUCKETS - 1));
     return __float_as_int(__fadd_rz(u, 8388608.0f)) - 0x4B000000;
+}
+
+// #{i : Tn_i < v} for v >= 0 (Tn the knots rounded to nearest float) from the evaluation's
+// bucket table in global memory (read through L1), as the scan computes it.
+__device__ __forceinline__ int knot_count_bk(const int2* bk, float scale, float v) {
+    const int2 e = __ldg(&bk[knot_bucket(v, scale)]);
+    return e.x + (__int_as_float(e.y) < v ? 1 : 0);
 }
 
 // ------------------------------------------------------------------ layout
@@ -219,7 +228,6 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass1_kernel(const LocalParam
     extern __shared__ float4 sm4[];
     float* tile = reinterpret_cast<float*>(sm4);                    // [LOC_TILE][PR]
     float* A = tile + LOC_TILE * PR;                                // [32][LOC_THREADS]
-    float* Tdn = A + LOC_KNOTS * LOC_THREADS;                       // [32]
     const int tid = threadIdx.x;
     const int64_t k = (int64_t)blockIdx.x * LOC_THREADS + tid;
     const bool valid = k < P.N;
@@ -229,11 +237,11 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass1_kernel(const LocalParam
     for (int i = 0; i < DP; ++i) xk[i] = valid ? P.rec[k * PR + i] : 0.f;
     if (valid) yk = P.rec[k * PR + DP];
     for (int s = 0; s < LOC_KNOTS; ++s) A[s * LOC_THREADS + tid] = 0.f;
-    if (tid < LOC_KNOTS) Tdn[tid] = P.Tf[LOC_KNOTS + tid];
     const float R = __uint_as_float(P.meta->rbits);
     const float e_rel = ldexpf((float)(P.d + 2), -22);
     const float e_abs = e_rel * R;
     const float lo_margin = 1.f - ldexpf(1.f, -20);
+    const float scale = P.meta->scale, knot_up = 1.f + ldexpf(1.f, -22);
     // FP64 data: y rounded to float carries 2^-24 |y|, so |dy32 - dy64| <= 2^-22 (|y_k| + |y_j|)
     const float ey = ldexpf(1.f, -22);
     float U = INFINITY;
@@ -247,12 +255,13 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass1_kernel(const LocalParam
         for (int j = 0; j < n; ++j) {
             const float* xj = tile + j * PR;
             float d32 = dist32<NORM, DP>(xk, xj);
-            if (NORM == LIP_L2) d32 = sqrtf(d32);
+            if (NORM == LIP_L2) d32 = sqrt_approx(d32);
             const float del = fmaf(e_rel, d32, e_abs);
             if (d32 > del) {                          // surely a positive distance
                 const float hi = d32 + 2.f * del;
                 U = fminf(U, hi);
-                const int s = knot_count(Tdn, hi);    // the highest segment d64 may fall in
+                // the highest segment d64 may fall in: #{T < hi} <= #{Tn < hi (1 + 2^-22)}
+                const int s = knot_count_bk(P.buckets, scale, hi * knot_up);
                 float dy = fabsf(yk - xj[DP]);
                 if (Y64) dy = fmaxf(dy - ey * (fabsf(yk) + fabsf(xj[DP])), 0.f);
                 const float rlo = dy * rcp_approx(hi) * lo_margin;
@@ -278,7 +287,6 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParam
     extern __shared__ float4 sm4[];
     float* tile = reinterpret_cast<float*>(sm4);                    // [LOC_TILE][PR]
     float* Lb = tile + LOC_TILE * PR;                               // [32][LOC_THREADS]
-    float* Tup = Lb + LOC_KNOTS * LOC_THREADS;                      // [32]
     __shared__ double T64[LOC_KNOTS];
     const int tid = threadIdx.x;
     const int64_t k = (int64_t)blockIdx.x * LOC_THREADS + tid;
@@ -293,10 +301,8 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParam
         U = P.ubound[k];
         for (int s = 0; s < LOC_KNOTS; ++s) Lb[s * LOC_THREADS + tid] = P.mt[k * LOC_KNOTS + s];
     }
-    if (tid < LOC_KNOTS) {
-        Tup[tid] = P.Tf[2 * LOC_KNOTS + tid];
-        T64[tid] = P.T64[tid];
-    }
+    if (tid < LOC_KNOTS) T64[tid] = P.T64[tid];
+    const float scale = P.meta->scale, knot_dn = 1.f - ldexpf(1.f, -22);
     const int m = P.meta->m;
     const float R = __uint_as_float(P.meta->rbits);
     const float e_rel = ldexpf((float)(P.d + 2), -22);
@@ -318,12 +324,13 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParam
         for (int j = 0; j < n; ++j) {
             const float* xj = tile + j * PR;
             float d32 = dist32<NORM, DP>(xk, xj);
-            if (NORM == LIP_L2) d32 = sqrtf(d32);
+            if (NORM == LIP_L2) d32 = sqrt_approx(d32);
             const float del = fmaf(e_rel, d32, e_abs);
             const float lo = d32 - 2.f * del;         // d64 >= lo
             bool cand = lo <= U;                      // may be (tied) nearest
             if (!cand) {
-                const int s = knot_count(Tup, lo);    // the lowest segment d64 may fall in
+                // the lowest segment d64 may fall in: #{Tn < lo (1 - 2^-22)} <= #{T < lo}
+                const int s = knot_count_bk(P.buckets, scale, fmaxf(lo, 0.f) * knot_dn);
                 float dy = fabsf(yk - xj[DP]);
                 if (Y64) dy += ey * (fabsf(yk) + fabsf(xj[DP]));
                 cand = dy * up_margin > Lb[s * LOC_THREADS + tid] * lo * lo_margin;
@@ -661,7 +668,7 @@ __global__ void loc_merge_kernel(const LocalMergeParams P) {
     if (P.idx_lo) P.idx_lo[qi] = il;
 }
 
-size_t pass_smem(int pr) { return ((size_t)LOC_TILE * pr + LOC_KNOTS * LOC_THREADS + LOC_KNOTS) * sizeof(float); }
+size_t pass_smem(int pr) { return ((size_t)LOC_TILE * pr + LOC_KNOTS * LOC_THREADS) * sizeof(float); }
 
 }  // namespace
 

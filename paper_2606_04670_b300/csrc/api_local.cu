@@ -6,7 +6,7 @@
 
 namespace {
 
-constexpr size_t LOC_SMALL_BYTES = LOC_BUCKETS * sizeof(int2) + 2 * LOC_KNOTS * sizeof(double) +
+constexpr size_t LOC_SMALL_BYTES = LOC_BUCKETS * (sizeof(int2) + sizeof(unsigned)) + 2 * LOC_KNOTS * sizeof(double) +
                                    3 * LOC_KNOTS * sizeof(float) + sizeof(LocMeta);
 
 lip_status local_supported(const lip_model* h) {
@@ -52,7 +52,8 @@ lip_status local_buffers(lip_model* h, int64_t S, LocalParams& P) {
     P.d1 = reinterpret_cast<double*>(b + b_rec + b_mt + b_mt64);
     P.F = reinterpret_cast<double*>(b + b_rec + b_mt + b_mt64 + b_vec);
     P.buckets = reinterpret_cast<int2*>(h->loc_small);
-    P.T64 = reinterpret_cast<double*>(P.buckets + LOC_BUCKETS);
+    P.bpack = reinterpret_cast<unsigned*>(P.buckets + LOC_BUCKETS);
+    P.T64 = reinterpret_cast<double*>(P.bpack + LOC_BUCKETS);
     P.raw = P.T64 + LOC_KNOTS;
     P.Tf = reinterpret_cast<float*>(P.raw + LOC_KNOTS);
     P.meta = reinterpret_cast<LocMeta*>(P.Tf + 3 * LOC_KNOTS);
@@ -177,7 +178,7 @@ lip_status lip_eval_local_k(lip_handle h, const void* Q, int64_t nq, int32_t k, 
     S.rec = P.rec;
     S.mt = P.mt;
     S.Tf = P.Tf;
-    S.buckets = P.buckets;
+    S.bpack = P.bpack;
     S.scale = h->loc_scale;
     S.bucket_ok = h->loc_bucket ? 1 : 0;
     S.npad = P.npad;
@@ -241,7 +242,7 @@ lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void
     S.rec = P.rec;
     S.mt = P.mt;
     S.Tf = P.Tf;
-    S.buckets = P.buckets;
+    S.bpack = P.bpack;
     S.scale = h->loc_scale;
     S.bucket_ok = h->loc_bucket ? 1 : 0;
     S.npad = P.npad;

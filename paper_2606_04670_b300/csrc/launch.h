@@ -161,6 +161,8 @@ struct LocalParams {
     double* sample;                  // [S] sampled distances
     float* ubound;                   // [N] pass-1 upper bounds of d1
     int2* buckets;                   // [LOC_BUCKETS]: knots below the bucket, knot inside (bits)
+    unsigned* bpack;                 // [LOC_BUCKETS]: the same in 4 bytes, for the evaluation scans:
+                                     // knot-inside bits with the low 5 bits replaced by the count below
     LocMeta* meta;
 };
 
@@ -173,7 +175,7 @@ struct LocalScanParams {
     const float* rec;
     const float* mt;
     const float* Tf;
-    const int2* buckets;
+    const unsigned* bpack;           // packed bucket table (LocalParams::bpack)
     float scale;
     int bucket_ok;                   // the bucket lookup applies (else binary search)
     int64_t npad, points_per_split;

@@ -99,6 +99,20 @@ __device__ __forceinline__ float dist32(const float* xk, const float* xj) {
     return acc;
 }
 
+// A bucket entry in 4 bytes: the bits of the knot inside the bucket with the low 5 bits
+// replaced by the number of knots below (at most 31).  Read as a float it is the knot moved
+// by less than 32 ulp (2^-18 relative, below the FP32 distance error bound the evaluation's
+// FP64 merge allows for); with no knot inside (+inf) it is a NaN, so the comparison is
+// false.
+__device__ __forceinline__ unsigned pack_bucket(int below, float knot) {
+    return (__float_as_uint(knot) & ~31u) | (unsigned)below;
+}
+
+// #{knots < t} for t in the entry's bucket, from a packed entry.
+__device__ __forceinline__ int packed_count(unsigned e, float t) {
+    return (int)(e & 31u) + (__uint_as_float(e) < t ? 1 : 0);
+}
+
 // Bucket of a non-negative distance for the knot lookup: floor(min(t * scale, NB - 1)),
 // monotone in t (the rounding-toward-zero add to 2^23 is the floor for 0 <= u < 2^23).
 // A NaN t lands in the last bucket.
@@ -180,7 +194,9 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_rank_kernel(const LocalParams
 // Distinct knots (raw is non-decreasing) into T64, padded with +inf, and their float
 // roundings: to nearest (evaluation), down and up (the screen's bounds).  Then the
 // evaluation's bucket table: bucket b holds the number of knots in lower buckets and the
-// knot inside it (+inf if none); bucket_ok is cleared if a bucket holds two knots.
+// knot inside it (+inf if none); bucket_ok is cleared if a bucket holds two knots.  The
+// evaluation scans read a 4-byte copy, pack_bucket, whose random per-lane shared loads
+// conflict about half as often as 8-byte ones.
 __global__ void loc_knots_kernel(const LocalParams P, int sampled) {
     if (blockIdx.x != 0) return;
     if (threadIdx.x == 0) {
@@ -217,6 +233,7 @@ __global__ void loc_knots_kernel(const LocalParams P, int sampled) {
         }
         if (inside > 1) atomicExch(&P.meta->bucket_ok, 0);
         P.buckets[b] = make_int2(below, __float_as_int(first));
+        P.bpack[b] = pack_bucket(below, first);
     }
 }
 
@@ -371,7 +388,7 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParam
 // index whose value equals the extremum bit for bit.
 template <int NORM, int DP, bool BUCKET>
 __device__ __forceinline__ void loc_pair_values(const float2 (&q2)[DP], const float* xj, const float* mtj,
-                                                const int2* bk, const float* Tn, float scale, float2& vu,
+                                                const unsigned* bk, const float* Tn, float scale, float2& vu,
                                                 float2& vl) {
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
@@ -388,9 +405,8 @@ __device__ __forceinline__ void loc_pair_values(const float2 (&q2)[DP], const fl
         const float2 u = mul2(t, make_float2(scale, scale));
         const int b0 = __float_as_int(__fadd_rz(fminf(u.x, (float)(LOC_BUCKETS - 1)), 8388608.0f)) - 0x4B000000;
         const int b1 = __float_as_int(__fadd_rz(fminf(u.y, (float)(LOC_BUCKETS - 1)), 8388608.0f)) - 0x4B000000;
-        const int2 e0 = bk[b0], e1 = bk[b1];
-        s0 = e0.x + (__int_as_float(e0.y) < t.x ? 1 : 0);
-        s1 = e1.x + (__int_as_float(e1.y) < t.y ? 1 : 0);
+        s0 = packed_count(bk[b0], t.x);
+        s1 = packed_count(bk[b1], t.y);
     } else {
         s0 = knot_count(Tn, t.x);
         s1 = knot_count(Tn, t.y);
@@ -407,7 +423,7 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanPa
     constexpr int PR = DP + 4;
     __shared__ float4 rec4[LOC_SCAN_TILE * PR / 4];
     __shared__ float4 mt4[LOC_SCAN_TILE * LOC_KNOTS / 4];
-    __shared__ int2 bk[BUCKET ? LOC_BUCKETS : 1];
+    __shared__ unsigned bk[BUCKET ? LOC_BUCKETS : 1];
     __shared__ float Tn[LOC_KNOTS];
     const float* rec = reinterpret_cast<const float*>(rec4);
     const float* mt = reinterpret_cast<const float*>(mt4);
@@ -422,7 +438,7 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanPa
         q2[i] = make_float2(a, b);
     }
     if (BUCKET) {
-        for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.buckets[b];
+        for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.bpack[b];
     } else if (tid < LOC_KNOTS) {
         Tn[tid] = P.Tf[tid];
     }
@@ -492,7 +508,7 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_topk_scan_kernel(const LocalS
     constexpr int PR = DP + 4;
     __shared__ float4 rec4[LOC_SCAN_TILE * PR / 4];
     __shared__ float4 mt4[LOC_SCAN_TILE * LOC_KNOTS / 4];
-    __shared__ int2 bk[LOC_BUCKETS];
+    __shared__ unsigned bk[LOC_BUCKETS];
     __shared__ float Tn[LOC_KNOTS];
     const float* rec = reinterpret_cast<const float*>(rec4);
     const float* mt = reinterpret_cast<const float*>(mt4);
@@ -502,7 +518,7 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_topk_scan_kernel(const LocalS
     float q[DP];
 #pragma unroll
     for (int i = 0; i < DP; ++i) q[i] = (qi < P.nq && i < P.d) ? (float)(P.w[i] * ldv(P.Q, P.es, qi * P.d + i)) : 0.f;
-    for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.buckets[b];
+    for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.bpack[b];
     if (tid < LOC_KNOTS) Tn[tid] = P.Tf[tid];
     const float scale = P.scale;
     const bool bucket = P.bucket_ok != 0;
@@ -525,8 +541,7 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_topk_scan_kernel(const LocalS
             if (NORM == LIP_L2) t = sqrt_approx(t);
             int s;
             if (bucket) {
-                const int2 e = bk[knot_bucket(t, scale)];
-                s = e.x + (__int_as_float(e.y) < t ? 1 : 0);
+                s = packed_count(bk[knot_bucket(t, scale)], t);
             } else {
                 s = knot_count(Tn, t);
             }

@@ -235,7 +235,9 @@ LIP_API lip_status lip_estimate_M_noalloc(const float* X, const float* y, int64_
  * found by an FP32 screen with a rigorous error bound and FP64 re-computation of every
  * pair the bound cannot rule out.  Handles: any precision without monotone coordinates,
  * else LIP_ERR_UNSUPPORTED (FP64 handles: float or double arrays as for lip_eval).  Adding or clearing data invalidates
- * the table (LIP_ERR_STATE until the next fit).  N^2 work per fit (two passes). */
+ * the table (LIP_ERR_STATE until the next fit).  N^2 work per fit: one screening scan that
+ * lists, per datum, the pairs its running bounds cannot rule out (a second scan for the data
+ * whose list overflows). */
 
 /* Largest number of knots. */
 #define LIP_LOCAL_KNOTS_MAX 31
@@ -266,6 +268,11 @@ LIP_API lip_status lip_local_knots(lip_handle h, double* knots, int32_t* nknots)
  * (d1 = +Inf and F = 0 for a datum without a neighbour at positive distance) and
  * Mtab [N][m + 1], row-major.  Ordered on the stream. */
 LIP_API lip_status lip_local_table(lip_handle h, double* d1, double* F, double* Mtab, void* stream);
+
+/* Statistics of the last table fit (each pointer may be NULL): the number of data whose
+ * candidate list overflowed (their rows took the second scan) and the longest list that
+ * did not.  Diagnostics only.  LIP_ERR_STATE without a current table. */
+LIP_API lip_status lip_local_stats(lip_handle h, int32_t* overflow_rows, int32_t* max_candidates);
 
 /* The envelopes with the local constants.  Arguments, outputs and NaN handling as for
  * lip_eval (element type of the handle, device).  The scan runs in FP32 and picks the winning data; their

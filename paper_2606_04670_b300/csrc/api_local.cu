@@ -6,7 +6,7 @@
 
 namespace {
 
-constexpr size_t LOC_SMALL_BYTES = LOC_BUCKETS * (sizeof(int2) + sizeof(unsigned)) + 2 * LOC_KNOTS * sizeof(double) +
+constexpr size_t LOC_SMALL_BYTES = LOC_BUCKETS * sizeof(unsigned) + 2 * LOC_KNOTS * sizeof(double) +
                                    3 * LOC_KNOTS * sizeof(float) + sizeof(LocMeta);
 
 lip_status local_supported(const lip_model* h) {
@@ -25,8 +25,9 @@ lip_status local_buffers(lip_model* h, int64_t S, LocalParams& P) {
     const size_t b_rec = al((size_t)npad * pr * 4), b_mt = al((size_t)npad * LOC_KNOTS * 4);
     const size_t b_mt64 = al((size_t)N * LOC_KNOTS * 8), b_vec = al((size_t)N * 8);
     LIP_TRY(h->loc_buf.ensure(b_rec + b_mt + b_mt64 + 2 * b_vec, "local Lipschitz tables"));
-    const size_t b_s = al((size_t)std::max<int64_t>(S, 1) * 8);
-    LIP_TRY(h->loc_tmp.ensure(b_s + al((size_t)N * 4), "local Lipschitz scratch"));
+    const size_t b_s = al((size_t)std::max<int64_t>(S, 1) * 8), b_n = al((size_t)N * 4);
+    const size_t b_c = al((size_t)N * local_candidates() * 4);
+    LIP_TRY(h->loc_tmp.ensure(b_s + 3 * b_n + b_c, "local Lipschitz scratch"));
     if (!h->loc_small) {
         cudaError_t e = cudaMalloc(&h->loc_small, LOC_SMALL_BYTES);
         if (e != cudaSuccess) {
@@ -51,14 +52,17 @@ lip_status local_buffers(lip_model* h, int64_t S, LocalParams& P) {
     P.mt64 = reinterpret_cast<double*>(b + b_rec + b_mt);
     P.d1 = reinterpret_cast<double*>(b + b_rec + b_mt + b_mt64);
     P.F = reinterpret_cast<double*>(b + b_rec + b_mt + b_mt64 + b_vec);
-    P.buckets = reinterpret_cast<int2*>(h->loc_small);
-    P.bpack = reinterpret_cast<unsigned*>(P.buckets + LOC_BUCKETS);
+    P.bpack = reinterpret_cast<unsigned*>(h->loc_small);
     P.T64 = reinterpret_cast<double*>(P.bpack + LOC_BUCKETS);
     P.raw = P.T64 + LOC_KNOTS;
     P.Tf = reinterpret_cast<float*>(P.raw + LOC_KNOTS);
     P.meta = reinterpret_cast<LocMeta*>(P.Tf + 3 * LOC_KNOTS);
     P.sample = static_cast<double*>(h->loc_tmp.p);
-    P.ubound = reinterpret_cast<float*>(static_cast<char*>(h->loc_tmp.p) + b_s);
+    char* t = static_cast<char*>(h->loc_tmp.p);
+    P.ubound = reinterpret_cast<float*>(t + b_s);
+    P.over = reinterpret_cast<int*>(t + b_s + b_n);
+    P.ncand = reinterpret_cast<int*>(t + b_s + 2 * b_n);
+    P.cand = reinterpret_cast<int*>(t + b_s + 3 * b_n);
     P.S = S;
     return LIP_OK;
 }
@@ -76,15 +80,20 @@ lip_status local_run(lip_model* h, bool sampled, int m, int64_t S, uint64_t seed
     if (!sampled && m > 0) CUDA_TRY(cudaMemcpyAsync(P.raw, knots, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, st));
     CUDA_TRY(launch_local_layout(P, st));
     CUDA_TRY(launch_local_knots(P, sampled, st));
-    CUDA_TRY(launch_local_table(P, st));
-    count_launches(4 + (sampled && S > 0 ? 2 : 0));
+    // the table kernels' lookup depends on whether a bucket holds two knots
     LocMeta meta{};
+    CUDA_TRY(cudaMemcpyAsync(&meta, P.meta, sizeof meta, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(launch_local_table(P, meta.bucket_ok != 0, st));
+    count_launches(4 + (sampled && S > 0 ? 2 : 0));
     CUDA_TRY(cudaMemcpyAsync(&meta, P.meta, sizeof meta, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(h->loc_T, P.T64, sizeof h->loc_T, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     h->loc_m = meta.m;
     h->loc_bucket = meta.bucket_ok != 0;
     h->loc_scale = meta.scale;
+    h->loc_over = meta.n_over;
+    h->loc_max_cand = meta.max_cand;
     h->loc_valid = true;
     return LIP_OK;
 }
@@ -125,6 +134,14 @@ lip_status lip_local_knots(lip_handle h, double* knots, int32_t* nknots) {
     if (nknots) *nknots = h->loc_m;
     if (knots)
         for (int i = 0; i < h->loc_m; ++i) knots[i] = h->loc_T[i];
+    return LIP_OK;
+}
+
+lip_status lip_local_stats(lip_handle h, int32_t* overflow_rows, int32_t* max_candidates) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (!h->loc_valid) return fail(LIP_ERR_STATE, "no local Lipschitz table: call lip_local_fit after the last data change");
+    if (overflow_rows) *overflow_rows = h->loc_over;
+    if (max_candidates) *max_candidates = h->loc_max_cand;
     return LIP_OK;
 }
 

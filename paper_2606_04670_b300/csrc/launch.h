@@ -137,7 +137,9 @@ struct LocMeta {
     unsigned rbits;                  // largest |scaled coordinate| (float bits)
     int bucket_ok;                   // 1 if no lookup bucket holds two knots
     float scale;                     // lookup buckets per unit distance
-    int pad[3];
+    int n_over;                      // data whose table candidate list overflowed
+    int max_cand;                    // longest candidate list that did not
+    int pad;
 };
 
 struct LocalParams {
@@ -160,9 +162,11 @@ struct LocalParams {
     double* raw;                     // [LOC_KNOTS] quantile picks (or the given knots)
     double* sample;                  // [S] sampled distances
     float* ubound;                   // [N] pass-1 upper bounds of d1
-    int2* buckets;                   // [LOC_BUCKETS]: knots below the bucket, knot inside (bits)
-    unsigned* bpack;                 // [LOC_BUCKETS]: the same in 4 bytes, for the evaluation scans:
-                                     // knot-inside bits with the low 5 bits replaced by the count below
+    unsigned* bpack;                 // [LOC_BUCKETS] bucket table: bits of the knot inside the
+                                     // bucket (+inf if none), low 5 bits replaced by the count below
+    int* cand;                       // [N][local_candidates()] table candidate lists
+    int* ncand;                      // [N] their lengths
+    int* over;                       // [N] data whose list overflowed
     LocMeta* meta;
 };
 
@@ -213,7 +217,8 @@ int local_scan_tile();
 int local_queries_per_block();
 cudaError_t launch_local_layout(const LocalParams& P, cudaStream_t st);
 cudaError_t launch_local_knots(const LocalParams& P, bool sampled, cudaStream_t st);
-cudaError_t launch_local_table(const LocalParams& P, cudaStream_t st);
+int local_candidates();
+cudaError_t launch_local_table(const LocalParams& P, bool bucket_ok, cudaStream_t st);
 cudaError_t launch_local_eval(int norm, const LocalScanParams& S, int gx, int nsplit, bool bucket,
                               const LocalMergeParams& M, cudaStream_t st);
 

@@ -22,13 +22,14 @@
 //    2^-22 (d + 2), e_abs = e_rel * R (R the largest scaled coordinate): the coordinates
 //    are scaled and rounded once (2^-24 |w x|), differenced (2^-24 of the difference) and
 //    accumulated ((d + 1) roundings), which the factor 4 over 2^-24 covers with room.
-//    Segment counts come from the evaluation's bucket table of the knots rounded to
-//    nearest, with the argument moved outward by 2^-22 so that they bound the exact count.
-//    Pass 1 gathers, per datum, an upper bound U_k >= d1_k and per-segment lower bounds
-//    Lb_k[s] <= Mtab_k[s].  Pass 2 recomputes in FP64 every pair whose distance may be
-//    within U_k (a nearest-neighbour candidate) or whose ratio may exceed Lb_k at the
-//    lowest segment its distance may fall in; no other pair can be a nearest neighbour
-//    or attain a table entry, so the table is the exact FP64 one.
+//    Segment counts are bounded from the bucket table (seg_up, seg_dn).  The screen keeps,
+//    per datum, an upper bound U_k >= d1_k and cumulative lower bounds Lb_k[s] <=
+//    Mtab_k[s]; a pair may decide row k only if its distance may be within U_k (a
+//    nearest-neighbour candidate) or its ratio may exceed Lb_k at the lowest segment its
+//    distance may fall in.  Every other pair is ruled out, and those that are not are
+//    recomputed in FP64, so the table is the exact FP64 one.  One scan does both: a pair
+//    that passes the test against the running bounds is listed, and the list is tested
+//    again against the final bounds (loc_table_kernel).
 // The evaluation scan runs in FP32 from the same layout; the winners are re-evaluated in
 // FP64 with the exact table.
 #include "launch.h"
@@ -41,6 +42,8 @@ constexpr int LOC_THREADS = 128;
 constexpr int LOC_TILE = 128;       // data points per shared-memory tile (table passes)
 constexpr int LOC_SCAN_TILE = 64;   // data points per shared-memory tile (evaluation)
 constexpr int LOC_RANK_TILE = 1024;
+constexpr int LOC_CAND = 64;        // table candidates listed per datum (more: the second scan)
+constexpr int LOC_PILOT = 1024;     // strided data that warm the screen's bounds
 
 __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
 
@@ -121,13 +124,6 @@ __device__ __forceinline__ int knot_bucket(float t, float scale) {
     return __float_as_int(__fadd_rz(u, 8388608.0f)) - 0x4B000000;
 }
 
-// #{i : Tn_i < v} for v >= 0 (Tn the knots rounded to nearest float) from the evaluation's
-// bucket table in global memory (read through L1), as the scan computes it.
-__device__ __forceinline__ int knot_count_bk(const int2* bk, float scale, float v) {
-    const int2 e = __ldg(&bk[knot_bucket(v, scale)]);
-    return e.x + (__int_as_float(e.y) < v ? 1 : 0);
-}
-
 // ------------------------------------------------------------------ layout
 
 __global__ void loc_layout_kernel(const LocalParams P) {
@@ -192,11 +188,11 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_rank_kernel(const LocalParams
 }
 
 // Distinct knots (raw is non-decreasing) into T64, padded with +inf, and their float
-// roundings: to nearest (evaluation), down and up (the screen's bounds).  Then the
-// evaluation's bucket table: bucket b holds the number of knots in lower buckets and the
-// knot inside it (+inf if none); bucket_ok is cleared if a bucket holds two knots.  The
-// evaluation scans read a 4-byte copy, pack_bucket, whose random per-lane shared loads
-// conflict about half as often as 8-byte ones.
+// roundings: to nearest (evaluation), down and up (the screen's bounds).  Then the bucket
+// table: bucket b holds the number of knots in lower buckets and the knot inside it (+inf
+// if none), packed in 4 bytes (pack_bucket: random per-lane shared loads of 4-byte entries
+// conflict about half as often as of 8-byte ones); bucket_ok is cleared if a bucket holds
+// two knots.
 __global__ void loc_knots_kernel(const LocalParams P, int sampled) {
     if (blockIdx.x != 0) return;
     if (threadIdx.x == 0) {
@@ -232,19 +228,165 @@ __global__ void loc_knots_kernel(const LocalParams P, int sampled) {
             }
         }
         if (inside > 1) atomicExch(&P.meta->bucket_ok, 0);
-        P.buckets[b] = make_int2(below, __float_as_int(first));
         P.bpack[b] = pack_bucket(below, first);
     }
 }
 
-// ------------------------------------------------------------------ table, pass 1
+// ------------------------------------------------------------------ table
 
-template <int NORM, int DP, bool Y64>
-__global__ void __launch_bounds__(LOC_THREADS) loc_pass1_kernel(const LocalParams P) {
+// Bounds on the segment index #{i : T_i < v} of an FP64 distance known only to lie in
+// [lo, hi], from float data.  With the packed bucket table (no bucket holds two knots):
+//  * up(hi) counts the packed table at v = hi (1 + 2^-22).  Each knot T < hi has its
+//    nearest float Tn <= T (1 + 2^-24) < v, so it lies in a lower bucket (counted) or in
+//    v's bucket, where the packed knot K' <= Tn < v is counted too: up(hi) >= #{T < hi}.
+//  * dn(lo) counts it at v = lo (1 - 2^-17).  A knot counted from a lower bucket has
+//    Tn < v; the knot inside v's bucket is counted when K' < v, and K' >= Tn (1 - 31 2^-23).
+//    Either way T <= Tn (1 + 2^-24) < lo, so dn(lo) <= #{T < lo}.
+// Without it (two knots share a bucket), the binary search over the knots rounded down
+// (for up) and up (for dn) gives the same bounds.
+template <bool BK>
+__device__ __forceinline__ int seg_up(const unsigned* bk, const float* Tdn, float scale, float hi) {
+    if (BK) {
+        const float v = hi * (1.f + 0x1p-22f);
+        return packed_count(bk[knot_bucket(v, scale)], v);
+    }
+    return knot_count(Tdn, hi);
+}
+
+template <bool BK>
+__device__ __forceinline__ int seg_dn(const unsigned* bk, const float* Tup, float scale, float lo) {
+    if (BK) {
+        const float v = fmaxf(lo, 0.f) * (1.f - 0x1p-17f);
+        return packed_count(bk[knot_bucket(v, scale)], v);
+    }
+    return knot_count(Tup, lo);
+}
+
+// The screen's constants: |d32 - d64| <= e_rel d32 + e_abs, and with FP64 data the float y
+// carries 2^-24 |y|, so |dy32 - dy64| <= 2^-22 (|y_k| + |y_j|).
+struct ScreenConsts {
+    float e_rel, e_abs, up_margin, lo_margin, ey;
+};
+
+__device__ __forceinline__ ScreenConsts screen_consts(const LocalParams& P) {
+    ScreenConsts c;
+    c.e_rel = ldexpf((float)(P.d + 2), -22);
+    c.e_abs = c.e_rel * __uint_as_float(P.meta->rbits);
+    c.up_margin = 1.f + ldexpf(1.f, -20);
+    c.lo_margin = 1.f - ldexpf(1.f, -20);
+    c.ey = ldexpf(1.f, -22);
+    return c;
+}
+
+// Whether the pair (k, j) may decide row k's table given U >= d1_k and the cumulative lower
+// bounds Lb[s] <= Mtab_k[s] (stride LOC_THREADS): it may be a (tied) nearest neighbour, or
+// its ratio may exceed Lb at the lowest segment its distance may fall in.
+template <int NORM, int DP, bool Y64, bool BK>
+__device__ __forceinline__ bool table_candidate(const float* xk, float yk, const float* xj, float U, const float* Lb,
+                                                const unsigned* bk, const float* Tup, float scale,
+                                                const ScreenConsts& c) {
+    float d32 = dist32<NORM, DP>(xk, xj);
+    if (NORM == LIP_L2) d32 = sqrt_approx(d32);
+    const float del = fmaf(c.e_rel, d32, c.e_abs);
+    const float lo = d32 - 2.f * del;
+    if (lo <= U) return true;
+    const int s = seg_dn<BK>(bk, Tup, scale, lo);
+    float dy = fabsf(yk - xj[DP]);
+    if (Y64) dy += c.ey * (fabsf(yk) + fabsf(xj[DP]));
+    return dy * c.up_margin > Lb[s * LOC_THREADS] * lo * c.lo_margin;
+}
+
+// Exact FP64 contribution of the pair (k, jj) to row k: nearest distance d1, its ratio F
+// (largest among ties) and the per-segment maxima E.
+struct ExactRow {
+    double d1, F;
+    double E[LOC_KNOTS];
+};
+
+__device__ __forceinline__ void exact_pair(const LocalParams& P, int64_t k, int64_t jj, double yk64, const double* T64,
+                                           int m, ExactRow& r) {
+    const double d64 = loc_dist64(P.X0, k * P.d, P.X0, jj * P.d, P.es, P.d, P.norm, P.w);
+    if (!(d64 > 0.0)) return;
+    const double q = __ddiv_rn(fabs(__dsub_rn(yk64, ldv(P.y0, P.es, jj))), d64);
+    if (d64 < r.d1) { r.d1 = d64; r.F = q; }
+    else if (d64 == r.d1 && q > r.F) r.F = q;
+    int s = 0;
+    while (s < m && T64[s] < d64) ++s;
+    r.E[s] = fmax(r.E[s], q);
+}
+
+template <int PR>
+__device__ __forceinline__ void write_row(const LocalParams& P, int64_t k, int m, const ExactRow& r) {
+    constexpr int DP = PR - 4;
+    P.d1[k] = r.d1;
+    P.F[k] = r.F;
+    P.rec[k * PR + DP + 1] = (float)r.d1;
+    P.rec[k * PR + DP + 2] = (float)r.F;
+    double run = r.F;
+    for (int s = 0; s < LOC_KNOTS; ++s) {
+        if (s <= m) run = fmax(run, r.E[s]);
+        P.mt64[k * LOC_KNOTS + s] = run;
+        P.mt[k * LOC_KNOTS + s] = (float)run;
+    }
+}
+
+// Shared memory of the table kernels: the data tile, the per-thread cumulative lower
+// bounds, the packed bucket table (BK) and the knots rounded down and up.
+size_t table_smem(int pr, bool bk) {
+    return ((size_t)LOC_TILE * pr + (size_t)LOC_KNOTS * LOC_THREADS + (bk ? LOC_BUCKETS : 0) + 2 * LOC_KNOTS) *
+           sizeof(float);
+}
+
+// Running bounds of one datum in the screen: U >= d1_k, and cumulative lower bounds
+// Lb_k[s] <= Mtab_k[s] in shared memory (stride LOC_THREADS), Lb0 = Lb_k[0] in a register.
+// raise() adds a pair known to be at a positive distance in [lo, hi]: U falls to hi, and
+// its ratio lower bound is entered from segment up(hi) on (Lb is non-decreasing, so the
+// loop stops at the first entry already at least as large).
+template <bool Y64, bool BK>
+__device__ __forceinline__ void screen_raise(float* Ak, float& U, float& Lb0, float hi, float dy, float yk, float yj,
+                                             const unsigned* bk, const float* Tdn, float scale,
+                                             const ScreenConsts& c) {
+    U = fminf(U, hi);
+    const float dyl = Y64 ? fmaxf(dy - c.ey * (fabsf(yk) + fabsf(yj)), 0.f) : dy;
+    const float rlo = dyl * rcp_approx(hi) * c.lo_margin;
+    if (rlo <= Lb0) return;                                   // Lb[up(hi)] >= Lb[0]
+    const int su = seg_up<BK>(bk, Tdn, scale, hi);
+    for (int s = su; s < LOC_KNOTS; ++s) {
+        if (Ak[s * LOC_THREADS] >= rlo) break;
+        Ak[s * LOC_THREADS] = rlo;
+    }
+    Lb0 = Ak[0];
+}
+
+// Load rows idx(i), i < n, of the record layout into the shared tile.
+template <int PR, typename Idx>
+__device__ __forceinline__ void load_tile(float4* sm4, const float* rec, int n, Idx idx) {
+    for (int i = threadIdx.x; i < n * PR / 4; i += LOC_THREADS) {
+        const int row = i / (PR / 4), part = i % (PR / 4);
+        sm4[i] = reinterpret_cast<const float4*>(rec + idx(row) * PR)[part];
+    }
+}
+
+// The table's N^2 screen.  A thread owns datum k and keeps the running bounds; a pair that
+// passes the screen's test (table_candidate) against them is appended to k's candidate
+// list.  The running bounds are never tighter than the final ones (U only falls, Lb only
+// rises), so every pair that passes the test against the final bounds is on the list;
+// loc_exact_kernel tests the list again against the final bounds and recomputes the
+// survivors in FP64.  A pair that fails the test cannot raise the bounds (its ratio lower
+// bound is below Lb at its lowest segment), so only candidates update them, and most far
+// pairs are rejected against Lb_k[0] <= Lb_k[s] without a segment lookup.  The bounds are
+// first warmed on a pilot of (up to) 1024 strided data, so that fewer pairs of the main scan
+// pass against early, loose bounds.  Outputs per datum: U, the cumulative Lb, the list
+// length and the list; a list longer than LOC_CAND sends the datum to loc_pass2_kernel.
+template <int NORM, int DP, bool Y64, bool BK>
+__global__ void __launch_bounds__(LOC_THREADS) loc_screen_kernel(const LocalParams P) {
     constexpr int PR = DP + 4;
     extern __shared__ float4 sm4[];
-    float* tile = reinterpret_cast<float*>(sm4);                    // [LOC_TILE][PR]
-    float* A = tile + LOC_TILE * PR;                                // [32][LOC_THREADS]
+    float* tile = reinterpret_cast<float*>(sm4);                                 // [LOC_TILE][PR]
+    float* A = tile + LOC_TILE * PR;                                             // [LOC_KNOTS][LOC_THREADS]
+    unsigned* bk = reinterpret_cast<unsigned*>(A + LOC_KNOTS * LOC_THREADS);     // [LOC_BUCKETS] if BK
+    float* Tdn = reinterpret_cast<float*>(bk + (BK ? LOC_BUCKETS : 0));          // [LOC_KNOTS]
+    float* Tup = Tdn + LOC_KNOTS;                                                // [LOC_KNOTS]
     const int tid = threadIdx.x;
     const int64_t k = (int64_t)blockIdx.x * LOC_THREADS + tid;
     const bool valid = k < P.N;
@@ -253,84 +395,162 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass1_kernel(const LocalParam
 #pragma unroll
     for (int i = 0; i < DP; ++i) xk[i] = valid ? P.rec[k * PR + i] : 0.f;
     if (valid) yk = P.rec[k * PR + DP];
-    for (int s = 0; s < LOC_KNOTS; ++s) A[s * LOC_THREADS + tid] = 0.f;
-    const float R = __uint_as_float(P.meta->rbits);
-    const float e_rel = ldexpf((float)(P.d + 2), -22);
-    const float e_abs = e_rel * R;
-    const float lo_margin = 1.f - ldexpf(1.f, -20);
-    const float scale = P.meta->scale, knot_up = 1.f + ldexpf(1.f, -22);
-    // FP64 data: y rounded to float carries 2^-24 |y|, so |dy32 - dy64| <= 2^-22 (|y_k| + |y_j|)
-    const float ey = ldexpf(1.f, -22);
-    float U = INFINITY;
-    for (int64_t j0 = 0; j0 < P.N; j0 += LOC_TILE) {
-        const int n = (int)lmin(LOC_TILE, P.N - j0);
+    float* Ak = A + tid;
+    for (int s = 0; s < LOC_KNOTS; ++s) Ak[s * LOC_THREADS] = 0.f;
+    if (BK)
+        for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.bpack[b];
+    if (tid < LOC_KNOTS) {
+        Tdn[tid] = P.Tf[LOC_KNOTS + tid];
+        Tup[tid] = P.Tf[2 * LOC_KNOTS + tid];
+    }
+    const float scale = P.meta->scale;
+    const ScreenConsts c = screen_consts(P);
+    const float A0m = c.lo_margin;
+    float U = INFINITY, Lb0 = 0.f;
+    // pilot: bounds only
+    const int64_t pn = P.N >= 8 * LOC_PILOT ? LOC_PILOT : P.N / 8;
+    const int64_t stride = pn > 0 ? P.N / pn : 1;
+    for (int64_t p0 = 0; p0 < pn; p0 += LOC_TILE) {
+        const int n = (int)lmin(LOC_TILE, pn - p0);
         __syncthreads();
-        const float4* src = reinterpret_cast<const float4*>(P.rec + j0 * PR);
-        for (int i = tid; i < n * PR / 4; i += LOC_THREADS) sm4[i] = src[i];
+        load_tile<PR>(sm4, P.rec, n, [&](int row) { return (p0 + row) * stride; });
         __syncthreads();
         if (!valid) continue;
         for (int j = 0; j < n; ++j) {
             const float* xj = tile + j * PR;
             float d32 = dist32<NORM, DP>(xk, xj);
             if (NORM == LIP_L2) d32 = sqrt_approx(d32);
-            const float del = fmaf(e_rel, d32, e_abs);
-            if (d32 > del) {                          // surely a positive distance
-                const float hi = d32 + 2.f * del;
-                U = fminf(U, hi);
-                // the highest segment d64 may fall in: #{T < hi} <= #{Tn < hi (1 + 2^-22)}
-                const int s = knot_count_bk(P.buckets, scale, hi * knot_up);
-                float dy = fabsf(yk - xj[DP]);
-                if (Y64) dy = fmaxf(dy - ey * (fabsf(yk) + fabsf(xj[DP])), 0.f);
-                const float rlo = dy * rcp_approx(hi) * lo_margin;
-                float* a = A + s * LOC_THREADS + tid;
-                *a = fmaxf(*a, rlo);
+            const float del = fmaf(c.e_rel, d32, c.e_abs);
+            if (d32 > del)
+                screen_raise<Y64, BK>(Ak, U, Lb0, d32 + 2.f * del, fabsf(yk - xj[DP]), yk, xj[DP], bk, Tdn, scale, c);
+        }
+    }
+    int* list = P.cand + k * LOC_CAND;
+    int cnt = 0;
+    for (int64_t j0 = 0; j0 < P.N; j0 += LOC_TILE) {
+        const int n = (int)lmin(LOC_TILE, P.N - j0);
+        __syncthreads();
+        load_tile<PR>(sm4, P.rec, n, [&](int row) { return j0 + row; });
+        __syncthreads();
+        if (!valid) continue;
+        for (int j = 0; j < n; ++j) {
+            const float* xj = tile + j * PR;
+            float d32 = dist32<NORM, DP>(xk, xj);
+            if (NORM == LIP_L2) d32 = sqrt_approx(d32);
+            const float del = fmaf(c.e_rel, d32, c.e_abs);
+            const float lo = d32 - 2.f * del;
+            const float yj = xj[DP];
+            const float dy = fabsf(yk - yj);
+            bool cand = lo <= U;                                  // may be (tied) nearest
+            if (!cand) {
+                const float dyu = (Y64 ? dy + c.ey * (fabsf(yk) + fabsf(yj)) : dy) * c.up_margin;
+                const float lom = lo * A0m;
+                if (dyu > Lb0 * lom) {                            // else rejected at segment 0
+                    const int sd = seg_dn<BK>(bk, Tup, scale, lo);
+                    cand = dyu > Ak[sd * LOC_THREADS] * lom;
+                }
+            }
+            if (cand) {
+                if (cnt < LOC_CAND) list[cnt] = (int)(j0 + j);
+                ++cnt;
+                if (d32 > del) screen_raise<Y64, BK>(Ak, U, Lb0, d32 + 2.f * del, dy, yk, yj, bk, Tdn, scale, c);
             }
         }
     }
     if (!valid) return;
     P.ubound[k] = U;
-    float run = 0.f;
-    for (int s = 0; s < LOC_KNOTS; ++s) {
-        run = fmaxf(run, A[s * LOC_THREADS + tid]);
-        P.mt[k * LOC_KNOTS + s] = run;                // Lb_k[s] until pass 2 overwrites it
-    }
+    P.ncand[k] = cnt;
+    for (int s = 0; s < LOC_KNOTS; ++s) P.mt[k * LOC_KNOTS + s] = Ak[s * LOC_THREADS];
+    if (cnt > LOC_CAND) P.over[atomicAdd(&P.meta->n_over, 1)] = (int)k;
+    else atomicMax(&P.meta->max_cand, cnt);
 }
 
-// ------------------------------------------------------------------ table, pass 2
-
-template <int NORM, int DP, bool Y64>
-__global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParams P) {
+// The exact table rows of the data whose lists did not overflow: each listed pair is
+// tested against the final bounds and, if it passes, recomputed in FP64.
+template <int NORM, int DP, bool Y64, bool BK>
+__global__ void __launch_bounds__(LOC_THREADS) loc_exact_kernel(const LocalParams P) {
     constexpr int PR = DP + 4;
-    extern __shared__ float4 sm4[];
-    float* tile = reinterpret_cast<float*>(sm4);                    // [LOC_TILE][PR]
-    float* Lb = tile + LOC_TILE * PR;                               // [32][LOC_THREADS]
+    __shared__ float Lb[LOC_KNOTS * LOC_THREADS];
     __shared__ double T64[LOC_KNOTS];
+    __shared__ float Tup[LOC_KNOTS];
     const int tid = threadIdx.x;
     const int64_t k = (int64_t)blockIdx.x * LOC_THREADS + tid;
-    const bool valid = k < P.N;
+    if (tid < LOC_KNOTS) {
+        T64[tid] = P.T64[tid];
+        Tup[tid] = P.Tf[2 * LOC_KNOTS + tid];
+    }
+    const bool valid = k < P.N && P.ncand[k] <= LOC_CAND;
+    if (valid)
+        for (int s = 0; s < LOC_KNOTS; ++s) Lb[s * LOC_THREADS + tid] = P.mt[k * LOC_KNOTS + s];
+    __syncthreads();
+    if (!valid) return;
     float xk[DP];
-    float yk = 0.f;
+#pragma unroll
+    for (int i = 0; i < DP; ++i) xk[i] = P.rec[k * PR + i];
+    const float yk = P.rec[k * PR + DP], U = P.ubound[k];
+    const float scale = P.meta->scale;
+    const int m = P.meta->m;
+    const ScreenConsts c = screen_consts(P);
+    const double yk64 = ldv(P.y0, P.es, k);
+    const int cnt = P.ncand[k];
+    const int* list = P.cand + k * LOC_CAND;
+    ExactRow r;
+    r.d1 = INFINITY;
+    r.F = 0.0;
+    for (int s = 0; s < LOC_KNOTS; ++s) r.E[s] = 0.0;
+    for (int i = 0; i < cnt; ++i) {
+        const int64_t jj = list[i];
+        float xj[PR];
+#pragma unroll
+        for (int e = 0; e < PR; e += 4) {
+            const float4 v = reinterpret_cast<const float4*>(P.rec + jj * PR)[e / 4];
+            xj[e] = v.x; xj[e + 1] = v.y; xj[e + 2] = v.z; xj[e + 3] = v.w;
+        }
+        if (!table_candidate<NORM, DP, Y64, BK>(xk, yk, xj, U, Lb + tid, P.bpack, Tup, scale, c)) continue;
+        exact_pair(P, k, jj, yk64, T64, m, r);
+    }
+    write_row<PR>(P, k, m, r);
+}
+
+// The exact table of the data whose candidate lists overflowed: a full N^2 scan per datum
+// against its final bounds from loc_table_kernel, FP64 for the pairs that pass.
+template <int NORM, int DP, bool Y64, bool BK>
+__global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParams P) {
+    constexpr int PR = DP + 4;
+    if ((int64_t)blockIdx.x * LOC_THREADS >= P.meta->n_over) return;   // the whole block
+    extern __shared__ float4 sm4[];
+    float* tile = reinterpret_cast<float*>(sm4);
+    float* Lb = tile + LOC_TILE * PR;
+    unsigned* bk = reinterpret_cast<unsigned*>(Lb + LOC_KNOTS * LOC_THREADS);
+    float* Tup = reinterpret_cast<float*>(bk + (BK ? LOC_BUCKETS : 0)) + LOC_KNOTS;
+    __shared__ double T64[LOC_KNOTS];
+    const int tid = threadIdx.x;
+    const int64_t slot = (int64_t)blockIdx.x * LOC_THREADS + tid;
+    const bool valid = slot < P.meta->n_over;
+    const int64_t k = valid ? P.over[slot] : 0;
+    float xk[DP];
+    float yk = 0.f, U = 0.f;
 #pragma unroll
     for (int i = 0; i < DP; ++i) xk[i] = valid ? P.rec[k * PR + i] : 0.f;
-    float U = 0.f;
     if (valid) {
         yk = P.rec[k * PR + DP];
         U = P.ubound[k];
         for (int s = 0; s < LOC_KNOTS; ++s) Lb[s * LOC_THREADS + tid] = P.mt[k * LOC_KNOTS + s];
     }
-    if (tid < LOC_KNOTS) T64[tid] = P.T64[tid];
-    const float scale = P.meta->scale, knot_dn = 1.f - ldexpf(1.f, -22);
+    if (BK)
+        for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.bpack[b];
+    if (tid < LOC_KNOTS) {
+        Tup[tid] = P.Tf[2 * LOC_KNOTS + tid];
+        T64[tid] = P.T64[tid];
+    }
+    const float scale = P.meta->scale;
     const int m = P.meta->m;
-    const float R = __uint_as_float(P.meta->rbits);
-    const float e_rel = ldexpf((float)(P.d + 2), -22);
-    const float e_abs = e_rel * R;
-    const float up_margin = 1.f + ldexpf(1.f, -20);
-    const float lo_margin = 1.f - ldexpf(1.f, -20);
-    const float ey = ldexpf(1.f, -22);
+    const ScreenConsts c = screen_consts(P);
     const double yk64 = valid ? ldv(P.y0, P.es, k) : 0.0;
-    double d1 = INFINITY, F = 0.0;
-    double E[LOC_KNOTS];
-    for (int s = 0; s < LOC_KNOTS; ++s) E[s] = 0.0;
+    ExactRow r;
+    r.d1 = INFINITY;
+    r.F = 0.0;
+    for (int s = 0; s < LOC_KNOTS; ++s) r.E[s] = 0.0;
     for (int64_t j0 = 0; j0 < P.N; j0 += LOC_TILE) {
         const int n = (int)lmin(LOC_TILE, P.N - j0);
         __syncthreads();
@@ -339,42 +559,11 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParam
         __syncthreads();
         if (!valid) continue;
         for (int j = 0; j < n; ++j) {
-            const float* xj = tile + j * PR;
-            float d32 = dist32<NORM, DP>(xk, xj);
-            if (NORM == LIP_L2) d32 = sqrt_approx(d32);
-            const float del = fmaf(e_rel, d32, e_abs);
-            const float lo = d32 - 2.f * del;         // d64 >= lo
-            bool cand = lo <= U;                      // may be (tied) nearest
-            if (!cand) {
-                // the lowest segment d64 may fall in: #{Tn < lo (1 - 2^-22)} <= #{T < lo}
-                const int s = knot_count_bk(P.buckets, scale, fmaxf(lo, 0.f) * knot_dn);
-                float dy = fabsf(yk - xj[DP]);
-                if (Y64) dy += ey * (fabsf(yk) + fabsf(xj[DP]));
-                cand = dy * up_margin > Lb[s * LOC_THREADS + tid] * lo * lo_margin;
-            }
-            if (!cand) continue;
-            const int64_t jj = j0 + j;
-            const double d64 = loc_dist64(P.X0, k * P.d, P.X0, jj * P.d, P.es, P.d, P.norm, P.w);
-            if (!(d64 > 0.0)) continue;
-            const double r = __ddiv_rn(fabs(__dsub_rn(yk64, ldv(P.y0, P.es, jj))), d64);
-            if (d64 < d1) { d1 = d64; F = r; }
-            else if (d64 == d1 && r > F) F = r;
-            int s = 0;
-            while (s < m && T64[s] < d64) ++s;
-            E[s] = fmax(E[s], r);
+            if (!table_candidate<NORM, DP, Y64, BK>(xk, yk, tile + j * PR, U, Lb + tid, bk, Tup, scale, c)) continue;
+            exact_pair(P, k, j0 + j, yk64, T64, m, r);
         }
     }
-    if (!valid) return;
-    P.d1[k] = d1;
-    P.F[k] = F;
-    P.rec[k * PR + DP + 1] = (float)d1;
-    P.rec[k * PR + DP + 2] = (float)F;
-    double run = F;
-    for (int s = 0; s < LOC_KNOTS; ++s) {
-        if (s <= m) run = fmax(run, E[s]);
-        P.mt64[k * LOC_KNOTS + s] = run;
-        P.mt[k * LOC_KNOTS + s] = (float)run;
-    }
+    if (valid) write_row<PR>(P, k, m, r);
 }
 
 // ------------------------------------------------------------------ evaluation
@@ -683,8 +872,6 @@ __global__ void loc_merge_kernel(const LocalMergeParams P) {
     if (P.idx_lo) P.idx_lo[qi] = il;
 }
 
-size_t pass_smem(int pr) { return ((size_t)LOC_TILE * pr + LOC_KNOTS * LOC_THREADS) * sizeof(float); }
-
 }  // namespace
 
 int local_dim_pad(int d) { return (d + 3) / 4 * 4; }
@@ -713,36 +900,42 @@ cudaError_t launch_local_knots(const LocalParams& P, bool sampled, cudaStream_t 
     return cudaGetLastError();
 }
 
-template <int NORM, int DP, bool Y64>
-static cudaError_t table_passes(const LocalParams& P, cudaStream_t st) {
-    const size_t smem = pass_smem(DP + 4);
+template <int NORM, int DP, bool Y64, bool BK>
+static cudaError_t table_run(const LocalParams& P, cudaStream_t st) {
+    const size_t smem = table_smem(DP + 4, BK);
     const unsigned blocks = (unsigned)((P.N + LOC_THREADS - 1) / LOC_THREADS);
-    loc_pass1_kernel<NORM, DP, Y64><<<blocks, LOC_THREADS, smem, st>>>(P);
+    loc_screen_kernel<NORM, DP, Y64, BK><<<blocks, LOC_THREADS, smem, st>>>(P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    loc_pass2_kernel<NORM, DP, Y64><<<blocks, LOC_THREADS, smem, st>>>(P);
+    loc_exact_kernel<NORM, DP, Y64, BK><<<blocks, LOC_THREADS, 0, st>>>(P);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    loc_pass2_kernel<NORM, DP, Y64, BK><<<blocks, LOC_THREADS, smem, st>>>(P);
     return cudaGetLastError();
 }
 
 template <int NORM, int DP>
-static cudaError_t table_shape(const LocalParams& P, cudaStream_t st) {
-    return P.es == 8 ? table_passes<NORM, DP, true>(P, st) : table_passes<NORM, DP, false>(P, st);
+static cudaError_t table_shape(const LocalParams& P, bool bk, cudaStream_t st) {
+    if (P.es == 8) return bk ? table_run<NORM, DP, true, true>(P, st) : table_run<NORM, DP, true, false>(P, st);
+    return bk ? table_run<NORM, DP, false, true>(P, st) : table_run<NORM, DP, false, false>(P, st);
 }
 
 template <int NORM>
-static cudaError_t table_norm(const LocalParams& P, cudaStream_t st) {
+static cudaError_t table_norm(const LocalParams& P, bool bk, cudaStream_t st) {
     switch (P.dp) {
-        case 4: return table_shape<NORM, 4>(P, st);
-        case 8: return table_shape<NORM, 8>(P, st);
-        case 12: return table_shape<NORM, 12>(P, st);
-        default: return table_shape<NORM, 16>(P, st);
+        case 4: return table_shape<NORM, 4>(P, bk, st);
+        case 8: return table_shape<NORM, 8>(P, bk, st);
+        case 12: return table_shape<NORM, 12>(P, bk, st);
+        default: return table_shape<NORM, 16>(P, bk, st);
     }
 }
 
-cudaError_t launch_local_table(const LocalParams& P, cudaStream_t st) {
-    if (P.norm == LIP_L1) return table_norm<LIP_L1>(P, st);
-    if (P.norm == LIP_L2) return table_norm<LIP_L2>(P, st);
-    return table_norm<LIP_LINF>(P, st);
+int local_candidates() { return LOC_CAND; }
+
+cudaError_t launch_local_table(const LocalParams& P, bool bucket_ok, cudaStream_t st) {
+    if (P.norm == LIP_L1) return table_norm<LIP_L1>(P, bucket_ok, st);
+    if (P.norm == LIP_L2) return table_norm<LIP_L2>(P, bucket_ok, st);
+    return table_norm<LIP_LINF>(P, bucket_ok, st);
 }
 
 template <int NORM, int DP>

@@ -127,6 +127,7 @@ struct lip_model {
     bool loc_valid = false;
     bool loc_bucket = true;            // the evaluation's bucket lookup applies (else binary search)
     float loc_scale = 0.f;
+    int32_t loc_over = 0, loc_max_cand = 0;   // statistics of the last table fit
     int loc_m = 0;
     double loc_T[LOC_KNOTS] = {};
     Scratch loc_buf, loc_tmp;          // layout and tables; sampled distances and bounds

@@ -97,6 +97,7 @@ def _load():
         "lip_local_fit_knots": [H, P, i32, P],
         "lip_local_knots": [H, P, P],
         "lip_local_table": [H, P, P, P, P],
+        "lip_local_stats": [H, P, P],
         "lip_eval_local": [H, P, i64, P, P, P, P, P, P],
         "lip_eval_local_k": [H, P, i64, i32, P, P, P, P, P, P, P],
         "lip_smooth_objective": [H, f64, f64, P, ctypes.POINTER(f64), P, P],
@@ -227,6 +228,12 @@ def lip_local_knots(h):
 
 def lip_local_table(h, d1, F, Mtab, stream=0):
     return _lib.lip_local_table(h, d1, F, Mtab, stream)
+
+
+def lip_local_stats(h):
+    over, mc = ctypes.c_int32(), ctypes.c_int32()
+    s = _lib.lip_local_stats(h, ctypes.byref(over), ctypes.byref(mc))
+    return s, over.value, mc.value
 
 
 def lip_eval_local(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream=0):
@@ -492,6 +499,12 @@ class LipFit:
         s, k = lip_local_knots(self.h)
         _check(s, "lip_local_knots")
         return np.array(k, np.float64)
+
+    def local_stats(self):
+        """(overflow rows, longest candidate list) of the last table fit."""
+        s, over, mc = lip_local_stats(self.h)
+        _check(s, "lip_local_stats")
+        return over, mc
 
     def local_table(self):
         """(d1 [N], F [N], Mtab [N, m+1]) as float64 CUDA tensors."""

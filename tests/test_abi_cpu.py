@@ -134,6 +134,7 @@ def test_local_lipschitz_argument_errors():
     assert L.lip_local_fit_knots(None, kn.ctypes.data, 2) == L.LIP_ERR_ARG
     assert L.lip_local_knots(None)[0] == L.LIP_ERR_ARG
     assert L.lip_local_table(None, None, None, None) == L.LIP_ERR_ARG
+    assert L.lip_local_stats(None)[0] == L.LIP_ERR_ARG
     assert L.lip_eval_local(None, None, 1, None, None, None, None, None) == L.LIP_ERR_ARG
     assert L.LIP_LOCAL_KNOTS_MAX == 31 and L.LIP_LOCAL_SAMPLE_MAX == 1 << 20
     assert L.status_string(L.LIP_ERR_STATE) == "call out of order"

@@ -242,6 +242,43 @@ def test_full_size_local_d4_sampled():
     m.close()
 
 
+def test_two_knots_in_one_bucket_table_segments():
+    """Knots 0.5 and 0.50002 share a lookup bucket (width 1/2048 with the last knot at 1).
+    Datum 0's pair at distance 0.50003 lies beyond both; its ratio (6) must not bound
+    segment 1, which holds only the pair at 0.50001 (ratio 2): Mtab_0 = [F, 2, 6, 6]."""
+    X = np.array([[0.0], [0.2], [0.50001], [0.50003]], np.float32)
+    y = np.array([0.0, 0.01, 1.0, 3.0], np.float32)
+    T = np.array([0.5, 0.50002, 1.0])
+    m = _model(X, y, 2)
+    assert np.array_equal(m.compute_local_lipschitz(knots=T), T)
+    d1, F, Mtab = _table(m)
+    od1, oF, oM = O.local_table(_f64(X), _f64(y), T, 2)
+    assert np.array_equal(d1, od1) and np.array_equal(F, oF)
+    assert np.array_equal(Mtab, oM), (Mtab[0], oM[0])
+    assert oM[0, 1] > oF[0] and oM[0, 2] > oM[0, 1]
+    m.close()
+
+
+def test_candidate_list_overflow_rows():
+    """150 copies of each of two points after 500 random ones: the copies' rows list every
+    duplicate (distance 0 passes the nearest-neighbour test), overflow the candidate list and
+    take the second scan; the table is still exact."""
+    r = np.random.default_rng(7)
+    X = np.concatenate([r.random((500, 3)), np.tile([[0.25, 0.5, 0.75]], (150, 1)),
+                        np.tile([[0.6, 0.1, 0.3]], (150, 1))]).astype(np.float32)
+    y = (np.sin(3 * X[:, 0]) + X[:, 1] * X[:, 2]).astype(np.float32)
+    for norm in (1, 2, 3):
+        m = _model(X, y, norm)
+        T = m.compute_local_lipschitz(12, 4096, 5)
+        over, longest = m.local_stats()
+        assert 300 <= over < 800, over
+        assert 0 < longest <= 64
+        d1, F, Mtab = _table(m)
+        od1, oF, oM = O.local_table(_f64(X), _f64(y), T, norm)
+        assert np.array_equal(d1, od1) and np.array_equal(F, oF) and np.array_equal(Mtab, oM), norm
+        m.close()
+
+
 def test_close_knots_use_the_search_lookup():
     """Two knots in one lookup bucket switch the evaluation to the binary search over the
     knots; results still match the oracle."""

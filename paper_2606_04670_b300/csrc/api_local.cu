@@ -84,7 +84,7 @@ lip_status local_run(lip_model* h, bool sampled, int m, int64_t S, uint64_t seed
     LocMeta meta{};
     CUDA_TRY(cudaMemcpyAsync(&meta, P.meta, sizeof meta, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    CUDA_TRY(launch_local_table(P, meta.bucket_ok != 0, st));
+    CUDA_TRY(launch_local_table(P, meta.bucket_ok != 0, meta.m, st));
     count_launches(4 + (sampled && S > 0 ? 2 : 0));
     CUDA_TRY(cudaMemcpyAsync(&meta, P.meta, sizeof meta, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(h->loc_T, P.T64, sizeof h->loc_T, cudaMemcpyDeviceToHost, st));

@@ -218,7 +218,8 @@ int local_queries_per_block();
 cudaError_t launch_local_layout(const LocalParams& P, cudaStream_t st);
 cudaError_t launch_local_knots(const LocalParams& P, bool sampled, cudaStream_t st);
 int local_candidates();
-cudaError_t launch_local_table(const LocalParams& P, bool bucket_ok, cudaStream_t st);
+// m: the distinct knots the knots kernel kept (sizes the screen's shared memory)
+cudaError_t launch_local_table(const LocalParams& P, bool bucket_ok, int m, cudaStream_t st);
 cudaError_t launch_local_eval(int norm, const LocalScanParams& S, int gx, int nsplit, bool bucket,
                               const LocalMergeParams& M, cudaStream_t st);
 

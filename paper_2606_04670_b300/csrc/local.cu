@@ -331,31 +331,66 @@ __device__ __forceinline__ void write_row(const LocalParams& P, int64_t k, int m
 }
 
 // Shared memory of the table kernels: the data tile, the per-thread cumulative lower
-// bounds, the packed bucket table (BK) and the knots rounded down and up.
-size_t table_smem(int pr, bool bk) {
-    return ((size_t)LOC_TILE * pr + (size_t)LOC_KNOTS * LOC_THREADS + (bk ? LOC_BUCKETS : 0) + 2 * LOC_KNOTS) *
+// bounds (nseg segments), the packed bucket table (BK) and the knots rounded down and up.
+size_t table_smem(int pr, int nseg, bool bk) {
+    return ((size_t)LOC_TILE * pr + (size_t)nseg * LOC_THREADS + (bk ? LOC_BUCKETS : 0) + 2 * LOC_KNOTS) *
            sizeof(float);
 }
 
 // Running bounds of one datum in the screen: U >= d1_k, and cumulative lower bounds
-// Lb_k[s] <= Mtab_k[s] in shared memory (stride LOC_THREADS), Lb0 = Lb_k[0] in a register.
-// raise() adds a pair known to be at a positive distance in [lo, hi]: U falls to hi, and
-// its ratio lower bound is entered from segment up(hi) on (Lb is non-decreasing, so the
-// loop stops at the first entry already at least as large).
+// Lb_k[s] <= Mtab_k[s], s <= m, in shared memory (stride LOC_THREADS), with copies of
+// Lb_k at four coarse segments 0 <= c1 <= c2 <= c3 (about m/4, m/2, 3m/4) in registers.
+// coarse() bounds Lb_k at the lowest segment of a distance >= lo from below without a
+// lookup: lo above the c-th knot rounded up puts at least c knots below the distance,
+// and Lb is non-decreasing.  raise() adds a pair known to be at a positive distance in
+// [lo, hi]: U falls to hi, and its ratio lower bound is entered from segment up(hi) on
+// (the loop stops at the first entry already at least as large).
+struct ScreenRow {
+    float U;
+    float L0, L1, L2, L3;            // Lb_k[0], Lb_k[c1], Lb_k[c2], Lb_k[c3]
+};
+
+struct CoarseKnots {
+    int c1, c2, c3;
+    float t1, t2, t3;                // knots c1, c2, c3 rounded up (+inf without knots)
+};
+
+__device__ __forceinline__ CoarseKnots coarse_knots(const float* Tup, int m) {
+    CoarseKnots q;
+    q.c1 = m >= 4 ? m / 4 : (m > 0 ? 1 : 0);
+    q.c2 = m / 2 > q.c1 ? m / 2 : q.c1;
+    q.c3 = 3 * m / 4 > q.c2 ? 3 * m / 4 : q.c2;
+    q.t1 = q.c1 > 0 ? Tup[q.c1 - 1] : INFINITY;
+    q.t2 = q.c2 > 0 ? Tup[q.c2 - 1] : INFINITY;
+    q.t3 = q.c3 > 0 ? Tup[q.c3 - 1] : INFINITY;
+    return q;
+}
+
+__device__ __forceinline__ float coarse_lb(const ScreenRow& w, const CoarseKnots& q, float lo) {
+    float L = w.L0;
+    L = lo > q.t1 ? w.L1 : L;
+    L = lo > q.t2 ? w.L2 : L;
+    L = lo > q.t3 ? w.L3 : L;
+    return L;
+}
+
 template <bool Y64, bool BK>
-__device__ __forceinline__ void screen_raise(float* Ak, float& U, float& Lb0, float hi, float dy, float yk, float yj,
-                                             const unsigned* bk, const float* Tdn, float scale,
+__device__ __forceinline__ void screen_raise(float* Ak, int m, const CoarseKnots& q, ScreenRow& w, float hi, float dy,
+                                             float yk, float yj, const unsigned* bk, const float* Tdn, float scale,
                                              const ScreenConsts& c) {
-    U = fminf(U, hi);
+    w.U = fminf(w.U, hi);
     const float dyl = Y64 ? fmaxf(dy - c.ey * (fabsf(yk) + fabsf(yj)), 0.f) : dy;
     const float rlo = dyl * rcp_approx(hi) * c.lo_margin;
-    if (rlo <= Lb0) return;                                   // Lb[up(hi)] >= Lb[0]
+    if (rlo <= w.L0) return;                                  // Lb[up(hi)] >= Lb[0]
     const int su = seg_up<BK>(bk, Tdn, scale, hi);
-    for (int s = su; s < LOC_KNOTS; ++s) {
+    for (int s = su; s <= m; ++s) {
         if (Ak[s * LOC_THREADS] >= rlo) break;
         Ak[s * LOC_THREADS] = rlo;
     }
-    Lb0 = Ak[0];
+    w.L0 = Ak[0];
+    w.L1 = Ak[q.c1 * LOC_THREADS];
+    w.L2 = Ak[q.c2 * LOC_THREADS];
+    w.L3 = Ak[q.c3 * LOC_THREADS];
 }
 
 // Load rows idx(i), i < n, of the record layout into the shared tile.
@@ -381,10 +416,11 @@ __device__ __forceinline__ void load_tile(float4* sm4, const float* rec, int n, 
 template <int NORM, int DP, bool Y64, bool BK>
 __global__ void __launch_bounds__(LOC_THREADS) loc_screen_kernel(const LocalParams P) {
     constexpr int PR = DP + 4;
+    const int m = P.meta->m;
     extern __shared__ float4 sm4[];
     float* tile = reinterpret_cast<float*>(sm4);                                 // [LOC_TILE][PR]
-    float* A = tile + LOC_TILE * PR;                                             // [LOC_KNOTS][LOC_THREADS]
-    unsigned* bk = reinterpret_cast<unsigned*>(A + LOC_KNOTS * LOC_THREADS);     // [LOC_BUCKETS] if BK
+    float* A = tile + LOC_TILE * PR;                                             // [m + 1][LOC_THREADS]
+    unsigned* bk = reinterpret_cast<unsigned*>(A + (m + 1) * LOC_THREADS);       // [LOC_BUCKETS] if BK
     float* Tdn = reinterpret_cast<float*>(bk + (BK ? LOC_BUCKETS : 0));          // [LOC_KNOTS]
     float* Tup = Tdn + LOC_KNOTS;                                                // [LOC_KNOTS]
     const int tid = threadIdx.x;
@@ -396,17 +432,20 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_screen_kernel(const LocalPara
     for (int i = 0; i < DP; ++i) xk[i] = valid ? P.rec[k * PR + i] : 0.f;
     if (valid) yk = P.rec[k * PR + DP];
     float* Ak = A + tid;
-    for (int s = 0; s < LOC_KNOTS; ++s) Ak[s * LOC_THREADS] = 0.f;
+    for (int s = 0; s <= m; ++s) Ak[s * LOC_THREADS] = 0.f;
     if (BK)
         for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.bpack[b];
     if (tid < LOC_KNOTS) {
         Tdn[tid] = P.Tf[LOC_KNOTS + tid];
         Tup[tid] = P.Tf[2 * LOC_KNOTS + tid];
     }
+    __syncthreads();
     const float scale = P.meta->scale;
     const ScreenConsts c = screen_consts(P);
-    const float A0m = c.lo_margin;
-    float U = INFINITY, Lb0 = 0.f;
+    const CoarseKnots q = coarse_knots(Tup, m);
+    ScreenRow w;
+    w.U = INFINITY;
+    w.L0 = w.L1 = w.L2 = w.L3 = 0.f;
     // pilot: bounds only
     const int64_t pn = P.N >= 8 * LOC_PILOT ? LOC_PILOT : P.N / 8;
     const int64_t stride = pn > 0 ? P.N / pn : 1;
@@ -422,7 +461,7 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_screen_kernel(const LocalPara
             if (NORM == LIP_L2) d32 = sqrt_approx(d32);
             const float del = fmaf(c.e_rel, d32, c.e_abs);
             if (d32 > del)
-                screen_raise<Y64, BK>(Ak, U, Lb0, d32 + 2.f * del, fabsf(yk - xj[DP]), yk, xj[DP], bk, Tdn, scale, c);
+                screen_raise<Y64, BK>(Ak, m, q, w, d32 + 2.f * del, fabsf(yk - xj[DP]), yk, xj[DP], bk, Tdn, scale, c);
         }
     }
     int* list = P.cand + k * LOC_CAND;
@@ -441,11 +480,11 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_screen_kernel(const LocalPara
             const float lo = d32 - 2.f * del;
             const float yj = xj[DP];
             const float dy = fabsf(yk - yj);
-            bool cand = lo <= U;                                  // may be (tied) nearest
+            bool cand = lo <= w.U;                                // may be (tied) nearest
             if (!cand) {
                 const float dyu = (Y64 ? dy + c.ey * (fabsf(yk) + fabsf(yj)) : dy) * c.up_margin;
-                const float lom = lo * A0m;
-                if (dyu > Lb0 * lom) {                            // else rejected at segment 0
+                const float lom = lo * c.lo_margin;
+                if (dyu > coarse_lb(w, q, lo) * lom) {            // else rejected at a coarse segment
                     const int sd = seg_dn<BK>(bk, Tup, scale, lo);
                     cand = dyu > Ak[sd * LOC_THREADS] * lom;
                 }
@@ -453,14 +492,15 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_screen_kernel(const LocalPara
             if (cand) {
                 if (cnt < LOC_CAND) list[cnt] = (int)(j0 + j);
                 ++cnt;
-                if (d32 > del) screen_raise<Y64, BK>(Ak, U, Lb0, d32 + 2.f * del, dy, yk, yj, bk, Tdn, scale, c);
+                if (d32 > del)
+                    screen_raise<Y64, BK>(Ak, m, q, w, d32 + 2.f * del, dy, yk, yj, bk, Tdn, scale, c);
             }
         }
     }
     if (!valid) return;
-    P.ubound[k] = U;
+    P.ubound[k] = w.U;
     P.ncand[k] = cnt;
-    for (int s = 0; s < LOC_KNOTS; ++s) P.mt[k * LOC_KNOTS + s] = Ak[s * LOC_THREADS];
+    for (int s = 0; s < LOC_KNOTS; ++s) P.mt[k * LOC_KNOTS + s] = Ak[(s <= m ? s : m) * LOC_THREADS];
     if (cnt > LOC_CAND) P.over[atomicAdd(&P.meta->n_over, 1)] = (int)k;
     else atomicMax(&P.meta->max_cand, cnt);
 }
@@ -901,41 +941,40 @@ cudaError_t launch_local_knots(const LocalParams& P, bool sampled, cudaStream_t 
 }
 
 template <int NORM, int DP, bool Y64, bool BK>
-static cudaError_t table_run(const LocalParams& P, cudaStream_t st) {
-    const size_t smem = table_smem(DP + 4, BK);
+static cudaError_t table_run(const LocalParams& P, int m, cudaStream_t st) {
     const unsigned blocks = (unsigned)((P.N + LOC_THREADS - 1) / LOC_THREADS);
-    loc_screen_kernel<NORM, DP, Y64, BK><<<blocks, LOC_THREADS, smem, st>>>(P);
+    loc_screen_kernel<NORM, DP, Y64, BK><<<blocks, LOC_THREADS, table_smem(DP + 4, m + 1, BK), st>>>(P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     loc_exact_kernel<NORM, DP, Y64, BK><<<blocks, LOC_THREADS, 0, st>>>(P);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    loc_pass2_kernel<NORM, DP, Y64, BK><<<blocks, LOC_THREADS, smem, st>>>(P);
+    loc_pass2_kernel<NORM, DP, Y64, BK><<<blocks, LOC_THREADS, table_smem(DP + 4, LOC_KNOTS, BK), st>>>(P);
     return cudaGetLastError();
 }
 
 template <int NORM, int DP>
-static cudaError_t table_shape(const LocalParams& P, bool bk, cudaStream_t st) {
-    if (P.es == 8) return bk ? table_run<NORM, DP, true, true>(P, st) : table_run<NORM, DP, true, false>(P, st);
-    return bk ? table_run<NORM, DP, false, true>(P, st) : table_run<NORM, DP, false, false>(P, st);
+static cudaError_t table_shape(const LocalParams& P, bool bk, int m, cudaStream_t st) {
+    if (P.es == 8) return bk ? table_run<NORM, DP, true, true>(P, m, st) : table_run<NORM, DP, true, false>(P, m, st);
+    return bk ? table_run<NORM, DP, false, true>(P, m, st) : table_run<NORM, DP, false, false>(P, m, st);
 }
 
 template <int NORM>
-static cudaError_t table_norm(const LocalParams& P, bool bk, cudaStream_t st) {
+static cudaError_t table_norm(const LocalParams& P, bool bk, int m, cudaStream_t st) {
     switch (P.dp) {
-        case 4: return table_shape<NORM, 4>(P, bk, st);
-        case 8: return table_shape<NORM, 8>(P, bk, st);
-        case 12: return table_shape<NORM, 12>(P, bk, st);
-        default: return table_shape<NORM, 16>(P, bk, st);
+        case 4: return table_shape<NORM, 4>(P, bk, m, st);
+        case 8: return table_shape<NORM, 8>(P, bk, m, st);
+        case 12: return table_shape<NORM, 12>(P, bk, m, st);
+        default: return table_shape<NORM, 16>(P, bk, m, st);
     }
 }
 
 int local_candidates() { return LOC_CAND; }
 
-cudaError_t launch_local_table(const LocalParams& P, bool bucket_ok, cudaStream_t st) {
-    if (P.norm == LIP_L1) return table_norm<LIP_L1>(P, bucket_ok, st);
-    if (P.norm == LIP_L2) return table_norm<LIP_L2>(P, bucket_ok, st);
-    return table_norm<LIP_LINF>(P, bucket_ok, st);
+cudaError_t launch_local_table(const LocalParams& P, bool bucket_ok, int m, cudaStream_t st) {
+    if (P.norm == LIP_L1) return table_norm<LIP_L1>(P, bucket_ok, m, st);
+    if (P.norm == LIP_L2) return table_norm<LIP_L2>(P, bucket_ok, m, st);
+    return table_norm<LIP_LINF>(P, bucket_ok, m, st);
 }
 
 template <int NORM, int DP>

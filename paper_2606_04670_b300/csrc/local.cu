@@ -330,8 +330,10 @@ __device__ __forceinline__ void write_row(const LocalParams& P, int64_t k, int m
     }
 }
 
-// Shared memory of the table kernels: the data tile, the per-thread cumulative lower
-// bounds (nseg segments), the packed bucket table (BK) and the knots rounded down and up.
+// Shared memory of the table kernels: the data tile (LOC_TILE points of pr floats), the
+// per-thread cumulative lower bounds (nseg segments), the packed bucket table (BK) and the
+// knots rounded down and up.  The screen's pair records (pr - 2 float2 per two points) fit
+// in the same tile size.
 size_t table_smem(int pr, int nseg, bool bk) {
     return ((size_t)LOC_TILE * pr + (size_t)nseg * LOC_THREADS + (bk ? LOC_BUCKETS : 0) + 2 * LOC_KNOTS) *
            sizeof(float);
@@ -393,13 +395,44 @@ __device__ __forceinline__ void screen_raise(float* Ak, int m, const CoarseKnots
     w.L3 = Ak[q.c3 * LOC_THREADS];
 }
 
-// Load rows idx(i), i < n, of the record layout into the shared tile.
-template <int PR, typename Idx>
-__device__ __forceinline__ void load_tile(float4* sm4, const float* rec, int n, Idx idx) {
-    for (int i = threadIdx.x; i < n * PR / 4; i += LOC_THREADS) {
-        const int row = i / (PR / 4), part = i % (PR / 4);
-        sm4[i] = reinterpret_cast<const float4*>(rec + idx(row) * PR)[part];
+// Two data points per shared-memory record, coordinate-interleaved: record p holds
+// (x_2p[i], x_2p+1[i]) for i < DP, then (y_2p, y_2p+1) and a zero pad, so that a pair of
+// points feeds packed f32x2 instructions.  Points idx(r), r < n; a missing partner (odd n)
+// is NaN, which no test passes.
+template <int DP>
+constexpr int pair_rec() { return DP + 2; }          // float2 per record
+
+template <int DP, typename Idx>
+__device__ __forceinline__ void load_pairs(float2* t2, const float* rec, int n, Idx idx) {
+    constexpr int PR = DP + 4, W = pair_rec<DP>();
+    const float nan = __int_as_float(0x7fc00000);
+    const int np = (n + 1) / 2;
+    for (int i = threadIdx.x; i < np * W; i += LOC_THREADS) {
+        const int p = i / W, c = i % W;
+        float2 v = make_float2(0.f, 0.f);
+        if (c <= DP) {
+            const int r0 = 2 * p, r1 = 2 * p + 1;
+            v.x = rec[idx(r0) * PR + c];
+            v.y = r1 < n ? rec[idx(r1) * PR + c] : nan;
+        }
+        t2[i] = v;
     }
+}
+
+// Distances from datum k (coordinates duplicated in both halves) to the two points of a
+// pair record.
+template <int NORM, int DP>
+__device__ __forceinline__ float2 dist32x2(const float2 (&xk2)[DP], const float2* x2) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < DP; ++i) {
+        const float2 t = sub2(xk2[i], x2[i]);
+        if (NORM == LIP_L2) acc = fma2(t, t, acc);
+        else if (NORM == LIP_L1) acc = make_float2(acc.x + fabsf(t.x), acc.y + fabsf(t.y));
+        else acc = make_float2(fmaxf(acc.x, fabsf(t.x)), fmaxf(acc.y, fabsf(t.y)));
+    }
+    if (NORM == LIP_L2) acc = make_float2(sqrt_approx(acc.x), sqrt_approx(acc.y));
+    return acc;
 }
 
 // The table's N^2 screen.  A thread owns datum k and keeps the running bounds; a pair that
@@ -409,28 +442,34 @@ __device__ __forceinline__ void load_tile(float4* sm4, const float* rec, int n, 
 // loc_exact_kernel tests the list again against the final bounds and recomputes the
 // survivors in FP64.  A pair that fails the test cannot raise the bounds (its ratio lower
 // bound is below Lb at its lowest segment), so only candidates update them, and most far
-// pairs are rejected against Lb_k[0] <= Lb_k[s] without a segment lookup.  The bounds are
+// pairs are rejected against Lb_k at a coarse segment without a lookup.  The bounds are
 // first warmed on a pilot of (up to) 1024 strided data, so that fewer pairs of the main scan
-// pass against early, loose bounds.  Outputs per datum: U, the cumulative Lb, the list
-// length and the list; a list longer than LOC_CAND sends the datum to loc_pass2_kernel.
+// pass against early, loose bounds.  Data points come two at a time (load_pairs): both are
+// tested against the same snapshot of the bounds, which is valid since any earlier bounds
+// are looser.  Outputs per datum: U, the cumulative Lb, the list length and the list; a
+// list longer than LOC_CAND sends the datum to loc_pass2_kernel.
 template <int NORM, int DP, bool Y64, bool BK>
 __global__ void __launch_bounds__(LOC_THREADS) loc_screen_kernel(const LocalParams P) {
-    constexpr int PR = DP + 4;
+    constexpr int PR = DP + 4, W = pair_rec<DP>();
     const int m = P.meta->m;
     extern __shared__ float4 sm4[];
-    float* tile = reinterpret_cast<float*>(sm4);                                 // [LOC_TILE][PR]
-    float* A = tile + LOC_TILE * PR;                                             // [m + 1][LOC_THREADS]
+    float2* t2 = reinterpret_cast<float2*>(sm4);                                 // [LOC_TILE / 2][W]
+    float* A = reinterpret_cast<float*>(t2 + LOC_TILE / 2 * W);                  // [m + 1][LOC_THREADS]
     unsigned* bk = reinterpret_cast<unsigned*>(A + (m + 1) * LOC_THREADS);       // [LOC_BUCKETS] if BK
     float* Tdn = reinterpret_cast<float*>(bk + (BK ? LOC_BUCKETS : 0));          // [LOC_KNOTS]
     float* Tup = Tdn + LOC_KNOTS;                                                // [LOC_KNOTS]
     const int tid = threadIdx.x;
     const int64_t k = (int64_t)blockIdx.x * LOC_THREADS + tid;
     const bool valid = k < P.N;
-    float xk[DP];
+    float2 xk2[DP];
     float yk = 0.f;
 #pragma unroll
-    for (int i = 0; i < DP; ++i) xk[i] = valid ? P.rec[k * PR + i] : 0.f;
+    for (int i = 0; i < DP; ++i) {
+        const float v = valid ? P.rec[k * PR + i] : 0.f;
+        xk2[i] = make_float2(v, v);
+    }
     if (valid) yk = P.rec[k * PR + DP];
+    const float2 yk2 = make_float2(yk, yk);
     float* Ak = A + tid;
     for (int s = 0; s <= m; ++s) Ak[s * LOC_THREADS] = 0.f;
     if (BK)
@@ -443,6 +482,9 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_screen_kernel(const LocalPara
     const float scale = P.meta->scale;
     const ScreenConsts c = screen_consts(P);
     const CoarseKnots q = coarse_knots(Tup, m);
+    const float2 erel2 = make_float2(c.e_rel, c.e_rel), eabs2 = make_float2(c.e_abs, c.e_abs);
+    const float2 m2 = make_float2(-2.f, -2.f), up2 = make_float2(c.up_margin, c.up_margin);
+    const float2 lm2 = make_float2(c.lo_margin, c.lo_margin);
     ScreenRow w;
     w.U = INFINITY;
     w.L0 = w.L1 = w.L2 = w.L3 = 0.f;
@@ -452,16 +494,16 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_screen_kernel(const LocalPara
     for (int64_t p0 = 0; p0 < pn; p0 += LOC_TILE) {
         const int n = (int)lmin(LOC_TILE, pn - p0);
         __syncthreads();
-        load_tile<PR>(sm4, P.rec, n, [&](int row) { return (p0 + row) * stride; });
+        load_pairs<DP>(t2, P.rec, n, [&](int row) { return (p0 + row) * stride; });
         __syncthreads();
         if (!valid) continue;
-        for (int j = 0; j < n; ++j) {
-            const float* xj = tile + j * PR;
-            float d32 = dist32<NORM, DP>(xk, xj);
-            if (NORM == LIP_L2) d32 = sqrt_approx(d32);
-            const float del = fmaf(c.e_rel, d32, c.e_abs);
-            if (d32 > del)
-                screen_raise<Y64, BK>(Ak, m, q, w, d32 + 2.f * del, fabsf(yk - xj[DP]), yk, xj[DP], bk, Tdn, scale, c);
+        for (int p = 0; p < (n + 1) / 2; ++p) {
+            const float2* x2 = t2 + p * W;
+            const float2 d = dist32x2<NORM, DP>(xk2, x2);
+            const float2 del = fma2(erel2, d, eabs2), hi = fma2(make_float2(2.f, 2.f), del, d);
+            const float2 y2 = x2[DP];
+            if (d.x > del.x) screen_raise<Y64, BK>(Ak, m, q, w, hi.x, fabsf(yk - y2.x), yk, y2.x, bk, Tdn, scale, c);
+            if (d.y > del.y) screen_raise<Y64, BK>(Ak, m, q, w, hi.y, fabsf(yk - y2.y), yk, y2.y, bk, Tdn, scale, c);
         }
     }
     int* list = P.cand + k * LOC_CAND;
@@ -469,31 +511,44 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_screen_kernel(const LocalPara
     for (int64_t j0 = 0; j0 < P.N; j0 += LOC_TILE) {
         const int n = (int)lmin(LOC_TILE, P.N - j0);
         __syncthreads();
-        load_tile<PR>(sm4, P.rec, n, [&](int row) { return j0 + row; });
+        load_pairs<DP>(t2, P.rec, n, [&](int row) { return j0 + row; });
         __syncthreads();
         if (!valid) continue;
-        for (int j = 0; j < n; ++j) {
-            const float* xj = tile + j * PR;
-            float d32 = dist32<NORM, DP>(xk, xj);
-            if (NORM == LIP_L2) d32 = sqrt_approx(d32);
-            const float del = fmaf(c.e_rel, d32, c.e_abs);
-            const float lo = d32 - 2.f * del;
-            const float yj = xj[DP];
-            const float dy = fabsf(yk - yj);
-            bool cand = lo <= w.U;                                // may be (tied) nearest
-            if (!cand) {
-                const float dyu = (Y64 ? dy + c.ey * (fabsf(yk) + fabsf(yj)) : dy) * c.up_margin;
-                const float lom = lo * c.lo_margin;
-                if (dyu > coarse_lb(w, q, lo) * lom) {            // else rejected at a coarse segment
-                    const int sd = seg_dn<BK>(bk, Tup, scale, lo);
-                    cand = dyu > Ak[sd * LOC_THREADS] * lom;
+        for (int p = 0; p < (n + 1) / 2; ++p) {
+            const float2* x2 = t2 + p * W;
+            const float2 d = dist32x2<NORM, DP>(xk2, x2);
+            const float2 del = fma2(erel2, d, eabs2);
+            const float2 lo = fma2(m2, del, d);
+            const float2 y2 = x2[DP];
+            float2 dy = sub2(yk2, y2);
+            dy = make_float2(fabsf(dy.x), fabsf(dy.y));
+            float2 dyu = dy;
+            if (Y64) dyu = fma2(make_float2(c.ey, c.ey), make_float2(fabsf(yk) + fabsf(y2.x), fabsf(yk) + fabsf(y2.y)), dy);
+            dyu = mul2(dyu, up2);
+            const float2 lom = mul2(lo, lm2);
+            const float2 Lc = mul2(make_float2(coarse_lb(w, q, lo.x), coarse_lb(w, q, lo.y)), lom);
+            // per point: 1 = nearest candidate, 2 = needs the segment test, 0 = rejected
+            const int f0 = lo.x <= w.U ? 1 : (dyu.x > Lc.x ? 2 : 0);
+            const int f1 = lo.y <= w.U ? 1 : (dyu.y > Lc.y ? 2 : 0);
+            if ((f0 | f1) == 0) continue;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int f = e == 0 ? f0 : f1;
+                if (f == 0) continue;
+                const float lo_e = e == 0 ? lo.x : lo.y;
+                bool cand = f == 1;
+                if (!cand) {
+                    const int sd = seg_dn<BK>(bk, Tup, scale, lo_e);
+                    cand = (e == 0 ? dyu.x : dyu.y) > Ak[sd * LOC_THREADS] * (e == 0 ? lom.x : lom.y);
                 }
-            }
-            if (cand) {
-                if (cnt < LOC_CAND) list[cnt] = (int)(j0 + j);
+                if (!cand) continue;
+                if (cnt < LOC_CAND) list[cnt] = (int)(j0 + 2 * p + e);
                 ++cnt;
-                if (d32 > del)
-                    screen_raise<Y64, BK>(Ak, m, q, w, d32 + 2.f * del, dy, yk, yj, bk, Tdn, scale, c);
+                const float d_e = e == 0 ? d.x : d.y, del_e = e == 0 ? del.x : del.y;
+                const float yj = e == 0 ? y2.x : y2.y;
+                if (d_e > del_e)
+                    screen_raise<Y64, BK>(Ak, m, q, w, d_e + 2.f * del_e, e == 0 ? dy.x : dy.y, yk, yj, bk, Tdn,
+                                          scale, c);
             }
         }
     }

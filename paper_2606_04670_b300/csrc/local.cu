@@ -739,12 +739,15 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanPa
         for (int i = tid; i < LOC_SCAN_TILE * LOC_KNOTS / 4; i += LOC_THREADS) mt4[i] = ms[i];
         __syncthreads();
         float2 cu = bu, cl = bl;
-#pragma unroll 2
-        for (int j = 0; j < LOC_SCAN_TILE; ++j) {
-            float2 vu, vl;
-            loc_pair_values<NORM, DP, BUCKET>(q2, rec + j * PR, mt + j * LOC_KNOTS, bk, Tn, scale, vu, vl);
-            cu = make_float2(fminf(cu.x, vu.x), fminf(cu.y, vu.y));      // NaN (padding) is ignored
-            cl = make_float2(fmaxf(cl.x, vl.x), fmaxf(cl.y, vl.y));
+        // two data points per step, folded with the three-input min / max (NaN, i.e.
+        // padding, is ignored)
+        for (int j = 0; j < LOC_SCAN_TILE; j += 2) {
+            float2 vu0, vl0, vu1, vl1;
+            loc_pair_values<NORM, DP, BUCKET>(q2, rec + j * PR, mt + j * LOC_KNOTS, bk, Tn, scale, vu0, vl0);
+            loc_pair_values<NORM, DP, BUCKET>(q2, rec + (j + 1) * PR, mt + (j + 1) * LOC_KNOTS, bk, Tn, scale, vu1,
+                                              vl1);
+            cu = make_float2(min3f(cu.x, vu0.x, vu1.x), min3f(cu.y, vu0.y, vu1.y));
+            cl = make_float2(max3f(cl.x, vl0.x, vl1.x), max3f(cl.y, vl0.y, vl1.y));
         }
         if (cu.x < bu.x) tu0 = (int)j0;
         if (cu.y < bu.y) tu1 = (int)j0;

@@ -240,7 +240,7 @@ lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     LocalParams P;
     LIP_TRY(local_buffers(h, 0, P));
-    const int64_t gx = ceil_div(nq, (int64_t)local_queries_per_block());
+    const int64_t gx = ceil_div(nq, (int64_t)local_queries_per_block(h->d));
     if (gx > 0x7fffffff) return fail(LIP_ERR_ARG, "nq = %lld is too large", (long long)nq);
     const int64_t tile = local_scan_tile();
     const int64_t tiles = P.npad / tile;

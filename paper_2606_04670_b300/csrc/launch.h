@@ -214,7 +214,7 @@ cudaError_t launch_local_eval_k(int norm, int k, int K, const LocalScanParams& S
 int local_record_floats(int d);
 int64_t local_pad(int64_t N);
 int local_scan_tile();
-int local_queries_per_block();
+int local_queries_per_block(int d);
 cudaError_t launch_local_layout(const LocalParams& P, cudaStream_t st);
 cudaError_t launch_local_knots(const LocalParams& P, bool sampled, cudaStream_t st);
 int local_candidates();

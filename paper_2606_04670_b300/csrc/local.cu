@@ -45,6 +45,9 @@ constexpr int LOC_RANK_TILE = 1024;
 constexpr int LOC_CAND = 64;        // table candidates listed per datum (more: the second scan)
 constexpr int LOC_PILOT = 1024;     // strided data that warm the screen's bounds
 
+// Query pairs per thread of the evaluation scan for DP padded coordinates.
+constexpr int local_scan_groups(int dp) { return dp <= 4 ? 2 : 1; }
+
 __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t c) {
@@ -702,7 +705,9 @@ __device__ __forceinline__ void loc_pair_values(const float2 (&q2)[DP], const fl
     vl = fma2(make_float2(-M.x, -M.y), t, y2);
 }
 
-template <int NORM, int DP, bool BUCKET>
+// G groups of two queries per thread (G = 2 for d <= 4: the data point's loads and the loop
+// are shared by four queries).
+template <int NORM, int DP, bool BUCKET, int G>
 __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanParams P) {
     constexpr int PR = DP + 4;
     __shared__ float4 rec4[LOC_SCAN_TILE * PR / 4];
@@ -713,13 +718,18 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanPa
     const float* mt = reinterpret_cast<const float*>(mt4);
     const int tid = threadIdx.x;
     const int split = blockIdx.y;
-    float2 q2[DP];
-    const int64_t qa = (int64_t)blockIdx.x * LOC_THREADS * 2 + tid, qb = qa + LOC_THREADS;
+    float2 q2[G][DP];
+    int64_t qi[G][2];
 #pragma unroll
-    for (int i = 0; i < DP; ++i) {
-        const float a = (qa < P.nq && i < P.d) ? (float)(P.w[i] * ldv(P.Q, P.es, qa * P.d + i)) : 0.f;
-        const float b = (qb < P.nq && i < P.d) ? (float)(P.w[i] * ldv(P.Q, P.es, qb * P.d + i)) : 0.f;
-        q2[i] = make_float2(a, b);
+    for (int g = 0; g < G; ++g) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) qi[g][h] = (int64_t)blockIdx.x * LOC_THREADS * 2 * G + (2 * g + h) * LOC_THREADS + tid;
+#pragma unroll
+        for (int i = 0; i < DP; ++i) {
+            const float a = (qi[g][0] < P.nq && i < P.d) ? (float)(P.w[i] * ldv(P.Q, P.es, qi[g][0] * P.d + i)) : 0.f;
+            const float b = (qi[g][1] < P.nq && i < P.d) ? (float)(P.w[i] * ldv(P.Q, P.es, qi[g][1] * P.d + i)) : 0.f;
+            q2[g][i] = make_float2(a, b);
+        }
     }
     if (BUCKET) {
         for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.bpack[b];
@@ -727,8 +737,14 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanPa
         Tn[tid] = P.Tf[tid];
     }
     const float scale = P.scale;
-    float2 bu = make_float2(INFINITY, INFINITY), bl = make_float2(-INFINITY, -INFINITY);
-    int tu0 = -1, tu1 = -1, tl0 = -1, tl1 = -1;            // tile of the last strict improvement
+    float2 bu[G], bl[G];
+    int tu[G][2], tl[G][2];                                   // tile of the last strict improvement
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        bu[g] = make_float2(INFINITY, INFINITY);
+        bl[g] = make_float2(-INFINITY, -INFINITY);
+        tu[g][0] = tu[g][1] = tl[g][0] = tl[g][1] = -1;
+    }
     const int64_t j_begin = (int64_t)split * P.points_per_split;
     const int64_t j_end = lmin(j_begin + P.points_per_split, P.npad);
     for (int64_t j0 = j_begin; j0 < j_end; j0 += LOC_SCAN_TILE) {
@@ -738,49 +754,60 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_scan_kernel(const LocalScanPa
         const float4* ms = reinterpret_cast<const float4*>(P.mt + j0 * LOC_KNOTS);
         for (int i = tid; i < LOC_SCAN_TILE * LOC_KNOTS / 4; i += LOC_THREADS) mt4[i] = ms[i];
         __syncthreads();
-        float2 cu = bu, cl = bl;
+        float2 cu[G], cl[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) { cu[g] = bu[g]; cl[g] = bl[g]; }
         // two data points per step, folded with the three-input min / max (NaN, i.e.
         // padding, is ignored)
         for (int j = 0; j < LOC_SCAN_TILE; j += 2) {
-            float2 vu0, vl0, vu1, vl1;
-            loc_pair_values<NORM, DP, BUCKET>(q2, rec + j * PR, mt + j * LOC_KNOTS, bk, Tn, scale, vu0, vl0);
-            loc_pair_values<NORM, DP, BUCKET>(q2, rec + (j + 1) * PR, mt + (j + 1) * LOC_KNOTS, bk, Tn, scale, vu1,
-                                              vl1);
-            cu = make_float2(min3f(cu.x, vu0.x, vu1.x), min3f(cu.y, vu0.y, vu1.y));
-            cl = make_float2(max3f(cl.x, vl0.x, vl1.x), max3f(cl.y, vl0.y, vl1.y));
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                float2 vu0, vl0, vu1, vl1;
+                loc_pair_values<NORM, DP, BUCKET>(q2[g], rec + j * PR, mt + j * LOC_KNOTS, bk, Tn, scale, vu0, vl0);
+                loc_pair_values<NORM, DP, BUCKET>(q2[g], rec + (j + 1) * PR, mt + (j + 1) * LOC_KNOTS, bk, Tn, scale,
+                                                  vu1, vl1);
+                cu[g] = make_float2(min3f(cu[g].x, vu0.x, vu1.x), min3f(cu[g].y, vu0.y, vu1.y));
+                cl[g] = make_float2(max3f(cl[g].x, vl0.x, vl1.x), max3f(cl[g].y, vl0.y, vl1.y));
+            }
         }
-        if (cu.x < bu.x) tu0 = (int)j0;
-        if (cu.y < bu.y) tu1 = (int)j0;
-        if (cl.x > bl.x) tl0 = (int)j0;
-        if (cl.y > bl.y) tl1 = (int)j0;
-        bu = cu;
-        bl = cl;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (cu[g].x < bu[g].x) tu[g][0] = (int)j0;
+            if (cu[g].y < bu[g].y) tu[g][1] = (int)j0;
+            if (cl[g].x > bl[g].x) tl[g][0] = (int)j0;
+            if (cl[g].y > bl[g].y) tl[g][1] = (int)j0;
+            bu[g] = cu[g];
+            bl[g] = cl[g];
+        }
     }
     // lowest index in the remembered tile whose value equals the extremum
-    const int tiles[4] = {tu0, tu1, tl0, tl1};
-    int idx[4] = {-1, -1, -1, -1};
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        if (tiles[c] < 0) continue;
-        const float target = c == 0 ? bu.x : (c == 1 ? bu.y : (c == 2 ? bl.x : bl.y));
-        for (int j = 0; j < LOC_SCAN_TILE; ++j) {
-            const int64_t k = (int64_t)tiles[c] + j;
-            float2 vu, vl;
-            loc_pair_values<NORM, DP, BUCKET>(q2, P.rec + k * PR, P.mt + k * LOC_KNOTS, bk, Tn, scale, vu, vl);
-            const float v = c == 0 ? vu.x : (c == 1 ? vu.y : (c == 2 ? vl.x : vl.y));
-            if (v == target) { idx[c] = (int)k; break; }
-        }
-    }
     PartialRec<float>* part = static_cast<PartialRec<float>*>(P.partial);
-    if (qa < P.nq) {
-        PartialRec<float> rr;
-        rr.vu = bu.x; rr.iu = idx[0]; rr.vl = bl.x; rr.il = idx[2];
-        part[(int64_t)split * P.nq + qa] = rr;
-    }
-    if (qb < P.nq) {
-        PartialRec<float> rr;
-        rr.vu = bu.y; rr.iu = idx[1]; rr.vl = bl.y; rr.il = idx[3];
-        part[(int64_t)split * P.nq + qb] = rr;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int tiles[4] = {tu[g][0], tu[g][1], tl[g][0], tl[g][1]};
+        int idx[4] = {-1, -1, -1, -1};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (tiles[c] < 0) continue;
+            const float target = c == 0 ? bu[g].x : (c == 1 ? bu[g].y : (c == 2 ? bl[g].x : bl[g].y));
+            for (int j = 0; j < LOC_SCAN_TILE; ++j) {
+                const int64_t k = (int64_t)tiles[c] + j;
+                float2 vu, vl;
+                loc_pair_values<NORM, DP, BUCKET>(q2[g], P.rec + k * PR, P.mt + k * LOC_KNOTS, bk, Tn, scale, vu, vl);
+                const float v = c == 0 ? vu.x : (c == 1 ? vu.y : (c == 2 ? vl.x : vl.y));
+                if (v == target) { idx[c] = (int)k; break; }
+            }
+        }
+        if (qi[g][0] < P.nq) {
+            PartialRec<float> rr;
+            rr.vu = bu[g].x; rr.iu = idx[0]; rr.vl = bl[g].x; rr.il = idx[2];
+            part[(int64_t)split * P.nq + qi[g][0]] = rr;
+        }
+        if (qi[g][1] < P.nq) {
+            PartialRec<float> rr;
+            rr.vu = bu[g].y; rr.iu = idx[1]; rr.vl = bl[g].y; rr.il = idx[3];
+            part[(int64_t)split * P.nq + qi[g][1]] = rr;
+        }
     }
 }
 
@@ -976,7 +1003,7 @@ int local_dim_pad(int d) { return (d + 3) / 4 * 4; }
 int local_record_floats(int d) { return local_dim_pad(d) + 4; }
 int64_t local_pad(int64_t N) { return (N + LOC_TILE - 1) / LOC_TILE * LOC_TILE; }
 int local_scan_tile() { return LOC_SCAN_TILE; }
-int local_queries_per_block() { return LOC_THREADS * 2; }
+int local_queries_per_block(int d) { return LOC_THREADS * 2 * local_scan_groups(local_dim_pad(d)); }
 
 cudaError_t launch_local_layout(const LocalParams& P, cudaStream_t st) {
     const unsigned blocks = (unsigned)((P.npad + 255) / 256);
@@ -1037,8 +1064,9 @@ cudaError_t launch_local_table(const LocalParams& P, bool bucket_ok, int m, cuda
 
 template <int NORM, int DP>
 static void scan_shape(const LocalScanParams& S, dim3 grid, bool bucket, cudaStream_t st) {
-    if (bucket) loc_scan_kernel<NORM, DP, true><<<grid, LOC_THREADS, 0, st>>>(S);
-    else loc_scan_kernel<NORM, DP, false><<<grid, LOC_THREADS, 0, st>>>(S);
+    constexpr int G = local_scan_groups(DP);
+    if (bucket) loc_scan_kernel<NORM, DP, true, G><<<grid, LOC_THREADS, 0, st>>>(S);
+    else loc_scan_kernel<NORM, DP, false, G><<<grid, LOC_THREADS, 0, st>>>(S);
 }
 
 template <int NORM>

@@ -762,10 +762,12 @@ def wl_smooth(ctx, name="smooth_d4"):
         torch.cuda.synchronize()
         pass_ms.append(a.elapsed_time(b))
     ms_pass = statistics.median(pass_ms)
-    # per ordered pair: distance 2d, dz, two terms, two positive parts, two sums, one FMA; one MUFU sqrt
-    ip = 2 * p.d + 8
-    roof = ctx.roofline(f"smooth_pass_kernel<{NNAME[p.norm]}, DP=4> (+ layout and sums)", ip * pairs, ms_pass, ip,
+    # the pass visits each unordered pair once: distance 2d, dz, the two term arguments, two
+    # positive parts, the R and C sums, two FMAs for S and one maximum; one MUFU sqrt
+    ip = 2 * p.d + 10
+    roof = ctx.roofline(f"smooth_pass_kernel<{NNAME[p.norm]}, DP=4> (+ layout and sums)", ip * pairs / 2, ms_pass, ip,
                         1 if p.norm == W.NORM_L2 else 0, clocks)
+    roof["pairs_per_launch"] = "N (N - 1) / 2 unordered pairs"
     e2e = None
     if not args.no_e2e:
         hX, hy = (torch.as_tensor(a).pin_memory() for a in (p.X, p.y))

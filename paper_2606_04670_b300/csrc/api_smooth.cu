@@ -51,11 +51,14 @@ lip_status smooth_setup(lip_model* h, double M, double p, cudaStream_t st, Smoot
     P.points_per_split = round_up(ceil_div(P.npad, s), tile);
     P.nsplit = (int)ceil_div(P.npad, P.points_per_split);
     LIP_TRY(h->sm_rec.ensure((size_t)P.npad * (P.dp + 4) * sizeof(float), "smoothing layout"));
-    LIP_TRY(h->sm_part.ensure((size_t)P.nsplit * h->N * 3 * sizeof(double), "smoothing partials"));
+    const size_t part_b = (size_t)P.nsplit * h->N * 3 * sizeof(double), col_b = (size_t)h->N * 2 * 8;
+    LIP_TRY(h->sm_part.ensure(part_b + col_b + 16, "smoothing partials"));
     const int rb = smooth_reduce_blocks();
     LIP_TRY(h->sm_small.ensure((size_t)(4 + 3 * rb) * sizeof(double), "smoothing scalars"));
     P.rec = static_cast<float*>(h->sm_rec.p);
     P.partial = static_cast<double*>(h->sm_part.p);
+    P.colfix = reinterpret_cast<unsigned long long*>(static_cast<char*>(h->sm_part.p) + part_b);
+    P.zbits = reinterpret_cast<unsigned*>(static_cast<char*>(h->sm_part.p) + part_b + col_b);
     r.out = static_cast<double*>(h->sm_small.p);
     r.red = r.out + 2;
     r.bsum = r.out + 4;

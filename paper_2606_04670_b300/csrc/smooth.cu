@@ -4,15 +4,23 @@
 //   S1 = sum_{i != k} ((z_i - z_k - M dist_up(x^i, x^k))_+)^2          Eq. (const1)
 //   S2 = sum_{i != k} ((z_k - z_i - M dist_lo(x^i, x^k))_+)^2          Eq. (const2)
 //
-// with z = y + eps, and its gradient, as one fused pass over all ordered pairs (no N x N
+// with z = y + eps, and its gradient, as one fused pass over the pairs (no N x N
 // storage), driven by L-BFGS.  dist_lo(x^i, x^k) = dist_up(x^k, x^i), so Eq. (const2)'s
 // term of (i, k) is Eq. (const1)'s term of (k, i): S2 = S1 and
 //
 //   Phi = ||eps||^2 / p + 2 S1,   dPhi/deps_j = 2 eps_j / p + 4 (R_j - C_j),
 //   R_j = sum_k (z_j - z_k - M dist_up(x^j, x^k))_+,  C_j = sum_i (z_i - z_j - M dist_up(x^i, x^j))_+.
 //
-// The pass gives each thread two rows i: for every k it forms both v_ik (the const1 term)
-// and v_ki (the term with i second), so R_i, C_i and the row's share of S1 need no atomics.
+// The pass visits each unordered pair {i, k} once, from row i < k: it forms v_ik (the
+// const1 term) and v_ki (the term with i second), adds them to R_i, C_i and the row's share
+// of S1 without atomics, and owes row k the same two terms (as C_k and R_k).  Those column
+// terms are zero unless a term is positive (a pair that violates the Lipschitz condition),
+// and they go to 64-bit fixed-point accumulators with integer atomics.  Integer sums do not
+// depend on the order of the atomics, so results stay reproducible; the scale 2^(61 - e)
+// with N (max z - min z) < 2^e keeps every column sum below 2^61.  Terms come four data
+// points at a time; one warp vote per group decides whether the warp sums the group's
+// column terms (shuffle tree in a fixed order) and lane 0 adds them, so the cost stays
+// bounded when many pairs violate (line-search trial points).
 // Pair terms are FP32 on the scaled layout (coordinates times M w, mirrored where
 // decreasing, constrained first); each thread adds them in FP32 within a 128-point tile
 // and in FP64 across tiles, and the splits are summed in FP64 in a fixed order.
@@ -26,10 +34,28 @@ constexpr int SM_THREADS = 128;
 constexpr int SM_TILE = 128;
 constexpr int RED_BLOCKS = 256;     // fixed reduction shape: results do not depend on timing
 
+// Order-preserving unsigned bits of a float (larger float, larger bits).
+__device__ __forceinline__ unsigned ord_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord_float(unsigned o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// Fixed-point scale of the column sums: 2^(61 - e) with N (max z - min z) < 2^e.
+__device__ __forceinline__ double col_scale(const SmoothParams& P) {
+    const double range = (double)ord_float(P.zbits[0]) + (double)ord_float(P.zbits[1]);
+    const double bound = fmax((double)P.N * range, 0x1p-60);       // the scale stays below 2^121
+    return ldexp(1.0, 61 - (ilogb(bound) + 1));
+}
+
+// The layout of z = y + eps; also zeroes the column sums and records the range of z.
 __global__ void smooth_layout_kernel(const SmoothParams P, const double* eps) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= P.npad) return;
     float* r = P.rec + k * (P.dp + 4);
+    unsigned zmax = 0u, nzmax = 0u;
     if (k < P.N) {
         for (int j = 0; j < P.dp; ++j) {
             const int64_t i = k * P.d + P.perm[j];
@@ -37,80 +63,144 @@ __global__ void smooth_layout_kernel(const SmoothParams P, const double* eps) {
             r[j] = j < P.d ? (float)(P.scale[j] * x) : 0.f;
         }
         const double y = P.es == 8 ? static_cast<const double*>(P.y0)[k] : (double)static_cast<const float*>(P.y0)[k];
-        r[P.dp] = (float)(y + eps[k]);
+        const float z = (float)(y + eps[k]);
+        r[P.dp] = z;
+        zmax = ord_bits(z);
+        nzmax = ord_bits(-z);
+        P.colfix[k] = 0ull;
+        P.colfix[P.N + k] = 0ull;
     } else {
         for (int j = 0; j < P.dp; ++j) r[j] = 0.f;
         r[P.dp] = __int_as_float(0x7fc00000);          // padding: NaN terms are never positive
     }
     r[P.dp + 1] = r[P.dp + 2] = r[P.dp + 3] = 0.f;
+    const unsigned act = __activemask();
+    zmax = __reduce_max_sync(act, zmax);
+    nzmax = __reduce_max_sync(act, nzmax);
+    if ((int)(threadIdx.x & 31) == __ffs(act) - 1) {
+        atomicMax(&P.zbits[0], zmax);
+        atomicMax(&P.zbits[1], nzmax);
+    }
+}
+
+// Distances from the two rows (halves of x2) to data point xk: dist_up(x^i, x^k) in au
+// and dist_up(x^k, x^i) in ar (the same for the symmetric distance).
+template <int NORM, int DP, bool MONO>
+__device__ __forceinline__ void smooth_dists(const float2 (&x2)[DP], const float* xk, int C, float2& au, float2& ar) {
+    au = make_float2(0.f, 0.f);
+    ar = au;
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+        const float2 t = sub2(x2[j], make_float2(xk[j], xk[j]));
+        if (MONO && j < C) {
+            const float2 u = make_float2(fmaxf(t.x, 0.f), fmaxf(t.y, 0.f));
+            const float2 v = make_float2(fmaxf(-t.x, 0.f), fmaxf(-t.y, 0.f));
+            if (NORM == LIP_L1) { au = add2(au, u); ar = add2(ar, v); }
+            else if (NORM == LIP_L2) { au = fma2(u, u, au); ar = fma2(v, v, ar); }
+            else {
+                au = make_float2(fmaxf(au.x, u.x), fmaxf(au.y, u.y));
+                ar = make_float2(fmaxf(ar.x, v.x), fmaxf(ar.y, v.y));
+            }
+        } else {
+            if (NORM == LIP_L1) au = make_float2(au.x + fabsf(t.x), au.y + fabsf(t.y));
+            else if (NORM == LIP_L2) au = fma2(t, t, au);
+            else au = make_float2(fmaxf(au.x, fabsf(t.x)), fmaxf(au.y, fabsf(t.y)));
+            if (MONO) {
+                if (NORM == LIP_L1) ar = make_float2(ar.x + fabsf(t.x), ar.y + fabsf(t.y));
+                else if (NORM == LIP_L2) ar = fma2(t, t, ar);
+                else ar = make_float2(fmaxf(ar.x, fabsf(t.x)), fmaxf(ar.y, fabsf(t.y)));
+            }
+        }
+    }
+    if (NORM == LIP_L2) {
+        au = make_float2(sqrt_approx(au.x), sqrt_approx(au.y));
+        if (MONO) ar = make_float2(sqrt_approx(ar.x), sqrt_approx(ar.y));
+    }
+    if (!MONO) ar = au;
+}
+
+// The two terms of the pairs (i, k) for both rows: p1 = (z_i - z_k - M dist_up(x^i, x^k))_+
+// and p2 = (z_k - z_i - M dist_up(x^k, x^i))_+ (NaN, i.e. padding, gives 0); before the
+// positive part, v1 = p1's argument and nw2 = p2's.
+__device__ __forceinline__ void smooth_terms(float2 z2, float zk, float2 au, float2 ar, float2& v1, float2& nw2,
+                                             float2& p1, float2& p2) {
+    const float2 dz = sub2(z2, make_float2(zk, zk));
+    v1 = sub2(dz, au);
+    nw2 = sub2(make_float2(-dz.x, -dz.y), ar);
+    p1 = make_float2(v1.x > 0.f ? v1.x : 0.f, v1.y > 0.f ? v1.y : 0.f);
+    p2 = make_float2(nw2.x > 0.f ? nw2.x : 0.f, nw2.y > 0.f ? nw2.y : 0.f);
 }
 
 // Each thread owns two rows (i and i + 128 of its block's 256), packed into the halves of
 // float2 registers, so the distance, the two terms and the three sums are f32x2 operations.
+// A row takes the data k > i of its split; on the two tiles that hold the block's own rows
+// the pairs with k <= i are masked.
 template <int NORM, int DP, bool MONO>
 __global__ void __launch_bounds__(SM_THREADS) smooth_pass_kernel(const SmoothParams P) {
     constexpr int PR = DP + 4;
     __shared__ float4 tile4[SM_TILE * PR / 4];
     const float* tile = reinterpret_cast<const float*>(tile4);
     const int tid = threadIdx.x;
-    const int64_t ia = (int64_t)blockIdx.x * SM_THREADS * 2 + tid, ib = ia + SM_THREADS;
+    const int64_t i0 = (int64_t)blockIdx.x * SM_THREADS * 2;
+    const int64_t ia = i0 + tid, ib = ia + SM_THREADS;
     const int split = blockIdx.y;
     const bool va = ia < P.N, vb = ib < P.N;
     float2 x2[DP];
 #pragma unroll
     for (int j = 0; j < DP; ++j)
         x2[j] = make_float2(va ? P.rec[ia * PR + j] : 0.f, vb ? P.rec[ib * PR + j] : 0.f);
-    const float2 z2 = make_float2(va ? P.rec[ia * PR + DP] : 0.f, vb ? P.rec[ib * PR + DP] : 0.f);
+    // an invalid row's z is NaN: its terms are 0
+    const float nan = __int_as_float(0x7fc00000);
+    const float2 z2 = make_float2(va ? P.rec[ia * PR + DP] : nan, vb ? P.rec[ib * PR + DP] : nan);
+    const float fscale = (float)col_scale(P);                        // a power of 2
     double Ra = 0.0, Ca = 0.0, Sa = 0.0, Rb = 0.0, Cb = 0.0, Sb = 0.0;
-    const int64_t k_begin = (int64_t)split * P.points_per_split;
-    const int64_t k_end = k_begin + P.points_per_split < P.npad ? k_begin + P.points_per_split : P.npad;
+    const int64_t split_begin = (int64_t)split * P.points_per_split;
+    const int64_t k_begin = split_begin > i0 ? split_begin : i0;     // i0 is a multiple of the tile
+    const int64_t k_end = split_begin + P.points_per_split < P.npad ? split_begin + P.points_per_split : P.npad;
     for (int64_t k0 = k_begin; k0 < k_end; k0 += SM_TILE) {
         __syncthreads();
         const float4* src = reinterpret_cast<const float4*>(P.rec + k0 * PR);
         for (int t = tid; t < SM_TILE * PR / 4; t += SM_THREADS) tile4[t] = src[t];
         __syncthreads();
+        const bool diag = k0 < i0 + 2 * SM_THREADS;                     // holds some k <= i
         float2 r = make_float2(0.f, 0.f), c = r, s = r;
-#pragma unroll 4
-        for (int k = 0; k < SM_TILE; ++k) {
-            const float* xk = tile + k * PR;
-            float2 au = make_float2(0.f, 0.f), ar = au;
+        for (int kg = 0; kg < SM_TILE; kg += 4) {
+            float2 q1[4], q2[4];
+            float top = -INFINITY;                                       // largest term argument
 #pragma unroll
-            for (int j = 0; j < DP; ++j) {
-                const float2 t = sub2(x2[j], make_float2(xk[j], xk[j]));
-                if (MONO && j < P.C) {
-                    const float2 u = make_float2(fmaxf(t.x, 0.f), fmaxf(t.y, 0.f));
-                    const float2 v = make_float2(fmaxf(-t.x, 0.f), fmaxf(-t.y, 0.f));
-                    if (NORM == LIP_L1) { au = add2(au, u); ar = add2(ar, v); }
-                    else if (NORM == LIP_L2) { au = fma2(u, u, au); ar = fma2(v, v, ar); }
-                    else {
-                        au = make_float2(fmaxf(au.x, u.x), fmaxf(au.y, u.y));
-                        ar = make_float2(fmaxf(ar.x, v.x), fmaxf(ar.y, v.y));
+            for (int u = 0; u < 4; ++u) {
+                const float* xk = tile + (kg + u) * PR;
+                float2 au, ar, v1, nw2;
+                smooth_dists<NORM, DP, MONO>(x2, xk, P.C, au, ar);
+                smooth_terms(z2, xk[DP], au, ar, v1, nw2, q1[u], q2[u]);
+                if (diag) {
+                    const int64_t kk = k0 + kg + u;
+                    if (kk <= ia) { q1[u].x = q2[u].x = 0.f; v1.x = nw2.x = -INFINITY; }
+                    if (kk <= ib) { q1[u].y = q2[u].y = 0.f; v1.y = nw2.y = -INFINITY; }
+                }
+                top = max3f(top, max3f(v1.x, v1.y, nw2.x), nw2.y);
+                r = add2(r, q1[u]);
+                c = add2(c, q2[u]);
+                s = fma2(q1[u], q1[u], fma2(q2[u], q2[u], s));
+            }
+            if (__any_sync(0xffffffffu, top > 0.f)) {
+                // row k is owed C_k += p1 and R_k += p2: summed over the warp's 64 rows in a
+                // fixed shuffle order, then added in fixed point by lane 0
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float cs = q1[u].x + q1[u].y, rs = q2[u].x + q2[u].y;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        cs += __shfl_xor_sync(0xffffffffu, cs, o);
+                        rs += __shfl_xor_sync(0xffffffffu, rs, o);
                     }
-                } else {
-                    if (NORM == LIP_L1) au = make_float2(au.x + fabsf(t.x), au.y + fabsf(t.y));
-                    else if (NORM == LIP_L2) au = fma2(t, t, au);
-                    else au = make_float2(fmaxf(au.x, fabsf(t.x)), fmaxf(au.y, fabsf(t.y)));
-                    if (MONO) {
-                        if (NORM == LIP_L1) ar = make_float2(ar.x + fabsf(t.x), ar.y + fabsf(t.y));
-                        else if (NORM == LIP_L2) ar = fma2(t, t, ar);
-                        else ar = make_float2(fmaxf(ar.x, fabsf(t.x)), fmaxf(ar.y, fabsf(t.y)));
+                    const int64_t kk = k0 + kg + u;
+                    if ((tid & 31) == 0 && kk < P.N) {
+                        if (cs > 0.f) atomicAdd(&P.colfix[P.N + kk], __float2ull_rn(cs * fscale));
+                        if (rs > 0.f) atomicAdd(&P.colfix[kk], __float2ull_rn(rs * fscale));
                     }
                 }
             }
-            if (NORM == LIP_L2) {
-                au = make_float2(sqrt_approx(au.x), sqrt_approx(au.y));
-                if (MONO) ar = make_float2(sqrt_approx(ar.x), sqrt_approx(ar.y));
-            }
-            if (!MONO) ar = au;
-            const float zk = xk[DP];
-            const float2 dz = sub2(z2, make_float2(zk, zk));
-            const float2 v1 = sub2(dz, au);                       // const1 term of (i, k)
-            const float2 w2 = add2(dz, ar);                       // minus the const1 term of (k, i)
-            const float2 p1 = make_float2(v1.x > 0.f ? v1.x : 0.f, v1.y > 0.f ? v1.y : 0.f);   // NaN gives 0
-            const float2 p2 = make_float2(-w2.x > 0.f ? -w2.x : 0.f, -w2.y > 0.f ? -w2.y : 0.f);
-            r = add2(r, p1);
-            c = add2(c, p2);
-            s = fma2(p1, p1, s);
         }
         Ra += (double)r.x; Ca += (double)c.x; Sa += (double)s.x;
         Rb += (double)r.y; Cb += (double)c.y; Sb += (double)s.y;
@@ -129,6 +219,7 @@ __global__ void __launch_bounds__(SM_THREADS) smooth_pass_kernel(const SmoothPar
 __global__ void __launch_bounds__(256) smooth_finish_kernel(const SmoothParams P, const double* eps, double* grad,
                                                             double* block_sums) {
     __shared__ double red[2][256];
+    const double cscale = col_scale(P);
     double sS = 0.0, sE = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += (int64_t)gridDim.x * blockDim.x) {
         double R = 0.0, C = 0.0, S = 0.0;
@@ -138,6 +229,8 @@ __global__ void __launch_bounds__(256) smooth_finish_kernel(const SmoothParams P
             C += v[1];
             S += v[2];
         }
+        R += (double)P.colfix[i] / cscale;
+        C += (double)P.colfix[P.N + i] / cscale;
         if (grad) grad[i] = 2.0 * eps[i] / P.p + 4.0 * (R - C);
         sS += S;
         sE += eps[i] * eps[i];
@@ -249,8 +342,10 @@ int smooth_reduce_blocks() { return RED_BLOCKS; }
 // out[1] = S1 (device); grad may be NULL.  block_sums holds 2 * RED_BLOCKS doubles.
 cudaError_t launch_smooth_objective(const SmoothParams& P, const double* eps, double* grad, double* block_sums,
                                     double* out, int gx, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(P.zbits, 0, 2 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
     smooth_layout_kernel<<<(unsigned)((P.npad + 255) / 256), 256, 0, st>>>(P, eps);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)gx, (unsigned)P.nsplit);
     if (P.norm == LIP_L1) pass_norm<LIP_L1>(P, grid, st);

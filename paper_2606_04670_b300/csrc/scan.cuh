@@ -97,8 +97,9 @@ __device__ __forceinline__ void group_values(const float2 (&qq)[C + U], const fl
                 float2 su, sl;
 #pragma unroll
                 for (int j = 0; j < C; ++j) {
+                    // the positive and negative parts on the ALU pipe, next to the busier FMA pipe
                     const float2 p = make_float2(fmaxf(t[j].x, 0.f), fmaxf(t[j].y, 0.f));
-                    const float2 n = sub2(t[j], p);
+                    const float2 n = make_float2(fminf(t[j].x, 0.f), fminf(t[j].y, 0.f));
                     if (j == 0 && U == 0) { su = mul2(p, p); sl = mul2(n, n); }
                     else if (j == 0) { su = fma2(p, p, s0); sl = fma2(n, n, s0); }
                     else { su = fma2(p, p, su); sl = fma2(n, n, sl); }

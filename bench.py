@@ -50,11 +50,25 @@ SMOOTH_ITERS = 10
 LOCAL_KNOTS, LOCAL_SAMPLE, LOCAL_SEED = 16, 32768, 0
 # TF32 dense peak: the measured BF16 peak times the nominal TF32 / BF16 ratio (1.1 / 2.25)
 TF32_OVER_BF16 = 1.1 / 2.25
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant scan kernel of
-# the default workload, from the ncu capture summarised in
-# profiles/scan_exact_l2_monotone_d4.md (None whenever that kernel changes until it is
-# captured again).
-SCAN_DRAM_BYTES = {("monotone_d4", 2): 18.106624e6 + 2.477824e6}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of each workload's dominant
+# kernel at the full workload size (one-pass ncu captures of the timed step's launch; the
+# commands and figures are in profiles/dram_traffic_bench_workloads.md).  An entry is
+# removed whenever its kernel changes, until it is captured again.
+KERNEL_DRAM_BYTES = {
+    ("monotone_d4", 2): 19.136000e6 + 11.619840e6,     # scan_exact_kernel<L2, C=2, U=2, R=4>
+    ("grad_d8", 2): 16.66e6 + 13.47e6,                 # scan_exact_kernel<L2, C=4, U=4, R=2>
+    ("cluster_d16", 2): 618.02e6 + 185.20e6,           # scan_exact_kernel<L2, C=0, U=16, R=2>
+    ("cluster_d16_tc", 2): 18426.68e6 + 1521.30e6,     # tc_scan_kernel<K=24, 4 parts, TF32>
+    ("cluster_d16_bf16", 2): 21212.12e6 + 1781.97e6,   # tc_scan_kernel<K=32, 4 parts, BF16>
+    ("local_d4", 2): 32.64e6 + 1.43e6,                 # loc_scan_kernel<L2, 4, bucket, G=2>
+    ("smooth_d4", 2): 4.63e6 + 0.0,                    # smooth_pass_kernel<L2, 4> (symmetric)
+    ("batch_4096", 0): 4817.68e6 + 1598.16e6,          # batch_scan_kernel
+}
+
+
+def traffic_for(args, name, norm):
+    """The stored DRAM bytes of a workload's dominant kernel, at the full workload size only."""
+    return None if getattr(args, "queries", 0) else KERNEL_DRAM_BYTES.get((name, norm))
 
 
 def i_pair(norm: int, d: int, c: int) -> int:
@@ -426,7 +440,7 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
     if rd["prec"] == "fp64":
         kern = "FP32 screen " + kern.replace(" fp64", "") + " + screen64_kernel (FP64 candidates)"
     roof = ctx.roofline(kern, ip * p.nq * p.N, avg[kdom], ip, mufu_per_pair(p.norm, c), clocks,
-                        SCAN_DRAM_BYTES.get((name, p.norm)) if rd["prec"] == "fp32" else None)
+                        traffic_for(args, name, p.norm) if rd["prec"] == "fp32" else None)
     if rd["prec"] in ("tc_tf32", "tc_bf16"):
         bf = rd["prec"] == "tc_bf16"
         # tensor-core form: three TF32 products over K = 8 ceil((d + 2) / 8), or six BF16
@@ -439,7 +453,7 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
         roof = {"bound": "tensor", "kernel": f"tc_scan_kernel<K={kk}, {'BF16' if bf else 'TF32'}> (+ build and rescreen)",
                 "achieved": flops / (avg[kdom] / 1e3) / 1e12, "peak": peak / 1e12,
                 "unit": f"TFLOP/s ({'BF16' if bf else 'TF32'})", "frac": flops / (avg[kdom] / 1e3) / peak,
-                "traffic": None,
+                "traffic": traffic_for(args, name, p.norm),
                 "peak_source": ("measured bf16 dense peak of MEASURED_PEAKS.json" if bf else
                                 "measured bf16 dense peak of MEASURED_PEAKS.json x 1.1/2.25 (nominal TF32/BF16)"),
                 "flops_per_pair": 2 * npass * kk,
@@ -584,7 +598,7 @@ def wl_batch(ctx):
     for bs in plan:
         ops += bs.nq * bs.N * i_pair(bs.norm, bs.d, int((bs.mon != 0).sum()))
     roof = ctx.roofline("batch_scan_kernel (persistent, 4096 sets)", ops, min(scan_ms),
-                        ops / info["total_pairs"], None, clocks)
+                        ops / info["total_pairs"], None, clocks, traffic_for(args, "batch_4096", 0))
     e2e = None
     if not args.no_e2e:
         hout = {k: torch.empty(tq, dtype=v.dtype).pin_memory() for k, v in dout.items()}
@@ -654,7 +668,8 @@ def wl_local(ctx, name="local_d4"):
     # select, two FMAs, two (compare + two selects) for the running extrema; one MUFU sqrt
     ip = 2 * p.d + 20
     roof = ctx.roofline(f"loc_scan_kernel<{NNAME[p.norm]}> (d={p.d}, {LOCAL_KNOTS} knots)", ip * p.nq * p.N,
-                        ms_scan, ip, 1 if p.norm == W.NORM_L2 else 0, clocks)
+                        ms_scan, ip, 1 if p.norm == W.NORM_L2 else 0, clocks,
+                        traffic_for(args, name, p.norm))
     e2e = None
     if not args.no_e2e:
         hX, hy, hQ = (torch.as_tensor(a).pin_memory() for a in (p.X, p.y, p.Q))
@@ -766,7 +781,7 @@ def wl_smooth(ctx, name="smooth_d4"):
     # positive parts, the R and C sums, two FMAs for S and one maximum; one MUFU sqrt
     ip = 2 * p.d + 10
     roof = ctx.roofline(f"smooth_pass_kernel<{NNAME[p.norm]}, DP=4> (+ layout and sums)", ip * pairs / 2, ms_pass, ip,
-                        1 if p.norm == W.NORM_L2 else 0, clocks)
+                        1 if p.norm == W.NORM_L2 else 0, clocks, traffic_for(args, name, p.norm))
     roof["pairs_per_launch"] = "N (N - 1) / 2 unordered pairs"
     e2e = None
     if not args.no_e2e:

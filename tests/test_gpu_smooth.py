@@ -156,3 +156,17 @@ def test_full_size_gradient_rows():
     assert np.abs(g[rows] - go).max() <= tol, (np.abs(g[rows] - go).max(), tol)
     assert f >= eps @ eps / pen
     m.close()
+
+
+def test_objective_reproducible_bit_for_bit():
+    """The column terms arrive through atomics in any order; they are summed in 64-bit fixed
+    point, so two evaluations at a point with many violating pairs agree bit for bit."""
+    p = _noisy(460, 3000, 3, 2, noise=0.8)
+    m = _model(p)
+    eps = torch.as_tensor(0.3 * np.random.default_rng(3).standard_normal(p.N)).cuda()
+    f1, g1 = m.smooth_objective(eps, 0.5 * p.M, 20.0)
+    f2, g2 = m.smooth_objective(eps, 0.5 * p.M, 20.0)
+    assert f1 == f2 and torch.equal(g1, g2)
+    _, go, s1, _ = O.smooth_objective(p.X, p.y, eps.cpu().numpy(), 0.5 * p.M, 20.0, p.norm)
+    assert s1 > 0.0 and np.abs(g1.cpu().numpy() - go).max() <= 4.0 * p.N * EPS32 * _scale(p, 0.5 * p.M)
+    m.close()

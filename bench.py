@@ -48,6 +48,8 @@ WORKLOADS = ("monotone_d4", "plain_d2", "cluster_d16", "cluster_d16_tc", "cluste
              "batch_4096", "local_d4", "smooth_d4")
 SMOOTH_ITERS = 10
 LOCAL_KNOTS, LOCAL_SAMPLE, LOCAL_SEED = 16, 32768, 0
+# special-function (MUFU) results per SM per clock
+MUFU_PER_SM = 16
 # TF32 dense peak: the measured BF16 peak times the nominal TF32 / BF16 ratio (1.1 / 2.25)
 TF32_OVER_BF16 = 1.1 / 2.25
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of each workload's dominant
@@ -343,7 +345,18 @@ class Ctx:
              "i_pair": ipair, "mufu_per_pair": mufu}
         if clocks and clocks.get("sm_mhz"):
             r["frac_at_measured_clock"] = achieved / (self.sms * FP32_LANES_PER_SM * clocks["sm_mhz"] * 1e6)
+        if mufu:
+            r["mufu"] = self.mufu_bound(achieved / ipair, mufu)
         return r
+
+    def mufu_bound(self, pairs_per_s, mufu_per_pair):
+        """The special-function (MUFU) pipe as a second bound: square roots per second against
+        148 SMs x 16 per clock x the maximum SM clock (a throughput kernel measured 15.0
+        sqrt.approx, and as many rsqrt.approx, per SM per clock on the B300s)."""
+        peak = self.sms * MUFU_PER_SM * self.sm_max * 1e6
+        ach = pairs_per_s * mufu_per_pair
+        return {"achieved": ach / 1e12, "peak": peak / 1e12, "unit": "T MUFU ops/s", "frac": ach / peak,
+                "per_pair": mufu_per_pair}
 
     def line(self, value, ms_total, steps, dtype, config, roof, cpu, e2e, clocks, launches, detail):
         return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": self.world, "steps": steps,
@@ -457,6 +470,7 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
                 "peak_source": ("measured bf16 dense peak of MEASURED_PEAKS.json" if bf else
                                 "measured bf16 dense peak of MEASURED_PEAKS.json x 1.1/2.25 (nominal TF32/BF16)"),
                 "flops_per_pair": 2 * npass * kk,
+                "mufu": ctx.mufu_bound(p.nq * p.N / (avg[kdom] / 1e3), 1),
                 "alu_view": {k: alu[k] for k in ("achieved", "peak", "frac", "i_pair")}}
 
     e2e = None

@@ -109,6 +109,12 @@ def dist_env():
 
 # ------------------------------------------------------------------ clocks
 
+def out_dir():
+    """Where the bench writes its side files (clock samples, the autotune cache it collects):
+    $LIPFIT_BENCH_OUT, else bench_out/ at the repository root."""
+    return os.environ.get("LIPFIT_BENCH_OUT") or os.path.join(ROOT, "bench_out")
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -117,7 +123,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(out_dir(), f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -368,10 +374,11 @@ class Ctx:
 
 
 def _tune_cache():
-    """The autotune cache: the one collected in this tree's gpurun_out/ by earlier runs, else
-    the committed default.  Saved back to gpurun_out/ (copy it to the default to keep it)."""
+    """The autotune cache: the one collected in the output folder (out_dir()) by earlier
+    runs, else the committed default.  Saved back to the output folder (copy it to the
+    default to keep it)."""
     from paper_2606_04670_b300 import autotune as AT
-    local = os.path.join(ROOT, "gpurun_out", "autotune_cache.json")
+    local = os.path.join(out_dir(), "autotune_cache.json")
     cache = AT.load_cache(local) if os.path.exists(local) else AT.load_cache()
     return cache, (lambda: AT.save_cache(cache, local))
 

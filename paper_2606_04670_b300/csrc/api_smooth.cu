@@ -46,7 +46,9 @@ lip_status smooth_setup(lip_model* h, double M, double p, cudaStream_t st, Smoot
     P.p = p;
     r.gx = (int)ceil_div(h->N, (int64_t)smooth_rows_per_block());
     const int64_t tiles = P.npad / tile;
-    const int64_t want = std::max<int64_t>(1, ceil_div((int64_t)h->sms * 16, r.gx));
+    // the pass is triangular (row i takes k > i), so many blocks are short or empty: fine
+    // splits (up to 64) keep the last wave short
+    const int64_t want = std::max<int64_t>(1, ceil_div((int64_t)h->sms * 256, r.gx));
     const int64_t s = std::min<int64_t>(std::min<int64_t>(want, 64), tiles);
     P.points_per_split = round_up(ceil_div(P.npad, s), tile);
     P.nsplit = (int)ceil_div(P.npad, P.points_per_split);

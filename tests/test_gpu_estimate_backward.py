@@ -139,6 +139,28 @@ def test_backward_grad_d8(oracle_mod):
     assert checked > 2000
 
 
+def test_backward_grad_d8_full_size(oracle_mod):
+    """The differentiation workload at the benchmark's size (N = 200,000, Q = 262,144): the
+    backward pass of the GPU's own argmin/argmax against the oracle's analytic gradient on
+    every query (given the indices, the gradient is O(Q d), so the oracle takes all of it)."""
+    import torch
+    p = W.grad_d8()
+    m = _model(p)
+    Q = torch.as_tensor(p.Q).cuda()
+    r = m.eval(Q)
+    gbar = torch.as_tensor(np.random.default_rng(5).uniform(0.5, 1.5, p.nq).astype(np.float32)).cuda()
+    gQ, gy, gM = m.backward(Q, r["idx_up"], r["idx_lo"], gbar)
+    torch.cuda.synchronize()
+    m.close()
+    iu, il = r["idx_up"].cpu().numpy(), r["idx_lo"].cpu().numpy()
+    assert (iu >= 0).all() and (il >= 0).all()
+    oQ, oy, oM = oracle_mod.gradient(p.X, p.y, p.Q, p.M, iu, il, gbar.cpu().numpy().astype(np.float64), p.norm,
+                                     p.mon, p.w)
+    np.testing.assert_allclose(gQ.cpu().numpy(), oQ, rtol=1e-4, atol=1e-4 * p.M)
+    np.testing.assert_allclose(gy.cpu().numpy(), oy, rtol=1e-5, atol=1e-5 * np.abs(oy).max())
+    assert abs(gM.item() - oM) <= 1e-4 * max(1.0, abs(oM))
+
+
 def test_autograd_gradcheck_fp64():
     import torch
 

@@ -122,6 +122,25 @@ def test_tc_full_size_cluster_sampled(oracle_mod):
     _check_exact(ps, {k: v[idx] for k, v in r.items()}, orc, "tc full cluster", fb)
 
 
+def test_bf16_full_size_cluster_sampled(oracle_mod):
+    """The BF16 form at the full precision workload (N = Q = 1e6, d = 16), as the benchmark
+    launches it, checked on 400 sampled queries against the FP64 oracle."""
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    p = W.cluster_d16()
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, precision="tc_bf16")
+    r = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
+    fb = m.last_fallback()
+    m.check()
+    m.close()
+    assert fb <= p.nq // 100
+    idx = np.sort(np.random.default_rng(22).choice(p.nq, 400, replace=False))
+    ps = W.Problem("c", p.X, p.y, p.Q[idx], p.M, p.norm, None, None)
+    orc = oracle_mod.evaluate(p.X, p.y, ps.Q, p.M, p.norm)
+    _check_exact(ps, {k: v[idx] for k, v in r.items()}, orc, "bf16 full cluster", fb)
+
+
 @pytest.mark.parametrize("d,weighted", [(1, False), (2, True), (6, True), (13, False), (14, True), (15, False),
                                         (16, True)])
 def test_bf16_random_shapes(oracle_mod, d, weighted):

@@ -798,9 +798,10 @@ def wl_smooth(ctx, name="smooth_d4"):
         torch.cuda.synchronize()
         pass_ms.append(a.elapsed_time(b))
     ms_pass = statistics.median(pass_ms)
-    # the pass visits each unordered pair once: distance 2d, dz, the two term arguments, two
-    # positive parts, the R and C sums, two FMAs for S and one maximum; one MUFU sqrt
-    ip = 2 * p.d + 10
+    # the pass visits each unordered pair once: distance 2d, dz, the two term arguments, their
+    # positive and negative parts and the share q, the R - C sum, one FMA for S and one
+    # maximum for the vote; one MUFU sqrt
+    ip = 2 * p.d + 9
     roof = ctx.roofline(f"smooth_pass_kernel<{NNAME[p.norm]}, DP=4> (+ layout and sums)", ip * pairs / 2, ms_pass, ip,
                         1 if p.norm == W.NORM_L2 else 0, clocks, traffic_for(args, name, p.norm))
     roof["pairs_per_launch"] = "N (N - 1) / 2 unordered pairs"

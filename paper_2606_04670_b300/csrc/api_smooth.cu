@@ -53,7 +53,7 @@ lip_status smooth_setup(lip_model* h, double M, double p, cudaStream_t st, Smoot
     P.points_per_split = round_up(ceil_div(P.npad, s), tile);
     P.nsplit = (int)ceil_div(P.npad, P.points_per_split);
     LIP_TRY(h->sm_rec.ensure((size_t)P.npad * (P.dp + 4) * sizeof(float), "smoothing layout"));
-    const size_t part_b = (size_t)P.nsplit * h->N * 3 * sizeof(double), col_b = (size_t)h->N * 2 * 8;
+    const size_t part_b = (size_t)P.nsplit * h->N * 2 * sizeof(double), col_b = (size_t)h->N * 8;
     LIP_TRY(h->sm_part.ensure(part_b + col_b + 16, "smoothing partials"));
     const int rb = smooth_reduce_blocks();
     LIP_TRY(h->sm_small.ensure((size_t)(4 + 3 * rb) * sizeof(double), "smoothing scalars"));

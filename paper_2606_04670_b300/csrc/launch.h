@@ -235,8 +235,8 @@ struct SmoothParams {
     double scale[D_MAX];             // M * w * sign, in layout order
     double p;                        // penalty weight of Eq. (optim)
     float* rec;                      // [npad][dp + 4]: scaled coordinates, z = y + eps, 0, 0, 0
-    double* partial;                 // [nsplit][N][3]: R, C, S per split (row side)
-    unsigned long long* colfix;      // [2][N]: R and C of the column side, fixed point
+    double* partial;                 // [nsplit][N][2]: R - C and S per split (row side)
+    unsigned long long* colfix;      // [N]: R - C of the column side, signed fixed point
     unsigned* zbits;                 // [2]: largest z and -z (order-preserving bits)
     int nsplit;
     int64_t points_per_split;

@@ -12,12 +12,12 @@
 //   R_j = sum_k (z_j - z_k - M dist_up(x^j, x^k))_+,  C_j = sum_i (z_i - z_j - M dist_up(x^i, x^j))_+.
 //
 // The pass visits each unordered pair {i, k} once, from row i < k: it forms v_ik (the
-// const1 term) and v_ki (the term with i second), adds them to R_i, C_i and the row's share
-// of S1 without atomics, and owes row k the same two terms (as C_k and R_k).  Those column
-// terms are zero unless a term is positive (a pair that violates the Lipschitz condition),
-// and they go to 64-bit fixed-point accumulators with integer atomics.  Integer sums do not
+// const1 term) and v_ki (the term with i second), of which at most one is positive, adds
+// q = (v_ik)_+ - (v_ki)_+ to R_i - C_i and q^2 to the row's share of S1 without atomics, and
+// owes row k the term -q.  That column term is zero unless the pair violates the Lipschitz
+// condition, and it goes to a signed 64-bit fixed-point accumulator with integer atomics.  Integer sums do not
 // depend on the order of the atomics, so results stay reproducible; the scale 2^(61 - e)
-// with N (max z - min z) < 2^e keeps every column sum below 2^61.  Terms come four data
+// with N (max z - min z) < 2^e keeps every column sum below 2^61 in magnitude.  Terms come four data
 // points at a time; one warp vote per group decides whether the warp sums the group's
 // column terms (shuffle tree in a fixed order) and lane 0 adds them, so the cost stays
 // bounded when many pairs violate (line-search trial points).
@@ -68,7 +68,6 @@ __global__ void smooth_layout_kernel(const SmoothParams P, const double* eps) {
         zmax = ord_bits(z);
         nzmax = ord_bits(-z);
         P.colfix[k] = 0ull;
-        P.colfix[P.N + k] = 0ull;
     } else {
         for (int j = 0; j < P.dp; ++j) r[j] = 0.f;
         r[P.dp] = __int_as_float(0x7fc00000);          // padding: NaN terms are never positive
@@ -119,22 +118,28 @@ __device__ __forceinline__ void smooth_dists(const float2 (&x2)[DP], const float
     if (!MONO) ar = au;
 }
 
-// The two terms of the pairs (i, k) for both rows: p1 = (z_i - z_k - M dist_up(x^i, x^k))_+
-// and p2 = (z_k - z_i - M dist_up(x^k, x^i))_+ (NaN, i.e. padding, gives 0); before the
-// positive part, v1 = p1's argument and nw2 = p2's.
-__device__ __forceinline__ void smooth_terms(float2 z2, float zk, float2 au, float2 ar, float2& v1, float2& nw2,
-                                             float2& p1, float2& p2) {
+// The pair (i, k)'s share of the gradient for both rows: q = (v_ik)_+ - (v_ki)_+, with
+// v_ik = z_i - z_k - M dist_up(x^i, x^k) (Eq. (const1)) and v_ki = z_k - z_i - M
+// dist_up(x^k, x^i).  v_ik + v_ki = -M (dist_up(x^i, x^k) + dist_up(x^k, x^i)) <= 0, so at
+// most one is positive: q = max(v_ik, 0) + min(-v_ki, 0), and q^2 is the pair's share of
+// S1 (both orders).  Row i gains R_i - C_i += q and row k gains R_k - C_k -= q.  top
+// tracks the largest of v_ik and v_ki (a positive one means a column term is owed).
+// NaN (padding, absent rows) gives q = 0 and leaves top alone.
+template <bool MASK>
+__device__ __forceinline__ float2 smooth_q(float2 z2, float zk, float2 au, float2 ar, bool ma, bool mb, float& top) {
     const float2 dz = sub2(z2, make_float2(zk, zk));
-    v1 = sub2(dz, au);
-    nw2 = sub2(make_float2(-dz.x, -dz.y), ar);
-    p1 = make_float2(v1.x > 0.f ? v1.x : 0.f, v1.y > 0.f ? v1.y : 0.f);
-    p2 = make_float2(nw2.x > 0.f ? nw2.x : 0.f, nw2.y > 0.f ? nw2.y : 0.f);
+    float2 v1 = sub2(dz, au);                     // v_ik
+    float2 w2 = add2(dz, ar);                     // -v_ki
+    if (MASK && ma) { v1.x = -INFINITY; w2.x = INFINITY; }
+    if (MASK && mb) { v1.y = -INFINITY; w2.y = INFINITY; }
+    top = max3f(top, max3f(v1.x, v1.y, -w2.x), -w2.y);
+    return add2(make_float2(fmaxf(v1.x, 0.f), fmaxf(v1.y, 0.f)), make_float2(fminf(w2.x, 0.f), fminf(w2.y, 0.f)));
 }
 
 // Each thread owns two rows (i and i + 128 of its block's 256), packed into the halves of
-// float2 registers, so the distance, the two terms and the three sums are f32x2 operations.
-// A row takes the data k > i of its split; on the two tiles that hold the block's own rows
-// the pairs with k <= i are masked.
+// float2 registers, so the distance, the pair's share q and the two sums are f32x2
+// operations.  A row takes the data k > i of its split; on the two tiles that hold the
+// block's own rows the pairs with k <= i are masked.
 template <int NORM, int DP, bool MONO>
 __global__ void __launch_bounds__(SM_THREADS) smooth_pass_kernel(const SmoothParams P) {
     constexpr int PR = DP + 4;
@@ -149,11 +154,11 @@ __global__ void __launch_bounds__(SM_THREADS) smooth_pass_kernel(const SmoothPar
 #pragma unroll
     for (int j = 0; j < DP; ++j)
         x2[j] = make_float2(va ? P.rec[ia * PR + j] : 0.f, vb ? P.rec[ib * PR + j] : 0.f);
-    // an invalid row's z is NaN: its terms are 0
+    // an absent row's z is NaN: its q is 0
     const float nan = __int_as_float(0x7fc00000);
     const float2 z2 = make_float2(va ? P.rec[ia * PR + DP] : nan, vb ? P.rec[ib * PR + DP] : nan);
     const float fscale = (float)col_scale(P);                        // a power of 2
-    double Ra = 0.0, Ca = 0.0, Sa = 0.0, Rb = 0.0, Cb = 0.0, Sb = 0.0;
+    double Da = 0.0, Sa = 0.0, Db = 0.0, Sb = 0.0;
     const int64_t split_begin = (int64_t)split * P.points_per_split;
     const int64_t k_begin = split_begin > i0 ? split_begin : i0;     // i0 is a multiple of the tile
     const int64_t k_end = split_begin + P.points_per_split < P.npad ? split_begin + P.points_per_split : P.npad;
@@ -163,55 +168,57 @@ __global__ void __launch_bounds__(SM_THREADS) smooth_pass_kernel(const SmoothPar
         for (int t = tid; t < SM_TILE * PR / 4; t += SM_THREADS) tile4[t] = src[t];
         __syncthreads();
         const bool diag = k0 < i0 + 2 * SM_THREADS;                     // holds some k <= i
-        float2 r = make_float2(0.f, 0.f), c = r, s = r;
+        float2 dsum = make_float2(0.f, 0.f), ssum = dsum;
         for (int kg = 0; kg < SM_TILE; kg += 4) {
-            float2 q1[4], q2[4];
-            float top = -INFINITY;                                       // largest term argument
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float* xk = tile + (kg + u) * PR;
-                float2 au, ar, v1, nw2;
-                smooth_dists<NORM, DP, MONO>(x2, xk, P.C, au, ar);
-                smooth_terms(z2, xk[DP], au, ar, v1, nw2, q1[u], q2[u]);
-                if (diag) {
-                    const int64_t kk = k0 + kg + u;
-                    if (kk <= ia) { q1[u].x = q2[u].x = 0.f; v1.x = nw2.x = -INFINITY; }
-                    if (kk <= ib) { q1[u].y = q2[u].y = 0.f; v1.y = nw2.y = -INFINITY; }
-                }
-                top = max3f(top, max3f(v1.x, v1.y, nw2.x), nw2.y);
-                r = add2(r, q1[u]);
-                c = add2(c, q2[u]);
-                s = fma2(q1[u], q1[u], fma2(q2[u], q2[u], s));
-            }
-            if (__any_sync(0xffffffffu, top > 0.f)) {
-                // row k is owed C_k += p1 and R_k += p2: summed over the warp's 64 rows in a
-                // fixed shuffle order, then added in fixed point by lane 0
+            float2 q[4];
+            float top = -INFINITY;
+            if (!diag) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    float cs = q1[u].x + q1[u].y, rs = q2[u].x + q2[u].y;
+                    const float* xk = tile + (kg + u) * PR;
+                    float2 au, ar;
+                    smooth_dists<NORM, DP, MONO>(x2, xk, P.C, au, ar);
+                    q[u] = smooth_q<false>(z2, xk[DP], au, ar, false, false, top);
+                }
+            } else {
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        cs += __shfl_xor_sync(0xffffffffu, cs, o);
-                        rs += __shfl_xor_sync(0xffffffffu, rs, o);
-                    }
+                for (int u = 0; u < 4; ++u) {
+                    const float* xk = tile + (kg + u) * PR;
+                    float2 au, ar;
+                    smooth_dists<NORM, DP, MONO>(x2, xk, P.C, au, ar);
                     const int64_t kk = k0 + kg + u;
-                    if ((tid & 31) == 0 && kk < P.N) {
-                        if (cs > 0.f) atomicAdd(&P.colfix[P.N + kk], __float2ull_rn(cs * fscale));
-                        if (rs > 0.f) atomicAdd(&P.colfix[kk], __float2ull_rn(rs * fscale));
-                    }
+                    q[u] = smooth_q<true>(z2, xk[DP], au, ar, kk <= ia, kk <= ib, top);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                dsum = add2(dsum, q[u]);
+                ssum = fma2(q[u], q[u], ssum);
+            }
+            if (__any_sync(0xffffffffu, top > 0.f)) {
+                // row k is owed R_k - C_k -= q: summed over the warp's 64 rows in a fixed
+                // shuffle order, then added in signed fixed point by lane 0
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float cs = q[u].x + q[u].y;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+                    const int64_t kk = k0 + kg + u;
+                    if ((tid & 31) == 0 && kk < P.N && cs != 0.f)
+                        atomicAdd(&P.colfix[kk], (unsigned long long)__float2ll_rn(-cs * fscale));
                 }
             }
         }
-        Ra += (double)r.x; Ca += (double)c.x; Sa += (double)s.x;
-        Rb += (double)r.y; Cb += (double)c.y; Sb += (double)s.y;
+        Da += (double)dsum.x; Sa += (double)ssum.x;
+        Db += (double)dsum.y; Sb += (double)ssum.y;
     }
     if (va) {
-        double* out = P.partial + ((int64_t)split * P.N + ia) * 3;
-        out[0] = Ra; out[1] = Ca; out[2] = Sa;
+        double* out = P.partial + ((int64_t)split * P.N + ia) * 2;
+        out[0] = Da; out[1] = Sa;
     }
     if (vb) {
-        double* out = P.partial + ((int64_t)split * P.N + ib) * 3;
-        out[0] = Rb; out[1] = Cb; out[2] = Sb;
+        double* out = P.partial + ((int64_t)split * P.N + ib) * 2;
+        out[0] = Db; out[1] = Sb;
     }
 }
 
@@ -222,16 +229,14 @@ __global__ void __launch_bounds__(256) smooth_finish_kernel(const SmoothParams P
     const double cscale = col_scale(P);
     double sS = 0.0, sE = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += (int64_t)gridDim.x * blockDim.x) {
-        double R = 0.0, C = 0.0, S = 0.0;
+        double D = 0.0, S = 0.0;                     // D = R_i - C_i
         for (int s = 0; s < P.nsplit; ++s) {
-            const double* v = P.partial + ((int64_t)s * P.N + i) * 3;
-            R += v[0];
-            C += v[1];
-            S += v[2];
+            const double* v = P.partial + ((int64_t)s * P.N + i) * 2;
+            D += v[0];
+            S += v[1];
         }
-        R += (double)P.colfix[i] / cscale;
-        C += (double)P.colfix[P.N + i] / cscale;
-        if (grad) grad[i] = 2.0 * eps[i] / P.p + 4.0 * (R - C);
+        D += (double)(long long)P.colfix[i] / cscale;
+        if (grad) grad[i] = 2.0 * eps[i] / P.p + 4.0 * D;
         sS += S;
         sE += eps[i] * eps[i];
     }

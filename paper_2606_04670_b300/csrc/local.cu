@@ -517,6 +517,7 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_screen_kernel(const LocalPara
         load_pairs<DP>(t2, P.rec, n, [&](int row) { return j0 + row; });
         __syncthreads();
         if (!valid) continue;
+#pragma unroll 4
         for (int p = 0; p < (n + 1) / 2; ++p) {
             const float2* x2 = t2 + p * W;
             const float2 d = dist32x2<NORM, DP>(xk2, x2);

@@ -63,7 +63,7 @@ KERNEL_DRAM_BYTES = {
     ("cluster_d16_tc", 2): 18426.68e6 + 1521.30e6,     # tc_scan_kernel<K=24, 4 parts, TF32>
     ("cluster_d16_bf16", 2): 21212.12e6 + 1781.97e6,   # tc_scan_kernel<K=32, 4 parts, BF16>
     ("local_d4", 2): 32.64e6 + 1.43e6,                 # loc_scan_kernel<L2, 4, bucket, G=2>
-    ("smooth_d4", 2): 4.63e6 + 0.0,                    # smooth_pass_kernel<L2, 4> (symmetric)
+    ("smooth_d4", 2): 4.54e6 + 40.80e6,                # smooth_pass_kernel<L2, 4> (share q, 64 splits)
     ("batch_4096", 0): 4817.68e6 + 1598.16e6,          # batch_scan_kernel
 }
 

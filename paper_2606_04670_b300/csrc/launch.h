@@ -153,7 +153,7 @@ struct LocalParams {
     uint64_t seed;
     float* rec;                      // [npad][pr = dp + 4]: w-scaled coordinates (0-padded to dp),
                                      // y, d1 (float), F (float), 0
-    float* mt;                       // [npad][LOC_KNOTS]: FP32 table (pass 1: lower bounds)
+    float* mt;                       // [npad][LOC_KNOTS]: FP32 table (the screen's lower bounds until the table)
     double* mt64;                    // [N][LOC_KNOTS]: exact table
     double* d1;                      // [N]
     double* F;                       // [N]
@@ -161,7 +161,7 @@ struct LocalParams {
     float* Tf;                       // [3][LOC_KNOTS] knots rounded to nearest, down, up
     double* raw;                     // [LOC_KNOTS] quantile picks (or the given knots)
     double* sample;                  // [S] sampled distances
-    float* ubound;                   // [N] pass-1 upper bounds of d1
+    float* ubound;                   // [N] the screen's upper bounds of d1
     unsigned* bpack;                 // [LOC_BUCKETS] bucket table: bits of the knot inside the
                                      // bucket (+inf if none), low 5 bits replaced by the count below
     int* cand;                       // [N][local_candidates()] table candidate lists

@@ -28,8 +28,8 @@
 //    nearest-neighbour candidate) or its ratio may exceed Lb_k at the lowest segment its
 //    distance may fall in.  Every other pair is ruled out, and those that are not are
 //    recomputed in FP64, so the table is the exact FP64 one.  One scan does both: a pair
-//    that passes the test against the running bounds is listed, and the list is tested
-//    again against the final bounds (loc_table_kernel).
+//    that passes the test against the running bounds is listed (loc_screen_kernel), and
+//    the list is tested again against the final bounds (loc_exact_kernel).
 // The evaluation scan runs in FP32 from the same layout; the winners are re-evaluated in
 // FP64 with the exact table.
 #include "launch.h"
@@ -612,7 +612,7 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_exact_kernel(const LocalParam
 }
 
 // The exact table of the data whose candidate lists overflowed: a full N^2 scan per datum
-// against its final bounds from loc_table_kernel, FP64 for the pairs that pass.
+// against its final bounds from loc_screen_kernel, FP64 for the pairs that pass.
 template <int NORM, int DP, bool Y64, bool BK>
 __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParams P) {
     constexpr int PR = DP + 4;

@@ -11,16 +11,17 @@
 //   Phi = ||eps||^2 / p + 2 S1,   dPhi/deps_j = 2 eps_j / p + 4 (R_j - C_j),
 //   R_j = sum_k (z_j - z_k - M dist_up(x^j, x^k))_+,  C_j = sum_i (z_i - z_j - M dist_up(x^i, x^j))_+.
 //
-// The pass visits each unordered pair {i, k} once, from row i < k: it forms v_ik (the
+// The pass visits each unordered pair {i, k} once, from row i < k.  It forms v_ik (the
 // const1 term) and v_ki (the term with i second), of which at most one is positive, adds
-// q = (v_ik)_+ - (v_ki)_+ to R_i - C_i and q^2 to the row's share of S1 without atomics, and
-// owes row k the term -q.  That column term is zero unless the pair violates the Lipschitz
-// condition, and it goes to a signed 64-bit fixed-point accumulator with integer atomics.  Integer sums do not
-// depend on the order of the atomics, so results stay reproducible; the scale 2^(61 - e)
-// with N (max z - min z) < 2^e keeps every column sum below 2^61 in magnitude.  Terms come four data
-// points at a time; one warp vote per group decides whether the warp sums the group's
-// column terms (shuffle tree in a fixed order) and lane 0 adds them, so the cost stays
-// bounded when many pairs violate (line-search trial points).
+// q = (v_ik)_+ - (v_ki)_+ to R_i - C_i and q^2 to the row's share of S1 without atomics,
+// and owes row k the term -q.  That column term is zero unless the pair violates the
+// Lipschitz condition; it goes to a signed 64-bit fixed-point accumulator with integer
+// atomics.  Integer sums do not depend on the order of the atomics, so results stay
+// reproducible; the scale 2^(61 - e) with N (max z - min z) < 2^e keeps every column sum
+// below 2^61 in magnitude.  Terms come four data points at a time: one warp vote per group
+// decides whether the warp sums the group's column terms (a shuffle tree in a fixed order)
+// for lane 0 to add, so the cost stays bounded when many pairs violate (line-search trial
+// points).
 // Pair terms are FP32 on the scaled layout (coordinates times M w, mirrored where
 // decreasing, constrained first); each thread adds them in FP32 within a 128-point tile
 // and in FP64 across tiles, and the splits are summed in FP64 in a fixed order.

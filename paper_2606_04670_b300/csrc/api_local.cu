@@ -25,8 +25,9 @@ lip_status local_buffers(lip_model* h, int64_t S, LocalParams& P) {
     const size_t b_rec = al((size_t)npad * pr * 4), b_mt = al((size_t)npad * LOC_KNOTS * 4);
     const size_t b_mt64 = al((size_t)N * LOC_KNOTS * 8), b_vec = al((size_t)N * 8);
     LIP_TRY(h->loc_buf.ensure(b_rec + b_mt + b_mt64 + 2 * b_vec, "local Lipschitz tables"));
-    const size_t b_s = al((size_t)std::max<int64_t>(S, 1) * 8), b_n = al((size_t)N * 4);
-    const size_t b_c = al((size_t)N * local_candidates() * 4);
+    // the samples and their two counts, then the screen's per-datum buffers
+    const size_t b_s = al((size_t)std::max<int64_t>(S, 1) * 8) + al((size_t)std::max<int64_t>(S, 1) * 2 * 4);
+    const size_t b_n = al((size_t)N * 4), b_c = al((size_t)N * local_candidates() * 4);
     LIP_TRY(h->loc_tmp.ensure(b_s + 3 * b_n + b_c, "local Lipschitz scratch"));
     if (!h->loc_small) {
         cudaError_t e = cudaMalloc(&h->loc_small, LOC_SMALL_BYTES);
@@ -59,6 +60,7 @@ lip_status local_buffers(lip_model* h, int64_t S, LocalParams& P) {
     P.meta = reinterpret_cast<LocMeta*>(P.Tf + 3 * LOC_KNOTS);
     P.sample = static_cast<double*>(h->loc_tmp.p);
     char* t = static_cast<char*>(h->loc_tmp.p);
+    P.counts = reinterpret_cast<int*>(t + al((size_t)std::max<int64_t>(S, 1) * 8));
     P.ubound = reinterpret_cast<float*>(t + b_s);
     P.over = reinterpret_cast<int*>(t + b_s + b_n);
     P.ncand = reinterpret_cast<int*>(t + b_s + 2 * b_n);
@@ -85,7 +87,7 @@ lip_status local_run(lip_model* h, bool sampled, int m, int64_t S, uint64_t seed
     CUDA_TRY(cudaMemcpyAsync(&meta, P.meta, sizeof meta, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     CUDA_TRY(launch_local_table(P, meta.bucket_ok != 0, meta.m, st));
-    count_launches(4 + (sampled && S > 0 ? 2 : 0));
+    count_launches(5 + (sampled && S > 0 ? 3 : 0));   // layout, knots, screen, exact, pass 2; sample, rank, pick
     CUDA_TRY(cudaMemcpyAsync(&meta, P.meta, sizeof meta, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(h->loc_T, P.T64, sizeof h->loc_T, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));

@@ -161,6 +161,7 @@ struct LocalParams {
     float* Tf;                       // [3][LOC_KNOTS] knots rounded to nearest, down, up
     double* raw;                     // [LOC_KNOTS] quantile picks (or the given knots)
     double* sample;                  // [S] sampled distances
+    int* counts;                     // [2][S] samples below / at most each sample
     float* ubound;                   // [N] the screen's upper bounds of d1
     unsigned* bpack;                 // [LOC_BUCKETS] bucket table: bits of the knot inside the
                                      // bucket (+inf if none), low 5 bits replaced by the count below

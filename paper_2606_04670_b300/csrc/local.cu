@@ -42,6 +42,7 @@ constexpr int LOC_THREADS = 128;
 constexpr int LOC_TILE = 128;       // data points per shared-memory tile (table passes)
 constexpr int LOC_SCAN_TILE = 64;   // data points per shared-memory tile (evaluation)
 constexpr int LOC_RANK_TILE = 1024;
+constexpr int LOC_RANK_SLICES = 8;  // slices of the samples per rank count (grid y)
 constexpr int LOC_CAND = 64;        // table candidates listed per datum (more: the second scan)
 constexpr int LOC_PILOT = 1024;     // strided data that warm the screen's bounds
 
@@ -165,29 +166,48 @@ __global__ void loc_sample_kernel(const LocalParams P) {
     if (dd > 0.0) atomicAdd(&P.meta->npos, 1);
 }
 
-// Rank of every positive sample among the positive samples (ties by sample index), and
-// the samples at the quantile positions ceil(i S' / m), i = 1..m, into raw[i - 1].
+// For every sample v, #{u < v} and #{u <= v} over the samples (zeros included), counted over
+// LOC_RANK_SLICES slices of the samples (grid y) and added atomically.  Positive doubles
+// order as their bit patterns.
 __global__ void __launch_bounds__(LOC_THREADS) loc_rank_kernel(const LocalParams P) {
     __shared__ unsigned long long tile[LOC_RANK_TILE];
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long v = s < P.S ? (unsigned long long)__double_as_longlong(P.sample[s]) : 0ull;
-    int64_t rank = 0;
-    for (int64_t t0 = 0; t0 < P.S; t0 += LOC_RANK_TILE) {
-        const int n = (int)lmin(LOC_RANK_TILE, P.S - t0);
+    const int64_t span = (P.S + gridDim.y - 1) / gridDim.y;
+    const int64_t t_begin = (int64_t)blockIdx.y * span, t_end = lmin(t_begin + span, P.S);
+    int lt = 0, le = 0;
+    for (int64_t t0 = t_begin; t0 < t_end; t0 += LOC_RANK_TILE) {
+        const int n = (int)lmin(LOC_RANK_TILE, t_end - t0);
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x)
             tile[i] = (unsigned long long)__double_as_longlong(P.sample[t0 + i]);
         __syncthreads();
-        // positive doubles order as their bit patterns; 0 (bits 0) is not a sample
         for (int i = 0; i < n; ++i) {
             const unsigned long long u = tile[i];
-            rank += (u != 0ull && (u < v || (u == v && t0 + i < s))) ? 1 : 0;
+            lt += u < v ? 1 : 0;
+            le += u <= v ? 1 : 0;
         }
     }
     if (s >= P.S || v == 0ull) return;
-    const int64_t npos = P.meta->npos;
-    for (int i = 1; i <= P.m; ++i)
-        if (((int64_t)i * npos + P.m - 1) / P.m - 1 == rank) P.raw[i - 1] = __longlong_as_double((long long)v);
+    atomicAdd(&P.counts[s], lt);
+    atomicAdd(&P.counts[P.S + s], le);
+}
+
+// The samples at the quantile positions ceil(i S' / m), i = 1..m, of the positive samples
+// (S' of them) into raw[i - 1].  The sample at 0-based position p is any v with
+// #{0 < u < v} <= p < #{0 < u <= v}: all such samples are equal, so whichever writes, the
+// bits are the same.
+__global__ void loc_pick_kernel(const LocalParams P) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= P.S) return;
+    const double v = P.sample[s];
+    if (!(v > 0.0)) return;
+    const int64_t npos = P.meta->npos, nzero = P.S - npos;
+    const int64_t lt = P.counts[s] - nzero, le = P.counts[P.S + s] - nzero;
+    for (int i = 1; i <= P.m; ++i) {
+        const int64_t p = ((int64_t)i * npos + P.m - 1) / P.m - 1;
+        if (lt <= p && p < le) P.raw[i - 1] = v;
+    }
 }
 
 // Distinct knots (raw is non-decreasing) into T64, padded with +inf, and their float
@@ -1018,7 +1038,12 @@ cudaError_t launch_local_knots(const LocalParams& P, bool sampled, cudaStream_t 
         loc_sample_kernel<<<blocks, LOC_THREADS, 0, st>>>(P);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        loc_rank_kernel<<<blocks, LOC_THREADS, 0, st>>>(P);
+        e = cudaMemsetAsync(P.counts, 0, (size_t)P.S * 2 * sizeof(int), st);
+        if (e != cudaSuccess) return e;
+        loc_rank_kernel<<<dim3(blocks, LOC_RANK_SLICES), LOC_THREADS, 0, st>>>(P);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        loc_pick_kernel<<<blocks, LOC_THREADS, 0, st>>>(P);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

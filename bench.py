@@ -60,8 +60,6 @@ KERNEL_DRAM_BYTES = {
     ("monotone_d4", 2): 19.136000e6 + 11.619840e6,     # scan_exact_kernel<L2, C=2, U=2, R=4>
     ("grad_d8", 2): 16.66e6 + 13.47e6,                 # scan_exact_kernel<L2, C=4, U=4, R=2>
     ("cluster_d16", 2): 618.02e6 + 185.20e6,           # scan_exact_kernel<L2, C=0, U=16, R=2>
-    ("cluster_d16_tc", 2): 18426.68e6 + 1521.30e6,     # tc_scan_kernel<K=24, 4 parts, TF32>
-    ("cluster_d16_bf16", 2): 21212.12e6 + 1781.97e6,   # tc_scan_kernel<K=32, 4 parts, BF16>
     ("local_d4", 2): 32.64e6 + 1.43e6,                 # loc_scan_kernel<L2, 4, bucket, G=2>
     ("smooth_d4", 2): 4.54e6 + 40.80e6,                # smooth_pass_kernel<L2, 4> (share q, 64 splits)
     ("batch_4096", 0): 4817.68e6 + 1598.16e6,          # batch_scan_kernel
@@ -477,7 +475,6 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
                 "peak_source": ("measured bf16 dense peak of MEASURED_PEAKS.json" if bf else
                                 "measured bf16 dense peak of MEASURED_PEAKS.json x 1.1/2.25 (nominal TF32/BF16)"),
                 "flops_per_pair": 2 * npass * kk,
-                "mufu": ctx.mufu_bound(p.nq * p.N / (avg[kdom] / 1e3), 1),
                 "alu_view": {k: alu[k] for k in ("achieved", "peak", "frac", "i_pair")}}
 
     e2e = None

@@ -122,6 +122,7 @@ struct lip_model {
     double* tc_stats = nullptr;        // [D_MAX] sums of the scaled coordinates
     unsigned* tc_maxbits = nullptr;    // [2] max |x^|, max |y| (float bits)
     Scratch tc_q, tc_fb;
+    Scratch tc_order;                  // the data's spatial order and position-ordered copies
     int64_t last_fallback = 0;
     // local Lipschitz constants (Sec. 4.3), valid until the data change
     bool loc_valid = false;

@@ -116,6 +116,9 @@ struct TcPrepParams {
     char* tiles;          // [ntiles][tile_bytes]
     int64_t ntiles;
     bool bf;              // BF16 pieces instead of TF32
+    const int* perm;      // [N] position -> data index (tiles are in position order)
+    float* Xs;            // [N][d] position-ordered copy of the data
+    float* ys;            // [N]
 };
 
 __global__ void tc_sum_kernel(const TcPrepParams P) {
@@ -129,7 +132,8 @@ __global__ void tc_sum_kernel(const TcPrepParams P) {
     if (threadIdx.x < P.d) atomicAdd(&P.stats[threadIdx.x], acc[threadIdx.x]);
 }
 
-// One thread per (padded) data point: its row of the B pieces and y in the tile layout.
+// One thread per (padded) position: the row of the B pieces and y of the datum at that
+// position, in the tile layout, and the position-ordered copy of its row.
 template <bool BF>
 __global__ void tc_build_b_kernel(const TcPrepParams P) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -143,16 +147,20 @@ __global__ void tc_build_b_kernel(const TcPrepParams P) {
     for (int j = 0; j < P.K; ++j) b[j] = 0.f;
     float yy = __int_as_float(0x7fc00000);
     if (k < P.N) {
+        const int64_t src = P.perm[k];
         double n2 = 0.0;
         for (int j = 0; j < P.d; ++j) {
+            const float x = P.X0[src * P.d + j];
+            P.Xs[k * P.d + j] = x;
             const double c = P.stats[j] / (double)P.N;
-            const float xh = (float)(P.scale[j] * (double)P.X0[k * P.d + j] - c);
+            const float xh = (float)(P.scale[j] * (double)x - c);
             b[j] = xh;
             n2 += (double)xh * (double)xh;
         }
         b[P.d] = (float)n2;
         b[P.d + 1] = 1.f;
-        yy = P.y0[k];
+        yy = P.y0[src];
+        P.ys[k] = yy;
         atomicMax(&P.maxbits[0], __float_as_uint((float)sqrt(n2)));
         atomicMax(&P.maxbits[1], __float_as_uint(fabsf(yy)));
     }
@@ -160,8 +168,23 @@ __global__ void tc_build_b_kernel(const TcPrepParams P) {
     yv[r] = yy;
 }
 
+// (min y, max y) of each 32-position chunk (NaN if it holds no datum): the epilogue's
+// chunk bounds.
+__global__ void tc_chunk_bounds_kernel(const float* ys, int64_t N, int64_t nchunks, float2* cb) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nchunks) return;
+    const float nan = __int_as_float(0x7fc00000);
+    float lo = nan, hi = nan;
+    for (int64_t k = c * 32; k < c * 32 + 32 && k < N; ++k) {
+        lo = fminf(lo, ys[k]);        // NaN operands are ignored
+        hi = fmaxf(hi, ys[k]);
+    }
+    cb[c] = make_float2(lo, hi);
+}
+
 struct TcQueryParams {
     const float* Q;        // caller's queries [nq][d]
+    const int* qperm;      // [nq] position -> query index (tiles are in position order)
     int64_t nq;
     int d, K;
     double scale[D_MAX];
@@ -185,10 +208,11 @@ __global__ void tc_build_a_kernel(const TcQueryParams P) {
     float a[32];
     for (int j = 0; j < P.K; ++j) a[j] = 0.f;
     if (qi < P.nq) {
+        const int64_t src = P.qperm[qi];
         double n2 = 0.0;
         for (int j = 0; j < P.d; ++j) {
             const double c = P.stats[j] / (double)P.N;
-            const float qh = (float)(P.scale[j] * (double)P.Q[qi * P.d + j] - c);
+            const float qh = (float)(P.scale[j] * (double)P.Q[src * P.d + j] - c);
             a[j] = -2.f * qh;
             n2 += (double)qh * (double)qh;
         }
@@ -286,9 +310,10 @@ struct TcScanParams {
     const char* atiles;
     const char* btiles;
     const float2* eps;
+    const float2* cbound;  // [ntiles * TC_N / 32] (min y, max y) per chunk
     int64_t nq;
     int64_t ntiles;
-    TcRec* rec;            // [nq][2 bounds][2 halves]
+    TcRec* rec;            // [nq positions][2 bounds][TC_MAX_PARTS column slices]
     unsigned* err;
 };
 
@@ -440,15 +465,29 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int col = col0 + h * 32;
-                    // four interleaved partial extrema per chunk keep the dependent chains short
-                    float cs[4], cu[4], cl[4];
+                    const int chunk = (int)(t * (TC_N / 32) + col / 32);
+                    // the chunk's smallest s~, then its bounds test: no square root unless
+                    // some query of the warp may find an extremum in it
+                    float cs[4];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) { cs[a] = INF; cu[a] = INF; cl[a] = -INF; }
+                    for (int a = 0; a < 4; ++a) cs[a] = INF;
+#pragma unroll
+                    for (int e = 0; e < 32; e += 4)
+                        cs[(e / 4) % 4] = min3f(min3f(cs[(e / 4) % 4], sv[h][e], sv[h][e + 1]), sv[h][e + 2], sv[h][e + 3]);
+                    const float csm = min2f(min3f(cs[0], cs[1], cs[2]), cs[3]);
+                    const float2 cb = __ldg(&P.cbound[chunk]);
+                    const float slo = sqrt_approx(fmaxf(csm - eps, 0.f) * (1.f - 0x1p-22f)) * (1.f - 0x1p-21f);
+                    const float lbu = (cb.x + slo) - 0x1p-22f * (fabsf(cb.x) + slo);
+                    const float ubl = (cb.y - slo) + 0x1p-22f * (fabsf(cb.y) + slo);
+                    if (!__any_sync(0xffffffffu, valid && (lbu <= U || ubl >= Bl))) continue;
+                    // four interleaved partial extrema per chunk keep the dependent chains short
+                    float cu[4], cl[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) { cu[a] = INF; cl[a] = -INF; }
 #pragma unroll
                     for (int e = 0; e < 32; e += 4) {
                         const int a = (e / 4) % 4;
                         const float4 y4 = *reinterpret_cast<const float4*>(ys + col + e);
-                        cs[a] = min3f(min3f(cs[a], sv[h][e], sv[h][e + 1]), sv[h][e + 2], sv[h][e + 3]);
                         const float2 r0 = make_float2(sqrt_approx(fabsf(sv[h][e])), sqrt_approx(fabsf(sv[h][e + 1])));
                         const float2 r1 = make_float2(sqrt_approx(fabsf(sv[h][e + 2])), sqrt_approx(fabsf(sv[h][e + 3])));
                         const float2 y0 = make_float2(y4.x, y4.y), y1 = make_float2(y4.z, y4.w);
@@ -456,12 +495,10 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                         cu[a] = min3f(min3f(cu[a], u0.x, u0.y), u1.x, u1.y);
                         cl[a] = max3f(max3f(cl[a], l0.x, l0.y), l1.x, l1.y);
                     }
-                    const float csm = min2f(min3f(cs[0], cs[1], cs[2]), cs[3]);
                     const float cum = min2f(min3f(cu[0], cu[1], cu[2]), cu[3]);
                     const float clm = max2f(max3f(cl[0], cl[1], cl[2]), cl[3]);
                     if (valid) {
                         const float dlt = 1.001f * eps * rsqrt_approx(fmaxf(csm, eps)) + epsv;
-                        const int chunk = (int)(t * (TC_N / 32) + col / 32);
                         U = fminf(U, cum + dlt);
                         if (cum - dlt <= U) tc_append(Ru, nu, chunk, cum - dlt, U, true);
                         Bl = fmaxf(Bl, clm - dlt);
@@ -496,6 +533,10 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
 struct TcRescreenParams {
     int parts;              // candidate lists per (query, bound) that the scan filled
     const float* Q;
+    const int* qperm;       // [nq] query position -> query index
+    const int* dperm;       // [N] data position -> data index
+    const float* Xs;        // [N][d] data rows in position order
+    const float* ys;        // [N]
     int64_t nq;
     int d;
     double M;
@@ -534,13 +575,14 @@ __device__ __forceinline__ bool tc_better(int side, double v, int k, double bv, 
 // extremum, and only those points are re-evaluated in FP64.  FP32 error of
 // y +- M |diag(w)(q - x)|_2 with correctly rounded sqrt: at most (d + 10) 2^-24 (r + |y|).
 __global__ void tc_rescreen_kernel(const TcRescreenParams P) {
-    const int64_t qi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int64_t pos = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;   // query position
     const int lane = threadIdx.x % 32;
-    if (qi >= P.nq) return;
+    if (pos >= P.nq) return;
+    const int64_t qi = P.qperm[pos];
     const float* q = P.Q + qi * P.d;
     bool finite = true;
     for (int i = 0; i < P.d; ++i) finite = finite && isfinite(q[i]);
-    const TcRec* R = P.rec + qi * 2 * TC_MAX_PARTS;
+    const TcRec* R = P.rec + pos * 2 * TC_MAX_PARTS;
     bool over = false;
     for (int b = 0; b < 2; ++b)
         for (int h = 0; h < P.parts; ++h) over = over || R[b * TC_MAX_PARTS + h].n < 0;
@@ -568,17 +610,17 @@ __global__ void tc_rescreen_kernel(const TcRescreenParams P) {
                 const TcRec& r = R[b * TC_MAX_PARTS + h];
                 for (int e = 0; e < r.n; ++e) {
                     if (b == 0 ? !(r.L[e] <= bound) : !(r.L[e] >= bound)) continue;   // warp-uniform
-                    const int64_t k = (int64_t)r.id[e] * 32 + lane;
+                    const int64_t k = (int64_t)r.id[e] * 32 + lane;      // data position
                     const bool in = k < P.N;
                     float v32 = b == 0 ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000), err = 0.f;
                     if (in) {
-                        const float* x = P.X0 + k * P.d;
+                        const float* x = P.Xs + k * P.d;
                         float acc = 0.f;
                         for (int i = 0; i < P.d; ++i) {
                             const float t = (qs[i] - x[i]) * sc[i];
                             acc = fmaf(t, t, acc);
                         }
-                        const float rr = sqrtf(acc), yy = P.y0[k];
+                        const float rr = sqrtf(acc), yy = P.ys[k];
                         v32 = b == 0 ? yy + rr : yy - rr;
                         err = erel * (rr + fabsf(yy));
                     }
@@ -591,9 +633,12 @@ __global__ void tc_rescreen_kernel(const TcRescreenParams P) {
                     }
                     const bool cand = in && (b == 0 ? v32 <= ext + 2.f * emax : v32 >= ext - 2.f * emax);
                     if (cand) {
-                        const double dist = P.M * tc_dist64(P, q, P.X0 + k * P.d);
-                        const double v = b == 0 ? (double)P.y0[k] + dist : (double)P.y0[k] - dist;
-                        if (tc_better(b, v, (int)k, bv, bk)) { bv = v; bk = (int)k; }
+                        // the position-ordered copy holds the caller's values; ties go to
+                        // the lowest data index
+                        const double dist = P.M * tc_dist64(P, q, P.Xs + k * P.d);
+                        const double v = b == 0 ? (double)P.ys[k] + dist : (double)P.ys[k] - dist;
+                        const int ko = P.dperm[k];
+                        if (tc_better(b, v, ko, bv, bk)) { bv = v; bk = ko; }
                     }
                 }
             }
@@ -646,8 +691,15 @@ size_t tc_tile_bytes_for(int d, bool bf) { return (size_t)tc_tile_bytes(tc_k_for
 size_t tc_a_bytes_for(int d, bool bf) { return (size_t)tc_a_bytes(tc_k_for_dim(d, bf), bf); }
 size_t tc_rec_bytes() { return sizeof(TcRec) * 2 * TC_MAX_PARTS; }   // candidate lists per query
 
+int tc_chunks_per_tile() { return TC_N / 32; }
+
+// The data's spatial order, then the tiles in that order, the position-ordered copies and
+// the chunk bounds.
 cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, const double* scale, double* stats,
-                            unsigned* maxbits, char* tiles, int64_t ntiles, bool bf, cudaStream_t st) {
+                            unsigned* maxbits, char* tiles, int64_t ntiles, bool bf, const TcDataOrder& O,
+                            cudaStream_t st) {
+    cudaError_t e = spatial_order(X0, N, d, O.dperm, O.scratch, st);
+    if (e != cudaSuccess) return e;
     TcPrepParams P{};
     P.X0 = X0;
     P.y0 = y0;
@@ -660,7 +712,10 @@ cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, 
     P.maxbits = maxbits;
     P.tiles = tiles;
     P.ntiles = ntiles;
-    cudaError_t e = cudaMemsetAsync(stats, 0, D_MAX * sizeof(double), st);
+    P.perm = O.dperm;
+    P.Xs = O.Xs;
+    P.ys = O.ys;
+    e = cudaMemsetAsync(stats, 0, D_MAX * sizeof(double), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(maxbits, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     if (N > 0) tc_sum_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(P);
@@ -668,6 +723,8 @@ cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, 
     if (rows > 0) {
         if (bf) tc_build_b_kernel<true><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P);
         else tc_build_b_kernel<false><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P);
+        const int64_t nchunks = ntiles * (TC_N / 32);
+        tc_chunk_bounds_kernel<<<(unsigned)((nchunks + 255) / 256), 256, 0, st>>>(O.ys, N, nchunks, O.cbound);
     }
     return cudaGetLastError();
 }
@@ -698,12 +755,16 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
                            const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float2* eps,
                            void* rec, const double* w, double M, const float* X0, const float* y0, float* g, float* lo,
                            float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, unsigned* err,
-                           int variant, bool bf, cudaStream_t st) {
+                           int variant, bool bf, const TcDataOrder& O, const TcQueryOrder& QO, cudaStream_t st) {
     const int K = tc_k_for_dim(d, bf);
+    // the queries' spatial order: a tile of 128 positions holds nearby queries
+    cudaError_t e = spatial_order(Q, nq, d, QO.qperm, QO.scratch, st);
+    if (e != cudaSuccess) return e;
     const int parts = variant == 1 ? 2 : 4;   // variant 0: 16 epilogue warps, 1: 8
     const int64_t nqt = (nq + TC_M - 1) / TC_M;
     TcQueryParams A{};
     A.Q = Q;
+    A.qperm = QO.qperm;
     A.nq = nq;
     A.d = d;
     A.K = K;
@@ -715,12 +776,13 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     A.eps = eps;
     if (bf) tc_build_a_kernel<true><<<(unsigned)((nqt * TC_M + 255) / 256), 256, 0, st>>>(A);
     else tc_build_a_kernel<false><<<(unsigned)((nqt * TC_M + 255) / 256), 256, 0, st>>>(A);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     TcScanParams S{};
     S.atiles = atiles;
     S.btiles = btiles;
     S.eps = eps;
+    S.cbound = O.cbound;
     S.nq = nq;
     S.ntiles = ntiles;
     S.rec = static_cast<TcRec*>(rec);
@@ -731,6 +793,10 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     TcRescreenParams R{};
     R.parts = parts;
     R.Q = Q;
+    R.qperm = QO.qperm;
+    R.dperm = O.dperm;
+    R.Xs = O.Xs;
+    R.ys = O.ys;
     R.nq = nq;
     R.d = d;
     R.M = M;

@@ -60,6 +60,8 @@ KERNEL_DRAM_BYTES = {
     ("monotone_d4", 2): 19.136000e6 + 11.619840e6,     # scan_exact_kernel<L2, C=2, U=2, R=4>
     ("grad_d8", 2): 16.66e6 + 13.47e6,                 # scan_exact_kernel<L2, C=4, U=4, R=2>
     ("cluster_d16", 2): 618.02e6 + 185.20e6,           # scan_exact_kernel<L2, C=0, U=16, R=2>
+    ("cluster_d16_tc", 2): 12726.69e6 + 1268.34e6,     # tc_scan_kernel<K=24, 4 parts, TF32> (spatial order)
+    ("cluster_d16_bf16", 2): 11715.55e6 + 1336.01e6,   # tc_scan_kernel<K=32, 4 parts, BF16> (spatial order)
     ("local_d4", 2): 32.64e6 + 1.43e6,                 # loc_scan_kernel<L2, 4, bucket, G=2>
     ("smooth_d4", 2): 4.54e6 + 40.80e6,                # smooth_pass_kernel<L2, 4> (share q, 64 splits)
     ("batch_4096", 0): 4817.68e6 + 1598.16e6,          # batch_scan_kernel

@@ -60,8 +60,8 @@ KERNEL_DRAM_BYTES = {
     ("monotone_d4", 2): 19.136000e6 + 11.619840e6,     # scan_exact_kernel<L2, C=2, U=2, R=4>
     ("grad_d8", 2): 16.66e6 + 13.47e6,                 # scan_exact_kernel<L2, C=4, U=4, R=2>
     ("cluster_d16", 2): 618.02e6 + 185.20e6,           # scan_exact_kernel<L2, C=0, U=16, R=2>
-    ("cluster_d16_tc", 2): 12726.69e6 + 1268.34e6,     # tc_scan_kernel<K=24, 4 parts, TF32> (spatial order)
-    ("cluster_d16_bf16", 2): 11715.55e6 + 1336.01e6,   # tc_scan_kernel<K=32, 4 parts, BF16> (spatial order)
+    ("cluster_d16_tc", 2): 141000.57e6 + 3419.05e6,    # tc_scan_kernel<K=16, 4 parts, TF32> (norm block, 4 stages)
+    ("cluster_d16_bf16", 2): 84545.86e6 + 2910.17e6,   # tc_scan_kernel<K=16, 4 parts, BF16> (norm block, 4 stages)
     ("local_d4", 2): 32.64e6 + 1.43e6,                 # loc_scan_kernel<L2, 4, bucket, G=2>
     ("smooth_d4", 2): 4.54e6 + 40.80e6,                # smooth_pass_kernel<L2, 4> (share q, 64 splits)
     ("batch_4096", 0): 4817.68e6 + 1598.16e6,          # batch_scan_kernel
@@ -463,9 +463,9 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
                         traffic_for(args, name, p.norm) if rd["prec"] == "fp32" else None)
     if rd["prec"] in ("tc_tf32", "tc_bf16"):
         bf = rd["prec"] == "tc_bf16"
-        # tensor-core form: three TF32 products over K = 8 ceil((d + 2) / 8), or six BF16
-        # products over K = 16 ceil((d + 2) / 16), per pair
-        kk = 16 * ((p.d + 2 + 15) // 16) if bf else 8 * ((p.d + 2 + 7) // 8)
+        # tensor-core form: the cross product only (the norms are added in the epilogue),
+        # three TF32 products over K = 8 ceil(d / 8), or six BF16 products over K = 16, per pair
+        kk = 16 * ((p.d + 15) // 16) if bf else 8 * ((p.d + 7) // 8)
         npass = 6 if bf else 3
         flops = 2.0 * npass * kk * p.nq * p.N
         peak = float(ctx.peaks.get("bf16_tflops", 1800.0)) * (1.0 if bf else TF32_OVER_BF16) * 1e12

@@ -116,7 +116,6 @@ void free_model(lip_model* h) {
     h->tc_order.release();
     h->tc_fb.release();
     if (h->tc_btiles) cudaFree(h->tc_btiles);
-    if (h->tc_stats) cudaFree(h->tc_stats);
     if (h->tc_maxbits) cudaFree(h->tc_maxbits);
     h->loc_buf.release();
     h->loc_tmp.release();
@@ -240,7 +239,6 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
         struct { void** p; size_t n; const char* what; } tca[] = {
             {reinterpret_cast<void**>(&h->tc_btiles), (size_t)h->tc_ntiles_cap * tc_tile_bytes_for(d, h->tc_bf),
              "tensor-core data tiles"},
-            {reinterpret_cast<void**>(&h->tc_stats), D_MAX * sizeof(double), "tensor-core centre"},
             {reinterpret_cast<void**>(&h->tc_maxbits), 2 * sizeof(unsigned), "tensor-core bounds"},
         };
         for (auto& a : tca) {
@@ -411,21 +409,20 @@ lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, v
     for (int j = 0; j < D_MAX; ++j) scale[j] = j < d ? h->M * h->w[j] : 0.0;
     const int64_t ntiles = ceil_div(h->N, 256);
     // the data's spatial order and its position-ordered copies (kept with the handle)
-    const int64_t nchunks = ntiles * tc_chunks_per_tile();
     const size_t p_b = round_up(h->N * 4, 256), x_b = round_up(h->N * d * 4, 256), y_b = round_up(h->N * 4, 256),
-                 c_b = round_up(nchunks * 8, 256);
-    LIP_TRY(h->tc_order.ensure(p_b + x_b + y_b + c_b + spatial_order_scratch(h->N), "tensor-core data order"));
+                 b_b = round_up(D_MAX * 8, 256);
+    LIP_TRY(h->tc_order.ensure(p_b + x_b + y_b + b_b + spatial_order_scratch(h->N), "tensor-core data order"));
     char* ob = static_cast<char*>(h->tc_order.p);
     TcDataOrder O{};
     O.dperm = reinterpret_cast<int*>(ob);
     O.Xs = reinterpret_cast<float*>(ob + p_b);
     O.ys = reinterpret_cast<float*>(ob + p_b + x_b);
-    O.cbound = reinterpret_cast<float2*>(ob + p_b + x_b + y_b);
-    O.scratch = ob + p_b + x_b + y_b + c_b;
+    O.bounds = reinterpret_cast<float2*>(ob + p_b + x_b + y_b);
+    O.scratch = ob + p_b + x_b + y_b + b_b;
     if (h->tc_dirty) {
         CUDA_TRY(tc_prepare_data(static_cast<const float*>(h->X0), static_cast<const float*>(h->y0), h->N, d, scale,
-                                 h->tc_stats, h->tc_maxbits, h->tc_btiles, ntiles, h->tc_bf, O, st));
-        count_launches(3 + spatial_order_launches());
+                                 h->tc_maxbits, h->tc_btiles, ntiles, h->tc_bf, O, st));
+        count_launches(2 + spatial_order_launches());
         h->tc_dirty = false;
     }
     const int64_t nqt = ceil_div(nq, 128);
@@ -440,7 +437,7 @@ lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, v
     QO.qperm = reinterpret_cast<int*>(base + a_b + eps_b + rec_b + list_b);
     QO.scratch = base + a_b + eps_b + rec_b + list_b + qp_b;
     if (h->ev_scan0) CUDA_TRY(cudaEventRecord(h->ev_scan0, st));
-    CUDA_TRY(tc_eval_launch(static_cast<const float*>(Q), nq, d, scale, h->tc_stats, h->N, h->tc_maxbits, h->tc_btiles,
+    CUDA_TRY(tc_eval_launch(static_cast<const float*>(Q), nq, d, scale, h->N, h->tc_maxbits, h->tc_btiles,
                             ntiles, base, reinterpret_cast<float2*>(base + a_b), base + a_b + eps_b, h->w, h->M,
                             static_cast<const float*>(h->X0), static_cast<const float*>(h->y0), static_cast<float*>(g),
                             static_cast<float*>(lo), static_cast<float*>(hi), iu, il, fb_count, fb_list, h->status,

@@ -82,7 +82,9 @@ size_t tc_rec_bytes();
 // Spatial order of n points (row-major [n][d]): perm[position] = index, by a 16-bit Morton
 // key of the first min(d, 16) coordinates and a stable radix sort (deterministic).
 size_t spatial_order_scratch(int64_t n);
-cudaError_t spatial_order(const float* X, int64_t n, int d, int* perm, void* scratch, cudaStream_t st);
+// bounds (nullable): [d] (min, max) of each coordinate's finite values, (0, 0) when none.
+cudaError_t spatial_order(const float* X, int64_t n, int d, int* perm, float2* bounds, void* scratch,
+                          cudaStream_t st);
 int spatial_order_launches();
 // The tensor-core form's data in spatial order (spatial_order of the data): tiles are
 // built in position order, and the rescreen reads the position-ordered copies.
@@ -90,19 +92,17 @@ struct TcDataOrder {
     int* dperm;                      // [N] position -> data index
     float* Xs;                       // [N][d] the data rows in position order
     float* ys;                       // [N]
-    float2* cbound;                  // [ntiles * chunks per tile] (min y, max y) of each
-                                     // 32-position chunk, NaN when it holds no datum
+    float2* bounds;                  // [D_MAX] the data's bounding box, the centring of the pieces
     void* scratch;                   // spatial_order_scratch(N)
 };
 struct TcQueryOrder {
     int* qperm;                      // [nq] position -> query index
     void* scratch;                   // spatial_order_scratch(nq)
 };
-cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, const double* scale, double* stats,
+cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, const double* scale,
                             unsigned* maxbits, char* tiles, int64_t ntiles, bool bf, const TcDataOrder& O,
                             cudaStream_t st);
-int tc_chunks_per_tile();
-cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scale, const double* stats, int64_t N,
+cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scale, int64_t N,
                            const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float2* eps,
                            void* rec, const double* w, double M, const float* X0, const float* y0, float* g, float* lo,
                            float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, unsigned* err,

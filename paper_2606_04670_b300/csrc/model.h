@@ -119,7 +119,6 @@ struct lip_model {
     int tc_variant = 0;                // 0: 16 epilogue warps, 1: 8
     int64_t tc_ntiles_cap = 0;
     char* tc_btiles = nullptr;
-    double* tc_stats = nullptr;        // [D_MAX] sums of the scaled coordinates
     unsigned* tc_maxbits = nullptr;    // [2] max |x^|, max |y| (float bits)
     Scratch tc_q, tc_fb;
     Scratch tc_order;                  // the data's spatial order and position-ordered copies

@@ -4,16 +4,20 @@
 // position -> index.  Points close in space get close positions, so consecutive runs of
 // points are spatially coherent.  Every step is deterministic: counts are atomics on
 // integers, the scan has a fixed shape, and within a block the scatter ranks equal digits
-// by warp, then lane, which is index order.
+// by sub-tile, then warp, then lane, which is index order.
 #include "launch.h"
 
 namespace lip {
 
 namespace {
 
-constexpr int ORD_THREADS = 256;     // elements per block in the radix passes
+constexpr int ORD_THREADS = 256;                    // threads per block in the radix passes
 constexpr int ORD_WARPS = ORD_THREADS / 32;
+constexpr int ORD_SUB = 16;                         // 256-key sub-tiles per block, in index order
+constexpr int ORD_TILE = ORD_THREADS * ORD_SUB;     // keys per block
 constexpr int ORD_BINS = 256;
+constexpr int ORD_BOX_BLOCKS = 296;                 // grid of the bounding-box pass (2 per SM)
+constexpr int ORD_SCAN_THREADS = 1024;              // the one-block scan, 4 entries per thread
 
 __device__ __forceinline__ unsigned ord_key_bits(float f) {
     const unsigned u = __float_as_uint(f);
@@ -23,27 +27,57 @@ __device__ __forceinline__ float ord_key_float(unsigned o) {
     return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
 }
 
-// Per-coordinate bounding box of the finite coordinates (order-preserving bits).
-__global__ void ord_bbox_kernel(const float* X, int64_t n, int d, unsigned* box) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int j = 0; j < d && j < 16; ++j) {
-        const float v = X[i * d + j];
-        if (!isfinite(v)) continue;
-        atomicMin(&box[j], ord_key_bits(v));
-        atomicMax(&box[16 + j], ord_key_bits(v));
+// Per-coordinate bounding box of the finite coordinates (order-preserving bits):
+// box[j] = min, box[D_MAX + j] = max.  The grid strides over the row-major array with
+// `per` = d * floor(256 / d) threads a block, so thread t always sees coordinate t % d and
+// the loads are coalesced; a block folds its threads' extrema per coordinate, then one
+// atomic per coordinate and block.
+__global__ void __launch_bounds__(ORD_THREADS) ord_bbox_kernel(const float* X, int64_t n, int d, unsigned* box) {
+    __shared__ unsigned slo[ORD_THREADS], shi[ORD_THREADS];
+    const int per = ORD_THREADS / d * d;
+    const int t = threadIdx.x;
+    unsigned lo = 0xffffffffu, hi = 0u;
+    if (t < per) {
+        const int64_t total = n * d, stride = (int64_t)gridDim.x * per;
+#pragma unroll 4
+        for (int64_t e = (int64_t)blockIdx.x * per + t; e < total; e += stride) {
+            const float v = X[e];
+            if (isfinite(v)) {
+                const unsigned k = ord_key_bits(v);
+                lo = min(lo, k);
+                hi = max(hi, k);
+            }
+        }
+    }
+    slo[t] = lo;
+    shi[t] = hi;
+    __syncthreads();
+    if (t < d) {
+        for (int s = t + d; s < per; s += d) {
+            lo = min(lo, slo[s]);
+            hi = max(hi, shi[s]);
+        }
+        atomicMin(&box[t], lo);
+        atomicMax(&box[D_MAX + t], hi);
     }
 }
 
-__global__ void ord_key_kernel(const float* X, int64_t n, int d, const unsigned* box, unsigned* keys, int* idx) {
+// The Morton key of each point.  Block 0 also writes the box as floats, (0, 0) for a
+// coordinate with no finite value.
+__global__ void ord_key_kernel(const float* X, int64_t n, int d, const unsigned* box, unsigned* keys, int* idx,
+                               float2* bounds) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (bounds && blockIdx.x == 0 && threadIdx.x < d) {
+        const unsigned a = box[threadIdx.x], b = box[D_MAX + threadIdx.x];
+        bounds[threadIdx.x] = a <= b ? make_float2(ord_key_float(a), ord_key_float(b)) : make_float2(0.f, 0.f);
+    }
     if (i >= n) return;
     const int D = d < 16 ? d : 16;
     const int b = 16 / D;                          // bits per coordinate
     const int cells = 1 << b;
     int cell[16];
     for (int j = 0; j < D; ++j) {
-        const float lo = ord_key_float(box[j]), hi = ord_key_float(box[16 + j]);
+        const float lo = ord_key_float(box[j]), hi = ord_key_float(box[D_MAX + j]);
         const float v = X[i * d + j];
         int c = 0;
         if (isfinite(v) && hi > lo) {
@@ -59,108 +93,152 @@ __global__ void ord_key_kernel(const float* X, int64_t n, int d, const unsigned*
     idx[i] = (int)i;
 }
 
-// Digit counts per block, stored digit-major: table[digit * nblocks + block].
+// Digit counts per block of ORD_TILE keys, stored digit-major: table[digit * nblocks +
+// block].  Lanes with equal digits add once per warp (their leader adds the group's size).
 __global__ void __launch_bounds__(ORD_THREADS) ord_hist_kernel(const unsigned* keys, int64_t n, int shift,
                                                               int* table, int nblocks) {
-    __shared__ int cnt[ORD_BINS];
+    __shared__ int cnt[ORD_BINS + 1];
     cnt[threadIdx.x] = 0;
+    if (threadIdx.x == 0) cnt[ORD_BINS] = 0;
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * ORD_THREADS + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 0xffu], 1);
+    const int lane = threadIdx.x % 32;
+    const int64_t base = (int64_t)blockIdx.x * ORD_TILE;
+    for (int s = 0; s < ORD_SUB; ++s) {
+        const int64_t i = base + (int64_t)s * ORD_THREADS + threadIdx.x;
+        const int digit = i < n ? (int)((keys[i] >> shift) & 0xffu) : ORD_BINS;
+        const unsigned peers = __match_any_sync(0xffffffffu, digit);
+        if (lane == __ffs(peers) - 1) atomicAdd(&cnt[digit], __popc(peers));
+    }
     __syncthreads();
     table[(int64_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Exclusive prefix sums of the table in place (one block; each thread takes a contiguous
-// run, then the runs' totals are scanned).
-__global__ void __launch_bounds__(1024) ord_scan_kernel(int* table, int64_t total) {
-    __shared__ int part[1024];
-    const int t = threadIdx.x;
-    const int64_t per = (total + 1023) / 1024;
-    const int64_t a = (int64_t)t * per, b = a + per < total ? a + per : total;
-    int s = 0;
-    for (int64_t i = a; i < b; ++i) s += table[i];
-    part[t] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const int v = t >= off ? part[t - off] : 0;
+// Exclusive prefix sums of the table in place (one block; total is a multiple of 4).  The
+// block walks the table in chunks of 4096 entries: each thread loads 4 consecutive entries
+// as one int4, the threads' sums are scanned by warp shuffles and then across the warps,
+// and a running carry links the chunks.
+__global__ void __launch_bounds__(ORD_SCAN_THREADS) ord_scan_kernel(int* table, int64_t total) {
+    __shared__ int wsum[ORD_SCAN_THREADS / 32];
+    const int t = threadIdx.x, lane = t % 32, warp = t / 32;
+    int carry = 0;
+    for (int64_t c = 0; c < total; c += 4 * ORD_SCAN_THREADS) {
+        const int64_t i = c + 4 * (int64_t)t;
+        int4 v = make_int4(0, 0, 0, 0);
+        if (i < total) v = *reinterpret_cast<const int4*>(table + i);
+        const int own = v.x + v.y + v.z + v.w;
+        int x = own;                               // inclusive scan over the warp
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
         __syncthreads();
-        part[t] += v;
+        if (warp == 0) {
+            int s = wsum[lane];                    // inclusive scan over the warps' totals
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;
+        }
         __syncthreads();
-    }
-    int run = t > 0 ? part[t - 1] : 0;
-    for (int64_t i = a; i < b; ++i) {
-        const int v = table[i];
-        table[i] = run;
-        run += v;
+        int run = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - own;
+        if (i < total) {
+            int4 o;
+            o.x = run;
+            run += v.x;
+            o.y = run;
+            run += v.y;
+            o.z = run;
+            run += v.z;
+            o.w = run;
+            *reinterpret_cast<int4*>(table + i) = o;
+        }
+        carry += wsum[ORD_SCAN_THREADS / 32 - 1];
+        __syncthreads();                           // wsum is rewritten by the next chunk
     }
 }
 
-// Stable scatter: position = start of the digit in this block (from the scanned table) +
-// count of the digit in earlier warps of the block + count among earlier lanes.
+// Stable scatter, one sub-tile of 256 keys at a time in index order: position = running
+// start of the digit in this block (from the scanned table, advanced by each sub-tile's
+// counts) + count of the digit in earlier warps of the sub-tile + count among earlier lanes.
 __global__ void __launch_bounds__(ORD_THREADS) ord_scatter_kernel(const unsigned* keys, const int* idx, int64_t n,
                                                                  int shift, const int* table, int nblocks,
                                                                  unsigned* keys_out, int* idx_out) {
-    __shared__ int wc[ORD_WARPS][ORD_BINS + 1];
-    for (int i = threadIdx.x; i < ORD_WARPS * (ORD_BINS + 1); i += ORD_THREADS) (&wc[0][0])[i] = 0;
-    __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * ORD_THREADS + threadIdx.x;
-    const bool valid = i < n;
-    const unsigned key = valid ? keys[i] : 0u;
-    const int digit = valid ? (int)((key >> shift) & 0xffu) : ORD_BINS;     // ORD_BINS: no element
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const unsigned peers = __match_any_sync(0xffffffffu, digit);
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    if (rank == 0) wc[warp][digit] = __popc(peers);
-    __syncthreads();
-    {
-        // exclusive prefix over the warps, one digit per thread
-        const int dgt = threadIdx.x;
-        int run = 0;
+    __shared__ int wc[ORD_WARPS][ORD_BINS + 1];    // column ORD_BINS: lanes past the end
+    __shared__ int run[ORD_BINS];
+    const int t = threadIdx.x, warp = t / 32, lane = t % 32;
+    for (int k = t; k < ORD_WARPS * (ORD_BINS + 1); k += ORD_THREADS) (&wc[0][0])[k] = 0;
+    run[t] = table[(int64_t)t * nblocks + blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * ORD_TILE;
+    for (int s = 0; s < ORD_SUB; ++s) {
+        const int64_t first = base + (int64_t)s * ORD_THREADS;
+        if (first >= n) break;                     // uniform over the block
+        __syncthreads();                           // wc cleared, run advanced
+        const int64_t i = first + t;
+        const bool valid = i < n;
+        const unsigned key = valid ? keys[i] : 0u;
+        const int digit = valid ? (int)((key >> shift) & 0xffu) : ORD_BINS;
+        const unsigned peers = __match_any_sync(0xffffffffu, digit);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (rank == 0) wc[warp][digit] = __popc(peers);
+        __syncthreads();
+        int tot = 0;                               // digit t: exclusive prefix over the warps
         for (int w = 0; w < ORD_WARPS; ++w) {
-            const int v = wc[w][dgt];
-            wc[w][dgt] = run;
-            run += v;
+            const int v = wc[w][t];
+            wc[w][t] = tot;
+            tot += v;
         }
+        __syncthreads();
+        if (valid) {
+            const int64_t pos = (int64_t)run[digit] + wc[warp][digit] + rank;
+            keys_out[pos] = key;
+            idx_out[pos] = idx[i];
+        }
+        __syncthreads();                           // every read of run and wc is done
+        for (int w = 0; w < ORD_WARPS; ++w) wc[w][t] = 0;
+        run[t] += tot;
     }
-    __syncthreads();
-    if (!valid) return;
-    const int64_t pos = (int64_t)table[(int64_t)digit * nblocks + blockIdx.x] + wc[warp][digit] + rank;
-    keys_out[pos] = key;
-    idx_out[pos] = idx[i];
 }
+
+size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
 }  // namespace
 
 size_t spatial_order_scratch(int64_t n) {
-    const int64_t nb = (n + ORD_THREADS - 1) / ORD_THREADS;
-    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    return al(32 * sizeof(unsigned)) + 2 * al((size_t)n * sizeof(unsigned)) + al((size_t)n * sizeof(int)) +
-           al((size_t)nb * ORD_BINS * sizeof(int));
+    const int64_t nb = (n + ORD_TILE - 1) / ORD_TILE;
+    return al256(2 * D_MAX * sizeof(unsigned)) + 2 * al256((size_t)n * sizeof(unsigned)) +
+           al256((size_t)n * sizeof(int)) + al256((size_t)nb * ORD_BINS * sizeof(int));
 }
 
-cudaError_t spatial_order(const float* X, int64_t n, int d, int* perm, void* scratch, cudaStream_t st) {
+cudaError_t spatial_order(const float* X, int64_t n, int d, int* perm, float2* bounds, void* scratch,
+                          cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const int nb = (int)((n + ORD_THREADS - 1) / ORD_THREADS);
+    if (d < 1 || d > D_MAX) return cudaErrorInvalidValue;
+    const int nb = (int)((n + ORD_TILE - 1) / ORD_TILE);
     char* s = static_cast<char*>(scratch);
     unsigned* box = reinterpret_cast<unsigned*>(s);
-    unsigned* ka = reinterpret_cast<unsigned*>(s + al(32 * sizeof(unsigned)));
-    unsigned* kb = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(ka) + al((size_t)n * sizeof(unsigned)));
-    int* ia = reinterpret_cast<int*>(reinterpret_cast<char*>(kb) + al((size_t)n * sizeof(unsigned)));
-    int* table = reinterpret_cast<int*>(reinterpret_cast<char*>(ia) + al((size_t)n * sizeof(int)));
-    cudaError_t e = cudaMemsetAsync(box, 0xff, 16 * sizeof(unsigned), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(box + 16, 0, 16 * sizeof(unsigned), st);
+    unsigned* ka = reinterpret_cast<unsigned*>(s + al256(2 * D_MAX * sizeof(unsigned)));
+    unsigned* kb = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(ka) + al256((size_t)n * sizeof(unsigned)));
+    int* ia = reinterpret_cast<int*>(reinterpret_cast<char*>(kb) + al256((size_t)n * sizeof(unsigned)));
+    int* table = reinterpret_cast<int*>(reinterpret_cast<char*>(ia) + al256((size_t)n * sizeof(int)));
+    cudaError_t e = cudaMemsetAsync(box, 0xff, D_MAX * sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(box + D_MAX, 0, D_MAX * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
-    const unsigned blocks = (unsigned)nb;
-    ord_bbox_kernel<<<blocks, ORD_THREADS, 0, st>>>(X, n, d, box);
-    ord_key_kernel<<<blocks, ORD_THREADS, 0, st>>>(X, n, d, box, ka, perm);
+    const int per = ORD_THREADS / d * d;
+    const int64_t box_need = (n * d + per - 1) / per;
+    const unsigned box_blocks = (unsigned)(box_need < ORD_BOX_BLOCKS ? box_need : ORD_BOX_BLOCKS);
+    ord_bbox_kernel<<<box_blocks, ORD_THREADS, 0, st>>>(X, n, d, box);
+    ord_key_kernel<<<(unsigned)((n + ORD_THREADS - 1) / ORD_THREADS), ORD_THREADS, 0, st>>>(X, n, d, box, ka, perm,
+                                                                                          bounds);
     // pass 1: low byte (ka, perm) -> (kb, ia); pass 2: high byte (kb, ia) -> (ka, perm)
+    const unsigned blocks = (unsigned)nb;
+    const int64_t entries = (int64_t)nb * ORD_BINS;
     ord_hist_kernel<<<blocks, ORD_THREADS, 0, st>>>(ka, n, 0, table, nb);
-    ord_scan_kernel<<<1, 1024, 0, st>>>(table, (int64_t)nb * ORD_BINS);
+    ord_scan_kernel<<<1, ORD_SCAN_THREADS, 0, st>>>(table, entries);
     ord_scatter_kernel<<<blocks, ORD_THREADS, 0, st>>>(ka, perm, n, 0, table, nb, kb, ia);
     ord_hist_kernel<<<blocks, ORD_THREADS, 0, st>>>(kb, n, 8, table, nb);
-    ord_scan_kernel<<<1, 1024, 0, st>>>(table, (int64_t)nb * ORD_BINS);
+    ord_scan_kernel<<<1, ORD_SCAN_THREADS, 0, st>>>(table, entries);
     ord_scatter_kernel<<<blocks, ORD_THREADS, 0, st>>>(kb, ia, n, 8, table, nb, ka, perm);
     return cudaGetLastError();
 }

@@ -1,25 +1,31 @@
 // Tensor-core form of the unmasked L2 envelope scan (LIP_TC_TF32 and LIP_TC_BF16).
 //
-// Squared distance as one augmented product: with q^ = M w (q - c), x^ = M w (x - c)
-// (c = the data mean; distances do not depend on it),
-//     s(q, x) = |q^|^2 + |x^|^2 - 2 q^.x^ = a . b,   a = [-2 q^, 1, |q^|^2],  b = [x^, |x^|^2, 1],
-// padded with zeros to K = 8, 16 or 24.  Every operand is split v = hi + lo with hi the
-// value truncated to TF32 and lo the FP32 remainder, and s~ = a_hi.b_hi + a_hi.b_lo +
-// a_lo.b_hi runs as three tcgen05.mma kind::tf32 passes accumulating in FP32 in TMEM.
+// Squared distance as products: with q^ = M w (q - c), x^ = M w (x - c) (c = the centre
+// of the data's bounding box; distances do not depend on it),
+//     s(q, x) = |q^|^2 + |x^|^2 - 2 q^.x^ = a . b + n_a . n_b,
+//     a = -2 q^, b = x^ (K = d padded to 8 or 16),
+//     n_a = [1, .., 1, pieces of |q^|^2],  n_b = [pieces of |x^|^2, 1, .., 1]
+// (the norm block: one more MMA of 32 bytes of K, so the two norms no longer widen K).
+// Every operand is split v = hi + lo with hi the value truncated to TF32 and lo the FP32
+// remainder, and a . b runs as three tcgen05.mma kind::tf32 passes a_hi.b_hi + a_hi.b_lo +
+// a_lo.b_hi accumulating in FP32 in TMEM; the norm block holds the norms' hi and lo.
 //
-// BF16 (LIP_TC_BF16): K padded to 16 or 32, every operand split into three bf16 pieces
-// v = h + m + l (each the bf16 rounding of the remainder; |v - h - m - l| <= 2^-24 |v|),
-// and s~ = hh + hm + mh + hl + lh + mm (products of bf16 pieces are exact in FP32) runs as
-// six tcgen05.mma kind::f16 passes with both operands bf16.  The dropped products and the
-// representation error are <= 2^-22 |a||b|; FP32 accumulation of 6 K products adds at most
-// 6 K 2^-23 (<= 2.3e-5 at K = 32); with the input rounding the bound is 3e-5 (|q^| + R)^2.
+// BF16 (LIP_TC_BF16): K = 16, every operand split into three bf16 pieces v = h + m + l (each
+// the bf16 rounding of the remainder; |v - h - m - l| <= 2^-24 |v|), and a . b =
+// hh + hm + mh + hl + lh + mm (products of bf16 pieces are exact in FP32) runs as six
+// tcgen05.mma kind::f16 passes with both operands bf16; the norm block holds h, m, l.
 //
-// Error bound used to prune (conservative, per query):
-//   |s~ - s| <= eps = 2e-5 (|q^| + R)^2,  R = max_k |x^_k|, from
-//   * 3 * 2^-20 |a||b| for the dropped and truncated split terms;
-//   * 72 * 2^-23 for FP32 accumulation of 72 products;
-//   * 4 * 2^-22 sqrt(d) + 2^-23 for the FP32 rounding of the inputs;
-//   together <= 1.54e-5 times sum |a_j b_j| <= (|q^| + |x^|)^2.
+// Error bound used to prune (conservative, per query): |s~ - s| <= eps = C (|q^| + R)^2,
+// R = max_k |x^_k|.  Every term of the products is bounded by S = sum_j |a_j b_j| + |x^|^2
+// + |q^|^2 <= (|q^| + R)^2:
+//   * TF32: 3 * 2^-20 S for the dropped and truncated split terms (the norms' lo pieces are
+//     truncated to TF32 too), plus (3K + 4) * 2^-23 S for FP32 accumulation of 3K + 4
+//     products (52 at K = 16);
+//   * BF16: 2^-22 S for the dropped products and the representation error, plus
+//     (6K + 6) * 2^-23 S (102 products at K = 16);
+//   * the FP32 rounding of the inputs and of the two norms: <= 2^-23 (|q^| + R)^2 + 2^-24 S.
+// Together at most 9.3e-6 (TF32) and 1.3e-5 (BF16) times (|q^| + R)^2; C = 1.3e-5 and
+// 1.7e-5.
 // Then |sqrt(s~+) - sqrt(s)| <= eps / sqrt(max(s~+, eps)); for a 32-point chunk the
 // smallest s~ in it bounds every pair.  With the FP32 evaluation error of the bounds,
 //   delta_c = 1.001 eps rsqrt(max(min_chunk s~, eps)) + 2^-19 (max|y| + |q^| + R).
@@ -32,11 +38,13 @@
 // A query whose list overflows is recomputed by the plain FP32 scan.
 //
 // Kernel: one CTA per 128-query tile, 18 warps.  Warp 0 streams 256-point data tiles
-// (pre-tiled hi/lo operands and y, one 1-D bulk copy each) into a 3-stage ring; warp 1
+// (pre-tiled operand pieces, norm block and y, one 1-D bulk copy each) into a 4-stage ring; warp 1
 // owns TMEM (512 columns = two 128 x 256 FP32 accumulators) and issues the MMAs; warps
 // 2..17 are the epilogue: each reads one 32-lane quarter of the accumulator rows (one
-// query per thread) over a quarter of the columns with tcgen05.ld, takes sqrt(|s~|),
-// forms y +- sqrt and keeps the chunk extrema and candidate lists.  Every wait is bounded.
+// query per thread) over a quarter of the columns with tcgen05.ld, tests each 32-column
+// chunk's smallest s~ against the running bounds and, only where the chunk
+// may hold an extremum, takes sqrt(|s~|), forms y +- sqrt and keeps the chunk extrema and
+// candidate lists.  Every wait is bounded.
 // (sqrt(|s~|) needs no clamp: s~ < 0 only when s < eps, and then both roots are below
 // sqrt(eps), which delta already covers.)
 #include <cstdio>
@@ -49,14 +57,14 @@ namespace lip {
 
 constexpr int TC_M = 128;
 constexpr int TC_N = 256;
-constexpr int TC_STAGES = 3;
+constexpr int TC_STAGES = 4;
 constexpr int TC_CAP = 8;
 // Epilogue warps: 4 lane quarters x PARTS column slices (PARTS = 2 or 4, a launch variant);
 // each (query, bound) keeps one candidate list per column slice.
 constexpr int TC_MAX_PARTS = 4;
 __host__ __device__ constexpr int tc_threads(int parts) { return 32 * (2 + 4 * parts); }
-constexpr float TC_C_EPS = 2.0e-5f;        // TF32 split
-constexpr float TC_C_EPS_BF16 = 3.0e-5f;   // BF16 three-piece split
+constexpr float TC_C_EPS = 1.3e-5f;        // TF32 split (bound 9.3e-6)
+constexpr float TC_C_EPS_BF16 = 1.7e-5f;   // BF16 three-piece split (bound 1.3e-5)
 
 struct TcRec {      // candidate list of one (query, bound, column quarter)
     float U;        // upper bound of H_up (bound 0) or lower bound of H_lo (bound 1)
@@ -68,12 +76,22 @@ struct TcRec {      // candidate list of one (query, bound, column quarter)
 // Operand geometry per format: TF32 keeps 2 pieces of 4-byte elements with K a multiple
 // of 8; BF16 keeps 3 pieces of 2-byte elements with K a multiple of 16.  Either way one
 // MMA consumes 32 bytes of K per row (two 8-row x 16-byte core matrices).
-__host__ __device__ constexpr int tc_k_for_dim(int d, bool bf) { return bf ? ((d + 2 + 15) / 16) * 16 : ((d + 2 + 7) / 8) * 8; }
+__host__ __device__ constexpr int tc_k_for_dim(int d, bool bf) { return bf ? ((d + 15) / 16) * 16 : ((d + 7) / 8) * 8; }
 __host__ __device__ constexpr int tc_pieces(bool bf) { return bf ? 3 : 2; }
 __host__ __device__ constexpr int tc_esz(bool bf) { return bf ? 2 : 4; }
 __host__ __device__ constexpr uint32_t tc_sbo_bytes(int row_bytes) { return (uint32_t)(row_bytes / 16) * 128u; }
-__host__ __device__ constexpr int tc_tile_bytes(int K, bool bf) { return tc_pieces(bf) * TC_N * K * tc_esz(bf) + TC_N * 4; }
-__host__ __device__ constexpr int tc_a_bytes(int K, bool bf) { return tc_pieces(bf) * TC_M * K * tc_esz(bf); }
+// The norm block: one more K-major operand of 32 bytes per row (one MMA's K), holding the
+// pieces of |x^|^2 against ones (B) and ones against the pieces of |q^|^2 (A).
+constexpr int TC_NORM_ROW = 32;
+constexpr int TC_CHUNKS = TC_N / 32;       // 32-point chunks per tile
+// a data tile: the pieces, the norm block, y of its 256 points, then (min y, max y) of each
+// chunk (NaN when it holds no datum)
+__host__ __device__ constexpr int tc_tile_bytes(int K, bool bf) {
+    return tc_pieces(bf) * TC_N * K * tc_esz(bf) + TC_N * TC_NORM_ROW + TC_N * 4 + TC_CHUNKS * 8;
+}
+// a tile's slot in the shared-memory ring (1024-byte aligned operands in every stage)
+__host__ __device__ constexpr int tc_stage_bytes(int K, bool bf) { return (tc_tile_bytes(K, bf) + 1023) / 1024 * 1024; }
+__host__ __device__ constexpr int tc_a_bytes(int K, bool bf) { return tc_pieces(bf) * TC_M * K * tc_esz(bf) + TC_M * TC_NORM_ROW; }
 
 // byte offset of the element at row r, byte kb along K, in a canonical no-swizzle K-major
 // operand whose rows hold row_bytes of K (core matrices of 8 rows x 16 bytes)
@@ -103,6 +121,39 @@ __device__ __forceinline__ void tc_store_pieces(char* base, int piece_bytes, int
     }
 }
 
+// Writes row r of a norm block: the pieces of nv at the front and the matching ones after
+// them when ones_first is false (B: [nv pieces, 1, 1(, 1)]), the ones first when it is true
+// (A: [1, 1(, 1), nv pieces]); the rest of the row is zero.  TF32: 2 pieces of 4 bytes
+// (hi truncated, FP32 remainder); BF16: 3 pieces of 2 bytes.
+template <bool BF>
+__device__ __forceinline__ void tc_store_norm(char* base, int r, float nv, bool ones_first) {
+    const int np = tc_pieces(BF), per = TC_NORM_ROW / tc_esz(BF);
+    float pc[3];
+    if (BF) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(nv);
+        const float r1 = nv - __bfloat162float(h);
+        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(m);
+        pc[0] = __bfloat162float(h);
+        pc[1] = __bfloat162float(m);
+        pc[2] = __bfloat162float(__float2bfloat16_rn(r2));
+    } else {
+        pc[0] = __uint_as_float(__float_as_uint(nv) & 0xFFFFE000u);
+        pc[1] = nv - pc[0];
+        pc[2] = 0.f;
+    }
+    for (int k = 0; k < per; ++k) {
+        float v = 0.f;
+        if (k < 2 * np) {
+            const bool one = ones_first ? (k < np) : (k >= np);
+            v = one ? 1.f : pc[ones_first ? k - np : k];
+        }
+        const uint32_t off = tc_off(r, k * tc_esz(BF), TC_NORM_ROW);
+        if (BF) *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+        else *reinterpret_cast<float*>(base + off) = v;
+    }
+}
+
 // --------------------------------------------------------------- data preparation
 
 struct TcPrepParams {
@@ -111,7 +162,7 @@ struct TcPrepParams {
     int64_t N;
     int d, K;
     double scale[D_MAX];  // M * w_j (caller's coordinate order; unmasked, so no mirroring)
-    double* stats;        // [D_MAX] sums, then centre; stats[D_MAX] = R (as double), [D_MAX+1] = Ymax
+    const float2* bounds; // [d] (min, max) of the data's finite coordinates (the centre is their midpoint)
     unsigned* maxbits;    // [2]: float bits of R and of max|y|
     char* tiles;          // [ntiles][tile_bytes]
     int64_t ntiles;
@@ -121,19 +172,15 @@ struct TcPrepParams {
     float* ys;            // [N]
 };
 
-__global__ void tc_sum_kernel(const TcPrepParams P) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    __shared__ double acc[D_MAX];
-    if (threadIdx.x < D_MAX) acc[threadIdx.x] = 0.0;
-    __syncthreads();
-    if (k < P.N)
-        for (int j = 0; j < P.d; ++j) atomicAdd(&acc[j], P.scale[j] * (double)P.X0[k * P.d + j]);
-    __syncthreads();
-    if (threadIdx.x < P.d) atomicAdd(&P.stats[threadIdx.x], acc[threadIdx.x]);
+// The centre of the scaled coordinates: the midpoint of the data's bounding box, the same
+// double for the data and the query pieces.
+__device__ __forceinline__ double tc_centre(const float2 b, double scale) {
+    return scale * 0.5 * ((double)b.x + (double)b.y);
 }
 
-// One thread per (padded) position: the row of the B pieces and y of the datum at that
-// position, in the tile layout, and the position-ordered copy of its row.
+// One thread per (padded) position: the row of the B pieces, of the norm block and y of
+// the datum at that position, in the tile layout, and the position-ordered copy of its
+// row.  A padding position has zero rows (s~ = 0) and y = NaN.
 template <bool BF>
 __global__ void tc_build_b_kernel(const TcPrepParams P) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -142,44 +189,59 @@ __global__ void tc_build_b_kernel(const TcPrepParams P) {
     const int r = (int)(k % TC_N);
     char* tile = P.tiles + t * (int64_t)tc_tile_bytes(P.K, BF);
     const int piece = TC_N * P.K * tc_esz(BF);
-    float* yv = reinterpret_cast<float*>(tile + tc_pieces(BF) * piece);
-    float b[32];
+    char* norm = tile + tc_pieces(BF) * piece;
+    float* yv = reinterpret_cast<float*>(norm + TC_N * TC_NORM_ROW);
+    float b[16];
     for (int j = 0; j < P.K; ++j) b[j] = 0.f;
     float yy = __int_as_float(0x7fc00000);
+    bool real = false;
+    unsigned rbits = 0u, ybits = 0u;
     if (k < P.N) {
         const int64_t src = P.perm[k];
         double n2 = 0.0;
         for (int j = 0; j < P.d; ++j) {
             const float x = P.X0[src * P.d + j];
             P.Xs[k * P.d + j] = x;
-            const double c = P.stats[j] / (double)P.N;
+            const double c = tc_centre(P.bounds[j], P.scale[j]);
             const float xh = (float)(P.scale[j] * (double)x - c);
             b[j] = xh;
             n2 += (double)xh * (double)xh;
         }
-        b[P.d] = (float)n2;
-        b[P.d + 1] = 1.f;
+        tc_store_norm<BF>(norm, r, (float)n2, false);
+        real = true;
         yy = P.y0[src];
         P.ys[k] = yy;
-        atomicMax(&P.maxbits[0], __float_as_uint((float)sqrt(n2)));
-        atomicMax(&P.maxbits[1], __float_as_uint(fabsf(yy)));
+        rbits = __float_as_uint((float)sqrt(n2));
+        ybits = __float_as_uint(fabsf(yy));
+    }
+    // R and max |y|: one atomic per warp (non-negative floats order as their bits)
+    const unsigned act = __activemask();
+    rbits = __reduce_max_sync(act, rbits);
+    ybits = __reduce_max_sync(act, ybits);
+    if (threadIdx.x % 32 == __ffs(act) - 1) {
+        atomicMax(&P.maxbits[0], rbits);
+        atomicMax(&P.maxbits[1], ybits);
     }
     for (int j = 0; j < P.K; ++j) tc_store_pieces<BF>(tile, piece, r, j, P.K, b[j]);
+    if (!real)
+        for (int kb = 0; kb < TC_NORM_ROW; kb += 4) *reinterpret_cast<float*>(norm + tc_off(r, kb, TC_NORM_ROW)) = 0.f;
     yv[r] = yy;
 }
 
-// (min y, max y) of each 32-position chunk (NaN if it holds no datum): the epilogue's
-// chunk bounds.
-__global__ void tc_chunk_bounds_kernel(const float* ys, int64_t N, int64_t nchunks, float2* cb) {
+// (min y, max y) of each 32-position chunk (NaN if it holds no datum), the epilogue's chunk
+// bounds, written at the end of the chunk's tile.
+__global__ void tc_chunk_bounds_kernel(const float* ys, int64_t N, int64_t nchunks, char* tiles, int tile_bytes) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nchunks) return;
+    float2* cb = reinterpret_cast<float2*>(tiles + (c / TC_CHUNKS) * (int64_t)tile_bytes + tile_bytes - TC_CHUNKS * 8) +
+                 c % TC_CHUNKS;
     const float nan = __int_as_float(0x7fc00000);
     float lo = nan, hi = nan;
     for (int64_t k = c * 32; k < c * 32 + 32 && k < N; ++k) {
         lo = fminf(lo, ys[k]);        // NaN operands are ignored
         hi = fmaxf(hi, ys[k]);
     }
-    cb[c] = make_float2(lo, hi);
+    *cb = make_float2(lo, hi);
 }
 
 struct TcQueryParams {
@@ -188,7 +250,7 @@ struct TcQueryParams {
     int64_t nq;
     int d, K;
     double scale[D_MAX];
-    const double* stats;   // sums (centre = sums / N)
+    const float2* bounds;  // [d] the data's bounding box (the centre is its midpoint)
     int64_t N;
     const unsigned* maxbits;
     char* atiles;          // [nqt][a_bytes]: the A pieces
@@ -205,27 +267,31 @@ __global__ void tc_build_a_kernel(const TcQueryParams P) {
     const int r = (int)(qi % TC_M);
     char* at = P.atiles + t * (int64_t)tc_a_bytes(P.K, BF);
     const int piece = TC_M * P.K * tc_esz(BF);
-    float a[32];
+    float a[16];
     for (int j = 0; j < P.K; ++j) a[j] = 0.f;
+    char* norm = at + tc_pieces(BF) * piece;
+    bool real = false;
     if (qi < P.nq) {
         const int64_t src = P.qperm[qi];
         double n2 = 0.0;
         for (int j = 0; j < P.d; ++j) {
-            const double c = P.stats[j] / (double)P.N;
+            const double c = tc_centre(P.bounds[j], P.scale[j]);
             const float qh = (float)(P.scale[j] * (double)P.Q[src * P.d + j] - c);
             a[j] = -2.f * qh;
             n2 += (double)qh * (double)qh;
         }
-        a[P.d] = 1.f;
-        a[P.d + 1] = (float)n2;
         const double R = (double)__uint_as_float(P.maxbits[0]);
         const double Y = (double)__uint_as_float(P.maxbits[1]);
         const double nq = sqrt(n2);
         const float eps = (float)((double)(BF ? TC_C_EPS_BF16 : TC_C_EPS) * (nq + R) * (nq + R));
         const float epsv = (float)(ldexp(1.0, -19) * (Y + nq + R));
         P.eps[qi] = make_float2(eps, epsv);
+        tc_store_norm<BF>(norm, r, (float)n2, true);
+        real = true;
     }
     for (int j = 0; j < P.K; ++j) tc_store_pieces<BF>(at, piece, r, j, P.K, a[j]);
+    if (!real)
+        for (int kb = 0; kb < TC_NORM_ROW; kb += 4) *reinterpret_cast<float*>(norm + tc_off(r, kb, TC_NORM_ROW)) = 0.f;
 }
 
 // --------------------------------------------------------------- tcgen05 helpers
@@ -309,8 +375,7 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 struct TcScanParams {
     const char* atiles;
     const char* btiles;
-    const float2* eps;
-    const float2* cbound;  // [ntiles * TC_N / 32] (min y, max y) per chunk
+    const float2* eps;     // [nq]: (eps, eps_v)
     int64_t nq;
     int64_t ntiles;
     TcRec* rec;            // [nq positions][2 bounds][TC_MAX_PARTS column slices]
@@ -342,7 +407,7 @@ __device__ __forceinline__ void tc_append(TcRec* R, int& n, int id, float L, flo
 template <int K, int PARTS, bool BF>
 __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcScanParams P) {
     constexpr int EPI_WARPS = 4 * PARTS;
-    constexpr int TILE_BYTES = tc_tile_bytes(K, BF);
+    constexpr int TILE_BYTES = tc_tile_bytes(K, BF), STAGE_BYTES = tc_stage_bytes(K, BF);
     constexpr int A_BYTES = tc_a_bytes(K, BF);
     constexpr int ROW_BYTES = K * tc_esz(BF);
     constexpr int KS = ROW_BYTES / 32;                  // MMAs per pass (32 bytes of K each)
@@ -392,7 +457,7 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                     break;
                 }
                 mbar_expect_tx(&b_full[s], TILE_BYTES);
-                bulk_g2s(sB + (size_t)s * TILE_BYTES, P.btiles + t * (int64_t)TILE_BYTES, TILE_BYTES, &b_full[s]);
+                bulk_g2s(sB + (size_t)s * STAGE_BYTES, P.btiles + t * (int64_t)TILE_BYTES, TILE_BYTES, &b_full[s]);
             }
             // wait (bounded) for the copies still in flight before leaving
             const int64_t first = t > TC_STAGES ? t - TC_STAGES : 0;
@@ -416,7 +481,7 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                     if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / TC_STAGES) & 1), P.err)) break;
                     if (t >= 2 && !mbar_wait_bounded(&acc_empty[b], (uint32_t)((t / 2 - 1) & 1), P.err)) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t b0 = smem_u32(sB + (size_t)s * TILE_BYTES);
+                    const uint32_t b0 = smem_u32(sB + (size_t)s * STAGE_BYTES);
                     const uint32_t d = tb + (uint32_t)b * TC_N;
                     // piece pairs: TF32 hi.hi, hi.lo, lo.hi; BF16 hh, hm, mh, hl, lh, mm
                     constexpr int NPASS = BF ? 6 : 3;
@@ -429,6 +494,10 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                             tc_mma<BF>(d, tc_desc(ap + ks * 256, ROW_BYTES), tc_desc(bp + ks * 256, ROW_BYTES), idesc,
                                        (ps > 0 || ks > 0) ? 1u : 0u);
                     }
+                    // the norm block: |x^|^2 + |q^|^2 in one more MMA of 32 bytes of K
+                    tc_mma<BF>(d, tc_desc(a0 + tc_pieces(BF) * A_PIECE, TC_NORM_ROW),
+                               tc_desc(b0 + tc_pieces(BF) * B_PIECE, TC_NORM_ROW),
+                               idesc, 1u);
                     tc_commit(&b_empty[s]);
                     tc_commit(&acc_full[b]);
                 }
@@ -441,7 +510,7 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
         const int quarter = warp % 4, part = (warp - 2) / 4;
         const int64_t qi = qt * TC_M + quarter * 32 + lane;
         const bool valid = qi < P.nq;
-        float2 e2 = valid ? P.eps[qi] : make_float2(1.f, 1.f);
+        const float2 e2 = valid ? P.eps[qi] : make_float2(1.f, 1.f);
         // a zero bound (M = 0) must not turn eps * rsqrt(0) into NaN
         const float eps = fmaxf(e2.x, 1e-30f), epsv = e2.y;
         TcRec* Ru = P.rec + (valid ? ((qi * 2 + 0) * TC_MAX_PARTS + part) : 0);
@@ -452,34 +521,52 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
         for (int64_t t = 0; t < T; ++t) {
             const int s = (int)(t % TC_STAGES), b = (int)(t & 1);
             if (!mbar_wait_bounded(&acc_full[b], (uint32_t)((t / 2) & 1), P.err)) break;
-            // acquire the tile's y values written by the bulk copy
+            // acquire the tile's y values and chunk bounds written by the bulk copy
             if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / TC_STAGES) & 1), P.err)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const float* ys = reinterpret_cast<const float*>(sB + (size_t)s * TILE_BYTES + tc_pieces(BF) * B_PIECE);
+            const float* ys = reinterpret_cast<const float*>(sB + (size_t)s * STAGE_BYTES + tc_pieces(BF) * B_PIECE +
+                                                             TC_N * TC_NORM_ROW);
+            const float2* cbs = reinterpret_cast<const float2*>(ys + TC_N);
             // two 32-column chunks per TMEM wait: both loads are in flight together
 #pragma unroll 1
             for (int j = 0; j < TC_N / 32 / PARTS; j += 2) {
                 const int col0 = part * (TC_N / PARTS) + j * 32;
                 float sv[2][32];
                 tmem_ld32x2(tb + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * TC_N + col0, sv);
+                if (j + 2 >= TC_N / 32 / PARTS) {
+                    // the warp's last columns of this accumulator are in registers: hand the
+                    // buffer back to the MMA warp now, before any square-root work
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acc_empty[b]);
+                }
+                // both chunks' smallest s~ and bounds tests first (independent chains), then
+                // the square roots only where some query of the warp may find an extremum
+                float csm[2];
+                bool take[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int col = col0 + h * 32;
-                    const int chunk = (int)(t * (TC_N / 32) + col / 32);
-                    // the chunk's smallest s~, then its bounds test: no square root unless
-                    // some query of the warp may find an extremum in it
                     float cs[4];
 #pragma unroll
                     for (int a = 0; a < 4; ++a) cs[a] = INF;
 #pragma unroll
                     for (int e = 0; e < 32; e += 4)
                         cs[(e / 4) % 4] = min3f(min3f(cs[(e / 4) % 4], sv[h][e], sv[h][e + 1]), sv[h][e + 2], sv[h][e + 3]);
-                    const float csm = min2f(min3f(cs[0], cs[1], cs[2]), cs[3]);
-                    const float2 cb = __ldg(&P.cbound[chunk]);
-                    const float slo = sqrt_approx(fmaxf(csm - eps, 0.f) * (1.f - 0x1p-22f)) * (1.f - 0x1p-21f);
+                    csm[h] = min2f(min3f(cs[0], cs[1], cs[2]), cs[3]);
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 cb = cbs[col0 / 32 + h];
+                    const float slo = sqrt_approx(fmaxf(csm[h] - eps, 0.f) * (1.f - 0x1p-22f)) * (1.f - 0x1p-21f);
                     const float lbu = (cb.x + slo) - 0x1p-22f * (fabsf(cb.x) + slo);
                     const float ubl = (cb.y - slo) + 0x1p-22f * (fabsf(cb.y) + slo);
-                    if (!__any_sync(0xffffffffu, valid && (lbu <= U || ubl >= Bl))) continue;
+                    take[h] = __any_sync(0xffffffffu, valid && (lbu <= U || ubl >= Bl));
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!take[h]) continue;
+                    const int col = col0 + h * 32;
+                    const int chunk = (int)(t * TC_CHUNKS + col / 32);
                     // four interleaved partial extrema per chunk keep the dependent chains short
                     float cu[4], cl[4];
 #pragma unroll
@@ -498,7 +585,7 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                     const float cum = min2f(min3f(cu[0], cu[1], cu[2]), cu[3]);
                     const float clm = max2f(max3f(cl[0], cl[1], cl[2]), cl[3]);
                     if (valid) {
-                        const float dlt = 1.001f * eps * rsqrt_approx(fmaxf(csm, eps)) + epsv;
+                        const float dlt = 1.001f * eps * rsqrt_approx(fmaxf(csm[h], eps)) + epsv;
                         U = fminf(U, cum + dlt);
                         if (cum - dlt <= U) tc_append(Ru, nu, chunk, cum - dlt, U, true);
                         Bl = fmaxf(Bl, clm - dlt);
@@ -506,12 +593,8 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                     }
                 }
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&acc_empty[b]);
-                mbar_arrive(&b_empty[s]);
-            }
+            if (lane == 0) mbar_arrive(&b_empty[s]);     // the stage's y values are no longer read
         }
         if (valid) {
             Ru->U = U;
@@ -691,14 +774,14 @@ size_t tc_tile_bytes_for(int d, bool bf) { return (size_t)tc_tile_bytes(tc_k_for
 size_t tc_a_bytes_for(int d, bool bf) { return (size_t)tc_a_bytes(tc_k_for_dim(d, bf), bf); }
 size_t tc_rec_bytes() { return sizeof(TcRec) * 2 * TC_MAX_PARTS; }   // candidate lists per query
 
-int tc_chunks_per_tile() { return TC_N / 32; }
 
 // The data's spatial order, then the tiles in that order, the position-ordered copies and
 // the chunk bounds.
-cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, const double* scale, double* stats,
+cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, const double* scale,
                             unsigned* maxbits, char* tiles, int64_t ntiles, bool bf, const TcDataOrder& O,
                             cudaStream_t st) {
-    cudaError_t e = spatial_order(X0, N, d, O.dperm, O.scratch, st);
+    cudaError_t e = cudaMemsetAsync(O.bounds, 0, D_MAX * sizeof(float2), st);   // an empty set centres at 0
+    if (e == cudaSuccess) e = spatial_order(X0, N, d, O.dperm, O.bounds, O.scratch, st);
     if (e != cudaSuccess) return e;
     TcPrepParams P{};
     P.X0 = X0;
@@ -708,30 +791,29 @@ cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, 
     P.K = tc_k_for_dim(d, bf);
     P.bf = bf;
     for (int j = 0; j < D_MAX; ++j) P.scale[j] = scale[j];
-    P.stats = stats;
+    P.bounds = O.bounds;
     P.maxbits = maxbits;
     P.tiles = tiles;
     P.ntiles = ntiles;
     P.perm = O.dperm;
     P.Xs = O.Xs;
     P.ys = O.ys;
-    e = cudaMemsetAsync(stats, 0, D_MAX * sizeof(double), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(maxbits, 0, 2 * sizeof(unsigned), st);
+    e = cudaMemsetAsync(maxbits, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
-    if (N > 0) tc_sum_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(P);
     const int64_t rows = ntiles * TC_N;
     if (rows > 0) {
         if (bf) tc_build_b_kernel<true><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P);
         else tc_build_b_kernel<false><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P);
-        const int64_t nchunks = ntiles * (TC_N / 32);
-        tc_chunk_bounds_kernel<<<(unsigned)((nchunks + 255) / 256), 256, 0, st>>>(O.ys, N, nchunks, O.cbound);
+        const int64_t nchunks = ntiles * TC_CHUNKS;
+        tc_chunk_bounds_kernel<<<(unsigned)((nchunks + 255) / 256), 256, 0, st>>>(O.ys, N, nchunks, tiles,
+                                                                                 tc_tile_bytes(P.K, bf));
     }
     return cudaGetLastError();
 }
 
 template <int K, int PARTS, bool BF>
 static cudaError_t launch_tc_scan_k(const TcScanParams& P, int64_t nqt, cudaStream_t st) {
-    const size_t smem = (size_t)tc_a_bytes(K, BF) + (size_t)TC_STAGES * tc_tile_bytes(K, BF);
+    const size_t smem = (size_t)tc_a_bytes(K, BF) + (size_t)TC_STAGES * tc_stage_bytes(K, BF);
     static cudaError_t attr =
         cudaFuncSetAttribute(tc_scan_kernel<K, PARTS, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return attr;
@@ -741,24 +823,20 @@ static cudaError_t launch_tc_scan_k(const TcScanParams& P, int64_t nqt, cudaStre
 
 template <int PARTS>
 static cudaError_t launch_tc_scan_parts(int K, bool bf, const TcScanParams& P, int64_t nqt, cudaStream_t st) {
-    if (bf) {
-        if (K == 16) return launch_tc_scan_k<16, PARTS, true>(P, nqt, st);
-        return launch_tc_scan_k<32, PARTS, true>(P, nqt, st);
-    }
+    if (bf) return launch_tc_scan_k<16, PARTS, true>(P, nqt, st);   // d <= 16: K = 16
     if (K == 8) return launch_tc_scan_k<8, PARTS, false>(P, nqt, st);
-    if (K == 16) return launch_tc_scan_k<16, PARTS, false>(P, nqt, st);
-    return launch_tc_scan_k<24, PARTS, false>(P, nqt, st);
+    return launch_tc_scan_k<16, PARTS, false>(P, nqt, st);
 }
 
 // Queries: build A, scan, rescreen.  Returns the fallback count through fb (device).
-cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scale, const double* stats, int64_t N,
+cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scale, int64_t N,
                            const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float2* eps,
                            void* rec, const double* w, double M, const float* X0, const float* y0, float* g, float* lo,
                            float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, unsigned* err,
                            int variant, bool bf, const TcDataOrder& O, const TcQueryOrder& QO, cudaStream_t st) {
     const int K = tc_k_for_dim(d, bf);
     // the queries' spatial order: a tile of 128 positions holds nearby queries
-    cudaError_t e = spatial_order(Q, nq, d, QO.qperm, QO.scratch, st);
+    cudaError_t e = spatial_order(Q, nq, d, QO.qperm, nullptr, QO.scratch, st);
     if (e != cudaSuccess) return e;
     const int parts = variant == 1 ? 2 : 4;   // variant 0: 16 epilogue warps, 1: 8
     const int64_t nqt = (nq + TC_M - 1) / TC_M;
@@ -769,7 +847,7 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     A.d = d;
     A.K = K;
     for (int j = 0; j < D_MAX; ++j) A.scale[j] = scale[j];
-    A.stats = stats;
+    A.bounds = O.bounds;
     A.N = N;
     A.maxbits = maxbits;
     A.atiles = atiles;
@@ -782,7 +860,6 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     S.atiles = atiles;
     S.btiles = btiles;
     S.eps = eps;
-    S.cbound = O.cbound;
     S.nq = nq;
     S.ntiles = ntiles;
     S.rec = static_cast<TcRec*>(rec);

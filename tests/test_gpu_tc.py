@@ -144,7 +144,8 @@ def test_bf16_full_size_cluster_sampled(oracle_mod):
 @pytest.mark.parametrize("d,weighted", [(1, False), (2, True), (6, True), (13, False), (14, True), (15, False),
                                         (16, True)])
 def test_bf16_random_shapes(oracle_mod, d, weighted):
-    """The BF16 three-piece split (K = 16 up to d = 14, 32 above): the same exact results."""
+    """The BF16 three-piece split (K = 16 for every d; the norms are added in the epilogue):
+    the same exact results."""
     p = W.random_problem(970 + d, 5_003, d, 1_201, norm=W.NORM_L2, weighted=weighted)
     orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm, w=p.w)
     r, fb = _tc_eval(p, "tc_bf16")

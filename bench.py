@@ -44,8 +44,8 @@ UNIT = "G pairs/s"
 NORMS = (W.NORM_L1, W.NORM_L2, W.NORM_LINF)
 NNAME = {1: "L1", 2: "L2", 3: "Linf"}
 FP32_LANES_PER_SM = 128
-WORKLOADS = ("monotone_d4", "plain_d2", "cluster_d16", "cluster_d16_tc", "cluster_d16_bf16", "grad_d8",
-             "batch_4096", "local_d4", "smooth_d4")
+WORKLOADS = ("monotone_d4", "plain_d2", "cluster_d16", "cluster_d16_tc", "cluster_d16_bf16", "cluster_d16_fp16",
+             "grad_d8", "batch_4096", "local_d4", "smooth_d4")
 SMOOTH_ITERS = 10
 LOCAL_KNOTS, LOCAL_SAMPLE, LOCAL_SEED = 16, 32768, 0
 # special-function (MUFU) results per SM per clock
@@ -244,7 +244,7 @@ def reference_problems(workload):
         return [base.with_norm(n) for n in NORMS]
     if workload == "plain_d2":
         return [W.plain_d2(dtype=np.float64)]
-    if workload in ("cluster_d16", "cluster_d16_tc", "cluster_d16_bf16"):
+    if workload in ("cluster_d16", "cluster_d16_tc", "cluster_d16_bf16", "cluster_d16_fp16"):
         return [W.cluster_d16(n_query=20_000)]
     if workload == "grad_d8":
         return [W.grad_d8()]
@@ -461,22 +461,25 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
         kern = "FP32 screen " + kern.replace(" fp64", "") + " + screen64_kernel (FP64 candidates)"
     roof = ctx.roofline(kern, ip * p.nq * p.N, avg[kdom], ip, mufu_per_pair(p.norm, c), clocks,
                         traffic_for(args, name, p.norm) if rd["prec"] == "fp32" else None)
-    if rd["prec"] in ("tc_tf32", "tc_bf16"):
-        bf = rd["prec"] == "tc_bf16"
-        # tensor-core form: the cross product only (the norms are added in the epilogue),
-        # three TF32 products over K = 8 ceil(d / 8), or six BF16 products over K = 16, per pair
-        kk = 16 * ((p.d + 15) // 16) if bf else 8 * ((p.d + 7) // 8)
-        npass = 6 if bf else 3
-        flops = 2.0 * npass * kk * p.nq * p.N
-        peak = float(ctx.peaks.get("bf16_tflops", 1800.0)) * (1.0 if bf else TF32_OVER_BF16) * 1e12
+    if rd["prec"] in ("tc_tf32", "tc_bf16", "tc_fp16"):
+        fmt = {"tc_tf32": "TF32", "tc_bf16": "BF16", "tc_fp16": "FP16"}[rd["prec"]]
+        f16 = fmt != "TF32"
+        # tensor-core form, MMA work per pair: the piece products over K = d padded (8 for
+        # TF32, 16 for the 16-bit kinds; three products for TF32 and FP16, six for BF16) plus
+        # the norm block, one more MMA of 32 bytes of K (8 TF32 or 16 16-bit elements)
+        kk = 16 * ((p.d + 15) // 16) if f16 else 8 * ((p.d + 7) // 8)
+        npass = 6 if fmt == "BF16" else 3
+        fpp = 2 * (npass * kk + (16 if f16 else 8))
+        flops = float(fpp) * p.nq * p.N
+        peak = float(ctx.peaks.get("bf16_tflops", 1800.0)) * (1.0 if f16 else TF32_OVER_BF16) * 1e12
         alu = roof
-        roof = {"bound": "tensor", "kernel": f"tc_scan_kernel<K={kk}, {'BF16' if bf else 'TF32'}> (+ build and rescreen)",
+        roof = {"bound": "tensor", "kernel": f"tc_scan_kernel<K={kk}, {fmt}> (+ build and rescreen)",
                 "achieved": flops / (avg[kdom] / 1e3) / 1e12, "peak": peak / 1e12,
-                "unit": f"TFLOP/s ({'BF16' if bf else 'TF32'})", "frac": flops / (avg[kdom] / 1e3) / peak,
+                "unit": f"TFLOP/s ({fmt})", "frac": flops / (avg[kdom] / 1e3) / peak,
                 "traffic": traffic_for(args, name, p.norm),
-                "peak_source": ("measured bf16 dense peak of MEASURED_PEAKS.json" if bf else
+                "peak_source": ("measured bf16 dense peak of MEASURED_PEAKS.json (fp16 dense rate = bf16)" if f16 else
                                 "measured bf16 dense peak of MEASURED_PEAKS.json x 1.1/2.25 (nominal TF32/BF16)"),
-                "flops_per_pair": 2 * npass * kk,
+                "flops_per_pair": fpp,
                 "alu_view": {k: alu[k] for k in ("achieved", "peak", "frac", "i_pair")}}
 
     e2e = None
@@ -867,6 +870,8 @@ def run_ours(args):
         line = wl_single(ctx, w, [W.cluster_d16()], precisions=("tc_tf32",), with_est=False, flush=False)
     elif w == "cluster_d16_bf16":
         line = wl_single(ctx, w, [W.cluster_d16()], precisions=("tc_bf16",), with_est=False, flush=False)
+    elif w == "cluster_d16_fp16":
+        line = wl_single(ctx, w, [W.cluster_d16()], precisions=("tc_fp16",), with_est=False, flush=False)
     elif w == "grad_d8":
         line = wl_single(ctx, w, [W.grad_d8()], with_bwd=True)
     elif w == "local_d4":

@@ -66,13 +66,18 @@ typedef enum {
     LIP_FP32 = 0,      /* FP32 arithmetic in the all-pairs scan, FP64 re-evaluation of winners */
     LIP_FP64 = 1,      /* FP64 data and results: FP32 screen, FP64 values (see lip_set_tuning) */
     LIP_TC_BF16 = 2,   /* L2 only: tensor-core cross term (bf16 split), exact FP64 rescreen  */
-    LIP_TC_TF32 = 3    /* L2 only: tensor-core cross term (tf32 split), exact FP64 rescreen  */
+    LIP_TC_TF32 = 3,   /* L2 only: tensor-core cross term (tf32 split), exact FP64 rescreen  */
+    LIP_TC_FP16 = 4    /* L2 only: tensor-core cross term (fp16 split), exact FP64 rescreen  */
     /* The tensor-core precisions need the L2 norm and no monotone coordinates (the squared
-     * distance is then one augmented product).  TF32: each operand split into a TF32 head
-     * and an FP32 tail, three kind::tf32 products.  BF16: each operand split into three
-     * bf16 pieces, six kind::f16 products.  lip_eval synchronises the stream once; the
-     * returned bounds are the exact FP64 envelopes (see the kernel's error bound), with
-     * the plain FP32 scan as fallback for queries with too many near-ties. */
+     * distance is then a cross product plus the two squared norms, which one more MMA adds).
+     * TF32: each operand split into a TF32 head and an FP32 tail, three kind::tf32
+     * products.  BF16: each operand split into three bf16 pieces, six kind::f16 products.
+     * FP16: each operand scaled by a power of two (from the data's bounding box) and split
+     * into two fp16 pieces, three kind::f16 products; a query farther than 2^14 / 2^7 times
+     * the box's half-diagonal from its centre in some coordinate (outside the fp16 range)
+     * goes to the fallback.  lip_eval synchronises the stream once; the returned bounds are
+     * the exact FP64 envelopes (see the kernel's error bound), with the plain FP32 scan as
+     * fallback for queries with too many near-ties. */
 } lip_precision;
 
 /* Largest dimension d accepted by lip_fit / lip_reserve. */
@@ -462,8 +467,9 @@ LIP_API lip_status lip_get_tuning(lip_handle h, int32_t* tile_groups, int32_t* s
  * be timed alone on the stream it runs on.  NULL, NULL turns this off. */
 LIP_API lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, void* ev_after_scan);
 
-/* LIP_TC_TF32 handles: number of queries of the last lip_eval whose candidate lists
- * overflowed and were recomputed by the plain FP32 scan (0 when the tensor-core form and
+/* Tensor-core handles (LIP_TC_*): number of queries of the last lip_eval whose candidate
+ * lists overflowed (or, for LIP_TC_FP16, that lay outside the fp16 range) and were
+ * recomputed by the plain FP32 scan (0 when the tensor-core form and
  * its exact rescreen settled every query); -1 for a NULL handle. */
 LIP_API int64_t lip_last_fallback(lip_handle h);
 

@@ -48,7 +48,7 @@ lip_status check_params(int32_t d, double M, const lip_params* p) {
     if (d < 1 || d > D_MAX) return fail(LIP_ERR_ARG, "d = %d is outside [1, %d]", d, D_MAX);
     if (!(M >= 0.0) || !std::isfinite(M)) return fail(LIP_ERR_ARG, "M = %g must be finite and >= 0", M);
     if (p->norm < LIP_L1 || p->norm > LIP_LINF) return fail(LIP_ERR_ARG, "norm = %d is not L1/L2/Linf", p->norm);
-    if (p->precision < LIP_FP32 || p->precision > LIP_TC_TF32)
+    if (p->precision < LIP_FP32 || p->precision > LIP_TC_FP16)
         return fail(LIP_ERR_ARG, "precision = %d is not a lip_precision", p->precision);
     if (p->mon)
         for (int i = 0; i < d; ++i)
@@ -57,7 +57,7 @@ lip_status check_params(int32_t d, double M, const lip_params* p) {
         for (int i = 0; i < d; ++i)
             if (!(p->w[i] > 0.0) || !std::isfinite(p->w[i]))
                 return fail(LIP_ERR_ARG, "w[%d] = %g must be finite and > 0", i, p->w[i]);
-    if (p->precision == LIP_TC_BF16 || p->precision == LIP_TC_TF32) {
+    if (p->precision == LIP_TC_BF16 || p->precision == LIP_TC_TF32 || p->precision == LIP_TC_FP16) {
         if (p->norm != LIP_L2) return fail(LIP_ERR_UNSUPPORTED, "tensor-core precision needs the L2 norm");
         if (p->mon)
             for (int i = 0; i < d; ++i)
@@ -165,8 +165,8 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
         if (h->mon[i] != 0) h->C++;
     }
     const int U = d - h->C;
-    h->tc = h->prec == LIP_TC_TF32 || h->prec == LIP_TC_BF16;
-    h->tc_bf = h->prec == LIP_TC_BF16;
+    h->tc = h->prec == LIP_TC_TF32 || h->prec == LIP_TC_BF16 || h->prec == LIP_TC_FP16;
+    h->tc_fmt = h->prec == LIP_TC_BF16 ? TC_BF16 : (h->prec == LIP_TC_FP16 ? TC_FP16 : TC_TF32);
     if ((h->prec == LIP_FP32 || h->tc) && exact_shape_available(h->C, U)) {
         h->exact = true;
         h->dl = d;
@@ -237,7 +237,7 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
     if (h->tc) {
         h->tc_ntiles_cap = ceil_div(cap, 256);
         struct { void** p; size_t n; const char* what; } tca[] = {
-            {reinterpret_cast<void**>(&h->tc_btiles), (size_t)h->tc_ntiles_cap * tc_tile_bytes_for(d, h->tc_bf),
+            {reinterpret_cast<void**>(&h->tc_btiles), (size_t)h->tc_ntiles_cap * tc_tile_bytes_for(d, h->tc_fmt),
              "tensor-core data tiles"},
             {reinterpret_cast<void**>(&h->tc_maxbits), 2 * sizeof(unsigned), "tensor-core bounds"},
         };
@@ -421,12 +421,12 @@ lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, v
     O.scratch = ob + p_b + x_b + y_b + b_b;
     if (h->tc_dirty) {
         CUDA_TRY(tc_prepare_data(static_cast<const float*>(h->X0), static_cast<const float*>(h->y0), h->N, d, scale,
-                                 h->tc_maxbits, h->tc_btiles, ntiles, h->tc_bf, O, st));
+                                 h->tc_maxbits, h->tc_btiles, ntiles, h->tc_fmt, O, st));
         count_launches(2 + spatial_order_launches());
         h->tc_dirty = false;
     }
     const int64_t nqt = ceil_div(nq, 128);
-    const size_t a_b = round_up((int64_t)(nqt * tc_a_bytes_for(d, h->tc_bf)), 256), eps_b = round_up(nq * 8, 256),
+    const size_t a_b = round_up((int64_t)(nqt * tc_a_bytes_for(d, h->tc_fmt)), 256), eps_b = round_up(nq * 16, 256),
                  rec_b = round_up((int64_t)(nq * tc_rec_bytes()), 256), list_b = round_up(nq * 4 + 4, 256),
                  qp_b = round_up(nq * 4, 256);
     LIP_TRY(h->tc_q.ensure(a_b + eps_b + rec_b + list_b + qp_b + spatial_order_scratch(nq), "tensor-core query scratch"));
@@ -438,10 +438,10 @@ lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, v
     QO.scratch = base + a_b + eps_b + rec_b + list_b + qp_b;
     if (h->ev_scan0) CUDA_TRY(cudaEventRecord(h->ev_scan0, st));
     CUDA_TRY(tc_eval_launch(static_cast<const float*>(Q), nq, d, scale, h->N, h->tc_maxbits, h->tc_btiles,
-                            ntiles, base, reinterpret_cast<float2*>(base + a_b), base + a_b + eps_b, h->w, h->M,
+                            ntiles, base, reinterpret_cast<float4*>(base + a_b), base + a_b + eps_b, h->w, h->M,
                             static_cast<const float*>(h->X0), static_cast<const float*>(h->y0), static_cast<float*>(g),
                             static_cast<float*>(lo), static_cast<float*>(hi), iu, il, fb_count, fb_list, h->status,
-                            h->tc_variant, h->tc_bf, O, QO, st));
+                            h->tc_variant, h->tc_fmt, O, QO, st));
     count_launches(3 + spatial_order_launches());
     if (h->ev_scan1) CUDA_TRY(cudaEventRecord(h->ev_scan1, st));
     int nfb = 0;

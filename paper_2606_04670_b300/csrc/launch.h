@@ -76,8 +76,10 @@ cudaError_t launch_estimate_layout(int elem_bytes, const HotParams& P, cudaStrea
 cudaError_t launch_estimate(int norm, int d, const EstParams& P, cudaStream_t st);
 cudaError_t launch_estimate_final(const EstFinalParams& P, cudaStream_t st);
 
-size_t tc_tile_bytes_for(int d, bool bf);
-size_t tc_a_bytes_for(int d, bool bf);
+// tensor-core operand formats
+constexpr int TC_TF32 = 0, TC_BF16 = 1, TC_FP16 = 2;
+size_t tc_tile_bytes_for(int d, int fmt);
+size_t tc_a_bytes_for(int d, int fmt);
 size_t tc_rec_bytes();
 // Spatial order of n points (row-major [n][d]): perm[position] = index, by a 16-bit Morton
 // key of the first min(d, 16) coordinates and a stable radix sort (deterministic).
@@ -100,13 +102,13 @@ struct TcQueryOrder {
     void* scratch;                   // spatial_order_scratch(nq)
 };
 cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, const double* scale,
-                            unsigned* maxbits, char* tiles, int64_t ntiles, bool bf, const TcDataOrder& O,
+                            unsigned* maxbits, char* tiles, int64_t ntiles, int fmt, const TcDataOrder& O,
                             cudaStream_t st);
 cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scale, int64_t N,
-                           const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float2* eps,
+                           const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float4* qc,
                            void* rec, const double* w, double M, const float* X0, const float* y0, float* g, float* lo,
                            float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, unsigned* err,
-                           int variant, bool bf, const TcDataOrder& O, const TcQueryOrder& QO, cudaStream_t st);
+                           int variant, int fmt, const TcDataOrder& O, const TcQueryOrder& QO, cudaStream_t st);
 cudaError_t tc_gather(const float* Q, int d, const int* list, int n, float* out, cudaStream_t st);
 cudaError_t tc_scatter(const int* list, int n, const float* g, const float* lo, const float* hi, const int32_t* iu,
                        const int32_t* il, float* G, float* LO, float* HI, int32_t* IU, int32_t* IL, cudaStream_t st);

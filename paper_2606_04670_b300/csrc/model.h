@@ -104,7 +104,7 @@ struct lip_model {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
     cudaEvent_t ev_scan0 = nullptr, ev_scan1 = nullptr;   // caller's timing events
-    // tensor-core form (LIP_TC_TF32)
+    // tensor-core forms (LIP_TC_TF32, LIP_TC_BF16, LIP_TC_FP16)
     // FP64 handles: a float copy of the layout for the FP32 screen of the exact FP64 scan
     void* hot32 = nullptr;
     int dl32 = 0, nch32 = 0, aux32 = 0;
@@ -115,7 +115,7 @@ struct lip_model {
     unsigned* s32_max = nullptr;       // [2] largest |scaled coordinate| and |y| (float bits)
     Scratch s64;                       // float queries and the FP32 pass's partials
     bool tc = false, tc_dirty = true;
-    bool tc_bf = false;                // BF16 three-piece split instead of TF32
+    int tc_fmt = 0;                    // TC_TF32, TC_BF16 or TC_FP16 (operand split)
     int tc_variant = 0;                // 0: 16 epilogue warps, 1: 8
     int64_t tc_ntiles_cap = 0;
     char* tc_btiles = nullptr;

@@ -50,6 +50,7 @@
 #include <cstdio>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "launch.h"
 
@@ -63,8 +64,14 @@ constexpr int TC_CAP = 8;
 // each (query, bound) keeps one candidate list per column slice.
 constexpr int TC_MAX_PARTS = 4;
 __host__ __device__ constexpr int tc_threads(int parts) { return 32 * (2 + 4 * parts); }
-constexpr float TC_C_EPS = 1.3e-5f;        // TF32 split (bound 9.3e-6)
+// Operand formats: the TF32 two-piece split, the BF16 three-piece split and the FP16
+// two-piece split (tc_fmt in launch.h).
+constexpr float TC_C_EPS_TF32 = 1.3e-5f;   // TF32 split (bound 9.3e-6)
 constexpr float TC_C_EPS_BF16 = 1.7e-5f;   // BF16 three-piece split (bound 1.3e-5)
+constexpr float TC_C_EPS_FP16 = 1.0e-5f;   // FP16 two-piece split (bound 7.2e-6)
+__host__ __device__ constexpr float tc_c_eps(int fmt) {
+    return fmt == TC_BF16 ? TC_C_EPS_BF16 : (fmt == TC_FP16 ? TC_C_EPS_FP16 : TC_C_EPS_TF32);
+}
 
 struct TcRec {      // candidate list of one (query, bound, column quarter)
     float U;        // upper bound of H_up (bound 0) or lower bound of H_lo (bound 1)
@@ -74,11 +81,15 @@ struct TcRec {      // candidate list of one (query, bound, column quarter)
 };
 
 // Operand geometry per format: TF32 keeps 2 pieces of 4-byte elements with K a multiple
-// of 8; BF16 keeps 3 pieces of 2-byte elements with K a multiple of 16.  Either way one
-// MMA consumes 32 bytes of K per row (two 8-row x 16-byte core matrices).
-__host__ __device__ constexpr int tc_k_for_dim(int d, bool bf) { return bf ? ((d + 15) / 16) * 16 : ((d + 7) / 8) * 8; }
-__host__ __device__ constexpr int tc_pieces(bool bf) { return bf ? 3 : 2; }
-__host__ __device__ constexpr int tc_esz(bool bf) { return bf ? 2 : 4; }
+// of 8; BF16 keeps 3 pieces and FP16 2 pieces of 2-byte elements with K a multiple of 16.
+// Either way one MMA consumes 32 bytes of K per row (two 8-row x 16-byte core matrices).
+__host__ __device__ constexpr int tc_k_for_dim(int d, int fmt) {
+    return fmt == TC_TF32 ? ((d + 7) / 8) * 8 : ((d + 15) / 16) * 16;
+}
+__host__ __device__ constexpr int tc_pieces(int fmt) { return fmt == TC_BF16 ? 3 : 2; }
+__host__ __device__ constexpr int tc_esz(int fmt) { return fmt == TC_TF32 ? 4 : 2; }
+// piece products per pair: TF32 and FP16 hi.hi + hi.lo + lo.hi; BF16 hh + hm + mh + hl + lh + mm
+__host__ __device__ constexpr int tc_npass(int fmt) { return fmt == TC_BF16 ? 6 : 3; }
 __host__ __device__ constexpr uint32_t tc_sbo_bytes(int row_bytes) { return (uint32_t)(row_bytes / 16) * 128u; }
 // The norm block: one more K-major operand of 32 bytes per row (one MMA's K), holding the
 // pieces of |x^|^2 against ones (B) and ones against the pieces of |q^|^2 (A).
@@ -86,12 +97,14 @@ constexpr int TC_NORM_ROW = 32;
 constexpr int TC_CHUNKS = TC_N / 32;       // 32-point chunks per tile
 // a data tile: the pieces, the norm block, y of its 256 points, then (min y, max y) of each
 // chunk (NaN when it holds no datum)
-__host__ __device__ constexpr int tc_tile_bytes(int K, bool bf) {
-    return tc_pieces(bf) * TC_N * K * tc_esz(bf) + TC_N * TC_NORM_ROW + TC_N * 4 + TC_CHUNKS * 8;
+__host__ __device__ constexpr int tc_tile_bytes(int K, int fmt) {
+    return tc_pieces(fmt) * TC_N * K * tc_esz(fmt) + TC_N * TC_NORM_ROW + TC_N * 4 + TC_CHUNKS * 8;
 }
 // a tile's slot in the shared-memory ring (1024-byte aligned operands in every stage)
-__host__ __device__ constexpr int tc_stage_bytes(int K, bool bf) { return (tc_tile_bytes(K, bf) + 1023) / 1024 * 1024; }
-__host__ __device__ constexpr int tc_a_bytes(int K, bool bf) { return tc_pieces(bf) * TC_M * K * tc_esz(bf) + TC_M * TC_NORM_ROW; }
+__host__ __device__ constexpr int tc_stage_bytes(int K, int fmt) { return (tc_tile_bytes(K, fmt) + 1023) / 1024 * 1024; }
+__host__ __device__ constexpr int tc_a_bytes(int K, int fmt) {
+    return tc_pieces(fmt) * TC_M * K * tc_esz(fmt) + TC_M * TC_NORM_ROW;
+}
 
 // byte offset of the element at row r, byte kb along K, in a canonical no-swizzle K-major
 // operand whose rows hold row_bytes of K (core matrices of 8 rows x 16 bytes)
@@ -101,9 +114,15 @@ __host__ __device__ inline uint32_t tc_off(int r, int kb, int row_bytes) {
 }
 
 // Writes the pieces of v at (r, k) of a piece-major operand block (piece p at p * piece_bytes).
-template <bool BF>
+template <int FMT>
 __device__ __forceinline__ void tc_store_pieces(char* base, int piece_bytes, int r, int k, int K, float v) {
-    if (BF) {
+    if (FMT == TC_FP16) {
+        const __half h = __float2half_rn(v);
+        const __half l = __float2half_rn(v - __half2float(h));
+        const uint32_t off = tc_off(r, k * 2, K * 2);
+        *reinterpret_cast<__half*>(base + off) = h;
+        *reinterpret_cast<__half*>(base + piece_bytes + off) = l;
+    } else if (FMT == TC_BF16) {
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
         const float r1 = v - __bfloat162float(h);
         const __nv_bfloat16 m = __float2bfloat16_rn(r1);
@@ -121,15 +140,18 @@ __device__ __forceinline__ void tc_store_pieces(char* base, int piece_bytes, int
     }
 }
 
-// Writes row r of a norm block: the pieces of nv at the front and the matching ones after
-// them when ones_first is false (B: [nv pieces, 1, 1(, 1)]), the ones first when it is true
-// (A: [1, 1(, 1), nv pieces]); the rest of the row is zero.  TF32: 2 pieces of 4 bytes
-// (hi truncated, FP32 remainder); BF16: 3 pieces of 2 bytes.
-template <bool BF>
+// Writes row r of a norm block.  B rows (ones_first false): the pieces of nv, then ones
+// matching the A side's norm pieces.  A rows (ones_first true): ones matching the B side's
+// pieces, then the pieces of nv.  The rest of the row is zero.  TF32: 2 pieces of 4 bytes
+// (hi truncated, FP32 remainder); BF16: 3 pieces of 2 bytes.  FP16: 2 pieces of 2 bytes,
+// and only |x^|^2 goes through the block (|q^|^2 would leave the f16 range for distant
+// queries; the epilogue adds it), so A rows are [1, 1, 0, ..].
+template <int FMT>
 __device__ __forceinline__ void tc_store_norm(char* base, int r, float nv, bool ones_first) {
-    const int np = tc_pieces(BF), per = TC_NORM_ROW / tc_esz(BF);
-    float pc[3];
-    if (BF) {
+    constexpr int np = tc_pieces(FMT), per = TC_NORM_ROW / tc_esz(FMT);
+    constexpr int nq = FMT == TC_FP16 ? 0 : np;          // pieces of the A side's norm
+    float pc[3] = {0.f, 0.f, 0.f};
+    if (FMT == TC_BF16) {
         const __nv_bfloat16 h = __float2bfloat16_rn(nv);
         const float r1 = nv - __bfloat162float(h);
         const __nv_bfloat16 m = __float2bfloat16_rn(r1);
@@ -137,19 +159,25 @@ __device__ __forceinline__ void tc_store_norm(char* base, int r, float nv, bool 
         pc[0] = __bfloat162float(h);
         pc[1] = __bfloat162float(m);
         pc[2] = __bfloat162float(__float2bfloat16_rn(r2));
+    } else if (FMT == TC_FP16) {
+        pc[0] = __half2float(__float2half_rn(nv));
+        pc[1] = __half2float(__float2half_rn(nv - pc[0]));
     } else {
         pc[0] = __uint_as_float(__float_as_uint(nv) & 0xFFFFE000u);
         pc[1] = nv - pc[0];
-        pc[2] = 0.f;
     }
     for (int k = 0; k < per; ++k) {
         float v = 0.f;
-        if (k < 2 * np) {
-            const bool one = ones_first ? (k < np) : (k >= np);
-            v = one ? 1.f : pc[ones_first ? k - np : k];
+        if (ones_first) {
+            if (k < np) v = 1.f;
+            else if (k < np + nq) v = pc[k - np];
+        } else {
+            if (k < np) v = pc[k];
+            else if (k < np + nq) v = 1.f;
         }
-        const uint32_t off = tc_off(r, k * tc_esz(BF), TC_NORM_ROW);
-        if (BF) *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+        const uint32_t off = tc_off(r, k * tc_esz(FMT), TC_NORM_ROW);
+        if (FMT == TC_BF16) *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+        else if (FMT == TC_FP16) *reinterpret_cast<__half*>(base + off) = __float2half_rn(v);
         else *reinterpret_cast<float*>(base + off) = v;
     }
 }
@@ -166,7 +194,6 @@ struct TcPrepParams {
     unsigned* maxbits;    // [2]: float bits of R and of max|y|
     char* tiles;          // [ntiles][tile_bytes]
     int64_t ntiles;
-    bool bf;              // BF16 pieces instead of TF32
     const int* perm;      // [N] position -> data index (tiles are in position order)
     float* Xs;            // [N][d] position-ordered copy of the data
     float* ys;            // [N]
@@ -178,18 +205,37 @@ __device__ __forceinline__ double tc_centre(const float2 b, double scale) {
     return scale * 0.5 * ((double)b.x + (double)b.y);
 }
 
+// FP16 operands are scaled by 2^k (exactly, a power of two) with k chosen from the box's
+// half-diagonal Rb >= max |x^|: Rb 2^k lies in [64, 128), so every centred data coordinate
+// stays below 128 and |x^|^2 below 2^14 in the f16 range; queries up to 2^14 per coordinate
+// fit (-2 q^ <= 2^15).  k = 0 for a box of one point.
+constexpr float TC_F16_QMAX = 16384.f;
+__device__ __forceinline__ int tc_f16_shift(const float2* bounds, const double* scale, int d) {
+    double r2 = 0.0;
+    for (int j = 0; j < d; ++j) {
+        const double h = 0.5 * scale[j] * ((double)bounds[j].y - (double)bounds[j].x);
+        r2 += h * h;
+    }
+    if (!(r2 > 0.0)) return 0;
+    int e;
+    frexp(sqrt(r2), &e);                   // Rb = m 2^e, m in [0.5, 1): Rb 2^(7 - e) in [64, 128)
+    const int k = 7 - e;
+    return k < -60 ? -60 : (k > 60 ? 60 : k);
+}
+
 // One thread per (padded) position: the row of the B pieces, of the norm block and y of
 // the datum at that position, in the tile layout, and the position-ordered copy of its
 // row.  A padding position has zero rows (s~ = 0) and y = NaN.
-template <bool BF>
+template <int FMT>
 __global__ void tc_build_b_kernel(const TcPrepParams P) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= P.ntiles * TC_N) return;
     const int64_t t = k / TC_N;
     const int r = (int)(k % TC_N);
-    char* tile = P.tiles + t * (int64_t)tc_tile_bytes(P.K, BF);
-    const int piece = TC_N * P.K * tc_esz(BF);
-    char* norm = tile + tc_pieces(BF) * piece;
+    char* tile = P.tiles + t * (int64_t)tc_tile_bytes(P.K, FMT);
+    const int piece = TC_N * P.K * tc_esz(FMT);
+    char* norm = tile + tc_pieces(FMT) * piece;
+    const double f = FMT == TC_FP16 ? ldexp(1.0, tc_f16_shift(P.bounds, P.scale, P.d)) : 1.0;
     float* yv = reinterpret_cast<float*>(norm + TC_N * TC_NORM_ROW);
     float b[16];
     for (int j = 0; j < P.K; ++j) b[j] = 0.f;
@@ -204,10 +250,10 @@ __global__ void tc_build_b_kernel(const TcPrepParams P) {
             P.Xs[k * P.d + j] = x;
             const double c = tc_centre(P.bounds[j], P.scale[j]);
             const float xh = (float)(P.scale[j] * (double)x - c);
-            b[j] = xh;
+            b[j] = (float)((double)xh * f);
             n2 += (double)xh * (double)xh;
         }
-        tc_store_norm<BF>(norm, r, (float)n2, false);
+        tc_store_norm<FMT>(norm, r, (float)(n2 * f * f), false);
         real = true;
         yy = P.y0[src];
         P.ys[k] = yy;
@@ -222,7 +268,7 @@ __global__ void tc_build_b_kernel(const TcPrepParams P) {
         atomicMax(&P.maxbits[0], rbits);
         atomicMax(&P.maxbits[1], ybits);
     }
-    for (int j = 0; j < P.K; ++j) tc_store_pieces<BF>(tile, piece, r, j, P.K, b[j]);
+    for (int j = 0; j < P.K; ++j) tc_store_pieces<FMT>(tile, piece, r, j, P.K, b[j]);
     if (!real)
         for (int kb = 0; kb < TC_NORM_ROW; kb += 4) *reinterpret_cast<float*>(norm + tc_off(r, kb, TC_NORM_ROW)) = 0.f;
     yv[r] = yy;
@@ -254,42 +300,55 @@ struct TcQueryParams {
     int64_t N;
     const unsigned* maxbits;
     char* atiles;          // [nqt][a_bytes]: the A pieces
-    float2* eps;           // [nq]: (eps, eps_v)
+    float4* qc;            // [nq] per-query constants of the scan (below)
 };
 
-// One thread per (padded) query: its row of the A pieces and its error bounds.
-template <bool BF>
+// Per-query constants of the scan, one float4: x = eps, y = eps_v (the error bounds), and
+// for FP16 z = |q^|^2 (added in the epilogue) and w = 2^-2k (the products' unscaling; w < 0
+// marks a query outside the f16 range, which goes through the fallback).  TF32 and BF16:
+// z = 0, w = 1.
+
+// One thread per (padded) query: its row of the A pieces and its constants.
+template <int FMT>
 __global__ void tc_build_a_kernel(const TcQueryParams P) {
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nqp = (P.nq + TC_M - 1) / TC_M * TC_M;
     if (qi >= nqp) return;
     const int64_t t = qi / TC_M;
     const int r = (int)(qi % TC_M);
-    char* at = P.atiles + t * (int64_t)tc_a_bytes(P.K, BF);
-    const int piece = TC_M * P.K * tc_esz(BF);
+    char* at = P.atiles + t * (int64_t)tc_a_bytes(P.K, FMT);
+    const int piece = TC_M * P.K * tc_esz(FMT);
     float a[16];
     for (int j = 0; j < P.K; ++j) a[j] = 0.f;
-    char* norm = at + tc_pieces(BF) * piece;
+    char* norm = at + tc_pieces(FMT) * piece;
     bool real = false;
     if (qi < P.nq) {
         const int64_t src = P.qperm[qi];
+        const int ks = FMT == TC_FP16 ? tc_f16_shift(P.bounds, P.scale, P.d) : 0;
+        const double f = ldexp(1.0, ks);
         double n2 = 0.0;
+        bool inside = true;
         for (int j = 0; j < P.d; ++j) {
             const double c = tc_centre(P.bounds[j], P.scale[j]);
             const float qh = (float)(P.scale[j] * (double)P.Q[src * P.d + j] - c);
-            a[j] = -2.f * qh;
+            const float qs = (float)((double)qh * f);
+            if (FMT == TC_FP16 && fabsf(qs) > TC_F16_QMAX) inside = false;   // also +-inf; NaN stays
+            a[j] = -2.f * qs;
             n2 += (double)qh * (double)qh;
         }
         const double R = (double)__uint_as_float(P.maxbits[0]);
         const double Y = (double)__uint_as_float(P.maxbits[1]);
         const double nq = sqrt(n2);
-        const float eps = (float)((double)(BF ? TC_C_EPS_BF16 : TC_C_EPS) * (nq + R) * (nq + R));
+        const float eps = (float)((double)tc_c_eps(FMT) * (nq + R) * (nq + R));
         const float epsv = (float)(ldexp(1.0, -19) * (Y + nq + R));
-        P.eps[qi] = make_float2(eps, epsv);
-        tc_store_norm<BF>(norm, r, (float)n2, true);
+        const float usc = (float)ldexp(1.0, -2 * ks);
+        P.qc[qi] = make_float4(eps, epsv, FMT == TC_FP16 ? (float)n2 : 0.f, inside ? usc : -usc);
+        if (!inside)
+            for (int j = 0; j < P.K; ++j) a[j] = 0.f;
+        tc_store_norm<FMT>(norm, r, (float)n2, true);
         real = true;
     }
-    for (int j = 0; j < P.K; ++j) tc_store_pieces<BF>(at, piece, r, j, P.K, a[j]);
+    for (int j = 0; j < P.K; ++j) tc_store_pieces<FMT>(at, piece, r, j, P.K, a[j]);
     if (!real)
         for (int kb = 0; kb < TC_NORM_ROW; kb += 4) *reinterpret_cast<float*>(norm + tc_off(r, kb, TC_NORM_ROW)) = 0.f;
 }
@@ -305,9 +364,9 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, int row_bytes) {
     return d;                                               // no swizzle, base offset 0
 }
 
-template <bool BF>
+template <int FMT>
 __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
-    if (BF)   // both operands bf16 (the instruction descriptor says so for A and for B)
+    if (FMT != TC_TF32)   // both operands bf16, or both f16 (the instruction descriptor says which)
         asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
                      ::"r"(dtmem), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
@@ -375,7 +434,7 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 struct TcScanParams {
     const char* atiles;
     const char* btiles;
-    const float2* eps;     // [nq]: (eps, eps_v)
+    const float4* qc;      // [nq] per-query constants (eps, eps_v, FP16: |q^|^2 and 2^-2k)
     int64_t nq;
     int64_t ntiles;
     TcRec* rec;            // [nq positions][2 bounds][TC_MAX_PARTS column slices]
@@ -404,12 +463,12 @@ __device__ __forceinline__ void tc_append(TcRec* R, int& n, int id, float L, flo
     ++n;
 }
 
-template <int K, int PARTS, bool BF>
+template <int K, int PARTS, int FMT>
 __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcScanParams P) {
     constexpr int EPI_WARPS = 4 * PARTS;
-    constexpr int TILE_BYTES = tc_tile_bytes(K, BF), STAGE_BYTES = tc_stage_bytes(K, BF);
-    constexpr int A_BYTES = tc_a_bytes(K, BF);
-    constexpr int ROW_BYTES = K * tc_esz(BF);
+    constexpr int TILE_BYTES = tc_tile_bytes(K, FMT), STAGE_BYTES = tc_stage_bytes(K, FMT);
+    constexpr int A_BYTES = tc_a_bytes(K, FMT);
+    constexpr int ROW_BYTES = K * tc_esz(FMT);
     constexpr int KS = ROW_BYTES / 32;                  // MMAs per pass (32 bytes of K each)
     constexpr int A_PIECE = TC_M * ROW_BYTES, B_PIECE = TC_N * ROW_BYTES;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -469,8 +528,8 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             // D = FP32 (bits 4-5); A and B formats (bits 7-9, 10-12): TF32 = 2 in kind::tf32,
-            // BF16 = 1 in kind::f16; K-major A and B; N / 8 and M / 16
-            const uint32_t fmt = BF ? 1u : 2u;
+            // F16 = 0 and BF16 = 1 in kind::f16; K-major A and B; N / 8 and M / 16
+            const uint32_t fmt = FMT == TC_BF16 ? 1u : (FMT == TC_FP16 ? 0u : 2u);
             const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_N >> 3) << 17) |
                                    ((uint32_t)(TC_M >> 4) << 24);
             const uint32_t a0 = smem_u32(sA);
@@ -483,20 +542,20 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t b0 = smem_u32(sB + (size_t)s * STAGE_BYTES);
                     const uint32_t d = tb + (uint32_t)b * TC_N;
-                    // piece pairs: TF32 hi.hi, hi.lo, lo.hi; BF16 hh, hm, mh, hl, lh, mm
-                    constexpr int NPASS = BF ? 6 : 3;
+                    // piece pairs: TF32 and FP16 hi.hi, hi.lo, lo.hi; BF16 hh, hm, mh, hl, lh, mm
+                    constexpr int NPASS = tc_npass(FMT);
                     constexpr int PA[6] = {0, 0, 1, 0, 2, 1}, PB[6] = {0, 1, 0, 2, 0, 1};
 #pragma unroll
                     for (int ps = 0; ps < NPASS; ++ps) {
                         const uint32_t ap = a0 + PA[ps] * A_PIECE, bp = b0 + PB[ps] * B_PIECE;
 #pragma unroll
                         for (int ks = 0; ks < KS; ++ks)
-                            tc_mma<BF>(d, tc_desc(ap + ks * 256, ROW_BYTES), tc_desc(bp + ks * 256, ROW_BYTES), idesc,
+                            tc_mma<FMT>(d, tc_desc(ap + ks * 256, ROW_BYTES), tc_desc(bp + ks * 256, ROW_BYTES), idesc,
                                        (ps > 0 || ks > 0) ? 1u : 0u);
                     }
-                    // the norm block: |x^|^2 + |q^|^2 in one more MMA of 32 bytes of K
-                    tc_mma<BF>(d, tc_desc(a0 + tc_pieces(BF) * A_PIECE, TC_NORM_ROW),
-                               tc_desc(b0 + tc_pieces(BF) * B_PIECE, TC_NORM_ROW),
+                    // the norm block: |x^|^2 (+ |q^|^2 but for FP16) in one more MMA of 32 bytes of K
+                    tc_mma<FMT>(d, tc_desc(a0 + tc_pieces(FMT) * A_PIECE, TC_NORM_ROW),
+                               tc_desc(b0 + tc_pieces(FMT) * B_PIECE, TC_NORM_ROW),
                                idesc, 1u);
                     tc_commit(&b_empty[s]);
                     tc_commit(&acc_full[b]);
@@ -510,21 +569,25 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
         const int quarter = warp % 4, part = (warp - 2) / 4;
         const int64_t qi = qt * TC_M + quarter * 32 + lane;
         const bool valid = qi < P.nq;
-        const float2 e2 = valid ? P.eps[qi] : make_float2(1.f, 1.f);
+        const float4 qc = valid ? P.qc[qi] : make_float4(1.f, 1.f, 0.f, 1.f);
         // a zero bound (M = 0) must not turn eps * rsqrt(0) into NaN
-        const float eps = fmaxf(e2.x, 1e-30f), epsv = e2.y;
+        const float eps = fmaxf(qc.x, 1e-30f), epsv = qc.y;
+        // FP16: s~ = |q^|^2 + 2^-2k (product); a query outside the f16 range (w < 0) keeps
+        // overflowed lists, so it goes through the fallback
+        const float2 nq22 = make_float2(qc.z, qc.z), usc2 = make_float2(fabsf(qc.w), fabsf(qc.w));
+        const bool act = valid && qc.w > 0.f;
         TcRec* Ru = P.rec + (valid ? ((qi * 2 + 0) * TC_MAX_PARTS + part) : 0);
         TcRec* Rl = P.rec + (valid ? ((qi * 2 + 1) * TC_MAX_PARTS + part) : 0);
         const float INF = __int_as_float(0x7f800000);
         float U = INF, Bl = -INF;
-        int nu = 0, nl = 0;
+        int nu = act ? 0 : -1, nl = nu;
         for (int64_t t = 0; t < T; ++t) {
             const int s = (int)(t % TC_STAGES), b = (int)(t & 1);
             if (!mbar_wait_bounded(&acc_full[b], (uint32_t)((t / 2) & 1), P.err)) break;
             // acquire the tile's y values and chunk bounds written by the bulk copy
             if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / TC_STAGES) & 1), P.err)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const float* ys = reinterpret_cast<const float*>(sB + (size_t)s * STAGE_BYTES + tc_pieces(BF) * B_PIECE +
+            const float* ys = reinterpret_cast<const float*>(sB + (size_t)s * STAGE_BYTES + tc_pieces(FMT) * B_PIECE +
                                                              TC_N * TC_NORM_ROW);
             const float2* cbs = reinterpret_cast<const float2*>(ys + TC_N);
             // two 32-column chunks per TMEM wait: both loads are in flight together
@@ -553,6 +616,7 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                     for (int e = 0; e < 32; e += 4)
                         cs[(e / 4) % 4] = min3f(min3f(cs[(e / 4) % 4], sv[h][e], sv[h][e + 1]), sv[h][e + 2], sv[h][e + 3]);
                     csm[h] = min2f(min3f(cs[0], cs[1], cs[2]), cs[3]);
+                    if (FMT == TC_FP16) csm[h] = fmaf(csm[h], usc2.x, nq22.x);   // monotone: the min s~
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -560,7 +624,7 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                     const float slo = sqrt_approx(fmaxf(csm[h] - eps, 0.f) * (1.f - 0x1p-22f)) * (1.f - 0x1p-21f);
                     const float lbu = (cb.x + slo) - 0x1p-22f * (fabsf(cb.x) + slo);
                     const float ubl = (cb.y - slo) + 0x1p-22f * (fabsf(cb.y) + slo);
-                    take[h] = __any_sync(0xffffffffu, valid && (lbu <= U || ubl >= Bl));
+                    take[h] = __any_sync(0xffffffffu, act && (lbu <= U || ubl >= Bl));
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -575,8 +639,13 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                     for (int e = 0; e < 32; e += 4) {
                         const int a = (e / 4) % 4;
                         const float4 y4 = *reinterpret_cast<const float4*>(ys + col + e);
-                        const float2 r0 = make_float2(sqrt_approx(fabsf(sv[h][e])), sqrt_approx(fabsf(sv[h][e + 1])));
-                        const float2 r1 = make_float2(sqrt_approx(fabsf(sv[h][e + 2])), sqrt_approx(fabsf(sv[h][e + 3])));
+                        float2 s0 = make_float2(sv[h][e], sv[h][e + 1]), s1 = make_float2(sv[h][e + 2], sv[h][e + 3]);
+                        if (FMT == TC_FP16) {
+                            s0 = fma2(s0, usc2, nq22);
+                            s1 = fma2(s1, usc2, nq22);
+                        }
+                        const float2 r0 = make_float2(sqrt_approx(fabsf(s0.x)), sqrt_approx(fabsf(s0.y)));
+                        const float2 r1 = make_float2(sqrt_approx(fabsf(s1.x)), sqrt_approx(fabsf(s1.y)));
                         const float2 y0 = make_float2(y4.x, y4.y), y1 = make_float2(y4.z, y4.w);
                         const float2 u0 = add2(y0, r0), u1 = add2(y1, r1), l0 = sub2(y0, r0), l1 = sub2(y1, r1);
                         cu[a] = min3f(min3f(cu[a], u0.x, u0.y), u1.x, u1.y);
@@ -584,7 +653,7 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                     }
                     const float cum = min2f(min3f(cu[0], cu[1], cu[2]), cu[3]);
                     const float clm = max2f(max3f(cl[0], cl[1], cl[2]), cl[3]);
-                    if (valid) {
+                    if (act) {
                         const float dlt = 1.001f * eps * rsqrt_approx(fmaxf(csm[h], eps)) + epsv;
                         U = fminf(U, cum + dlt);
                         if (cum - dlt <= U) tc_append(Ru, nu, chunk, cum - dlt, U, true);
@@ -770,15 +839,15 @@ __global__ void tc_scatter_kernel(const int* list, int n, const float* g, const 
 
 // --------------------------------------------------------------- launchers
 
-size_t tc_tile_bytes_for(int d, bool bf) { return (size_t)tc_tile_bytes(tc_k_for_dim(d, bf), bf); }
-size_t tc_a_bytes_for(int d, bool bf) { return (size_t)tc_a_bytes(tc_k_for_dim(d, bf), bf); }
+size_t tc_tile_bytes_for(int d, int fmt) { return (size_t)tc_tile_bytes(tc_k_for_dim(d, fmt), fmt); }
+size_t tc_a_bytes_for(int d, int fmt) { return (size_t)tc_a_bytes(tc_k_for_dim(d, fmt), fmt); }
 size_t tc_rec_bytes() { return sizeof(TcRec) * 2 * TC_MAX_PARTS; }   // candidate lists per query
 
 
 // The data's spatial order, then the tiles in that order, the position-ordered copies and
 // the chunk bounds.
 cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, const double* scale,
-                            unsigned* maxbits, char* tiles, int64_t ntiles, bool bf, const TcDataOrder& O,
+                            unsigned* maxbits, char* tiles, int64_t ntiles, int fmt, const TcDataOrder& O,
                             cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(O.bounds, 0, D_MAX * sizeof(float2), st);   // an empty set centres at 0
     if (e == cudaSuccess) e = spatial_order(X0, N, d, O.dperm, O.bounds, O.scratch, st);
@@ -788,8 +857,7 @@ cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, 
     P.y0 = y0;
     P.N = N;
     P.d = d;
-    P.K = tc_k_for_dim(d, bf);
-    P.bf = bf;
+    P.K = tc_k_for_dim(d, fmt);
     for (int j = 0; j < D_MAX; ++j) P.scale[j] = scale[j];
     P.bounds = O.bounds;
     P.maxbits = maxbits;
@@ -802,39 +870,42 @@ cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, 
     if (e != cudaSuccess) return e;
     const int64_t rows = ntiles * TC_N;
     if (rows > 0) {
-        if (bf) tc_build_b_kernel<true><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P);
-        else tc_build_b_kernel<false><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P);
+        const unsigned blocks = (unsigned)((rows + 255) / 256);
+        if (fmt == TC_BF16) tc_build_b_kernel<TC_BF16><<<blocks, 256, 0, st>>>(P);
+        else if (fmt == TC_FP16) tc_build_b_kernel<TC_FP16><<<blocks, 256, 0, st>>>(P);
+        else tc_build_b_kernel<TC_TF32><<<blocks, 256, 0, st>>>(P);
         const int64_t nchunks = ntiles * TC_CHUNKS;
         tc_chunk_bounds_kernel<<<(unsigned)((nchunks + 255) / 256), 256, 0, st>>>(O.ys, N, nchunks, tiles,
-                                                                                 tc_tile_bytes(P.K, bf));
+                                                                                 tc_tile_bytes(P.K, fmt));
     }
     return cudaGetLastError();
 }
 
-template <int K, int PARTS, bool BF>
+template <int K, int PARTS, int FMT>
 static cudaError_t launch_tc_scan_k(const TcScanParams& P, int64_t nqt, cudaStream_t st) {
-    const size_t smem = (size_t)tc_a_bytes(K, BF) + (size_t)TC_STAGES * tc_stage_bytes(K, BF);
+    const size_t smem = (size_t)tc_a_bytes(K, FMT) + (size_t)TC_STAGES * tc_stage_bytes(K, FMT);
     static cudaError_t attr =
-        cudaFuncSetAttribute(tc_scan_kernel<K, PARTS, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(tc_scan_kernel<K, PARTS, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return attr;
-    tc_scan_kernel<K, PARTS, BF><<<(unsigned)nqt, tc_threads(PARTS), smem, st>>>(P);
+    tc_scan_kernel<K, PARTS, FMT><<<(unsigned)nqt, tc_threads(PARTS), smem, st>>>(P);
     return cudaGetLastError();
 }
 
 template <int PARTS>
-static cudaError_t launch_tc_scan_parts(int K, bool bf, const TcScanParams& P, int64_t nqt, cudaStream_t st) {
-    if (bf) return launch_tc_scan_k<16, PARTS, true>(P, nqt, st);   // d <= 16: K = 16
-    if (K == 8) return launch_tc_scan_k<8, PARTS, false>(P, nqt, st);
-    return launch_tc_scan_k<16, PARTS, false>(P, nqt, st);
+static cudaError_t launch_tc_scan_parts(int K, int fmt, const TcScanParams& P, int64_t nqt, cudaStream_t st) {
+    if (fmt == TC_BF16) return launch_tc_scan_k<16, PARTS, TC_BF16>(P, nqt, st);   // d <= 16: K = 16
+    if (fmt == TC_FP16) return launch_tc_scan_k<16, PARTS, TC_FP16>(P, nqt, st);
+    if (K == 8) return launch_tc_scan_k<8, PARTS, TC_TF32>(P, nqt, st);
+    return launch_tc_scan_k<16, PARTS, TC_TF32>(P, nqt, st);
 }
 
 // Queries: build A, scan, rescreen.  Returns the fallback count through fb (device).
 cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scale, int64_t N,
-                           const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float2* eps,
+                           const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float4* qc,
                            void* rec, const double* w, double M, const float* X0, const float* y0, float* g, float* lo,
                            float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, unsigned* err,
-                           int variant, bool bf, const TcDataOrder& O, const TcQueryOrder& QO, cudaStream_t st) {
-    const int K = tc_k_for_dim(d, bf);
+                           int variant, int fmt, const TcDataOrder& O, const TcQueryOrder& QO, cudaStream_t st) {
+    const int K = tc_k_for_dim(d, fmt);
     // the queries' spatial order: a tile of 128 positions holds nearby queries
     cudaError_t e = spatial_order(Q, nq, d, QO.qperm, nullptr, QO.scratch, st);
     if (e != cudaSuccess) return e;
@@ -851,20 +922,22 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     A.N = N;
     A.maxbits = maxbits;
     A.atiles = atiles;
-    A.eps = eps;
-    if (bf) tc_build_a_kernel<true><<<(unsigned)((nqt * TC_M + 255) / 256), 256, 0, st>>>(A);
-    else tc_build_a_kernel<false><<<(unsigned)((nqt * TC_M + 255) / 256), 256, 0, st>>>(A);
+    A.qc = qc;
+    const unsigned ablocks = (unsigned)((nqt * TC_M + 255) / 256);
+    if (fmt == TC_BF16) tc_build_a_kernel<TC_BF16><<<ablocks, 256, 0, st>>>(A);
+    else if (fmt == TC_FP16) tc_build_a_kernel<TC_FP16><<<ablocks, 256, 0, st>>>(A);
+    else tc_build_a_kernel<TC_TF32><<<ablocks, 256, 0, st>>>(A);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     TcScanParams S{};
     S.atiles = atiles;
     S.btiles = btiles;
-    S.eps = eps;
+    S.qc = qc;
     S.nq = nq;
     S.ntiles = ntiles;
     S.rec = static_cast<TcRec*>(rec);
     S.err = err;
-    e = parts == 2 ? launch_tc_scan_parts<2>(K, bf, S, nqt, st) : launch_tc_scan_parts<4>(K, bf, S, nqt, st);
+    e = parts == 2 ? launch_tc_scan_parts<2>(K, fmt, S, nqt, st) : launch_tc_scan_parts<4>(K, fmt, S, nqt, st);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(fb_count, 0, sizeof(int), st)) != cudaSuccess) return e;
     TcRescreenParams R{};

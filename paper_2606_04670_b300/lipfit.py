@@ -26,14 +26,15 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "lipfit.h")
 LIP_OK, LIP_ERR_ARG, LIP_ERR_NONFINITE, LIP_ERR_OOM, LIP_ERR_CUDA = 0, 1, 2, 3, 4
 LIP_ERR_CAPACITY, LIP_ERR_TIMEOUT, LIP_ERR_UNSUPPORTED, LIP_ERR_NO_DEVICE, LIP_ERR_STATE = 5, 6, 7, 8, 9
 LIP_L1, LIP_L2, LIP_LINF = 1, 2, 3
-LIP_FP32, LIP_FP64, LIP_TC_BF16, LIP_TC_TF32 = 0, 1, 2, 3
+LIP_FP32, LIP_FP64, LIP_TC_BF16, LIP_TC_TF32, LIP_TC_FP16 = 0, 1, 2, 3, 4
 LIP_NOALLOC_N_MAX = 32768
 LIP_LOCAL_KNOTS_MAX = 31
 LIP_LOCAL_SAMPLE_MAX = 1 << 20
 NORMS = {"L1": LIP_L1, "L2": LIP_L2, "Linf": LIP_LINF, "LINF": LIP_LINF,
          LIP_L1: LIP_L1, LIP_L2: LIP_L2, LIP_LINF: LIP_LINF}
 PRECISIONS = {"fp32": LIP_FP32, "fp64": LIP_FP64, "tc_bf16": LIP_TC_BF16, "tc_tf32": LIP_TC_TF32,
-              LIP_FP32: LIP_FP32, LIP_FP64: LIP_FP64, LIP_TC_BF16: LIP_TC_BF16, LIP_TC_TF32: LIP_TC_TF32}
+              "tc_fp16": LIP_TC_FP16, LIP_FP32: LIP_FP32, LIP_FP64: LIP_FP64, LIP_TC_BF16: LIP_TC_BF16,
+              LIP_TC_TF32: LIP_TC_TF32, LIP_TC_FP16: LIP_TC_FP16}
 
 
 class lip_params(ctypes.Structure):

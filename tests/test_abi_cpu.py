@@ -42,6 +42,8 @@ def _arr(*shape):
     ({"w": [1.0, float("nan")]}, L.LIP_ERR_ARG),
     ({"norm": L.LIP_L1, "precision": L.LIP_TC_BF16}, L.LIP_ERR_UNSUPPORTED),
     ({"norm": L.LIP_LINF, "precision": L.LIP_TC_TF32}, L.LIP_ERR_UNSUPPORTED),
+    ({"norm": L.LIP_L1, "precision": L.LIP_TC_FP16}, L.LIP_ERR_UNSUPPORTED),
+    ({"precision": 5}, L.LIP_ERR_ARG),
     ({"nullX": True}, L.LIP_ERR_ARG),
 ])
 def test_fit_argument_errors(kw, status):
@@ -117,7 +119,8 @@ def test_batch_argument_errors():
 def test_tensor_core_precision_rules():
     X, y = _arr(8, 2), _arr(8)
     for norm, prec, mon in [(L.LIP_L1, L.LIP_TC_TF32, None), (L.LIP_L2, L.LIP_TC_TF32, [1, 0]),
-                            (L.LIP_L1, L.LIP_TC_BF16, None), (L.LIP_L2, L.LIP_TC_BF16, [0, -1])]:
+                            (L.LIP_L1, L.LIP_TC_BF16, None), (L.LIP_L2, L.LIP_TC_BF16, [0, -1]),
+                            (L.LIP_LINF, L.LIP_TC_FP16, None), (L.LIP_L2, L.LIP_TC_FP16, [1, 1])]:
         p, keep = L.make_params(norm, prec, mon, None)
         s, h = L.lip_fit(X.ctypes.data, y.ctypes.data, 8, 2, 1.0, p)
         assert s == L.LIP_ERR_UNSUPPORTED and not h.value, L.last_error()

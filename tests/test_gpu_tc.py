@@ -1,5 +1,6 @@
-"""Tensor-core L2 form (LIP_TC_TF32, LIP_TC_BF16): the TF32- or BF16-split product on
-tcgen05 with an error bound, candidate pruning and an exact FP64 rescreen.  Its bounds are the FP64
+"""Tensor-core L2 form (LIP_TC_TF32, LIP_TC_BF16, LIP_TC_FP16): the TF32-, BF16- or
+FP16-split product on tcgen05 with an error bound, candidate pruning and an exact FP64
+rescreen.  Its bounds are the FP64
 envelopes, so indices must match the oracle's wherever the oracle's gap exceeds
 1e-9 M diam (far below the FP32 tolerance).  Needs a CUDA device."""
 import numpy as np
@@ -162,3 +163,66 @@ def test_bf16_cluster_subsample(oracle_mod):
     rt, _ = _tc_eval(p, "tc_tf32")
     for k in ("idx_up", "idx_lo"):
         assert np.array_equal(r[k], rt[k]) or fb > 0
+
+
+@pytest.mark.parametrize("d,weighted", [(1, False), (2, True), (5, False), (8, True), (13, False), (16, True)])
+def test_fp16_random_shapes(oracle_mod, d, weighted):
+    """The FP16 two-piece split (operands scaled by a power of two into the fp16 range):
+    the same exact results."""
+    p = W.random_problem(990 + d, 5_003, d, 1_201, norm=W.NORM_L2, weighted=weighted)
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm, w=p.w)
+    r, fb = _tc_eval(p, "tc_fp16")
+    _check_exact(p, r, orc, f"fp16 d={d}", fb)
+    if d >= 6:
+        assert fb <= 2, f"{fb} fallback queries at d={d}"
+
+
+def test_fp16_cluster_and_far_queries(oracle_mod):
+    """The precision workload's shape at a reduced size, plus queries far outside the data
+    (beyond the fp16 range after scaling): those go through the plain scan, the rest stay
+    exact."""
+    p = W.cluster_d16(n_data=30_000, n_query=1_500)
+    Q = p.Q.copy()
+    far = np.array([3, 700, 1499])
+    Q[far] *= 1e6                      # far beyond 2^14 times the box's half-diagonal
+    ps = W.Problem("f", p.X, p.y, Q, p.M, p.norm, None, None)
+    orc = oracle_mod.evaluate(p.X, p.y, Q, p.M, p.norm)
+    r, fb = _tc_eval(ps, "tc_fp16")
+    assert fb >= far.size, f"{fb} fallback queries, {far.size} outside the fp16 range"
+    assert fb <= far.size + 15
+    _check_exact(ps, r, orc, "fp16 cluster + far", fb)
+
+
+def test_fp16_single_point_and_constant_coordinate(oracle_mod):
+    """A data set of one point (a box of zero size: scale 2^0) and one whose coordinates are
+    all equal in one dimension."""
+    p = W.random_problem(996, 1, 3, 257)
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm)
+    r, fb = _tc_eval(p, "tc_fp16")
+    compare(p, r, orc, FP32_TOL, "fp16 N=1")
+    p = W.random_problem(997, 2_000, 4, 300)
+    X = p.X.copy()
+    X[:, 1] = 0.375
+    ps = W.Problem("c", X, p.y, p.Q, p.M, p.norm, None, None)
+    orc = oracle_mod.evaluate(X, p.y, p.Q, p.M, p.norm)
+    r, fb = _tc_eval(ps, "tc_fp16")
+    _check_exact(ps, r, orc, "fp16 flat coordinate", fb)
+
+
+def test_fp16_full_size_cluster_sampled(oracle_mod):
+    """The FP16 form at the full precision workload (N = Q = 1e6, d = 16), as the benchmark
+    launches it, checked on 400 sampled queries against the FP64 oracle."""
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    p = W.cluster_d16()
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, precision="tc_fp16")
+    r = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
+    fb = m.last_fallback()
+    m.check()
+    m.close()
+    assert fb <= p.nq // 100
+    idx = np.sort(np.random.default_rng(23).choice(p.nq, 400, replace=False))
+    ps = W.Problem("c", p.X, p.y, p.Q[idx], p.M, p.norm, None, None)
+    orc = oracle_mod.evaluate(p.X, p.y, ps.Q, p.M, p.norm)
+    _check_exact(ps, {k: v[idx] for k, v in r.items()}, orc, "fp16 full cluster", fb)

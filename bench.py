@@ -62,6 +62,7 @@ KERNEL_DRAM_BYTES = {
     ("cluster_d16", 2): 618.02e6 + 185.20e6,           # scan_exact_kernel<L2, C=0, U=16, R=2>
     ("cluster_d16_tc", 2): 141000.57e6 + 3419.05e6,    # tc_scan_kernel<K=16, 4 parts, TF32> (norm block, 4 stages)
     ("cluster_d16_bf16", 2): 84545.86e6 + 2910.17e6,   # tc_scan_kernel<K=16, 4 parts, BF16> (norm block, 4 stages)
+    ("cluster_d16_fp16", 2): 12953.22e6 + 1845.91e6,   # tc_scan_kernel<K=16, 4 parts, FP16> (norm block, 4 stages)
     ("local_d4", 2): 32.64e6 + 1.43e6,                 # loc_scan_kernel<L2, 4, bucket, G=2>
     ("smooth_d4", 2): 4.54e6 + 40.80e6,                # smooth_pass_kernel<L2, 4> (share q, 64 splits)
     ("batch_4096", 0): 4817.68e6 + 1598.16e6,          # batch_scan_kernel

@@ -581,8 +581,9 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
         const float INF = __int_as_float(0x7f800000);
         float U = INF, Bl = -INF;
         int nu = act ? 0 : -1, nl = nu;
-        for (int64_t t = 0; t < T; ++t) {
-            const int s = (int)(t % TC_STAGES), b = (int)(t & 1);
+        const int T32 = (int)T;                            // N < 2^31, so T < 2^23
+        for (int t = 0; t < T32; ++t) {
+            const int s = t % TC_STAGES, b = t & 1;
             if (!mbar_wait_bounded(&acc_full[b], (uint32_t)((t / 2) & 1), P.err)) break;
             // acquire the tile's y values and chunk bounds written by the bulk copy
             if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / TC_STAGES) & 1), P.err)) break;
@@ -618,13 +619,20 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                     csm[h] = min2f(min3f(cs[0], cs[1], cs[2]), cs[3]);
                     if (FMT == TC_FP16) csm[h] = fmaf(csm[h], usc2.x, nq22.x);   // monotone: the min s~
                 }
+                // Every pair of the chunk has s >= S0 = max(min s~ - eps, 0), so its upper value
+                // is >= y_min + sqrt(S0) and its lower value <= y_max - sqrt(S0).  The chunk
+                // can hold an extremum (or a tie) only if sqrt(S0) <= G = max(U - y_min,
+                // y_max - Bl), that is G >= 0 and S0 <= G^2.  In FP32: S0 is taken low by
+                // (1 - 2^-23) (one rounding in the subtraction), G^2 high by (1 + 2^-21) (the
+                // roundings of the two differences and of the two products), so no chunk that
+                // passes the exact test is skipped.  A chunk without data has NaN bounds and
+                // fails G >= 0.
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const float2 cb = cbs[col0 / 32 + h];
-                    const float slo = sqrt_approx(fmaxf(csm[h] - eps, 0.f) * (1.f - 0x1p-22f)) * (1.f - 0x1p-21f);
-                    const float lbu = (cb.x + slo) - 0x1p-22f * (fabsf(cb.x) + slo);
-                    const float ubl = (cb.y - slo) + 0x1p-22f * (fabsf(cb.y) + slo);
-                    take[h] = __any_sync(0xffffffffu, act && (lbu <= U || ubl >= Bl));
+                    const float s0 = fmaxf(csm[h] - eps, 0.f) * (1.f - 0x1p-23f);
+                    const float G = fmaxf(U - cb.x, cb.y - Bl);
+                    take[h] = __any_sync(0xffffffffu, act && G >= 0.f && s0 <= (G * G) * (1.f + 0x1p-21f));
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {

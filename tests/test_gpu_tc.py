@@ -226,3 +226,18 @@ def test_fp16_full_size_cluster_sampled(oracle_mod):
     ps = W.Problem("c", p.X, p.y, p.Q[idx], p.M, p.norm, None, None)
     orc = oracle_mod.evaluate(p.X, p.y, ps.Q, p.M, p.norm)
     _check_exact(ps, {k: v[idx] for k, v in r.items()}, orc, "fp16 full cluster", fb)
+
+
+def test_tc_forms_agree_bitwise(oracle_mod):
+    """TF32, BF16 and FP16 all return the FP64 envelopes rounded once, so with no fallback
+    query their outputs are bit for bit the same (values and indices)."""
+    p = W.cluster_d16(n_data=20_000, n_query=1_000)
+    outs = {}
+    for prec in ("tc_tf32", "tc_bf16", "tc_fp16"):
+        outs[prec] = _tc_eval(p, prec)
+    if any(fb for _, fb in outs.values()):
+        pytest.skip("a fallback query makes the comparison inexact")
+    ref = outs["tc_tf32"][0]
+    for prec in ("tc_bf16", "tc_fp16"):
+        for k in ("g", "lo", "hi", "idx_up", "idx_lo"):
+            assert np.array_equal(outs[prec][0][k], ref[k]), f"{prec} {k} differs from tc_tf32"

@@ -330,7 +330,10 @@ lip_status fit_common(const void* X, const void* y, int64_t N, int32_t d, double
 int choose_splits(const lip_model* h, int64_t gx, int64_t tiles) {
     if (h->splits > 0) return (int)std::max<int64_t>(1, std::min<int64_t>(h->splits, tiles));
     const int64_t wave = (int64_t)h->sms * h->occ_blocks;
-    const int64_t smax = std::max<int64_t>(1, std::min<int64_t>(64, tiles / 2));
+    // up to 64 slices, more when a few query blocks could not fill a wave otherwise (the
+    // tensor-core fallback's handful of queries)
+    const int64_t cap = std::max<int64_t>(64, wave / std::max<int64_t>(gx, 1));
+    const int64_t smax = std::max<int64_t>(1, std::min<int64_t>(cap, tiles / 2));
     int best = 1;
     double best_eff = 0.0;
     for (int64_t s = 1; s <= smax; ++s) {

@@ -228,6 +228,12 @@ __device__ __forceinline__ int tc_f16_shift(const float2* bounds, const double* 
 // row.  A padding position has zero rows (s~ = 0) and y = NaN.
 template <int FMT>
 __global__ void tc_build_b_kernel(const TcPrepParams P) {
+    __shared__ double f_s;                 // FP16: the operand scale 2^k, once per block
+    __shared__ double c_s[D_MAX];          // the centre, once per block
+    if (FMT == TC_FP16 && threadIdx.x == 0) f_s = ldexp(1.0, tc_f16_shift(P.bounds, P.scale, P.d));
+    if (threadIdx.x < P.d) c_s[threadIdx.x] = tc_centre(P.bounds[threadIdx.x], P.scale[threadIdx.x]);
+    __syncthreads();
+    const double f = FMT == TC_FP16 ? f_s : 1.0;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= P.ntiles * TC_N) return;
     const int64_t t = k / TC_N;
@@ -235,7 +241,6 @@ __global__ void tc_build_b_kernel(const TcPrepParams P) {
     char* tile = P.tiles + t * (int64_t)tc_tile_bytes(P.K, FMT);
     const int piece = TC_N * P.K * tc_esz(FMT);
     char* norm = tile + tc_pieces(FMT) * piece;
-    const double f = FMT == TC_FP16 ? ldexp(1.0, tc_f16_shift(P.bounds, P.scale, P.d)) : 1.0;
     float* yv = reinterpret_cast<float*>(norm + TC_N * TC_NORM_ROW);
     float b[16];
     for (int j = 0; j < P.K; ++j) b[j] = 0.f;
@@ -248,8 +253,7 @@ __global__ void tc_build_b_kernel(const TcPrepParams P) {
         for (int j = 0; j < P.d; ++j) {
             const float x = P.X0[src * P.d + j];
             P.Xs[k * P.d + j] = x;
-            const double c = tc_centre(P.bounds[j], P.scale[j]);
-            const float xh = (float)(P.scale[j] * (double)x - c);
+            const float xh = (float)(P.scale[j] * (double)x - c_s[j]);
             b[j] = (float)((double)xh * f);
             n2 += (double)xh * (double)xh;
         }
@@ -311,6 +315,11 @@ struct TcQueryParams {
 // One thread per (padded) query: its row of the A pieces and its constants.
 template <int FMT>
 __global__ void tc_build_a_kernel(const TcQueryParams P) {
+    __shared__ int ks_s;                   // FP16: the operand scale's exponent, once per block
+    __shared__ double c_s[D_MAX];          // the centre, once per block
+    if (FMT == TC_FP16 && threadIdx.x == 0) ks_s = tc_f16_shift(P.bounds, P.scale, P.d);
+    if (threadIdx.x < P.d) c_s[threadIdx.x] = tc_centre(P.bounds[threadIdx.x], P.scale[threadIdx.x]);
+    __syncthreads();
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nqp = (P.nq + TC_M - 1) / TC_M * TC_M;
     if (qi >= nqp) return;
@@ -324,13 +333,12 @@ __global__ void tc_build_a_kernel(const TcQueryParams P) {
     bool real = false;
     if (qi < P.nq) {
         const int64_t src = P.qperm[qi];
-        const int ks = FMT == TC_FP16 ? tc_f16_shift(P.bounds, P.scale, P.d) : 0;
+        const int ks = FMT == TC_FP16 ? ks_s : 0;
         const double f = ldexp(1.0, ks);
         double n2 = 0.0;
         bool inside = true;
         for (int j = 0; j < P.d; ++j) {
-            const double c = tc_centre(P.bounds[j], P.scale[j]);
-            const float qh = (float)(P.scale[j] * (double)P.Q[src * P.d + j] - c);
+            const float qh = (float)(P.scale[j] * (double)P.Q[src * P.d + j] - c_s[j]);
             const float qs = (float)((double)qh * f);
             if (FMT == TC_FP16 && fabsf(qs) > TC_F16_QMAX) inside = false;   // also +-inf; NaN stays
             a[j] = -2.f * qs;

@@ -709,6 +709,8 @@ struct TcRescreenParams {
     int d;
     double M;
     double w[D_MAX];
+    float sc[D_MAX];        // (float)(M w_j), rounded once on the host (the FP32 filter)
+    bool unit_w;            // every w_j == 1: the FP64 distance skips the exact product by 1
     const float* X0;
     const float* y0;
     int64_t N;
@@ -721,9 +723,16 @@ struct TcRescreenParams {
 
 __device__ __forceinline__ double tc_dist64(const TcRescreenParams& P, const float* q, const float* x) {
     double acc = 0.0;
-    for (int i = 0; i < P.d; ++i) {
-        const double t = ((double)q[i] - (double)x[i]) * P.w[i];
-        acc += t * t;
+    if (P.unit_w) {
+        for (int i = 0; i < P.d; ++i) {
+            const double t = (double)q[i] - (double)x[i];
+            acc += t * t;
+        }
+    } else {
+        for (int i = 0; i < P.d; ++i) {
+            const double t = ((double)q[i] - (double)x[i]) * P.w[i];
+            acc += t * t;
+        }
     }
     return sqrt(acc);
 }
@@ -738,13 +747,20 @@ __device__ __forceinline__ bool tc_better(int side, double v, int k, double bv, 
 }
 
 // One warp per query.  For each bound, every surviving candidate chunk is evaluated by
-// the 32 lanes (one point each, coalesced rows) in FP32; a point can only be the chunk's
-// extremum if its FP32 value is within twice the FP32 error bound of the chunk's FP32
-// extremum, and only those points are re-evaluated in FP64.  FP32 error of
-// y +- M |diag(w)(q - x)|_2 with correctly rounded sqrt: at most (d + 10) 2^-24 (r + |y|).
-__global__ void tc_rescreen_kernel(const TcRescreenParams P) {
+// the 32 lanes (one point each, coalesced rows) in FP32.  FP32 error of
+// y +- M |diag(w)(q - x)|_2 with correctly rounded sqrt: at most err = (d + 10) 2^-24 (r + |y|).
+// A point p can be the FP64 extremum (or tie with it) only if v32(p) is within
+// err(p) + err(e) of v32(e) for the best point e seen so far, so the warp keeps the running
+// FP32 extremum and the largest error seen, and lists for FP64 only the points within twice
+// that error of it.  The listed points of both bounds are evaluated together, one per lane:
+// the FP64 pipe (narrow on this part) then runs one batch of full warps per query.
+constexpr int TC_RS_THREADS = 256;
+constexpr int TC_RS_CAND = 64;             // per-warp list of points for FP64 evaluation
+__global__ void __launch_bounds__(TC_RS_THREADS) tc_rescreen_kernel(const TcRescreenParams P) {
+    __shared__ int cbuf[TC_RS_THREADS / 32][TC_RS_CAND];   // data position; ~position for H_lo
     const int64_t pos = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;   // query position
     const int lane = threadIdx.x % 32;
+    int* const mybuf = cbuf[threadIdx.x / 32];
     if (pos >= P.nq) return;
     const int64_t qi = P.qperm[pos];
     const float* q = P.Q + qi * P.d;
@@ -762,18 +778,34 @@ __global__ void tc_rescreen_kernel(const TcRescreenParams P) {
 #pragma unroll
     for (int i = 0; i < D_MAX; ++i) {
         qs[i] = i < P.d ? q[i] : 0.f;
-        sc[i] = i < P.d ? (float)(P.M * P.w[i]) : 0.f;
+        sc[i] = i < P.d ? P.sc[i] : 0.f;
     }
     const float erel = (float)(P.d + 10) * 5.9604645e-8f;   // (d + 10) 2^-24
-    double best[2] = {0.0, 0.0};
-    int bidx[2] = {-1, -1};
+    double bv[2] = {0.0, 0.0};
+    int bk[2] = {-1, -1};
+    int nc = 0;                                            // warp-uniform list length
+    // FP64 values of the listed points, one per lane; ties go to the lowest data index
+    auto flush = [&]() {
+        __syncwarp();
+        for (int c = lane; c < nc; c += 32) {
+            const int e = mybuf[c];
+            const int side = e < 0 ? 1 : 0;
+            const int64_t k = e < 0 ? ~e : e;
+            const double dist = P.M * tc_dist64(P, q, P.Xs + k * P.d);
+            const double v = side == 0 ? (double)P.ys[k] + dist : (double)P.ys[k] - dist;
+            const int ko = P.dperm[k];
+            if (tc_better(side, v, ko, bv[side], bk[side])) { bv[side] = v; bk[side] = ko; }
+        }
+        __syncwarp();
+        nc = 0;
+    };
     if (finite) {
         for (int b = 0; b < 2; ++b) {
             float bound = R[b * TC_MAX_PARTS].U;
             for (int h = 1; h < P.parts; ++h)
                 bound = b == 0 ? fminf(bound, R[b * TC_MAX_PARTS + h].U) : fmaxf(bound, R[b * TC_MAX_PARTS + h].U);
-            double bv = 0.0;
-            int bk = -1;
+            // running FP32 extremum of the bound and the largest error seen (warp-uniform)
+            float ext = b == 0 ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000), emax = 0.f;
             for (int h = 0; h < P.parts; ++h) {
                 const TcRec& r = R[b * TC_MAX_PARTS + h];
                 for (int e = 0; e < r.n; ++e) {
@@ -792,45 +824,47 @@ __global__ void tc_rescreen_kernel(const TcRescreenParams P) {
                         v32 = b == 0 ? yy + rr : yy - rr;
                         err = erel * (rr + fabsf(yy));
                     }
-                    float ext = v32, emax = err;
+                    float cext = v32, cerr = err;
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1) {
-                        const float o = __shfl_xor_sync(0xffffffffu, ext, off);
-                        ext = b == 0 ? fminf(ext, o) : fmaxf(ext, o);
-                        emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+                        const float o = __shfl_xor_sync(0xffffffffu, cext, off);
+                        cext = b == 0 ? fminf(cext, o) : fmaxf(cext, o);
+                        cerr = fmaxf(cerr, __shfl_xor_sync(0xffffffffu, cerr, off));
                     }
+                    ext = b == 0 ? fminf(ext, cext) : fmaxf(ext, cext);
+                    emax = fmaxf(emax, cerr);
                     const bool cand = in && (b == 0 ? v32 <= ext + 2.f * emax : v32 >= ext - 2.f * emax);
-                    if (cand) {
-                        // the position-ordered copy holds the caller's values; ties go to
-                        // the lowest data index
-                        const double dist = P.M * tc_dist64(P, q, P.Xs + k * P.d);
-                        const double v = b == 0 ? (double)P.ys[k] + dist : (double)P.ys[k] - dist;
-                        const int ko = P.dperm[k];
-                        if (tc_better(b, v, ko, bv, bk)) { bv = v; bk = ko; }
-                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, cand);
+                    const int n = __popc(m);
+                    if (nc + n > TC_RS_CAND) flush();
+                    if (cand) mybuf[nc + __popc(m & ((1u << lane) - 1u))] = b == 0 ? (int)k : ~(int)k;
+                    nc += n;
                 }
             }
+        }
+        flush();
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
-                const int ok = __shfl_xor_sync(0xffffffffu, bk, off);
-                if (tc_better(b, ov, ok, bv, bk)) { bv = ov; bk = ok; }
+                const double ov = __shfl_xor_sync(0xffffffffu, bv[b], off);
+                const int ok = __shfl_xor_sync(0xffffffffu, bk[b], off);
+                if (tc_better(b, ov, ok, bv[b], bk[b])) { bv[b] = ov; bk[b] = ok; }
             }
-            best[b] = bv;
-            bidx[b] = bk;
         }
     }
     if (lane != 0) return;
-    double hi = best[0], lo = best[1];
-    if (!finite || bidx[0] < 0 || bidx[1] < 0) {
+    double hi = bv[0], lo = bv[1];
+    int iu = bk[0], il = bk[1];
+    if (!finite || iu < 0 || il < 0) {
         hi = lo = __longlong_as_double(0x7ff8000000000000ll);
-        bidx[0] = bidx[1] = -1;
+        iu = il = -1;
     }
     if (P.g) P.g[qi] = (float)(0.5 * (hi + lo));
     if (P.lo) P.lo[qi] = (float)lo;
     if (P.hi) P.hi[qi] = (float)hi;
-    if (P.idx_up) P.idx_up[qi] = bidx[0];
-    if (P.idx_lo) P.idx_lo[qi] = bidx[1];
+    if (P.idx_up) P.idx_up[qi] = iu;
+    if (P.idx_lo) P.idx_lo[qi] = il;
 }
 
 // Gather the fallback queries into a compact block, and scatter their results back.
@@ -966,7 +1000,12 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     R.nq = nq;
     R.d = d;
     R.M = M;
-    for (int j = 0; j < D_MAX; ++j) R.w[j] = w[j];
+    R.unit_w = true;
+    for (int j = 0; j < D_MAX; ++j) {
+        R.w[j] = w[j];
+        R.sc[j] = j < d ? (float)(M * w[j]) : 0.f;
+        if (j < d && w[j] != 1.0) R.unit_w = false;
+    }
     R.X0 = X0;
     R.y0 = y0;
     R.N = N;
@@ -978,7 +1017,7 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     R.idx_lo = il;
     R.fb_count = fb_count;
     R.fb_list = fb_list;
-    tc_rescreen_kernel<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(R);
+    tc_rescreen_kernel<<<(unsigned)((nq * 32 + TC_RS_THREADS - 1) / TC_RS_THREADS), TC_RS_THREADS, 0, st>>>(R);
     return cudaGetLastError();
 }
 

@@ -746,45 +746,50 @@ __device__ __forceinline__ bool tc_better(int side, double v, int k, double bv, 
     return k < bk;
 }
 
-// One warp per query.  For each bound, every surviving candidate chunk is evaluated by
-// the 32 lanes (one point each, coalesced rows) in FP32.  FP32 error of
-// y +- M |diag(w)(q - x)|_2 with correctly rounded sqrt: at most err = (d + 10) 2^-24 (r + |y|).
-// A point p can be the FP64 extremum (or tie with it) only if v32(p) is within
-// err(p) + err(e) of v32(e) for the best point e seen so far, so the warp keeps the running
-// FP32 extremum and the largest error seen, and lists for FP64 only the points within twice
-// that error of it.  The listed points of both bounds are evaluated together, one per lane:
-// the FP64 pipe (narrow on this part) then runs one batch of full warps per query.
+// One warp per query, eight queries per block.  For each bound, every surviving candidate
+// chunk is evaluated by the 32 lanes (one point each, coalesced rows) in FP32.  FP32 error
+// of y +- M |diag(w)(q - x)|_2 with correctly rounded sqrt: at most
+// err = (d + 10) 2^-24 (r + |y|).  A point p can be the FP64 extremum (or tie with it) only
+// if v32(p) is within err(p) + err(e) of v32(e) for the best point e seen so far, so the
+// warp keeps the running FP32 extremum and the largest error seen, and lists for FP64 only
+// the points within twice that error of it.  The lists of the block's eight queries (both
+// bounds) are then evaluated in FP64 as one dense batch, one point per thread: the FP64
+// pipe (narrow on this part) runs about one full warp per block instead of one per query.
 constexpr int TC_RS_THREADS = 256;
+constexpr int TC_RS_WARPS = TC_RS_THREADS / 32;
 constexpr int TC_RS_CAND = 64;             // per-warp list of points for FP64 evaluation
 __global__ void __launch_bounds__(TC_RS_THREADS) tc_rescreen_kernel(const TcRescreenParams P) {
-    __shared__ int cbuf[TC_RS_THREADS / 32][TC_RS_CAND];   // data position; ~position for H_lo
-    const int64_t pos = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;   // query position
-    const int lane = threadIdx.x % 32;
-    int* const mybuf = cbuf[threadIdx.x / 32];
-    if (pos >= P.nq) return;
-    const int64_t qi = P.qperm[pos];
+    __shared__ int cbuf[TC_RS_WARPS][TC_RS_CAND];      // data position; ~position for H_lo
+    __shared__ double cval[TC_RS_WARPS][TC_RS_CAND];   // their FP64 values
+    __shared__ int ccount[TC_RS_WARPS], coff[TC_RS_WARPS + 1];
+    __shared__ long long cq[TC_RS_WARPS];              // the warp's query index
+    const int wq = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int64_t pos = (int64_t)blockIdx.x * TC_RS_WARPS + wq;   // query position
+    int* const mybuf = cbuf[wq];
+    // every warp reaches the block barriers below, so no warp returns early
+    bool active = pos < P.nq;
+    int64_t qi = 0;
+    bool finite = false;
+    const TcRec* R = P.rec;
+    if (active) {
+        qi = P.qperm[pos];
+        const float* q = P.Q + qi * P.d;
+        finite = true;
+        for (int i = 0; i < P.d; ++i) finite = finite && isfinite(q[i]);
+        R = P.rec + pos * 2 * TC_MAX_PARTS;
+        bool over = false;
+        for (int b = 0; b < 2; ++b)
+            for (int h = 0; h < P.parts; ++h) over = over || R[b * TC_MAX_PARTS + h].n < 0;
+        if (finite && over) {
+            if (lane == 0) P.fb_list[atomicAdd(P.fb_count, 1)] = (int)qi;
+            active = false;
+        }
+    }
     const float* q = P.Q + qi * P.d;
-    bool finite = true;
-    for (int i = 0; i < P.d; ++i) finite = finite && isfinite(q[i]);
-    const TcRec* R = P.rec + pos * 2 * TC_MAX_PARTS;
-    bool over = false;
-    for (int b = 0; b < 2; ++b)
-        for (int h = 0; h < P.parts; ++h) over = over || R[b * TC_MAX_PARTS + h].n < 0;
-    if (finite && over) {
-        if (lane == 0) P.fb_list[atomicAdd(P.fb_count, 1)] = (int)qi;
-        return;
-    }
-    float qs[D_MAX], sc[D_MAX];
-#pragma unroll
-    for (int i = 0; i < D_MAX; ++i) {
-        qs[i] = i < P.d ? q[i] : 0.f;
-        sc[i] = i < P.d ? P.sc[i] : 0.f;
-    }
-    const float erel = (float)(P.d + 10) * 5.9604645e-8f;   // (d + 10) 2^-24
     double bv[2] = {0.0, 0.0};
     int bk[2] = {-1, -1};
     int nc = 0;                                            // warp-uniform list length
-    // FP64 values of the listed points, one per lane; ties go to the lowest data index
+    // a full list is evaluated by the warp itself, one point per lane (rare)
     auto flush = [&]() {
         __syncwarp();
         for (int c = lane; c < nc; c += 32) {
@@ -799,7 +804,14 @@ __global__ void __launch_bounds__(TC_RS_THREADS) tc_rescreen_kernel(const TcResc
         __syncwarp();
         nc = 0;
     };
-    if (finite) {
+    if (active && finite) {
+        float qs[D_MAX], sc[D_MAX];
+#pragma unroll
+        for (int i = 0; i < D_MAX; ++i) {
+            qs[i] = i < P.d ? q[i] : 0.f;
+            sc[i] = i < P.d ? P.sc[i] : 0.f;
+        }
+        const float erel = (float)(P.d + 10) * 5.9604645e-8f;   // (d + 10) 2^-24
         for (int b = 0; b < 2; ++b) {
             float bound = R[b * TC_MAX_PARTS].U;
             for (int h = 1; h < P.parts; ++h)
@@ -842,7 +854,36 @@ __global__ void __launch_bounds__(TC_RS_THREADS) tc_rescreen_kernel(const TcResc
                 }
             }
         }
-        flush();
+    }
+    if (lane == 0) {
+        ccount[wq] = (active && finite) ? nc : 0;
+        cq[wq] = (long long)qi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        coff[0] = 0;
+        for (int w = 0; w < TC_RS_WARPS; ++w) coff[w + 1] = coff[w] + ccount[w];
+    }
+    __syncthreads();
+    // the block's listed points, densely, one per thread
+    for (int t = threadIdx.x; t < coff[TC_RS_WARPS]; t += TC_RS_THREADS) {
+        int w = 0;
+        while (coff[w + 1] <= t) ++w;
+        const int c = t - coff[w];
+        const int e = cbuf[w][c];
+        const int64_t k = e < 0 ? ~e : e;
+        const double dist = P.M * tc_dist64(P, P.Q + (int64_t)cq[w] * P.d, P.Xs + k * P.d);
+        cval[w][c] = e < 0 ? (double)P.ys[k] - dist : (double)P.ys[k] + dist;
+    }
+    __syncthreads();
+    if (!active) return;
+    if (finite) {
+        for (int c = lane; c < ccount[wq]; c += 32) {
+            const int e = mybuf[c];
+            const int side = e < 0 ? 1 : 0;
+            const int ko = P.dperm[e < 0 ? ~e : e];
+            if (tc_better(side, cval[wq][c], ko, bv[side], bk[side])) { bv[side] = cval[wq][c]; bk[side] = ko; }
+        }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
 #pragma unroll
@@ -1017,7 +1058,7 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     R.idx_lo = il;
     R.fb_count = fb_count;
     R.fb_list = fb_list;
-    tc_rescreen_kernel<<<(unsigned)((nq * 32 + TC_RS_THREADS - 1) / TC_RS_THREADS), TC_RS_THREADS, 0, st>>>(R);
+    tc_rescreen_kernel<<<(unsigned)((nq + TC_RS_WARPS - 1) / TC_RS_WARPS), TC_RS_THREADS, 0, st>>>(R);
     return cudaGetLastError();
 }
 

@@ -67,16 +67,17 @@ def test_tc_equals_plain_within_tolerance(oracle_mod):
     compare(p, b, orc, FP32_TOL, "plain")
 
 
-def test_tc_edge_cases_and_fallback(oracle_mod):
+@pytest.mark.parametrize("prec", ["tc_tf32", "tc_bf16", "tc_fp16"])
+def test_tc_edge_cases_and_fallback(oracle_mod, prec):
     import torch
 
     from paper_2606_04670_b300.lipfit import LipFit
     # a single data point, one query, a NaN query, sizes that are not tile multiples
     p = W.random_problem(960, 1, 4, 3)
     orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm)
-    compare(p, gpu_eval(p, "tc_tf32"), orc, FP32_TOL, "tc N=1")
+    compare(p, gpu_eval(p, prec), orc, FP32_TOL, "tc N=1")
     p = W.random_problem(961, 257, 5, 129)
-    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, precision="tc_tf32")
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, precision=prec)
     Q = torch.as_tensor(p.Q).cuda().clone()
     Q[5, 2] = float("nan")
     r = {k: v.cpu().numpy() for k, v in m.eval(Q).items()}
@@ -96,7 +97,7 @@ def test_tc_edge_cases_and_fallback(oracle_mod):
     # through the plain scan; the result is still the lowest index
     p = W.random_problem(962, 3_000, 5, 300)
     yc = np.full(p.N, 0.25, np.float32)
-    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(yc).cuda(), 0.0, norm=p.norm, precision="tc_tf32")
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(yc).cuda(), 0.0, norm=p.norm, precision=prec)
     r = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
     assert m.last_fallback() == p.nq
     assert np.all(r["idx_up"] == 0) and np.all(r["idx_lo"] == 0) and np.allclose(r["g"], 0.25)

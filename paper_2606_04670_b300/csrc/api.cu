@@ -152,14 +152,14 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
     // the caller's order; decreasing coordinates are mirrored (sign -1).
     int j = 0;
     for (int pass = 0; pass < 2; ++pass)
-        for (int i = 0; i < d; ++i) {
+        for (int i = 0; i < d && i < D_MAX; ++i) {             // d <= D_MAX (checked above)
             const int8_t m = p->mon ? p->mon[i] : 0;
             if ((pass == 0) != (m != 0)) continue;
             h->perm[j] = i;
             h->sgnw[j] = (m < 0 ? -1.0 : 1.0) * (p->w ? p->w[i] : 1.0);
             ++j;
         }
-    for (int i = 0; i < d; ++i) {
+    for (int i = 0; i < d && i < D_MAX; ++i) {
         h->mon[i] = p->mon ? p->mon[i] : 0;
         h->w[i] = p->w ? p->w[i] : 1.0;
         if (h->mon[i] != 0) h->C++;

@@ -242,3 +242,19 @@ def test_tc_forms_agree_bitwise(oracle_mod):
     for prec in ("tc_bf16", "tc_fp16"):
         for k in ("g", "lo", "hi", "idx_up", "idx_lo"):
             assert np.array_equal(outs[prec][0][k], ref[k]), f"{prec} {k} differs from tc_tf32"
+
+
+@pytest.mark.parametrize("prec", ["tc_tf32", "tc_bf16", "tc_fp16"])
+def test_tc_offset_data(oracle_mod, prec):
+    """Data and queries 1e4 away from the origin with a unit spread: the operands are centred
+    (in FP64, before any rounding), so the split products and their error bound see the
+    unit spread, and the results stay exact."""
+    p = W.random_problem(1001, 4_000, 4, 800, norm=W.NORM_L2)
+    off = np.float32(1.0e4)
+    X = (p.X + off).astype(np.float32)
+    Q = (p.Q + off).astype(np.float32)
+    ps = W.Problem("o", X, p.y, Q, p.M, p.norm, None, None)
+    orc = oracle_mod.evaluate(X, p.y, Q, p.M, p.norm)
+    r, fb = _tc_eval(ps, prec)
+    _check_exact(ps, r, orc, f"{prec} offset", fb)
+    assert fb <= 8, f"{fb} fallback queries"

@@ -474,7 +474,7 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
         flops = float(fpp) * p.nq * p.N
         peak = float(ctx.peaks.get("bf16_tflops", 1800.0)) * (1.0 if f16 else TF32_OVER_BF16) * 1e12
         alu = roof
-        roof = {"bound": "tensor", "kernel": f"tc_scan_kernel<K={kk}, {fmt}> (+ build and rescreen)",
+        roof = {"bound": "tensor", "kernel": f"tc_scan_kernel<K={kk}, {fmt}>",
                 "achieved": flops / (avg[kdom] / 1e3) / 1e12, "peak": peak / 1e12,
                 "unit": f"TFLOP/s ({fmt})", "frac": flops / (avg[kdom] / 1e3) / peak,
                 "traffic": traffic_for(args, name, p.norm),

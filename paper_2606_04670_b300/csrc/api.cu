@@ -439,14 +439,12 @@ lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, v
     TcQueryOrder QO{};
     QO.qperm = reinterpret_cast<int*>(base + a_b + eps_b + rec_b + list_b);
     QO.scratch = base + a_b + eps_b + rec_b + list_b + qp_b;
-    if (h->ev_scan0) CUDA_TRY(cudaEventRecord(h->ev_scan0, st));
     CUDA_TRY(tc_eval_launch(static_cast<const float*>(Q), nq, d, scale, h->N, h->tc_maxbits, h->tc_btiles,
                             ntiles, base, reinterpret_cast<float4*>(base + a_b), base + a_b + eps_b, h->w, h->M,
                             static_cast<const float*>(h->X0), static_cast<const float*>(h->y0), static_cast<float*>(g),
                             static_cast<float*>(lo), static_cast<float*>(hi), iu, il, fb_count, fb_list, h->status,
-                            h->tc_variant, h->tc_fmt, O, QO, st));
+                            h->tc_variant, h->tc_fmt, O, QO, h->ev_scan0, h->ev_scan1, st));
     count_launches(3 + spatial_order_launches());
-    if (h->ev_scan1) CUDA_TRY(cudaEventRecord(h->ev_scan1, st));
     int nfb = 0;
     CUDA_TRY(cudaMemcpyAsync(&nfb, fb_count, sizeof nfb, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));

@@ -995,7 +995,8 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
                            const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float4* qc,
                            void* rec, const double* w, double M, const float* X0, const float* y0, float* g, float* lo,
                            float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, unsigned* err,
-                           int variant, int fmt, const TcDataOrder& O, const TcQueryOrder& QO, cudaStream_t st) {
+                           int variant, int fmt, const TcDataOrder& O, const TcQueryOrder& QO, cudaEvent_t ev0,
+                           cudaEvent_t ev1, cudaStream_t st) {
     const int K = tc_k_for_dim(d, fmt);
     // the queries' spatial order: a tile of 128 positions holds nearby queries
     cudaError_t e = spatial_order(Q, nq, d, QO.qperm, nullptr, QO.scratch, st);
@@ -1028,8 +1029,10 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     S.ntiles = ntiles;
     S.rec = static_cast<TcRec*>(rec);
     S.err = err;
+    if (ev0 && (e = cudaEventRecord(ev0, st)) != cudaSuccess) return e;     // the scan kernel alone
     e = parts == 2 ? launch_tc_scan_parts<2>(K, fmt, S, nqt, st) : launch_tc_scan_parts<4>(K, fmt, S, nqt, st);
     if (e != cudaSuccess) return e;
+    if (ev1 && (e = cudaEventRecord(ev1, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(fb_count, 0, sizeof(int), st)) != cudaSuccess) return e;
     TcRescreenParams R{};
     R.parts = parts;

@@ -258,3 +258,30 @@ def test_tc_offset_data(oracle_mod, prec):
     r, fb = _tc_eval(ps, prec)
     _check_exact(ps, r, orc, f"{prec} offset", fb)
     assert fb <= 8, f"{fb} fallback queries"
+
+
+def test_tc_timing_events_bracket_the_scan():
+    """lip_set_timing_events on a tensor-core handle: the two events are recorded around
+    the tc_scan launch on the handle's stream, so they bracket a positive interval that is
+    shorter than the whole evaluation."""
+    import time
+
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    p = W.cluster_d16(n_data=50_000, n_query=8_192)
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, precision="tc_fp16")
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    m.set_timing_events(*ev)
+    Q = torch.as_tensor(p.Q).cuda()
+    m.eval(Q)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m.eval(Q)
+    torch.cuda.synchronize()
+    whole_ms = 1e3 * (time.perf_counter() - t0)
+    scan_ms = ev[0].elapsed_time(ev[1])
+    m.set_timing_events(None, None)
+    m.check()
+    m.close()
+    assert 0.0 < scan_ms < whole_ms

@@ -93,9 +93,9 @@ class Oracle:
         lib.oracle_local_knots.argtypes = [P, i64, i32, i32, P, u64, i64, i32, P, P, P]
         lib.oracle_local_table.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, i32]
         lib.oracle_local_table_rows.argtypes = [P, P, i64, i32, i32, P, P, i32, P, i64, P, P, P, i32]
-        lib.oracle_eval_local.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, f64, P, P, P, P, P,
-                                          P, P, i32]
-        lib.oracle_local_terms.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, P, i32, P]
+        lib.oracle_eval_local.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, f64, f64, P, P, P, P, P,
+                                          P, P, P, P, i32]
+        lib.oracle_local_terms.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, P, i32, f64, P]
         lib.oracle_eval_local_k.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, i32, P, P, P, P, P, P,
                                             i32]
         lib.oracle_eval_local_k.restype = ctypes.c_int
@@ -236,8 +236,11 @@ class Oracle:
         return d1, F, Mtab
 
     def evaluate_local(self, X, y, Q, knots, table, norm: int = NORM_L2, w=None, eta: float = 0.0,
-                       nthreads: Optional[int] = None) -> EvalResult:
-        """Envelopes with M replaced by M_k(dist); eta > 0 adds the amb_up / amb_lo flags."""
+                       tau: float = 0.0, nthreads: Optional[int] = None) -> EvalResult:
+        """Envelopes with M replaced by M_k(dist).  eta > 0 (a distance error) and tau >= 0
+        (a bound-value error) add hi_plus / lo_minus, the envelopes with every constant at
+        M_k(t + eta), and the amb_up / amb_lo flags: some datum that an evaluation with
+        those errors could pick has an exact value more than tau from the envelope."""
         X, y, Q, w = _f64(X), _f64(y), _f64(Q), _f64(w)
         T = _f64(np.asarray(knots, np.float64).reshape(-1))
         d1, F, Mtab = (_f64(a) for a in table)
@@ -246,13 +249,15 @@ class Oracle:
         out = {k: np.empty(nq) for k in ("hi", "lo", "g")}
         iu, il = np.empty(nq, np.int64), np.empty(nq, np.int64)
         au, al = np.zeros(nq, np.int8), np.zeros(nq, np.int8)
+        hp, lm = np.full(nq, np.nan), np.full(nq, np.nan)
         rc = self.lib.oracle_eval_local(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(T), T.shape[0], _ptr(d1),
-                                        _ptr(F), _ptr(Mtab), _ptr(Q), nq, float(eta), _ptr(out["hi"]),
+                                        _ptr(F), _ptr(Mtab), _ptr(Q), nq, float(eta), float(tau), _ptr(out["hi"]),
                                         _ptr(out["lo"]), _ptr(out["g"]), _ptr(iu), _ptr(il), _ptr(au), _ptr(al),
-                                        nthreads or default_threads())
+                                        _ptr(hp), _ptr(lm), nthreads or default_threads())
         if rc != 0:
             raise ValueError("oracle_eval_local: bad arguments")
-        return EvalResult(idx_up=iu, idx_lo=il, amb_up=au.astype(bool), amb_lo=al.astype(bool), **out)
+        return EvalResult(idx_up=iu, idx_lo=il, amb_up=au.astype(bool), amb_lo=al.astype(bool), hi_plus=hp,
+                          lo_minus=lm, **out)
 
     def evaluate_local_k(self, X, y, Q, knots, table, k: int, wk, norm: int = NORM_L2, w=None,
                          nthreads: Optional[int] = None) -> EvalResult:
@@ -272,8 +277,9 @@ class Oracle:
             raise ValueError("oracle_eval_local_k: bad arguments")
         return EvalResult(idx_up=iu, idx_lo=il, **out)
 
-    def local_terms(self, X, y, Q, knots, table, idx, side: int, norm: int = NORM_L2, w=None):
-        """y_k + M_k(t) t (side +1) or y_k - M_k(t) t (side -1) for k = idx[q]."""
+    def local_terms(self, X, y, Q, knots, table, idx, side: int, norm: int = NORM_L2, w=None, shift: float = 0.0):
+        """y_k + M_k(t + shift) t (side +1) or y_k - M_k(t + shift) t (side -1) for k = idx[q],
+        t = dist(q, x^k); NaN where idx[q] is not a datum."""
         X, y, Q, w = _f64(X), _f64(y), _f64(Q), _f64(w)
         T = _f64(np.asarray(knots, np.float64).reshape(-1))
         d1, F, Mtab = (_f64(a) for a in table)
@@ -282,7 +288,8 @@ class Oracle:
         ix = np.ascontiguousarray(idx, np.int64)
         out = np.empty(nq)
         rc = self.lib.oracle_local_terms(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(T), T.shape[0], _ptr(d1),
-                                         _ptr(F), _ptr(Mtab), _ptr(Q), nq, _ptr(ix), int(side), _ptr(out))
+                                         _ptr(F), _ptr(Mtab), _ptr(Q), nq, _ptr(ix), int(side), float(shift),
+                                         _ptr(out))
         if rc != 0:
             raise ValueError("oracle_local_terms: bad arguments")
         return out

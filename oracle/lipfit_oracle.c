@@ -506,8 +506,8 @@ static double local_M(const double* T, int m, double d1, double F, const double*
 typedef struct {
     const double* X; const double* y; int64_t N; int d; int norm; const double* w;
     const double* T; int m; const double *d1, *F, *Mtab;
-    const double* Q; int64_t q0, q1; double eta;
-    double *hi, *lo, *g; int64_t *iu, *il; int8_t *amb_up, *amb_lo;
+    const double* Q; int64_t q0, q1; double eta, tau;
+    double *hi, *lo, *g; int64_t *iu, *il; int8_t *amb_up, *amb_lo; double *hi_plus, *lo_minus;
 } leval_job;
 
 static void* leval_worker(void* arg) {
@@ -528,23 +528,38 @@ static void* leval_worker(void* arg) {
                 if (vu < bu) { bu = vu; ku = k; }
                 if (vl > bl) { bl = vl; kl = k; }
             }
-            /* An evaluation whose distances are off by up to eta may decide a segment
-             * differently.  Flag the query when that can change the outcome: a datum whose
-             * constant may come out lower (M_k(t - eta) < M_k(t)) reaches the envelope with
-             * it, or the winning datum's own constant may come out higher. */
+            /* An evaluation whose distances are off by up to eta, and whose bound values
+             * are off by up to tau / 2, may decide a segment differently and pick another
+             * datum.  With every constant taken as high as such an error allows,
+             * M_k(t + eta), the envelopes are hi_plus and lo_minus.  Datum k can be
+             * picked only if its value with its lowest possible constant M_k(t - eta)
+             * comes within tau of them (every other datum's value is then at least as
+             * unfavourable).  The query is flagged when such a datum's exact value is
+             * more than tau from the exact envelope. */
             if (J->eta > 0.0) {
+                double hp = INFINITY, lm = -INFINITY;
+                for (int64_t k = 0; k < J->N; k++) {
+                    const double* row = J->Mtab + k * (J->m + 1);
+                    double t = sym_dist(q, J->X + k * d, d, J->norm, J->w);
+                    double mb = local_M(J->T, J->m, J->d1[k], J->F[k], row, t + J->eta);
+                    if (J->y[k] + mb * t < hp) hp = J->y[k] + mb * t;
+                    if (J->y[k] - mb * t > lm) lm = J->y[k] - mb * t;
+                }
                 for (int64_t k = 0; k < J->N; k++) {
                     const double* row = J->Mtab + k * (J->m + 1);
                     double t = sym_dist(q, J->X + k * d, d, J->norm, J->w);
                     double mt = local_M(J->T, J->m, J->d1[k], J->F[k], row, t);
                     double ma = local_M(J->T, J->m, J->d1[k], J->F[k], row, t - J->eta);
-                    double mb = local_M(J->T, J->m, J->d1[k], J->F[k], row, t + J->eta);
-                    if (ma < mt && J->y[k] + ma * t <= bu) au = 1;
-                    if (ma < mt && J->y[k] - ma * t >= bl) al = 1;
-                    if (mb > mt && k == ku) au = 1;
-                    if (mb > mt && k == kl) al = 1;
+                    if (J->y[k] + ma * t <= hp + J->tau && J->y[k] + mt * t > bu + J->tau) au = 1;
+                    if (J->y[k] - ma * t >= lm - J->tau && J->y[k] - mt * t < bl - J->tau) al = 1;
                 }
+                if (J->hi_plus) J->hi_plus[qi] = hp;
+                if (J->lo_minus) J->lo_minus[qi] = lm;
             }
+        }
+        if (J->eta > 0.0 && bad) {
+            if (J->hi_plus) J->hi_plus[qi] = NAN;
+            if (J->lo_minus) J->lo_minus[qi] = NAN;
         }
         double hi = bad ? NAN : bu, lo = bad ? NAN : bl;
         if (J->hi) J->hi[qi] = hi;
@@ -558,11 +573,13 @@ static void* leval_worker(void* arg) {
     return NULL;
 }
 
-/* Envelopes with the local constants; eta > 0 also fills the ambiguity flags. */
+/* Envelopes with the local constants; eta > 0 also fills the ambiguity flags and the
+ * envelopes with every constant at its highest within eta (hi_plus, lo_minus). */
 int oracle_eval_local(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
                       const double* T, int m, const double* d1, const double* F, const double* Mtab,
-                      const double* Q, int64_t nq, double eta, double* hi, double* lo, double* g,
-                      int64_t* iu, int64_t* il, int8_t* amb_up, int8_t* amb_lo, int nthreads) {
+                      const double* Q, int64_t nq, double eta, double tau, double* hi, double* lo, double* g,
+                      int64_t* iu, int64_t* il, int8_t* amb_up, int8_t* amb_lo, double* hi_plus,
+                      double* lo_minus, int nthreads) {
     if (N < 1 || d < 1 || nq < 0 || norm < 1 || norm > 3 || m < 0) return 1;
     if (nq == 0) return 0;
     nthreads = clamp_threads(nthreads, nq);
@@ -570,7 +587,7 @@ int oracle_eval_local(const double* X, const double* y, int64_t N, int d, int no
     leval_job jobs[256];
     for (int t = 0; t < nthreads; t++) {
         leval_job j = {X, y, N, d, norm, w, T, m, d1, F, Mtab, Q, nq * t / nthreads, nq * (t + 1) / nthreads,
-                       eta, hi, lo, g, iu, il, amb_up, amb_lo};
+                       eta, tau, hi, lo, g, iu, il, amb_up, amb_lo, hi_plus, lo_minus};
         jobs[t] = j;
         pthread_create(&th[t], NULL, leval_worker, &jobs[t]);
     }
@@ -644,16 +661,18 @@ int oracle_eval_local_k(const double* X, const double* y, int64_t N, int d, int 
     return 0;
 }
 
-/* The value datum idx[q] gives query q: y + M_k(t) t (side > 0) or y - M_k(t) t. */
+/* The value datum idx[q] gives query q: y + M_k(t + shift) t (side > 0) or
+ * y - M_k(t + shift) t, t = dist(q, x^k): shift = 0 is the exact value, shift = -eta or
+ * +eta the value with the constant an evaluation off by eta in distance may take. */
 int oracle_local_terms(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
                        const double* T, int m, const double* d1, const double* F, const double* Mtab,
-                       const double* Q, int64_t nq, const int64_t* idx, int side, double* out) {
+                       const double* Q, int64_t nq, const int64_t* idx, int side, double shift, double* out) {
     if (N < 1 || d < 1 || nq < 0 || norm < 1 || norm > 3 || m < 0) return 1;
     for (int64_t qi = 0; qi < nq; qi++) {
         int64_t k = idx[qi];
         if (k < 0 || k >= N) { out[qi] = NAN; continue; }
         double t = sym_dist(Q + qi * d, X + k * d, d, norm, w);
-        double Mk = local_M(T, m, d1[k], F[k], Mtab + k * (m + 1), t);
+        double Mk = local_M(T, m, d1[k], F[k], Mtab + k * (m + 1), t + shift);
         out[qi] = side > 0 ? y[k] + Mk * t : y[k] - Mk * t;
     }
     return 0;

@@ -274,6 +274,12 @@ def check_estimate_M(O):
     assert O.estimate_M(X, np.array([0.0, 1.0, 0.0]))[0] == 1.0
     M, i, j = O.estimate_M(X, np.array([0.0, 1.0, 0.5]))
     assert M == np.inf and (i, j) == (0, 2)
+    # constant y at distinct points: every ratio is 0, so M = 0 with the first pair;
+    # only repeated points with equal y leave no pair at all (-1, -1)
+    Xd = np.array([[0.3, 0.1], [0.9, 0.4], [0.2, 0.8]])
+    for norm in (1, 2, 3):
+        assert O.estimate_M(Xd, np.full(3, 2.5), norm) == (0.0, 0, 1)
+        assert O.estimate_M(np.tile(Xd[:1], (4, 1)), np.full(4, 2.5), norm) == (0.0, -1, -1)
     # the configured workloads' closed-form M bounds the data's estimate
     for p in (W.plain_d2(dtype=np.float64, n_data=400), W.toy_d3(dtype=np.float64, n_data=400),
               W.grad_d8(dtype=np.float64, n_data=400)):
@@ -510,6 +516,95 @@ def check_local_eval(O):
 
 
 
+def _local_M_searchsorted(T, tab, D):
+    """M_k(t) for the distance matrix D [q, k] by the paper's primitive (Sec. 5,
+    torch.searchsorted): F_k on [0, d1_k], else Mtab_k[#{i : T_i < t}]."""
+    d1, F, Mtab = tab
+    seg = np.searchsorted(np.asarray(T), D, side="left")
+    return np.where(D <= d1[None, :], F[None, :], Mtab[np.arange(len(d1))[None, :], seg])
+
+
+def check_local_terms(O):
+    """The value of a chosen datum with its constant at a shifted distance (the GPU tests'
+    yardstick): y_k +- M_k(t + shift) t on scipy distances, for both sides, shifts of 0 and
+    +-eta, and indices outside the data (NaN)."""
+    rng = np.random.default_rng(17)
+    for p in _local_problems()[:4] + _local_problems()[-1:]:
+        T, _, _ = O.local_knots(p.X, 9, 600, 5, p.norm, w=p.w)
+        tab = O.local_table(p.X, p.y, T, p.norm, w=p.w)
+        D = cdist(_scaled(p.Q, p.w), _scaled(p.X, p.w), METRIC[p.norm])
+        eta = 0.05 * float(np.median(D))
+        N = len(p.y)
+        idx = rng.integers(-1, N + 1, len(p.Q))
+        ok = (idx >= 0) & (idx < N)
+        rows = np.arange(len(p.Q))
+        for shift in (0.0, -eta, eta):
+            Ms = _local_M_searchsorted(T, tab, D + shift)
+            for side in (+1, -1):
+                want = np.where(ok, (p.y[None, :] + side * Ms * D)[rows, np.clip(idx, 0, N - 1)], np.nan)
+                got = O.local_terms(p.X, p.y, p.Q, T, tab, idx, side, p.norm, w=p.w, shift=shift)
+                assert np.array_equal(np.isnan(got), ~ok)
+                np.testing.assert_allclose(got[ok], want[ok], rtol=1e-12, atol=1e-13)
+        # at the evaluation's own indices the terms are its envelopes
+        r = O.evaluate_local(p.X, p.y, p.Q, T, tab, p.norm, w=p.w)
+        assert np.array_equal(O.local_terms(p.X, p.y, p.Q, T, tab, r.idx_up, +1, p.norm, w=p.w), r.hi)
+        assert np.array_equal(O.local_terms(p.X, p.y, p.Q, T, tab, r.idx_lo, -1, p.norm, w=p.w), r.lo)
+
+
+def check_local_eval_flags(O):
+    """The ambiguity flags of the local evaluation (eta > 0) against brute force: a query is
+    flagged exactly when some datum, given its lowest constant within eta (M_k(t - eta))
+    while every other datum takes its highest (M_j(t + eta)) and bound values are off by
+    tau / 2 against it, wins the minimum (maximum) although its exact value is more than
+    tau from the envelope.  Random perturbations of the distances and values never pick a
+    datum beyond tau of the envelope on an unflagged query, and every datum they pick
+    passes the possible-winner test against hi_plus / lo_minus.  Flags grow with eta."""
+    rng = np.random.default_rng(23)
+    for seed, (N, d, norm) in enumerate([(45, 2, 2), (60, 3, 1), (52, 2, 3), (70, 1, 2)]):
+        p = W.random_problem(700 + seed, N, d, 48, norm=norm, dtype=np.float64)
+        T, _, _ = O.local_knots(p.X, 8, 800, 3 + seed, norm)
+        tab = O.local_table(p.X, p.y, T, norm)
+        D = cdist(p.Q, p.X, METRIC[norm])
+        eta = 0.04 * float(D.max())
+        scale = float(np.abs(p.y).max() + tab[2].max() * D.max())
+        tau = 1e-3 * scale
+        r = O.evaluate_local(p.X, p.y, p.Q, T, tab, norm, eta=eta, tau=tau)
+        Mt, Ml, Mh = (_local_M_searchsorted(T, tab, D + s) for s in (0.0, -eta, eta))
+        y = p.y[None, :]
+        exact_u, exact_l = y + Mt * D, y - Mt * D
+        bu, bl = exact_u.min(1), exact_l.max(1)
+        np.testing.assert_allclose(r.hi, bu, rtol=1e-12, atol=1e-13)
+        high_u, high_l = y + Mh * D, y - Mh * D
+        np.testing.assert_allclose(r.hi_plus, high_u.min(1), rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(r.lo_minus, high_l.max(1), rtol=1e-12, atol=1e-13)
+        flag_u = np.zeros(len(p.Q), bool)
+        flag_l = np.zeros(len(p.Q), bool)
+        for q in range(len(p.Q)):
+            for k in range(N):
+                others_u = np.delete(high_u[q], k).min() if N > 1 else np.inf
+                others_l = np.delete(high_l[q], k).max() if N > 1 else -np.inf
+                if (p.y[k] + Ml[q, k] * D[q, k]) - tau / 2 <= others_u + tau / 2 and exact_u[q, k] > bu[q] + tau:
+                    flag_u[q] = True
+                if (p.y[k] - Ml[q, k] * D[q, k]) + tau / 2 >= others_l - tau / 2 and exact_l[q, k] < bl[q] - tau:
+                    flag_l[q] = True
+        assert np.array_equal(r.amb_up, flag_u), (seed, np.nonzero(r.amb_up != flag_u)[0])
+        assert np.array_equal(r.amb_lo, flag_l), (seed, np.nonzero(r.amb_lo != flag_l)[0])
+        assert 0 < flag_u.sum() < len(p.Q) and 0 < flag_l.sum() < len(p.Q), (seed, flag_u.sum(), flag_l.sum())
+        rows = np.arange(len(p.Q))
+        for _ in range(300):
+            Dp = np.clip(D + rng.uniform(-eta, eta, D.shape), 0.0, None)
+            Mp = _local_M_searchsorted(T, tab, Dp)
+            vu = y + Mp * D + rng.uniform(-tau / 2, tau / 2, D.shape)
+            vl = y - Mp * D + rng.uniform(-tau / 2, tau / 2, D.shape)
+            ku, kl = vu.argmin(1), vl.argmax(1)
+            assert np.all(~(exact_u[rows, ku] > bu + tau) | r.amb_up)
+            assert np.all(~(exact_l[rows, kl] < bl - tau) | r.amb_lo)
+            assert np.all(p.y[ku] + Ml[rows, ku] * D[rows, ku] <= r.hi_plus + tau)
+            assert np.all(p.y[kl] - Ml[rows, kl] * D[rows, kl] >= r.lo_minus - tau)
+        half = O.evaluate_local(p.X, p.y, p.Q, T, tab, norm, eta=eta / 2, tau=tau)
+        assert np.all(r.amb_up | ~half.amb_up) and np.all(r.amb_lo | ~half.amb_lo)
+
+
 def check_local_k_neighbours(O):
     """k > 1 neighbours with the local constants: the k smallest / largest of the local bound
     values built from scipy distances and the searchsorted form of M_k (stable sort); k = 1
@@ -616,4 +711,4 @@ ALL_CHECKS = [check_hand_examples, check_closed_form_1d, check_unmasked_cdist, c
               check_enclosure, check_lipschitz_monotone, check_width_bound, check_special_cases,
               check_estimate_M, check_gradient_fd, check_k_neighbours, check_splitmix64,
               check_local_hand_example, check_local_knots, check_local_table, check_local_eval,
-              check_local_k_neighbours, check_smoothing]
+              check_local_terms, check_local_eval_flags, check_local_k_neighbours, check_smoothing]

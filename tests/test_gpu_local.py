@@ -8,9 +8,13 @@ values are within the FP32 tolerance of the exact envelopes."""
 import numpy as np
 import pytest
 
+from scipy.spatial.distance import cdist
+
 import oracle as O
 from paper_2606_04670_b300 import workloads as W
 from parity import FP32_TOL, diam
+
+METRIC = {1: "cityblock", 2: "euclidean", 3: "chebyshev"}
 
 pytestmark = pytest.mark.gpu
 
@@ -45,29 +49,54 @@ def _cases():
 CASES = _cases()
 
 
-def _check_eval(p, X, y, Q, T, tab, out, label, min_clear=0.9):
-    """Validity of every query, the envelope within FP32 tolerance where the decision is
-    unambiguous (at least min_clear of the queries for random queries; at the data, exact
-    ties with the datum's own value make many flags harmless)."""
+def _check_eval(p, X, y, Q, T, tab, out, label):
+    """Every query, both bounds (the upper shown; the lower is its mirror):
+    * the returned bound is the exact FP64 value of the returned datum, rounded once;
+    * it is never better than the exact envelope H_up;
+    * the returned datum is one an FP32 evaluation can pick: its value with the lowest
+      constant its distance error allows, y_k + M_k(t - eta) t, is at most tau above
+      hi_plus, the envelope with every constant at its highest, M_j(t + eta) (so a far-off
+      datum cannot pass, flagged or not);
+    * where the oracle finds that no datum such an evaluation could pick has an exact value
+      more than tau above H_up (the query is not flagged), the bound is within tau of H_up;
+    * a query is flagged only where some datum's constant can change within eta of its
+      distance (M_k(t - eta) < M_k(t + eta)): the flags are a subset of those queries."""
     hi, lo, g = (_f64(out[k].cpu().numpy()) for k in ("hi", "lo", "g"))
     iu, il = (out[k].cpu().numpy().astype(np.int64) for k in ("idx_up", "idx_lo"))
     Z = np.abs(np.concatenate([X, Q]) * (1.0 if p.w is None else np.asarray(p.w)))
-    eta = 2.0 ** -20 * (X.shape[1] + 2) * (Z.max() + diam(X, Q, p.norm, p.w))
-    r = O.evaluate_local(X, y, Q, T, tab, p.norm, w=p.w, eta=eta)
+    dm = diam(X, Q, p.norm, p.w)
+    eta = 2.0 ** -20 * (X.shape[1] + 2) * (Z.max() + dm)
+    mmax = float(tab[2].max()) if tab[2].size else 0.0
+    scale = float(np.abs(y).max()) + mmax * dm + 1e-30
+    tau = max(FP32_TOL * scale, 2.0 * (mmax * eta + 2.0 ** -21 * scale))
+    r = O.evaluate_local(X, y, Q, T, tab, p.norm, w=p.w, eta=eta, tau=tau)
     tu = O.local_terms(X, y, Q, T, tab, iu, +1, p.norm, w=p.w)
     tl = O.local_terms(X, y, Q, T, tab, il, -1, p.norm, w=p.w)
     # the returned values are the exact FP64 values of the returned data, rounded once
     assert np.array_equal(hi.astype(np.float32), tu.astype(np.float32)), label
     assert np.array_equal(lo.astype(np.float32), tl.astype(np.float32)), label
     assert np.array_equal(g.astype(np.float32), (0.5 * (tu + tl)).astype(np.float32)), label
-    scale = float(np.abs(y).max()) + float(tab[2].max()) * diam(X, Q, p.norm, p.w) + 1e-30
-    tol = FP32_TOL * scale
     # never better than the exact envelope
     assert np.all(tu >= r.hi - 1e-12 * scale) and np.all(tl <= r.lo + 1e-12 * scale), label
+    # a datum an FP32 evaluation can pick (every query)
+    tu_low = O.local_terms(X, y, Q, T, tab, iu, +1, p.norm, w=p.w, shift=-eta)
+    tl_low = O.local_terms(X, y, Q, T, tab, il, -1, p.norm, w=p.w, shift=-eta)
+    assert np.all(tu_low <= r.hi_plus + tau), (label, np.max(tu_low - r.hi_plus), tau)
+    assert np.all(tl_low >= r.lo_minus - tau), (label, np.max(r.lo_minus - tl_low), tau)
+    # unflagged queries: within tau of the exact envelope
     su, sl = ~r.amb_up, ~r.amb_lo
-    assert su.mean() >= min_clear and sl.mean() >= min_clear, (label, su.mean(), sl.mean())
-    assert np.all(np.abs(tu - r.hi)[su] <= tol), (label, np.abs(tu - r.hi)[su].max(), tol)
-    assert np.all(np.abs(tl - r.lo)[sl] <= tol), (label, np.abs(tl - r.lo)[sl].max(), tol)
+    assert np.all(np.abs(tu - r.hi)[su] <= tau), (label, np.abs(tu - r.hi)[su].max(), tau)
+    assert np.all(np.abs(tl - r.lo)[sl] <= tau), (label, np.abs(tl - r.lo)[sl].max(), tau)
+    # flags only where a constant can change within eta
+    if len(Q) * len(X) <= 8_000_000:
+        D = cdist(Q * (1.0 if p.w is None else np.asarray(p.w)), X * (1.0 if p.w is None else np.asarray(p.w)),
+                  METRIC[p.norm])
+        d1, F, Mtab = tab
+        def mk(Dm):
+            seg = np.searchsorted(np.asarray(T), Dm, side="left")
+            return np.where(Dm <= d1[None, :], F[None, :], Mtab[np.arange(len(d1))[None, :], seg])
+        near = np.any(mk(D - eta) < mk(D + eta), axis=1)
+        assert np.all(near | ~(r.amb_up | r.amb_lo)), label
     return r
 
 
@@ -89,7 +118,7 @@ def test_knots_table_and_eval_match_oracle(case):
         _check_eval(p, X, y, Q, T, (d1, F, Mtab), out, p.name)
         # interpolation at the data (Sec. 4.3: the approximation interpolates the data)
         outd = m.eval_local(torch.as_tensor(p.X).cuda())
-        _check_eval(p, X, y, X, T, (d1, F, Mtab), outd, p.name + "@data", min_clear=0.0)
+        _check_eval(p, X, y, X, T, (d1, F, Mtab), outd, p.name + "@data")
         tol = 1e-6 * (np.abs(y).max() + 1)
         assert np.all(np.abs(outd["g"].cpu().numpy() - y) <= tol)
     m.check()
@@ -110,7 +139,7 @@ def test_explicit_knots_at_pair_distances():
     assert np.array_equal(d1, od1) and np.array_equal(F, oF) and np.array_equal(Mtab, oM)
     # data points at knot distances from others: still interpolated
     out = m.eval_local(torch.as_tensor(p.X).cuda())
-    _check_eval(p, X, y, X, T, (d1, F, Mtab), out, "knots-at-pairs", min_clear=0.0)
+    _check_eval(p, X, y, X, T, (d1, F, Mtab), out, "knots-at-pairs")
     m.close()
 
 
@@ -177,7 +206,7 @@ def test_fp64_handle_local():
         assert np.array_equal(a, b)
     out = m.eval_local(torch.as_tensor(p.Q).cuda())
     assert out["g"].dtype == torch.float64
-    r = O.evaluate_local(p.X, p.y, p.Q, T, tab, 2, w=p.w, eta=1e-5)
+    r = O.evaluate_local(p.X, p.y, p.Q, T, tab, 2, w=p.w, eta=1e-5, tau=1e-5)
     tu = O.local_terms(p.X, p.y, p.Q, T, tab, out["idx_up"].cpu().numpy().astype(np.int64), +1, 2, w=p.w)
     assert np.allclose(out["hi"].cpu().numpy(), tu, rtol=0, atol=1e-12)
     clear = ~r.amb_up
@@ -312,8 +341,8 @@ def test_local_k_neighbours(k):
     r = O.evaluate_local_k(X, y, Q, T, tab, k, wk, p.norm, w=p.w)
     Z = np.abs(np.concatenate([X, Q]) * np.asarray(p.w))
     eta = 2.0 ** -20 * (X.shape[1] + 2) * (Z.max() + diam(X, Q, p.norm, p.w))
-    amb = O.evaluate_local(X, y, Q, T, tab, p.norm, w=p.w, eta=eta)
     tol = FP32_TOL * (float(np.abs(y).max()) + float(tab[2].max()) * diam(X, Q, p.norm, p.w))
+    amb = O.evaluate_local(X, y, Q, T, tab, p.norm, w=p.w, eta=eta, tau=tol)
     # validity: the outputs are the weighted sums of the exact values of the returned data,
     # which come sorted by value
     for key, idx, side in (("hi", "idx_up", +1), ("lo", "idx_lo", -1)):

@@ -53,6 +53,24 @@ MUTANTS = {
                           "double dlo = oracle_dist(xi, xk, d, norm, mon, w, +1);", 1),
     # L-BFGS search direction along +H g
     "lbfgs_ascent": ("for (int64_t i = 0; i < N; i++) dir[i] = -q[i];", "for (int64_t i = 0; i < N; i++) dir[i] = q[i];", 1),
+    # local terms (the GPU tests' yardstick): sides swapped, a row stride off by one, the
+    # distance shift ignored
+    "local_terms_side": ("out[qi] = side > 0 ? y[k] + Mk * t : y[k] - Mk * t;",
+                         "out[qi] = side < 0 ? y[k] + Mk * t : y[k] - Mk * t;", 1),
+    "local_terms_row_stride": ("double Mk = local_M(T, m, d1[k], F[k], Mtab + k * (m + 1), t + shift);",
+                               "double Mk = local_M(T, m, d1[k], F[k], Mtab + k * m, t + shift);", 1),
+    "local_terms_no_shift": ("double Mk = local_M(T, m, d1[k], F[k], Mtab + k * (m + 1), t + shift);",
+                             "double Mk = local_M(T, m, d1[k], F[k], Mtab + k * (m + 1), t);", 1),
+    # ambiguity flags: raised for every query with a possible winner (over-flagging), the
+    # constants' possible drop ignored (under-flagging), hi_plus from the low constants
+    "local_flags_over": ("if (J->y[k] + ma * t <= hp + J->tau && J->y[k] + mt * t > bu + J->tau) au = 1;",
+                         "if (J->y[k] + ma * t <= hp + J->tau) au = 1;", 1),
+    "local_flags_under": ("double ma = local_M(J->T, J->m, J->d1[k], J->F[k], row, t - J->eta);",
+                          "double ma = local_M(J->T, J->m, J->d1[k], J->F[k], row, t);", 1),
+    "local_flags_lower_side_over": ("if (J->y[k] - ma * t >= lm - J->tau && J->y[k] - mt * t < bl - J->tau) al = 1;",
+                                    "if (J->y[k] - ma * t >= lm - J->tau) al = 1;", 1),
+    "local_hi_plus_low": ("double mb = local_M(J->T, J->m, J->d1[k], J->F[k], row, t + J->eta);",
+                          "double mb = local_M(J->T, J->m, J->d1[k], J->F[k], row, t - J->eta);", 1),
     "splitmix_shift": ("z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBull;", 1),
 }
 

@@ -38,20 +38,60 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 void* g_addr[MAX_DEVICES] = {};
+unsigned long long g_ctx_id[MAX_DEVICES] = {};    // context the address belongs to (0: none yet)
 
-// Device address of g_noalloc_scratch on the current device, looked up once per device.
+// The driver's context queries, reached through the runtime so that the library does not
+// link the driver library itself (it must load on machines without a GPU driver).
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+bool g_ctx_fns_looked_up = false;
+
+// Identifier of the context current on this thread, or 0 when none is current (or the
+// driver cannot say).
+unsigned long long current_context_id() {
+    if (!g_ctx_fns_looked_up) {
+        g_ctx_fns_looked_up = true;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+        }
+        cudaGetLastError();
+    }
+    if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != 0 || !ctx) return 0;
+    if (g_ctx_get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of g_noalloc_scratch on the current device.  It is looked up once per
+// device and context: cudaDeviceReset destroys the device's primary context, the module
+// is loaded again in the next one and the array may move, so a new context id triggers a
+// new lookup.  (Without the driver's context id the address is looked up on every call.)
 lip_status scratch_address(int dev, void** out) {
     std::lock_guard<std::mutex> lock(g_mu);
     if (dev < 0 || dev >= MAX_DEVICES) return set_error(LIP_ERR_UNSUPPORTED, "device ordinal beyond 63");
-    if (!g_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_addr[dev] || ctx == 0 || ctx != g_ctx_id[dev]) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             char buf[256];
             snprintf(buf, sizeof buf, "cudaGetSymbolAddress(g_noalloc_scratch): %s", cudaGetErrorString(e));
+            g_addr[dev] = nullptr;
             return set_error(LIP_ERR_CUDA, buf);
         }
         g_addr[dev] = p;
+        // the lookup made the device's context current if none was
+        g_ctx_id[dev] = ctx != 0 ? ctx : current_context_id();
     }
     *out = g_addr[dev];
     return LIP_OK;

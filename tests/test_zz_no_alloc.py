@@ -55,6 +55,42 @@ def test_noalloc_matches_estimate_M_on_consecutive_calls():
         assert (i1, j1) == (i0, j0)
 
 
+def test_noalloc_at_its_exact_capacity():
+    """N = LIP_NOALLOC_N_MAX at d = LIP_D_MAX fills the fixed array's layout and its
+    candidate records to the last byte; the result must still equal lip_estimate_M's, and
+    the pair must be the FP64 oracle's maximum on a row sample."""
+    import torch
+
+    from paper_2606_04670_b300 import lipfit as L
+    out = torch.full((3,), -7.0, dtype=torch.float64, device="cuda")
+    n = L.LIP_NOALLOC_N_MAX
+    for seed, d, norm in ((903, 16, W.NORM_L2), (904, 3, W.NORM_LINF)):
+        p = W.random_problem(seed, n, d, 1, norm=norm, weighted=True)
+        M0, i0, j0 = _via_handle(p)
+        for _ in range(2):
+            M1, i1, j1 = _via_noalloc(p, out)
+            assert abs(M1 - M0) <= 1e-5 * M0, (d, M1, M0)
+            assert (i1, j1) == (i0, j0)
+        # the returned pair's exact ratio is the returned M (FP64 re-evaluation)
+        Z = p.X.astype(np.float64) * np.asarray(p.w)[None, :]
+        t = np.abs(Z[i1] - Z[j1])
+        dist = {W.NORM_L1: t.sum(), W.NORM_L2: np.sqrt((t * t).sum()), W.NORM_LINF: t.max()}[norm]
+        assert abs(M1 - abs(float(p.y[i1]) - float(p.y[j1])) / dist) <= 1e-12 * M1
+
+
+def test_noalloc_constant_values():
+    """Constant y at distinct points gives M = 0 with a real pair (the lowest), like the
+    handle path; repeated points with equal y give -1 / -1."""
+    import torch
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    p = W.random_problem(905, 700, 4, 1, norm=W.NORM_L2)
+    p = W.Problem(p.name, p.X, np.full_like(p.y, 0.75), p.Q, p.M, p.norm, p.mon, p.w, None)
+    assert _via_noalloc(p, out) == _via_handle(p) == (0.0, 0, 1)
+    X = np.tile(p.X[:1], (5, 1))
+    q = W.Problem(p.name, X, np.full(5, 0.75, np.float32), p.Q, p.M, p.norm, None, None, None)
+    assert _via_noalloc(q, out) == (0.0, -1, -1)
+
+
 def test_noalloc_rejects_sizes_beyond_its_capacity():
     import torch
 

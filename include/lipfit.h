@@ -187,11 +187,68 @@ LIP_API lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* 
  * i < j of |y^i - y^j| / dist(x^i, x^j) with the symmetric weighted norm of the handle
  * (monotonicity does not enter).  N^2/2 work and no pair matrix is stored (Sec. 5).
  * Pairs with dist = 0 and equal y are skipped; dist = 0 with different y gives +Inf.
- * The candidate maximum is found in FP32 and the winning pair is re-evaluated in FP64.
- * Outputs (host): *M_out, and the pair (*i_out < *j_out), or -1/-1 with *M_out = 0 when
- * N < 2 or all the data are equal.  Synchronises the stream. */
+ * The candidate maximum is found in FP32 and the winning pair is re-evaluated in FP64;
+ * ties go to the lowest (i, j).
+ * Outputs (host): *M_out, and the pair (*i_out < *j_out).  *i_out = *j_out = -1 with
+ * *M_out = 0 only when no pair has a defined ratio: N < 2, or every pair is a repeated
+ * point (dist = 0) with equal y.  Data at distinct points with constant y give M = 0 with
+ * a real pair, the lowest (i, j) at positive distance.  Synchronises the stream. */
 LIP_API lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, int64_t* j_out,
                           void* stream);
+
+/* ------------------------------------------------ several GPUs (one process per GPU) */
+/* The paper computes every bound and the estimate as one reduction over all data (Sec. 5:
+ * O(N) work per query, N^2 for the Lipschitz constant, no pair matrix); these calls split
+ * that reduction across GPUs.  The collectives between them are the caller's (the Python
+ * package uses torch.distributed, NCCL on GPUs); each call runs on this process's GPU.
+ *
+ * Data-sharded evaluation: rank r holds the contiguous slice of the data starting at
+ * global index index_base_r in its own handle (same d, M, norm, mon, w and precision on
+ * every rank).  Per call:
+ *   1. lip_shard_scan       on every rank: packed keys key_up, key_lo [nq] (device int64);
+ *   2. all-reduce MIN of key_up and key_lo over the ranks;
+ *   3. lip_shard_reeval     on every rank: hi64, lo64 [nq] (device double);
+ *   4. all-reduce MIN of hi64 and MAX of lo64 over the ranks;
+ *   5. lip_shard_finish     on any rank that wants the outputs.
+ * The results equal lip_eval's on one handle holding all the data, bit for bit (the keys
+ * order the ranks' FP32 scan extrema exactly as lip_eval's split merge does, and the
+ * winners are re-evaluated in FP64 by the rank that holds them).  FP32 and tensor-core
+ * handles (the plain FP32 scan runs on either); LIP_ERR_UNSUPPORTED for FP64 handles. */
+
+/* Step 1: the all-pairs scan of this rank's data.  key_up[q] (key_lo[q]) = (the FP32 scan's
+ * smallest upper (largest lower) bound value v made order-preserving as an unsigned 32-bit
+ * integer, of -v for the lower bound) << 31 | (index_base + local index of its datum), the
+ * lowest index on ties; INT64_MAX when the handle holds no points or the query is not
+ * finite.  The MIN over ranks of these keys is the single-GPU choice.
+ *   Q [nq][d] device, handle element type; index_base >= 0 with index_base + capacity
+ *   <= 2^31 (LIP_ERR_ARG otherwise).  Asynchronous on `stream`. */
+LIP_API lip_status lip_shard_scan(lip_handle h, const void* Q, int64_t nq, int64_t index_base, int64_t* key_up,
+                                  int64_t* key_lo, void* stream);
+
+/* Step 3: for every query whose merged key names a datum of this rank (global index in
+ * [index_base, index_base + N)), its exact FP64 bound y + M dist_up (hi64) and
+ * y - M dist_lo (lo64), computed as lip_eval's merge does; +Inf (hi64) and -Inf (lo64)
+ * for the others, the neutral values of step 4.  Asynchronous on `stream`. */
+LIP_API lip_status lip_shard_reeval(lip_handle h, const void* Q, int64_t nq, int64_t index_base,
+                                    const int64_t* key_up, const int64_t* key_lo, double* hi64, double* lo64,
+                                    void* stream);
+
+/* Step 5: g = (hi + lo) / 2 (in FP64, rounded once to the handle's element type), lo, hi
+ * and the global indices idx_up, idx_lo from the merged keys and values; NaN and -1 where
+ * a key is INT64_MAX.  Any output may be NULL.  Asynchronous on `stream`. */
+LIP_API lip_status lip_shard_finish(lip_handle h, int64_t nq, const int64_t* key_up, const int64_t* key_lo,
+                                    const double* hi64, const double* lo64, void* g, void* lo, void* hi,
+                                    int32_t* idx_up, int32_t* idx_lo, void* stream);
+
+/* The Lipschitz-constant estimate over one block-cyclic share of the pairs, for ranks that
+ * all hold the same data: the N^2/2 pairs are cut into tile pairs (I, J >= I) of 512
+ * points, and part p of nparts takes the tile pairs with (I * tiles + J) mod nparts = p.
+ * out (host double[4]) = {M over the part's pairs (FP64 re-evaluation of its FP32
+ * winner), i, j, the winner's FP32 squared ratio}, or {0, -1, -1, -1} when the part has
+ * no pair with a defined ratio.  The estimate over all pairs is the part whose FP32
+ * squared ratio is largest, the lowest (i, j) on ties (lip_estimate_M's choice, bit for
+ * bit).  0 <= part < nparts, else LIP_ERR_ARG.  Synchronises the stream. */
+LIP_API lip_status lip_estimate_M_part(lip_handle h, int32_t part, int32_t nparts, double* out, void* stream);
 
 /* Largest N accepted by lip_estimate_M_noalloc. */
 #define LIP_NOALLOC_N_MAX 32768
@@ -206,12 +263,14 @@ LIP_API lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, i
  *   X [N][d], y [N]  device, float, finite (not checked); read only.
  *   N                1 <= N <= LIP_NOALLOC_N_MAX, else LIP_ERR_ARG (fixed capacity).
  *   d, norm, w       as for lip_fit (w: host array of d weights > 0, or NULL).
- *   out              device double[3], written with {M_est, i, j} (i < j as doubles,
- *                    -1 and M_est = 0 when no pair qualifies), same definition and
- *                    same kernels as lip_estimate_M.
+ *   out              device double[3], written with {M_est, i, j} (i < j as doubles),
+ *                    the definition, kernels and results of lip_estimate_M, including
+ *                    its rule for -1 / -1 (no pair with a defined ratio).
  * The call is asynchronous on `stream` (it does not synchronise).  The first call on
  * each device looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  Every call on a device shares the one array,
+ * first call before any stream capture.  The address is kept per device and CUDA
+ * context, so after a cudaDeviceReset the next call looks it up again in the new
+ * context (that call, too, must come before any capture).  Every call on a device shares the one array,
  * which keeps the last call's contents (each call writes everything it later reads, so
  * nothing needs clearing): calls whose GPU work overlaps -- on different streams, or
  * from several host threads -- race and give wrong results, so order them on one
@@ -496,6 +555,29 @@ LIP_API size_t lip_last_error_detail(char* buf, size_t len);
 
 /* Library version, e.g. "0.1.0 sm_103a". */
 LIP_API const char* lip_version(void);
+
+/* ---------------------------------------------------------------- fault injection (tests) */
+/* The paper has no counterpart: these two calls let tests reach the library's failure
+ * paths without a real device fault. */
+
+/* Makes the n-th device allocation the library attempts from now on (counting from 1, on
+ * any handle or thread) fail as if the device were out of memory: it returns
+ * LIP_ERR_OOM through the usual path, without calling cudaMalloc.  n = 0 turns this off.
+ * Allocations after the failing one succeed again.  LIP_ERR_ARG for n < 0. */
+LIP_API lip_status lip_debug_fail_alloc(int64_t n);
+
+/* Fault injection for the exact FP32 scan kernel of handle h (FP32 handles whose shape has
+ * an exact instantiation; other kernels ignore it):
+ *   wait_limit_ns  limit of the kernel's bounded waits on its data tiles, in ns of the GPU's
+ *                  global timer (0 = the default, 2 s; at most the default).
+ *   skip_tile      every thread block leaves out the bulk copy of its data tile number
+ *                  skip_tile (0 = its first), so its wait for that tile runs out: the block
+ *                  records the timeout in the handle's status word, waits for the copies it
+ *                  did issue, writes NaN / index -1 for its queries and returns.  lip_check
+ *                  then reports LIP_ERR_TIMEOUT.  -1 = no tile left out.
+ * The handle stays usable: lip_debug_scan_fault(h, 0, -1) restores normal evaluation.
+ * LIP_ERR_ARG for a NULL handle, skip_tile < -1 or a limit above the default. */
+LIP_API lip_status lip_debug_scan_fault(lip_handle h, uint64_t wait_limit_ns, int32_t skip_tile);
 
 #ifdef __cplusplus
 }

@@ -32,6 +32,22 @@ lip_status cuda_fail(cudaError_t e, const char* what) {
 
 void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+namespace {
+// > 0: the device allocation that brings this to 0 fails (lip_debug_fail_alloc)
+std::atomic<int64_t> g_fail_alloc_countdown{0};
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    int64_t c = g_fail_alloc_countdown.load(std::memory_order_relaxed);
+    while (c > 0 && !g_fail_alloc_countdown.compare_exchange_weak(c, c - 1, std::memory_order_relaxed)) {
+    }
+    if (c == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 // Records an error for lip_last_error from other translation units of the library.
 lip_status set_error(lip_status s, const char* msg) { return fail(s, "%s", msg); }
 
@@ -78,6 +94,8 @@ void fill_scan_params(const lip_model* h, ScanParams& P) {
     }
     P.hot = h->hot;
     P.err = h->status;
+    P.wait_ns = h->dbg_wait_ns ? h->dbg_wait_ns : WAIT_LIMIT_NS;
+    P.skip_tile = h->dbg_skip_tile;
 }
 
 void fill_hot_params(const lip_model* h, HotParams& P, int64_t k0, int64_t k1) {
@@ -227,7 +245,7 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
         {reinterpret_cast<void**>(&h->status), 2 * sizeof(unsigned), "status word"},
     };
     for (auto& a : allocs) {
-        e = cudaMalloc(a.p, a.n);
+        e = dev_malloc(a.p, a.n);
         if (e != cudaSuccess) {
             *a.p = nullptr;
             free_model(h);
@@ -242,7 +260,7 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
             {reinterpret_cast<void**>(&h->tc_maxbits), 2 * sizeof(unsigned), "tensor-core bounds"},
         };
         for (auto& a : tca) {
-            e = cudaMalloc(a.p, a.n);
+            e = dev_malloc(a.p, a.n);
             if (e != cudaSuccess) {
                 *a.p = nullptr;
                 free_model(h);
@@ -256,7 +274,7 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
             {reinterpret_cast<void**>(&h->s32_max), 2 * sizeof(unsigned), "screen bounds"},
         };
         for (auto& a : s32) {
-            e = cudaMalloc(a.p, a.n);
+            e = dev_malloc(a.p, a.n);
             if (e != cudaSuccess) {
                 *a.p = nullptr;
                 free_model(h);
@@ -345,8 +363,9 @@ int choose_splits(const lip_model* h, int64_t gx, int64_t tiles) {
     return best;
 }
 
-lip_status eval_plain(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* iu, int32_t* il,
-                      cudaStream_t st) {
+// The all-pairs scan of the plain layout into per-split partial records (h->partial);
+// *nsplit_out receives the number of splits (0 when the handle holds no points).
+lip_status scan_partials(lip_model* h, const void* Q, int64_t nq, cudaStream_t st, int* nsplit_out) {
     const int64_t ngroups = round_up(h->N, PAD_POINTS) / GROUP;
     const int tg = h->exact ? h->tile_groups : 1;
     const int64_t gx = ceil_div(nq, (int64_t)SCAN_THREADS * h->kinfo.rows);
@@ -377,6 +396,29 @@ lip_status eval_plain(lip_model* h, const void* Q, int64_t nq, void* g, void* lo
         if (h->ev_scan1) CUDA_TRY(cudaEventRecord(h->ev_scan1, st));
         count_launches(1);
     }
+    *nsplit_out = nsplit;
+    return LIP_OK;
+}
+
+// The handle's parameters of the FP64 re-evaluation (split merge and shard re-evaluation).
+void fill_merge_params(const lip_model* h, const void* Q, int64_t nq, MergeParams& Mp) {
+    Mp.Q = Q;
+    Mp.nq = nq;
+    Mp.d = h->d;
+    Mp.M = h->M;
+    Mp.norm = h->norm;
+    for (int i = 0; i < D_MAX; ++i) {
+        Mp.mon[i] = h->mon[i];
+        Mp.w[i] = h->w[i];
+    }
+    Mp.X0 = h->X0;
+    Mp.y0 = h->y0;
+}
+
+lip_status eval_plain(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* iu, int32_t* il,
+                      cudaStream_t st) {
+    int nsplit = 0;
+    LIP_TRY(scan_partials(h, Q, nq, st, &nsplit));
     MergeParams Mp;
     Mp.Q = Q;
     Mp.nq = nq;
@@ -581,6 +623,70 @@ lip_status eval_screen64(lip_model* h, const void* Q, int64_t nq, void* g, void*
     Mp.idx_lo = il;
     CUDA_TRY(launch_merge(8, Mp, st));
     count_launches(1);
+    return LIP_OK;
+}
+
+// The estimate over the tile pairs of block-cyclic part `part` of nparts (all pairs for
+// 0 of 1): res = {M_est, i, j, the winner's FP32 squared ratio (-1 without one)}.
+// Synchronises the stream.
+lip_status estimate_part(lip_model* h, int part, int nparts, double* res, cudaStream_t st) {
+    DeviceGuard gd(h->device);
+    res[0] = 0.0;
+    res[1] = res[2] = -1.0;
+    res[3] = -1.0;
+    if (h->N < 2) return LIP_OK;
+    const int tile = estimate_tile_points();
+    const int64_t nb = ceil_div(h->N, tile);
+    if (nb > 65535) return fail(LIP_ERR_UNSUPPORTED, "N = %lld is too large for lip_estimate_M", (long long)h->N);
+    const int64_t pts = nb * tile;
+    const int nch = h->d + 1;
+    const size_t lay_b = round_up(pts * nch * 4, 256), cand_b = round_up(nb * nb * 16, 256);
+    LIP_TRY(h->est.ensure(lay_b + cand_b + 256, "estimate scratch"));
+    char* base = static_cast<char*>(h->est.p);
+    // unscaled layout: coordinates times the weights, caller's order, FP32
+    HotParams Hp;
+    Hp.X0 = h->X0;
+    Hp.y0 = h->y0;
+    Hp.k0 = 0;
+    Hp.k1 = h->N;
+    Hp.d = h->d;
+    Hp.C = 0;
+    Hp.dl = h->d;
+    Hp.nch = nch;
+    Hp.aux = 0;
+    for (int j = 0; j < D_MAX; ++j) {
+        Hp.perm[j] = j;
+        Hp.scale[j] = h->w[j];
+    }
+    Hp.hot = base;
+    Hp.err = h->status + 1;
+    CUDA_TRY(launch_estimate_layout(h->esize, Hp, st));
+    CUDA_TRY(launch_pad_hot(4, base, h->N, pts, nch, h->d, st));
+    EstParams P;
+    P.lay = reinterpret_cast<const float4*>(base);
+    P.N = h->N;
+    P.nb = (int)nb;
+    P.cand = reinterpret_cast<float4*>(base + lay_b);
+    P.part = part;
+    P.nparts = nparts;
+    CUDA_TRY(launch_estimate(h->norm, h->d, P, st));
+    EstFinalParams F;
+    F.cand = P.cand;
+    F.nb = (int)nb;
+    F.X0 = h->X0;
+    F.y0 = h->y0;
+    F.d = h->d;
+    F.norm = h->norm;
+    F.elem_bytes = h->esize;
+    for (int j = 0; j < D_MAX; ++j) F.w[j] = h->w[j];
+    F.out = reinterpret_cast<double*>(base + lay_b + cand_b);
+    F.part = part;
+    F.nparts = nparts;
+    F.write_key = 1;
+    CUDA_TRY(launch_estimate_final(F, st));
+    count_launches(4);
+    CUDA_TRY(cudaMemcpyAsync(res, F.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
     return LIP_OK;
 }
 
@@ -804,62 +910,67 @@ lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* g, void*
 lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, int64_t* j_out, void* stream) {
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
     if (!M_out || !i_out || !j_out) return fail(LIP_ERR_ARG, "an output pointer is NULL");
-    DeviceGuard gd(h->device);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    *M_out = 0.0;
-    *i_out = *j_out = -1;
-    if (h->N < 2) return LIP_OK;
-    const int tile = estimate_tile_points();
-    const int64_t nb = ceil_div(h->N, tile);
-    if (nb > 65535) return fail(LIP_ERR_UNSUPPORTED, "N = %lld is too large for lip_estimate_M", (long long)h->N);
-    const int64_t pts = nb * tile;
-    const int nch = h->d + 1;
-    const size_t lay_b = round_up(pts * nch * 4, 256), cand_b = round_up(nb * nb * 16, 256);
-    LIP_TRY(h->est.ensure(lay_b + cand_b + 256, "estimate scratch"));
-    char* base = static_cast<char*>(h->est.p);
-    // unscaled layout: coordinates times the weights, caller's order, FP32
-    HotParams Hp;
-    Hp.X0 = h->X0;
-    Hp.y0 = h->y0;
-    Hp.k0 = 0;
-    Hp.k1 = h->N;
-    Hp.d = h->d;
-    Hp.C = 0;
-    Hp.dl = h->d;
-    Hp.nch = nch;
-    Hp.aux = 0;
-    for (int j = 0; j < D_MAX; ++j) {
-        Hp.perm[j] = j;
-        Hp.scale[j] = h->w[j];
-    }
-    Hp.hot = base;
-    Hp.err = h->status + 1;
-    CUDA_TRY(launch_estimate_layout(h->esize, Hp, st));
-    CUDA_TRY(launch_pad_hot(4, base, h->N, pts, nch, h->d, st));
-    EstParams P;
-    P.lay = reinterpret_cast<const float4*>(base);
-    P.N = h->N;
-    P.nb = (int)nb;
-    P.cand = reinterpret_cast<float4*>(base + lay_b);
-    CUDA_TRY(launch_estimate(h->norm, h->d, P, st));
-    EstFinalParams F;
-    F.cand = P.cand;
-    F.nb = (int)nb;
-    F.X0 = h->X0;
-    F.y0 = h->y0;
-    F.d = h->d;
-    F.norm = h->norm;
-    F.elem_bytes = h->esize;
-    for (int j = 0; j < D_MAX; ++j) F.w[j] = h->w[j];
-    F.out = reinterpret_cast<double*>(base + lay_b + cand_b);
-    CUDA_TRY(launch_estimate_final(F, st));
-    count_launches(4);
-    double res[3];
-    CUDA_TRY(cudaMemcpyAsync(res, F.out, sizeof res, cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
+    double res[4];
+    LIP_TRY(estimate_part(h, 0, 1, res, static_cast<cudaStream_t>(stream)));
     *M_out = res[0];
     *i_out = (int64_t)res[1];
     *j_out = (int64_t)res[2];
+    return LIP_OK;
+}
+
+lip_status lip_estimate_M_part(lip_handle h, int32_t part, int32_t nparts, double* out, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (!out) return fail(LIP_ERR_ARG, "out is NULL");
+    if (nparts < 1 || part < 0 || part >= nparts) return fail(LIP_ERR_ARG, "part %d of %d is not valid", part, nparts);
+    return estimate_part(h, part, nparts, out, static_cast<cudaStream_t>(stream));
+}
+
+lip_status lip_shard_scan(lip_handle h, const void* Q, int64_t nq, int64_t index_base, int64_t* key_up,
+                          int64_t* key_lo, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (nq < 0) return fail(LIP_ERR_ARG, "nq = %lld < 0", (long long)nq);
+    if (index_base < 0 || index_base + h->cap > ((int64_t)1 << 31))
+        return fail(LIP_ERR_ARG, "index_base %lld + capacity %lld exceeds 2^31", (long long)index_base,
+                    (long long)h->cap);
+    if (h->esize == 8) return fail(LIP_ERR_UNSUPPORTED, "data-sharded evaluation needs an FP32 or tensor-core handle");
+    if (nq == 0) return LIP_OK;
+    if (!Q || !key_up || !key_lo) return fail(LIP_ERR_ARG, "Q or a key array is NULL");
+    DeviceGuard gd(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int nsplit = 0;
+    LIP_TRY(scan_partials(h, Q, nq, st, &nsplit));
+    CUDA_TRY(launch_shard_keys(h->esize, h->partial.p, nsplit, nq, Q, h->d, index_base, key_up, key_lo, st));
+    count_launches(1);
+    return LIP_OK;
+}
+
+lip_status lip_shard_reeval(lip_handle h, const void* Q, int64_t nq, int64_t index_base, const int64_t* key_up,
+                            const int64_t* key_lo, double* hi64, double* lo64, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (nq < 0) return fail(LIP_ERR_ARG, "nq = %lld < 0", (long long)nq);
+    if (index_base < 0) return fail(LIP_ERR_ARG, "index_base = %lld < 0", (long long)index_base);
+    if (nq == 0) return LIP_OK;
+    if (!Q || !key_up || !key_lo || !hi64 || !lo64) return fail(LIP_ERR_ARG, "a pointer is NULL");
+    DeviceGuard gd(h->device);
+    MergeParams Mp;
+    fill_merge_params(h, Q, nq, Mp);
+    CUDA_TRY(launch_shard_reeval(h->esize, Mp, index_base, h->N, key_up, key_lo, hi64, lo64,
+                                 static_cast<cudaStream_t>(stream)));
+    count_launches(1);
+    return LIP_OK;
+}
+
+lip_status lip_shard_finish(lip_handle h, int64_t nq, const int64_t* key_up, const int64_t* key_lo,
+                            const double* hi64, const double* lo64, void* g, void* lo, void* hi, int32_t* idx_up,
+                            int32_t* idx_lo, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (nq < 0) return fail(LIP_ERR_ARG, "nq = %lld < 0", (long long)nq);
+    if (nq == 0) return LIP_OK;
+    if (!key_up || !key_lo || !hi64 || !lo64) return fail(LIP_ERR_ARG, "a key or value array is NULL");
+    DeviceGuard gd(h->device);
+    CUDA_TRY(launch_shard_finish(h->esize, nq, key_up, key_lo, hi64, lo64, g, lo, hi, idx_up, idx_lo,
+                                 static_cast<cudaStream_t>(stream)));
+    count_launches(1);
     return LIP_OK;
 }
 
@@ -974,7 +1085,7 @@ lip_status lip_autotune(lip_handle h, const void* Q, int64_t nq, int32_t reps, i
     DeviceGuard gd(h->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     void* out = nullptr;
-    CUDA_TRY(cudaMalloc(&out, (size_t)nq * (3 * h->esize + 8)));
+    CUDA_TRY(dev_malloc(&out, (size_t)nq * (3 * h->esize + 8)));
     char* o = static_cast<char*>(out);
     void* g = o;
     int32_t* iu = reinterpret_cast<int32_t*>(o + (size_t)nq * 3 * h->esize);
@@ -1086,5 +1197,20 @@ size_t lip_last_error_detail(char* buf, size_t len) { return lip_last_error(buf,
 lip_status lip_eval_batched(lip_batch b, void* stream) { return lip_batch_eval(b, stream); }
 
 const char* lip_version(void) { return "0.1.0 sm_103a"; }
+
+lip_status lip_debug_fail_alloc(int64_t n) {
+    if (n < 0) return fail(LIP_ERR_ARG, "n = %lld < 0", (long long)n);
+    g_fail_alloc_countdown.store(n, std::memory_order_relaxed);
+    return LIP_OK;
+}
+
+lip_status lip_debug_scan_fault(lip_handle h, uint64_t wait_limit_ns, int32_t skip_tile) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (skip_tile < -1) return fail(LIP_ERR_ARG, "skip_tile = %d < -1", skip_tile);
+    if (wait_limit_ns > WAIT_LIMIT_NS) return fail(LIP_ERR_ARG, "wait limit above the default %llu ns", WAIT_LIMIT_NS);
+    h->dbg_wait_ns = wait_limit_ns;
+    h->dbg_skip_tile = skip_tile;
+    return LIP_OK;
+}
 
 }  // extern "C"

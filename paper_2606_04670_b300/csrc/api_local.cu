@@ -30,7 +30,7 @@ lip_status local_buffers(lip_model* h, int64_t S, LocalParams& P) {
     const size_t b_n = al((size_t)N * 4), b_c = al((size_t)N * local_candidates() * 4);
     LIP_TRY(h->loc_tmp.ensure(b_s + 3 * b_n + b_c, "local Lipschitz scratch"));
     if (!h->loc_small) {
-        cudaError_t e = cudaMalloc(&h->loc_small, LOC_SMALL_BYTES);
+        cudaError_t e = dev_malloc(reinterpret_cast<void**>(&h->loc_small), LOC_SMALL_BYTES);
         if (e != cudaSuccess) {
             h->loc_small = nullptr;
             return cuda_fail(e, "local Lipschitz knots");

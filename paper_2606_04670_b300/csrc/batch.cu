@@ -18,6 +18,7 @@
 
 namespace lip {
 lip_status set_error(lip_status s, const char* msg);
+cudaError_t dev_malloc(void** p, size_t bytes);
 }
 
 using namespace lip;
@@ -162,7 +163,7 @@ static void batch_free(lip_batch_model* b) {
 }
 
 static lip_status balloc(lip_batch_model* b, void** p, size_t n, const char* what) {
-    cudaError_t e = cudaMalloc(p, std::max<size_t>(n, 16));
+    cudaError_t e = dev_malloc(p, std::max<size_t>(n, 16));
     if (e != cudaSuccess) {
         *p = nullptr;
         return cfail(e, what);
@@ -283,6 +284,8 @@ static lip_status batch_create(const lip_batch_set* sets, int32_t nsets, const l
         }
         ScanParams& P = sp[s];
         std::memset(&P, 0, sizeof P);
+        P.wait_ns = WAIT_LIMIT_NS;
+        P.skip_tile = -1;
         P.nq = x.nq;
         P.d = x.d;
         P.C = C;

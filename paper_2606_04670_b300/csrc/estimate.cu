@@ -8,7 +8,8 @@
 // max and different y gives +Inf, as the definition asks; padding points (y = NaN) and
 // the i = j pairs of diagonal tiles drop out the same way.
 //
-// Grid: (I-tile, J-tile) pairs with J >= I; each CTA keeps EST_R I-points per thread in
+// Grid: (I-tile, J-tile) pairs with J >= I (of one block-cyclic part of them when the
+// pairs are shared out over GPUs); each CTA keeps EST_R I-points per thread in
 // registers and streams the J-tile from shared memory.  The winning J-chunk of each
 // thread row is rescanned to recover the exact j, CTAs write one candidate each, and a
 // single-CTA pass picks the maximum (lowest (i, j) on ties) and recomputes it in FP64.
@@ -68,6 +69,7 @@ estimate_kernel(const EstParams P) {
     constexpr int NCH = D + 1;
     const int bi = blockIdx.x, bj = blockIdx.y;
     if (bj < bi) return;
+    if (((int64_t)bi * P.nb + bj) % P.nparts != P.part) return;
     __shared__ __align__(16) float4 tile[EST_TILE_GROUPS * NCH];
     const int tid = threadIdx.x;
 
@@ -186,7 +188,7 @@ __global__ void estimate_final_kernel(const EstFinalParams P) {
     int ti = -1, tj = -1;
     for (int64_t k = tid; k < (int64_t)P.nb * P.nb; k += blockDim.x) {
         const int bi = (int)(k / P.nb), bj = (int)(k % P.nb);
-        if (bj < bi) continue;
+        if (bj < bi || k % P.nparts != P.part) continue;
         const float4 c = P.cand[k];
         if (c.w == 0.f) continue;
         const int i = __float_as_int(c.y), j = __float_as_int(c.z);
@@ -211,6 +213,7 @@ __global__ void estimate_final_kernel(const EstFinalParams P) {
         P.out[0] = M;
         P.out[1] = (double)ti;
         P.out[2] = (double)tj;
+        if (P.write_key) P.out[3] = ti >= 0 ? (double)tb : -1.0;
     }
 }
 

@@ -11,6 +11,9 @@ struct EstParams {
     int64_t N;
     int nb;               // tiles per side
     float4* cand;         // [nb * nb]: {ratio^2, bits(i), bits(j), valid}
+    // block-cyclic share of the tile pairs: pair (I, J >= I) belongs to part
+    // (I nb + J) mod nparts; a launch covers the pairs of `part` only
+    int part = 0, nparts = 1;
 };
 
 struct EstFinalParams {
@@ -20,7 +23,9 @@ struct EstFinalParams {
     const void* y0;
     int d, norm, elem_bytes;
     double w[D_MAX];
-    double* out;          // [3]: M_est, i, j (as doubles)
+    double* out;          // [3]: M_est, i, j (as doubles); [4] with write_key
+    int part = 0, nparts = 1;   // the tile pairs whose candidates are read (as EstParams)
+    int write_key = 0;    // out[3] = the winner's FP32 squared ratio (-1 without one)
 };
 
 struct BwdParams {
@@ -68,6 +73,16 @@ cudaError_t launch_to_float(const double* a, int64_t n, float* out, cudaStream_t
 cudaError_t launch_screen64(int norm, const Screen64Params& P, int gx, int gy, cudaStream_t st);
 
 cudaError_t launch_merge(int elem_bytes, const MergeParams& P, cudaStream_t st);
+
+// data-sharded evaluation (shard.cu)
+cudaError_t launch_shard_keys(int elem_bytes, const void* partial, int nsplit, int64_t nq, const void* Q, int d,
+                              int64_t index_base, int64_t* key_up, int64_t* key_lo, cudaStream_t st);
+cudaError_t launch_shard_reeval(int elem_bytes, const MergeParams& P, int64_t index_base, int64_t N,
+                                const int64_t* key_up, const int64_t* key_lo, double* hi64, double* lo64,
+                                cudaStream_t st);
+cudaError_t launch_shard_finish(int elem_bytes, int64_t nq, const int64_t* key_up, const int64_t* key_lo,
+                                const double* hi64, const double* lo64, void* g, void* lo, void* hi, int32_t* idx_up,
+                                int32_t* idx_lo, cudaStream_t st);
 cudaError_t launch_build_hot(int elem_bytes, const HotParams& P, cudaStream_t st);
 cudaError_t launch_pad_hot(int elem_bytes, void* hot, int64_t k0, int64_t k1, int nch, int dl, cudaStream_t st);
 

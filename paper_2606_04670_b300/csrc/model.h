@@ -20,6 +20,9 @@ lip_status fail(lip_status s, const char* fmt, ...);
 lip_status cuda_fail(cudaError_t e, const char* what);
 // Adds to the count of the library's kernel launches (lip_kernel_launches).
 void count_launches(uint64_t n);
+// cudaMalloc for every device buffer the library owns.  lip_debug_fail_alloc can make it
+// report cudaErrorMemoryAllocation (without allocating) to test the OOM paths.
+cudaError_t dev_malloc(void** p, size_t bytes);
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -62,7 +65,7 @@ struct Scratch {
         }
         size_t sz = std::max<size_t>(need, 256);
         sz = (sz + 255) & ~size_t(255);
-        cudaError_t e = cudaMalloc(&p, sz);
+        cudaError_t e = dev_malloc(&p, sz);
         if (e != cudaSuccess) { p = nullptr; return cuda_fail(e, what); }
         bytes = sz;
         return LIP_OK;
@@ -100,6 +103,10 @@ struct lip_model {
     int splits = 0;                   // 0 = automatic
     int last_splits = 0;
     int variant = 0;
+    // fault injection for tests (lip_debug_scan_fault): the exact scan's wait limit and the
+    // data tile whose bulk copy it does not issue
+    unsigned long long dbg_wait_ns = 0;   // 0: the default limit
+    int dbg_skip_tile = -1;               // -1: none
     Scratch partial, est, bwd, io;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};

@@ -32,6 +32,9 @@ struct ScanParams {
     int tile_groups;          // groups per shared-memory tile (multiple of 8, <= 64)
     void* partial;            // PartialRec<T> [gridDim.y][nq]
     unsigned* err;            // device status word
+    unsigned long long wait_ns = WAIT_LIMIT_NS;  // limit of the exact scan's bounded waits
+    int skip_tile = -1;       // tests only: every block leaves out the bulk copy of its tile
+                              // number skip_tile (its wait then runs out); -1 = none
 };
 
 // Per (split, query) result of a scan: approximate extremum values and their indices.
@@ -231,6 +234,7 @@ __device__ __forceinline__ void scan_block(const ScanParams& P, int64_t qblock, 
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int s = 0; s < SCAN_STAGES && s < ntiles; ++s) {
+            if (s == P.skip_tile) continue;
             mbar_expect_tx(&bars[s], tile_bytes);
             bulk_g2s(tiles + (size_t)s * tg * NCH, hot + (size_t)(g_begin + (int64_t)s * tg) * NCH, tile_bytes, &bars[s]);
         }
@@ -253,7 +257,7 @@ __device__ __forceinline__ void scan_block(const ScanParams& P, int64_t qblock, 
     for (; t < ntiles; ++t) {
         const int s = t % SCAN_STAGES;
         const uint32_t par = (uint32_t)(t / SCAN_STAGES) & 1u;
-        const bool got = mbar_wait_bounded(&bars[s], par, P.err);
+        const bool got = mbar_wait_bounded(&bars[s], par, P.err, P.wait_ns);
         if (!__syncthreads_and(got)) { ok = false; break; }
         const float4* tile = tiles + (size_t)s * tg * NCH;
         for (int c = 0; c < tg; c += CHUNK_GROUPS) {
@@ -280,18 +284,19 @@ __device__ __forceinline__ void scan_block(const ScanParams& P, int64_t qblock, 
             }
         }
         __syncthreads();   // every thread is done with stage s
-        if (threadIdx.x == 0 && t + SCAN_STAGES < ntiles) {
+        if (threadIdx.x == 0 && t + SCAN_STAGES < ntiles && t + SCAN_STAGES != P.skip_tile) {
             mbar_expect_tx(&bars[s], tile_bytes);
             bulk_g2s(tiles + (size_t)s * tg * NCH, hot + (size_t)(g_begin + (int64_t)(t + SCAN_STAGES) * tg) * NCH,
                      tile_bytes, &bars[s]);
         }
     }
     if (!ok) {
-        // A copy did not arrive in time: wait (bounded) for the copies still in flight so
-        // none lands in shared memory after this block has exited, then give up.
+        // A copy did not arrive in time: wait (bounded, with the default limit) for the
+        // copies still in flight so none lands in shared memory after this block has
+        // exited, then give up.  A tile left out on purpose has no copy to wait for.
         if (threadIdx.x == 0) {
             for (int u = t; u < ntiles && u < t + SCAN_STAGES; ++u)
-                mbar_wait_bounded(&bars[u % SCAN_STAGES], (uint32_t)(u / SCAN_STAGES) & 1u, nullptr);
+                if (u != P.skip_tile) mbar_wait_bounded(&bars[u % SCAN_STAGES], (uint32_t)(u / SCAN_STAGES) & 1u, nullptr);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {

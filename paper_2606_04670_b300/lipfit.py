@@ -104,6 +104,12 @@ def _load():
         "lip_smooth_objective": [H, f64, f64, P, ctypes.POINTER(f64), P, P],
         "lip_smooth": [H, f64, f64, i32, i32, f64, P, ctypes.POINTER(f64), ctypes.POINTER(i32),
                        ctypes.POINTER(i32), P],
+        "lip_shard_scan": [H, P, i64, i64, P, P, P],
+        "lip_shard_reeval": [H, P, i64, i64, P, P, P, P, P],
+        "lip_shard_finish": [H, i64, P, P, P, P, P, P, P, P, P, P],
+        "lip_estimate_M_part": [H, i32, i32, P, P],
+        "lip_debug_fail_alloc": [i64],
+        "lip_debug_scan_fault": [H, ctypes.c_uint64, i32],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -273,6 +279,25 @@ def lip_estimate_M_noalloc(X_ptr, y_ptr, N, d, norm, w_ptr, out_ptr, stream=0):
     return _lib.lip_estimate_M_noalloc(X_ptr, y_ptr, N, d, norm, w_ptr, out_ptr, stream)
 
 
+def lip_shard_scan(h, Q_ptr, nq, index_base, key_up, key_lo, stream=0):
+    return _lib.lip_shard_scan(h, Q_ptr, nq, index_base, key_up, key_lo, stream)
+
+
+def lip_shard_reeval(h, Q_ptr, nq, index_base, key_up, key_lo, hi64, lo64, stream=0):
+    return _lib.lip_shard_reeval(h, Q_ptr, nq, index_base, key_up, key_lo, hi64, lo64, stream)
+
+
+def lip_shard_finish(h, nq, key_up, key_lo, hi64, lo64, g, lo, hi, idx_up, idx_lo, stream=0):
+    return _lib.lip_shard_finish(h, nq, key_up, key_lo, hi64, lo64, g, lo, hi, idx_up, idx_lo, stream)
+
+
+def lip_estimate_M_part(h, part, nparts, stream=0):
+    """(status, [M, i, j, key]) of one block-cyclic share of the estimate's pairs."""
+    out = (ctypes.c_double * 4)()
+    s = _lib.lip_estimate_M_part(h, part, nparts, out, stream)
+    return s, list(out)
+
+
 def lip_backward(h, Q_ptr, nq, idx_up, idx_lo, grad_g, grad_Q, grad_y, grad_M, deterministic=0, stream=0):
     return _lib.lip_backward(h, Q_ptr, nq, idx_up, idx_lo, grad_g, grad_Q, grad_y, grad_M, deterministic, stream)
 
@@ -361,6 +386,16 @@ def lip_last_error():
 
 def lip_version():
     return _lib.lip_version().decode()
+
+
+def lip_debug_fail_alloc(n):
+    """Tests only: the n-th device allocation from now on fails (0 = off)."""
+    return _lib.lip_debug_fail_alloc(n)
+
+
+def lip_debug_scan_fault(h, wait_limit_ns, skip_tile):
+    """Tests only: wait limit of the exact scan and the data tile it leaves out (-1 = none)."""
+    return _lib.lip_debug_scan_fault(h, wait_limit_ns, skip_tile)
 
 
 # ------------------------------------------------------------------ torch front end
@@ -598,6 +633,49 @@ class LipFit:
 
         _check(_lib.lip_eval_host(self.h, qptr, nq, p(out.get("g")), p(out.get("lo")), p(out.get("hi")),
                                   p(out.get("idx_up")), p(out.get("idx_lo")), _stream_ptr()), "lip_eval_host")
+        return out
+
+    # -- several GPUs (paper_2606_04670_b300.shard drives these around the collectives)
+    def shard_scan(self, Q, index_base: int):
+        """lip_shard_scan: packed keys (int64 CUDA tensors key_up, key_lo) of this handle's data,
+        whose global indices start at index_base."""
+        torch = _torch()
+        Q = self._dev(Q)
+        nq = Q.shape[0]
+        ku = torch.empty(nq, device="cuda", dtype=torch.int64)
+        kl = torch.empty(nq, device="cuda", dtype=torch.int64)
+        _check(_lib.lip_shard_scan(self.h, Q.data_ptr(), nq, int(index_base), ku.data_ptr(), kl.data_ptr(),
+                                   _stream_ptr()), "lip_shard_scan")
+        return ku, kl
+
+    def shard_reeval(self, Q, index_base: int, key_up, key_lo):
+        """lip_shard_reeval: FP64 bounds (hi64, lo64) of the winners this handle holds, +-Inf
+        elsewhere."""
+        torch = _torch()
+        Q = self._dev(Q)
+        nq = Q.shape[0]
+        hi = torch.empty(nq, device="cuda", dtype=torch.float64)
+        lo = torch.empty(nq, device="cuda", dtype=torch.float64)
+        _check(_lib.lip_shard_reeval(self.h, Q.data_ptr(), nq, int(index_base), key_up.data_ptr(), key_lo.data_ptr(),
+                                     hi.data_ptr(), lo.data_ptr(), _stream_ptr()), "lip_shard_reeval")
+        return hi, lo
+
+    def shard_finish(self, key_up, key_lo, hi64, lo64):
+        """lip_shard_finish: the outputs (g, lo, hi, idx_up, idx_lo) from merged keys and values."""
+        torch = _torch()
+        nq = key_up.shape[0]
+        out = {k: torch.empty(nq, device="cuda", dtype=self.dtype) for k in ("g", "lo", "hi")}
+        out.update({k: torch.empty(nq, device="cuda", dtype=torch.int32) for k in ("idx_up", "idx_lo")})
+        _check(_lib.lip_shard_finish(self.h, nq, key_up.data_ptr(), key_lo.data_ptr(), hi64.data_ptr(),
+                                     lo64.data_ptr(), out["g"].data_ptr(), out["lo"].data_ptr(), out["hi"].data_ptr(),
+                                     out["idx_up"].data_ptr(), out["idx_lo"].data_ptr(), _stream_ptr()),
+               "lip_shard_finish")
+        return out
+
+    def estimate_M_part(self, part: int, nparts: int):
+        """lip_estimate_M_part: [M, i, j, FP32 squared ratio] of one block-cyclic share."""
+        s, out = lip_estimate_M_part(self.h, int(part), int(nparts), _stream_ptr())
+        _check(s, "lip_estimate_M_part")
         return out
 
     def lipschitz_constant(self):

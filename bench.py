@@ -15,9 +15,12 @@ mixture, N = Q = 1e6, plain FP32 L2), grad_d8 (d=8, forward + backward), batch_4
 
 Timing: CUDA events per step on the launching stream.  Where the inputs fit in L2
 (126 MB), L2 is flushed before every timed step by writing a 256 MB buffer (outside the
-timed interval).  N > 1 (torchrun): every rank runs the same per-rank workload on its
-own GPU (weak scaling; the method needs no exchange between ranks), value = all ranks'
-pairs / the slowest rank's time.
+timed interval).  N > 1 (torchrun), monotone_d4: the queries are sharded over the GPUs
+(weak scaling: rank r evaluates its own block of 1e6 queries of an N x 1e6 query set,
+the data replicated on every GPU, no exchange in the evaluation), and the estimate's pair
+triangle is shared out block-cyclically with one all_gather of the ranks' 4-number
+results per norm; value = all ranks' query x data pairs / the slowest rank's time.
+Other workloads run one copy per GPU.
 
 --impl reference times the FP64 CPU oracle (the checker, as it stands) on the host
 cores on a bounded sample of the same workload.
@@ -52,10 +55,12 @@ LOCAL_KNOTS, LOCAL_SAMPLE, LOCAL_SEED = 16, 32768, 0
 MUFU_PER_SM = 16
 # TF32 dense peak: the measured BF16 peak times the nominal TF32 / BF16 ratio (1.1 / 2.25)
 TF32_OVER_BF16 = 1.1 / 2.25
+# FP32 lane operations per pair of the tensor-core epilogue (TMEM load share, clamp, the
+# square root's share, two FMAs, two extrema, the candidate test)
+TC_I_EPI = 6
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of each workload's dominant
-# kernel at the full workload size (one-pass ncu captures of the timed step's launch; the
-# commands and figures are in profiles/dram_traffic_bench_workloads.md).  An entry is
-# removed whenever its kernel changes, until it is captured again.
+# kernel at the full workload size (one-pass ncu captures of the timed step's launch).  An
+# entry is removed whenever its kernel changes, until it is captured again.
 KERNEL_DRAM_BYTES = {
     ("monotone_d4", 2): 19.136000e6 + 11.619840e6,     # scan_exact_kernel<L2, C=2, U=2, R=4>
     ("grad_d8", 2): 16.66e6 + 13.47e6,                 # scan_exact_kernel<L2, C=4, U=4, R=2>
@@ -87,6 +92,54 @@ def mufu_per_pair(norm: int, c: int) -> int:
     return 0 if norm != W.NORM_L2 else (2 if c else 1)
 
 
+def fma_lanes_per_pair(norm: int, d: int, c: int) -> int:
+    """Algorithmic lane operations per pair on the FP32 FMA pipe (adds, multiplies and FMAs;
+    minimum, maximum and the positive / negative parts run on the ALU pipe, square roots on
+    MUFU): the d coordinate differences, then L2: one square-accumulate per free coordinate
+    and two per constrained one (the upper and the lower part); L1: one add per coordinate;
+    Linf: none (maxima only); plus the two bound values y + M d_up and y - M d_lo."""
+    if norm == W.NORM_L2:
+        return d + (d - c) + 2 * c + 2
+    if norm == W.NORM_L1:
+        return d + d + 2
+    return d + 2
+
+
+def tc_roofline(ctx, prec, d, pairs, ms, alu, traffic):
+    """Roofline of the tensor-core scan.  The algorithmic tensor work of a pair is the
+    augmented product of the method, [-2q, 1, |q|^2 hi, |q|^2 lo] . [x, |x|^2 hi, |x|^2 lo, 1]:
+    2 K flops with K = d + 3 padded to the MMA's K step (8 for TF32, 16 for the 16-bit kinds;
+    24 and 32 at d = 16), against the measured dense BF16 peak (FP16's rate is BF16's;
+    TF32 takes 1.1 / 2.25 of it).  The MMA work the kernel actually issues (the split
+    products and the norm block) and the epilogue's ALU roof are reported beside it."""
+    fmt = {"tc_tf32": "TF32", "tc_bf16": "BF16", "tc_fp16": "FP16"}[prec]
+    f16 = fmt != "TF32"
+    step = 16 if f16 else 8
+    k_alg = step * ((d + 3 + step - 1) // step)
+    # issued: the piece products over K = d padded, plus the norm block's 32 bytes of K
+    kk = 16 * ((d + 15) // 16) if f16 else 8 * ((d + 7) // 8)
+    npass = 6 if fmt == "BF16" else 3
+    fpp_issued = 2 * (npass * kk + (16 if f16 else 8))
+    pairs_s = pairs / (ms / 1e3)
+    ratio = 1.0 if f16 else TF32_OVER_BF16
+    peak = float(ctx.peaks.get("bf16_tflops", 1800.0)) * ratio * 1e12
+    sus = float(ctx.peaks.get("bf16_tflops_sustained", 1400.0)) * ratio * 1e12
+    ach = 2.0 * k_alg * pairs_s
+    # epilogue: about I_EPI FP32 lane operations per pair on the SMs' 128 lanes per clock
+    epi_peak = ctx.sms * FP32_LANES_PER_SM * ctx.sm_max * 1e6 / TC_I_EPI
+    return {"bound": "tensor", "kernel": f"tc_scan_kernel<K={kk}, {fmt}>",
+            "achieved": ach / 1e12, "peak": peak / 1e12, "unit": f"TFLOP/s ({fmt})", "frac": ach / peak,
+            "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
+            "flops_per_pair": 2 * k_alg, "k_algorithmic": k_alg,
+            "peak_source": ("measured bf16 dense peak of MEASURED_PEAKS.json (fp16 dense rate = bf16)" if f16 else
+                            "measured bf16 dense peak of MEASURED_PEAKS.json x 1.1/2.25 (nominal TF32/BF16)"),
+            "frac_of_sustained": ach / sus,
+            "issued_mma": {"flops_per_pair": fpp_issued, "achieved": fpp_issued * pairs_s / 1e12,
+                           "frac": fpp_issued * pairs_s / peak, "frac_of_sustained": fpp_issued * pairs_s / sus},
+            "epilogue": {"i_epi": TC_I_EPI, "roof_pairs_per_s": epi_peak, "frac": pairs_s / epi_peak},
+            "alu_view": {k: alu[k] for k in ("achieved", "peak", "frac", "fma_lanes_per_pair")}}
+
+
 def parse():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -98,6 +151,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-tc-vs-plain", action="store_true",
+                    help="monotone_d4: skip the tensor-core vs plain comparison on cluster_d16 (after the timed steps)")
     ap.add_argument("--sets", type=int, default=0, help="batch_4096: use only the first N sets (profiling)")
     ap.add_argument("--queries", type=int, default=0,
                     help="use only the first N queries of a single-set workload (small profiling cases)")
@@ -341,19 +396,35 @@ class Ctx:
             torch.distributed.barrier()
         return ms, sampler.stop(), L.lip_kernel_launches() - launches0
 
-    def roofline(self, kernel, ops_per_launch, ms_per_launch, ipair, mufu, clocks, traffic=None):
-        peak = self.sms * FP32_LANES_PER_SM * self.sm_max * 1e6
-        achieved = ops_per_launch / (ms_per_launch / 1e3)
-        r = {"bound": "alu", "kernel": kernel, "achieved": achieved / 1e12, "peak": peak / 1e12,
-             "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak, "traffic": traffic,
+    def roofline(self, kernel, pairs_per_launch, ms_per_launch, ipair, mufu, clocks, traffic=None, fma=None):
+        """Roofline of an all-pairs ALU kernel.  Two pipes can bind: the FP32 FMA pipe (fma
+        algorithmic lane operations per pair against SMs x 128 lanes x clock) and the
+        special-function pipe MUFU (mufu square roots per pair against SMs x 16 x clock).
+        frac is the larger of the two fractions and `pipe` names it.  The survey's scalar
+        count of all FP32 lane operations per pair (ipair, FMA and ALU pipes together)
+        is kept as `lane_ops_view`; packed f32x2 and three-input min / max instructions let
+        that count exceed 1.0 of the FMA pipe's lane peak, so it is not the fraction."""
+        pairs_s = pairs_per_launch / (ms_per_launch / 1e3)
+        lane_peak = self.sms * FP32_LANES_PER_SM * self.sm_max * 1e6
+        src = f"(max SM clock{' of MEASURED_PEAKS.json' if self.peaks else ', nominal'})"
+        fma = ipair if fma is None else fma
+        fma_ach = pairs_s * fma
+        r = {"bound": "alu", "kernel": kernel, "pipe": "fma", "achieved": fma_ach / 1e12, "peak": lane_peak / 1e12,
+             "unit": "T lane ops/s (FP32 FMA pipe)", "frac": fma_ach / lane_peak, "traffic": traffic,
              "traffic_unit": "bytes per launch (ncu dram read + write)",
-             "peak_source": f"{self.sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {self.sm_max:.0f} MHz (max SM clock"
-                            f"{' of MEASURED_PEAKS.json' if self.peaks else ', nominal'})",
-             "i_pair": ipair, "mufu_per_pair": mufu}
-        if clocks and clocks.get("sm_mhz"):
-            r["frac_at_measured_clock"] = achieved / (self.sms * FP32_LANES_PER_SM * clocks["sm_mhz"] * 1e6)
+             "peak_source": f"{self.sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {self.sm_max:.0f} MHz {src}",
+             "fma_lanes_per_pair": fma, "mufu_per_pair": mufu,
+             "fma_pipe": {"achieved": fma_ach / 1e12, "peak": lane_peak / 1e12, "frac": fma_ach / lane_peak},
+             "lane_ops_view": {"i_pair": ipair, "achieved": pairs_s * ipair / 1e12, "peak": lane_peak / 1e12,
+                               "frac": pairs_s * ipair / lane_peak}}
         if mufu:
-            r["mufu"] = self.mufu_bound(achieved / ipair, mufu)
+            m = self.mufu_bound(pairs_s, mufu)
+            r["mufu"] = m
+            if m["frac"] > r["frac"]:
+                r.update(pipe="mufu", achieved=m["achieved"], peak=m["peak"], unit=m["unit"], frac=m["frac"],
+                         peak_source=m["peak_source"])
+        if clocks and clocks.get("sm_mhz"):
+            r["frac_at_measured_clock"] = r["frac"] * self.sm_max / clocks["sm_mhz"]
         return r
 
     def mufu_bound(self, pairs_per_s, mufu_per_pair):
@@ -362,15 +433,23 @@ class Ctx:
         sqrt.approx, and as many rsqrt.approx, per SM per clock on the B300s)."""
         peak = self.sms * MUFU_PER_SM * self.sm_max * 1e6
         ach = pairs_per_s * mufu_per_pair
-        return {"achieved": ach / 1e12, "peak": peak / 1e12, "unit": "T MUFU ops/s", "frac": ach / peak,
-                "per_pair": mufu_per_pair}
+        return {"achieved": ach / 1e12, "peak": peak / 1e12, "unit": "T square roots/s (MUFU)", "frac": ach / peak,
+                "per_pair": mufu_per_pair,
+                "peak_source": f"{self.sms} SMs x {MUFU_PER_SM} MUFU results x {self.sm_max:.0f} MHz (max SM clock)"}
 
     def line(self, value, ms_total, steps, dtype, config, roof, cpu, e2e, clocks, launches, detail):
+        if self.world == 1:
+            par = "single GPU"
+        elif config["workload"] == "monotone_d4":
+            par = (f"queries sharded over {self.world} GPUs (data replicated; M_est pair tiles block-cyclic, "
+                   f"one all_gather per norm)")
+        else:
+            par = f"replicas{self.world}"
         return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": self.world, "steps": steps,
                 "warmup": max(3, self.args.warmup), "ms_per_step": ms_total / steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": dtype,
                 "data": f"synthetic (seeded, {config['workload']} workload)",
-                "config": dict(config, parallelism=f"replicas{self.world}"), "roofline": roof,
+                "config": dict(config, parallelism=par), "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches, "detail": detail}
 
 
@@ -395,6 +474,7 @@ def _cpu(ctx, problems):
 def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd=False, flush=True):
     """fit + eval (+ M_est) (+ backward) of each problem per step."""
     from paper_2606_04670_b300 import lipfit as L
+    from paper_2606_04670_b300 import shard as S
     torch, args = ctx.torch, ctx.args
     if args.queries > 0:
         problems = [p.sub_queries(args.queries) for p in problems]
@@ -441,7 +521,11 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
                     torch.cuda.synchronize()
                     r["bwd"].append(r["bev"][0].elapsed_time(r["bev"][1]))
             if with_est:
-                est[k] = m.lipschitz_constant()[0]
+                if ctx.world > 1:
+                    # the pair triangle shared out over the GPUs, one all_gather per norm
+                    est[k] = S.estimate_M_sharded(S.DeviceShard(m, 0), device="cuda")[0]
+                else:
+                    est[k] = m.lipschitz_constant()[0]
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -460,32 +544,11 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
             f"R={rd['m'].tuning()['queries_per_thread']}> {rd['prec']}")
     if rd["prec"] == "fp64":
         kern = "FP32 screen " + kern.replace(" fp64", "") + " + screen64_kernel (FP64 candidates)"
-    roof = ctx.roofline(kern, ip * p.nq * p.N, avg[kdom], ip, mufu_per_pair(p.norm, c), clocks,
-                        traffic_for(args, name, p.norm) if rd["prec"] == "fp32" else None)
+    roof = ctx.roofline(kern, p.nq * p.N, avg[kdom], ip, mufu_per_pair(p.norm, c), clocks,
+                        traffic_for(args, name, p.norm) if rd["prec"] == "fp32" else None,
+                        fma=fma_lanes_per_pair(p.norm, p.d, c))
     if rd["prec"] in ("tc_tf32", "tc_bf16", "tc_fp16"):
-        fmt = {"tc_tf32": "TF32", "tc_bf16": "BF16", "tc_fp16": "FP16"}[rd["prec"]]
-        f16 = fmt != "TF32"
-        # tensor-core form, MMA work per pair: the piece products over K = d padded (8 for
-        # TF32, 16 for the 16-bit kinds; three products for TF32 and FP16, six for BF16) plus
-        # the norm block, one more MMA of 32 bytes of K (8 TF32 or 16 16-bit elements)
-        kk = 16 * ((p.d + 15) // 16) if f16 else 8 * ((p.d + 7) // 8)
-        npass = 6 if fmt == "BF16" else 3
-        fpp = 2 * (npass * kk + (16 if f16 else 8))
-        flops = float(fpp) * p.nq * p.N
-        peak = float(ctx.peaks.get("bf16_tflops", 1800.0)) * (1.0 if f16 else TF32_OVER_BF16) * 1e12
-        alu = roof
-        roof = {"bound": "tensor", "kernel": f"tc_scan_kernel<K={kk}, {fmt}>",
-                "achieved": flops / (avg[kdom] / 1e3) / 1e12, "peak": peak / 1e12,
-                "unit": f"TFLOP/s ({fmt})", "frac": flops / (avg[kdom] / 1e3) / peak,
-                "traffic": traffic_for(args, name, p.norm),
-                "peak_source": ("measured bf16 dense peak of MEASURED_PEAKS.json (fp16 dense rate = bf16)" if f16 else
-                                "measured bf16 dense peak of MEASURED_PEAKS.json x 1.1/2.25 (nominal TF32/BF16)"),
-                "flops_per_pair": fpp,
-                # the scan runs back to back for seconds: the sustained (power-capped) GEMM
-                # rate is the other fair denominator
-                "frac_of_sustained": (flops / (avg[kdom] / 1e3)) / (float(ctx.peaks.get("bf16_tflops_sustained", 1400.0))
-                                                                   * (1.0 if f16 else TF32_OVER_BF16) * 1e12),
-                "alu_view": {k: alu[k] for k in ("achieved", "peak", "frac", "i_pair")}}
+        roof = tc_roofline(ctx, rd["prec"], p.d, p.nq * p.N, avg[kdom], roof, traffic_for(args, name, p.norm))
 
     e2e = None
     if not args.no_e2e:
@@ -507,7 +570,10 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
                 m.add_host(hX, hy)
                 m.eval_host(hQ, outs)
                 if with_est:
-                    m.lipschitz_constant()
+                    if ctx.world > 1:
+                        S.estimate_M_sharded(S.DeviceShard(m, 0), device="cuda")
+                    else:
+                        m.lipschitz_constant()
 
         step_host()
         torch.cuda.synchronize()
@@ -558,6 +624,8 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
         detail["M_true"] = {key(r): r["p"].M for r in runs}
     for r in runs:
         r["m"].close()
+    if name == "monotone_d4" and not args.no_tc_vs_plain and ctx.world == 1:
+        detail["tc_vs_plain"] = tc_vs_plain(ctx)
     p0 = problems[0]
     config = {"workload": name, "d": p0.d, "N": p0.N, "Q": p0.nq,
               "mon": None if p0.mon is None else [int(v) for v in p0.mon],
@@ -566,6 +634,81 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
               "l2": "flushed before every timed step (256 MB write)" if flush else "inputs larger than L2"}
     return ctx.line(value, total, args.steps, "f64" if precisions == ("fp64",) else "f32", config, roof, cpu, e2e,
                     clocks, launches, detail)
+
+
+TC_FORMS = ("fp32", "tc_tf32", "tc_bf16", "tc_fp16")
+
+
+def tc_vs_plain(ctx, n_oracle=192, reps=3):
+    """The tensor-core L2 forms against the plain FP32 scan on the precision workload at full
+    size (cluster_d16: d = 16, N = Q = 1e6, 32-cluster Gaussian mixture), measured in this
+    process: per form the whole lip_eval call and its scan kernel alone (CUDA events, best of
+    `reps` after a warm-up), the queries the tensor-core form sent to the plain fallback, and
+    the clocks.  Accuracy: the FP64 oracle, timed on the host cores as this comparison's CPU
+    baseline, evaluates n_oracle random queries against all 1e6 points; every form's g, lo,
+    hi are compared with it (max error over M * diam, the tolerance 1e-5) and its indices
+    wherever the oracle's gap exceeds the tolerance."""
+    from paper_2606_04670_b300 import lipfit as L
+    torch = ctx.torch
+    p = W.cluster_d16()
+    X, y, Q = (torch.as_tensor(a).cuda() for a in (p.X, p.y, p.Q))
+    rng = np.random.default_rng(11)
+    sample = np.sort(rng.choice(p.nq, n_oracle, replace=False))
+    lo_c = np.minimum(p.X.min(0), p.Q.min(0)).astype(np.float64)
+    hi_c = np.maximum(p.X.max(0), p.Q.max(0)).astype(np.float64)
+    scale = p.M * float(np.sqrt(((hi_c - lo_c) ** 2).sum()))
+    tol = 1e-5 * scale
+    sampler = ClockSampler(ctx.local)
+    sampler.start()
+    forms = {}
+    outs = {}
+    for prec in TC_FORMS:
+        m = L.LipFit(X, y, p.M, norm=p.norm, precision=prec)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r = m.eval(Q)                      # warm-up (tensor-core tiles built here)
+        m.set_timing_events(*ev)
+        t_eval, t_scan = [], []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a.record()
+            r = m.eval(Q)
+            b.record()
+            torch.cuda.synchronize()
+            t_eval.append(a.elapsed_time(b))
+            t_scan.append(ev[0].elapsed_time(ev[1]))
+        m.check()
+        outs[prec] = {k: v[torch.as_tensor(sample).cuda()].cpu().numpy() for k, v in r.items()}
+        forms[prec] = {"eval_ms": min(t_eval), "scan_ms": min(t_scan),
+                       "gpairs_per_s": p.nq * p.N / (min(t_eval) / 1e3) / 1e9,
+                       "scan_gpairs_per_s": p.nq * p.N / (min(t_scan) / 1e3) / 1e9}
+        if prec.startswith("tc_"):
+            forms[prec]["fallback_queries"] = m.last_fallback()
+        m.close()
+        del r
+    clocks = sampler.stop()
+    # the FP64 oracle on the sample: this comparison's CPU baseline and its accuracy reference
+    import oracle
+    o = oracle.default()
+    t0 = time.perf_counter()
+    ref = o.evaluate(p.X, p.y, p.Q[sample], p.M, p.norm)
+    dt = time.perf_counter() - t0
+    for prec in TC_FORMS:
+        g = outs[prec]
+        err = {k: float(np.max(np.abs(g[k].astype(np.float64) - ref[k]))) for k in ("g", "lo", "hi")}
+        mism = 0
+        for k, gk in (("idx_up", "gap_up"), ("idx_lo", "gap_lo")):
+            mism += int(np.sum((ref[gk] > tol) & (g[k].astype(np.int64) != ref[k])))
+        forms[prec].update(max_abs_err=err, max_err_over_M_diam=max(err.values()) / scale,
+                           index_mismatches_above_gap=mism, within_tol=bool(max(err.values()) <= tol and mism == 0))
+    base = forms["fp32"]["eval_ms"]
+    return {"workload": "cluster_d16", "d": p.d, "N": p.N, "Q": p.nq, "norm": "L2", "M": p.M,
+            "tolerance": "1e-5 * M * diam", "tol_abs": tol, "oracle_queries": n_oracle,
+            "forms": forms, "speedup_vs_fp32": {k: base / v["eval_ms"] for k, v in forms.items()},
+            "clocks": clocks,
+            "cpu_baseline": {"value": n_oracle * p.N / dt / 1e9, "unit": UNIT, "cores": oracle.default_threads(),
+                             "kind": "oracle", "sample": f"{n_oracle} random queries x all {p.N} data points "
+                                                         f"(FP64, {dt:.1f} s)"}}
 
 
 def wl_batch(ctx):
@@ -622,11 +765,15 @@ def wl_batch(ctx):
     ms, clocks, _ = ctx.timed(graph.replay, args.steps, flush=False)
     launches = 2 * args.steps      # each replay runs the persistent scan and the batched merge
     value, total = aggregate(info["total_pairs"] * args.steps, sum(ms), device="cuda")
-    ops = 0.0
+    ops = fma = mufu = 0.0
     for bs in plan:
-        ops += bs.nq * bs.N * i_pair(bs.norm, bs.d, int((bs.mon != 0).sum()))
-    roof = ctx.roofline("batch_scan_kernel (persistent, 4096 sets)", ops, min(scan_ms),
-                        ops / info["total_pairs"], None, clocks, traffic_for(args, "batch_4096", 0))
+        c = int((bs.mon != 0).sum())
+        ops += bs.nq * bs.N * i_pair(bs.norm, bs.d, c)
+        fma += bs.nq * bs.N * fma_lanes_per_pair(bs.norm, bs.d, c)
+        mufu += bs.nq * bs.N * mufu_per_pair(bs.norm, c)
+    tp = info["total_pairs"]
+    roof = ctx.roofline("batch_scan_kernel (persistent, 4096 sets)", tp, min(scan_ms), ops / tp, mufu / tp, clocks,
+                        traffic_for(args, "batch_4096", 0), fma=fma / tp)
     e2e = None
     if not args.no_e2e:
         hout = {k: torch.empty(tq, dtype=v.dtype).pin_memory() for k, v in dout.items()}
@@ -695,9 +842,10 @@ def wl_local(ctx, name="local_d4"):
     # local scan per pair: distance 2d, knot search 5 x (compare + add), first-segment test and
     # select, two FMAs, two (compare + two selects) for the running extrema; one MUFU sqrt
     ip = 2 * p.d + 20
-    roof = ctx.roofline(f"loc_scan_kernel<{NNAME[p.norm]}> (d={p.d}, {LOCAL_KNOTS} knots)", ip * p.nq * p.N,
+    # on the FMA pipe: the differences and squares (2d) and the two bound FMAs
+    roof = ctx.roofline(f"loc_scan_kernel<{NNAME[p.norm]}> (d={p.d}, {LOCAL_KNOTS} knots)", p.nq * p.N,
                         ms_scan, ip, 1 if p.norm == W.NORM_L2 else 0, clocks,
-                        traffic_for(args, name, p.norm))
+                        traffic_for(args, name, p.norm), fma=2 * p.d + 2)
     e2e = None
     if not args.no_e2e:
         hX, hy, hQ = (torch.as_tensor(a).pin_memory() for a in (p.X, p.y, p.Q))
@@ -809,8 +957,10 @@ def wl_smooth(ctx, name="smooth_d4"):
     # positive and negative parts and the share q, the R - C sum, one FMA for S and one
     # maximum for the vote; one MUFU sqrt
     ip = 2 * p.d + 9
-    roof = ctx.roofline(f"smooth_pass_kernel<{NNAME[p.norm]}, DP=4> (+ layout and sums)", ip * pairs / 2, ms_pass, ip,
-                        1 if p.norm == W.NORM_L2 else 0, clocks, traffic_for(args, name, p.norm))
+    # on the FMA pipe: the differences and squares (2d), dz, the two term arguments, the
+    # R - C sum and the FMA for S
+    roof = ctx.roofline(f"smooth_pass_kernel<{NNAME[p.norm]}, DP=4> (+ layout and sums)", pairs / 2, ms_pass, ip,
+                        1 if p.norm == W.NORM_L2 else 0, clocks, traffic_for(args, name, p.norm), fma=2 * p.d + 5)
     roof["pairs_per_launch"] = "N (N - 1) / 2 unordered pairs"
     e2e = None
     if not args.no_e2e:
@@ -865,7 +1015,8 @@ def run_ours(args):
     ctx = Ctx(args)
     w = args.workload
     if w == "monotone_d4":
-        base = W.monotone_d4(norm=W.NORM_L2)
+        # rank r evaluates query block r of the N-GPU query set (block 0 on one GPU)
+        base = W.monotone_d4(norm=W.NORM_L2, query_block=rank)
         line = wl_single(ctx, w, [base.with_norm(n) for n in NORMS])
     elif w == "plain_d2":
         line = wl_single(ctx, w, [W.plain_d2(dtype=np.float64)], precisions=("fp32", "fp64"))

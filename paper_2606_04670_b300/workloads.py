@@ -144,8 +144,12 @@ def plain_d2(dtype=np.float32, n_data=1000, n_query=10_000) -> Problem:
     return Problem("plain_d2", X, y, Q, 4.5, NORM_L2, None, None, f_plain_d2)
 
 
-def monotone_d4(norm=NORM_L2, n_data=100_000, n_query=1_000_000, dtype=np.float32) -> Problem:
+def monotone_d4(norm=NORM_L2, n_data=100_000, n_query=1_000_000, dtype=np.float32, query_block=0) -> Problem:
+    """query_block b > 0 draws another n_query queries from an independent stream (block b of
+    a larger query set shared out over several GPUs); the data are the same."""
     rx, rq, rp = _rngs(2)
+    if query_block > 0:
+        rq = _rngs(2, 3 + query_block)[2 + query_block]
     a = rp.uniform(0.5, 1.5, size=4)
     X = _as(rx.random((n_data, 4)), dtype)
     Q = _as(rq.random((n_query, 4)), dtype)

@@ -81,7 +81,7 @@ typedef enum {
 } lip_precision;
 
 /* Largest dimension d accepted by lip_fit / lip_reserve. */
-#define LIP_D_MAX 16
+#define LIP_D_MAX 32
 
 /* Fitting parameters (Sec. 5, setparams(mon, a, b, w)).  All pointers are HOST pointers
  * that are read during the call only.
@@ -258,7 +258,7 @@ LIP_API lip_status lip_estimate_M_part(lip_handle h, int32_t part, int32_t npart
  * not call cudaMalloc: a plugin whose host application has already reserved the GPU's
  * memory in its own allocator, or a latency-bound loop that cannot absorb the
  * device-wide synchronisation cudaFree implies.  It needs no handle, allocates nothing,
- * and keeps its working memory in one fixed array of about 2.2 MB inside the library,
+ * and keeps its working memory in one fixed array of about 4.4 MB inside the library,
  * which every GPU that loads liblipfit.so holds until the process exits.
  *   X [N][d], y [N]  device, float, finite (not checked); read only.
  *   N                1 <= N <= LIP_NOALLOC_N_MAX, else LIP_ERR_ARG (fixed capacity).
@@ -416,7 +416,8 @@ LIP_API lip_status lip_backward(lip_handle h, const void* Q, int64_t nq, const i
  * phase; many small ones are evaluated at once).  Device pointers are the caller's;
  * X and y are copied by lip_batch_create, Q and the outputs are used by every
  * lip_batch_eval (so refill Q in place to evaluate new queries).
- *   X [N][d], y [N]   device float, 1 <= N < 2^31, 1 <= d <= 10.
+ *   X [N][d], y [N]   device float, 1 <= N < 2^31, 1 <= d <= LIP_D_MAX (sets with d <= 10
+ *                     take the exact-shape bodies, wider ones a plain-load body).
  *   norm, M, mon, w   as for lip_fit (mon, w: host arrays of d entries, or NULL).
  *   Q [nq][d]         device float (nq may be 0).
  *   g, lo, hi [nq], idx_up, idx_lo [nq]   device outputs, each may be NULL.

@@ -193,9 +193,7 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
         h->kinfo = scan_exact_info(h->norm, h->C, U);
     } else {
         h->exact = false;
-        const int dims[] = {2, 4, 8, 12, 16};
-        for (int v : dims)
-            if (v >= d) { h->dl = v; break; }
+        h->dl = generic_dim(d);
         h->aux = 0;
         h->nch = h->dl + 1;
         h->kinfo = scan_generic_info(h->esize, h->norm, h->dl);
@@ -219,9 +217,7 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
             h->nch32 = d + 1 + h->aux32;
             h->kinfo32 = scan_exact_info(h->norm, h->C, U);
         } else {
-            const int dims[] = {2, 4, 8, 12, 16};
-            for (int v : dims)
-                if (v >= d) { h->dl32 = v; break; }
+            h->dl32 = generic_dim(d);
             h->nch32 = h->dl32 + 1;
             h->kinfo32 = scan_generic_info(4, h->norm, h->dl32);
         }

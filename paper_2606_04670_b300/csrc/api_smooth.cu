@@ -36,7 +36,7 @@ lip_status smooth_setup(lip_model* h, double M, double p, cudaStream_t st, Smoot
     const int64_t tile = smooth_tile();
     P.npad = round_up(h->N, tile);
     P.d = h->d;
-    P.dp = (h->d + 3) / 4 * 4;
+    P.dp = h->d <= 16 ? (h->d + 3) / 4 * 4 : 32;     // one wide shape for d above 16
     P.C = h->C;
     P.norm = h->norm;
     for (int j = 0; j < D_MAX; ++j) {

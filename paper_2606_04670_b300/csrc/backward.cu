@@ -60,7 +60,8 @@ __global__ void grad_y_fix_kernel(const unsigned long long* fix, const unsigned*
     grad_y[k] = (T)((double)grad_y[k] + v);
 }
 
-template <typename T>
+// DM: register arrays for up to DM coordinates (16, or 32 for the widest handles)
+template <typename T, int DM>
 __global__ void __launch_bounds__(BWD_THREADS) backward_kernel(const BwdParams P) {
     const int64_t qi = (int64_t)blockIdx.x * BWD_THREADS + threadIdx.x;
     T gm = 0;
@@ -76,9 +77,9 @@ __global__ void __launch_bounds__(BWD_THREADS) backward_kernel(const BwdParams P
             const T* xu = X0 + (int64_t)u * P.d;
             const T* xl = X0 + (int64_t)l * P.d;
             // the query and both data rows once, in registers, with dt'/dq_i = sign_i w_i
-            T qv[D_MAX], tu[D_MAX], tl[D_MAX], sq[D_MAX];
+            T qv[DM], tu[DM], tl[DM], sq[DM];
 #pragma unroll
-            for (int i = 0; i < D_MAX; ++i) {
+            for (int i = 0; i < DM; ++i) {
                 if (i < P.d) {
                     sq[i] = sizeof(T) == 4 ? (T)P.sqf[i] : (P.mon[i] < 0 ? (T)-1 : (T)1) * (T)P.w[i];
                     qv[i] = q[i];
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(BWD_THREADS) backward_kernel(const BwdParams P
             T au = 0, al = 0;
             int mu = -1, ml = -1;
 #pragma unroll
-            for (int i = 0; i < D_MAX; ++i) {
+            for (int i = 0; i < DM; ++i) {
                 if (i >= P.d) break;
                 T vu, vl, dv;
                 const bool c = P.mon[i] != 0;
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(BWD_THREADS) backward_kernel(const BwdParams P
                 const T hm = (T)(0.5 * P.M) * gb;
                 const T ru = du > 0 ? (T)1 / du : (T)0, rl = dl > 0 ? (T)1 / dl : (T)0;
 #pragma unroll
-                for (int i = 0; i < D_MAX; ++i) {
+                for (int i = 0; i < DM; ++i) {
                     if (i >= P.d) break;
                     T vu, vl, dvu, dvl;
                     const bool c = P.mon[i] != 0;
@@ -194,8 +195,14 @@ cudaError_t launch_grad_y_fix(int elem_bytes, const unsigned long long* gy_fix, 
 cudaError_t launch_backward(int elem_bytes, const BwdParams& P, cudaStream_t st) {
     const int nb = backward_blocks(P.nq);
     if (nb > 0) {
-        if (elem_bytes == 8) backward_kernel<double><<<nb, BWD_THREADS, 0, st>>>(P);
-        else backward_kernel<float><<<nb, BWD_THREADS, 0, st>>>(P);
+        const bool wide = P.d > 16;
+        if (elem_bytes == 8) {
+            if (wide) backward_kernel<double, 32><<<nb, BWD_THREADS, 0, st>>>(P);
+            else backward_kernel<double, 16><<<nb, BWD_THREADS, 0, st>>>(P);
+        } else {
+            if (wide) backward_kernel<float, 32><<<nb, BWD_THREADS, 0, st>>>(P);
+            else backward_kernel<float, 16><<<nb, BWD_THREADS, 0, st>>>(P);
+        }
     }
     return cudaGetLastError();
 }

@@ -71,6 +71,60 @@ __device__ __forceinline__ void dispatch(int shape, const ScanParams& P, int64_t
     (try_body<K>(shape, P, qb, sp, tiles, bars, reinit) || ...);
 }
 
+// Sets wider than the exact bodies (d = 11 .. LIP_D_MAX, any number of constrained
+// coordinates): one query per thread against the set's layout (constrained coordinates
+// first, mirrored and scaled; y after the d coordinates; the L1 auxiliary channel is not
+// needed), read with plain loads, the index tracked per pair with strict comparisons (so
+// the lowest index on ties), in the arithmetic of the generic scan kernel.
+constexpr int WIDE_SHAPE0 = 3 * 121;       // shape ids WIDE_SHAPE0 + norm - 1
+constexpr int WIDE_ROWS = 1;
+
+template <int NORM>
+__device__ __noinline__ void wide_item_body(const ScanParams& P, int64_t qblock, int split) {
+    const int64_t qi = qblock * SCAN_THREADS + threadIdx.x;
+    if (qi >= P.nq) return;
+    const float* Q = static_cast<const float*>(P.Q);
+    const float4* hot = static_cast<const float4*>(P.hot);
+    float q[D_MAX];
+#pragma unroll
+    for (int j = 0; j < D_MAX; ++j) q[j] = j < P.d ? (float)(P.scale[j] * (double)Q[qi * P.d + P.perm[j]]) : 0.f;
+    float mu = __int_as_float(0x7f800000), ml = -mu;
+    int iu = -1, il = -1;
+    const int64_t g0 = (int64_t)split * P.groups_per_split;
+    const int64_t g1 = g0 + P.groups_per_split < P.ngroups ? g0 + P.groups_per_split : P.ngroups;
+    for (int64_t g = g0; g < g1; ++g) {
+        float au[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < D_MAX; ++j) {
+            if (j >= P.dl) break;
+            const float4 xv = hot[g * P.nch + j];
+            const float xe[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float t = q[j] - xe[e];
+                float u, l;
+                if (j < P.C) { u = fmaxf(t, 0.f); l = fmaxf(-t, 0.f); }
+                else { u = fabsf(t); l = u; }
+                if (NORM == LIP_L1) { au[e] += u; al[e] += l; }
+                else if (NORM == LIP_L2) { au[e] = fmaf(u, u, au[e]); al[e] = fmaf(l, l, al[e]); }
+                else { au[e] = fmaxf(au[e], u); al[e] = fmaxf(al[e], l); }
+            }
+        }
+        const float4 yv = hot[g * P.nch + P.dl];
+        const float ye[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float du = NORM == LIP_L2 ? sqrtf(au[e]) : au[e];
+            const float dl = NORM == LIP_L2 ? sqrtf(al[e]) : al[e];
+            const float vu = ye[e] + du, vl = ye[e] - dl;      // NaN (padding) fails both tests
+            const int k = (int)(g * GROUP + e);
+            if (vu < mu) { mu = vu; iu = k; }
+            if (vl > ml) { ml = vl; il = k; }
+        }
+    }
+    static_cast<PartialRec<float>*>(P.partial)[(int64_t)split * P.nq + qi] = PartialRec<float>{mu, iu, ml, il};
+}
+
 __global__ void __launch_bounds__(SCAN_THREADS, 4) batch_scan_kernel(const BatchParams B) {
     extern __shared__ __align__(128) float4 tiles[];
     __shared__ __align__(8) uint64_t bars[SCAN_STAGES];
@@ -83,9 +137,16 @@ __global__ void __launch_bounds__(SCAN_THREADS, 4) batch_scan_kernel(const Batch
         __syncthreads();
         if (it >= B.n_items) break;
         const BatchItem item = B.items[it];
-        dispatch(B.shape[item.set], B.sets[item.set], item.qblock, item.split, tiles, bars, reinit,
-                 std::make_integer_sequence<int, 3 * 121>{});
-        reinit = true;
+        const int shape = B.shape[item.set];
+        if (shape >= WIDE_SHAPE0) {
+            if (shape == WIDE_SHAPE0) wide_item_body<LIP_L1>(B.sets[item.set], item.qblock, item.split);
+            else if (shape == WIDE_SHAPE0 + 1) wide_item_body<LIP_L2>(B.sets[item.set], item.qblock, item.split);
+            else wide_item_body<LIP_LINF>(B.sets[item.set], item.qblock, item.split);
+        } else {
+            dispatch(shape, B.sets[item.set], item.qblock, item.split, tiles, bars, reinit,
+                     std::make_integer_sequence<int, 3 * 121>{});
+            reinit = true;                 // the barriers have been initialised once
+        }
         __syncthreads();
     }
 }
@@ -180,7 +241,7 @@ static lip_status batch_create(const lip_batch_set* sets, int32_t nsets, const l
         const lip_batch_set& x = sets[s];
         const char* bad = nullptr;
         if (x.N < 1 || x.N >= ((int64_t)1 << 31)) bad = "N outside [1, 2^31)";
-        else if (x.d < 1 || x.d > B_DMAX) bad = "d outside [1, 10] (the batched kernel's shapes)";
+        else if (x.d < 1 || x.d > D_MAX) bad = "d outside [1, LIP_D_MAX]";
         else if (x.norm < LIP_L1 || x.norm > LIP_LINF) bad = "norm is not L1/L2/Linf";
         else if (!(x.M >= 0.0) || !std::isfinite(x.M)) bad = "M must be finite and >= 0";
         else if (!x.X || !x.y) bad = "X or y is NULL";
@@ -209,7 +270,7 @@ static lip_status batch_create(const lip_batch_set* sets, int32_t nsets, const l
     std::vector<MergeParams> mp(nsets);
     std::vector<int32_t> shape(nsets);
     std::vector<int64_t> x_off(nsets), y_off(nsets), hot_off(nsets), part_off(nsets), qprefix(nsets + 1, 0);
-    std::vector<int> tg(nsets), rows(nsets), nch(nsets), aux(nsets);
+    std::vector<int> tg(nsets), rows(nsets), nch(nsets), aux(nsets), cset(nsets);
     std::vector<int64_t> ngroups(nsets);
     int64_t xs = 0, ys = 0, hs = 0;
     size_t smem = 0;
@@ -218,15 +279,18 @@ static lip_status batch_create(const lip_batch_set* sets, int32_t nsets, const l
         int C = 0;
         for (int i = 0; i < x.d; ++i) C += (x.mon && x.mon[i] != 0) ? 1 : 0;
         const int U = x.d - C;
-        shape[s] = (x.norm - 1) * 121 + C * 11 + U;
+        cset[s] = C;
+        const bool wide = x.d > B_DMAX;
+        shape[s] = wide ? WIDE_SHAPE0 + x.norm - 1 : (x.norm - 1) * 121 + C * 11 + U;
         aux[s] = (x.norm == LIP_L1 && C > 0) ? 1 : 0;
         nch[s] = x.d + 1 + aux[s];
-        rows[s] = batch_rows(x.d);
+        rows[s] = wide ? WIDE_ROWS : batch_rows(x.d);
         int t = x.tile_groups;
         if (t == 0) t = x.N <= 128 ? 8 : (x.N <= 512 ? 16 : (opt && opt->tile_groups ? opt->tile_groups : 32));
         tg[s] = t;
         ngroups[s] = rup(cdiv(x.N, GROUP), t);
-        smem = std::max(smem, (size_t)SCAN_STAGES * t * nch[s] * sizeof(float4));
+        // the wide body reads its set with plain loads: no shared-memory tiles
+        if (!wide) smem = std::max(smem, (size_t)SCAN_STAGES * t * nch[s] * sizeof(float4));
         x_off[s] = xs;
         xs += x.N * x.d;
         y_off[s] = ys;
@@ -253,7 +317,7 @@ static lip_status batch_create(const lip_batch_set* sets, int32_t nsets, const l
     // ---- work items: split large sets so that items stay well below the per-block share
     double weighted = 0;
     for (int s = 0; s < nsets; ++s) {
-        const int C = (shape[s] % 121) / 11, U = shape[s] % 11;
+        const int C = cset[s], U = sets[s].d - C;
         weighted += (double)sets[s].nq * sets[s].N * pair_cost(sets[s].norm, C, U);
     }
     const int per_block = opt && opt->items_per_block > 0 ? opt->items_per_block : 8;
@@ -264,7 +328,7 @@ static lip_status batch_create(const lip_batch_set* sets, int32_t nsets, const l
     int64_t ps = 0;
     for (int s = 0; s < nsets; ++s) {
         const lip_batch_set& x = sets[s];
-        const int C = (shape[s] % 121) / 11, U = shape[s] % 11;
+        const int C = cset[s], U = sets[s].d - C;
         const double pc = pair_cost(x.norm, C, U);
         const int64_t qb = (int64_t)SCAN_THREADS * rows[s];
         const int64_t tiles = ngroups[s] / tg[s];

@@ -21,6 +21,7 @@ constexpr int EST_THREADS = 128;
 constexpr int EST_R = 4;
 constexpr int EST_TILE = EST_THREADS * EST_R;        // points per I-tile and per J-tile
 constexpr int EST_TILE_GROUPS = EST_TILE / GROUP;
+constexpr int EST_NARROW_MAX = 16;                   // d above this takes estimate_wide_kernel
 
 template <int NORM, int D>
 __device__ __forceinline__ void est_group(const float2 (&xi)[D], float2 yi, const float4 (&x)[D + 1], float (&r2)[4]) {
@@ -61,6 +62,28 @@ __device__ __forceinline__ bool est_better(float r, int i, int j, float rb, int 
     if (r != rb) return r > rb;
     if (i != ib) return i < ib;
     return j < jb;
+}
+
+// Block reduction of the threads' best pairs (fixed shape, so the result does not depend
+// on timing) and the block's candidate record.
+__device__ __forceinline__ void est_block_write(const EstParams& P, int bi, int bj, float tb, int ti, int tj) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, tb, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, ti, off);
+        const int oj = __shfl_xor_sync(0xffffffffu, tj, off);
+        if (est_better(ob, oi, oj, tb, ti, tj)) { tb = ob; ti = oi; tj = oj; }
+    }
+    __shared__ float sb[EST_THREADS / 32];
+    __shared__ int si[EST_THREADS / 32], sj[EST_THREADS / 32];
+    if ((tid & 31) == 0) { sb[tid >> 5] = tb; si[tid >> 5] = ti; sj[tid >> 5] = tj; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < EST_THREADS / 32; ++w)
+            if (est_better(sb[w], si[w], sj[w], tb, ti, tj)) { tb = sb[w]; ti = si[w]; tj = sj[w]; }
+        P.cand[(size_t)bi * P.nb + bj] = make_float4(tb, __int_as_float(ti), __int_as_float(tj), ti >= 0 ? 1.f : 0.f);
+    }
 }
 
 template <int NORM, int D>
@@ -146,23 +169,82 @@ estimate_kernel(const EstParams P) {
         if (est_better(best[r], a, b, tb, ti, tj)) { tb = best[r]; ti = a; tj = b; }
     }
 
-    // Block reduction (fixed shape, so the result does not depend on timing).
+    est_block_write(P, bi, bj, tb, ti, tj);
+}
+
+// d > 16: the same tiles, grid and candidate records.  Each thread keeps its EST_R
+// I-points as plain floats and reads a J-group's coordinates from shared memory one
+// channel at a time (the packed form's duplicated registers do not fit at these widths);
+// the squared ratio is formed in the same order of operations as est_group, and the row
+// maximum is tracked per pair (strict >, so the lowest j on ties; NaN never wins).
+template <int NORM>
+__global__ void __launch_bounds__(EST_THREADS)
+estimate_wide_kernel(const EstParams P, int d) {
+    const int nch = d + 1;
+    const int bi = blockIdx.x, bj = blockIdx.y;
+    if (bj < bi) return;
+    if (((int64_t)bi * P.nb + bj) % P.nparts != P.part) return;
+    extern __shared__ __align__(16) float4 wtile[];     // EST_TILE_GROUPS * nch
+    const int tid = threadIdx.x;
+    const float4* src = P.lay + (size_t)bj * EST_TILE_GROUPS * nch;
+    for (int k = tid; k < EST_TILE_GROUPS * nch; k += EST_THREADS) wtile[k] = __ldg(src + k);
+    float xi[EST_R][D_MAX];
+    float yi[EST_R];
+    int ii[EST_R];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, tb, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, ti, off);
-        const int oj = __shfl_xor_sync(0xffffffffu, tj, off);
-        if (est_better(ob, oi, oj, tb, ti, tj)) { tb = ob; ti = oi; tj = oj; }
+    for (int r = 0; r < EST_R; ++r) {
+        const int64_t i = (int64_t)bi * EST_TILE + r * EST_THREADS + tid;
+        ii[r] = (int)i;
+        const float* g = reinterpret_cast<const float*>(P.lay + (size_t)(i / GROUP) * nch);
+        const int lane = (int)(i % GROUP);
+#pragma unroll
+        for (int j = 0; j < D_MAX; ++j) xi[r][j] = j < d ? __ldg(g + j * GROUP + lane) : 0.f;
+        yi[r] = __ldg(g + d * GROUP + lane);
     }
-    __shared__ float sb[EST_THREADS / 32];
-    __shared__ int si[EST_THREADS / 32], sj[EST_THREADS / 32];
-    if ((tid & 31) == 0) { sb[tid >> 5] = tb; si[tid >> 5] = ti; sj[tid >> 5] = tj; }
     __syncthreads();
-    if (tid == 0) {
-        for (int w = 1; w < EST_THREADS / 32; ++w)
-            if (est_better(sb[w], si[w], sj[w], tb, ti, tj)) { tb = sb[w]; ti = si[w]; tj = sj[w]; }
-        P.cand[(size_t)bi * P.nb + bj] = make_float4(tb, __int_as_float(ti), __int_as_float(tj), ti >= 0 ? 1.f : 0.f);
+    float best[EST_R];
+    int bjr[EST_R];
+#pragma unroll
+    for (int r = 0; r < EST_R; ++r) { best[r] = -1.f; bjr[r] = -1; }
+    for (int gi = 0; gi < EST_TILE_GROUPS; ++gi) {
+        const float4* grp = wtile + gi * nch;
+        float acc[EST_R][4];
+#pragma unroll
+        for (int j = 0; j < D_MAX; ++j) {
+            if (j >= d) break;
+            const float4 xv = grp[j];
+            const float xe[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+            for (int r = 0; r < EST_R; ++r)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float t = xi[r][j] - xe[e];
+                    if (NORM == LIP_L2) acc[r][e] = j == 0 ? t * t : fmaf(t, t, acc[r][e]);
+                    else if (NORM == LIP_L1) acc[r][e] = j == 0 ? fabsf(t) : acc[r][e] + fabsf(t);
+                    else acc[r][e] = j == 0 ? fabsf(t) : fmaxf(acc[r][e], fabsf(t));
+                }
+        }
+        const float4 yv = grp[d];
+        const float ye[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+        for (int r = 0; r < EST_R; ++r)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float den = NORM == LIP_L2 ? acc[r][e] : acc[r][e] * acc[r][e];
+                const float dy = yi[r] - ye[e];
+                const float q = (dy * dy) * rcp_approx(den);
+                if (q > best[r]) { best[r] = q; bjr[r] = bj * EST_TILE + gi * GROUP + e; }
+            }
     }
+    float tb = -1.f;
+    int ti = -1, tj = -1;
+#pragma unroll
+    for (int r = 0; r < EST_R; ++r) {
+        if (bjr[r] < 0) continue;
+        const int a = min(ii[r], bjr[r]), b = max(ii[r], bjr[r]);
+        if (est_better(best[r], a, b, tb, ti, tj)) { tb = best[r]; ti = a; tj = b; }
+    }
+    est_block_write(P, bi, bj, tb, ti, tj);
 }
 
 template <typename T>
@@ -253,8 +335,26 @@ cudaError_t launch_estimate_layout(int elem_bytes, const HotParams& P, cudaStrea
     return cudaGetLastError();
 }
 
+template <int NORM>
+static cudaError_t launch_est_wide(int d, const EstParams& P, cudaStream_t st) {
+    const int smem = EST_TILE_GROUPS * (D_MAX + 1) * (int)sizeof(float4);
+    static cudaError_t attr = cudaFuncSetAttribute(estimate_wide_kernel<NORM>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (attr != cudaSuccess) return attr;
+    estimate_wide_kernel<NORM><<<dim3(P.nb, P.nb), EST_THREADS, EST_TILE_GROUPS * (d + 1) * sizeof(float4), st>>>(P, d);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_estimate(int norm, int d, const EstParams& P, cudaStream_t st) {
-    auto seq = std::make_integer_sequence<int, D_MAX>{};
+    if (d > EST_NARROW_MAX) {
+        switch (norm) {
+            case LIP_L1: return launch_est_wide<LIP_L1>(d, P, st);
+            case LIP_L2: return launch_est_wide<LIP_L2>(d, P, st);
+            case LIP_LINF: return launch_est_wide<LIP_LINF>(d, P, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    auto seq = std::make_integer_sequence<int, EST_NARROW_MAX>{};
     switch (norm) {
         case LIP_L1: return est_dispatch_d<LIP_L1>(d, P, st, seq);
         case LIP_L2: return est_dispatch_d<LIP_L2>(d, P, st, seq);

@@ -1020,7 +1020,8 @@ __global__ void loc_merge_kernel(const LocalMergeParams P) {
 
 }  // namespace
 
-int local_dim_pad(int d) { return (d + 3) / 4 * 4; }
+// Coordinates per record: d rounded up to 4, and 32 for every d above 16 (one wide shape).
+int local_dim_pad(int d) { return d <= 16 ? (d + 3) / 4 * 4 : 32; }
 int local_record_floats(int d) { return local_dim_pad(d) + 4; }
 int64_t local_pad(int64_t N) { return (N + LOC_TILE - 1) / LOC_TILE * LOC_TILE; }
 int local_scan_tile() { return LOC_SCAN_TILE; }
@@ -1076,7 +1077,8 @@ static cudaError_t table_norm(const LocalParams& P, bool bk, int m, cudaStream_t
         case 4: return table_shape<NORM, 4>(P, bk, m, st);
         case 8: return table_shape<NORM, 8>(P, bk, m, st);
         case 12: return table_shape<NORM, 12>(P, bk, m, st);
-        default: return table_shape<NORM, 16>(P, bk, m, st);
+        case 16: return table_shape<NORM, 16>(P, bk, m, st);
+        default: return table_shape<NORM, 32>(P, bk, m, st);
     }
 }
 
@@ -1101,7 +1103,8 @@ static void scan_norm(const LocalScanParams& S, dim3 grid, bool bucket, cudaStre
         case 4: scan_shape<NORM, 4>(S, grid, bucket, st); break;
         case 8: scan_shape<NORM, 8>(S, grid, bucket, st); break;
         case 12: scan_shape<NORM, 12>(S, grid, bucket, st); break;
-        default: scan_shape<NORM, 16>(S, grid, bucket, st); break;
+        case 16: scan_shape<NORM, 16>(S, grid, bucket, st); break;
+        default: scan_shape<NORM, 32>(S, grid, bucket, st); break;
     }
 }
 
@@ -1118,7 +1121,8 @@ static void topk_norm(int K, const LocalScanParams& S, dim3 grid, cudaStream_t s
         case 4: topk_shape<NORM, 4>(K, S, grid, st); break;
         case 8: topk_shape<NORM, 8>(K, S, grid, st); break;
         case 12: topk_shape<NORM, 12>(K, S, grid, st); break;
-        default: topk_shape<NORM, 16>(K, S, grid, st); break;
+        case 16: topk_shape<NORM, 16>(K, S, grid, st); break;
+        default: topk_shape<NORM, 32>(K, S, grid, st); break;
     }
 }
 

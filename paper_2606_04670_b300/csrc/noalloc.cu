@@ -27,7 +27,7 @@ constexpr int64_t NA_POINTS = ((int64_t)LIP_NOALLOC_N_MAX + NA_TILE - 1) / NA_TI
 constexpr int64_t NA_LAYOUT_BYTES = (NA_POINTS * (D_MAX + 1) * 4 + 255) / 256 * 256;
 constexpr int64_t NA_TILES = NA_POINTS / NA_TILE;
 constexpr int64_t NA_CAND_BYTES = (NA_TILES * NA_TILES * 16 + 255) / 256 * 256;
-constexpr int64_t NA_BYTES = NA_LAYOUT_BYTES + NA_CAND_BYTES;   // about 2.2 MB
+constexpr int64_t NA_BYTES = NA_LAYOUT_BYTES + NA_CAND_BYTES;   // about 4.4 MB (d up to 32)
 
 // Working memory of every lip_estimate_M_noalloc call on this device: the FP32 point
 // layout followed by one candidate record per tile pair.  Host code must not pass this

@@ -347,7 +347,8 @@ scan_exact_kernel(const ScanParams P) {
 }
 
 // ------------------------------------------------------------------ generic scan
-// Any (d <= D_MAX, C) and FP32 or FP64: coordinates padded to DP with zeros; the
+// Any (d <= D_MAX, C) and FP32 or FP64: coordinates padded to DP with zeros (2, 4, 8, 12,
+// 16, 24 or 32); the
 // monotone parts come from per-coordinate clamps (0 for constrained coordinates,
 // +-Inf otherwise).  Plain global loads, index tracked per pair.  Used for FP64
 // handles and for FP32 shapes without an exact instantiation.
@@ -565,10 +566,21 @@ __host__ __device__ constexpr int rows_for_variant(int D, int v) {
     return v == 0 ? rows_for_dim(D) : (rows_for_dim(D) / 2 > 0 ? rows_for_dim(D) / 2 : 1);
 }
 
-// Exact instantiations: every (C, U) with 1 <= C + U <= 10, and unconstrained D up to 16.
+// Exact instantiations: every (C, U) with 1 <= C + U <= 10, and unconstrained D up to 16
+// (EXACT_DMAX).  Wider shapes (up to D_MAX = 32) take the generic kernel: the exact body
+// holds a whole group's channels and the duplicated query coordinates in registers, which
+// does not fit beyond 16 coordinates.
+constexpr int EXACT_DMAX = 16;
 __host__ __device__ constexpr bool exact_shape_available(int C, int U) {
-    return (C + U >= 1 && C + U <= 10 && C >= 0 && U >= 0) || (C == 0 && U >= 11 && U <= D_MAX);
+    return (C + U >= 1 && C + U <= 10 && C >= 0 && U >= 0) || (C == 0 && U >= 11 && U <= EXACT_DMAX);
 }
+
+// Layout dimension of the generic kernel for d coordinates (zero-padded).
+__host__ __device__ constexpr int generic_dim(int d) {
+    return d <= 2 ? 2 : (d <= 4 ? 4 : (d <= 8 ? 8 : (d <= 12 ? 12 : (d <= 16 ? 16 : (d <= 24 ? 24 : 32)))));
+}
+// Queries per thread of the generic kernel (each holds DP coordinates in registers).
+__host__ __device__ constexpr int generic_rows(int DP) { return DP <= 16 ? 2 : 1; }
 
 using ScanLaunchFn = cudaError_t (*)(const ScanParams&, int gx, int gy, cudaStream_t);
 

@@ -5,7 +5,7 @@ namespace lip {
 
 template <typename T, int NORM, int DP>
 cudaError_t launch_scan_generic(const ScanParams& P, int gx, int gy, cudaStream_t st) {
-    constexpr int R = 2;
+    constexpr int R = generic_rows(DP);
     scan_generic_kernel<T, NORM, DP, R><<<dim3(gx, gy), SCAN_THREADS, 0, st>>>(P);
     return cudaGetLastError();
 }
@@ -14,8 +14,8 @@ template <typename T, int NORM, int DP>
 static ScanKernelInfo gen_info() {
     ScanKernelInfo e;
     e.launch = &launch_scan_generic<T, NORM, DP>;
-    e.kernel = reinterpret_cast<const void*>(&scan_generic_kernel<T, NORM, DP, 2>);
-    e.rows = 2;
+    e.kernel = reinterpret_cast<const void*>(&scan_generic_kernel<T, NORM, DP, generic_rows(DP)>);
+    e.rows = generic_rows(DP);
     e.nch = DP + 1;
     return e;
 }
@@ -28,6 +28,8 @@ static ScanKernelInfo gen_by_dim(int dl) {
         case 8: return gen_info<T, NORM, 8>();
         case 12: return gen_info<T, NORM, 12>();
         case 16: return gen_info<T, NORM, 16>();
+        case 24: return gen_info<T, NORM, 24>();
+        case 32: return gen_info<T, NORM, 32>();
         default: return {};
     }
 }

@@ -21,7 +21,7 @@ cudaError_t launch_scan_exact(const ScanParams& P, int gx, int gy, cudaStream_t 
 
 template <int NORM>
 struct ExactTable {
-    ScanKernelInfo tab[D_MAX + 1][D_MAX + 1][SCAN_VARIANTS];
+    ScanKernelInfo tab[EXACT_DMAX + 1][EXACT_DMAX + 1][SCAN_VARIANTS];
     template <int C, int U, int V>
     void fill_variant() {
         ScanKernelInfo& e = tab[C][U][V];
@@ -32,7 +32,7 @@ struct ExactTable {
     }
     template <int K>
     void fill_one() {
-        constexpr int C = K / (D_MAX + 1), U = K % (D_MAX + 1);
+        constexpr int C = K / (EXACT_DMAX + 1), U = K % (EXACT_DMAX + 1);
         if constexpr (exact_shape_available(C, U)) {
             fill_variant<C, U, 0>();
             fill_variant<C, U, 1>();
@@ -40,7 +40,7 @@ struct ExactTable {
     }
     template <int... K>
     void fill(std::integer_sequence<int, K...>) { (fill_one<K>(), ...); }
-    ExactTable() { fill(std::make_integer_sequence<int, (D_MAX + 1) * (D_MAX + 1)>{}); }
+    ExactTable() { fill(std::make_integer_sequence<int, (EXACT_DMAX + 1) * (EXACT_DMAX + 1)>{}); }
 };
 
 }  // namespace lip

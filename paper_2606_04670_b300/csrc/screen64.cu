@@ -132,7 +132,9 @@ static void screen_norm(const Screen64Params& P, dim3 grid, cudaStream_t st) {
     if (P.dl <= 4) screen64_kernel<NORM, 4><<<grid, S64_THREADS, 0, st>>>(P);
     else if (P.dl <= 8) screen64_kernel<NORM, 8><<<grid, S64_THREADS, 0, st>>>(P);
     else if (P.dl <= 12) screen64_kernel<NORM, 12><<<grid, S64_THREADS, 0, st>>>(P);
-    else screen64_kernel<NORM, 16><<<grid, S64_THREADS, 0, st>>>(P);
+    else if (P.dl <= 16) screen64_kernel<NORM, 16><<<grid, S64_THREADS, 0, st>>>(P);
+    else if (P.dl <= 24) screen64_kernel<NORM, 24><<<grid, S64_THREADS, 0, st>>>(P);
+    else screen64_kernel<NORM, 32><<<grid, S64_THREADS, 0, st>>>(P);
 }
 
 }  // namespace

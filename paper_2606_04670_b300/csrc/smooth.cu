@@ -334,7 +334,8 @@ void pass_norm(const SmoothParams& P, dim3 grid, cudaStream_t st) {
         case 4: pass_shape<NORM, 4>(P, grid, st); break;
         case 8: pass_shape<NORM, 8>(P, grid, st); break;
         case 12: pass_shape<NORM, 12>(P, grid, st); break;
-        default: pass_shape<NORM, 16>(P, grid, st); break;
+        case 16: pass_shape<NORM, 16>(P, grid, st); break;
+        default: pass_shape<NORM, 32>(P, grid, st); break;
     }
 }
 

@@ -69,8 +69,18 @@ __host__ __device__ constexpr int tc_threads(int parts) { return 32 * (2 + 4 * p
 constexpr float TC_C_EPS_TF32 = 1.3e-5f;   // TF32 split (bound 9.3e-6)
 constexpr float TC_C_EPS_BF16 = 1.7e-5f;   // BF16 three-piece split (bound 1.3e-5)
 constexpr float TC_C_EPS_FP16 = 1.0e-5f;   // FP16 two-piece split (bound 7.2e-6)
-__host__ __device__ constexpr float tc_c_eps(int fmt) {
-    return fmt == TC_BF16 ? TC_C_EPS_BF16 : (fmt == TC_FP16 ? TC_C_EPS_FP16 : TC_C_EPS_TF32);
+// The error bound of |s~ - s| / (|q^| + R)^2 as a function of K (the derivation's terms:
+// the split's dropped products, K-proportional FP32 accumulation, the input roundings).
+__host__ __device__ constexpr double tc_eps_bound(int fmt, int K) {
+    return fmt == TC_BF16 ? 0x1p-22 + (6.0 * K + 6.0) * 0x1p-23 + 0x1p-23 + 0x1p-24
+         : fmt == TC_FP16 ? 3 * 0x1p-22 + (3.0 * K + 2.0) * 0x1p-23 + 0x1p-24 + 0x1p-23 + 0x1p-24
+                          : 3 * 0x1p-20 + (3.0 * K + 4.0) * 0x1p-23 + 0x1p-23 + 0x1p-24;
+}
+// The constant used for eps: the K = 16 constant above (about 1.4 times its bound), and for
+// wider K (d above 16) the same constant scaled by the bound's growth with K.
+__host__ __device__ constexpr float tc_c_eps(int fmt, int K) {
+    const float c16 = fmt == TC_BF16 ? TC_C_EPS_BF16 : (fmt == TC_FP16 ? TC_C_EPS_FP16 : TC_C_EPS_TF32);
+    return K <= 16 ? c16 : (float)(c16 * (tc_eps_bound(fmt, K) / tc_eps_bound(fmt, 16)));
 }
 
 struct TcRec {      // candidate list of one (query, bound, column quarter)
@@ -104,6 +114,15 @@ __host__ __device__ constexpr int tc_tile_bytes(int K, int fmt) {
 __host__ __device__ constexpr int tc_stage_bytes(int K, int fmt) { return (tc_tile_bytes(K, fmt) + 1023) / 1024 * 1024; }
 __host__ __device__ constexpr int tc_a_bytes(int K, int fmt) {
     return tc_pieces(fmt) * TC_M * K * tc_esz(fmt) + TC_M * TC_NORM_ROW;
+}
+// Stages of the data-tile ring: TC_STAGES where they fit in the 227 KB of shared memory next
+// to the A operand (every K up to 16, and FP16 at 32); fewer for the widest tiles (TF32 at
+// K = 24 and BF16 at 32 keep 3, TF32 at 32 keeps 2).
+constexpr int TC_SMEM_BYTES = 227 * 1024 - 1024;    // a margin for the static barriers
+__host__ __device__ constexpr int tc_stages(int K, int fmt) {
+    return (TC_SMEM_BYTES - tc_a_bytes(K, fmt)) / tc_stage_bytes(K, fmt) < TC_STAGES
+               ? (TC_SMEM_BYTES - tc_a_bytes(K, fmt)) / tc_stage_bytes(K, fmt)
+               : TC_STAGES;
 }
 
 // byte offset of the element at row r, byte kb along K, in a canonical no-swizzle K-major
@@ -242,7 +261,7 @@ __global__ void tc_build_b_kernel(const TcPrepParams P) {
     const int piece = TC_N * P.K * tc_esz(FMT);
     char* norm = tile + tc_pieces(FMT) * piece;
     float* yv = reinterpret_cast<float*>(norm + TC_N * TC_NORM_ROW);
-    float b[16];
+    float b[D_MAX];
     for (int j = 0; j < P.K; ++j) b[j] = 0.f;
     float yy = __int_as_float(0x7fc00000);
     bool real = false;
@@ -327,7 +346,7 @@ __global__ void tc_build_a_kernel(const TcQueryParams P) {
     const int r = (int)(qi % TC_M);
     char* at = P.atiles + t * (int64_t)tc_a_bytes(P.K, FMT);
     const int piece = TC_M * P.K * tc_esz(FMT);
-    float a[16];
+    float a[D_MAX];
     for (int j = 0; j < P.K; ++j) a[j] = 0.f;
     char* norm = at + tc_pieces(FMT) * piece;
     bool real = false;
@@ -347,7 +366,7 @@ __global__ void tc_build_a_kernel(const TcQueryParams P) {
         const double R = (double)__uint_as_float(P.maxbits[0]);
         const double Y = (double)__uint_as_float(P.maxbits[1]);
         const double nq = sqrt(n2);
-        const float eps = (float)((double)tc_c_eps(FMT) * (nq + R) * (nq + R));
+        const float eps = (float)((double)tc_c_eps(FMT, P.K) * (nq + R) * (nq + R));
         const float epsv = (float)(ldexp(1.0, -19) * (Y + nq + R));
         const float usc = (float)ldexp(1.0, -2 * ks);
         P.qc[qi] = make_float4(eps, epsv, FMT == TC_FP16 ? (float)n2 : 0.f, inside ? usc : -usc);
@@ -473,6 +492,8 @@ __device__ __forceinline__ void tc_append(TcRec* R, int& n, int id, float L, flo
 
 template <int K, int PARTS, int FMT>
 __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcScanParams P) {
+    constexpr int ST = tc_stages(K, FMT);                // the ring's stages at this K
+    static_assert(ST >= 2, "the data-tile ring needs two stages");
     constexpr int EPI_WARPS = 4 * PARTS;
     constexpr int TILE_BYTES = tc_tile_bytes(K, FMT), STAGE_BYTES = tc_stage_bytes(K, FMT);
     constexpr int A_BYTES = tc_a_bytes(K, FMT);
@@ -481,8 +502,8 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
     constexpr int A_PIECE = TC_M * ROW_BYTES, B_PIECE = TC_N * ROW_BYTES;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                               // A_hi, A_lo
-    unsigned char* sB = smem + A_BYTES;                     // TC_STAGES tiles
-    __shared__ __align__(8) uint64_t a_full, b_full[TC_STAGES], b_empty[TC_STAGES], acc_full[2], acc_empty[2];
+    unsigned char* sB = smem + A_BYTES;                     // ST tiles
+    __shared__ __align__(8) uint64_t a_full, b_full[ST], b_empty[ST], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -491,7 +512,7 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
 
     if (threadIdx.x == 0) {
         mbar_init(&a_full, 1);
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < ST; ++s) {
             mbar_init(&b_full[s], 1);
             mbar_init(&b_empty[s], 1 + EPI_WARPS);         // MMA commit + epilogue warps
         }
@@ -518,8 +539,8 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
             mbar_expect_tx(&a_full, A_BYTES);
             bulk_g2s(sA, P.atiles + qt * (int64_t)A_BYTES, A_BYTES, &a_full);
             for (; t < T; ++t) {
-                const int s = (int)(t % TC_STAGES);
-                if (t >= TC_STAGES && !mbar_wait_bounded(&b_empty[s], (uint32_t)((t / TC_STAGES - 1) & 1), P.err)) {
+                const int s = (int)(t % ST);
+                if (t >= ST && !mbar_wait_bounded(&b_empty[s], (uint32_t)((t / ST - 1) & 1), P.err)) {
                     ok = false;
                     break;
                 }
@@ -527,9 +548,9 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                 bulk_g2s(sB + (size_t)s * STAGE_BYTES, P.btiles + t * (int64_t)TILE_BYTES, TILE_BYTES, &b_full[s]);
             }
             // wait (bounded) for the copies still in flight before leaving
-            const int64_t first = t > TC_STAGES ? t - TC_STAGES : 0;
+            const int64_t first = t > ST ? t - ST : 0;
             for (int64_t u = first; u < t; ++u)
-                mbar_wait_bounded(&b_full[u % TC_STAGES], (uint32_t)((u / TC_STAGES) & 1), ok ? P.err : nullptr);
+                mbar_wait_bounded(&b_full[u % ST], (uint32_t)((u / ST) & 1), ok ? P.err : nullptr);
             mbar_wait_bounded(&a_full, 0, nullptr);
         }
     } else if (warp == 1) {
@@ -544,8 +565,8 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
             int64_t t = 0;
             if (mbar_wait_bounded(&a_full, 0, P.err)) {
                 for (; t < T; ++t) {
-                    const int s = (int)(t % TC_STAGES), b = (int)(t & 1);
-                    if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / TC_STAGES) & 1), P.err)) break;
+                    const int s = (int)(t % ST), b = (int)(t & 1);
+                    if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / ST) & 1), P.err)) break;
                     if (t >= 2 && !mbar_wait_bounded(&acc_empty[b], (uint32_t)((t / 2 - 1) & 1), P.err)) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t b0 = smem_u32(sB + (size_t)s * STAGE_BYTES);
@@ -591,10 +612,10 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
         int nu = act ? 0 : -1, nl = nu;
         const int T32 = (int)T;                            // N < 2^31, so T < 2^23
         for (int t = 0; t < T32; ++t) {
-            const int s = t % TC_STAGES, b = t & 1;
+            const int s = t % ST, b = t & 1;
             if (!mbar_wait_bounded(&acc_full[b], (uint32_t)((t / 2) & 1), P.err)) break;
             // acquire the tile's y values and chunk bounds written by the bulk copy
-            if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / TC_STAGES) & 1), P.err)) break;
+            if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / ST) & 1), P.err)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const float* ys = reinterpret_cast<const float*>(sB + (size_t)s * STAGE_BYTES + tc_pieces(FMT) * B_PIECE +
                                                              TC_N * TC_NORM_ROW);
@@ -974,7 +995,7 @@ cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, 
 
 template <int K, int PARTS, int FMT>
 static cudaError_t launch_tc_scan_k(const TcScanParams& P, int64_t nqt, cudaStream_t st) {
-    const size_t smem = (size_t)tc_a_bytes(K, FMT) + (size_t)TC_STAGES * tc_stage_bytes(K, FMT);
+    const size_t smem = (size_t)tc_a_bytes(K, FMT) + (size_t)tc_stages(K, FMT) * tc_stage_bytes(K, FMT);
     static cudaError_t attr =
         cudaFuncSetAttribute(tc_scan_kernel<K, PARTS, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return attr;
@@ -984,10 +1005,14 @@ static cudaError_t launch_tc_scan_k(const TcScanParams& P, int64_t nqt, cudaStre
 
 template <int PARTS>
 static cudaError_t launch_tc_scan_parts(int K, int fmt, const TcScanParams& P, int64_t nqt, cudaStream_t st) {
-    if (fmt == TC_BF16) return launch_tc_scan_k<16, PARTS, TC_BF16>(P, nqt, st);   // d <= 16: K = 16
-    if (fmt == TC_FP16) return launch_tc_scan_k<16, PARTS, TC_FP16>(P, nqt, st);
+    if (fmt == TC_BF16) return K <= 16 ? launch_tc_scan_k<16, PARTS, TC_BF16>(P, nqt, st)
+                                       : launch_tc_scan_k<32, PARTS, TC_BF16>(P, nqt, st);
+    if (fmt == TC_FP16) return K <= 16 ? launch_tc_scan_k<16, PARTS, TC_FP16>(P, nqt, st)
+                                       : launch_tc_scan_k<32, PARTS, TC_FP16>(P, nqt, st);
     if (K == 8) return launch_tc_scan_k<8, PARTS, TC_TF32>(P, nqt, st);
-    return launch_tc_scan_k<16, PARTS, TC_TF32>(P, nqt, st);
+    if (K == 16) return launch_tc_scan_k<16, PARTS, TC_TF32>(P, nqt, st);
+    if (K == 24) return launch_tc_scan_k<24, PARTS, TC_TF32>(P, nqt, st);
+    return launch_tc_scan_k<32, PARTS, TC_TF32>(P, nqt, st);
 }
 
 // Queries: build A, scan, rescreen.  Returns the fallback count through fb (device).

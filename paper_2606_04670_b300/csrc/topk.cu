@@ -12,16 +12,17 @@ namespace lip {
 
 constexpr int TOPK_THREADS = 128;
 
-template <typename T, int NORM, int K>
+// DM: register arrays for a layout of up to DM coordinates (16, or 32 for the widest handles)
+template <typename T, int NORM, int K, int DM>
 __global__ void __launch_bounds__(TOPK_THREADS) topk_scan_kernel(const TopkParams P) {
     using V4 = typename Vec4<T>::type;
     const int64_t qi = (int64_t)blockIdx.x * TOPK_THREADS + threadIdx.x;
     const int split = blockIdx.y;
     const T inf = (T)INFINITY;
-    T q[D_MAX];
+    T q[DM];
     const T* Qp = static_cast<const T*>(P.Q);
 #pragma unroll
-    for (int j = 0; j < D_MAX; ++j)
+    for (int j = 0; j < DM; ++j)
         q[j] = (qi < P.nq && j < P.d) ? (T)(P.scale[j] * (double)Qp[qi * P.d + P.perm[j]]) : (T)0;
     T bu[K], bl[K];
     int ku[K], kl[K];
@@ -31,12 +32,12 @@ __global__ void __launch_bounds__(TOPK_THREADS) topk_scan_kernel(const TopkParam
     const int64_t g0 = (int64_t)split * P.groups_per_split;
     const int64_t g1 = g0 + P.groups_per_split < P.ngroups ? g0 + P.groups_per_split : P.ngroups;
     for (int64_t g = g0; g < g1 && qi < P.nq; ++g) {
-        T x[D_MAX + 1][4];
+        T x[DM + 1][4];
 #pragma unroll
-        for (int ch = 0; ch <= D_MAX; ++ch) {
+        for (int ch = 0; ch <= DM; ++ch) {
             if (ch < P.dl || ch == P.dl) {
                 const V4 v = hot[g * P.nch + (ch < P.dl ? ch : P.dl)];
-                const int c = ch < P.dl ? ch : D_MAX;
+                const int c = ch < P.dl ? ch : DM;
                 x[c][0] = v.x; x[c][1] = v.y; x[c][2] = v.z; x[c][3] = v.w;
             }
         }
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(TOPK_THREADS) topk_scan_kernel(const TopkParam
         for (int e = 0; e < 4; ++e) {
             T au = 0, al = 0;
 #pragma unroll
-            for (int j = 0; j < D_MAX; ++j) {
+            for (int j = 0; j < DM; ++j) {
                 if (j >= P.dl) break;
                 const T t = q[j] - x[j][e];
                 T u, l;
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(TOPK_THREADS) topk_scan_kernel(const TopkParam
             }
             if (NORM == LIP_L2) { au = sqrt(au); al = sqrt(al); }
             const int k = (int)(g * 4 + e);
-            T vu = x[D_MAX][e] + au, vl = x[D_MAX][e] - al;
+            T vu = x[DM][e] + au, vl = x[DM][e] - al;
             if (vu < bu[K - 1]) {           // bubble the new value into the ascending list
                 int kk = k;
 #pragma unroll
@@ -157,19 +158,24 @@ __global__ void topk_merge_kernel(const TopkMergeParams P) {
     if (P.lo) static_cast<T*>(P.lo)[qi] = (T)res[1];
 }
 
-template <typename T, int NORM>
+template <typename T, int NORM, int DM>
 static cudaError_t topk_by_k(int K, const TopkParams& P, int gx, int gy, cudaStream_t st) {
-    if (K == 2) topk_scan_kernel<T, NORM, 2><<<dim3(gx, gy), TOPK_THREADS, 0, st>>>(P);
-    else if (K == 4) topk_scan_kernel<T, NORM, 4><<<dim3(gx, gy), TOPK_THREADS, 0, st>>>(P);
-    else topk_scan_kernel<T, NORM, 8><<<dim3(gx, gy), TOPK_THREADS, 0, st>>>(P);
+    if (K == 2) topk_scan_kernel<T, NORM, 2, DM><<<dim3(gx, gy), TOPK_THREADS, 0, st>>>(P);
+    else if (K == 4) topk_scan_kernel<T, NORM, 4, DM><<<dim3(gx, gy), TOPK_THREADS, 0, st>>>(P);
+    else topk_scan_kernel<T, NORM, 8, DM><<<dim3(gx, gy), TOPK_THREADS, 0, st>>>(P);
     return cudaGetLastError();
+}
+
+template <typename T, int DM>
+static cudaError_t topk_by_norm_w(int norm, int K, const TopkParams& P, int gx, int gy, cudaStream_t st) {
+    if (norm == LIP_L1) return topk_by_k<T, LIP_L1, DM>(K, P, gx, gy, st);
+    if (norm == LIP_L2) return topk_by_k<T, LIP_L2, DM>(K, P, gx, gy, st);
+    return topk_by_k<T, LIP_LINF, DM>(K, P, gx, gy, st);
 }
 
 template <typename T>
 static cudaError_t topk_by_norm(int norm, int K, const TopkParams& P, int gx, int gy, cudaStream_t st) {
-    if (norm == LIP_L1) return topk_by_k<T, LIP_L1>(K, P, gx, gy, st);
-    if (norm == LIP_L2) return topk_by_k<T, LIP_L2>(K, P, gx, gy, st);
-    return topk_by_k<T, LIP_LINF>(K, P, gx, gy, st);
+    return P.dl > 16 ? topk_by_norm_w<T, 32>(norm, K, P, gx, gy, st) : topk_by_norm_w<T, 16>(norm, K, P, gx, gy, st);
 }
 
 int topk_threads() { return TOPK_THREADS; }

@@ -28,6 +28,7 @@ LIP_ERR_CAPACITY, LIP_ERR_TIMEOUT, LIP_ERR_UNSUPPORTED, LIP_ERR_NO_DEVICE, LIP_E
 LIP_L1, LIP_L2, LIP_LINF = 1, 2, 3
 LIP_FP32, LIP_FP64, LIP_TC_BF16, LIP_TC_TF32, LIP_TC_FP16 = 0, 1, 2, 3, 4
 LIP_NOALLOC_N_MAX = 32768
+LIP_D_MAX = 32
 LIP_LOCAL_KNOTS_MAX = 31
 LIP_LOCAL_SAMPLE_MAX = 1 << 20
 NORMS = {"L1": LIP_L1, "L2": LIP_L2, "Linf": LIP_LINF, "LINF": LIP_LINF,

@@ -31,7 +31,7 @@ def _arr(*shape):
     ({"N": 0}, L.LIP_ERR_ARG),
     ({"N": 1 << 31}, L.LIP_ERR_ARG),
     ({"d": 0}, L.LIP_ERR_ARG),
-    ({"d": 17}, L.LIP_ERR_ARG),
+    ({"d": 33}, L.LIP_ERR_ARG),
     ({"M": -1.0}, L.LIP_ERR_ARG),
     ({"M": float("nan")}, L.LIP_ERR_ARG),
     ({"M": float("inf")}, L.LIP_ERR_ARG),
@@ -98,7 +98,7 @@ def test_batch_argument_errors():
     arr = (L.lip_batch_set * 2)()
     ok = L.lip_batch_set(1, 1, 10, 3, L.LIP_L2, 1.0, None, None, 1, 5, None, None, None, None, None, 0, 0)
     arr[0] = ok
-    arr[1] = L.lip_batch_set(1, 1, 10, 11, L.LIP_L2, 1.0, None, None, 1, 5, None, None, None, None, None, 0, 0)
+    arr[1] = L.lip_batch_set(1, 1, 10, 33, L.LIP_L2, 1.0, None, None, 1, 5, None, None, None, None, None, 0, 0)
     s, h = L.lip_batch_create(arr)
     assert s == L.LIP_ERR_ARG and "set 1" in L.last_error() and not h.value
     arr[1] = L.lip_batch_set(1, 1, 10, 3, L.LIP_L2, -1.0, None, None, 1, 5, None, None, None, None, None, 0, 0)

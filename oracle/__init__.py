@@ -90,13 +90,13 @@ class Oracle:
         u64 = ctypes.c_uint64
         lib.oracle_splitmix64.argtypes = [u64, u64]
         lib.oracle_splitmix64.restype = u64
-        lib.oracle_local_knots.argtypes = [P, i64, i32, i32, P, u64, i64, i32, P, P, P]
-        lib.oracle_local_table.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, i32]
-        lib.oracle_local_table_rows.argtypes = [P, P, i64, i32, i32, P, P, i32, P, i64, P, P, P, i32]
-        lib.oracle_eval_local.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, f64, f64, P, P, P, P, P,
+        lib.oracle_local_knots.argtypes = [P, i64, i32, i32, P, P, u64, i64, i32, P, P, P]
+        lib.oracle_local_table.argtypes = [P, P, i64, i32, i32, P, P, P, i32, P, P, P, i32]
+        lib.oracle_local_table_rows.argtypes = [P, P, i64, i32, i32, P, P, P, i32, P, i64, P, P, P, i32]
+        lib.oracle_eval_local.argtypes = [P, P, i64, i32, i32, P, P, P, i32, P, P, P, P, i64, f64, f64, P, P, P, P, P,
                                           P, P, P, P, i32]
-        lib.oracle_local_terms.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, P, i32, f64, P]
-        lib.oracle_eval_local_k.argtypes = [P, P, i64, i32, i32, P, P, i32, P, P, P, P, i64, i32, P, P, P, P, P, P,
+        lib.oracle_local_terms.argtypes = [P, P, i64, i32, i32, P, P, P, i32, P, P, P, P, i64, P, i32, f64, P]
+        lib.oracle_eval_local_k.argtypes = [P, P, i64, i32, i32, P, P, P, i32, P, P, P, P, i64, i32, P, P, P, P, P, P,
                                             i32]
         lib.oracle_eval_local_k.restype = ctypes.c_int
         lib.oracle_smooth_objective.argtypes = [P, P, i64, i32, f64, i32, P, P, f64, P, P, P, P, P]
@@ -193,50 +193,56 @@ class Oracle:
         """Output number c (0-based) of SplitMix64 seeded with `seed`."""
         return int(self.lib.oracle_splitmix64(seed & (2**64 - 1), c & (2**64 - 1)))
 
-    def local_knots(self, X, m: int, S: int, seed: int, norm: int = NORM_L2, w=None):
-        """(knots, pairs [S,2], dist [S]): quantile knots from S sampled pairs."""
+    def local_knots(self, X, m: int, S: int, seed: int, norm: int = NORM_L2, w=None, mon=None):
+        """(knots, pairs [S,2], dist [S]): quantile knots from S sampled pairs (with monotone
+        coordinates, the upper-side distance dist_up(x^a, x^b) of pair (a, b))."""
         X, w = _f64(X), _f64(w)
         N, d = X.shape
+        mon = _mon(mon, d)
         knots = np.empty(max(m, 1))
         pairs = np.empty((S, 2), np.int64)
         dist = np.empty(S)
-        n = self.lib.oracle_local_knots(_ptr(X), N, d, int(norm), _ptr(w), seed & (2**64 - 1), int(S), int(m),
+        n = self.lib.oracle_local_knots(_ptr(X), N, d, int(norm), _ptr(w), _ptr(mon), seed & (2**64 - 1), int(S), int(m),
                                         _ptr(knots), _ptr(pairs), _ptr(dist))
         if n < 0:
             raise ValueError("oracle_local_knots: bad arguments")
         return knots[:n].copy(), pairs, dist
 
-    def local_table(self, X, y, knots, norm: int = NORM_L2, w=None, nthreads: Optional[int] = None):
+    def local_table(self, X, y, knots, norm: int = NORM_L2, w=None, nthreads: Optional[int] = None, mon=None):
         """(d1 [N], F [N], Mtab [N, m+1]) for the given knots."""
         X, y, w = _f64(X), _f64(y), _f64(w)
         T = _f64(np.asarray(knots, np.float64).reshape(-1))
         N, d = X.shape
+        mon = _mon(mon, d)
         m = T.shape[0]
         d1, F = np.empty(N), np.empty(N)
         Mtab = np.empty((N, m + 1))
-        rc = self.lib.oracle_local_table(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(T), m, _ptr(d1), _ptr(F),
+        rc = self.lib.oracle_local_table(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(mon), _ptr(T), m, _ptr(d1), _ptr(F),
                                          _ptr(Mtab), nthreads or default_threads())
         if rc != 0:
             raise ValueError("oracle_local_table: bad arguments")
         return d1, F, Mtab
 
-    def local_table_rows(self, X, y, knots, rows, norm: int = NORM_L2, w=None, nthreads: Optional[int] = None):
+    def local_table_rows(self, X, y, knots, rows, norm: int = NORM_L2, w=None, nthreads: Optional[int] = None,
+                         mon=None):
         """(d1, F, Mtab) of the data rows[i] only (row i of each output)."""
         X, y, w = _f64(X), _f64(y), _f64(w)
         T = _f64(np.asarray(knots, np.float64).reshape(-1))
         rows = np.ascontiguousarray(rows, np.int64)
         N, d = X.shape
+        mon = _mon(mon, d)
         m, n = T.shape[0], rows.shape[0]
         d1, F = np.empty(n), np.empty(n)
         Mtab = np.empty((n, m + 1))
-        rc = self.lib.oracle_local_table_rows(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(T), m, _ptr(rows), n,
+        rc = self.lib.oracle_local_table_rows(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(mon), _ptr(T), m,
+                                              _ptr(rows), n,
                                               _ptr(d1), _ptr(F), _ptr(Mtab), nthreads or default_threads())
         if rc != 0:
             raise ValueError("oracle_local_table_rows: bad arguments")
         return d1, F, Mtab
 
     def evaluate_local(self, X, y, Q, knots, table, norm: int = NORM_L2, w=None, eta: float = 0.0,
-                       tau: float = 0.0, nthreads: Optional[int] = None) -> EvalResult:
+                       tau: float = 0.0, nthreads: Optional[int] = None, mon=None) -> EvalResult:
         """Envelopes with M replaced by M_k(dist).  eta > 0 (a distance error) and tau >= 0
         (a bound-value error) add hi_plus / lo_minus, the envelopes with every constant at
         M_k(t + eta), and the amb_up / amb_lo flags: some datum that an evaluation with
@@ -250,7 +256,9 @@ class Oracle:
         iu, il = np.empty(nq, np.int64), np.empty(nq, np.int64)
         au, al = np.zeros(nq, np.int8), np.zeros(nq, np.int8)
         hp, lm = np.full(nq, np.nan), np.full(nq, np.nan)
-        rc = self.lib.oracle_eval_local(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(T), T.shape[0], _ptr(d1),
+        mon = _mon(mon, d)
+        rc = self.lib.oracle_eval_local(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(mon), _ptr(T), T.shape[0],
+                                        _ptr(d1),
                                         _ptr(F), _ptr(Mtab), _ptr(Q), nq, float(eta), float(tau), _ptr(out["hi"]),
                                         _ptr(out["lo"]), _ptr(out["g"]), _ptr(iu), _ptr(il), _ptr(au), _ptr(al),
                                         _ptr(hp), _ptr(lm), nthreads or default_threads())
@@ -260,7 +268,7 @@ class Oracle:
                           lo_minus=lm, **out)
 
     def evaluate_local_k(self, X, y, Q, knots, table, k: int, wk, norm: int = NORM_L2, w=None,
-                         nthreads: Optional[int] = None) -> EvalResult:
+                         nthreads: Optional[int] = None, mon=None) -> EvalResult:
         """k > 1 neighbours with the local constants: weighted sums of the k best bounds."""
         X, y, Q, w, wk = _f64(X), _f64(y), _f64(Q), _f64(w), _f64(wk)
         T = _f64(np.asarray(knots, np.float64).reshape(-1))
@@ -269,7 +277,9 @@ class Oracle:
         nq = Q.shape[0]
         out = {key: np.empty(nq) for key in ("hi", "lo", "g")}
         iu, il = np.empty((nq, k), np.int64), np.empty((nq, k), np.int64)
-        rc = self.lib.oracle_eval_local_k(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(T), T.shape[0], _ptr(d1),
+        mon = _mon(mon, d)
+        rc = self.lib.oracle_eval_local_k(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(mon), _ptr(T), T.shape[0],
+                                          _ptr(d1),
                                           _ptr(F), _ptr(Mtab), _ptr(Q), nq, int(k), _ptr(wk), _ptr(out["hi"]),
                                           _ptr(out["lo"]), _ptr(out["g"]), _ptr(iu), _ptr(il),
                                           nthreads or default_threads())
@@ -277,9 +287,11 @@ class Oracle:
             raise ValueError("oracle_eval_local_k: bad arguments")
         return EvalResult(idx_up=iu, idx_lo=il, **out)
 
-    def local_terms(self, X, y, Q, knots, table, idx, side: int, norm: int = NORM_L2, w=None, shift: float = 0.0):
+    def local_terms(self, X, y, Q, knots, table, idx, side: int, norm: int = NORM_L2, w=None, shift: float = 0.0,
+                    mon=None):
         """y_k + M_k(t + shift) t (side +1) or y_k - M_k(t + shift) t (side -1) for k = idx[q],
-        t = dist(q, x^k); NaN where idx[q] is not a datum."""
+        t = dist(q, x^k) (with monotone coordinates dist_up for side +1, dist_lo for -1); NaN
+        where idx[q] is not a datum."""
         X, y, Q, w = _f64(X), _f64(y), _f64(Q), _f64(w)
         T = _f64(np.asarray(knots, np.float64).reshape(-1))
         d1, F, Mtab = (_f64(a) for a in table)
@@ -287,7 +299,9 @@ class Oracle:
         nq = Q.shape[0]
         ix = np.ascontiguousarray(idx, np.int64)
         out = np.empty(nq)
-        rc = self.lib.oracle_local_terms(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(T), T.shape[0], _ptr(d1),
+        mon = _mon(mon, d)
+        rc = self.lib.oracle_local_terms(_ptr(X), _ptr(y), N, d, int(norm), _ptr(w), _ptr(mon), _ptr(T), T.shape[0],
+                                         _ptr(d1),
                                          _ptr(F), _ptr(Mtab), _ptr(Q), nq, _ptr(ix), int(side), float(shift),
                                          _ptr(out))
         if rc != 0:

@@ -402,18 +402,38 @@ static int cmp_double(const void* a, const void* b) {
     return x < y ? -1 : (x > y ? 1 : 0);
 }
 
+/* Monotone coordinates (Sec. 5: values_local(query, model, k) follows the same
+ * convention as to monotonicity types as values()): mon, or NULL when no coordinate is
+ * constrained, in which case every local function takes the symmetric distance. */
+static const int8_t* mono_or_null(const int8_t* mon, int d) {
+    if (!mon) return NULL;
+    for (int i = 0; i < d; i++) if (mon[i] != 0) return mon;
+    return NULL;
+}
+
+/* The distance of the local constants between point a and datum b for the bound on side
+ * `which`: with monotone coordinates the one-sided distances of Eq. (distmon), dist_up
+ * (which = +1, (a - b)_+ on constrained coordinates) or dist_lo (which = -1, (b - a)_+);
+ * without them the symmetric distance. */
+static double local_dist(const double* a, const double* b, int d, int norm, const int8_t* mon,
+                         const double* w, int which) {
+    return mon ? oracle_dist(a, b, d, norm, mon, w, which) : sym_dist(a, b, d, norm, w);
+}
+
 /* Knots from S sampled pairs; returns the number of distinct knots (<= m), -1 on bad
  * arguments.  pairs_out (2S) and dist_out (S) receive the sample when not NULL. */
-int oracle_local_knots(const double* X, int64_t N, int d, int norm, const double* w, uint64_t seed,
-                       int64_t S, int m, double* knots_out, int64_t* pairs_out, double* dist_out) {
+int oracle_local_knots(const double* X, int64_t N, int d, int norm, const double* w, const int8_t* mon,
+                       uint64_t seed, int64_t S, int m, double* knots_out, int64_t* pairs_out, double* dist_out) {
     if (N < 1 || d < 1 || norm < 1 || norm > 3 || S < 0 || m < 0) return -1;
+    mon = mono_or_null(mon, d);
     double* D = (double*)malloc((size_t)(S > 0 ? S : 1) * sizeof(double));
     if (!D) return -1;
     int64_t kept = 0;
     for (int64_t s = 0; s < S; s++) {
         int64_t a = (int64_t)(oracle_splitmix64(seed, 2 * (uint64_t)s) % (uint64_t)N);
         int64_t b = (int64_t)(oracle_splitmix64(seed, 2 * (uint64_t)s + 1) % (uint64_t)N);
-        double dd = sym_dist(X + a * d, X + b * d, d, norm, w);
+        /* with monotone coordinates: the upper-side distance of datum b's pair with a */
+        double dd = local_dist(X + a * d, X + b * d, d, norm, mon, w, +1);
         if (pairs_out) { pairs_out[2 * s] = a; pairs_out[2 * s + 1] = b; }
         if (dist_out) dist_out[s] = dd;
         if (dd > 0.0) D[kept++] = dd;
@@ -432,36 +452,57 @@ int oracle_local_knots(const double* X, int64_t N, int d, int norm, const double
 }
 
 typedef struct {
-    const double* X; const double* y; int64_t N; int d; int norm; const double* w;
+    const double* X; const double* y; int64_t N; int d; int norm; const double* w; const int8_t* mon;
     const double* T; int m; int64_t k0, k1; const int64_t* rows;
     double *d1, *F, *Mtab;
 } ltab_job;
 
+/* Event e of the pair (k, j) for datum k's table: its distance *dd and ratio *r; returns 0
+ * when the event does not exist (distance 0).  Without monotone coordinates one event,
+ * the symmetric distance with |y^k - y^j| / d.  With them two: the upper bound of datum k
+ * at x^j needs M_k(u) u >= y^j - y^k at u = dist_up(x^j, x^k) (event 0, ratio
+ * (y^j - y^k)_+ / u), the lower bound needs M_k(l) l >= y^k - y^j at l = dist_lo(x^j, x^k)
+ * (event 1, ratio (y^k - y^j)_+ / l). */
+static int local_event(const ltab_job* J, int64_t k, int64_t j, int e, double* dd, double* r) {
+    const double* xk = J->X + k * J->d;
+    const double* xj = J->X + j * J->d;
+    if (!J->mon) {
+        *dd = sym_dist(xk, xj, J->d, J->norm, J->w);
+        if (*dd == 0.0) return 0;
+        *r = fabs(J->y[k] - J->y[j]) / *dd;
+        return 1;
+    }
+    *dd = oracle_dist(xj, xk, J->d, J->norm, J->mon, J->w, e == 0 ? +1 : -1);
+    if (*dd == 0.0) return 0;
+    double dy = e == 0 ? J->y[j] - J->y[k] : J->y[k] - J->y[j];
+    *r = (dy > 0.0 ? dy : 0.0) / *dd;
+    return 1;
+}
+
 static void* ltab_worker(void* arg) {
     ltab_job* J = (ltab_job*)arg;
-    const int d = J->d;
+    const int nev = J->mon ? 2 : 1;
     for (int64_t o = J->k0; o < J->k1; o++) {
         const int64_t k = J->rows ? J->rows[o] : o;       /* datum of output row o */
-        const double* xk = J->X + k * d;
         double d1 = INFINITY, F = 0.0;
-        for (int64_t j = 0; j < J->N; j++) {                 /* nearest distance and its ratio */
-            double dd = sym_dist(xk, J->X + j * d, d, J->norm, J->w);
-            if (dd == 0.0) continue;
-            double r = fabs(J->y[k] - J->y[j]) / dd;
-            if (dd < d1) { d1 = dd; F = r; }
-            else if (dd == d1 && r > F) F = r;
-        }
+        for (int64_t j = 0; j < J->N; j++)                   /* nearest distance and its ratio */
+            for (int e = 0; e < nev; e++) {
+                double dd, r;
+                if (!local_event(J, k, j, e, &dd, &r)) continue;
+                if (dd < d1) { d1 = dd; F = r; }
+                else if (dd == d1 && r > F) F = r;
+            }
         double* row = J->Mtab + o * (J->m + 1);
         for (int s = 0; s <= J->m; s++) row[s] = F;
-        for (int64_t j = 0; j < J->N; j++) {                 /* every segment whose knot covers d_kj */
-            double dd = sym_dist(xk, J->X + j * d, d, J->norm, J->w);
-            if (dd == 0.0) continue;
-            double r = fabs(J->y[k] - J->y[j]) / dd;
-            for (int s = 0; s <= J->m; s++) {
-                double knot = s < J->m ? J->T[s] : INFINITY;
-                if (dd <= knot && r > row[s]) row[s] = r;
+        for (int64_t j = 0; j < J->N; j++)                   /* every segment whose knot covers d_kj */
+            for (int e = 0; e < nev; e++) {
+                double dd, r;
+                if (!local_event(J, k, j, e, &dd, &r)) continue;
+                for (int s = 0; s <= J->m; s++) {
+                    double knot = s < J->m ? J->T[s] : INFINITY;
+                    if (dd <= knot && r > row[s]) row[s] = r;
+                }
             }
-        }
         J->d1[o] = d1;
         J->F[o] = F;
     }
@@ -471,9 +512,10 @@ static void* ltab_worker(void* arg) {
 /* d1, F and Mtab [.][m + 1] for knots T [m] (strictly increasing): for every datum
  * (rows = NULL, nrows = N) or for the data rows[0..nrows) only. */
 int oracle_local_table_rows(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
-                            const double* T, int m, const int64_t* rows, int64_t nrows,
+                            const int8_t* mon, const double* T, int m, const int64_t* rows, int64_t nrows,
                             double* d1, double* F, double* Mtab, int nthreads) {
     if (N < 1 || d < 1 || norm < 1 || norm > 3 || m < 0 || nrows < 0) return 1;
+    mon = mono_or_null(mon, d);
     if (rows)
         for (int64_t o = 0; o < nrows; o++) if (rows[o] < 0 || rows[o] >= N) return 1;
     if (nrows == 0) return 0;
@@ -481,7 +523,7 @@ int oracle_local_table_rows(const double* X, const double* y, int64_t N, int d, 
     pthread_t th[256];
     ltab_job jobs[256];
     for (int t = 0; t < nthreads; t++) {
-        ltab_job j = {X, y, N, d, norm, w, T, m, nrows * t / nthreads, nrows * (t + 1) / nthreads, rows,
+        ltab_job j = {X, y, N, d, norm, w, mon, T, m, nrows * t / nthreads, nrows * (t + 1) / nthreads, rows,
                       d1, F, Mtab};
         jobs[t] = j;
         pthread_create(&th[t], NULL, ltab_worker, &jobs[t]);
@@ -491,8 +533,8 @@ int oracle_local_table_rows(const double* X, const double* y, int64_t N, int d, 
 }
 
 int oracle_local_table(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
-                       const double* T, int m, double* d1, double* F, double* Mtab, int nthreads) {
-    return oracle_local_table_rows(X, y, N, d, norm, w, T, m, NULL, N, d1, F, Mtab, nthreads);
+                       const int8_t* mon, const double* T, int m, double* d1, double* F, double* Mtab, int nthreads) {
+    return oracle_local_table_rows(X, y, N, d, norm, w, mon, T, m, NULL, N, d1, F, Mtab, nthreads);
 }
 
 /* M_k(t) from datum k's table row. */
@@ -504,7 +546,7 @@ static double local_M(const double* T, int m, double d1, double F, const double*
 }
 
 typedef struct {
-    const double* X; const double* y; int64_t N; int d; int norm; const double* w;
+    const double* X; const double* y; int64_t N; int d; int norm; const double* w; const int8_t* mon;
     const double* T; int m; const double *d1, *F, *Mtab;
     const double* Q; int64_t q0, q1; double eta, tau;
     double *hi, *lo, *g; int64_t *iu, *il; int8_t *amb_up, *amb_lo; double *hi_plus, *lo_minus;
@@ -522,9 +564,11 @@ static void* leval_worker(void* arg) {
         int au = 0, al = 0;
         if (!bad) {
             for (int64_t k = 0; k < J->N; k++) {
-                double t = sym_dist(q, J->X + k * d, d, J->norm, J->w);
-                double Mk = local_M(J->T, J->m, J->d1[k], J->F[k], J->Mtab + k * (J->m + 1), t);
-                double vu = J->y[k] + Mk * t, vl = J->y[k] - Mk * t;
+                const double* row = J->Mtab + k * (J->m + 1);
+                double tu = local_dist(q, J->X + k * d, d, J->norm, J->mon, J->w, +1);
+                double tl = J->mon ? local_dist(q, J->X + k * d, d, J->norm, J->mon, J->w, -1) : tu;
+                double vu = J->y[k] + local_M(J->T, J->m, J->d1[k], J->F[k], row, tu) * tu;
+                double vl = J->y[k] - local_M(J->T, J->m, J->d1[k], J->F[k], row, tl) * tl;
                 if (vu < bu) { bu = vu; ku = k; }
                 if (vl > bl) { bl = vl; kl = k; }
             }
@@ -540,18 +584,23 @@ static void* leval_worker(void* arg) {
                 double hp = INFINITY, lm = -INFINITY;
                 for (int64_t k = 0; k < J->N; k++) {
                     const double* row = J->Mtab + k * (J->m + 1);
-                    double t = sym_dist(q, J->X + k * d, d, J->norm, J->w);
-                    double mb = local_M(J->T, J->m, J->d1[k], J->F[k], row, t + J->eta);
-                    if (J->y[k] + mb * t < hp) hp = J->y[k] + mb * t;
-                    if (J->y[k] - mb * t > lm) lm = J->y[k] - mb * t;
+                    double tu = local_dist(q, J->X + k * d, d, J->norm, J->mon, J->w, +1);
+                    double tl = J->mon ? local_dist(q, J->X + k * d, d, J->norm, J->mon, J->w, -1) : tu;
+                    double mbu = local_M(J->T, J->m, J->d1[k], J->F[k], row, tu + J->eta);
+                    double mbl = local_M(J->T, J->m, J->d1[k], J->F[k], row, tl + J->eta);
+                    if (J->y[k] + mbu * tu < hp) hp = J->y[k] + mbu * tu;
+                    if (J->y[k] - mbl * tl > lm) lm = J->y[k] - mbl * tl;
                 }
                 for (int64_t k = 0; k < J->N; k++) {
                     const double* row = J->Mtab + k * (J->m + 1);
-                    double t = sym_dist(q, J->X + k * d, d, J->norm, J->w);
-                    double mt = local_M(J->T, J->m, J->d1[k], J->F[k], row, t);
-                    double ma = local_M(J->T, J->m, J->d1[k], J->F[k], row, t - J->eta);
-                    if (J->y[k] + ma * t <= hp + J->tau && J->y[k] + mt * t > bu + J->tau) au = 1;
-                    if (J->y[k] - ma * t >= lm - J->tau && J->y[k] - mt * t < bl - J->tau) al = 1;
+                    double tu = local_dist(q, J->X + k * d, d, J->norm, J->mon, J->w, +1);
+                    double tl = J->mon ? local_dist(q, J->X + k * d, d, J->norm, J->mon, J->w, -1) : tu;
+                    double mtu = local_M(J->T, J->m, J->d1[k], J->F[k], row, tu);
+                    double mau = local_M(J->T, J->m, J->d1[k], J->F[k], row, tu - J->eta);
+                    double mtl = local_M(J->T, J->m, J->d1[k], J->F[k], row, tl);
+                    double mal = local_M(J->T, J->m, J->d1[k], J->F[k], row, tl - J->eta);
+                    if (J->y[k] + mau * tu <= hp + J->tau && J->y[k] + mtu * tu > bu + J->tau) au = 1;
+                    if (J->y[k] - mal * tl >= lm - J->tau && J->y[k] - mtl * tl < bl - J->tau) al = 1;
                 }
                 if (J->hi_plus) J->hi_plus[qi] = hp;
                 if (J->lo_minus) J->lo_minus[qi] = lm;
@@ -576,17 +625,18 @@ static void* leval_worker(void* arg) {
 /* Envelopes with the local constants; eta > 0 also fills the ambiguity flags and the
  * envelopes with every constant at its highest within eta (hi_plus, lo_minus). */
 int oracle_eval_local(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
-                      const double* T, int m, const double* d1, const double* F, const double* Mtab,
+                      const int8_t* mon, const double* T, int m, const double* d1, const double* F, const double* Mtab,
                       const double* Q, int64_t nq, double eta, double tau, double* hi, double* lo, double* g,
                       int64_t* iu, int64_t* il, int8_t* amb_up, int8_t* amb_lo, double* hi_plus,
                       double* lo_minus, int nthreads) {
     if (N < 1 || d < 1 || nq < 0 || norm < 1 || norm > 3 || m < 0) return 1;
     if (nq == 0) return 0;
+    mon = mono_or_null(mon, d);
     nthreads = clamp_threads(nthreads, nq);
     pthread_t th[256];
     leval_job jobs[256];
     for (int t = 0; t < nthreads; t++) {
-        leval_job j = {X, y, N, d, norm, w, T, m, d1, F, Mtab, Q, nq * t / nthreads, nq * (t + 1) / nthreads,
+        leval_job j = {X, y, N, d, norm, w, mon, T, m, d1, F, Mtab, Q, nq * t / nthreads, nq * (t + 1) / nthreads,
                        eta, tau, hi, lo, g, iu, il, amb_up, amb_lo, hi_plus, lo_minus};
         jobs[t] = j;
         pthread_create(&th[t], NULL, leval_worker, &jobs[t]);
@@ -599,7 +649,7 @@ int oracle_eval_local(const double* X, const double* y, int64_t N, int d, int no
  * weighted sums of the k smallest y^i + M_i(t_i) t_i and of the k largest y^i - M_i(t_i) t_i,
  * equal values in increasing data index, as in oracle_eval_k. */
 typedef struct {
-    const double* X; const double* y; int64_t N; int d; int norm; const double* w;
+    const double* X; const double* y; int64_t N; int d; int norm; const double* w; const int8_t* mon;
     const double* T; int m; const double *d1, *F, *Mtab;
     const double* Q; int64_t q0, q1; int k; const double* wk;
     double *hi, *lo, *g; int64_t *iu, *il;
@@ -614,9 +664,11 @@ static void* levalk_worker(void* arg) {
         int nu = 0, nl = 0, bad = 0;
         for (int i = 0; i < J->d; i++) if (!isfinite(q[i])) bad = 1;
         for (int64_t k = 0; k < J->N && !bad; k++) {
-            double t = sym_dist(q, J->X + k * J->d, J->d, J->norm, J->w);
-            double Mk = local_M(J->T, J->m, J->d1[k], J->F[k], J->Mtab + k * (J->m + 1), t);
-            double vu = J->y[k] + Mk * t, vl = J->y[k] - Mk * t;
+            const double* row = J->Mtab + k * (J->m + 1);
+            double tu = local_dist(q, J->X + k * J->d, J->d, J->norm, J->mon, J->w, +1);
+            double tl = J->mon ? local_dist(q, J->X + k * J->d, J->d, J->norm, J->mon, J->w, -1) : tu;
+            double vu = J->y[k] + local_M(J->T, J->m, J->d1[k], J->F[k], row, tu) * tu;
+            double vl = J->y[k] - local_M(J->T, J->m, J->d1[k], J->F[k], row, tl) * tl;
             if (nu < J->k || vu < bu[nu - 1]) {
                 int p = nu < J->k ? nu++ : J->k - 1;
                 while (p > 0 && bu[p - 1] > vu) { bu[p] = bu[p - 1]; ku[p] = ku[p - 1]; p--; }
@@ -643,16 +695,17 @@ static void* levalk_worker(void* arg) {
 }
 
 int oracle_eval_local_k(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
-                        const double* T, int m, const double* d1, const double* F, const double* Mtab,
+                        const int8_t* mon, const double* T, int m, const double* d1, const double* F, const double* Mtab,
                         const double* Q, int64_t nq, int k, const double* wk,
                         double* hi, double* lo, double* g, int64_t* iu, int64_t* il, int nthreads) {
     if (N < 1 || d < 1 || nq < 0 || norm < 1 || norm > 3 || m < 0 || k < 1 || k > 64) return 1;
     if (nq == 0) return 0;
+    mon = mono_or_null(mon, d);
     nthreads = clamp_threads(nthreads, nq);
     pthread_t th[256];
     levalk_job jobs[256];
     for (int t = 0; t < nthreads; t++) {
-        levalk_job j = {X, y, N, d, norm, w, T, m, d1, F, Mtab, Q, nq * t / nthreads, nq * (t + 1) / nthreads, k, wk,
+        levalk_job j = {X, y, N, d, norm, w, mon, T, m, d1, F, Mtab, Q, nq * t / nthreads, nq * (t + 1) / nthreads, k, wk,
                         hi, lo, g, iu, il};
         jobs[t] = j;
         pthread_create(&th[t], NULL, levalk_worker, &jobs[t]);
@@ -665,13 +718,15 @@ int oracle_eval_local_k(const double* X, const double* y, int64_t N, int d, int 
  * y - M_k(t + shift) t, t = dist(q, x^k): shift = 0 is the exact value, shift = -eta or
  * +eta the value with the constant an evaluation off by eta in distance may take. */
 int oracle_local_terms(const double* X, const double* y, int64_t N, int d, int norm, const double* w,
-                       const double* T, int m, const double* d1, const double* F, const double* Mtab,
-                       const double* Q, int64_t nq, const int64_t* idx, int side, double shift, double* out) {
+                       const int8_t* mon, const double* T, int m, const double* d1, const double* F,
+                       const double* Mtab, const double* Q, int64_t nq, const int64_t* idx, int side, double shift,
+                       double* out) {
     if (N < 1 || d < 1 || nq < 0 || norm < 1 || norm > 3 || m < 0) return 1;
+    mon = mono_or_null(mon, d);
     for (int64_t qi = 0; qi < nq; qi++) {
         int64_t k = idx[qi];
         if (k < 0 || k >= N) { out[qi] = NAN; continue; }
-        double t = sym_dist(Q + qi * d, X + k * d, d, norm, w);
+        double t = local_dist(Q + qi * d, X + k * d, d, norm, mon, w, side > 0 ? +1 : -1);
         double Mk = local_M(T, m, d1[k], F[k], Mtab + k * (m + 1), t + shift);
         out[qi] = side > 0 ? y[k] + Mk * t : y[k] - Mk * t;
     }

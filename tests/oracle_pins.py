@@ -605,6 +605,105 @@ def check_local_eval_flags(O):
         assert np.all(r.amb_up | ~half.amb_up) and np.all(r.amb_lo | ~half.amb_lo)
 
 
+def _one_sided(A, B, mon, w, norm, side):
+    """dist_up (side +1) or dist_lo (side -1) of Eq. (distmon) between every row of A and
+    every row of B, with numpy: differences mirrored where decreasing and weighted, positive
+    (side +1) or negative (side -1) parts on the constrained coordinates, |.| elsewhere."""
+    sg = np.where(np.asarray(mon) < 0, -1.0, 1.0) * (1.0 if w is None else np.asarray(w))
+    T = (A[:, None, :] - B[None, :, :]) * sg
+    con = np.asarray(mon) != 0
+    V = np.where(con, np.maximum(side * T, 0.0), np.abs(T))
+    if norm == 1:
+        return V.sum(2)
+    if norm == 2:
+        return np.sqrt((V * V).sum(2))
+    return V.max(2)
+
+
+def check_local_monotone(O):
+    """Local constants with monotone coordinates (Sec. 5: values_local follows values()'s
+    monotonicity convention).  Reading: datum k's table takes, from every other datum j, the
+    event (dist_up(x^j, x^k), (y^j - y^k)_+ / dist) that its upper bound at x^j needs and the
+    event (dist_lo(x^j, x^k), (y^k - y^j)_+ / dist) that its lower bound needs; the bounds use
+    M_k at the one-sided distance of their side.  Pins: the table against numpy events;
+    interpolation of monotone data; the envelopes non-decreasing along constrained
+    coordinates (non-increasing along decreasing ones); 1-D linear increasing data give the
+    global monotone evaluation; an all-zero mask gives the symmetric results bit for bit."""
+    rng = np.random.default_rng(31)
+    for seed, (N, d, norm, weighted) in enumerate([(60, 3, 2, False), (75, 2, 1, True), (50, 4, 3, True),
+                                                   (40, 1, 2, False)]):
+        p = W.random_problem(740 + seed, N, d, 40, norm=norm, masked=True, weighted=weighted, decreasing=True,
+                             dtype=np.float64)
+        mon = p.mon if np.any(p.mon != 0) else np.ones(d, np.int8)
+        T, _, dist = O.local_knots(p.X, 8, 600, 5 + seed, norm, w=p.w, mon=mon)
+        # the knots sample the upper-side distances of the drawn pairs
+        _, pairs, _ = O.local_knots(p.X, 1, 600, 5 + seed, norm, w=p.w)
+        want = np.array([_one_sided(p.X[a][None], p.X[b][None], mon, p.w, norm, +1)[0, 0] for a, b in pairs])
+        np.testing.assert_allclose(dist, want, rtol=1e-13, atol=1e-15)
+        # the table against numpy events, with knots away from every event distance
+        U = _one_sided(p.X, p.X, mon, p.w, norm, +1)        # U[j, k] = dist_up(x^j, x^k)
+        L = _one_sided(p.X, p.X, mon, p.w, norm, -1)
+        y = p.y
+        D = np.concatenate([U.T, L.T], 1)                   # row k: the events of datum k
+        dy = np.concatenate([np.maximum(y[None, :] - y[:, None], 0.0), np.maximum(y[:, None] - y[None, :], 0.0)], 1)
+        pos = D > 0
+        R = np.where(pos, dy / np.where(pos, D, 1.0), 0.0)
+        Tf = np.sort(rng.uniform(D[pos].min(), D.max(), 7))
+        d1 = np.where(pos, D, np.inf).min(1)
+        near = pos & (D <= d1[:, None] * (1 + 1e-12))
+        F = np.where(near, R, 0.0).max(1)
+        cols = [np.maximum(F, np.where(pos & (D <= t), R, 0.0).max(1)) for t in list(Tf) + [np.inf]]
+        od1, oF, oM = O.local_table(p.X, p.y, Tf, norm, w=p.w, mon=mon)
+        np.testing.assert_allclose(od1, d1, rtol=1e-12)
+        np.testing.assert_allclose(oF, F, rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(oM, np.stack(cols, 1), rtol=1e-12, atol=1e-300)
+        tab = O.local_table(p.X, p.y, T, norm, w=p.w, mon=mon)
+        # evaluation by the searchsorted form on the one-sided distances
+        Uq = _one_sided(p.Q, p.X, mon, p.w, norm, +1)
+        Lq = _one_sided(p.Q, p.X, mon, p.w, norm, -1)
+        r = O.evaluate_local(p.X, p.y, p.Q, T, tab, norm, w=p.w, mon=mon)
+        np.testing.assert_allclose(r.hi, (y[None, :] + _local_M_searchsorted(T, tab, Uq) * Uq).min(1), atol=1e-12)
+        np.testing.assert_allclose(r.lo, (y[None, :] - _local_M_searchsorted(T, tab, Lq) * Lq).max(1), atol=1e-12)
+        # interpolation of monotone data
+        rd = O.evaluate_local(p.X, p.y, p.X, T, tab, norm, w=p.w, mon=mon)
+        np.testing.assert_allclose(rd.hi, p.y, atol=1e-12)
+        np.testing.assert_allclose(rd.lo, p.y, atol=1e-12)
+        # monotone along the constrained coordinates
+        for i in np.nonzero(mon)[0]:
+            Qs = p.Q.copy()
+            Qs[:, i] += float(mon[i]) * rng.uniform(0.0, 0.3, len(Qs))
+            rs = O.evaluate_local(p.X, p.y, Qs, T, tab, norm, w=p.w, mon=mon)
+            assert np.all(rs.hi >= r.hi - 1e-12) and np.all(rs.lo >= r.lo - 1e-12), (seed, i)
+        # local terms take the side's distance
+        ti = rng.integers(0, N, len(p.Q))
+        np.testing.assert_allclose(O.local_terms(p.X, p.y, p.Q, T, tab, ti, +1, norm, w=p.w, mon=mon),
+                                   y[ti] + _local_M_searchsorted(T, tab, Uq)[np.arange(len(ti)), ti]
+                                   * Uq[np.arange(len(ti)), ti], atol=1e-12)
+        np.testing.assert_allclose(O.local_terms(p.X, p.y, p.Q, T, tab, ti, -1, norm, w=p.w, mon=mon),
+                                   y[ti] - _local_M_searchsorted(T, tab, Lq)[np.arange(len(ti)), ti]
+                                   * Lq[np.arange(len(ti)), ti], atol=1e-12)
+        # an all-zero mask is the symmetric method
+        z = np.zeros(d, np.int8)
+        assert np.array_equal(O.local_knots(p.X, 8, 600, 5, norm, w=p.w, mon=z)[0], O.local_knots(p.X, 8, 600, 5, norm, w=p.w)[0])
+        for a, b in zip(O.local_table(p.X, p.y, T, norm, w=p.w, mon=z), O.local_table(p.X, p.y, T, norm, w=p.w)):
+            assert np.array_equal(a, b)
+    # 1-D linear increasing data: every event ratio is the slope, so the local evaluation is
+    # the global monotone one with that M (Sec. 4.1)
+    X = rng.uniform(-1, 1, (35, 1))
+    y = 1.7 * X[:, 0]
+    Q = rng.uniform(-1.5, 1.5, (25, 1))
+    one = np.ones(1, np.int8)
+    T, _, _ = O.local_knots(X, 6, 300, 2, mon=one)
+    tab = O.local_table(X, y, T, mon=one)
+    # (ratios of differences of nearby points carry a few hundred ulps)
+    np.testing.assert_allclose(tab[2], 1.7, rtol=1e-10)
+    for norm in (1, 2, 3):
+        rl = O.evaluate_local(X, y, Q, T, tab, norm, mon=one)
+        rg = O.evaluate(X, y, Q, 1.7, norm, mon=one)
+        np.testing.assert_allclose(rl.hi, rg.hi, atol=1e-10)
+        np.testing.assert_allclose(rl.lo, rg.lo, atol=1e-10)
+
+
 def check_local_k_neighbours(O):
     """k > 1 neighbours with the local constants: the k smallest / largest of the local bound
     values built from scipy distances and the searchsorted form of M_k (stable sort); k = 1
@@ -711,4 +810,5 @@ ALL_CHECKS = [check_hand_examples, check_closed_form_1d, check_unmasked_cdist, c
               check_enclosure, check_lipschitz_monotone, check_width_bound, check_special_cases,
               check_estimate_M, check_gradient_fd, check_k_neighbours, check_splitmix64,
               check_local_hand_example, check_local_knots, check_local_table, check_local_eval,
-              check_local_terms, check_local_eval_flags, check_local_k_neighbours, check_smoothing]
+              check_local_terms, check_local_eval_flags, check_local_monotone, check_local_k_neighbours,
+              check_smoothing]

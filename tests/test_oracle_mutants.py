@@ -37,8 +37,7 @@ MUTANTS = {
     "local_no_first_segment": ("if (t <= d1) return F;", "if (t < 0) return F;", 1),
     # quantile position rounded to nearest instead of up
     "local_quantile_round": ("((int64_t)i * kept + m - 1) / m;", "((int64_t)i * kept + m / 2) / m;", 1),
-    "local_ratio_signed": ("double r = fabs(J->y[k] - J->y[j]) / dd;\n            if (dd < d1)",
-                           "double r = (J->y[k] - J->y[j]) / dd;\n            if (dd < d1)", 1),
+    "local_ratio_signed": ("*r = fabs(J->y[k] - J->y[j]) / *dd;", "*r = (J->y[k] - J->y[j]) / *dd;", 1),
     # local k neighbours: the upper list keeps the largest values
     "local_topk_upper_order": ("while (p > 0 && bu[p - 1] > vu) { bu[p] = bu[p - 1]; ku[p] = ku[p - 1]; p--; }\n                bu[p] = vu; ku[p] = k;\n            }\n            if (nl < J->k || vl > bl[nl - 1]) {\n                int p = nl < J->k ? nl++ : J->k - 1;\n                while (p > 0 && bl[p - 1] < vl) { bl[p] = bl[p - 1]; kl[p] = kl[p - 1]; p--; }\n                bl[p] = vl; kl[p] = k;\n            }\n        }\n        double hu = 0.0, hl = 0.0;\n        for (int j = 0; j < J->k; j++) {\n            hu += J->wk[j] * (j < nu ? bu[j] : NAN);\n            hl += J->wk[j] * (j < nl ? bl[j] : NAN);\n            if (J->iu) J->iu[qi * J->k + j] = j < nu ? ku[j] : -1;\n            if (J->il) J->il[qi * J->k + j] = j < nl ? kl[j] : -1;\n        }\n        if (J->hi) J->hi[qi] = hu;\n        if (J->lo) J->lo[qi] = hl;\n        if (J->g) J->g[qi] = 0.5 * (hu + hl);\n    }\n    return NULL;\n}\n\nint oracle_eval_local_k",
                                "while (p > 0 && bu[p - 1] < vu) { bu[p] = bu[p - 1]; ku[p] = ku[p - 1]; p--; }\n                bu[p] = vu; ku[p] = k;\n            }\n            if (nl < J->k || vl > bl[nl - 1]) {\n                int p = nl < J->k ? nl++ : J->k - 1;\n                while (p > 0 && bl[p - 1] < vl) { bl[p] = bl[p - 1]; kl[p] = kl[p - 1]; p--; }\n                bl[p] = vl; kl[p] = k;\n            }\n        }\n        double hu = 0.0, hl = 0.0;\n        for (int j = 0; j < J->k; j++) {\n            hu += J->wk[j] * (j < nu ? bu[j] : NAN);\n            hl += J->wk[j] * (j < nl ? bl[j] : NAN);\n            if (J->iu) J->iu[qi * J->k + j] = j < nu ? ku[j] : -1;\n            if (J->il) J->il[qi * J->k + j] = j < nl ? kl[j] : -1;\n        }\n        if (J->hi) J->hi[qi] = hu;\n        if (J->lo) J->lo[qi] = hl;\n        if (J->g) J->g[qi] = 0.5 * (hu + hl);\n    }\n    return NULL;\n}\n\nint oracle_eval_local_k", 1),
@@ -63,14 +62,24 @@ MUTANTS = {
                              "double Mk = local_M(T, m, d1[k], F[k], Mtab + k * (m + 1), t);", 1),
     # ambiguity flags: raised for every query with a possible winner (over-flagging), the
     # constants' possible drop ignored (under-flagging), hi_plus from the low constants
-    "local_flags_over": ("if (J->y[k] + ma * t <= hp + J->tau && J->y[k] + mt * t > bu + J->tau) au = 1;",
-                         "if (J->y[k] + ma * t <= hp + J->tau) au = 1;", 1),
-    "local_flags_under": ("double ma = local_M(J->T, J->m, J->d1[k], J->F[k], row, t - J->eta);",
-                          "double ma = local_M(J->T, J->m, J->d1[k], J->F[k], row, t);", 1),
-    "local_flags_lower_side_over": ("if (J->y[k] - ma * t >= lm - J->tau && J->y[k] - mt * t < bl - J->tau) al = 1;",
-                                    "if (J->y[k] - ma * t >= lm - J->tau) al = 1;", 1),
-    "local_hi_plus_low": ("double mb = local_M(J->T, J->m, J->d1[k], J->F[k], row, t + J->eta);",
-                          "double mb = local_M(J->T, J->m, J->d1[k], J->F[k], row, t - J->eta);", 1),
+    "local_flags_over": ("if (J->y[k] + mau * tu <= hp + J->tau && J->y[k] + mtu * tu > bu + J->tau) au = 1;",
+                         "if (J->y[k] + mau * tu <= hp + J->tau) au = 1;", 1),
+    "local_flags_under": ("double mau = local_M(J->T, J->m, J->d1[k], J->F[k], row, tu - J->eta);",
+                          "double mau = local_M(J->T, J->m, J->d1[k], J->F[k], row, tu);", 1),
+    "local_flags_lower_side_over": ("if (J->y[k] - mal * tl >= lm - J->tau && J->y[k] - mtl * tl < bl - J->tau) al = 1;",
+                                    "if (J->y[k] - mal * tl >= lm - J->tau) al = 1;", 1),
+    "local_hi_plus_low": ("double mbu = local_M(J->T, J->m, J->d1[k], J->F[k], row, tu + J->eta);",
+                          "double mbu = local_M(J->T, J->m, J->d1[k], J->F[k], row, tu - J->eta);", 1),
+    # monotone local constants: the events' sides swapped, |dy| instead of the side's
+    # positive part, the lower bound on the upper-side distance, knots on the lower side
+    "local_mono_event_sides": ("*dd = oracle_dist(xj, xk, J->d, J->norm, J->mon, J->w, e == 0 ? +1 : -1);",
+                               "*dd = oracle_dist(xj, xk, J->d, J->norm, J->mon, J->w, e == 0 ? -1 : +1);", 1),
+    "local_mono_ratio_abs": ("*r = (dy > 0.0 ? dy : 0.0) / *dd;", "*r = fabs(dy) / *dd;", 1),
+    "local_mono_eval_lower_side": ("double tl = J->mon ? local_dist(q, J->X + k * d, d, J->norm, J->mon, J->w, -1) : tu;\n"
+                                   "                double vu",
+                                   "double tl = tu;\n                double vu", 1),
+    "local_mono_knots_side": ("double dd = local_dist(X + a * d, X + b * d, d, norm, mon, w, +1);",
+                              "double dd = local_dist(X + a * d, X + b * d, d, norm, mon, w, -1);", 1),
     "splitmix_shift": ("z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBull;", 1),
 }
 

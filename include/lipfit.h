@@ -293,12 +293,21 @@ LIP_API lip_status lip_estimate_M_noalloc(const float* X, const float* y, int64_
  * T_m are common to all data.  dist is the symmetric weighted norm of the handle
  * (|x_i - x'_i| w_i; L1, L2 or Linf).  Pairs at distance 0 are skipped.  The result
  * interpolates the data.
+ * Handles with monotone coordinates (Sec. 5: values_local follows values()'s monotonicity
+ * convention) use the one-sided distances of Sec. 4.1 Eq. (distmon): the upper bound takes
+ * M_k(dist_up(q, x^k)) dist_up(q, x^k), the lower M_k(dist_lo(q, x^k)) dist_lo(q, x^k), and
+ * datum k's table is built from the two events each other datum j gives it -- the distance
+ * dist_up(x^j, x^k) with ratio (y^j - y^k)_+ / dist (what its upper bound needs to
+ * interpolate x^j) and dist_lo(x^j, x^k) with (y^k - y^j)_+ / dist -- in place of the pairs
+ * above (d1_k is the smallest positive event distance, F_k the largest ratio there); the
+ * knots are quantiles of the sampled pairs' dist_up(x^a, x^b).  Data consistent with the
+ * monotonicity are interpolated, and the envelopes are monotone in those coordinates.
  *
  * The table is exact: every distance and ratio that decides an entry is the IEEE double
  * result of the definition above (each operation rounded once, coordinates in order),
  * found by an FP32 screen with a rigorous error bound and FP64 re-computation of every
- * pair the bound cannot rule out.  Handles: any precision without monotone coordinates,
- * else LIP_ERR_UNSUPPORTED (FP64 handles: float or double arrays as for lip_eval).  Adding or clearing data invalidates
+ * pair the bound cannot rule out.  Handles: any precision, with or without monotone
+ * coordinates (FP64 handles: float or double arrays as for lip_eval).  Adding or clearing data invalidates
  * the table (LIP_ERR_STATE until the next fit).  N^2 work per fit: one screening scan that
  * lists, per datum, the pairs its running bounds cannot rule out (a second scan for the data
  * whose list overflows). */

@@ -10,9 +10,6 @@ constexpr size_t LOC_SMALL_BYTES = LOC_BUCKETS * sizeof(unsigned) + 2 * LOC_KNOT
                                    3 * LOC_KNOTS * sizeof(float) + sizeof(LocMeta);
 
 lip_status local_supported(const lip_model* h) {
-    if (h->C > 0)
-        return fail(LIP_ERR_UNSUPPORTED, "local Lipschitz constants use the symmetric distance; the handle has "
-                                         "monotone coordinates");
     if (h->N < 1) return fail(LIP_ERR_ARG, "the handle holds no data");
     return LIP_OK;
 }
@@ -48,6 +45,12 @@ lip_status local_buffers(lip_model* h, int64_t S, LocalParams& P) {
     P.pr = pr;
     P.norm = h->norm;
     for (int i = 0; i < D_MAX; ++i) P.w[i] = i < h->d ? h->w[i] : 1.0;
+    P.mono = h->C > 0 ? 1 : 0;
+    P.cmask = 0;
+    for (int i = 0; i < D_MAX; ++i) {
+        P.mon[i] = i < h->d ? h->mon[i] : 0;
+        if (P.mon[i] != 0) P.cmask |= 1u << i;
+    }
     P.rec = reinterpret_cast<float*>(b);
     P.mt = reinterpret_cast<float*>(b + b_rec);
     P.mt64 = reinterpret_cast<double*>(b + b_rec + b_mt);
@@ -193,7 +196,10 @@ lip_status lip_eval_local_k(lip_handle h, const void* Q, int64_t nq, int32_t k, 
     S.nq = nq;
     S.d = h->d;
     S.dp = P.dp;
-    for (int i = 0; i < D_MAX; ++i) S.w[i] = P.w[i];
+    // the query's scaling: mirrored where decreasing for monotone handles (as the records)
+    for (int i = 0; i < D_MAX; ++i) S.w[i] = (P.mono && P.mon[i] < 0) ? -P.w[i] : P.w[i];
+    S.mono = P.mono;
+    S.cmask = P.cmask;
     S.rec = P.rec;
     S.mt = P.mt;
     S.Tf = P.Tf;
@@ -211,7 +217,11 @@ lip_status lip_eval_local_k(lip_handle h, const void* Q, int64_t nq, int32_t k, 
     Mp.norm = h->norm;
     Mp.m = h->loc_m;
     Mp.nsplit = nsplit;
-    for (int i = 0; i < D_MAX; ++i) Mp.w[i] = P.w[i];
+    for (int i = 0; i < D_MAX; ++i) {
+        Mp.w[i] = P.w[i];
+        Mp.mon[i] = P.mon[i];
+    }
+    Mp.mono = P.mono;
     Mp.X0 = P.X0;
     Mp.y0 = P.y0;
     Mp.d1 = P.d1;
@@ -242,7 +252,7 @@ lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     LocalParams P;
     LIP_TRY(local_buffers(h, 0, P));
-    const int64_t gx = ceil_div(nq, (int64_t)local_queries_per_block(h->d));
+    const int64_t gx = ceil_div(nq, (int64_t)(P.mono ? local_queries_per_block_mono() : local_queries_per_block(h->d)));
     if (gx > 0x7fffffff) return fail(LIP_ERR_ARG, "nq = %lld is too large", (long long)nq);
     const int64_t tile = local_scan_tile();
     const int64_t tiles = P.npad / tile;
@@ -257,7 +267,10 @@ lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void
     S.nq = nq;
     S.d = h->d;
     S.dp = P.dp;
-    for (int i = 0; i < D_MAX; ++i) S.w[i] = P.w[i];
+    // the query's scaling: mirrored where decreasing for monotone handles (as the records)
+    for (int i = 0; i < D_MAX; ++i) S.w[i] = (P.mono && P.mon[i] < 0) ? -P.w[i] : P.w[i];
+    S.mono = P.mono;
+    S.cmask = P.cmask;
     S.rec = P.rec;
     S.mt = P.mt;
     S.Tf = P.Tf;
@@ -275,7 +288,11 @@ lip_status lip_eval_local(lip_handle h, const void* Q, int64_t nq, void* g, void
     Mp.norm = h->norm;
     Mp.m = h->loc_m;
     Mp.nsplit = nsplit;
-    for (int i = 0; i < D_MAX; ++i) Mp.w[i] = P.w[i];
+    for (int i = 0; i < D_MAX; ++i) {
+        Mp.w[i] = P.w[i];
+        Mp.mon[i] = P.mon[i];
+    }
+    Mp.mono = P.mono;
     Mp.X0 = P.X0;
     Mp.y0 = P.y0;
     Mp.d1 = P.d1;

@@ -188,6 +188,10 @@ struct LocalParams {
     int64_t N, npad;
     int d, dp, pr, norm, m;          // dp: d rounded up to 4; m: knots requested or given
     double w[D_MAX];
+    // monotone coordinates (one-sided distances; the records hold sign * w * x)
+    int mono;                        // 1 if some coordinate is constrained
+    unsigned cmask;                  // bit i: coordinate i is constrained
+    int8_t mon[D_MAX];
     int64_t S;                       // sampled pairs
     uint64_t seed;
     float* rec;                      // [npad][pr = dp + 4]: w-scaled coordinates (0-padded to dp),
@@ -215,7 +219,9 @@ struct LocalScanParams {
     int es;
     int64_t nq;
     int d, dp;
-    double w[D_MAX];
+    double w[D_MAX];                 // the query's scaling (sign * w with monotone coordinates)
+    int mono;
+    unsigned cmask;
     const float* rec;
     const float* mt;
     const float* Tf;
@@ -232,6 +238,8 @@ struct LocalMergeParams {
     int64_t nq;
     int d, norm, m, nsplit;
     double w[D_MAX];
+    int mono;
+    int8_t mon[D_MAX];
     const void* X0;
     const void* y0;
     const double* d1;
@@ -248,6 +256,7 @@ struct LocalTopkWeights {
 };
 
 int local_dim_pad(int d);
+int local_queries_per_block_mono();
 int local_topk_threads();
 cudaError_t launch_local_eval_k(int norm, int k, int K, const LocalScanParams& S, int gx, int nsplit,
                                 const LocalMergeParams& M, const LocalTopkWeights& W, cudaStream_t st);

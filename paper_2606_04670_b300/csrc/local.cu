@@ -82,6 +82,48 @@ __device__ __forceinline__ double loc_dist64(const void* A, int64_t a0, const vo
     return norm == LIP_L2 ? __dsqrt_rn(acc) : acc;
 }
 
+// Exact one-sided distance (monotone coordinates, Sec. 4.1 Eq. (distmon)) between rows a0
+// of A and b0 of B in FP64, every step one IEEE double operation in coordinate order:
+// t = a_i - b_i, negated where decreasing, times w_i; then on constrained coordinates the
+// side's part (side > 0: max(t, 0) for dist_up; side < 0: max(-t, 0) for dist_lo) and |t|
+// elsewhere; summed (L1), squared and summed then square-rooted (L2) or maxed (Linf).
+__device__ __forceinline__ double loc_mdist64(const void* A, int64_t a0, const void* B, int64_t b0, int es, int d,
+                                              int norm, const double* w, const int8_t* mon, int side) {
+    double acc = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double t = __dsub_rn(ldv(A, es, a0 + i), ldv(B, es, b0 + i));
+        if (mon[i] < 0) t = -t;
+        t = __dmul_rn(t, w[i]);
+        double v;
+        if (mon[i] != 0) v = side > 0 ? (t > 0.0 ? t : 0.0) : (t < 0.0 ? -t : 0.0);
+        else v = fabs(t);
+        if (norm == LIP_L1) acc = __dadd_rn(acc, v);
+        else if (norm == LIP_L2) acc = __dadd_rn(acc, __dmul_rn(v, v));
+        else if (v > acc) acc = v;
+    }
+    return norm == LIP_L2 ? __dsqrt_rn(acc) : acc;
+}
+
+// FP32 one-sided distances from record a to record b (both mirrored and scaled): with
+// t = a_i - b_i, du takes max(t, 0) and dl max(-t, 0) on the constrained coordinates (bits
+// of cmask), |t| elsewhere.  The error bound of the symmetric distance holds for both.
+template <int NORM, int DP>
+__device__ __forceinline__ void mdist32(const float* a, const float* b, unsigned cmask, float& du, float& dl) {
+    float au = 0.f, al = 0.f;
+#pragma unroll
+    for (int i = 0; i < DP; ++i) {
+        const float t = a[i] - b[i];
+        const bool c = (cmask >> i) & 1u;
+        const float u = c ? fmaxf(t, 0.f) : fabsf(t);
+        const float l = c ? fmaxf(-t, 0.f) : fabsf(t);
+        if (NORM == LIP_L1) { au += u; al += l; }
+        else if (NORM == LIP_L2) { au = fmaf(u, u, au); al = fmaf(l, l, al); }
+        else { au = fmaxf(au, u); al = fmaxf(al, l); }
+    }
+    du = NORM == LIP_L2 ? sqrt_approx(au) : au;
+    dl = NORM == LIP_L2 ? sqrt_approx(al) : al;
+}
+
 // #{i : T[i] < v} for a sorted 32-entry table whose unused tail is +inf.
 __device__ __forceinline__ int knot_count(const float* T, float v) {
     int c = 0;
@@ -137,7 +179,9 @@ __global__ void loc_layout_kernel(const LocalParams P) {
     float amax = 0.f;
     if (k < P.N) {
         for (int i = 0; i < P.dp; ++i) {
-            const float v = i < P.d ? (float)(P.w[i] * ldv(P.X0, P.es, k * P.d + i)) : 0.f;
+            // monotone coordinates: mirrored where decreasing (sign * w * x, the product in FP64)
+            const double sw = (P.mono && i < P.d && P.mon[i] < 0) ? -P.w[i] : P.w[i];
+            const float v = i < P.d ? (float)(sw * ldv(P.X0, P.es, k * P.d + i)) : 0.f;
             r[i] = v;
             amax = fmaxf(amax, fabsf(v));
         }
@@ -161,7 +205,10 @@ __global__ void loc_sample_kernel(const LocalParams P) {
     if (s >= P.S) return;
     const uint64_t a = splitmix64(P.seed, 2 * (uint64_t)s) % (uint64_t)P.N;
     const uint64_t b = splitmix64(P.seed, 2 * (uint64_t)s + 1) % (uint64_t)P.N;
-    const double dd = loc_dist64(P.X0, (int64_t)a * P.d, P.X0, (int64_t)b * P.d, P.es, P.d, P.norm, P.w);
+    // with monotone coordinates: the upper-side distance dist_up(x^a, x^b)
+    const double dd = P.mono ? loc_mdist64(P.X0, (int64_t)a * P.d, P.X0, (int64_t)b * P.d, P.es, P.d, P.norm, P.w,
+                                           P.mon, +1)
+                             : loc_dist64(P.X0, (int64_t)a * P.d, P.X0, (int64_t)b * P.d, P.es, P.d, P.norm, P.w);
     P.sample[s] = dd;
     if (dd > 0.0) atomicAdd(&P.meta->npos, 1);
 }
@@ -685,6 +732,264 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_pass2_kernel(const LocalParam
     if (valid) write_row<PR>(P, k, m, r);
 }
 
+// ------------------------------------------------ table with monotone coordinates
+
+// Datum k's two events with point j (Sec. 4.3 with the one-sided distances of Eq. (distmon)):
+// its upper bound at x^j needs M_k(u) u >= y^j - y^k at u = dist_up(x^j, x^k), its lower
+// bound needs M_k(l) l >= y^k - y^j at l = dist_lo(x^j, x^k).  Event e (0: upper, 1: lower)
+// has that distance and the ratio (y^j - y^k)_+ / u or (y^k - y^j)_+ / l.
+
+// Whether one event (FP32 distance d32, ratio numerator bound dy) may decide row k: the
+// symmetric screen's test (table_candidate) for that event.
+template <bool BK>
+__device__ __forceinline__ bool event_candidate(float d32, float dy, float U, const float* Lb, const unsigned* bk,
+                                                const float* Tup, float scale, const ScreenConsts& c) {
+    const float del = fmaf(c.e_rel, d32, c.e_abs);
+    const float lo = d32 - 2.f * del;
+    if (lo <= U) return true;
+    const int s = seg_dn<BK>(bk, Tup, scale, lo);
+    return dy * c.up_margin > Lb[s * LOC_THREADS] * lo * c.lo_margin;
+}
+
+// The events' FP32 distances and ratio numerators (upper bounds of the exact ones for the
+// candidate test; the raw float differences for raising the bounds).
+template <int NORM, int DP, bool Y64>
+__device__ __forceinline__ void mono_events(const float* xk, float yk, const float* xj, unsigned cmask,
+                                            const ScreenConsts& c, float (&d)[2], float (&dy)[2], float (&dyb)[2]) {
+    mdist32<NORM, DP>(xj, xk, cmask, d[0], d[1]);            // t = x^j - x^k
+    const float yj = xj[DP];
+    dy[0] = fmaxf(yj - yk, 0.f);
+    dy[1] = fmaxf(yk - yj, 0.f);
+    const float e = Y64 ? c.ey * (fabsf(yk) + fabsf(yj)) : 0.f;
+    dyb[0] = dy[0] + e;
+    dyb[1] = dy[1] + e;
+}
+
+template <int NORM, int DP, bool Y64, bool BK>
+__device__ __forceinline__ bool mono_candidate(const float* xk, float yk, const float* xj, unsigned cmask, float U,
+                                               const float* Lb, const unsigned* bk, const float* Tup, float scale,
+                                               const ScreenConsts& c) {
+    float d[2], dy[2], dyb[2];
+    mono_events<NORM, DP, Y64>(xk, yk, xj, cmask, c, d, dy, dyb);
+    return event_candidate<BK>(d[0], dyb[0], U, Lb, bk, Tup, scale, c) ||
+           event_candidate<BK>(d[1], dyb[1], U, Lb, bk, Tup, scale, c);
+}
+
+// Both exact FP64 events of the pair (k, jj) into row k.
+__device__ __forceinline__ void exact_pair_mono(const LocalParams& P, int64_t k, int64_t jj, double yk64,
+                                                const double* T64, int m, ExactRow& r) {
+    const double yj64 = ldv(P.y0, P.es, jj);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const double dd = loc_mdist64(P.X0, jj * P.d, P.X0, k * P.d, P.es, P.d, P.norm, P.w, P.mon, e == 0 ? +1 : -1);
+        if (!(dd > 0.0)) continue;
+        const double dy = e == 0 ? __dsub_rn(yj64, yk64) : __dsub_rn(yk64, yj64);
+        const double q = __ddiv_rn(dy > 0.0 ? dy : 0.0, dd);
+        if (dd < r.d1) { r.d1 = dd; r.F = q; }
+        else if (dd == r.d1 && q > r.F) r.F = q;
+        int s = 0;
+        while (s < m && T64[s] < dd) ++s;
+        r.E[s] = fmax(r.E[s], q);
+    }
+}
+
+// The N^2 screen with monotone coordinates: as loc_screen_kernel (running bounds, a
+// strided pilot, candidate lists), one point at a time, each pair tested and raised as its
+// two events.
+template <int NORM, int DP, bool Y64, bool BK>
+__global__ void __launch_bounds__(LOC_THREADS) loc_screen_mono_kernel(const LocalParams P) {
+    constexpr int PR = DP + 4;
+    const int m = P.meta->m;
+    extern __shared__ float4 sm4[];
+    float* tile = reinterpret_cast<float*>(sm4);                                 // [LOC_TILE][PR]
+    float* A = tile + LOC_TILE * PR;                                             // [m + 1][LOC_THREADS]
+    unsigned* bk = reinterpret_cast<unsigned*>(A + (m + 1) * LOC_THREADS);       // [LOC_BUCKETS] if BK
+    float* Tdn = reinterpret_cast<float*>(bk + (BK ? LOC_BUCKETS : 0));          // [LOC_KNOTS]
+    float* Tup = Tdn + LOC_KNOTS;                                                // [LOC_KNOTS]
+    const int tid = threadIdx.x;
+    const int64_t k = (int64_t)blockIdx.x * LOC_THREADS + tid;
+    const bool valid = k < P.N;
+    float xk[DP];
+    float yk = 0.f;
+#pragma unroll
+    for (int i = 0; i < DP; ++i) xk[i] = valid ? P.rec[k * PR + i] : 0.f;
+    if (valid) yk = P.rec[k * PR + DP];
+    float* Ak = A + tid;
+    for (int s = 0; s <= m; ++s) Ak[s * LOC_THREADS] = 0.f;
+    if (BK)
+        for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.bpack[b];
+    if (tid < LOC_KNOTS) {
+        Tdn[tid] = P.Tf[LOC_KNOTS + tid];
+        Tup[tid] = P.Tf[2 * LOC_KNOTS + tid];
+    }
+    __syncthreads();
+    const float scale = P.meta->scale;
+    const ScreenConsts c = screen_consts(P);
+    const CoarseKnots q = coarse_knots(Tup, m);
+    ScreenRow w;
+    w.U = INFINITY;
+    w.L0 = w.L1 = w.L2 = w.L3 = 0.f;
+    // pilot: bounds only
+    const int64_t pn = P.N >= 8 * LOC_PILOT ? LOC_PILOT : P.N / 8;
+    const int64_t stride = pn > 0 ? P.N / pn : 1;
+    for (int64_t p0 = 0; p0 < pn; p0 += LOC_TILE) {
+        const int n = (int)lmin(LOC_TILE, pn - p0);
+        __syncthreads();
+        for (int i = tid; i < n * PR; i += LOC_THREADS) tile[i] = P.rec[((p0 + i / PR) * stride) * PR + i % PR];
+        __syncthreads();
+        if (!valid) continue;
+        for (int j = 0; j < n; ++j) {
+            float d[2], dy[2], dyb[2];
+            mono_events<NORM, DP, Y64>(xk, yk, tile + j * PR, P.cmask, c, d, dy, dyb);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float del = fmaf(c.e_rel, d[e], c.e_abs);
+                if (d[e] > del)
+                    screen_raise<Y64, BK>(Ak, m, q, w, d[e] + 2.f * del, dy[e], yk, tile[j * PR + DP], bk, Tdn, scale,
+                                          c);
+            }
+        }
+    }
+    int* list = P.cand + k * LOC_CAND;
+    int cnt = 0;
+    for (int64_t j0 = 0; j0 < P.N; j0 += LOC_TILE) {
+        const int n = (int)lmin(LOC_TILE, P.N - j0);
+        __syncthreads();
+        const float4* src = reinterpret_cast<const float4*>(P.rec + j0 * PR);
+        for (int i = tid; i < n * PR / 4; i += LOC_THREADS) sm4[i] = src[i];
+        __syncthreads();
+        if (!valid) continue;
+        for (int j = 0; j < n; ++j) {
+            const float* xj = tile + j * PR;
+            float d[2], dy[2], dyb[2];
+            mono_events<NORM, DP, Y64>(xk, yk, xj, P.cmask, c, d, dy, dyb);
+            bool cand[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float del = fmaf(c.e_rel, d[e], c.e_abs);
+                const float lo = d[e] - 2.f * del;
+                const float lom = lo * c.lo_margin, dyu = dyb[e] * c.up_margin;
+                cand[e] = lo <= w.U;
+                if (!cand[e] && dyu > coarse_lb(w, q, lo) * lom) {
+                    const int sd = seg_dn<BK>(bk, Tup, scale, lo);
+                    cand[e] = dyu > Ak[sd * LOC_THREADS] * lom;
+                }
+            }
+            if (!cand[0] && !cand[1]) continue;
+            if (cnt < LOC_CAND) list[cnt] = (int)(j0 + j);
+            ++cnt;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float del = fmaf(c.e_rel, d[e], c.e_abs);
+                if (cand[e] && d[e] > del)
+                    screen_raise<Y64, BK>(Ak, m, q, w, d[e] + 2.f * del, dy[e], yk, xj[DP], bk, Tdn, scale, c);
+            }
+        }
+    }
+    if (!valid) return;
+    P.ubound[k] = w.U;
+    P.ncand[k] = cnt;
+    for (int s = 0; s < LOC_KNOTS; ++s) P.mt[k * LOC_KNOTS + s] = Ak[(s <= m ? s : m) * LOC_THREADS];
+    if (cnt > LOC_CAND) P.over[atomicAdd(&P.meta->n_over, 1)] = (int)k;
+    else atomicMax(&P.meta->max_cand, cnt);
+}
+
+// Exact rows of the data whose lists did not overflow (monotone coordinates).
+template <int NORM, int DP, bool Y64, bool BK>
+__global__ void __launch_bounds__(LOC_THREADS) loc_exact_mono_kernel(const LocalParams P) {
+    constexpr int PR = DP + 4;
+    __shared__ float Lb[LOC_KNOTS * LOC_THREADS];
+    __shared__ double T64[LOC_KNOTS];
+    __shared__ float Tup[LOC_KNOTS];
+    const int tid = threadIdx.x;
+    const int64_t k = (int64_t)blockIdx.x * LOC_THREADS + tid;
+    if (tid < LOC_KNOTS) {
+        T64[tid] = P.T64[tid];
+        Tup[tid] = P.Tf[2 * LOC_KNOTS + tid];
+    }
+    const bool valid = k < P.N && P.ncand[k] <= LOC_CAND;
+    if (valid)
+        for (int s = 0; s < LOC_KNOTS; ++s) Lb[s * LOC_THREADS + tid] = P.mt[k * LOC_KNOTS + s];
+    __syncthreads();
+    if (!valid) return;
+    float xk[DP];
+#pragma unroll
+    for (int i = 0; i < DP; ++i) xk[i] = P.rec[k * PR + i];
+    const float yk = P.rec[k * PR + DP], U = P.ubound[k];
+    const float scale = P.meta->scale;
+    const int m = P.meta->m;
+    const ScreenConsts c = screen_consts(P);
+    const double yk64 = ldv(P.y0, P.es, k);
+    const int cnt = P.ncand[k];
+    const int* list = P.cand + k * LOC_CAND;
+    ExactRow r;
+    r.d1 = INFINITY;
+    r.F = 0.0;
+    for (int s = 0; s < LOC_KNOTS; ++s) r.E[s] = 0.0;
+    for (int i = 0; i < cnt; ++i) {
+        const int64_t jj = list[i];
+        const float* xj = P.rec + jj * PR;
+        if (!mono_candidate<NORM, DP, Y64, BK>(xk, yk, xj, P.cmask, U, Lb + tid, P.bpack, Tup, scale, c)) continue;
+        exact_pair_mono(P, k, jj, yk64, T64, m, r);
+    }
+    write_row<PR>(P, k, m, r);
+}
+
+// Exact rows of the data whose lists overflowed (monotone coordinates): a full scan
+// against the final bounds.
+template <int NORM, int DP, bool Y64, bool BK>
+__global__ void __launch_bounds__(LOC_THREADS) loc_pass2_mono_kernel(const LocalParams P) {
+    constexpr int PR = DP + 4;
+    if ((int64_t)blockIdx.x * LOC_THREADS >= P.meta->n_over) return;   // the whole block
+    extern __shared__ float4 sm4[];
+    float* tile = reinterpret_cast<float*>(sm4);
+    float* Lb = tile + LOC_TILE * PR;
+    unsigned* bk = reinterpret_cast<unsigned*>(Lb + LOC_KNOTS * LOC_THREADS);
+    float* Tup = reinterpret_cast<float*>(bk + (BK ? LOC_BUCKETS : 0)) + LOC_KNOTS;
+    __shared__ double T64[LOC_KNOTS];
+    const int tid = threadIdx.x;
+    const int64_t slot = (int64_t)blockIdx.x * LOC_THREADS + tid;
+    const bool valid = slot < P.meta->n_over;
+    const int64_t k = valid ? P.over[slot] : 0;
+    float xk[DP];
+    float yk = 0.f, U = 0.f;
+#pragma unroll
+    for (int i = 0; i < DP; ++i) xk[i] = valid ? P.rec[k * PR + i] : 0.f;
+    if (valid) {
+        yk = P.rec[k * PR + DP];
+        U = P.ubound[k];
+        for (int s = 0; s < LOC_KNOTS; ++s) Lb[s * LOC_THREADS + tid] = P.mt[k * LOC_KNOTS + s];
+    }
+    if (BK)
+        for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.bpack[b];
+    if (tid < LOC_KNOTS) {
+        Tup[tid] = P.Tf[2 * LOC_KNOTS + tid];
+        T64[tid] = P.T64[tid];
+    }
+    const float scale = P.meta->scale;
+    const int m = P.meta->m;
+    const ScreenConsts c = screen_consts(P);
+    const double yk64 = valid ? ldv(P.y0, P.es, k) : 0.0;
+    ExactRow r;
+    r.d1 = INFINITY;
+    r.F = 0.0;
+    for (int s = 0; s < LOC_KNOTS; ++s) r.E[s] = 0.0;
+    for (int64_t j0 = 0; j0 < P.N; j0 += LOC_TILE) {
+        const int n = (int)lmin(LOC_TILE, P.N - j0);
+        __syncthreads();
+        const float4* src = reinterpret_cast<const float4*>(P.rec + j0 * PR);
+        for (int i = tid; i < n * PR / 4; i += LOC_THREADS) sm4[i] = src[i];
+        __syncthreads();
+        if (!valid) continue;
+        for (int j = 0; j < n; ++j) {
+            if (!mono_candidate<NORM, DP, Y64, BK>(xk, yk, tile + j * PR, P.cmask, U, Lb + tid, bk, Tup, scale, c))
+                continue;
+            exact_pair_mono(P, k, j0 + j, yk64, T64, m, r);
+        }
+    }
+    if (valid) write_row<PR>(P, k, m, r);
+}
+
 // ------------------------------------------------------------------ evaluation
 
 // The two queries a thread holds share every instruction that can be packed: their
@@ -917,6 +1222,145 @@ __global__ void __launch_bounds__(LOC_THREADS) loc_topk_scan_kernel(const LocalS
     (void)K_out;
 }
 
+// ------------------------------------------------ evaluation with monotone coordinates
+
+// The segment of a non-negative FP32 distance: the packed bucket table, or the binary
+// search over the knots when a bucket holds two of them.
+__device__ __forceinline__ int loc_segment(float t, bool bucket, const unsigned* bk, const float* Tn, float scale) {
+    return bucket ? packed_count(bk[knot_bucket(t, scale)], t) : knot_count(Tn, t);
+}
+
+// Bound values of query q (mirrored and scaled) against record xj with its table row: the
+// upper with M_j(dist_up(q, x^j)), the lower with M_j(dist_lo(q, x^j)).
+template <int NORM, int DP>
+__device__ __forceinline__ void mono_values(const float* q, const float* xj, const float* mtj, unsigned cmask,
+                                            bool bucket, const unsigned* bk, const float* Tn, float scale, float& vu,
+                                            float& vl) {
+    float tu, tl;
+    mdist32<NORM, DP>(q, xj, cmask, tu, tl);                 // t = q - x^j
+    const float y = xj[DP], d1 = xj[DP + 1], Fj = xj[DP + 2];
+    const float Mu = tu <= d1 ? Fj : mtj[loc_segment(tu, bucket, bk, Tn, scale)];
+    const float Ml = tl <= d1 ? Fj : mtj[loc_segment(tl, bucket, bk, Tn, scale)];
+    vu = fmaf(Mu, tu, y);
+    vl = fmaf(-Ml, tl, y);                                    // NaN (padding) never enters
+}
+
+// One query per thread; the running extrema with their indices (strict comparisons, so the
+// lowest index on ties), per data split.
+template <int NORM, int DP>
+__global__ void __launch_bounds__(LOC_THREADS) loc_scan_mono_kernel(const LocalScanParams P) {
+    constexpr int PR = DP + 4;
+    __shared__ float4 rec4[LOC_SCAN_TILE * PR / 4];
+    __shared__ float4 mt4[LOC_SCAN_TILE * LOC_KNOTS / 4];
+    __shared__ unsigned bk[LOC_BUCKETS];
+    __shared__ float Tn[LOC_KNOTS];
+    const float* rec = reinterpret_cast<const float*>(rec4);
+    const float* mt = reinterpret_cast<const float*>(mt4);
+    const int tid = threadIdx.x;
+    const int split = blockIdx.y;
+    const int64_t qi = (int64_t)blockIdx.x * LOC_THREADS + tid;
+    float q[DP];
+#pragma unroll
+    for (int i = 0; i < DP; ++i) q[i] = (qi < P.nq && i < P.d) ? (float)(P.w[i] * ldv(P.Q, P.es, qi * P.d + i)) : 0.f;
+    for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.bpack[b];
+    if (tid < LOC_KNOTS) Tn[tid] = P.Tf[tid];
+    const float scale = P.scale;
+    const bool bucket = P.bucket_ok != 0;
+    float bu = INFINITY, bl = -INFINITY;
+    int iu = -1, il = -1;
+    const int64_t j_begin = (int64_t)split * P.points_per_split;
+    const int64_t j_end = lmin(j_begin + P.points_per_split, P.npad);
+    for (int64_t j0 = j_begin; j0 < j_end; j0 += LOC_SCAN_TILE) {
+        __syncthreads();
+        const float4* rs = reinterpret_cast<const float4*>(P.rec + j0 * PR);
+        for (int i = tid; i < LOC_SCAN_TILE * PR / 4; i += LOC_THREADS) rec4[i] = rs[i];
+        const float4* ms = reinterpret_cast<const float4*>(P.mt + j0 * LOC_KNOTS);
+        for (int i = tid; i < LOC_SCAN_TILE * LOC_KNOTS / 4; i += LOC_THREADS) mt4[i] = ms[i];
+        __syncthreads();
+        for (int j = 0; j < LOC_SCAN_TILE; ++j) {
+            float vu, vl;
+            mono_values<NORM, DP>(q, rec + j * PR, mt + j * LOC_KNOTS, P.cmask, bucket, bk, Tn, scale, vu, vl);
+            if (vu < bu) { bu = vu; iu = (int)(j0 + j); }
+            if (vl > bl) { bl = vl; il = (int)(j0 + j); }
+        }
+    }
+    if (qi >= P.nq) return;
+    PartialRec<float> rr;
+    rr.vu = bu; rr.iu = iu; rr.vl = bl; rr.il = il;
+    static_cast<PartialRec<float>*>(P.partial)[(int64_t)split * P.nq + qi] = rr;
+}
+
+// k > 1 neighbours with monotone coordinates: the sorted K-lists of loc_topk_scan_kernel
+// over the one-sided bound values.
+template <int NORM, int DP, int K>
+__global__ void __launch_bounds__(LOC_THREADS) loc_topk_scan_mono_kernel(const LocalScanParams P) {
+    constexpr int PR = DP + 4;
+    __shared__ float4 rec4[LOC_SCAN_TILE * PR / 4];
+    __shared__ float4 mt4[LOC_SCAN_TILE * LOC_KNOTS / 4];
+    __shared__ unsigned bk[LOC_BUCKETS];
+    __shared__ float Tn[LOC_KNOTS];
+    const float* rec = reinterpret_cast<const float*>(rec4);
+    const float* mt = reinterpret_cast<const float*>(mt4);
+    const int tid = threadIdx.x;
+    const int split = blockIdx.y;
+    const int64_t qi = (int64_t)blockIdx.x * LOC_THREADS + tid;
+    float q[DP];
+#pragma unroll
+    for (int i = 0; i < DP; ++i) q[i] = (qi < P.nq && i < P.d) ? (float)(P.w[i] * ldv(P.Q, P.es, qi * P.d + i)) : 0.f;
+    for (int b = tid; b < LOC_BUCKETS; b += LOC_THREADS) bk[b] = P.bpack[b];
+    if (tid < LOC_KNOTS) Tn[tid] = P.Tf[tid];
+    const float scale = P.scale;
+    const bool bucket = P.bucket_ok != 0;
+    float bu[K], bl[K];
+    int ku[K], kl[K];
+#pragma unroll
+    for (int e = 0; e < K; ++e) { bu[e] = INFINITY; bl[e] = -INFINITY; ku[e] = -1; kl[e] = -1; }
+    const int64_t j_begin = (int64_t)split * P.points_per_split;
+    const int64_t j_end = lmin(j_begin + P.points_per_split, P.npad);
+    for (int64_t j0 = j_begin; j0 < j_end; j0 += LOC_SCAN_TILE) {
+        __syncthreads();
+        const float4* rs = reinterpret_cast<const float4*>(P.rec + j0 * PR);
+        for (int i = tid; i < LOC_SCAN_TILE * PR / 4; i += LOC_THREADS) rec4[i] = rs[i];
+        const float4* ms = reinterpret_cast<const float4*>(P.mt + j0 * LOC_KNOTS);
+        for (int i = tid; i < LOC_SCAN_TILE * LOC_KNOTS / 4; i += LOC_THREADS) mt4[i] = ms[i];
+        __syncthreads();
+        for (int j = 0; j < LOC_SCAN_TILE; ++j) {
+            float vu, vl;
+            mono_values<NORM, DP>(q, rec + j * PR, mt + j * LOC_KNOTS, P.cmask, bucket, bk, Tn, scale, vu, vl);
+            const int idx = (int)(j0 + j);
+            if (vu < bu[K - 1]) {
+                int kk = idx;
+#pragma unroll
+                for (int p = 0; p < K; ++p)
+                    if (vu < bu[p]) {
+                        const float tv = bu[p]; bu[p] = vu; vu = tv;
+                        const int tk = ku[p]; ku[p] = kk; kk = tk;
+                    }
+            }
+            if (vl > bl[K - 1]) {
+                int kk = idx;
+#pragma unroll
+                for (int p = 0; p < K; ++p)
+                    if (vl > bl[p]) {
+                        const float tv = bl[p]; bl[p] = vl; vl = tv;
+                        const int tk = kl[p]; kl[p] = kk; kk = tk;
+                    }
+            }
+        }
+    }
+    if (qi >= P.nq) return;
+    float* pv = static_cast<float*>(P.partial);
+    int* pk = reinterpret_cast<int*>(pv + (int64_t)gridDim.y * P.nq * 2 * K);
+    const int64_t base = ((int64_t)split * P.nq + qi) * 2 * K;
+#pragma unroll
+    for (int e = 0; e < K; ++e) {
+        pv[base + e] = bu[e];
+        pk[base + e] = ku[e];
+        pv[base + K + e] = bl[e];
+        pk[base + K + e] = kl[e];
+    }
+}
+
 __device__ __forceinline__ double local_M64(const LocalMergeParams& P, int64_t k, double t);
 
 // The k best over the splits by (value, index), their exact FP64 values with the exact
@@ -956,7 +1400,9 @@ __global__ void loc_topk_merge_kernel(const LocalMergeParams P, int k, int K, Lo
         for (int e = 0; e < k; ++e) {
             ek[e] = sk[e];
             if (sk[e] < 0) { all = false; ev[e] = 0.0; continue; }
-            const double t = loc_dist64(P.Q, q0, P.X0, (int64_t)sk[e] * P.d, P.es, P.d, P.norm, P.w);
+            const double t = P.mono ? loc_mdist64(P.Q, q0, P.X0, (int64_t)sk[e] * P.d, P.es, P.d, P.norm, P.w, P.mon,
+                                                  side == 0 ? +1 : -1)
+                                    : loc_dist64(P.Q, q0, P.X0, (int64_t)sk[e] * P.d, P.es, P.d, P.norm, P.w);
             const double yy = ldv(P.y0, P.es, sk[e]), Mt = __dmul_rn(local_M64(P, sk[e], t), t);
             ev[e] = side == 0 ? __dadd_rn(yy, Mt) : __dsub_rn(yy, Mt);
         }
@@ -1006,8 +1452,11 @@ __global__ void loc_merge_kernel(const LocalMergeParams P) {
         hi = lo = __longlong_as_double(0x7ff8000000000000ll);
         iu = il = -1;
     } else {
-        const double tu = loc_dist64(P.Q, q0, P.X0, (int64_t)iu * P.d, P.es, P.d, P.norm, P.w);
-        const double tl = loc_dist64(P.Q, q0, P.X0, (int64_t)il * P.d, P.es, P.d, P.norm, P.w);
+        // with monotone coordinates the upper bound's datum at dist_up, the lower's at dist_lo
+        const double tu = P.mono ? loc_mdist64(P.Q, q0, P.X0, (int64_t)iu * P.d, P.es, P.d, P.norm, P.w, P.mon, +1)
+                                 : loc_dist64(P.Q, q0, P.X0, (int64_t)iu * P.d, P.es, P.d, P.norm, P.w);
+        const double tl = P.mono ? loc_mdist64(P.Q, q0, P.X0, (int64_t)il * P.d, P.es, P.d, P.norm, P.w, P.mon, -1)
+                                 : loc_dist64(P.Q, q0, P.X0, (int64_t)il * P.d, P.es, P.d, P.norm, P.w);
         hi = __dadd_rn(ldv(P.y0, P.es, iu), __dmul_rn(local_M64(P, iu, tu), tu));
         lo = __dsub_rn(ldv(P.y0, P.es, il), __dmul_rn(local_M64(P, il, tl), tl));
     }
@@ -1026,6 +1475,7 @@ int local_record_floats(int d) { return local_dim_pad(d) + 4; }
 int64_t local_pad(int64_t N) { return (N + LOC_TILE - 1) / LOC_TILE * LOC_TILE; }
 int local_scan_tile() { return LOC_SCAN_TILE; }
 int local_queries_per_block(int d) { return LOC_THREADS * 2 * local_scan_groups(local_dim_pad(d)); }
+int local_queries_per_block_mono() { return LOC_THREADS; }
 
 cudaError_t launch_local_layout(const LocalParams& P, cudaStream_t st) {
     const unsigned blocks = (unsigned)((P.npad + 255) / 256);
@@ -1053,7 +1503,21 @@ cudaError_t launch_local_knots(const LocalParams& P, bool sampled, cudaStream_t 
 }
 
 template <int NORM, int DP, bool Y64, bool BK>
+static cudaError_t table_run_mono(const LocalParams& P, int m, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((P.N + LOC_THREADS - 1) / LOC_THREADS);
+    loc_screen_mono_kernel<NORM, DP, Y64, BK><<<blocks, LOC_THREADS, table_smem(DP + 4, m + 1, BK), st>>>(P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    loc_exact_mono_kernel<NORM, DP, Y64, BK><<<blocks, LOC_THREADS, 0, st>>>(P);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    loc_pass2_mono_kernel<NORM, DP, Y64, BK><<<blocks, LOC_THREADS, table_smem(DP + 4, LOC_KNOTS, BK), st>>>(P);
+    return cudaGetLastError();
+}
+
+template <int NORM, int DP, bool Y64, bool BK>
 static cudaError_t table_run(const LocalParams& P, int m, cudaStream_t st) {
+    if (P.mono) return table_run_mono<NORM, DP, Y64, BK>(P, m, st);
     const unsigned blocks = (unsigned)((P.N + LOC_THREADS - 1) / LOC_THREADS);
     loc_screen_kernel<NORM, DP, Y64, BK><<<blocks, LOC_THREADS, table_smem(DP + 4, m + 1, BK), st>>>(P);
     cudaError_t e = cudaGetLastError();
@@ -1092,6 +1556,10 @@ cudaError_t launch_local_table(const LocalParams& P, bool bucket_ok, int m, cuda
 
 template <int NORM, int DP>
 static void scan_shape(const LocalScanParams& S, dim3 grid, bool bucket, cudaStream_t st) {
+    if (S.mono) {
+        loc_scan_mono_kernel<NORM, DP><<<grid, LOC_THREADS, 0, st>>>(S);
+        return;
+    }
     constexpr int G = local_scan_groups(DP);
     if (bucket) loc_scan_kernel<NORM, DP, true, G><<<grid, LOC_THREADS, 0, st>>>(S);
     else loc_scan_kernel<NORM, DP, false, G><<<grid, LOC_THREADS, 0, st>>>(S);
@@ -1110,6 +1578,12 @@ static void scan_norm(const LocalScanParams& S, dim3 grid, bool bucket, cudaStre
 
 template <int NORM, int DP>
 static void topk_shape(int K, const LocalScanParams& S, dim3 grid, cudaStream_t st) {
+    if (S.mono) {
+        if (K == 2) loc_topk_scan_mono_kernel<NORM, DP, 2><<<grid, LOC_THREADS, 0, st>>>(S);
+        else if (K == 4) loc_topk_scan_mono_kernel<NORM, DP, 4><<<grid, LOC_THREADS, 0, st>>>(S);
+        else loc_topk_scan_mono_kernel<NORM, DP, 8><<<grid, LOC_THREADS, 0, st>>>(S);
+        return;
+    }
     if (K == 2) loc_topk_scan_kernel<NORM, DP, 2><<<grid, LOC_THREADS, 0, st>>>(S, K);
     else if (K == 4) loc_topk_scan_kernel<NORM, DP, 4><<<grid, LOC_THREADS, 0, st>>>(S, K);
     else loc_topk_scan_kernel<NORM, DP, 8><<<grid, LOC_THREADS, 0, st>>>(S, K);

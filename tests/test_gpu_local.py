@@ -49,6 +49,14 @@ def _cases():
 CASES = _cases()
 
 
+def _one_sided(A, B, mon, w, norm, side):
+    """dist_up (side +1) / dist_lo (side -1) of Eq. (distmon) between the rows of A and B."""
+    sg = np.where(np.asarray(mon) < 0, -1.0, 1.0) * (1.0 if w is None else np.asarray(w))
+    V = (A[:, None, :] - B[None, :, :]) * sg
+    V = np.where(np.asarray(mon) != 0, np.maximum(side * V, 0.0), np.abs(V))
+    return V.sum(2) if norm == 1 else (np.sqrt((V * V).sum(2)) if norm == 2 else V.max(2))
+
+
 def _check_eval(p, X, y, Q, T, tab, out, label):
     """Every query, both bounds (the upper shown; the lower is its mirror):
     * the returned bound is the exact FP64 value of the returned datum, rounded once;
@@ -69,9 +77,10 @@ def _check_eval(p, X, y, Q, T, tab, out, label):
     mmax = float(tab[2].max()) if tab[2].size else 0.0
     scale = float(np.abs(y).max()) + mmax * dm + 1e-30
     tau = max(FP32_TOL * scale, 2.0 * (mmax * eta + 2.0 ** -21 * scale))
-    r = O.evaluate_local(X, y, Q, T, tab, p.norm, w=p.w, eta=eta, tau=tau)
-    tu = O.local_terms(X, y, Q, T, tab, iu, +1, p.norm, w=p.w)
-    tl = O.local_terms(X, y, Q, T, tab, il, -1, p.norm, w=p.w)
+    mon = p.mon
+    r = O.evaluate_local(X, y, Q, T, tab, p.norm, w=p.w, eta=eta, tau=tau, mon=mon)
+    tu = O.local_terms(X, y, Q, T, tab, iu, +1, p.norm, w=p.w, mon=mon)
+    tl = O.local_terms(X, y, Q, T, tab, il, -1, p.norm, w=p.w, mon=mon)
     # the returned values are the exact FP64 values of the returned data, rounded once
     assert np.array_equal(hi.astype(np.float32), tu.astype(np.float32)), label
     assert np.array_equal(lo.astype(np.float32), tl.astype(np.float32)), label
@@ -79,8 +88,8 @@ def _check_eval(p, X, y, Q, T, tab, out, label):
     # never better than the exact envelope
     assert np.all(tu >= r.hi - 1e-12 * scale) and np.all(tl <= r.lo + 1e-12 * scale), label
     # a datum an FP32 evaluation can pick (every query)
-    tu_low = O.local_terms(X, y, Q, T, tab, iu, +1, p.norm, w=p.w, shift=-eta)
-    tl_low = O.local_terms(X, y, Q, T, tab, il, -1, p.norm, w=p.w, shift=-eta)
+    tu_low = O.local_terms(X, y, Q, T, tab, iu, +1, p.norm, w=p.w, shift=-eta, mon=mon)
+    tl_low = O.local_terms(X, y, Q, T, tab, il, -1, p.norm, w=p.w, shift=-eta, mon=mon)
     assert np.all(tu_low <= r.hi_plus + tau), (label, np.max(tu_low - r.hi_plus), tau)
     assert np.all(tl_low >= r.lo_minus - tau), (label, np.max(r.lo_minus - tl_low), tau)
     # unflagged queries: within tau of the exact envelope
@@ -89,14 +98,20 @@ def _check_eval(p, X, y, Q, T, tab, out, label):
     assert np.all(np.abs(tl - r.lo)[sl] <= tau), (label, np.abs(tl - r.lo)[sl].max(), tau)
     # flags only where a constant can change within eta
     if len(Q) * len(X) <= 8_000_000:
-        D = cdist(Q * (1.0 if p.w is None else np.asarray(p.w)), X * (1.0 if p.w is None else np.asarray(p.w)),
-                  METRIC[p.norm])
         d1, F, Mtab = tab
+
         def mk(Dm):
             seg = np.searchsorted(np.asarray(T), Dm, side="left")
             return np.where(Dm <= d1[None, :], F[None, :], Mtab[np.arange(len(d1))[None, :], seg])
-        near = np.any(mk(D - eta) < mk(D + eta), axis=1)
-        assert np.all(near | ~(r.amb_up | r.amb_lo)), label
+        if mon is None or not np.any(mon):
+            D = cdist(Q * (1.0 if p.w is None else np.asarray(p.w)), X * (1.0 if p.w is None else np.asarray(p.w)),
+                      METRIC[p.norm])
+            Ds = (D, D)
+        else:
+            Ds = (_one_sided(Q, X, mon, p.w, p.norm, +1), _one_sided(Q, X, mon, p.w, p.norm, -1))
+        near_u = np.any(mk(Ds[0] - eta) < mk(Ds[0] + eta), axis=1)
+        near_l = np.any(mk(Ds[1] - eta) < mk(Ds[1] + eta), axis=1)
+        assert np.all(near_u | ~r.amb_up) and np.all(near_l | ~r.amb_lo), label
     return r
 
 
@@ -186,11 +201,10 @@ def test_edge_cases():
         m.compute_local_lipschitz(4, 10, 1)
     assert e.value.status == LIP_ERR_ARG
     m.close()
-    # monotone handles are not supported
+    # monotone handles with a table: the one-sided distances (test_monotone_local_constants)
     m = _model(X, y, 2, mon=[1, 0])
-    with pytest.raises(LipError) as e:
-        m.compute_local_lipschitz(4, 10, 1)
-    assert e.value.status == LIP_ERR_UNSUPPORTED
+    T = m.compute_local_lipschitz(4, 10, 1)
+    assert np.array_equal(T, O.local_knots(_f64(X), 4, 10, 1, 2, mon=np.array([1, 0], np.int8))[0])
     m.close()
 
 
@@ -358,4 +372,42 @@ def test_local_k_neighbours(k):
         assert np.mean(err[clear] <= tol) >= 0.995, (key, err[clear].max(), tol)
     same = np.all(out["idx_up"].cpu().numpy() == r.idx_up, axis=1)
     assert same.mean() > 0.95, same.mean()
+    m.close()
+
+
+MONO_CASES = [W.random_problem(290 + 7 * n + d, N, d, 300, norm=n, masked=True, weighted=(d % 2 == 0),
+                               decreasing=(n != 2))
+              for n, (N, d) in zip((1, 2, 3, 2, 1), [(900, 3), (1500, 4), (700, 2), (1100, 8), (600, 20)])]
+
+
+@pytest.mark.parametrize("case", range(len(MONO_CASES)),
+                         ids=lambda i: f"L{MONO_CASES[i].norm}-N{MONO_CASES[i].N}-d{MONO_CASES[i].d}")
+def test_monotone_local_constants(case):
+    """Monotone coordinates (one-sided distances of Eq. (distmon)): knots and table bit for
+    bit against the oracle, the evaluation by validity and the envelope (both bounds with
+    their own one-sided distance), interpolation at the data, and k > 1 neighbours."""
+    p = MONO_CASES[case]
+    if not np.any(p.mon):
+        p.mon[0] = 1
+    m = _model(p.X, p.y, p.norm, w=p.w, mon=p.mon)
+    X, y, Q = _f64(p.X), _f64(p.y), _f64(p.Q)
+    T = m.compute_local_lipschitz(14, 5000, 11 + case)
+    To, _, _ = O.local_knots(X, 14, 5000, 11 + case, p.norm, w=p.w, mon=p.mon)
+    assert np.array_equal(T, To), (T, To)
+    tab = _table(m)
+    for a, b in zip(tab, O.local_table(X, y, T, p.norm, w=p.w, mon=p.mon)):
+        assert np.array_equal(a, b), np.abs(a - b).max()
+    _check_eval(p, X, y, Q, T, tab, m.eval_local(torch.as_tensor(p.Q).cuda()), f"mono {case}")
+    outd = m.eval_local(torch.as_tensor(p.X).cuda())
+    _check_eval(p, X, y, X, T, tab, outd, f"mono {case} @data")
+    assert np.all(np.abs(outd["g"].cpu().numpy() - y) <= 1e-6 * (np.abs(y).max() + 1))
+    k = 3
+    wk = np.array([0.5, 0.3, 0.2])
+    outk = m.eval_local_k(torch.as_tensor(p.Q).cuda(), k, wk)
+    rk = O.evaluate_local_k(X, y, Q, T, tab, k, wk, p.norm, w=p.w, mon=p.mon)
+    tol = FP32_TOL * (float(np.abs(y).max()) + float(tab[2].max()) * diam(X, Q, p.norm, p.w))
+    for key in ("hi", "lo"):
+        err = np.abs(outk[key].cpu().numpy().astype(np.float64) - rk[key])
+        assert np.mean(err <= tol) >= 0.99, (key, err.max(), tol)
+    m.check()
     m.close()

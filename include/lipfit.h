@@ -497,19 +497,26 @@ LIP_API void lip_batch_free(lip_batch b);
 
 /* ---------------------------------------------------------------- launch shape */
 
-/* Launch shape of lip_eval on this handle (what the autotuner sets).  The results do not
- * depend on it.
+/* Launch shape of lip_eval on this handle (what the autotuner sets).  tile_groups, splits
+ * and variants 0 / 1 do not change the results.
  *   tile_groups  groups of 4 data points staged per shared-memory tile: 8, 16, 32 or 64
  *                (0 keeps the current value).  Ignored by the generic kernel.
  *   splits       number of slices of the data scanned by separate thread blocks and
  *                merged afterwards; 0 = chosen per call to fill the GPU in whole waves.
  *   variant      scan kernel variant: 0 holds the default number of queries per thread,
  *                1 half as many (more resident warps); -1 keeps the current one.
- *                Ignored by the generic kernel.  For tensor-core handles: 0 runs the
+ *                2 / 3 and 4 / 5 are 0 / 1 with one in eight (2, 3) or one in sixteen
+ *                (4, 5) of the square roots of the L2 scans with monotone coordinates
+ *                (two roots per pair, which load the special-function unit) computed on
+ *                the FMA pipe (Lomont's seed and three Newton steps, a few ulps); their
+ *                FP32 values differ in the last bits, so the selected index can differ
+ *                where two bound values are that close (the bounds returned are the FP64
+ *                values of the selected data either way); other shapes run 0 / 1.
+ *                Ignored by the generic kernel.  For tensor-core handles (0 or 1): 0 runs the
  *                tensor-core epilogue on 16 warps, 1 on 8.  For LIP_FP64 handles: 0 (the
  *                default) scans a float copy of the layout and recomputes in FP64 only
  *                the pairs within the FP32 error bound of the extremum, 1 scans in FP64
- *                throughout; both return the FP64 envelopes.
+ *                throughout (0 or 1); both return the FP64 envelopes.
  * LIP_ERR_ARG for other values. */
 LIP_API lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits, int32_t variant);
 
@@ -575,6 +582,11 @@ LIP_API const char* lip_version(void);
  * LIP_ERR_OOM through the usual path, without calling cudaMalloc.  n = 0 turns this off.
  * Allocations after the failing one succeed again.  LIP_ERR_ARG for n < 0. */
 LIP_API lip_status lip_debug_fail_alloc(int64_t n);
+
+/* The square root the exact scan's variants 2-5 compute on the FMA pipe (lip_set_tuning),
+ * element by element: out[i] = sqrt(s[i]) for device float arrays of n entries (tests;
+ * asynchronous on `stream`).  The paper has no counterpart. */
+LIP_API lip_status lip_debug_sqrt_fma(const float* s, float* out, int64_t n, void* stream);
 
 /* Fault injection for the exact FP32 scan kernel of handle h (FP32 handles whose shape has
  * an exact instantiation; other kernels ignore it):

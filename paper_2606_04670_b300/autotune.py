@@ -32,7 +32,8 @@ def _bucket(n: int) -> int:
 
 def eval_key(model, nq: int) -> str:
     c = 0 if model.mon is None else int((model.mon != 0).sum())
-    return f"eval/norm{model.norm}/C{c}/U{model.d - c}/prec{model.precision}/N2^{_bucket(model.N)}/Q2^{_bucket(nq)}"
+    # "eval2": the exact FP32 kernels have six variants (the FMA-pipe square roots)
+    return f"eval2/norm{model.norm}/C{c}/U{model.d - c}/prec{model.precision}/N2^{_bucket(model.N)}/Q2^{_bucket(nq)}"
 
 
 def load_cache(path: Optional[str] = None) -> Dict:
@@ -70,8 +71,13 @@ def _time(fn, reps: int = 3, warm: int = 1) -> float:
 
 
 def tune_eval(model, Q, tiles: Iterable[int] = (8, 16, 32, 64), splits: Iterable[int] = (0, 1, 2, 3, 4, 6, 8, 12, 16),
-              variants: Iterable[int] = (0, 1), cache: Optional[Dict] = None, reps: int = 3) -> Dict:
-    """Time lip_eval on `model` for every (variant, tile_groups, splits); apply the fastest."""
+              variants: Optional[Iterable[int]] = None, cache: Optional[Dict] = None, reps: int = 3) -> Dict:
+    """Time lip_eval on `model` for every (variant, tile_groups, splits); apply the fastest.
+    The variants default to the six of FP32 handles (queries per thread x the share of
+    square roots on the FMA pipe) and to 0, 1 for FP64 and tensor-core handles."""
+    from .lipfit import LIP_FP32
+    if variants is None:
+        variants = range(6) if model.precision == LIP_FP32 else (0, 1)
     key = eval_key(model, Q.shape[0])
     if cache is not None and key in cache:
         best = cache[key]

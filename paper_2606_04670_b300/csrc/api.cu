@@ -1041,7 +1041,10 @@ lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits, int
     if (tile_groups != 0 && tile_groups != 8 && tile_groups != 16 && tile_groups != 32 && tile_groups != 64)
         return fail(LIP_ERR_ARG, "tile_groups = %d is not 0, 8, 16, 32 or 64", tile_groups);
     if (splits < 0 || splits > 4096) return fail(LIP_ERR_ARG, "splits = %d is outside [0, 4096]", splits);
-    if (variant < -1 || variant >= SCAN_VARIANTS) return fail(LIP_ERR_ARG, "variant = %d is not -1, 0 or 1", variant);
+    if (variant < -1 || variant >= SCAN_VARIANTS)
+        return fail(LIP_ERR_ARG, "variant = %d is outside [-1, %d]", variant, SCAN_VARIANTS - 1);
+    if ((h->tc || h->esize == 8) && variant > 1)
+        return fail(LIP_ERR_ARG, "variant = %d: tensor-core and FP64 handles take 0 or 1", variant);
     DeviceGuard gd(h->device);
     if (tile_groups) h->tile_groups = tile_groups;
     h->splits = splits;
@@ -1095,7 +1098,7 @@ lip_status lip_autotune(lip_handle h, const void* Q, int64_t nq, int32_t reps, i
     double best = 1e300;
     int32_t btg = keep_tg, bsp = keep_sp, bv = keep_v;
     const int tiles[] = {8, 16, 32, 64}, splits[] = {0, 1, 2, 3, 4, 6, 8, 12, 16};
-    const int nv = h->tc || h->esize == 8 || h->exact ? 2 : 1;
+    const int nv = h->tc || h->esize == 8 ? 2 : (h->exact ? SCAN_VARIANTS : 1);
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         s = fail(LIP_ERR_CUDA, "cudaEventCreate failed");
     } else {
@@ -1197,6 +1200,14 @@ const char* lip_version(void) { return "0.1.0 sm_103a"; }
 lip_status lip_debug_fail_alloc(int64_t n) {
     if (n < 0) return fail(LIP_ERR_ARG, "n = %lld < 0", (long long)n);
     g_fail_alloc_countdown.store(n, std::memory_order_relaxed);
+    return LIP_OK;
+}
+
+lip_status lip_debug_sqrt_fma(const float* s, float* out, int64_t n, void* stream) {
+    if (n < 0) return fail(LIP_ERR_ARG, "n = %lld < 0", (long long)n);
+    if (n > 0 && (!s || !out)) return fail(LIP_ERR_ARG, "s or out is NULL");
+    CUDA_TRY(launch_sqrt_fma(s, out, n, static_cast<cudaStream_t>(stream)));
+    count_launches(n > 0 ? 1 : 0);
     return LIP_OK;
 }
 

@@ -73,6 +73,7 @@ cudaError_t launch_to_float(const double* a, int64_t n, float* out, cudaStream_t
 cudaError_t launch_screen64(int norm, const Screen64Params& P, int gx, int gy, cudaStream_t st);
 
 cudaError_t launch_merge(int elem_bytes, const MergeParams& P, cudaStream_t st);
+cudaError_t launch_sqrt_fma(const float* s, float* out, int64_t n, cudaStream_t st);
 
 // data-sharded evaluation (shard.cu)
 cudaError_t launch_shard_keys(int elem_bytes, const void* partial, int nsplit, int64_t nq, const void* Q, int d,

@@ -77,10 +77,13 @@ __device__ __forceinline__ float max_reduce(const float (&v)[K]) {
 // coordinates, each duplicated into both halves of a float2).  vu = y + M dist_up;
 // vl = y - M dist_lo, except with AUX where vl = (y - Sx) - M dist_up (the caller adds
 // sum_{j<C} q_j).  Exactly the same instruction sequence is used by the scan and by the
-// rescan that recovers the index, so the values compare bitwise.
+// rescan that recovers the index, so the values compare bitwise.  fs (L2 with constrained
+// coordinates): the lower distances of the group's second pair of points take the FMA-pipe
+// square root (sqrt_fma2) instead of the special-function unit, which the two roots per
+// pair otherwise saturate.
 template <int NORM, int C, int U>
 __device__ __forceinline__ void group_values(const float2 (&qq)[C + U], const float4 (&x)[ExactShape<NORM, C, U>::NCH],
-                                             float (&vu)[4], float (&vl)[4]) {
+                                             float (&vu)[4], float (&vl)[4], bool fs = false) {
     constexpr int D = C + U;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -108,7 +111,7 @@ __device__ __forceinline__ void group_values(const float2 (&qq)[C + U], const fl
                     else { su = fma2(p, p, su); sl = fma2(n, n, sl); }
                 }
                 du = make_float2(sqrt_approx(su.x), sqrt_approx(su.y));
-                dl = make_float2(sqrt_approx(sl.x), sqrt_approx(sl.y));
+                dl = (fs && h == 1) ? sqrt_fma2(sl) : make_float2(sqrt_approx(sl.x), sqrt_approx(sl.y));
             } else {
                 du = make_float2(sqrt_approx(s0.x), sqrt_approx(s0.y));
                 dl = du;
@@ -201,8 +204,10 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
 // One block's share of the scan: queries [qblock * 128 R, +128 R) against data split
 // `split` of P.  Used by the one-launch-per-data-set kernel below and by the batched
 // persistent kernel (which calls it once per work item and re-initialises the
-// barriers between items: reinit = true invalidates them first).
-template <int NORM, int C, int U, int R>
+// barriers between items: reinit = true invalidates them first).  FSR > 0: query rows
+// r with r % FSR == FSR - 1 take group_values' FMA-pipe square roots (one in 4 FSR of the
+// pair's roots).
+template <int NORM, int C, int U, int R, int FSR = 0>
 __device__ __forceinline__ void scan_block(const ScanParams& P, int64_t qblock, int split, float4* tiles,
                                            uint64_t* bars, bool reinit) {
     using S = ExactShape<NORM, C, U>;
@@ -269,7 +274,7 @@ __device__ __forceinline__ void scan_block(const ScanParams& P, int64_t qblock, 
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     float vu[4], vl[4];
-                    group_values<NORM, C, U>(qq[r], x, vu, vl);
+                    group_values<NORM, C, U>(qq[r], x, vu, vl, FSR > 0 && r % FSR == FSR - 1);
                     mu[r] = min3f(min3f(mu[r], vu[0], vu[1]), vu[2], vu[3]);
                     ml[r] = max3f(max3f(ml[r], vl[0], vl[1]), vl[2], vl[3]);
                 }
@@ -325,7 +330,7 @@ __device__ __forceinline__ void scan_block(const ScanParams& P, int64_t qblock, 
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) x[ch] = __ldg(hot + g * NCH + ch);
                 float vu[4], vl[4];
-                group_values<NORM, C, U>(qq[r], x, vu, vl);
+                group_values<NORM, C, U>(qq[r], x, vu, vl, FSR > 0 && r % FSR == FSR - 1);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     if (side == 0 && iu < 0 && vu[e] == mu[r]) iu = (int)(g * 4 + e);
@@ -338,12 +343,12 @@ __device__ __forceinline__ void scan_block(const ScanParams& P, int64_t qblock, 
     }
 }
 
-template <int NORM, int C, int U, int R>
+template <int NORM, int C, int U, int R, int FSR = 0>
 __global__ void __launch_bounds__(SCAN_THREADS)
 scan_exact_kernel(const ScanParams P) {
     extern __shared__ __align__(128) float4 tiles[];   // SCAN_STAGES * tile_groups * NCH
     __shared__ __align__(8) uint64_t bars[SCAN_STAGES];
-    scan_block<NORM, C, U, R>(P, blockIdx.x, blockIdx.y, tiles, bars, false);
+    scan_block<NORM, C, U, R, FSR>(P, blockIdx.x, blockIdx.y, tiles, bars, false);
 }
 
 // ------------------------------------------------------------------ generic scan
@@ -560,10 +565,18 @@ __host__ __device__ constexpr int rows_for_dim(int D) { return D <= 4 ? 8 : (D <
 
 // Launch variants of the exact kernel (chosen by lip_set_tuning / the autotuner):
 // variant 0 holds rows_for_dim(D) queries per thread, variant 1 half as many (fewer
-// registers, more resident warps, more shared-memory broadcasts per pair).
-constexpr int SCAN_VARIANTS = 2;
+// registers, more resident warps, more shared-memory broadcasts per pair).  Variants 2-5
+// (L2 scans with constrained coordinates, the two square roots per pair) are 0 and 1 with
+// one in eight (2, 3) or one in sixteen (4, 5) of the roots on the FMA pipe; other shapes
+// take them as 0 and 1.
+constexpr int SCAN_VARIANTS = 6;
 __host__ __device__ constexpr int rows_for_variant(int D, int v) {
-    return v == 0 ? rows_for_dim(D) : (rows_for_dim(D) / 2 > 0 ? rows_for_dim(D) / 2 : 1);
+    return (v & 1) == 0 ? rows_for_dim(D) : (rows_for_dim(D) / 2 > 0 ? rows_for_dim(D) / 2 : 1);
+}
+__host__ __device__ constexpr int fsr_for_variant(int v) { return v >= 4 ? 4 : (v >= 2 ? 2 : 0); }
+// Shapes with the FMA-pipe square-root variants: L2 with 1..6 coordinates, some constrained.
+__host__ __device__ constexpr bool fma_sqrt_shape(int norm, int C, int U) {
+    return norm == LIP_L2 && C >= 1 && C + U <= 6;
 }
 
 // Exact instantiations: every (C, U) with 1 <= C + U <= 10, and unconstrained D up to 16

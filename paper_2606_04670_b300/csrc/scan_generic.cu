@@ -78,6 +78,21 @@ cudaError_t launch_build_hot(int elem_bytes, const HotParams& P, cudaStream_t st
     return cudaGetLastError();
 }
 
+// The FMA-pipe square root of the exact kernels' variants 2-5, element by element (tests).
+__global__ void sqrt_fma_kernel(const float* s, float* out, int64_t n) {
+    const int64_t i = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= n) return;
+    const float2 r = sqrt_fma2(make_float2(s[i], i + 1 < n ? s[i + 1] : 0.f));
+    out[i] = r.x;
+    if (i + 1 < n) out[i + 1] = r.y;
+}
+
+cudaError_t launch_sqrt_fma(const float* s, float* out, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    sqrt_fma_kernel<<<blocks_for((n + 1) / 2, 256), 256, 0, st>>>(s, out, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pad_hot(int elem_bytes, void* hot, int64_t k0, int64_t k1, int nch, int dl, cudaStream_t st) {
     const int64_t n = k1 - k0;
     if (n <= 0) return cudaSuccess;

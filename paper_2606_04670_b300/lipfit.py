@@ -110,6 +110,7 @@ def _load():
         "lip_shard_finish": [H, i64, P, P, P, P, P, P, P, P, P, P],
         "lip_estimate_M_part": [H, i32, i32, P, P],
         "lip_debug_fail_alloc": [i64],
+        "lip_debug_sqrt_fma": [P, P, i64, P],
         "lip_debug_scan_fault": [H, ctypes.c_uint64, i32],
     }
     for name, args in sig.items():
@@ -392,6 +393,11 @@ def lip_version():
 def lip_debug_fail_alloc(n):
     """Tests only: the n-th device allocation from now on fails (0 = off)."""
     return _lib.lip_debug_fail_alloc(n)
+
+
+def lip_debug_sqrt_fma(s_ptr, out_ptr, n, stream=0):
+    """Tests only: the FMA-pipe square root of the scan variants 2-5, element by element."""
+    return _lib.lip_debug_sqrt_fma(s_ptr, out_ptr, n, stream)
 
 
 def lip_debug_scan_fault(h, wait_limit_ns, skip_tile):

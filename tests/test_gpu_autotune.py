@@ -17,7 +17,9 @@ def test_tune_eval_keeps_results_and_caches(tmp_path):
     Q = torch.as_tensor(p.Q).cuda()
     ref = {k: v.cpu().numpy() for k, v in m.eval(Q).items()}
     cache = {}
-    rec = AT.tune_eval(m, Q, tiles=(8, 32), splits=(0, 1, 4), cache=cache, reps=2)
+    # variants 0 / 1 (queries per thread) with tiles and splits never change a result; the
+    # FMA-pipe square-root variants 2-5 are checked against the oracle in test_gpu_eval
+    rec = AT.tune_eval(m, Q, tiles=(8, 32), splits=(0, 1, 4), variants=(0, 1), cache=cache, reps=2)
     assert not rec["cached"] and rec["ms"] <= rec["default_ms"] + 1e-9 and rec["candidates"] == 12
     assert m.tuning()["tile_groups"] == rec["tile_groups"]
     got = {k: v.cpu().numpy() for k, v in m.eval(Q).items()}
@@ -66,3 +68,25 @@ def test_c_abi_autotune_keeps_results():
         for k in ref:
             np.testing.assert_array_equal(got[k], ref[k])
         m.close()
+
+
+def test_tune_eval_sweeps_the_square_root_variants(oracle_mod):
+    """FP32 handles sweep all six variants by default; the tuned evaluation still matches the
+    oracle within the FP32 tolerance."""
+    import torch
+
+    from paper_2606_04670_b300 import autotune as AT
+    from paper_2606_04670_b300.lipfit import LipFit
+    from parity import FP32_TOL, compare
+    p = W.monotone_d4(norm=W.NORM_L2, n_data=12_000, n_query=30_000)
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, mon=p.mon)
+    Q = torch.as_tensor(p.Q).cuda()
+    rec = AT.tune_eval(m, Q, tiles=(32,), splits=(0, 4), cache={}, reps=2)
+    assert rec["candidates"] == 12 and 0 <= rec["variant"] < 6
+    got = {k: v.cpu().numpy() for k, v in m.eval(Q).items()}
+    m.close()
+    sub = np.arange(0, p.nq, 15)
+    ps = p.sub_queries(p.nq)
+    ps.Q = p.Q[sub]
+    orc = oracle_mod.evaluate(p.X, p.y, ps.Q, p.M, p.norm, mon=p.mon)
+    compare(ps, {k: v[sub] for k, v in got.items()}, orc, FP32_TOL, "tuned")

@@ -219,3 +219,42 @@ def test_full_size_monotone_d4_sampled(oracle_mod, norm):
     # properties that hold at any size, on every query: lo <= g <= hi (M is a valid bound)
     assert np.all(r["lo"] <= r["g"]) and np.all(r["g"] <= r["hi"])
     assert r["idx_up"].min() >= 0 and r["idx_up"].max() < p.N
+
+
+def test_fma_pipe_square_root():
+    """The FMA-pipe square root (Lomont's seed, three Newton steps) against FP64 sqrt: within
+    4 ulps for normal inputs, exactly 0 at 0, NaN for NaN, and within 1.1e-19 below FLT_MIN."""
+    import torch
+
+    from paper_2606_04670_b300 import lipfit as L
+    rng = np.random.default_rng(0)
+    s = np.concatenate([np.exp(rng.uniform(np.log(1.2e-38), np.log(3e38), 200_000)), rng.random(50_000),
+                        np.array([0.0, 1.0, 4.0, 2.0, 1e-42, 1e-39, 3.4e38, np.nan])]).astype(np.float32)
+    sd = torch.as_tensor(s).cuda()
+    out = torch.empty_like(sd)
+    assert L.lip_debug_sqrt_fma(sd.data_ptr(), out.data_ptr(), len(s), torch.cuda.current_stream().cuda_stream) == 0
+    r = out.cpu().numpy().astype(np.float64)
+    ref = np.sqrt(s.astype(np.float64))
+    normal = s >= np.float32(1.17549435e-38)
+    rel = np.abs(r[normal] - ref[normal]) / ref[normal]
+    assert rel.max() <= 4 * 2.0 ** -24, rel.max()
+    assert r[s == 0].tolist() == [0.0] and np.isnan(r[np.isnan(s)]).all()
+    tiny = (s > 0) & ~normal
+    assert np.all(np.abs(r[tiny] - ref[tiny]) <= 1.1e-19)
+
+
+@pytest.mark.parametrize("variant", [2, 3, 4, 5])
+@pytest.mark.parametrize("d,seed", [(4, 0), (3, 1), (6, 2)])
+def test_fma_sqrt_variants_vs_oracle(oracle_mod, variant, d, seed):
+    """Variants 2-5 (a share of the L2 scan's square roots on the FMA pipe) against the oracle
+    on monotone shapes, and independent of tiles and splits bit for bit."""
+    p = W.random_problem(450 + 3 * d + seed, 6_007, d, 2_111, norm=W.NORM_L2, masked=True, weighted=(seed == 1),
+                         decreasing=(seed == 2))
+    if not np.any(p.mon):
+        p.mon[0] = 1
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm, mon=p.mon, w=p.w)
+    a = gpu_eval(p, variant=variant)
+    compare(p, a, orc, FP32_TOL, f"variant {variant} d={d}")
+    b = gpu_eval(p, variant=variant, splits=5, tile_groups=16)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])

@@ -466,6 +466,7 @@ struct TcScanParams {
     int64_t ntiles;
     TcRec* rec;            // [nq positions][2 bounds][TC_MAX_PARTS column slices]
     unsigned* err;
+    int wave;              // CTAs resident at once (one per SM): the sweep direction's period
 };
 
 // Candidate list append with compaction when full (entries that can no longer qualify
@@ -509,6 +510,14 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t qt = blockIdx.x;
     const int64_t T = P.ntiles;
+    // Sweep direction: the CTAs of one wave (one per SM) read the data tiles in increasing
+    // order, the next wave's in decreasing order, and so on.  A CTA of the next wave starts
+    // when one of the previous wave finishes, at the end of the sweep the others are still
+    // reading, so its first tiles are the ones most recently brought into L2 (with one
+    // direction it would start from the tiles read longest ago).  Tile order does not change
+    // the results: the candidate chunks are collected in any order and the rescreen takes
+    // the exact extremum with the lowest index.
+    const bool rev = P.wave > 0 && ((qt / P.wave) & 1) != 0;
 
     if (threadIdx.x == 0) {
         mbar_init(&a_full, 1);
@@ -545,7 +554,8 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                     break;
                 }
                 mbar_expect_tx(&b_full[s], TILE_BYTES);
-                bulk_g2s(sB + (size_t)s * STAGE_BYTES, P.btiles + t * (int64_t)TILE_BYTES, TILE_BYTES, &b_full[s]);
+                const int64_t tt = rev ? T - 1 - t : t;
+                bulk_g2s(sB + (size_t)s * STAGE_BYTES, P.btiles + tt * (int64_t)TILE_BYTES, TILE_BYTES, &b_full[s]);
             }
             // wait (bounded) for the copies still in flight before leaving
             const int64_t first = t > ST ? t - ST : 0;
@@ -667,7 +677,7 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                 for (int h = 0; h < 2; ++h) {
                     if (!take[h]) continue;
                     const int col = col0 + h * 32;
-                    const int chunk = (int)(t * TC_CHUNKS + col / 32);
+                    const int chunk = (int)((rev ? T32 - 1 - t : t) * TC_CHUNKS + col / 32);
                     // four interleaved partial extrema per chunk keep the dependent chains short
                     float cu[4], cl[4];
 #pragma unroll
@@ -1054,6 +1064,13 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     S.ntiles = ntiles;
     S.rec = static_cast<TcRec*>(rec);
     S.err = err;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
+                                                       cudaSuccess)
+            S.wave = sms;                                    // one CTA per SM (all of TMEM each)
+        cudaGetLastError();
+    }
     if (ev0 && (e = cudaEventRecord(ev0, st)) != cudaSuccess) return e;     // the scan kernel alone
     e = parts == 2 ? launch_tc_scan_parts<2>(K, fmt, S, nqt, st) : launch_tc_scan_parts<4>(K, fmt, S, nqt, st);
     if (e != cudaSuccess) return e;

@@ -75,9 +75,10 @@ typedef enum {
      * FP16: each operand scaled by a power of two (from the data's bounding box) and split
      * into two fp16 pieces, three kind::f16 products; a query farther than 2^14 / 2^7 times
      * the box's half-diagonal from its centre in some coordinate (outside the fp16 range)
-     * goes to the fallback.  lip_eval synchronises the stream once; the returned bounds are
-     * the exact FP64 envelopes (see the kernel's error bound), with the plain FP32 scan as
-     * fallback for queries with too many near-ties. */
+     * goes to the fallback.  The returned bounds are the exact FP64 envelopes rounded once
+     * (see the kernel's error bound); queries with too many near-ties go to a device-side
+     * fallback (an FP32 screen of all points, then FP64 on the survivors) that gives the
+     * same exact envelopes.  lip_eval does not synchronise on these handles either. */
 } lip_precision;
 
 /* Largest dimension d accepted by lip_fit / lip_reserve. */
@@ -544,9 +545,10 @@ LIP_API lip_status lip_get_tuning(lip_handle h, int32_t* tile_groups, int32_t* s
 LIP_API lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, void* ev_after_scan);
 
 /* Tensor-core handles (LIP_TC_*): number of queries of the last lip_eval whose candidate
- * lists overflowed (or, for LIP_TC_FP16, that lay outside the fp16 range) and were
- * recomputed by the plain FP32 scan (0 when the tensor-core form and
- * its exact rescreen settled every query); -1 for a NULL handle. */
+ * lists overflowed (or, for LIP_TC_FP16, that lay outside the fp16 range) and were settled
+ * by the device-side fallback (0 when the tensor-core form and its exact rescreen settled
+ * every query, and for other handles); -1 for a NULL handle or a CUDA error.  The count
+ * stays on the device during lip_eval: this call synchronises the device to read it. */
 LIP_API int64_t lip_last_fallback(lip_handle h);
 
 /* Number of kernels this library has launched in this process (all handles). */

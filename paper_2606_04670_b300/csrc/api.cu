@@ -132,7 +132,6 @@ void free_model(lip_model* h) {
     h->io.release();
     h->tc_q.release();
     h->tc_order.release();
-    h->tc_fb.release();
     if (h->tc_btiles) cudaFree(h->tc_btiles);
     if (h->tc_maxbits) cudaFree(h->tc_maxbits);
     h->loc_buf.release();
@@ -440,9 +439,9 @@ lip_status eval_plain(lip_model* h, const void* Q, int64_t nq, void* g, void* lo
 }
 
 // Tensor-core form: prepare the data tiles if the data or M changed, then build the
-// query tiles, scan on the tensor cores, rescreen candidates in FP64, and send the
-// queries whose candidate lists overflowed through the plain scan.  Synchronises once
-// to read the overflow count.
+// query tiles, scan on the tensor cores, rescreen candidates in FP64, and settle the
+// queries whose candidate lists overflowed with the device-side fallback passes (their
+// count stays on the device: no synchronisation).
 lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* iu, int32_t* il,
                    cudaStream_t st) {
     const int d = h->d;
@@ -469,45 +468,24 @@ lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, v
     const int64_t nqt = ceil_div(nq, 128);
     const size_t a_b = round_up((int64_t)(nqt * tc_a_bytes_for(d, h->tc_fmt)), 256), eps_b = round_up(nq * 16, 256),
                  rec_b = round_up((int64_t)(nq * tc_rec_bytes()), 256), list_b = round_up(nq * 4 + 4, 256),
-                 qp_b = round_up(nq * 4, 256);
-    LIP_TRY(h->tc_q.ensure(a_b + eps_b + rec_b + list_b + qp_b + spatial_order_scratch(nq), "tensor-core query scratch"));
+                 qp_b = round_up(nq * 4, 256), fb_b = round_up((int64_t)tc_fallback_state_bytes(nq), 256);
+    h->tc_fb_count = nullptr;
+    LIP_TRY(h->tc_q.ensure(a_b + eps_b + rec_b + list_b + qp_b + fb_b + spatial_order_scratch(nq),
+                           "tensor-core query scratch"));
     char* base = static_cast<char*>(h->tc_q.p);
     int* fb_list = reinterpret_cast<int*>(base + a_b + eps_b + rec_b);
     int* fb_count = fb_list + nq;
     TcQueryOrder QO{};
     QO.qperm = reinterpret_cast<int*>(base + a_b + eps_b + rec_b + list_b);
-    QO.scratch = base + a_b + eps_b + rec_b + list_b + qp_b;
+    void* fb_state = base + a_b + eps_b + rec_b + list_b + qp_b;
+    QO.scratch = base + a_b + eps_b + rec_b + list_b + qp_b + fb_b;
     CUDA_TRY(tc_eval_launch(static_cast<const float*>(Q), nq, d, scale, h->N, h->tc_maxbits, h->tc_btiles,
                             ntiles, base, reinterpret_cast<float4*>(base + a_b), base + a_b + eps_b, h->w, h->M,
                             static_cast<const float*>(h->X0), static_cast<const float*>(h->y0), static_cast<float*>(g),
-                            static_cast<float*>(lo), static_cast<float*>(hi), iu, il, fb_count, fb_list, h->status,
-                            h->tc_variant, h->tc_fmt, O, QO, h->ev_scan0, h->ev_scan1, st));
-    count_launches(3 + spatial_order_launches());
-    int nfb = 0;
-    CUDA_TRY(cudaMemcpyAsync(&nfb, fb_count, sizeof nfb, cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-    h->last_fallback = nfb;
-    if (nfb > 0) {
-        const size_t q_b = round_up((int64_t)nfb * d * 4, 256), v_b = round_up((int64_t)nfb * 4, 256);
-        LIP_TRY(h->tc_fb.ensure(q_b + 5 * v_b, "tensor-core fallback scratch"));
-        char* fb = static_cast<char*>(h->tc_fb.p);
-        float* fq = reinterpret_cast<float*>(fb);
-        float* fg = reinterpret_cast<float*>(fb + q_b);
-        float* flo = reinterpret_cast<float*>(fb + q_b + v_b);
-        float* fhi = reinterpret_cast<float*>(fb + q_b + 2 * v_b);
-        int32_t* fiu = reinterpret_cast<int32_t*>(fb + q_b + 3 * v_b);
-        int32_t* fil = reinterpret_cast<int32_t*>(fb + q_b + 4 * v_b);
-        CUDA_TRY(tc_gather(static_cast<const float*>(Q), d, fb_list, nfb, fq, st));
-        cudaEvent_t e0 = h->ev_scan0, e1 = h->ev_scan1;
-        h->ev_scan0 = h->ev_scan1 = nullptr;
-        const lip_status s = eval_plain(h, fq, nfb, fg, flo, fhi, fiu, fil, st);
-        h->ev_scan0 = e0;
-        h->ev_scan1 = e1;
-        LIP_TRY(s);
-        CUDA_TRY(tc_scatter(fb_list, nfb, fg, flo, fhi, fiu, fil, static_cast<float*>(g), static_cast<float*>(lo),
-                            static_cast<float*>(hi), iu, il, st));
-        count_launches(2);
-    }
+                            static_cast<float*>(lo), static_cast<float*>(hi), iu, il, fb_count, fb_list, fb_state,
+                            h->status, h->tc_variant, h->tc_fmt, O, QO, h->ev_scan0, h->ev_scan1, st));
+    count_launches(7 + spatial_order_launches());
+    h->tc_fb_count = fb_count;          // read back by lip_last_fallback only
     return LIP_OK;
 }
 
@@ -1161,7 +1139,17 @@ lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, void* ev_af
 
 uint64_t lip_kernel_launches(void) { return launches_total(); }
 
-int64_t lip_last_fallback(lip_handle h) { return h ? h->last_fallback : -1; }
+int64_t lip_last_fallback(lip_handle h) {
+    if (!h) return -1;
+    if (!h->tc_fb_count) return 0;
+    int n = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(&n, h->tc_fb_count, sizeof n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return n;
+}
 
 void lip_free(lip_handle h) { free_model(h); }
 

@@ -123,12 +123,11 @@ cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, 
 cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scale, int64_t N,
                            const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float4* qc,
                            void* rec, const double* w, double M, const float* X0, const float* y0, float* g, float* lo,
-                           float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, unsigned* err,
-                           int variant, int fmt, const TcDataOrder& O, const TcQueryOrder& QO, cudaEvent_t ev0,
-                           cudaEvent_t ev1, cudaStream_t st);
-cudaError_t tc_gather(const float* Q, int d, const int* list, int n, float* out, cudaStream_t st);
-cudaError_t tc_scatter(const int* list, int n, const float* g, const float* lo, const float* hi, const int32_t* iu,
-                       const int32_t* il, float* G, float* LO, float* HI, int32_t* IU, int32_t* IL, cudaStream_t st);
+                           float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, void* fb_state,
+                           unsigned* err, int variant, int fmt, const TcDataOrder& O, const TcQueryOrder& QO,
+                           cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t st);
+// Scratch of the device-side fallback for nq queries (fb_state above).
+size_t tc_fallback_state_bytes(int64_t nq);
 
 struct TopkParams {
     const void* Q;

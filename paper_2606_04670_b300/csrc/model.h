@@ -127,9 +127,9 @@ struct lip_model {
     int64_t tc_ntiles_cap = 0;
     char* tc_btiles = nullptr;
     unsigned* tc_maxbits = nullptr;    // [2] max |x^|, max |y| (float bits)
-    Scratch tc_q, tc_fb;
+    Scratch tc_q;
     Scratch tc_order;                  // the data's spatial order and position-ordered copies
-    int64_t last_fallback = 0;
+    int* tc_fb_count = nullptr;         // device count of the last tensor-core lip_eval's fallback
     // local Lipschitz constants (Sec. 4.3), valid until the data change
     bool loc_valid = false;
     bool loc_bucket = true;            // the evaluation's bucket lookup applies (else binary search)

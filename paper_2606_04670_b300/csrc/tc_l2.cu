@@ -748,8 +748,11 @@ struct TcRescreenParams {
     const TcRec* rec;
     float *g, *lo, *hi;
     int32_t *idx_up, *idx_lo;
-    int* fb_count;          // queries sent to the fallback scan
+    int* fb_count;          // queries sent to the fallback (device-side count)
     int* fb_list;
+    unsigned* fb_ext;       // [nq][4] the fallback's accumulators, initialised when a query is listed
+    unsigned long long* fb_best;    // [nq][2]
+    int* fb_idx;            // [nq][2]
 };
 
 __device__ __forceinline__ double tc_dist64(const TcRescreenParams& P, const float* q, const float* x) {
@@ -812,7 +815,14 @@ __global__ void __launch_bounds__(TC_RS_THREADS) tc_rescreen_kernel(const TcResc
         for (int b = 0; b < 2; ++b)
             for (int h = 0; h < P.parts; ++h) over = over || R[b * TC_MAX_PARTS + h].n < 0;
         if (finite && over) {
-            if (lane == 0) P.fb_list[atomicAdd(P.fb_count, 1)] = (int)qi;
+            if (lane == 0) {
+                const int slot = atomicAdd(P.fb_count, 1);
+                P.fb_list[slot] = (int)qi;
+                P.fb_ext[4 * slot + 0] = P.fb_ext[4 * slot + 2] = 0xffffffffu;   // min keys: none yet
+                P.fb_ext[4 * slot + 1] = P.fb_ext[4 * slot + 3] = 0u;            // max errors: 0
+                P.fb_best[2 * slot] = P.fb_best[2 * slot + 1] = ~0ull;
+                P.fb_idx[2 * slot] = P.fb_idx[2 * slot + 1] = 0x7fffffff;
+            }
             active = false;
         }
     }
@@ -939,24 +949,165 @@ __global__ void __launch_bounds__(TC_RS_THREADS) tc_rescreen_kernel(const TcResc
     if (P.idx_lo) P.idx_lo[qi] = il;
 }
 
-// Gather the fallback queries into a compact block, and scatter their results back.
-__global__ void tc_gather_kernel(const float* Q, int d, const int* list, int n, float* out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)n * d) return;
-    out[i] = Q[(int64_t)list[i / d] * d + i % d];
+// --------------------------------------------------------------- device-side fallback
+// Queries whose candidate lists overflowed (or, in the fp16 form, lie outside the fp16
+// range) are listed by the rescreen in fb_list / fb_count and settled here without the
+// host: the grid has a fixed shape and reads the count on the device, so lip_eval on a
+// tensor-core handle never waits for the GPU and can be captured in a CUDA graph.  Three
+// passes over all N points, each bound handled as a minimum (H_lo as the minimum of
+// M |q - x| - y, which negates exactly):
+//   pass 0: the FP32 minimum v32 of each bound and the largest FP32 error bound
+//           err(p) = (d + 10) 2^-24 (r + |y|) (the rescreen's bound), by atomic min / max
+//           of order-preserving keys, so the result does not depend on the order;
+//   pass 1: every point with v32 <= min + 2 max err is evaluated in FP64 (the exact
+//           minimiser p* and its ties pass: v32(p*) <= v64(p*) + err <= v64(e) + err <=
+//           v32(e) + 2 err for the FP32 minimiser e); atomic min of the FP64 value's key;
+//   pass 2: the lowest data index whose FP64 value equals that minimum.
+// A work item is a group of TC_FB_QG listed queries and a chunk of TC_FB_CHUNK points, so
+// a chunk is read once per group.  The results are the exact FP64 envelopes, rounded once,
+// like the rescreen's.
+constexpr int TC_FB_THREADS = 256, TC_FB_QG = 4, TC_FB_CHUNK = 2048;
+
+struct TcFallbackParams {
+    const float* Q;
+    int d;
+    const float* X0;        // [N][d] the data in index order
+    const float* y0;
+    int64_t N;
+    double M;
+    double w[D_MAX];
+    float sc[D_MAX];        // (float)(M w_j), as in the rescreen
+    bool unit_w;
+    const int* fb_count;
+    const int* fb_list;
+    unsigned* ext;                  // [slot][4]: f2ord(min up), max err up, f2ord(min -lo), max err lo
+    unsigned long long* best;       // [slot][2]: d2ord of the FP64 minima
+    int* idx;                       // [slot][2]
+    float *g, *lo, *hi;
+    int32_t *idx_up, *idx_lo;
+};
+
+__device__ __forceinline__ unsigned long long d2ord(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord2d(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+__device__ __forceinline__ float ord2f(unsigned k) {
+    return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k);
 }
 
-__global__ void tc_scatter_kernel(const int* list, int n, const float* g, const float* lo, const float* hi,
-                                  const int32_t* iu, const int32_t* il, float* G, float* LO, float* HI, int32_t* IU,
-                                  int32_t* IL) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int q = list[i];
-    if (G) G[q] = g[i];
-    if (LO) LO[q] = lo[i];
-    if (HI) HI[q] = hi[i];
-    if (IU) IU[q] = iu[i];
-    if (IL) IL[q] = il[i];
+template <int PASS>
+__global__ void __launch_bounds__(TC_FB_THREADS) tc_fallback_kernel(const TcFallbackParams P) {
+    __shared__ float qs[TC_FB_QG][D_MAX];
+    __shared__ float scs[D_MAX];
+    __shared__ double thr[TC_FB_QG][2];
+    __shared__ unsigned long long bv[TC_FB_QG][2];
+    const int cnt = *P.fb_count;
+    const int d = P.d;
+    const int64_t nchunks = (P.N + TC_FB_CHUNK - 1) / TC_FB_CHUNK, ngroups = (cnt + TC_FB_QG - 1) / TC_FB_QG;
+    const float erel = (float)(d + 10) * 5.9604645e-8f;   // (d + 10) 2^-24
+    const int lane = threadIdx.x % 32;
+    if (threadIdx.x < D_MAX) scs[threadIdx.x] = P.sc[threadIdx.x];
+    for (int64_t it = blockIdx.x; it < ngroups * nchunks; it += gridDim.x) {
+        const int s0 = (int)(it / nchunks) * TC_FB_QG;          // first slot of the group
+        const int64_t k0 = (it % nchunks) * TC_FB_CHUNK;
+        const int ng = min(TC_FB_QG, cnt - s0);
+        __syncthreads();                                        // the previous item is done with qs
+        for (int t = threadIdx.x; t < TC_FB_QG * D_MAX; t += TC_FB_THREADS) {
+            const int gq = t / D_MAX, i = t % D_MAX;
+            qs[gq][i] = gq < ng && i < d ? P.Q[(int64_t)P.fb_list[s0 + gq] * d + i] : 0.f;
+        }
+        if (PASS > 0 && threadIdx.x < 2 * TC_FB_QG) {
+            const int gq = threadIdx.x / 2, b = threadIdx.x % 2;
+            if (gq < ng) {
+                const unsigned* e = P.ext + 4 * (int64_t)(s0 + gq) + 2 * b;
+                thr[gq][b] = (double)ord2f(e[0]) + 2.0 * (double)__uint_as_float(e[1]);
+                if (PASS == 2) bv[gq][b] = P.best[2 * (int64_t)(s0 + gq) + b];
+            }
+        }
+        __syncthreads();
+        float mn[TC_FB_QG][2], em[TC_FB_QG][2];
+#pragma unroll
+        for (int gq = 0; gq < TC_FB_QG; ++gq)
+            mn[gq][0] = mn[gq][1] = __int_as_float(0x7f800000), em[gq][0] = em[gq][1] = 0.f;
+        for (int j = threadIdx.x; j < TC_FB_CHUNK; j += TC_FB_THREADS) {
+            const int64_t k = k0 + j;
+            if (k >= P.N) break;
+            const float* x = P.X0 + k * d;
+            const float yy = P.y0[k];
+#pragma unroll
+            for (int gq = 0; gq < TC_FB_QG; ++gq) {
+                if (gq >= ng) break;
+                float acc = 0.f;
+                for (int i = 0; i < d; ++i) {
+                    const float t = (qs[gq][i] - x[i]) * scs[i];
+                    acc = fmaf(t, t, acc);
+                }
+                const float rr = sqrtf(acc);
+                const float v[2] = {yy + rr, rr - yy};
+                if (PASS == 0) {
+                    const float err = erel * (rr + fabsf(yy));
+                    mn[gq][0] = fminf(mn[gq][0], v[0]);
+                    mn[gq][1] = fminf(mn[gq][1], v[1]);
+                    em[gq][0] = em[gq][1] = fmaxf(em[gq][0], err);
+                } else {
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        if (!((double)v[b] <= thr[gq][b])) continue;
+                        double acc64 = 0.0;
+                        for (int i = 0; i < d; ++i) {
+                            const double t = (double)qs[gq][i] - (double)x[i];
+                            const double u = P.unit_w ? t : t * P.w[i];
+                            acc64 += u * u;
+                        }
+                        const double dist = P.M * sqrt(acc64);
+                        const double v64 = b == 0 ? (double)yy + dist : dist - (double)yy;
+                        const int64_t slot = s0 + gq;
+                        if (PASS == 1) atomicMin(P.best + 2 * slot + b, d2ord(v64));
+                        else if (d2ord(v64) == bv[gq][b]) atomicMin(P.idx + 2 * slot + b, (int)k);
+                    }
+                }
+            }
+        }
+        if (PASS == 0) {
+#pragma unroll
+            for (int gq = 0; gq < TC_FB_QG; ++gq) {
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        mn[gq][b] = fminf(mn[gq][b], __shfl_xor_sync(0xffffffffu, mn[gq][b], off));
+                        em[gq][b] = fmaxf(em[gq][b], __shfl_xor_sync(0xffffffffu, em[gq][b], off));
+                    }
+                    if (lane == 0 && gq < ng) {
+                        unsigned* e = P.ext + 4 * (int64_t)(s0 + gq) + 2 * b;
+                        atomicMin(e, f2ord(mn[gq][b]));
+                        atomicMax(e + 1, __float_as_uint(em[gq][b]));
+                    }
+                }
+            }
+        }
+    }
+}
+
+__global__ void tc_fallback_finish_kernel(const TcFallbackParams P) {
+    const int cnt = *P.fb_count;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < cnt; s += gridDim.x * blockDim.x) {
+        const int64_t qi = P.fb_list[s];
+        int iu = P.idx[2 * s], il = P.idx[2 * s + 1];
+        double hi = ord2d(P.best[2 * s]), lo = -ord2d(P.best[2 * s + 1]);
+        if (iu == 0x7fffffff || il == 0x7fffffff) {             // no data
+            hi = lo = __longlong_as_double(0x7ff8000000000000ll);
+            iu = il = -1;
+        }
+        if (P.g) P.g[qi] = (float)(0.5 * (hi + lo));
+        if (P.lo) P.lo[qi] = (float)lo;
+        if (P.hi) P.hi[qi] = (float)hi;
+        if (P.idx_up) P.idx_up[qi] = iu;
+        if (P.idx_lo) P.idx_lo[qi] = il;
+    }
 }
 
 // --------------------------------------------------------------- launchers
@@ -1029,9 +1180,9 @@ static cudaError_t launch_tc_scan_parts(int K, int fmt, const TcScanParams& P, i
 cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scale, int64_t N,
                            const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float4* qc,
                            void* rec, const double* w, double M, const float* X0, const float* y0, float* g, float* lo,
-                           float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, unsigned* err,
-                           int variant, int fmt, const TcDataOrder& O, const TcQueryOrder& QO, cudaEvent_t ev0,
-                           cudaEvent_t ev1, cudaStream_t st) {
+                           float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, void* fb_state,
+                           unsigned* err, int variant, int fmt, const TcDataOrder& O, const TcQueryOrder& QO,
+                           cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t st) {
     const int K = tc_k_for_dim(d, fmt);
     // the queries' spatial order: a tile of 128 positions holds nearby queries
     cudaError_t e = spatial_order(Q, nq, d, QO.qperm, nullptr, QO.scratch, st);
@@ -1064,12 +1215,14 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     S.ntiles = ntiles;
     S.rec = static_cast<TcRec*>(rec);
     S.err = err;
+    int sms = 148;
     {
-        int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
-                                                       cudaSuccess)
-            S.wave = sms;                                    // one CTA per SM (all of TMEM each)
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 148;
         cudaGetLastError();
+        S.wave = sms;                                        // one CTA per SM (all of TMEM each)
     }
     if (ev0 && (e = cudaEventRecord(ev0, st)) != cudaSuccess) return e;     // the scan kernel alone
     e = parts == 2 ? launch_tc_scan_parts<2>(K, fmt, S, nqt, st) : launch_tc_scan_parts<4>(K, fmt, S, nqt, st);
@@ -1103,21 +1256,45 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     R.idx_lo = il;
     R.fb_count = fb_count;
     R.fb_list = fb_list;
+    unsigned* fb_ext = static_cast<unsigned*>(fb_state);
+    unsigned long long* fb_best = reinterpret_cast<unsigned long long*>(fb_ext + 4 * nq);
+    int* fb_idx = reinterpret_cast<int*>(fb_best + 2 * nq);
+    R.fb_ext = fb_ext;
+    R.fb_best = fb_best;
+    R.fb_idx = fb_idx;
     tc_rescreen_kernel<<<(unsigned)((nq + TC_RS_WARPS - 1) / TC_RS_WARPS), TC_RS_THREADS, 0, st>>>(R);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the listed queries, without reading their count back
+    TcFallbackParams F{};
+    F.Q = Q;
+    F.d = d;
+    F.X0 = X0;
+    F.y0 = y0;
+    F.N = N;
+    F.M = M;
+    for (int j = 0; j < D_MAX; ++j) {
+        F.w[j] = w[j];
+        F.sc[j] = R.sc[j];
+    }
+    F.unit_w = R.unit_w;
+    F.fb_count = fb_count;
+    F.fb_list = fb_list;
+    F.ext = fb_ext;
+    F.best = fb_best;
+    F.idx = fb_idx;
+    F.g = g;
+    F.lo = lo;
+    F.hi = hi;
+    F.idx_up = iu;
+    F.idx_lo = il;
+    const unsigned fgrid = (unsigned)sms * 4;
+    tc_fallback_kernel<0><<<fgrid, TC_FB_THREADS, 0, st>>>(F);
+    tc_fallback_kernel<1><<<fgrid, TC_FB_THREADS, 0, st>>>(F);
+    tc_fallback_kernel<2><<<fgrid, TC_FB_THREADS, 0, st>>>(F);
+    tc_fallback_finish_kernel<<<(unsigned)sms, 256, 0, st>>>(F);
     return cudaGetLastError();
 }
 
-cudaError_t tc_gather(const float* Q, int d, const int* list, int n, float* out, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    tc_gather_kernel<<<(unsigned)(((int64_t)n * d + 255) / 256), 256, 0, st>>>(Q, d, list, n, out);
-    return cudaGetLastError();
-}
-
-cudaError_t tc_scatter(const int* list, int n, const float* g, const float* lo, const float* hi, const int32_t* iu,
-                       const int32_t* il, float* G, float* LO, float* HI, int32_t* IU, int32_t* IL, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    tc_scatter_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(list, n, g, lo, hi, iu, il, G, LO, HI, IU, IL);
-    return cudaGetLastError();
-}
+size_t tc_fallback_state_bytes(int64_t nq) { return (size_t)nq * (4 * sizeof(unsigned) + 2 * 8 + 2 * sizeof(int)); }
 
 }  // namespace lip

@@ -15,7 +15,7 @@ EXACT_GAP = 1e-9
 
 def _tc_eval(p, precision="tc_tf32"):
     """Outputs of a tensor-core handle and the number of its queries that went through
-    the plain FP32 fallback (those only meet the FP32 index rule)."""
+    the device-side fallback (whose results are exact too)."""
     import torch
 
     from paper_2606_04670_b300.lipfit import LipFit
@@ -29,13 +29,16 @@ def _tc_eval(p, precision="tc_tf32"):
 
 
 def _check_exact(p, gpu, orc, label, fallback=0):
+    """Values within the FP32 tolerance, every index equal to the oracle's wherever the
+    oracle's gap exceeds EXACT_GAP M diam (fallback queries included: the device-side
+    fallback is exact as well; `fallback` only labels the message)."""
     compare(p, gpu, orc, FP32_TOL, label)
     scale = p.M * diam(p.X, p.Q[: len(orc["hi"])], p.norm, p.w)
     for k, gk in (("idx_up", "gap_up"), ("idx_lo", "gap_lo")):
         clear = orc[gk] > EXACT_GAP * scale
         bad = np.nonzero(clear & (gpu[k].astype(np.int64) != orc[k]))[0]
-        assert bad.size <= fallback, (f"{label} {k}: {bad.size} mismatches with gap > {EXACT_GAP} M diam, "
-                                      f"{fallback} fallback queries")
+        assert bad.size == 0, (f"{label} {k}: {bad.size} mismatches with gap > {EXACT_GAP} M diam "
+                               f"({fallback} fallback queries)")
     # the outputs are FP64 values rounded once to FP32
     for k in ("hi", "lo"):
         np.testing.assert_allclose(gpu[k], orc[k].astype(np.float32), rtol=0, atol=2e-7 * (1 + np.abs(orc[k]).max()))
@@ -93,8 +96,8 @@ def test_tc_edge_cases_and_fallback(oracle_mod, prec):
     m.check()
     m.close()
     # M = 0 with a constant y over 3000 points: every 32-point chunk ties, so each
-    # query's candidate lists (8 chunks per half row) overflow and the queries go
-    # through the plain scan; the result is still the lowest index
+    # query's candidate lists (8 chunks per half row) overflow and every query goes
+    # through the device-side fallback; the result is still the lowest index
     p = W.random_problem(962, 3_000, 5, 300)
     yc = np.full(p.N, 0.25, np.float32)
     m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(yc).cuda(), 0.0, norm=p.norm, precision=prec)
@@ -180,8 +183,8 @@ def test_fp16_random_shapes(oracle_mod, d, weighted):
 
 def test_fp16_cluster_and_far_queries(oracle_mod):
     """The precision workload's shape at a reduced size, plus queries far outside the data
-    (beyond the fp16 range after scaling): those go through the plain scan, the rest stay
-    exact."""
+    (beyond the fp16 range after scaling): those go through the device-side fallback; every
+    query stays exact."""
     p = W.cluster_d16(n_data=30_000, n_query=1_500)
     Q = p.Q.copy()
     far = np.array([3, 700, 1499])
@@ -230,14 +233,12 @@ def test_fp16_full_size_cluster_sampled(oracle_mod):
 
 
 def test_tc_forms_agree_bitwise(oracle_mod):
-    """TF32, BF16 and FP16 all return the FP64 envelopes rounded once, so with no fallback
-    query their outputs are bit for bit the same (values and indices)."""
+    """TF32, BF16 and FP16 all return the FP64 envelopes rounded once (the rescreen and the
+    fallback alike), so their outputs are bit for bit the same (values and indices)."""
     p = W.cluster_d16(n_data=20_000, n_query=1_000)
     outs = {}
     for prec in ("tc_tf32", "tc_bf16", "tc_fp16"):
         outs[prec] = _tc_eval(p, prec)
-    if any(fb for _, fb in outs.values()):
-        pytest.skip("a fallback query makes the comparison inexact")
     ref = outs["tc_tf32"][0]
     for prec in ("tc_bf16", "tc_fp16"):
         for k in ("g", "lo", "hi", "idx_up", "idx_lo"):
@@ -285,3 +286,85 @@ def test_tc_timing_events_bracket_the_scan():
     m.check()
     m.close()
     assert 0.0 < scan_ms < whole_ms
+
+
+def _fallback_problem(seed=1010, n=6_000, nq=1_500, n_far=400, dup=True):
+    """Data with exact duplicates (ties in value: the lowest index must win) and queries of
+    which n_far lie beyond the fp16 range (so the fp16 form sends them to the fallback)."""
+    p = W.random_problem(seed, n, 6, nq, norm=W.NORM_L2)
+    X, y = p.X.copy(), p.y.copy()
+    if dup:
+        X[n // 2:n // 2 + 500] = X[:500]          # duplicated points with equal values
+        y[n // 2:n // 2 + 500] = y[:500]
+    Q = p.Q.copy()
+    Q[:50] = X[:50]                                # queries on data points
+    far = 50 + np.random.default_rng(seed).choice(nq - 50, n_far, replace=False)
+    Q[far] = Q[far] * 3e5 + 7.0
+    return W.Problem("fb", X, y, Q, p.M, p.norm, None, None), far
+
+
+@pytest.mark.parametrize("prec", ["tc_tf32", "tc_fp16"])
+def test_fallback_is_exact(oracle_mod, prec):
+    """Hundreds of queries through the device-side fallback (fp16: outside the fp16 range),
+    against the FP64 oracle with the exact index rule, duplicates included."""
+    p, far = _fallback_problem()
+    orc = oracle_mod.evaluate(p.X, p.y, p.Q, p.M, p.norm)
+    r, fb = _tc_eval(p, prec)
+    if prec == "tc_fp16":
+        assert fb >= far.size, (fb, far.size)
+    _check_exact(p, r, orc, f"{prec} fallback", fb)
+    # ties between duplicates resolve to the lower index, as in the oracle
+    for k in ("idx_up", "idx_lo"):
+        tie = orc["gap_" + k[4:]] == 0
+        assert np.array_equal(r[k][tie], orc[k][tie]), k
+
+
+def test_fallback_all_queries_random_values(oracle_mod):
+    """Every query through the fallback (fp16 form, all queries far away) on random data:
+    equal to the oracle's envelopes rounded once."""
+    p = W.random_problem(1011, 3_001, 3, 700, norm=W.NORM_L2, weighted=True)
+    Q = (p.Q * 4e5 - 2e5).astype(np.float32)
+    ps = W.Problem("fa", p.X, p.y, Q, p.M, p.norm, None, p.w)
+    orc = oracle_mod.evaluate(ps.X, ps.y, ps.Q, ps.M, ps.norm, w=ps.w)
+    r, fb = _tc_eval(ps, "tc_fp16")
+    assert fb == ps.nq
+    _check_exact(ps, r, orc, "fp16 all far", fb)
+
+
+@pytest.mark.parametrize("prec", ["tc_tf32", "tc_fp16"])
+def test_tc_eval_captured_in_a_cuda_graph(oracle_mod, prec):
+    """lip_eval on a tensor-core handle does not synchronise, so it can be captured in a CUDA
+    graph (after one eager call that sizes the scratch); replays with new query values
+    (a different number of fallback queries each time) equal eager calls bit for bit."""
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    p, _ = _fallback_problem(1012, 5_000, 1_024, 100)
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, precision=prec)
+    Qs = torch.as_tensor(p.Q).cuda().clone()
+    m.eval(Qs)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            out = m.eval(Qs)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    for rep in range(3):
+        Qn = p.Q.copy()
+        far = rng.choice(p.nq, 40 * rep, replace=False)
+        Qn[far] = Qn[far] * 3e5
+        Qs.copy_(torch.as_tensor(Qn).cuda())
+        g.replay()
+        torch.cuda.synchronize()
+        got = {k: v.cpu().numpy().copy() for k, v in out.items()}
+        ref = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(Qn).cuda()).items()}
+        for k in ref:
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=f"{prec} replay {rep} {k}")
+        if rep == 2:
+            ps = W.Problem("g", p.X, p.y, Qn, p.M, p.norm, None, None)
+            _check_exact(ps, got, oracle_mod.evaluate(p.X, p.y, Qn, p.M, p.norm), f"{prec} graph")
+    m.check()
+    m.close()

@@ -65,9 +65,9 @@ KERNEL_DRAM_BYTES = {
     ("monotone_d4", 2): 19.136000e6 + 11.619840e6,     # scan_exact_kernel<L2, C=2, U=2, R=4>
     ("grad_d8", 2): 16.66e6 + 13.47e6,                 # scan_exact_kernel<L2, C=4, U=4, R=2>
     ("cluster_d16", 2): 618.02e6 + 185.20e6,           # scan_exact_kernel<L2, C=0, U=16, R=2>
-    ("cluster_d16_tc", 2): 46099.46e6 + 2158.52e6,     # tc_scan_kernel<K=16, 4 parts, TF32> (serpentine sweep)
-    ("cluster_d16_bf16", 2): 21533.21e6 + 1710.58e6,   # tc_scan_kernel<K=16, 4 parts, BF16> (serpentine sweep)
-    ("cluster_d16_fp16", 2): 7593.19e6 + 1251.66e6,    # tc_scan_kernel<K=16, 4 parts, FP16> (serpentine sweep)
+    ("cluster_d16_tc", 2): 7185.37e6 + 1213.84e6,      # tc_scan_kernel<K=16, 4 parts, TF32> (persistent, soft lockstep)
+    ("cluster_d16_bf16", 2): 5275.18e6 + 1081.80e6,    # tc_scan_kernel<K=16, 4 parts, BF16> (persistent, soft lockstep)
+    ("cluster_d16_fp16", 2): 3413.92e6 + 943.47e6,     # tc_scan_kernel<K=16, 4 parts, FP16> (persistent, soft lockstep)
     ("local_d4", 2): 32.64e6 + 1.43e6,                 # loc_scan_kernel<L2, 4, bucket, G=2>
     ("smooth_d4", 2): 4.54e6 + 40.80e6,                # smooth_pass_kernel<L2, 4> (share q, 64 splits)
     ("batch_4096", 0): 4817.68e6 + 1598.16e6,          # batch_scan_kernel

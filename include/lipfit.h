@@ -513,8 +513,12 @@ LIP_API void lip_batch_free(lip_batch b);
  *                FP32 values differ in the last bits, so the selected index can differ
  *                where two bound values are that close (the bounds returned are the FP64
  *                values of the selected data either way); other shapes run 0 / 1.
- *                Ignored by the generic kernel.  For tensor-core handles (0 or 1): 0 runs the
- *                tensor-core epilogue on 16 warps, 1 on 8.  For LIP_FP64 handles: 0 (the
+ *                Ignored by the generic kernel.  For tensor-core handles (0 to 5): bit 0
+ *                runs the tensor-core epilogue on 8 warps instead of 16; 0 / 1 run one
+ *                persistent CTA per SM whose data sweeps keep a soft lockstep (the CTAs
+ *                of a round read each data tile at about the same time, so it comes from
+ *                L2), 2 / 3 the same without the lockstep, 4 / 5 one CTA per query tile;
+ *                the results do not depend on the variant.  For LIP_FP64 handles: 0 (the
  *                default) scans a float copy of the layout and recomputes in FP64 only
  *                the pairs within the FP32 error bound of the extremum, 1 scans in FP64
  *                throughout (0 or 1); both return the FP64 envelopes.
@@ -543,6 +547,14 @@ LIP_API lip_status lip_get_tuning(lip_handle h, int32_t* tile_groups, int32_t* s
  * stream immediately before and after its all-pairs scan kernel, so that the kernel can
  * be timed alone on the stream it runs on.  NULL, NULL turns this off. */
 LIP_API lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, void* ev_after_scan);
+
+/* Tensor-core handles, variants 0 / 1 of lip_set_tuning: the data bytes over which the
+ * persistent CTAs of one round may spread their sweeps of the data tiles (a producer runs
+ * at most that far ahead of the slowest CTA of its round, and waits at most 2 ms for it).
+ * Smaller windows keep the tiles a round reads in L2 for less DRAM traffic; larger ones let
+ * the CTAs absorb differences in their speed.  0 (the default) selects 32 MB.  Ignored by
+ * other handles and variants; the results do not depend on it.  LIP_ERR_ARG if bytes < 0. */
+LIP_API lip_status lip_set_tc_window(lip_handle h, int64_t bytes);
 
 /* Tensor-core handles (LIP_TC_*): number of queries of the last lip_eval whose candidate
  * lists overflowed (or, for LIP_TC_FP16, that lay outside the fp16 range) and were settled

@@ -74,10 +74,14 @@ def tune_eval(model, Q, tiles: Iterable[int] = (8, 16, 32, 64), splits: Iterable
               variants: Optional[Iterable[int]] = None, cache: Optional[Dict] = None, reps: int = 3) -> Dict:
     """Time lip_eval on `model` for every (variant, tile_groups, splits); apply the fastest.
     The variants default to the six of FP32 handles (queries per thread x the share of
-    square roots on the FMA pipe) and to 0, 1 for FP64 and tensor-core handles."""
-    from .lipfit import LIP_FP32
+    square roots on the FMA pipe), to 0, 1 for FP64 handles and to 0-5 for tensor-core
+    handles (epilogue warps x the launch form), which ignore tiles and splits."""
+    from .lipfit import LIP_FP32, LIP_FP64
+    tc = model.precision not in (LIP_FP32, LIP_FP64)
     if variants is None:
-        variants = range(6) if model.precision == LIP_FP32 else (0, 1)
+        variants = range(6) if model.precision == LIP_FP32 else (range(6) if tc else (0, 1))
+    if tc:
+        tiles, splits = (32,), (0,)
     key = eval_key(model, Q.shape[0])
     if cache is not None and key in cache:
         best = cache[key]

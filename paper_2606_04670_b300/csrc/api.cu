@@ -468,9 +468,10 @@ lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, v
     const int64_t nqt = ceil_div(nq, 128);
     const size_t a_b = round_up((int64_t)(nqt * tc_a_bytes_for(d, h->tc_fmt)), 256), eps_b = round_up(nq * 16, 256),
                  rec_b = round_up((int64_t)(nq * tc_rec_bytes()), 256), list_b = round_up(nq * 4 + 4, 256),
-                 qp_b = round_up(nq * 4, 256), fb_b = round_up((int64_t)tc_fallback_state_bytes(nq), 256);
+                 qp_b = round_up(nq * 4, 256), fb_b = round_up((int64_t)tc_fallback_state_bytes(nq), 256),
+                 ar_b = round_up((int64_t)tc_arrive_bytes(nq, ntiles), 256);
     h->tc_fb_count = nullptr;
-    LIP_TRY(h->tc_q.ensure(a_b + eps_b + rec_b + list_b + qp_b + fb_b + spatial_order_scratch(nq),
+    LIP_TRY(h->tc_q.ensure(a_b + eps_b + rec_b + list_b + qp_b + fb_b + ar_b + spatial_order_scratch(nq),
                            "tensor-core query scratch"));
     char* base = static_cast<char*>(h->tc_q.p);
     int* fb_list = reinterpret_cast<int*>(base + a_b + eps_b + rec_b);
@@ -478,12 +479,13 @@ lip_status eval_tc(lip_model* h, const void* Q, int64_t nq, void* g, void* lo, v
     TcQueryOrder QO{};
     QO.qperm = reinterpret_cast<int*>(base + a_b + eps_b + rec_b + list_b);
     void* fb_state = base + a_b + eps_b + rec_b + list_b + qp_b;
-    QO.scratch = base + a_b + eps_b + rec_b + list_b + qp_b + fb_b;
+    int* arrive = reinterpret_cast<int*>(base + a_b + eps_b + rec_b + list_b + qp_b + fb_b);
+    QO.scratch = base + a_b + eps_b + rec_b + list_b + qp_b + fb_b + ar_b;
     CUDA_TRY(tc_eval_launch(static_cast<const float*>(Q), nq, d, scale, h->N, h->tc_maxbits, h->tc_btiles,
                             ntiles, base, reinterpret_cast<float4*>(base + a_b), base + a_b + eps_b, h->w, h->M,
                             static_cast<const float*>(h->X0), static_cast<const float*>(h->y0), static_cast<float*>(g),
                             static_cast<float*>(lo), static_cast<float*>(hi), iu, il, fb_count, fb_list, fb_state,
-                            h->status, h->tc_variant, h->tc_fmt, O, QO, h->ev_scan0, h->ev_scan1, st));
+                            arrive, h->tc_window, h->status, h->tc_variant, h->tc_fmt, O, QO, h->ev_scan0, h->ev_scan1, st));
     count_launches(7 + spatial_order_launches());
     h->tc_fb_count = fb_count;          // read back by lip_last_fallback only
     return LIP_OK;
@@ -1021,8 +1023,8 @@ lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits, int
     if (splits < 0 || splits > 4096) return fail(LIP_ERR_ARG, "splits = %d is outside [0, 4096]", splits);
     if (variant < -1 || variant >= SCAN_VARIANTS)
         return fail(LIP_ERR_ARG, "variant = %d is outside [-1, %d]", variant, SCAN_VARIANTS - 1);
-    if ((h->tc || h->esize == 8) && variant > 1)
-        return fail(LIP_ERR_ARG, "variant = %d: tensor-core and FP64 handles take 0 or 1", variant);
+    if (h->tc && variant > 5) return fail(LIP_ERR_ARG, "variant = %d: tensor-core handles take 0 to 5", variant);
+    if (h->esize == 8 && variant > 1) return fail(LIP_ERR_ARG, "variant = %d: FP64 handles take 0 or 1", variant);
     DeviceGuard gd(h->device);
     if (tile_groups) h->tile_groups = tile_groups;
     h->splits = splits;
@@ -1076,13 +1078,14 @@ lip_status lip_autotune(lip_handle h, const void* Q, int64_t nq, int32_t reps, i
     double best = 1e300;
     int32_t btg = keep_tg, bsp = keep_sp, bv = keep_v;
     const int tiles[] = {8, 16, 32, 64}, splits[] = {0, 1, 2, 3, 4, 6, 8, 12, 16};
-    const int nv = h->tc || h->esize == 8 ? 2 : (h->exact ? SCAN_VARIANTS : 1);
+    const int nv = h->tc ? 6 : (h->esize == 8 ? 2 : (h->exact ? SCAN_VARIANTS : 1));
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         s = fail(LIP_ERR_CUDA, "cudaEventCreate failed");
     } else {
         for (int v = 0; v < nv && s == LIP_OK; ++v)
-            for (int tg : tiles)
+            for (int ti = 0; ti < (h->tc ? 1 : 4) && s == LIP_OK; ++ti)
                 for (int sp : splits) {
+                    const int tg = h->tc ? keep_tg : tiles[ti];
                     if ((s = lip_set_tuning(h, tg, sp, v)) != LIP_OK) break;
                     std::vector<float> ms;
                     for (int r = 0; r <= reps && s == LIP_OK; ++r) {      // the first run warms up
@@ -1138,6 +1141,13 @@ lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, void* ev_af
 }
 
 uint64_t lip_kernel_launches(void) { return launches_total(); }
+
+lip_status lip_set_tc_window(lip_handle h, int64_t bytes) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (bytes < 0) return fail(LIP_ERR_ARG, "window = %lld < 0", (long long)bytes);
+    h->tc_window = bytes;
+    return LIP_OK;
+}
 
 int64_t lip_last_fallback(lip_handle h) {
     if (!h) return -1;

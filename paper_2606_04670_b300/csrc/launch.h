@@ -124,8 +124,11 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
                            const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float4* qc,
                            void* rec, const double* w, double M, const float* X0, const float* y0, float* g, float* lo,
                            float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, void* fb_state,
-                           unsigned* err, int variant, int fmt, const TcDataOrder& O, const TcQueryOrder& QO,
-                           cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t st);
+                           int* arrive, int64_t window, unsigned* err, int variant, int fmt,
+                           const TcDataOrder& O, const TcQueryOrder& QO, cudaEvent_t ev0, cudaEvent_t ev1,
+                           cudaStream_t st);
+// Scratch of the scan's soft lockstep counters for nq queries against ntiles data tiles.
+size_t tc_arrive_bytes(int64_t nq, int64_t ntiles);
 // Scratch of the device-side fallback for nq queries (fb_state above).
 size_t tc_fallback_state_bytes(int64_t nq);
 

@@ -129,6 +129,7 @@ struct lip_model {
     unsigned* tc_maxbits = nullptr;    // [2] max |x^|, max |y| (float bits)
     Scratch tc_q;
     Scratch tc_order;                  // the data's spatial order and position-ordered copies
+    int64_t tc_window = 0;              // lip_set_tc_window (0: the library's default)
     int* tc_fb_count = nullptr;         // device count of the last tensor-core lip_eval's fallback
     // local Lipschitz constants (Sec. 4.3), valid until the data change
     bool loc_valid = false;

@@ -466,8 +466,31 @@ struct TcScanParams {
     int64_t ntiles;
     TcRec* rec;            // [nq positions][2 bounds][TC_MAX_PARTS column slices]
     unsigned* err;
-    int wave;              // CTAs resident at once (one per SM): the sweep direction's period
+    int64_t nqt;           // query tiles; CTA c takes tiles c, c + grid, ... (one per round)
+    // Soft lockstep of the CTAs of a round (lag > 0): arrive[round][c] counts the CTAs whose
+    // producer has reached data chunk c (ctiles tiles each) of that round; a producer waits,
+    // for at most THROTTLE_NS, until every CTA of its round has reached chunk c - lag.
+    int* arrive;           // [rounds][nch], zeroed before the launch
+    int nch;
+    int ctiles;
+    int lag;
+    int wave;              // SMs: query tile qt belongs to round qt / wave (its sweep direction)
 };
+
+constexpr unsigned long long TC_THROTTLE_NS = 2000000;     // 2 ms, then the CTA stops waiting
+
+// The soft lockstep's wait: true when *cnt >= need; false (stop waiting for the rest of the
+// kernel) after TC_THROTTLE_NS.  Only the order of the data tiles' L2 reuse depends on it,
+// never a result.
+__device__ __forceinline__ bool tc_throttle(const int* cnt, int need) {
+    if (*reinterpret_cast<const volatile int*>(cnt) >= need) return true;
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        __nanosleep(256);
+        if (*reinterpret_cast<const volatile int*>(cnt) >= need) return true;
+        if (globaltimer() - t0 > TC_THROTTLE_NS) return false;
+    }
+}
 
 // Candidate list append with compaction when full (entries that can no longer qualify
 // are dropped; the bound only tightens).  upper = true for H_up (keep L <= U).
@@ -504,23 +527,25 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                               // A_hi, A_lo
     unsigned char* sB = smem + A_BYTES;                     // ST tiles
-    __shared__ __align__(8) uint64_t a_full, b_full[ST], b_empty[ST], acc_full[2], acc_empty[2];
+    __shared__ __align__(8) uint64_t a_full, a_empty, b_full[ST], b_empty[ST], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int64_t qt = blockIdx.x;
     const int64_t T = P.ntiles;
-    // Sweep direction: the CTAs of one wave (one per SM) read the data tiles in increasing
-    // order, the next wave's in decreasing order, and so on.  A CTA of the next wave starts
-    // when one of the previous wave finishes, at the end of the sweep the others are still
-    // reading, so its first tiles are the ones most recently brought into L2 (with one
-    // direction it would start from the tiles read longest ago).  Tile order does not change
-    // the results: the candidate chunks are collected in any order and the rescreen takes
-    // the exact extremum with the lowest index.
-    const bool rev = P.wave > 0 && ((qt / P.wave) & 1) != 0;
+    // Persistent CTAs (one per SM, a cooperative launch): round r of CTA c scans query tile
+    // c + r * grid against every data tile (with a grid of one CTA per query tile, each CTA
+    // runs one round).  Sweep direction: even rounds (query tiles qt with qt / SMs even)
+    // read the data tiles in increasing order, odd rounds in decreasing order, so a round
+    // starts on the tiles the last one read most recently (still in L2).  With P.lag > 0 the producers of
+    // a round keep within lag chunks of one another (tc_throttle), so the round's CTAs read
+    // each data tile from L2 at about the same time and DRAM sees the tile set about once
+    // per round.  Tile order does not change the results: the candidate chunks are collected
+    // in any order and the rescreen takes the exact extremum with the lowest index.
+    const int grid = (int)gridDim.x, nqt = (int)P.nqt;   // nq < 2^31: fewer than 2^24 query tiles
 
     if (threadIdx.x == 0) {
         mbar_init(&a_full, 1);
+        mbar_init(&a_empty, 1);
         for (int s = 0; s < ST; ++s) {
             mbar_init(&b_full[s], 1);
             mbar_init(&b_empty[s], 1 + EPI_WARPS);         // MMA commit + epilogue warps
@@ -543,25 +568,42 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
     if (warp == 0) {
         // ------------------------------------------------ producer
         if (lane == 0) {
-            int64_t t = 0;
-            bool ok = true;
-            mbar_expect_tx(&a_full, A_BYTES);
-            bulk_g2s(sA, P.atiles + qt * (int64_t)A_BYTES, A_BYTES, &a_full);
-            for (; t < T; ++t) {
-                const int s = (int)(t % ST);
-                if (t >= ST && !mbar_wait_bounded(&b_empty[s], (uint32_t)((t / ST - 1) & 1), P.err)) {
+            uint32_t g = 0;                                // data tiles issued by this CTA (< 2^31)
+            uint32_t na = 0;                               // query tiles issued
+            bool ok = true, throttle = true;
+            for (int qt = (int)blockIdx.x, r = 0; ok && qt < nqt; qt += grid, ++r) {
+                if (r > 0 && !mbar_wait_bounded(&a_empty, (uint32_t)((r - 1) & 1), P.err)) {
                     ok = false;
                     break;
                 }
-                mbar_expect_tx(&b_full[s], TILE_BYTES);
-                const int64_t tt = rev ? T - 1 - t : t;
-                bulk_g2s(sB + (size_t)s * STAGE_BYTES, P.btiles + tt * (int64_t)TILE_BYTES, TILE_BYTES, &b_full[s]);
+                mbar_expect_tx(&a_full, A_BYTES);
+                bulk_g2s(sA, P.atiles + qt * (int64_t)A_BYTES, A_BYTES, &a_full);
+                ++na;
+                const bool rev = ((qt / P.wave) & 1) != 0;
+                const int members = nqt - r * grid < grid ? nqt - r * grid : grid;
+                int* row = P.arrive + (int64_t)r * P.nch;
+                for (int64_t t = 0; t < T; ++t, ++g) {
+                    if (P.lag > 0 && t % P.ctiles == 0) {
+                        // every CTA counts itself in, also after it has stopped waiting
+                        const int c = (int)(t / P.ctiles);
+                        atomicAdd(row + c, 1);
+                        if (throttle && c >= P.lag) throttle = tc_throttle(row + c - P.lag, members);
+                    }
+                    const int s = (int)(g % ST);
+                    if (g >= (uint32_t)ST && !mbar_wait_bounded(&b_empty[s], (g / ST - 1) & 1u, P.err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&b_full[s], TILE_BYTES);
+                    const int64_t tt = rev ? T - 1 - t : t;
+                    bulk_g2s(sB + (size_t)s * STAGE_BYTES, P.btiles + tt * (int64_t)TILE_BYTES, TILE_BYTES, &b_full[s]);
+                }
             }
             // wait (bounded) for the copies still in flight before leaving
-            const int64_t first = t > ST ? t - ST : 0;
-            for (int64_t u = first; u < t; ++u)
-                mbar_wait_bounded(&b_full[u % ST], (uint32_t)((u / ST) & 1), ok ? P.err : nullptr);
-            mbar_wait_bounded(&a_full, 0, nullptr);
+            const uint32_t first = g > (uint32_t)ST ? g - ST : 0u;
+            for (uint32_t u = first; u < g; ++u)
+                mbar_wait_bounded(&b_full[u % ST], (u / ST) & 1u, ok ? P.err : nullptr);
+            if (na > 0) mbar_wait_bounded(&a_full, (na - 1) & 1u, nullptr);
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
@@ -572,12 +614,17 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
             const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_N >> 3) << 17) |
                                    ((uint32_t)(TC_M >> 4) << 24);
             const uint32_t a0 = smem_u32(sA);
-            int64_t t = 0;
-            if (mbar_wait_bounded(&a_full, 0, P.err)) {
-                for (; t < T; ++t) {
-                    const int s = (int)(t % ST), b = (int)(t & 1);
-                    if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / ST) & 1), P.err)) break;
-                    if (t >= 2 && !mbar_wait_bounded(&acc_empty[b], (uint32_t)((t / 2 - 1) & 1), P.err)) break;
+            uint32_t g = 0;
+            bool ok = true;
+            for (int qt = (int)blockIdx.x, r = 0; ok && qt < nqt; qt += grid, ++r) {
+                if (!mbar_wait_bounded(&a_full, (uint32_t)(r & 1), P.err)) break;
+                for (int64_t t = 0; t < T; ++t, ++g) {
+                    const int s = (int)(g % ST), b = (int)(g & 1);
+                    if (!mbar_wait_bounded(&b_full[s], (g / ST) & 1u, P.err) ||
+                        (g >= 2 && !mbar_wait_bounded(&acc_empty[b], (g / 2 - 1) & 1u, P.err))) {
+                        ok = false;
+                        break;
+                    }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t b0 = smem_u32(sB + (size_t)s * STAGE_BYTES);
                     const uint32_t d = tb + (uint32_t)b * TC_N;
@@ -599,33 +646,42 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                     tc_commit(&b_empty[s]);
                     tc_commit(&acc_full[b]);
                 }
+                if (ok) tc_commit(&a_empty);               // the query tile is no longer read
             }
             // the last MMAs must finish before TMEM is released
-            if (t > 0) mbar_wait_bounded(&acc_full[(t - 1) & 1], (uint32_t)(((t - 1) / 2) & 1), nullptr);
+            if (g > 0) mbar_wait_bounded(&acc_full[(g - 1) & 1], ((g - 1) / 2) & 1u, nullptr);
         }
     } else {
         // ------------------------------------------------ epilogue (warps 2 .. 2 + EPI_WARPS)
         const int quarter = warp % 4, part = (warp - 2) / 4;
-        const int64_t qi = qt * TC_M + quarter * 32 + lane;
+        const float INF = __int_as_float(0x7f800000);
+        const int T32 = (int)T;                            // N < 2^31, so T < 2^23
+        uint32_t g = 0;                                    // data tiles consumed by this CTA
+        bool ok = true;
+#pragma unroll 1
+        for (int qt = (int)blockIdx.x, r = 0; ok && qt < nqt; qt += grid, ++r) {
+        const bool rev = ((qt / P.wave) & 1) != 0;
+        const int64_t qi = (int64_t)qt * TC_M + quarter * 32 + lane;
         const bool valid = qi < P.nq;
         const float4 qc = valid ? P.qc[qi] : make_float4(1.f, 1.f, 0.f, 1.f);
         // a zero bound (M = 0) must not turn eps * rsqrt(0) into NaN
         const float eps = fmaxf(qc.x, 1e-30f), epsv = qc.y;
         // FP16: s~ = |q^|^2 + 2^-2k (product); a query outside the f16 range (w < 0) keeps
         // overflowed lists, so it goes through the fallback
-        const float2 nq22 = make_float2(qc.z, qc.z), usc2 = make_float2(fabsf(qc.w), fabsf(qc.w));
+        const float nq2 = qc.z, usc = fabsf(qc.w);
         const bool act = valid && qc.w > 0.f;
+        // the H_up list of this query and column slice; the H_lo list follows TC_MAX_PARTS later
         TcRec* Ru = P.rec + (valid ? ((qi * 2 + 0) * TC_MAX_PARTS + part) : 0);
-        TcRec* Rl = P.rec + (valid ? ((qi * 2 + 1) * TC_MAX_PARTS + part) : 0);
-        const float INF = __int_as_float(0x7f800000);
         float U = INF, Bl = -INF;
         int nu = act ? 0 : -1, nl = nu;
-        const int T32 = (int)T;                            // N < 2^31, so T < 2^23
-        for (int t = 0; t < T32; ++t) {
-            const int s = t % ST, b = t & 1;
-            if (!mbar_wait_bounded(&acc_full[b], (uint32_t)((t / 2) & 1), P.err)) break;
-            // acquire the tile's y values and chunk bounds written by the bulk copy
-            if (!mbar_wait_bounded(&b_full[s], (uint32_t)((t / ST) & 1), P.err)) break;
+        for (int t = 0; t < T32; ++t, ++g) {
+            const int s = (int)(g % ST), b = (int)(g & 1);
+            // the accumulator, then the tile's y values and chunk bounds written by the bulk copy
+            if (!mbar_wait_bounded(&acc_full[b], (g / 2) & 1u, P.err) ||
+                !mbar_wait_bounded(&b_full[s], (g / ST) & 1u, P.err)) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const float* ys = reinterpret_cast<const float*>(sB + (size_t)s * STAGE_BYTES + tc_pieces(FMT) * B_PIECE +
                                                              TC_N * TC_NORM_ROW);
@@ -656,7 +712,7 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                     for (int e = 0; e < 32; e += 4)
                         cs[(e / 4) % 4] = min3f(min3f(cs[(e / 4) % 4], sv[h][e], sv[h][e + 1]), sv[h][e + 2], sv[h][e + 3]);
                     csm[h] = min2f(min3f(cs[0], cs[1], cs[2]), cs[3]);
-                    if (FMT == TC_FP16) csm[h] = fmaf(csm[h], usc2.x, nq22.x);   // monotone: the min s~
+                    if (FMT == TC_FP16) csm[h] = fmaf(csm[h], usc, nq2);   // monotone: the min s~
                 }
                 // Every pair of the chunk has s >= S0 = max(min s~ - eps, 0), so its upper value
                 // is >= y_min + sqrt(S0) and its lower value <= y_max - sqrt(S0).  The chunk
@@ -688,8 +744,10 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                         const float4 y4 = *reinterpret_cast<const float4*>(ys + col + e);
                         float2 s0 = make_float2(sv[h][e], sv[h][e + 1]), s1 = make_float2(sv[h][e + 2], sv[h][e + 3]);
                         if (FMT == TC_FP16) {
-                            s0 = fma2(s0, usc2, nq22);
-                            s1 = fma2(s1, usc2, nq22);
+                            // (scalar FMAs: this path is rare, and two more float2 constants
+                            // would not fit the epilogue's registers)
+                            s0 = make_float2(fmaf(s0.x, usc, nq2), fmaf(s0.y, usc, nq2));
+                            s1 = make_float2(fmaf(s1.x, usc, nq2), fmaf(s1.y, usc, nq2));
                         }
                         const float2 r0 = make_float2(sqrt_approx(fabsf(s0.x)), sqrt_approx(fabsf(s0.y)));
                         const float2 r1 = make_float2(sqrt_approx(fabsf(s1.x)), sqrt_approx(fabsf(s1.y)));
@@ -705,7 +763,7 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
                         U = fminf(U, cum + dlt);
                         if (cum - dlt <= U) tc_append(Ru, nu, chunk, cum - dlt, U, true);
                         Bl = fmaxf(Bl, clm - dlt);
-                        if (clm + dlt >= Bl) tc_append(Rl, nl, chunk, clm + dlt, Bl, false);
+                        if (clm + dlt >= Bl) tc_append(Ru + TC_MAX_PARTS, nl, chunk, clm + dlt, Bl, false);
                     }
                 }
             }
@@ -714,9 +772,10 @@ __global__ void __launch_bounds__(tc_threads(PARTS), 1) tc_scan_kernel(const TcS
         }
         if (valid) {
             Ru->U = U;
-            Ru->n = nu;
-            Rl->U = Bl;
-            Rl->n = nl;
+            Ru->n = ok ? nu : -1;
+            Ru[TC_MAX_PARTS].U = Bl;
+            Ru[TC_MAX_PARTS].n = ok ? nl : -1;
+        }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1154,26 +1213,66 @@ cudaError_t tc_prepare_data(const float* X0, const float* y0, int64_t N, int d, 
     return cudaGetLastError();
 }
 
+// SMs of the current device (148 if the query fails): the scan's persistent grid.
+static int tc_sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 148;
+    cudaGetLastError();
+    return sms;
+}
+
+constexpr int TC_CTILES = 16;                          // data tiles per lockstep chunk
+constexpr int64_t TC_WINDOW_DEFAULT = 32ll << 20;      // data bytes a round's sweeps may spread over
+
+static int64_t tc_grid(int64_t nqt) {
+    const int64_t sms = tc_sm_count();
+    return nqt < sms ? nqt : sms;
+}
+
+size_t tc_arrive_bytes(int64_t nq, int64_t ntiles) {
+    const int64_t nqt = (nq + TC_M - 1) / TC_M, grid = tc_grid(nqt);
+    if (grid < 1) return 0;
+    return (size_t)((nqt + grid - 1) / grid) * (size_t)((ntiles + TC_CTILES - 1) / TC_CTILES) * sizeof(int);
+}
+
+// One CTA per SM (all of TMEM each, one CTA fits), launched cooperatively so that the
+// CTAs of a round are resident together while the soft lockstep waits for one another.
 template <int K, int PARTS, int FMT>
-static cudaError_t launch_tc_scan_k(const TcScanParams& P, int64_t nqt, cudaStream_t st) {
+static cudaError_t launch_tc_scan_k(const TcScanParams& P, int64_t nqt, bool persistent, cudaStream_t st) {
     const size_t smem = (size_t)tc_a_bytes(K, FMT) + (size_t)tc_stages(K, FMT) * tc_stage_bytes(K, FMT);
     static cudaError_t attr =
         cudaFuncSetAttribute(tc_scan_kernel<K, PARTS, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return attr;
-    tc_scan_kernel<K, PARTS, FMT><<<(unsigned)nqt, tc_threads(PARTS), smem, st>>>(P);
-    return cudaGetLastError();
+    if (!persistent) {
+        tc_scan_kernel<K, PARTS, FMT><<<(unsigned)nqt, tc_threads(PARTS), smem, st>>>(P);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)tc_grid(nqt));
+    cfg.blockDim = dim3(tc_threads(PARTS));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tc_scan_kernel<K, PARTS, FMT>, P);
 }
 
 template <int PARTS>
-static cudaError_t launch_tc_scan_parts(int K, int fmt, const TcScanParams& P, int64_t nqt, cudaStream_t st) {
-    if (fmt == TC_BF16) return K <= 16 ? launch_tc_scan_k<16, PARTS, TC_BF16>(P, nqt, st)
-                                       : launch_tc_scan_k<32, PARTS, TC_BF16>(P, nqt, st);
-    if (fmt == TC_FP16) return K <= 16 ? launch_tc_scan_k<16, PARTS, TC_FP16>(P, nqt, st)
-                                       : launch_tc_scan_k<32, PARTS, TC_FP16>(P, nqt, st);
-    if (K == 8) return launch_tc_scan_k<8, PARTS, TC_TF32>(P, nqt, st);
-    if (K == 16) return launch_tc_scan_k<16, PARTS, TC_TF32>(P, nqt, st);
-    if (K == 24) return launch_tc_scan_k<24, PARTS, TC_TF32>(P, nqt, st);
-    return launch_tc_scan_k<32, PARTS, TC_TF32>(P, nqt, st);
+static cudaError_t launch_tc_scan_parts(int K, int fmt, const TcScanParams& P, int64_t nqt, bool pers,
+                                         cudaStream_t st) {
+    if (fmt == TC_BF16) return K <= 16 ? launch_tc_scan_k<16, PARTS, TC_BF16>(P, nqt, pers, st)
+                                       : launch_tc_scan_k<32, PARTS, TC_BF16>(P, nqt, pers, st);
+    if (fmt == TC_FP16) return K <= 16 ? launch_tc_scan_k<16, PARTS, TC_FP16>(P, nqt, pers, st)
+                                       : launch_tc_scan_k<32, PARTS, TC_FP16>(P, nqt, pers, st);
+    if (K == 8) return launch_tc_scan_k<8, PARTS, TC_TF32>(P, nqt, pers, st);
+    if (K == 16) return launch_tc_scan_k<16, PARTS, TC_TF32>(P, nqt, pers, st);
+    if (K == 24) return launch_tc_scan_k<24, PARTS, TC_TF32>(P, nqt, pers, st);
+    return launch_tc_scan_k<32, PARTS, TC_TF32>(P, nqt, pers, st);
 }
 
 // Queries: build A, scan, rescreen.  Returns the fallback count through fb (device).
@@ -1181,13 +1280,14 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
                            const unsigned* maxbits, const char* btiles, int64_t ntiles, char* atiles, float4* qc,
                            void* rec, const double* w, double M, const float* X0, const float* y0, float* g, float* lo,
                            float* hi, int32_t* iu, int32_t* il, int* fb_count, int* fb_list, void* fb_state,
-                           unsigned* err, int variant, int fmt, const TcDataOrder& O, const TcQueryOrder& QO,
-                           cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t st) {
+                           int* arrive, int64_t window, unsigned* err, int variant, int fmt,
+                           const TcDataOrder& O, const TcQueryOrder& QO, cudaEvent_t ev0, cudaEvent_t ev1,
+                           cudaStream_t st) {
     const int K = tc_k_for_dim(d, fmt);
     // the queries' spatial order: a tile of 128 positions holds nearby queries
     cudaError_t e = spatial_order(Q, nq, d, QO.qperm, nullptr, QO.scratch, st);
     if (e != cudaSuccess) return e;
-    const int parts = variant == 1 ? 2 : 4;   // variant 0: 16 epilogue warps, 1: 8
+    const int parts = (variant & 1) ? 2 : 4;   // variant bit 0: 8 epilogue warps instead of 16
     const int64_t nqt = (nq + TC_M - 1) / TC_M;
     TcQueryParams A{};
     A.Q = Q;
@@ -1215,17 +1315,26 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
     S.ntiles = ntiles;
     S.rec = static_cast<TcRec*>(rec);
     S.err = err;
-    int sms = 148;
-    {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-            sms = 148;
-        cudaGetLastError();
-        S.wave = sms;                                        // one CTA per SM (all of TMEM each)
+    S.nqt = nqt;
+    const int sms = tc_sm_count();
+    S.wave = sms;
+    // variant bit 2: one CTA per query tile instead of persistent CTAs (no lockstep then);
+    // bit 1 turns the soft lockstep of the persistent CTAs' data sweep off
+    const int64_t rounds = nqt > 0 ? (nqt + (nqt < sms ? nqt : sms) - 1) / (nqt < sms ? nqt : sms) : 0;
+    const bool persistent = (variant & 4) == 0 && rounds * ntiles < ((int64_t)1 << 31);   // 32-bit ring counters
+    if (persistent && (variant & 2) == 0 && nqt > 0) {
+        S.arrive = arrive;
+        S.ctiles = TC_CTILES;
+        S.nch = (int)((ntiles + TC_CTILES - 1) / TC_CTILES);
+        // a producer may run ahead of its round's slowest by about `window` bytes of tiles
+        const int64_t win = window > 0 ? window : TC_WINDOW_DEFAULT;
+        const int64_t lag = win / ((int64_t)tc_tile_bytes(K, fmt) * TC_CTILES);
+        S.lag = (int)(lag < 1 ? 1 : (lag > S.nch ? S.nch : lag));
+        if ((e = cudaMemsetAsync(arrive, 0, tc_arrive_bytes(nq, ntiles), st)) != cudaSuccess) return e;
     }
     if (ev0 && (e = cudaEventRecord(ev0, st)) != cudaSuccess) return e;     // the scan kernel alone
-    e = parts == 2 ? launch_tc_scan_parts<2>(K, fmt, S, nqt, st) : launch_tc_scan_parts<4>(K, fmt, S, nqt, st);
+    e = parts == 2 ? launch_tc_scan_parts<2>(K, fmt, S, nqt, persistent, st)
+                   : launch_tc_scan_parts<4>(K, fmt, S, nqt, persistent, st);
     if (e != cudaSuccess) return e;
     if (ev1 && (e = cudaEventRecord(ev1, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(fb_count, 0, sizeof(int), st)) != cudaSuccess) return e;

@@ -109,6 +109,7 @@ def _load():
         "lip_shard_reeval": [H, P, i64, i64, P, P, P, P, P],
         "lip_shard_finish": [H, i64, P, P, P, P, P, P, P, P, P, P],
         "lip_estimate_M_part": [H, i32, i32, P, P],
+        "lip_set_tc_window": [H, i64],
         "lip_debug_fail_alloc": [i64],
         "lip_debug_sqrt_fma": [P, P, i64, P],
         "lip_debug_scan_fault": [H, ctypes.c_uint64, i32],
@@ -705,6 +706,11 @@ class LipFit:
 
     def check(self):
         _check(_lib.lip_check(self.h, _stream_ptr()), "lip_check")
+
+    def set_tc_window(self, nbytes: int = 0):
+        """Tensor-core handles: the data bytes a round's persistent CTAs may spread their
+        sweeps over (0: the default)."""
+        _check(_lib.lip_set_tc_window(self.h, int(nbytes)), "lip_set_tc_window")
 
     def last_fallback(self) -> int:
         return lip_last_fallback(self.h)

@@ -368,3 +368,31 @@ def test_tc_eval_captured_in_a_cuda_graph(oracle_mod, prec):
             _check_exact(ps, got, oracle_mod.evaluate(p.X, p.y, Qn, p.M, p.norm), f"{prec} graph")
     m.check()
     m.close()
+
+
+@pytest.mark.parametrize("prec", ["tc_tf32", "tc_bf16", "tc_fp16"])
+def test_tc_variants_and_rounds(oracle_mod, prec):
+    """40,000 queries are 313 query tiles: three rounds of the persistent scan (148, 148 and
+    17 CTAs), the last one partial.  The six variants (epilogue warps x persistent CTAs with
+    or without the soft lockstep of the data sweep, or one CTA per query tile) give the
+    same outputs bit for bit, and a sample of queries matches the oracle under the exact
+    index rule."""
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    p = W.cluster_d16(n_data=20_000, n_query=40_000)
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, precision=prec)
+    Q = torch.as_tensor(p.Q).cuda()
+    outs = []
+    for v in range(6):
+        m.set_tuning(0, 0, v)
+        outs.append({k: t.cpu().numpy() for k, t in m.eval(Q).items()})
+    m.check()
+    m.close()
+    for v in range(1, 6):
+        for k in outs[0]:
+            assert np.array_equal(outs[v][k], outs[0][k]), f"variant {v} {k}"
+    idx = np.sort(np.random.default_rng(31).choice(p.nq, 500, replace=False))
+    ps = W.Problem("r", p.X, p.y, p.Q[idx], p.M, p.norm, None, None)
+    orc = oracle_mod.evaluate(p.X, p.y, ps.Q, p.M, p.norm)
+    _check_exact(ps, {k: v[idx] for k, v in outs[0].items()}, orc, f"{prec} rounds")

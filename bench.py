@@ -151,6 +151,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--tc-variant", type=int, default=-1,
+                    help="tensor-core handles: lip_set_tuning variant (0-5; -1 keeps the default 0)")
+    ap.add_argument("--tc-window-mb", type=int, default=0,
+                    help="tensor-core handles: lockstep window in MB (lip_set_tc_window; 0 = default)")
     ap.add_argument("--no-tc-vs-plain", action="store_true",
                     help="monotone_d4: skip the tensor-core vs plain comparison on cluster_d16 (after the timed steps)")
     ap.add_argument("--sets", type=int, default=0, help="batch_4096: use only the first N sets (profiling)")
@@ -486,6 +490,10 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
             y = torch.as_tensor(p.y).to("cuda", dt)
             Q = torch.as_tensor(p.Q).to("cuda", dt)
             m = L.LipFit(M=p.M, norm=p.norm, mon=p.mon, w=p.w, capacity=p.N, d=p.d, precision=prec)
+            if prec.startswith("tc_"):
+                if args.tc_variant >= 0:
+                    m.set_tuning(0, 0, args.tc_variant)
+                m.set_tc_window(args.tc_window_mb << 20)
             ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             m.set_timing_events(*ev)
             runs.append(dict(p=p, prec=prec, X=X, y=y, Q=Q, m=m, ev=ev, scan=[], bwd=[],
@@ -604,7 +612,9 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
                                     for r in runs},
               "splits": tun["last_splits"], "tile_groups": tun["tile_groups"],
               "queries_per_thread": tun["queries_per_thread"], "sms": ctx.sms, "autotune": tuning,
-              "tc_fallback_queries": {key(r): r["m"].last_fallback() for r in runs if r["prec"].startswith("tc_")}}
+              "tc_fallback_queries": {key(r): r["m"].last_fallback() for r in runs if r["prec"].startswith("tc_")},
+              "tc_variant": {key(r): r["m"].tuning()["variant"] for r in runs if r["prec"].startswith("tc_")},
+              "tc_window_mb": args.tc_window_mb or 32}
     if with_bwd:
         # backward (one launch): per query it reads q, both indices and grad_g, gathers the
         # two chosen data rows, writes grad_q and adds to grad_y (two atomic read-modify-

@@ -516,7 +516,7 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
         for k, r in enumerate(runs):
             m = r["m"]
             m.clear()
-            m.add(r["X"], r["y"])
+            m.add_async(r["X"], r["y"])       # the finiteness check reported by check() below
             out = m.eval(r["Q"], need=("g", "lo", "hi", "idx_up", "idx_lo"))
             if record:
                 torch.cuda.synchronize()
@@ -534,6 +534,8 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
                     est[k] = S.estimate_M_sharded(S.DeviceShard(m, 0), device="cuda")[0]
                 else:
                     est[k] = m.lipschitz_constant()[0]
+        for r in runs:
+            r["m"].check()
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -575,13 +577,14 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
             for r, hX, hy, hQ, outs in hostruns:
                 m = r["m"]
                 m.clear()
-                m.add_host(hX, hy)
+                m.add_host_async(hX, hy)
                 m.eval_host(hQ, outs)
                 if with_est:
                     if ctx.world > 1:
                         S.estimate_M_sharded(S.DeviceShard(m, 0), device="cuda")
                     else:
                         m.lipschitz_constant()
+                m.check()
 
         step_host()
         torch.cuda.synchronize()

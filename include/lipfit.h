@@ -135,6 +135,19 @@ LIP_API lip_status lip_add(lip_handle h, const void* X, const void* y, int64_t n
 /* lip_add with X and y in host memory. */
 LIP_API lip_status lip_add_host(lip_handle h, const void* X, const void* y, int64_t n, void* stream);
 
+/* lip_add / lip_add_host without waiting for the GPU: the finiteness check of the new
+ * points runs on the device.  A point holding NaN or Inf is replaced on the device by a
+ * copy of a finite point (the handle's first point if it already held data, else the
+ * first finite new point, else x = 0, y = 0) so that no kernel reads a non-finite
+ * datum, and the next lip_check returns LIP_ERR_NONFINITE; the results computed in
+ * between are those of the data with the replaced points (lip_clear starts over).  The
+ * points count as added either way.  Argument errors (LIP_ERR_ARG, LIP_ERR_CAPACITY)
+ * are returned at once and leave the handle unchanged.  X and y must stay valid until the
+ * stream has passed this call (for lip_add_host_async, pinned host memory keeps the copy
+ * asynchronous). */
+LIP_API lip_status lip_add_async(lip_handle h, const void* X, const void* y, int64_t n, void* stream);
+LIP_API lip_status lip_add_host_async(lip_handle h, const void* X, const void* y, int64_t n, void* stream);
+
 /* Remove every point (Sec. 5: clear()).  The capacity is kept. */
 LIP_API lip_status lip_clear(lip_handle h, void* stream);
 
@@ -570,7 +583,9 @@ LIP_API uint64_t lip_kernel_launches(void);
 
 /* Synchronise the stream and report a failure recorded by the device since the last
  * lip_check on this handle: LIP_ERR_TIMEOUT if a bounded wait inside a kernel gave up
- * (the kernel then skipped its work and returned), LIP_ERR_CUDA for a CUDA error. */
+ * (the kernel then skipped its work and returned), LIP_ERR_NONFINITE if a lip_add_async /
+ * lip_add_host_async met NaN or Inf (TIMEOUT is reported first when both happened),
+ * LIP_ERR_CUDA for a CUDA error.  The recorded failures are cleared. */
 LIP_API lip_status lip_check(lip_handle h, void* stream);
 
 LIP_API void lip_free(lip_handle h);

@@ -237,7 +237,7 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
         {&h->X0, (size_t)cap * d * h->esize, "data copy"},
         {&h->y0, (size_t)cap * h->esize, "value copy"},
         {&h->hot, (size_t)h->cap_pad * h->nch * h->esize, "scan layout"},
-        {reinterpret_cast<void**>(&h->status), 2 * sizeof(unsigned), "status word"},
+        {reinterpret_cast<void**>(&h->status), 4 * sizeof(unsigned), "status word"},
     };
     for (auto& a : allocs) {
         e = dev_malloc(a.p, a.n);
@@ -277,7 +277,7 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
             }
         }
     }
-    e = cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), st);
+    e = cudaMemsetAsync(h->status, 0, 4 * sizeof(unsigned), st);
     if (e == cudaSuccess) e = launch_pad_hot(h->esize, h->hot, 0, h->cap_pad, h->nch, h->dl, st);
     count_launches(1);
     if (e != cudaSuccess) {
@@ -288,8 +288,11 @@ lip_status create_model(int64_t cap, int32_t d, double M, const lip_params* p, c
     return LIP_OK;
 }
 
-// Copy n points after the current ones and build their scan layout; synchronises.
-lip_status add_points(lip_model* h, const void* X, const void* y, int64_t n, cudaStream_t st, cudaMemcpyKind kind) {
+// Copy n points after the current ones and build their scan layout.  Synchronises to read
+// the finiteness check back, unless `deferred`: then the check and the replacement of
+// non-finite points run on the device (sanitize.cu) and lip_check reports them.
+lip_status add_points(lip_model* h, const void* X, const void* y, int64_t n, cudaStream_t st, cudaMemcpyKind kind,
+                      bool deferred = false) {
     if (n < 0) return fail(LIP_ERR_ARG, "n = %lld < 0", (long long)n);
     if (n == 0) return LIP_OK;
     if (!X || !y) return fail(LIP_ERR_ARG, "X or y is NULL");
@@ -299,11 +302,22 @@ lip_status add_points(lip_model* h, const void* X, const void* y, int64_t n, cud
     const size_t es = h->esize;
     CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(h->X0) + (size_t)h->N * h->d * es, X, (size_t)n * h->d * es, kind, st));
     CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(h->y0) + (size_t)h->N * es, y, (size_t)n * es, kind, st));
+    if (deferred) {
+        CUDA_TRY(launch_sanitize(h->esize, h->X0, h->y0, h->N, n, h->d, h->status, h->status + 2, st));
+        count_launches(2);
+    }
     CUDA_TRY(cudaMemsetAsync(h->status + 1, 0, sizeof(unsigned), st));
     HotParams P;
     fill_hot_params(h, P, h->N, h->N + n);
     CUDA_TRY(launch_build_hot(h->esize, P, st));
     count_launches(1);
+    if (deferred) {                     // every new point is finite now
+        h->N += n;
+        h->tc_dirty = true;
+        h->s32_dirty = true;
+        h->loc_valid = false;
+        return LIP_OK;
+    }
     unsigned bad = 0;
     CUDA_TRY(cudaMemcpyAsync(&bad, h->status + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -713,6 +727,18 @@ lip_status lip_add_host(lip_handle h, const void* X, const void* y, int64_t n, v
     return add_points(h, X, y, n, static_cast<cudaStream_t>(stream), cudaMemcpyHostToDevice);
 }
 
+lip_status lip_add_async(lip_handle h, const void* X, const void* y, int64_t n, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    DeviceGuard g(h->device);
+    return add_points(h, X, y, n, static_cast<cudaStream_t>(stream), cudaMemcpyDeviceToDevice, true);
+}
+
+lip_status lip_add_host_async(lip_handle h, const void* X, const void* y, int64_t n, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    DeviceGuard g(h->device);
+    return add_points(h, X, y, n, static_cast<cudaStream_t>(stream), cudaMemcpyHostToDevice, true);
+}
+
 lip_status lip_clear(lip_handle h, void* stream) {
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
     DeviceGuard g(h->device);
@@ -1013,6 +1039,8 @@ lip_status lip_check(lip_handle h, void* stream) {
         CUDA_TRY(cudaStreamSynchronize(st));
     }
     if (bits & ERRBIT_TIMEOUT) return fail(LIP_ERR_TIMEOUT, "a bounded wait in a kernel gave up");
+    if (bits & ERRBIT_NONFINITE)
+        return fail(LIP_ERR_NONFINITE, "a deferred add held NaN or Inf (those points were replaced)");
     return LIP_OK;
 }
 

@@ -129,6 +129,11 @@ cudaError_t tc_eval_launch(const float* Q, int64_t nq, int d, const double* scal
                            cudaStream_t st);
 // Scratch of the scan's soft lockstep counters for nq queries against ntiles data tiles.
 size_t tc_arrive_bytes(int64_t nq, int64_t ntiles);
+// Deferred finiteness check of rows [n0, n0 + n) of X0 / y0 (element size es): records
+// ERRBIT_NONFINITE in *err and replaces non-finite rows by a finite one (sanitize.cu).
+// first_ok: one unsigned of scratch.
+cudaError_t launch_sanitize(int es, void* X0, void* y0, int64_t n0, int64_t n, int d, unsigned* err,
+                            unsigned* first_ok, cudaStream_t st);
 // Scratch of the device-side fallback for nq queries (fb_state above).
 size_t tc_fallback_state_bytes(int64_t nq);
 

@@ -110,6 +110,8 @@ def _load():
         "lip_shard_finish": [H, i64, P, P, P, P, P, P, P, P, P, P],
         "lip_estimate_M_part": [H, i32, i32, P, P],
         "lip_set_tc_window": [H, i64],
+        "lip_add_async": [H, P, P, i64, P],
+        "lip_add_host_async": [H, P, P, i64, P],
         "lip_debug_fail_alloc": [i64],
         "lip_debug_sqrt_fma": [P, P, i64, P],
         "lip_debug_scan_fault": [H, ctypes.c_uint64, i32],
@@ -199,6 +201,18 @@ def lip_add(h, X_ptr, y_ptr, n, stream=0):
 
 def lip_add_host(h, X_ptr, y_ptr, n, stream=0):
     return _lib.lip_add_host(h, X_ptr, y_ptr, n, stream)
+
+
+def lip_add_async(h, X_ptr, y_ptr, n, stream=0):
+    return _lib.lip_add_async(h, X_ptr, y_ptr, n, stream)
+
+
+def lip_add_host_async(h, X_ptr, y_ptr, n, stream=0):
+    return _lib.lip_add_host_async(h, X_ptr, y_ptr, n, stream)
+
+
+def lip_set_tc_window(h, nbytes):
+    return _lib.lip_set_tc_window(h, nbytes)
 
 
 def lip_clear(h, stream=0):
@@ -477,6 +491,22 @@ class LipFit:
             return a.data_ptr() if torch.is_tensor(a) else a.ctypes.data
 
         _check(_lib.lip_add_host(self.h, p(X), p(y), X.shape[0], _stream_ptr()), "lip_add_host")
+
+    def add_async(self, X, y):
+        """lip_add_async: no wait for the GPU; non-finite points are replaced on the device and
+        reported by the next check() (LIP_ERR_NONFINITE)."""
+        X, y = self._dev(X), self._dev(y)
+        _check(_lib.lip_add_async(self.h, X.data_ptr(), y.data_ptr(), X.shape[0], _stream_ptr()), "lip_add_async")
+
+    def add_host_async(self, X, y):
+        """lip_add_host_async: X, y host arrays (pinned CPU tensors keep the copy asynchronous;
+        they must stay alive until the stream has passed this call)."""
+        torch = _torch()
+
+        def p(a):
+            return a.data_ptr() if torch.is_tensor(a) else a.ctypes.data
+
+        _check(_lib.lip_add_host_async(self.h, p(X), p(y), X.shape[0], _stream_ptr()), "lip_add_host_async")
 
     def clear(self):
         _check(_lib.lip_clear(self.h, _stream_ptr()), "lip_clear")

@@ -258,3 +258,67 @@ def test_fma_sqrt_variants_vs_oracle(oracle_mod, variant, d, seed):
     b = gpu_eval(p, variant=variant, splits=5, tile_groups=16)
     for k in a:
         np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "tc_tf32"])
+def test_deferred_add_checks_on_the_device(oracle_mod, precision):
+    """lip_add_async / lip_add_host_async do not wait for the GPU: finite data give the same
+    handle as lip_add (bit for bit); a batch holding NaN / Inf is accepted, the bad points
+    are replaced on the device by the handle's first point, lip_check then reports
+    LIP_ERR_NONFINITE once, and the results equal those of the data with that replacement."""
+    import torch
+
+    from paper_2606_04670_b300 import lipfit as L
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    ndt = np.float64 if precision == "fp64" else np.float32
+    p = W.random_problem(1900, 3_000, 3, 500, norm=W.NORM_L2, dtype=ndt)
+    X, y, Q = (torch.as_tensor(a).to("cuda", dt) for a in (p.X, p.y, p.Q))
+
+    def model():
+        return L.LipFit(M=p.M, norm=p.norm, capacity=2 * p.N, d=p.d, precision=precision)
+
+    ref = model()
+    ref.add(X[:1000], y[:1000])
+    ref.add(X[1000:], y[1000:])
+    r_ref = {k: v.cpu().numpy() for k, v in ref.eval(Q).items()}
+    m = model()
+    m.add_async(X[:1000], y[:1000])
+    m.add_host_async(torch.as_tensor(p.X[1000:]).to(dt).pin_memory(), torch.as_tensor(p.y[1000:]).to(dt).pin_memory())
+    r = {k: v.cpu().numpy() for k, v in m.eval(Q).items()}
+    m.check()
+    for k in r_ref:
+        np.testing.assert_array_equal(r[k], r_ref[k], err_msg=k)
+    # a batch with NaN and Inf: accepted, replaced by point 0, reported once by check()
+    Xb, yb = p.X[:200].copy(), p.y[:200].copy()
+    Xb[3, 1] = np.nan
+    yb[17] = np.inf
+    Xb[150] = -np.inf
+    m.add_async(torch.as_tensor(Xb).to("cuda", dt), torch.as_tensor(yb).to("cuda", dt))
+    assert m.N == p.N + 200
+    r = {k: v.cpu().numpy() for k, v in m.eval(Q).items()}
+    with pytest.raises(L.LipError) as e:
+        m.check()
+    assert e.value.status == L.LIP_ERR_NONFINITE
+    m.check()                                  # reported once
+    Xf, yf = Xb.copy(), yb.copy()
+    for i in (3, 17, 150):
+        Xf[i], yf[i] = p.X[0], p.y[0]
+    Xall = np.concatenate([p.X, Xf]).astype(np.float64)
+    yall = np.concatenate([p.y, yf]).astype(np.float64)
+    orc = oracle_mod.evaluate(Xall, yall, p.Q, p.M, p.norm)
+    tol = FP64_TOL if precision == "fp64" else FP32_TOL
+    pf = W.Problem("d", Xall, yall, p.Q, p.M, p.norm, None, None)
+    compare(pf, r, orc, tol, f"deferred {precision}")
+    # an empty handle whose first new point is bad takes the first finite new point
+    e2 = model()
+    e2.add_async(torch.as_tensor(Xb[3:]).to("cuda", dt), torch.as_tensor(yb[3:]).to("cuda", dt))
+    with pytest.raises(L.LipError):
+        e2.check()
+    Xg, yg = Xb[3:].copy(), yb[3:].copy()
+    for i in (0, 14, 147):                     # rows 3, 17, 150 of the batch
+        Xg[i], yg[i] = Xb[4], yb[4]
+    orc = oracle_mod.evaluate(Xg.astype(np.float64), yg.astype(np.float64), p.Q, p.M, p.norm)
+    r = {k: v.cpu().numpy() for k, v in e2.eval(Q).items()}
+    compare(W.Problem("e", Xg, yg, p.Q, p.M, p.norm, None, None), r, orc, tol, f"deferred empty {precision}")
+    for h in (ref, m, e2):
+        h.close()

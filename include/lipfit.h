@@ -388,10 +388,10 @@ LIP_API lip_status lip_eval_local_k(lip_handle h, const void* Q, int64_t nq, int
  * (Eq. (optim)), d+_ik = dist_up(x^i, x^k) and d-_ik = dist_lo(x^i, x^k) of the handle's
  * norm, weights and monotone coordinates (both the symmetric distance without them).
  * One evaluation is a fused pass over the N (N - 1) / 2 unordered pairs (each pair's two
- * terms at once) in FP32 with FP64 sums; nothing pairwise is stored, and the terms owed to
- * the second datum of a violating pair are summed in 64-bit fixed point, so an evaluation
- * is reproducible bit for bit.  Any handle with N >= 1 (on FP64 handles the pair terms are
- * still FP32, from the values rounded once); M finite >= 0, p finite > 0. */
+ * terms at once) in FP32 with FP64 sums (in FP64 throughout on FP64 handles); nothing
+ * pairwise is stored, and the terms owed to the second datum of a violating pair are summed
+ * in 64-bit fixed point, so an evaluation is reproducible bit for bit.  Any handle with
+ * N >= 1; M finite >= 0, p finite > 0. */
 
 /* Phi and its gradient at eps (device double [N]): *f_out (host), grad (device double [N],
  * may be NULL).  Synchronises the stream. */

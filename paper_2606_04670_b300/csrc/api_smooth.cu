@@ -44,7 +44,7 @@ lip_status smooth_setup(lip_model* h, double M, double p, cudaStream_t st, Smoot
         P.scale[j] = M * h->sgnw[j];
     }
     P.p = p;
-    r.gx = (int)ceil_div(h->N, (int64_t)smooth_rows_per_block());
+    r.gx = (int)ceil_div(h->N, (int64_t)smooth_rows_per_block(h->esize));
     const int64_t tiles = P.npad / tile;
     // the pass is triangular (row i takes k > i), so many blocks are short or empty: fine
     // splits (up to 64) keep the last wave short
@@ -52,12 +52,17 @@ lip_status smooth_setup(lip_model* h, double M, double p, cudaStream_t st, Smoot
     const int64_t s = std::min<int64_t>(std::min<int64_t>(want, 64), tiles);
     P.points_per_split = round_up(ceil_div(P.npad, s), tile);
     P.nsplit = (int)ceil_div(P.npad, P.points_per_split);
-    LIP_TRY(h->sm_rec.ensure((size_t)P.npad * (P.dp + 4) * sizeof(float), "smoothing layout"));
+    if (h->esize == 8) {               // FP64 pair terms: the double layout
+        LIP_TRY(h->sm_rec.ensure((size_t)P.npad * (P.dp + 2) * sizeof(double), "smoothing layout"));
+        P.rec64 = static_cast<double*>(h->sm_rec.p);
+    } else {
+        LIP_TRY(h->sm_rec.ensure((size_t)P.npad * (P.dp + 4) * sizeof(float), "smoothing layout"));
+    }
     const size_t part_b = (size_t)P.nsplit * h->N * 2 * sizeof(double), col_b = (size_t)h->N * 8;
     LIP_TRY(h->sm_part.ensure(part_b + col_b + 16, "smoothing partials"));
     const int rb = smooth_reduce_blocks();
     LIP_TRY(h->sm_small.ensure((size_t)(4 + 3 * rb) * sizeof(double), "smoothing scalars"));
-    P.rec = static_cast<float*>(h->sm_rec.p);
+    if (h->esize != 8) P.rec = static_cast<float*>(h->sm_rec.p);
     P.partial = static_cast<double*>(h->sm_part.p);
     P.colfix = reinterpret_cast<unsigned long long*>(static_cast<char*>(h->sm_part.p) + part_b);
     P.zbits = reinterpret_cast<unsigned*>(static_cast<char*>(h->sm_part.p) + part_b + col_b);

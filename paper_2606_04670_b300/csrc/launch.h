@@ -292,6 +292,7 @@ struct SmoothParams {
     double scale[D_MAX];             // M * w * sign, in layout order
     double p;                        // penalty weight of Eq. (optim)
     float* rec;                      // [npad][dp + 4]: scaled coordinates, z = y + eps, 0, 0, 0
+    double* rec64;                   // FP64 handles: [npad][dp + 2] scaled coordinates, z, 0 (FP64 pass)
     double* partial;                 // [nsplit][N][2]: R - C and S per split (row side)
     unsigned long long* colfix;      // [N]: R - C of the column side, signed fixed point
     unsigned* zbits;                 // [2]: largest z and -z (order-preserving bits)
@@ -300,7 +301,7 @@ struct SmoothParams {
 };
 
 int smooth_tile();
-int smooth_rows_per_block();
+int smooth_rows_per_block(int es);
 int smooth_reduce_blocks();
 cudaError_t launch_smooth_objective(const SmoothParams& P, const double* eps, double* grad, double* block_sums,
                                     double* out, int gx, cudaStream_t st);

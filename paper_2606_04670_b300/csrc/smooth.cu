@@ -24,7 +24,8 @@
 // points).
 // Pair terms are FP32 on the scaled layout (coordinates times M w, mirrored where
 // decreasing, constrained first); each thread adds them in FP32 within a 128-point tile
-// and in FP64 across tiles, and the splits are summed in FP64 in a fixed order.
+// and in FP64 across tiles, and the splits are summed in FP64 in a fixed order.  FP64
+// handles take an FP64 layout and FP64 pair terms (smooth_pass64_kernel below).
 #include "launch.h"
 
 namespace lip {
@@ -223,6 +224,135 @@ __global__ void __launch_bounds__(SM_THREADS) smooth_pass_kernel(const SmoothPar
     }
 }
 
+// ------------------------------------------------------------ FP64 handles
+// The same objective with every pair term in FP64: the layout holds the scaled
+// coordinates and z in double, each thread owns one row, and the row and column sums are
+// formed exactly as above (the column terms in the same signed fixed point; its scale
+// comes from the range of z rounded outwards to FP32).
+
+__global__ void smooth_layout64_kernel(const SmoothParams P, const double* eps) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.npad) return;
+    double* r = P.rec64 + k * (P.dp + 2);
+    unsigned zmax = 0u, nzmax = 0u;
+    if (k < P.N) {
+        const double* X = static_cast<const double*>(P.X0);
+        for (int j = 0; j < P.dp; ++j) r[j] = j < P.d ? P.scale[j] * X[k * P.d + P.perm[j]] : 0.0;
+        const double z = static_cast<const double*>(P.y0)[k] + eps[k];
+        r[P.dp] = z;
+        zmax = ord_bits(__double2float_ru(z));
+        nzmax = ord_bits(__double2float_ru(-z));
+        P.colfix[k] = 0ull;
+    } else {
+        for (int j = 0; j < P.dp; ++j) r[j] = 0.0;
+        r[P.dp] = __longlong_as_double(0x7ff8000000000000ll);   // padding: NaN terms are never positive
+    }
+    r[P.dp + 1] = 0.0;
+    const unsigned act = __activemask();
+    zmax = __reduce_max_sync(act, zmax);
+    nzmax = __reduce_max_sync(act, nzmax);
+    if ((int)(threadIdx.x & 31) == __ffs(act) - 1) {
+        atomicMax(&P.zbits[0], zmax);
+        atomicMax(&P.zbits[1], nzmax);
+    }
+}
+
+// dist_up(x^i, x^k) in au and dist_up(x^k, x^i) in ar, in FP64.
+template <int NORM, int DP, bool MONO>
+__device__ __forceinline__ void smooth_dists64(const double (&xi)[DP], const double* xk, int C, double& au,
+                                               double& ar) {
+    au = 0.0;
+    ar = 0.0;
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+        const double t = xi[j] - xk[j];
+        if (MONO && j < C) {
+            const double u = fmax(t, 0.0), v = fmax(-t, 0.0);
+            if (NORM == LIP_L1) { au += u; ar += v; }
+            else if (NORM == LIP_L2) { au = fma(u, u, au); ar = fma(v, v, ar); }
+            else { au = fmax(au, u); ar = fmax(ar, v); }
+        } else {
+            const double a = fabs(t);
+            if (NORM == LIP_L1) au += a;
+            else if (NORM == LIP_L2) au = fma(t, t, au);
+            else au = fmax(au, a);
+            if (MONO) {
+                if (NORM == LIP_L1) ar += a;
+                else if (NORM == LIP_L2) ar = fma(t, t, ar);
+                else ar = fmax(ar, a);
+            }
+        }
+    }
+    if (NORM == LIP_L2) {
+        au = sqrt(au);
+        if (MONO) ar = sqrt(ar);
+    }
+    if (!MONO) ar = au;
+}
+
+// One row per thread: q = (v_ik)_+ - (v_ki)_+ for the data k > i of the split, summed into
+// R_i - C_i and S1 in FP64; the column terms -q as in smooth_pass_kernel.
+template <int NORM, int DP, bool MONO>
+__global__ void __launch_bounds__(SM_THREADS) smooth_pass64_kernel(const SmoothParams P) {
+    constexpr int PR = DP + 2;
+    __shared__ double tile[SM_TILE * PR];
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * SM_THREADS;
+    const int64_t ia = i0 + tid;
+    const int split = blockIdx.y;
+    const bool va = ia < P.N;
+    double xi[DP];
+#pragma unroll
+    for (int j = 0; j < DP; ++j) xi[j] = va ? P.rec64[ia * PR + j] : 0.0;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    const double z = va ? P.rec64[ia * PR + DP] : nan;           // an absent row's q is 0
+    const double fscale = col_scale(P);
+    double Da = 0.0, Sa = 0.0;
+    const int64_t split_begin = (int64_t)split * P.points_per_split;
+    const int64_t k_begin = split_begin > i0 ? split_begin : i0;     // i0 is a multiple of the tile
+    const int64_t k_end = split_begin + P.points_per_split < P.npad ? split_begin + P.points_per_split : P.npad;
+    for (int64_t k0 = k_begin; k0 < k_end; k0 += SM_TILE) {
+        __syncthreads();
+        for (int t = tid; t < SM_TILE * PR; t += SM_THREADS) tile[t] = P.rec64[k0 * PR + t];
+        __syncthreads();
+        const bool diag = k0 < i0 + SM_THREADS;                          // holds some k <= i
+        for (int kg = 0; kg < SM_TILE; kg += 4) {
+            double q[4];
+            double top = -INFINITY;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double* xk = tile + (kg + u) * PR;
+                double au, ar;
+                smooth_dists64<NORM, DP, MONO>(xi, xk, P.C, au, ar);
+                const double dz = z - xk[DP];
+                double v1 = dz - au;                  // v_ik
+                double w2 = dz + ar;                  // -v_ki
+                if (diag && k0 + kg + u <= ia) { v1 = -INFINITY; w2 = INFINITY; }
+                top = fmax(top, fmax(v1, -w2));
+                q[u] = fmax(v1, 0.0) + fmin(w2, 0.0);
+                Da += q[u];
+                Sa = fma(q[u], q[u], Sa);
+            }
+            if (__any_sync(0xffffffffu, top > 0.0)) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    double cs = q[u];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+                    const int64_t kk = k0 + kg + u;
+                    if ((tid & 31) == 0 && kk < P.N && cs != 0.0)
+                        atomicAdd(&P.colfix[kk], (unsigned long long)__double2ll_rn(-cs * fscale));
+                }
+            }
+        }
+    }
+    if (va) {
+        double* out = P.partial + ((int64_t)split * P.N + ia) * 2;
+        out[0] = Da;
+        out[1] = Sa;
+    }
+}
+
 // grad_i = 2 eps_i / p + 4 (R_i - C_i); per-block sums of S_i and eps_i^2.
 __global__ void __launch_bounds__(256) smooth_finish_kernel(const SmoothParams P, const double* eps, double* grad,
                                                             double* block_sums) {
@@ -328,8 +458,29 @@ void pass_shape(const SmoothParams& P, dim3 grid, cudaStream_t st) {
     else smooth_pass_kernel<NORM, DP, false><<<grid, SM_THREADS, 0, st>>>(P);
 }
 
+template <int NORM, int DP>
+void pass64_shape(const SmoothParams& P, dim3 grid, cudaStream_t st) {
+    if (P.C > 0) smooth_pass64_kernel<NORM, DP, true><<<grid, SM_THREADS, 0, st>>>(P);
+    else smooth_pass64_kernel<NORM, DP, false><<<grid, SM_THREADS, 0, st>>>(P);
+}
+
+template <int NORM>
+void pass64_norm(const SmoothParams& P, dim3 grid, cudaStream_t st) {
+    switch (P.dp) {
+        case 4: pass64_shape<NORM, 4>(P, grid, st); break;
+        case 8: pass64_shape<NORM, 8>(P, grid, st); break;
+        case 12: pass64_shape<NORM, 12>(P, grid, st); break;
+        case 16: pass64_shape<NORM, 16>(P, grid, st); break;
+        default: pass64_shape<NORM, 32>(P, grid, st); break;
+    }
+}
+
 template <int NORM>
 void pass_norm(const SmoothParams& P, dim3 grid, cudaStream_t st) {
+    if (P.es == 8) {
+        pass64_norm<NORM>(P, grid, st);
+        return;
+    }
     switch (P.dp) {
         case 4: pass_shape<NORM, 4>(P, grid, st); break;
         case 8: pass_shape<NORM, 8>(P, grid, st); break;
@@ -342,7 +493,7 @@ void pass_norm(const SmoothParams& P, dim3 grid, cudaStream_t st) {
 }  // namespace
 
 int smooth_tile() { return SM_TILE; }
-int smooth_rows_per_block() { return SM_THREADS * 2; }
+int smooth_rows_per_block(int es) { return es == 8 ? SM_THREADS : SM_THREADS * 2; }
 int smooth_reduce_blocks() { return RED_BLOCKS; }
 
 // Phi and its gradient at eps: layout, the pair pass, the finishing sums.  out[0] = Phi,
@@ -351,7 +502,8 @@ cudaError_t launch_smooth_objective(const SmoothParams& P, const double* eps, do
                                     double* out, int gx, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(P.zbits, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
-    smooth_layout_kernel<<<(unsigned)((P.npad + 255) / 256), 256, 0, st>>>(P, eps);
+    if (P.es == 8) smooth_layout64_kernel<<<(unsigned)((P.npad + 255) / 256), 256, 0, st>>>(P, eps);
+    else smooth_layout_kernel<<<(unsigned)((P.npad + 255) / 256), 256, 0, st>>>(P, eps);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)gx, (unsigned)P.nsplit);

@@ -1,6 +1,7 @@
 """Penalty smoothing (Sec. 4.4, Eq. (optim)) on the GPU against the FP64 oracle.
 
-The objective pass forms every pair term in FP32 and sums in FP64.  A term
+The objective pass forms every pair term in FP32 and sums in FP64 (FP64 handles: FP64
+pair terms, checked separately).  A term
 v = z_i - z_k - M d has an FP32 error below 2^-20 (|z_i| + |z_k| + M d) (the scaled
 coordinates, the distance and two subtractions, each a few ulps); a row of the gradient
 adds 4 N such terms, and the objective adds 2 |v| dv per positive term.  The tolerances
@@ -71,6 +72,29 @@ def test_objective_and_gradient_match_oracle(case):
     m.close()
 
 
+@pytest.mark.parametrize("case", range(len(CASES)), ids=lambda i: f"L{CASES[i].norm}-N{CASES[i].N}-d{CASES[i].d}")
+def test_fp64_handles_use_fp64_pair_terms(case):
+    """FP64 handles form the pair terms in FP64: each term's error is a few units of 2^-52
+    of |z_i| + |z_k| + M d, and the column terms are summed in fixed point with a resolution
+    of N (max z - min z) 2^-60 per term, so the gradient and the objective agree with the
+    oracle far below the FP32 path's tolerance."""
+    q = CASES[case]
+    p = W.Problem(q.name, np.asarray(q.X, np.float64), np.asarray(q.y, np.float64), q.Q, q.M, q.norm, q.mon, q.w)
+    m = _model(p, precision="fp64")
+    r = np.random.default_rng(100 + case)
+    M, pen = 1.3 * p.M, 50.0
+    for scale in (0.0, 0.05):
+        eps = scale * r.standard_normal(p.N)
+        f, g = m.smooth_objective(torch.as_tensor(eps).cuda(), M, pen)
+        fo, go, s1, s2 = O.smooth_objective(p.X, p.y, eps, M, pen, p.norm, mon=p.mon, w=p.w)
+        sc = _scale(p, M)
+        tol_g = 4.0 * p.N * 2.0 ** -45 * sc + p.N ** 2 * sc * 2.0 ** -58
+        err = np.abs(g.cpu().numpy() - go).max()
+        assert err <= tol_g, (err, tol_g)
+        assert abs(f - fo) <= 1e-10 * max(fo, 1.0) + 4.0 * 2.0 ** -45 * sc * np.sqrt(s1 + s2) * p.N, (f, fo)
+    m.close()
+
+
 def test_smooth_matches_oracle_minimiser():
     for k, p in enumerate([CASES[0], CASES[1], _noisy(440, 250, 4, 2, masked=True), _noisy(441, 300, 3, 3)]):
         M, pen = p.M, 30.0
@@ -133,7 +157,7 @@ def test_consistent_data_unchanged_and_errors():
     eps0 = 0.01 * np.random.default_rng(1).standard_normal(q.N)
     f, g = m.smooth_objective(torch.as_tensor(eps0).cuda(), q.M, 10.0)
     fo, go, _, _ = O.smooth_objective(q.X, q.y, eps0, q.M, 10.0, 2)
-    assert np.abs(g.cpu().numpy() - go).max() <= 4.0 * q.N * EPS32 * _scale(q, q.M)
+    assert np.abs(g.cpu().numpy() - go).max() <= 1e-9 * _scale(q, q.M)
     eps, f, it, _ = m.smooth_lipschitz(q.M, 10.0)
     out = m.eval(torch.as_tensor(q.X).cuda())
     ro = O.evaluate(q.X, q.y + eps.cpu().numpy(), q.X, q.M, 2)

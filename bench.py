@@ -151,6 +151,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--scan-variant", type=int, default=-1,
+                    help="FP32 handles: lip_set_tuning variant (0-7) instead of the autotuned one")
     ap.add_argument("--tc-variant", type=int, default=-1,
                     help="tensor-core handles: lip_set_tuning variant (0-5; -1 keeps the default 0)")
     ap.add_argument("--tc-window-mb", type=int, default=0,
@@ -494,6 +496,8 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
                 if args.tc_variant >= 0:
                     m.set_tuning(0, 0, args.tc_variant)
                 m.set_tc_window(args.tc_window_mb << 20)
+            elif prec == "fp32" and args.scan_variant >= 0:
+                m.set_tuning(0, 0, args.scan_variant)
             ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             m.set_timing_events(*ev)
             runs.append(dict(p=p, prec=prec, X=X, y=y, Q=Q, m=m, ev=ev, scan=[], bwd=[],
@@ -504,8 +508,8 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
         from paper_2606_04670_b300 import autotune as AT
         cache, save = _tune_cache()
         for r in runs:
-            if r["prec"].startswith("tc_"):
-                continue               # the launch shape knobs belong to the plain scan
+            if r["prec"].startswith("tc_") or (r["prec"] == "fp32" and args.scan_variant >= 0):
+                continue               # the launch shape knobs belong to the plain scan (or are set)
             r["m"].clear()
             r["m"].add(r["X"], r["y"])
             tuning[f"{NNAME[r['p'].norm]}/{r['prec']}"] = AT.tune_eval(r["m"], r["Q"], cache=cache)

@@ -526,6 +526,16 @@ LIP_API void lip_batch_free(lip_batch b);
  *                FP32 values differ in the last bits, so the selected index can differ
  *                where two bound values are that close (the bounds returned are the FP64
  *                values of the selected data either way); other shapes run 0 / 1.
+ *                6 / 7 (FP32 handles, exact shapes with d <= 8): the pruned scan, with half /
+ *                all of variant 0's queries per thread.  The data are kept in a spatial order
+ *                with a bounding box and value range per 32-point chunk, the queries are put
+ *                in spatial order per call, and a warp skips every chunk that provably cannot
+ *                lower H_up or raise H_lo of any of its queries (the test repeats the pair
+ *                arithmetic's FP32 operations on the box, so it is exact); the scan starts
+ *                near the block's queries and runs over all the data in one split.  The
+ *                extrema are those of the full scan; among data with exactly equal FP32
+ *                values the one met first in that order is chosen (the returned bounds are
+ *                its FP64 values).  Other shapes run 6 / 7 as 0 / 1.
  *                Ignored by the generic kernel.  For tensor-core handles (0 to 5): bit 0
  *                runs the tensor-core epilogue on 8 warps instead of 16; 0 / 1 run one
  *                persistent CTA per SM whose data sweeps keep a soft lockstep (the CTAs
@@ -560,6 +570,12 @@ LIP_API lip_status lip_get_tuning(lip_handle h, int32_t* tile_groups, int32_t* s
  * stream immediately before and after its all-pairs scan kernel, so that the kernel can
  * be timed alone on the stream it runs on.  NULL, NULL turns this off. */
 LIP_API lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, void* ev_after_scan);
+
+/* After a pruned scan (lip_set_tuning variants 6 / 7): *evaluated = the (warp, chunk)
+ * pairs the last scan of this handle evaluated, *total = all its (warp, chunk) pairs
+ * (warps x 32-point chunks); both -1 / *total = -1 when the last scan was not pruned.
+ * Synchronises the device to read the count. */
+LIP_API lip_status lip_last_scan_work(lip_handle h, int64_t* evaluated, int64_t* total);
 
 /* Tensor-core handles, variants 0 / 1 of lip_set_tuning: the data bytes over which the
  * persistent CTAs of one round may spread their sweeps of the data tiles (a producer runs

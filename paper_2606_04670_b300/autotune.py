@@ -32,8 +32,9 @@ def _bucket(n: int) -> int:
 
 def eval_key(model, nq: int) -> str:
     c = 0 if model.mon is None else int((model.mon != 0).sum())
-    # "eval2": the exact FP32 kernels have six variants (the FMA-pipe square roots)
-    return f"eval2/norm{model.norm}/C{c}/U{model.d - c}/prec{model.precision}/N2^{_bucket(model.N)}/Q2^{_bucket(nq)}"
+    # "eval3": the exact FP32 kernels have eight variants (the FMA-pipe square roots, the
+    # pruned scan)
+    return f"eval3/norm{model.norm}/C{c}/U{model.d - c}/prec{model.precision}/N2^{_bucket(model.N)}/Q2^{_bucket(nq)}"
 
 
 def load_cache(path: Optional[str] = None) -> Dict:
@@ -73,13 +74,14 @@ def _time(fn, reps: int = 3, warm: int = 1) -> float:
 def tune_eval(model, Q, tiles: Iterable[int] = (8, 16, 32, 64), splits: Iterable[int] = (0, 1, 2, 3, 4, 6, 8, 12, 16),
               variants: Optional[Iterable[int]] = None, cache: Optional[Dict] = None, reps: int = 3) -> Dict:
     """Time lip_eval on `model` for every (variant, tile_groups, splits); apply the fastest.
-    The variants default to the six of FP32 handles (queries per thread x the share of
-    square roots on the FMA pipe), to 0, 1 for FP64 handles and to 0-5 for tensor-core
-    handles (epilogue warps x the launch form), which ignore tiles and splits."""
+    The variants default to the eight of FP32 handles (queries per thread x the share of
+    square roots on the FMA pipe, and the pruned scan, which ignores splits), to 0, 1 for
+    FP64 handles and to 0-5 for tensor-core handles (epilogue warps x the launch form),
+    which ignore tiles and splits."""
     from .lipfit import LIP_FP32, LIP_FP64
     tc = model.precision not in (LIP_FP32, LIP_FP64)
     if variants is None:
-        variants = range(6) if model.precision == LIP_FP32 else (range(6) if tc else (0, 1))
+        variants = range(8) if model.precision == LIP_FP32 else (range(6) if tc else (0, 1))
     if tc:
         tiles, splits = (32,), (0,)
     key = eval_key(model, Q.shape[0])
@@ -90,7 +92,7 @@ def tune_eval(model, Q, tiles: Iterable[int] = (8, 16, 32, 64), splits: Iterable
     results = []
     for v in variants:
         for tg in tiles:
-            for sp in splits:
+            for sp in (splits if v < 6 or tc else list(splits)[:1]):
                 model.set_tuning(tg, sp, v)
                 ms = _time(lambda: model.eval(Q, need=("g", "idx_up", "idx_lo")), reps=reps)
                 results.append({"variant": model.tuning()["variant"], "tile_groups": tg, "splits": sp, "ms": ms,

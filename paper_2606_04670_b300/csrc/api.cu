@@ -131,6 +131,8 @@ void free_model(lip_model* h) {
     h->bwd.release();
     h->io.release();
     h->tc_q.release();
+    h->sp_data.release();
+    h->sp_q.release();
     h->tc_order.release();
     if (h->tc_btiles) cudaFree(h->tc_btiles);
     if (h->tc_maxbits) cudaFree(h->tc_maxbits);
@@ -315,6 +317,7 @@ lip_status add_points(lip_model* h, const void* X, const void* y, int64_t n, cud
         h->N += n;
         h->tc_dirty = true;
         h->s32_dirty = true;
+        h->sp_dirty = true;
         h->loc_valid = false;
         return LIP_OK;
     }
@@ -330,6 +333,7 @@ lip_status add_points(lip_model* h, const void* X, const void* y, int64_t n, cud
     h->N += n;
     h->tc_dirty = true;
     h->s32_dirty = true;
+    h->sp_dirty = true;
     h->loc_valid = false;
     return LIP_OK;
 }
@@ -372,9 +376,81 @@ int choose_splits(const lip_model* h, int64_t gx, int64_t tiles) {
     return best;
 }
 
+// The pruned scan (variants 6 / 7, scan_pruned.cuh): the data in spatial order with the
+// chunk records (rebuilt lazily after the data or M change), the queries in spatial order,
+// one launch over all the data (one split).
+lip_status scan_partials_pruned(lip_model* h, const void* Q, int64_t nq, cudaStream_t st, int* nsplit_out) {
+    const int64_t N = h->N;
+    const int64_t npad = round_up(N, PAD_POINTS), ngroups = npad / GROUP, nchunks = ngroups / CHUNK_GROUPS;
+    const int D = h->dl;
+    h->last_splits = ngroups > 0 ? 1 : 0;
+    *nsplit_out = 0;
+    if (ngroups == 0) return LIP_OK;
+    const int64_t gx = ceil_div(nq, (int64_t)SCAN_THREADS * h->pinfo.rows);
+    if (gx > 0x7fffffff) return fail(LIP_ERR_ARG, "nq = %lld is too large", (long long)nq);
+    const size_t perm_b = round_up(N * 4, 256), hot_b = round_up(ngroups * h->nch * 16, 256),
+                 box_b = round_up(nchunks * pruned_box_f4(D) * 16, 256), bnd_b = round_up(D_MAX * 8, 256),
+                 cnt_b = 256, sbox_b = round_up(nchunks / 8 * pruned_box_f4(D) * 16, 256);
+    LIP_TRY(h->sp_data.ensure(perm_b + hot_b + box_b + bnd_b + cnt_b + sbox_b + spatial_order_scratch(N),
+                              "pruned scan data"));
+    char* base = static_cast<char*>(h->sp_data.p);
+    int* dperm = reinterpret_cast<int*>(base);
+    void* shot = base + perm_b;
+    void* box = base + perm_b + hot_b;
+    float2* bounds = reinterpret_cast<float2*>(base + perm_b + hot_b + box_b);
+    unsigned long long* work = reinterpret_cast<unsigned long long*>(base + perm_b + hot_b + box_b + bnd_b);
+    void* sbox = base + perm_b + hot_b + box_b + bnd_b + cnt_b;
+    void* oscratch = base + perm_b + hot_b + box_b + bnd_b + cnt_b + sbox_b;
+    if (h->sp_dirty) {
+        CUDA_TRY(spatial_order(static_cast<const float*>(h->X0), N, h->d, dperm, bounds, oscratch, st));
+        HotParams Hp;
+        fill_hot_params(h, Hp, 0, N);
+        Hp.hot = shot;
+        Hp.gather = dperm;
+        Hp.err = h->status + 3;                         // the data were checked when added
+        CUDA_TRY(launch_build_hot(4, Hp, st));
+        CUDA_TRY(launch_pad_hot(4, shot, N, npad, h->nch, h->dl, st));
+        CUDA_TRY(launch_pruned_boxes(shot, N, nchunks, D, h->nch, h->aux != 0, box, sbox, st));
+        count_launches(4 + spatial_order_launches());
+        h->sp_dirty = false;
+    }
+    const size_t qp_b = round_up(nq * 4, 256);
+    LIP_TRY(h->sp_q.ensure(qp_b + spatial_order_scratch(nq), "pruned scan query order"));
+    int* qperm = static_cast<int*>(h->sp_q.p);
+    CUDA_TRY(spatial_order(static_cast<const float*>(Q), nq, h->d, qperm, nullptr,
+                           static_cast<char*>(h->sp_q.p) + qp_b, st));
+    count_launches(spatial_order_launches());
+    LIP_TRY(h->partial.ensure(std::max<size_t>(1, (size_t)nq * sizeof(PartialRec<float>)), "scan scratch"));
+    PrunedParams PP{};
+    fill_scan_params(h, PP.S);
+    PP.S.Q = Q;
+    PP.S.nq = nq;
+    PP.S.hot = shot;
+    PP.S.ngroups = ngroups;
+    PP.S.groups_per_split = ngroups;
+    PP.S.tile_groups = h->tile_groups;
+    PP.S.partial = h->partial.p;
+    PP.qperm = qperm;
+    PP.dperm = dperm;
+    PP.box = static_cast<const float4*>(box);
+    PP.sbox = static_cast<const float4*>(sbox);
+    PP.nchunks = nchunks;
+    PP.work = work;
+    CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), st));
+    if (h->ev_scan0) CUDA_TRY(cudaEventRecord(h->ev_scan0, st));
+    CUDA_TRY(h->pinfo.launch(PP, (int)gx, st));
+    if (h->ev_scan1) CUDA_TRY(cudaEventRecord(h->ev_scan1, st));
+    count_launches(1);
+    h->sp_total = gx * (SCAN_THREADS / 32) * nchunks;
+    *nsplit_out = 1;
+    return LIP_OK;
+}
+
 // The all-pairs scan of the plain layout into per-split partial records (h->partial);
 // *nsplit_out receives the number of splits (0 when the handle holds no points).
 lip_status scan_partials(lip_model* h, const void* Q, int64_t nq, cudaStream_t st, int* nsplit_out) {
+    if (h->pruned) return scan_partials_pruned(h, Q, nq, st, nsplit_out);
+    h->sp_total = -1;
     const int64_t ngroups = round_up(h->N, PAD_POINTS) / GROUP;
     const int tg = h->exact ? h->tile_groups : 1;
     const int64_t gx = ceil_div(nq, (int64_t)SCAN_THREADS * h->kinfo.rows);
@@ -747,6 +823,7 @@ lip_status lip_clear(lip_handle h, void* stream) {
     h->N = 0;
     h->tc_dirty = true;
     h->s32_dirty = true;
+    h->sp_dirty = true;
     h->loc_valid = false;
     return LIP_OK;
 }
@@ -760,6 +837,7 @@ lip_status lip_set_M(lip_handle h, double M, void* stream) {
     h->M = M;
     h->tc_dirty = true;
     h->s32_dirty = true;
+    h->sp_dirty = true;
     HotParams P;
     fill_hot_params(h, P, 0, h->N);
     CUDA_TRY(launch_build_hot(h->esize, P, static_cast<cudaStream_t>(stream)));
@@ -1049,8 +1127,8 @@ lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits, int
     if (tile_groups != 0 && tile_groups != 8 && tile_groups != 16 && tile_groups != 32 && tile_groups != 64)
         return fail(LIP_ERR_ARG, "tile_groups = %d is not 0, 8, 16, 32 or 64", tile_groups);
     if (splits < 0 || splits > 4096) return fail(LIP_ERR_ARG, "splits = %d is outside [0, 4096]", splits);
-    if (variant < -1 || variant >= SCAN_VARIANTS)
-        return fail(LIP_ERR_ARG, "variant = %d is outside [-1, %d]", variant, SCAN_VARIANTS - 1);
+    if (variant < -1 || variant >= SCAN_VARIANTS_ALL)
+        return fail(LIP_ERR_ARG, "variant = %d is outside [-1, %d]", variant, SCAN_VARIANTS_ALL - 1);
     if (h->tc && variant > 5) return fail(LIP_ERR_ARG, "variant = %d: tensor-core handles take 0 to 5", variant);
     if (h->esize == 8 && variant > 1) return fail(LIP_ERR_ARG, "variant = %d: FP64 handles take 0 or 1", variant);
     DeviceGuard gd(h->device);
@@ -1067,10 +1145,20 @@ lip_status lip_set_tuning(lip_handle h, int32_t tile_groups, int32_t splits, int
         }
     }
     if (variant >= 0 && h->exact) {
-        const ScanKernelInfo k = scan_exact_info(h->norm, h->C, h->d - h->C, variant);
+        // variants 6 / 7 (the pruned scan) keep the exact kernel of 0 / 1 for the shapes
+        // and precisions without a pruned instantiation
+        const ScanKernelInfo k = scan_exact_info(h->norm, h->C, h->d - h->C, variant < SCAN_VARIANTS ? variant : variant & 1);
         if (k.launch) {
             h->kinfo = k;
             h->variant = variant;
+            h->pruned = false;
+            if (variant >= SCAN_VARIANTS && h->esize == 4) {
+                const PrunedKernelInfo pk = scan_pruned_info(h->norm, h->C, h->d - h->C, variant);
+                if (pk.launch) {
+                    h->pinfo = pk;
+                    h->pruned = true;
+                }
+            }
         }
     }
     if (h->exact) {
@@ -1106,7 +1194,7 @@ lip_status lip_autotune(lip_handle h, const void* Q, int64_t nq, int32_t reps, i
     double best = 1e300;
     int32_t btg = keep_tg, bsp = keep_sp, bv = keep_v;
     const int tiles[] = {8, 16, 32, 64}, splits[] = {0, 1, 2, 3, 4, 6, 8, 12, 16};
-    const int nv = h->tc ? 6 : (h->esize == 8 ? 2 : (h->exact ? SCAN_VARIANTS : 1));
+    const int nv = h->tc ? 6 : (h->esize == 8 ? 2 : (h->exact ? SCAN_VARIANTS_ALL : 1));
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         s = fail(LIP_ERR_CUDA, "cudaEventCreate failed");
     } else {
@@ -1129,7 +1217,8 @@ lip_status lip_autotune(lip_handle h, const void* Q, int64_t nq, int32_t reps, i
                     std::sort(ms.begin(), ms.end());
                     const double med = ms[ms.size() / 2];
                     if (med < best) { best = med; btg = tg; bsp = sp; bv = v; }
-                    if (h->tc) break;                  // the tensor-core form ignores tiles and splits
+                    if (h->tc || h->pruned) break;     // the tensor-core form ignores tiles and splits,
+                                                       // the pruned scan the splits
                 }
     }
     if (e0) cudaEventDestroy(e0);
@@ -1156,7 +1245,9 @@ lip_status lip_get_tuning(lip_handle h, int32_t* tile_groups, int32_t* splits, i
     if (tile_groups) *tile_groups = h->tile_groups;
     if (splits) *splits = h->splits;
     if (last_splits) *last_splits = h->last_splits;
-    if (queries_per_thread) *queries_per_thread = (h->esize == 8 && h->fp64_mode == 0) ? h->kinfo32.rows : h->kinfo.rows;
+    if (queries_per_thread)
+        *queries_per_thread = h->pruned ? h->pinfo.rows
+                                        : ((h->esize == 8 && h->fp64_mode == 0) ? h->kinfo32.rows : h->kinfo.rows);
     return LIP_OK;
 }
 
@@ -1169,6 +1260,23 @@ lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, void* ev_af
 }
 
 uint64_t lip_kernel_launches(void) { return launches_total(); }
+
+lip_status lip_last_scan_work(lip_handle h, int64_t* evaluated, int64_t* total) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (!evaluated || !total) return fail(LIP_ERR_ARG, "an output pointer is NULL");
+    *evaluated = -1;
+    *total = h->sp_total;
+    if (h->sp_total < 0 || !h->sp_data.p) return LIP_OK;
+    const int64_t N = h->N, npad = round_up(N, PAD_POINTS), ngroups = npad / GROUP;
+    const size_t off = round_up(N * 4, 256) + round_up(ngroups * h->nch * 16, 256) +
+                       round_up(ngroups / CHUNK_GROUPS * pruned_box_f4(h->dl) * 16, 256) + round_up(D_MAX * 8, 256);
+    unsigned long long w = 0;
+    DeviceGuard gd(h->device);
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(&w, static_cast<char*>(h->sp_data.p) + off, sizeof w, cudaMemcpyDeviceToHost));
+    *evaluated = (int64_t)w;
+    return LIP_OK;
+}
 
 lip_status lip_set_tc_window(lip_handle h, int64_t bytes) {
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");

@@ -225,6 +225,7 @@ lip_status lip_smooth(lip_handle h, double M, double p, int32_t max_iter, int32_
     // y <- y + eps, M <- the smoothing constant, and the scan layout rebuilt for both
     CUDA_TRY(launch_apply_eps(h->y0, h->esize, x, h->N, st));
     h->s32_dirty = true;
+    h->sp_dirty = true;
     h->M = M;
     HotParams hp;
     fill_hot_params(h, hp, 0, h->N);

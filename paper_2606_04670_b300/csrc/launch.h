@@ -134,6 +134,39 @@ size_t tc_arrive_bytes(int64_t nq, int64_t ntiles);
 // first_ok: one unsigned of scratch.
 cudaError_t launch_sanitize(int es, void* X0, void* y0, int64_t n0, int64_t n, int d, unsigned* err,
                             unsigned* first_ok, cudaStream_t st);
+// ------------------------------------------------ pruned scan (scan_pruned.cuh)
+// Variants 6 and 7 of the exact FP32 scan: the data in spatial order with a box and value
+// range per 32-point chunk, chunks skipped when they cannot change a query's extrema.
+struct PrunedParams {
+    ScanParams S;                 // hot: the layout in position order; partial: [nq] records
+    const int* qperm;             // [nq] query position -> query index (spatial order)
+    const int* dperm;             // [N] data position -> data index
+    const float4* box;            // [nchunks][pruned_box_f4(D)] chunk records
+    const float4* sbox;           // [nchunks / 8][pruned_box_f4(D)]: records of 8 chunks (64 groups)
+    int64_t nchunks;
+    unsigned long long* work;     // nullable: evaluated (warp, chunk) pairs, summed per launch
+};
+// Chunk record: lo[D], hi[D] (layout coordinates), ylo (smallest y), yhv (largest value of
+// the lower bound's channel: y, or the aux channel for L1 with constrained coordinates).
+__host__ __device__ constexpr int pruned_box_f4(int D) { return (2 * D + 2 + 3) / 4; }
+// Largest dimension with a pruned instantiation.
+constexpr int PRUNED_DMAX = 8;
+__host__ __device__ constexpr bool pruned_shape_available(int C, int U) {
+    return C + U >= 1 && C + U <= PRUNED_DMAX;
+}
+using PrunedLaunchFn = cudaError_t (*)(const PrunedParams&, int gx, cudaStream_t);
+struct PrunedKernelInfo {
+    PrunedLaunchFn launch = nullptr;
+    const void* kernel = nullptr;
+    int rows = 0;
+    int nch = 0;
+};
+PrunedKernelInfo scan_pruned_info(int norm, int C, int U, int variant);
+// The chunk records of the position-ordered layout `hot` (N real points), then the
+// records of every 8 consecutive chunks (sbox, nchunks a multiple of 8).
+cudaError_t launch_pruned_boxes(const void* hot, int64_t N, int64_t nchunks, int D, int nch, bool aux, void* box,
+                                void* sbox, cudaStream_t st);
+
 // Scratch of the device-side fallback for nq queries (fb_state above).
 size_t tc_fallback_state_bytes(int64_t nq);
 

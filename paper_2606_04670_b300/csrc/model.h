@@ -130,6 +130,11 @@ struct lip_model {
     Scratch tc_q;
     Scratch tc_order;                  // the data's spatial order and position-ordered copies
     int64_t tc_window = 0;              // lip_set_tc_window (0: the library's default)
+    bool pruned = false;                // variants 6 / 7: the pruned scan (scan_pruned.cuh)
+    PrunedKernelInfo pinfo;
+    Scratch sp_data, sp_q;              // position-ordered layout and chunk records; query order
+    bool sp_dirty = true;               // the position-ordered layout needs a rebuild
+    int64_t sp_total = -1;              // (warp, chunk) pairs of the last pruned scan, -1 if none
     int* tc_fb_count = nullptr;         // device count of the last tensor-core lip_eval's fallback
     // local Lipschitz constants (Sec. 4.3), valid until the data change
     bool loc_valid = false;

@@ -518,14 +518,16 @@ struct HotParams {
     double scale[D_MAX];
     void* hot;
     unsigned* err;       // ERRBIT_NONFINITE if any value is not finite
+    const int* gather = nullptr;   // layout position k holds data point gather[k] (nullptr: k)
 };
 
 template <typename T>
 __global__ void build_hot_kernel(const HotParams P) {
     const int64_t k = P.k0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= P.k1) return;
-    const T* x = static_cast<const T*>(P.X0) + k * P.d;
-    const T yv = static_cast<const T*>(P.y0)[k];
+    const int64_t src = P.gather ? (int64_t)P.gather[k] : k;
+    const T* x = static_cast<const T*>(P.X0) + src * P.d;
+    const T yv = static_cast<const T*>(P.y0)[src];
     T* hot = static_cast<T*>(P.hot);
     const int64_t base = (k / GROUP) * (int64_t)P.nch * GROUP + (k % GROUP);
     bool finite = isfinite((double)yv);
@@ -570,6 +572,8 @@ __host__ __device__ constexpr int rows_for_dim(int D) { return D <= 4 ? 8 : (D <
 // one in eight (2, 3) or one in sixteen (4, 5) of the roots on the FMA pipe; other shapes
 // take them as 0 and 1.
 constexpr int SCAN_VARIANTS = 6;
+// Variants 6 and 7: the pruned scan (scan_pruned.cuh) with half / all of rows_for_dim.
+constexpr int SCAN_VARIANTS_ALL = 8;
 __host__ __device__ constexpr int rows_for_variant(int D, int v) {
     return (v & 1) == 0 ? rows_for_dim(D) : (rows_for_dim(D) / 2 > 0 ? rows_for_dim(D) / 2 : 1);
 }

@@ -110,6 +110,7 @@ def _load():
         "lip_shard_finish": [H, i64, P, P, P, P, P, P, P, P, P, P],
         "lip_estimate_M_part": [H, i32, i32, P, P],
         "lip_set_tc_window": [H, i64],
+        "lip_last_scan_work": [H, ctypes.POINTER(i64), ctypes.POINTER(i64)],
         "lip_add_async": [H, P, P, i64, P],
         "lip_add_host_async": [H, P, P, i64, P],
         "lip_debug_fail_alloc": [i64],
@@ -736,6 +737,13 @@ class LipFit:
 
     def check(self):
         _check(_lib.lip_check(self.h, _stream_ptr()), "lip_check")
+
+    def last_scan_work(self):
+        """(evaluated, total) (warp, chunk) pairs of the last pruned scan (variants 6 / 7);
+        (-1, -1) when the last scan was not pruned."""
+        e, t = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.lip_last_scan_work(self.h, ctypes.byref(e), ctypes.byref(t)), "lip_last_scan_work")
+        return e.value, t.value
 
     def set_tc_window(self, nbytes: int = 0):
         """Tensor-core handles: the data bytes a round's persistent CTAs may spread their

@@ -110,6 +110,84 @@ __device__ __forceinline__ bool chunk_needed(const float2 (&q)[C + U], const flo
     return !(skip_u && skip_l);
 }
 
+// True when the record (lo, hi, ylo, yhv) may lower mu_max or raise ml_min for some query
+// of the box [qlo, qhi] (the warp's queries).  The per-coordinate differences are bounded
+// for every query of the box at once: q - x >= qlo - hi and x - q >= lo - qhi, rounded the
+// same way, so each magnitude the pair code forms is at least the one used here; the
+// accumulation then mirrors chunk_needed, and with mu_max (ml_min) the loosest running
+// bound of the warp a record that fails here fails chunk_needed for every query.
+template <int NORM, int C, int U>
+__device__ __forceinline__ bool box_needed(const float* qlo, const float* qhi, const float* lo, const float* hi,
+                                           float ylo, float yhv, float mu_max, float ml_min) {
+    constexpr int D = C + U;
+    float a[D], b[D];                  // a: lower bound of q - x; b: lower bound of x - q
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        a[j] = __fsub_rn(qlo[j], hi[j]);
+        b[j] = __fsub_rn(lo[j], qhi[j]);
+    }
+    bool skip_u, skip_l;
+    if constexpr (NORM == LIP_L2) {
+        float s0 = 0.f;
+        if constexpr (U > 0) {
+            const float g = fmaxf(fmaxf(a[C], b[C]), 0.f);
+            s0 = __fmul_rn(g, g);
+#pragma unroll
+            for (int j = C + 1; j < D; ++j) {
+                const float gj = fmaxf(fmaxf(a[j], b[j]), 0.f);
+                s0 = __fmaf_rn(gj, gj, s0);
+            }
+        }
+        float su = s0, sl = s0;
+        if constexpr (C > 0) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                const float p = fmaxf(a[j], 0.f), n = fmaxf(b[j], 0.f);
+                if (j == 0 && U == 0) { su = __fmul_rn(p, p); sl = __fmul_rn(n, n); }
+                else { su = __fmaf_rn(p, p, su); sl = __fmaf_rn(n, n, sl); }
+            }
+        }
+        constexpr float GROW = 1.00000762939453125f;     // 1 + 2^-17
+        constexpr float TINY = 1.17549435e-38f;          // FLT_MIN
+        const float du = __fsub_rn(mu_max, ylo), dl = __fsub_rn(yhv, ml_min);
+        skip_u = du <= 0.f || su > fmaxf(__fmul_rn(__fmul_rn(du, du), GROW), TINY);
+        skip_l = dl <= 0.f || sl > fmaxf(__fmul_rn(__fmul_rn(dl, dl), GROW), TINY);
+    } else if constexpr (NORM == LIP_L1) {
+        float acc = 0.f;
+        if constexpr (U >= 2) {
+            acc = __fadd_rn(fmaxf(fmaxf(a[C], b[C]), 0.f), fmaxf(fmaxf(a[C + 1], b[C + 1]), 0.f));
+#pragma unroll
+            for (int j = C + 2; j < D; ++j) acc = __fadd_rn(acc, fmaxf(fmaxf(a[j], b[j]), 0.f));
+        } else if constexpr (U == 1) {
+            acc = fmaxf(fmaxf(a[C], b[C]), 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const float p = fmaxf(a[j], 0.f);
+            acc = (j == 0 && U == 0) ? p : __fadd_rn(acc, p);
+        }
+        skip_u = __fadd_rn(ylo, acc) >= mu_max;
+        skip_l = __fsub_rn(yhv, acc) <= ml_min;
+    } else {
+        float uu = 0.f;
+#pragma unroll
+        for (int j = C; j < D; ++j) uu = fmaxf(uu, fmaxf(a[j], b[j]));
+        float du = uu, dl = uu;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            du = fmaxf(du, a[j]);
+            dl = fmaxf(dl, b[j]);
+        }
+        skip_u = __fadd_rn(ylo, du) >= mu_max;
+        skip_l = __fsub_rn(yhv, dl) <= ml_min;
+    }
+    return !(skip_u && skip_l);
+}
+
+constexpr int PRUNED_LEAD = 2;     // super-chunks streamed before the first window
+constexpr int PRUNED_STAGES = 6;   // the pruned scan's ring of tiles
+constexpr int PRUNED_WIN = 256;    // super-chunks per window
+
 template <int NORM, int C, int U, int R>
 __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedParams PP) {
     using S = ExactShape<NORM, C, U>;
@@ -117,8 +195,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
     constexpr int NCH = S::NCH;
     constexpr int NB4 = pruned_box_f4(D);
     constexpr int NW = SCAN_THREADS / 32;
-    extern __shared__ __align__(128) float4 tiles[];   // SCAN_STAGES * tile_groups * NCH
-    __shared__ __align__(8) uint64_t bars[SCAN_STAGES];
+    // PRUNED_STAGES * tile_groups * NCH data, then PRUNED_STAGES * 8 chunk records
+    extern __shared__ __align__(128) float4 tiles[];
+    __shared__ __align__(8) uint64_t bars[PRUNED_STAGES];
+    __shared__ int fin[PRUNED_STAGES];           // warps done with the stage's current tile
+    __shared__ int last_issued[PRUNED_STAGES];   // ring step of the stage's last copy, -1 none
     __shared__ float red_c[NW][D + 1];
     __shared__ float red_d[NW];
     __shared__ int red_k[NW];
@@ -162,6 +243,29 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
             csum[D] += 1.f;
         }
     }
+    // the warp's query box (its finite queries), for the tests of whole records
+    float qlo[D], qhi[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        float a = __int_as_float(0x7f800000), b = -__int_as_float(0x7f800000);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (live[r]) {
+                a = fminf(a, qq[r][j].x);
+                b = fmaxf(b, qq[r][j].x);
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fminf(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        qlo[j] = a;
+        qhi[j] = b;
+    }
+    bool any_live = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) any_live = any_live || live[r];
+    const bool wlive = __any_sync(0xffffffffu, any_live);
     // the start chunk: the box centre nearest the centroid of the block's finite queries
 #pragma unroll
     for (int j = 0; j <= D; ++j)
@@ -172,7 +276,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
         for (int j = 0; j <= D; ++j) red_c[warp][j] = csum[j];
     if (tid == 0) {
 #pragma unroll
-        for (int s = 0; s < SCAN_STAGES; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < PRUNED_STAGES; ++s) {
+            mbar_init(&bars[s], 1);
+            fin[s] = 0;
+            last_issued[s] = -1;
+        }
         fence_mbar_init();
     }
     __syncthreads();
@@ -220,16 +328,49 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
     }
     __syncthreads();
 
-    const int ntiles = (int)(P.ngroups / tg);
-    const int t0 = (int)((int64_t)start_chunk * CHUNK_GROUPS / tg);
-    auto tile_of = [&](int t) { const int u = t0 + t; return u >= ntiles ? u - ntiles : u; };
-    if (tid == 0) {
-        for (int s = 0; s < SCAN_STAGES && s < ntiles; ++s) {
-            if (s == P.skip_tile) continue;
-            mbar_expect_tx(&bars[s], tile_bytes);
-            bulk_g2s(tiles + (size_t)s * tg * NCH, hot + (size_t)tile_of(s) * tg * NCH, tile_bytes, &bars[s]);
+    // The sweep runs over super-chunks (8 chunks, 64 groups) in cyclic order from the start
+    // one.  The first PRUNED_LEAD are streamed as they are; the rest go in windows of
+    // PRUNED_WIN, each reduced first to the super-chunks that some warp of the block may
+    // still need (tested against the running bounds, which only tighten afterwards, so a
+    // super-chunk left out then would be skipped later too).  Only the listed tiles are
+    // copied to shared memory.
+    const int nsuper = (int)(PP.nchunks / 8);
+    const int sup0 = start_chunk / 8;
+    const int tps = TILE_GROUPS_MAX / tg;             // tiles per super-chunk
+    __shared__ int seq[PRUNED_WIN * (TILE_GROUPS_MAX / 8)];
+    __shared__ unsigned wmask[PRUNED_WIN / 32];
+    __shared__ int seq_len;
+    // the stages' copies of the tile's chunk records follow the data stages
+    float4* recs = tiles + (size_t)PRUNED_STAGES * tg * NCH;
+    const uint32_t rec_bytes = (uint32_t)(tg / CHUNK_GROUPS) * NB4 * 16u;
+    auto issue = [&](int step, int tile) {            // one thread: the bulk copies of ring step `step`
+        if (step == P.skip_tile) return;
+        const int st = step % PRUNED_STAGES;
+        last_issued[st] = step;
+        mbar_expect_tx(&bars[st], tile_bytes + rec_bytes);
+        bulk_g2s(tiles + (size_t)st * tg * NCH, hot + (size_t)tile * tg * NCH, tile_bytes, &bars[st]);
+        bulk_g2s(recs + (size_t)st * 8 * NB4, PP.box + (size_t)tile * (tg / CHUNK_GROUPS) * NB4, rec_bytes, &bars[st]);
+    };
+    auto load_rec = [&](const float4* rec, float (&b)[NB4 * 4]) {     // from shared memory
+#pragma unroll
+        for (int k = 0; k < NB4; ++k) {
+            const float4 v = rec[k];
+            b[4 * k] = v.x;
+            b[4 * k + 1] = v.y;
+            b[4 * k + 2] = v.z;
+            b[4 * k + 3] = v.w;
         }
-    }
+    };
+    auto load_box = [&](const float4* rec, float (&b)[NB4 * 4]) {
+#pragma unroll
+        for (int k = 0; k < NB4; ++k) {
+            const float4 v = __ldg(rec + k);
+            b[4 * k] = v.x;
+            b[4 * k + 1] = v.y;
+            b[4 * k + 2] = v.z;
+            b[4 * k + 3] = v.w;
+        }
+    };
 
     float mu[R], ml[R], pu[R], pl[R];
     int bu[R], bl[R];
@@ -242,96 +383,163 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
         bu[r] = -1;
         bl[r] = -1;
     }
+    // true when some query of this thread may need the record b
+    auto needs = [&](const float (&b)[NB4 * 4]) {
+        bool need = false;
+        if (b[2 * D] == b[2 * D]) {                    // the record holds data
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                need = need || (live[r] && chunk_needed<NORM, C, U>(qq[r], b, b + D, b[2 * D], b[2 * D + 1], mu[r], ml[r]));
+        }
+        return need;
+    };
     unsigned evaluated = 0;
-    bool super_need = false;        // the current 8 chunks (64 groups) may be needed
+    // the warp's loosest running bounds (largest mu, smallest ml of its finite queries)
+    auto warp_bounds = [&](float& mmax, float& mmin) {
+        mmax = -__int_as_float(0x7f800000);
+        mmin = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (live[r]) {
+                mmax = fmaxf(mmax, mu[r]);
+                mmin = fminf(mmin, ml[r]);
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mmax = fmaxf(mmax, __shfl_xor_sync(0xffffffffu, mmax, o));
+            mmin = fminf(mmin, __shfl_xor_sync(0xffffffffu, mmin, o));
+        }
+    };
 
-    int t = 0;
+    int step = 0;                   // tiles this block has taken from the ring
     bool ok = true;
-    for (; t < ntiles; ++t) {
-        const int s = t % SCAN_STAGES;
-        const uint32_t par = (uint32_t)(t / SCAN_STAGES) & 1u;
-        const bool got = mbar_wait_bounded(&bars[s], par, P.err, P.wait_ns);
-        if (!__syncthreads_and(got)) { ok = false; break; }
-        const float4* tile = tiles + (size_t)s * tg * NCH;
-        const int64_t tg0 = (int64_t)tile_of(t) * tg;        // first group of the tile
-        for (int c = 0; c < tg; c += CHUNK_GROUPS) {
-            const int chunk = (int)((tg0 + c) / CHUNK_GROUPS);
-            // the record of 8 chunks first: its box contains theirs and its value range
-            // theirs, so where it rules a query out, each of the 8 would too
-            if ((chunk & 7) == 0) {
-                float sb[NB4 * 4];
-#pragma unroll
-                for (int k = 0; k < NB4; ++k) {
-                    const float4 v = __ldg(PP.sbox + (int64_t)(chunk >> 3) * NB4 + k);
-                    sb[4 * k] = v.x;
-                    sb[4 * k + 1] = v.y;
-                    sb[4 * k + 2] = v.z;
-                    sb[4 * k + 3] = v.w;
+    for (int s_begin = 0; ok && s_begin < nsuper;) {
+        const bool lead = s_begin == 0;
+        const int s_count = min(lead ? PRUNED_LEAD : PRUNED_WIN, nsuper - s_begin);
+        if (lead) {
+            if (tid == 0) {
+                for (int i = 0; i < s_count * tps; ++i) {
+                    int sp = sup0 + i / tps;
+                    if (sp >= nsuper) sp -= nsuper;
+                    seq[i] = sp * tps + i % tps;
                 }
+                seq_len = s_count * tps;
+            }
+        } else {
+            if (tid < PRUNED_WIN / 32) wmask[tid] = 0u;
+            __syncthreads();
+            float mmax, mmin;
+            warp_bounds(mmax, mmin);
+            for (int i0 = 0; i0 < s_count; i0 += 32) {
                 bool need8 = false;
-                if (sb[2 * D] == sb[2 * D]) {
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        need8 = need8 ||
-                                (live[r] && chunk_needed<NORM, C, U>(qq[r], sb, sb + D, sb[2 * D], sb[2 * D + 1], mu[r], ml[r]));
+                if (wlive && i0 + lane < s_count) {
+                    int sp = sup0 + s_begin + i0 + lane;
+                    if (sp >= nsuper) sp -= nsuper;
+                    float sb[NB4 * 4];
+                    load_box(PP.sbox + (int64_t)sp * NB4, sb);
+                    need8 = sb[2 * D] == sb[2 * D] &&
+                            box_needed<NORM, C, U>(qlo, qhi, sb, sb + D, sb[2 * D], sb[2 * D + 1], mmax, mmin);
                 }
-                super_need = __any_sync(0xffffffffu, need8);
+                const unsigned bits = __ballot_sync(0xffffffffu, need8);
+                if (lane == 0 && bits) atomicOr(&wmask[i0 >> 5], bits);
             }
-            if (!super_need) continue;
-            float bx[NB4 * 4];
-#pragma unroll
-            for (int k = 0; k < NB4; ++k) {
-                const float4 v = __ldg(PP.box + (int64_t)chunk * NB4 + k);
-                bx[4 * k] = v.x;
-                bx[4 * k + 1] = v.y;
-                bx[4 * k + 2] = v.z;
-                bx[4 * k + 3] = v.w;
+            __syncthreads();
+            if (tid == 0) {
+                int n = 0;
+                for (int i = 0; i < s_count; ++i) {
+                    if (!((wmask[i >> 5] >> (i & 31)) & 1u)) continue;
+                    int sp = sup0 + s_begin + i;
+                    if (sp >= nsuper) sp -= nsuper;
+                    for (int k = 0; k < tps; ++k) seq[n++] = sp * tps + k;
+                }
+                seq_len = n;
             }
-            const float ylo = bx[2 * D], yhv = bx[2 * D + 1];
-            bool need = false;
-            if (ylo == ylo) {                                 // the chunk holds data
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    need = need || (live[r] && chunk_needed<NORM, C, U>(qq[r], bx, bx + D, ylo, yhv, mu[r], ml[r]));
+        }
+        __syncthreads();
+        const int len = seq_len;
+        if (tid == 0)
+            for (int k = 0; k < PRUNED_STAGES && k < len; ++k) issue(step + k, seq[k]);
+        // The warps take the batch's tiles independently: a warp waits for a tile's copies,
+        // tests and evaluates its chunks, and counts itself out of the stage; the last warp
+        // out of a stage refills it with the tile PRUNED_STAGES ahead, so a warp with little
+        // to evaluate runs up to that far ahead of the others instead of waiting at a block
+        // barrier after every tile.
+        bool ok_w = true;
+        for (int i = 0; i < len; ++i) {
+            const int st = (step + i) % PRUNED_STAGES;
+            const uint32_t par = (uint32_t)((step + i) / PRUNED_STAGES) & 1u;
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[st], par, P.err, P.wait_ns))) {
+                ok_w = false;
+                break;
             }
-            if (!__any_sync(0xffffffffu, need)) continue;
-            ++evaluated;
+            const float4* tile = tiles + (size_t)st * tg * NCH;
+            const float4* trec = recs + (size_t)st * 8 * NB4;
+            const int64_t tg0 = (int64_t)seq[i] * tg;           // first group of the tile
+            const int chunk0 = (int)(tg0 / CHUNK_GROUPS), nck = tg / CHUNK_GROUPS;
+            // lane k tests chunk k of the tile against the warp's query box and loosest
+            // bounds; only the chunks that pass get the per-query test
+            float mmax, mmin;
+            warp_bounds(mmax, mmin);
+            bool cand = false;
+            if (wlive && lane < nck) {
+                float cb[NB4 * 4];
+                load_rec(trec + lane * NB4, cb);
+                cand = cb[2 * D] == cb[2 * D] &&
+                       box_needed<NORM, C, U>(qlo, qhi, cb, cb + D, cb[2 * D], cb[2 * D + 1], mmax, mmin);
+            }
+            for (unsigned left = __ballot_sync(0xffffffffu, cand); left; left &= left - 1) {
+                const int k = __ffs(left) - 1;
+                const int chunk = chunk0 + k, c = k * CHUNK_GROUPS;
+                float bx[NB4 * 4];
+                load_rec(trec + k * NB4, bx);
+                if (!__any_sync(0xffffffffu, needs(bx))) continue;
+                ++evaluated;
 #pragma unroll 2
-            for (int gi = 0; gi < CHUNK_GROUPS; ++gi) {
-                float4 x[NCH];
+                for (int gi = 0; gi < CHUNK_GROUPS; ++gi) {
+                    float4 x[NCH];
 #pragma unroll
-                for (int ch = 0; ch < NCH; ++ch) x[ch] = tile[(c + gi) * NCH + ch];
+                    for (int ch = 0; ch < NCH; ++ch) x[ch] = tile[(c + gi) * NCH + ch];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        float vu[4], vl[4];
+                        group_values<NORM, C, U>(qq[r], x, vu, vl);
+                        mu[r] = min3f(min3f(mu[r], vu[0], vu[1]), vu[2], vu[3]);
+                        ml[r] = max3f(max3f(ml[r], vl[0], vl[1]), vl[2], vl[3]);
+                    }
+                }
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    float vu[4], vl[4];
-                    group_values<NORM, C, U>(qq[r], x, vu, vl);
-                    mu[r] = min3f(min3f(mu[r], vu[0], vu[1]), vu[2], vu[3]);
-                    ml[r] = max3f(max3f(ml[r], vl[0], vl[1]), vl[2], vl[3]);
+                    bu[r] = (mu[r] < pu[r]) ? chunk : bu[r];
+                    pu[r] = mu[r];
+                    bl[r] = (ml[r] > pl[r]) ? chunk : bl[r];
+                    pl[r] = ml[r];
                 }
             }
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                bu[r] = (mu[r] < pu[r]) ? chunk : bu[r];
-                pu[r] = mu[r];
-                bl[r] = (ml[r] > pl[r]) ? chunk : bl[r];
-                pl[r] = ml[r];
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();                          // this warp's reads of the stage are done
+                if (atomicAdd(&fin[st], 1) == NW - 1) {
+                    fin[st] = 0;
+                    if (i + PRUNED_STAGES < len) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue(step + i + PRUNED_STAGES, seq[i + PRUNED_STAGES]);
+                    }
+                }
             }
         }
-        __syncthreads();   // every thread is done with stage s
-        if (tid == 0 && t + SCAN_STAGES < ntiles && t + SCAN_STAGES != P.skip_tile) {
-            mbar_expect_tx(&bars[s], tile_bytes);
-            bulk_g2s(tiles + (size_t)s * tg * NCH, hot + (size_t)tile_of(t + SCAN_STAGES) * tg * NCH, tile_bytes,
-                     &bars[s]);
+        ok = __syncthreads_and(ok_w);
+        if (!ok && tid == 0) {
+            // as in scan_block: wait (bounded) for every copy still in flight
+            for (int s2 = 0; s2 < PRUNED_STAGES; ++s2)
+                if (last_issued[s2] >= 0)
+                    mbar_wait_bounded(&bars[s2], (uint32_t)(last_issued[s2] / PRUNED_STAGES) & 1u, nullptr);
         }
+        step += len;
+        s_begin += s_count;
     }
     if (PP.work && lane == 0 && evaluated) atomicAdd(PP.work, (unsigned long long)evaluated);
     PartialRec<float>* out = static_cast<PartialRec<float>*>(P.partial);
     if (!ok) {
-        // as in scan_block: wait (bounded) for the copies still in flight, then give up
-        if (tid == 0) {
-            for (int u = t; u < ntiles && u < t + SCAN_STAGES; ++u)
-                if (u != P.skip_tile) mbar_wait_bounded(&bars[u % SCAN_STAGES], (uint32_t)(u / SCAN_STAGES) & 1u, nullptr);
-        }
 #pragma unroll
         for (int r = 0; r < R; ++r)
             if (qidx[r] >= 0)

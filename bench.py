@@ -63,6 +63,9 @@ TC_I_EPI = 6
 # entry is removed whenever its kernel changes, until it is captured again.
 KERNEL_DRAM_BYTES = {
     ("monotone_d4", 2): 19.136000e6 + 11.619840e6,     # scan_exact_kernel<L2, C=2, U=2, R=4>
+    ("monotone_d4", 1, "pruned"): 24.820e6 + 1.462e6,  # scan_pruned_kernel<L1, C=2, U=2, R=4>
+    ("monotone_d4", 2, "pruned"): 24.520e6 + 1.815e6,  # scan_pruned_kernel<L2, C=2, U=2, R=4>
+    ("monotone_d4", 3, "pruned"): 24.930e6 + 2.070e6,  # scan_pruned_kernel<Linf, C=2, U=2, R=4>
     ("grad_d8", 2): 16.66e6 + 13.47e6,                 # scan_exact_kernel<L2, C=4, U=4, R=2>
     ("cluster_d16", 2): 618.02e6 + 185.20e6,           # scan_exact_kernel<L2, C=0, U=16, R=2>
     ("cluster_d16_tc", 2): 7185.37e6 + 1213.84e6,      # tc_scan_kernel<K=16, 4 parts, TF32> (persistent, soft lockstep)
@@ -74,9 +77,10 @@ KERNEL_DRAM_BYTES = {
 }
 
 
-def traffic_for(args, name, norm):
+def traffic_for(args, name, norm, pruned=False):
     """The stored DRAM bytes of a workload's dominant kernel, at the full workload size only."""
-    return None if getattr(args, "queries", 0) else KERNEL_DRAM_BYTES.get((name, norm))
+    key = (name, norm, "pruned") if pruned else (name, norm)
+    return None if getattr(args, "queries", 0) else KERNEL_DRAM_BYTES.get(key)
 
 
 def i_pair(norm: int, d: int, c: int) -> int:
@@ -558,9 +562,22 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
             f"R={rd['m'].tuning()['queries_per_thread']}> {rd['prec']}")
     if rd["prec"] == "fp64":
         kern = "FP32 screen " + kern.replace(" fp64", "") + " + screen64_kernel (FP64 candidates)"
-    roof = ctx.roofline(kern, p.nq * p.N, avg[kdom], ip, mufu_per_pair(p.norm, c), clocks,
-                        traffic_for(args, name, p.norm) if rd["prec"] == "fp32" else None,
+    # the pruned scan (variants 6, 7) evaluates only the (warp, chunk) pairs its bound test
+    # keeps: its roofline counts the pairs it evaluated, the whole pair space stays in value
+    tun_dom = rd["m"].tuning()
+    evaluated, wtotal = rd["m"].last_scan_work() if rd["prec"] == "fp32" else (-1, -1)
+    share = evaluated / wtotal if wtotal > 0 and evaluated >= 0 else 1.0
+    if wtotal > 0:
+        kern = (f"scan_pruned_kernel<{NNAME[p.norm]}, C={c}, U={p.d - c}, R={tun_dom['queries_per_thread']}> fp32 "
+                f"(variant {tun_dom['variant']})")
+    roof = ctx.roofline(kern, p.nq * p.N * share, avg[kdom], ip, mufu_per_pair(p.norm, c), clocks,
+                        traffic_for(args, name, p.norm, pruned=wtotal > 0) if rd["prec"] == "fp32" else None,
                         fma=fma_lanes_per_pair(p.norm, p.d, c))
+    if wtotal > 0:
+        roof["pruned"] = {"evaluated_warp_chunks": evaluated, "warp_chunks": wtotal, "evaluated_share": share,
+                          "pairs_per_s_whole_space": p.nq * p.N / (avg[kdom] / 1e3),
+                          "note": "achieved counts the pairs of the evaluated 32-point chunks (share x Q x N); "
+                                  "the per-chunk bound tests are not counted"}
     if rd["prec"] in ("tc_tf32", "tc_bf16", "tc_fp16"):
         roof = tc_roofline(ctx, rd["prec"], p.d, p.nq * p.N, avg[kdom], roof, traffic_for(args, name, p.norm))
 

@@ -30,11 +30,20 @@ def _bucket(n: int) -> int:
     return int(math.floor(math.log2(max(1, n))))
 
 
+PRUNED_DMAX = 8        # the pruned scan's instantiations (FP32, d <= 8)
+
+
+def pruned_capable(model) -> bool:
+    from .lipfit import LIP_FP32
+    return model.precision == LIP_FP32 and model.d <= PRUNED_DMAX
+
+
 def eval_key(model, nq: int) -> str:
     c = 0 if model.mon is None else int((model.mon != 0).sum())
-    # "eval3": the exact FP32 kernels have eight variants (the FMA-pipe square roots, the
-    # pruned scan)
-    return f"eval3/norm{model.norm}/C{c}/U{model.d - c}/prec{model.precision}/N2^{_bucket(model.N)}/Q2^{_bucket(nq)}"
+    # "eval3": shapes with the pruned scan (variants 6, 7) among their eight variants;
+    # "eval2": the others (six FP32 variants, the FMA-pipe square roots)
+    tag = "eval3" if pruned_capable(model) else "eval2"
+    return f"{tag}/norm{model.norm}/C{c}/U{model.d - c}/prec{model.precision}/N2^{_bucket(model.N)}/Q2^{_bucket(nq)}"
 
 
 def load_cache(path: Optional[str] = None) -> Dict:
@@ -81,7 +90,8 @@ def tune_eval(model, Q, tiles: Iterable[int] = (8, 16, 32, 64), splits: Iterable
     from .lipfit import LIP_FP32, LIP_FP64
     tc = model.precision not in (LIP_FP32, LIP_FP64)
     if variants is None:
-        variants = range(8) if model.precision == LIP_FP32 else (range(6) if tc else (0, 1))
+        variants = ((range(8) if pruned_capable(model) else range(6)) if model.precision == LIP_FP32
+                    else (range(6) if tc else (0, 1)))
     if tc:
         tiles, splits = (32,), (0,)
     key = eval_key(model, Q.shape[0])

@@ -71,8 +71,9 @@ def test_c_abi_autotune_keeps_results():
 
 
 def test_tune_eval_sweeps_the_square_root_variants(oracle_mod):
-    """FP32 handles sweep all six variants by default; the tuned evaluation still matches the
-    oracle within the FP32 tolerance."""
+    """FP32 handles sweep all eight variants by default (the pruned ones, 6 and 7, take one
+    split candidate: they scan all the data in one launch); the tuned evaluation still
+    matches the oracle within the FP32 tolerance."""
     import torch
 
     from paper_2606_04670_b300 import autotune as AT
@@ -82,7 +83,7 @@ def test_tune_eval_sweeps_the_square_root_variants(oracle_mod):
     m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, mon=p.mon)
     Q = torch.as_tensor(p.Q).cuda()
     rec = AT.tune_eval(m, Q, tiles=(32,), splits=(0, 4), cache={}, reps=2)
-    assert rec["candidates"] == 12 and 0 <= rec["variant"] < 6
+    assert rec["candidates"] == 6 * 2 + 2 and 0 <= rec["variant"] < 8
     got = {k: v.cpu().numpy() for k, v in m.eval(Q).items()}
     m.close()
     sub = np.arange(0, p.nq, 15)

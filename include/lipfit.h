@@ -201,14 +201,36 @@ LIP_API lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* 
  * i < j of |y^i - y^j| / dist(x^i, x^j) with the symmetric weighted norm of the handle
  * (monotonicity does not enter).  N^2/2 work and no pair matrix is stored (Sec. 5).
  * Pairs with dist = 0 and equal y are skipped; dist = 0 with different y gives +Inf.
- * The candidate maximum is found in FP32 and the winning pair is re-evaluated in FP64;
- * ties go to the lowest (i, j).
+ * The result is the FP64 definition's, exactly: each pair's ratio in plain IEEE double
+ * arithmetic (|x^i_k - x^j_k| w_k per coordinate, summed / squared and summed / the
+ * largest, the square root for L2, then |y^i - y^j| / dist), the largest of them, the
+ * lowest (i, j) among equal values.  An FP32 screen finds the largest FP32 squared ratio
+ * q*; every pair whose FP32 squared ratio reaches q* (1 - 2^-16) is re-evaluated in FP64
+ * (the screen's relative error, (2d + 16) 2^-24 for FP32 data, keeps the exact maximum
+ * among them).  Norm weights that are not powers of two multiply the FP32 coordinate
+ * differences, so points a few FP32 units apart keep their exact difference.  FP64
+ * handles screen the data rounded to FP32: pairs closer than FP32 resolution are outside
+ * the bound there.
  * Outputs (host): *M_out, and the pair (*i_out < *j_out).  *i_out = *j_out = -1 with
  * *M_out = 0 only when no pair has a defined ratio: N < 2, or every pair is a repeated
  * point (dist = 0) with equal y.  Data at distinct points with constant y give M = 0 with
  * a real pair, the lowest (i, j) at positive distance.  Synchronises the stream. */
 LIP_API lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, int64_t* j_out,
                           void* stream);
+
+/* Form of lip_estimate_M on this handle.  0 (the default): FP32 handles with d <= 8 and
+ * the L2 or L-infinity norm take the pruned form (with L1 the box bound rules out too few
+ * pairs to pay for the spatial order); 2: the pruned form for every norm.  The pruned form: the data in spatial order with a box and y range per 32-point chunk
+ * and per 512-point tile; pass 1 finds the largest FP32 squared ratio q*, skipping the
+ * tile pairs and chunks whose exact FP32 upper bound (box gaps with the pair arithmetic's
+ * own operations, rcp.approx with a 2^-18 margin) is below the largest value already
+ * found; pass 2 re-evaluates in FP64 the pairs whose FP32 value reaches q* (1 - 2^-16)
+ * and keeps the largest; pass 3 finds the lowest (i, j) attaining it.  Other handles, and
+ * lip_estimate_M_part, run the full all-pairs screen followed by the same FP64 selection
+ * over the tile pairs whose screen maximum reaches q* (1 - 2^-16).  Both forms give the
+ * same result bit for bit.  1: always the full kernel.  LIP_ERR_ARG for a NULL handle or
+ * another value. */
+LIP_API lip_status lip_set_estimate_full(lip_handle h, int32_t full);
 
 /* ------------------------------------------------ several GPUs (one process per GPU) */
 /* The paper computes every bound and the estimate as one reduction over all data (Sec. 5:
@@ -257,11 +279,11 @@ LIP_API lip_status lip_shard_finish(lip_handle h, int64_t nq, const int64_t* key
 /* The Lipschitz-constant estimate over one block-cyclic share of the pairs, for ranks that
  * all hold the same data: the N^2/2 pairs are cut into tile pairs (I, J >= I) of 512
  * points, and part p of nparts takes the tile pairs with (I * tiles + J) mod nparts = p.
- * out (host double[4]) = {M over the part's pairs (FP64 re-evaluation of its FP32
- * winner), i, j, the winner's FP32 squared ratio}, or {0, -1, -1, -1} when the part has
- * no pair with a defined ratio.  The estimate over all pairs is the part whose FP32
- * squared ratio is largest, the lowest (i, j) on ties (lip_estimate_M's choice, bit for
- * bit).  0 <= part < nparts, else LIP_ERR_ARG.  Synchronises the stream. */
+ * out (host double[4]) = {M over the part's pairs (lip_estimate_M's exact FP64 selection
+ * restricted to them), i, j, M again as the ordering key}, or {0, -1, -1, -1} when the
+ * part has no pair with a defined ratio.  The estimate over all pairs is the part whose
+ * key is largest, the lowest (i, j) on ties (lip_estimate_M's result, bit for bit).
+ * 0 <= part < nparts, else LIP_ERR_ARG.  Synchronises the stream. */
 LIP_API lip_status lip_estimate_M_part(lip_handle h, int32_t part, int32_t nparts, double* out, void* stream);
 
 /* Largest N accepted by lip_estimate_M_noalloc. */

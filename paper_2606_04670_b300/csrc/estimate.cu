@@ -1,8 +1,9 @@
 // Lipschitz constant of the data (Sec. 5): M_est = max_{i<j} |y^i - y^j| / dist(x^i, x^j)
 // with the symmetric weighted norm, N^2/2 pair work and no pair matrix in memory.
 //
-// Layout: the same 4-point AoSoA groups as the envelope scan, but unscaled (w * sign
-// only) and without the aux channel.  Pair (i, j) is compared through the squared ratio
+// Layout: the same 4-point AoSoA groups as the envelope scan, without M, signs or the
+// aux channel; power-of-two norm weights scale it exactly, other weights multiply the
+// coordinate differences in the kernel (WT).  Pair (i, j) is compared through the squared ratio
 // (y_i - y_j)^2 * rcp(dist^2): one reciprocal per pair, no square root, no divide.
 // dist = 0 gives rcp = +Inf, so equal y (0 * Inf = NaN) drops out of the NaN-ignoring
 // max and different y gives +Inf, as the definition asks; padding points (y = NaN) and
@@ -13,56 +14,9 @@
 // registers and streams the J-tile from shared memory.  The winning J-chunk of each
 // thread row is rescanned to recover the exact j, CTAs write one candidate each, and a
 // single-CTA pass picks the maximum (lowest (i, j) on ties) and recomputes it in FP64.
-#include "launch.h"
+#include "estimate.cuh"
 
 namespace lip {
-
-constexpr int EST_THREADS = 128;
-constexpr int EST_R = 4;
-constexpr int EST_TILE = EST_THREADS * EST_R;        // points per I-tile and per J-tile
-constexpr int EST_TILE_GROUPS = EST_TILE / GROUP;
-constexpr int EST_NARROW_MAX = 16;                   // d above this takes estimate_wide_kernel
-
-template <int NORM, int D>
-__device__ __forceinline__ void est_group(const float2 (&xi)[D], float2 yi, const float4 (&x)[D + 1], float (&r2)[4]) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        float2 t[D];
-#pragma unroll
-        for (int j = 0; j < D; ++j) t[j] = sub2(xi[j], half_of(x[j], h));
-        float2 den;
-        if constexpr (NORM == LIP_L2) {
-            den = mul2(t[0], t[0]);
-#pragma unroll
-            for (int j = 1; j < D; ++j) den = fma2(t[j], t[j], den);
-        } else if constexpr (NORM == LIP_L1) {
-            float2 acc = make_float2(fabsf(t[0].x), fabsf(t[0].y));
-#pragma unroll
-            for (int j = 1; j < D; ++j) acc = make_float2(acc.x + fabsf(t[j].x), acc.y + fabsf(t[j].y));
-            den = mul2(acc, acc);
-        } else {
-            float a[D], b[D];
-#pragma unroll
-            for (int j = 0; j < D; ++j) { a[j] = fabsf(t[j].x); b[j] = fabsf(t[j].y); }
-            const float2 acc = make_float2(max_reduce<D>(a), max_reduce<D>(b));
-            den = mul2(acc, acc);
-        }
-        const float2 dy = sub2(yi, half_of(x[D], h));
-        const float2 num = mul2(dy, dy);
-        const float2 q = mul2(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
-        r2[2 * h] = q.x;
-        r2[2 * h + 1] = q.y;
-    }
-}
-
-// (ratio, i, j) ordering: larger ratio first, then lower i, then lower j.
-__device__ __forceinline__ bool est_better(float r, int i, int j, float rb, int ib, int jb) {
-    if (ib < 0) return i >= 0;
-    if (i < 0) return false;
-    if (r != rb) return r > rb;
-    if (i != ib) return i < ib;
-    return j < jb;
-}
 
 // Block reduction of the threads' best pairs (fixed shape, so the result does not depend
 // on timing) and the block's candidate record.
@@ -86,7 +40,7 @@ __device__ __forceinline__ void est_block_write(const EstParams& P, int bi, int 
     }
 }
 
-template <int NORM, int D>
+template <int NORM, int D, bool WT>
 __global__ void __launch_bounds__(EST_THREADS)
 estimate_kernel(const EstParams P) {
     constexpr int NCH = D + 1;
@@ -118,6 +72,9 @@ estimate_kernel(const EstParams P) {
         const float v = __ldg(g + D * GROUP + lane);
         yi[r] = make_float2(v, v);
     }
+    float2 wt[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) wt[j] = WT ? make_float2(P.w[j], P.w[j]) : make_float2(1.f, 1.f);
     __syncthreads();
 
     float best[EST_R], prev[EST_R];
@@ -134,7 +91,7 @@ estimate_kernel(const EstParams P) {
 #pragma unroll
             for (int r = 0; r < EST_R; ++r) {
                 float q[4];
-                est_group<NORM, D>(xi[r], yi[r], x, q);
+                est_group<NORM, D, WT>(xi[r], yi[r], x, wt, q);
                 best[r] = max3f(max3f(best[r], q[0], q[1]), q[2], q[3]);
             }
         }
@@ -159,7 +116,7 @@ estimate_kernel(const EstParams P) {
 #pragma unroll
             for (int ch = 0; ch < NCH; ++ch) x[ch] = tile[g * NCH + ch];
             float q[4];
-            est_group<NORM, D>(xi[r], yi[r], x, q);
+            est_group<NORM, D, WT>(xi[r], yi[r], x, wt, q);
 #pragma unroll
             for (int e = 0; e < 4; ++e)
                 if (jbest < 0 && q[e] == best[r]) jbest = bj * EST_TILE + g * GROUP + e;
@@ -177,7 +134,7 @@ estimate_kernel(const EstParams P) {
 // channel at a time (the packed form's duplicated registers do not fit at these widths);
 // the squared ratio is formed in the same order of operations as est_group, and the row
 // maximum is tracked per pair (strict >, so the lowest j on ties; NaN never wins).
-template <int NORM>
+template <int NORM, bool WT>
 __global__ void __launch_bounds__(EST_THREADS)
 estimate_wide_kernel(const EstParams P, int d) {
     const int nch = d + 1;
@@ -218,7 +175,7 @@ estimate_wide_kernel(const EstParams P, int d) {
             for (int r = 0; r < EST_R; ++r)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float t = xi[r][j] - xe[e];
+                    const float t = WT ? __fmul_rn(__fsub_rn(xi[r][j], xe[e]), P.w[j]) : xi[r][j] - xe[e];
                     if (NORM == LIP_L2) acc[r][e] = j == 0 ? t * t : fmaf(t, t, acc[r][e]);
                     else if (NORM == LIP_L1) acc[r][e] = j == 0 ? fabsf(t) : acc[r][e] + fabsf(t);
                     else acc[r][e] = j == 0 ? fabsf(t) : fmaxf(acc[r][e], fabsf(t));
@@ -247,23 +204,28 @@ estimate_wide_kernel(const EstParams P, int d) {
     est_block_write(P, bi, bj, tb, ti, tj);
 }
 
+// The ratio of data points i and j in FP64, in the definition's order of operations with
+// no contraction (the value of a plain IEEE double evaluation of Sec. 5's formula); -1 for
+// a pair at distance 0 with equal values, which the definition leaves out.
 template <typename T>
-__device__ double est_ratio_fp64(const EstFinalParams& P, int i, int j) {
+__device__ double est_ratio_fp64(const EstFinalParams& P, int64_t i, int64_t j) {
     const T* X = static_cast<const T*>(P.X0);
     const T* y = static_cast<const T*>(P.y0);
     double acc = 0.0;
     for (int c = 0; c < P.d; ++c) {
-        const double v = fabs((double)X[(int64_t)i * P.d + c] - (double)X[(int64_t)j * P.d + c]) * P.w[c];
-        if (P.norm == LIP_L1) acc += v;
-        else if (P.norm == LIP_L2) acc += v * v;
+        const double v = __dmul_rn(fabs(__dsub_rn((double)X[i * P.d + c], (double)X[j * P.d + c])), P.w[c]);
+        if (P.norm == LIP_L1) acc = __dadd_rn(acc, v);
+        else if (P.norm == LIP_L2) acc = __dadd_rn(acc, __dmul_rn(v, v));
         else acc = v > acc ? v : acc;
     }
-    const double dist = P.norm == LIP_L2 ? sqrt(acc) : acc;
-    const double dy = fabs((double)y[i] - (double)y[j]);
-    if (dist == 0.0) return dy == 0.0 ? 0.0 : (double)INFINITY;
-    return dy / dist;
+    const double dist = P.norm == LIP_L2 ? __dsqrt_rn(acc) : acc;
+    const double dy = fabs(__dsub_rn((double)y[i], (double)y[j]));
+    if (dist == 0.0) return dy == 0.0 ? -1.0 : (double)INFINITY;
+    return __ddiv_rn(dy, dist);
 }
 
+// q*: the largest FP32 squared ratio over the part's candidates; the exact selection's
+// words start from it.
 __global__ void estimate_final_kernel(const EstFinalParams P) {
     const int tid = threadIdx.x;
     float tb = -1.f;
@@ -290,18 +252,107 @@ __global__ void estimate_final_kernel(const EstFinalParams P) {
     if (tid == 0) {
         for (int w = 1; w < (int)(blockDim.x / 32); ++w)
             if (est_better(sb[w], si[w], sj[w], tb, ti, tj)) { tb = sb[w]; ti = si[w]; tj = sj[w]; }
-        double M = 0.0;
-        if (ti >= 0) M = P.elem_bytes == 8 ? est_ratio_fp64<double>(P, ti, tj) : est_ratio_fp64<float>(P, ti, tj);
-        P.out[0] = M;
-        P.out[1] = (double)ti;
-        P.out[2] = (double)tj;
-        if (P.write_key) P.out[3] = ti >= 0 ? (double)tb : -1.0;
+        P.state->q = ti >= 0 ? __float_as_int(tb) : -1;
+        P.state->ratio = 0ull;
+        P.state->key = ~0ull;
     }
+}
+
+// Exact selection (Sec. 5's maximum and the lowest (i, j) on ties, in FP64).  The screen's
+// FP32 squared ratio q of a pair is within a relative (2d + 16) 2^-24 of the exact one for
+// FP32 data (each weighted difference rounded at most three times, at most d + 2 roundings
+// in the sums and squares, a reciprocal of at most 2 ulps and the product), so the pair
+// with the largest FP64 ratio has q >= T = q* (1 - 2^-16) for every d <= 32, and its tile
+// pair's screen maximum reaches T.  Each such tile pair is visited again: its pairs' q
+// from the layout in shared memory (the same bound holds for this scalar form), and the
+// FP64 ratio of those with q >= T.  PASS 1 keeps the largest ratio R* (atomicMax of its
+// bits: non-negative doubles order as integers), PASS 2 the smallest key among the pairs
+// whose ratio is R*.  Data whose weighted coordinate differences fall into FP32's
+// subnormal range, or whose ratios overflow FP32, are outside the bound.
+template <typename T, int PASS>
+__global__ void __launch_bounds__(256) estimate_exact_kernel(const EstFinalParams P) {
+    const int bi = blockIdx.x, bj = blockIdx.y;
+    if (bj < bi || ((int64_t)bi * P.nb + bj) % P.nparts != P.part) return;
+    const int qb = *reinterpret_cast<const volatile int*>(&P.state->q);
+    if (qb < 0) return;
+    const float Tq = __fmul_rd(__int_as_float(qb), 0.9999847412109375f);      // q* (1 - 2^-16)
+    const float4 c = P.cand[(size_t)bi * P.nb + bj];
+    if (c.w == 0.f || !(c.x >= Tq)) return;
+    const double Rs =
+        PASS == 2 ? __longlong_as_double(*reinterpret_cast<const volatile long long*>(&P.state->ratio)) : 0.0;
+    const int nch = P.d + 1;
+    extern __shared__ __align__(16) float4 xs[];          // I-tile then J-tile, groups of the layout
+    float4* ti4 = xs;
+    float4* tj4 = xs + EST_TILE_GROUPS * nch;
+    for (int k = threadIdx.x; k < EST_TILE_GROUPS * nch; k += blockDim.x) {
+        ti4[k] = P.lay[(size_t)bi * EST_TILE_GROUPS * nch + k];
+        tj4[k] = P.lay[(size_t)bj * EST_TILE_GROUPS * nch + k];
+    }
+    __syncthreads();
+    const float* fi = reinterpret_cast<const float*>(ti4);
+    const float* fj = reinterpret_cast<const float*>(tj4);
+    double rbest = -1.0;
+    unsigned long long kbest = ~0ull;
+    for (int p = threadIdx.x; p < EST_TILE * EST_TILE; p += blockDim.x) {
+        const int a = p / EST_TILE, b = p % EST_TILE;
+        const int64_t i = (int64_t)bi * EST_TILE + a, j = (int64_t)bj * EST_TILE + b;
+        if (i >= j || j >= P.N) continue;
+        const float* pa = fi + (a / GROUP) * nch * GROUP + a % GROUP;
+        const float* pb = fj + (b / GROUP) * nch * GROUP + b % GROUP;
+        float acc = 0.f;
+        for (int k = 0; k < P.d; ++k) {
+            float t = __fsub_rn(pa[k * GROUP], pb[k * GROUP]);
+            if (P.weighted) t = __fmul_rn(t, (float)P.w[k]);
+            if (P.norm == LIP_L2) acc = __fmaf_rn(t, t, acc);
+            else if (P.norm == LIP_L1) acc = __fadd_rn(acc, fabsf(t));
+            else acc = fmaxf(acc, fabsf(t));
+        }
+        const float den = P.norm == LIP_L2 ? acc : __fmul_rn(acc, acc);
+        const float dy = __fsub_rn(pa[P.d * GROUP], pb[P.d * GROUP]);
+        const float q = __fmul_rn(__fmul_rn(dy, dy), rcp_approx(den));
+        if (!(q >= Tq)) continue;
+        const double r = est_ratio_fp64<T>(P, i, j);
+        if (PASS == 1) {
+            rbest = r > rbest ? r : rbest;
+        } else if (r == Rs) {
+            const unsigned long long key = ((unsigned long long)i << 32) | (unsigned long long)j;
+            kbest = key < kbest ? key : kbest;
+        }
+    }
+    unsigned long long v = PASS == 1 ? (rbest >= 0.0 ? (unsigned long long)__double_as_longlong(rbest) : 0ull) : kbest;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = PASS == 1 ? (u > v ? u : v) : (u < v ? u : v);
+    }
+    __shared__ unsigned long long red[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            v = PASS == 1 ? (red[w] > v ? red[w] : v) : (red[w] < v ? red[w] : v);
+        if (PASS == 1 && v != 0ull) atomicMax(&P.state->ratio, v);
+        if (PASS == 2 && v != ~0ull) atomicMin(&P.state->key, v);
+    }
+}
+
+// {R*, i, j} (and R* again as the key that orders parts), or {0, -1, -1} without a pair.
+__global__ void estimate_exact_finish_kernel(const EstFinalParams P) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const EstExactState S = *P.state;
+    const bool ok = S.q >= 0 && S.key != ~0ull;
+    const double M = ok ? __longlong_as_double((long long)S.ratio) : 0.0;
+    P.out[0] = M;
+    P.out[1] = ok ? (double)(S.key >> 32) : -1.0;
+    P.out[2] = ok ? (double)(S.key & 0xffffffffull) : -1.0;
+    if (P.write_key) P.out[3] = ok ? M : -1.0;
 }
 
 template <int NORM, int D>
 static cudaError_t launch_est(const EstParams& P, cudaStream_t st) {
-    estimate_kernel<NORM, D><<<dim3(P.nb, P.nb), EST_THREADS, 0, st>>>(P);
+    if (P.weighted) estimate_kernel<NORM, D, true><<<dim3(P.nb, P.nb), EST_THREADS, 0, st>>>(P);
+    else estimate_kernel<NORM, D, false><<<dim3(P.nb, P.nb), EST_THREADS, 0, st>>>(P);
     return cudaGetLastError();
 }
 
@@ -319,11 +370,12 @@ template <typename T>
 __global__ void est_layout_kernel(const HotParams P) {
     const int64_t k = P.k0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= P.k1) return;
-    const T* x = static_cast<const T*>(P.X0) + k * P.d;
+    const int64_t src = P.gather ? (int64_t)P.gather[k] : k;     // position k holds point src
+    const T* x = static_cast<const T*>(P.X0) + src * P.d;
     float* lay = static_cast<float*>(P.hot);
     const int64_t base = (k / GROUP) * (int64_t)P.nch * GROUP + (k % GROUP);
     for (int j = 0; j < P.d; ++j) lay[base + (int64_t)j * GROUP] = (float)(P.scale[j] * (double)x[j]);
-    lay[base + (int64_t)P.d * GROUP] = (float)static_cast<const T*>(P.y0)[k];
+    lay[base + (int64_t)P.d * GROUP] = (float)static_cast<const T*>(P.y0)[src];
 }
 
 cudaError_t launch_estimate_layout(int elem_bytes, const HotParams& P, cudaStream_t st) {
@@ -335,22 +387,23 @@ cudaError_t launch_estimate_layout(int elem_bytes, const HotParams& P, cudaStrea
     return cudaGetLastError();
 }
 
-template <int NORM>
+template <int NORM, bool WT>
 static cudaError_t launch_est_wide(int d, const EstParams& P, cudaStream_t st) {
     const int smem = EST_TILE_GROUPS * (D_MAX + 1) * (int)sizeof(float4);
-    static cudaError_t attr = cudaFuncSetAttribute(estimate_wide_kernel<NORM>,
+    static cudaError_t attr = cudaFuncSetAttribute(estimate_wide_kernel<NORM, WT>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (attr != cudaSuccess) return attr;
-    estimate_wide_kernel<NORM><<<dim3(P.nb, P.nb), EST_THREADS, EST_TILE_GROUPS * (d + 1) * sizeof(float4), st>>>(P, d);
+    estimate_wide_kernel<NORM, WT><<<dim3(P.nb, P.nb), EST_THREADS, EST_TILE_GROUPS * (d + 1) * sizeof(float4), st>>>(P, d);
     return cudaGetLastError();
 }
 
 cudaError_t launch_estimate(int norm, int d, const EstParams& P, cudaStream_t st) {
     if (d > EST_NARROW_MAX) {
         switch (norm) {
-            case LIP_L1: return launch_est_wide<LIP_L1>(d, P, st);
-            case LIP_L2: return launch_est_wide<LIP_L2>(d, P, st);
-            case LIP_LINF: return launch_est_wide<LIP_LINF>(d, P, st);
+            case LIP_L1: return P.weighted ? launch_est_wide<LIP_L1, true>(d, P, st) : launch_est_wide<LIP_L1, false>(d, P, st);
+            case LIP_L2: return P.weighted ? launch_est_wide<LIP_L2, true>(d, P, st) : launch_est_wide<LIP_L2, false>(d, P, st);
+            case LIP_LINF:
+                return P.weighted ? launch_est_wide<LIP_LINF, true>(d, P, st) : launch_est_wide<LIP_LINF, false>(d, P, st);
             default: return cudaErrorInvalidValue;
         }
     }
@@ -363,8 +416,53 @@ cudaError_t launch_estimate(int norm, int d, const EstParams& P, cudaStream_t st
     }
 }
 
+// The pruned estimate's result: R* from pass 2 and the pair from pass 3 (lowest i, then j,
+// among the pairs whose FP64 ratio is R*); out[3] is R* again, as in the full path.
+__global__ void estimate_pruned_finish_kernel(const EstFinalParams P, const int* gbest,
+                                              const unsigned long long* gratio, const unsigned long long* gkey) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int ti = -1, tj = -1;
+    double M = 0.0;
+    if (*gbest >= 0 && *gkey != ~0ull) {
+        M = __longlong_as_double((long long)*gratio);
+        ti = (int)(*gkey >> 32);
+        tj = (int)(*gkey & 0xffffffffull);
+    }
+    P.out[0] = M;
+    P.out[1] = (double)ti;
+    P.out[2] = (double)tj;
+    if (P.write_key) P.out[3] = ti >= 0 ? M : -1.0;
+}
+
+cudaError_t launch_estimate_pruned_finish(const EstFinalParams& F, const int* gbest, const unsigned long long* gratio,
+                                          const unsigned long long* gkey, cudaStream_t st) {
+    estimate_pruned_finish_kernel<<<1, 32, 0, st>>>(F, gbest, gratio, gkey);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_estimate_final(const EstFinalParams& P, cudaStream_t st) {
     estimate_final_kernel<<<1, 1024, 0, st>>>(P);
+    const int smem = 2 * EST_TILE_GROUPS * (P.d + 1) * (int)sizeof(float4);
+    if (smem > 48 * 1024) {          // per device, so set on every call that needs it
+        cudaError_t e = P.elem_bytes == 8
+            ? cudaFuncSetAttribute(estimate_exact_kernel<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+            : cudaFuncSetAttribute(estimate_exact_kernel<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = P.elem_bytes == 8
+                ? cudaFuncSetAttribute(estimate_exact_kernel<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                : cudaFuncSetAttribute(estimate_exact_kernel<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    const dim3 grid(P.nb, P.nb);
+    if (P.nb == 0) {                 // no pair: the final kernel has recorded none
+    } else if (P.elem_bytes == 8) {
+        estimate_exact_kernel<double, 1><<<grid, 256, smem, st>>>(P);
+        estimate_exact_kernel<double, 2><<<grid, 256, smem, st>>>(P);
+    } else {
+        estimate_exact_kernel<float, 1><<<grid, 256, smem, st>>>(P);
+        estimate_exact_kernel<float, 2><<<grid, 256, smem, st>>>(P);
+    }
+    estimate_exact_finish_kernel<<<1, 32, 0, st>>>(P);
     return cudaGetLastError();
 }
 

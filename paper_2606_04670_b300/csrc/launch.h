@@ -1,19 +1,46 @@
 // Parameter blocks and host launchers shared between the kernel units and the C ABI.
 #pragma once
+#include <cmath>
 #include <utility>
 
 #include "scan.cuh"
 
 namespace lip {
 
+// The estimate's norm weights (Sec. 5 M_est, weighted norm): a power of two scales the
+// layout's coordinate exactly; any other weight is applied to the FP32 coordinate
+// differences in the pair kernels instead, because rounding w x into the layout leaves an
+// error of the order of the difference of two points one FP32 unit apart.
+inline bool est_weighted(const double* w, int d) {
+    for (int j = 0; j < d; ++j) {
+        int e;
+        if (std::frexp(w[j], &e) != 0.5) return true;
+    }
+    return false;
+}
+// Layout scale of coordinate j: the weight when it is applied exactly there, else 1.
+inline double est_layout_scale(const double* w, int j, bool weighted) { return weighted ? 1.0 : w[j]; }
+
 struct EstParams {
-    const float4* lay;    // unscaled layout (w * sign), nch = D + 1 channels per group
+    const float4* lay;    // layout: coordinates times est_layout_scale, nch = D + 1 channels per group
     int64_t N;
     int nb;               // tiles per side
     float4* cand;         // [nb * nb]: {ratio^2, bits(i), bits(j), valid}
     // block-cyclic share of the tile pairs: pair (I, J >= I) belongs to part
     // (I nb + J) mod nparts; a launch covers the pairs of `part` only
     int part = 0, nparts = 1;
+    bool weighted = false;   // est_weighted: the pair kernels multiply differences by w
+    float w[D_MAX] = {};     // the weights in FP32 (read only when weighted)
+};
+
+// Device words of the exact selection that follows the FP32 screen: q* (bits of the
+// largest FP32 squared ratio, -1 without a pair), R* (bits of the largest FP64 ratio among
+// the pairs near q*, starting at +0) and the smallest key i << 32 | j attaining R*.
+struct EstExactState {
+    int q;
+    int pad;
+    unsigned long long ratio;
+    unsigned long long key;
 };
 
 struct EstFinalParams {
@@ -25,7 +52,12 @@ struct EstFinalParams {
     double w[D_MAX];
     double* out;          // [3]: M_est, i, j (as doubles); [4] with write_key
     int part = 0, nparts = 1;   // the tile pairs whose candidates are read (as EstParams)
-    int write_key = 0;    // out[3] = the winner's FP32 squared ratio (-1 without one)
+    int write_key = 0;    // out[3] = the FP64 ratio again, the key that orders parts (-1 without a pair)
+    // the exact selection: the screen's layout and weighting, and its device words
+    const float4* lay = nullptr;
+    int64_t N = 0;
+    bool weighted = false;
+    EstExactState* state = nullptr;
 };
 
 struct BwdParams {
@@ -90,7 +122,10 @@ cudaError_t launch_pad_hot(int elem_bytes, void* hot, int64_t k0, int64_t k1, in
 int estimate_tile_points();
 cudaError_t launch_estimate_layout(int elem_bytes, const HotParams& P, cudaStream_t st);
 cudaError_t launch_estimate(int norm, int d, const EstParams& P, cudaStream_t st);
+// After launch_estimate: q* of the part, then the exact selection among the pairs near it
+// (two passes over the tile pairs whose screen maximum reaches q* (1 - 2^-16)), then out.
 cudaError_t launch_estimate_final(const EstFinalParams& P, cudaStream_t st);
+constexpr int ESTIMATE_FINAL_LAUNCHES = 4;
 
 // tensor-core operand formats
 constexpr int TC_TF32 = 0, TC_BF16 = 1, TC_FP16 = 2;
@@ -166,6 +201,38 @@ PrunedKernelInfo scan_pruned_info(int norm, int C, int U, int variant);
 // records of every 8 consecutive chunks (sbox, nchunks a multiple of 8).
 cudaError_t launch_pruned_boxes(const void* hot, int64_t N, int64_t nchunks, int D, int nch, bool aux, void* box,
                                 void* sbox, cudaStream_t st);
+// The records of every 32-point chunk of a layout (as above, without the unions).
+cudaError_t launch_chunk_records(const void* hot, int64_t N, int64_t nchunks, int D, int nch, bool aux, void* box,
+                                 cudaStream_t st);
+// The union of every `per` consecutive records of `box` (nsuper of them) into sbox.
+cudaError_t launch_record_union(const void* box, int64_t nsuper, int per, int D, void* sbox, cudaStream_t st);
+
+// ------------------------------------------------ pruned estimate (estimate_pruned.cu)
+// M_est over the data in spatial order: pass 1 finds the largest FP32 squared ratio,
+// skipping tile pairs and 32-point chunks whose exact FP32 bound stays below the largest
+// value found so far; pass 2 finds the lowest (i, j) attaining it.  Same result as the
+// full estimate kernel bit for bit.
+struct EstPrunedParams {
+    const float4* lay;            // the estimate layout in position order
+    int64_t N;
+    int nb;                       // 512-point tiles
+    const int* dperm;             // [N] position -> data index
+    const float4* cbox;           // [nb * 16][pruned_box_f4(d)] chunk records
+    const float4* tbox;           // [nb][pruned_box_f4(d)] tile records
+    int* gbest;                   // pass 1: bits of the largest FP32 squared ratio q*, -1 none
+    unsigned long long* gratio;   // pass 2: bits of the largest FP64 ratio among the candidates (init 0)
+    unsigned long long* gkey;     // pass 3: smallest (i << 32 | j), i < j, attaining it (init ~0)
+    bool weighted = false;        // as EstParams
+    float w[PRUNED_DMAX] = {};
+    // the caller's data (FP32, row-major [N, d]) and weights for the FP64 ratios
+    const float* X = nullptr;
+    const float* y = nullptr;
+    double w64[PRUNED_DMAX] = {};
+};
+cudaError_t launch_estimate_pruned(int norm, int d, const EstPrunedParams& P, int pass, cudaStream_t st);
+bool estimate_pruned_available(int d);
+cudaError_t launch_estimate_pruned_finish(const EstFinalParams& F, const int* gbest, const unsigned long long* gratio,
+                                          const unsigned long long* gkey, cudaStream_t st);
 
 // Scratch of the device-side fallback for nq queries (fb_state above).
 size_t tc_fallback_state_bytes(int64_t nq);

@@ -27,10 +27,11 @@ constexpr int64_t NA_POINTS = ((int64_t)LIP_NOALLOC_N_MAX + NA_TILE - 1) / NA_TI
 constexpr int64_t NA_LAYOUT_BYTES = (NA_POINTS * (D_MAX + 1) * 4 + 255) / 256 * 256;
 constexpr int64_t NA_TILES = NA_POINTS / NA_TILE;
 constexpr int64_t NA_CAND_BYTES = (NA_TILES * NA_TILES * 16 + 255) / 256 * 256;
-constexpr int64_t NA_BYTES = NA_LAYOUT_BYTES + NA_CAND_BYTES;   // about 4.4 MB (d up to 32)
+constexpr int64_t NA_STATE_BYTES = 256;
+constexpr int64_t NA_BYTES = NA_LAYOUT_BYTES + NA_CAND_BYTES + NA_STATE_BYTES;   // about 4.4 MB (d up to 32)
 
 // Working memory of every lip_estimate_M_noalloc call on this device: the FP32 point
-// layout followed by one candidate record per tile pair.  Host code must not pass this
+// layout, one candidate record per tile pair, and the exact selection's device words.  Host code must not pass this
 // name to a kernel (on the host it only stands for the symbol); it uses the address
 // obtained from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
@@ -134,6 +135,7 @@ extern "C" lip_status lip_estimate_M_noalloc(const float* X, const float* y, int
     const int nch = d + 1;
     char* lay = static_cast<char*>(base);
     float4* cand = reinterpret_cast<float4*>(static_cast<char*>(base) + NA_LAYOUT_BYTES);
+    EstExactState* state = reinterpret_cast<EstExactState*>(static_cast<char*>(base) + NA_LAYOUT_BYTES + NA_CAND_BYTES);
 
     // Every byte read below is written first by this call: the layout covers [0, pts)
     // (data, then padding) and the candidate pass writes every tile pair it later reads.
@@ -147,9 +149,12 @@ extern "C" lip_status lip_estimate_M_noalloc(const float* X, const float* y, int
     Hp.dl = d;
     Hp.nch = nch;
     Hp.aux = 0;
+    double wd[D_MAX];
+    for (int j = 0; j < D_MAX; ++j) wd[j] = (w && j < d) ? w[j] : 1.0;
+    const bool weighted = est_weighted(wd, d);
     for (int j = 0; j < D_MAX; ++j) {
         Hp.perm[j] = j;
-        Hp.scale[j] = (w && j < d) ? w[j] : 1.0;
+        Hp.scale[j] = est_layout_scale(wd, j, weighted);
     }
     Hp.hot = lay;
     Hp.err = nullptr;
@@ -163,6 +168,10 @@ extern "C" lip_status lip_estimate_M_noalloc(const float* X, const float* y, int
     F.elem_bytes = 4;
     for (int j = 0; j < D_MAX; ++j) F.w[j] = (w && j < d) ? w[j] : 1.0;
     F.out = out;
+    F.lay = reinterpret_cast<const float4*>(lay);
+    F.N = N;
+    F.weighted = weighted;
+    F.state = state;
     if (N >= 2) {
         if ((e = launch_estimate_layout(4, Hp, st)) != cudaSuccess) return launch_fail(e, "estimate layout");
         if ((e = launch_pad_hot(4, lay, N, pts, nch, d, st)) != cudaSuccess) return launch_fail(e, "estimate padding");
@@ -171,6 +180,8 @@ extern "C" lip_status lip_estimate_M_noalloc(const float* X, const float* y, int
         P.N = N;
         P.nb = (int)nb;
         P.cand = cand;
+        P.weighted = weighted;
+        for (int j = 0; j < d; ++j) P.w[j] = (float)wd[j];
         if ((e = launch_estimate(norm, d, P, st)) != cudaSuccess) return launch_fail(e, "estimate kernel");
     }
     if ((e = launch_estimate_final(F, st)) != cudaSuccess) return launch_fail(e, "estimate final");

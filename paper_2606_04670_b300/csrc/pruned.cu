@@ -52,9 +52,9 @@ __global__ void pruned_box_kernel(const float* hot, int64_t N, int64_t nchunks, 
     for (int k = 2 * D + 2; k < nb4 * 4; ++k) out[k] = 0.f;
 }
 
-// One thread per 8 consecutive chunks: the union of their records (chunks without data,
-// NaN, drop out of the min / max; 8 empty chunks give NaN).
-__global__ void pruned_super_kernel(const float4* box, int64_t nsuper, int D, int nb4, float4* sbox) {
+// One thread per `per` consecutive chunks: the union of their records (chunks without
+// data, NaN, drop out of the min / max; all empty gives NaN).
+__global__ void pruned_super_kernel(const float4* box, int64_t nsuper, int per, int D, int nb4, float4* sbox) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsuper) return;
     float* out = reinterpret_cast<float*>(sbox + s * nb4);
@@ -66,8 +66,8 @@ __global__ void pruned_super_kernel(const float4* box, int64_t nsuper, int D, in
     out[2 * D] = inf;
     out[2 * D + 1] = -inf;
     bool any = false;
-    for (int c = 0; c < 8; ++c) {
-        const float* b = reinterpret_cast<const float*>(box + (s * 8 + c) * nb4);
+    for (int c = 0; c < per; ++c) {
+        const float* b = reinterpret_cast<const float*>(box + (s * per + c) * nb4);
         if (!(b[2 * D] == b[2 * D])) continue;
         any = true;
         for (int j = 0; j < D; ++j) {
@@ -95,14 +95,25 @@ PrunedKernelInfo scan_pruned_info(int norm, int C, int U, int variant) {
 
 int pruned_box_floats(int D) { return pruned_box_f4(D) * 4; }
 
-cudaError_t launch_pruned_boxes(const void* hot, int64_t N, int64_t nchunks, int D, int nch, bool aux, void* box,
-                                void* sbox, cudaStream_t st) {
+cudaError_t launch_chunk_records(const void* hot, int64_t N, int64_t nchunks, int D, int nch, bool aux, void* box,
+                                 cudaStream_t st) {
     if (nchunks <= 0) return cudaSuccess;
     pruned_box_kernel<<<(unsigned)((nchunks + 127) / 128), 128, 0, st>>>(
         static_cast<const float*>(hot), N, nchunks, D, nch, aux ? 1 : 0, pruned_box_f4(D), static_cast<float4*>(box));
-    const int64_t nsuper = nchunks / 8;
-    pruned_super_kernel<<<(unsigned)((nsuper + 127) / 128), 128, 0, st>>>(static_cast<const float4*>(box), nsuper, D,
-                                                                          pruned_box_f4(D),
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pruned_boxes(const void* hot, int64_t N, int64_t nchunks, int D, int nch, bool aux, void* box,
+                                void* sbox, cudaStream_t st) {
+    cudaError_t e = launch_chunk_records(hot, N, nchunks, D, nch, aux, box, st);
+    if (e != cudaSuccess) return e;
+    return launch_record_union(box, nchunks / 8, 8, D, sbox, st);
+}
+
+cudaError_t launch_record_union(const void* box, int64_t nsuper, int per, int D, void* sbox, cudaStream_t st) {
+    if (nsuper <= 0) return cudaSuccess;
+    pruned_super_kernel<<<(unsigned)((nsuper + 127) / 128), 128, 0, st>>>(static_cast<const float4*>(box), nsuper, per,
+                                                                          D, pruned_box_f4(D),
                                                                           static_cast<float4*>(sbox));
     return cudaGetLastError();
 }

@@ -110,6 +110,7 @@ def _load():
         "lip_shard_finish": [H, i64, P, P, P, P, P, P, P, P, P, P],
         "lip_estimate_M_part": [H, i32, i32, P, P],
         "lip_set_tc_window": [H, i64],
+        "lip_set_estimate_full": [H, i32],
         "lip_last_scan_work": [H, ctypes.POINTER(i64), ctypes.POINTER(i64)],
         "lip_add_async": [H, P, P, i64, P],
         "lip_add_host_async": [H, P, P, i64, P],
@@ -214,6 +215,10 @@ def lip_add_host_async(h, X_ptr, y_ptr, n, stream=0):
 
 def lip_set_tc_window(h, nbytes):
     return _lib.lip_set_tc_window(h, nbytes)
+
+
+def lip_set_estimate_full(h, full):
+    return _lib.lip_set_estimate_full(h, full)
 
 
 def lip_clear(h, stream=0):
@@ -712,13 +717,14 @@ class LipFit:
         return out
 
     def estimate_M_part(self, part: int, nparts: int):
-        """lip_estimate_M_part: [M, i, j, FP32 squared ratio] of one block-cyclic share."""
+        """lip_estimate_M_part: [M, i, j, key = M] of one block-cyclic share."""
         s, out = lip_estimate_M_part(self.h, int(part), int(nparts), _stream_ptr())
         _check(s, "lip_estimate_M_part")
         return out
 
     def lipschitz_constant(self):
-        """(M_est, i, j) (Sec. 5: lipschitz_constant()); synchronises."""
+        """(M_est, i, j) (Sec. 5: lipschitz_constant()), the FP64 definition's maximum and
+        its lowest pair exactly; synchronises."""
         s, M, i, j = lip_estimate_M(self.h, _stream_ptr())
         _check(s, "lip_estimate_M")
         return M, i, j
@@ -744,6 +750,17 @@ class LipFit:
         e, t = ctypes.c_int64(), ctypes.c_int64()
         _check(_lib.lip_last_scan_work(self.h, ctypes.byref(e), ctypes.byref(t)), "lip_last_scan_work")
         return e.value, t.value
+
+    def set_estimate_full(self, full: bool = True):
+        """lip_estimate_M with the full all-pairs kernel (True) or the default choice
+        (False: the pruned form for L2 / L-infinity where available); same result."""
+        _check(_lib.lip_set_estimate_full(self.h, int(bool(full))), "lip_set_estimate_full")
+
+    def set_estimate_form(self, form: str = "auto"):
+        """lip_estimate_M's form: "auto" (the default), "full" or "pruned" (every norm,
+        where available); all give the same result."""
+        code = {"auto": 0, "full": 1, "pruned": 2}[form]
+        _check(_lib.lip_set_estimate_full(self.h, code), "lip_set_estimate_full")
 
     def set_tc_window(self, nbytes: int = 0):
         """Tensor-core handles: the data bytes a round's persistent CTAs may spread their

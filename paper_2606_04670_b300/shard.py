@@ -98,7 +98,8 @@ def gather_outputs(out: Dict, counts: Sequence[int], dst: int = 0, group=None):
 
 def _better(a: Sequence[float], b: Sequence[float]) -> bool:
     """lip_estimate_M's order of candidates [M, i, j, key]: a part without a pair (i < 0)
-    loses; then the larger FP32 squared ratio; then the lower i, then the lower j."""
+    loses; then the larger key (the part's exact FP64 maximum); then the lower i, then the
+    lower j."""
     if b[1] < 0:
         return a[1] >= 0
     if a[1] < 0:

@@ -88,7 +88,7 @@ class OracleShard:
 
 class OracleEstimateShard:
     """lip_estimate_M_part on the host: the tile pairs (I, J >= I) with (I nb + J) mod nparts
-    = part, each pair's ratio in FP64; the key is the squared ratio rounded to float32."""
+    = part, each pair's ratio in FP64; the key is that ratio."""
 
     def __init__(self, p):
         self.p = p
@@ -117,7 +117,7 @@ class OracleEstimateShard:
                 R = np.where(ok, R, -1.0)
                 k = np.argmax(R)
                 i, j = a[k // len(b)], b[k % len(b)]
-                cand = [float(R.flat[k]), float(i), float(j), float(np.float32(R.flat[k] ** 2))]
+                cand = [float(R.flat[k]), float(i), float(j), float(R.flat[k])]
                 if S._better(cand, best):
                     best = cand
         return best

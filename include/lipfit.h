@@ -218,18 +218,15 @@ LIP_API lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* 
 LIP_API lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, int64_t* j_out,
                           void* stream);
 
-/* Form of lip_estimate_M on this handle.  0 (the default): FP32 handles with d <= 8 and
- * the L2 or L-infinity norm take the pruned form (with L1 the box bound rules out too few
- * pairs to pay for the spatial order); 2: the pruned form for every norm.  The pruned form: the data in spatial order with a box and y range per 32-point chunk
- * and per 512-point tile; pass 1 finds the largest FP32 squared ratio q*, skipping the
- * tile pairs and chunks whose exact FP32 upper bound (box gaps with the pair arithmetic's
- * own operations, rcp.approx with a 2^-18 margin) is below the largest value already
- * found; pass 2 re-evaluates in FP64 the pairs whose FP32 value reaches q* (1 - 2^-16)
- * and keeps the largest; pass 3 finds the lowest (i, j) attaining it.  Other handles, and
- * lip_estimate_M_part, run the full all-pairs screen followed by the same FP64 selection
- * over the tile pairs whose screen maximum reaches q* (1 - 2^-16).  Both forms give the
- * same result bit for bit.  1: always the full kernel.  LIP_ERR_ARG for a NULL handle or
- * another value. */
+/* Form of lip_estimate_M on this handle.  0 (the default) and 2: FP32 handles with
+ * d <= 8 take the pruned form; 1: always the full kernel.  The pruned form puts the data in spatial order with a box and y range per
+ * 32-point chunk and per 512-point tile, and its FP32 screen skips the tile pairs and
+ * chunks whose exact FP32 upper bound (box gaps with the pair arithmetic's own operations,
+ * rcp.approx with a 2^-18 margin) is below (1 - 2^-16) times the largest value already
+ * found.  Other handles, and lip_estimate_M_part, screen all pairs.  Both forms are
+ * followed by the same FP64 selection over the tile pairs whose screen maximum reaches
+ * q* (1 - 2^-16), and give the same result bit for bit.  LIP_ERR_ARG for a NULL handle
+ * or another value. */
 LIP_API lip_status lip_set_estimate_full(lip_handle h, int32_t full);
 
 /* ------------------------------------------------ several GPUs (one process per GPU) */
@@ -598,6 +595,13 @@ LIP_API lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, voi
  * (warps x 32-point chunks); both -1 / *total = -1 when the last scan was not pruned.
  * Synchronises the device to read the count. */
 LIP_API lip_status lip_last_scan_work(lip_handle h, int64_t* evaluated, int64_t* total);
+
+/* After a pruned lip_estimate_M: out (host int64[3]) = the tile pairs that passed the tile
+ * bound test, the (warp, chunk) pairs the screen evaluated (a warp holds 128 row points, a
+ * chunk 32 column points), and the total (warp, chunk) pairs of the tile triangle; all -1
+ * when the last estimate of this handle did not take the pruned form.  Reads what the
+ * estimate (which synchronises) left on the host.  LIP_ERR_ARG for NULL. */
+LIP_API lip_status lip_last_estimate_work(lip_handle h, int64_t* out);
 
 /* Tensor-core handles, variants 0 / 1 of lip_set_tuning: the data bytes over which the
  * persistent CTAs of one round may spread their sweeps of the data tiles (a producer runs

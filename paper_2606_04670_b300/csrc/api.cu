@@ -703,25 +703,31 @@ lip_status eval_screen64(lip_model* h, const void* Q, int64_t nq, void* g, void*
 lip_status estimate_pruned(lip_model* h, double* res, cudaStream_t st) {
     const int tile = estimate_tile_points();
     const int64_t N = h->N, nb = ceil_div(N, tile), pts = nb * tile, nchunks = pts / 32;
+    const int64_t npairs = nb * (nb + 1) / 2;
     const int d = h->d, nch = d + 1;
     const size_t rec = (size_t)pruned_box_f4(d) * 16;
     const size_t lay_b = round_up(pts * nch * 4, 256), perm_b = round_up(N * 4, 256),
                  cbox_b = round_up((int64_t)(nchunks * rec), 256), tbox_b = round_up((int64_t)(nb * rec), 256),
-                 bnd_b = round_up(D_MAX * 8, 256), small_b = 256;
-    LIP_TRY(h->est.ensure(lay_b + perm_b + cbox_b + tbox_b + bnd_b + small_b + spatial_order_scratch(N),
+                 bnd_b = round_up(D_MAX * 8, 256), pair_b = round_up(npairs * 4, 256), small_b = 256;
+    LIP_TRY(h->est.ensure(lay_b + perm_b + cbox_b + tbox_b + bnd_b + 2 * pair_b + small_b + spatial_order_scratch(N),
                           "estimate scratch"));
     char* base = static_cast<char*>(h->est.p);
-    void* lay = base;
-    int* perm = reinterpret_cast<int*>(base + lay_b);
-    void* cbox = base + lay_b + perm_b;
-    void* tbox = base + lay_b + perm_b + cbox_b;
-    float2* bounds = reinterpret_cast<float2*>(base + lay_b + perm_b + cbox_b + tbox_b);
-    char* small = base + lay_b + perm_b + cbox_b + tbox_b + bnd_b;
+    char* at = base;
+    auto take = [&](size_t bytes) { char* p = at; at += bytes; return p; };
+    void* lay = take(lay_b);
+    int* perm = reinterpret_cast<int*>(take(perm_b));
+    void* cbox = take(cbox_b);
+    void* tbox = take(tbox_b);
+    float2* bounds = reinterpret_cast<float2*>(take(bnd_b));
+    float* bq = reinterpret_cast<float*>(take(pair_b));
+    unsigned* list = reinterpret_cast<unsigned*>(take(pair_b));
+    // small: gbest at 0, the selection's words at 64, out (4 doubles) at 128, work (2) at 160
+    char* small = take(small_b);
     int* gbest = reinterpret_cast<int*>(small);
-    unsigned long long* gkey = reinterpret_cast<unsigned long long*>(small + 8);
-    unsigned long long* gratio = reinterpret_cast<unsigned long long*>(small + 16);
-    double* out = reinterpret_cast<double*>(small + 64);
-    void* oscratch = small + small_b;
+    EstExactState* state = reinterpret_cast<EstExactState*>(small + 64);
+    double* out = reinterpret_cast<double*>(small + 128);
+    unsigned long long* work = reinterpret_cast<unsigned long long*>(small + 160);
+    void* oscratch = at;
     CUDA_TRY(spatial_order(static_cast<const float*>(h->X0), N, d, perm, bounds, oscratch, st));
     HotParams Hp;
     Hp.X0 = h->X0;
@@ -745,28 +751,20 @@ lip_status estimate_pruned(lip_model* h, double* res, cudaStream_t st) {
     CUDA_TRY(launch_pad_hot(4, lay, N, pts, nch, d, st));
     CUDA_TRY(launch_chunk_records(lay, N, nchunks, d, nch, false, cbox, st));
     CUDA_TRY(launch_record_union(cbox, nb, tile / 32, d, tbox, st));
-    CUDA_TRY(cudaMemsetAsync(small, 0xff, 16, st));            // gbest = -1, gkey = all ones
-    CUDA_TRY(cudaMemsetAsync(gratio, 0, 8, st));               // R* = +0
+    CUDA_TRY(cudaMemsetAsync(gbest, 0xff, 4, st));             // no value yet
+    CUDA_TRY(cudaMemsetAsync(work, 0, 16, st));
     EstPrunedParams P;
     P.lay = static_cast<const float4*>(lay);
     P.N = N;
     P.nb = (int)nb;
-    P.dperm = perm;
     P.cbox = static_cast<const float4*>(cbox);
     P.tbox = static_cast<const float4*>(tbox);
     P.gbest = gbest;
-    P.gkey = gkey;
-    P.gratio = gratio;
+    P.bq = bq;
     P.weighted = weighted;
-    for (int j = 0; j < d; ++j) {
-        P.w[j] = (float)h->w[j];
-        P.w64[j] = h->w[j];
-    }
-    P.X = static_cast<const float*>(h->X0);
-    P.y = static_cast<const float*>(h->y0);
-    CUDA_TRY(launch_estimate_pruned(h->norm, d, P, 1, st));
-    CUDA_TRY(launch_estimate_pruned(h->norm, d, P, 2, st));
-    CUDA_TRY(launch_estimate_pruned(h->norm, d, P, 3, st));
+    for (int j = 0; j < d; ++j) P.w[j] = (float)h->w[j];
+    P.work = work;
+    CUDA_TRY(launch_estimate_pruned(h->norm, d, P, st));
     EstFinalParams F;
     F.cand = nullptr;
     F.nb = (int)nb;
@@ -778,15 +776,31 @@ lip_status estimate_pruned(lip_model* h, double* res, cudaStream_t st) {
     for (int j = 0; j < D_MAX; ++j) F.w[j] = h->w[j];
     F.out = out;
     F.write_key = 1;
-    CUDA_TRY(launch_estimate_pruned_finish(F, gbest, gratio, gkey, st));
-    count_launches(8 + spatial_order_launches());
-    CUDA_TRY(cudaMemcpyAsync(res, out, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    F.lay = P.lay;
+    F.N = N;
+    F.weighted = weighted;
+    F.perm = perm;
+    F.list = list;
+    F.state = state;
+    CUDA_TRY(launch_estimate_pruned_select(P, F, st));
+    CUDA_TRY(launch_estimate_exact(F, st));
+    count_launches(6 + ESTIMATE_EXACT_LAUNCHES + spatial_order_launches());
+    // the result (4 doubles) and the work counters in one read
+    unsigned char back[48];
+    CUDA_TRY(cudaMemcpyAsync(back, out, sizeof back, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    memcpy(res, back, 4 * sizeof(double));
+    unsigned long long wk[2];
+    memcpy(wk, back + 32, sizeof wk);
+    h->est_work[0] = (int64_t)wk[0];
+    h->est_work[1] = (int64_t)wk[1];
+    h->est_work[2] = npairs * (tile / 128) * (tile / 32);   // 128-row warps x 32-point chunks
     return LIP_OK;
 }
 
 lip_status estimate_part(lip_model* h, int part, int nparts, double* res, cudaStream_t st) {
     DeviceGuard gd(h->device);
+    for (int k = 0; k < 3; ++k) h->est_work[k] = -1;
     res[0] = 0.0;
     res[1] = res[2] = -1.0;
     res[3] = -1.0;
@@ -794,15 +808,14 @@ lip_status estimate_part(lip_model* h, int part, int nparts, double* res, cudaSt
     const int tile = estimate_tile_points();
     const int64_t nb = ceil_div(h->N, tile);
     if (nb > 65535) return fail(LIP_ERR_UNSUPPORTED, "N = %lld is too large for lip_estimate_M", (long long)h->N);
-    // The L1 box bound prunes too little to pay for the spatial order (N = 1e5, d = 4:
-    // 2.97 ms pruned against 2.54 ms full), so L1 takes the full kernel by default.
-    const bool pruned = h->est_form == 2 || (h->est_form == 0 && h->norm != LIP_L1);
+    const bool pruned = h->est_form != 1;
     if (nparts == 1 && h->esize == 4 && estimate_pruned_available(h->d) && pruned)
         return estimate_pruned(h, res, st);
     const int64_t pts = nb * tile;
     const int nch = h->d + 1;
-    const size_t lay_b = round_up(pts * nch * 4, 256), cand_b = round_up(nb * nb * 16, 256);
-    LIP_TRY(h->est.ensure(lay_b + cand_b + 256, "estimate scratch"));
+    const size_t lay_b = round_up(pts * nch * 4, 256), cand_b = round_up(nb * nb * 16, 256),
+                 list_b = round_up(nb * nb * 4, 256);
+    LIP_TRY(h->est.ensure(lay_b + cand_b + 256 + list_b, "estimate scratch"));
     char* base = static_cast<char*>(h->est.p);
     // FP32 layout in the caller's order: coordinates times est_layout_scale
     const bool weighted = est_weighted(h->w, h->d);
@@ -851,6 +864,7 @@ lip_status estimate_part(lip_model* h, int part, int nparts, double* res, cudaSt
     F.N = h->N;
     F.weighted = weighted;
     F.state = reinterpret_cast<EstExactState*>(base + lay_b + cand_b + 64);
+    F.list = reinterpret_cast<unsigned*>(base + lay_b + cand_b + 256);
     CUDA_TRY(launch_estimate_final(F, st));
     count_launches(3 + ESTIMATE_FINAL_LAUNCHES);
     CUDA_TRY(cudaMemcpyAsync(res, F.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1362,6 +1376,13 @@ lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, void* ev_af
 }
 
 uint64_t lip_kernel_launches(void) { return launches_total(); }
+
+lip_status lip_last_estimate_work(lip_handle h, int64_t* out) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (!out) return fail(LIP_ERR_ARG, "out is NULL");
+    for (int k = 0; k < 3; ++k) out[k] = h->est_work[k];
+    return LIP_OK;
+}
 
 lip_status lip_last_scan_work(lip_handle h, int64_t* evaluated, int64_t* total) {
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");

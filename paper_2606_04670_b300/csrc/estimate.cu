@@ -224,13 +224,17 @@ __device__ double est_ratio_fp64(const EstFinalParams& P, int64_t i, int64_t j) 
     return __ddiv_rn(dy, dist);
 }
 
-// q*: the largest FP32 squared ratio over the part's candidates; the exact selection's
-// words start from it.
+// T = q* (1 - 2^-16), the exact selection's threshold (rounded down).
+__device__ __forceinline__ float est_threshold(float qs) { return __fmul_rd(qs, 0.9999847412109375f); }
+
+// q*: the largest FP32 squared ratio over the part's candidates; then the list of the
+// part's tile pairs whose candidate reaches T, for the exact selection.
 __global__ void estimate_final_kernel(const EstFinalParams P) {
     const int tid = threadIdx.x;
     float tb = -1.f;
     int ti = -1, tj = -1;
-    for (int64_t k = tid; k < (int64_t)P.nb * P.nb; k += blockDim.x) {
+    const int64_t n = (int64_t)P.nb * P.nb;
+    for (int64_t k = tid; k < n; k += blockDim.x) {
         const int bi = (int)(k / P.nb), bj = (int)(k % P.nb);
         if (bj < bi || k % P.nparts != P.part) continue;
         const float4 c = P.cand[k];
@@ -247,12 +251,31 @@ __global__ void estimate_final_kernel(const EstFinalParams P) {
     }
     __shared__ float sb[32];
     __shared__ int si[32], sj[32];
+    __shared__ float s_q;
+    __shared__ int s_count;
     if ((tid & 31) == 0) { sb[tid >> 5] = tb; si[tid >> 5] = ti; sj[tid >> 5] = tj; }
     __syncthreads();
     if (tid == 0) {
         for (int w = 1; w < (int)(blockDim.x / 32); ++w)
             if (est_better(sb[w], si[w], sj[w], tb, ti, tj)) { tb = sb[w]; ti = si[w]; tj = sj[w]; }
-        P.state->q = ti >= 0 ? __float_as_int(tb) : -1;
+        s_q = ti >= 0 ? tb : -1.f;
+        s_count = 0;
+    }
+    __syncthreads();
+    const float qs = s_q;
+    if (qs >= 0.f) {
+        const float T = est_threshold(qs);
+        for (int64_t k = tid; k < n; k += blockDim.x) {
+            const int bi = (int)(k / P.nb), bj = (int)(k % P.nb);
+            if (bj < bi || k % P.nparts != P.part) continue;
+            const float4 c = P.cand[k];
+            if (c.w != 0.f && c.x >= T) P.list[atomicAdd(&s_count, 1)] = ((unsigned)bi << 16) | (unsigned)bj;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        P.state->q = qs >= 0.f ? __float_as_int(qs) : -1;
+        P.state->count = s_count;
         P.state->ratio = 0ull;
         P.state->key = ~0ull;
     }
@@ -263,60 +286,70 @@ __global__ void estimate_final_kernel(const EstFinalParams P) {
 // FP32 data (each weighted difference rounded at most three times, at most d + 2 roundings
 // in the sums and squares, a reciprocal of at most 2 ulps and the product), so the pair
 // with the largest FP64 ratio has q >= T = q* (1 - 2^-16) for every d <= 32, and its tile
-// pair's screen maximum reaches T.  Each such tile pair is visited again: its pairs' q
-// from the layout in shared memory (the same bound holds for this scalar form), and the
-// FP64 ratio of those with q >= T.  PASS 1 keeps the largest ratio R* (atomicMax of its
-// bits: non-negative doubles order as integers), PASS 2 the smallest key among the pairs
-// whose ratio is R*.  Data whose weighted coordinate differences fall into FP32's
-// subnormal range, or whose ratios overflow FP32, are outside the bound.
+// pair's screen maximum reaches T.  The listed tile pairs are cut into items of
+// EXACT_ROWS row positions against the 512 column positions; a block stages an item's
+// rows and columns from the layout in shared memory, forms each pair's q again with a
+// scalar form of the same arithmetic (the same bound holds), and re-evaluates the pairs
+// with q >= T in FP64 (est_ratio_fp64, on data indices through P.perm).  PASS 1 keeps the
+// largest ratio R* (atomicMax of its bits: non-negative doubles order as integers), PASS
+// 2 the smallest key among the pairs whose ratio is R*.  Data whose weighted coordinate
+// differences fall into FP32's subnormal range, or whose ratios overflow FP32, are
+// outside the bound.
+constexpr int EXACT_ROWS = 64;
+constexpr int EXACT_THREADS = 256;
+
 template <typename T, int PASS>
-__global__ void __launch_bounds__(256) estimate_exact_kernel(const EstFinalParams P) {
-    const int bi = blockIdx.x, bj = blockIdx.y;
-    if (bj < bi || ((int64_t)bi * P.nb + bj) % P.nparts != P.part) return;
+__global__ void __launch_bounds__(EXACT_THREADS) estimate_exact_kernel(const EstFinalParams P) {
     const int qb = *reinterpret_cast<const volatile int*>(&P.state->q);
     if (qb < 0) return;
-    const float Tq = __fmul_rd(__int_as_float(qb), 0.9999847412109375f);      // q* (1 - 2^-16)
-    const float4 c = P.cand[(size_t)bi * P.nb + bj];
-    if (c.w == 0.f || !(c.x >= Tq)) return;
+    const int64_t items = (int64_t)*reinterpret_cast<const volatile int*>(&P.state->count) * (EST_TILE / EXACT_ROWS);
+    const float Tq = est_threshold(__int_as_float(qb));
     const double Rs =
         PASS == 2 ? __longlong_as_double(*reinterpret_cast<const volatile long long*>(&P.state->ratio)) : 0.0;
     const int nch = P.d + 1;
-    extern __shared__ __align__(16) float4 xs[];          // I-tile then J-tile, groups of the layout
-    float4* ti4 = xs;
-    float4* tj4 = xs + EST_TILE_GROUPS * nch;
-    for (int k = threadIdx.x; k < EST_TILE_GROUPS * nch; k += blockDim.x) {
-        ti4[k] = P.lay[(size_t)bi * EST_TILE_GROUPS * nch + k];
-        tj4[k] = P.lay[(size_t)bj * EST_TILE_GROUPS * nch + k];
-    }
-    __syncthreads();
-    const float* fi = reinterpret_cast<const float*>(ti4);
-    const float* fj = reinterpret_cast<const float*>(tj4);
+    extern __shared__ __align__(16) float4 xs[];          // the item's rows, then the column tile
+    float* fi = reinterpret_cast<float*>(xs);
+    float* fj = reinterpret_cast<float*>(xs + (EXACT_ROWS / GROUP) * nch);
     double rbest = -1.0;
     unsigned long long kbest = ~0ull;
-    for (int p = threadIdx.x; p < EST_TILE * EST_TILE; p += blockDim.x) {
-        const int a = p / EST_TILE, b = p % EST_TILE;
-        const int64_t i = (int64_t)bi * EST_TILE + a, j = (int64_t)bj * EST_TILE + b;
-        if (i >= j || j >= P.N) continue;
-        const float* pa = fi + (a / GROUP) * nch * GROUP + a % GROUP;
-        const float* pb = fj + (b / GROUP) * nch * GROUP + b % GROUP;
-        float acc = 0.f;
-        for (int k = 0; k < P.d; ++k) {
-            float t = __fsub_rn(pa[k * GROUP], pb[k * GROUP]);
-            if (P.weighted) t = __fmul_rn(t, (float)P.w[k]);
-            if (P.norm == LIP_L2) acc = __fmaf_rn(t, t, acc);
-            else if (P.norm == LIP_L1) acc = __fadd_rn(acc, fabsf(t));
-            else acc = fmaxf(acc, fabsf(t));
-        }
-        const float den = P.norm == LIP_L2 ? acc : __fmul_rn(acc, acc);
-        const float dy = __fsub_rn(pa[P.d * GROUP], pb[P.d * GROUP]);
-        const float q = __fmul_rn(__fmul_rn(dy, dy), rcp_approx(den));
-        if (!(q >= Tq)) continue;
-        const double r = est_ratio_fp64<T>(P, i, j);
-        if (PASS == 1) {
-            rbest = r > rbest ? r : rbest;
-        } else if (r == Rs) {
-            const unsigned long long key = ((unsigned long long)i << 32) | (unsigned long long)j;
-            kbest = key < kbest ? key : kbest;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const unsigned tp = P.list[it / (EST_TILE / EXACT_ROWS)];
+        const int bi = (int)(tp >> 16), bj = (int)(tp & 0xffffu);
+        const int r0 = (int)(it % (EST_TILE / EXACT_ROWS)) * EXACT_ROWS;      // first row within tile bi
+        __syncthreads();                                   // the previous item's reads are done
+        const float4* rs = P.lay + ((size_t)bi * EST_TILE + r0) / GROUP * nch;
+        for (int k = threadIdx.x; k < (EXACT_ROWS / GROUP) * nch; k += blockDim.x) xs[k] = rs[k];
+        const float4* cs = P.lay + (size_t)bj * EST_TILE_GROUPS * nch;
+        for (int k = threadIdx.x; k < EST_TILE_GROUPS * nch; k += blockDim.x)
+            xs[(EXACT_ROWS / GROUP) * nch + k] = cs[k];
+        __syncthreads();
+        for (int p = threadIdx.x; p < EXACT_ROWS * EST_TILE; p += blockDim.x) {
+            const int a = p / EST_TILE, b = p % EST_TILE;
+            const int64_t pa = (int64_t)bi * EST_TILE + r0 + a, pb = (int64_t)bj * EST_TILE + b;
+            if (pa >= pb || pb >= P.N) continue;           // each unordered pair once, no padding
+            const float* xa = fi + (a / GROUP) * nch * GROUP + a % GROUP;
+            const float* xb = fj + (b / GROUP) * nch * GROUP + b % GROUP;
+            float acc = 0.f;
+            for (int k = 0; k < P.d; ++k) {
+                float t = __fsub_rn(xa[k * GROUP], xb[k * GROUP]);
+                if (P.weighted) t = __fmul_rn(t, (float)P.w[k]);
+                if (P.norm == LIP_L2) acc = __fmaf_rn(t, t, acc);
+                else if (P.norm == LIP_L1) acc = __fadd_rn(acc, fabsf(t));
+                else acc = fmaxf(acc, fabsf(t));
+            }
+            const float den = P.norm == LIP_L2 ? acc : __fmul_rn(acc, acc);
+            const float dy = __fsub_rn(xa[P.d * GROUP], xb[P.d * GROUP]);
+            const float q = __fmul_rn(__fmul_rn(dy, dy), rcp_approx(den));
+            if (!(q >= Tq)) continue;
+            const int64_t da = P.perm ? P.perm[pa] : pa, db = P.perm ? P.perm[pb] : pb;
+            const int64_t i = da < db ? da : db, j = da < db ? db : da;
+            const double r = est_ratio_fp64<T>(P, i, j);
+            if (PASS == 1) {
+                rbest = r > rbest ? r : rbest;
+            } else if (r == Rs) {
+                const unsigned long long key = ((unsigned long long)i << 32) | (unsigned long long)j;
+                kbest = key < kbest ? key : kbest;
+            }
         }
     }
     unsigned long long v = PASS == 1 ? (rbest >= 0.0 ? (unsigned long long)__double_as_longlong(rbest) : 0ull) : kbest;
@@ -325,12 +358,12 @@ __global__ void __launch_bounds__(256) estimate_exact_kernel(const EstFinalParam
         const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
         v = PASS == 1 ? (u > v ? u : v) : (u < v ? u : v);
     }
-    __shared__ unsigned long long red[8];
+    __shared__ unsigned long long red[EXACT_THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) red[warp] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        for (int w = 1; w < EXACT_THREADS / 32; ++w)
             v = PASS == 1 ? (red[w] > v ? red[w] : v) : (red[w] < v ? red[w] : v);
         if (PASS == 1 && v != 0ull) atomicMax(&P.state->ratio, v);
         if (PASS == 2 && v != ~0ull) atomicMin(&P.state->key, v);
@@ -416,33 +449,13 @@ cudaError_t launch_estimate(int norm, int d, const EstParams& P, cudaStream_t st
     }
 }
 
-// The pruned estimate's result: R* from pass 2 and the pair from pass 3 (lowest i, then j,
-// among the pairs whose FP64 ratio is R*); out[3] is R* again, as in the full path.
-__global__ void estimate_pruned_finish_kernel(const EstFinalParams P, const int* gbest,
-                                              const unsigned long long* gratio, const unsigned long long* gkey) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int ti = -1, tj = -1;
-    double M = 0.0;
-    if (*gbest >= 0 && *gkey != ~0ull) {
-        M = __longlong_as_double((long long)*gratio);
-        ti = (int)(*gkey >> 32);
-        tj = (int)(*gkey & 0xffffffffull);
-    }
-    P.out[0] = M;
-    P.out[1] = (double)ti;
-    P.out[2] = (double)tj;
-    if (P.write_key) P.out[3] = ti >= 0 ? M : -1.0;
-}
-
-cudaError_t launch_estimate_pruned_finish(const EstFinalParams& F, const int* gbest, const unsigned long long* gratio,
-                                          const unsigned long long* gkey, cudaStream_t st) {
-    estimate_pruned_finish_kernel<<<1, 32, 0, st>>>(F, gbest, gratio, gkey);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_estimate_final(const EstFinalParams& P, cudaStream_t st) {
-    estimate_final_kernel<<<1, 1024, 0, st>>>(P);
-    const int smem = 2 * EST_TILE_GROUPS * (P.d + 1) * (int)sizeof(float4);
+// The exact passes run on a fixed grid of two blocks per SM (the listed items are few
+// except for degenerate data such as constant y).
+cudaError_t launch_estimate_exact(const EstFinalParams& P, cudaStream_t st) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int smem = (EXACT_ROWS / GROUP + EST_TILE_GROUPS) * (P.d + 1) * (int)sizeof(float4);
     if (smem > 48 * 1024) {          // per device, so set on every call that needs it
         cudaError_t e = P.elem_bytes == 8
             ? cudaFuncSetAttribute(estimate_exact_kernel<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
@@ -453,17 +466,21 @@ cudaError_t launch_estimate_final(const EstFinalParams& P, cudaStream_t st) {
                 : cudaFuncSetAttribute(estimate_exact_kernel<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
     }
-    const dim3 grid(P.nb, P.nb);
-    if (P.nb == 0) {                 // no pair: the final kernel has recorded none
-    } else if (P.elem_bytes == 8) {
-        estimate_exact_kernel<double, 1><<<grid, 256, smem, st>>>(P);
-        estimate_exact_kernel<double, 2><<<grid, 256, smem, st>>>(P);
+    const int grid = 2 * sms;
+    if (P.elem_bytes == 8) {
+        estimate_exact_kernel<double, 1><<<grid, EXACT_THREADS, smem, st>>>(P);
+        estimate_exact_kernel<double, 2><<<grid, EXACT_THREADS, smem, st>>>(P);
     } else {
-        estimate_exact_kernel<float, 1><<<grid, 256, smem, st>>>(P);
-        estimate_exact_kernel<float, 2><<<grid, 256, smem, st>>>(P);
+        estimate_exact_kernel<float, 1><<<grid, EXACT_THREADS, smem, st>>>(P);
+        estimate_exact_kernel<float, 2><<<grid, EXACT_THREADS, smem, st>>>(P);
     }
     estimate_exact_finish_kernel<<<1, 32, 0, st>>>(P);
     return cudaGetLastError();
+}
+
+cudaError_t launch_estimate_final(const EstFinalParams& P, cudaStream_t st) {
+    estimate_final_kernel<<<1, 1024, 0, st>>>(P);
+    return launch_estimate_exact(P, st);
 }
 
 }  // namespace lip

@@ -1,6 +1,7 @@
 // Pruned Lipschitz-constant estimate (Sec. 5: M_est = max_{i<j} |y^i - y^j| / dist): the
-// FP64 definition's result exactly (the value, then the lowest i, then the lowest j), with
-// most of the N^2/2 pairs ruled out by bounds.
+// FP32 screen of the full estimate with most of the N^2/2 pairs ruled out by bounds,
+// followed by the same exact FP64 selection (estimate.cu), so the result is the FP64
+// definition's exactly (the value, then the lowest i, then the lowest j).
 //
 // The estimate layout is built in the spatial order of the points, with a record (box of
 // the points in layout coordinates, smallest and largest y) per 32-point chunk and per
@@ -11,21 +12,14 @@
 // so its FP32 squared ratio q = (y_i - y_j)^2 rcp(dist^2) is at most
 //   UB = num_ub rcp(den_lb) (1 + 2^-18)
 // (rcp.approx's relative error and the final product's rounding are far below the
-// margin).  Three passes over the tile pairs, diagonal band first (neighbouring tiles in
-// the spatial order hold the close pairs, whose ratios are the large ones):
-//   1. the largest q, q*, in one device word (atomicMax of its bits): a block skips a tile
-//      pair whose UB is below the largest q found so far, a warp skips a chunk whose UB
-//      against the box of its 128 row points is below that or its own running maximum;
-//   2. every pair with q >= T = q* (1 - 2^-16) gets its ratio in FP64, in the definition's
-//      order of operations, and the largest of those, R*, is kept (atomicMax of its bits);
-//   3. the same pairs again: the smallest (i, j) (data indices, i < j) whose FP64 ratio is
-//      R* (atomicMin of i << 32 | j).
-// For FP32 data q is within a relative (2d + 16) 2^-24 of the exact squared ratio (each
-// difference exact or rounded once, the weight rounded to FP32 and applied once, at most
-// d + 2 roundings in the sums and squares, one reciprocal of at most 2 ulps and one
-// product), so for d <= 8 the pair with the largest FP64 ratio has q >= T, and passes 2
-// and 3 skip only where UB < T.  The bound leaves out data whose weighted coordinate
-// differences fall into FP32's subnormal range or whose ratios overflow FP32.
+// margin).  The screen runs the tile pairs diagonal band first (neighbouring tiles in the
+// spatial order hold the close pairs, whose ratios are the large ones) and keeps the
+// largest q found so far in one device word (atomicMax of its bits): a block skips a tile
+// pair whose UB is below (1 - 2^-16) times it, a warp skips a chunk whose UB against the
+// box of its 128 row points is below (1 - 2^-16) times that or its own running maximum.
+// Every pair with q >= q* (1 - 2^-16) -- the exact selection's threshold -- is therefore
+// evaluated, and each tile pair's largest evaluated q is recorded; the select kernel lists
+// the tile pairs whose record reaches the threshold.
 #include "estimate.cuh"
 
 namespace lip {
@@ -91,45 +85,23 @@ __device__ __forceinline__ void band_pair(int64_t k, int nb, int& I, int& J) {
     J = I + b;
 }
 
-// The ratio of data points a and b in FP64 with the definition's order of operations and
-// no contraction (|x_a - x_b| w per coordinate, summed, squared and summed, or the
-// largest; the square root for L2; |y_a - y_b| / dist); -1 for a pair at distance 0 with
-// equal values, which the definition leaves out.
-template <int NORM, int D>
-__device__ double ratio64(const EstPrunedParams& P, int a, int b) {
-    double acc = 0.0;
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-        const double xa = __ldg(P.X + (int64_t)a * D + j), xb = __ldg(P.X + (int64_t)b * D + j);
-        const double v = __dmul_rn(fabs(__dsub_rn(xa, xb)), P.w64[j]);
-        if constexpr (NORM == LIP_L1) acc = __dadd_rn(acc, v);
-        else if constexpr (NORM == LIP_L2) acc = __dadd_rn(acc, __dmul_rn(v, v));
-        else acc = v > acc ? v : acc;
-    }
-    const double dist = NORM == LIP_L2 ? __dsqrt_rn(acc) : acc;
-    const double dy = fabs(__dsub_rn((double)__ldg(P.y + a), (double)__ldg(P.y + b)));
-    if (dist == 0.0) return dy == 0.0 ? -1.0 : (double)INFINITY;
-    return __ddiv_rn(dy, dist);
-}
+// (1 - 2^-16) x, rounded down: what a bound must reach for its pairs to stay candidates.
+__device__ __forceinline__ float ep_margin(float x) { return __fmul_rd(x, 0.9999847412109375f); }
 
-template <int NORM, int D, int PASS, bool WT>
+template <int NORM, int D, bool WT>
 __global__ void __launch_bounds__(EST_THREADS) estimate_pruned_kernel(const EstPrunedParams P) {
     constexpr int NCH = D + 1;
     constexpr int NB4 = pruned_box_f4(D);
     __shared__ __align__(16) float4 tile[EST_TILE_GROUPS * NCH];
     __shared__ __align__(16) float4 crec[EP_CHUNKS * NB4];
     __shared__ float red[EST_THREADS / 32];
-    __shared__ unsigned long long red64[EST_THREADS / 32];
+    __shared__ int wcnt[EST_THREADS / 32];
     int I, J;
     band_pair(blockIdx.x, P.nb, I, J);
     const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
     const int gb = *reinterpret_cast<const volatile int*>(P.gbest);
-    // pass 1: the largest squared ratio found so far; passes 2 and 3: q*
+    // the largest squared ratio found so far
     const float L = gb >= 0 ? __int_as_float(gb) : -1.f;
-    if (PASS > 1 && gb < 0) return;
-    const float T = PASS == 1 ? L : __fmul_rd(L, 0.9999847412109375f);      // q* (1 - 2^-16)
-    // pass 3: R*
-    const double Rs = PASS == 3 ? __longlong_as_double(*reinterpret_cast<const volatile long long*>(P.gratio)) : 0.0;
     float w1[D];
     float2 wt[D];
 #pragma unroll
@@ -141,8 +113,11 @@ __global__ void __launch_bounds__(EST_THREADS) estimate_pruned_kernel(const EstP
         float A[NB4 * 4], B[NB4 * 4];
         load_record<D>(P.tbox + (int64_t)I * NB4, A);
         load_record<D>(P.tbox + (int64_t)J * NB4, B);
-        // a tile without data has NaN bounds; a pair below T cannot reach the maximum
-        if (!(A[2 * D] == A[2 * D]) || !(B[2 * D] == B[2 * D]) || pair_ub<NORM, D, WT>(A, B, w1) < T) return;
+        // a tile without data has NaN bounds; a tile pair below the margin of L holds no candidate
+        if (!(A[2 * D] == A[2 * D]) || !(B[2 * D] == B[2 * D]) || pair_ub<NORM, D, WT>(A, B, w1) < ep_margin(L)) {
+            if (tid == 0) P.bq[blockIdx.x] = -1.f;
+            return;
+        }
     }
     const float4* src = P.lay + (size_t)J * EST_TILE_GROUPS * NCH;
     for (int k = tid; k < EST_TILE_GROUPS * NCH; k += EST_THREADS) tile[k] = __ldg(src + k);
@@ -198,28 +173,26 @@ __global__ void __launch_bounds__(EST_THREADS) estimate_pruned_kernel(const EstP
         W[2 * D] = lo;
         W[2 * D + 1] = hi;
     }
+    if (P.work && tid == 0) atomicAdd(P.work, 1ull);     // tile pairs entered
     bool live_row = false;
 #pragma unroll
     for (int r = 0; r < EST_R; ++r) live_row = live_row || yi[r].x == yi[r].x;
     const bool wlive = __any_sync(0xffffffffu, live_row);     // the warp holds data
     __syncthreads();
 
-    float best = -1.f;                    // pass 1: this thread's largest squared ratio
-    double rbest = -1.0;                  // pass 2: its largest FP64 ratio
-    unsigned long long kbest = ~0ull;     // pass 3: its smallest key with ratio R*
+    float best = -1.f;                    // this thread's largest squared ratio
+    int nev = 0;                          // chunks this warp evaluated
     for (int c = 0; c < EP_CHUNKS; ++c) {
-        // the warp's bound: the largest of its running maximum and L (pass 1), T (passes 2, 3)
-        float lim = T;
-        if constexpr (PASS == 1) {
-            float wb = best;
+        // the warp's bound: the margin of the larger of its running maximum and L
+        float wb = best;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) wb = fmaxf(wb, __shfl_xor_sync(0xffffffffu, wb, o));
-            lim = fmaxf(wb, L);
-        }
+        for (int o = 16; o > 0; o >>= 1) wb = fmaxf(wb, __shfl_xor_sync(0xffffffffu, wb, o));
+        const float lim = ep_margin(fmaxf(wb, L));
         float B[NB4 * 4];
         load_record<D>(crec + c * NB4, B);
         const bool need = wlive && B[2 * D] == B[2 * D] && !(pair_ub<NORM, D, WT>(W, B, w1) < lim);
         if (!__any_sync(0xffffffffu, need)) continue;
+        ++nev;
 #pragma unroll 2
         for (int gi = 0; gi < CHUNK_GROUPS; ++gi) {
             const int g = c * CHUNK_GROUPS + gi;
@@ -230,76 +203,67 @@ __global__ void __launch_bounds__(EST_THREADS) estimate_pruned_kernel(const EstP
             for (int r = 0; r < EST_R; ++r) {
                 float q[4];
                 est_group<NORM, D, WT>(xi[r], yi[r], x, wt, q);
-                if (PASS == 1) {
-                    best = max3f(max3f(best, q[0], q[1]), q[2], q[3]);
-                } else if (q[0] >= T || q[1] >= T || q[2] >= T || q[3] >= T) {
-                    const int a = P.dperm[g0 * GROUP + r];
-#pragma unroll 1
-                    for (int e = 0; e < 4; ++e) {
-                        if (!(q[e] >= T)) continue;
-                        const int b = P.dperm[(int64_t)J * EST_TILE + g * GROUP + e];
-                        const int lo = a < b ? a : b, hi = a < b ? b : a;
-                        const double rr = ratio64<NORM, D>(P, lo, hi);
-                        if (PASS == 2) {
-                            rbest = rr > rbest ? rr : rbest;
-                        } else if (rr == Rs) {
-                            const unsigned long long key = ((unsigned long long)lo << 32) | (unsigned)hi;
-                            kbest = key < kbest ? key : kbest;
-                        }
-                    }
-                }
+                best = max3f(max3f(best, q[0], q[1]), q[2], q[3]);
             }
         }
     }
-    if (PASS == 1) {
+    if (lane == 0) wcnt[warp] = nev;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-        if (lane == 0) red[warp] = best;
-        __syncthreads();
-        if (tid == 0) {
-            float b = red[0];
-            for (int w = 1; w < EST_THREADS / 32; ++w) b = fmaxf(b, red[w]);
-            if (b >= 0.f && b > L) atomicMax(P.gbest, __float_as_int(b));   // non-negative floats order as ints
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0) red[warp] = best;
+    __syncthreads();
+    if (tid == 0) {
+        float b = red[0];
+        int n = wcnt[0];
+        for (int w = 1; w < EST_THREADS / 32; ++w) {
+            b = fmaxf(b, red[w]);
+            n += wcnt[w];
         }
-    } else {
-        // pass 2: the largest ratio (non-negative doubles order as their bits), pass 3: the
-        // smallest key
-        unsigned long long v = PASS == 2 ? (rbest >= 0.0 ? (unsigned long long)__double_as_longlong(rbest) : 0ull) : kbest;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
-            v = PASS == 2 ? (u > v ? u : v) : (u < v ? u : v);
-        }
-        if (lane == 0) red64[warp] = v;
-        __syncthreads();
-        if (tid == 0) {
-            for (int w = 1; w < EST_THREADS / 32; ++w)
-                v = PASS == 2 ? (red64[w] > v ? red64[w] : v) : (red64[w] < v ? red64[w] : v);
-            if (PASS == 2 && v != 0ull) atomicMax(P.gratio, v);
-            if (PASS == 3 && v != ~0ull) atomicMin(P.gkey, v);
-        }
+        P.bq[blockIdx.x] = b >= 0.f ? b : -1.f;
+        if (b >= 0.f && b > L) atomicMax(P.gbest, __float_as_int(b));   // non-negative floats order as ints
+        if (P.work && n) atomicAdd(P.work + 1, (unsigned long long)n);
     }
 }
 
-template <int NORM, int D, bool WT>
-void launch_ep_w(const EstPrunedParams& P, int pass, cudaStream_t st) {
-    const int64_t npairs = (int64_t)P.nb * (P.nb + 1) / 2;
-    if (pass == 1) estimate_pruned_kernel<NORM, D, 1, WT><<<(unsigned)npairs, EST_THREADS, 0, st>>>(P);
-    else if (pass == 2) estimate_pruned_kernel<NORM, D, 2, WT><<<(unsigned)npairs, EST_THREADS, 0, st>>>(P);
-    else estimate_pruned_kernel<NORM, D, 3, WT><<<(unsigned)npairs, EST_THREADS, 0, st>>>(P);
+// q* and the list of tile pairs whose largest value reaches q* (1 - 2^-16), for the exact
+// selection; one block.
+__global__ void estimate_pruned_select_kernel(const EstPrunedParams P, const EstFinalParams F) {
+    __shared__ int s_count;
+    const int gb = *P.gbest;
+    const float qs = gb >= 0 ? __int_as_float(gb) : -1.f;
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    if (qs >= 0.f) {
+        const float T = ep_margin(qs);
+        const int64_t npairs = (int64_t)P.nb * (P.nb + 1) / 2;
+        for (int64_t k = threadIdx.x; k < npairs; k += blockDim.x) {
+            if (!(P.bq[k] >= T)) continue;
+            int I, J;
+            band_pair(k, P.nb, I, J);
+            F.list[atomicAdd(&s_count, 1)] = ((unsigned)I << 16) | (unsigned)J;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        F.state->q = qs >= 0.f ? gb : -1;
+        F.state->count = s_count;
+        F.state->ratio = 0ull;
+        F.state->key = ~0ull;
+    }
 }
 
 template <int NORM, int D>
-cudaError_t launch_ep(const EstPrunedParams& P, int pass, cudaStream_t st) {
-    if (P.weighted) launch_ep_w<NORM, D, true>(P, pass, st);
-    else launch_ep_w<NORM, D, false>(P, pass, st);
+cudaError_t launch_ep(const EstPrunedParams& P, cudaStream_t st) {
+    const int64_t npairs = (int64_t)P.nb * (P.nb + 1) / 2;
+    if (P.weighted) estimate_pruned_kernel<NORM, D, true><<<(unsigned)npairs, EST_THREADS, 0, st>>>(P);
+    else estimate_pruned_kernel<NORM, D, false><<<(unsigned)npairs, EST_THREADS, 0, st>>>(P);
     return cudaGetLastError();
 }
 
 template <int NORM, int... Ds>
-cudaError_t ep_dispatch(int d, const EstPrunedParams& P, int pass, cudaStream_t st, std::integer_sequence<int, Ds...>) {
+cudaError_t ep_dispatch(int d, const EstPrunedParams& P, cudaStream_t st, std::integer_sequence<int, Ds...>) {
     cudaError_t e = cudaErrorInvalidValue;
-    ((d == Ds + 1 ? (e = launch_ep<NORM, Ds + 1>(P, pass, st), 0) : 0), ...);
+    ((d == Ds + 1 ? (e = launch_ep<NORM, Ds + 1>(P, st), 0) : 0), ...);
     return e;
 }
 
@@ -309,12 +273,17 @@ constexpr int EP_DMAX = 8;
 
 bool estimate_pruned_available(int d) { return d >= 1 && d <= EP_DMAX; }
 
-cudaError_t launch_estimate_pruned(int norm, int d, const EstPrunedParams& P, int pass, cudaStream_t st) {
+cudaError_t launch_estimate_pruned_select(const EstPrunedParams& P, const EstFinalParams& F, cudaStream_t st) {
+    estimate_pruned_select_kernel<<<1, 1024, 0, st>>>(P, F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_estimate_pruned(int norm, int d, const EstPrunedParams& P, cudaStream_t st) {
     if (!estimate_pruned_available(d)) return cudaErrorInvalidValue;
     const auto seq = std::make_integer_sequence<int, EP_DMAX>{};
-    if (norm == LIP_L1) return ep_dispatch<LIP_L1>(d, P, pass, st, seq);
-    if (norm == LIP_L2) return ep_dispatch<LIP_L2>(d, P, pass, st, seq);
-    return ep_dispatch<LIP_LINF>(d, P, pass, st, seq);
+    if (norm == LIP_L1) return ep_dispatch<LIP_L1>(d, P, st, seq);
+    if (norm == LIP_L2) return ep_dispatch<LIP_L2>(d, P, st, seq);
+    return ep_dispatch<LIP_LINF>(d, P, st, seq);
 }
 
 }  // namespace lip

@@ -34,11 +34,12 @@ struct EstParams {
 };
 
 // Device words of the exact selection that follows the FP32 screen: q* (bits of the
-// largest FP32 squared ratio, -1 without a pair), R* (bits of the largest FP64 ratio among
-// the pairs near q*, starting at +0) and the smallest key i << 32 | j attaining R*.
+// largest FP32 squared ratio, -1 without a pair), the number of tile pairs listed for the
+// FP64 passes, R* (bits of the largest FP64 ratio among the pairs near q*, starting at +0)
+// and the smallest key i << 32 | j attaining R*.
 struct EstExactState {
     int q;
-    int pad;
+    int count;
     unsigned long long ratio;
     unsigned long long key;
 };
@@ -53,10 +54,14 @@ struct EstFinalParams {
     double* out;          // [3]: M_est, i, j (as doubles); [4] with write_key
     int part = 0, nparts = 1;   // the tile pairs whose candidates are read (as EstParams)
     int write_key = 0;    // out[3] = the FP64 ratio again, the key that orders parts (-1 without a pair)
-    // the exact selection: the screen's layout and weighting, and its device words
+    // the exact selection: the screen's layout (positions), its weighting, the position ->
+    // data index map (nullptr: the identity), the list of tile pairs I << 16 | J to visit
+    // (capacity: every tile pair) and the device words
     const float4* lay = nullptr;
     int64_t N = 0;
     bool weighted = false;
+    const int* perm = nullptr;
+    unsigned* list = nullptr;
     EstExactState* state = nullptr;
 };
 
@@ -122,10 +127,14 @@ cudaError_t launch_pad_hot(int elem_bytes, void* hot, int64_t k0, int64_t k1, in
 int estimate_tile_points();
 cudaError_t launch_estimate_layout(int elem_bytes, const HotParams& P, cudaStream_t st);
 cudaError_t launch_estimate(int norm, int d, const EstParams& P, cudaStream_t st);
-// After launch_estimate: q* of the part, then the exact selection among the pairs near it
-// (two passes over the tile pairs whose screen maximum reaches q* (1 - 2^-16)), then out.
+// After launch_estimate: q* of the part and the list of its tile pairs whose screen
+// maximum reaches q* (1 - 2^-16), then launch_estimate_exact.
 cudaError_t launch_estimate_final(const EstFinalParams& P, cudaStream_t st);
 constexpr int ESTIMATE_FINAL_LAUNCHES = 4;
+// The exact selection over the listed tile pairs (state->q, state->count and P.list set):
+// R*, then the lowest pair attaining it, then out.  Three launches.
+cudaError_t launch_estimate_exact(const EstFinalParams& P, cudaStream_t st);
+constexpr int ESTIMATE_EXACT_LAUNCHES = 3;
 
 // tensor-core operand formats
 constexpr int TC_TF32 = 0, TC_BF16 = 1, TC_FP16 = 2;
@@ -208,31 +217,28 @@ cudaError_t launch_chunk_records(const void* hot, int64_t N, int64_t nchunks, in
 cudaError_t launch_record_union(const void* box, int64_t nsuper, int per, int D, void* sbox, cudaStream_t st);
 
 // ------------------------------------------------ pruned estimate (estimate_pruned.cu)
-// M_est over the data in spatial order: pass 1 finds the largest FP32 squared ratio,
-// skipping tile pairs and 32-point chunks whose exact FP32 bound stays below the largest
-// value found so far; pass 2 finds the lowest (i, j) attaining it.  Same result as the
-// full estimate kernel bit for bit.
+// M_est over the data in spatial order: the screen pass finds the largest FP32 squared
+// ratio q*, skipping tile pairs and 32-point chunks whose exact FP32 bound stays below
+// the largest value found so far (with the selection's 2^-16 margin), and records each
+// tile pair's largest value; the select kernel lists the tile pairs that reach
+// q* (1 - 2^-16) for the exact selection (launch_estimate_exact).
 struct EstPrunedParams {
     const float4* lay;            // the estimate layout in position order
     int64_t N;
     int nb;                       // 512-point tiles
-    const int* dperm;             // [N] position -> data index
     const float4* cbox;           // [nb * 16][pruned_box_f4(d)] chunk records
     const float4* tbox;           // [nb][pruned_box_f4(d)] tile records
-    int* gbest;                   // pass 1: bits of the largest FP32 squared ratio q*, -1 none
-    unsigned long long* gratio;   // pass 2: bits of the largest FP64 ratio among the candidates (init 0)
-    unsigned long long* gkey;     // pass 3: smallest (i << 32 | j), i < j, attaining it (init ~0)
+    int* gbest;                   // bits of the largest FP32 squared ratio q*, -1 none
+    float* bq;                    // [nb (nb + 1) / 2] each tile pair's largest value (-1: none, skipped)
     bool weighted = false;        // as EstParams
     float w[PRUNED_DMAX] = {};
-    // the caller's data (FP32, row-major [N, d]) and weights for the FP64 ratios
-    const float* X = nullptr;
-    const float* y = nullptr;
-    double w64[PRUNED_DMAX] = {};
+    // optional counters: tile pairs entered, (warp, chunk) pairs evaluated
+    unsigned long long* work = nullptr;
 };
-cudaError_t launch_estimate_pruned(int norm, int d, const EstPrunedParams& P, int pass, cudaStream_t st);
+cudaError_t launch_estimate_pruned(int norm, int d, const EstPrunedParams& P, cudaStream_t st);
 bool estimate_pruned_available(int d);
-cudaError_t launch_estimate_pruned_finish(const EstFinalParams& F, const int* gbest, const unsigned long long* gratio,
-                                          const unsigned long long* gkey, cudaStream_t st);
+// q* from P.gbest and the list of tile pairs whose P.bq reaches q* (1 - 2^-16), into F.state / F.list.
+cudaError_t launch_estimate_pruned_select(const EstPrunedParams& P, const EstFinalParams& F, cudaStream_t st);
 
 // Scratch of the device-side fallback for nq queries (fb_state above).
 size_t tc_fallback_state_bytes(int64_t nq);

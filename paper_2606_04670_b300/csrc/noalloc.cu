@@ -28,10 +28,12 @@ constexpr int64_t NA_LAYOUT_BYTES = (NA_POINTS * (D_MAX + 1) * 4 + 255) / 256 * 
 constexpr int64_t NA_TILES = NA_POINTS / NA_TILE;
 constexpr int64_t NA_CAND_BYTES = (NA_TILES * NA_TILES * 16 + 255) / 256 * 256;
 constexpr int64_t NA_STATE_BYTES = 256;
-constexpr int64_t NA_BYTES = NA_LAYOUT_BYTES + NA_CAND_BYTES + NA_STATE_BYTES;   // about 4.4 MB (d up to 32)
+constexpr int64_t NA_LIST_BYTES = (NA_TILES * NA_TILES * 4 + 255) / 256 * 256;
+constexpr int64_t NA_BYTES = NA_LAYOUT_BYTES + NA_CAND_BYTES + NA_STATE_BYTES + NA_LIST_BYTES;   // about 4.4 MB (d up to 32)
 
 // Working memory of every lip_estimate_M_noalloc call on this device: the FP32 point
-// layout, one candidate record per tile pair, and the exact selection's device words.  Host code must not pass this
+// layout, one candidate record per tile pair, and the exact selection's device words and
+// list of tile pairs.  Host code must not pass this
 // name to a kernel (on the host it only stands for the symbol); it uses the address
 // obtained from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
@@ -172,6 +174,7 @@ extern "C" lip_status lip_estimate_M_noalloc(const float* X, const float* y, int
     F.N = N;
     F.weighted = weighted;
     F.state = state;
+    F.list = reinterpret_cast<unsigned*>(static_cast<char*>(base) + NA_LAYOUT_BYTES + NA_CAND_BYTES + NA_STATE_BYTES);
     if (N >= 2) {
         if ((e = launch_estimate_layout(4, Hp, st)) != cudaSuccess) return launch_fail(e, "estimate layout");
         if ((e = launch_pad_hot(4, lay, N, pts, nch, d, st)) != cudaSuccess) return launch_fail(e, "estimate padding");

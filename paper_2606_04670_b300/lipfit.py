@@ -112,6 +112,7 @@ def _load():
         "lip_set_tc_window": [H, i64],
         "lip_set_estimate_full": [H, i32],
         "lip_last_scan_work": [H, ctypes.POINTER(i64), ctypes.POINTER(i64)],
+        "lip_last_estimate_work": [H, ctypes.POINTER(i64)],
         "lip_add_async": [H, P, P, i64, P],
         "lip_add_host_async": [H, P, P, i64, P],
         "lip_debug_fail_alloc": [i64],
@@ -744,6 +745,13 @@ class LipFit:
     def check(self):
         _check(_lib.lip_check(self.h, _stream_ptr()), "lip_check")
 
+    def last_estimate_work(self):
+        """[tile pairs entered, (warp, chunk) pairs evaluated, total (warp, chunk) pairs] of
+        the last pruned lip_estimate_M's screen; all -1 when it was not pruned."""
+        out = (ctypes.c_int64 * 3)()
+        _check(_lib.lip_last_estimate_work(self.h, out), "lip_last_estimate_work")
+        return list(out)
+
     def last_scan_work(self):
         """(evaluated, total) (warp, chunk) pairs of the last pruned scan (variants 6 / 7);
         (-1, -1) when the last scan was not pruned."""
@@ -753,12 +761,12 @@ class LipFit:
 
     def set_estimate_full(self, full: bool = True):
         """lip_estimate_M with the full all-pairs kernel (True) or the default choice
-        (False: the pruned form for L2 / L-infinity where available); same result."""
+        (False: the pruned form where available); same result."""
         _check(_lib.lip_set_estimate_full(self.h, int(bool(full))), "lip_set_estimate_full")
 
     def set_estimate_form(self, form: str = "auto"):
-        """lip_estimate_M's form: "auto" (the default), "full" or "pruned" (every norm,
-        where available); all give the same result."""
+        """lip_estimate_M's form: "auto" (the default: pruned where available), "full" or
+        "pruned"; all give the same result."""
         code = {"auto": 0, "full": 1, "pruned": 2}[form]
         _check(_lib.lip_set_estimate_full(self.h, code), "lip_set_estimate_full")
 

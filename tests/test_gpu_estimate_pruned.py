@@ -93,10 +93,19 @@ def test_estimate_degenerate_data(oracle_mod):
 
 @pytest.mark.parametrize("norm", (1, 2, 3))
 def test_estimate_benchmark_size(norm):
-    """N = 1e5 (the benchmark's data): both forms agree bit for bit, and the result is its
-    pair's FP64 ratio."""
+    """N = 1e5 (the benchmark's data): both forms agree bit for bit, the result is its
+    pair's FP64 ratio, and the pruned screen evaluates part of the (warp, chunk) pairs."""
+    from paper_2606_04670_b300.lipfit import LipFit
     p = W.monotone_d4(norm=norm, n_query=16)
-    a, b = _both(p.X, p.y, norm)
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), 1.0, norm=norm)
+    a = m.lipschitz_constant()                       # the default form: pruned
+    entered, evaluated, total = m.last_estimate_work()
+    nb = (p.N + 511) // 512
+    assert 0 < entered <= nb * (nb + 1) // 2 and 0 < evaluated < 0.5 * total, (entered, evaluated, total)
+    m.set_estimate_form("full")
+    b = m.lipschitz_constant()
+    assert m.last_estimate_work() == [-1, -1, -1]
+    m.close()
     assert a == b, (a, b)
     assert 0 <= a[1] < a[2] < p.N
     assert abs(_ratio64(p.X, p.y, a[1], a[2], norm) - a[0]) <= 1e-15 * a[0]

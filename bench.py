@@ -63,9 +63,9 @@ TC_I_EPI = 6
 # entry is removed whenever its kernel changes, until it is captured again.
 KERNEL_DRAM_BYTES = {
     ("monotone_d4", 2): 19.136000e6 + 11.619840e6,     # scan_exact_kernel<L2, C=2, U=2, R=4>
-    ("monotone_d4", 1, "pruned"): 24.820e6 + 1.462e6,  # scan_pruned_kernel<L1, C=2, U=2, R=4>
-    ("monotone_d4", 2, "pruned"): 24.520e6 + 1.815e6,  # scan_pruned_kernel<L2, C=2, U=2, R=4>
-    ("monotone_d4", 3, "pruned"): 24.930e6 + 2.070e6,  # scan_pruned_kernel<Linf, C=2, U=2, R=4>
+    ("monotone_d4", 1, "pruned"): 24.483e6 + 1.459e6,  # scan_pruned_kernel<L1, C=2, U=2, R=4>
+    ("monotone_d4", 2, "pruned"): 24.567e6 + 1.808e6,  # scan_pruned_kernel<L2, C=2, U=2, R=4>
+    ("monotone_d4", 3, "pruned"): 24.763e6 + 2.085e6,  # scan_pruned_kernel<Linf, C=2, U=2, R=4>
     ("grad_d8", 2): 16.66e6 + 13.47e6,                 # scan_exact_kernel<L2, C=4, U=4, R=2>
     ("cluster_d16", 2): 618.02e6 + 185.20e6,           # scan_exact_kernel<L2, C=0, U=16, R=2>
     ("cluster_d16_tc", 2): 7185.37e6 + 1213.84e6,      # tc_scan_kernel<K=16, 4 parts, TF32> (persistent, soft lockstep)
@@ -562,8 +562,9 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
             f"R={rd['m'].tuning()['queries_per_thread']}> {rd['prec']}")
     if rd["prec"] == "fp64":
         kern = "FP32 screen " + kern.replace(" fp64", "") + " + screen64_kernel (FP64 candidates)"
-    # the pruned scan (variants 6, 7) evaluates only the (warp, chunk) pairs its bound test
-    # keeps: its roofline counts the pairs it evaluated, the whole pair space stays in value
+    # the pruned scan (variants 6, 7) evaluates only the (32-query row, 32-point chunk) pairs
+    # its bound test keeps: its roofline counts the pairs it evaluated, the whole pair space
+    # stays in value
     tun_dom = rd["m"].tuning()
     evaluated, wtotal = rd["m"].last_scan_work() if rd["prec"] == "fp32" else (-1, -1)
     share = evaluated / wtotal if wtotal > 0 and evaluated >= 0 else 1.0
@@ -574,9 +575,9 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
                         traffic_for(args, name, p.norm, pruned=wtotal > 0) if rd["prec"] == "fp32" else None,
                         fma=fma_lanes_per_pair(p.norm, p.d, c))
     if wtotal > 0:
-        roof["pruned"] = {"evaluated_warp_chunks": evaluated, "warp_chunks": wtotal, "evaluated_share": share,
+        roof["pruned"] = {"evaluated_row_chunks": evaluated, "row_chunks": wtotal, "evaluated_share": share,
                           "pairs_per_s_whole_space": p.nq * p.N / (avg[kdom] / 1e3),
-                          "note": "achieved counts the pairs of the evaluated 32-point chunks (share x Q x N); "
+                          "note": "achieved counts the pairs of the evaluated (row, chunk) blocks (share x Q x N); "
                                   "the per-chunk bound tests are not counted"}
     if rd["prec"] in ("tc_tf32", "tc_bf16", "tc_fp16"):
         roof = tc_roofline(ctx, rd["prec"], p.d, p.nq * p.N, avg[kdom], roof, traffic_for(args, name, p.norm))
@@ -656,6 +657,16 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
     if with_est:
         detail["M_est"] = {key(r): est[k] for k, r in enumerate(runs)}
         detail["M_true"] = {key(r): r["p"].M for r in runs}
+        # the pruned estimate's screen: tile pairs entered, (warp, chunk) pairs evaluated, total
+        detail["estimate_work"] = {key(r): r["m"].last_estimate_work() for r in runs}
+    # the pruned scan's evaluated share of its (row, chunk) pairs, per norm
+    shares = {}
+    for r in runs:
+        if r["prec"] == "fp32":
+            ev_r, tot_r = r["m"].last_scan_work()
+            if tot_r > 0:
+                shares[key(r)] = ev_r / tot_r
+    detail["pruned_scan_share"] = shares
     for r in runs:
         r["m"].close()
     if name == "monotone_d4" and not args.no_tc_vs_plain and ctx.world == 1:

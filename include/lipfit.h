@@ -218,8 +218,10 @@ LIP_API lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* 
 LIP_API lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, int64_t* j_out,
                           void* stream);
 
-/* Form of lip_estimate_M on this handle.  0 (the default) and 2: FP32 handles with
- * d <= 8 take the pruned form; 1: always the full kernel.  The pruned form puts the data in spatial order with a box and y range per
+/* Form of lip_estimate_M on this handle.  0 (the default): FP32 handles with d <= 8 and
+ * N >= 32768 take the pruned form (below that the full screen is cheaper than the pruned
+ * form's setup); 2: the pruned form wherever available (FP32, d <= 8); 1: always the full
+ * kernel.  The pruned form puts the data in spatial order with a box and y range per
  * 32-point chunk and per 512-point tile, and its FP32 screen skips the tile pairs and
  * chunks whose exact FP32 upper bound (box gaps with the pair arithmetic's own operations,
  * rcp.approx with a 2^-18 margin) is below (1 - 2^-16) times the largest value already
@@ -590,9 +592,10 @@ LIP_API lip_status lip_get_tuning(lip_handle h, int32_t* tile_groups, int32_t* s
  * be timed alone on the stream it runs on.  NULL, NULL turns this off. */
 LIP_API lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, void* ev_after_scan);
 
-/* After a pruned scan (lip_set_tuning variants 6 / 7): *evaluated = the (warp, chunk)
- * pairs the last scan of this handle evaluated, *total = all its (warp, chunk) pairs
- * (warps x 32-point chunks); both -1 / *total = -1 when the last scan was not pruned.
+/* After a pruned scan (lip_set_tuning variants 6 / 7): *evaluated = the (row, chunk)
+ * pairs the last scan of this handle evaluated, *total = all its (row, chunk) pairs (rows
+ * of 32 consecutive queries of the spatial order x 32-point chunks, each 1,024 query-point
+ * pairs); *evaluated = *total = -1 when the last scan was not pruned.
  * Synchronises the device to read the count. */
 LIP_API lip_status lip_last_scan_work(lip_handle h, int64_t* evaluated, int64_t* total);
 

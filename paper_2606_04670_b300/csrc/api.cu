@@ -441,7 +441,7 @@ lip_status scan_partials_pruned(lip_model* h, const void* Q, int64_t nq, cudaStr
     CUDA_TRY(h->pinfo.launch(PP, (int)gx, st));
     if (h->ev_scan1) CUDA_TRY(cudaEventRecord(h->ev_scan1, st));
     count_launches(1);
-    h->sp_total = gx * (SCAN_THREADS / 32) * nchunks;
+    h->sp_total = gx * (SCAN_THREADS / 32) * h->pinfo.rows * nchunks;   // (32-query row, chunk) pairs
     *nsplit_out = 1;
     return LIP_OK;
 }
@@ -728,7 +728,11 @@ lip_status estimate_pruned(lip_model* h, double* res, cudaStream_t st) {
     double* out = reinterpret_cast<double*>(small + 128);
     unsigned long long* work = reinterpret_cast<unsigned long long*>(small + 160);
     void* oscratch = at;
-    CUDA_TRY(spatial_order(static_cast<const float*>(h->X0), N, d, perm, bounds, oscratch, st));
+    // The pruned scan's position order of the same data (built by the same deterministic
+    // spatial_order, so identical) is reused while the data are unchanged.
+    const bool reuse = h->sp_data.p && !h->sp_dirty;
+    if (reuse) perm = static_cast<int*>(h->sp_data.p);
+    else CUDA_TRY(spatial_order(static_cast<const float*>(h->X0), N, d, perm, bounds, oscratch, st));
     HotParams Hp;
     Hp.X0 = h->X0;
     Hp.y0 = h->y0;
@@ -784,7 +788,7 @@ lip_status estimate_pruned(lip_model* h, double* res, cudaStream_t st) {
     F.state = state;
     CUDA_TRY(launch_estimate_pruned_select(P, F, st));
     CUDA_TRY(launch_estimate_exact(F, st));
-    count_launches(6 + ESTIMATE_EXACT_LAUNCHES + spatial_order_launches());
+    count_launches(6 + ESTIMATE_EXACT_LAUNCHES + (reuse ? 0 : spatial_order_launches()));
     // the result (4 doubles) and the work counters in one read
     unsigned char back[48];
     CUDA_TRY(cudaMemcpyAsync(back, out, sizeof back, cudaMemcpyDeviceToHost, st));
@@ -808,7 +812,9 @@ lip_status estimate_part(lip_model* h, int part, int nparts, double* res, cudaSt
     const int tile = estimate_tile_points();
     const int64_t nb = ceil_div(h->N, tile);
     if (nb > 65535) return fail(LIP_ERR_UNSUPPORTED, "N = %lld is too large for lip_estimate_M", (long long)h->N);
-    const bool pruned = h->est_form != 1;
+    // Below 32,768 points the full screen's N^2 work is a few tens of microseconds and the
+    // pruned form's spatial order and records (a dozen launches) cost more than they save.
+    const bool pruned = h->est_form == 2 || (h->est_form == 0 && h->N >= 32768);
     if (nparts == 1 && h->esize == 4 && estimate_pruned_available(h->d) && pruned)
         return estimate_pruned(h, res, st);
     const int64_t pts = nb * tile;

@@ -21,8 +21,9 @@
 //     lower side mirrors it with (yhi - ml).
 // A skipped chunk holds no value below mu (above ml), so it can neither change the
 // running extrema nor the chunk where they were reached: the results are those of an
-// unpruned scan over the same order.  The warp evaluates a chunk when any of its queries
-// needs it (queries in spatial order make the warp's needs coherent).
+// unpruned scan over the same order.  A warp holds R rows of 32 consecutive queries of the
+// spatial order (one query per lane and row); it evaluates a chunk for each row in which
+// any query needs it (queries in spatial order make a row's needs coherent).
 //
 // Processing order: the block's queries (R per thread, in spatial order) pick a start
 // chunk, the one whose box centre is nearest their centroid, rounded down to a multiple
@@ -211,9 +212,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
     const float4* hot = static_cast<const float4*>(P.hot);
     const float* Q = static_cast<const float*>(P.Q);
 
-    // the block's queries: a warp holds 32 R consecutive positions of the spatial order
-    // (lane l, row r: position qblock * 128 R + warp * 32 R + l R + r), so its queries are
-    // neighbours and its chunk decisions agree
+    // the block's queries: a warp holds 32 R consecutive positions of the spatial order,
+    // row r the 32 of them at warp * 32 R + 32 r (lane l: position qblock * 128 R +
+    // warp * 32 R + 32 r + l), so a row's queries are neighbours and its decisions agree
     float2 qq[R][D];
     float sq[R];
     int64_t qidx[R];
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
     for (int j = 0; j <= D; ++j) csum[j] = 0.f;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int64_t pos = (int64_t)blockIdx.x * (SCAN_THREADS * R) + (int64_t)warp * 32 * R + lane * R + r;
+        const int64_t pos = (int64_t)blockIdx.x * (SCAN_THREADS * R) + (int64_t)warp * 32 * R + 32 * r + lane;
         qidx[r] = pos < P.nq ? (int64_t)PP.qperm[pos] : -1;
         float s = 0.f;
         bool fin = qidx[r] >= 0;
@@ -383,15 +384,16 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
         bu[r] = -1;
         bl[r] = -1;
     }
-    // true when some query of this thread may need the record b
-    auto needs = [&](const float (&b)[NB4 * 4]) {
-        bool need = false;
-        if (b[2 * D] == b[2 * D]) {                    // the record holds data
+    // bit r set when some query of row r of the warp may need the record b
+    auto row_needs = [&](const float (&b)[NB4 * 4]) {
+        unsigned rows = 0u;
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-                need = need || (live[r] && chunk_needed<NORM, C, U>(qq[r], b, b + D, b[2 * D], b[2 * D + 1], mu[r], ml[r]));
+        for (int r = 0; r < R; ++r) {
+            const bool n = b[2 * D] == b[2 * D] && live[r] &&        // the record holds data
+                           chunk_needed<NORM, C, U>(qq[r], b, b + D, b[2 * D], b[2 * D + 1], mu[r], ml[r]);
+            if (__any_sync(0xffffffffu, n)) rows |= 1u << r;
         }
-        return need;
+        return rows;
     };
     unsigned evaluated = 0;
     // the warp's loosest running bounds (largest mu, smallest ml of its finite queries)
@@ -492,8 +494,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
                 const int chunk = chunk0 + k, c = k * CHUNK_GROUPS;
                 float bx[NB4 * 4];
                 load_rec(trec + k * NB4, bx);
-                if (!__any_sync(0xffffffffu, needs(bx))) continue;
-                ++evaluated;
+                const unsigned rows = row_needs(bx);
+                if (!rows) continue;
+                evaluated += __popc(rows);
 #pragma unroll 2
                 for (int gi = 0; gi < CHUNK_GROUPS; ++gi) {
                     float4 x[NCH];
@@ -501,6 +504,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
                     for (int ch = 0; ch < NCH; ++ch) x[ch] = tile[(c + gi) * NCH + ch];
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
+                        if (!((rows >> r) & 1u)) continue;      // warp-uniform
                         float vu[4], vl[4];
                         group_values<NORM, C, U>(qq[r], x, vu, vl);
                         mu[r] = min3f(min3f(mu[r], vu[0], vu[1]), vu[2], vu[3]);

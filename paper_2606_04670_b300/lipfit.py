@@ -753,20 +753,20 @@ class LipFit:
         return list(out)
 
     def last_scan_work(self):
-        """(evaluated, total) (warp, chunk) pairs of the last pruned scan (variants 6 / 7);
-        (-1, -1) when the last scan was not pruned."""
+        """(evaluated, total) (32-query row, 32-point chunk) pairs of the last pruned scan
+        (variants 6 / 7); (-1, -1) when the last scan was not pruned."""
         e, t = ctypes.c_int64(), ctypes.c_int64()
         _check(_lib.lip_last_scan_work(self.h, ctypes.byref(e), ctypes.byref(t)), "lip_last_scan_work")
         return e.value, t.value
 
     def set_estimate_full(self, full: bool = True):
         """lip_estimate_M with the full all-pairs kernel (True) or the default choice
-        (False: the pruned form where available); same result."""
+        (False: the pruned form from N = 32768 where available); same result."""
         _check(_lib.lip_set_estimate_full(self.h, int(bool(full))), "lip_set_estimate_full")
 
     def set_estimate_form(self, form: str = "auto"):
-        """lip_estimate_M's form: "auto" (the default: pruned where available), "full" or
-        "pruned"; all give the same result."""
+        """lip_estimate_M's form: "auto" (the default: pruned from N = 32768 where
+        available), "full" or "pruned" (wherever available); all give the same result."""
         code = {"auto": 0, "full": 1, "pruned": 2}[form]
         _check(_lib.lip_set_estimate_full(self.h, code), "lip_set_estimate_full")
 

@@ -192,8 +192,9 @@ LIP_API lip_status lip_eval_k(lip_handle h, const void* Q, int64_t nq, int32_t k
                               void* stream);
 
 /* lip_eval with Q and the outputs in host memory: the queries are copied in, evaluated
- * and the results copied out in chunks, with copies overlapping the kernels of other
- * chunks.  Synchronises the stream before returning (the outputs are then valid). */
+ * and the results copied out in chunks (2^19 queries; 2^23 with the pruned scan, which
+ * prunes better on all the queries at once), with copies overlapping the kernels of
+ * other chunks.  Synchronises the stream before returning (the outputs are then valid). */
 LIP_API lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi,
                          int32_t* idx_up, int32_t* idx_lo, void* stream);
 

@@ -1060,7 +1060,10 @@ lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* g, void*
         }
     }
     const size_t es = h->esize;
-    const int64_t chunk = std::min<int64_t>(nq, (int64_t)1 << 19);
+    // Chunks of 2^19 queries overlap the copies with the kernels.  The pruned scan orders
+    // its queries in space and prunes per row of 32 neighbours, so it loses far more on a
+    // chunk (sparser queries, looser rows) than the overlap gains: it takes up to 2^23 at once.
+    const int64_t chunk = std::min<int64_t>(nq, (int64_t)1 << (h->pruned && !h->tc ? 23 : 19));
     // per buffer: Q chunk, g, lo, hi, idx_up, idx_lo
     const size_t qb = round_up((int64_t)(chunk * h->d * es), 256), vb = round_up((int64_t)(chunk * es), 256),
                  ib = round_up((int64_t)(chunk * 4), 256);

@@ -184,12 +184,16 @@ def test_set_M_equals_refit(oracle_mod):
     m.close()
 
 
-def test_eval_host_equals_eval():
+@pytest.mark.parametrize("variant", (0, 6))
+def test_eval_host_equals_eval(variant):
+    """The host path equals the device path bit for bit: in three chunks with copies
+    overlapping the kernels (variant 0), in one chunk for the pruned scan (variant 6)."""
     import torch
 
     from paper_2606_04670_b300.lipfit import LipFit
     p = W.monotone_d4(norm=W.NORM_L1, n_data=10_000, n_query=1_200_000)
     m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, mon=p.mon)
+    m.set_tuning(0, 0, variant)
     dev = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
     Qp = torch.as_tensor(p.Q).pin_memory()
     host = m.eval_host(Qp)

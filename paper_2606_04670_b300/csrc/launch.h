@@ -141,7 +141,7 @@ constexpr int TC_TF32 = 0, TC_BF16 = 1, TC_FP16 = 2;
 size_t tc_tile_bytes_for(int d, int fmt);
 size_t tc_a_bytes_for(int d, int fmt);
 size_t tc_rec_bytes();
-// Spatial order of n points (row-major [n][d]): perm[position] = index, by a 16-bit Morton
+// Spatial order of n points (row-major [n][d]): perm[position] = index, by a 16-bit Hilbert
 // key of the first min(d, 16) coordinates and a stable radix sort (deterministic).
 size_t spatial_order_scratch(int64_t n);
 // bounds (nullable): [d] (min, max) of each coordinate's finite values, (0, 0) when none.

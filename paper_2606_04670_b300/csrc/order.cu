@@ -1,5 +1,5 @@
-// Spatial order of a point set: a 16-bit Morton key per point (the first min(d, 16)
-// coordinates, each cut into 2^(16 / D) cells of its bounding box and interleaved), then a
+// Spatial order of a point set: a 16-bit Hilbert key per point (the first min(d, 16)
+// coordinates, each cut into 2^(16 / D) cells of its bounding box), then a
 // stable LSD radix sort of the keys in two 8-bit passes, giving the permutation
 // position -> index.  Points close in space get close positions, so consecutive runs of
 // points are spatially coherent.  Every step is deterministic: counts are atomics on
@@ -62,8 +62,14 @@ __global__ void __launch_bounds__(ORD_THREADS) ord_bbox_kernel(const float* X, i
     }
 }
 
-// The Morton key of each point.  Block 0 also writes the box as floats, (0, 0) for a
-// coordinate with no finite value.
+// The Hilbert key of each point: the cell coordinates are turned into the "transposed"
+// Hilbert index by J. Skilling's method (Programming the Hilbert curve, AIP Conf. Proc.
+// 707, 2004: from the top bit down, each coordinate either inverts the low bits of the
+// first or exchanges its low bits with it; then a Gray code across the coordinates), and
+// the transposed bits are interleaved as a Morton key would be.  Consecutive cells of the
+// Hilbert curve are always neighbours, so runs of the order have smaller boxes than
+// Morton runs, which jump at every level boundary.  Block 0 also writes the box as
+// floats, (0, 0) for a coordinate with no finite value.
 __global__ void ord_key_kernel(const float* X, int64_t n, int d, const unsigned* box, unsigned* keys, int* idx,
                                float2* bounds) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -85,6 +91,26 @@ __global__ void ord_key_kernel(const float* X, int64_t n, int d, const unsigned*
             c = u >= (float)(cells - 1) ? cells - 1 : (u > 0.f ? (int)u : 0);
         }
         cell[j] = c;
+    }
+    if (D > 1) {
+        const int top = 1 << (b - 1);
+        for (int q = top; q > 1; q >>= 1) {
+            const int p = q - 1;
+            for (int j = 0; j < D; ++j) {
+                if (cell[j] & q) {
+                    cell[0] ^= p;                               // invert the low bits
+                } else {
+                    const int t = (cell[0] ^ cell[j]) & p;      // exchange the low bits
+                    cell[0] ^= t;
+                    cell[j] ^= t;
+                }
+            }
+        }
+        for (int j = 1; j < D; ++j) cell[j] ^= cell[j - 1];   // Gray code
+        int t = 0;
+        for (int q = top; q > 1; q >>= 1)
+            if (cell[D - 1] & q) t ^= q - 1;
+        for (int j = 0; j < D; ++j) cell[j] ^= t;
     }
     unsigned key = 0u;
     for (int l = b - 1; l >= 0; --l)

@@ -2,7 +2,7 @@
 // extrema as scan_exact_kernel, over the data in spatial order, skipping every 32-point
 // chunk that provably cannot lower H_up nor raise H_lo of any query of the warp.
 //
-// The data are laid out in the spatial order of their points (a Morton order), so a
+// The data are laid out in the spatial order of their points (a Hilbert order), so a
 // chunk's points are close together; each chunk carries its bounding box in the layout's
 // coordinates (already scaled by M w, mirrored where decreasing) and the range of its
 // values.  From a query q and the box, the kernel forms the smallest distance any point

@@ -659,14 +659,20 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
         detail["M_true"] = {key(r): r["p"].M for r in runs}
         # the pruned estimate's screen: tile pairs entered, (warp, chunk) pairs evaluated, total
         detail["estimate_work"] = {key(r): r["m"].last_estimate_work() for r in runs}
-    # the pruned scan's evaluated share of its (row, chunk) pairs, per norm
-    shares = {}
+    # the pruned scan's evaluated share of its (row, chunk) pairs and the share of the data
+    # tiles its blocks copied, per norm
+    shares, tiles, raw = {}, {}, {}
     for r in runs:
         if r["prec"] == "fp32":
-            ev_r, tot_r = r["m"].last_scan_work()
-            if tot_r > 0:
-                shares[key(r)] = ev_r / tot_r
+            st = r["m"].last_scan_stats()
+            if st[1] > 0:
+                shares[key(r)] = st[0] / st[1]
+                tiles[key(r)] = st[2] / st[3]
+                raw[key(r)] = st
     detail["pruned_scan_share"] = shares
+    detail["pruned_tiles_copied_share"] = tiles
+    # [evaluated (row, chunk), all (row, chunk), tiles copied, blocks x tiles, (warp, chunk) past the warp-box test]
+    detail["pruned_scan_stats"] = raw
     for r in runs:
         r["m"].close()
     if name == "monotone_d4" and not args.no_tc_vs_plain and ctx.world == 1:

@@ -600,6 +600,14 @@ LIP_API lip_status lip_set_timing_events(lip_handle h, void* ev_before_scan, voi
  * Synchronises the device to read the count. */
 LIP_API lip_status lip_last_scan_work(lip_handle h, int64_t* evaluated, int64_t* total);
 
+/* The same and more (host int64[5]): out[0] evaluated and out[1] all (row, chunk) pairs as
+ * lip_last_scan_work, out[2] the data tiles the blocks copied to shared memory, out[3]
+ * blocks x data tiles, out[4] the (warp, chunk) pairs of the copied tiles that passed the
+ * warp-box test (and went to the per-query tests); all -1 when the last scan was not
+ * pruned.
+ * Synchronises the device.  LIP_ERR_ARG for NULL. */
+LIP_API lip_status lip_last_scan_stats(lip_handle h, int64_t* out);
+
 /* After a pruned lip_estimate_M: out (host int64[3]) = the tile pairs that passed the tile
  * bound test, the (warp, chunk) pairs the screen evaluated (a warp holds 128 row points, a
  * chunk 32 column points), and the total (warp, chunk) pairs of the tile triangle; all -1

@@ -436,12 +436,13 @@ lip_status scan_partials_pruned(lip_model* h, const void* Q, int64_t nq, cudaStr
     PP.sbox = static_cast<const float4*>(sbox);
     PP.nchunks = nchunks;
     PP.work = work;
-    CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), st));
+    CUDA_TRY(cudaMemsetAsync(work, 0, 3 * sizeof(unsigned long long), st));
     if (h->ev_scan0) CUDA_TRY(cudaEventRecord(h->ev_scan0, st));
     CUDA_TRY(h->pinfo.launch(PP, (int)gx, st));
     if (h->ev_scan1) CUDA_TRY(cudaEventRecord(h->ev_scan1, st));
     count_launches(1);
     h->sp_total = gx * (SCAN_THREADS / 32) * h->pinfo.rows * nchunks;   // (32-query row, chunk) pairs
+    h->sp_tiles = gx * (ngroups / h->tile_groups);                       // blocks x tiles of the data
     *nsplit_out = 1;
     return LIP_OK;
 }
@@ -1393,20 +1394,33 @@ lip_status lip_last_estimate_work(lip_handle h, int64_t* out) {
     return LIP_OK;
 }
 
-lip_status lip_last_scan_work(lip_handle h, int64_t* evaluated, int64_t* total) {
+lip_status lip_last_scan_stats(lip_handle h, int64_t* out) {
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
-    if (!evaluated || !total) return fail(LIP_ERR_ARG, "an output pointer is NULL");
-    *evaluated = -1;
-    *total = h->sp_total;
+    if (!out) return fail(LIP_ERR_ARG, "out is NULL");
+    out[0] = out[2] = out[4] = -1;
+    out[1] = h->sp_total;
+    out[3] = h->sp_total < 0 ? -1 : h->sp_tiles;
     if (h->sp_total < 0 || !h->sp_data.p) return LIP_OK;
     const int64_t N = h->N, npad = round_up(N, PAD_POINTS), ngroups = npad / GROUP;
     const size_t off = round_up(N * 4, 256) + round_up(ngroups * h->nch * 16, 256) +
                        round_up(ngroups / CHUNK_GROUPS * pruned_box_f4(h->dl) * 16, 256) + round_up(D_MAX * 8, 256);
-    unsigned long long w = 0;
+    unsigned long long w[3] = {0, 0, 0};
     DeviceGuard gd(h->device);
     CUDA_TRY(cudaDeviceSynchronize());
-    CUDA_TRY(cudaMemcpy(&w, static_cast<char*>(h->sp_data.p) + off, sizeof w, cudaMemcpyDeviceToHost));
-    *evaluated = (int64_t)w;
+    CUDA_TRY(cudaMemcpy(w, static_cast<char*>(h->sp_data.p) + off, sizeof w, cudaMemcpyDeviceToHost));
+    out[0] = (int64_t)w[0];
+    out[2] = (int64_t)w[1];
+    out[4] = (int64_t)w[2];
+    return LIP_OK;
+}
+
+lip_status lip_last_scan_work(lip_handle h, int64_t* evaluated, int64_t* total) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (!evaluated || !total) return fail(LIP_ERR_ARG, "an output pointer is NULL");
+    int64_t s[5];
+    LIP_TRY(lip_last_scan_stats(h, s));
+    *evaluated = s[0];
+    *total = s[1];
     return LIP_OK;
 }
 

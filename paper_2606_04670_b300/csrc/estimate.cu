@@ -92,7 +92,7 @@ estimate_kernel(const EstParams P) {
             for (int r = 0; r < EST_R; ++r) {
                 float q[4];
                 est_group<NORM, D, WT>(xi[r], yi[r], x, wt, q);
-                best[r] = max3f(max3f(best[r], q[0], q[1]), q[2], q[3]);
+                best[r] = max3f(best[r], max3f(q[0], q[1], q[2]), q[3]);   // one link of the chain per group
             }
         }
 #pragma unroll

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(EST_THREADS) estimate_pruned_kernel(const EstP
             for (int r = 0; r < EST_R; ++r) {
                 float q[4];
                 est_group<NORM, D, WT>(xi[r], yi[r], x, wt, q);
-                best = max3f(max3f(best, q[0], q[1]), q[2], q[3]);
+                best = max3f(best, max3f(q[0], q[1], q[2]), q[3]);   // one link of the chain per group
             }
         }
     }

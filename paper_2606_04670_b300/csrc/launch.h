@@ -188,7 +188,8 @@ struct PrunedParams {
     const float4* box;            // [nchunks][pruned_box_f4(D)] chunk records
     const float4* sbox;           // [nchunks / 8][pruned_box_f4(D)]: records of 8 chunks (64 groups)
     int64_t nchunks;
-    unsigned long long* work;     // nullable: evaluated (warp, chunk) pairs, summed per launch
+    unsigned long long* work;     // nullable: [0] evaluated (row, chunk) pairs, [1] tiles copied,
+                                  // [2] (warp, chunk) pairs passing the warp-box test, per launch
 };
 // Chunk record: lo[D], hi[D] (layout coordinates), ylo (smallest y), yhv (largest value of
 // the lower bound's channel: y, or the aux channel for L1 with constrained coordinates).

@@ -134,7 +134,8 @@ struct lip_model {
     PrunedKernelInfo pinfo;
     Scratch sp_data, sp_q;              // position-ordered layout and chunk records; query order
     bool sp_dirty = true;               // the position-ordered layout needs a rebuild
-    int64_t sp_total = -1;              // (warp, chunk) pairs of the last pruned scan, -1 if none
+    int64_t sp_total = -1;              // (row, chunk) pairs of the last pruned scan, -1 if none
+    int64_t sp_tiles = -1;              // its blocks x data tiles
     int est_form = 0;                   // lip_estimate_M: 0 pruned from N = 32768, 1 always full, 2 pruned where available
     int64_t est_work[3] = {-1, -1, -1};   // lip_last_estimate_work
     int* tc_fb_count = nullptr;         // device count of the last tensor-core lip_eval's fallback

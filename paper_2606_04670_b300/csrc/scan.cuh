@@ -275,8 +275,9 @@ __device__ __forceinline__ void scan_block(const ScanParams& P, int64_t qblock, 
                 for (int r = 0; r < R; ++r) {
                     float vu[4], vl[4];
                     group_values<NORM, C, U>(qq[r], x, vu, vl, FSR > 0 && r % FSR == FSR - 1);
-                    mu[r] = min3f(min3f(mu[r], vu[0], vu[1]), vu[2], vu[3]);
-                    ml[r] = max3f(max3f(ml[r], vl[0], vl[1]), vl[2], vl[3]);
+                    // the group's own extrema first: one link of each running chain per group
+                    mu[r] = min3f(mu[r], min3f(vu[0], vu[1], vu[2]), vu[3]);
+                    ml[r] = max3f(ml[r], max3f(vl[0], vl[1], vl[2]), vl[3]);
                 }
             }
             const int chunk = (int)((g_begin + (int64_t)t * tg + c) / CHUNK_GROUPS);

@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
         }
         return rows;
     };
-    unsigned evaluated = 0;
+    unsigned evaluated = 0, candidates = 0;
     // the warp's loosest running bounds (largest mu, smallest ml of its finite queries)
     auto warp_bounds = [&](float& mmax, float& mmin) {
         mmax = -__int_as_float(0x7f800000);
@@ -459,6 +459,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
         }
         __syncthreads();
         const int len = seq_len;
+        if (PP.work && tid == 0 && len) atomicAdd(PP.work + 1, (unsigned long long)len);
         if (tid == 0)
             for (int k = 0; k < PRUNED_STAGES && k < len; ++k) issue(step + k, seq[k]);
         // The warps take the batch's tiles independently: a warp waits for a tile's copies,
@@ -489,7 +490,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
                 cand = cb[2 * D] == cb[2 * D] &&
                        box_needed<NORM, C, U>(qlo, qhi, cb, cb + D, cb[2 * D], cb[2 * D + 1], mmax, mmin);
             }
-            for (unsigned left = __ballot_sync(0xffffffffu, cand); left; left &= left - 1) {
+            const unsigned cands = __ballot_sync(0xffffffffu, cand);
+            candidates += __popc(cands);
+            for (unsigned left = cands; left; left &= left - 1) {
                 const int k = __ffs(left) - 1;
                 const int chunk = chunk0 + k, c = k * CHUNK_GROUPS;
                 float bx[NB4 * 4];
@@ -507,8 +510,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
                         if (!((rows >> r) & 1u)) continue;      // warp-uniform
                         float vu[4], vl[4];
                         group_values<NORM, C, U>(qq[r], x, vu, vl);
-                        mu[r] = min3f(min3f(mu[r], vu[0], vu[1]), vu[2], vu[3]);
-                        ml[r] = max3f(max3f(ml[r], vl[0], vl[1]), vl[2], vl[3]);
+                        // the group's own extrema first: one link of each running chain per group
+                        mu[r] = min3f(mu[r], min3f(vu[0], vu[1], vu[2]), vu[3]);
+                        ml[r] = max3f(ml[r], max3f(vl[0], vl[1], vl[2]), vl[3]);
                     }
                 }
 #pragma unroll
@@ -542,6 +546,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
         s_begin += s_count;
     }
     if (PP.work && lane == 0 && evaluated) atomicAdd(PP.work, (unsigned long long)evaluated);
+    if (PP.work && lane == 0 && candidates) atomicAdd(PP.work + 2, (unsigned long long)candidates);
     PartialRec<float>* out = static_cast<PartialRec<float>*>(P.partial);
     if (!ok) {
 #pragma unroll

@@ -113,6 +113,7 @@ def _load():
         "lip_set_estimate_full": [H, i32],
         "lip_last_scan_work": [H, ctypes.POINTER(i64), ctypes.POINTER(i64)],
         "lip_last_estimate_work": [H, ctypes.POINTER(i64)],
+        "lip_last_scan_stats": [H, ctypes.POINTER(i64)],
         "lip_add_async": [H, P, P, i64, P],
         "lip_add_host_async": [H, P, P, i64, P],
         "lip_debug_fail_alloc": [i64],
@@ -750,6 +751,14 @@ class LipFit:
         the last pruned lip_estimate_M's screen; all -1 when it was not pruned."""
         out = (ctypes.c_int64 * 3)()
         _check(_lib.lip_last_estimate_work(self.h, out), "lip_last_estimate_work")
+        return list(out)
+
+    def last_scan_stats(self):
+        """[evaluated (row, chunk) pairs, all of them, tiles copied, blocks x tiles,
+        (warp, chunk) pairs past the warp-box test] of the last pruned scan; -1 entries when
+        it was not pruned."""
+        out = (ctypes.c_int64 * 5)()
+        _check(_lib.lip_last_scan_stats(self.h, out), "lip_last_scan_stats")
         return list(out)
 
     def last_scan_work(self):

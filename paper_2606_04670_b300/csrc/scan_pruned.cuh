@@ -188,6 +188,7 @@ __device__ __forceinline__ bool box_needed(const float* qlo, const float* qhi, c
 constexpr int PRUNED_LEAD = 2;     // super-chunks streamed before the first window
 constexpr int PRUNED_STAGES = 6;   // the pruned scan's ring of tiles
 constexpr int PRUNED_WIN = 256;    // super-chunks per window
+constexpr int PRUNED_SORT = 1024;  // most super-chunks put in nearest-first order per block
 
 template <int NORM, int C, int U, int R>
 __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedParams PP) {
@@ -298,7 +299,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
     }
     float bd = __int_as_float(0x7f800000);
     int bk = 0x7fffffff;
-    for (int64_t k = tid; k < PP.nchunks; k += SCAN_THREADS) {
+    // (only for the cyclic order, taken when the super-chunks are too many to sort)
+    const int64_t nsearch = PP.nchunks / 8 <= PRUNED_SORT ? 0 : PP.nchunks;
+    for (int64_t k = tid; k < nsearch; k += SCAN_THREADS) {
         const float* b = reinterpret_cast<const float*>(PP.box + k * NB4);
         if (!(b[2 * D] == b[2 * D])) continue;             // a chunk without data
         float dd = 0.f;
@@ -329,14 +332,67 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
     }
     __syncthreads();
 
-    // The sweep runs over super-chunks (8 chunks, 64 groups) in cyclic order from the start
-    // one.  The first PRUNED_LEAD are streamed as they are; the rest go in windows of
-    // PRUNED_WIN, each reduced first to the super-chunks that some warp of the block may
-    // still need (tested against the running bounds, which only tighten afterwards, so a
-    // super-chunk left out then would be skipped later too).  Only the listed tiles are
-    // copied to shared memory.
+    // The sweep runs over super-chunks (8 chunks, 64 groups).  Up to PRUNED_SORT of them it
+    // takes them nearest first: by the distance from the centre of their box to the
+    // centroid of the block's queries (ties by index), sorted in shared memory by a bitonic
+    // network, so the running extrema approach their final values within the first few
+    // and the rest are tested against nearly final bounds.  With more super-chunks it runs
+    // in cyclic order from the start one.  The first PRUNED_LEAD are streamed as they are;
+    // the rest go in windows of PRUNED_WIN, each reduced first to the super-chunks that
+    // some warp of the block may still need (tested against the running bounds, which only
+    // tighten afterwards, so a super-chunk left out then would be skipped later too).  Only
+    // the listed tiles are copied to shared memory.
     const int nsuper = (int)(PP.nchunks / 8);
     const int sup0 = start_chunk / 8;
+    const bool sorted = nsuper <= PRUNED_SORT;
+    __shared__ float skey[PRUNED_SORT];
+    __shared__ short sidx[PRUNED_SORT];
+    if (sorted) {
+        int n2 = 1;
+        while (n2 < nsuper) n2 <<= 1;
+        for (int s = tid; s < n2; s += SCAN_THREADS) {
+            float dd = __int_as_float(0x7f800000);
+            if (s < nsuper) {
+                const float* b = reinterpret_cast<const float*>(PP.sbox + (int64_t)s * NB4);
+                if (b[2 * D] == b[2 * D]) {                   // a super-chunk with data
+                    dd = 0.f;
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        const float e = 0.5f * (b[j] + b[D + j]) - cen[j];
+                        dd = fmaf(e, e, dd);
+                    }
+                }
+            }
+            skey[s] = dd;
+            sidx[s] = (short)s;            // padding entries (s >= nsuper) sort last
+        }
+        __syncthreads();
+        for (int k = 2; k <= n2; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = tid; i < n2; i += SCAN_THREADS) {
+                    const int x = i ^ j;
+                    if (x > i) {
+                        const float ki = skey[i], kx = skey[x];
+                        const int ii = sidx[i], ix = sidx[x];
+                        const bool gt = ki > kx || (ki == kx && ii > ix);
+                        if (gt == ((i & k) == 0)) {           // ascending where bit k of i is 0
+                            skey[i] = kx;
+                            skey[x] = ki;
+                            sidx[i] = (short)ix;
+                            sidx[x] = (short)ii;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    // the super-chunk taken at place s of the sweep
+    auto super_at = [&](int s) {
+        if (sorted) return (int)sidx[s];
+        int sp = sup0 + s;
+        return sp >= nsuper ? sp - nsuper : sp;
+    };
     const int tps = TILE_GROUPS_MAX / tg;             // tiles per super-chunk
     __shared__ int seq[PRUNED_WIN * (TILE_GROUPS_MAX / 8)];
     __shared__ unsigned wmask[PRUNED_WIN / 32];
@@ -420,11 +476,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
         const int s_count = min(lead ? PRUNED_LEAD : PRUNED_WIN, nsuper - s_begin);
         if (lead) {
             if (tid == 0) {
-                for (int i = 0; i < s_count * tps; ++i) {
-                    int sp = sup0 + i / tps;
-                    if (sp >= nsuper) sp -= nsuper;
-                    seq[i] = sp * tps + i % tps;
-                }
+                for (int i = 0; i < s_count * tps; ++i) seq[i] = super_at(i / tps) * tps + i % tps;
                 seq_len = s_count * tps;
             }
         } else {
@@ -435,8 +487,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
             for (int i0 = 0; i0 < s_count; i0 += 32) {
                 bool need8 = false;
                 if (wlive && i0 + lane < s_count) {
-                    int sp = sup0 + s_begin + i0 + lane;
-                    if (sp >= nsuper) sp -= nsuper;
+                    const int sp = super_at(s_begin + i0 + lane);
                     float sb[NB4 * 4];
                     load_box(PP.sbox + (int64_t)sp * NB4, sb);
                     need8 = sb[2 * D] == sb[2 * D] &&
@@ -450,8 +501,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
                 int n = 0;
                 for (int i = 0; i < s_count; ++i) {
                     if (!((wmask[i >> 5] >> (i & 31)) & 1u)) continue;
-                    int sp = sup0 + s_begin + i;
-                    if (sp >= nsuper) sp -= nsuper;
+                    const int sp = super_at(s_begin + i);
                     for (int k = 0; k < tps; ++k) seq[n++] = sp * tps + k;
                 }
                 seq_len = n;

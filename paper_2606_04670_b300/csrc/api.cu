@@ -388,7 +388,8 @@ lip_status scan_partials_pruned(lip_model* h, const void* Q, int64_t nq, cudaStr
     if (ngroups == 0) return LIP_OK;
     const int64_t gx = ceil_div(nq, (int64_t)SCAN_THREADS * h->pinfo.rows);
     if (gx > 0x7fffffff) return fail(LIP_ERR_ARG, "nq = %lld is too large", (long long)nq);
-    const size_t perm_b = round_up(N * 4, 256), hot_b = round_up(ngroups * h->nch * 16, 256),
+    const int pnch = h->pinfo.nch;                   // the pruned layout: no aux channel
+    const size_t perm_b = round_up(N * 4, 256), hot_b = round_up(ngroups * pnch * 16, 256),
                  box_b = round_up(nchunks * pruned_box_f4(D) * 16, 256), bnd_b = round_up(D_MAX * 8, 256),
                  cnt_b = 256, sbox_b = round_up(nchunks / 8 * pruned_box_f4(D) * 16, 256);
     LIP_TRY(h->sp_data.ensure(perm_b + hot_b + box_b + bnd_b + cnt_b + sbox_b + spatial_order_scratch(N),
@@ -407,10 +408,12 @@ lip_status scan_partials_pruned(lip_model* h, const void* Q, int64_t nq, cudaStr
         fill_hot_params(h, Hp, 0, N);
         Hp.hot = shot;
         Hp.gather = dperm;
+        Hp.nch = pnch;
+        Hp.aux = 0;
         Hp.err = h->status + 3;                         // the data were checked when added
         CUDA_TRY(launch_build_hot(4, Hp, st));
-        CUDA_TRY(launch_pad_hot(4, shot, N, npad, h->nch, h->dl, st));
-        CUDA_TRY(launch_pruned_boxes(shot, N, nchunks, D, h->nch, h->aux != 0, box, sbox, st));
+        CUDA_TRY(launch_pad_hot(4, shot, N, npad, pnch, h->dl, st));
+        CUDA_TRY(launch_pruned_boxes(shot, N, nchunks, D, pnch, false, box, sbox, st));
         count_launches(4 + spatial_order_launches());
         h->sp_dirty = false;
     }
@@ -1402,7 +1405,7 @@ lip_status lip_last_scan_stats(lip_handle h, int64_t* out) {
     out[3] = h->sp_total < 0 ? -1 : h->sp_tiles;
     if (h->sp_total < 0 || !h->sp_data.p) return LIP_OK;
     const int64_t N = h->N, npad = round_up(N, PAD_POINTS), ngroups = npad / GROUP;
-    const size_t off = round_up(N * 4, 256) + round_up(ngroups * h->nch * 16, 256) +
+    const size_t off = round_up(N * 4, 256) + round_up(ngroups * h->pinfo.nch * 16, 256) +
                        round_up(ngroups / CHUNK_GROUPS * pruned_box_f4(h->dl) * 16, 256) + round_up(D_MAX * 8, 256);
     unsigned long long w[3] = {0, 0, 0};
     DeviceGuard gd(h->device);

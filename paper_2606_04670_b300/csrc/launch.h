@@ -192,7 +192,7 @@ struct PrunedParams {
                                   // [2] (warp, chunk) pairs passing the warp-box test, per launch
 };
 // Chunk record: lo[D], hi[D] (layout coordinates), ylo (smallest y), yhv (largest value of
-// the lower bound's channel: y, or the aux channel for L1 with constrained coordinates).
+// the lower bound's channel: y, or the aux channel where the layout has one).
 __host__ __device__ constexpr int pruned_box_f4(int D) { return (2 * D + 2 + 3) / 4; }
 // Largest dimension with a pruned instantiation.
 constexpr int PRUNED_DMAX = 8;

@@ -49,10 +49,13 @@ constexpr int SCAN_THREADS = 128;
 constexpr int SCAN_STAGES = 3;
 constexpr int CHUNK_GROUPS = 8;   // argmin/argmax are localised to 32-point chunks
 
-template <int NORM, int C, int U>
+// DIRECT: the lower distance is formed from the negative parts of the constrained
+// differences instead of through the aux channel (used by the pruned scan, whose chunk
+// bounds are tighter on the direct form; no aux channel then).
+template <int NORM, int C, int U, bool DIRECT = false>
 struct ExactShape {
     static constexpr int D = C + U;
-    static constexpr bool AUX = (NORM == LIP_L1 && C > 0);
+    static constexpr bool AUX = !DIRECT && (NORM == LIP_L1 && C > 0);
     static constexpr int NCH = D + 1 + (AUX ? 1 : 0);
 };
 
@@ -81,8 +84,9 @@ __device__ __forceinline__ float max_reduce(const float (&v)[K]) {
 // coordinates): the lower distances of the group's second pair of points take the FMA-pipe
 // square root (sqrt_fma2) instead of the special-function unit, which the two roots per
 // pair otherwise saturate.
-template <int NORM, int C, int U>
-__device__ __forceinline__ void group_values(const float2 (&qq)[C + U], const float4 (&x)[ExactShape<NORM, C, U>::NCH],
+template <int NORM, int C, int U, bool DIRECT = false>
+__device__ __forceinline__ void group_values(const float2 (&qq)[C + U],
+                                             const float4 (&x)[ExactShape<NORM, C, U, DIRECT>::NCH],
                                              float (&vu)[4], float (&vl)[4], bool fs = false) {
     constexpr int D = C + U;
 #pragma unroll
@@ -117,8 +121,9 @@ __device__ __forceinline__ void group_values(const float2 (&qq)[C + U], const fl
                 dl = du;
             }
         } else if constexpr (NORM == LIP_L1) {
-            float2 acc;
-            // unconstrained: |t|, constrained: (t)_+ (upper); the lower comes from AUX
+            float2 acc = make_float2(0.f, 0.f);
+            // unconstrained: |t|, constrained: (t)_+ (upper); the lower comes from AUX, or
+            // (DIRECT) from the same unconstrained sum plus the negative parts (-t)_+
             if constexpr (U >= 2) {
                 acc = make_float2(fabsf(t[C].x) + fabsf(t[C + 1].x), fabsf(t[C].y) + fabsf(t[C + 1].y));
 #pragma unroll
@@ -126,14 +131,20 @@ __device__ __forceinline__ void group_values(const float2 (&qq)[C + U], const fl
             } else if constexpr (U == 1) {
                 acc = make_float2(fabsf(t[C].x), fabsf(t[C].y));
             }
+            float2 accl = acc;
 #pragma unroll
             for (int j = 0; j < C; ++j) {
                 const float2 p = make_float2(fmaxf(t[j].x, 0.f), fmaxf(t[j].y, 0.f));
                 if (j == 0 && U == 0) acc = p;
                 else acc = add2(acc, p);
+                if constexpr (DIRECT) {
+                    const float2 n = make_float2(fmaxf(-t[j].x, 0.f), fmaxf(-t[j].y, 0.f));
+                    if (j == 0 && U == 0) accl = n;
+                    else accl = add2(accl, n);
+                }
             }
             du = acc;
-            dl = acc;
+            dl = DIRECT ? accl : acc;
         } else {  // LINF
             float du_[2], dl_[2];
 #pragma unroll
@@ -167,7 +178,7 @@ __device__ __forceinline__ void group_values(const float2 (&qq)[C + U], const fl
         }
         float2 v_up = add2(yv, du);
         float2 v_lo;
-        if constexpr (ExactShape<NORM, C, U>::AUX) v_lo = sub2(half_of(x[D + 1], h), dl);
+        if constexpr (ExactShape<NORM, C, U, DIRECT>::AUX) v_lo = sub2(half_of(x[D + 1], h), dl);
         else v_lo = sub2(yv, dl);
         vu[2 * h] = v_up.x;
         vu[2 * h + 1] = v_up.y;

@@ -86,15 +86,17 @@ __device__ __forceinline__ bool chunk_needed(const float2 (&q)[C + U], const flo
         } else if constexpr (U == 1) {
             acc = fabsf(t[C]);
         }
+        // the lower side's distance (the direct form of group_values): the unconstrained sum
+        // plus the negative parts (x - q)_+, smallest at x = lo
+        float accl = acc;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-            const float p = fmaxf(t[j], 0.f);
+            const float p = fmaxf(t[j], 0.f), n = fmaxf(-tl[j], 0.f);
             acc = (j == 0 && U == 0) ? p : __fadd_rn(acc, p);
+            accl = (j == 0 && U == 0) ? n : __fadd_rn(accl, n);
         }
-        // with constrained coordinates the lower side runs on the aux channel with the
-        // same (upper) distance; without them both sides take the symmetric distance
         skip_u = __fadd_rn(ylo, acc) >= mu;
-        skip_l = __fsub_rn(yhv, acc) <= ml;
+        skip_l = __fsub_rn(yhv, accl) <= ml;
     } else {
         float uu = 0.f;
 #pragma unroll
@@ -162,13 +164,15 @@ __device__ __forceinline__ bool box_needed(const float* qlo, const float* qhi, c
         } else if constexpr (U == 1) {
             acc = fmaxf(fmaxf(a[C], b[C]), 0.f);
         }
+        float accl = acc;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-            const float p = fmaxf(a[j], 0.f);
+            const float p = fmaxf(a[j], 0.f), n = fmaxf(b[j], 0.f);
             acc = (j == 0 && U == 0) ? p : __fadd_rn(acc, p);
+            accl = (j == 0 && U == 0) ? n : __fadd_rn(accl, n);
         }
         skip_u = __fadd_rn(ylo, acc) >= mu_max;
-        skip_l = __fsub_rn(yhv, acc) <= ml_min;
+        skip_l = __fsub_rn(yhv, accl) <= ml_min;
     } else {
         float uu = 0.f;
 #pragma unroll
@@ -192,7 +196,7 @@ constexpr int PRUNED_SORT = 1024;  // most super-chunks put in nearest-first ord
 
 template <int NORM, int C, int U, int R>
 __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedParams PP) {
-    using S = ExactShape<NORM, C, U>;
+    using S = ExactShape<NORM, C, U, true>;        // the direct lower distance, no aux channel
     constexpr int D = S::D;
     constexpr int NCH = S::NCH;
     constexpr int NB4 = pruned_box_f4(D);
@@ -559,7 +563,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
                     for (int r = 0; r < R; ++r) {
                         if (!((rows >> r) & 1u)) continue;      // warp-uniform
                         float vu[4], vl[4];
-                        group_values<NORM, C, U>(qq[r], x, vu, vl);
+                        group_values<NORM, C, U, true>(qq[r], x, vu, vl);
                         // the group's own extrema first: one link of each running chain per group
                         mu[r] = min3f(mu[r], min3f(vu[0], vu[1], vu[2]), vu[3]);
                         ml[r] = max3f(ml[r], max3f(vl[0], vl[1], vl[2]), vl[3]);
@@ -622,7 +626,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) x[ch] = __ldg(hot + g * NCH + ch);
                 float vu[4], vl[4];
-                group_values<NORM, C, U>(qq[r], x, vu, vl);
+                group_values<NORM, C, U, true>(qq[r], x, vu, vl);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     if (side == 0 && iu < 0 && vu[e] == mu[r]) iu = PP.dperm[g * 4 + e];

@@ -11,7 +11,7 @@ __host__ __device__ constexpr int pruned_rows(int D, int v) { return rows_for_va
 
 template <int NORM, int C, int U, int R>
 cudaError_t launch_scan_pruned(const PrunedParams& P, int gx, cudaStream_t st) {
-    constexpr int NCH = ExactShape<NORM, C, U>::NCH;
+    constexpr int NCH = ExactShape<NORM, C, U, true>::NCH;
     auto kern = scan_pruned_kernel<NORM, C, U, R>;
     constexpr int NB4 = pruned_box_f4(C + U);
     const size_t smem = (size_t)PRUNED_STAGES * (P.S.tile_groups * NCH + 8 * NB4) * sizeof(float4);
@@ -32,7 +32,7 @@ struct PrunedTable {
         e.launch = &launch_scan_pruned<NORM, C, U, R>;
         e.kernel = reinterpret_cast<const void*>(&scan_pruned_kernel<NORM, C, U, R>);
         e.rows = R;
-        e.nch = ExactShape<NORM, C, U>::NCH;
+        e.nch = ExactShape<NORM, C, U, true>::NCH;
     }
     template <int K>
     void fill_one() {

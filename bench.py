@@ -596,17 +596,22 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
             r["m"].set_timing_events(None, None)
 
         def step_host():
+            # every problem's fit and evaluation queued first (lip_eval_host_async: the
+            # copies of one overlap the kernels of another), then the estimates, then
+            # lip_check, which also waits for the host-path copies
             for r, hX, hy, hQ, outs in hostruns:
                 m = r["m"]
                 m.clear()
                 m.add_host_async(hX, hy)
-                m.eval_host(hQ, outs)
-                if with_est:
+                m.eval_host(hQ, outs, wait=False)
+            if with_est:
+                for r, *_ in hostruns:
                     if ctx.world > 1:
-                        S.estimate_M_sharded(S.DeviceShard(m, 0), device="cuda")
+                        S.estimate_M_sharded(S.DeviceShard(r["m"], 0), device="cuda")
                     else:
-                        m.lipschitz_constant()
-                m.check()
+                        r["m"].lipschitz_constant()
+            for r, *_ in hostruns:
+                r["m"].check()
 
         step_host()
         torch.cuda.synchronize()

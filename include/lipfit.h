@@ -198,6 +198,16 @@ LIP_API lip_status lip_eval_k(lip_handle h, const void* Q, int64_t nq, int32_t k
 LIP_API lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi,
                          int32_t* idx_up, int32_t* idx_lo, void* stream);
 
+/* lip_eval_host without the final synchronisation: returns once the copies (on the
+ * handle's own copy stream) and the kernels (on `stream`) are queued.  Q and the outputs
+ * must stay valid, and the outputs unread, until lip_check(h, stream) has returned (it
+ * waits for the handle's copies); pinned host memory keeps the copies asynchronous.  The
+ * copies of one handle's call overlap the kernels queued before it on `stream`, so calls
+ * on several handles overlap one another's transfers and kernels.  The handle's next
+ * host-path call reuses its staging buffers in order. */
+LIP_API lip_status lip_eval_host_async(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi,
+                                       int32_t* idx_up, int32_t* idx_lo, void* stream);
+
 /* Lipschitz constant of the data (Sec. 5: lipschitz_constant()): the maximum over pairs
  * i < j of |y^i - y^j| / dist(x^i, x^j) with the symmetric weighted norm of the handle
  * (monotonicity does not enter).  N^2/2 work and no pair matrix is stored (Sec. 5).
@@ -636,7 +646,8 @@ LIP_API uint64_t lip_kernel_launches(void);
 /* ---------------------------------------------------------------- status */
 
 /* Synchronise the stream and report a failure recorded by the device since the last
- * lip_check on this handle: LIP_ERR_TIMEOUT if a bounded wait inside a kernel gave up
+ * lip_check on this handle (it also waits for lip_eval_host_async's copies):
+ * LIP_ERR_TIMEOUT if a bounded wait inside a kernel gave up
  * (the kernel then skipped its work and returned), LIP_ERR_NONFINITE if a lip_add_async /
  * lip_add_host_async met NaN or Inf (TIMEOUT is reported first when both happened),
  * LIP_ERR_CUDA for a CUDA error.  The recorded failures are cleared. */

@@ -1048,8 +1048,13 @@ lip_status lip_eval_k(lip_handle h, const void* Q, int64_t nq, int32_t k, const 
     return LIP_OK;
 }
 
-lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* idx_up,
-                         int32_t* idx_lo, void* stream) {
+// The host path.  With wait, both streams are synchronised before returning.  Without,
+// the call returns once everything is queued: the kernels on the caller's stream, the
+// copies on the handle's copy stream, which needs no wait on the caller's stream (the
+// staging buffers are reused only by this path, whose copies are ordered on that stream
+// and whose kernels wait for their inputs' copies); lip_check waits for the copies.
+static lip_status eval_host(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* idx_up,
+                            int32_t* idx_lo, void* stream, bool wait) {
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
     if (nq < 0) return fail(LIP_ERR_ARG, "nq = %lld < 0", (long long)nq);
     if (nq == 0) return LIP_OK;
@@ -1079,9 +1084,11 @@ lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* g, void*
     auto dI = [&](int b, int k) { return base + b * per + qb + 3 * vb + k * ib; };
     const int64_t nchunks = ceil_div(nq, chunk);
     cudaStream_t cs = h->copy_stream;
-    // the copy stream starts after everything already queued on the caller's stream
-    CUDA_TRY(cudaEventRecord(h->ev_out[0], st));
-    CUDA_TRY(cudaStreamWaitEvent(cs, h->ev_out[0], 0));
+    if (wait) {
+        // the copy stream starts after everything already queued on the caller's stream
+        CUDA_TRY(cudaEventRecord(h->ev_out[0], st));
+        CUDA_TRY(cudaStreamWaitEvent(cs, h->ev_out[0], 0));
+    }
     auto h2d = [&](int64_t c) -> lip_status {
         const int b = (int)(c & 1);
         const int64_t q0 = c * chunk, n = std::min(chunk, nq - q0);
@@ -1111,9 +1118,21 @@ lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* g, void*
             if (idx[k]) CUDA_TRY(cudaMemcpyAsync(idx[k] + q0, dI(b, k), (size_t)n * 4, cudaMemcpyDeviceToHost, cs));
         if (c + 2 < nchunks) LIP_TRY(h2d(c + 2));
     }
-    CUDA_TRY(cudaStreamSynchronize(cs));
-    CUDA_TRY(cudaStreamSynchronize(st));
+    if (wait) {
+        CUDA_TRY(cudaStreamSynchronize(cs));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
     return LIP_OK;
+}
+
+lip_status lip_eval_host(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi, int32_t* idx_up,
+                         int32_t* idx_lo, void* stream) {
+    return eval_host(h, Q, nq, g, lo, hi, idx_up, idx_lo, stream, true);
+}
+
+lip_status lip_eval_host_async(lip_handle h, const void* Q, int64_t nq, void* g, void* lo, void* hi,
+                               int32_t* idx_up, int32_t* idx_lo, void* stream) {
+    return eval_host(h, Q, nq, g, lo, hi, idx_up, idx_lo, stream, false);
 }
 
 lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, int64_t* j_out, void* stream) {
@@ -1241,6 +1260,7 @@ lip_status lip_check(lip_handle h, void* stream) {
     unsigned bits = 0;
     CUDA_TRY(cudaMemcpyAsync(&bits, h->status, sizeof bits, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    if (h->copy_stream) CUDA_TRY(cudaStreamSynchronize(h->copy_stream));   // lip_eval_host_async's copies
     if (bits) {
         CUDA_TRY(cudaMemsetAsync(h->status, 0, sizeof bits, st));
         CUDA_TRY(cudaStreamSynchronize(st));

@@ -79,6 +79,7 @@ def _load():
         "lip_set_M": [H, f64, P],
         "lip_eval": [H, P, i64, P, P, P, P, P, P],
         "lip_eval_host": [H, P, i64, P, P, P, P, P, P],
+        "lip_eval_host_async": [H, P, i64, P, P, P, P, P, P],
         "lip_eval_k": [H, P, i64, i32, P, P, P, P, P, P, P],
         "lip_estimate_M": [H, ctypes.POINTER(f64), ctypes.POINTER(i64), ctypes.POINTER(i64), P],
         "lip_backward": [H, P, i64, P, P, P, P, P, P, i32, P],
@@ -291,6 +292,10 @@ def lip_smooth(h, M, p, max_iter, history, gtol, eps_ptr, stream=0):
 
 def lip_eval_host(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream=0):
     return _lib.lip_eval_host(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream)
+
+
+def lip_eval_host_async(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream=0):
+    return _lib.lip_eval_host_async(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream)
 
 
 def lip_estimate_M(h, stream=0):
@@ -656,8 +661,10 @@ class LipFit:
             return self.eval_local(Q, need=("g",))["g"]
         return self.eval_local_k(Q, k, np.ones(k) / k if wk is None else wk)["g"]
 
-    def eval_host(self, Q, out=None):
-        """lip_eval_host: Q and the outputs in host memory (numpy or pinned CPU tensors)."""
+    def eval_host(self, Q, out=None, wait=True):
+        """lip_eval_host: Q and the outputs in host memory (numpy or pinned CPU tensors).
+        wait=False: lip_eval_host_async, the outputs are valid once check() has returned
+        (Q and out must stay alive until then)."""
         torch = _torch()
         if torch.is_tensor(Q):
             Qh = Q
@@ -677,8 +684,9 @@ class LipFit:
                 return None
             return a.data_ptr() if torch.is_tensor(a) else a.ctypes.data
 
-        _check(_lib.lip_eval_host(self.h, qptr, nq, p(out.get("g")), p(out.get("lo")), p(out.get("hi")),
-                                  p(out.get("idx_up")), p(out.get("idx_lo")), _stream_ptr()), "lip_eval_host")
+        fn = _lib.lip_eval_host if wait else _lib.lip_eval_host_async
+        _check(fn(self.h, qptr, nq, p(out.get("g")), p(out.get("lo")), p(out.get("hi")),
+                  p(out.get("idx_up")), p(out.get("idx_lo")), _stream_ptr()), "lip_eval_host")
         return out
 
     # -- several GPUs (paper_2606_04670_b300.shard drives these around the collectives)

@@ -67,6 +67,7 @@ def test_null_handle_calls():
     assert L.lip_set_estimate_full(None, 3) == L.LIP_ERR_ARG
     assert L._lib.lip_last_estimate_work(None, None) == L.LIP_ERR_ARG
     assert L._lib.lip_last_scan_stats(None, None) == L.LIP_ERR_ARG
+    assert L.lip_eval_host_async(None, None, 0, None, None, None, None, None) == L.LIP_ERR_ARG
     assert L.lip_clear(None) == L.LIP_ERR_ARG
     assert L.lip_set_M(None, 1.0) == L.LIP_ERR_ARG
     assert L.lip_estimate_M(None)[0] == L.LIP_ERR_ARG

@@ -202,6 +202,31 @@ def test_eval_host_equals_eval(variant):
     m.close()
 
 
+def test_eval_host_async_on_several_handles():
+    """lip_eval_host_async on three handles queued back to back (their copies overlap the
+    others' kernels), the results read after lip_check: equal to the device path."""
+    import torch
+
+    from paper_2606_04670_b300.lipfit import LipFit
+    runs = []
+    for norm, variant in ((W.NORM_L1, 6), (W.NORM_L2, 0), (W.NORM_LINF, 6)):
+        p = W.monotone_d4(norm=norm, n_data=20_000, n_query=700_000)
+        m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, mon=p.mon)
+        m.set_tuning(0, 0, variant)
+        dev = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
+        Qp = torch.as_tensor(p.Q).pin_memory()
+        out = {k: torch.empty(p.nq, dtype=torch.float32).pin_memory() for k in ("g", "lo", "hi")}
+        out.update({k: torch.empty(p.nq, dtype=torch.int32).pin_memory() for k in ("idx_up", "idx_lo")})
+        runs.append((m, dev, Qp, out))
+    for m, _, Qp, out in runs:
+        m.eval_host(Qp, out, wait=False)
+    for m, dev, _, out in runs:
+        m.check()
+        for k in dev:
+            np.testing.assert_array_equal(out[k].numpy(), dev[k], err_msg=k)
+        m.close()
+
+
 @pytest.mark.parametrize("norm", NORMS)
 def test_full_size_monotone_d4_sampled(oracle_mod, norm):
     """The benchmark workload at full size (N = 1e5, Q = 1e6, same launch shape as the

@@ -40,10 +40,10 @@ def pruned_capable(model) -> bool:
 
 def eval_key(model, nq: int) -> str:
     c = 0 if model.mon is None else int((model.mon != 0).sum())
-    # "eval5": shapes with the pruned scan (variants 6, 7, skipping chunks per 32-query
-    # row, Hilbert order) among their eight variants; "eval2": the others (six FP32
-    # variants, the FMA-pipe square roots)
-    tag = "eval5" if pruned_capable(model) else "eval2"
+    # "eval6": shapes with the pruned scan (variants 6, 7: 16-point chunks skipped per
+    # 32-query row, Hilbert order, nearest first) among their eight variants; "eval2":
+    # the others (six FP32 variants, the FMA-pipe square roots)
+    tag = "eval6" if pruned_capable(model) else "eval2"
     return f"{tag}/norm{model.norm}/C{c}/U{model.d - c}/prec{model.precision}/N2^{_bucket(model.N)}/Q2^{_bucket(nq)}"
 
 

@@ -381,7 +381,7 @@ int choose_splits(const lip_model* h, int64_t gx, int64_t tiles) {
 // one launch over all the data (one split).
 lip_status scan_partials_pruned(lip_model* h, const void* Q, int64_t nq, cudaStream_t st, int* nsplit_out) {
     const int64_t N = h->N;
-    const int64_t npad = round_up(N, PAD_POINTS), ngroups = npad / GROUP, nchunks = ngroups / CHUNK_GROUPS;
+    const int64_t npad = round_up(N, PAD_POINTS), ngroups = npad / GROUP, nchunks = ngroups / PRUNED_CG;
     const int D = h->dl;
     h->last_splits = ngroups > 0 ? 1 : 0;
     *nsplit_out = 0;
@@ -391,7 +391,7 @@ lip_status scan_partials_pruned(lip_model* h, const void* Q, int64_t nq, cudaStr
     const int pnch = h->pinfo.nch;                   // the pruned layout: no aux channel
     const size_t perm_b = round_up(N * 4, 256), hot_b = round_up(ngroups * pnch * 16, 256),
                  box_b = round_up(nchunks * pruned_box_f4(D) * 16, 256), bnd_b = round_up(D_MAX * 8, 256),
-                 cnt_b = 256, sbox_b = round_up(nchunks / 8 * pruned_box_f4(D) * 16, 256);
+                 cnt_b = 256, sbox_b = round_up(nchunks / PRUNED_CPS * pruned_box_f4(D) * 16, 256);
     LIP_TRY(h->sp_data.ensure(perm_b + hot_b + box_b + bnd_b + cnt_b + sbox_b + spatial_order_scratch(N),
                               "pruned scan data"));
     char* base = static_cast<char*>(h->sp_data.p);
@@ -444,7 +444,7 @@ lip_status scan_partials_pruned(lip_model* h, const void* Q, int64_t nq, cudaStr
     CUDA_TRY(h->pinfo.launch(PP, (int)gx, st));
     if (h->ev_scan1) CUDA_TRY(cudaEventRecord(h->ev_scan1, st));
     count_launches(1);
-    h->sp_total = gx * (SCAN_THREADS / 32) * h->pinfo.rows * nchunks;   // (32-query row, chunk) pairs
+    h->sp_total = gx * (SCAN_THREADS / 32) * h->pinfo.rows * nchunks;   // (32-query row, 16-point chunk) pairs
     h->sp_tiles = gx * (ngroups / h->tile_groups);                       // blocks x tiles of the data
     *nsplit_out = 1;
     return LIP_OK;
@@ -1426,7 +1426,7 @@ lip_status lip_last_scan_stats(lip_handle h, int64_t* out) {
     if (h->sp_total < 0 || !h->sp_data.p) return LIP_OK;
     const int64_t N = h->N, npad = round_up(N, PAD_POINTS), ngroups = npad / GROUP;
     const size_t off = round_up(N * 4, 256) + round_up(ngroups * h->pinfo.nch * 16, 256) +
-                       round_up(ngroups / CHUNK_GROUPS * pruned_box_f4(h->dl) * 16, 256) + round_up(D_MAX * 8, 256);
+                       round_up(ngroups / PRUNED_CG * pruned_box_f4(h->dl) * 16, 256) + round_up(D_MAX * 8, 256);
     unsigned long long w[3] = {0, 0, 0};
     DeviceGuard gd(h->device);
     CUDA_TRY(cudaDeviceSynchronize());

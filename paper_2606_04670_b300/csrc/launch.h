@@ -196,6 +196,9 @@ struct PrunedParams {
 __host__ __device__ constexpr int pruned_box_f4(int D) { return (2 * D + 2 + 3) / 4; }
 // Largest dimension with a pruned instantiation.
 constexpr int PRUNED_DMAX = 8;
+// The pruned scan's chunks: 16 points (4 groups), 16 of them to a 64-group super-chunk.
+constexpr int PRUNED_CG = 4;
+constexpr int PRUNED_CPS = 64 / PRUNED_CG;
 __host__ __device__ constexpr bool pruned_shape_available(int C, int U) {
     return C + U >= 1 && C + U <= PRUNED_DMAX;
 }
@@ -207,13 +210,14 @@ struct PrunedKernelInfo {
     int nch = 0;
 };
 PrunedKernelInfo scan_pruned_info(int norm, int C, int U, int variant);
-// The chunk records of the position-ordered layout `hot` (N real points), then the
-// records of every 8 consecutive chunks (sbox, nchunks a multiple of 8).
+// The records of the pruned scan's 16-point chunks of the position-ordered layout `hot`
+// (N real points), then the records of every PRUNED_CPS consecutive chunks (sbox,
+// nchunks a multiple of PRUNED_CPS).
 cudaError_t launch_pruned_boxes(const void* hot, int64_t N, int64_t nchunks, int D, int nch, bool aux, void* box,
                                 void* sbox, cudaStream_t st);
-// The records of every 32-point chunk of a layout (as above, without the unions).
+// The records of every `cpts`-point chunk of a layout (as above, without the unions).
 cudaError_t launch_chunk_records(const void* hot, int64_t N, int64_t nchunks, int D, int nch, bool aux, void* box,
-                                 cudaStream_t st);
+                                 cudaStream_t st, int cpts = 32);
 // The union of every `per` consecutive records of `box` (nsuper of them) into sbox.
 cudaError_t launch_record_union(const void* box, int64_t nsuper, int per, int D, void* sbox, cudaStream_t st);
 

@@ -11,12 +11,12 @@ PrunedKernelInfo scan_pruned_info_linf(int C, int U, int v);
 
 namespace {
 
-// One thread per 32-point chunk of the layout `hot` (groups of 4 points, nch float4
+// One thread per `cpts`-point chunk of the layout `hot` (groups of 4 points, nch float4
 // channels: coordinates 0..D-1, y, then aux when `aux`): the box of its real points
 // (positions < N) in layout coordinates, the smallest y and the largest value of the
 // lower bound's channel (aux when present, else y).  A chunk without real points gets NaN.
 __global__ void pruned_box_kernel(const float* hot, int64_t N, int64_t nchunks, int D, int nch, int aux, int nb4,
-                                  float4* box) {
+                                  int cpts, float4* box) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nchunks) return;
     float lo[D_MAX], hi[D_MAX];
@@ -26,8 +26,8 @@ __global__ void pruned_box_kernel(const float* hot, int64_t N, int64_t nchunks, 
     }
     float ylo = __int_as_float(0x7f800000), yhv = -__int_as_float(0x7f800000);
     bool any = false;
-    for (int p = 0; p < 32; ++p) {
-        const int64_t pos = c * 32 + p;
+    for (int p = 0; p < cpts; ++p) {
+        const int64_t pos = c * cpts + p;
         if (pos >= N) break;
         const int64_t g = pos / GROUP, e = pos % GROUP;
         const float* base = hot + (g * nch) * GROUP + e;
@@ -96,18 +96,19 @@ PrunedKernelInfo scan_pruned_info(int norm, int C, int U, int variant) {
 int pruned_box_floats(int D) { return pruned_box_f4(D) * 4; }
 
 cudaError_t launch_chunk_records(const void* hot, int64_t N, int64_t nchunks, int D, int nch, bool aux, void* box,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, int cpts) {
     if (nchunks <= 0) return cudaSuccess;
     pruned_box_kernel<<<(unsigned)((nchunks + 127) / 128), 128, 0, st>>>(
-        static_cast<const float*>(hot), N, nchunks, D, nch, aux ? 1 : 0, pruned_box_f4(D), static_cast<float4*>(box));
+        static_cast<const float*>(hot), N, nchunks, D, nch, aux ? 1 : 0, pruned_box_f4(D), cpts,
+        static_cast<float4*>(box));
     return cudaGetLastError();
 }
 
 cudaError_t launch_pruned_boxes(const void* hot, int64_t N, int64_t nchunks, int D, int nch, bool aux, void* box,
                                 void* sbox, cudaStream_t st) {
-    cudaError_t e = launch_chunk_records(hot, N, nchunks, D, nch, aux, box, st);
+    cudaError_t e = launch_chunk_records(hot, N, nchunks, D, nch, aux, box, st, PRUNED_CG * GROUP);
     if (e != cudaSuccess) return e;
-    return launch_record_union(box, nchunks / 8, 8, D, sbox, st);
+    return launch_record_union(box, nchunks / PRUNED_CPS, PRUNED_CPS, D, sbox, st);
 }
 
 cudaError_t launch_record_union(const void* box, int64_t nsuper, int per, int D, void* sbox, cudaStream_t st) {

@@ -1,6 +1,6 @@
 // Exact scan with chunk bounds (lip_set_tuning variants 6 and 7): the same values and
-// extrema as scan_exact_kernel, over the data in spatial order, skipping every 32-point
-// chunk that provably cannot lower H_up nor raise H_lo of any query of the warp.
+// extrema as scan_exact_kernel, over the data in spatial order, skipping every 16-point
+// chunk that provably cannot lower H_up nor raise H_lo of any query of a row.
 //
 // The data are laid out in the spatial order of their points (a Hilbert order), so a
 // chunk's points are close together; each chunk carries its bounding box in the layout's
@@ -25,10 +25,9 @@
 // spatial order (one query per lane and row); it evaluates a chunk for each row in which
 // any query needs it (queries in spatial order make a row's needs coherent).
 //
-// Processing order: the block's queries (R per thread, in spatial order) pick a start
-// chunk, the one whose box centre is nearest their centroid, rounded down to a multiple
-// of 8 chunks (64 groups, so the order is the same for every tile size), and the sweep
-// wraps around from there; the near chunks tighten mu and ml first.  Among data with
+// Processing order: 64-group super-chunks (16 chunks, so the order is the same for every
+// tile size), nearest first from the centroid of the block's queries (below); with too
+// many super-chunks to sort, cyclically from the one whose box centre is nearest.  Among data with
 // exactly equal FP32 values the earliest in this order wins, which can differ from the
 // lowest index (the FP64 re-evaluation of the merge returns the chosen datum's exact
 // value either way).
@@ -201,7 +200,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
     constexpr int NCH = S::NCH;
     constexpr int NB4 = pruned_box_f4(D);
     constexpr int NW = SCAN_THREADS / 32;
-    // PRUNED_STAGES * tile_groups * NCH data, then PRUNED_STAGES * 8 chunk records
+    // PRUNED_STAGES * tile_groups * NCH data, then PRUNED_STAGES * RECS chunk records
+    constexpr int RECS = TILE_GROUPS_MAX / PRUNED_CG;
     extern __shared__ __align__(128) float4 tiles[];
     __shared__ __align__(8) uint64_t bars[PRUNED_STAGES];
     __shared__ int fin[PRUNED_STAGES];           // warps done with the stage's current tile
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
     float bd = __int_as_float(0x7f800000);
     int bk = 0x7fffffff;
     // (only for the cyclic order, taken when the super-chunks are too many to sort)
-    const int64_t nsearch = PP.nchunks / 8 <= PRUNED_SORT ? 0 : PP.nchunks;
+    const int64_t nsearch = PP.nchunks / PRUNED_CPS <= PRUNED_SORT ? 0 : PP.nchunks;
     for (int64_t k = tid; k < nsearch; k += SCAN_THREADS) {
         const float* b = reinterpret_cast<const float*>(PP.box + k * NB4);
         if (!(b[2 * D] == b[2 * D])) continue;             // a chunk without data
@@ -332,11 +332,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
         int k0 = red_k[0];
         for (int w = 1; w < NW; ++w)
             if (red_d[w] < d0 || (red_d[w] == d0 && red_k[w] < k0)) { d0 = red_d[w]; k0 = red_k[w]; }
-        start_chunk = k0 == 0x7fffffff ? 0 : (k0 / 8) * 8;   // a multiple of 64 groups
+        start_chunk = k0 == 0x7fffffff ? 0 : (k0 / PRUNED_CPS) * PRUNED_CPS;   // a multiple of 64 groups
     }
     __syncthreads();
 
-    // The sweep runs over super-chunks (8 chunks, 64 groups).  Up to PRUNED_SORT of them it
+    // The sweep runs over super-chunks (PRUNED_CPS chunks, 64 groups).  Up to PRUNED_SORT of them it
     // takes them nearest first: by the distance from the centre of their box to the
     // centroid of the block's queries (ties by index), sorted in shared memory by a bitonic
     // network, so the running extrema approach their final values within the first few
@@ -346,8 +346,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
     // some warp of the block may still need (tested against the running bounds, which only
     // tighten afterwards, so a super-chunk left out then would be skipped later too).  Only
     // the listed tiles are copied to shared memory.
-    const int nsuper = (int)(PP.nchunks / 8);
-    const int sup0 = start_chunk / 8;
+    const int nsuper = (int)(PP.nchunks / PRUNED_CPS);
+    const int sup0 = start_chunk / PRUNED_CPS;
     const bool sorted = nsuper <= PRUNED_SORT;
     __shared__ float skey[PRUNED_SORT];
     __shared__ short sidx[PRUNED_SORT];
@@ -403,14 +403,14 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
     __shared__ int seq_len;
     // the stages' copies of the tile's chunk records follow the data stages
     float4* recs = tiles + (size_t)PRUNED_STAGES * tg * NCH;
-    const uint32_t rec_bytes = (uint32_t)(tg / CHUNK_GROUPS) * NB4 * 16u;
+    const uint32_t rec_bytes = (uint32_t)(tg / PRUNED_CG) * NB4 * 16u;
     auto issue = [&](int step, int tile) {            // one thread: the bulk copies of ring step `step`
         if (step == P.skip_tile) return;
         const int st = step % PRUNED_STAGES;
         last_issued[st] = step;
         mbar_expect_tx(&bars[st], tile_bytes + rec_bytes);
         bulk_g2s(tiles + (size_t)st * tg * NCH, hot + (size_t)tile * tg * NCH, tile_bytes, &bars[st]);
-        bulk_g2s(recs + (size_t)st * 8 * NB4, PP.box + (size_t)tile * (tg / CHUNK_GROUPS) * NB4, rec_bytes, &bars[st]);
+        bulk_g2s(recs + (size_t)st * RECS * NB4, PP.box + (size_t)tile * (tg / PRUNED_CG) * NB4, rec_bytes, &bars[st]);
     };
     auto load_rec = [&](const float4* rec, float (&b)[NB4 * 4]) {     // from shared memory
 #pragma unroll
@@ -530,9 +530,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
                 break;
             }
             const float4* tile = tiles + (size_t)st * tg * NCH;
-            const float4* trec = recs + (size_t)st * 8 * NB4;
+            const float4* trec = recs + (size_t)st * RECS * NB4;
             const int64_t tg0 = (int64_t)seq[i] * tg;           // first group of the tile
-            const int chunk0 = (int)(tg0 / CHUNK_GROUPS), nck = tg / CHUNK_GROUPS;
+            const int chunk0 = (int)(tg0 / PRUNED_CG), nck = tg / PRUNED_CG;
             // lane k tests chunk k of the tile against the warp's query box and loosest
             // bounds; only the chunks that pass get the per-query test
             float mmax, mmin;
@@ -548,14 +548,14 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
             candidates += __popc(cands);
             for (unsigned left = cands; left; left &= left - 1) {
                 const int k = __ffs(left) - 1;
-                const int chunk = chunk0 + k, c = k * CHUNK_GROUPS;
+                const int chunk = chunk0 + k, c = k * PRUNED_CG;
                 float bx[NB4 * 4];
                 load_rec(trec + k * NB4, bx);
                 const unsigned rows = row_needs(bx);
                 if (!rows) continue;
                 evaluated += __popc(rows);
 #pragma unroll 2
-                for (int gi = 0; gi < CHUNK_GROUPS; ++gi) {
+                for (int gi = 0; gi < PRUNED_CG; ++gi) {
                     float4 x[NCH];
 #pragma unroll
                     for (int ch = 0; ch < NCH; ++ch) x[ch] = tile[(c + gi) * NCH + ch];
@@ -620,8 +620,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_pruned_kernel(const PrunedP
             const int chunk = side == 0 ? bu[r] : bl[r];
             if (chunk < 0) continue;
 #pragma unroll 1
-            for (int gi = 0; gi < CHUNK_GROUPS; ++gi) {
-                const int64_t g = (int64_t)chunk * CHUNK_GROUPS + gi;
+            for (int gi = 0; gi < PRUNED_CG; ++gi) {
+                const int64_t g = (int64_t)chunk * PRUNED_CG + gi;
                 float4 x[NCH];
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) x[ch] = __ldg(hot + g * NCH + ch);

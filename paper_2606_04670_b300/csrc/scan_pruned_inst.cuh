@@ -14,9 +14,10 @@ cudaError_t launch_scan_pruned(const PrunedParams& P, int gx, cudaStream_t st) {
     constexpr int NCH = ExactShape<NORM, C, U, true>::NCH;
     auto kern = scan_pruned_kernel<NORM, C, U, R>;
     constexpr int NB4 = pruned_box_f4(C + U);
-    const size_t smem = (size_t)PRUNED_STAGES * (P.S.tile_groups * NCH + 8 * NB4) * sizeof(float4);
+    constexpr int RECS = TILE_GROUPS_MAX / PRUNED_CG;        // chunk records a stage holds
+    const size_t smem = (size_t)PRUNED_STAGES * (P.S.tile_groups * NCH + RECS * NB4) * sizeof(float4);
     static cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   PRUNED_STAGES * (TILE_GROUPS_MAX * NCH + 8 * NB4) * (int)sizeof(float4));
+                                                   PRUNED_STAGES * (TILE_GROUPS_MAX * NCH + RECS * NB4) * (int)sizeof(float4));
     if (attr != cudaSuccess) return attr;
     kern<<<gx, SCAN_THREADS, smem, st>>>(P);
     return cudaGetLastError();

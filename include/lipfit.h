@@ -619,8 +619,9 @@ LIP_API lip_status lip_last_scan_work(lip_handle h, int64_t* evaluated, int64_t*
 LIP_API lip_status lip_last_scan_stats(lip_handle h, int64_t* out);
 
 /* After a pruned lip_estimate_M: out (host int64[3]) = the tile pairs that passed the tile
- * bound test, the (warp, chunk) pairs the screen evaluated (a warp holds 128 row points, a
- * chunk 32 column points), and the total (warp, chunk) pairs of the tile triangle; all -1
+ * bound test, the (row, chunk) pairs the screen evaluated (a row holds 32 consecutive
+ * points of the spatial order, a chunk 32 column points), and the total (row, chunk)
+ * pairs of the tile triangle; all -1
  * when the last estimate of this handle did not take the pruned form.  Reads what the
  * estimate (which synchronises) left on the host.  LIP_ERR_ARG for NULL. */
 LIP_API lip_status lip_last_estimate_work(lip_handle h, int64_t* out);

@@ -802,7 +802,7 @@ lip_status estimate_pruned(lip_model* h, double* res, cudaStream_t st) {
     memcpy(wk, back + 32, sizeof wk);
     h->est_work[0] = (int64_t)wk[0];
     h->est_work[1] = (int64_t)wk[1];
-    h->est_work[2] = npairs * (tile / 128) * (tile / 32);   // 128-row warps x 32-point chunks
+    h->est_work[2] = npairs * (tile / 32) * (tile / 32);    // 32-point rows x 32-point chunks
     return LIP_OK;
 }
 

@@ -15,8 +15,9 @@
 // margin).  The screen runs the tile pairs diagonal band first (neighbouring tiles in the
 // spatial order hold the close pairs, whose ratios are the large ones) and keeps the
 // largest q found so far in one device word (atomicMax of its bits): a block skips a tile
-// pair whose UB is below (1 - 2^-16) times it, a warp skips a chunk whose UB against the
-// box of its 128 row points is below (1 - 2^-16) times that or its own running maximum.
+// pair whose UB is below (1 - 2^-16) times it, and a warp skips a chunk for each of its
+// four rows of 32 points whose UB against the chunk is below (1 - 2^-16) times the larger
+// of that word and the warp's own running maximum.
 // Every pair with q >= q* (1 - 2^-16) -- the exact selection's threshold -- is therefore
 // evaluated, and each tile pair's largest evaluated q is recorded; the select kernel lists
 // the tile pairs whose record reaches the threshold.
@@ -122,77 +123,72 @@ __global__ void __launch_bounds__(EST_THREADS) estimate_pruned_kernel(const EstP
     const float4* src = P.lay + (size_t)J * EST_TILE_GROUPS * NCH;
     for (int k = tid; k < EST_TILE_GROUPS * NCH; k += EST_THREADS) tile[k] = __ldg(src + k);
     for (int k = tid; k < EP_CHUNKS * NB4; k += EST_THREADS) crec[k] = __ldg(P.cbox + (int64_t)J * EP_CHUNKS * NB4 + k);
-    // row points: a warp holds 128 consecutive positions (one group of 4 per lane)
+    // row points: row r of the warp is the 32 consecutive positions warp * 128 + 32 r + lane
+    // of tile I (one per lane), so that a row's points are neighbours in space
     float2 xi[EST_R][D];
     float2 yi[EST_R];
-    const int64_t g0 = (int64_t)I * EST_TILE_GROUPS + warp * 32 + lane;
     {
-        const float4* gp = P.lay + g0 * NCH;
-#pragma unroll
-        for (int j = 0; j <= D; ++j) {
-            const float4 v = __ldg(gp + j);
-            const float c[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int r = 0; r < EST_R; ++r) {
-                if (j < D) xi[r][j] = make_float2(c[r], c[r]);
-                else yi[r] = make_float2(c[r], c[r]);
-            }
-        }
-    }
-    // the warp's record of its row points (padding, y = NaN, drops out)
-    float W[NB4 * 4];
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-        float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
-#pragma unroll
-        for (int r = 0; r < EST_R; ++r)
-            if (yi[r].x == yi[r].x) {
-                lo = fminf(lo, xi[r][j].x);
-                hi = fmaxf(hi, xi[r][j].x);
-            }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-        }
-        W[j] = lo;
-        W[D + j] = hi;
-    }
-    {
-        float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
+        const float* layf = reinterpret_cast<const float*>(P.lay);
 #pragma unroll
         for (int r = 0; r < EST_R; ++r) {
-            lo = fminf(lo, yi[r].x);          // fminf / fmaxf ignore NaN
-            hi = fmaxf(hi, yi[r].x);
-        }
+            const int64_t p = (int64_t)I * EST_TILE + warp * 128 + 32 * r + lane;
+            const float* gp = layf + (p / GROUP) * NCH * GROUP + p % GROUP;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            for (int j = 0; j < D; ++j) {
+                const float v = __ldg(gp + j * GROUP);
+                xi[r][j] = make_float2(v, v);
+            }
+            const float v = __ldg(gp + D * GROUP);
+            yi[r] = make_float2(v, v);
         }
-        W[2 * D] = lo;
-        W[2 * D + 1] = hi;
+    }
+    // each row's record (padding, y = NaN, drops out), in shared memory for the tests
+    __shared__ __align__(16) float rrec[EST_THREADS / 32][EST_R][NB4 * 4];
+    unsigned rlive = 0u;                  // rows holding data
+#pragma unroll
+    for (int r = 0; r < EST_R; ++r) {
+        const bool live = yi[r].x == yi[r].x;
+        if (__any_sync(0xffffffffu, live)) rlive |= 1u << r;
+#pragma unroll
+        for (int j = 0; j <= D; ++j) {
+            const float v = j < D ? xi[r][j].x : yi[r].x;
+            float lo = live ? v : __int_as_float(0x7f800000), hi = live ? v : -__int_as_float(0x7f800000);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            if (lane == 0) {
+                rrec[warp][r][j < D ? j : 2 * D] = lo;
+                rrec[warp][r][j < D ? D + j : 2 * D + 1] = hi;
+            }
+        }
+        if (lane == 0)
+            for (int k = 2 * D + 2; k < NB4 * 4; ++k) rrec[warp][r][k] = 0.f;
     }
     if (P.work && tid == 0) atomicAdd(P.work, 1ull);     // tile pairs entered
-    bool live_row = false;
-#pragma unroll
-    for (int r = 0; r < EST_R; ++r) live_row = live_row || yi[r].x == yi[r].x;
-    const bool wlive = __any_sync(0xffffffffu, live_row);     // the warp holds data
     __syncthreads();
 
     float best = -1.f;                    // this thread's largest squared ratio
-    int nev = 0;                          // chunks this warp evaluated
+    int nev = 0;                          // (row, chunk) pairs this warp evaluated
     for (int c = 0; c < EP_CHUNKS; ++c) {
         // the warp's bound: the margin of the larger of its running maximum and L
         float wb = best;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wb = fmaxf(wb, __shfl_xor_sync(0xffffffffu, wb, o));
         const float lim = ep_margin(fmaxf(wb, L));
-        float B[NB4 * 4];
-        load_record<D>(crec + c * NB4, B);
-        const bool need = wlive && B[2 * D] == B[2 * D] && !(pair_ub<NORM, D, WT>(W, B, w1) < lim);
-        if (!__any_sync(0xffffffffu, need)) continue;
-        ++nev;
+        // lane r < EST_R tests row r's record against the chunk's
+        bool need = false;
+        if (lane < EST_R && ((rlive >> lane) & 1u)) {
+            float A[NB4 * 4], B[NB4 * 4];
+            load_record<D>(crec + c * NB4, B);
+#pragma unroll
+            for (int k = 0; k < NB4 * 4; ++k) A[k] = rrec[warp][lane][k];
+            need = B[2 * D] == B[2 * D] && !(pair_ub<NORM, D, WT>(A, B, w1) < lim);
+        }
+        const unsigned rows = __ballot_sync(0xffffffffu, need);
+        if (!rows) continue;
+        nev += __popc(rows);
 #pragma unroll 2
         for (int gi = 0; gi < CHUNK_GROUPS; ++gi) {
             const int g = c * CHUNK_GROUPS + gi;
@@ -201,6 +197,7 @@ __global__ void __launch_bounds__(EST_THREADS) estimate_pruned_kernel(const EstP
             for (int ch = 0; ch < NCH; ++ch) x[ch] = tile[g * NCH + ch];
 #pragma unroll
             for (int r = 0; r < EST_R; ++r) {
+                if (!((rows >> r) & 1u)) continue;         // warp-uniform
                 float q[4];
                 est_group<NORM, D, WT>(xi[r], yi[r], x, wt, q);
                 best = max3f(best, max3f(q[0], q[1], q[2]), q[3]);   // one link of the chain per group

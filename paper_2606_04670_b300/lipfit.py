@@ -755,7 +755,7 @@ class LipFit:
         _check(_lib.lip_check(self.h, _stream_ptr()), "lip_check")
 
     def last_estimate_work(self):
-        """[tile pairs entered, (warp, chunk) pairs evaluated, total (warp, chunk) pairs] of
+        """[tile pairs entered, (row, chunk) pairs evaluated, total (row, chunk) pairs] of
         the last pruned lip_estimate_M's screen; all -1 when it was not pruned."""
         out = (ctypes.c_int64 * 3)()
         _check(_lib.lip_last_estimate_work(self.h, out), "lip_last_estimate_work")

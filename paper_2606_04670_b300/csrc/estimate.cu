@@ -295,7 +295,7 @@ __global__ void estimate_final_kernel(const EstFinalParams P) {
 // 2 the smallest key among the pairs whose ratio is R*.  Data whose weighted coordinate
 // differences fall into FP32's subnormal range, or whose ratios overflow FP32, are
 // outside the bound.
-constexpr int EXACT_ROWS = 64;
+constexpr int EXACT_ROWS = 16;      // 32 items a tile pair, so a few listed pairs spread over many blocks
 constexpr int EXACT_THREADS = 256;
 
 template <typename T, int PASS>

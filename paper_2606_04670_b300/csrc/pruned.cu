@@ -11,75 +11,64 @@ PrunedKernelInfo scan_pruned_info_linf(int C, int U, int v);
 
 namespace {
 
-// One thread per `cpts`-point chunk of the layout `hot` (groups of 4 points, nch float4
-// channels: coordinates 0..D-1, y, then aux when `aux`): the box of its real points
-// (positions < N) in layout coordinates, the smallest y and the largest value of the
-// lower bound's channel (aux when present, else y).  A chunk without real points gets NaN.
+// One warp per `cpts`-point chunk (cpts <= 32) of the layout `hot` (groups of 4 points,
+// nch float4 channels: coordinates 0..D-1, y, then aux when `aux`), lane p reading point
+// p: the box of its real points (positions < N) in layout coordinates, the smallest y and
+// the largest value of the lower bound's channel (aux when present, else y).  A chunk
+// without real points gets NaN.
 __global__ void pruned_box_kernel(const float* hot, int64_t N, int64_t nchunks, int D, int nch, int aux, int nb4,
                                   int cpts, float4* box) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nchunks) return;
-    float lo[D_MAX], hi[D_MAX];
-    for (int j = 0; j < D; ++j) {
-        lo[j] = __int_as_float(0x7f800000);
-        hi[j] = -__int_as_float(0x7f800000);
-    }
-    float ylo = __int_as_float(0x7f800000), yhv = -__int_as_float(0x7f800000);
-    bool any = false;
-    for (int p = 0; p < cpts; ++p) {
-        const int64_t pos = c * cpts + p;
-        if (pos >= N) break;
-        const int64_t g = pos / GROUP, e = pos % GROUP;
-        const float* base = hot + (g * nch) * GROUP + e;
-        for (int j = 0; j < D; ++j) {
-            const float v = base[j * GROUP];
-            lo[j] = fminf(lo[j], v);
-            hi[j] = fmaxf(hi[j], v);
-        }
-        const float y = base[D * GROUP];
-        ylo = fminf(ylo, y);
-        yhv = fmaxf(yhv, aux ? base[(D + 1) * GROUP] : y);
-        any = true;
-    }
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (c >= nchunks) return;                      // whole warps leave together
+    const int64_t pos = c * cpts + lane;
+    const bool real = lane < cpts && pos < N;
+    const float* base = hot + ((pos / GROUP) * nch) * GROUP + pos % GROUP;
+    const float inf = __int_as_float(0x7f800000), nan = __int_as_float(0x7fc00000);
+    const bool any = __any_sync(0xffffffffu, real);
     float* out = reinterpret_cast<float*>(box + c * nb4);
-    const float nan = __int_as_float(0x7fc00000);
-    for (int j = 0; j < D; ++j) {
-        out[j] = any ? lo[j] : nan;
-        out[D + j] = any ? hi[j] : nan;
+    for (int k = 0; k < 2 * D + 2; ++k) {
+        // lo (k < D) and ylo (k = 2D) fold by min from the coordinate / y channel, hi and
+        // the value maximum by max from the coordinate / lower-bound channel
+        const bool is_min = k < D || k == 2 * D;
+        const int ch = k < D ? k : (k < 2 * D ? k - D : (k == 2 * D ? D : (aux ? D + 1 : D)));
+        float v = real ? base[ch * GROUP] : (is_min ? inf : -inf);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = is_min ? fminf(v, w) : fmaxf(v, w);
+        }
+        if (lane == 0) out[k] = any ? v : nan;
     }
-    out[2 * D] = any ? ylo : nan;
-    out[2 * D + 1] = any ? yhv : nan;
-    for (int k = 2 * D + 2; k < nb4 * 4; ++k) out[k] = 0.f;
+    if (lane == 0)
+        for (int k = 2 * D + 2; k < nb4 * 4; ++k) out[k] = 0.f;
 }
 
-// One thread per `per` consecutive chunks: the union of their records (chunks without
-// data, NaN, drop out of the min / max; all empty gives NaN).
+// One warp per `per` consecutive chunks (per <= 32): lane c reads chunk c's record and
+// the lanes fold the union (chunks without data, NaN, drop out of the min / max; all
+// empty gives NaN).
 __global__ void pruned_super_kernel(const float4* box, int64_t nsuper, int per, int D, int nb4, float4* sbox) {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nsuper) return;
-    float* out = reinterpret_cast<float*>(sbox + s * nb4);
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (s >= nsuper) return;                       // whole warps leave together
     const float inf = __int_as_float(0x7f800000), nan = __int_as_float(0x7fc00000);
-    for (int j = 0; j < D; ++j) {
-        out[j] = inf;
-        out[D + j] = -inf;
-    }
-    out[2 * D] = inf;
-    out[2 * D + 1] = -inf;
-    bool any = false;
-    for (int c = 0; c < per; ++c) {
-        const float* b = reinterpret_cast<const float*>(box + (s * per + c) * nb4);
-        if (!(b[2 * D] == b[2 * D])) continue;
-        any = true;
-        for (int j = 0; j < D; ++j) {
-            out[j] = fminf(out[j], b[j]);
-            out[D + j] = fmaxf(out[D + j], b[D + j]);
+    const float* b = reinterpret_cast<const float*>(box + (s * per + lane) * nb4);
+    const bool has = lane < per && b[2 * D] == b[2 * D];
+    const bool any = __any_sync(0xffffffffu, has);
+    float* out = reinterpret_cast<float*>(sbox + s * nb4);
+    for (int k = 0; k < 2 * D + 2; ++k) {
+        // lo (k < D) and ylo (k = 2D) fold by min, hi and the value maximum by max
+        const bool is_min = k < D || k == 2 * D;
+        float v = has ? b[k] : (is_min ? inf : -inf);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = is_min ? fminf(v, w) : fmaxf(v, w);
         }
-        out[2 * D] = fminf(out[2 * D], b[2 * D]);
-        out[2 * D + 1] = fmaxf(out[2 * D + 1], b[2 * D + 1]);
+        if (lane == 0) out[k] = any ? v : nan;
     }
-    if (!any)
-        for (int k = 0; k < 2 * D + 2; ++k) out[k] = nan;
-    for (int k = 2 * D + 2; k < nb4 * 4; ++k) out[k] = 0.f;
+    if (lane == 0)
+        for (int k = 2 * D + 2; k < nb4 * 4; ++k) out[k] = 0.f;
 }
 
 }  // namespace
@@ -98,7 +87,8 @@ int pruned_box_floats(int D) { return pruned_box_f4(D) * 4; }
 cudaError_t launch_chunk_records(const void* hot, int64_t N, int64_t nchunks, int D, int nch, bool aux, void* box,
                                  cudaStream_t st, int cpts) {
     if (nchunks <= 0) return cudaSuccess;
-    pruned_box_kernel<<<(unsigned)((nchunks + 127) / 128), 128, 0, st>>>(
+    if (cpts < 1 || cpts > 32) return cudaErrorInvalidValue;
+    pruned_box_kernel<<<(unsigned)((nchunks * 32 + 127) / 128), 128, 0, st>>>(
         static_cast<const float*>(hot), N, nchunks, D, nch, aux ? 1 : 0, pruned_box_f4(D), cpts,
         static_cast<float4*>(box));
     return cudaGetLastError();
@@ -113,9 +103,10 @@ cudaError_t launch_pruned_boxes(const void* hot, int64_t N, int64_t nchunks, int
 
 cudaError_t launch_record_union(const void* box, int64_t nsuper, int per, int D, void* sbox, cudaStream_t st) {
     if (nsuper <= 0) return cudaSuccess;
-    pruned_super_kernel<<<(unsigned)((nsuper + 127) / 128), 128, 0, st>>>(static_cast<const float4*>(box), nsuper, per,
-                                                                          D, pruned_box_f4(D),
-                                                                          static_cast<float4*>(sbox));
+    if (per < 1 || per > 32) return cudaErrorInvalidValue;
+    pruned_super_kernel<<<(unsigned)((nsuper * 32 + 127) / 128), 128, 0, st>>>(static_cast<const float4*>(box), nsuper,
+                                                                               per, D, pruned_box_f4(D),
+                                                                               static_cast<float4*>(sbox));
     return cudaGetLastError();
 }
 

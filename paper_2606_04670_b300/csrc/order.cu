@@ -13,8 +13,9 @@ namespace {
 
 constexpr int ORD_THREADS = 256;                    // threads per block in the radix passes
 constexpr int ORD_WARPS = ORD_THREADS / 32;
-constexpr int ORD_SUB = 16;                         // 256-key sub-tiles per block, in index order
-constexpr int ORD_TILE = ORD_THREADS * ORD_SUB;     // keys per block
+constexpr int ORD_SUB = 16;                         // most 256-key sub-tiles per block, in index order
+constexpr int ORD_TILE = ORD_THREADS * ORD_SUB;     // most keys per block
+constexpr int ORD_NB_TARGET = 64;                   // blocks wanted before sub-tiles grow past 1
 constexpr int ORD_BINS = 256;
 constexpr int ORD_BOX_BLOCKS = 296;                 // grid of the bounding-box pass (2 per SM)
 constexpr int ORD_SCAN_THREADS = 1024;              // the one-block scan, 4 entries per thread
@@ -81,14 +82,19 @@ __global__ void ord_key_kernel(const float* X, int64_t n, int d, const unsigned*
     const int D = d < 16 ? d : 16;
     const int b = 16 / D;                          // bits per coordinate
     const int cells = 1 << b;
+    // the loops over the coordinates are unrolled to 16 with a guard, so that cell[] stays
+    // in registers (its indices are compile-time constants)
     int cell[16];
-    for (int j = 0; j < D; ++j) {
-        const float lo = ord_key_float(box[j]), hi = ord_key_float(box[D_MAX + j]);
-        const float v = X[i * d + j];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
         int c = 0;
-        if (isfinite(v) && hi > lo) {
-            const float u = (v - lo) / (hi - lo) * (float)cells;
-            c = u >= (float)(cells - 1) ? cells - 1 : (u > 0.f ? (int)u : 0);
+        if (j < D) {
+            const float lo = ord_key_float(box[j]), hi = ord_key_float(box[D_MAX + j]);
+            const float v = X[i * d + j];
+            if (isfinite(v) && hi > lo) {
+                const float u = (v - lo) / (hi - lo) * (float)cells;
+                c = u >= (float)(cells - 1) ? cells - 1 : (u > 0.f ? (int)u : 0);
+            }
         }
         cell[j] = c;
     }
@@ -96,7 +102,9 @@ __global__ void ord_key_kernel(const float* X, int64_t n, int d, const unsigned*
         const int top = 1 << (b - 1);
         for (int q = top; q > 1; q >>= 1) {
             const int p = q - 1;
-            for (int j = 0; j < D; ++j) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                if (j >= D) break;
                 if (cell[j] & q) {
                     cell[0] ^= p;                               // invert the low bits
                 } else {
@@ -106,30 +114,40 @@ __global__ void ord_key_kernel(const float* X, int64_t n, int d, const unsigned*
                 }
             }
         }
-        for (int j = 1; j < D; ++j) cell[j] ^= cell[j - 1];   // Gray code
+#pragma unroll
+        for (int j = 1; j < 16; ++j)
+            if (j < D) cell[j] ^= cell[j - 1];                 // Gray code
+        int last = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j == D - 1) last = cell[j];
         int t = 0;
         for (int q = top; q > 1; q >>= 1)
-            if (cell[D - 1] & q) t ^= q - 1;
-        for (int j = 0; j < D; ++j) cell[j] ^= t;
+            if (last & q) t ^= q - 1;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < D) cell[j] ^= t;
     }
     unsigned key = 0u;
     for (int l = b - 1; l >= 0; --l)
-        for (int j = 0; j < D; ++j) key = (key << 1) | (unsigned)((cell[j] >> l) & 1);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < D) key = (key << 1) | (unsigned)((cell[j] >> l) & 1);
     keys[i] = key;
     idx[i] = (int)i;
 }
 
-// Digit counts per block of ORD_TILE keys, stored digit-major: table[digit * nblocks +
+// Digit counts per block of sub x 256 keys, stored digit-major: table[digit * nblocks +
 // block].  Lanes with equal digits add once per warp (their leader adds the group's size).
 __global__ void __launch_bounds__(ORD_THREADS) ord_hist_kernel(const unsigned* keys, int64_t n, int shift,
-                                                              int* table, int nblocks) {
+                                                              int* table, int nblocks, int sub) {
     __shared__ int cnt[ORD_BINS + 1];
     cnt[threadIdx.x] = 0;
     if (threadIdx.x == 0) cnt[ORD_BINS] = 0;
     __syncthreads();
     const int lane = threadIdx.x % 32;
-    const int64_t base = (int64_t)blockIdx.x * ORD_TILE;
-    for (int s = 0; s < ORD_SUB; ++s) {
+    const int64_t base = (int64_t)blockIdx.x * sub * ORD_THREADS;
+    for (int s = 0; s < sub; ++s) {
         const int64_t i = base + (int64_t)s * ORD_THREADS + threadIdx.x;
         const int digit = i < n ? (int)((keys[i] >> shift) & 0xffu) : ORD_BINS;
         const unsigned peers = __match_any_sync(0xffffffffu, digit);
@@ -140,18 +158,24 @@ __global__ void __launch_bounds__(ORD_THREADS) ord_hist_kernel(const unsigned* k
 }
 
 // Exclusive prefix sums of the table in place (one block; total is a multiple of 4).  The
-// block walks the table in chunks of 4096 entries: each thread loads 4 consecutive entries
-// as one int4, the threads' sums are scanned by warp shuffles and then across the warps,
-// and a running carry links the chunks.
+// block walks the table in chunks of 16384 entries: each thread loads 16 consecutive
+// entries as four int4, the threads' sums are scanned by warp shuffles and then across the
+// warps, and a running carry links the chunks.
+constexpr int ORD_SCAN_PER = 16;                    // entries a thread takes per chunk
 __global__ void __launch_bounds__(ORD_SCAN_THREADS) ord_scan_kernel(int* table, int64_t total) {
     __shared__ int wsum[ORD_SCAN_THREADS / 32];
     const int t = threadIdx.x, lane = t % 32, warp = t / 32;
     int carry = 0;
-    for (int64_t c = 0; c < total; c += 4 * ORD_SCAN_THREADS) {
-        const int64_t i = c + 4 * (int64_t)t;
-        int4 v = make_int4(0, 0, 0, 0);
-        if (i < total) v = *reinterpret_cast<const int4*>(table + i);
-        const int own = v.x + v.y + v.z + v.w;
+    for (int64_t c = 0; c < total; c += ORD_SCAN_PER * ORD_SCAN_THREADS) {
+        const int64_t i = c + ORD_SCAN_PER * (int64_t)t;
+        int4 v[ORD_SCAN_PER / 4];
+        int own = 0;
+#pragma unroll
+        for (int k = 0; k < ORD_SCAN_PER / 4; ++k) {
+            v[k] = make_int4(0, 0, 0, 0);
+            if (i + 4 * k < total) v[k] = *reinterpret_cast<const int4*>(table + i + 4 * k);
+            own += v[k].x + v[k].y + v[k].z + v[k].w;
+        }
         int x = own;                               // inclusive scan over the warp
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -169,16 +193,20 @@ __global__ void __launch_bounds__(ORD_SCAN_THREADS) ord_scan_kernel(int* table, 
         }
         __syncthreads();
         int run = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - own;
-        if (i < total) {
-            int4 o;
-            o.x = run;
-            run += v.x;
-            o.y = run;
-            run += v.y;
-            o.z = run;
-            run += v.z;
-            o.w = run;
-            *reinterpret_cast<int4*>(table + i) = o;
+#pragma unroll
+        for (int k = 0; k < ORD_SCAN_PER / 4; ++k) {
+            if (i + 4 * k < total) {
+                int4 o;
+                o.x = run;
+                run += v[k].x;
+                o.y = run;
+                run += v[k].y;
+                o.z = run;
+                run += v[k].z;
+                o.w = run;
+                run += v[k].w;
+                *reinterpret_cast<int4*>(table + i + 4 * k) = o;
+            }
         }
         carry += wsum[ORD_SCAN_THREADS / 32 - 1];
         __syncthreads();                           // wsum is rewritten by the next chunk
@@ -189,15 +217,15 @@ __global__ void __launch_bounds__(ORD_SCAN_THREADS) ord_scan_kernel(int* table, 
 // start of the digit in this block (from the scanned table, advanced by each sub-tile's
 // counts) + count of the digit in earlier warps of the sub-tile + count among earlier lanes.
 __global__ void __launch_bounds__(ORD_THREADS) ord_scatter_kernel(const unsigned* keys, const int* idx, int64_t n,
-                                                                 int shift, const int* table, int nblocks,
+                                                                 int shift, const int* table, int nblocks, int sub,
                                                                  unsigned* keys_out, int* idx_out) {
     __shared__ int wc[ORD_WARPS][ORD_BINS + 1];    // column ORD_BINS: lanes past the end
     __shared__ int run[ORD_BINS];
     const int t = threadIdx.x, warp = t / 32, lane = t % 32;
     for (int k = t; k < ORD_WARPS * (ORD_BINS + 1); k += ORD_THREADS) (&wc[0][0])[k] = 0;
     run[t] = table[(int64_t)t * nblocks + blockIdx.x];
-    const int64_t base = (int64_t)blockIdx.x * ORD_TILE;
-    for (int s = 0; s < ORD_SUB; ++s) {
+    const int64_t base = (int64_t)blockIdx.x * sub * ORD_THREADS;
+    for (int s = 0; s < sub; ++s) {
         const int64_t first = base + (int64_t)s * ORD_THREADS;
         if (first >= n) break;                     // uniform over the block
         __syncthreads();                           // wc cleared, run advanced
@@ -229,10 +257,18 @@ __global__ void __launch_bounds__(ORD_THREADS) ord_scatter_kernel(const unsigned
 
 size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// 256-key sub-tiles per block: as few as keep about ORD_NB_TARGET blocks busy (more
+// blocks, shorter serial loops), at most ORD_SUB (a bounded digit table to scan).
+int ord_sub(int64_t n) {
+    const int64_t s = (n + (int64_t)ORD_NB_TARGET * ORD_THREADS - 1) / ((int64_t)ORD_NB_TARGET * ORD_THREADS);
+    return (int)(s < 1 ? 1 : (s > ORD_SUB ? ORD_SUB : s));
+}
+
 }  // namespace
 
 size_t spatial_order_scratch(int64_t n) {
-    const int64_t nb = (n + ORD_TILE - 1) / ORD_TILE;
+    const int64_t tile = (int64_t)ord_sub(n) * ORD_THREADS;
+    const int64_t nb = (n + tile - 1) / tile;
     return al256(2 * D_MAX * sizeof(unsigned)) + 2 * al256((size_t)n * sizeof(unsigned)) +
            al256((size_t)n * sizeof(int)) + al256((size_t)nb * ORD_BINS * sizeof(int));
 }
@@ -241,7 +277,8 @@ cudaError_t spatial_order(const float* X, int64_t n, int d, int* perm, float2* b
                           cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     if (d < 1 || d > D_MAX) return cudaErrorInvalidValue;
-    const int nb = (int)((n + ORD_TILE - 1) / ORD_TILE);
+    const int sub = ord_sub(n);
+    const int nb = (int)((n + (int64_t)sub * ORD_THREADS - 1) / ((int64_t)sub * ORD_THREADS));
     char* s = static_cast<char*>(scratch);
     unsigned* box = reinterpret_cast<unsigned*>(s);
     unsigned* ka = reinterpret_cast<unsigned*>(s + al256(2 * D_MAX * sizeof(unsigned)));
@@ -260,12 +297,12 @@ cudaError_t spatial_order(const float* X, int64_t n, int d, int* perm, float2* b
     // pass 1: low byte (ka, perm) -> (kb, ia); pass 2: high byte (kb, ia) -> (ka, perm)
     const unsigned blocks = (unsigned)nb;
     const int64_t entries = (int64_t)nb * ORD_BINS;
-    ord_hist_kernel<<<blocks, ORD_THREADS, 0, st>>>(ka, n, 0, table, nb);
+    ord_hist_kernel<<<blocks, ORD_THREADS, 0, st>>>(ka, n, 0, table, nb, sub);
     ord_scan_kernel<<<1, ORD_SCAN_THREADS, 0, st>>>(table, entries);
-    ord_scatter_kernel<<<blocks, ORD_THREADS, 0, st>>>(ka, perm, n, 0, table, nb, kb, ia);
-    ord_hist_kernel<<<blocks, ORD_THREADS, 0, st>>>(kb, n, 8, table, nb);
+    ord_scatter_kernel<<<blocks, ORD_THREADS, 0, st>>>(ka, perm, n, 0, table, nb, sub, kb, ia);
+    ord_hist_kernel<<<blocks, ORD_THREADS, 0, st>>>(kb, n, 8, table, nb, sub);
     ord_scan_kernel<<<1, ORD_SCAN_THREADS, 0, st>>>(table, entries);
-    ord_scatter_kernel<<<blocks, ORD_THREADS, 0, st>>>(kb, ia, n, 8, table, nb, ka, perm);
+    ord_scatter_kernel<<<blocks, ORD_THREADS, 0, st>>>(kb, ia, n, 8, table, nb, sub, ka, perm);
     return cudaGetLastError();
 }
 

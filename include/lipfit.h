@@ -233,7 +233,7 @@ LIP_API lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, i
  * N >= 32768 take the pruned form (below that the full screen is cheaper than the pruned
  * form's setup); 2: the pruned form wherever available (FP32, d <= 8); 1: always the full
  * kernel.  The pruned form puts the data in spatial order with a box and y range per
- * 32-point chunk and per 512-point tile, and its FP32 screen skips the tile pairs and
+ * 16-point chunk and per 512-point tile, and its FP32 screen skips the tile pairs and
  * chunks whose exact FP32 upper bound (box gaps with the pair arithmetic's own operations,
  * rcp.approx with a 2^-18 margin) is below (1 - 2^-16) times the largest value already
  * found.  Other handles, and lip_estimate_M_part, screen all pairs.  Both forms are
@@ -620,7 +620,7 @@ LIP_API lip_status lip_last_scan_stats(lip_handle h, int64_t* out);
 
 /* After a pruned lip_estimate_M: out (host int64[3]) = the tile pairs that passed the tile
  * bound test, the (row, chunk) pairs the screen evaluated (a row holds 32 consecutive
- * points of the spatial order, a chunk 32 column points), and the total (row, chunk)
+ * points of the spatial order, a chunk 16 column points), and the total (row, chunk)
  * pairs of the tile triangle; all -1
  * when the last estimate of this handle did not take the pruned form.  Reads what the
  * estimate (which synchronises) left on the host.  LIP_ERR_ARG for NULL. */

@@ -706,7 +706,7 @@ lip_status eval_screen64(lip_model* h, const void* Q, int64_t nq, void* g, void*
 // the FP64 definition's result exactly.
 lip_status estimate_pruned(lip_model* h, double* res, cudaStream_t st) {
     const int tile = estimate_tile_points();
-    const int64_t N = h->N, nb = ceil_div(N, tile), pts = nb * tile, nchunks = pts / 32;
+    const int64_t N = h->N, nb = ceil_div(N, tile), pts = nb * tile, nchunks = pts / 16;   // 16-point chunks
     const int64_t npairs = nb * (nb + 1) / 2;
     const int d = h->d, nch = d + 1;
     const size_t rec = (size_t)pruned_box_f4(d) * 16;
@@ -757,10 +757,10 @@ lip_status estimate_pruned(lip_model* h, double* res, cudaStream_t st) {
     Hp.gather = perm;
     CUDA_TRY(launch_estimate_layout(4, Hp, st));
     CUDA_TRY(launch_pad_hot(4, lay, N, pts, nch, d, st));
-    CUDA_TRY(launch_chunk_records(lay, N, nchunks, d, nch, false, cbox, st));
-    CUDA_TRY(launch_record_union(cbox, nb, tile / 32, d, tbox, st));
+    CUDA_TRY(launch_chunk_records(lay, N, nchunks, d, nch, false, cbox, st, 16));
+    CUDA_TRY(launch_record_union(cbox, nb, tile / 16, d, tbox, st));
+    CUDA_TRY(cudaMemsetAsync(small, 0, small_b, st));          // the selection's words, out, work
     CUDA_TRY(cudaMemsetAsync(gbest, 0xff, 4, st));             // no value yet
-    CUDA_TRY(cudaMemsetAsync(work, 0, 16, st));
     EstPrunedParams P;
     P.lay = static_cast<const float4*>(lay);
     P.N = N;
@@ -802,7 +802,7 @@ lip_status estimate_pruned(lip_model* h, double* res, cudaStream_t st) {
     memcpy(wk, back + 32, sizeof wk);
     h->est_work[0] = (int64_t)wk[0];
     h->est_work[1] = (int64_t)wk[1];
-    h->est_work[2] = npairs * (tile / 32) * (tile / 32);    // 32-point rows x 32-point chunks
+    h->est_work[2] = npairs * (tile / 32) * (tile / 16);    // 32-point rows x 16-point chunks
     return LIP_OK;
 }
 

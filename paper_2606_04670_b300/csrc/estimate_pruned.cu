@@ -4,7 +4,7 @@
 // definition's exactly (the value, then the lowest i, then the lowest j).
 //
 // The estimate layout is built in the spatial order of the points, with a record (box of
-// the points in layout coordinates, smallest and largest y) per 32-point chunk and per
+// the points in layout coordinates, smallest and largest y) per 16-point chunk and per
 // 512-point tile.  For two records A and B, every pair (i in A, j in B) has
 //   |y_i - y_j| <= max(yhi_A - ylo_B, yhi_B - ylo_A)           (IEEE rounding is monotone)
 //   FP32 dist^2 >= the same FP32 operations on the gaps between the boxes
@@ -27,7 +27,8 @@ namespace lip {
 
 namespace {
 
-constexpr int EP_CHUNKS = EST_TILE_GROUPS / CHUNK_GROUPS;      // 16 chunks per tile
+constexpr int EP_CG = 4;                                   // groups per chunk: 16-point chunks
+constexpr int EP_CHUNKS = EST_TILE_GROUPS / EP_CG;         // 32 chunks per tile
 
 // Record layout: lo[D], hi[D], ylo, yhi (the same as the pruned scan's, aux-free).  With
 // WT the gaps are multiplied by the weights as the pair arithmetic multiplies the
@@ -190,8 +191,8 @@ __global__ void __launch_bounds__(EST_THREADS) estimate_pruned_kernel(const EstP
         if (!rows) continue;
         nev += __popc(rows);
 #pragma unroll 2
-        for (int gi = 0; gi < CHUNK_GROUPS; ++gi) {
-            const int g = c * CHUNK_GROUPS + gi;
+        for (int gi = 0; gi < EP_CG; ++gi) {
+            const int g = c * EP_CG + gi;
             float4 x[NCH];
 #pragma unroll
             for (int ch = 0; ch < NCH; ++ch) x[ch] = tile[g * NCH + ch];

@@ -63,9 +63,9 @@ TC_I_EPI = 6
 # entry is removed whenever its kernel changes, until it is captured again.
 KERNEL_DRAM_BYTES = {
     ("monotone_d4", 2): 19.136000e6 + 11.619840e6,     # scan_exact_kernel<L2, C=2, U=2, R=4>
-    ("monotone_d4", 1, "pruned"): 23.158e6 + 0.369e6,  # scan_pruned_kernel<L1, C=2, U=2, R=4>
-    ("monotone_d4", 2, "pruned"): 24.801e6 + 1.908e6,  # scan_pruned_kernel<L2, C=2, U=2, R=4>
-    ("monotone_d4", 3, "pruned"): 24.914e6 + 2.100e6,  # scan_pruned_kernel<Linf, C=2, U=2, R=4>
+    ("monotone_d4", 1, "pruned"): 23.162e6 + 0.374e6,  # scan_pruned_kernel<L1, C=2, U=2, R=4>
+    ("monotone_d4", 2, "pruned"): 24.757e6 + 1.910e6,  # scan_pruned_kernel<L2, C=2, U=2, R=4>
+    ("monotone_d4", 3, "pruned"): 24.953e6 + 2.098e6,  # scan_pruned_kernel<Linf, C=2, U=2, R=4>
     ("grad_d8", 2): 16.66e6 + 13.47e6,                 # scan_exact_kernel<L2, C=4, U=4, R=2>
     ("cluster_d16", 2): 618.02e6 + 185.20e6,           # scan_exact_kernel<L2, C=0, U=16, R=2>
     ("cluster_d16_tc", 2): 7185.37e6 + 1213.84e6,      # tc_scan_kernel<K=16, 4 parts, TF32> (persistent, soft lockstep)

@@ -1,5 +1,5 @@
 """The pruned scan (lip_set_tuning variants 6 and 7): the data in spatial order with a
-bounding box and value range per 32-point chunk, chunks skipped when their exact FP32 bound
+bounding box and value range per 16-point chunk, chunks skipped when their exact FP32 bound
 shows they cannot change any query's extrema.  Against the FP64 oracle on every norm and
 shape up to d = 8 (monotone, decreasing, weighted), ragged sizes, edge cases, tile sizes
 (bit for bit), incremental data, and the benchmark workload at full size on sampled
@@ -124,7 +124,7 @@ def test_pruned_duplicates_and_constant_y(oracle_mod):
 def test_pruned_full_size_benchmark_workload(oracle_mod):
     """The benchmark workload (N = 1e5, Q = 1e6, monotone d = 4) at full size, all three
     norms, on 1,000 sampled queries per norm, plus lo <= g <= hi everywhere; the scan
-    evaluates a small share of the (warp, chunk) pairs."""
+    evaluates a small share of the (row, chunk) pairs."""
     from paper_2606_04670_b300.lipfit import LipFit
     rng = np.random.default_rng(5)
     for norm in (1, 2, 3):
@@ -133,9 +133,13 @@ def test_pruned_full_size_benchmark_workload(oracle_mod):
         m.set_tuning(0, 0, 6)
         r = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
         ev, tot = m.last_scan_work()
+        st = m.last_scan_stats()
         m.check()
         m.close()
         assert 0 < ev < 0.5 * tot, (norm, ev, tot)
+        # the same counts, the tiles copied out of blocks x tiles, and the (warp, chunk)
+        # pairs past the warp-box test: at most 16 chunks a tile, 4 warps a block
+        assert st[:2] == [ev, tot] and 0 < st[2] <= st[3] and 0 < st[4] <= 16 * 4 * st[2], st
         assert np.all(r["lo"] <= r["g"]) and np.all(r["g"] <= r["hi"])
         idx = np.sort(rng.choice(p.nq, 1_000, replace=False))
         ps = W.Problem("s", p.X, p.y, p.Q[idx], p.M, norm, p.mon, None)
@@ -154,6 +158,7 @@ def test_pruned_autotune_and_tuning_report():
     m.set_tuning(0, 0, 1)
     m.eval(torch.as_tensor(p.Q).cuda())
     assert m.last_scan_work() == (-1, -1)
+    assert m.last_scan_stats() == [-1, -1, -1, -1, -1]
     assert L.lip_set_tuning(m.h, 0, 0, 8) == L.LIP_ERR_ARG
     m.close()
     # d = 9 has no pruned instantiation: 6 / 7 run as 0 / 1

@@ -16,8 +16,8 @@
 // spatial order hold the close pairs, whose ratios are the large ones) and keeps the
 // largest q found so far in one device word (atomicMax of its bits): a block skips a tile
 // pair whose UB is below (1 - 2^-16) times it, and a warp skips a chunk for each of its
-// four rows of 32 points whose UB against the chunk is below (1 - 2^-16) times the larger
-// of that word and the warp's own running maximum.
+// four rows of 32 points whose UB against the chunk is below (1 - 2^-16) times that word
+// (all (row, chunk) pairs of the tile pair tested at once, one chunk per lane).
 // Every pair with q >= q* (1 - 2^-16) -- the exact selection's threshold -- is therefore
 // evaluated, and each tile pair's largest evaluated q is recorded; the select kernel lists
 // the tile pairs whose record reaches the threshold.
@@ -172,23 +172,36 @@ __global__ void __launch_bounds__(EST_THREADS) estimate_pruned_kernel(const EstP
 
     float best = -1.f;                    // this thread's largest squared ratio
     int nev = 0;                          // (row, chunk) pairs this warp evaluated
-    for (int c = 0; c < EP_CHUNKS; ++c) {
-        // the warp's bound: the margin of the larger of its running maximum and L
-        float wb = best;
+    // Every (row, chunk) pair of the tile pair is tested at once, against the margin of the
+    // latest global maximum: lane c takes chunk c, one round per row (bit c of cm[r]).
+    static_assert(EP_CHUNKS == 32, "one chunk per lane");
+    unsigned cm[EST_R];
+    {
+        const int gn = *reinterpret_cast<const volatile int*>(P.gbest);
+        const float lim = ep_margin(fmaxf(L, gn >= 0 ? __int_as_float(gn) : -1.f));
+        float B[NB4 * 4];
+        load_record<D>(crec + lane * NB4, B);
+        const bool cvalid = B[2 * D] == B[2 * D];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wb = fmaxf(wb, __shfl_xor_sync(0xffffffffu, wb, o));
-        const float lim = ep_margin(fmaxf(wb, L));
-        // lane r < EST_R tests row r's record against the chunk's
-        bool need = false;
-        if (lane < EST_R && ((rlive >> lane) & 1u)) {
-            float A[NB4 * 4], B[NB4 * 4];
-            load_record<D>(crec + c * NB4, B);
+        for (int r = 0; r < EST_R; ++r) {
+            bool need = false;
+            if (cvalid && ((rlive >> r) & 1u)) {
+                float A[NB4 * 4];
 #pragma unroll
-            for (int k = 0; k < NB4 * 4; ++k) A[k] = rrec[warp][lane][k];
-            need = B[2 * D] == B[2 * D] && !(pair_ub<NORM, D, WT>(A, B, w1) < lim);
+                for (int k = 0; k < NB4 * 4; ++k) A[k] = rrec[warp][r][k];
+                need = !(pair_ub<NORM, D, WT>(A, B, w1) < lim);
+            }
+            cm[r] = __ballot_sync(0xffffffffu, need);
         }
-        const unsigned rows = __ballot_sync(0xffffffffu, need);
-        if (!rows) continue;
+    }
+    unsigned any = 0u;
+#pragma unroll
+    for (int r = 0; r < EST_R; ++r) any |= cm[r];
+    for (unsigned left = any; left; left &= left - 1) {
+        const int c = __ffs(left) - 1;
+        unsigned rows = 0u;
+#pragma unroll
+        for (int r = 0; r < EST_R; ++r) rows |= ((cm[r] >> c) & 1u) << r;
         nev += __popc(rows);
 #pragma unroll 2
         for (int gi = 0; gi < EP_CG; ++gi) {

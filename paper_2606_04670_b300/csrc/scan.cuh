@@ -463,14 +463,34 @@ struct MergeParams {
     int32_t *idx_up, *idx_lo;
 };
 
+// A float widened to double exactly from its IEEE-754 fields on the integer pipe
+// (normal: exponent rebias by 1023 - 127 and the mantissa moved up 29 bits; subnormal:
+// normalised from its leading bit; zeros, infinities and NaN kept), which leaves the
+// FP64 pipe, the merge's bound, to the arithmetic.  to_f64 of a double is itself.
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned long long s = (unsigned long long)(u >> 31) << 63;
+    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned long long bits;
+    if (e == 0xffu) bits = s | (0x7ffull << 52) | ((unsigned long long)m << 29);
+    else if (e != 0u) bits = s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+    else if (m == 0u) bits = s;
+    else {
+        const int p = 31 - __clz((int)m);                 // the leading bit, 0..22
+        bits = s | ((unsigned long long)(p + 874) << 52) | (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull);
+    }
+    return __longlong_as_double((long long)bits);
+}
+
 // dist_up (side > 0) or dist_lo (side < 0) in FP64 in the caller's coordinates.
 template <typename T>
 __device__ __forceinline__ double dist_fp64(const MergeParams& P, const T* q, const T* x, int side) {
     double acc = 0.0;
     for (int i = 0; i < P.d; ++i) {
-        double t = (double)q[i] - (double)x[i];
+        double t = to_f64(q[i]) - to_f64(x[i]);
         if (P.mon[i] < 0) t = -t;
-        t *= P.w[i];
+        if (P.w[i] != 1.0) t *= P.w[i];                 // a product by 1 is exact: skip it
         double v;
         if (P.mon[i] != 0) v = side > 0 ? (t > 0 ? t : 0.0) : (t < 0 ? -t : 0.0);
         else v = fabs(t);
@@ -495,7 +515,7 @@ __device__ __forceinline__ void merge_one(const MergeParams& P, int64_t qi) {
     }
     const T* q = static_cast<const T*>(P.Q) + qi * P.d;
     bool finite = true;
-    for (int i = 0; i < P.d; ++i) finite = finite && isfinite((double)q[i]);
+    for (int i = 0; i < P.d; ++i) finite = finite && isfinite(q[i]);
     double hi, lo;
     if (!finite || iu < 0 || il < 0) {
         hi = lo = __longlong_as_double(0x7ff8000000000000ll);
@@ -503,8 +523,8 @@ __device__ __forceinline__ void merge_one(const MergeParams& P, int64_t qi) {
     } else {
         const T* X0 = static_cast<const T*>(P.X0);
         const T* y0 = static_cast<const T*>(P.y0);
-        hi = (double)y0[iu] + P.M * dist_fp64<T>(P, q, X0 + (int64_t)iu * P.d, +1);
-        lo = (double)y0[il] - P.M * dist_fp64<T>(P, q, X0 + (int64_t)il * P.d, -1);
+        hi = to_f64(y0[iu]) + P.M * dist_fp64<T>(P, q, X0 + (int64_t)iu * P.d, +1);
+        lo = to_f64(y0[il]) - P.M * dist_fp64<T>(P, q, X0 + (int64_t)il * P.d, -1);
     }
     if (P.g) static_cast<T*>(P.g)[qi] = (T)(0.5 * (hi + lo));
     if (P.lo) static_cast<T*>(P.lo)[qi] = (T)lo;

@@ -23,6 +23,8 @@ import os
 import statistics
 from typing import Dict, Iterable, Optional
 
+import numpy as np
+
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning", "b300_cache.json")
 
 
@@ -30,12 +32,15 @@ def _bucket(n: int) -> int:
     return int(math.floor(math.log2(max(1, n))))
 
 
-PRUNED_DMAX = 8        # the pruned scan's instantiations (FP32, d <= 8)
+PRUNED_DMAX = 8        # the pruned scan's instantiations (FP32, d <= 8, and unconstrained
+PRUNED_UMAX = 16       # shapes up to d = 16)
 
 
 def pruned_capable(model) -> bool:
+    """FP32 handles whose shape has a pruned instantiation: d <= 8, or unconstrained up to 16."""
     from .lipfit import LIP_FP32
-    return model.precision == LIP_FP32 and model.d <= PRUNED_DMAX
+    c = 0 if model.mon is None else int((np.asarray(model.mon) != 0).sum())
+    return model.precision == LIP_FP32 and (model.d <= PRUNED_DMAX or (c == 0 and model.d <= PRUNED_UMAX))
 
 
 def eval_key(model, nq: int) -> str:

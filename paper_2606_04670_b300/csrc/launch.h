@@ -199,8 +199,10 @@ constexpr int PRUNED_DMAX = 8;
 // The pruned scan's chunks: 16 points (4 groups), 16 of them to a 64-group super-chunk.
 constexpr int PRUNED_CG = 4;
 constexpr int PRUNED_CPS = 64 / PRUNED_CG;
+// Unconstrained shapes (C = 0) have a pruned instantiation up to this many coordinates.
+constexpr int PRUNED_UMAX = 16;
 __host__ __device__ constexpr bool pruned_shape_available(int C, int U) {
-    return C + U >= 1 && C + U <= PRUNED_DMAX;
+    return C + U >= 1 && (C + U <= PRUNED_DMAX || (C == 0 && U <= PRUNED_UMAX));
 }
 using PrunedLaunchFn = cudaError_t (*)(const PrunedParams&, int gx, cudaStream_t);
 struct PrunedKernelInfo {

@@ -25,7 +25,7 @@ cudaError_t launch_scan_pruned(const PrunedParams& P, int gx, cudaStream_t st) {
 
 template <int NORM>
 struct PrunedTable {
-    PrunedKernelInfo tab[PRUNED_DMAX + 1][PRUNED_DMAX + 1][2];
+    PrunedKernelInfo tab[PRUNED_DMAX + 1][PRUNED_UMAX + 1][2];
     template <int C, int U, int V>
     void fill_variant() {
         constexpr int R = pruned_rows(C + U, V);
@@ -37,7 +37,7 @@ struct PrunedTable {
     }
     template <int K>
     void fill_one() {
-        constexpr int C = K / (PRUNED_DMAX + 1), U = K % (PRUNED_DMAX + 1);
+        constexpr int C = K / (PRUNED_UMAX + 1), U = K % (PRUNED_UMAX + 1);
         if constexpr (pruned_shape_available(C, U)) {
             fill_variant<C, U, 6>();
             fill_variant<C, U, 7>();
@@ -45,7 +45,7 @@ struct PrunedTable {
     }
     template <int... K>
     void fill(std::integer_sequence<int, K...>) { (fill_one<K>(), ...); }
-    PrunedTable() { fill(std::make_integer_sequence<int, (PRUNED_DMAX + 1) * (PRUNED_DMAX + 1)>{}); }
+    PrunedTable() { fill(std::make_integer_sequence<int, (PRUNED_DMAX + 1) * (PRUNED_UMAX + 1)>{}); }
 };
 
 }  // namespace lip

@@ -4,7 +4,7 @@
 namespace lip {
 PrunedKernelInfo scan_pruned_info_linf(int C, int U, int v) {
     static PrunedTable<LIP_LINF> t;
-    if (C < 0 || U < 0 || C > PRUNED_DMAX || U > PRUNED_DMAX || (v != 6 && v != 7)) return {};
+    if (C < 0 || U < 0 || C > PRUNED_DMAX || U > PRUNED_UMAX || (v != 6 && v != 7)) return {};
     return t.tab[C][U][v - 6];
 }
 }  // namespace lip

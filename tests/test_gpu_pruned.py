@@ -16,7 +16,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-SHAPES = [(1, 0), (1, 1), (2, 0), (2, 2), (3, 1), (4, 2), (4, 4), (5, 3), (6, 0), (7, 2), (8, 3), (8, 8)]
+SHAPES = [(1, 0), (1, 1), (2, 0), (2, 2), (3, 1), (4, 2), (4, 4), (5, 3), (6, 0), (7, 2), (8, 3), (8, 8), (9, 0),
+          (12, 0), (16, 0)]
 
 
 @pytest.mark.parametrize("norm", (1, 2, 3))
@@ -161,8 +162,9 @@ def test_pruned_autotune_and_tuning_report():
     assert m.last_scan_stats() == [-1, -1, -1, -1, -1]
     assert L.lip_set_tuning(m.h, 0, 0, 8) == L.LIP_ERR_ARG
     m.close()
-    # d = 9 has no pruned instantiation: 6 / 7 run as 0 / 1
-    p = W.random_problem(2401, 1_000, 9, 300, norm=W.NORM_L1)
+    # d = 17 has no pruned instantiation (nor has d = 9..16 with constrained coordinates):
+    # 6 / 7 run as 0 / 1
+    p = W.random_problem(2401, 1_000, 17, 300, norm=W.NORM_L1)
     m = L.LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm)
     m.set_tuning(0, 0, 6)
     m.eval(torch.as_tensor(p.Q).cuda())

@@ -693,10 +693,14 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
 
 
 TC_FORMS = ("fp32", "tc_tf32", "tc_bf16", "tc_fp16")
+# the comparison's forms: the plain FP32 scan (default launch), the pruned FP32 scan
+# (variant 7) and the three tensor-core forms
+CMP_FORMS = ("fp32", "fp32_pruned", "tc_tf32", "tc_bf16", "tc_fp16")
 
 
 def tc_vs_plain(ctx, n_oracle=192, reps=3):
-    """The tensor-core L2 forms against the plain FP32 scan on the precision workload at full
+    """The tensor-core L2 forms against the plain FP32 scan (its default launch and the pruned
+    scan) on the precision workload at full
     size (cluster_d16: d = 16, N = Q = 1e6, 32-cluster Gaussian mixture), measured in this
     process: per form the whole lip_eval call and its scan kernel alone (CUDA events, best of
     `reps` after a warm-up), the queries the tensor-core form sent to the plain fallback, and
@@ -718,8 +722,10 @@ def tc_vs_plain(ctx, n_oracle=192, reps=3):
     sampler.start()
     forms = {}
     outs = {}
-    for prec in TC_FORMS:
-        m = L.LipFit(X, y, p.M, norm=p.norm, precision=prec)
+    for prec in CMP_FORMS:
+        m = L.LipFit(X, y, p.M, norm=p.norm, precision="fp32" if prec == "fp32_pruned" else prec)
+        if prec == "fp32_pruned":
+            m.set_tuning(0, 0, 7)
         ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         r = m.eval(Q)                      # warm-up (tensor-core tiles built here)
@@ -749,7 +755,7 @@ def tc_vs_plain(ctx, n_oracle=192, reps=3):
     t0 = time.perf_counter()
     ref = o.evaluate(p.X, p.y, p.Q[sample], p.M, p.norm)
     dt = time.perf_counter() - t0
-    for prec in TC_FORMS:
+    for prec in CMP_FORMS:
         g = outs[prec]
         err = {k: float(np.max(np.abs(g[k].astype(np.float64) - ref[k]))) for k in ("g", "lo", "hi")}
         mism = 0

@@ -68,6 +68,7 @@ KERNEL_DRAM_BYTES = {
     ("monotone_d4", 3, "pruned"): 24.953e6 + 2.098e6,  # scan_pruned_kernel<Linf, C=2, U=2, R=4>
     ("grad_d8", 2): 16.66e6 + 13.47e6,                 # scan_exact_kernel<L2, C=4, U=4, R=2>
     ("cluster_d16", 2): 618.02e6 + 185.20e6,           # scan_exact_kernel<L2, C=0, U=16, R=2>
+    ("cluster_d16", 2, "pruned"): 659.572e6 + 34.959e6,  # scan_pruned_kernel<L2, C=0, U=16, R=1>
     ("cluster_d16_tc", 2): 7185.37e6 + 1213.84e6,      # tc_scan_kernel<K=16, 4 parts, TF32> (persistent, soft lockstep)
     ("cluster_d16_bf16", 2): 5275.18e6 + 1081.80e6,    # tc_scan_kernel<K=16, 4 parts, BF16> (persistent, soft lockstep)
     ("cluster_d16_fp16", 2): 3413.92e6 + 943.47e6,     # tc_scan_kernel<K=16, 4 parts, FP16> (persistent, soft lockstep)

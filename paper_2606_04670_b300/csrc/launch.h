@@ -186,7 +186,7 @@ struct PrunedParams {
     const int* qperm;             // [nq] query position -> query index (spatial order)
     const int* dperm;             // [N] data position -> data index
     const float4* box;            // [nchunks][pruned_box_f4(D)] chunk records
-    const float4* sbox;           // [nchunks / 8][pruned_box_f4(D)]: records of 8 chunks (64 groups)
+    const float4* sbox;           // [nchunks / PRUNED_CPS][pruned_box_f4(D)]: records of 64 groups
     int64_t nchunks;
     unsigned long long* work;     // nullable: [0] evaluated (row, chunk) pairs, [1] tiles copied,
                                   // [2] (warp, chunk) pairs passing the warp-box test, per launch

@@ -170,3 +170,29 @@ def test_pruned_autotune_and_tuning_report():
     m.eval(torch.as_tensor(p.Q).cuda())
     assert m.last_scan_work() == (-1, -1)
     m.close()
+
+
+@pytest.mark.parametrize("case", ("cluster_d16", "monotone_d5_L1"))
+def test_pruned_cyclic_order(oracle_mod, case):
+    """More than 1,024 super-chunks (N > 262,144 data): the sweep runs in cyclic order from
+    the block's start chunk instead of sorting the super-chunks.  The clustered d = 16 workload at full size (N = Q = 1e6, as the benchmark
+    runs it) on 400 sampled queries, and a monotone, weighted d = 5 problem under L1 on all
+    of its queries, against the FP64 oracle."""
+    from paper_2606_04670_b300.lipfit import LipFit
+    if case == "cluster_d16":
+        p = W.cluster_d16()
+        idx = np.sort(np.random.default_rng(23).choice(p.nq, 400, replace=False))
+    else:
+        p = W.random_problem(2402, 300_000, 5, 3_000, norm=W.NORM_L1, masked=True, weighted=True, decreasing=True)
+        idx = np.arange(p.nq)
+    m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), p.M, norm=p.norm, mon=p.mon, w=p.w)
+    m.set_tuning(0, 0, 6)
+    r = {k: v.cpu().numpy() for k, v in m.eval(torch.as_tensor(p.Q).cuda()).items()}
+    ev, tot = m.last_scan_work()
+    m.check()
+    m.close()
+    assert 0 < ev < 0.5 * tot, (ev, tot)
+    assert np.all(r["lo"] <= r["g"]) and np.all(r["g"] <= r["hi"])
+    ps = W.Problem("s", p.X, p.y, p.Q[idx], p.M, p.norm, p.mon, p.w)
+    orc = oracle_mod.evaluate(p.X, p.y, ps.Q, p.M, p.norm, mon=p.mon, w=p.w)
+    compare(ps, {k: v[idx] for k, v in r.items()}, orc, FP32_TOL, case)

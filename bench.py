@@ -162,6 +162,8 @@ def parse():
                     help="tensor-core handles: lip_set_tuning variant (0-5; -1 keeps the default 0)")
     ap.add_argument("--tc-window-mb", type=int, default=0,
                     help="tensor-core handles: lockstep window in MB (lip_set_tc_window; 0 = default)")
+    ap.add_argument("--serial-problems", action="store_true",
+                    help="run a step's problems one after another on one stream (default: one stream each)")
     ap.add_argument("--no-tc-vs-plain", action="store_true",
                     help="monotone_d4: skip the tensor-core vs plain comparison on cluster_d16 (after the timed steps)")
     ap.add_argument("--sets", type=int, default=0, help="batch_4096: use only the first N sets (profiling)")
@@ -520,35 +522,66 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
             tuning[f"{NNAME[r['p'].norm]}/{r['prec']}"] = AT.tune_eval(r["m"], r["Q"], cache=cache)
         save()
     est = {}
+    # One stream per problem on one GPU: the problems of a step are independent, so their
+    # kernels run side by side (one scan's last wave overlaps the next problem's start, and
+    # the small latency-bound kernels overlap the others' scans); the estimates are queued
+    # with lip_estimate_M_async and read once everything is queued.
+    side = [torch.cuda.Stream() for _ in runs] if len(runs) > 1 and ctx.world == 1 and not args.serial_problems \
+        else None
 
-    def step(record=False):
+    def step(record=False, serial=False):
+        main = torch.cuda.current_stream()
+        streams = None if serial else side
         for k, r in enumerate(runs):
-            m = r["m"]
-            m.clear()
-            m.add_async(r["X"], r["y"])       # the finiteness check reported by check() below
-            out = m.eval(r["Q"], need=("g", "lo", "hi", "idx_up", "idx_lo"))
-            if record:
-                torch.cuda.synchronize()
-                r["scan"].append(r["ev"][0].elapsed_time(r["ev"][1]))
-            if with_bwd:
-                r["bev"][0].record()
-                m.backward(r["Q"], out["idx_up"], out["idx_lo"], r["gb"])
-                r["bev"][1].record()
-                if record:
-                    torch.cuda.synchronize()
-                    r["bwd"].append(r["bev"][0].elapsed_time(r["bev"][1]))
-            if with_est:
-                if ctx.world > 1:
-                    # the pair triangle shared out over the GPUs, one all_gather per norm
-                    est[k] = S.estimate_M_sharded(S.DeviceShard(m, 0), device="cuda")[0]
-                else:
-                    est[k] = m.lipschitz_constant()[0]
+            s = streams[k] if streams else main
+            if streams:
+                s.wait_stream(main)
+            with torch.cuda.stream(s):
+                m = r["m"]
+                m.clear()
+                m.add_async(r["X"], r["y"])       # the finiteness check reported by check() below
+                out = m.eval(r["Q"], need=("g", "lo", "hi", "idx_up", "idx_lo"))
+                if with_bwd:
+                    r["bev"][0].record()
+                    m.backward(r["Q"], out["idx_up"], out["idx_lo"], r["gb"])
+                    r["bev"][1].record()
+                if with_est:
+                    if ctx.world > 1:
+                        # the pair triangle shared out over the GPUs, one all_gather per norm
+                        est[k] = S.estimate_M_sharded(S.DeviceShard(m, 0), device="cuda")[0]
+                    else:
+                        m.lipschitz_constant_async()
+        if with_est and ctx.world == 1:
+            for k, r in enumerate(runs):
+                est[k] = r["m"].lipschitz_constant_result()[0]
+        if streams:
+            for s in streams:
+                main.wait_stream(s)
         for r in runs:
             r["m"].check()
+        if record:
+            torch.cuda.synchronize()
+            for r in runs:
+                r["scan"].append(r["ev"][0].elapsed_time(r["ev"][1]))
+                if with_bwd:
+                    r["bwd"].append(r["bev"][0].elapsed_time(r["bev"][1]))
 
     for _ in range(max(3, args.warmup)):
         step()
     ms, clocks, launches = ctx.timed(lambda: step(True), args.steps, flush=flush)
+    concurrent_scan_ms = {}
+    if side:
+        # The scans' own durations for the roofline come from steps with the problems one
+        # after another on one stream (the same kernels, nothing beside them); those of
+        # the timed steps, shared with the other problems' kernels, are reported as well.
+        concurrent_scan_ms = {f"{NNAME[r['p'].norm]}/{r['prec']}": statistics.mean(r["scan"]) for r in runs}
+        for r in runs:
+            r["scan"].clear()
+            r["bwd"].clear()
+        for _ in range(max(3, min(args.steps, 5))):
+            if flush:
+                ctx.flush()
+            step(True, serial=True)
     pairs_step = sum(r["p"].nq * r["p"].N for r in runs)
     value, total = aggregate(pairs_step * args.steps, sum(ms), device="cuda")
     # dominant kernel: the scan with the largest average time
@@ -597,20 +630,31 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
             r["m"].set_timing_events(None, None)
 
         def step_host():
-            # every problem's fit and evaluation queued first (lip_eval_host_async: the
-            # copies of one overlap the kernels of another), then the estimates, then
-            # lip_check, which also waits for the host-path copies
-            for r, hX, hy, hQ, outs in hostruns:
-                m = r["m"]
-                m.clear()
-                m.add_host_async(hX, hy)
-                m.eval_host(hQ, outs, wait=False)
+            # every problem's fit, evaluation and estimate queued first, each on its own
+            # stream as in the device step (lip_eval_host_async: the copies of one overlap
+            # the kernels of another), then the estimates' results, then lip_check, which
+            # also waits for the host-path copies
+            main = torch.cuda.current_stream()
+            for k, (r, hX, hy, hQ, outs) in enumerate(hostruns):
+                s = side[k] if side else main
+                if side:
+                    s.wait_stream(main)
+                with torch.cuda.stream(s):
+                    m = r["m"]
+                    m.clear()
+                    m.add_host_async(hX, hy)
+                    m.eval_host(hQ, outs, wait=False)
+                    if with_est and ctx.world == 1:
+                        m.lipschitz_constant_async()
             if with_est:
                 for r, *_ in hostruns:
                     if ctx.world > 1:
                         S.estimate_M_sharded(S.DeviceShard(r["m"], 0), device="cuda")
                     else:
-                        r["m"].lipschitz_constant()
+                        r["m"].lipschitz_constant_result()
+            if side:
+                for s in side:
+                    main.wait_stream(s)
             for r, *_ in hostruns:
                 r["m"].check()
 
@@ -639,6 +683,8 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
     tun = rd["m"].tuning()
     key = lambda r: f"{NNAME[r['p'].norm]}/{r['prec']}"  # noqa: E731
     detail = {"scan_ms": {key(r): statistics.mean(r["scan"]) for r in runs},
+              "problems_concurrent": bool(side),
+              "scan_ms_concurrent": concurrent_scan_ms,
               "scan_gpairs_per_s": {key(r): r["p"].nq * r["p"].N / (statistics.mean(r["scan"]) / 1e3) / 1e9
                                     for r in runs},
               "splits": tun["last_splits"], "tile_groups": tun["tile_groups"],
@@ -687,7 +733,8 @@ def wl_single(ctx, name, problems, precisions=("fp32",), with_est=True, with_bwd
     config = {"workload": name, "d": p0.d, "N": p0.N, "Q": p0.nq,
               "mon": None if p0.mon is None else [int(v) for v in p0.mon],
               "norms": [NNAME[p.norm] for p in problems], "precisions": list(precisions),
-              "step": "per problem: fit + eval" + (" + M_est" if with_est else "") + (" + backward" if with_bwd else ""),
+              "step": "per problem: fit + eval" + (" + M_est" if with_est else "") + (" + backward" if with_bwd else "")
+                      + ("; the problems side by side, one stream each" if side else ""),
               "l2": "flushed before every timed step (256 MB write)" if flush else "inputs larger than L2"}
     return ctx.line(value, total, args.steps, "f64" if precisions == ("fp64",) else "f32", config, roof, cpu, e2e,
                     clocks, launches, detail)

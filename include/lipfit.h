@@ -229,6 +229,20 @@ LIP_API lip_status lip_eval_host_async(lip_handle h, const void* Q, int64_t nq, 
 LIP_API lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, int64_t* j_out,
                           void* stream);
 
+/* lip_estimate_M without the wait: queues the same computation on `stream` (the result's
+ * 48 bytes are copied to pinned memory the handle owns) and returns; lip_estimate_M_result
+ * waits for that copy and gives the result, the same as lip_estimate_M's bit for bit.  So
+ * the estimates of several handles, each on its own stream, run side by side.  One estimate
+ * per handle is outstanding: a second call (or lip_estimate_M) first waits for the copy of
+ * the first and drops its result.  The data must stay unchanged until the result is read.
+ * LIP_ERR_ARG for a NULL handle, LIP_ERR_OOM when the 64 pinned bytes cannot be had. */
+LIP_API lip_status lip_estimate_M_async(lip_handle h, void* stream);
+
+/* The result of the estimate lip_estimate_M_async queued on h (outputs as lip_estimate_M),
+ * after waiting for it; lip_last_estimate_work then reports its work.  LIP_ERR_STATE when
+ * none is outstanding (never queued, or already read), LIP_ERR_ARG for NULL pointers. */
+LIP_API lip_status lip_estimate_M_result(lip_handle h, double* M_out, int64_t* i_out, int64_t* j_out);
+
 /* Form of lip_estimate_M on this handle.  0 (the default): FP32 handles with d <= 8 and
  * N >= 32768 take the pruned form (below that the full screen is cheaper than the pruned
  * form's setup); 2: the pruned form wherever available (FP32, d <= 8); 1: always the full

@@ -148,6 +148,11 @@ void free_model(lip_model* h) {
         if (h->ev_out[b]) cudaEventDestroy(h->ev_out[b]);
     }
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->est_done) {
+        if (h->est_pending == 1) cudaEventSynchronize(h->est_done);   // the result's copy
+        cudaEventDestroy(h->est_done);
+    }
+    if (h->est_back) cudaFreeHost(h->est_back);
     delete h;
 }
 
@@ -704,7 +709,7 @@ lip_status eval_screen64(lip_model* h, const void* Q, int64_t nq, void* g, void*
 // layout in spatial order with chunk and tile records, then the three pruned passes (the
 // FP32 maximum, the FP64 maximum over the pairs near it, the lowest pair attaining it);
 // the FP64 definition's result exactly.
-lip_status estimate_pruned(lip_model* h, double* res, cudaStream_t st) {
+lip_status estimate_pruned(lip_model* h, double* res, cudaStream_t st, bool wait) {
     const int tile = estimate_tile_points();
     const int64_t N = h->N, nb = ceil_div(N, tile), pts = nb * tile, nchunks = pts / 16;   // 16-point chunks
     const int64_t npairs = nb * (nb + 1) / 2;
@@ -793,6 +798,14 @@ lip_status estimate_pruned(lip_model* h, double* res, cudaStream_t st) {
     CUDA_TRY(launch_estimate_pruned_select(P, F, st));
     CUDA_TRY(launch_estimate_exact(F, st));
     count_launches(6 + ESTIMATE_EXACT_LAUNCHES + (reuse ? 0 : spatial_order_launches()));
+    const int64_t total = npairs * (tile / 32) * (tile / 16);    // 32-point rows x 16-point chunks
+    if (!wait) {                                                  // lip_estimate_M_async
+        CUDA_TRY(cudaMemcpyAsync(h->est_back, out, 48, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaEventRecord(h->est_done, st));
+        h->est_pending = 1;
+        h->est_pending_total = total;
+        return LIP_OK;
+    }
     // the result (4 doubles) and the work counters in one read
     unsigned char back[48];
     CUDA_TRY(cudaMemcpyAsync(back, out, sizeof back, cudaMemcpyDeviceToHost, st));
@@ -802,11 +815,14 @@ lip_status estimate_pruned(lip_model* h, double* res, cudaStream_t st) {
     memcpy(wk, back + 32, sizeof wk);
     h->est_work[0] = (int64_t)wk[0];
     h->est_work[1] = (int64_t)wk[1];
-    h->est_work[2] = npairs * (tile / 32) * (tile / 16);    // 32-point rows x 16-point chunks
+    h->est_work[2] = total;
     return LIP_OK;
 }
 
-lip_status estimate_part(lip_model* h, int part, int nparts, double* res, cudaStream_t st) {
+// With wait = false (lip_estimate_M_async, part 0 of 1) the result is left to
+// estimate_collect: est_pending becomes 1 when device work was queued, and stays 0 when
+// res already holds the result (fewer than two points).
+lip_status estimate_part(lip_model* h, int part, int nparts, double* res, cudaStream_t st, bool wait) {
     DeviceGuard gd(h->device);
     for (int k = 0; k < 3; ++k) h->est_work[k] = -1;
     res[0] = 0.0;
@@ -820,7 +836,7 @@ lip_status estimate_part(lip_model* h, int part, int nparts, double* res, cudaSt
     // pruned form's spatial order and records (a dozen launches) cost more than they save.
     const bool pruned = h->est_form == 2 || (h->est_form == 0 && h->N >= 32768);
     if (nparts == 1 && h->esize == 4 && estimate_pruned_available(h->d) && pruned)
-        return estimate_pruned(h, res, st);
+        return estimate_pruned(h, res, st, wait);
     const int64_t pts = nb * tile;
     const int nch = h->d + 1;
     const size_t lay_b = round_up(pts * nch * 4, 256), cand_b = round_up(nb * nb * 16, 256),
@@ -877,8 +893,39 @@ lip_status estimate_part(lip_model* h, int part, int nparts, double* res, cudaSt
     F.list = reinterpret_cast<unsigned*>(base + lay_b + cand_b + 256);
     CUDA_TRY(launch_estimate_final(F, st));
     count_launches(3 + ESTIMATE_FINAL_LAUNCHES);
+    if (!wait) {
+        CUDA_TRY(cudaMemcpyAsync(h->est_back, F.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaEventRecord(h->est_done, st));
+        h->est_pending = 1;
+        h->est_pending_total = -1;
+        return LIP_OK;
+    }
     CUDA_TRY(cudaMemcpyAsync(res, F.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    return LIP_OK;
+}
+
+// The result of the estimate lip_estimate_M_async queued: waits for its copy.
+lip_status estimate_collect(lip_model* h, double* res) {
+    if (h->est_pending == 0) return fail(LIP_ERR_STATE, "no estimate queued on this handle");
+    if (h->est_pending == 2) {
+        memcpy(res, h->est_host_res, 4 * sizeof(double));
+    } else {
+        const cudaError_t e = cudaEventSynchronize(h->est_done);
+        if (e != cudaSuccess) {
+            h->est_pending = 0;
+            return cuda_fail(e, "cudaEventSynchronize (estimate)");
+        }
+        memcpy(res, h->est_back, 4 * sizeof(double));
+        if (h->est_pending_total >= 0) {
+            unsigned long long wk[2];
+            memcpy(wk, h->est_back + 32, sizeof wk);
+            h->est_work[0] = (int64_t)wk[0];
+            h->est_work[1] = (int64_t)wk[1];
+            h->est_work[2] = h->est_pending_total;
+        }
+    }
+    h->est_pending = 0;
     return LIP_OK;
 }
 
@@ -1139,7 +1186,43 @@ lip_status lip_estimate_M(lip_handle h, double* M_out, int64_t* i_out, int64_t* 
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
     if (!M_out || !i_out || !j_out) return fail(LIP_ERR_ARG, "an output pointer is NULL");
     double res[4];
-    LIP_TRY(estimate_part(h, 0, 1, res, static_cast<cudaStream_t>(stream)));
+    h->est_pending = 0;                  // a queued estimate's result is dropped
+    LIP_TRY(estimate_part(h, 0, 1, res, static_cast<cudaStream_t>(stream), true));
+    *M_out = res[0];
+    *i_out = (int64_t)res[1];
+    *j_out = (int64_t)res[2];
+    return LIP_OK;
+}
+
+lip_status lip_estimate_M_async(lip_handle h, void* stream) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    DeviceGuard gd(h->device);
+    if (h->est_pending == 1) CUDA_TRY(cudaEventSynchronize(h->est_done));   // est_back is reused
+    h->est_pending = 0;
+    if (!h->est_back) {
+        void* p = nullptr;
+        if (cudaMallocHost(&p, 64) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LIP_ERR_OOM, "pinned estimate result (64 bytes)");
+        }
+        h->est_back = static_cast<unsigned char*>(p);
+    }
+    if (!h->est_done) CUDA_TRY(cudaEventCreateWithFlags(&h->est_done, cudaEventDisableTiming));
+    double res[4];
+    LIP_TRY(estimate_part(h, 0, 1, res, static_cast<cudaStream_t>(stream), false));
+    if (h->est_pending == 0) {           // known on the host (fewer than two points)
+        memcpy(h->est_host_res, res, sizeof res);
+        h->est_pending = 2;
+    }
+    return LIP_OK;
+}
+
+lip_status lip_estimate_M_result(lip_handle h, double* M_out, int64_t* i_out, int64_t* j_out) {
+    if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
+    if (!M_out || !i_out || !j_out) return fail(LIP_ERR_ARG, "an output pointer is NULL");
+    DeviceGuard gd(h->device);
+    double res[4];
+    LIP_TRY(estimate_collect(h, res));
     *M_out = res[0];
     *i_out = (int64_t)res[1];
     *j_out = (int64_t)res[2];
@@ -1150,7 +1233,7 @@ lip_status lip_estimate_M_part(lip_handle h, int32_t part, int32_t nparts, doubl
     if (!h) return fail(LIP_ERR_ARG, "handle is NULL");
     if (!out) return fail(LIP_ERR_ARG, "out is NULL");
     if (nparts < 1 || part < 0 || part >= nparts) return fail(LIP_ERR_ARG, "part %d of %d is not valid", part, nparts);
-    return estimate_part(h, part, nparts, out, static_cast<cudaStream_t>(stream));
+    return estimate_part(h, part, nparts, out, static_cast<cudaStream_t>(stream), true);
 }
 
 lip_status lip_shard_scan(lip_handle h, const void* Q, int64_t nq, int64_t index_base, int64_t* key_up,

@@ -138,6 +138,13 @@ struct lip_model {
     int64_t sp_tiles = -1;              // its blocks x data tiles
     int est_form = 0;                   // lip_estimate_M: 0 pruned from N = 32768, 1 always full, 2 pruned where available
     int64_t est_work[3] = {-1, -1, -1};   // lip_last_estimate_work
+    // lip_estimate_M_async: the result (4 doubles) and the pruned form's work counters are
+    // copied to est_back (pinned) and est_done is recorded after the copy
+    unsigned char* est_back = nullptr;  // 64 bytes
+    cudaEvent_t est_done = nullptr;
+    int est_pending = 0;                // 0 none, 1 queued on the device, 2 known on the host
+    double est_host_res[4] = {0, -1, -1, -1};   // the result when est_pending == 2
+    int64_t est_pending_total = -1;     // est_work[2] of the queued estimate (-1: full form)
     int* tc_fb_count = nullptr;         // device count of the last tensor-core lip_eval's fallback
     // local Lipschitz constants (Sec. 4.3), valid until the data change
     bool loc_valid = false;

@@ -110,6 +110,8 @@ def _load():
         "lip_shard_reeval": [H, P, i64, i64, P, P, P, P, P],
         "lip_shard_finish": [H, i64, P, P, P, P, P, P, P, P, P, P],
         "lip_estimate_M_part": [H, i32, i32, P, P],
+        "lip_estimate_M_async": [H, P],
+        "lip_estimate_M_result": [H, ctypes.POINTER(f64), ctypes.POINTER(i64), ctypes.POINTER(i64)],
         "lip_set_tc_window": [H, i64],
         "lip_set_estimate_full": [H, i32],
         "lip_last_scan_work": [H, ctypes.POINTER(i64), ctypes.POINTER(i64)],
@@ -301,6 +303,16 @@ def lip_eval_host_async(h, Q_ptr, nq, g, lo, hi, idx_up, idx_lo, stream=0):
 def lip_estimate_M(h, stream=0):
     M, i, j = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
     s = _lib.lip_estimate_M(h, ctypes.byref(M), ctypes.byref(i), ctypes.byref(j), stream)
+    return s, M.value, i.value, j.value
+
+
+def lip_estimate_M_async(h, stream=0):
+    return _lib.lip_estimate_M_async(h, stream)
+
+
+def lip_estimate_M_result(h):
+    M, i, j = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+    s = _lib.lip_estimate_M_result(h, ctypes.byref(M), ctypes.byref(i), ctypes.byref(j))
     return s, M.value, i.value, j.value
 
 
@@ -737,6 +749,18 @@ class LipFit:
         its lowest pair exactly; synchronises."""
         s, M, i, j = lip_estimate_M(self.h, _stream_ptr())
         _check(s, "lip_estimate_M")
+        return M, i, j
+
+    def lipschitz_constant_async(self):
+        """Queue lipschitz_constant() on the current stream without waiting; the result is
+        read by lipschitz_constant_result()."""
+        _check(lip_estimate_M_async(self.h, _stream_ptr()), "lip_estimate_M_async")
+
+    def lipschitz_constant_result(self):
+        """(M_est, i, j) of the estimate lipschitz_constant_async() queued, after waiting
+        for it."""
+        s, M, i, j = lip_estimate_M_result(self.h)
+        _check(s, "lip_estimate_M_result")
         return M, i, j
 
     def backward(self, Q, idx_up, idx_lo, grad_g, need_Q=True, need_y=True, need_M=True, deterministic=False):

@@ -71,6 +71,8 @@ def test_null_handle_calls():
     assert L.lip_clear(None) == L.LIP_ERR_ARG
     assert L.lip_set_M(None, 1.0) == L.LIP_ERR_ARG
     assert L.lip_estimate_M(None)[0] == L.LIP_ERR_ARG
+    assert L.lip_estimate_M_async(None) == L.LIP_ERR_ARG
+    assert L.lip_estimate_M_result(None)[0] == L.LIP_ERR_ARG
     assert L.lip_backward(None, None, 0, None, None, None, None, None, None) == L.LIP_ERR_ARG
     assert L.lip_backward(None, None, 0, None, None, None, None, None, None, 1) == L.LIP_ERR_ARG
     assert L.lip_eval_batched(None) == L.LIP_ERR_ARG

@@ -109,3 +109,39 @@ def test_estimate_benchmark_size(norm):
     assert a == b, (a, b)
     assert 0 <= a[1] < a[2] < p.N
     assert abs(_ratio64(p.X, p.y, a[1], a[2], norm) - a[0]) <= 1e-15 * a[0]
+
+
+def test_estimate_async_on_several_streams(oracle_mod):
+    """lip_estimate_M_async on three handles, each on its own stream, all queued before
+    the first result is read: each result equals lip_estimate_M's and the oracle's, in
+    both forms, and reading a result twice is an error."""
+    from paper_2606_04670_b300 import lipfit as L
+    from paper_2606_04670_b300.lipfit import LipFit
+    probs = [W.random_problem(3100 + k, 40_000 + 1_111 * k, 4, 1, norm=k + 1, weighted=(k == 1)) for k in range(3)]
+    probs.append(W.random_problem(3104, 1, 3, 1))                   # one point: known on the host
+    for form in ("pruned", "full"):
+        ms, streams = [], []
+        for p in probs:
+            m = LipFit(torch.as_tensor(p.X).cuda(), torch.as_tensor(p.y).cuda(), 1.0, norm=p.norm, w=p.w)
+            m.set_estimate_form(form)
+            ms.append(m)
+            streams.append(torch.cuda.Stream())
+        torch.cuda.synchronize()
+        for m, s in zip(ms, streams):
+            with torch.cuda.stream(s):
+                m.lipschitz_constant_async()
+        got = []
+        for m, s in zip(ms, streams):
+            got.append(m.lipschitz_constant_result())
+            with torch.cuda.stream(s):
+                assert L.lip_estimate_M_result(m.h)[0] == L.LIP_ERR_STATE
+                if m.N > 1:
+                    work = m.last_estimate_work()
+                    assert (work[0] > 0) == (form == "pruned"), work
+                assert m.lipschitz_constant() == got[-1]
+                m.check()
+        for m in ms:
+            m.close()
+        for p, g in zip(probs[:3], got):
+            assert g == oracle_mod.estimate_M(p.X, p.y, p.norm, w=p.w), (form, g)
+        assert got[3][1] == -1 and got[3][0] == 0.0
